@@ -1,0 +1,269 @@
+"""FP64 CPU oracle for the antiplane-shear lattice Boltzmann method with
+dynamic mode III cracks (arXiv 2206.12412).
+
+TEST INFRASTRUCTURE ONLY: the test suite, the package smoke check and the
+benchmark's CPU-baseline leg are the only users.  The product path never
+imports this package.  The arithmetic lives in ``lbm_oracle.c`` (plain C,
+compiled here with gcc on first use); this module only marshals arguments.
+
+A problem is described by a plain dict (see ``make_config``): lattice size,
+spacing, edge kinds, material, boundary mode, crack and loads.  The same dict
+is understood by the CUDA library's Python binding; nothing else is shared.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lbm_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+QONE = 1 << 32  # tip fixed point: 1 dh = 2^32 units
+
+EDGE = {"free": 0, "dirichlet": 1, "periodic": 2}
+EDGE_INDEX = {"left": 0, "right": 1, "bottom": 2, "top": 3}
+BC = {"bounceback": 0, "macroscopic": 1}
+CRACK = {"none": 0, "stationary": 1, "prescribed": 2, "kcrit": 3}
+LOAD = {"zero": 0, "linear": 1, "sin2": 2, "halfsine": 3, "series": 4, "const": 5}
+FLAG_CLAMPED, FLAG_UNSUPPORTED, FLAG_NONFINITE = 1, 2, 4
+
+
+def build(force: bool = False) -> str:
+    """Compile lbm_oracle.c into liboracle.so next to it (gcc, -O2)."""
+    with _lock:
+        stale = (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)
+        if force or stale:
+            tmp = _LIB + f".{os.getpid()}.tmp"
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+            os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Config(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32),
+        ("dh", C.c_double), ("dt", C.c_double),
+        ("edge", C.c_int32 * 4),
+        ("rho", C.c_double), ("mu", C.c_double),
+        ("omega", C.c_double),
+        ("bc_mode", C.c_int32),
+        ("crack_mode", C.c_int32),
+        ("jc", C.c_int32),
+        ("x_start", C.c_double), ("x_tip", C.c_double),
+        ("v_rel", C.c_double), ("K_C", C.c_double), ("v_max", C.c_double),
+        ("r0", C.c_double), ("r_min_fixed", C.c_double), ("fit_width", C.c_double),
+        ("load_kind", C.c_int32 * 4),
+        ("load_amp", C.c_double * 4), ("load_t", C.c_double * 4),
+        ("load_series", C.POINTER(C.c_double) * 4),
+        ("load_n", C.c_int64 * 4),
+        ("hist_cap", C.c_int64),
+    ]
+
+
+class _CrackInfo(C.Structure):
+    _fields_ = [
+        ("step", C.c_int64), ("tip_q", C.c_int64), ("hist_n", C.c_int64),
+        ("K", C.c_double), ("v_prev", C.c_double),
+        ("npairs", C.c_int32), ("flags", C.c_int32), ("n_bpoints", C.c_int32), ("pad", C.c_int32),
+    ]
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = C.CDLL(build())
+        P = C.c_void_p
+        d = C.POINTER(C.c_double)
+        lib.orc_create.argtypes = [C.POINTER(_Config)]
+        lib.orc_create.restype = P
+        lib.orc_destroy.argtypes = [P]
+        lib.orc_set_fields.argtypes = [P, d, d]
+        lib.orc_get_fields.argtypes = [P, d, d]
+        lib.orc_get_distributions.argtypes = [P, d]
+        lib.orc_get_cuts.argtypes = [P, C.c_char_p, C.c_char_p]
+        lib.orc_step.argtypes = [P, C.c_int64]
+        lib.orc_get_crack.argtypes = [P, C.POINTER(_CrackInfo)]
+        lib.orc_get_history.argtypes = [P, d, d, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                        C.POINTER(C.c_int32), C.c_int64]
+        lib.orc_get_history.restype = C.c_int64
+        lib.orc_get_bpoints.argtypes = [P, C.POINTER(C.c_int32), C.c_int32]
+        lib.orc_get_bpoints.restype = C.c_int32
+        lib.orc_evaluate_K.argtypes = [P, d, C.c_int64, C.c_double, C.c_double, C.POINTER(C.c_int32)]
+        lib.orc_evaluate_K.restype = C.c_double
+        lib.orc_equilibrium.argtypes = [C.c_double, C.c_double, C.c_double, d]
+        lib.orc_macro_poly.argtypes = [C.c_double] * 5
+        lib.orc_macro_poly.restype = C.c_double
+        lib.orc_segments_intersect.argtypes = [C.c_int64] * 8
+        lib.orc_segments_intersect.restype = C.c_int
+        lib.orc_checklinks_standalone.argtypes = [
+            C.c_int32, C.c_int32, C.c_char_p, C.c_char_p, C.POINTER(C.c_int32), C.c_int32,
+            C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.POINTER(C.c_int32), C.c_int32]
+        lib.orc_checklinks_standalone.restype = C.c_int32
+        lib.orc_load_value.argtypes = [P, C.c_int32, C.c_int64]
+        lib.orc_load_value.restype = C.c_double
+        lib.orc_g.argtypes = [P]
+        lib.orc_g.restype = C.c_double
+        _lib = lib
+    return _lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def make_config(problem: dict):
+    """Translate a problem dict into the oracle's C struct.
+
+    Returns (struct, keepalive) -- keepalive holds the series arrays."""
+    cfg = _Config()
+    cfg.nx, cfg.ny = int(problem["nx"]), int(problem["ny"])
+    cfg.dh, cfg.dt = float(problem.get("dh", 1.0)), float(problem.get("dt", 1.0))
+    edges = problem.get("edges", ("free", "free", "dirichlet", "dirichlet"))
+    for e in range(4):
+        cfg.edge[e] = EDGE[edges[e]]
+    cfg.rho, cfg.mu = float(problem.get("rho", 1.0)), float(problem["mu"])
+    cfg.omega = float(problem.get("omega", 1.0))
+    cfg.bc_mode = BC[problem.get("bc_mode", "bounceback")]
+    cr = problem.get("crack") or {"mode": "none"}
+    cfg.crack_mode = CRACK[cr.get("mode", "none")]
+    if cfg.crack_mode:
+        jc = float(cr["y"]) / cfg.dh
+        cfg.jc = int(round(jc))
+        cfg.x_start, cfg.x_tip = float(cr.get("x_start", 0.0)), float(cr["x_tip"])
+        cfg.v_rel = float(cr.get("v_rel", 0.0))
+        cfg.K_C = float(cr.get("K_C", 0.0))
+        cfg.v_max = float(cr.get("v_max", 0.85))
+        cfg.r0 = float(cr.get("r0", 2.0 * cfg.dh))
+        cfg.r_min_fixed = float(cr.get("r_min", 0.0))
+        cfg.fit_width = float(cr.get("fit_width", cfg.dh))
+    keep = []
+    for ld in problem.get("loads", []):
+        e = EDGE_INDEX[ld["edge"]]
+        cfg.load_kind[e] = LOAD[ld["kind"]]
+        cfg.load_amp[e] = float(ld.get("amp", 0.0))
+        cfg.load_t[e] = float(ld.get("t", 0.0))
+        if ld["kind"] == "series":
+            arr = np.ascontiguousarray(ld["series"], dtype=np.float64)
+            keep.append(arr)
+            cfg.load_series[e] = _dptr(arr)
+            cfg.load_n[e] = arr.size
+    cfg.hist_cap = int(problem.get("hist_cap", 1 << 16))
+    return cfg, keep
+
+
+class Oracle:
+    """One lattice, stepped in FP64 in the paper's distribution form."""
+
+    def __init__(self, problem: dict):
+        self.lib = _load()
+        self.problem = problem
+        self.nx, self.ny = int(problem["nx"]), int(problem["ny"])
+        cfg, keep = make_config(problem)
+        self._cfg = cfg
+        self.h = self.lib.orc_create(C.byref(cfg))
+        if not self.h:
+            raise ValueError("oracle rejected the configuration")
+        del keep  # the library copies series at create
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.orc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def set_fields(self, w: np.ndarray, wdot: np.ndarray):
+        w = np.ascontiguousarray(w, dtype=np.float64).reshape(self.ny, self.nx)
+        wd = np.ascontiguousarray(wdot, dtype=np.float64).reshape(self.ny, self.nx)
+        self.lib.orc_set_fields(self.h, _dptr(w), _dptr(wd))
+
+    def fields(self):
+        w = np.empty((self.ny, self.nx))
+        wd = np.empty((self.ny, self.nx))
+        self.lib.orc_get_fields(self.h, _dptr(w), _dptr(wd))
+        return w, wd
+
+    def distributions(self):
+        f = np.empty((5, self.ny, self.nx))
+        self.lib.orc_get_distributions(self.h, _dptr(f))
+        return f
+
+    def step(self, n: int = 1):
+        self.lib.orc_step(self.h, int(n))
+
+    def cuts(self):
+        """(cut_h, cut_v) as (ny, nx) uint8: link (i,j)-(i+1,j) / (i,j)-(i,j+1) severed."""
+        ch = np.zeros((self.ny, self.nx), np.uint8)
+        cv = np.zeros((self.ny, self.nx), np.uint8)
+        self.lib.orc_get_cuts(self.h, ch.ctypes.data_as(C.c_char_p), cv.ctypes.data_as(C.c_char_p))
+        return ch, cv
+
+    def crack(self) -> dict:
+        info = _CrackInfo()
+        self.lib.orc_get_crack(self.h, C.byref(info))
+        return {k: getattr(info, k) for k, _ in _CrackInfo._fields_ if k != "pad"}
+
+    def history(self) -> dict:
+        cap = int(self.problem.get("hist_cap", 1 << 16))
+        K = np.zeros(cap); v = np.zeros(cap)
+        tip = np.zeros(cap, np.int64); npairs = np.zeros(cap, np.int32); grew = np.zeros(cap, np.int32)
+        n = self.lib.orc_get_history(self.h, _dptr(K), _dptr(v), tip.ctypes.data_as(C.POINTER(C.c_int64)),
+                                     npairs.ctypes.data_as(C.POINTER(C.c_int32)),
+                                     grew.ctypes.data_as(C.POINTER(C.c_int32)), cap)
+        return {"K": K[:n], "v": v[:n], "tip_q": tip[:n], "npairs": npairs[:n], "grew": grew[:n]}
+
+    def bpoints(self) -> np.ndarray:
+        cap = 4 * (self.nx + self.ny) + 64
+        out = np.zeros(cap, np.int32)
+        n = self.lib.orc_get_bpoints(self.h, out.ctypes.data_as(C.POINTER(C.c_int32)), cap)
+        return out[:n]
+
+    def evaluate_K(self, w: np.ndarray, tip_q: int, r_min: float, fit_width: float):
+        w = np.ascontiguousarray(w, dtype=np.float64).reshape(self.ny, self.nx)
+        npairs = C.c_int32(0)
+        K = self.lib.orc_evaluate_K(self.h, _dptr(w), int(tip_q), float(r_min), float(fit_width), C.byref(npairs))
+        return K, npairs.value
+
+    def load_value(self, edge: str, n: int) -> float:
+        return self.lib.orc_load_value(self.h, EDGE_INDEX[edge], int(n))
+
+    @property
+    def g(self) -> float:
+        return self.lib.orc_g(self.h)
+
+
+def equilibrium(w: float, wdot: float, g: float) -> np.ndarray:
+    out = np.zeros(5)
+    _load().orc_equilibrium(w, wdot, g, _dptr(out))
+    return out
+
+
+def macro_poly(sB, sI, sII, wI, wII) -> float:
+    return _load().orc_macro_poly(sB, sI, sII, wI, wII)
+
+
+def segments_intersect(p1, p2, q1, q2) -> bool:
+    return bool(_load().orc_segments_intersect(*p1, *p2, *q1, *q2))
+
+
+def checklinks(nx, ny, cut_h, cut_v, bprev, seg_a, seg_b, nmax=256):
+    """Alg. 1 CheckLinks on a bare lattice.  cut_h / cut_v are (ny, nx) uint8
+    arrays updated in place; returns the sorted new boundary points."""
+    assert cut_h.dtype == np.uint8 and cut_h.flags.c_contiguous
+    assert cut_v.dtype == np.uint8 and cut_v.flags.c_contiguous
+    bp = np.ascontiguousarray(bprev, dtype=np.int32)
+    out = np.zeros(nmax, np.int32)
+    n = _load().orc_checklinks_standalone(
+        nx, ny, cut_h.ctypes.data_as(C.c_char_p), cut_v.ctypes.data_as(C.c_char_p),
+        bp.ctypes.data_as(C.POINTER(C.c_int32)), bp.size,
+        int(seg_a[0]), int(seg_a[1]), int(seg_b[0]), int(seg_b[1]),
+        out.ctypes.data_as(C.POINTER(C.c_int32)), nmax)
+    return np.sort(out[:n])

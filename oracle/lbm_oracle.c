@@ -1,0 +1,735 @@
+/*
+ * lbm_oracle.c -- plain, slow FP64 CPU oracle for the lattice Boltzmann method
+ * for antiplane shear with dynamic mode III crack propagation
+ * (Schlueter-Kuhn et al., arXiv 2206.12412).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the package smoke check and
+ * the CPU-baseline leg of the benchmark may load this code.  It shares no code,
+ * header, table or helper with the CUDA library; the two are checked against
+ * each other only through their outputs.
+ *
+ * What it implements, in the paper's order and notation:
+ *   Sec. 3, eq. 2           D2Q5 velocity set c^0..c^4
+ *   Sec. 3, eq. (LBE)       BGK collision f* = f - (dt/tau)(f - f_eq), then
+ *                           streaming f(x + c dt, t + dt) = f*(x, t)
+ *   Sec. 3, eq. (distrib-macro)  wdot = sum_a f^a
+ *   Sec. 3, eq. (f-eq)      equilibrium, read as f_eq^k = g w (k = 1..4),
+ *                           f_eq^0 = wdot - 4 g w, g = c_s^2 dt / dh^2, so that
+ *                           sum_a f_eq^a = wdot and the scheme is the wave
+ *                           equation with speed c_s (the printed scale is garbled)
+ *   Sec. 3, eq. (integration)  w(t) = w(t - dt) + dt wdot(t)
+ *   Sec. 3.1                links that a site misses: bounce-back on free
+ *                           edges and crack faces, anti-bounce-back on
+ *                           Dirichlet edges (link-local mode), or the
+ *                           macroscopic rule of Sec. 3.1: a quadratic polynomial
+ *                           through the boundary condition and w at two interior
+ *                           points x_I, x_II (bilinear interpolation), evaluated
+ *                           at x_B, then eq. (f-macro-bc) for the missing f^a
+ *   Sec. 4.1, Alg. 1        CrackGrowth / CheckLinks (breadth-first search from
+ *                           the neighbours of the previous boundary points) /
+ *                           ProcessPoints
+ *   Sec. 2.2, eq. (sif)     K = delta (mu/4) sqrt(2 pi / r) from the crack
+ *                           opening of site pairs adjacent to the crack, at
+ *                           r in [r_min, r_min + w_fit) (Sec. 4.2), least
+ *                           squares over the pairs when w_fit > dh
+ *   Sec. 4.2, eq. (r(v))    r_min = r0 / (1 - v)
+ *   Sec. 4.2, eq. (v-tanh)  v = v_max tanh(sqrt((K/K_C)^4 - 1)), K > K_C
+ *
+ * Readings where the paper is silent or garbled (each one also listed in the
+ * design notes of the repository):
+ *   - sites sit at cell centres ((i + 1/2) dh, (j + 1/2) dh); outer edges and
+ *     the crack line y = jc dh lie on half links;
+ *   - the initial state is w = wdot = 0 unless set; f is set to f_eq(w, wdot);
+ *   - a Dirichlet edge value w*(t_n) enters the step t_n -> t_n+1;
+ *   - "intersects" is closed-segment intersection, tested exactly on a fixed
+ *     point grid of 2^-32 dh; the tip is kept on that grid and every advance
+ *     is rounded to nearest (ties to even) onto it;
+ *   - r is measured along the crack from the tip, phi = +-pi, the window is
+ *     half open; delta = w(above) - w(below), the criterion uses |K|;
+ *   - r_min uses the v of the previous step (0 while arrested);
+ *   - the tip stops (and stays) at x = (nx - 1) dh.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_Q 32 /* fixed point: 1 dh = 2^32 units */
+#define ORC_PI 3.14159265358979323846
+
+enum { ORC_FREE = 0, ORC_DIRICHLET = 1, ORC_PERIODIC = 2 };
+enum { ORC_LEFT = 0, ORC_RIGHT = 1, ORC_BOTTOM = 2, ORC_TOP = 3 };
+enum { ORC_BC_BOUNCEBACK = 0, ORC_BC_MACROSCOPIC = 1 };
+enum { ORC_CRACK_NONE = 0, ORC_CRACK_STATIONARY = 1, ORC_CRACK_PRESCRIBED = 2, ORC_CRACK_KCRIT = 3 };
+enum { ORC_LOAD_ZERO = 0, ORC_LOAD_LINEAR = 1, ORC_LOAD_SIN2 = 2, ORC_LOAD_HALFSINE = 3,
+       ORC_LOAD_SERIES = 4, ORC_LOAD_CONST = 5 };
+enum { ORC_FLAG_CLAMPED = 1, ORC_FLAG_UNSUPPORTED = 2, ORC_FLAG_NONFINITE = 4 };
+
+typedef struct {
+    int32_t nx, ny;
+    double dh, dt;
+    int32_t edge[4];     /* left, right, bottom, top */
+    double rho, mu;
+    double omega;        /* dt / tau; the paper fixes tau = dt */
+    int32_t bc_mode;
+    int32_t crack_mode;
+    int32_t jc;          /* the crack lies on y = jc * dh */
+    double x_start, x_tip;
+    double v_rel, K_C, v_max, r0, r_min_fixed, fit_width;
+    int32_t load_kind[4];
+    double load_amp[4], load_t[4];
+    const double *load_series[4];
+    int64_t load_n[4];
+    int64_t hist_cap;
+} orc_config;
+
+typedef struct {
+    int32_t site;
+    int32_t nI, idxI[4];
+    double wI[4];
+    int32_t nII, idxII[4];
+    double wII[4];
+    double sB, sI, sII;  /* distances from the crack face along the normal */
+} orc_bpoint;
+
+typedef struct {
+    orc_config c;
+    int64_t step;
+    double cs, g;
+    double *f[5], *fs[5], *w, *w_old;
+    uint8_t *cut_h;      /* link (i,j)-(i+1,j), i = nx-1 is the periodic wrap */
+    uint8_t *cut_v;      /* link (i,j)-(i,j+1), j = ny-1 is the periodic wrap */
+    int64_t start_q, tip_q, clamp_q;
+    double v_prev, K_last;
+    int32_t npairs_last, flags, arrested_for_good;
+    int32_t *bprev, nbprev;
+    orc_bpoint *bl;
+    int32_t nbl, capbl;
+    uint8_t *is_bpoint;
+    int64_t hist_n;
+    double *hK, *hv;
+    int64_t *htip;
+    int32_t *hnp, *hgrow;
+    int32_t *queue;
+    uint8_t *inq, *visited;
+    double *series[4];
+} orc_state;
+
+/* D2Q5 lattice velocities in units of c = dh/dt (Sec. 3, eq. 2). */
+static const int CX[5] = {0, 1, 0, -1, 0};
+static const int CY[5] = {0, 0, 1, 0, -1};
+static const int OPP[5] = {0, 3, 4, 1, 2};
+
+static int64_t qone(void) { return (int64_t)1 << ORC_Q; }
+
+/* ------------------------------------------------------------------ loading */
+
+/* Boundary value w*(t) of a Dirichlet edge.
+ * LINEAR: ramp amp * min(t / t_ramp, 1).
+ * SIN2:   amp * sin^2(pi t / (2 t0)) for t < t0, then amp (Sec. 5.1).
+ * HALFSINE: amp * sin(pi t / T) for t < T, then 0 (Sec. 5.2).
+ * SERIES: series[n] at step n, last value afterwards. */
+static double load_value(const orc_state *s, int e, int64_t n)
+{
+    const orc_config *c = &s->c;
+    double t = (double)n * c->dt;
+    double a = c->load_amp[e], T = c->load_t[e];
+    switch (c->load_kind[e]) {
+    case ORC_LOAD_LINEAR:
+        if (T <= 0.0 || t >= T) return a;
+        return a * (t / T);
+    case ORC_LOAD_SIN2: {
+        if (T <= 0.0 || t >= T) return a;
+        double sn = sin(ORC_PI * t / (2.0 * T));
+        return a * sn * sn;
+    }
+    case ORC_LOAD_HALFSINE:
+        if (t >= T) return 0.0;
+        return a * sin(ORC_PI * t / T);
+    case ORC_LOAD_SERIES:
+        if (c->load_n[e] <= 0) return 0.0;
+        return s->series[e][n < c->load_n[e] ? n : c->load_n[e] - 1];
+    case ORC_LOAD_CONST:
+        return a;
+    default:
+        return 0.0;
+    }
+}
+
+/* -------------------------------------------------------------- equilibrium */
+
+/* Equilibrium distributions for the wave equation (Sec. 3, eq. f-eq), in the
+ * reading f_eq^k = g w for the four moving directions and
+ * f_eq^0 = wdot - 4 g w for the rest direction, g = c_s^2 dt / dh^2. */
+static void equilibrium(double w, double wdot, double g, double feq[5])
+{
+    feq[0] = wdot - 4.0 * g * w;
+    for (int a = 1; a < 5; ++a) feq[a] = g * w;
+}
+
+void orc_equilibrium(double w, double wdot, double g, double *feq5) { equilibrium(w, wdot, g, feq5); }
+
+/* ------------------------------------------------------------------ geometry */
+
+static int64_t site_cx_q(int i) { return (int64_t)(2 * i + 1) << (ORC_Q - 1); }
+
+static int orient(int64_t ax, int64_t ay, int64_t bx, int64_t by, int64_t cx, int64_t cy)
+{
+    __int128 v = (__int128)(bx - ax) * (__int128)(cy - ay) - (__int128)(by - ay) * (__int128)(cx - ax);
+    return (v > 0) - (v < 0);
+}
+
+static int in_box(int64_t ax, int64_t ay, int64_t bx, int64_t by, int64_t px, int64_t py)
+{
+    int64_t lox = ax < bx ? ax : bx, hix = ax < bx ? bx : ax;
+    int64_t loy = ay < by ? ay : by, hiy = ay < by ? by : ay;
+    return px >= lox && px <= hix && py >= loy && py <= hiy;
+}
+
+/* Closed-segment intersection of p1p2 and q1q2, exact (orientation tests). */
+int orc_segments_intersect(int64_t p1x, int64_t p1y, int64_t p2x, int64_t p2y,
+                           int64_t q1x, int64_t q1y, int64_t q2x, int64_t q2y)
+{
+    int d1 = orient(q1x, q1y, q2x, q2y, p1x, p1y);
+    int d2 = orient(q1x, q1y, q2x, q2y, p2x, p2y);
+    int d3 = orient(p1x, p1y, p2x, p2y, q1x, q1y);
+    int d4 = orient(p1x, p1y, p2x, p2y, q2x, q2y);
+    if (d1 * d2 < 0 && d3 * d4 < 0) return 1;
+    if (d1 == 0 && in_box(q1x, q1y, q2x, q2y, p1x, p1y)) return 1;
+    if (d2 == 0 && in_box(q1x, q1y, q2x, q2y, p2x, p2y)) return 1;
+    if (d3 == 0 && in_box(p1x, p1y, p2x, p2y, q1x, q1y)) return 1;
+    if (d4 == 0 && in_box(p1x, p1y, p2x, p2y, q2x, q2y)) return 1;
+    return 0;
+}
+
+/* Link between site k and its neighbour in direction a (a = 1..4).  Returns
+ * the neighbour index, or -1 if the link leaves a non-periodic domain.  *cut
+ * points at the severed flag of the link. */
+static int32_t link_of(const orc_state *s, int32_t k, int a, uint8_t **cut)
+{
+    int nx = s->c.nx, ny = s->c.ny;
+    int i = k % nx, j = k / nx;
+    int ni = i + CX[a], nj = j + CY[a];
+    if (ni < 0 || ni >= nx) {
+        int e = ni < 0 ? ORC_LEFT : ORC_RIGHT;
+        if (s->c.edge[e] != ORC_PERIODIC) return -1;
+        ni = (ni + nx) % nx;
+    }
+    if (nj < 0 || nj >= ny) {
+        int e = nj < 0 ? ORC_BOTTOM : ORC_TOP;
+        if (s->c.edge[e] != ORC_PERIODIC) return -1;
+        nj = (nj + ny) % ny;
+    }
+    /* the flag is stored at the site from which the link points in +x / +y */
+    if (a == 1) *cut = &s->cut_h[j * nx + i];
+    else if (a == 3) *cut = &s->cut_h[nj * nx + ni];
+    else if (a == 2) *cut = &s->cut_v[j * nx + i];
+    else *cut = &s->cut_v[nj * nx + ni];
+    return nj * nx + ni;
+}
+
+/* ------------------------------------------------------------ state set-up */
+
+static void *xcalloc(size_t n, size_t sz) { return calloc(n ? n : 1, sz); }
+
+void orc_destroy(orc_state *s)
+{
+    if (!s) return;
+    for (int a = 0; a < 5; ++a) { free(s->f[a]); free(s->fs[a]); }
+    free(s->w); free(s->w_old); free(s->cut_h); free(s->cut_v);
+    free(s->bprev); free(s->bl); free(s->is_bpoint);
+    free(s->hK); free(s->hv); free(s->htip); free(s->hnp); free(s->hgrow);
+    free(s->queue); free(s->inq); free(s->visited);
+    for (int e = 0; e < 4; ++e) free(s->series[e]);
+    free(s);
+}
+
+static void add_bpoint(orc_state *s, int32_t k);
+
+/* Cut every link the initial crack segment intersects (brute force over all
+ * links) and register both end points as boundary points; they form B_prev
+ * for the first CheckLinks. */
+static void initial_crack(orc_state *s)
+{
+    int nx = s->c.nx, ny = s->c.ny;
+    int64_t yq = (int64_t)s->c.jc << ORC_Q;
+    int32_t *B = malloc(sizeof(int32_t) * 4 * (size_t)nx * ny);
+    int nB = 0;
+    for (int32_t k = 0; k < nx * ny; ++k) {
+        for (int a = 1; a <= 2; ++a) {       /* each link once: +x and +y */
+            uint8_t *cut;
+            int32_t m = link_of(s, k, a, &cut);
+            if (m < 0) continue;
+            int i = k % nx, j = k / nx, mi = m % nx, mj = m / nx;
+            if ((a == 1 && mi < i) || (a == 2 && mj < j)) continue;  /* periodic wrap link */
+            if (orc_segments_intersect(site_cx_q(i), site_cx_q(j), site_cx_q(mi), site_cx_q(mj),
+                                       s->start_q, yq, s->tip_q, yq)) {
+                *cut = 1;
+                B[nB++] = k;
+                B[nB++] = m;
+            }
+        }
+    }
+    s->nbprev = 0;
+    for (int b = 0; b < nB; ++b) {
+        int dup = 0;
+        for (int q = 0; q < s->nbprev; ++q) dup |= s->bprev[q] == B[b];
+        if (!dup) s->bprev[s->nbprev++] = B[b];
+    }
+    for (int b = 0; b < s->nbprev; ++b) add_bpoint(s, s->bprev[b]);
+    free(B);
+}
+
+orc_state *orc_create(const orc_config *cfg)
+{
+    if (cfg->nx < 1 || cfg->ny < 1 || !(cfg->dh > 0) || !(cfg->dt > 0)) return NULL;
+    orc_state *s = xcalloc(1, sizeof(orc_state));
+    s->c = *cfg;
+    size_t n = (size_t)cfg->nx * cfg->ny;
+    s->cs = sqrt(cfg->mu / cfg->rho);
+    s->g = s->cs * s->cs * cfg->dt / (cfg->dh * cfg->dh);
+    for (int a = 0; a < 5; ++a) { s->f[a] = xcalloc(n, sizeof(double)); s->fs[a] = xcalloc(n, sizeof(double)); }
+    s->w = xcalloc(n, sizeof(double));
+    s->w_old = xcalloc(n, sizeof(double));
+    s->cut_h = xcalloc(n, 1);
+    s->cut_v = xcalloc(n, 1);
+    s->is_bpoint = xcalloc(n, 1);
+    s->bprev = xcalloc(n, sizeof(int32_t));
+    s->capbl = 64;
+    s->bl = xcalloc((size_t)s->capbl, sizeof(orc_bpoint));
+    s->queue = xcalloc(8 * n + 8, sizeof(int32_t));
+    s->inq = xcalloc(n, 1);
+    s->visited = xcalloc(n, 1);
+    s->hist_n = 0;
+    int64_t hc = cfg->hist_cap > 0 ? cfg->hist_cap : 1;
+    s->hK = xcalloc((size_t)hc, sizeof(double));
+    s->hv = xcalloc((size_t)hc, sizeof(double));
+    s->htip = xcalloc((size_t)hc, sizeof(int64_t));
+    s->hnp = xcalloc((size_t)hc, sizeof(int32_t));
+    s->hgrow = xcalloc((size_t)hc, sizeof(int32_t));
+    for (int e = 0; e < 4; ++e) {
+        if (cfg->load_kind[e] == ORC_LOAD_SERIES && cfg->load_n[e] > 0) {
+            s->series[e] = malloc(sizeof(double) * (size_t)cfg->load_n[e]);
+            memcpy(s->series[e], cfg->load_series[e], sizeof(double) * (size_t)cfg->load_n[e]);
+        }
+        s->c.load_series[e] = NULL;
+    }
+    /* the initial state: w = wdot = 0, f = f_eq(0, 0) = 0 */
+    s->v_prev = cfg->crack_mode == ORC_CRACK_PRESCRIBED ? cfg->v_rel : 0.0;
+    s->clamp_q = (int64_t)(cfg->nx - 1) << ORC_Q;
+    if (cfg->crack_mode != ORC_CRACK_NONE) {
+        s->start_q = llrint(cfg->x_start / cfg->dh * (double)qone());
+        s->tip_q = llrint(cfg->x_tip / cfg->dh * (double)qone());
+        initial_crack(s);
+    }
+    return s;
+}
+
+/* Set w and wdot; the distributions become f_eq(w, wdot), whose sum is wdot. */
+void orc_set_fields(orc_state *s, const double *w, const double *wdot)
+{
+    size_t n = (size_t)s->c.nx * s->c.ny;
+    for (size_t k = 0; k < n; ++k) {
+        double feq[5];
+        equilibrium(w[k], wdot[k], s->g, feq);
+        s->w[k] = w[k];
+        for (int a = 0; a < 5; ++a) s->f[a][k] = feq[a];
+    }
+}
+
+/* w and wdot = sum_a f^a (eq. distrib-macro). */
+void orc_get_fields(const orc_state *s, double *w, double *wdot)
+{
+    size_t n = (size_t)s->c.nx * s->c.ny;
+    for (size_t k = 0; k < n; ++k) {
+        w[k] = s->w[k];
+        wdot[k] = s->f[0][k] + s->f[1][k] + s->f[2][k] + s->f[3][k] + s->f[4][k];
+    }
+}
+
+void orc_get_distributions(const orc_state *s, double *f5)
+{
+    size_t n = (size_t)s->c.nx * s->c.ny;
+    for (int a = 0; a < 5; ++a) memcpy(f5 + (size_t)a * n, s->f[a], n * sizeof(double));
+}
+
+void orc_get_cuts(const orc_state *s, uint8_t *cut_h, uint8_t *cut_v)
+{
+    size_t n = (size_t)s->c.nx * s->c.ny;
+    memcpy(cut_h, s->cut_h, n);
+    memcpy(cut_v, s->cut_v, n);
+}
+
+/* --------------------------------------------- macroscopic boundary points */
+
+/* Bilinear interpolation stencil of the point (px, py) (units of dh, site
+ * centres at half integers): up to four sites and weights. */
+static int bilinear(const orc_state *s, double px, double py, int32_t idx[4], double wt[4])
+{
+    double gx = px - 0.5, gy = py - 0.5;
+    int i0 = (int)floor(gx), j0 = (int)floor(gy);
+    double tx = gx - i0, ty = gy - j0;
+    int n = 0;
+    for (int dj = 0; dj <= 1; ++dj)
+        for (int di = 0; di <= 1; ++di) {
+            double wgt = (di ? tx : 1.0 - tx) * (dj ? ty : 1.0 - ty);
+            if (wgt == 0.0) continue;
+            int i = i0 + di, j = j0 + dj;
+            if (i < 0 || i >= s->c.nx || j < 0 || j >= s->c.ny) return -1;
+            idx[n] = j * s->c.nx + i;
+            wt[n] = wgt;
+            ++n;
+        }
+    return n;
+}
+
+/* ProcessPoints for one new boundary point x_B (Sec. 3.1 and Alg. 1): the
+ * closest point x_C on the crack, the normal through x_B, the interior points
+ * x_I = x_B + dh n and x_II = x_B + 2 dh n with their bilinear stencils. */
+static void add_bpoint(orc_state *s, int32_t k)
+{
+    if (s->is_bpoint[k]) return;
+    int nx = s->c.nx;
+    int i = k % nx, j = k / nx;
+    double bx = i + 0.5, by = j + 0.5;                   /* units of dh */
+    double x0 = (double)s->start_q / (double)qone(), x1 = (double)s->tip_q / (double)qone();
+    double yc = (double)s->c.jc;
+    double cx = bx < x0 ? x0 : (bx > x1 ? x1 : bx);      /* closest point on the crack line segment */
+    double cy = yc;
+    double dx = bx - cx, dy = by - cy;
+    double d = sqrt(dx * dx + dy * dy);
+    if (s->nbl == s->capbl) {
+        s->capbl *= 2;
+        s->bl = realloc(s->bl, sizeof(orc_bpoint) * (size_t)s->capbl);
+    }
+    orc_bpoint *b = &s->bl[s->nbl];
+    memset(b, 0, sizeof(*b));
+    b->site = k;
+    double nxv = dx / d, nyv = dy / d;
+    b->sB = d;
+    b->sI = d + 1.0;
+    b->sII = d + 2.0;
+    b->nI = bilinear(s, bx + nxv, by + nyv, b->idxI, b->wI);
+    b->nII = bilinear(s, bx + 2.0 * nxv, by + 2.0 * nyv, b->idxII, b->wII);
+    if (b->nI < 0 || b->nII < 0) s->flags |= ORC_FLAG_UNSUPPORTED;
+    s->is_bpoint[k] = 1;
+    s->nbl++;
+}
+
+/* w at x_B from the quadratic polynomial p(s) = a + b s^2 (zero normal
+ * derivative on a traction-free face) through (s_I, w_I) and (s_II, w_II). */
+static double macro_value(const orc_bpoint *b, const double *w)
+{
+    double wI = 0.0, wII = 0.0;
+    for (int q = 0; q < b->nI; ++q) wI += b->wI[q] * w[b->idxI[q]];
+    for (int q = 0; q < b->nII; ++q) wII += b->wII[q] * w[b->idxII[q]];
+    double bb = (wII - wI) / (b->sII * b->sII - b->sI * b->sI);
+    double aa = wI - bb * b->sI * b->sI;
+    return aa + bb * b->sB * b->sB;
+}
+
+/* The same polynomial evaluated for given values (for the tests). */
+double orc_macro_poly(double sB, double sI, double sII, double wI, double wII)
+{
+    orc_bpoint b;
+    double w[2] = {wI, wII};
+    memset(&b, 0, sizeof b);
+    b.nI = 1; b.idxI[0] = 0; b.wI[0] = 1.0;
+    b.nII = 1; b.idxII[0] = 1; b.wII[0] = 1.0;
+    b.sB = sB; b.sI = sI; b.sII = sII;
+    return macro_value(&b, w);
+}
+
+/* -------------------------------------------------------------- LBM step */
+
+static void lbm_step(orc_state *s)
+{
+    int nx = s->c.nx, ny = s->c.ny;
+    size_t n = (size_t)nx * ny;
+    double g = s->g, om = s->c.omega, dt = s->c.dt;
+    double wstar[4];
+    for (int e = 0; e < 4; ++e) wstar[e] = load_value(s, e, s->step);
+
+    /* collision (eq. LBE, right-hand side) */
+    for (size_t k = 0; k < n; ++k) {
+        double wdot = s->f[0][k] + s->f[1][k] + s->f[2][k] + s->f[3][k] + s->f[4][k];
+        double feq[5];
+        equilibrium(s->w[k], wdot, g, feq);
+        for (int a = 0; a < 5; ++a) s->fs[a][k] = s->f[a][k] - om * (s->f[a][k] - feq[a]);
+    }
+    /* streaming along intact links (eq. LBE, left-hand side); a missing link
+     * takes bounce-back (free edge, crack face) or anti-bounce-back (Dirichlet) */
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            int32_t k = j * nx + i;
+            s->f[0][k] = s->fs[0][k];
+            for (int a = 1; a < 5; ++a) {
+                int b = OPP[a];
+                uint8_t *cut;
+                int32_t src = link_of(s, k, b, &cut);     /* f^a arrives from x - c^a */
+                if (src >= 0 && !*cut) {
+                    s->f[a][k] = s->fs[a][src];
+                } else if (src < 0) {
+                    int e = (b == 1) ? ORC_RIGHT : (b == 3) ? ORC_LEFT : (b == 2) ? ORC_TOP : ORC_BOTTOM;
+                    if (s->c.edge[e] == ORC_DIRICHLET)
+                        s->f[a][k] = -s->fs[b][k] + 2.0 * g * wstar[e];
+                    else
+                        s->f[a][k] = s->fs[b][k];
+                } else {
+                    s->f[a][k] = s->fs[b][k];
+                }
+            }
+        }
+    /* moment and Euler integration (eqs. distrib-macro, integration) */
+    memcpy(s->w_old, s->w, n * sizeof(double));
+    for (size_t k = 0; k < n; ++k) {
+        double wdot = s->f[0][k] + s->f[1][k] + s->f[2][k] + s->f[3][k] + s->f[4][k];
+        s->w[k] = s->w_old[k] + dt * wdot;
+    }
+    /* macroscopic non-lattice-conforming rule on the crack boundary points */
+    if (s->c.bc_mode == ORC_BC_MACROSCOPIC && s->nbl > 0) {
+        double *wB = malloc(sizeof(double) * (size_t)s->nbl);
+        for (int b = 0; b < s->nbl; ++b) wB[b] = macro_value(&s->bl[b], s->w);
+        for (int b = 0; b < s->nbl; ++b) {
+            int32_t k = s->bl[b].site;
+            int miss[4], nmiss = 0;
+            double known = s->f[0][k];
+            for (int a = 1; a < 5; ++a) {
+                uint8_t *cut;
+                int32_t src = link_of(s, k, OPP[a], &cut);
+                if (src < 0 || *cut) miss[nmiss++] = a;
+                else known += s->f[a][k];
+            }
+            double target = (wB[b] - s->w_old[k]) / dt;     /* eq. f-macro-bc */
+            for (int q = 0; q < nmiss; ++q) s->f[miss[q]][k] = (target - known) / (double)nmiss;
+            s->w[k] = wB[b];
+        }
+        free(wB);
+    }
+    s->step += 1;
+}
+
+/* --------------------------------------------------------- crack handling */
+
+/* K from the crack opening of the site pairs (i, jc-1) / (i, jc) whose
+ * distance r = tip - (i + 1/2) dh along the crack lies in [r_min, r_min + W)
+ * (Sec. 4.2): least squares of delta_i = (4K/mu) s_i, s_i = sqrt(r_i / 2pi)
+ * (eq. sif).  With one pair this is K = delta (mu/4) sqrt(2pi/r). */
+static double evaluate_K(const orc_state *s, const double *w, int64_t tip_q, double r_min, double wfit, int32_t *npairs)
+{
+    int nx = s->c.nx, jc = s->c.jc;
+    double dh = s->c.dh;
+    double num = 0.0, den = 0.0;
+    int np = 0;
+    double lo = r_min / dh, hi = (r_min + wfit) / dh;
+    for (int i = 0; i < nx; ++i) {
+        if (!s->cut_v[(jc - 1) * nx + i]) continue;       /* the pair must straddle the crack */
+        double r_h = (double)(tip_q - site_cx_q(i)) / (double)qone();
+        if (!(r_h >= lo && r_h < hi)) continue;
+        double r = r_h * dh;
+        double sfac = sqrt(r / (2.0 * ORC_PI));
+        double delta = w[jc * nx + i] - w[(jc - 1) * nx + i];
+        num += delta * sfac;
+        den += sfac * sfac;
+        ++np;
+    }
+    *npairs = np;
+    if (np == 0) return 0.0;
+    return s->c.mu / 4.0 * num / den;
+}
+
+double orc_evaluate_K(const orc_state *s, const double *w, int64_t tip_q, double r_min, double wfit, int32_t *npairs)
+{
+    return evaluate_K(s, w, tip_q, r_min, wfit, npairs);
+}
+
+/* Alg. 1, CheckLinks: breadth-first search from the neighbours of the
+ * previous boundary points.  A popped point p is marked visited, each intact
+ * link (p, n_p) is tested against the new crack segment; an intersected link
+ * puts both end points into B and the unvisited neighbours of n_p into the
+ * queue.  The links found are severed after the search. */
+static int checklinks(orc_state *s, int64_t ax, int64_t ay, int64_t bx, int64_t by, int32_t *B, int nBmax)
+{
+    int nx = s->c.nx;
+    size_t n = (size_t)nx * s->c.ny;
+    int32_t qh = 0, qt = 0;
+    int nB = 0;
+    uint8_t *tocut[4096];
+    int ncut = 0;
+    memset(s->inq, 0, n);
+    memset(s->visited, 0, n);
+    for (int b = 0; b < s->nbprev; ++b)
+        for (int a = 1; a < 5; ++a) {
+            uint8_t *cut;
+            int32_t m = link_of(s, s->bprev[b], a, &cut);
+            if (m >= 0 && !*cut && !s->inq[m]) { s->inq[m] = 1; s->queue[qt++] = m; }
+        }
+    if (s->nbprev == 0) {
+        /* no previous boundary points: start from the sites around the old tip */
+        int64_t half = qone() / 2;
+        int i0 = (int)((ax - half) >> ORC_Q), j0 = (int)((ay - half) >> ORC_Q);   /* floor(x/dh - 1/2) */
+        for (int j = j0; j <= j0 + 1; ++j)
+            for (int i = i0; i <= i0 + 1; ++i)
+                if (i >= 0 && i < nx && j >= 0 && j < s->c.ny && !s->inq[j * nx + i]) {
+                    s->inq[j * nx + i] = 1;
+                    s->queue[qt++] = j * nx + i;
+                }
+    }
+    while (qh < qt) {
+        int32_t p = s->queue[qh++];
+        s->visited[p] = 1;
+        int pi = p % nx, pj = p / nx;
+        for (int a = 1; a < 5; ++a) {
+            uint8_t *cut;
+            int32_t m = link_of(s, p, a, &cut);
+            if (m < 0 || *cut) continue;
+            int mi = m % nx, mj = m / nx;
+            if (!orc_segments_intersect(site_cx_q(pi), site_cx_q(pj), site_cx_q(mi), site_cx_q(mj), ax, ay, bx, by))
+                continue;
+            int seen = 0;
+            for (int q = 0; q < ncut; ++q) seen |= tocut[q] == cut;
+            if (!seen && ncut < 4096) tocut[ncut++] = cut;
+            int hp = 0, hm = 0;
+            for (int q = 0; q < nB; ++q) { hp |= B[q] == p; hm |= B[q] == m; }
+            if (!hp && nB < nBmax) B[nB++] = p;
+            if (!hm && nB < nBmax) B[nB++] = m;
+            for (int c2 = 1; c2 < 5; ++c2) {
+                uint8_t *cut2;
+                int32_t r = link_of(s, m, c2, &cut2);
+                if (r >= 0 && !*cut2 && !s->visited[r] && !s->inq[r]) { s->inq[r] = 1; s->queue[qt++] = r; }
+            }
+        }
+    }
+    for (int q = 0; q < ncut; ++q) *tocut[q] = 1;
+    return nB;
+}
+
+static int cmp_i32(const void *a, const void *b)
+{
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* Alg. 1, CrackGrowth, appended after the LBM step (Sec. 4.1). */
+static void crack_growth(orc_state *s)
+{
+    const orc_config *c = &s->c;
+    if (c->crack_mode == ORC_CRACK_NONE) return;
+    double r_min = c->r_min_fixed > 0.0 ? c->r_min_fixed : c->r0 / (1.0 - s->v_prev);  /* eq. r(v) */
+    int32_t np = 0;
+    double K = evaluate_K(s, s->w, s->tip_q, r_min, c->fit_width, &np);
+    int propagate = 0;
+    double v = 0.0;
+    if (c->crack_mode == ORC_CRACK_PRESCRIBED) {
+        propagate = 1;
+        v = c->v_rel;
+    } else if (c->crack_mode == ORC_CRACK_KCRIT && np > 0 && fabs(K) > c->K_C) {
+        double ratio = fabs(K) / c->K_C;
+        propagate = 1;
+        v = c->v_max * tanh(sqrt(ratio * ratio * ratio * ratio - 1.0));  /* eq. v-tanh */
+    }
+    if (!isfinite(K)) s->flags |= ORC_FLAG_NONFINITE;
+    if (s->arrested_for_good) { propagate = 0; v = 0.0; }
+    int grew = 0;
+    if (propagate) {
+        double adot = v * s->cs;
+        int64_t dq = llrint(adot * c->dt / c->dh * (double)qone());   /* Delta a = adot dt */
+        int64_t prev = s->tip_q, next = prev + dq;
+        if (next >= s->clamp_q) { next = s->clamp_q; s->arrested_for_good = 1; s->flags |= ORC_FLAG_CLAMPED; }
+        if (next > prev) {
+            int64_t yq = (int64_t)c->jc << ORC_Q;
+            int32_t B[64];
+            s->tip_q = next;
+            int nB = checklinks(s, prev, yq, next, yq, B, 64);
+            qsort(B, (size_t)nB, sizeof(int32_t), cmp_i32);
+            for (int b = 0; b < nB; ++b) add_bpoint(s, B[b]);        /* ProcessPoints */
+            if (nB > 0) { memcpy(s->bprev, B, sizeof(int32_t) * (size_t)nB); s->nbprev = nB; }
+            grew = 1;
+        }
+    }
+    s->v_prev = c->crack_mode == ORC_CRACK_PRESCRIBED ? c->v_rel : v;
+    s->K_last = K;
+    s->npairs_last = np;
+    if (s->hist_n < c->hist_cap) {
+        int64_t h = s->hist_n;
+        s->hK[h] = K; s->hv[h] = v; s->htip[h] = s->tip_q; s->hnp[h] = np; s->hgrow[h] = grew;
+    }
+    s->hist_n += 1;
+}
+
+/* Advance n time steps: the LBM step including its boundary rules, then the
+ * crack handling (Sec. 4.1: appended at the end of each step). */
+void orc_step(orc_state *s, int64_t n)
+{
+    for (int64_t q = 0; q < n; ++q) {
+        lbm_step(s);
+        crack_growth(s);
+    }
+}
+
+/* ------------------------------------------------------------- inspection */
+
+typedef struct {
+    int64_t step, tip_q, hist_n;
+    double K, v_prev;
+    int32_t npairs, flags, n_bpoints, pad;
+} orc_crack_info;
+
+void orc_get_crack(const orc_state *s, orc_crack_info *out)
+{
+    out->step = s->step;
+    out->tip_q = s->tip_q;
+    out->hist_n = s->hist_n;
+    out->K = s->K_last;
+    out->v_prev = s->v_prev;
+    out->npairs = s->npairs_last;
+    out->flags = s->flags;
+    out->n_bpoints = s->nbl;
+    out->pad = 0;
+}
+
+int64_t orc_get_history(const orc_state *s, double *K, double *v, int64_t *tip_q, int32_t *npairs, int32_t *grew, int64_t cap)
+{
+    int64_t n = s->hist_n < s->c.hist_cap ? s->hist_n : s->c.hist_cap;
+    if (n > cap) n = cap;
+    for (int64_t h = 0; h < n; ++h) {
+        K[h] = s->hK[h]; v[h] = s->hv[h]; tip_q[h] = s->htip[h]; npairs[h] = s->hnp[h]; grew[h] = s->hgrow[h];
+    }
+    return n;
+}
+
+int32_t orc_get_bpoints(const orc_state *s, int32_t *sites, int32_t cap)
+{
+    int32_t n = s->nbl < cap ? s->nbl : cap;
+    for (int32_t b = 0; b < n; ++b) sites[b] = s->bl[b].site;
+    return n;
+}
+
+/* Stand-alone CheckLinks on a lattice with the given severed links and
+ * previous boundary points (for the brute-force comparison tests).  The cut
+ * arrays are updated in place; returns the number of new boundary points. */
+int32_t orc_checklinks_standalone(int32_t nx, int32_t ny, uint8_t *cut_h, uint8_t *cut_v,
+                                  const int32_t *bprev, int32_t nbprev,
+                                  int64_t ax, int64_t ay, int64_t bx, int64_t by,
+                                  int32_t *B, int32_t nBmax)
+{
+    orc_state s;
+    memset(&s, 0, sizeof s);
+    s.c.nx = nx;
+    s.c.ny = ny;
+    s.cut_h = cut_h;
+    s.cut_v = cut_v;
+    size_t n = (size_t)nx * ny;
+    s.queue = calloc(8 * n + 8, sizeof(int32_t));
+    s.inq = calloc(n, 1);
+    s.visited = calloc(n, 1);
+    s.bprev = (int32_t *)bprev;
+    s.nbprev = nbprev;
+    int nB = checklinks(&s, ax, ay, bx, by, B, nBmax);
+    free(s.queue); free(s.inq); free(s.visited);
+    return nB;
+}
+
+double orc_load_value(const orc_state *s, int32_t edge, int64_t n) { return load_value(s, edge, n); }
+double orc_g(const orc_state *s) { return s->g; }
+int32_t orc_abi_version(void) { return 1; }

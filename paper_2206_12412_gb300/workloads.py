@@ -1,0 +1,115 @@
+"""Seeded synthetic workloads shaped like the paper's problems.
+
+Problem dicts only (lattice, material, edges, crack, loads) and seeded random
+inputs; nothing here computes any part of the method.  Both the CUDA binding
+(``lbm.Lattice``) and the CPU oracle read these dicts, so that both sides are
+always given the same inputs.
+
+Lattice units throughout: dh = dt = 1, rho = 1, c_s = 0.5 (mu = 0.25), which
+gives c = dh/dt = 2 c_s (kappa = 2 in Sec. 4.1) and g = c_s^2 dt^2/dh^2 = 1/4.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+DEFAULT_HIST_CAP = 1 << 16
+
+
+def base_problem(nx: int, ny: int, *, bc_mode: str = "macroscopic", edges=("free", "free", "dirichlet", "dirichlet"),
+                 cs: float = 0.5, rho: float = 1.0, dh: float = 1.0, dt: float = 1.0) -> dict:
+    return {
+        "nx": int(nx), "ny": int(ny), "dh": float(dh), "dt": float(dt),
+        "edges": tuple(edges), "rho": float(rho), "mu": float(rho * cs * cs), "omega": 1.0,
+        "bc_mode": bc_mode, "crack": {"mode": "none"}, "loads": [], "hist_cap": DEFAULT_HIST_CAP,
+    }
+
+
+def with_crack(p: dict, *, mode: str, y: float, x_tip: float, x_start: float = 0.0, v_rel: float = 0.0,
+               K_C: float = 0.0, v_max: float = 0.85, r0: float = 2.0, r_min: float = 0.0,
+               fit_width: float = 1.0) -> dict:
+    q = dict(p)
+    q["crack"] = {"mode": mode, "y": float(y), "x_start": float(x_start), "x_tip": float(x_tip),
+                  "v_rel": float(v_rel), "K_C": float(K_C), "v_max": float(v_max), "r0": float(r0),
+                  "r_min": float(r_min), "fit_width": float(fit_width)}
+    return q
+
+
+def with_antisymmetric_ramp(p: dict, u0: float, t_ramp: float, kind: str = "linear") -> dict:
+    """Top edge +u0, bottom edge -u0, ramped over t_ramp."""
+    q = dict(p)
+    q["loads"] = [{"edge": "top", "kind": kind, "amp": float(u0), "t": float(t_ramp)},
+                  {"edge": "bottom", "kind": kind, "amp": -float(u0), "t": float(t_ramp)}]
+    return q
+
+
+def strip_reference_K(mu: float, u0: float, height: float) -> float:
+    """Textbook LEFM value for a semi-infinite crack on the midline of a strip
+    of the given height whose edges are held at +-u0: K0 = mu * 2 u0 /
+    sqrt(height).  Used only to pick a critical K_C of the right magnitude."""
+    return mu * 2.0 * u0 / math.sqrt(height)
+
+
+# ------------------------------------------------------------------ configs
+
+def plain_fp64(bc_mode: str = "macroscopic") -> dict:
+    """128x128, crack on y = 64 from x = 0 to 32, stationary, +-1e-3 on the
+    top/bottom edges ramped linearly over 200 steps; run for 2000 steps."""
+    p = base_problem(128, 128, bc_mode=bc_mode)
+    p = with_crack(p, mode="stationary", y=64.0, x_tip=32.0, r0=2.0)
+    return with_antisymmetric_ramp(p, 1e-3, 200.0)
+
+
+PLAIN_FP64_STEPS = 2000
+
+
+def kcrit_single(scale: int = 1, seed: int = 2, bc_mode: str = "macroscopic") -> dict:
+    """4096x2048 / scale: edge crack to x = 512 / scale on the midline, top and
+    bottom ramped to +-2e-3 over 5000 / scale steps, K-criterion with
+    v_max = 0.85, r0 = 2 dh and K_C = 0.5 K_ref (1 + 0.1 U(-1, 1)) drawn from
+    the seed, so that growth starts around mid-ramp."""
+    nx, ny = 4096 // scale, 2048 // scale
+    rng = np.random.default_rng(seed)
+    K_ref = strip_reference_K(0.25, 2e-3, float(ny))
+    K_C = 0.5 * K_ref * (1.0 + 0.1 * rng.uniform(-1.0, 1.0))
+    p = base_problem(nx, ny, bc_mode=bc_mode)
+    p = with_crack(p, mode="kcrit", y=float(ny // 2), x_tip=512.0 / scale, K_C=K_C, v_max=0.85, r0=2.0)
+    return with_antisymmetric_ramp(p, 2e-3, 5000.0 / scale)
+
+
+KCRIT_SINGLE_STEPS = 50000
+
+
+def prescribed_strip(nx: int, ny: int, v_rel: float, *, u0: float = 1e-3, t_ramp: float = 200.0,
+                     crack_len: float | None = None, r_min: float = 0.0, bc_mode: str = "macroscopic") -> dict:
+    """Strip with a midline edge crack growing at the prescribed speed."""
+    p = base_problem(nx, ny, bc_mode=bc_mode)
+    p = with_crack(p, mode="prescribed", y=float(ny // 2), x_tip=crack_len if crack_len is not None else nx / 4,
+                   v_rel=v_rel, r_min=r_min)
+    return with_antisymmetric_ramp(p, u0, t_ramp)
+
+
+# ------------------------------------------------------------ random inputs
+
+def smooth_field(nx: int, ny: int, seed: int, amp: float = 1e-3, modes: int = 6) -> np.ndarray:
+    """Sum of a few random Fourier modes plus small white noise, (ny, nx) FP64."""
+    rng = np.random.default_rng(seed)
+    x = (np.arange(nx) + 0.5) / nx
+    y = (np.arange(ny) + 0.5) / ny
+    X, Y = np.meshgrid(x, y)
+    f = np.zeros((ny, nx))
+    for _ in range(modes):
+        kx, ky = rng.integers(1, 6, size=2)
+        ph = rng.uniform(0, 2 * np.pi, size=2)
+        f += rng.normal() * np.sin(2 * np.pi * kx * X + ph[0]) * np.cos(2 * np.pi * ky * Y + ph[1])
+    f += 0.05 * rng.standard_normal((ny, nx))
+    return amp * f / max(np.abs(f).max(), 1e-300)
+
+
+def random_state(nx: int, ny: int, seed: int, amp: float = 1e-3, dtype=np.float64):
+    """Seeded (w, wdot) pair; rounded to `dtype` first so that both sides start
+    from bit-identical values."""
+    w = smooth_field(nx, ny, seed, amp)
+    wd = smooth_field(nx, ny, seed + 7919, amp * 0.05)
+    return w.astype(dtype).astype(np.float64), wd.astype(dtype).astype(np.float64)
