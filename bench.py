@@ -1,0 +1,330 @@
+#!/usr/bin/env python
+"""Throughput of the fused lattice Boltzmann time step with dynamic mode III
+crack propagation (arXiv 2206.12412) on GB300.
+
+Workload: the 4096 x 2048 FP32 single run with K-criterion propagation (edge
+crack to x = 512 on the midline, top/bottom ramped to +-2e-3 over 5000
+steps).  One benchmark step is one full time step of the method: the bulk
+stream + collide + integrate kernel over all 8.4 M sites, then the crack-face
+rule and the crack step (K_III evaluation, criterion, advance, link cuts).
+
+Timing: the lattice first runs --prelude steps (load ramp active), then
+--warmup untimed steps; each of the --steps timed steps is bracketed by CUDA
+events on the lattice's stream, with a 256 MiB buffer written between steps
+(outside the events) so that every step starts with a cold L2.  The bulk
+kernel is timed on its own by the library's event hooks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference runs the plain FP64 CPU oracle on the same workload (the
+reference arm: there is no other implementation of the method).  With N > 1
+(torchrun) every rank runs its own independent replica (weak scaling, no data
+exchange); the reference arm runs on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GLUPS and HBM GB/s vs GB300 roofline; batched and adjoint vs plain FP32 forward"
+UNIT = "GLUPS"
+BYTES_PER_SITE = 16            # FP32 moment form: read w, wdot; write w, wdot
+WORKLOAD = "kcrit_single_4096x2048_f32"
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "bulk_kernel_f32_4096x2048.md")
+KERNEL_SOURCE = os.path.join(ROOT, "paper_2206_12412_gb300", "csrc", "lbm_kernels.cu")
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_from_profile():
+    """Per-launch DRAM bytes of the bulk kernel from the committed ncu summary,
+    or None if there is none or the kernel source changed since it was taken."""
+    try:
+        text = open(PROFILE_SUMMARY).read()
+        src = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    m = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", text)
+    b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m or not b or m.group(1) != src:
+        return None
+    return float(b.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        loaded = [s for s in sm if s > 0.5 * (max(sm) if sm else 1)]
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(problem, target_s=15.0):
+    """The FP64 CPU oracle, as it stands, single-threaded on a bounded sample."""
+    import oracle
+    oracle.build()
+    o = oracle.Oracle(problem)
+    t = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter() - t
+    n = max(2, min(200, int(target_s / max(t1, 1e-6))))
+    t = time.perf_counter()
+    o.step(n)
+    dt = time.perf_counter() - t
+    sites = problem["nx"] * problem["ny"]
+    o.close()
+    return {"value": sites * n / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{problem['nx']}x{problem['ny']} lattice, {n} consecutive steps from the initial state, "
+                      f"FP64 distribution form, one thread ({dt:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from paper_2206_12412_gb300 import workloads as W
+    import oracle
+    oracle.build()
+    p = W.kcrit_single()
+    o = oracle.Oracle(p)
+    sites = p["nx"] * p["ny"]
+    t = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter() - t
+    # a step is the whole lattice if the run fits in ~3 minutes, else a band of rows
+    budget = 180.0
+    frac = min(1.0, budget / max(t1 * (args.steps + args.warmup), 1e-9))
+    if frac < 1.0:
+        o.close()
+        ny = max(16, int(p["ny"] * frac) // 2 * 2)
+        q = dict(p)
+        q["ny"] = ny
+        q["crack"] = dict(p["crack"], y=float(ny // 2))
+        p, o = q, oracle.Oracle(q)
+        sites = p["nx"] * ny
+    o.step(args.warmup)
+    t = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t
+    value = sites * args.steps / dt / 1e9
+    sample = (f"{p['nx']}x{p['ny']} lattice per step" + ("" if frac >= 1.0 else " (row band of the 4096x2048 workload)")
+              + ", FP64 distribution form, one thread")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "nx": 4096, "ny": 2048},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+    from paper_2206_12412_gb300 import lbm
+    from paper_2206_12412_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+
+    def allmax(x: float) -> float:
+        if pg is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        return float(t.item())
+
+    problem = W.kcrit_single()
+    sites = problem["nx"] * problem["ny"]
+    stream = torch.cuda.current_stream()
+    lat = lbm.Lattice(problem, "f32", stream=stream)
+    lat.step(args.prelude)
+    lat.sync()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    lat.set_profiling(True)
+    for _ in range(args.warmup):
+        flush.zero_()
+        lat.step(1)
+    lat.sync()
+    lat.profile(reset=True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        lat.step(1)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    step_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    prof = lat.profile(reset=True)
+    lat.set_profiling(False)
+    total_s = allmax(step_ms * 1e-3)
+    value = world * sites * args.steps / total_s / 1e9
+    bulk_s = prof["bulk_ms"] / max(prof["n_bulk"], 1) * 1e-3
+    crack_s = prof["crack_ms"] / max(prof["n_crack"], 1) * 1e-3
+    achieved = BYTES_PER_SITE * sites / bulk_s / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = traffic_from_profile()
+
+    # steady back-to-back replay (CUDA graph, no flush): context only
+    lat.sync()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    lat.step(256)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    steady = sites * 256 / (ev0.elapsed_time(ev1) * 1e-3) / 1e9
+
+    # end to end through the public API with host buffers: upload the state from
+    # pinned memory, run the steps, read back the fields and the per-step crack record
+    w_h = torch.empty((problem["ny"], problem["nx"]), dtype=torch.float32, pin_memory=True)
+    wd_h = torch.empty_like(w_h, pin_memory=True)
+    w_np, wd_np = w_h.numpy(), wd_h.numpy()
+    w0, wd0 = lat.fields()
+    w_np[...] = w0
+    wd_np[...] = wd0
+    e2e_vals = []
+    for _ in range(2):
+        barrier()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        lbm.lbm_set_fields(lat.h, 0, w_np.ctypes.data, False, lat.dtype_code)
+        lbm.lbm_set_fields(lat.h, 1, wd_np.ctypes.data, False, lat.dtype_code)
+        lat.step(args.steps)
+        lbm.lbm_fields(lat.h, 0, w_np.ctypes.data, False, lat.dtype_code)
+        lbm.lbm_fields(lat.h, 1, wd_np.ctypes.data, False, lat.dtype_code)
+        hist = lat.history(cap=args.steps)
+        e2e_vals.append(time.perf_counter() - t)
+    e2e_s = allmax(min(e2e_vals))
+    plane = sites * 4
+    h2d = 2 * plane / args.steps
+    d2h = (2 * plane + len(hist["K"]) * (8 + 8 + 8 + 4)) / args.steps
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": problem["nx"], "ny": problem["ny"], "storage": "f32",
+                   "crack": "kcrit", "bc_mode": problem["bc_mode"], "prelude_steps": args.prelude,
+                   "l2": "256 MiB buffer written between timed steps (outside the events)",
+                   "parallelism": f"{world} independent replicas" if world > 1 else "single GPU",
+                   "bulk_launch": dict(zip(("rows_per_cta", "grid_x", "grid_y"), lat.launch()))},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "bulk_kernel<float>", "bulk_ms": bulk_s * 1e3, "crack_ms": crack_s * 1e3,
+                     "bytes_per_site": BYTES_PER_SITE},
+        "e2e": {"value": world * sites * args.steps / e2e_s / 1e9, "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 2 * args.steps,
+        "steady_graph_glups": steady,
+        "wall_s": wall,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(problem)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prelude", type=int, default=2500)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

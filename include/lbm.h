@@ -1,0 +1,236 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) lattice Boltzmann library for
+ * antiplane shear with dynamic mode III crack propagation
+ * (Schlueter-Kuhn et al., "Dynamic Propagation of Mode III Cracks in a
+ * Lattice Boltzmann Method for Solids", arXiv 2206.12412).
+ *
+ * One handle holds one lattice on one GPU.  Every time step is
+ *   (1) the fused D2Q5 stream + collide + integrate update of all sites
+ *       (Sec. 3: eqs. LBE, distrib-macro, f-eq, integration), with bounce-back
+ *       on severed links and free edges and anti-bounce-back on Dirichlet
+ *       edges (Sec. 3.1, link-local treatment of missing links);
+ *   (2) optionally the macroscopic non-lattice-conforming rule on the crack
+ *       boundary points (Sec. 3.1, eq. f-macro-bc);
+ *   (3) the crack step of Alg. 1 (Sec. 4.1): K_III from the crack opening
+ *       (Sec. 2.2, eq. sif; Sec. 4.2 evaluation window and eq. r(v)), the
+ *       criterion (prescribed growth, or the K-criterion with the velocity of
+ *       eq. v-tanh), tip advance by Delta a = adot dt, and severing of the
+ *       links the new crack segment intersects.
+ * All of it runs in this library's CUDA kernels; the library owns the device
+ * state.  Conventions shared by every call:
+ *   - every call returns lbm_status; nothing throws or exits across the ABI;
+ *   - inputs are copied at create; no caller pointer is retained, except the
+ *     allocator callbacks and their context, which must outlive the handle;
+ *   - lbm_step only enqueues work on the handle's stream; calls that hand data
+ *     to the host (lbm_fields to host memory, lbm_cut_mask, lbm_crack_state,
+ *     lbm_sync) synchronise that stream;
+ *   - a device-side error (a non-finite field) is sticky: every later call on
+ *     the handle returns LBM_ERR_UNSTABLE;
+ *   - lbm_last_error() describes the most recent failure on the calling thread.
+ *
+ * Geometry: sites sit at cell centres ((i + 1/2) dh, (j + 1/2) dh),
+ * 0 <= i < nx, 0 <= j < ny; outer edges lie on half links.  Field planes are
+ * exchanged as dense row-major ny x nx arrays (element (j, i) at j * nx + i).
+ * The crack is a straight segment along +x on the line y = jc dh (jc an
+ * integer), i.e. between rows jc-1 and jc; its tip is kept on a fixed-point
+ * grid of 2^-32 dh.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lbm_status {
+    LBM_OK = 0,
+    LBM_ERR_ARG = -1,      /* invalid argument or unsupported configuration */
+    LBM_ERR_CUDA = -2,     /* a CUDA runtime call failed */
+    LBM_ERR_OOM = -3,      /* the allocator returned NULL */
+    LBM_ERR_UNSTABLE = -4, /* a non-finite value appeared in the fields or in K */
+    LBM_ERR_TIMEOUT = -5,  /* a bounded device-side wait gave up */
+    LBM_ERR_STATE = -6,    /* call not valid in the handle's current state */
+    LBM_ERR_IO = -7        /* file input/output failed */
+} lbm_status;
+
+/* edge kinds, one per outer edge */
+enum { LBM_EDGE_FREE = 0, LBM_EDGE_DIRICHLET = 1, LBM_EDGE_PERIODIC = 2 };
+/* edge indices into lbm_grid.edge and lbm_loading.edge */
+enum { LBM_LEFT = 0, LBM_RIGHT = 1, LBM_BOTTOM = 2, LBM_TOP = 3 };
+enum { LBM_D2Q5 = 0 };
+enum { LBM_FORM_MOMENT = 0 };
+/* storage (and arithmetic) precision of the fields */
+enum { LBM_F64 = 0, LBM_F32 = 1 };
+/* treatment of the crack faces */
+enum { LBM_BC_BOUNCEBACK = 0, LBM_BC_MACROSCOPIC = 1 };
+/* crack modes (Alg. 1 "criterion") */
+enum { LBM_CRACK_NONE = 0, LBM_CRACK_STATIONARY = 1, LBM_CRACK_PRESCRIBED = 2, LBM_CRACK_KCRIT = 3 };
+/* loading kinds of a Dirichlet edge */
+enum { LBM_LOAD_ZERO = 0, LBM_LOAD_LINEAR = 1, LBM_LOAD_SIN2 = 2, LBM_LOAD_HALFSINE = 3,
+       LBM_LOAD_SERIES = 4, LBM_LOAD_CONST = 5 };
+/* field planes */
+enum { LBM_FIELD_W = 0, LBM_FIELD_WDOT = 1 };
+/* cut masks */
+enum { LBM_MASK_H = 0, LBM_MASK_V = 1 };
+/* bits of lbm_crack_state_t.flags */
+enum { LBM_FLAG_CLAMPED = 1, LBM_FLAG_NONFINITE = 4 };
+
+/* Lattice extent and spacing.  dh, dt > 0.  edge[] holds an LBM_EDGE_* per
+ * edge index; periodic edges come in opposite pairs. */
+typedef struct lbm_grid {
+    int32_t nx, ny;
+    double dh, dt;
+    int32_t edge[4];
+} lbm_grid;
+
+/* Lattice model.  velocity_set = LBM_D2Q5, form = LBM_FORM_MOMENT,
+ * omega = dt / tau = 1 (the paper fixes tau = dt; Sec. 3).  storage is
+ * LBM_F64 or LBM_F32; bc_mode selects the crack-face treatment. */
+typedef struct lbm_lattice {
+    int32_t velocity_set;
+    int32_t form;
+    double omega;
+    int32_t storage;
+    int32_t bc_mode;
+} lbm_lattice;
+
+/* Density and shear modulus; c_s = sqrt(mu / rho) (Sec. 2.1).  The update is
+ * stable only for g = c_s^2 dt^2 / dh^2 <= 1/2; larger g is rejected. */
+typedef struct lbm_material {
+    double rho, mu;
+} lbm_material;
+
+/* Straight crack along +x on the line y (a multiple of dh, at least 3 dh from
+ * the bottom and top edges), from x_start to x_tip (physical units).
+ * v_rel: prescribed relative speed adot / c_s (LBM_CRACK_PRESCRIBED).
+ * K_C, v_max: K-criterion and eq. v-tanh (LBM_CRACK_KCRIT).
+ * r0: eq. r(v); r_min > 0 overrides it with a fixed evaluation distance.
+ * fit_width: width W of the evaluation window [r_min, r_min + W) (dh if <= 0).
+ * hist_cap: capacity of the per-step history ring (records kept on device). */
+typedef struct lbm_crack {
+    int32_t mode;
+    int32_t reserved;
+    double y, x_start, x_tip;
+    double v_rel, K_C, v_max, r0, r_min, fit_width;
+    int64_t hist_cap;
+} lbm_crack;
+
+/* Boundary value w*(t) of one Dirichlet edge:
+ * LINEAR amp*min(t/t_ramp,1); SIN2 amp*sin^2(pi t/(2 t_ramp)) then amp
+ * (Sec. 5.1); HALFSINE amp*sin(pi t/t_ramp) then 0 (Sec. 5.2); SERIES
+ * series[n] at step n, holding the last value (copied at create); CONST amp.
+ * The value at t_n = n dt is applied in the step t_n -> t_n+1. */
+typedef struct lbm_loading {
+    int32_t edge;
+    int32_t kind;
+    double amp;
+    double t_ramp;
+    const double *series;
+    int64_t n_series;
+} lbm_loading;
+
+/* Optional device allocator (for example a framework's caching allocator).
+ * alloc returns device memory of at least `bytes` bytes aligned to 256 bytes,
+ * or NULL; release frees it.  When NULL is passed, cudaMalloc / cudaFree are
+ * used.  The library allocates only inside lbm_create. */
+typedef struct lbm_allocator {
+    void *(*alloc)(size_t bytes, void *ctx);
+    void (*release)(void *ptr, void *ctx);
+    void *ctx;
+} lbm_allocator;
+
+/* Crack state after the last completed step.  tip_q is the tip in units of
+ * 2^-32 dh; n_cut counts severed crack links; r_min is the evaluation
+ * distance used in the last K evaluation; npairs the number of site pairs
+ * that entered it (0: K undefined, no growth). */
+typedef struct lbm_crack_state_t {
+    int64_t step, tip_q, n_cut, hist_n;
+    double tip_x, K, v, r_min;
+    int32_t npairs, flags;
+} lbm_crack_state_t;
+
+typedef struct lbm_handle lbm_handle;
+
+/* Build a lattice on the current CUDA device.  stream (a cudaStream_t, NULL
+ * for the legacy default stream) is where every later call enqueues work.
+ * loads: n_loads entries, at most one per edge; a Dirichlet edge without an
+ * entry is held at w* = 0.  The fields start at w = wdot = 0 with the initial
+ * crack's links severed.  Returns LBM_ERR_ARG for invalid input (non-positive
+ * sizes, g > 1/2, omega != 1, a crack outside the lattice, unpaired periodic
+ * edges, periodic left/right edges with macroscopic crack faces). */
+lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lbm_material *material,
+                      const lbm_crack *crack, const lbm_loading *loads, int32_t n_loads,
+                      void *stream, const lbm_allocator *allocator, lbm_handle **out);
+
+/* Enqueue n >= 0 time steps (each: bulk update, crack-face rule, crack step)
+ * on the handle's stream.  Asynchronous; errors of the device work surface at
+ * the next synchronising call. */
+lbm_status lbm_step(lbm_handle *h, int64_t n);
+
+/* Copy field `which` (LBM_FIELD_W or LBM_FIELD_WDOT) as a dense ny x nx
+ * row-major array of the storage precision (dtype = storage) into dst, which
+ * lies in device memory if dst_on_device, else in host memory (then the
+ * stream is synchronised before returning). */
+lbm_status lbm_fields(lbm_handle *h, int32_t which, void *dst, int32_t dst_on_device, int32_t dtype);
+
+/* Overwrite field `which` from a dense ny x nx row-major array of the storage
+ * precision.  Crack, step counter and history are left unchanged. */
+lbm_status lbm_set_fields(lbm_handle *h, int32_t which, const void *src, int32_t src_on_device, int32_t dtype);
+
+/* Copy a cut mask into host memory: row j occupies words_per_row =
+ * ceil(nx / 32) words starting at j * words_per_row; bit b of word w is
+ * column 32 w + b.  LBM_MASK_H bit (i, j): link (i,j)-(i+1,j) severed (i =
+ * nx-1: the periodic wrap link); LBM_MASK_V bit (i, j): link (i,j)-(i,j+1).
+ * n_words must be at least ny * words_per_row.  Synchronises the stream. */
+lbm_status lbm_cut_mask(lbm_handle *h, int32_t which, uint32_t *dst_host, int64_t n_words);
+
+/* Current crack state, plus (if the pointers are not NULL) the last
+ * min(cap, hist_n, hist_cap) per-step records in chronological order: K,
+ * relative speed v, tip_q and number of pairs.  *n_written receives the
+ * number of records copied.  Synchronises the stream. */
+lbm_status lbm_crack_state(lbm_handle *h, lbm_crack_state_t *now, double *K_hist, double *v_hist,
+                           int64_t *tip_hist, int32_t *npairs_hist, int64_t cap, int64_t *n_written);
+
+/* Synchronise the handle's stream and report sticky device errors. */
+lbm_status lbm_sync(lbm_handle *h);
+
+/* Move later work to another stream (the caller orders the two streams). */
+lbm_status lbm_set_stream(lbm_handle *h, void *stream);
+
+/* Launch shape of the bulk kernel: each CTA marches over rows_per_cta rows
+ * (0 picks the built-in default for the lattice size).  Synchronises the
+ * stream and drops the cached step graph. */
+lbm_status lbm_set_launch(lbm_handle *h, int32_t rows_per_cta);
+
+/* Current launch shape of the bulk kernel (any pointer may be NULL). */
+lbm_status lbm_get_launch(const lbm_handle *h, int32_t *rows_per_cta, int32_t *grid_x, int32_t *grid_y);
+
+/* Per-kernel timing: while enabled, lbm_step launches each step directly
+ * (no graph) with CUDA events on the handle's stream around the bulk kernel
+ * and around the crack kernel. */
+lbm_status lbm_set_profiling(lbm_handle *h, int32_t enable);
+
+/* Sum of the measured kernel durations (milliseconds) and launch counts since
+ * the last reset; reset != 0 clears them.  Synchronises the stream. */
+lbm_status lbm_profile_read(lbm_handle *h, double *bulk_ms, int64_t *n_bulk, double *crack_ms, int64_t *n_crack,
+                            int32_t reset);
+
+/* Bytes of device memory the handle holds. */
+lbm_status lbm_device_bytes(const lbm_handle *h, int64_t *bytes);
+
+/* Release the handle and its device memory (NULL is ignored).  Synchronises
+ * the stream first. */
+void lbm_destroy(lbm_handle *h);
+
+/* Message of the most recent failure on the calling thread ("" if none).
+ * The pointer stays valid until the next call on this thread. */
+const char *lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

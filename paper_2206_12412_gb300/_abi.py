@@ -1,0 +1,85 @@
+"""ctypes mirror of include/lbm.h (structs, constants, prototypes)."""
+from __future__ import annotations
+
+import ctypes as C
+
+LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_OOM = 0, -1, -2, -3
+LBM_ERR_UNSTABLE, LBM_ERR_TIMEOUT, LBM_ERR_STATE, LBM_ERR_IO = -4, -5, -6, -7
+STATUS_NAMES = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_OOM",
+                -4: "LBM_ERR_UNSTABLE", -5: "LBM_ERR_TIMEOUT", -6: "LBM_ERR_STATE", -7: "LBM_ERR_IO"}
+
+EDGE = {"free": 0, "dirichlet": 1, "periodic": 2}
+EDGE_INDEX = {"left": 0, "right": 1, "bottom": 2, "top": 3}
+STORAGE = {"f64": 0, "f32": 1}
+BC = {"bounceback": 0, "macroscopic": 1}
+CRACK = {"none": 0, "stationary": 1, "prescribed": 2, "kcrit": 3}
+LOAD = {"zero": 0, "linear": 1, "sin2": 2, "halfsine": 3, "series": 4, "const": 5}
+FIELD = {"w": 0, "wdot": 1}
+MASK = {"h": 0, "v": 1}
+FLAG_CLAMPED, FLAG_NONFINITE = 1, 4
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("dh", C.c_double), ("dt", C.c_double),
+                ("edge", C.c_int32 * 4)]
+
+
+class Lattice_(C.Structure):
+    _fields_ = [("velocity_set", C.c_int32), ("form", C.c_int32), ("omega", C.c_double),
+                ("storage", C.c_int32), ("bc_mode", C.c_int32)]
+
+
+class Material(C.Structure):
+    _fields_ = [("rho", C.c_double), ("mu", C.c_double)]
+
+
+class Crack(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("reserved", C.c_int32),
+                ("y", C.c_double), ("x_start", C.c_double), ("x_tip", C.c_double),
+                ("v_rel", C.c_double), ("K_C", C.c_double), ("v_max", C.c_double),
+                ("r0", C.c_double), ("r_min", C.c_double), ("fit_width", C.c_double),
+                ("hist_cap", C.c_int64)]
+
+
+class Loading(C.Structure):
+    _fields_ = [("edge", C.c_int32), ("kind", C.c_int32), ("amp", C.c_double), ("t_ramp", C.c_double),
+                ("series", C.POINTER(C.c_double)), ("n_series", C.c_int64)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+RELEASE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class Allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("release", RELEASE_FN), ("ctx", C.c_void_p)]
+
+
+class CrackStateT(C.Structure):
+    _fields_ = [("step", C.c_int64), ("tip_q", C.c_int64), ("n_cut", C.c_int64), ("hist_n", C.c_int64),
+                ("tip_x", C.c_double), ("K", C.c_double), ("v", C.c_double), ("r_min", C.c_double),
+                ("npairs", C.c_int32), ("flags", C.c_int32)]
+
+
+# name -> (restype, argtypes); every symbol include/lbm.h declares
+PROTOTYPES = {
+    "lbm_create": (C.c_int, [C.POINTER(Grid), C.POINTER(Lattice_), C.POINTER(Material), C.POINTER(Crack),
+                             C.POINTER(Loading), C.c_int32, C.c_void_p, C.POINTER(Allocator),
+                             C.POINTER(C.c_void_p)]),
+    "lbm_step": (C.c_int, [C.c_void_p, C.c_int64]),
+    "lbm_fields": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int32]),
+    "lbm_set_fields": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int32]),
+    "lbm_cut_mask": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_uint32), C.c_int64]),
+    "lbm_crack_state": (C.c_int, [C.c_void_p, C.POINTER(CrackStateT), C.POINTER(C.c_double),
+                                  C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                  C.c_int64, C.POINTER(C.c_int64)]),
+    "lbm_sync": (C.c_int, [C.c_void_p]),
+    "lbm_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "lbm_set_launch": (C.c_int, [C.c_void_p, C.c_int32]),
+    "lbm_get_launch": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "lbm_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
+    "lbm_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                                   C.POINTER(C.c_int64), C.c_int32]),
+    "lbm_device_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "lbm_destroy": (None, [C.c_void_p]),
+    "lbm_last_error": (C.c_char_p, []),
+}

@@ -1,0 +1,686 @@
+// lbm_api.cu -- host runtime behind the C ABI declared in include/lbm.h:
+// validation, device memory layout, initial crack, CUDA-graph replay of the
+// per-step kernel sequence, and the copy-out calls.
+#include "lbm.h"
+#include "lbm_internal.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace lbm;
+
+namespace {
+
+thread_local std::string g_err;
+
+lbm_status fail(lbm_status s, const std::string &msg)
+{
+    g_err = msg;
+    return s;
+}
+
+lbm_status cuda_fail(cudaError_t e, const char *what)
+{
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return LBM_ERR_CUDA;
+}
+
+#define LBM_CUDA(call)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+constexpr int64_t kGraphChunk = 64;   // time steps per captured graph (even)
+constexpr int64_t kDefaultHistCap = 65536;
+
+int64_t floor_div(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct lbm_handle {
+    lbm_grid grid;
+    lbm_lattice lat;
+    lbm_material mat;
+    lbm_crack crack;
+    size_t esize;
+    int64_t pitch;      // elements per padded row
+    int32_t words;      // 32-bit mask words per row
+    int32_t rows;       // rows per CTA of the bulk kernel
+    dim3 bulk_grid;
+    lbm_allocator alloc;
+    bool custom_alloc;
+    void *block;
+    size_t block_bytes;
+    void *w[2];         // element (0, 0) of each W buffer
+    void *wd;
+    uint32_t *cut_h, *cut_v;
+    uint8_t *rowflag;
+    CrackState *st;
+    History hist;
+    LoadDesc load[4];
+    CrackParams cp;
+    double g;
+    int parity;
+    cudaStream_t stream;
+    cudaStream_t cap_stream;
+    cudaGraphExec_t gexec;
+    int gparity;
+    lbm_status sticky;
+    // per-kernel CUDA-event timing of direct launches (lbm_set_profiling)
+    int profiling;
+    std::vector<cudaEvent_t> *ev;   // three events per profiled step
+    size_t ev_used;
+    double bulk_ms, crack_ms;
+    int64_t n_bulk, n_crack;
+};
+
+namespace {
+
+template <typename T>
+void make_bulk_args(const lbm_handle *h, int par, BulkArgs<T> &a)
+{
+    a.w_in = static_cast<const T *>(h->w[par]);
+    a.w_out = static_cast<T *>(h->w[par ^ 1]);
+    a.wd = static_cast<T *>(h->wd);
+    a.pitch = h->pitch;
+    a.nx = h->grid.nx;
+    a.ny = h->grid.ny;
+    a.rows = h->rows;
+    for (int e = 0; e < 4; ++e) a.edge[e] = h->grid.edge[e];
+    a.g = (T)h->g;
+    a.dt = (T)h->grid.dt;
+    a.cut_h = h->cut_h;
+    a.cut_v = h->cut_v;
+    a.rowflag = h->rowflag;
+    a.words = h->words;
+    a.st = h->st;
+}
+
+template <typename T>
+void make_crack_args(const lbm_handle *h, int par, CrackArgs<T> &a)
+{
+    a.w_in = static_cast<const T *>(h->w[par]);
+    a.w_out = static_cast<T *>(h->w[par ^ 1]);
+    a.wd = static_cast<T *>(h->wd);
+    a.pitch = h->pitch;
+    a.dt = (T)h->grid.dt;
+    a.p = h->cp;
+    for (int e = 0; e < 4; ++e) { a.load[e] = h->load[e]; a.edge[e] = h->grid.edge[e]; }
+    a.cut_v = h->cut_v;
+    a.rowflag = h->rowflag;
+    a.st = h->st;
+    a.hist = h->hist;
+}
+
+// One time step: bulk update W[par] -> W[par^1], then the crack-face rule and
+// the crack step.
+cudaError_t enqueue_step(const lbm_handle *h, int par, cudaStream_t s)
+{
+    cudaError_t e;
+    if (h->lat.storage == LBM_F32) {
+        BulkArgs<float> b;
+        make_bulk_args(h, par, b);
+        if ((e = launch_bulk(b, h->bulk_grid, s)) != cudaSuccess) return e;
+        CrackArgs<float> c;
+        make_crack_args(h, par, c);
+        return launch_crack(c, s);
+    }
+    BulkArgs<double> b;
+    make_bulk_args(h, par, b);
+    if ((e = launch_bulk(b, h->bulk_grid, s)) != cudaSuccess) return e;
+    CrackArgs<double> c;
+    make_crack_args(h, par, c);
+    return launch_crack(c, s);
+}
+
+// Fold the elapsed times of the recorded event triples into the totals.
+cudaError_t drain_profile(lbm_handle *h)
+{
+    if (!h->ev || h->ev_used == 0) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return e;
+    for (size_t q = 0; q + 3 <= h->ev_used; q += 3) {
+        float a = 0.f, b = 0.f;
+        if ((e = cudaEventElapsedTime(&a, (*h->ev)[q], (*h->ev)[q + 1])) != cudaSuccess) return e;
+        if ((e = cudaEventElapsedTime(&b, (*h->ev)[q + 1], (*h->ev)[q + 2])) != cudaSuccess) return e;
+        h->bulk_ms += a;
+        h->crack_ms += b;
+        h->n_bulk += 1;
+        h->n_crack += 1;
+    }
+    h->ev_used = 0;
+    return cudaSuccess;
+}
+
+// One step with events around each kernel (direct launches, no graph).
+cudaError_t enqueue_step_profiled(lbm_handle *h, int par, cudaStream_t s)
+{
+    cudaError_t e;
+    if (h->ev_used + 3 > h->ev->size()) {
+        if ((e = drain_profile(h)) != cudaSuccess) return e;
+    }
+    cudaEvent_t *E = &(*h->ev)[h->ev_used];
+    h->ev_used += 3;
+    if ((e = cudaEventRecord(E[0], s)) != cudaSuccess) return e;
+    if (h->lat.storage == LBM_F32) {
+        BulkArgs<float> b;
+        make_bulk_args(h, par, b);
+        if ((e = launch_bulk(b, h->bulk_grid, s)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(E[1], s)) != cudaSuccess) return e;
+        CrackArgs<float> c;
+        make_crack_args(h, par, c);
+        if ((e = launch_crack(c, s)) != cudaSuccess) return e;
+    } else {
+        BulkArgs<double> b;
+        make_bulk_args(h, par, b);
+        if ((e = launch_bulk(b, h->bulk_grid, s)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(E[1], s)) != cudaSuccess) return e;
+        CrackArgs<double> c;
+        make_crack_args(h, par, c);
+        if ((e = launch_crack(c, s)) != cudaSuccess) return e;
+    }
+    return cudaEventRecord(E[2], s);
+}
+
+void set_launch(lbm_handle *h, int rows)
+{
+    const int vec = (int)(16 / h->esize);
+    const int gx = (int)(((h->grid.nx + vec - 1) / vec + kBulkThreads - 1) / kBulkThreads);
+    if (rows <= 0) {
+        // enough CTAs for about eight resident per SM on 152 SMs, 4..64 rows each
+        const int64_t target = 152 * 8;
+        int64_t r = (int64_t)h->grid.ny * gx / target;
+        rows = (int)(r < 4 ? 4 : (r > 64 ? 64 : r));
+    }
+    h->rows = rows;
+    h->bulk_grid = dim3((unsigned)gx, (unsigned)((h->grid.ny + rows - 1) / rows), 1);
+}
+
+lbm_status check_sticky(lbm_handle *h)
+{
+    CrackState hs;
+    cudaError_t e = cudaMemcpyAsync(&hs, h->st, sizeof hs, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        h->sticky = LBM_ERR_CUDA;
+        return cuda_fail(e, "synchronising the lattice stream");
+    }
+    if (hs.flags & FLAG_NONFINITE) {
+        h->sticky = LBM_ERR_UNSTABLE;
+        return fail(LBM_ERR_UNSTABLE, "non-finite value in the fields or in K");
+    }
+    return LBM_OK;
+}
+
+void *dev_alloc(lbm_handle *h, size_t bytes)
+{
+    if (h->custom_alloc) return h->alloc.alloc(bytes, h->alloc.ctx);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+    return p;
+}
+
+void dev_free(lbm_handle *h, void *p)
+{
+    if (!p) return;
+    if (h->custom_alloc) h->alloc.release(p, h->alloc.ctx);
+    else cudaFree(p);
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lbm_material *material,
+                      const lbm_crack *crack, const lbm_loading *loads, int32_t n_loads,
+                      void *stream, const lbm_allocator *allocator, lbm_handle **out)
+{
+    if (!out) return fail(LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!grid || !lattice || !material) return fail(LBM_ERR_ARG, "grid, lattice and material are required");
+    if (grid->nx < 1 || grid->ny < 2) return fail(LBM_ERR_ARG, "need nx >= 1 and ny >= 2");
+    if ((int64_t)grid->nx * grid->ny > ((int64_t)1 << 34)) return fail(LBM_ERR_ARG, "lattice too large");
+    if (!(grid->dh > 0.0) || !(grid->dt > 0.0) || !std::isfinite(grid->dh) || !std::isfinite(grid->dt))
+        return fail(LBM_ERR_ARG, "dh and dt must be positive and finite");
+    for (int e = 0; e < 4; ++e)
+        if (grid->edge[e] < LBM_EDGE_FREE || grid->edge[e] > LBM_EDGE_PERIODIC)
+            return fail(LBM_ERR_ARG, "unknown edge kind");
+    if ((grid->edge[LBM_LEFT] == LBM_EDGE_PERIODIC) != (grid->edge[LBM_RIGHT] == LBM_EDGE_PERIODIC) ||
+        (grid->edge[LBM_BOTTOM] == LBM_EDGE_PERIODIC) != (grid->edge[LBM_TOP] == LBM_EDGE_PERIODIC))
+        return fail(LBM_ERR_ARG, "periodic edges must come in opposite pairs");
+    if (lattice->velocity_set != LBM_D2Q5) return fail(LBM_ERR_ARG, "only the D2Q5 velocity set is built");
+    if (lattice->form != LBM_FORM_MOMENT) return fail(LBM_ERR_ARG, "only the moment form is built");
+    if (lattice->omega != 1.0) return fail(LBM_ERR_ARG, "omega = dt/tau must be 1 (tau = dt)");
+    if (lattice->storage != LBM_F64 && lattice->storage != LBM_F32) return fail(LBM_ERR_ARG, "storage must be F64 or F32");
+    if (lattice->bc_mode != LBM_BC_BOUNCEBACK && lattice->bc_mode != LBM_BC_MACROSCOPIC)
+        return fail(LBM_ERR_ARG, "unknown crack-face mode");
+    if (!(material->rho > 0.0) || !(material->mu > 0.0) || !std::isfinite(material->rho) || !std::isfinite(material->mu))
+        return fail(LBM_ERR_ARG, "rho and mu must be positive and finite");
+    const double cs = std::sqrt(material->mu / material->rho);
+    const double g = cs * cs * grid->dt / (grid->dh * grid->dh);
+    if (g * grid->dt > 0.5) return fail(LBM_ERR_ARG, "unstable: c_s^2 dt^2 / dh^2 > 1/2");
+
+    lbm_crack cr;
+    std::memset(&cr, 0, sizeof cr);
+    if (crack) cr = *crack;
+    if (cr.mode < LBM_CRACK_NONE || cr.mode > LBM_CRACK_KCRIT) return fail(LBM_ERR_ARG, "unknown crack mode");
+    int32_t jc = 0;
+    int64_t start_q = 0, tip_q = 0;
+    const int64_t qone = (int64_t)1 << kQBits;
+    const int64_t clamp_q = (int64_t)(grid->nx - 1) * qone;
+    if (cr.mode != LBM_CRACK_NONE) {
+        const double yj = cr.y / grid->dh;
+        if (!std::isfinite(yj) || std::fabs(yj - std::nearbyint(yj)) > 1e-9)
+            return fail(LBM_ERR_ARG, "the crack line y must be a multiple of dh (between two rows)");
+        jc = (int32_t)std::nearbyint(yj);
+        const int margin = lattice->bc_mode == LBM_BC_MACROSCOPIC ? 3 : 1;
+        if (jc < margin || jc > grid->ny - margin)
+            return fail(LBM_ERR_ARG, "the crack line is too close to the bottom or top edge");
+        if (!(cr.x_start >= 0.0) || !(cr.x_tip >= cr.x_start)) return fail(LBM_ERR_ARG, "need 0 <= x_start <= x_tip");
+        start_q = llrint(cr.x_start / grid->dh * 4294967296.0);
+        tip_q = llrint(cr.x_tip / grid->dh * 4294967296.0);
+        if (tip_q >= clamp_q) return fail(LBM_ERR_ARG, "the initial tip must lie left of x = (nx - 1) dh");
+        if (lattice->bc_mode == LBM_BC_MACROSCOPIC && grid->edge[LBM_LEFT] == LBM_EDGE_PERIODIC)
+            return fail(LBM_ERR_ARG, "macroscopic crack faces need non-periodic left/right edges");
+        if (cr.mode == LBM_CRACK_PRESCRIBED && !(cr.v_rel >= 0.0 && cr.v_rel < 1.0))
+            return fail(LBM_ERR_ARG, "prescribed v_rel must lie in [0, 1)");
+        if (cr.mode == LBM_CRACK_KCRIT && !(cr.K_C > 0.0 && cr.v_max >= 0.0 && cr.v_max < 1.0))
+            return fail(LBM_ERR_ARG, "K-criterion needs K_C > 0 and 0 <= v_max < 1");
+        if (!(cr.r_min > 0.0) && !(cr.r0 >= 0.0)) return fail(LBM_ERR_ARG, "r0 must be >= 0");
+        if (!(cr.fit_width > 0.0)) cr.fit_width = grid->dh;
+        if (cr.hist_cap <= 0) cr.hist_cap = kDefaultHistCap;
+    }
+    if (n_loads < 0 || (n_loads > 0 && !loads)) return fail(LBM_ERR_ARG, "bad loads array");
+
+    lbm_handle *h = new (std::nothrow) lbm_handle;
+    if (!h) return fail(LBM_ERR_OOM, "host allocation failed");
+    std::memset(h, 0, sizeof *h);
+    h->grid = *grid;
+    h->lat = *lattice;
+    h->mat = *material;
+    h->crack = cr;
+    h->esize = lattice->storage == LBM_F32 ? 4 : 8;
+    h->g = g;
+    h->stream = (cudaStream_t)stream;
+    h->sticky = LBM_OK;
+    h->gparity = -1;
+    if (allocator && allocator->alloc && allocator->release) {
+        h->alloc = *allocator;
+        h->custom_alloc = true;
+    }
+    std::memset(h->load, 0, sizeof h->load);
+    std::vector<int> seen(4, 0);
+    for (int q = 0; q < n_loads; ++q) {
+        const lbm_loading &L = loads[q];
+        if (L.edge < 0 || L.edge > 3 || seen[L.edge]) { delete h; return fail(LBM_ERR_ARG, "bad or repeated load edge"); }
+        if (L.kind < LBM_LOAD_ZERO || L.kind > LBM_LOAD_CONST) { delete h; return fail(LBM_ERR_ARG, "unknown load kind"); }
+        if (L.kind == LBM_LOAD_SERIES && (!L.series || L.n_series <= 0)) { delete h; return fail(LBM_ERR_ARG, "series load without data"); }
+        seen[L.edge] = 1;
+        h->load[L.edge].kind = L.kind;
+        h->load[L.edge].amp = L.amp;
+        h->load[L.edge].t = L.t_ramp;
+        h->load[L.edge].n = L.kind == LBM_LOAD_SERIES ? L.n_series : 0;
+    }
+
+    set_launch(h, 0);
+    const int vec = (int)(16 / h->esize);
+    const int64_t xoff = 128 / (int64_t)h->esize;
+    const int64_t cover = (int64_t)h->bulk_grid.x * kBulkThreads * vec;
+    h->pitch = xoff + cover + xoff;
+    h->words = (grid->nx + 31) / 32;
+    const int64_t hcap = cr.mode != LBM_CRACK_NONE ? cr.hist_cap : 1;
+
+    // one block for everything, carved at 256-byte boundaries
+    const size_t plane = (size_t)(grid->ny + 2) * (size_t)h->pitch * h->esize;
+    const size_t mask = (size_t)grid->ny * (size_t)h->words * 4;
+    size_t off = 0;
+    const size_t o_w0 = off; off = align256(off + plane);
+    const size_t o_w1 = off; off = align256(off + plane);
+    const size_t o_wd = off; off = align256(off + plane);
+    const size_t o_ch = off; off = align256(off + mask);
+    const size_t o_cv = off; off = align256(off + mask);
+    const size_t o_rf = off; off = align256(off + (size_t)grid->ny);
+    const size_t o_st = off; off = align256(off + sizeof(CrackState));
+    const size_t o_hK = off; off = align256(off + (size_t)hcap * 8);
+    const size_t o_hv = off; off = align256(off + (size_t)hcap * 8);
+    const size_t o_ht = off; off = align256(off + (size_t)hcap * 8);
+    const size_t o_hn = off; off = align256(off + (size_t)hcap * 4);
+    size_t o_ser[4];
+    for (int e = 0; e < 4; ++e) { o_ser[e] = off; off = align256(off + (size_t)h->load[e].n * 8); }
+    h->block_bytes = off;
+    h->block = dev_alloc(h, off);
+    if (!h->block) { delete h; return fail(LBM_ERR_OOM, "device allocation failed"); }
+    char *base = static_cast<char *>(h->block);
+    const size_t origin = ((size_t)h->pitch + (size_t)xoff) * h->esize;   // row 0, column 0
+    h->w[0] = base + o_w0 + origin;
+    h->w[1] = base + o_w1 + origin;
+    h->wd = base + o_wd + origin;
+    h->cut_h = reinterpret_cast<uint32_t *>(base + o_ch);
+    h->cut_v = reinterpret_cast<uint32_t *>(base + o_cv);
+    h->rowflag = reinterpret_cast<uint8_t *>(base + o_rf);
+    h->st = reinterpret_cast<CrackState *>(base + o_st);
+    h->hist.K = reinterpret_cast<double *>(base + o_hK);
+    h->hist.v = reinterpret_cast<double *>(base + o_hv);
+    h->hist.tip = reinterpret_cast<int64_t *>(base + o_ht);
+    h->hist.np = reinterpret_cast<int32_t *>(base + o_hn);
+
+    cudaStream_t s = h->stream;
+    lbm_status rc = LBM_OK;
+    auto bail = [&](cudaError_t e, const char *what) {
+        rc = cuda_fail(e, what);
+        cudaStreamSynchronize(s);
+        dev_free(h, h->block);
+        delete h;
+        return rc;
+    };
+    cudaError_t e = cudaMemsetAsync(h->block, 0, h->block_bytes, s);
+    if (e != cudaSuccess) return bail(e, "clearing device state");
+    for (int q = 0; q < 4; ++q) {
+        if (h->load[q].kind != LBM_LOAD_SERIES) continue;
+        const lbm_loading *L = nullptr;
+        for (int r = 0; r < n_loads; ++r) if (loads[r].edge == q) L = &loads[r];
+        double *dser = reinterpret_cast<double *>(base + o_ser[q]);
+        e = cudaMemcpyAsync(dser, L->series, (size_t)L->n_series * 8, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return bail(e, "copying a load series");
+        h->load[q].series = dser;
+    }
+
+    // crack parameters and the initial severed links (all x_start <= x_i <= x_tip)
+    CrackParams &cp = h->cp;
+    std::memset(&cp, 0, sizeof cp);
+    cp.mode = cr.mode;
+    cp.jc = jc;
+    cp.nx = grid->nx;
+    cp.ny = grid->ny;
+    cp.macro = lattice->bc_mode == LBM_BC_MACROSCOPIC;
+    cp.words = h->words;
+    cp.mu = material->mu;
+    cp.cs = cs;
+    cp.dt = grid->dt;
+    cp.dh = grid->dh;
+    cp.K_C = cr.K_C;
+    cp.v_max = cr.v_max;
+    cp.r0 = cr.r0;
+    cp.r_min_fixed = cr.r_min;
+    cp.fit_width = cr.fit_width;
+    cp.v_rel = cr.v_rel;
+    cp.start_q = start_q;
+    cp.clamp_q = clamp_q;
+    cp.hist_cap = cr.mode != LBM_CRACK_NONE ? cr.hist_cap : 0;
+
+    CrackState hs;
+    std::memset(&hs, 0, sizeof hs);
+    hs.tip_q = tip_q;
+    hs.i_first = 0;
+    hs.i_last = -1;
+    if (cr.mode != LBM_CRACK_NONE) {
+        const int64_t half = qone / 2;
+        int64_t first = -floor_div(-(start_q - half), qone);   // ceil((start - 1/2) / 1)
+        int64_t last = floor_div(tip_q - half, qone);
+        if (first < 0) first = 0;
+        if (last > grid->nx - 1) last = grid->nx - 1;
+        hs.i_first = (int32_t)first;
+        hs.i_last = (int32_t)(last < first ? first - 1 : last);
+        hs.v_prev = cr.mode == LBM_CRACK_PRESCRIBED ? cr.v_rel : 0.0;
+        if (hs.i_last >= hs.i_first) {
+            std::vector<uint32_t> row((size_t)h->words, 0u);
+            for (int i = hs.i_first; i <= hs.i_last; ++i) row[(size_t)(i >> 5)] |= 1u << (i & 31);
+            std::vector<uint8_t> rf((size_t)grid->ny, 0);
+            rf[(size_t)(jc - 1)] |= 2;
+            rf[(size_t)jc] |= 4;
+            e = cudaMemcpyAsync(h->cut_v + (size_t)(jc - 1) * h->words, row.data(), row.size() * 4, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(h->rowflag, rf.data(), rf.size(), cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // host vectors go out of scope
+            if (e != cudaSuccess) return bail(e, "writing the initial crack");
+        }
+    }
+    e = cudaMemcpyAsync(h->st, &hs, sizeof hs, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_wstar(h->st, h->load, h->grid.edge, grid->dt, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return bail(e, "initialising the crack state");
+    e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(e, "creating the capture stream");
+    *out = h;
+    g_err.clear();
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_handle *h, int64_t n)
+{
+    if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
+    if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");
+    if (n < 0) return fail(LBM_ERR_ARG, "n must be >= 0");
+    if (h->profiling) {
+        for (; n > 0; --n) {
+            LBM_CUDA(enqueue_step_profiled(h, h->parity, h->stream));
+            h->parity ^= 1;
+        }
+        return LBM_OK;
+    }
+    while (n > 0) {
+        if (n >= kGraphChunk) {
+            if (!h->gexec) {
+                cudaGraph_t graph;
+                LBM_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+                cudaError_t ce = cudaSuccess;
+                int par = h->parity;
+                for (int64_t q = 0; q < kGraphChunk && ce == cudaSuccess; ++q) {
+                    ce = enqueue_step(h, par, h->cap_stream);
+                    par ^= 1;
+                }
+                cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &graph);
+                if (ce != cudaSuccess) return cuda_fail(ce, "capturing the step graph");
+                if (ee != cudaSuccess) return cuda_fail(ee, "cudaStreamEndCapture");
+                ee = cudaGraphInstantiate(&h->gexec, graph, 0);
+                cudaGraphDestroy(graph);
+                if (ee != cudaSuccess) { h->gexec = nullptr; return cuda_fail(ee, "cudaGraphInstantiate"); }
+                h->gparity = h->parity;
+            }
+            if (h->parity == h->gparity) {
+                LBM_CUDA(cudaGraphLaunch(h->gexec, h->stream));
+                n -= kGraphChunk;
+                continue;
+            }
+        }
+        LBM_CUDA(enqueue_step(h, h->parity, h->stream));
+        h->parity ^= 1;
+        n -= 1;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_fields(lbm_handle *h, int32_t which, void *dst, int32_t dst_on_device, int32_t dtype)
+{
+    if (!h || !dst) return fail(LBM_ERR_ARG, "handle or dst is NULL");
+    if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");
+    if (which != LBM_FIELD_W && which != LBM_FIELD_WDOT) return fail(LBM_ERR_ARG, "unknown field");
+    if (dtype != h->lat.storage) return fail(LBM_ERR_ARG, "dtype must equal the storage precision");
+    const void *src = which == LBM_FIELD_W ? h->w[h->parity] : h->wd;
+    const size_t row = (size_t)h->grid.nx * h->esize;
+    LBM_CUDA(cudaMemcpy2DAsync(dst, row, src, (size_t)h->pitch * h->esize, row, (size_t)h->grid.ny,
+                               dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    if (!dst_on_device) return check_sticky(h);
+    return LBM_OK;
+}
+
+lbm_status lbm_set_fields(lbm_handle *h, int32_t which, const void *src, int32_t src_on_device, int32_t dtype)
+{
+    if (!h || !src) return fail(LBM_ERR_ARG, "handle or src is NULL");
+    if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");
+    if (which != LBM_FIELD_W && which != LBM_FIELD_WDOT) return fail(LBM_ERR_ARG, "unknown field");
+    if (dtype != h->lat.storage) return fail(LBM_ERR_ARG, "dtype must equal the storage precision");
+    void *dst = which == LBM_FIELD_W ? h->w[h->parity] : h->wd;
+    const size_t row = (size_t)h->grid.nx * h->esize;
+    LBM_CUDA(cudaMemcpy2DAsync(dst, (size_t)h->pitch * h->esize, src, row, row, (size_t)h->grid.ny,
+                               src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    if (which == LBM_FIELD_W) {
+        cudaError_t e = h->lat.storage == LBM_F32
+            ? launch_fill_pads<float>(static_cast<float *>(dst), h->pitch, h->grid.nx, h->grid.ny, h->grid.edge, h->stream)
+            : launch_fill_pads<double>(static_cast<double *>(dst), h->pitch, h->grid.nx, h->grid.ny, h->grid.edge, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "filling periodic pads");
+    }
+    if (!src_on_device) LBM_CUDA(cudaStreamSynchronize(h->stream));   // pageable source may be reused
+    return LBM_OK;
+}
+
+lbm_status lbm_cut_mask(lbm_handle *h, int32_t which, uint32_t *dst_host, int64_t n_words)
+{
+    if (!h || !dst_host) return fail(LBM_ERR_ARG, "handle or dst is NULL");
+    if (which != LBM_MASK_H && which != LBM_MASK_V) return fail(LBM_ERR_ARG, "unknown mask");
+    const int64_t need = (int64_t)h->grid.ny * h->words;
+    if (n_words < need) return fail(LBM_ERR_ARG, "dst too small");
+    LBM_CUDA(cudaMemcpyAsync(dst_host, which == LBM_MASK_H ? h->cut_h : h->cut_v, (size_t)need * 4,
+                             cudaMemcpyDeviceToHost, h->stream));
+    return check_sticky(h);
+}
+
+lbm_status lbm_crack_state(lbm_handle *h, lbm_crack_state_t *now, double *K_hist, double *v_hist,
+                           int64_t *tip_hist, int32_t *npairs_hist, int64_t cap, int64_t *n_written)
+{
+    if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
+    CrackState hs;
+    LBM_CUDA(cudaMemcpyAsync(&hs, h->st, sizeof hs, cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA(cudaStreamSynchronize(h->stream));
+    if (now) {
+        now->step = hs.step;
+        now->tip_q = hs.tip_q;
+        now->n_cut = hs.i_last >= hs.i_first ? (int64_t)(hs.i_last - hs.i_first + 1) : 0;
+        now->hist_n = hs.hist_n;
+        now->tip_x = (double)hs.tip_q * kTwoM32 * h->grid.dh;
+        now->K = hs.K;
+        now->v = hs.v;
+        now->r_min = hs.r_min;
+        now->npairs = hs.npairs;
+        now->flags = hs.flags;
+    }
+    int64_t n = 0;
+    const int64_t hcap = h->cp.hist_cap;
+    if (cap > 0 && hcap > 0) {
+        n = hs.hist_n < hcap ? hs.hist_n : hcap;
+        if (n > cap) n = cap;
+        const int64_t first = hs.hist_n - n;
+        std::vector<double> K((size_t)hcap), v((size_t)hcap);
+        std::vector<int64_t> tip((size_t)hcap);
+        std::vector<int32_t> np((size_t)hcap);
+        LBM_CUDA(cudaMemcpyAsync(K.data(), h->hist.K, (size_t)hcap * 8, cudaMemcpyDeviceToHost, h->stream));
+        LBM_CUDA(cudaMemcpyAsync(v.data(), h->hist.v, (size_t)hcap * 8, cudaMemcpyDeviceToHost, h->stream));
+        LBM_CUDA(cudaMemcpyAsync(tip.data(), h->hist.tip, (size_t)hcap * 8, cudaMemcpyDeviceToHost, h->stream));
+        LBM_CUDA(cudaMemcpyAsync(np.data(), h->hist.np, (size_t)hcap * 4, cudaMemcpyDeviceToHost, h->stream));
+        LBM_CUDA(cudaStreamSynchronize(h->stream));
+        for (int64_t q = 0; q < n; ++q) {
+            const size_t r = (size_t)((first + q) % hcap);
+            if (K_hist) K_hist[q] = K[r];
+            if (v_hist) v_hist[q] = v[r];
+            if (tip_hist) tip_hist[q] = tip[r];
+            if (npairs_hist) npairs_hist[q] = np[r];
+        }
+    }
+    if (n_written) *n_written = n;
+    if (hs.flags & FLAG_NONFINITE) {
+        h->sticky = LBM_ERR_UNSTABLE;
+        return fail(LBM_ERR_UNSTABLE, "non-finite value in the fields or in K");
+    }
+    return h->sticky;
+}
+
+lbm_status lbm_sync(lbm_handle *h)
+{
+    if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
+    if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");
+    return check_sticky(h);
+}
+
+lbm_status lbm_set_stream(lbm_handle *h, void *stream)
+{
+    if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
+    h->stream = (cudaStream_t)stream;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_launch(lbm_handle *h, int32_t rows_per_cta)
+{
+    if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
+    if (rows_per_cta < 0 || rows_per_cta > 4096) return fail(LBM_ERR_ARG, "rows_per_cta out of range");
+    LBM_CUDA(cudaStreamSynchronize(h->stream));
+    if (h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+        h->gparity = -1;
+    }
+    set_launch(h, rows_per_cta);
+    return LBM_OK;
+}
+
+lbm_status lbm_get_launch(const lbm_handle *h, int32_t *rows_per_cta, int32_t *grid_x, int32_t *grid_y)
+{
+    if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
+    if (rows_per_cta) *rows_per_cta = h->rows;
+    if (grid_x) *grid_x = (int32_t)h->bulk_grid.x;
+    if (grid_y) *grid_y = (int32_t)h->bulk_grid.y;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_profiling(lbm_handle *h, int32_t enable)
+{
+    if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
+    if (enable && !h->ev) {
+        h->ev = new (std::nothrow) std::vector<cudaEvent_t>(3 * 1024);
+        if (!h->ev) return fail(LBM_ERR_OOM, "host allocation failed");
+        for (auto &e : *h->ev) {
+            cudaError_t ce = cudaEventCreate(&e);
+            if (ce != cudaSuccess) return cuda_fail(ce, "cudaEventCreate");
+        }
+        h->ev_used = 0;
+    }
+    if (!enable && h->ev) LBM_CUDA(drain_profile(h));
+    h->profiling = enable ? 1 : 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_profile_read(lbm_handle *h, double *bulk_ms, int64_t *n_bulk, double *crack_ms, int64_t *n_crack,
+                            int32_t reset)
+{
+    if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
+    LBM_CUDA(drain_profile(h));
+    if (bulk_ms) *bulk_ms = h->bulk_ms;
+    if (n_bulk) *n_bulk = h->n_bulk;
+    if (crack_ms) *crack_ms = h->crack_ms;
+    if (n_crack) *n_crack = h->n_crack;
+    if (reset) {
+        h->bulk_ms = h->crack_ms = 0.0;
+        h->n_bulk = h->n_crack = 0;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_device_bytes(const lbm_handle *h, int64_t *bytes)
+{
+    if (!h || !bytes) return fail(LBM_ERR_ARG, "handle or bytes is NULL");
+    *bytes = (int64_t)h->block_bytes;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_handle *h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->ev) {
+        for (auto &e : *h->ev) cudaEventDestroy(e);
+        delete h->ev;
+    }
+    dev_free(h, h->block);
+    delete h;
+}
+
+const char *lbm_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,331 @@
+"""Python binding of liblbm.so: the C-ABI calls under their own names, plus a
+small ``Lattice`` convenience class driven by a problem dict.
+
+Argument marshalling only -- every step of the method runs in the library's
+CUDA kernels.  There is no CPU path: if the library cannot be loaded, every
+call raises.  Device memory comes from PyTorch's caching allocator (passed to
+``lbm_create`` as the allocator callbacks) and work is enqueued on the current
+PyTorch CUDA stream unless another stream is given.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import _abi as A
+
+_lib = None
+_lib_lock = threading.Lock()
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{A.STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def library_path() -> str:
+    from .build import LIB_PATH
+    return LIB_PATH
+
+
+def load_library():
+    """Load liblbm.so (building it in-tree first if it is missing or stale)."""
+    global _lib
+    with _lib_lock:
+        if _lib is None:
+            from . import build as _build
+            if _build.is_stale():
+                _build.build()
+            lib = C.CDLL(_build.LIB_PATH)
+            for name, (res, args) in A.PROTOTYPES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(status: int):
+    if status != A.LBM_OK:
+        msg = load_library().lbm_last_error()
+        raise LbmError(status, msg.decode() if msg else "")
+
+
+# ----------------------------------------------------------- C-ABI calls
+
+def lbm_create(grid: A.Grid, lattice: A.Lattice_, material: A.Material, crack: A.Crack | None,
+               loads, stream: int = 0, allocator: A.Allocator | None = None) -> int:
+    lib = load_library()
+    n = len(loads)
+    arr = (A.Loading * max(n, 1))(*loads) if n else None
+    out = C.c_void_p()
+    _check(lib.lbm_create(C.byref(grid), C.byref(lattice), C.byref(material),
+                          C.byref(crack) if crack is not None else None,
+                          arr, n, C.c_void_p(stream), C.byref(allocator) if allocator is not None else None,
+                          C.byref(out)))
+    return out.value
+
+
+def lbm_step(h: int, n: int):
+    _check(load_library().lbm_step(C.c_void_p(h), int(n)))
+
+
+def lbm_fields(h: int, which: int, dst_ptr: int, on_device: bool, dtype: int):
+    _check(load_library().lbm_fields(C.c_void_p(h), which, C.c_void_p(dst_ptr), int(bool(on_device)), dtype))
+
+
+def lbm_set_fields(h: int, which: int, src_ptr: int, on_device: bool, dtype: int):
+    _check(load_library().lbm_set_fields(C.c_void_p(h), which, C.c_void_p(src_ptr), int(bool(on_device)), dtype))
+
+
+def lbm_cut_mask(h: int, which: int, dst: np.ndarray):
+    assert dst.dtype == np.uint32 and dst.flags.c_contiguous
+    _check(load_library().lbm_cut_mask(C.c_void_p(h), which, dst.ctypes.data_as(C.POINTER(C.c_uint32)), dst.size))
+
+
+def lbm_crack_state(h: int, cap: int = 0):
+    st = A.CrackStateT()
+    K = np.zeros(max(cap, 1)); v = np.zeros(max(cap, 1))
+    tip = np.zeros(max(cap, 1), np.int64); np_ = np.zeros(max(cap, 1), np.int32)
+    nw = C.c_int64(0)
+    d = C.POINTER(C.c_double)
+    _check(load_library().lbm_crack_state(
+        C.c_void_p(h), C.byref(st), K.ctypes.data_as(d), v.ctypes.data_as(d),
+        tip.ctypes.data_as(C.POINTER(C.c_int64)), np_.ctypes.data_as(C.POINTER(C.c_int32)), cap, C.byref(nw)))
+    n = nw.value
+    return st, {"K": K[:n], "v": v[:n], "tip_q": tip[:n], "npairs": np_[:n]}
+
+
+def lbm_sync(h: int):
+    _check(load_library().lbm_sync(C.c_void_p(h)))
+
+
+def lbm_set_stream(h: int, stream: int):
+    _check(load_library().lbm_set_stream(C.c_void_p(h), C.c_void_p(stream)))
+
+
+def lbm_set_launch(h: int, rows_per_cta: int):
+    _check(load_library().lbm_set_launch(C.c_void_p(h), int(rows_per_cta)))
+
+
+def lbm_get_launch(h: int):
+    r, gx, gy = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(load_library().lbm_get_launch(C.c_void_p(h), C.byref(r), C.byref(gx), C.byref(gy)))
+    return r.value, gx.value, gy.value
+
+
+def lbm_set_profiling(h: int, enable: bool):
+    _check(load_library().lbm_set_profiling(C.c_void_p(h), int(bool(enable))))
+
+
+def lbm_profile_read(h: int, reset: bool = False):
+    bm, cm = C.c_double(), C.c_double()
+    nb, nc = C.c_int64(), C.c_int64()
+    _check(load_library().lbm_profile_read(C.c_void_p(h), C.byref(bm), C.byref(nb), C.byref(cm), C.byref(nc),
+                                           int(bool(reset))))
+    return {"bulk_ms": bm.value, "n_bulk": nb.value, "crack_ms": cm.value, "n_crack": nc.value}
+
+
+def lbm_device_bytes(h: int) -> int:
+    b = C.c_int64()
+    _check(load_library().lbm_device_bytes(C.c_void_p(h), C.byref(b)))
+    return b.value
+
+
+def lbm_destroy(h: int):
+    if h:
+        load_library().lbm_destroy(C.c_void_p(h))
+
+
+def lbm_last_error() -> str:
+    return load_library().lbm_last_error().decode()
+
+
+# ------------------------------------------------- problem dict -> structs
+
+def make_structs(problem: dict, storage: str = "f32"):
+    """C structs for a problem dict (the same dict the oracle reads)."""
+    g = A.Grid()
+    g.nx, g.ny = int(problem["nx"]), int(problem["ny"])
+    g.dh, g.dt = float(problem.get("dh", 1.0)), float(problem.get("dt", 1.0))
+    edges = problem.get("edges", ("free", "free", "dirichlet", "dirichlet"))
+    for e in range(4):
+        g.edge[e] = A.EDGE[edges[e]]
+    lat = A.Lattice_()
+    lat.velocity_set, lat.form = 0, 0
+    lat.omega = float(problem.get("omega", 1.0))
+    lat.storage = A.STORAGE[storage]
+    lat.bc_mode = A.BC[problem.get("bc_mode", "bounceback")]
+    mat = A.Material()
+    mat.rho, mat.mu = float(problem.get("rho", 1.0)), float(problem["mu"])
+    cr = A.Crack()
+    c = problem.get("crack") or {"mode": "none"}
+    cr.mode = A.CRACK[c.get("mode", "none")]
+    if cr.mode:
+        cr.y = float(c["y"])
+        cr.x_start, cr.x_tip = float(c.get("x_start", 0.0)), float(c["x_tip"])
+        cr.v_rel = float(c.get("v_rel", 0.0))
+        cr.K_C = float(c.get("K_C", 0.0))
+        cr.v_max = float(c.get("v_max", 0.85))
+        cr.r0 = float(c.get("r0", 2.0 * g.dh))
+        cr.r_min = float(c.get("r_min", 0.0))
+        cr.fit_width = float(c.get("fit_width", g.dh))
+        cr.hist_cap = int(problem.get("hist_cap", 1 << 16))
+    loads = []
+    keep = []
+    for ld in problem.get("loads", []):
+        L = A.Loading()
+        L.edge = A.EDGE_INDEX[ld["edge"]]
+        L.kind = A.LOAD[ld["kind"]]
+        L.amp = float(ld.get("amp", 0.0))
+        L.t_ramp = float(ld.get("t", 0.0))
+        if ld["kind"] == "series":
+            arr = np.ascontiguousarray(ld["series"], dtype=np.float64)
+            keep.append(arr)
+            L.series = arr.ctypes.data_as(C.POINTER(C.c_double))
+            L.n_series = arr.size
+        loads.append(L)
+    return g, lat, mat, cr, loads, keep
+
+
+class TorchAllocator:
+    """lbm_allocator callbacks backed by torch's CUDA caching allocator."""
+
+    def __init__(self, stream: int):
+        import torch
+        self._torch = torch
+        self._stream = stream
+
+        def _alloc(nbytes, ctx):
+            try:
+                return self._torch.cuda.caching_allocator_alloc(int(nbytes), stream=self._stream or None)
+            except Exception:
+                return None
+
+        def _release(ptr, ctx):
+            if ptr:
+                self._torch.cuda.caching_allocator_delete(ptr)
+
+        self._fa = A.ALLOC_FN(_alloc)
+        self._fr = A.RELEASE_FN(_release)
+        self.struct = A.Allocator(self._fa, self._fr, None)
+
+
+class Lattice:
+    """One lattice handle on the current CUDA device.
+
+    problem: dict with nx, ny, dh, dt, edges, rho, mu, omega, bc_mode, crack,
+    loads, hist_cap (see ``workloads``).  storage: "f32" or "f64"."""
+
+    def __init__(self, problem: dict, storage: str = "f32", stream=None, torch_allocator: bool = True):
+        import torch
+        self.torch = torch
+        self.problem = problem
+        self.storage = storage
+        self.nx, self.ny = int(problem["nx"]), int(problem["ny"])
+        self.np_dtype = np.float32 if storage == "f32" else np.float64
+        self.torch_dtype = torch.float32 if storage == "f32" else torch.float64
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream_obj = stream
+        self.stream = int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+        g, lat, mat, cr, loads, keep = make_structs(problem, storage)
+        self._alloc = TorchAllocator(self.stream) if torch_allocator else None
+        self.h = lbm_create(g, lat, mat, cr if cr.mode else None, loads, self.stream,
+                            self._alloc.struct if self._alloc else None)
+        del keep
+
+    @property
+    def dtype_code(self) -> int:
+        return A.STORAGE[self.storage]
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def step(self, n: int = 1):
+        lbm_step(self.h, n)
+
+    def set_launch(self, rows_per_cta: int):
+        lbm_set_launch(self.h, rows_per_cta)
+
+    def launch(self):
+        return lbm_get_launch(self.h)
+
+    def set_fields(self, w=None, wdot=None):
+        for which, arr in (("w", w), ("wdot", wdot)):
+            if arr is None:
+                continue
+            if isinstance(arr, self.torch.Tensor) and arr.is_cuda:
+                t = arr.to(self.torch_dtype).contiguous()
+                assert t.numel() == self.nx * self.ny
+                lbm_set_fields(self.h, A.FIELD[which], t.data_ptr(), True, self.dtype_code)
+                self.torch.cuda.current_stream().synchronize()
+            else:
+                a = np.ascontiguousarray(np.asarray(arr, dtype=self.np_dtype).reshape(self.ny, self.nx))
+                lbm_set_fields(self.h, A.FIELD[which], a.ctypes.data, False, self.dtype_code)
+
+    def fields(self):
+        """(w, wdot) as host numpy arrays of shape (ny, nx)."""
+        out = []
+        for which in ("w", "wdot"):
+            a = np.empty((self.ny, self.nx), self.np_dtype)
+            lbm_fields(self.h, A.FIELD[which], a.ctypes.data, False, self.dtype_code)
+            out.append(a)
+        return tuple(out)
+
+    def fields_device(self):
+        """(w, wdot) as CUDA tensors (copies, enqueued on the handle's stream)."""
+        out = []
+        for which in ("w", "wdot"):
+            t = self.torch.empty((self.ny, self.nx), dtype=self.torch_dtype, device="cuda")
+            lbm_fields(self.h, A.FIELD[which], t.data_ptr(), True, self.dtype_code)
+            out.append(t)
+        return tuple(out)
+
+    def cut_mask(self, which: str = "v") -> np.ndarray:
+        """Severed links as a (ny, nx) bool array (H: link to i+1, V: link to j+1)."""
+        words = (self.nx + 31) // 32
+        raw = np.zeros(self.ny * words, np.uint32)
+        lbm_cut_mask(self.h, A.MASK[which], raw)
+        bits = np.unpackbits(raw.view(np.uint8).reshape(self.ny, words * 4), axis=1, bitorder="little")
+        return bits[:, : self.nx].astype(bool)
+
+    def crack_state(self, cap: int = 0):
+        st, hist = lbm_crack_state(self.h, cap)
+        d = {k: getattr(st, k) for k, _ in A.CrackStateT._fields_}
+        return (d, hist) if cap else d
+
+    def history(self, cap: int | None = None) -> dict:
+        if cap is None:
+            cap = int(self.problem.get("hist_cap", 1 << 16))
+        return lbm_crack_state(self.h, cap)[1]
+
+    def sync(self):
+        lbm_sync(self.h)
+
+    def set_profiling(self, enable: bool = True):
+        lbm_set_profiling(self.h, enable)
+
+    def profile(self, reset: bool = False) -> dict:
+        return lbm_profile_read(self.h, reset)
+
+    def device_bytes(self) -> int:
+        return lbm_device_bytes(self.h)

@@ -1,0 +1,125 @@
+"""The C-ABI library builds, loads and exports what include/lbm.h declares;
+its struct layouts agree with the Python binding; argument validation
+rejects bad configurations before touching a GPU.  No CUDA device needed."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2206_12412_gb300 import _abi as A
+from paper_2206_12412_gb300 import build as B
+from paper_2206_12412_gb300 import lbm
+
+HEADER = os.path.join(B.INCLUDE, "lbm.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return lbm.load_library()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_core_calls():
+    names = declared_functions()
+    for core in ("lbm_create", "lbm_step", "lbm_fields", "lbm_crack_state", "lbm_destroy"):
+        assert core in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB_PATH], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(lbm_\w+)", out))
+    for name in declared_functions():
+        assert name in exported, name
+        assert hasattr(lib, name)
+        assert name in A.PROTOTYPES, name
+
+
+def test_struct_layout_matches_header(tmp_path):
+    structs = {"lbm_grid": A.Grid, "lbm_lattice": A.Lattice_, "lbm_material": A.Material, "lbm_crack": A.Crack,
+               "lbm_loading": A.Loading, "lbm_allocator": A.Allocator, "lbm_crack_state_t": A.CrackStateT}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "lbm.h"', "int main(void){"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("return 0;}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", B.INCLUDE, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for l in out:
+        if l:
+            c, f, v = l.split()
+            got[(c, f)] = int(v)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == C.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def _structs(**over):
+    from paper_2206_12412_gb300 import workloads as W
+    p = W.plain_fp64()
+    p.update(over.pop("problem", {}))
+    g, lat, mat, cr, loads, keep = lbm.make_structs(p, over.pop("storage", "f64"))
+    for k, v in over.items():
+        obj, field = k.split("__")
+        setattr({"g": g, "lat": lat, "mat": mat, "cr": cr}[obj], field, v)
+    return g, lat, mat, cr, loads, keep
+
+
+@pytest.mark.parametrize("over,msg", [
+    ({"g__nx": 0}, "nx"),
+    ({"g__ny": 1}, "ny"),
+    ({"g__dh": 0.0}, "dh"),
+    ({"g__dt": float("nan")}, "dt"),
+    ({"lat__omega": 0.8}, "omega"),
+    ({"lat__storage": 7}, "storage"),
+    ({"lat__velocity_set": 3}, "D2Q5"),
+    ({"mat__mu": 2.0}, "unstable"),
+    ({"mat__rho": -1.0}, "rho"),
+    ({"cr__y": 64.5}, "multiple of dh"),
+    ({"cr__y": 2.0}, "too close"),
+    ({"cr__x_tip": 127.5}, "left of"),
+    ({"cr__x_start": 40.0}, "x_start"),
+    ({"cr__mode": 9}, "crack mode"),
+])
+def test_create_rejects_bad_arguments(lib, over, msg):
+    g, lat, mat, cr, loads, keep = _structs(**over)
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_create(g, lat, mat, cr, loads, 0, None)
+    assert ei.value.status == A.LBM_ERR_ARG
+    assert msg in str(ei.value)
+
+
+def test_create_rejects_unpaired_periodic_and_bad_loads(lib):
+    g, lat, mat, cr, loads, keep = _structs()
+    g.edge[0] = A.EDGE["periodic"]
+    with pytest.raises(lbm.LbmError, match="pairs"):
+        lbm.lbm_create(g, lat, mat, cr, loads, 0, None)
+    g, lat, mat, cr, loads, keep = _structs()
+    loads[1].edge = loads[0].edge
+    with pytest.raises(lbm.LbmError, match="repeated"):
+        lbm.lbm_create(g, lat, mat, cr, loads, 0, None)
+    g, lat, mat, cr, loads, keep = _structs()
+    loads[0].kind = A.LOAD["series"]
+    with pytest.raises(lbm.LbmError, match="series"):
+        lbm.lbm_create(g, lat, mat, cr, loads, 0, None)
+
+
+def test_null_handles_are_rejected(lib):
+    assert lib.lbm_step(None, 1) == A.LBM_ERR_ARG
+    assert lib.lbm_sync(None) == A.LBM_ERR_ARG
+    assert lib.lbm_fields(None, 0, None, 0, 0) == A.LBM_ERR_ARG
+    assert lib.lbm_crack_state(None, None, None, None, None, None, 0, None) == A.LBM_ERR_ARG
+    lib.lbm_destroy(None)
+    assert lbm.lbm_last_error() != ""
