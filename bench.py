@@ -5,14 +5,15 @@ crack propagation (arXiv 2206.12412) on GB300.
 Workload: the 4096 x 2048 FP32 single run with K-criterion propagation (edge
 crack to x = 512 on the midline, top/bottom ramped to +-2e-3 over 5000
 steps).  One benchmark step is one full time step of the method: the bulk
-stream + collide + integrate kernel over all 8.4 M sites, then the crack-face
-rule and the crack step (K_III evaluation, criterion, advance, link cuts).
+stream + collide + integrate update of all 8.4 M sites with the crack-face
+rule and the crack step (K_III evaluation, criterion, advance, link cuts),
+one fused kernel launch.
 
 Timing: the lattice first runs --prelude steps (load ramp active), then
 --warmup untimed steps; each of the --steps timed steps is bracketed by CUDA
-events on the lattice's stream, with a 256 MiB buffer written between steps
-(outside the events) so that every step starts with a cold L2.  The bulk
-kernel is timed on its own by the library's event hooks.
+events on the lattice's stream, with a 256 MiB buffer written and then read
+between steps (outside the events) so that every step starts with a cold,
+clean L2.  The step kernel is also timed by the library's own event hooks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -41,7 +42,7 @@ METRIC = "GLUPS and HBM GB/s vs GB300 roofline; batched and adjoint vs plain FP3
 UNIT = "GLUPS"
 BYTES_PER_SITE = 16            # FP32 moment form: read w, wdot; write w, wdot
 WORKLOAD = "kcrit_single_4096x2048_f32"
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "bulk_kernel_f32_4096x2048.md")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_kernel_f32_4096x2048.md")
 KERNEL_SOURCE = os.path.join(ROOT, "paper_2206_12412_gb300", "csrc", "lbm_kernels.cu")
 
 
@@ -60,7 +61,7 @@ def measured_peaks():
 
 
 def traffic_from_profile():
-    """Per-launch DRAM bytes of the bulk kernel from the committed ncu summary,
+    """Per-launch DRAM bytes of the step kernel from the committed ncu summary,
     or None if there is none or the kernel source changed since it was taken."""
     try:
         text = open(PROFILE_SUMMARY).read()
@@ -212,10 +213,29 @@ def run_ours(args, rank, world, local):
     lat.step(args.prelude)
     lat.sync()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flush_sum = torch.empty((), dtype=torch.int64, device="cuda")
+
+    def flush_l2():
+        # write a buffer twice the size of L2, then read it back: L2 ends up
+        # holding clean lines of the flush buffer, none of the lattice state
+        flush.fill_(1)
+        flush_sum.copy_(flush.view(torch.int64).sum())
+
+    if args.profile_only:
+        lat.set_profiling(True)
+        for _ in range(args.warmup + args.steps):
+            flush_l2()
+            lat.step(1)
+        lat.sync()
+        prof = lat.profile(reset=True)
+        if rank == 0:
+            print(json.dumps({"profile_only": True, "steps": args.warmup + args.steps, **prof}), flush=True)
+        lat.close()
+        return 0
 
     lat.set_profiling(True)
     for _ in range(args.warmup):
-        flush.zero_()
+        flush_l2()
         lat.step(1)
     lat.sync()
     lat.profile(reset=True)
@@ -227,7 +247,7 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(args.steps):
-        flush.zero_()
+        flush_l2()
         starts[k].record(stream)
         lat.step(1)
         ends[k].record(stream)
@@ -240,9 +260,8 @@ def run_ours(args, rank, world, local):
     lat.set_profiling(False)
     total_s = allmax(step_ms * 1e-3)
     value = world * sites * args.steps / total_s / 1e9
-    bulk_s = prof["bulk_ms"] / max(prof["n_bulk"], 1) * 1e-3
-    crack_s = prof["crack_ms"] / max(prof["n_crack"], 1) * 1e-3
-    achieved = BYTES_PER_SITE * sites / bulk_s / 1e9
+    kern_s = prof["step_ms"] / max(prof["n_step"], 1) * 1e-3
+    achieved = BYTES_PER_SITE * sites / kern_s / 1e9
     peak, peak_kind = measured_peaks()
     traffic = traffic_from_profile()
 
@@ -286,16 +305,15 @@ def run_ours(args, rank, world, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "nx": problem["nx"], "ny": problem["ny"], "storage": "f32",
                    "crack": "kcrit", "bc_mode": problem["bc_mode"], "prelude_steps": args.prelude,
-                   "l2": "256 MiB buffer written between timed steps (outside the events)",
+                   "l2": "flushed between timed steps (256 MiB buffer written then read, outside the events)",
                    "parallelism": f"{world} independent replicas" if world > 1 else "single GPU",
-                   "bulk_launch": dict(zip(("rows_per_cta", "grid_x", "grid_y"), lat.launch()))},
+                   "launch": lat.launch()},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "bulk_kernel<float>", "bulk_ms": bulk_s * 1e3, "crack_ms": crack_s * 1e3,
-                     "bytes_per_site": BYTES_PER_SITE},
+                     "kernel": "step_kernel<float>", "kernel_ms": kern_s * 1e3, "bytes_per_site": BYTES_PER_SITE},
         "e2e": {"value": world * sites * args.steps / e2e_s / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": args.steps,
         "steady_graph_glups": steady,
         "wall_s": wall,
         "clocks": clk,
@@ -318,6 +336,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prelude", type=int, default=2500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-only", action="store_true",
+                    help="only prelude, warm-up and timed steps (for ncu); prints kernel times")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()

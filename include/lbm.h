@@ -16,14 +16,16 @@
  *       criterion (prescribed growth, or the K-criterion with the velocity of
  *       eq. v-tanh), tip advance by Delta a = adot dt, and severing of the
  *       links the new crack segment intersects.
- * All of it runs in this library's CUDA kernels; the library owns the device
- * state.  Conventions shared by every call:
+ * All of it runs in this library's CUDA kernels, one kernel launch per time
+ * step; the library owns the device state.  Conventions shared by every call:
  *   - every call returns lbm_status; nothing throws or exits across the ABI;
  *   - inputs are copied at create; no caller pointer is retained, except the
  *     allocator callbacks and their context, which must outlive the handle;
  *   - lbm_step only enqueues work on the handle's stream; calls that hand data
  *     to the host (lbm_fields to host memory, lbm_cut_mask, lbm_crack_state,
- *     lbm_sync) synchronise that stream;
+ *     lbm_sync) synchronise that stream.  The crack step that follows the last
+ *     enqueued time step is applied (one small kernel) by the next call that
+ *     reads or replaces the state, or by the next lbm_step;
  *   - a device-side error (a non-finite field) is sticky: every later call on
  *     the handle returns LBM_ERR_UNSTABLE;
  *   - lbm_last_error() describes the most recent failure on the calling thread.
@@ -200,22 +202,29 @@ lbm_status lbm_sync(lbm_handle *h);
 /* Move later work to another stream (the caller orders the two streams). */
 lbm_status lbm_set_stream(lbm_handle *h, void *stream);
 
-/* Launch shape of the bulk kernel: each CTA marches over rows_per_cta rows
- * (0 picks the built-in default for the lattice size).  Synchronises the
- * stream and drops the cached step graph. */
-lbm_status lbm_set_launch(lbm_handle *h, int32_t rows_per_cta);
+/* Launch shape of the step kernel.  Each CTA marches over a band of at most
+ * band_rows rows of one column block; 0 picks the built-in partition (the
+ * shortest bands for which every CTA of a step is resident at once).  The rows
+ * next to the crack line (jc-3 .. jc+2 with macroscopic crack faces, jc-1 and
+ * jc otherwise) always form two bands of their own.  Synchronises the stream
+ * and drops the cached step graph. */
+lbm_status lbm_set_launch(lbm_handle *h, int32_t band_rows);
 
-/* Current launch shape of the bulk kernel (any pointer may be NULL). */
-lbm_status lbm_get_launch(const lbm_handle *h, int32_t *rows_per_cta, int32_t *grid_x, int32_t *grid_y);
+/* Current launch shape: the longest band, the number of CTAs, threads per CTA
+ * and how many CTAs of the step kernel an SM holds (any pointer may be NULL). */
+lbm_status lbm_get_launch(const lbm_handle *h, int32_t *band_rows, int32_t *ctas, int32_t *threads,
+                          int32_t *ctas_per_sm);
 
-/* Per-kernel timing: while enabled, lbm_step launches each step directly
- * (no graph) with CUDA events on the handle's stream around the bulk kernel
- * and around the crack kernel. */
+/* Kernel timing: while enabled, lbm_step launches every step directly (no
+ * graph) with CUDA events on the handle's stream around the step kernel, and
+ * the deferred crack step that synchronising calls apply first is timed the
+ * same way. */
 lbm_status lbm_set_profiling(lbm_handle *h, int32_t enable);
 
 /* Sum of the measured kernel durations (milliseconds) and launch counts since
- * the last reset; reset != 0 clears them.  Synchronises the stream. */
-lbm_status lbm_profile_read(lbm_handle *h, double *bulk_ms, int64_t *n_bulk, double *crack_ms, int64_t *n_crack,
+ * the last reset, for step kernels and for deferred crack steps; reset != 0
+ * clears them.  Synchronises the stream. */
+lbm_status lbm_profile_read(lbm_handle *h, double *step_ms, int64_t *n_step, double *finalize_ms, int64_t *n_finalize,
                             int32_t reset);
 
 /* Bytes of device memory the handle holds. */

@@ -75,7 +75,8 @@ PROTOTYPES = {
     "lbm_sync": (C.c_int, [C.c_void_p]),
     "lbm_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_set_launch": (C.c_int, [C.c_void_p, C.c_int32]),
-    "lbm_get_launch": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "lbm_get_launch": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                 C.POINTER(C.c_int32)]),
     "lbm_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
     "lbm_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                    C.POINTER(C.c_int64), C.c_int32]),

@@ -1,9 +1,11 @@
 // lbm_api.cu -- host runtime behind the C ABI declared in include/lbm.h:
-// validation, device memory layout, initial crack, CUDA-graph replay of the
-// per-step kernel sequence, and the copy-out calls.
+// validation, device memory layout, initial crack, the static band partition
+// of the step kernel, CUDA-graph replay of step sequences, the deferred crack
+// step before host reads, and the copy-out calls.
 #include "lbm.h"
 #include "lbm_internal.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -30,9 +32,9 @@ lbm_status cuda_fail(cudaError_t e, const char *what)
     return LBM_ERR_CUDA;
 }
 
-#define LBM_CUDA(call)                                   \
-    do {                                                 \
-        cudaError_t e_ = (call);                         \
+#define LBM_CUDA(call)                                      \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
         if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
     } while (0)
 
@@ -50,41 +52,48 @@ struct lbm_handle {
     lbm_material mat;
     lbm_crack crack;
     size_t esize;
-    int64_t pitch;      // elements per padded row
-    int32_t words;      // 32-bit mask words per row
-    int32_t rows;       // rows per CTA of the bulk kernel
-    dim3 bulk_grid;
+    int64_t pitch;       // elements per padded row
+    int32_t words;       // 32-bit mask words per row
+    int32_t jc;          // crack line y = jc dh
+    // step kernel shape
+    int32_t ncb;         // column blocks of kThreads vectors
+    int32_t n_bands, band_rows, crack_band, sms, bps;
+    Unit *units;         // device table, capacity ny
+    // memory
     lbm_allocator alloc;
     bool custom_alloc;
     void *block;
     size_t block_bytes;
-    void *w[2];         // element (0, 0) of each W buffer
+    void *w[2];          // element (0, 0) of each W buffer
     void *wd;
     uint32_t *cut_h, *cut_v;
-    uint8_t *rowflag;
-    CrackState *st;
+    CrackState *st;      // two buffers
+    uint32_t *err;
     History hist;
     LoadDesc load[4];
     CrackParams cp;
     double g;
-    int parity;
+    // stepping
+    int parity;          // W buffer and state buffer holding the current step
+    bool pending;        // the crack step after the last enqueued LBM step is not applied yet
     cudaStream_t stream;
     cudaStream_t cap_stream;
     cudaGraphExec_t gexec;
     int gparity;
     lbm_status sticky;
-    // per-kernel CUDA-event timing of direct launches (lbm_set_profiling)
+    // CUDA-event timing (lbm_set_profiling)
     int profiling;
-    std::vector<cudaEvent_t> *ev;   // three events per profiled step
+    std::vector<cudaEvent_t> *ev;   // pairs: start, end
+    std::vector<int> *ev_kind;      // 0 step kernel, 1 finalize kernel
     size_t ev_used;
-    double bulk_ms, crack_ms;
-    int64_t n_bulk, n_crack;
+    double step_ms, fin_ms;
+    int64_t n_step, n_fin;
 };
 
 namespace {
 
 template <typename T>
-void make_bulk_args(const lbm_handle *h, int par, BulkArgs<T> &a)
+void make_step_args(const lbm_handle *h, int par, StepArgs<T> &a)
 {
     a.w_in = static_cast<const T *>(h->w[par]);
     a.w_out = static_cast<T *>(h->w[par ^ 1]);
@@ -92,130 +101,176 @@ void make_bulk_args(const lbm_handle *h, int par, BulkArgs<T> &a)
     a.pitch = h->pitch;
     a.nx = h->grid.nx;
     a.ny = h->grid.ny;
-    a.rows = h->rows;
-    for (int e = 0; e < 4; ++e) a.edge[e] = h->grid.edge[e];
+    a.ncb = h->ncb;
+    a.crack_band = h->crack_band;
+    for (int e = 0; e < 4; ++e) { a.edge[e] = h->grid.edge[e]; a.load[e] = h->load[e]; }
     a.g = (T)h->g;
     a.dt = (T)h->grid.dt;
     a.cut_h = h->cut_h;
     a.cut_v = h->cut_v;
-    a.rowflag = h->rowflag;
     a.words = h->words;
-    a.st = h->st;
-}
-
-template <typename T>
-void make_crack_args(const lbm_handle *h, int par, CrackArgs<T> &a)
-{
-    a.w_in = static_cast<const T *>(h->w[par]);
-    a.w_out = static_cast<T *>(h->w[par ^ 1]);
-    a.wd = static_cast<T *>(h->wd);
-    a.pitch = h->pitch;
-    a.dt = (T)h->grid.dt;
+    a.units = h->units;
+    a.s_in = h->st + par;
+    a.s_out = h->st + (par ^ 1);
+    a.err = h->err;
     a.p = h->cp;
-    for (int e = 0; e < 4; ++e) { a.load[e] = h->load[e]; a.edge[e] = h->grid.edge[e]; }
-    a.cut_v = h->cut_v;
-    a.rowflag = h->rowflag;
-    a.st = h->st;
     a.hist = h->hist;
 }
 
-// One time step: bulk update W[par] -> W[par^1], then the crack-face rule and
-// the crack step.
 cudaError_t enqueue_step(const lbm_handle *h, int par, cudaStream_t s)
 {
-    cudaError_t e;
     if (h->lat.storage == LBM_F32) {
-        BulkArgs<float> b;
-        make_bulk_args(h, par, b);
-        if ((e = launch_bulk(b, h->bulk_grid, s)) != cudaSuccess) return e;
-        CrackArgs<float> c;
-        make_crack_args(h, par, c);
-        return launch_crack(c, s);
+        StepArgs<float> a;
+        make_step_args(h, par, a);
+        return launch_step(a, h->n_bands, s);
     }
-    BulkArgs<double> b;
-    make_bulk_args(h, par, b);
-    if ((e = launch_bulk(b, h->bulk_grid, s)) != cudaSuccess) return e;
-    CrackArgs<double> c;
-    make_crack_args(h, par, c);
-    return launch_crack(c, s);
+    StepArgs<double> a;
+    make_step_args(h, par, a);
+    return launch_step(a, h->n_bands, s);
 }
 
-// Fold the elapsed times of the recorded event triples into the totals.
+cudaError_t enqueue_finalize(const lbm_handle *h, cudaStream_t s)
+{
+    if (h->lat.storage == LBM_F32) {
+        FinalizeArgs<float> a;
+        a.w = static_cast<const float *>(h->w[h->parity]);
+        a.pitch = h->pitch;
+        a.st = h->st + h->parity;
+        a.cut_v = h->cut_v;
+        a.p = h->cp;
+        a.hist = h->hist;
+        return launch_finalize(a, s);
+    }
+    FinalizeArgs<double> a;
+    a.w = static_cast<const double *>(h->w[h->parity]);
+    a.pitch = h->pitch;
+    a.st = h->st + h->parity;
+    a.cut_v = h->cut_v;
+    a.p = h->cp;
+    a.hist = h->hist;
+    return launch_finalize(a, s);
+}
+
 cudaError_t drain_profile(lbm_handle *h)
 {
     if (!h->ev || h->ev_used == 0) return cudaSuccess;
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return e;
-    for (size_t q = 0; q + 3 <= h->ev_used; q += 3) {
-        float a = 0.f, b = 0.f;
-        if ((e = cudaEventElapsedTime(&a, (*h->ev)[q], (*h->ev)[q + 1])) != cudaSuccess) return e;
-        if ((e = cudaEventElapsedTime(&b, (*h->ev)[q + 1], (*h->ev)[q + 2])) != cudaSuccess) return e;
-        h->bulk_ms += a;
-        h->crack_ms += b;
-        h->n_bulk += 1;
-        h->n_crack += 1;
+    for (size_t q = 0; q + 2 <= h->ev_used; q += 2) {
+        float ms = 0.f;
+        if ((e = cudaEventElapsedTime(&ms, (*h->ev)[q], (*h->ev)[q + 1])) != cudaSuccess) return e;
+        if ((*h->ev_kind)[q / 2] == 0) { h->step_ms += ms; h->n_step += 1; }
+        else { h->fin_ms += ms; h->n_fin += 1; }
     }
     h->ev_used = 0;
     return cudaSuccess;
 }
 
-// One step with events around each kernel (direct launches, no graph).
-cudaError_t enqueue_step_profiled(lbm_handle *h, int par, cudaStream_t s)
+// Enqueue one kernel, bracketed by events when profiling.
+template <typename F>
+cudaError_t timed(lbm_handle *h, int kind, F &&launch)
 {
+    if (!h->profiling) return launch();
     cudaError_t e;
-    if (h->ev_used + 3 > h->ev->size()) {
-        if ((e = drain_profile(h)) != cudaSuccess) return e;
-    }
+    if (h->ev_used + 2 > h->ev->size() && (e = drain_profile(h)) != cudaSuccess) return e;
     cudaEvent_t *E = &(*h->ev)[h->ev_used];
-    h->ev_used += 3;
-    if ((e = cudaEventRecord(E[0], s)) != cudaSuccess) return e;
-    if (h->lat.storage == LBM_F32) {
-        BulkArgs<float> b;
-        make_bulk_args(h, par, b);
-        if ((e = launch_bulk(b, h->bulk_grid, s)) != cudaSuccess) return e;
-        if ((e = cudaEventRecord(E[1], s)) != cudaSuccess) return e;
-        CrackArgs<float> c;
-        make_crack_args(h, par, c);
-        if ((e = launch_crack(c, s)) != cudaSuccess) return e;
-    } else {
-        BulkArgs<double> b;
-        make_bulk_args(h, par, b);
-        if ((e = launch_bulk(b, h->bulk_grid, s)) != cudaSuccess) return e;
-        if ((e = cudaEventRecord(E[1], s)) != cudaSuccess) return e;
-        CrackArgs<double> c;
-        make_crack_args(h, par, c);
-        if ((e = launch_crack(c, s)) != cudaSuccess) return e;
-    }
-    return cudaEventRecord(E[2], s);
+    (*h->ev_kind)[h->ev_used / 2] = kind;
+    h->ev_used += 2;
+    if ((e = cudaEventRecord(E[0], h->stream)) != cudaSuccess) return e;
+    if ((e = launch()) != cudaSuccess) return e;
+    return cudaEventRecord(E[1], h->stream);
 }
 
-void set_launch(lbm_handle *h, int rows)
+// Apply the crack step that follows the last enqueued LBM step.
+lbm_status finalize(lbm_handle *h)
 {
-    const int vec = (int)(16 / h->esize);
-    const int gx = (int)(((h->grid.nx + vec - 1) / vec + kBulkThreads - 1) / kBulkThreads);
-    if (rows <= 0) {
-        // enough CTAs for about eight resident per SM on 152 SMs, 4..64 rows each
-        const int64_t target = 152 * 8;
-        int64_t r = (int64_t)h->grid.ny * gx / target;
-        rows = (int)(r < 4 ? 4 : (r > 64 ? 64 : r));
-    }
-    h->rows = rows;
-    h->bulk_grid = dim3((unsigned)gx, (unsigned)((h->grid.ny + rows - 1) / rows), 1);
+    if (!h->pending) return LBM_OK;
+    LBM_CUDA(timed(h, 1, [&] { return enqueue_finalize(h, h->stream); }));
+    h->pending = false;
+    return LBM_OK;
 }
 
 lbm_status check_sticky(lbm_handle *h)
 {
+    if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");
+    lbm_status rc = finalize(h);
+    if (rc != LBM_OK) return rc;
     CrackState hs;
-    cudaError_t e = cudaMemcpyAsync(&hs, h->st, sizeof hs, cudaMemcpyDeviceToHost, h->stream);
+    uint32_t err = 0;
+    cudaError_t e = cudaMemcpyAsync(&hs, h->st + h->parity, sizeof hs, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, h->err, sizeof err, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
         h->sticky = LBM_ERR_CUDA;
         return cuda_fail(e, "synchronising the lattice stream");
     }
-    if (hs.flags & FLAG_NONFINITE) {
+    if ((err & ERR_NONFINITE) || (hs.flags & FLAG_NONFINITE)) {
         h->sticky = LBM_ERR_UNSTABLE;
         return fail(LBM_ERR_UNSTABLE, "non-finite value in the fields or in K");
     }
+    return LBM_OK;
+}
+
+// Static partition of the rows into bands of at most `rows` rows.  The rows
+// that the crack-face rule and the crack links touch form two bands of their
+// own, hh rows below the crack line (ending at row jc - 1) and hh rows above
+// it (starting at row jc), so that no other band holds a severed link.
+std::vector<Unit> partition_rows(int ny, int rows, int jc, int hh)
+{
+    std::vector<Unit> v;
+    auto push = [&](int j0, int j1) {
+        Unit u;
+        u.j0 = j0;
+        u.j1 = j1;
+        u.dir = 1;
+        u.pad = 0;
+        v.push_back(u);
+    };
+    auto fill = [&](int a, int b) {
+        for (int j = a; j < b; j = std::min(j + rows, b)) push(j, std::min(j + rows, b));
+    };
+    if (hh > 0) {
+        fill(0, jc - hh);
+        push(jc - hh, jc);
+        push(jc, jc + hh);
+        fill(jc + hh, ny);
+    } else {
+        fill(0, ny);
+    }
+    return v;
+}
+
+// Choose the band height (rows <= 0: balance the bands over the SMs) and
+// upload the unit table.
+lbm_status plan_bands(lbm_handle *h, int rows)
+{
+    const int ny = h->grid.ny;
+    const bool crack = h->cp.mode != CRACK_NONE;
+    const int hh = !crack ? 0 : (h->cp.macro ? 3 : 1);
+    std::vector<Unit> best;
+    if (rows > 0) {
+        best = partition_rows(ny, rows, h->jc, hh);
+    } else {
+        // all CTAs resident at once: bands * ncb <= sms * bps, bands as short as that allows
+        const int64_t slots = (int64_t)h->sms * h->bps;
+        const int64_t nb = std::max<int64_t>(1, slots / h->ncb);
+        int H = std::max(1, (int)((ny + nb - 1) / nb));
+        for (;; ++H) {
+            best = partition_rows(ny, H, h->jc, hh);
+            if ((int64_t)best.size() * h->ncb <= slots || H >= ny) break;
+        }
+    }
+    if ((int)best.size() > ny) return fail(LBM_ERR_ARG, "partition larger than the unit table");
+    h->n_bands = (int)best.size();
+    h->band_rows = 0;
+    h->crack_band = -1;
+    for (int b = 0; b < h->n_bands; ++b) {
+        h->band_rows = std::max(h->band_rows, best[b].j1 - best[b].j0);
+        if (crack && best[b].j0 == h->jc - hh && best[b].j1 == h->jc) h->crack_band = b;
+    }
+    if (crack && h->crack_band < 0) return fail(LBM_ERR_ARG, "the crack rows form no band of their own");
+    LBM_CUDA(cudaMemcpyAsync(h->units, best.data(), best.size() * sizeof(Unit), cudaMemcpyHostToDevice, h->stream));
+    LBM_CUDA(cudaStreamSynchronize(h->stream));
     return LBM_OK;
 }
 
@@ -232,6 +287,15 @@ void dev_free(lbm_handle *h, void *p)
     if (!p) return;
     if (h->custom_alloc) h->alloc.release(p, h->alloc.ctx);
     else cudaFree(p);
+}
+
+void drop_graph(lbm_handle *h)
+{
+    if (h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+        h->gparity = -1;
+    }
 }
 
 }  // namespace
@@ -306,6 +370,7 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lb
     h->lat = *lattice;
     h->mat = *material;
     h->crack = cr;
+    h->jc = jc;
     h->esize = lattice->storage == LBM_F32 ? 4 : 8;
     h->g = g;
     h->stream = (cudaStream_t)stream;
@@ -315,7 +380,6 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lb
         h->alloc = *allocator;
         h->custom_alloc = true;
     }
-    std::memset(h->load, 0, sizeof h->load);
     std::vector<int> seen(4, 0);
     for (int q = 0; q < n_loads; ++q) {
         const lbm_loading &L = loads[q];
@@ -329,11 +393,20 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lb
         h->load[L.edge].n = L.kind == LBM_LOAD_SERIES ? L.n_series : 0;
     }
 
-    set_launch(h, 0);
+    // step kernel shape: a thread per 16-byte vector of a row, kThreads a CTA
     const int vec = (int)(16 / h->esize);
+    const int cols = kThreads * vec;
+    h->ncb = (grid->nx + cols - 1) / cols;
+    const void *kfn = h->esize == 4 ? step_kernel_ptr<float>() : step_kernel_ptr<double>();
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->bps, kfn, kThreads, 0);
+    if (e != cudaSuccess) { delete h; return cuda_fail(e, "querying the device"); }
+    if (h->bps < 1) { delete h; return fail(LBM_ERR_ARG, "the step kernel does not fit on an SM"); }
+
     const int64_t xoff = 128 / (int64_t)h->esize;
-    const int64_t cover = (int64_t)h->bulk_grid.x * kBulkThreads * vec;
-    h->pitch = xoff + cover + xoff;
+    h->pitch = xoff + (int64_t)h->ncb * cols + xoff;
     h->words = (grid->nx + 31) / 32;
     const int64_t hcap = cr.mode != LBM_CRACK_NONE ? cr.hist_cap : 1;
 
@@ -346,14 +419,15 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lb
     const size_t o_wd = off; off = align256(off + plane);
     const size_t o_ch = off; off = align256(off + mask);
     const size_t o_cv = off; off = align256(off + mask);
-    const size_t o_rf = off; off = align256(off + (size_t)grid->ny);
-    const size_t o_st = off; off = align256(off + sizeof(CrackState));
+    const size_t o_st = off; off = align256(off + 2 * sizeof(CrackState));
+    const size_t o_er = off; off = align256(off + sizeof(uint32_t));
+    const size_t o_un = off; off = align256(off + (size_t)grid->ny * sizeof(Unit));
     const size_t o_hK = off; off = align256(off + (size_t)hcap * 8);
     const size_t o_hv = off; off = align256(off + (size_t)hcap * 8);
     const size_t o_ht = off; off = align256(off + (size_t)hcap * 8);
     const size_t o_hn = off; off = align256(off + (size_t)hcap * 4);
     size_t o_ser[4];
-    for (int e = 0; e < 4; ++e) { o_ser[e] = off; off = align256(off + (size_t)h->load[e].n * 8); }
+    for (int q = 0; q < 4; ++q) { o_ser[q] = off; off = align256(off + (size_t)h->load[q].n * 8); }
     h->block_bytes = off;
     h->block = dev_alloc(h, off);
     if (!h->block) { delete h; return fail(LBM_ERR_OOM, "device allocation failed"); }
@@ -364,35 +438,35 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lb
     h->wd = base + o_wd + origin;
     h->cut_h = reinterpret_cast<uint32_t *>(base + o_ch);
     h->cut_v = reinterpret_cast<uint32_t *>(base + o_cv);
-    h->rowflag = reinterpret_cast<uint8_t *>(base + o_rf);
     h->st = reinterpret_cast<CrackState *>(base + o_st);
+    h->err = reinterpret_cast<uint32_t *>(base + o_er);
+    h->units = reinterpret_cast<Unit *>(base + o_un);
     h->hist.K = reinterpret_cast<double *>(base + o_hK);
     h->hist.v = reinterpret_cast<double *>(base + o_hv);
     h->hist.tip = reinterpret_cast<int64_t *>(base + o_ht);
     h->hist.np = reinterpret_cast<int32_t *>(base + o_hn);
 
     cudaStream_t s = h->stream;
-    lbm_status rc = LBM_OK;
-    auto bail = [&](cudaError_t e, const char *what) {
-        rc = cuda_fail(e, what);
+    auto bail = [&](lbm_status rc) {
         cudaStreamSynchronize(s);
         dev_free(h, h->block);
         delete h;
         return rc;
     };
-    cudaError_t e = cudaMemsetAsync(h->block, 0, h->block_bytes, s);
-    if (e != cudaSuccess) return bail(e, "clearing device state");
+    e = cudaMemsetAsync(h->block, 0, h->block_bytes, s);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "clearing device state"));
     for (int q = 0; q < 4; ++q) {
         if (h->load[q].kind != LBM_LOAD_SERIES) continue;
         const lbm_loading *L = nullptr;
         for (int r = 0; r < n_loads; ++r) if (loads[r].edge == q) L = &loads[r];
         double *dser = reinterpret_cast<double *>(base + o_ser[q]);
         e = cudaMemcpyAsync(dser, L->series, (size_t)L->n_series * 8, cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) return bail(e, "copying a load series");
+        if (e != cudaSuccess) return bail(cuda_fail(e, "copying a load series"));
         h->load[q].series = dser;
     }
+    e = cudaStreamSynchronize(s);   // the caller's series buffers may go away after create
+    if (e != cudaSuccess) return bail(cuda_fail(e, "copying load series"));
 
-    // crack parameters and the initial severed links (all x_start <= x_i <= x_tip)
     CrackParams &cp = h->cp;
     std::memset(&cp, 0, sizeof cp);
     cp.mode = cr.mode;
@@ -415,38 +489,36 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lb
     cp.clamp_q = clamp_q;
     cp.hist_cap = cr.mode != LBM_CRACK_NONE ? cr.hist_cap : 0;
 
+    lbm_status rc = plan_bands(h, 0);
+    if (rc != LBM_OK) return bail(rc);
+
+    // initial state: the initial crack's links (x_start <= x_i <= x_tip) severed
     CrackState hs;
     std::memset(&hs, 0, sizeof hs);
     hs.tip_q = tip_q;
     hs.i_first = 0;
     hs.i_last = -1;
+    hs.decided = 1;
+    std::vector<uint32_t> row((size_t)h->words, 0u);
     if (cr.mode != LBM_CRACK_NONE) {
         const int64_t half = qone / 2;
-        int64_t first = -floor_div(-(start_q - half), qone);   // ceil((start - 1/2) / 1)
-        int64_t last = floor_div(tip_q - half, qone);
+        int64_t first = -floor_div(-(start_q - half), qone);   // smallest i with x_i >= x_start
+        int64_t last = floor_div(tip_q - half, qone);          // largest i with x_i <= x_tip
         if (first < 0) first = 0;
         if (last > grid->nx - 1) last = grid->nx - 1;
         hs.i_first = (int32_t)first;
         hs.i_last = (int32_t)(last < first ? first - 1 : last);
         hs.v_prev = cr.mode == LBM_CRACK_PRESCRIBED ? cr.v_rel : 0.0;
-        if (hs.i_last >= hs.i_first) {
-            std::vector<uint32_t> row((size_t)h->words, 0u);
-            for (int i = hs.i_first; i <= hs.i_last; ++i) row[(size_t)(i >> 5)] |= 1u << (i & 31);
-            std::vector<uint8_t> rf((size_t)grid->ny, 0);
-            rf[(size_t)(jc - 1)] |= 2;
-            rf[(size_t)jc] |= 4;
-            e = cudaMemcpyAsync(h->cut_v + (size_t)(jc - 1) * h->words, row.data(), row.size() * 4, cudaMemcpyHostToDevice, s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(h->rowflag, rf.data(), rf.size(), cudaMemcpyHostToDevice, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // host vectors go out of scope
-            if (e != cudaSuccess) return bail(e, "writing the initial crack");
-        }
+        for (int i = hs.i_first; i <= hs.i_last; ++i) row[(size_t)(i >> 5)] |= 1u << (i & 31);
+        e = cudaMemcpyAsync(h->cut_v + (size_t)(jc - 1) * h->words, row.data(), row.size() * 4, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "writing the initial crack"));
     }
     e = cudaMemcpyAsync(h->st, &hs, sizeof hs, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = launch_wstar(h->st, h->load, h->grid.edge, grid->dt, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return bail(e, "initialising the crack state");
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // host vectors go out of scope
+    if (e != cudaSuccess) return bail(cuda_fail(e, "initialising the crack state"));
     e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
-    if (e != cudaSuccess) return bail(e, "creating the capture stream");
+    if (e != cudaSuccess) return bail(cuda_fail(e, "creating the capture stream"));
     *out = h;
     g_err.clear();
     return LBM_OK;
@@ -457,15 +529,9 @@ lbm_status lbm_step(lbm_handle *h, int64_t n)
     if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
     if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");
     if (n < 0) return fail(LBM_ERR_ARG, "n must be >= 0");
-    if (h->profiling) {
-        for (; n > 0; --n) {
-            LBM_CUDA(enqueue_step_profiled(h, h->parity, h->stream));
-            h->parity ^= 1;
-        }
-        return LBM_OK;
-    }
+    if (n > 0 && h->cp.mode != CRACK_NONE) h->pending = true;
     while (n > 0) {
-        if (n >= kGraphChunk) {
+        if (n >= kGraphChunk && !h->profiling) {
             if (!h->gexec) {
                 cudaGraph_t graph;
                 LBM_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -489,7 +555,7 @@ lbm_status lbm_step(lbm_handle *h, int64_t n)
                 continue;
             }
         }
-        LBM_CUDA(enqueue_step(h, h->parity, h->stream));
+        LBM_CUDA(timed(h, 0, [&] { return enqueue_step(h, h->parity, h->stream); }));
         h->parity ^= 1;
         n -= 1;
     }
@@ -516,6 +582,8 @@ lbm_status lbm_set_fields(lbm_handle *h, int32_t which, const void *src, int32_t
     if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");
     if (which != LBM_FIELD_W && which != LBM_FIELD_WDOT) return fail(LBM_ERR_ARG, "unknown field");
     if (dtype != h->lat.storage) return fail(LBM_ERR_ARG, "dtype must equal the storage precision");
+    lbm_status rc = finalize(h);   // the pending crack step reads the fields being replaced
+    if (rc != LBM_OK) return rc;
     void *dst = which == LBM_FIELD_W ? h->w[h->parity] : h->wd;
     const size_t row = (size_t)h->grid.nx * h->esize;
     LBM_CUDA(cudaMemcpy2DAsync(dst, (size_t)h->pitch * h->esize, src, row, row, (size_t)h->grid.ny,
@@ -536,6 +604,8 @@ lbm_status lbm_cut_mask(lbm_handle *h, int32_t which, uint32_t *dst_host, int64_
     if (which != LBM_MASK_H && which != LBM_MASK_V) return fail(LBM_ERR_ARG, "unknown mask");
     const int64_t need = (int64_t)h->grid.ny * h->words;
     if (n_words < need) return fail(LBM_ERR_ARG, "dst too small");
+    lbm_status rc = finalize(h);
+    if (rc != LBM_OK) return rc;
     LBM_CUDA(cudaMemcpyAsync(dst_host, which == LBM_MASK_H ? h->cut_h : h->cut_v, (size_t)need * 4,
                              cudaMemcpyDeviceToHost, h->stream));
     return check_sticky(h);
@@ -545,8 +615,10 @@ lbm_status lbm_crack_state(lbm_handle *h, lbm_crack_state_t *now, double *K_hist
                            int64_t *tip_hist, int32_t *npairs_hist, int64_t cap, int64_t *n_written)
 {
     if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
+    lbm_status rc = finalize(h);
+    if (rc != LBM_OK) return rc;
     CrackState hs;
-    LBM_CUDA(cudaMemcpyAsync(&hs, h->st, sizeof hs, cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA(cudaMemcpyAsync(&hs, h->st + h->parity, sizeof hs, cudaMemcpyDeviceToHost, h->stream));
     LBM_CUDA(cudaStreamSynchronize(h->stream));
     if (now) {
         now->step = hs.step;
@@ -583,17 +655,12 @@ lbm_status lbm_crack_state(lbm_handle *h, lbm_crack_state_t *now, double *K_hist
         }
     }
     if (n_written) *n_written = n;
-    if (hs.flags & FLAG_NONFINITE) {
-        h->sticky = LBM_ERR_UNSTABLE;
-        return fail(LBM_ERR_UNSTABLE, "non-finite value in the fields or in K");
-    }
-    return h->sticky;
+    return check_sticky(h);
 }
 
 lbm_status lbm_sync(lbm_handle *h)
 {
     if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
-    if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");
     return check_sticky(h);
 }
 
@@ -604,26 +671,23 @@ lbm_status lbm_set_stream(lbm_handle *h, void *stream)
     return LBM_OK;
 }
 
-lbm_status lbm_set_launch(lbm_handle *h, int32_t rows_per_cta)
+lbm_status lbm_set_launch(lbm_handle *h, int32_t band_rows)
 {
     if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
-    if (rows_per_cta < 0 || rows_per_cta > 4096) return fail(LBM_ERR_ARG, "rows_per_cta out of range");
+    if (band_rows < 0 || band_rows > (1 << 20)) return fail(LBM_ERR_ARG, "band_rows out of range");
     LBM_CUDA(cudaStreamSynchronize(h->stream));
-    if (h->gexec) {
-        cudaGraphExecDestroy(h->gexec);
-        h->gexec = nullptr;
-        h->gparity = -1;
-    }
-    set_launch(h, rows_per_cta);
-    return LBM_OK;
+    drop_graph(h);
+    return plan_bands(h, band_rows);
 }
 
-lbm_status lbm_get_launch(const lbm_handle *h, int32_t *rows_per_cta, int32_t *grid_x, int32_t *grid_y)
+lbm_status lbm_get_launch(const lbm_handle *h, int32_t *band_rows, int32_t *ctas, int32_t *threads,
+                          int32_t *ctas_per_sm)
 {
     if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
-    if (rows_per_cta) *rows_per_cta = h->rows;
-    if (grid_x) *grid_x = (int32_t)h->bulk_grid.x;
-    if (grid_y) *grid_y = (int32_t)h->bulk_grid.y;
+    if (band_rows) *band_rows = h->band_rows;
+    if (ctas) *ctas = h->n_bands * h->ncb;
+    if (threads) *threads = kThreads;
+    if (ctas_per_sm) *ctas_per_sm = h->bps;
     return LBM_OK;
 }
 
@@ -631,8 +695,9 @@ lbm_status lbm_set_profiling(lbm_handle *h, int32_t enable)
 {
     if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
     if (enable && !h->ev) {
-        h->ev = new (std::nothrow) std::vector<cudaEvent_t>(3 * 1024);
-        if (!h->ev) return fail(LBM_ERR_OOM, "host allocation failed");
+        h->ev = new (std::nothrow) std::vector<cudaEvent_t>(2 * 1024);
+        h->ev_kind = new (std::nothrow) std::vector<int>(1024);
+        if (!h->ev || !h->ev_kind) return fail(LBM_ERR_OOM, "host allocation failed");
         for (auto &e : *h->ev) {
             cudaError_t ce = cudaEventCreate(&e);
             if (ce != cudaSuccess) return cuda_fail(ce, "cudaEventCreate");
@@ -644,18 +709,18 @@ lbm_status lbm_set_profiling(lbm_handle *h, int32_t enable)
     return LBM_OK;
 }
 
-lbm_status lbm_profile_read(lbm_handle *h, double *bulk_ms, int64_t *n_bulk, double *crack_ms, int64_t *n_crack,
+lbm_status lbm_profile_read(lbm_handle *h, double *step_ms, int64_t *n_step, double *finalize_ms, int64_t *n_finalize,
                             int32_t reset)
 {
     if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
     LBM_CUDA(drain_profile(h));
-    if (bulk_ms) *bulk_ms = h->bulk_ms;
-    if (n_bulk) *n_bulk = h->n_bulk;
-    if (crack_ms) *crack_ms = h->crack_ms;
-    if (n_crack) *n_crack = h->n_crack;
+    if (step_ms) *step_ms = h->step_ms;
+    if (n_step) *n_step = h->n_step;
+    if (finalize_ms) *finalize_ms = h->fin_ms;
+    if (n_finalize) *n_finalize = h->n_fin;
     if (reset) {
-        h->bulk_ms = h->crack_ms = 0.0;
-        h->n_bulk = h->n_crack = 0;
+        h->step_ms = h->fin_ms = 0.0;
+        h->n_step = h->n_fin = 0;
     }
     return LBM_OK;
 }
@@ -671,11 +736,12 @@ void lbm_destroy(lbm_handle *h)
 {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
-    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    drop_graph(h);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->ev) {
         for (auto &e : *h->ev) cudaEventDestroy(e);
         delete h->ev;
+        delete h->ev_kind;
     }
     dev_free(h, h->block);
     delete h;

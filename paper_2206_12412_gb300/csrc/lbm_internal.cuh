@@ -6,16 +6,19 @@
 //     (ny + 2) rows x pitch elements.  Row r = j + 1 holds lattice row j; rows
 //     0 and ny + 1 are halo rows.  Each row starts with XOFF pad elements
 //     (128 bytes), so lattice column 0 is 128-byte aligned and column -1 is the
-//     last pad element; the right pad holds column nx.  Pads carry periodic
-//     copies when an edge pair is periodic and are otherwise never used.
-//     The plane pointers below point at (j = 0, i = 0).
+//     last pad element; the pad after the covered columns holds column nx.
+//     After every step the pads next to free edges hold the edge sites' own
+//     values (bounce-back images) and those next to periodic edges the
+//     wrap-around values; pads next to Dirichlet edges are not read.  The plane pointers point at (j = 0, i = 0).
 //   * cut masks: one bit per link, ceil(nx / 32) 32-bit words per row;
 //     H bit (i, j) = link (i,j)-(i+1,j), V bit (i, j) = link (i,j)-(i,j+1).
-//   * rowflag[j]: bit 0 = row j has H cuts, bit 1 = row j has V cuts (links to
-//     row j + 1), bit 2 = the V link row below j has cuts.  Lets the bulk
-//     kernel skip the mask in the (almost all) rows without severed links.
-//   * CrackState: the mutable crack and step state, read by the bulk kernel
-//     (step-dependent edge values) and written by the crack kernel.
+//     Severed links of the straight crack all lie in V row jc-1; the rows
+//     they touch form the crack band of the step kernel's partition.
+//   * CrackState x 2: the crack and step state, double buffered.  The step
+//     kernel of step k reads buffer k & 1 and its one writer CTA writes buffer
+//     (k + 1) & 1, so no CTA ever reads a state that another CTA is writing.
+//   * Unit table: the row bands of the step kernel's static partition.
+//   * err: sticky device error bits (non-finite field).
 #pragma once
 
 #include <cstdint>
@@ -23,19 +26,21 @@
 
 namespace lbm {
 
-constexpr int kQBits = 32;                  // tip fixed point: 1 dh = 2^32 units
+constexpr int kQBits = 32;                          // tip fixed point: 1 dh = 2^32 units
 constexpr double kTwoM32 = 2.3283064365386963e-10;  // 2^-32
 constexpr double kPi = 3.14159265358979323846;
-constexpr int kBulkThreads = 128;
-constexpr int kCrackThreads = 256;
+constexpr int kThreads = 128;                       // threads per CTA of the step kernel
+constexpr int kMinBlocks = 8;                       // resident CTAs per SM the kernel is built for
 
 enum { EDGE_FREE = 0, EDGE_DIRICHLET = 1, EDGE_PERIODIC = 2 };
 enum { LEFT = 0, RIGHT = 1, BOTTOM = 2, TOP = 3 };
 enum { CRACK_NONE = 0, CRACK_STATIONARY = 1, CRACK_PRESCRIBED = 2, CRACK_KCRIT = 3 };
 enum { LOAD_ZERO = 0, LOAD_LINEAR = 1, LOAD_SIN2 = 2, LOAD_HALFSINE = 3, LOAD_SERIES = 4, LOAD_CONST = 5 };
 enum { FLAG_CLAMPED = 1, FLAG_NONFINITE = 4 };
+enum { ERR_NONFINITE = 1 };
 
 template <typename T> struct Pad { static constexpr int kElems = 128 / (int)sizeof(T); };
+template <typename T> struct Vec { static constexpr int N = 16 / (int)sizeof(T); };
 
 struct LoadDesc {
     int32_t kind, pad;
@@ -44,18 +49,19 @@ struct LoadDesc {
     int64_t n;
 };
 
-// Mutable per-handle state, resident in device memory.
+// Crack and step state after `step` LBM steps.  decided = 1 once the crack
+// step that follows LBM step `step` has been applied (Alg. 1 runs after every
+// LBM step); the step kernel applies a pending one before its own update.
 struct CrackState {
-    int64_t step;          // completed time steps
+    int64_t step;          // completed LBM steps
     int64_t tip_q;         // tip x in units of 2^-32 dh
     int64_t hist_n;        // records written to the history ring
     int32_t i_first, i_last;  // severed crack links: columns i_first..i_last of V row jc-1
     int32_t arrested, flags;
     int32_t npairs, grew;
-    uint32_t err_bits;     // set by the bulk kernel on a non-finite value
-    int32_t pad;
+    int32_t decided, pad;
     double v_prev, K, v, r_min;
-    double wstar[4];       // Dirichlet values w*(t_step) for the next step
+    double wstar[4];       // Dirichlet values w*(t_step) for the next LBM step
 };
 
 // Constant per-handle crack parameters (passed by value).
@@ -72,39 +78,47 @@ struct History {
     int32_t *np;
 };
 
+// One row band of the static partition: output rows [j0, j1).
+struct Unit {
+    int32_t j0, j1, dir, pad;
+};
+
 template <typename T>
-struct BulkArgs {
+struct StepArgs {
     const T *w_in;
     T *w_out;
     T *wd;
     int64_t pitch;
-    int32_t nx, ny, rows;
+    int32_t nx, ny;
+    int32_t ncb;               // column blocks of kThreads * 16 bytes
+    int32_t crack_band;        // band that holds the crack rows (-1: none)
     int32_t edge[4];
     T g, dt;
-    const uint32_t *cut_h, *cut_v;
-    const uint8_t *rowflag;
+    const uint32_t *cut_h;
+    uint32_t *cut_v;
     int32_t words;
-    CrackState *st;
-};
-
-template <typename T>
-struct CrackArgs {
-    const T *w_in;   // fields before the step (for the macroscopic rule)
-    T *w_out;        // fields after the bulk update
-    T *wd;
-    int64_t pitch;
-    T dt;
+    const Unit *units;
+    const CrackState *s_in;
+    CrackState *s_out;
+    uint32_t *err;
     CrackParams p;
     LoadDesc load[4];
-    int32_t edge[4];
-    uint32_t *cut_v;
-    uint8_t *rowflag;
-    CrackState *st;
     History hist;
 };
 
-template <typename T> cudaError_t launch_bulk(const BulkArgs<T> &a, dim3 grid, cudaStream_t s);
-template <typename T> cudaError_t launch_crack(const CrackArgs<T> &a, cudaStream_t s);
+template <typename T>
+struct FinalizeArgs {
+    const T *w;
+    int64_t pitch;
+    CrackState *st;
+    uint32_t *cut_v;
+    CrackParams p;
+    History hist;
+};
+
+template <typename T> const void *step_kernel_ptr();
+template <typename T> cudaError_t launch_step(const StepArgs<T> &a, int bands, cudaStream_t s);
+template <typename T> cudaError_t launch_finalize(const FinalizeArgs<T> &a, cudaStream_t s);
 cudaError_t launch_wstar(CrackState *st, const LoadDesc *load, const int32_t *edge, double dt, cudaStream_t s);
 template <typename T> cudaError_t launch_fill_pads(T *w, int64_t pitch, int nx, int ny, const int32_t *edge, cudaStream_t s);
 

@@ -1,4 +1,4 @@
-// lbm_kernels.cu -- CUDA kernels (sm_103a) of one lattice Boltzmann time step
+// lbm_kernels.cu -- CUDA kernels (sm_103a) of the lattice Boltzmann time step
 // for antiplane shear with dynamic mode III cracks (arXiv 2206.12412).
 //
 // Moment form.  With tau = dt (Sec. 3) the BGK collision sets every
@@ -10,44 +10,52 @@
 // (eq. integration), where a missing link contributes the value its boundary
 // rule streams back: bounce-back f*^opp(x) = g w(x) (free edge, severed crack
 // link), anti-bounce-back -f*^opp(x) + 2 g w* = g (2 w* - w(x)) (Dirichlet
-// edge, Sec. 3.1), or the periodic image.  The bulk kernel therefore moves
-// exactly 16 bytes per site in FP32 (read w, wdot; write w, wdot).
+// edge, Sec. 3.1), or the periodic image.  One step moves exactly 16 bytes
+// per site in FP32: read w and wdot, write w and wdot.
+//
+// One kernel per time step.  Each CTA owns a band of rows of a 512-column
+// (FP32) block and marches up through it.  The crack handling of Alg. 1 that
+// follows step k - 1 is done at the start of step k by the one CTA that owns
+// the next crack link (the crack band at the column of the next link); it
+// reads the fields written by step k - 1 and state buffer k & 1, severs the
+// link and writes state buffer (k + 1) & 1.  The macroscopic crack-face rule
+// (Sec. 3.1) is applied inside the crack band, whose rows jc-3 .. jc+2 form
+// a band of their own.
 #include "lbm_internal.cuh"
 
 namespace lbm {
 
-template <typename T> struct VecOf;
-template <> struct VecOf<float> { typedef float4 V; static constexpr int N = 4; };
-template <> struct VecOf<double> { typedef double2 V; static constexpr int N = 2; };
+// --------------------------------------------------------- vector rows
 
 template <typename T, int N> struct Row { T v[N]; };
 
-__device__ __forceinline__ void ld_row(const float *p, Row<float, 4> &r)
+// w of the input buffer is read-only during a step: non-coherent loads.
+__device__ __forceinline__ void ldg_row(const float *p, Row<float, 4> &r)
 {
     float4 q = __ldg(reinterpret_cast<const float4 *>(p));
     r.v[0] = q.x; r.v[1] = q.y; r.v[2] = q.z; r.v[3] = q.w;
 }
-__device__ __forceinline__ void ld_row(const double *p, Row<double, 2> &r)
+__device__ __forceinline__ void ldg_row(const double *p, Row<double, 2> &r)
 {
     double2 q = __ldg(reinterpret_cast<const double2 *>(p));
     r.v[0] = q.x; r.v[1] = q.y;
 }
-// wdot is updated in place: plain (coherent) loads.
-__device__ __forceinline__ void ld_row_rw(const float *p, Row<float, 4> &r)
+// wdot is updated in place: coherent loads.
+__device__ __forceinline__ void ld_row(const float *p, Row<float, 4> &r)
 {
     float4 q = *reinterpret_cast<const float4 *>(p);
     r.v[0] = q.x; r.v[1] = q.y; r.v[2] = q.z; r.v[3] = q.w;
 }
-__device__ __forceinline__ void ld_row_rw(const double *p, Row<double, 2> &r)
+__device__ __forceinline__ void ld_row(const double *p, Row<double, 2> &r)
 {
     double2 q = *reinterpret_cast<const double2 *>(p);
     r.v[0] = q.x; r.v[1] = q.y;
 }
-__device__ __forceinline__ void st_row(float *p, const Row<float, 4> &r)
+__device__ __forceinline__ void stg_row(float *p, const Row<float, 4> &r)
 {
     *reinterpret_cast<float4 *>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
 }
-__device__ __forceinline__ void st_row(double *p, const Row<double, 2> &r)
+__device__ __forceinline__ void stg_row(double *p, const Row<double, 2> &r)
 {
     *reinterpret_cast<double2 *>(p) = make_double2(r.v[0], r.v[1]);
 }
@@ -61,180 +69,9 @@ __device__ __forceinline__ T edge_value(int kind, T wstar, T wc, T raw)
     return raw;                                              // periodic image in the pad
 }
 
-// ---------------------------------------------------------------- bulk step
-//
-// Thread mapping: a thread owns N consecutive columns (one 16-byte vector) and
-// marches over `rows` consecutive rows, keeping rows j-1, j, j+1 of w in
-// registers, so each w value is loaded from memory once per step (plus one
-// halo row per strip end).  East/west neighbours come from the adjacent lanes
-// by warp shuffles; lanes 0 and 31 load the one halo column they need.  The
-// next row's loads are issued before the current row is computed.
-template <typename T>
-__global__ void __launch_bounds__(kBulkThreads) bulk_kernel(const BulkArgs<T> a)
-{
-    constexpr int N = VecOf<T>::N;
-    typedef Row<T, N> R;
-    const unsigned kFull = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int x0 = (blockIdx.x * kBulkThreads + threadIdx.x) * N;
-    const int j0 = blockIdx.y * a.rows;
-    const int j1 = min(j0 + a.rows, a.ny);
-    const int64_t P = a.pitch;
-    const int nx = a.nx, ny = a.ny;
-    if (j0 >= ny) return;  // uniform per block
-
-    T ws[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) ws[e] = (T)a.st->wstar[e];
-
-    const bool act = x0 < nx;
-    const bool col_edge = (x0 == 0) | (x0 + N >= nx);
-    const T *win = a.w_in + x0;
-    T *wout = a.w_out + x0;
-    T *wdp = a.wd + x0;
-    const int wi = x0 >> 5, bo = x0 & 31;
-    const uint32_t nmask = (1u << N) - 1u;
-
-    R wb, wc, wa, wdv;
-    ld_row(win + (int64_t)(j0 - 1) * P, wb);
-    ld_row(win + (int64_t)j0 * P, wc);
-    ld_row(win + (int64_t)(j0 + 1) * P, wa);
-    ld_row_rw(wdp + (int64_t)j0 * P, wdv);
-    T hl = win[(int64_t)j0 * P - 1];
-    T hr = win[(int64_t)j0 * P + N];
-    bool bad = false;
-
-    for (int j = j0; j < j1; ++j) {
-        // issue the next row's loads first
-        R wn, wdn;
-        T hln = (T)0, hrn = (T)0;
-        const bool more = j + 1 < j1;
-        if (more) {
-            ld_row(win + (int64_t)(j + 2) * P, wn);
-            ld_row_rw(wdp + (int64_t)(j + 1) * P, wdn);
-            if (lane == 0) hln = win[(int64_t)(j + 1) * P - 1];
-            if (lane == 31) hrn = win[(int64_t)(j + 1) * P + N];
-        }
-        T left0 = __shfl_up_sync(kFull, wc.v[N - 1], 1);
-        T rightN = __shfl_down_sync(kFull, wc.v[0], 1);
-        if (lane == 0) left0 = hl;
-        if (lane == 31) rightN = hr;
-
-        const uint8_t rf = a.rowflag[j];
-        const bool special = (j == 0) | (j == ny - 1) | (rf != 0) | col_edge;
-        R wnew, wdnew;
-        if (!special) {
-#pragma unroll
-            for (int k = 0; k < N; ++k) {
-                T wl = k == 0 ? left0 : wc.v[k - 1];
-                T wr = k == N - 1 ? rightN : wc.v[k + 1];
-                T lap = ((wa.v[k] + wb.v[k]) + (wl + wr)) - (T)4 * wc.v[k];
-                wdnew.v[k] = wdv.v[k] + a.g * lap;
-                wnew.v[k] = wc.v[k] + a.dt * wdnew.v[k];
-            }
-        } else {
-            uint32_t vup = 0, vdn = 0, hcur = 0, hprev = 0;
-            if (act) {
-                if (rf & 2) vup = (a.cut_v[(int64_t)j * a.words + wi] >> bo) & nmask;
-                if (rf & 4) {
-                    const int jb = j > 0 ? j - 1 : ny - 1;
-                    vdn = (a.cut_v[(int64_t)jb * a.words + wi] >> bo) & nmask;
-                }
-                if (rf & 1) {
-                    hcur = (a.cut_h[(int64_t)j * a.words + wi] >> bo) & nmask;
-                    if (x0 == 0) {
-                        hprev = (a.cut_h[(int64_t)j * a.words + ((nx - 1) >> 5)] >> ((nx - 1) & 31)) & 1u;
-                    } else if (bo == 0) {
-                        hprev = a.cut_h[(int64_t)j * a.words + wi - 1] >> 31;
-                    } else {
-                        hprev = (a.cut_h[(int64_t)j * a.words + wi] >> (bo - 1)) & 1u;
-                    }
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < N; ++k) {
-                const int i = x0 + k;
-                const T w0 = wc.v[k];
-                T wl = k == 0 ? left0 : wc.v[k - 1];
-                T wr = k == N - 1 ? rightN : wc.v[k + 1];
-                T wu = wa.v[k], wdw = wb.v[k];
-                // links to the row above / below
-                if (j == ny - 1 && a.edge[TOP] != EDGE_PERIODIC) wu = edge_value(a.edge[TOP], ws[TOP], w0, wu);
-                else if ((vup >> k) & 1u) wu = w0;
-                if (j == 0 && a.edge[BOTTOM] != EDGE_PERIODIC) wdw = edge_value(a.edge[BOTTOM], ws[BOTTOM], w0, wdw);
-                else if ((vdn >> k) & 1u) wdw = w0;
-                // links to the west / east neighbour
-                const uint32_t cut_w = k == 0 ? hprev : (hcur >> (k - 1)) & 1u;
-                if (i == 0 && a.edge[LEFT] != EDGE_PERIODIC) wl = edge_value(a.edge[LEFT], ws[LEFT], w0, wl);
-                else if (cut_w) wl = w0;
-                if (i == nx - 1 && a.edge[RIGHT] != EDGE_PERIODIC) wr = edge_value(a.edge[RIGHT], ws[RIGHT], w0, wr);
-                else if ((hcur >> k) & 1u) wr = w0;
-                T lap = ((wu + wdw) + (wl + wr)) - (T)4 * w0;
-                wdnew.v[k] = wdv.v[k] + a.g * lap;
-                wnew.v[k] = w0 + a.dt * wdnew.v[k];
-            }
-        }
-
-        if (act) {
-            T *ro = wout + (int64_t)j * P;
-            T *rd = wdp + (int64_t)j * P;
-            if (x0 + N <= nx) {
-                st_row(ro, wnew);
-                st_row(rd, wdnew);
-#pragma unroll
-                for (int k = 0; k < N; ++k) bad |= !(isfinite(wnew.v[k]) && isfinite(wdnew.v[k]));
-            } else {
-#pragma unroll
-                for (int k = 0; k < N; ++k)
-                    if (x0 + k < nx) {
-                        ro[k] = wnew.v[k];
-                        rd[k] = wdnew.v[k];
-                        bad |= !(isfinite(wnew.v[k]) && isfinite(wdnew.v[k]));
-                    }
-            }
-            // periodic images in the pads of the output buffer
-            if (a.edge[TOP] == EDGE_PERIODIC) {
-                if (j == 0) {
-                    T *rp = wout + (int64_t)ny * P;
-#pragma unroll
-                    for (int k = 0; k < N; ++k) if (x0 + k < nx) rp[k] = wnew.v[k];
-                }
-                if (j == ny - 1) {
-                    T *rp = wout - P;
-#pragma unroll
-                    for (int k = 0; k < N; ++k) if (x0 + k < nx) rp[k] = wnew.v[k];
-                }
-            }
-            if (a.edge[LEFT] == EDGE_PERIODIC) {
-                if (x0 == 0) ro[nx] = wnew.v[0];
-#pragma unroll
-                for (int k = 0; k < N; ++k) if (x0 + k == nx - 1) ro[-(x0 + 1)] = wnew.v[k];
-            }
-        }
-
-        // rotate the register window
-        wb = wc;
-        wc = wa;
-        if (more) {
-            wa = wn;
-            wdv = wdn;
-            hl = hln;
-            hr = hrn;
-        }
-    }
-    if (__any_sync(kFull, bad) && lane == 0) atomicOr(&a.st->err_bits, 1u);
-}
-
-template <typename T>
-cudaError_t launch_bulk(const BulkArgs<T> &a, dim3 grid, cudaStream_t s)
-{
-    bulk_kernel<T><<<grid, kBulkThreads, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
 // ------------------------------------------------------------ edge values
 
-__device__ double load_value(const LoadDesc &L, int64_t n, double dt)
+__device__ __forceinline__ double load_value(const LoadDesc L, int64_t n, double dt)
 {
     const double t = (double)n * dt;
     switch (L.kind) {
@@ -256,6 +93,501 @@ __device__ double load_value(const LoadDesc &L, int64_t n, double dt)
         return 0.0;
     }
 }
+
+// ------------------------------------------------------------ crack step
+//
+// Warp-collective crack handling of Alg. 1 for the state S (in shared
+// memory), given the fields w after the LBM step.  (1) K_III by least squares
+// of the crack opening over the site pairs straddling the crack at r in
+// [r_min, r_min + W) along the crack (eq. sif; Sec. 4.2 and eq. r(v)), in
+// FP64 with a warp reduction.  (2) The criterion: prescribed growth, or
+// |K| > K_C with v = v_max tanh(sqrt((K/K_C)^4 - 1)) (eq. v-tanh).  (3) The
+// advance Delta a = adot dt, rounded to the 2^-32 dh grid; the links at
+// x_i = (i + 1/2) dh with tip < x_i <= tip + Delta a are severed (closed
+// segment).  Lane 0 updates S and the cut mask and, if `commit`, writes the
+// history record.  Two CTAs may run it on the same state at once: both reach
+// the same decision and set the same mask bit.
+template <typename T>
+__device__ __forceinline__ void crack_step_warp(const CrackParams &p, const T *w, int64_t P, uint32_t *cut_v,
+                                                const History &hist, CrackState &S, bool commit)
+{
+    const int lane = threadIdx.x & 31;
+    if (p.mode == CRACK_NONE || S.decided) {
+        __syncwarp();
+        if (lane == 0) S.decided = 1;
+        __syncwarp();
+        return;
+    }
+    const int64_t tip = S.tip_q;
+    const int i_first = S.i_first, i_last = S.i_last;
+    const double r_min = p.r_min_fixed > 0.0 ? p.r_min_fixed : p.r0 / (1.0 - S.v_prev);   // eq. r(v)
+    const double lo = r_min / p.dh, hi = (r_min + p.fit_width) / p.dh;
+    const double tip_h = (double)tip * kTwoM32;
+    int c_lo = (int)floor(tip_h - hi - 0.5) - 1, c_hi = (int)floor(tip_h - lo - 0.5) + 1;
+    c_lo = c_lo < i_first ? i_first : c_lo;
+    c_hi = c_hi > i_last ? i_last : c_hi;
+    const int jc = p.jc;
+    double num = 0.0, den = 0.0;
+    int np = 0;
+    for (int i = c_lo + lane; i <= c_hi; i += 32) {
+        if (!((cut_v[(int64_t)(jc - 1) * p.words + (i >> 5)] >> (i & 31)) & 1u)) continue;
+        const double r_h = (double)(tip - ((int64_t)(2 * i + 1) << (kQBits - 1))) * kTwoM32;
+        if (!(r_h >= lo && r_h < hi)) continue;
+        const double r = r_h * p.dh;
+        const double sf = sqrt(r / (2.0 * kPi));
+        const double delta = (double)w[(int64_t)jc * P + i] - (double)w[(int64_t)(jc - 1) * P + i];
+        num += delta * sf;
+        den += sf * sf;
+        ++np;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        num += __shfl_xor_sync(0xffffffffu, num, o);
+        den += __shfl_xor_sync(0xffffffffu, den, o);
+        np += __shfl_xor_sync(0xffffffffu, np, o);
+    }
+    if (lane == 0) {
+        const double K = np > 0 ? p.mu / 4.0 * num / den : 0.0;
+        int propagate = 0;
+        double v = 0.0;
+        if (p.mode == CRACK_PRESCRIBED) {
+            propagate = 1;
+            v = p.v_rel;
+        } else if (p.mode == CRACK_KCRIT && np > 0 && fabs(K) > p.K_C) {
+            const double ratio = fabs(K) / p.K_C;
+            propagate = 1;
+            v = p.v_max * tanh(sqrt(ratio * ratio * ratio * ratio - 1.0));   // eq. v-tanh
+        }
+        int32_t flags = S.flags;
+        if (!isfinite(K)) flags |= FLAG_NONFINITE;
+        if (S.arrested) { propagate = 0; v = 0.0; }
+        int grew = 0;
+        int64_t tip_new = tip;
+        if (propagate) {
+            const double adot = v * p.cs;
+            const int64_t dq = __double2ll_rn(adot * p.dt / p.dh * 4294967296.0);   // Delta a = adot dt
+            int64_t next = tip + dq;
+            if (next >= p.clamp_q) { next = p.clamp_q; S.arrested = 1; flags |= FLAG_CLAMPED; }
+            if (next > tip) {
+                int64_t last = (next - ((int64_t)1 << (kQBits - 1))) >> kQBits;
+                if (last > p.nx - 1) last = p.nx - 1;
+                const int jr = p.jc - 1;
+                for (int64_t i = (int64_t)i_last + 1; i <= last; ++i) {
+                    if (i < i_first) continue;
+                    atomicOr(&cut_v[(int64_t)jr * p.words + (i >> 5)], 1u << (i & 31));
+                }
+                if (last > i_last && last >= i_first) S.i_last = (int32_t)last;
+                tip_new = next;
+                grew = 1;
+            }
+        }
+        S.tip_q = tip_new;
+        S.v_prev = p.mode == CRACK_PRESCRIBED ? p.v_rel : v;
+        S.K = K;
+        S.v = v;
+        S.r_min = r_min;
+        S.npairs = np;
+        S.grew = grew;
+        S.flags = flags;
+        if (commit && p.hist_cap > 0) {
+            const int64_t h = S.hist_n % p.hist_cap;
+            hist.K[h] = K;
+            hist.v[h] = v;
+            hist.tip[h] = tip_new;
+            hist.np[h] = np;
+        }
+        S.hist_n += 1;
+        S.decided = 1;
+    }
+    __syncwarp();
+}
+
+// ------------------------------------------------------------ step kernel
+//
+// Pads.  After every step the pad cell next to a free edge holds the edge
+// site's own value (the bounce-back image) and the pad next to a periodic
+// edge holds the wrap-around value, both written by the thread that owns the
+// edge site.  Reading the pad as the neighbour then gives the boundary rule
+// with no branch; only Dirichlet edges (value 2 w* - w, time dependent) and
+// severed links need code of their own.
+//
+// Bands.  The rows are split into bands; every band except the two crack
+// sub-bands runs the march below, which holds no severed link (all severed
+// links of the straight crack lie between rows jc-1 and jc).  The crack
+// sub-bands (rows jc-3 .. jc-1 and jc .. jc+2 with the macroscopic rule, rows
+// jc-1 and jc otherwise) run crack_rows; their CTAs that own the next crack
+// link first run the crack step of the previous time step.
+
+// The fields of StepArgs that the crack sub-bands need.  Their out-of-line
+// code receives them as scalars and rebuilds this struct (taking the address
+// of the kernel parameter block would move all of it to local memory, and a
+// struct argument copied field by field from it was not passed reliably).
+template <typename T>
+struct RowArgs {
+    const T *w_in;
+    T *w_out;
+    T *wd;
+    int64_t pitch;
+    int32_t nx, ny, jc, macro;
+    int32_t edge[4];
+    T g, dt;
+    const uint32_t *cut_v;
+    int32_t words;
+    const CrackState *s_in;
+};
+
+// Pad images of the new values of row j, for the next step's neighbours.
+template <typename A, typename T, int N>
+__device__ __forceinline__ void write_pads(const A &a, int x0, int j, const Row<T, N> &wnew)
+{
+    const int nx = a.nx, ny = a.ny;
+    const int64_t P = a.pitch;
+    const int eL = a.edge[LEFT], eR = a.edge[RIGHT], eB = a.edge[BOTTOM], eT = a.edge[TOP];
+    T *row = a.w_out + (int64_t)j * P;   // column 0 of row j
+    if (x0 == 0) {
+        if (eL == EDGE_FREE) row[-1] = wnew.v[0];
+        else if (eL == EDGE_PERIODIC) row[nx] = wnew.v[0];
+    }
+    const int kr = nx - 1 - x0;
+    if (kr >= 0 && kr < N) {
+        T v = wnew.v[0];
+#pragma unroll
+        for (int k = 1; k < N; ++k) if (k == kr) v = wnew.v[k];
+        if (eR == EDGE_FREE) row[nx] = v;
+        else if (eR == EDGE_PERIODIC) row[-1] = v;
+    }
+    if (j == 0 || j == ny - 1) {
+        T *pr = nullptr;
+        if (j == 0 && eB == EDGE_FREE) pr = row - P;
+        else if (j == 0 && eB == EDGE_PERIODIC) pr = a.w_out + (int64_t)ny * P;
+        if (j == ny - 1 && eT == EDGE_FREE) pr = row + P;
+        else if (j == ny - 1 && eT == EDGE_PERIODIC) pr = a.w_out - P;
+        if (pr) {
+#pragma unroll
+            for (int k = 0; k < N; ++k) if (x0 + k < nx) pr[x0 + k] = wnew.v[k];
+        }
+    }
+}
+
+// Store row j of the new fields (masked at the right end of the lattice).
+template <typename A, typename T, int N>
+__device__ __forceinline__ void store_row(const A &a, int x0, int j, const Row<T, N> &wnew,
+                                          const Row<T, N> &wdnew, T &acc)
+{
+    const int64_t o = (int64_t)j * a.pitch + x0;
+    if (x0 + N <= a.nx) {
+        stg_row(a.w_out + o, wnew);
+        stg_row(a.wd + o, wdnew);
+    } else {
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+            if (x0 + k < a.nx) {
+                a.w_out[o + k] = wnew.v[k];
+                a.wd[o + k] = wdnew.v[k];
+            }
+    }
+    acc += wnew.v[0];
+}
+
+// One row of the update with every boundary rule: Dirichlet edges
+// (anti-bounce-back, value 2 w* - w), severed links to the row above (cut_up)
+// and below (cut_dn) (bounce-back, value w); free and periodic edges come in
+// through the pads.
+// Twice the Dirichlet value of each edge at t_n (anti-bounce-back sends 2 w* - w),
+// read once per CTA.
+template <typename T> struct EdgeValues { T two_ws[4]; };
+
+template <typename T>
+__device__ __forceinline__ EdgeValues<T> edge_values(const CrackState *s_in)
+{
+    EdgeValues<T> E;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) E.two_ws[e] = (T)2 * (T)s_in->wstar[e];
+    return E;
+}
+
+template <typename A, typename T, int N>
+__device__ __forceinline__ void row_update(const A &a, const EdgeValues<T> &E, int x0, int j, const Row<T, N> &wc,
+                                           const Row<T, N> &up0, const Row<T, N> &dn0, const Row<T, N> &wdv, T left0,
+                                           T rightN, uint32_t cut_up, uint32_t cut_dn, Row<T, N> &wnew,
+                                           Row<T, N> &wdnew)
+{
+    const int nx = a.nx, ny = a.ny;
+    const bool dir_t = j == ny - 1 && a.edge[TOP] == EDGE_DIRICHLET;
+    const bool dir_b = j == 0 && a.edge[BOTTOM] == EDGE_DIRICHLET;
+    const bool dir_l = a.edge[LEFT] == EDGE_DIRICHLET, dir_r = a.edge[RIGHT] == EDGE_DIRICHLET;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const T w0 = wc.v[k];
+        T wl = k == 0 ? left0 : wc.v[k - 1];
+        T wr = k == N - 1 ? rightN : wc.v[k + 1];
+        T up = up0.v[k], dn = dn0.v[k];
+        if (dir_t) up = E.two_ws[TOP] - w0;
+        else if ((cut_up >> k) & 1u) up = w0;
+        if (dir_b) dn = E.two_ws[BOTTOM] - w0;
+        else if ((cut_dn >> k) & 1u) dn = w0;
+        if (dir_l && x0 + k == 0) wl = E.two_ws[LEFT] - w0;
+        if (dir_r && x0 + k == nx - 1) wr = E.two_ws[RIGHT] - w0;
+        const T lap = ((up + dn) + (wl + wr)) - (T)4 * w0;
+        wdnew.v[k] = wdv.v[k] + a.g * lap;
+        wnew.v[k] = w0 + a.dt * wdnew.v[k];
+    }
+}
+
+// A crack sub-band of HH rows: rows jc-HH .. jc-1 (below the crack) or
+// jc .. jc+HH-1 (above).  All of its loads are issued at once, then the rows
+// are computed from registers, so the sub-band costs about one memory latency
+// even while the rest of the lattice saturates HBM.  With the macroscopic
+// crack-face rule (Sec. 3.1, HH = 3), the boundary point x_B next to a severed
+// link takes w_B = 1.5 w_I - 0.5 w_II from the two new values of its column
+// further away from the crack, and wdot(x_B) = (w_B(t+dt) - w_B(t)) / dt.
+template <typename T, int HH>
+__device__ __noinline__ T crack_rows(const T *w_in_, T *w_out_, T *wd_, int64_t pitch_, int nx_, int ny_, int jc_,
+                                     int macro_, int edges, T g_, T dt_, const uint32_t *cut_v_, int words_,
+                                     const CrackState *s_in_, int cb, int j0)
+{
+    RowArgs<T> a;
+    a.w_in = w_in_;
+    a.w_out = w_out_;
+    a.wd = wd_;
+    a.pitch = pitch_;
+    a.nx = nx_;
+    a.ny = ny_;
+    a.jc = jc_;
+    a.macro = macro_;
+    for (int e = 0; e < 4; ++e) a.edge[e] = (edges >> (2 * e)) & 3;
+    a.g = g_;
+    a.dt = dt_;
+    a.cut_v = cut_v_;
+    a.words = words_;
+    a.s_in = s_in_;
+    T acc = (T)0;
+    constexpr int N = Vec<T>::N;
+    typedef Row<T, N> R;
+    const unsigned kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int x0 = (cb * kThreads + threadIdx.x) * N;
+    const int jc = a.jc;
+    const int64_t P = a.pitch;
+    const T *win = a.w_in + x0;
+    const bool below = j0 + HH == jc;
+    R w[HH + 2], wd[HH];
+    T hl[HH], hr[HH];
+#pragma unroll
+    for (int q = 0; q < HH + 2; ++q) ldg_row(win + (int64_t)(j0 - 1 + q) * P, w[q]);
+#pragma unroll
+    for (int q = 0; q < HH; ++q) {
+        ld_row(a.wd + x0 + (int64_t)(j0 + q) * P, wd[q]);
+        hl[q] = lane == 0 ? win[(int64_t)(j0 + q) * P - 1] : (T)0;
+        hr[q] = lane == 31 ? win[(int64_t)(j0 + q) * P + N] : (T)0;
+    }
+    const EdgeValues<T> E = edge_values<T>(a.s_in);
+    __syncthreads();   // the crack step of the writer CTA has severed the next link
+    const uint32_t cut = x0 < a.nx ? (a.cut_v[(int64_t)(jc - 1) * a.words + (x0 >> 5)] >> (x0 & 31)) & ((1u << N) - 1u) : 0u;
+    (void)jc;
+    R o[HH], od[HH];
+#pragma unroll
+    for (int q = 0; q < HH; ++q) {
+        const int j = j0 + q;
+        T left0 = __shfl_up_sync(kFull, w[q + 1].v[N - 1], 1);
+        T rightN = __shfl_down_sync(kFull, w[q + 1].v[0], 1);
+        if (lane == 0) left0 = hl[q];
+        if (lane == 31) rightN = hr[q];
+        const uint32_t cut_up = (below && j == jc - 1) ? cut : 0u;
+        const uint32_t cut_dn = (!below && j == jc) ? cut : 0u;
+        row_update(a, E, x0, j, w[q + 1], w[q + 2], w[q], wd[q], left0, rightN, cut_up, cut_dn, o[q], od[q]);
+    }
+    if (HH >= 3 && a.macro && cut) {
+        // x_B on row jc-1 (x_I, x_II on jc-2, jc-3) or on row jc (jc+1, jc+2)
+        const int qb = below ? HH - 1 : 0, qi = below ? HH - 2 : 1, qii = below ? HH - 3 : 2;
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+            if ((cut >> k) & 1u) {
+                const T wB = (T)1.5 * o[qi].v[k] - (T)0.5 * o[qii].v[k];
+                od[qb].v[k] = (wB - w[qb + 1].v[k]) / a.dt;
+                o[qb].v[k] = wB;
+            }
+    }
+    if (x0 < a.nx) {
+#pragma unroll
+        for (int q = 0; q < HH; ++q) {
+            store_row(a, x0, j0 + q, o[q], od[q], acc);
+            write_pads(a, x0, j0 + q, o[q]);
+        }
+    }
+    return acc;
+}
+
+// The bulk of the lattice: a thread owns N consecutive columns (one 16-byte
+// vector) of a band and marches up through it, keeping rows j-1, j, j+1 of w
+// in registers, so each w value is loaded once per step (plus one halo row at
+// each band end, which the neighbouring band reads at about the same time, so
+// it comes from L2).  East/west neighbours come from the adjacent lanes by
+// warp shuffles; lanes 0 and 31 load the halo column.  The next row's loads
+// are issued before the current row is computed.  EDGE = false is the
+// interior version (no edge row or column in the CTA): the bare update.
+template <typename T, bool EDGE>
+__device__ __forceinline__ void march(const StepArgs<T> &a, int cb, int j0, int j1, T &acc)
+{
+    constexpr int N = Vec<T>::N;
+    typedef Row<T, N> R;
+    const unsigned kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int x0 = (cb * kThreads + threadIdx.x) * N;
+    const int64_t P = a.pitch;
+    const T *win = a.w_in + x0;
+    T *wout = a.w_out + x0;
+    T *wdp = a.wd + x0;
+    R wb, wc, wa, wdv;
+    ldg_row(win + (int64_t)(j0 - 1) * P, wb);
+    ldg_row(win + (int64_t)j0 * P, wc);
+    ldg_row(win + (int64_t)(j0 + 1) * P, wa);
+    ld_row(wdp + (int64_t)j0 * P, wdv);
+    T hl = (T)0, hr = (T)0;
+    if (lane == 0) hl = win[(int64_t)j0 * P - 1];
+    if (lane == 31) hr = win[(int64_t)j0 * P + N];
+    const T g = a.g, dt = a.dt;
+    EdgeValues<T> E;
+    if (EDGE) E = edge_values<T>(a.s_in);
+    for (int j = j0; j < j1; ++j) {
+        R wn, wdn;
+        T hln = (T)0, hrn = (T)0;
+        const bool more = j + 1 < j1;
+        if (more) {
+            ldg_row(win + (int64_t)(j + 2) * P, wn);
+            ld_row(wdp + (int64_t)(j + 1) * P, wdn);
+            if (lane == 0) hln = win[(int64_t)(j + 1) * P - 1];
+            if (lane == 31) hrn = win[(int64_t)(j + 1) * P + N];
+        }
+        T left0 = __shfl_up_sync(kFull, wc.v[N - 1], 1);
+        T rightN = __shfl_down_sync(kFull, wc.v[0], 1);
+        if (lane == 0) left0 = hl;
+        if (lane == 31) rightN = hr;
+        R wnew, wdnew;
+        if (EDGE) {
+            row_update(a, E, x0, j, wc, wa, wb, wdv, left0, rightN, 0u, 0u, wnew, wdnew);
+            if (x0 < a.nx) {
+                store_row(a, x0, j, wnew, wdnew, acc);
+                write_pads(a, x0, j, wnew);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                const T wl = k == 0 ? left0 : wc.v[k - 1];
+                const T wr = k == N - 1 ? rightN : wc.v[k + 1];
+                const T lap = ((wa.v[k] + wb.v[k]) + (wl + wr)) - (T)4 * wc.v[k];
+                wdnew.v[k] = wdv.v[k] + g * lap;
+                wnew.v[k] = wc.v[k] + dt * wdnew.v[k];
+            }
+            stg_row(wout + (int64_t)j * P, wnew);
+            stg_row(wdp + (int64_t)j * P, wdnew);
+            acc += wnew.v[0];
+        }
+        wb = wc;
+        wc = wa;
+        if (more) {
+            wa = wn;
+            wdv = wdn;
+            hl = hln;
+            hr = hrn;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBlocks - 2) step_kernel(const StepArgs<T> a)
+{
+    constexpr int N = Vec<T>::N;
+    __shared__ CrackState sS;
+    const unsigned kFull = 0xffffffffu;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int cb = blockIdx.x, band = blockIdx.y;
+    const Unit U = a.units[band];
+    const int j0 = U.j0, j1 = U.j1;
+    const int nx = a.nx;
+    const CrackParams &p = a.p;
+    T acc = (T)0;
+
+    if (a.crack_band >= 0 && (band == a.crack_band || band == a.crack_band + 1)) {
+        // The crack step of Alg. 1 that follows the previous LBM step, by the
+        // two crack sub-band CTAs that own the next crack link: both reach the
+        // same decision; the one below the crack records it.
+        int i_next = a.s_in->i_last + 1;
+        i_next = max(i_next, a.s_in->i_first);
+        i_next = min(max(i_next, 0), nx - 1);
+        const bool commit = band == a.crack_band;
+        if (cb == i_next / (kThreads * N) && tid < 32) {
+            if (tid == 0) sS = *a.s_in;
+            __syncwarp();
+            crack_step_warp<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, commit);
+            if (tid == 0 && commit) {
+                const int64_t n = sS.step + 1;
+                sS.step = n;
+                sS.decided = 0;
+                for (int e = 0; e < 4; ++e)
+                    sS.wstar[e] = a.edge[e] == EDGE_DIRICHLET ? load_value(a.load[e], n, (double)p.dt) : 0.0;
+                *a.s_out = sS;
+            }
+        }
+        const int edges = a.edge[0] | (a.edge[1] << 2) | (a.edge[2] << 4) | (a.edge[3] << 6);
+        acc = p.macro ? crack_rows<T, 3>(a.w_in, a.w_out, a.wd, a.pitch, a.nx, a.ny, p.jc, p.macro, edges, a.g, a.dt,
+                                         a.cut_v, a.words, a.s_in, cb, j0)
+                      : crack_rows<T, 1>(a.w_in, a.w_out, a.wd, a.pitch, a.nx, a.ny, p.jc, p.macro, edges, a.g, a.dt,
+                                         a.cut_v, a.words, a.s_in, cb, j0);
+    } else {
+        if (a.crack_band < 0 && cb == 0 && band == 0 && tid == 0) {
+            // no crack: only the step counter and the Dirichlet values advance
+            sS = *a.s_in;
+            const int64_t n = sS.step + 1;
+            sS.step = n;
+            sS.decided = 1;
+            for (int e = 0; e < 4; ++e)
+                sS.wstar[e] = a.edge[e] == EDGE_DIRICHLET ? load_value(a.load[e], n, (double)p.dt) : 0.0;
+            *a.s_out = sS;
+        }
+        const bool edge = (cb == 0) | (cb == a.ncb - 1) | (j0 == 0) | (j1 == a.ny);
+        if (edge) march<T, true>(a, cb, j0, j1, acc);
+        else march<T, false>(a, cb, j0, j1, acc);
+    }
+    // a non-finite w (or wdot, which enters w) turns the sum of the first
+    // component of each vector non-finite within a step or two
+    if (__any_sync(kFull, !isfinite(acc)) && lane == 0) atomicOr(a.err, (uint32_t)ERR_NONFINITE);
+}
+
+template <typename T> const void *step_kernel_ptr()
+{
+    return reinterpret_cast<const void *>(&step_kernel<T>);
+}
+
+template <typename T>
+cudaError_t launch_step(const StepArgs<T> &a, int bands, cudaStream_t s)
+{
+    step_kernel<T><<<dim3((unsigned)a.ncb, (unsigned)bands), kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------- pending crack step
+
+// The crack step that follows the last enqueued LBM step, applied in place
+// before the host reads the state (one warp).
+template <typename T>
+__global__ void finalize_kernel(const FinalizeArgs<T> a)
+{
+    __shared__ CrackState sS;
+    if (threadIdx.x == 0) sS = *a.st;
+    __syncwarp();
+    crack_step_warp<T>(a.p, a.w, a.pitch, a.cut_v, a.hist, sS, true);
+    if (threadIdx.x == 0) *a.st = sS;
+}
+
+template <typename T>
+cudaError_t launch_finalize(const FinalizeArgs<T> &a, cudaStream_t s)
+{
+    finalize_kernel<T><<<1, 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- initial w*(t_0)
 
 struct WstarArgs {
     CrackState *st;
@@ -284,187 +616,48 @@ cudaError_t launch_wstar(CrackState *st, const LoadDesc *load, const int32_t *ed
 
 // ------------------------------------------------------ periodic pad images
 
+// Pad images for fields set from outside: the bounce-back image (the edge
+// site's own value) next to free edges, the wrap-around value next to
+// periodic ones; pads next to Dirichlet edges are not read.
+struct PadEdges {
+    int32_t e[4];
+};
+
 template <typename T>
-__global__ void fill_pads_kernel(T *w, int64_t P, int nx, int ny, int xper, int yper)
+__global__ void fill_pads_kernel(T *w, int64_t P, int nx, int ny, PadEdges E)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (yper && t < nx) {
-        w[(int64_t)ny * P + t] = w[t];                    // row ny <- row 0
-        w[-P + t] = w[(int64_t)(ny - 1) * P + t];         // row -1 <- row ny-1
+    if (t < nx) {
+        if (E.e[BOTTOM] == EDGE_FREE) w[-P + t] = w[t];
+        else if (E.e[BOTTOM] == EDGE_PERIODIC) w[-P + t] = w[(int64_t)(ny - 1) * P + t];
+        if (E.e[TOP] == EDGE_FREE) w[(int64_t)ny * P + t] = w[(int64_t)(ny - 1) * P + t];
+        else if (E.e[TOP] == EDGE_PERIODIC) w[(int64_t)ny * P + t] = w[t];
     }
-    if (xper && t < ny) {
-        w[(int64_t)t * P + nx] = w[(int64_t)t * P];       // column nx <- column 0
-        w[(int64_t)t * P - 1] = w[(int64_t)t * P + nx - 1];
+    if (t < ny) {
+        T *row = w + (int64_t)t * P;
+        if (E.e[LEFT] == EDGE_FREE) row[-1] = row[0];
+        else if (E.e[LEFT] == EDGE_PERIODIC) row[-1] = row[nx - 1];
+        if (E.e[RIGHT] == EDGE_FREE) row[nx] = row[nx - 1];
+        else if (E.e[RIGHT] == EDGE_PERIODIC) row[nx] = row[0];
     }
 }
 
 template <typename T>
 cudaError_t launch_fill_pads(T *w, int64_t pitch, int nx, int ny, const int32_t *edge, cudaStream_t s)
 {
-    const int xper = edge[LEFT] == EDGE_PERIODIC, yper = edge[BOTTOM] == EDGE_PERIODIC;
-    if (!xper && !yper) return cudaSuccess;
+    PadEdges E;
+    for (int q = 0; q < 4; ++q) E.e[q] = edge[q];
     const int n = nx > ny ? nx : ny;
-    fill_pads_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(w, pitch, nx, ny, xper, yper);
+    fill_pads_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(w, pitch, nx, ny, E);
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------------- crack step
-//
-// One CTA.  (1) Macroscopic crack-face rule (Sec. 3.1) on the boundary points
-// of every severed crack link: for a lattice-aligned crack the normal through
-// x_B is its column, x_I and x_II are the next two sites away from the face
-// (distances 3/2 dh and 5/2 dh from it, x_B at 1/2 dh), and the quadratic
-// p(s) = a + b s^2 with zero slope on the traction-free face gives
-// w_B = (3 w_I - w_II) / 2; eq. f-macro-bc then makes wdot(x_B) =
-// (w_B(t+dt) - w_B(t)) / dt.  (2) K_III by least squares of the crack opening
-// over the site pairs straddling the crack at r in [r_min, r_min + W)
-// (eq. sif, Sec. 4.2) in FP64 with a block reduction.  (3) Alg. 1: the
-// criterion, the advance Delta a = adot dt on the 2^-32 dh grid, and the
-// severing of the newly crossed links; then the history record and the
-// Dirichlet values for the next step.
-template <typename T>
-__global__ void __launch_bounds__(kCrackThreads) crack_kernel(const CrackArgs<T> a)
-{
-    CrackState *st = a.st;
-    const CrackParams &p = a.p;
-    const int tid = threadIdx.x;
-    const int64_t P = a.pitch;
-    __shared__ double s_num[kCrackThreads / 32], s_den[kCrackThreads / 32];
-    __shared__ int s_np[kCrackThreads / 32];
-
-    const int i_first = st->i_first, i_last = st->i_last;
-    if (p.mode != CRACK_NONE && p.macro && i_last >= i_first) {
-        const int jc = p.jc;
-        for (int c = i_first + tid; c <= i_last; c += kCrackThreads) {
-            {   // below the crack: x_I = (c, jc-2), x_II = (c, jc-3)
-                const T wI = a.w_out[(int64_t)(jc - 2) * P + c], wII = a.w_out[(int64_t)(jc - 3) * P + c];
-                const T wB = (T)1.5 * wI - (T)0.5 * wII;
-                const T wold = a.w_in[(int64_t)(jc - 1) * P + c];
-                a.w_out[(int64_t)(jc - 1) * P + c] = wB;
-                a.wd[(int64_t)(jc - 1) * P + c] = (wB - wold) / a.dt;
-            }
-            {   // above the crack: x_I = (c, jc+1), x_II = (c, jc+2)
-                const T wI = a.w_out[(int64_t)(jc + 1) * P + c], wII = a.w_out[(int64_t)(jc + 2) * P + c];
-                const T wB = (T)1.5 * wI - (T)0.5 * wII;
-                const T wold = a.w_in[(int64_t)jc * P + c];
-                a.w_out[(int64_t)jc * P + c] = wB;
-                a.wd[(int64_t)jc * P + c] = (wB - wold) / a.dt;
-            }
-        }
-    }
-    __syncthreads();
-
-    double r_min = 0.0, num = 0.0, den = 0.0;
-    int np = 0;
-    const int64_t tip = st->tip_q;
-    if (p.mode != CRACK_NONE) {
-        r_min = p.r_min_fixed > 0.0 ? p.r_min_fixed : p.r0 / (1.0 - st->v_prev);   // eq. r(v)
-        const double lo = r_min / p.dh, hi = (r_min + p.fit_width) / p.dh;
-        const double tip_h = (double)tip * kTwoM32;
-        int c_lo = (int)floor(tip_h - hi - 0.5) - 1, c_hi = (int)floor(tip_h - lo - 0.5) + 1;
-        c_lo = c_lo < i_first ? i_first : c_lo;
-        c_hi = c_hi > i_last ? i_last : c_hi;
-        const int jc = p.jc;
-        for (int i = c_lo + tid; i <= c_hi; i += kCrackThreads) {
-            if (!((a.cut_v[(int64_t)(jc - 1) * p.words + (i >> 5)] >> (i & 31)) & 1u)) continue;
-            const double r_h = (double)(tip - ((int64_t)(2 * i + 1) << (kQBits - 1))) * kTwoM32;
-            if (!(r_h >= lo && r_h < hi)) continue;
-            const double r = r_h * p.dh;
-            const double sf = sqrt(r / (2.0 * kPi));
-            const double delta = (double)a.w_out[(int64_t)jc * P + i] - (double)a.w_out[(int64_t)(jc - 1) * P + i];
-            num += delta * sf;
-            den += sf * sf;
-            ++np;
-        }
-    }
-    // block reduction (warp shuffles, then one value per warp)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        num += __shfl_down_sync(0xffffffffu, num, o);
-        den += __shfl_down_sync(0xffffffffu, den, o);
-        np += __shfl_down_sync(0xffffffffu, np, o);
-    }
-    if ((tid & 31) == 0) { s_num[tid >> 5] = num; s_den[tid >> 5] = den; s_np[tid >> 5] = np; }
-    __syncthreads();
-    if (tid != 0) return;
-    num = 0.0; den = 0.0; np = 0;
-    for (int q = 0; q < kCrackThreads / 32; ++q) { num += s_num[q]; den += s_den[q]; np += s_np[q]; }
-
-    int32_t flags = st->flags;
-    if (st->err_bits) flags |= FLAG_NONFINITE;
-    if (p.mode != CRACK_NONE) {
-        const double K = np > 0 ? p.mu / 4.0 * num / den : 0.0;
-        int propagate = 0;
-        double v = 0.0;
-        if (p.mode == CRACK_PRESCRIBED) {
-            propagate = 1;
-            v = p.v_rel;
-        } else if (p.mode == CRACK_KCRIT && np > 0 && fabs(K) > p.K_C) {
-            const double ratio = fabs(K) / p.K_C;
-            propagate = 1;
-            v = p.v_max * tanh(sqrt(ratio * ratio * ratio * ratio - 1.0));   // eq. v-tanh
-        }
-        if (!isfinite(K)) flags |= FLAG_NONFINITE;
-        if (st->arrested) { propagate = 0; v = 0.0; }
-        int grew = 0;
-        int64_t tip_new = tip;
-        if (propagate) {
-            const double adot = v * p.cs;
-            const int64_t dq = __double2ll_rn(adot * p.dt / p.dh * 4294967296.0);   // Delta a = adot dt
-            int64_t next = tip + dq;
-            if (next >= p.clamp_q) { next = p.clamp_q; st->arrested = 1; flags |= FLAG_CLAMPED; }
-            if (next > tip) {
-                // links at x_i = (i + 1/2) dh with tip < x_i <= next are crossed by the new segment
-                int64_t last = (next - ((int64_t)1 << (kQBits - 1))) >> kQBits;
-                if (last > p.nx - 1) last = p.nx - 1;
-                const int jr = p.jc - 1;
-                for (int64_t i = (int64_t)i_last + 1; i <= last; ++i) {
-                    if (i < i_first) continue;
-                    a.cut_v[(int64_t)jr * p.words + (i >> 5)] |= 1u << (i & 31);
-                }
-                if (last > i_last && last >= i_first) {
-                    st->i_last = (int32_t)last;
-                    a.rowflag[jr] |= 2;
-                    a.rowflag[jr + 1] |= 4;
-                }
-                tip_new = next;
-                grew = 1;
-            }
-        }
-        st->tip_q = tip_new;
-        st->v_prev = p.mode == CRACK_PRESCRIBED ? p.v_rel : v;
-        st->K = K;
-        st->v = v;
-        st->r_min = r_min;
-        st->npairs = np;
-        st->grew = grew;
-        if (p.hist_cap > 0) {
-            const int64_t h = st->hist_n % p.hist_cap;
-            a.hist.K[h] = K;
-            a.hist.v[h] = v;
-            a.hist.tip[h] = tip_new;
-            a.hist.np[h] = np;
-        }
-        st->hist_n += 1;
-    }
-    st->flags = flags;
-    const int64_t n = st->step + 1;
-    st->step = n;
-    for (int e = 0; e < 4; ++e)
-        st->wstar[e] = a.edge[e] == EDGE_DIRICHLET ? load_value(a.load[e], n, (double)p.dt) : 0.0;
-}
-
-template <typename T>
-cudaError_t launch_crack(const CrackArgs<T> &a, cudaStream_t s)
-{
-    crack_kernel<T><<<1, kCrackThreads, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-template cudaError_t launch_bulk<float>(const BulkArgs<float> &, dim3, cudaStream_t);
-template cudaError_t launch_bulk<double>(const BulkArgs<double> &, dim3, cudaStream_t);
-template cudaError_t launch_crack<float>(const CrackArgs<float> &, cudaStream_t);
-template cudaError_t launch_crack<double>(const CrackArgs<double> &, cudaStream_t);
+template const void *step_kernel_ptr<float>();
+template const void *step_kernel_ptr<double>();
+template cudaError_t launch_step<float>(const StepArgs<float> &, int, cudaStream_t);
+template cudaError_t launch_step<double>(const StepArgs<double> &, int, cudaStream_t);
+template cudaError_t launch_finalize<float>(const FinalizeArgs<float> &, cudaStream_t);
+template cudaError_t launch_finalize<double>(const FinalizeArgs<double> &, cudaStream_t);
 template cudaError_t launch_fill_pads<float>(float *, int64_t, int, int, const int32_t *, cudaStream_t);
 template cudaError_t launch_fill_pads<double>(double *, int64_t, int, int, const int32_t *, cudaStream_t);
 

@@ -108,14 +108,14 @@ def lbm_set_stream(h: int, stream: int):
     _check(load_library().lbm_set_stream(C.c_void_p(h), C.c_void_p(stream)))
 
 
-def lbm_set_launch(h: int, rows_per_cta: int):
-    _check(load_library().lbm_set_launch(C.c_void_p(h), int(rows_per_cta)))
+def lbm_set_launch(h: int, band_rows: int):
+    _check(load_library().lbm_set_launch(C.c_void_p(h), int(band_rows)))
 
 
-def lbm_get_launch(h: int):
-    r, gx, gy = C.c_int32(), C.c_int32(), C.c_int32()
-    _check(load_library().lbm_get_launch(C.c_void_p(h), C.byref(r), C.byref(gx), C.byref(gy)))
-    return r.value, gx.value, gy.value
+def lbm_get_launch(h: int) -> dict:
+    r, c, t, s = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+    _check(load_library().lbm_get_launch(C.c_void_p(h), C.byref(r), C.byref(c), C.byref(t), C.byref(s)))
+    return {"band_rows": r.value, "ctas": c.value, "threads": t.value, "ctas_per_sm": s.value}
 
 
 def lbm_set_profiling(h: int, enable: bool):
@@ -127,7 +127,7 @@ def lbm_profile_read(h: int, reset: bool = False):
     nb, nc = C.c_int64(), C.c_int64()
     _check(load_library().lbm_profile_read(C.c_void_p(h), C.byref(bm), C.byref(nb), C.byref(cm), C.byref(nc),
                                            int(bool(reset))))
-    return {"bulk_ms": bm.value, "n_bulk": nb.value, "crack_ms": cm.value, "n_crack": nc.value}
+    return {"step_ms": bm.value, "n_step": nb.value, "finalize_ms": cm.value, "n_finalize": nc.value}
 
 
 def lbm_device_bytes(h: int) -> int:
@@ -263,8 +263,8 @@ class Lattice:
     def step(self, n: int = 1):
         lbm_step(self.h, n)
 
-    def set_launch(self, rows_per_cta: int):
-        lbm_set_launch(self.h, rows_per_cta)
+    def set_launch(self, band_rows: int):
+        lbm_set_launch(self.h, band_rows)
 
     def launch(self):
         return lbm_get_launch(self.h)
