@@ -233,12 +233,11 @@ def run_ours(args, rank, world, local):
         lat.close()
         return 0
 
-    lat.set_profiling(True)
+    # timed region: one step per pair of events, L2 flushed in between (outside the events)
     for _ in range(args.warmup):
         flush_l2()
         lat.step(1)
     lat.sync()
-    lat.profile(reset=True)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clocks = ClockSampler(local)
@@ -256,10 +255,17 @@ def run_ours(args, rank, world, local):
     wall = time.perf_counter() - t0
     clk = clocks.stop()
     step_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    prof = lat.profile(reset=True)
-    lat.set_profiling(False)
     total_s = allmax(step_ms * 1e-3)
     value = world * sites * args.steps / total_s / 1e9
+
+    # the step kernel alone, timed by the library's events on the same stream
+    lat.set_profiling(True)
+    for _ in range(args.steps):
+        flush_l2()
+        lat.step(1)
+    lat.sync()
+    prof = lat.profile(reset=True)
+    lat.set_profiling(False)
     kern_s = prof["step_ms"] / max(prof["n_step"], 1) * 1e-3
     achieved = BYTES_PER_SITE * sites / kern_s / 1e9
     peak, peak_kind = measured_peaks()
