@@ -64,8 +64,12 @@ enum { LBM_EDGE_FREE = 0, LBM_EDGE_DIRICHLET = 1, LBM_EDGE_PERIODIC = 2 };
 enum { LBM_LEFT = 0, LBM_RIGHT = 1, LBM_BOTTOM = 2, LBM_TOP = 3 };
 enum { LBM_D2Q5 = 0 };
 enum { LBM_FORM_MOMENT = 0 };
-/* storage (and arithmetic) precision of the fields */
-enum { LBM_F64 = 0, LBM_F32 = 1 };
+/* storage of the fields.  LBM_F64: w and wdot in FP64, FP64 arithmetic.
+ * LBM_F32: w and wdot in FP32, FP32 arithmetic.  LBM_F32_WD_BF16 /
+ * LBM_F32_WD_F16: w in FP32, wdot stored in 16 bits (BF16, or FP16 holding
+ * wdot * scale, see lbm_set_wd_scale), FP32 arithmetic; 12 bytes per site
+ * update instead of 16.  Also the dtype codes of field exchange. */
+enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F32_WD_BF16 = 2, LBM_F32_WD_F16 = 3 };
 /* treatment of the crack faces */
 enum { LBM_BC_BOUNCEBACK = 0, LBM_BC_MACROSCOPIC = 1 };
 /* crack modes (Alg. 1 "criterion") */
@@ -89,8 +93,9 @@ typedef struct lbm_grid {
 } lbm_grid;
 
 /* Lattice model.  velocity_set = LBM_D2Q5, form = LBM_FORM_MOMENT,
- * omega = dt / tau = 1 (the paper fixes tau = dt; Sec. 3).  storage is
- * LBM_F64 or LBM_F32; bc_mode selects the crack-face treatment. */
+ * omega = dt / tau = 1 (the paper fixes tau = dt; Sec. 3).  storage is an
+ * LBM_F64 / LBM_F32 / LBM_F32_WD_* code; bc_mode selects the crack-face
+ * treatment. */
 typedef struct lbm_lattice {
     int32_t velocity_set;
     int32_t form;
@@ -173,13 +178,15 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lb
 lbm_status lbm_step(lbm_handle *h, int64_t n);
 
 /* Copy field `which` (LBM_FIELD_W or LBM_FIELD_WDOT) as a dense ny x nx
- * row-major array of the storage precision (dtype = storage) into dst, which
- * lies in device memory if dst_on_device, else in host memory (then the
- * stream is synchronised before returning). */
+ * row-major array into dst, which lies in device memory if dst_on_device,
+ * else in host memory (then the stream is synchronised before returning).
+ * dtype is LBM_F64 for F64 storage and LBM_F32 for every other storage
+ * (16-bit wdot planes are converted to FP32). */
 lbm_status lbm_fields(lbm_handle *h, int32_t which, void *dst, int32_t dst_on_device, int32_t dtype);
 
-/* Overwrite field `which` from a dense ny x nx row-major array of the storage
- * precision.  Crack, step counter and history are left unchanged. */
+/* Overwrite field `which` from a dense ny x nx row-major array of dtype
+ * (as for lbm_fields; FP32 input is rounded to a 16-bit wdot plane).  Crack,
+ * step counter and history are left unchanged. */
 lbm_status lbm_set_fields(lbm_handle *h, int32_t which, const void *src, int32_t src_on_device, int32_t dtype);
 
 /* Copy a cut mask into host memory: row j occupies words_per_row =
@@ -226,6 +233,15 @@ lbm_status lbm_set_profiling(lbm_handle *h, int32_t enable);
  * clears them.  Synchronises the stream. */
 lbm_status lbm_profile_read(lbm_handle *h, double *step_ms, int64_t *n_step, double *finalize_ms, int64_t *n_finalize,
                             int32_t reset);
+
+/* Scale of FP16 wdot storage (LBM_F32_WD_F16): the plane holds wdot * scale.
+ * scale must be a power of two; the stored plane is rescaled.  lbm_create
+ * picks 2^(10 - ceil(log2 r)), r the largest rate of change of the edge values
+ * (1024 without loads), so that waves up to 64 times that rate fit.  A value
+ * that overflows FP16 becomes infinite and is reported as LBM_ERR_UNSTABLE.
+ * Returns LBM_ERR_STATE for other storages. */
+lbm_status lbm_set_wd_scale(lbm_handle *h, double scale);
+lbm_status lbm_get_wd_scale(const lbm_handle *h, double *scale);
 
 /* Bytes of device memory the handle holds. */
 lbm_status lbm_device_bytes(const lbm_handle *h, int64_t *bytes);

@@ -10,7 +10,7 @@ STATUS_NAMES = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR
 
 EDGE = {"free": 0, "dirichlet": 1, "periodic": 2}
 EDGE_INDEX = {"left": 0, "right": 1, "bottom": 2, "top": 3}
-STORAGE = {"f64": 0, "f32": 1}
+STORAGE = {"f64": 0, "f32": 1, "f32_bf16": 2, "f32_f16": 3}
 BC = {"bounceback": 0, "macroscopic": 1}
 CRACK = {"none": 0, "stationary": 1, "prescribed": 2, "kcrit": 3}
 LOAD = {"zero": 0, "linear": 1, "sin2": 2, "halfsine": 3, "series": 4, "const": 5}
@@ -80,6 +80,8 @@ PROTOTYPES = {
     "lbm_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
     "lbm_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                    C.POINTER(C.c_int64), C.c_int32]),
+    "lbm_set_wd_scale": (C.c_int, [C.c_void_p, C.c_double]),
+    "lbm_get_wd_scale": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "lbm_device_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "lbm_destroy": (None, [C.c_void_p]),
     "lbm_last_error": (C.c_char_p, []),

@@ -51,7 +51,10 @@ struct lbm_handle {
     lbm_lattice lat;
     lbm_material mat;
     lbm_crack crack;
-    size_t esize;
+    size_t esize;        // bytes per w element (and per arithmetic value)
+    size_t esize_d;      // bytes per stored wdot element
+    double wd_scale;     // stored wdot = wdot * wd_scale (16-bit storage)
+    float *staging;      // nx * ny floats for 16-bit wdot conversions
     int64_t pitch;       // elements per padded row
     int32_t words;       // 32-bit mask words per row
     int32_t jc;          // crack line y = jc dh
@@ -92,12 +95,14 @@ struct lbm_handle {
 
 namespace {
 
-template <typename T>
-void make_step_args(const lbm_handle *h, int par, StepArgs<T> &a)
+template <typename T, typename D>
+void make_step_args(const lbm_handle *h, int par, StepArgs<T, D> &a)
 {
     a.w_in = static_cast<const T *>(h->w[par]);
     a.w_out = static_cast<T *>(h->w[par ^ 1]);
-    a.wd = static_cast<T *>(h->wd);
+    a.wd = static_cast<D *>(h->wd);
+    a.wd_scale = (T)h->wd_scale;
+    a.wd_inv = (T)(1.0 / h->wd_scale);
     a.pitch = h->pitch;
     a.nx = h->grid.nx;
     a.ny = h->grid.ny;
@@ -117,21 +122,54 @@ void make_step_args(const lbm_handle *h, int par, StepArgs<T> &a)
     a.hist = h->hist;
 }
 
-cudaError_t enqueue_step(const lbm_handle *h, int par, cudaStream_t s)
+template <typename T, typename D>
+cudaError_t enqueue_step_t(const lbm_handle *h, int par, cudaStream_t s)
 {
-    if (h->lat.storage == LBM_F32) {
-        StepArgs<float> a;
-        make_step_args(h, par, a);
-        return launch_step(a, h->n_bands, s);
-    }
-    StepArgs<double> a;
+    StepArgs<T, D> a;
     make_step_args(h, par, a);
     return launch_step(a, h->n_bands, s);
 }
 
+cudaError_t enqueue_step(const lbm_handle *h, int par, cudaStream_t s)
+{
+    switch (h->lat.storage) {
+    case LBM_F32: return enqueue_step_t<float, float>(h, par, s);
+    case LBM_F32_WD_BF16: return enqueue_step_t<float, __nv_bfloat16>(h, par, s);
+    case LBM_F32_WD_F16: return enqueue_step_t<float, __half>(h, par, s);
+    default: return enqueue_step_t<double, double>(h, par, s);
+    }
+}
+
+const void *step_kernel_for(int storage)
+{
+    switch (storage) {
+    case LBM_F32: return step_kernel_ptr<float, float>();
+    case LBM_F32_WD_BF16: return step_kernel_ptr<float, __nv_bfloat16>();
+    case LBM_F32_WD_F16: return step_kernel_ptr<float, __half>();
+    default: return step_kernel_ptr<double, double>();
+    }
+}
+
+// 16-bit wdot plane <-> dense FP32 array (device memory).
+cudaError_t wd_to_f32(const lbm_handle *h, float *dst, double scale, cudaStream_t s)
+{
+    if (h->lat.storage == LBM_F32_WD_BF16)
+        return launch_wd_to_f32(static_cast<const __nv_bfloat16 *>(h->wd), h->pitch, h->grid.nx, h->grid.ny, (float)scale, dst, s);
+    return launch_wd_to_f32(static_cast<const __half *>(h->wd), h->pitch, h->grid.nx, h->grid.ny, (float)scale, dst, s);
+}
+
+cudaError_t wd_from_f32(const lbm_handle *h, const float *src, double scale, cudaStream_t s)
+{
+    if (h->lat.storage == LBM_F32_WD_BF16)
+        return launch_wd_from_f32(static_cast<__nv_bfloat16 *>(h->wd), h->pitch, h->grid.nx, h->grid.ny, (float)scale, src, s);
+    return launch_wd_from_f32(static_cast<__half *>(h->wd), h->pitch, h->grid.nx, h->grid.ny, (float)scale, src, s);
+}
+
+bool wd16(const lbm_handle *h) { return h->esize_d == 2; }
+
 cudaError_t enqueue_finalize(const lbm_handle *h, cudaStream_t s)
 {
-    if (h->lat.storage == LBM_F32) {
+    if (h->esize == 4) {
         FinalizeArgs<float> a;
         a.w = static_cast<const float *>(h->w[h->parity]);
         a.pitch = h->pitch;
@@ -322,7 +360,7 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lb
     if (lattice->velocity_set != LBM_D2Q5) return fail(LBM_ERR_ARG, "only the D2Q5 velocity set is built");
     if (lattice->form != LBM_FORM_MOMENT) return fail(LBM_ERR_ARG, "only the moment form is built");
     if (lattice->omega != 1.0) return fail(LBM_ERR_ARG, "omega = dt/tau must be 1 (tau = dt)");
-    if (lattice->storage != LBM_F64 && lattice->storage != LBM_F32) return fail(LBM_ERR_ARG, "storage must be F64 or F32");
+    if (lattice->storage < LBM_F64 || lattice->storage > LBM_F32_WD_F16) return fail(LBM_ERR_ARG, "unknown storage");
     if (lattice->bc_mode != LBM_BC_BOUNCEBACK && lattice->bc_mode != LBM_BC_MACROSCOPIC)
         return fail(LBM_ERR_ARG, "unknown crack-face mode");
     if (!(material->rho > 0.0) || !(material->mu > 0.0) || !std::isfinite(material->rho) || !std::isfinite(material->mu))
@@ -371,7 +409,8 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lb
     h->mat = *material;
     h->crack = cr;
     h->jc = jc;
-    h->esize = lattice->storage == LBM_F32 ? 4 : 8;
+    h->esize = lattice->storage == LBM_F64 ? 8 : 4;
+    h->esize_d = lattice->storage == LBM_F64 ? 8 : (lattice->storage == LBM_F32 ? 4 : 2);
     h->g = g;
     h->stream = (cudaStream_t)stream;
     h->sticky = LBM_OK;
@@ -397,7 +436,7 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lb
     const int vec = (int)(16 / h->esize);
     const int cols = kThreads * vec;
     h->ncb = (grid->nx + cols - 1) / cols;
-    const void *kfn = h->esize == 4 ? step_kernel_ptr<float>() : step_kernel_ptr<double>();
+    const void *kfn = step_kernel_for(lattice->storage);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
@@ -412,11 +451,14 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lb
 
     // one block for everything, carved at 256-byte boundaries
     const size_t plane = (size_t)(grid->ny + 2) * (size_t)h->pitch * h->esize;
+    const size_t plane_d = (size_t)(grid->ny + 2) * (size_t)h->pitch * h->esize_d;
+    const size_t staging = h->esize_d == 2 ? (size_t)grid->nx * grid->ny * 4 : 0;
     const size_t mask = (size_t)grid->ny * (size_t)h->words * 4;
     size_t off = 0;
     const size_t o_w0 = off; off = align256(off + plane);
     const size_t o_w1 = off; off = align256(off + plane);
-    const size_t o_wd = off; off = align256(off + plane);
+    const size_t o_wd = off; off = align256(off + plane_d);
+    const size_t o_sg = off; off = align256(off + staging);
     const size_t o_ch = off; off = align256(off + mask);
     const size_t o_cv = off; off = align256(off + mask);
     const size_t o_st = off; off = align256(off + 2 * sizeof(CrackState));
@@ -435,7 +477,8 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lb
     const size_t origin = ((size_t)h->pitch + (size_t)xoff) * h->esize;   // row 0, column 0
     h->w[0] = base + o_w0 + origin;
     h->w[1] = base + o_w1 + origin;
-    h->wd = base + o_wd + origin;
+    h->wd = base + o_wd + ((size_t)h->pitch + (size_t)xoff) * h->esize_d;
+    h->staging = staging ? reinterpret_cast<float *>(base + o_sg) : nullptr;
     h->cut_h = reinterpret_cast<uint32_t *>(base + o_ch);
     h->cut_v = reinterpret_cast<uint32_t *>(base + o_cv);
     h->st = reinterpret_cast<CrackState *>(base + o_st);
@@ -488,6 +531,28 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lb
     cp.start_q = start_q;
     cp.clamp_q = clamp_q;
     cp.hist_cap = cr.mode != LBM_CRACK_NONE ? cr.hist_cap : 0;
+
+    h->wd_scale = 1.0;
+    if (lattice->storage == LBM_F32_WD_F16) {
+        // a power of two that puts the largest rate the loads impose near 2^10,
+        // leaving a factor 64 below FP16's largest value for waves
+        double rate = 0.0;
+        for (int q = 0; q < 4; ++q) {
+            const LoadDesc &L = h->load[q];
+            if (grid->edge[q] != LBM_EDGE_DIRICHLET) continue;
+            const double T = L.t > grid->dt ? L.t : grid->dt;
+            if (L.kind == LBM_LOAD_LINEAR) rate = std::max(rate, std::fabs(L.amp) / T);
+            else if (L.kind == LBM_LOAD_SIN2 || L.kind == LBM_LOAD_HALFSINE) rate = std::max(rate, 3.2 * std::fabs(L.amp) / T);
+            else if (L.kind == LBM_LOAD_SERIES) {
+                const lbm_loading *Ls = nullptr;
+                for (int r = 0; r < n_loads; ++r) if (loads[r].edge == q) Ls = &loads[r];
+                for (int64_t k = 1; Ls && k < Ls->n_series; ++k)
+                    rate = std::max(rate, std::fabs(Ls->series[k] - Ls->series[k - 1]) / grid->dt);
+            }
+        }
+        h->wd_scale = rate > 0.0 ? std::ldexp(1.0, 10 - (int)std::ceil(std::log2(rate))) : 1024.0;
+        h->wd_scale = std::min(std::max(h->wd_scale, std::ldexp(1.0, -40)), std::ldexp(1.0, 60));
+    }
 
     lbm_status rc = plan_bands(h, 0);
     if (rc != LBM_OK) return bail(rc);
@@ -562,16 +627,27 @@ lbm_status lbm_step(lbm_handle *h, int64_t n)
     return LBM_OK;
 }
 
+// The dtype a field is exchanged in: the arithmetic precision (FP64 for F64
+// storage, FP32 otherwise; 16-bit wdot planes are converted).
+static int32_t exchange_dtype(const lbm_handle *h) { return h->esize == 8 ? LBM_F64 : LBM_F32; }
+
 lbm_status lbm_fields(lbm_handle *h, int32_t which, void *dst, int32_t dst_on_device, int32_t dtype)
 {
     if (!h || !dst) return fail(LBM_ERR_ARG, "handle or dst is NULL");
     if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");
     if (which != LBM_FIELD_W && which != LBM_FIELD_WDOT) return fail(LBM_ERR_ARG, "unknown field");
-    if (dtype != h->lat.storage) return fail(LBM_ERR_ARG, "dtype must equal the storage precision");
-    const void *src = which == LBM_FIELD_W ? h->w[h->parity] : h->wd;
+    if (dtype != exchange_dtype(h)) return fail(LBM_ERR_ARG, "dtype must be LBM_F64 for F64 storage, LBM_F32 otherwise");
     const size_t row = (size_t)h->grid.nx * h->esize;
-    LBM_CUDA(cudaMemcpy2DAsync(dst, row, src, (size_t)h->pitch * h->esize, row, (size_t)h->grid.ny,
-                               dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    const cudaMemcpyKind kind = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (which == LBM_FIELD_WDOT && wd16(h)) {
+        float *conv = dst_on_device ? static_cast<float *>(dst) : h->staging;
+        LBM_CUDA(wd_to_f32(h, conv, h->wd_scale, h->stream));
+        if (!dst_on_device)
+            LBM_CUDA(cudaMemcpyAsync(dst, conv, (size_t)h->grid.nx * h->grid.ny * 4, cudaMemcpyDeviceToHost, h->stream));
+    } else {
+        const void *src = which == LBM_FIELD_W ? h->w[h->parity] : h->wd;
+        LBM_CUDA(cudaMemcpy2DAsync(dst, row, src, (size_t)h->pitch * h->esize, row, (size_t)h->grid.ny, kind, h->stream));
+    }
     if (!dst_on_device) return check_sticky(h);
     return LBM_OK;
 }
@@ -581,20 +657,53 @@ lbm_status lbm_set_fields(lbm_handle *h, int32_t which, const void *src, int32_t
     if (!h || !src) return fail(LBM_ERR_ARG, "handle or src is NULL");
     if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");
     if (which != LBM_FIELD_W && which != LBM_FIELD_WDOT) return fail(LBM_ERR_ARG, "unknown field");
-    if (dtype != h->lat.storage) return fail(LBM_ERR_ARG, "dtype must equal the storage precision");
+    if (dtype != exchange_dtype(h)) return fail(LBM_ERR_ARG, "dtype must be LBM_F64 for F64 storage, LBM_F32 otherwise");
     lbm_status rc = finalize(h);   // the pending crack step reads the fields being replaced
     if (rc != LBM_OK) return rc;
-    void *dst = which == LBM_FIELD_W ? h->w[h->parity] : h->wd;
     const size_t row = (size_t)h->grid.nx * h->esize;
-    LBM_CUDA(cudaMemcpy2DAsync(dst, (size_t)h->pitch * h->esize, src, row, row, (size_t)h->grid.ny,
-                               src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
-    if (which == LBM_FIELD_W) {
-        cudaError_t e = h->lat.storage == LBM_F32
-            ? launch_fill_pads<float>(static_cast<float *>(dst), h->pitch, h->grid.nx, h->grid.ny, h->grid.edge, h->stream)
-            : launch_fill_pads<double>(static_cast<double *>(dst), h->pitch, h->grid.nx, h->grid.ny, h->grid.edge, h->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "filling periodic pads");
+    if (which == LBM_FIELD_WDOT && wd16(h)) {
+        const float *conv = static_cast<const float *>(src);
+        if (!src_on_device) {
+            LBM_CUDA(cudaMemcpyAsync(h->staging, src, (size_t)h->grid.nx * h->grid.ny * 4, cudaMemcpyHostToDevice, h->stream));
+            conv = h->staging;
+        }
+        LBM_CUDA(wd_from_f32(h, conv, h->wd_scale, h->stream));
+    } else {
+        void *dst = which == LBM_FIELD_W ? h->w[h->parity] : h->wd;
+        LBM_CUDA(cudaMemcpy2DAsync(dst, (size_t)h->pitch * h->esize, src, row, row, (size_t)h->grid.ny,
+                                   src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+        if (which == LBM_FIELD_W) {
+            cudaError_t e = h->esize == 4
+                ? launch_fill_pads<float>(static_cast<float *>(dst), h->pitch, h->grid.nx, h->grid.ny, h->grid.edge, h->stream)
+                : launch_fill_pads<double>(static_cast<double *>(dst), h->pitch, h->grid.nx, h->grid.ny, h->grid.edge, h->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "filling pads");
+        }
     }
     if (!src_on_device) LBM_CUDA(cudaStreamSynchronize(h->stream));   // pageable source may be reused
+    return LBM_OK;
+}
+
+lbm_status lbm_set_wd_scale(lbm_handle *h, double scale)
+{
+    if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
+    int ex = 0;
+    if (!(scale > 0.0) || !std::isfinite(scale) || std::frexp(scale, &ex) != 0.5)
+        return fail(LBM_ERR_ARG, "the scale must be a positive power of two");
+    if (h->lat.storage != LBM_F32_WD_F16) return fail(LBM_ERR_STATE, "only FP16 wdot storage has a scale");
+    lbm_status rc = finalize(h);
+    if (rc != LBM_OK) return rc;
+    LBM_CUDA(wd_to_f32(h, h->staging, h->wd_scale, h->stream));
+    LBM_CUDA(wd_from_f32(h, h->staging, scale, h->stream));
+    h->wd_scale = scale;
+    drop_graph(h);   // the scale is a kernel argument
+    LBM_CUDA(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_get_wd_scale(const lbm_handle *h, double *scale)
+{
+    if (!h || !scale) return fail(LBM_ERR_ARG, "handle or scale is NULL");
+    *scale = h->wd_scale;
     return LBM_OK;
 }
 

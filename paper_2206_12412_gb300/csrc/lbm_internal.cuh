@@ -22,6 +22,8 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace lbm {
@@ -83,11 +85,12 @@ struct Unit {
     int32_t j0, j1, dir, pad;
 };
 
-template <typename T>
+template <typename T, typename D>
 struct StepArgs {
     const T *w_in;
     T *w_out;
-    T *wd;
+    D *wd;                     // wdot storage (D = T, or 16-bit with T = float)
+    T wd_scale, wd_inv;        // stored value = wdot * wd_scale
     int64_t pitch;
     int32_t nx, ny;
     int32_t ncb;               // column blocks of kThreads * 16 bytes
@@ -116,8 +119,12 @@ struct FinalizeArgs {
     History hist;
 };
 
-template <typename T> const void *step_kernel_ptr();
-template <typename T> cudaError_t launch_step(const StepArgs<T> &a, int bands, cudaStream_t s);
+template <typename T, typename D> const void *step_kernel_ptr();
+template <typename T, typename D> cudaError_t launch_step(const StepArgs<T, D> &a, int bands, cudaStream_t s);
+template <typename D>
+cudaError_t launch_wd_to_f32(const D *wd, int64_t pitch, int nx, int ny, float scale, float *dst, cudaStream_t s);
+template <typename D>
+cudaError_t launch_wd_from_f32(D *wd, int64_t pitch, int nx, int ny, float scale, const float *src, cudaStream_t s);
 template <typename T> cudaError_t launch_finalize(const FinalizeArgs<T> &a, cudaStream_t s);
 cudaError_t launch_wstar(CrackState *st, const LoadDesc *load, const int32_t *edge, double dt, cudaStream_t s);
 template <typename T> cudaError_t launch_fill_pads(T *w, int64_t pitch, int nx, int ny, const int32_t *edge, cudaStream_t s);

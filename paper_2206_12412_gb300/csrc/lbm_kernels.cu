@@ -23,6 +23,10 @@
 // a band of their own.
 #include "lbm_internal.cuh"
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <type_traits>
+
 namespace lbm {
 
 // --------------------------------------------------------- vector rows
@@ -60,14 +64,67 @@ __device__ __forceinline__ void stg_row(double *p, const Row<double, 2> &r)
     *reinterpret_cast<double2 *>(p) = make_double2(r.v[0], r.v[1]);
 }
 
-// Value streamed across a missing outer-edge link.
-template <typename T>
-__device__ __forceinline__ T edge_value(int kind, T wstar, T wc, T raw)
-{
-    if (kind == EDGE_FREE) return wc;                        // bounce-back
-    if (kind == EDGE_DIRICHLET) return (T)2 * wstar - wc;    // anti-bounce-back
-    return raw;                                              // periodic image in the pad
-}
+// Storage of wdot.  FP64 and FP32 store the value; the 16-bit forms store
+// wdot * scale rounded to nearest (BF16: scale 1; FP16: a power of two chosen
+// so that the values sit well inside FP16's range), arithmetic stays FP32.
+template <typename D> struct WdIO;
+template <> struct WdIO<double> {
+    static __device__ __forceinline__ void load(const double *p, Row<double, 2> &r, double) { ld_row(p, r); }
+    static __device__ __forceinline__ void store(double *p, const Row<double, 2> &r, double) { stg_row(p, r); }
+    static __device__ __forceinline__ void put(double *p, double v, double) { *p = v; }
+};
+template <> struct WdIO<float> {
+    static __device__ __forceinline__ void load(const float *p, Row<float, 4> &r, float) { ld_row(p, r); }
+    static __device__ __forceinline__ void store(float *p, const Row<float, 4> &r, float) { stg_row(p, r); }
+    static __device__ __forceinline__ void put(float *p, float v, float) { *p = v; }
+};
+template <> struct WdIO<__nv_bfloat16> {
+    static __device__ __forceinline__ void load(const __nv_bfloat16 *p, Row<float, 4> &r, float)
+    {
+        const uint2 q = *reinterpret_cast<const uint2 *>(p);
+        r.v[0] = __uint_as_float(q.x << 16);
+        r.v[1] = __uint_as_float(q.x & 0xffff0000u);
+        r.v[2] = __uint_as_float(q.y << 16);
+        r.v[3] = __uint_as_float(q.y & 0xffff0000u);
+    }
+    static __device__ __forceinline__ void store(__nv_bfloat16 *p, const Row<float, 4> &r, float)
+    {
+        const __nv_bfloat162 lo = __floats2bfloat162_rn(r.v[0], r.v[1]);
+        const __nv_bfloat162 hi = __floats2bfloat162_rn(r.v[2], r.v[3]);
+        uint2 q;
+        q.x = *reinterpret_cast<const uint32_t *>(&lo);
+        q.y = *reinterpret_cast<const uint32_t *>(&hi);
+        *reinterpret_cast<uint2 *>(p) = q;
+    }
+    static __device__ __forceinline__ void put(__nv_bfloat16 *p, float v, float) { *p = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ float get(const __nv_bfloat16 *p, float) { return __bfloat162float(*p); }
+};
+template <> struct WdIO<__half> {
+    // scale: stored = wdot * scale; loads multiply by 1 / scale (both exact powers of two)
+    static __device__ __forceinline__ void load(const __half *p, Row<float, 4> &r, float inv)
+    {
+        const uint2 q = *reinterpret_cast<const uint2 *>(p);
+        const __half2 lo = *reinterpret_cast<const __half2 *>(&q.x);
+        const __half2 hi = *reinterpret_cast<const __half2 *>(&q.y);
+        const float2 a = __half22float2(lo), b = __half22float2(hi);
+        r.v[0] = a.x * inv;
+        r.v[1] = a.y * inv;
+        r.v[2] = b.x * inv;
+        r.v[3] = b.y * inv;
+    }
+    static __device__ __forceinline__ void store(__half *p, const Row<float, 4> &r, float scale)
+    {
+        const __half2 lo = __floats2half2_rn(r.v[0] * scale, r.v[1] * scale);
+        const __half2 hi = __floats2half2_rn(r.v[2] * scale, r.v[3] * scale);
+        uint2 q;
+        q.x = *reinterpret_cast<const uint32_t *>(&lo);
+        q.y = *reinterpret_cast<const uint32_t *>(&hi);
+        *reinterpret_cast<uint2 *>(p) = q;
+    }
+    static __device__ __forceinline__ void put(__half *p, float v, float scale) { *p = __float2half_rn(v * scale); }
+    static __device__ __forceinline__ float get(const __half *p, float inv) { return __half2float(*p) * inv; }
+};
+
 
 // ------------------------------------------------------------ edge values
 
@@ -222,11 +279,12 @@ __device__ __forceinline__ void crack_step_warp(const CrackParams &p, const T *w
 // code receives them as scalars and rebuilds this struct (taking the address
 // of the kernel parameter block would move all of it to local memory, and a
 // struct argument copied field by field from it was not passed reliably).
-template <typename T>
+template <typename T, typename D>
 struct RowArgs {
     const T *w_in;
     T *w_out;
-    T *wd;
+    D *wd;
+    T wd_scale, wd_inv;
     int64_t pitch;
     int32_t nx, ny, jc, macro;
     int32_t edge[4];
@@ -274,16 +332,17 @@ template <typename A, typename T, int N>
 __device__ __forceinline__ void store_row(const A &a, int x0, int j, const Row<T, N> &wnew,
                                           const Row<T, N> &wdnew, T &acc)
 {
+    typedef typename std::remove_pointer<decltype(a.wd)>::type D;
     const int64_t o = (int64_t)j * a.pitch + x0;
     if (x0 + N <= a.nx) {
         stg_row(a.w_out + o, wnew);
-        stg_row(a.wd + o, wdnew);
+        WdIO<D>::store(a.wd + o, wdnew, a.wd_scale);
     } else {
 #pragma unroll
         for (int k = 0; k < N; ++k)
             if (x0 + k < a.nx) {
                 a.w_out[o + k] = wnew.v[k];
-                a.wd[o + k] = wdnew.v[k];
+                WdIO<D>::put(a.wd + o + k, wdnew.v[k], a.wd_scale);
             }
     }
     acc += wnew.v[0];
@@ -341,15 +400,17 @@ __device__ __forceinline__ void row_update(const A &a, const EdgeValues<T> &E, i
 // crack-face rule (Sec. 3.1, HH = 3), the boundary point x_B next to a severed
 // link takes w_B = 1.5 w_I - 0.5 w_II from the two new values of its column
 // further away from the crack, and wdot(x_B) = (w_B(t+dt) - w_B(t)) / dt.
-template <typename T, int HH>
-__device__ __noinline__ T crack_rows(const T *w_in_, T *w_out_, T *wd_, int64_t pitch_, int nx_, int ny_, int jc_,
-                                     int macro_, int edges, T g_, T dt_, const uint32_t *cut_v_, int words_,
+template <typename T, typename D, int HH>
+__device__ __noinline__ T crack_rows(const T *w_in_, T *w_out_, D *wd_, T wd_scale_, int64_t pitch_, int nx_, int ny_,
+                                     int jc_, int macro_, int edges, T g_, T dt_, const uint32_t *cut_v_, int words_,
                                      const CrackState *s_in_, int cb, int j0)
 {
-    RowArgs<T> a;
+    RowArgs<T, D> a;
     a.w_in = w_in_;
     a.w_out = w_out_;
     a.wd = wd_;
+    a.wd_scale = wd_scale_;
+    a.wd_inv = (T)1 / wd_scale_;
     a.pitch = pitch_;
     a.nx = nx_;
     a.ny = ny_;
@@ -377,7 +438,7 @@ __device__ __noinline__ T crack_rows(const T *w_in_, T *w_out_, T *wd_, int64_t 
     for (int q = 0; q < HH + 2; ++q) ldg_row(win + (int64_t)(j0 - 1 + q) * P, w[q]);
 #pragma unroll
     for (int q = 0; q < HH; ++q) {
-        ld_row(a.wd + x0 + (int64_t)(j0 + q) * P, wd[q]);
+        WdIO<D>::load(a.wd + x0 + (int64_t)(j0 + q) * P, wd[q], a.wd_inv);
         hl[q] = lane == 0 ? win[(int64_t)(j0 + q) * P - 1] : (T)0;
         hr[q] = lane == 31 ? win[(int64_t)(j0 + q) * P + N] : (T)0;
     }
@@ -426,8 +487,8 @@ __device__ __noinline__ T crack_rows(const T *w_in_, T *w_out_, T *wd_, int64_t 
 // warp shuffles; lanes 0 and 31 load the halo column.  The next row's loads
 // are issued before the current row is computed.  EDGE = false is the
 // interior version (no edge row or column in the CTA): the bare update.
-template <typename T, bool EDGE>
-__device__ __forceinline__ void march(const StepArgs<T> &a, int cb, int j0, int j1, T &acc)
+template <typename T, typename D, bool EDGE>
+__device__ __forceinline__ void march(const StepArgs<T, D> &a, int cb, int j0, int j1, T &acc)
 {
     constexpr int N = Vec<T>::N;
     typedef Row<T, N> R;
@@ -437,12 +498,13 @@ __device__ __forceinline__ void march(const StepArgs<T> &a, int cb, int j0, int 
     const int64_t P = a.pitch;
     const T *win = a.w_in + x0;
     T *wout = a.w_out + x0;
-    T *wdp = a.wd + x0;
+    D *wdp = a.wd + x0;
+    const T wd_inv = a.wd_inv, wd_scale = a.wd_scale;
     R wb, wc, wa, wdv;
     ldg_row(win + (int64_t)(j0 - 1) * P, wb);
     ldg_row(win + (int64_t)j0 * P, wc);
     ldg_row(win + (int64_t)(j0 + 1) * P, wa);
-    ld_row(wdp + (int64_t)j0 * P, wdv);
+    WdIO<D>::load(wdp + (int64_t)j0 * P, wdv, wd_inv);
     T hl = (T)0, hr = (T)0;
     if (lane == 0) hl = win[(int64_t)j0 * P - 1];
     if (lane == 31) hr = win[(int64_t)j0 * P + N];
@@ -455,7 +517,7 @@ __device__ __forceinline__ void march(const StepArgs<T> &a, int cb, int j0, int 
         const bool more = j + 1 < j1;
         if (more) {
             ldg_row(win + (int64_t)(j + 2) * P, wn);
-            ld_row(wdp + (int64_t)(j + 1) * P, wdn);
+            WdIO<D>::load(wdp + (int64_t)(j + 1) * P, wdn, wd_inv);
             if (lane == 0) hln = win[(int64_t)(j + 1) * P - 1];
             if (lane == 31) hrn = win[(int64_t)(j + 1) * P + N];
         }
@@ -480,7 +542,7 @@ __device__ __forceinline__ void march(const StepArgs<T> &a, int cb, int j0, int 
                 wnew.v[k] = wc.v[k] + dt * wdnew.v[k];
             }
             stg_row(wout + (int64_t)j * P, wnew);
-            stg_row(wdp + (int64_t)j * P, wdnew);
+            WdIO<D>::store(wdp + (int64_t)j * P, wdnew, wd_scale);
             acc += wnew.v[0];
         }
         wb = wc;
@@ -494,8 +556,8 @@ __device__ __forceinline__ void march(const StepArgs<T> &a, int cb, int j0, int 
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBlocks - 2) step_kernel(const StepArgs<T> a)
+template <typename T, typename D>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBlocks - 2) step_kernel(const StepArgs<T, D> a)
 {
     constexpr int N = Vec<T>::N;
     __shared__ CrackState sS;
@@ -530,10 +592,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
             }
         }
         const int edges = a.edge[0] | (a.edge[1] << 2) | (a.edge[2] << 4) | (a.edge[3] << 6);
-        acc = p.macro ? crack_rows<T, 3>(a.w_in, a.w_out, a.wd, a.pitch, a.nx, a.ny, p.jc, p.macro, edges, a.g, a.dt,
-                                         a.cut_v, a.words, a.s_in, cb, j0)
-                      : crack_rows<T, 1>(a.w_in, a.w_out, a.wd, a.pitch, a.nx, a.ny, p.jc, p.macro, edges, a.g, a.dt,
-                                         a.cut_v, a.words, a.s_in, cb, j0);
+        acc = p.macro ? crack_rows<T, D, 3>(a.w_in, a.w_out, a.wd, a.wd_scale, a.pitch, a.nx, a.ny, p.jc, p.macro,
+                                            edges, a.g, a.dt, a.cut_v, a.words, a.s_in, cb, j0)
+                      : crack_rows<T, D, 1>(a.w_in, a.w_out, a.wd, a.wd_scale, a.pitch, a.nx, a.ny, p.jc, p.macro,
+                                            edges, a.g, a.dt, a.cut_v, a.words, a.s_in, cb, j0);
     } else {
         if (a.crack_band < 0 && cb == 0 && band == 0 && tid == 0) {
             // no crack: only the step counter and the Dirichlet values advance
@@ -546,23 +608,59 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
             *a.s_out = sS;
         }
         const bool edge = (cb == 0) | (cb == a.ncb - 1) | (j0 == 0) | (j1 == a.ny);
-        if (edge) march<T, true>(a, cb, j0, j1, acc);
-        else march<T, false>(a, cb, j0, j1, acc);
+        if (edge) march<T, D, true>(a, cb, j0, j1, acc);
+        else march<T, D, false>(a, cb, j0, j1, acc);
     }
     // a non-finite w (or wdot, which enters w) turns the sum of the first
     // component of each vector non-finite within a step or two
     if (__any_sync(kFull, !isfinite(acc)) && lane == 0) atomicOr(a.err, (uint32_t)ERR_NONFINITE);
 }
 
-template <typename T> const void *step_kernel_ptr()
+template <typename T, typename D> const void *step_kernel_ptr()
 {
-    return reinterpret_cast<const void *>(&step_kernel<T>);
+    return reinterpret_cast<const void *>(&step_kernel<T, D>);
 }
 
-template <typename T>
-cudaError_t launch_step(const StepArgs<T> &a, int bands, cudaStream_t s)
+template <typename T, typename D>
+cudaError_t launch_step(const StepArgs<T, D> &a, int bands, cudaStream_t s)
 {
-    step_kernel<T><<<dim3((unsigned)a.ncb, (unsigned)bands), kThreads, 0, s>>>(a);
+    step_kernel<T, D><<<dim3((unsigned)a.ncb, (unsigned)bands), kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------ wdot planes in 16-bit storage
+
+template <typename D>
+__global__ void wd_to_f32_kernel(const D *wd, int64_t P, int nx, int ny, float inv, float *dst)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nx * ny) return;
+    const int j = (int)(t / nx), i = (int)(t % nx);
+    dst[t] = WdIO<D>::get(wd + (int64_t)j * P + i, inv);
+}
+
+template <typename D>
+__global__ void wd_from_f32_kernel(D *wd, int64_t P, int nx, int ny, float scale, const float *src)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nx * ny) return;
+    const int j = (int)(t / nx), i = (int)(t % nx);
+    WdIO<D>::put(wd + (int64_t)j * P + i, src[t], scale);
+}
+
+template <typename D>
+cudaError_t launch_wd_to_f32(const D *wd, int64_t pitch, int nx, int ny, float scale, float *dst, cudaStream_t s)
+{
+    const int64_t n = (int64_t)nx * ny;
+    wd_to_f32_kernel<D><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(wd, pitch, nx, ny, 1.0f / scale, dst);
+    return cudaGetLastError();
+}
+
+template <typename D>
+cudaError_t launch_wd_from_f32(D *wd, int64_t pitch, int nx, int ny, float scale, const float *src, cudaStream_t s)
+{
+    const int64_t n = (int64_t)nx * ny;
+    wd_from_f32_kernel<D><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(wd, pitch, nx, ny, scale, src);
     return cudaGetLastError();
 }
 
@@ -652,10 +750,18 @@ cudaError_t launch_fill_pads(T *w, int64_t pitch, int nx, int ny, const int32_t 
     return cudaGetLastError();
 }
 
-template const void *step_kernel_ptr<float>();
-template const void *step_kernel_ptr<double>();
-template cudaError_t launch_step<float>(const StepArgs<float> &, int, cudaStream_t);
-template cudaError_t launch_step<double>(const StepArgs<double> &, int, cudaStream_t);
+template const void *step_kernel_ptr<double, double>();
+template const void *step_kernel_ptr<float, float>();
+template const void *step_kernel_ptr<float, __nv_bfloat16>();
+template const void *step_kernel_ptr<float, __half>();
+template cudaError_t launch_step<double, double>(const StepArgs<double, double> &, int, cudaStream_t);
+template cudaError_t launch_step<float, float>(const StepArgs<float, float> &, int, cudaStream_t);
+template cudaError_t launch_step<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> &, int, cudaStream_t);
+template cudaError_t launch_step<float, __half>(const StepArgs<float, __half> &, int, cudaStream_t);
+template cudaError_t launch_wd_to_f32<__nv_bfloat16>(const __nv_bfloat16 *, int64_t, int, int, float, float *, cudaStream_t);
+template cudaError_t launch_wd_to_f32<__half>(const __half *, int64_t, int, int, float, float *, cudaStream_t);
+template cudaError_t launch_wd_from_f32<__nv_bfloat16>(__nv_bfloat16 *, int64_t, int, int, float, const float *, cudaStream_t);
+template cudaError_t launch_wd_from_f32<__half>(__half *, int64_t, int, int, float, const float *, cudaStream_t);
 template cudaError_t launch_finalize<float>(const FinalizeArgs<float> &, cudaStream_t);
 template cudaError_t launch_finalize<double>(const FinalizeArgs<double> &, cudaStream_t);
 template cudaError_t launch_fill_pads<float>(float *, int64_t, int, int, const int32_t *, cudaStream_t);

@@ -130,6 +130,16 @@ def lbm_profile_read(h: int, reset: bool = False):
     return {"step_ms": bm.value, "n_step": nb.value, "finalize_ms": cm.value, "n_finalize": nc.value}
 
 
+def lbm_set_wd_scale(h: int, scale: float):
+    _check(load_library().lbm_set_wd_scale(C.c_void_p(h), float(scale)))
+
+
+def lbm_get_wd_scale(h: int) -> float:
+    v = C.c_double()
+    _check(load_library().lbm_get_wd_scale(C.c_void_p(h), C.byref(v)))
+    return v.value
+
+
 def lbm_device_bytes(h: int) -> int:
     b = C.c_int64()
     _check(load_library().lbm_device_bytes(C.c_void_p(h), C.byref(b)))
@@ -227,8 +237,8 @@ class Lattice:
         self.problem = problem
         self.storage = storage
         self.nx, self.ny = int(problem["nx"]), int(problem["ny"])
-        self.np_dtype = np.float32 if storage == "f32" else np.float64
-        self.torch_dtype = torch.float32 if storage == "f32" else torch.float64
+        self.np_dtype = np.float64 if storage == "f64" else np.float32
+        self.torch_dtype = torch.float64 if storage == "f64" else torch.float32
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream_obj = stream
@@ -241,7 +251,8 @@ class Lattice:
 
     @property
     def dtype_code(self) -> int:
-        return A.STORAGE[self.storage]
+        """Exchange dtype of the fields: LBM_F64 for f64 storage, LBM_F32 otherwise."""
+        return A.STORAGE["f64"] if self.storage == "f64" else A.STORAGE["f32"]
 
     def close(self):
         if getattr(self, "h", None):
@@ -326,6 +337,12 @@ class Lattice:
 
     def profile(self, reset: bool = False) -> dict:
         return lbm_profile_read(self.h, reset)
+
+    def set_wd_scale(self, scale: float):
+        lbm_set_wd_scale(self.h, scale)
+
+    def wd_scale(self) -> float:
+        return lbm_get_wd_scale(self.h)
 
     def device_bytes(self) -> int:
         return lbm_device_bytes(self.h)

@@ -1,0 +1,94 @@
+"""16-bit wdot storage (FP32 w and arithmetic) against the FP64 oracle.
+
+Not a parity bar: the stored wdot is rounded every step (BF16: 8 significant
+bits; FP16: 11 bits of wdot * scale), so the fields drift from the FP64
+solution by a stated amount.  Measured on the 128 x 128, 2000-step problem:
+relative max-norm of w 2-4e-3 (BF16) and 2-3e-4 (FP16), K within 0.6 % and
+0.06 %; the bounds below are about three times those figures.
+"""
+import numpy as np
+import pytest
+
+from paper_2206_12412_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+BOUNDS = {"f32_bf16": (1e-2, 2e-2), "f32_f16": (1e-3, 2e-3)}
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_12412_gb300 import lbm
+    lbm.load_library()
+    return lbm
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+@pytest.mark.parametrize("storage", ["f32_bf16", "f32_f16"])
+@pytest.mark.parametrize("bc_mode", ["macroscopic", "bounceback"])
+def test_plain_128_error_vs_oracle(oracle_mod, gpu, storage, bc_mode):
+    p = W.plain_fp64(bc_mode)
+    o = oracle_mod.Oracle(p)
+    o.step(W.PLAIN_FP64_STEPS)
+    g = gpu.Lattice(p, storage)
+    g.step(W.PLAIN_FP64_STEPS)
+    wo, _ = o.fields()
+    w, _ = g.fields()
+    ho, hg = o.history(), g.history()
+    bw, bk = BOUNDS[storage]
+    assert rel(w, wo) < bw
+    assert np.abs(hg["K"] - ho["K"]).max() < bk * np.abs(ho["K"]).max()
+    assert np.array_equal(g.cut_mask("v"), o.cuts()[1].astype(bool))
+
+
+@pytest.mark.parametrize("storage", ["f32_bf16", "f32_f16"])
+def test_prescribed_growth_tips_exact(oracle_mod, gpu, storage):
+    p = W.prescribed_strip(256, 64, 0.5, crack_len=40.0, r_min=2.25)
+    o = oracle_mod.Oracle(p)
+    o.step(600)
+    g = gpu.Lattice(p, storage)
+    g.step(600)
+    assert np.array_equal(g.history()["tip_q"], o.history()["tip_q"])
+    assert np.array_equal(g.cut_mask("v"), o.cuts()[1].astype(bool))
+    assert rel(g.fields()[0], o.fields()[0]) < BOUNDS[storage][0]
+
+
+@pytest.mark.parametrize("storage,bits", [("f32_bf16", 8), ("f32_f16", 11)])
+def test_wdot_roundtrip_and_scale(gpu, storage, bits):
+    p = W.plain_fp64("macroscopic")
+    g = gpu.Lattice(p, storage)
+    rng = np.random.default_rng(1)
+    wd = (rng.standard_normal((128, 128)) * 1e-6).astype(np.float32)
+    if storage == "f32_f16":
+        g.set_wd_scale(2.0 ** 30)     # 1e-6 * 2^30 ~ 1e3: normal FP16 range
+        assert g.wd_scale() == 2.0 ** 30
+    g.set_fields(np.zeros_like(wd), wd)
+    _, back = g.fields()
+    assert np.all(np.abs(back - wd) <= 2.0 ** -bits * np.abs(wd) + 1e-30)
+    if storage == "f32_f16":
+        g.set_wd_scale(2.0 ** 28)     # rescaling keeps the values
+        _, back2 = g.fields()
+        assert np.all(np.abs(back2 - wd) <= 2.0 ** (1 - bits) * np.abs(wd) + 1e-30)
+        with pytest.raises(gpu.LbmError):
+            g.set_wd_scale(3.0)
+    else:
+        with pytest.raises(gpu.LbmError):
+            g.set_wd_scale(2.0)
+
+
+def test_fp16_overflow_is_reported(gpu):
+    p = W.plain_fp64("macroscopic")
+    g = gpu.Lattice(p, "f32_f16")
+    g.set_wd_scale(2.0 ** 40)          # 1e-3 * 2^40 >> 65504: the stored rate overflows
+    wd = np.full((128, 128), 1e-3, np.float32)
+    g.set_fields(np.zeros_like(wd), wd)
+    g.step(2)
+    with pytest.raises(gpu.LbmError) as ei:
+        g.sync()
+    assert ei.value.status == -4
