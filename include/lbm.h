@@ -247,8 +247,35 @@ lbm_status lbm_get_wd_scale(const lbm_handle *h, double *scale);
 lbm_status lbm_device_bytes(const lbm_handle *h, int64_t *bytes);
 
 /* Release the handle and its device memory (NULL is ignored).  Synchronises
- * the stream first. */
+ * the stream first.  Destroy any batch that holds the handle first. */
 void lbm_destroy(lbm_handle *h);
+
+/* ---- Batches: many independent lattices advanced by one kernel launch per
+ * time step (each lattice's time step exactly as lbm_step computes it, so a
+ * batched lattice ends bit-identical to the same lattice stepped alone).
+ *
+ * lbm_batch_create groups n existing handles (not owned; they must outlive
+ * the batch) of the same storage, on the same stream, stepped equally often.
+ * It re-partitions every lattice into bands of band_rows rows (0: 16) and
+ * uploads a table of the step-kernel arguments of every lattice and a table
+ * of all their (lattice, column block, band) units; allocator as in
+ * lbm_create (NULL: cudaMalloc).  While the batch exists, step its lattices
+ * only through lbm_batch_step (stepping one alone makes lbm_batch_step return
+ * LBM_ERR_STATE) and do not call lbm_set_launch or lbm_set_wd_scale on them.
+ * Fields, masks and crack states are read through the member handles. */
+typedef struct lbm_batch lbm_batch;
+lbm_status lbm_batch_create(lbm_handle *const *handles, int32_t n, int32_t band_rows, const lbm_allocator *allocator,
+                            lbm_batch **out);
+
+/* Enqueue n >= 0 time steps of every lattice of the batch on the shared
+ * stream (CUDA-graph replay of 64-step chunks). */
+lbm_status lbm_batch_step(lbm_batch *b, int64_t n);
+
+/* Number of lattices and CTAs per step of the batch (pointers may be NULL). */
+lbm_status lbm_batch_info(const lbm_batch *b, int32_t *n_lattices, int32_t *ctas);
+
+/* Release the batch (NULL is ignored); the member handles stay valid. */
+void lbm_batch_destroy(lbm_batch *b);
 
 /* Message of the most recent failure on the calling thread ("" if none).
  * The pointer stays valid until the next call on this thread. */

@@ -84,5 +84,10 @@ PROTOTYPES = {
     "lbm_get_wd_scale": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "lbm_device_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "lbm_destroy": (None, [C.c_void_p]),
+    "lbm_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_int32, C.POINTER(Allocator),
+                                   C.POINTER(C.c_void_p)]),
+    "lbm_batch_step": (C.c_int, [C.c_void_p, C.c_int64]),
+    "lbm_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "lbm_batch_destroy": (None, [C.c_void_p]),
     "lbm_last_error": (C.c_char_p, []),
 }

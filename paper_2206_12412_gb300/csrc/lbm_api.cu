@@ -856,6 +856,208 @@ void lbm_destroy(lbm_handle *h)
     delete h;
 }
 
+// ---------------------------------------------------------------- batches
+
+}  // extern "C"
+
+struct lbm_batch {
+    std::vector<lbm_handle *> hs;
+    int storage;
+    void *block;         // descriptors (2 per lattice: parity 0, 1) then units
+    size_t block_bytes;
+    void *descs;
+    BatchUnit *units;
+    int n_units;
+    lbm_allocator alloc;
+    bool custom_alloc;
+    cudaStream_t stream;
+    cudaStream_t cap_stream;
+    cudaGraphExec_t gexec;
+    int gparity;
+};
+
+namespace {
+
+template <typename T, typename D>
+void fill_descs(const lbm_batch *b, std::vector<char> &buf)
+{
+    buf.resize(2 * b->hs.size() * sizeof(StepArgs<T, D>));
+    StepArgs<T, D> *d = reinterpret_cast<StepArgs<T, D> *>(buf.data());
+    for (size_t i = 0; i < b->hs.size(); ++i) {
+        make_step_args(b->hs[i], 0, d[2 * i]);
+        make_step_args(b->hs[i], 1, d[2 * i + 1]);
+    }
+}
+
+cudaError_t enqueue_batch_step(const lbm_batch *b, int par, cudaStream_t s)
+{
+    switch (b->storage) {
+    case LBM_F32:
+        return launch_batch_step(static_cast<const StepArgs<float, float> *>(b->descs), b->units, b->n_units, par, s);
+    case LBM_F32_WD_BF16:
+        return launch_batch_step(static_cast<const StepArgs<float, __nv_bfloat16> *>(b->descs), b->units, b->n_units, par, s);
+    case LBM_F32_WD_F16:
+        return launch_batch_step(static_cast<const StepArgs<float, __half> *>(b->descs), b->units, b->n_units, par, s);
+    default:
+        return launch_batch_step(static_cast<const StepArgs<double, double> *>(b->descs), b->units, b->n_units, par, s);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_batch_create(lbm_handle *const *handles, int32_t n, int32_t band_rows, const lbm_allocator *allocator,
+                            lbm_batch **out)
+{
+    if (!out) return fail(LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!handles || n < 1) return fail(LBM_ERR_ARG, "need at least one lattice");
+    if (band_rows < 0) return fail(LBM_ERR_ARG, "band_rows must be >= 0");
+    for (int i = 0; i < n; ++i) {
+        const lbm_handle *h = handles[i];
+        if (!h) return fail(LBM_ERR_ARG, "a lattice handle is NULL");
+        if (h->sticky != LBM_OK) return fail(h->sticky, "a lattice is in an error state");
+        if (h->lat.storage != handles[0]->lat.storage) return fail(LBM_ERR_ARG, "all lattices need the same storage");
+        if (h->stream != handles[0]->stream) return fail(LBM_ERR_ARG, "all lattices need the same stream");
+        if (h->parity != handles[0]->parity) return fail(LBM_ERR_STATE, "all lattices need the same number of steps");
+        for (int k = 0; k < i; ++k)
+            if (handles[k] == h) return fail(LBM_ERR_ARG, "a lattice appears twice");
+    }
+    lbm_batch *b = new (std::nothrow) lbm_batch;
+    if (!b) return fail(LBM_ERR_OOM, "host allocation failed");
+    b->hs.assign(handles, handles + n);
+    b->storage = handles[0]->lat.storage;
+    b->block = nullptr;
+    b->stream = handles[0]->stream;
+    b->cap_stream = nullptr;
+    b->gexec = nullptr;
+    b->gparity = -1;
+    b->custom_alloc = allocator && allocator->alloc && allocator->release;
+    if (b->custom_alloc) b->alloc = *allocator;
+    auto bail = [&](lbm_status rc) {
+        if (b->block) {
+            cudaStreamSynchronize(b->stream);
+            if (b->custom_alloc) b->alloc.release(b->block, b->alloc.ctx);
+            else cudaFree(b->block);
+        }
+        if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+        delete b;
+        return rc;
+    };
+    // bands of band_rows rows (default 16): a batch has many CTAs, no need to fit one wave
+    std::vector<BatchUnit> units;
+    for (int i = 0; i < n; ++i) {
+        lbm_handle *h = handles[i];
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "synchronising a lattice"));
+        drop_graph(h);
+        lbm_status rc = plan_bands(h, band_rows > 0 ? band_rows : 16);
+        if (rc != LBM_OK) return bail(rc);
+        for (int band = 0; band < h->n_bands; ++band)
+            for (int cb = 0; cb < h->ncb; ++cb) {
+                BatchUnit u;
+                u.inst = i;
+                u.cb = cb;
+                u.band = band;
+                u.pad = 0;
+                units.push_back(u);
+            }
+    }
+    std::vector<char> descs;
+    switch (b->storage) {
+    case LBM_F32: fill_descs<float, float>(b, descs); break;
+    case LBM_F32_WD_BF16: fill_descs<float, __nv_bfloat16>(b, descs); break;
+    case LBM_F32_WD_F16: fill_descs<float, __half>(b, descs); break;
+    default: fill_descs<double, double>(b, descs); break;
+    }
+    b->n_units = (int)units.size();
+    const size_t o_units = align256(descs.size());
+    b->block_bytes = o_units + units.size() * sizeof(BatchUnit);
+    if (b->custom_alloc) b->block = b->alloc.alloc(b->block_bytes, b->alloc.ctx);
+    else if (cudaMalloc(&b->block, b->block_bytes) != cudaSuccess) b->block = nullptr;
+    if (!b->block) return bail(fail(LBM_ERR_OOM, "device allocation failed"));
+    b->descs = b->block;
+    b->units = reinterpret_cast<BatchUnit *>(static_cast<char *>(b->block) + o_units);
+    cudaError_t e = cudaMemcpyAsync(b->descs, descs.data(), descs.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->units, units.data(), units.size() * sizeof(BatchUnit), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "uploading the batch tables"));
+    *out = b;
+    g_err.clear();
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch *b, int64_t n)
+{
+    if (!b) return fail(LBM_ERR_ARG, "batch is NULL");
+    if (n < 0) return fail(LBM_ERR_ARG, "n must be >= 0");
+    const int par0 = b->hs[0]->parity;
+    for (lbm_handle *h : b->hs) {
+        if (h->sticky != LBM_OK) return fail(h->sticky, "a lattice is in an error state");
+        if (h->parity != par0) return fail(LBM_ERR_STATE, "the lattices were stepped apart since the batch was made");
+    }
+    int par = par0;
+    int64_t left = n;
+    while (left > 0) {
+        if (left >= kGraphChunk) {
+            if (!b->gexec) {
+                cudaGraph_t graph;
+                LBM_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+                cudaError_t ce = cudaSuccess;
+                int p = par;
+                for (int64_t q = 0; q < kGraphChunk && ce == cudaSuccess; ++q) {
+                    ce = enqueue_batch_step(b, p, b->cap_stream);
+                    p ^= 1;
+                }
+                cudaError_t ee = cudaStreamEndCapture(b->cap_stream, &graph);
+                if (ce != cudaSuccess) return cuda_fail(ce, "capturing the batch graph");
+                if (ee != cudaSuccess) return cuda_fail(ee, "cudaStreamEndCapture");
+                ee = cudaGraphInstantiate(&b->gexec, graph, 0);
+                cudaGraphDestroy(graph);
+                if (ee != cudaSuccess) { b->gexec = nullptr; return cuda_fail(ee, "cudaGraphInstantiate"); }
+                b->gparity = par;
+            }
+            if (par == b->gparity) {
+                LBM_CUDA(cudaGraphLaunch(b->gexec, b->stream));
+                left -= kGraphChunk;
+                continue;
+            }
+        }
+        LBM_CUDA(enqueue_batch_step(b, par, b->stream));
+        par ^= 1;
+        left -= 1;
+    }
+    for (lbm_handle *h : b->hs) {
+        h->parity = par;
+        if (n > 0 && h->cp.mode != CRACK_NONE) h->pending = true;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_info(const lbm_batch *b, int32_t *n_lattices, int32_t *ctas)
+{
+    if (!b) return fail(LBM_ERR_ARG, "batch is NULL");
+    if (n_lattices) *n_lattices = (int32_t)b->hs.size();
+    if (ctas) *ctas = b->n_units;
+    return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch *b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->block) {
+        if (b->custom_alloc) b->alloc.release(b->block, b->alloc.ctx);
+        else cudaFree(b->block);
+    }
+    delete b;
+}
+
 const char *lbm_last_error(void) { return g_err.c_str(); }
 
 }  // extern "C"

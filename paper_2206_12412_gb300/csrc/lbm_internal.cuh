@@ -119,7 +119,14 @@ struct FinalizeArgs {
     History hist;
 };
 
+// One CTA of a batched step: column block cb of band `band` of lattice `inst`.
+struct BatchUnit {
+    int32_t inst, cb, band, pad;
+};
+
 template <typename T, typename D> const void *step_kernel_ptr();
+template <typename T, typename D>
+cudaError_t launch_batch_step(const StepArgs<T, D> *descs, const BatchUnit *units, int n_units, int par, cudaStream_t s);
 template <typename T, typename D> cudaError_t launch_step(const StepArgs<T, D> &a, int bands, cudaStream_t s);
 template <typename D>
 cudaError_t launch_wd_to_f32(const D *wd, int64_t pitch, int nx, int ny, float scale, float *dst, cudaStream_t s);

@@ -556,14 +556,14 @@ __device__ __forceinline__ void march(const StepArgs<T, D> &a, int cb, int j0, i
     }
 }
 
+// One CTA of a time step: column block cb of band `band` of the lattice that
+// `a` describes (the kernel parameter block, or a copy in shared memory).
 template <typename T, typename D>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBlocks - 2) step_kernel(const StepArgs<T, D> a)
+__device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int band, CrackState &sS)
 {
     constexpr int N = Vec<T>::N;
-    __shared__ CrackState sS;
     const unsigned kFull = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31;
-    const int cb = blockIdx.x, band = blockIdx.y;
     const Unit U = a.units[band];
     const int j0 = U.j0, j1 = U.j1;
     const int nx = a.nx;
@@ -616,6 +616,30 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
     if (__any_sync(kFull, !isfinite(acc)) && lane == 0) atomicOr(a.err, (uint32_t)ERR_NONFINITE);
 }
 
+template <typename T, typename D>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBlocks - 2) step_kernel(const StepArgs<T, D> a)
+{
+    __shared__ CrackState sS;
+    step_cta<T, D>(a, blockIdx.x, blockIdx.y, sS);
+}
+
+// Many independent lattices in one launch: CTA u runs unit u of the batch,
+// with its lattice's arguments (for the current parity) copied to shared
+// memory first.
+template <typename T, typename D>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBlocks - 2)
+    batch_step_kernel(const StepArgs<T, D> *descs, const BatchUnit *units, int par)
+{
+    __shared__ CrackState sS;
+    __shared__ __align__(16) StepArgs<T, D> sa;
+    const BatchUnit u = units[blockIdx.x];
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(descs + 2 * u.inst + par);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(&sa);
+    for (int q = threadIdx.x; q < (int)(sizeof(StepArgs<T, D>) / 4); q += blockDim.x) dst[q] = src[q];
+    __syncthreads();
+    step_cta<T, D>(sa, u.cb, u.band, sS);
+}
+
 template <typename T, typename D> const void *step_kernel_ptr()
 {
     return reinterpret_cast<const void *>(&step_kernel<T, D>);
@@ -625,6 +649,13 @@ template <typename T, typename D>
 cudaError_t launch_step(const StepArgs<T, D> &a, int bands, cudaStream_t s)
 {
     step_kernel<T, D><<<dim3((unsigned)a.ncb, (unsigned)bands), kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, typename D>
+cudaError_t launch_batch_step(const StepArgs<T, D> *descs, const BatchUnit *units, int n_units, int par, cudaStream_t s)
+{
+    batch_step_kernel<T, D><<<(unsigned)n_units, kThreads, 0, s>>>(descs, units, par);
     return cudaGetLastError();
 }
 
@@ -758,6 +789,10 @@ template cudaError_t launch_step<double, double>(const StepArgs<double, double> 
 template cudaError_t launch_step<float, float>(const StepArgs<float, float> &, int, cudaStream_t);
 template cudaError_t launch_step<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> &, int, cudaStream_t);
 template cudaError_t launch_step<float, __half>(const StepArgs<float, __half> &, int, cudaStream_t);
+template cudaError_t launch_batch_step<double, double>(const StepArgs<double, double> *, const BatchUnit *, int, int, cudaStream_t);
+template cudaError_t launch_batch_step<float, float>(const StepArgs<float, float> *, const BatchUnit *, int, int, cudaStream_t);
+template cudaError_t launch_batch_step<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> *, const BatchUnit *, int, int, cudaStream_t);
+template cudaError_t launch_batch_step<float, __half>(const StepArgs<float, __half> *, const BatchUnit *, int, int, cudaStream_t);
 template cudaError_t launch_wd_to_f32<__nv_bfloat16>(const __nv_bfloat16 *, int64_t, int, int, float, float *, cudaStream_t);
 template cudaError_t launch_wd_to_f32<__half>(const __half *, int64_t, int, int, float, float *, cudaStream_t);
 template cudaError_t launch_wd_from_f32<__nv_bfloat16>(__nv_bfloat16 *, int64_t, int, int, float, const float *, cudaStream_t);

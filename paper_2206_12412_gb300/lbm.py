@@ -346,3 +346,55 @@ class Lattice:
 
     def device_bytes(self) -> int:
         return lbm_device_bytes(self.h)
+
+
+# ----------------------------------------------------------------- batches
+
+def lbm_batch_create(handles, band_rows: int = 0, allocator: A.Allocator | None = None) -> int:
+    arr = (C.c_void_p * len(handles))(*handles)
+    out = C.c_void_p()
+    _check(load_library().lbm_batch_create(arr, len(handles), int(band_rows),
+                                           C.byref(allocator) if allocator is not None else None, C.byref(out)))
+    return out.value
+
+
+def lbm_batch_step(b: int, n: int):
+    _check(load_library().lbm_batch_step(C.c_void_p(b), int(n)))
+
+
+def lbm_batch_info(b: int):
+    nl, ct = C.c_int32(), C.c_int32()
+    _check(load_library().lbm_batch_info(C.c_void_p(b), C.byref(nl), C.byref(ct)))
+    return {"lattices": nl.value, "ctas": ct.value}
+
+
+def lbm_batch_destroy(b: int):
+    if b:
+        load_library().lbm_batch_destroy(C.c_void_p(b))
+
+
+class Batch:
+    """Several Lattice objects advanced together, one kernel launch per step."""
+
+    def __init__(self, lattices, band_rows: int = 0, torch_allocator: bool = True):
+        self.lattices = list(lattices)
+        self._alloc = TorchAllocator(self.lattices[0].stream) if torch_allocator else None
+        self.b = lbm_batch_create([l.h for l in self.lattices], band_rows,
+                                  self._alloc.struct if self._alloc else None)
+
+    def step(self, n: int = 1):
+        lbm_batch_step(self.b, n)
+
+    def info(self) -> dict:
+        return lbm_batch_info(self.b)
+
+    def close(self):
+        if getattr(self, "b", None):
+            lbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -113,3 +113,31 @@ def random_state(nx: int, ny: int, seed: int, amp: float = 1e-3, dtype=np.float6
     w = smooth_field(nx, ny, seed, amp)
     wd = smooth_field(nx, ny, seed + 7919, amp * 0.05)
     return w.astype(dtype).astype(np.float64), wd.astype(dtype).astype(np.float64)
+
+
+def batch_problems(n: int = 256, seed: int = 3, bc_mode: str = "macroscopic") -> list:
+    """Independent fracture runs of uneven sizes: nx in {256, 288, ..., 1024},
+    ny in {128, 160, ..., 512}, an edge crack of U(0.1, 0.4) nx on the
+    midline, top/bottom +-u0 with u0 log-uniform in [5e-4, 5e-3] ramped over
+    1000 steps; half of them grow by the K-criterion with K_C = K_ref
+    U(0.7, 1.3), half at a prescribed v / c_s ~ U(0.1, 0.7)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        nx = int(rng.integers(256 // 32, 1024 // 32 + 1)) * 32
+        ny = int(rng.integers(128 // 32, 512 // 32 + 1)) * 32
+        length = float(rng.uniform(0.1, 0.4)) * nx
+        u0 = float(np.exp(rng.uniform(np.log(5e-4), np.log(5e-3))))
+        p = base_problem(nx, ny, bc_mode=bc_mode)
+        if rng.uniform() < 0.5:
+            K_C = strip_reference_K(0.25, u0, float(ny)) * float(rng.uniform(0.7, 1.3))
+            p = with_crack(p, mode="kcrit", y=float(ny // 2), x_tip=length, K_C=K_C, v_max=0.85, r0=2.0)
+        else:
+            p = with_crack(p, mode="prescribed", y=float(ny // 2), x_tip=length, v_rel=float(rng.uniform(0.1, 0.7)))
+        p = with_antisymmetric_ramp(p, u0, 1000.0)
+        p["hist_cap"] = 4096
+        out.append(p)
+    return out
+
+
+BATCH_STEPS = 20000

@@ -1,0 +1,102 @@
+"""Batched lattices: one kernel launch per step advances every lattice, and
+each one ends bit-identical to the same lattice stepped alone (same kernel
+arithmetic), with uneven sizes, crack modes and crack-face modes."""
+import numpy as np
+import pytest
+
+from paper_2206_12412_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_12412_gb300 import lbm
+    lbm.load_library()
+    return lbm
+
+
+def mixed_problems():
+    ps = []
+    ps.append(W.plain_fp64("macroscopic"))
+    ps.append(W.plain_fp64("bounceback"))
+    ps.append(W.prescribed_strip(96, 48, 0.6, crack_len=20.0, r_min=2.25))
+    p = W.base_problem(96, 48, bc_mode="macroscopic")
+    p = W.with_antisymmetric_ramp(p, 2e-3, 100.0)
+    ps.append(W.with_crack(p, mode="kcrit", y=24.0, x_tip=20.0,
+                           K_C=0.5 * W.strip_reference_K(0.25, 2e-3, 48.0), v_max=0.85, r0=2.0))
+    q = W.base_problem(37, 29, bc_mode="bounceback", edges=("free", "dirichlet", "dirichlet", "free"))
+    q = W.with_crack(q, mode="stationary", y=14.0, x_start=4.3, x_tip=20.7)
+    q["loads"] = [{"edge": "right", "kind": "const", "amp": 3e-4, "t": 0.0},
+                  {"edge": "bottom", "kind": "sin2", "amp": -5e-4, "t": 40.0}]
+    ps.append(q)
+    ps.append(W.base_problem(50, 34, edges=("periodic",) * 4))
+    ps.extend(W.batch_problems(6, seed=11))
+    return ps
+
+
+def _same(a, b):
+    wa, wda = a.fields()
+    wb, wdb = b.fields()
+    assert np.array_equal(wa, wb) and np.array_equal(wda, wdb)
+    assert np.array_equal(a.cut_mask("v"), b.cut_mask("v"))
+    sa, sb = a.crack_state(), b.crack_state()
+    assert sa == sb
+    ha, hb = a.history(), b.history()
+    for k in ha:
+        assert np.array_equal(ha[k], hb[k])
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64", "f32_f16"])
+@pytest.mark.parametrize("band_rows", [0, 5])
+def test_batch_equals_solo_runs(gpu, storage, band_rows):
+    ps = mixed_problems()
+    solo = [gpu.Lattice(p, storage) for p in ps]
+    mem = [gpu.Lattice(p, storage) for p in ps]
+    for p, s, m in zip(ps, solo, mem):
+        if p["crack"]["mode"] == "none":
+            init = W.random_state(p["nx"], p["ny"], seed=7, dtype=np.float64 if storage == "f64" else np.float32)
+            s.set_fields(*init)
+            m.set_fields(*init)
+    b = gpu.Batch(mem, band_rows=band_rows)
+    assert b.info()["lattices"] == len(ps)
+    b.step(1)
+    b.step(150)
+    for s in solo:
+        s.step(151)
+    for s, m in zip(solo, mem):
+        _same(s, m)
+    b.close()
+
+
+def test_batch_then_solo_steps_continue(gpu):
+    ps = W.batch_problems(4, seed=5)
+    solo = [gpu.Lattice(p, "f32") for p in ps]
+    mem = [gpu.Lattice(p, "f32") for p in ps]
+    b = gpu.Batch(mem)
+    b.step(70)
+    b.close()
+    for m in mem:
+        m.step(30)
+    for s in solo:
+        s.step(100)
+    for s, m in zip(solo, mem):
+        _same(s, m)
+
+
+def test_batch_rejects_mixed_storage_and_diverged_steps(gpu):
+    ps = W.batch_problems(2, seed=6)
+    a = gpu.Lattice(ps[0], "f32")
+    c = gpu.Lattice(ps[1], "f64")
+    with pytest.raises(gpu.LbmError):
+        gpu.Batch([a, c])
+    d = gpu.Lattice(ps[1], "f32")
+    b = gpu.Batch([a, d])
+    a.step(1)
+    with pytest.raises(gpu.LbmError) as ei:
+        b.step(1)
+    assert ei.value.status == -6
+    b.close()
