@@ -110,6 +110,9 @@ def _load():
         lib.orc_load_value.restype = C.c_double
         lib.orc_g.argtypes = [P]
         lib.orc_g.restype = C.c_double
+        i32p = C.POINTER(C.c_int32)
+        lib.orc_adjoint.argtypes = [C.POINTER(_Config), d, d, C.c_int64, C.c_int32, i32p, i32p, d, d, d, d, d, d]
+        lib.orc_adjoint.restype = C.c_int
         _lib = lib
     return _lib
 
@@ -267,3 +270,47 @@ def checklinks(nx, ny, cut_h, cut_v, bprev, seg_a, seg_b, nmax=256):
         int(seg_a[0]), int(seg_a[1]), int(seg_b[0]), int(seg_b[1]),
         out.ctypes.data_as(C.POINTER(C.c_int32)), nmax)
     return np.sort(out[:n])
+
+
+def adjoint(problem: dict, n_steps: int, sensors, targets, w0=None, wd0=None, grad: bool = True) -> dict:
+    """Sensor misfit L = sum_{n=1..T} sum_s (w^n_s - target[n-1, s])^2 of a
+    T-step oracle run from (w0, wd0), and (if grad) its gradient by the
+    transposed steps under the run's own cut schedule.
+
+    sensors: (ns, 2) integer (i, j) sites; targets: (T, ns).  Returns a dict
+    with loss, trace (T, ns) of w at the sensors, and if grad: dload (4, T)
+    (dL/dw*_e(t_n), edges left/right/bottom/top), dw0 and dwd0 (ny, nx)."""
+    lib = _load()
+    cfg, keep = make_config(problem)
+    nx, ny = int(problem["nx"]), int(problem["ny"])
+    T = int(n_steps)
+    sens = np.ascontiguousarray(np.asarray(sensors, dtype=np.int32).reshape(-1, 2))
+    si = np.ascontiguousarray(sens[:, 0])
+    sj = np.ascontiguousarray(sens[:, 1])
+    ns = sens.shape[0]
+    tgt = np.ascontiguousarray(np.asarray(targets, dtype=np.float64).reshape(T, ns))
+    zero = np.zeros((ny, nx))
+    w0a = np.ascontiguousarray(zero if w0 is None else np.asarray(w0, np.float64).reshape(ny, nx))
+    wd0a = np.ascontiguousarray(zero if wd0 is None else np.asarray(wd0, np.float64).reshape(ny, nx))
+    loss = C.c_double(0.0)
+    trace = np.zeros((T, ns))
+    out = {}
+    null = C.POINTER(C.c_double)()
+    if grad:
+        dload = np.zeros((4, T))
+        dw0 = np.zeros((ny, nx))
+        dwd0 = np.zeros((ny, nx))
+        args = (_dptr(dload), _dptr(dw0), _dptr(dwd0))
+    else:
+        args = (null, null, null)
+    i32 = C.POINTER(C.c_int32)
+    rc = lib.orc_adjoint(C.byref(cfg), _dptr(w0a), _dptr(wd0a), T, ns, si.ctypes.data_as(i32),
+                         sj.ctypes.data_as(i32), _dptr(tgt), C.byref(loss), _dptr(trace), *args)
+    del keep
+    if rc != 0:
+        raise ValueError("oracle rejected the adjoint problem")
+    out["loss"] = loss.value
+    out["trace"] = trace
+    if grad:
+        out["dload"], out["dw0"], out["dwd0"] = dload, dw0, dwd0
+    return out

@@ -733,3 +733,220 @@ int32_t orc_checklinks_standalone(int32_t nx, int32_t ny, uint8_t *cut_h, uint8_
 double orc_load_value(const orc_state *s, int32_t edge, int64_t n) { return load_value(s, edge, n); }
 double orc_g(const orc_state *s) { return s->g; }
 int32_t orc_abi_version(void) { return 1; }
+
+/* ------------------------------------------------------------ adjoint
+ *
+ * Gradient of the sensor misfit
+ *     L = sum_{n=1..T} sum_s (w^n(x_s) - wbar^n_s)^2
+ * with respect to the Dirichlet edge values w*_e(t_n) (n = 0..T-1), the
+ * initial displacement w^0 and the initial rate wdot^0, with the crack's
+ * cut schedule of the forward run held fixed (the crack decisions of Alg. 1
+ * are discrete).  Under a fixed schedule one step of Sec. 3 is affine in the
+ * state, so the gradient is the transpose of each step applied in reverse
+ * order.  The transpose below is taken operation by operation from lbm_step
+ * above (collision, streaming with bounce-back / anti-bounce-back,
+ * eqs. distrib-macro and integration, and the macroscopic rule of Sec. 3.1),
+ * on the oracle's own state (w, f^0..f^4). */
+
+typedef struct {
+    int32_t *ch, *cv;      /* step from which each link is severed (INT32_MAX: never) */
+    int32_t *nbl;          /* boundary points in force during each step */
+} orc_schedule;
+
+/* Cut flags in force during step n. */
+static void schedule_cuts(const orc_schedule *sc, size_t n_sites, int64_t n, uint8_t *cut_h, uint8_t *cut_v)
+{
+    for (size_t k = 0; k < n_sites; ++k) {
+        cut_h[k] = sc->ch[k] <= n;
+        cut_v[k] = sc->cv[k] <= n;
+    }
+}
+
+/* Transpose of lbm_step for step n, given the adjoint (lw, lf) of the state
+ * after the step; overwrites them with the adjoint of the state before it and
+ * adds dL/dw*_e(t_n) to dload[e] (if dload is not NULL).  s->cut_h, s->cut_v
+ * and the first nbl boundary points must be those in force during step n. */
+static void lbm_step_transpose(orc_state *s, int nbl, double *lw, double *lf[5], double *dload4)
+{
+    int nx = s->c.nx, ny = s->c.ny;
+    size_t n = (size_t)nx * ny;
+    double g = s->g, om = s->c.omega, dt = s->c.dt;
+    double *lw5 = malloc(sizeof(double) * n), *lwold = calloc(n, sizeof(double));
+    double *lf4[5], *lfs[5];
+    for (int a = 0; a < 5; ++a) {
+        lf4[a] = malloc(sizeof(double) * n);
+        lfs[a] = calloc(n, sizeof(double));
+        memcpy(lf4[a], lf[a], sizeof(double) * n);
+    }
+    memcpy(lw5, lw, sizeof(double) * n);
+
+    /* macroscopic rule: w(x_B) = p(s_B) from w at the stencils of x_I, x_II;
+     * the missing f at x_B carry (target - known) / nmiss, target =
+     * (w_B - w_old(x_B)) / dt */
+    if (s->c.bc_mode == ORC_BC_MACROSCOPIC && nbl > 0) {
+        double *lwB = calloc((size_t)nbl, sizeof(double));
+        for (int b = 0; b < nbl; ++b) {
+            int32_t k = s->bl[b].site;
+            lwB[b] += lw[k];
+            lw5[k] = 0.0;
+            int miss[4], nmiss = 0;
+            for (int a = 1; a < 5; ++a) {
+                uint8_t *cut;
+                int32_t src = link_of(s, k, OPP[a], &cut);
+                if (src < 0 || *cut) miss[nmiss++] = a;
+            }
+            if (nmiss == 0) continue;
+            /* sm is dL/dwdot at x_B after the step; it vanishes whenever x_B is
+             * still a boundary point in the next step (wdot(x_B) is then
+             * recomputed from w alone), i.e. always while the crack only grows.
+             * The terms are kept as the literal transpose. */
+            double sm = 0.0;
+            for (int q = 0; q < nmiss; ++q) sm += lf[miss[q]][k];
+            sm /= (double)nmiss;
+            for (int a = 0; a < 5; ++a) {
+                int is_miss = 0;
+                for (int q = 0; q < nmiss; ++q) is_miss |= miss[q] == a;
+                if (is_miss) lf4[a][k] = 0.0;
+                else lf4[a][k] -= sm;
+            }
+            lwB[b] += sm / dt;
+            lwold[k] -= sm / dt;
+        }
+        for (int b = 0; b < nbl; ++b) {
+            const orc_bpoint *B = &s->bl[b];
+            /* p(s_B) = (1 - r) w_I + r w_II, r = (s_B^2 - s_I^2) / (s_II^2 - s_I^2) */
+            double r = (B->sB * B->sB - B->sI * B->sI) / (B->sII * B->sII - B->sI * B->sI);
+            for (int q = 0; q < B->nI; ++q) lw5[B->idxI[q]] += (1.0 - r) * B->wI[q] * lwB[b];
+            for (int q = 0; q < B->nII; ++q) lw5[B->idxII[q]] += r * B->wII[q] * lwB[b];
+        }
+        free(lwB);
+    }
+    /* w = w_old + dt sum_a f^a */
+    for (size_t k = 0; k < n; ++k) {
+        lwold[k] += lw5[k];
+        for (int a = 0; a < 5; ++a) lf4[a][k] += dt * lw5[k];
+    }
+    /* streaming with the boundary rules */
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            int32_t k = j * nx + i;
+            lfs[0][k] += lf4[0][k];
+            for (int a = 1; a < 5; ++a) {
+                int b = OPP[a];
+                uint8_t *cut;
+                int32_t src = link_of(s, k, b, &cut);
+                if (src >= 0 && !*cut) {
+                    lfs[a][src] += lf4[a][k];
+                } else if (src < 0) {
+                    int e = (b == 1) ? ORC_RIGHT : (b == 3) ? ORC_LEFT : (b == 2) ? ORC_TOP : ORC_BOTTOM;
+                    if (s->c.edge[e] == ORC_DIRICHLET) {
+                        lfs[b][k] -= lf4[a][k];
+                        if (dload4) dload4[e] += 2.0 * g * lf4[a][k];
+                    } else {
+                        lfs[b][k] += lf4[a][k];
+                    }
+                } else {
+                    lfs[b][k] += lf4[a][k];
+                }
+            }
+        }
+    /* collision f* = f - om (f - f_eq(w, wdot)), wdot = sum_a f^a */
+    for (size_t k = 0; k < n; ++k) {
+        double lfeq[5], lwdot;
+        for (int a = 0; a < 5; ++a) lfeq[a] = om * lfs[a][k];
+        lwdot = lfeq[0];
+        double lwk = lwold[k] - 4.0 * g * lfeq[0];
+        for (int a = 1; a < 5; ++a) lwk += g * lfeq[a];
+        lw[k] = lwk;
+        for (int a = 0; a < 5; ++a) lf[a][k] = (1.0 - om) * lfs[a][k] + lwdot;
+    }
+    for (int a = 0; a < 5; ++a) { free(lf4[a]); free(lfs[a]); }
+    free(lw5);
+    free(lwold);
+}
+
+/* Forward run of T steps from (w0, wdot0) with the sensor trace, the misfit L
+ * and, if any of dload / dw0 / dwd0 is not NULL, its gradient by the
+ * transposed steps.  Sensors are sites (si[k], sj[k]); target and trace are
+ * T x ns (row n-1 holds state n).  dload is 4 x T (row e: dL/dw*_e(t_n),
+ * zero for edges that are not Dirichlet).  Returns 0, or -1 for bad input. */
+int orc_adjoint(const orc_config *cfg, const double *w0, const double *wd0, int64_t T, int32_t ns,
+                const int32_t *si, const int32_t *sj, const double *target, double *loss, double *trace,
+                double *dload, double *dw0, double *dwd0)
+{
+    if (T < 1 || ns < 0) return -1;
+    orc_state *s = orc_create(cfg);
+    if (!s) return -1;
+    int nx = s->c.nx, ny = s->c.ny;
+    size_t n = (size_t)nx * ny;
+    for (int32_t k = 0; k < ns; ++k)
+        if (si[k] < 0 || si[k] >= nx || sj[k] < 0 || sj[k] >= ny) { orc_destroy(s); return -1; }
+    double *wz = calloc(n, sizeof(double));
+    orc_set_fields(s, w0 ? w0 : wz, wd0 ? wd0 : wz);
+    free(wz);
+
+    orc_schedule sc;
+    sc.ch = malloc(sizeof(int32_t) * n);
+    sc.cv = malloc(sizeof(int32_t) * n);
+    sc.nbl = malloc(sizeof(int32_t) * (size_t)T);
+    for (size_t k = 0; k < n; ++k) {
+        sc.ch[k] = s->cut_h[k] ? 0 : INT32_MAX;
+        sc.cv[k] = s->cut_v[k] ? 0 : INT32_MAX;
+    }
+    double *res = malloc(sizeof(double) * (size_t)T * (size_t)(ns > 0 ? ns : 1));
+    double L = 0.0;
+    for (int64_t q = 0; q < T; ++q) {
+        sc.nbl[q] = s->nbl;
+        orc_step(s, 1);   /* LBM step q, then the crack step that fixes the cuts of step q + 1 */
+        for (size_t k = 0; k < n; ++k) {
+            if (s->cut_h[k] && sc.ch[k] == INT32_MAX) sc.ch[k] = (int32_t)(q + 1);
+            if (s->cut_v[k] && sc.cv[k] == INT32_MAX) sc.cv[k] = (int32_t)(q + 1);
+        }
+        for (int32_t k = 0; k < ns; ++k) {
+            double wk = s->w[(size_t)sj[k] * nx + si[k]];
+            double r = wk - target[q * ns + k];
+            if (trace) trace[q * ns + k] = wk;
+            res[q * ns + k] = r;
+            L += r * r;
+        }
+    }
+    if (loss) *loss = L;
+
+    if (dload || dw0 || dwd0) {
+        double *lw = calloc(n, sizeof(double)), *lf[5];
+        for (int a = 0; a < 5; ++a) lf[a] = calloc(n, sizeof(double));
+        uint8_t *keep_h = s->cut_h, *keep_v = s->cut_v;
+        uint8_t *ch = malloc(n), *cv = malloc(n);
+        s->cut_h = ch;
+        s->cut_v = cv;
+        if (dload) memset(dload, 0, sizeof(double) * 4 * (size_t)T);
+        /* dL/dw^T from the last state's misfit */
+        for (int32_t k = 0; k < ns; ++k) lw[(size_t)sj[k] * nx + si[k]] += 2.0 * res[(T - 1) * ns + k];
+        for (int64_t q = T - 1; q >= 0; --q) {
+            double d4[4] = {0.0, 0.0, 0.0, 0.0};
+            schedule_cuts(&sc, n, q, ch, cv);
+            lbm_step_transpose(s, sc.nbl[q], lw, lf, d4);
+            if (dload)
+                for (int e = 0; e < 4; ++e) dload[(size_t)e * T + q] = d4[e];
+            if (q >= 1)   /* misfit of state q */
+                for (int32_t k = 0; k < ns; ++k) lw[(size_t)sj[k] * nx + si[k]] += 2.0 * res[(q - 1) * ns + k];
+        }
+        /* f = f_eq(w0, wdot0) at the start: f^0 = wdot0 - 4 g w0, f^k = g w0 */
+        for (size_t k = 0; k < n; ++k) {
+            if (dw0) dw0[k] = lw[k] - 4.0 * s->g * lf[0][k] + s->g * (lf[1][k] + lf[2][k] + lf[3][k] + lf[4][k]);
+            if (dwd0) dwd0[k] = lf[0][k];
+        }
+        s->cut_h = keep_h;
+        s->cut_v = keep_v;
+        free(ch);
+        free(cv);
+        free(lw);
+        for (int a = 0; a < 5; ++a) free(lf[a]);
+    }
+    free(res);
+    free(sc.ch);
+    free(sc.cv);
+    free(sc.nbl);
+    orc_destroy(s);
+    return 0;
+}

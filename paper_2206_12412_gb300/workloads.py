@@ -141,3 +141,68 @@ def batch_problems(n: int = 256, seed: int = 3, bc_mode: str = "macroscopic") ->
 
 
 BATCH_STEPS = 20000
+
+
+# ------------------------------------------------------------------ adjoint
+
+def gp_series(n: int, length: float, sigma: float, seed: int) -> np.ndarray:
+    """Smooth random series of n samples: white noise filtered in the
+    frequency domain by the square root of a squared-exponential spectrum of
+    correlation length `length` (samples), scaled to standard deviation
+    sigma.  FP64."""
+    rng = np.random.default_rng(seed)
+    z = rng.standard_normal(n)
+    f = np.fft.rfftfreq(n)
+    filt = np.exp(-(np.pi * length * f) ** 2)   # sqrt of exp(-2 pi^2 l^2 f^2)
+    x = np.fft.irfft(np.fft.rfft(z) * filt, n)
+    return sigma * x / max(float(np.std(x)), 1e-300)
+
+
+def sensor_sites(nx: int, ny: int, ns: int, seed: int, jc: int | None = None, margin: int = 2) -> np.ndarray:
+    """ns distinct sites (i, j) drawn uniformly, keeping `margin` rows and
+    columns away from the edges and `margin` rows away from the crack rows
+    jc-1 and jc.  (ns, 2) int32."""
+    rng = np.random.default_rng(seed)
+    out, seen = [], set()
+    while len(out) < ns:
+        i = int(rng.integers(margin, nx - margin))
+        j = int(rng.integers(margin, ny - margin))
+        if jc is not None and jc - 1 - margin <= j <= jc + margin:
+            continue
+        if (i, j) in seen:
+            continue
+        seen.add((i, j))
+        out.append((i, j))
+    return np.asarray(out, dtype=np.int32)
+
+
+def with_series_load(p: dict, edge: str, series) -> dict:
+    """Replace (or add) the load of one Dirichlet edge by a tabulated series
+    (value series[n] in step n)."""
+    q = dict(p)
+    q["loads"] = [ld for ld in p.get("loads", []) if ld["edge"] != edge]
+    q["loads"].append({"edge": edge, "kind": "series", "series": np.asarray(series, dtype=np.float64)})
+    return q
+
+
+def adjoint_problem(nx: int = 1024, ny: int = 1024, n_steps: int = 8000, ns: int = 64, *, crack_len: float | None = None,
+                    v_rel: float = 0.4, length: float = 500.0, sigma: float = 1e-3, bc_mode: str = "macroscopic",
+                    seeds=(4, 5, 6)) -> dict:
+    """Sensor-misfit problem on an nx x ny strip (1024 x 1024, 8000 steps,
+    64 sensors at full size): crack on the midline from x = 0 to nx / 8
+    growing at the prescribed v / c_s = v_rel; top edge held at a series u[n],
+    bottom edge at 0, sides free.  Returns the problem for the control series
+    (seed seeds[2]), the reference series whose sensor trace gives the
+    targets (seed seeds[0]), and the sensor sites (seed seeds[1])."""
+    jc = ny // 2
+    p = base_problem(nx, ny, bc_mode=bc_mode)
+    p = with_crack(p, mode="prescribed", y=float(jc), x_tip=crack_len if crack_len is not None else nx / 8.0, v_rel=v_rel)
+    u_ref = gp_series(n_steps, length, sigma, seeds[0])
+    u_ctl = gp_series(n_steps, length, sigma, seeds[2])
+    p = with_series_load(p, "top", u_ctl)
+    p["hist_cap"] = 4096
+    sens = sensor_sites(nx, ny, ns, seeds[1], jc=jc)
+    return {"problem": p, "u_ref": u_ref, "u_ctl": u_ctl, "sensors": sens, "n_steps": int(n_steps)}
+
+
+ADJOINT_STEPS = 8000
