@@ -216,6 +216,63 @@ def measure_batched(lbm, W, torch, stream, steps, peak):
             "timing": "CUDA events around the whole run, no flush (state larger than L2)"}
 
 
+def measure_adjoint(lbm, W, torch, stream):
+    """Sensor-misfit gradient on the 1024 x 1024, 8000-step problem (FP32,
+    64 sensors): the plain forward run, the recording forward run and the
+    transposed sweep, with stored misfits and with sqrt(T) checkpoints.  The
+    16 MB state stays in L2 (the steps are timed back to back)."""
+    import numpy as np
+    a = W.adjoint_problem()
+    p, T, sens = a["problem"], a["n_steps"], a["sensors"]
+    ref = lbm.Lattice(W.with_series_load(p, "top", a["u_ref"]), "f32", stream=stream)
+    tref = lbm.Tape(ref, sens, T)
+    tref.forward(np.zeros((T, len(sens))))
+    targets = torch.tensor(tref.misfits(), device="cuda")
+    tref.close()
+    ref.close()
+    lat = lbm.Lattice(p, "f32", stream=stream)
+
+    def timed(fn, reps=2):
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
+    def plain():
+        lat.reset()
+        lat.step(T)
+
+    out = {"workload": f"sensor misfit {p['nx']}x{p['ny']} f32, {T} steps, {len(sens)} sensors, prescribed v=0.4",
+           "forward_ms": timed(plain)}
+    every_sqrt = int(round(np.sqrt(T)))
+    for every, key in ((0, "stored"), (every_sqrt, "checkpointed")):
+        tape = lbm.Tape(lat, sens, T, checkpoint_every=every)
+
+        def rec():
+            lat.reset()
+            tape.forward(targets, loss_to_host=False)
+
+        t_rec = timed(rec)
+        rec()
+        t_bwd = timed(lambda: tape.backward(device=True))
+        out[key] = {"checkpoint_every": every, "recording_forward_ms": t_rec, "adjoint_ms": t_bwd,
+                    "ratio_forward_plus_adjoint_over_forward": (t_rec + t_bwd) / out["forward_ms"]}
+        tape.close()
+    sites = p["nx"] * p["ny"]
+    out["adjoint_us_per_step"] = out["stored"]["adjoint_ms"] * 1e3 / (T + 1)
+    out["forward_us_per_step"] = out["forward_ms"] * 1e3 / T
+    out["adjoint_l2_gbs"] = 16 * sites / (out["adjoint_us_per_step"] * 1e-6) / 1e9
+    out["timing"] = "CUDA events around whole runs (graph replay), best of 2, no flush (L2-resident state)"
+    lat.close()
+    return out
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
@@ -322,6 +379,7 @@ def run_ours(args, rank, world, local):
         lm.close()
 
     batched = measure_batched(lbm, W, torch, stream, 128, peak) if not args.no_batched else None
+    adjoint = measure_adjoint(lbm, W, torch, stream) if not args.no_adjoint else None
 
     # steady back-to-back replay (CUDA graph, no flush): context only
     lat.sync()
@@ -375,6 +433,7 @@ def run_ours(args, rank, world, local):
         "steady_graph_glups": steady,
         "mixed_precision": mixed,
         "batched": batched,
+        "adjoint": adjoint,
         "wall_s": wall,
         "clocks": clk,
     }
@@ -397,6 +456,7 @@ def main():
     ap.add_argument("--prelude", type=int, default=2500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-lattice batched measurement")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the sensor-misfit gradient measurement")
     ap.add_argument("--profile-only", action="store_true",
                     help="only prelude, warm-up and timed steps (for ncu); prints kernel times")
     args = ap.parse_args()

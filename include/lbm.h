@@ -142,7 +142,8 @@ typedef struct lbm_loading {
 /* Optional device allocator (for example a framework's caching allocator).
  * alloc returns device memory of at least `bytes` bytes aligned to 256 bytes,
  * or NULL; release frees it.  When NULL is passed, cudaMalloc / cudaFree are
- * used.  The library allocates only inside lbm_create. */
+ * used.  The library allocates device memory only inside lbm_create,
+ * lbm_batch_create and lbm_tape_create (lbm_adjoint.h). */
 typedef struct lbm_allocator {
     void *(*alloc)(size_t bytes, void *ctx);
     void (*release)(void *ptr, void *ctx);
@@ -233,6 +234,20 @@ lbm_status lbm_set_profiling(lbm_handle *h, int32_t enable);
  * clears them.  Synchronises the stream. */
 lbm_status lbm_profile_read(lbm_handle *h, double *step_ms, int64_t *n_step, double *finalize_ms, int64_t *n_finalize,
                             int32_t reset);
+
+/* Return to the state lbm_create left: w = wdot = 0, step 0, the initial
+ * crack (mask, tip and crack state), an empty history.  The current loads,
+ * launch shape and FP16 scale are kept; a sticky error is not cleared.
+ * Synchronises the stream. */
+lbm_status lbm_reset(lbm_handle *h);
+
+/* Replace the loading of one edge (load->edge) from the next step on; the
+ * value w*(t_n) of the current step n is recomputed.  A SERIES load may be at
+ * most as long as the series that edge was created with (its device buffer is
+ * reused; an edge created without a series cannot take one).  The FP16
+ * scale is not re-derived.  Not for a lattice held by a batch.  Synchronises
+ * the stream and drops the cached step graph. */
+lbm_status lbm_set_loading(lbm_handle *h, const lbm_loading *load);
 
 /* Scale of FP16 wdot storage (LBM_F32_WD_F16): the plane holds wdot * scale.
  * scale must be a power of two; the stored plane is rescaled.  lbm_create

@@ -47,7 +47,8 @@
  *   - r is measured along the crack from the tip, phi = +-pi, the window is
  *     half open; delta = w(above) - w(below), the criterion uses |K|;
  *   - r_min uses the v of the previous step (0 while arrested);
- *   - the tip stops (and stays) at x = (nx - 1) dh.
+ *   - the tip stops (and stays) at the far edge x = nx dh, where the crack
+ *     has severed every link of its row and split the body.
  */
 #include <math.h>
 #include <stdint.h>
@@ -316,7 +317,7 @@ orc_state *orc_create(const orc_config *cfg)
     }
     /* the initial state: w = wdot = 0, f = f_eq(0, 0) = 0 */
     s->v_prev = cfg->crack_mode == ORC_CRACK_PRESCRIBED ? cfg->v_rel : 0.0;
-    s->clamp_q = (int64_t)(cfg->nx - 1) << ORC_Q;
+    s->clamp_q = (int64_t)cfg->nx << ORC_Q;
     if (cfg->crack_mode != ORC_CRACK_NONE) {
         s->start_q = llrint(cfg->x_start / cfg->dh * (double)qone());
         s->tip_q = llrint(cfg->x_tip / cfg->dh * (double)qone());

@@ -1,4 +1,5 @@
-"""ctypes mirror of include/lbm.h (structs, constants, prototypes)."""
+"""ctypes mirror of include/lbm.h and include/lbm_adjoint.h (structs,
+constants, prototypes)."""
 from __future__ import annotations
 
 import ctypes as C
@@ -89,5 +90,16 @@ PROTOTYPES = {
     "lbm_batch_step": (C.c_int, [C.c_void_p, C.c_int64]),
     "lbm_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "lbm_batch_destroy": (None, [C.c_void_p]),
+    "lbm_reset": (C.c_int, [C.c_void_p]),
+    "lbm_set_loading": (C.c_int, [C.c_void_p, C.POINTER(Loading)]),
     "lbm_last_error": (C.c_char_p, []),
+    # include/lbm_adjoint.h
+    "lbm_tape_create": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32, C.c_int64, C.c_int32,
+                                  C.POINTER(Allocator), C.POINTER(C.c_void_p)]),
+    "lbm_tape_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_double)]),
+    "lbm_tape_loss_device": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
+    "lbm_tape_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
+                                    C.c_int32]),
+    "lbm_tape_misfits": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "lbm_tape_destroy": (None, [C.c_void_p]),
 }

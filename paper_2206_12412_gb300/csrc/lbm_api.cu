@@ -2,8 +2,7 @@
 // validation, device memory layout, initial crack, the static band partition
 // of the step kernel, CUDA-graph replay of step sequences, the deferred crack
 // step before host reads, and the copy-out calls.
-#include "lbm.h"
-#include "lbm_internal.cuh"
+#include "lbm_host.h"
 
 #include <algorithm>
 #include <cmath>
@@ -15,10 +14,14 @@
 #include <vector>
 
 using namespace lbm;
+using namespace lbm::host;
+
+namespace lbm {
+namespace host {
 
 namespace {
-
 thread_local std::string g_err;
+}
 
 lbm_status fail(lbm_status s, const std::string &msg)
 {
@@ -32,11 +35,22 @@ lbm_status cuda_fail(cudaError_t e, const char *what)
     return LBM_ERR_CUDA;
 }
 
-#define LBM_CUDA(call)                                      \
-    do {                                                    \
-        cudaError_t e_ = (call);                            \
-        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
-    } while (0)
+void clear_error() { g_err.clear(); }
+
+const char *last_error() { return g_err.c_str(); }
+
+void ChunkGraph::reset()
+{
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    parity = -1;
+    gen = -1;
+}
+
+}  // namespace host
+}  // namespace lbm
+
+namespace {
 
 constexpr int64_t kGraphChunk = 64;   // time steps per captured graph (even)
 constexpr int64_t kDefaultHistCap = 65536;
@@ -46,81 +60,9 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 
-struct lbm_handle {
-    lbm_grid grid;
-    lbm_lattice lat;
-    lbm_material mat;
-    lbm_crack crack;
-    size_t esize;        // bytes per w element (and per arithmetic value)
-    size_t esize_d;      // bytes per stored wdot element
-    double wd_scale;     // stored wdot = wdot * wd_scale (16-bit storage)
-    float *staging;      // nx * ny floats for 16-bit wdot conversions
-    int64_t pitch;       // elements per padded row
-    int32_t words;       // 32-bit mask words per row
-    int32_t jc;          // crack line y = jc dh
-    // step kernel shape
-    int32_t ncb;         // column blocks of kThreads vectors
-    int32_t n_bands, band_rows, crack_band, sms, bps;
-    Unit *units;         // device table, capacity ny
-    // memory
-    lbm_allocator alloc;
-    bool custom_alloc;
-    void *block;
-    size_t block_bytes;
-    void *w[2];          // element (0, 0) of each W buffer
-    void *wd;
-    uint32_t *cut_h, *cut_v;
-    CrackState *st;      // two buffers
-    uint32_t *err;
-    History hist;
-    LoadDesc load[4];
-    CrackParams cp;
-    double g;
-    // stepping
-    int parity;          // W buffer and state buffer holding the current step
-    bool pending;        // the crack step after the last enqueued LBM step is not applied yet
-    cudaStream_t stream;
-    cudaStream_t cap_stream;
-    cudaGraphExec_t gexec;
-    int gparity;
-    lbm_status sticky;
-    // CUDA-event timing (lbm_set_profiling)
-    int profiling;
-    std::vector<cudaEvent_t> *ev;   // pairs: start, end
-    std::vector<int> *ev_kind;      // 0 step kernel, 1 finalize kernel
-    size_t ev_used;
-    double step_ms, fin_ms;
-    int64_t n_step, n_fin;
-};
 
 namespace {
 
-template <typename T, typename D>
-void make_step_args(const lbm_handle *h, int par, StepArgs<T, D> &a)
-{
-    a.w_in = static_cast<const T *>(h->w[par]);
-    a.w_out = static_cast<T *>(h->w[par ^ 1]);
-    a.wd = static_cast<D *>(h->wd);
-    a.wd_scale = (T)h->wd_scale;
-    a.wd_inv = (T)(1.0 / h->wd_scale);
-    a.pitch = h->pitch;
-    a.nx = h->grid.nx;
-    a.ny = h->grid.ny;
-    a.ncb = h->ncb;
-    a.crack_band = h->crack_band;
-    for (int e = 0; e < 4; ++e) { a.edge[e] = h->grid.edge[e]; a.load[e] = h->load[e]; }
-    a.g = (T)h->g;
-    a.dt = (T)h->grid.dt;
-    a.cut_h = h->cut_h;
-    a.cut_v = h->cut_v;
-    a.words = h->words;
-    a.units = h->units;
-    a.s_in = h->st + par;
-    a.s_out = h->st + (par ^ 1);
-    a.err = h->err;
-    a.p = h->cp;
-    a.hist = h->hist;
-}
 
 template <typename T, typename D>
 cudaError_t enqueue_step_t(const lbm_handle *h, int par, cudaStream_t s)
@@ -219,6 +161,11 @@ cudaError_t timed(lbm_handle *h, int kind, F &&launch)
     return cudaEventRecord(E[1], h->stream);
 }
 
+}  // namespace
+
+namespace lbm {
+namespace host {
+
 // Apply the crack step that follows the last enqueued LBM step.
 lbm_status finalize(lbm_handle *h)
 {
@@ -248,6 +195,11 @@ lbm_status check_sticky(lbm_handle *h)
     }
     return LBM_OK;
 }
+
+}  // namespace host
+}  // namespace lbm
+
+namespace {
 
 // Static partition of the rows into bands of at most `rows` rows.  The rows
 // that the crack-face rule and the crack links touch form two bands of their
@@ -309,6 +261,8 @@ lbm_status plan_bands(lbm_handle *h, int rows)
     if (crack && h->crack_band < 0) return fail(LBM_ERR_ARG, "the crack rows form no band of their own");
     LBM_CUDA(cudaMemcpyAsync(h->units, best.data(), best.size() * sizeof(Unit), cudaMemcpyHostToDevice, h->stream));
     LBM_CUDA(cudaStreamSynchronize(h->stream));
+    *h->units_h = best;
+    h->gen += 1;
     return LBM_OK;
 }
 
@@ -325,6 +279,13 @@ void dev_free(lbm_handle *h, void *p)
     if (!p) return;
     if (h->custom_alloc) h->alloc.release(p, h->alloc.ctx);
     else cudaFree(p);
+}
+
+void free_host(lbm_handle *h)
+{
+    delete h->units_h;
+    delete h->init_cut;
+    delete h;
 }
 
 void drop_graph(lbm_handle *h)
@@ -376,7 +337,7 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lb
     int32_t jc = 0;
     int64_t start_q = 0, tip_q = 0;
     const int64_t qone = (int64_t)1 << kQBits;
-    const int64_t clamp_q = (int64_t)(grid->nx - 1) * qone;
+    const int64_t clamp_q = (int64_t)grid->nx * qone;   // the far edge: the crack splits the body
     if (cr.mode != LBM_CRACK_NONE) {
         const double yj = cr.y / grid->dh;
         if (!std::isfinite(yj) || std::fabs(yj - std::nearbyint(yj)) > 1e-9)
@@ -388,7 +349,7 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lb
         if (!(cr.x_start >= 0.0) || !(cr.x_tip >= cr.x_start)) return fail(LBM_ERR_ARG, "need 0 <= x_start <= x_tip");
         start_q = llrint(cr.x_start / grid->dh * 4294967296.0);
         tip_q = llrint(cr.x_tip / grid->dh * 4294967296.0);
-        if (tip_q >= clamp_q) return fail(LBM_ERR_ARG, "the initial tip must lie left of x = (nx - 1) dh");
+        if (tip_q >= clamp_q) return fail(LBM_ERR_ARG, "the initial tip must lie left of x = nx dh");
         if (lattice->bc_mode == LBM_BC_MACROSCOPIC && grid->edge[LBM_LEFT] == LBM_EDGE_PERIODIC)
             return fail(LBM_ERR_ARG, "macroscopic crack faces need non-periodic left/right edges");
         if (cr.mode == LBM_CRACK_PRESCRIBED && !(cr.v_rel >= 0.0 && cr.v_rel < 1.0))
@@ -396,6 +357,16 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lb
         if (cr.mode == LBM_CRACK_KCRIT && !(cr.K_C > 0.0 && cr.v_max >= 0.0 && cr.v_max < 1.0))
             return fail(LBM_ERR_ARG, "K-criterion needs K_C > 0 and 0 <= v_max < 1");
         if (!(cr.r_min > 0.0) && !(cr.r0 >= 0.0)) return fail(LBM_ERR_ARG, "r0 must be >= 0");
+        if (lattice->bc_mode == LBM_BC_MACROSCOPIC) {
+            // with the macroscopic crack-face rule a single intact column between
+            // the crack and a free edge is an unstable ligament (a mode localised
+            // there grows without bound); two or more columns, or none, are fine
+            const int64_t half = qone / 2;
+            const int64_t first = -floor_div(-(start_q - half), qone), last = floor_div(tip_q - half, qone);
+            if (last >= first && ((first == 1 && grid->edge[LBM_LEFT] == LBM_EDGE_FREE) ||
+                                  (last == grid->nx - 2 && grid->edge[LBM_RIGHT] == LBM_EDGE_FREE)))
+                return fail(LBM_ERR_ARG, "macroscopic crack faces: the crack leaves one intact column at a free edge");
+        }
         if (!(cr.fit_width > 0.0)) cr.fit_width = grid->dh;
         if (cr.hist_cap <= 0) cr.hist_cap = kDefaultHistCap;
     }
@@ -415,6 +386,14 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lb
     h->stream = (cudaStream_t)stream;
     h->sticky = LBM_OK;
     h->gparity = -1;
+    h->units_h = new (std::nothrow) std::vector<Unit>();
+    h->init_cut = new (std::nothrow) std::vector<uint32_t>();
+    if (!h->units_h || !h->init_cut) {
+        delete h->units_h;
+        delete h->init_cut;
+        delete h;
+        return fail(LBM_ERR_OOM, "host allocation failed");
+    }
     if (allocator && allocator->alloc && allocator->release) {
         h->alloc = *allocator;
         h->custom_alloc = true;
@@ -422,14 +401,15 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lb
     std::vector<int> seen(4, 0);
     for (int q = 0; q < n_loads; ++q) {
         const lbm_loading &L = loads[q];
-        if (L.edge < 0 || L.edge > 3 || seen[L.edge]) { delete h; return fail(LBM_ERR_ARG, "bad or repeated load edge"); }
-        if (L.kind < LBM_LOAD_ZERO || L.kind > LBM_LOAD_CONST) { delete h; return fail(LBM_ERR_ARG, "unknown load kind"); }
-        if (L.kind == LBM_LOAD_SERIES && (!L.series || L.n_series <= 0)) { delete h; return fail(LBM_ERR_ARG, "series load without data"); }
+        if (L.edge < 0 || L.edge > 3 || seen[L.edge]) { free_host(h); return fail(LBM_ERR_ARG, "bad or repeated load edge"); }
+        if (L.kind < LBM_LOAD_ZERO || L.kind > LBM_LOAD_CONST) { free_host(h); return fail(LBM_ERR_ARG, "unknown load kind"); }
+        if (L.kind == LBM_LOAD_SERIES && (!L.series || L.n_series <= 0)) { free_host(h); return fail(LBM_ERR_ARG, "series load without data"); }
         seen[L.edge] = 1;
         h->load[L.edge].kind = L.kind;
         h->load[L.edge].amp = L.amp;
         h->load[L.edge].t = L.t_ramp;
         h->load[L.edge].n = L.kind == LBM_LOAD_SERIES ? L.n_series : 0;
+        h->series_cap[L.edge] = h->load[L.edge].n;
     }
 
     // step kernel shape: a thread per 16-byte vector of a row, kThreads a CTA
@@ -441,8 +421,8 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lb
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->bps, kfn, kThreads, 0);
-    if (e != cudaSuccess) { delete h; return cuda_fail(e, "querying the device"); }
-    if (h->bps < 1) { delete h; return fail(LBM_ERR_ARG, "the step kernel does not fit on an SM"); }
+    if (e != cudaSuccess) { free_host(h); return cuda_fail(e, "querying the device"); }
+    if (h->bps < 1) { free_host(h); return fail(LBM_ERR_ARG, "the step kernel does not fit on an SM"); }
 
     const int64_t xoff = 128 / (int64_t)h->esize;
     h->pitch = xoff + (int64_t)h->ncb * cols + xoff;
@@ -472,12 +452,17 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lb
     for (int q = 0; q < 4; ++q) { o_ser[q] = off; off = align256(off + (size_t)h->load[q].n * 8); }
     h->block_bytes = off;
     h->block = dev_alloc(h, off);
-    if (!h->block) { delete h; return fail(LBM_ERR_OOM, "device allocation failed"); }
+    if (!h->block) { free_host(h); return fail(LBM_ERR_OOM, "device allocation failed"); }
     char *base = static_cast<char *>(h->block);
     const size_t origin = ((size_t)h->pitch + (size_t)xoff) * h->esize;   // row 0, column 0
     h->w[0] = base + o_w0 + origin;
     h->w[1] = base + o_w1 + origin;
     h->wd = base + o_wd + ((size_t)h->pitch + (size_t)xoff) * h->esize_d;
+    h->wbase[0] = base + o_w0;
+    h->wbase[1] = base + o_w1;
+    h->wdbase = base + o_wd;
+    h->plane_bytes = plane;
+    h->plane_d_bytes = plane_d;
     h->staging = staging ? reinterpret_cast<float *>(base + o_sg) : nullptr;
     h->cut_h = reinterpret_cast<uint32_t *>(base + o_ch);
     h->cut_v = reinterpret_cast<uint32_t *>(base + o_cv);
@@ -493,7 +478,7 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lb
     auto bail = [&](lbm_status rc) {
         cudaStreamSynchronize(s);
         dev_free(h, h->block);
-        delete h;
+        free_host(h);
         return rc;
     };
     e = cudaMemsetAsync(h->block, 0, h->block_bytes, s);
@@ -578,6 +563,8 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lb
         e = cudaMemcpyAsync(h->cut_v + (size_t)(jc - 1) * h->words, row.data(), row.size() * 4, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return bail(cuda_fail(e, "writing the initial crack"));
     }
+    h->init_st = hs;
+    *h->init_cut = row;
     e = cudaMemcpyAsync(h->st, &hs, sizeof hs, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = launch_wstar(h->st, h->load, h->grid.edge, grid->dt, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // host vectors go out of scope
@@ -585,7 +572,7 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lb
     e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return bail(cuda_fail(e, "creating the capture stream"));
     *out = h;
-    g_err.clear();
+    clear_error();
     return LBM_OK;
 }
 
@@ -696,7 +683,58 @@ lbm_status lbm_set_wd_scale(lbm_handle *h, double scale)
     LBM_CUDA(wd_from_f32(h, h->staging, scale, h->stream));
     h->wd_scale = scale;
     drop_graph(h);   // the scale is a kernel argument
+    h->gen += 1;
     LBM_CUDA(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_reset(lbm_handle *h)
+{
+    if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
+    if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");
+    cudaStream_t s = h->stream;
+    const size_t mask = (size_t)h->grid.ny * (size_t)h->words * 4;
+    LBM_CUDA(cudaMemsetAsync(h->wbase[0], 0, h->plane_bytes, s));
+    LBM_CUDA(cudaMemsetAsync(h->wbase[1], 0, h->plane_bytes, s));
+    LBM_CUDA(cudaMemsetAsync(h->wdbase, 0, h->plane_d_bytes, s));
+    LBM_CUDA(cudaMemsetAsync(h->cut_h, 0, mask, s));
+    LBM_CUDA(cudaMemsetAsync(h->cut_v, 0, mask, s));
+    if (h->cp.mode != CRACK_NONE)
+        LBM_CUDA(cudaMemcpyAsync(h->cut_v + (size_t)(h->jc - 1) * h->words, h->init_cut->data(),
+                                 h->init_cut->size() * 4, cudaMemcpyHostToDevice, s));
+    LBM_CUDA(cudaMemcpyAsync(h->st, &h->init_st, sizeof(CrackState), cudaMemcpyHostToDevice, s));
+    LBM_CUDA(launch_wstar(h->st, h->load, h->grid.edge, h->grid.dt, s));
+    LBM_CUDA(cudaStreamSynchronize(s));
+    h->parity = 0;
+    h->pending = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_loading(lbm_handle *h, const lbm_loading *L)
+{
+    if (!h || !L) return fail(LBM_ERR_ARG, "handle or load is NULL");
+    if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");
+    if (L->edge < 0 || L->edge > 3) return fail(LBM_ERR_ARG, "bad load edge");
+    if (L->kind < LBM_LOAD_ZERO || L->kind > LBM_LOAD_CONST) return fail(LBM_ERR_ARG, "unknown load kind");
+    if (L->kind == LBM_LOAD_SERIES) {
+        if (!L->series || L->n_series <= 0) return fail(LBM_ERR_ARG, "series load without data");
+        if (L->n_series > h->series_cap[L->edge])
+            return fail(LBM_ERR_ARG, "series longer than the one this edge was created with");
+    }
+    LBM_CUDA(cudaStreamSynchronize(h->stream));   // steps in flight read the old series
+    LoadDesc &D = h->load[L->edge];
+    if (L->kind == LBM_LOAD_SERIES)
+        LBM_CUDA(cudaMemcpyAsync(const_cast<double *>(D.series), L->series, (size_t)L->n_series * 8,
+                                 cudaMemcpyHostToDevice, h->stream));
+    D.kind = L->kind;
+    D.amp = L->amp;
+    D.t = L->t_ramp;
+    D.n = L->kind == LBM_LOAD_SERIES ? L->n_series : 0;
+    // w*(t_n) of the current state follows the new loading
+    LBM_CUDA(launch_wstar(h->st + h->parity, h->load, h->grid.edge, h->grid.dt, h->stream));
+    LBM_CUDA(cudaStreamSynchronize(h->stream));
+    drop_graph(h);   // the loads are kernel arguments
+    h->gen += 1;
     return LBM_OK;
 }
 
@@ -853,7 +891,7 @@ void lbm_destroy(lbm_handle *h)
         delete h->ev_kind;
     }
     dev_free(h, h->block);
-    delete h;
+    free_host(h);
 }
 
 // ---------------------------------------------------------------- batches
@@ -986,7 +1024,7 @@ lbm_status lbm_batch_create(lbm_handle *const *handles, int32_t n, int32_t band_
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return bail(cuda_fail(e, "uploading the batch tables"));
     *out = b;
-    g_err.clear();
+    clear_error();
     return LBM_OK;
 }
 
@@ -1058,6 +1096,6 @@ void lbm_batch_destroy(lbm_batch *b)
     delete b;
 }
 
-const char *lbm_last_error(void) { return g_err.c_str(); }
+const char *lbm_last_error(void) { return last_error(); }
 
 }  // extern "C"

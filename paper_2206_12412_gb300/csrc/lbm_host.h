@@ -1,0 +1,127 @@
+// lbm_host.h -- host-side state of a lattice handle and the helpers that
+// the C-ABI translation units share (internal; not part of the ABI).
+#pragma once
+
+#include "lbm.h"
+#include "lbm_internal.cuh"
+
+#include <string>
+#include <vector>
+
+using lbm::Unit;
+using lbm::CrackState;
+using lbm::History;
+using lbm::LoadDesc;
+using lbm::CrackParams;
+
+struct lbm_handle {
+    lbm_grid grid;
+    lbm_lattice lat;
+    lbm_material mat;
+    lbm_crack crack;
+    size_t esize;        // bytes per w element (and per arithmetic value)
+    size_t esize_d;      // bytes per stored wdot element
+    double wd_scale;     // stored wdot = wdot * wd_scale (16-bit storage)
+    float *staging;      // nx * ny floats for 16-bit wdot conversions
+    int64_t pitch;       // elements per padded row
+    int32_t words;       // 32-bit mask words per row
+    int32_t jc;          // crack line y = jc dh
+    // step kernel shape
+    int32_t ncb;         // column blocks of kThreads vectors
+    int32_t n_bands, band_rows, crack_band, sms, bps;
+    Unit *units;         // device table, capacity ny
+    std::vector<Unit> *units_h;   // host copy of the current partition
+    int64_t gen;         // bumped whenever step-kernel arguments or the partition change
+    // memory
+    lbm_allocator alloc;
+    bool custom_alloc;
+    void *block;
+    size_t block_bytes;
+    void *w[2];          // element (0, 0) of each W buffer
+    void *wd;
+    void *wbase[2], *wdbase;   // first byte of each plane (halo row, pad)
+    size_t plane_bytes, plane_d_bytes;
+    int64_t series_cap[4];     // capacity of each edge's device series buffer
+    CrackState init_st;        // state and crack row of step 0 (lbm_reset)
+    std::vector<uint32_t> *init_cut;
+    uint32_t *cut_h, *cut_v;
+    CrackState *st;      // two buffers
+    uint32_t *err;
+    History hist;
+    LoadDesc load[4];
+    CrackParams cp;
+    double g;
+    // stepping
+    int parity;          // W buffer and state buffer holding the current step
+    bool pending;        // the crack step after the last enqueued LBM step is not applied yet
+    cudaStream_t stream;
+    cudaStream_t cap_stream;
+    cudaGraphExec_t gexec;
+    int gparity;
+    lbm_status sticky;
+    // CUDA-event timing (lbm_set_profiling)
+    int profiling;
+    std::vector<cudaEvent_t> *ev;   // pairs: start, end
+    std::vector<int> *ev_kind;      // 0 step kernel, 1 finalize kernel
+    size_t ev_used;
+    double step_ms, fin_ms;
+    int64_t n_step, n_fin;
+};
+
+namespace lbm {
+namespace host {
+
+lbm_status fail(lbm_status s, const std::string &msg);
+lbm_status cuda_fail(cudaError_t e, const char *what);
+void clear_error();
+const char *last_error();
+
+// Apply the pending crack step (if any) on the handle's stream.
+lbm_status finalize(lbm_handle *h);
+// Synchronise, then report sticky device errors.
+lbm_status check_sticky(lbm_handle *h);
+// Step-kernel arguments of the step that reads W buffer `par`.
+template <typename T, typename D>
+inline void make_step_args(const lbm_handle *h, int par, StepArgs<T, D> &a)
+{
+    a.w_in = static_cast<const T *>(h->w[par]);
+    a.w_out = static_cast<T *>(h->w[par ^ 1]);
+    a.wd = static_cast<D *>(h->wd);
+    a.wd_scale = (T)h->wd_scale;
+    a.wd_inv = (T)(1.0 / h->wd_scale);
+    a.pitch = h->pitch;
+    a.nx = h->grid.nx;
+    a.ny = h->grid.ny;
+    a.ncb = h->ncb;
+    a.crack_band = h->crack_band;
+    for (int e = 0; e < 4; ++e) { a.edge[e] = h->grid.edge[e]; a.load[e] = h->load[e]; }
+    a.g = (T)h->g;
+    a.dt = (T)h->grid.dt;
+    a.cut_h = h->cut_h;
+    a.cut_v = h->cut_v;
+    a.words = h->words;
+    a.units = h->units;
+    a.s_in = h->st + par;
+    a.s_out = h->st + (par ^ 1);
+    a.err = h->err;
+    a.p = h->cp;
+    a.hist = h->hist;
+}
+
+// Replays a fixed chunk of kernel launches that alternate between two
+// parities as a CUDA graph, captured on first use for the starting parity.
+struct ChunkGraph {
+    cudaGraphExec_t exec = nullptr;
+    int parity = -1;
+    int64_t gen = -1;
+    void reset();
+};
+
+}  // namespace host
+}  // namespace lbm
+
+#define LBM_CUDA(call)                                                  \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return ::lbm::host::cuda_fail(e_, #call); \
+    } while (0)

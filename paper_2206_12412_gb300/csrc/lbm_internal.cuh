@@ -124,10 +124,63 @@ struct BatchUnit {
     int32_t inst, cb, band, pad;
 };
 
+// Recording of a forward run for the adjoint (see the adjoint kernel).  The
+// sensors of each unit (CTA of the step kernel: band * ncb + cb) are the
+// entries s_off[u] .. s_off[u+1]-1 of s_ent, each an index k into s_i / s_j.
+// Step t of the recording (t = step - *n0, 0 <= t < n_steps) stores the misfit
+// r = w(x_k) - target[t][k] of the state it produces in resid[t % ring][k],
+// adds r^2 to loss[k] if acc_loss, and stores the last severed crack column
+// in force during step t in i_last[t].
+struct RecArgs {
+    const int32_t *s_off, *s_ent, *s_i, *s_j;
+    const double *target;
+    double *resid;
+    double *loss;
+    int32_t *i_last;
+    const int64_t *n0;
+    int64_t n_steps, ring;
+    int32_t ns, acc_loss;
+};
+
+// One step of the adjoint sweep (see lbm_adjoint.cu).  The adjoint state is
+// held as the pair (m, a) in the layout of (w, wdot): m in two ping-pong
+// planes with pads (w_in / w_out), a in one plane updated in place (wd).  The
+// step index n is read from cnt[par] and n - 1 written to cnt[par ^ 1].
+template <typename T>
+struct AdjArgs {
+    const T *w_in;             // m, input
+    T *w_out;                  // m, output
+    T *wd;                     // a
+    T wd_scale, wd_inv;        // 1 (the row helpers' storage scale)
+    int64_t pitch;
+    int32_t nx, ny, ncb, crack_band;
+    int32_t edge[4];
+    T g, dt;
+    int32_t jc, macro, i_first, ns;
+    const Unit *units;
+    const int32_t *i_last;     // [n_steps] last severed column in force during forward step t
+    const int64_t *cnt_in;
+    int64_t *cnt_out;
+    int64_t n_steps, ring;
+    const int32_t *s_off, *s_ent, *s_i, *s_j;
+    const double *resid;       // [ring][ns] misfits of the recorded states
+    double *part;              // [n_steps][4][slots] per-CTA sums of m along the Dirichlet edges
+    uint32_t *err;
+    int32_t slots, pad;
+};
+
 template <typename T, typename D> const void *step_kernel_ptr();
 template <typename T, typename D>
 cudaError_t launch_batch_step(const StepArgs<T, D> *descs, const BatchUnit *units, int n_units, int par, cudaStream_t s);
 template <typename T, typename D> cudaError_t launch_step(const StepArgs<T, D> &a, int bands, cudaStream_t s);
+template <typename T> cudaError_t launch_step_rec(const StepArgs<T, T> &a, const RecArgs &r, int bands, cudaStream_t s);
+template <typename T> const void *adjoint_kernel_ptr();
+template <typename T> cudaError_t launch_adjoint(const AdjArgs<T> &a, int bands, cudaStream_t s);
+cudaError_t launch_loss_sum(const double *acc, int ns, double *out, cudaStream_t s);
+cudaError_t launch_grad_sum(const double *part, int64_t T, int slots, int dir_mask, double g, double *grad,
+                            cudaStream_t s);
+template <typename T>
+cudaError_t launch_adjoint_out(const T *a, const T *m, int64_t pitch, int nx, int ny, T dt, T *dw, T *dwd, cudaStream_t s);
 template <typename D>
 cudaError_t launch_wd_to_f32(const D *wd, int64_t pitch, int nx, int ny, float scale, float *dst, cudaStream_t s);
 template <typename D>

@@ -151,6 +151,31 @@ def lbm_destroy(h: int):
         load_library().lbm_destroy(C.c_void_p(h))
 
 
+def lbm_reset(h: int):
+    _check(load_library().lbm_reset(C.c_void_p(h)))
+
+
+def make_loading(edge: str, kind: str, series=None, amp: float = 0.0, t_ramp: float = 0.0):
+    """(lbm_loading struct, keepalive) for one edge."""
+    L = A.Loading()
+    L.edge = A.EDGE_INDEX[edge]
+    L.kind = A.LOAD[kind]
+    L.amp = float(amp)
+    L.t_ramp = float(t_ramp)
+    arr = None
+    if kind == "series":
+        arr = np.ascontiguousarray(series, dtype=np.float64)
+        L.series = arr.ctypes.data_as(C.POINTER(C.c_double))
+        L.n_series = arr.size
+    return L, arr
+
+
+def lbm_set_loading(h: int, edge: str, kind: str, series=None, amp: float = 0.0, t_ramp: float = 0.0):
+    L, keep = make_loading(edge, kind, series, amp, t_ramp)
+    _check(load_library().lbm_set_loading(C.c_void_p(h), C.byref(L)))
+    del keep
+
+
 def lbm_last_error() -> str:
     return load_library().lbm_last_error().decode()
 
@@ -347,6 +372,16 @@ class Lattice:
     def device_bytes(self) -> int:
         return lbm_device_bytes(self.h)
 
+    def reset(self):
+        """Back to step 0: zero fields, the initial crack, empty history."""
+        lbm_reset(self.h)
+
+    def set_loading(self, edge: str, kind: str, series=None, amp: float = 0.0, t_ramp: float = 0.0):
+        """Replace one edge's loading (a series no longer than at creation)."""
+        if series is not None and isinstance(series, self.torch.Tensor):
+            series = series.detach().to("cpu", self.torch.float64).numpy()
+        lbm_set_loading(self.h, edge, kind, series, amp, t_ramp)
+
 
 # ----------------------------------------------------------------- batches
 
@@ -398,3 +433,146 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------- adjoint
+
+def lbm_tape_create(h: int, sensors, n_steps: int, checkpoint_every: int = 0,
+                    allocator: A.Allocator | None = None) -> int:
+    sens = np.ascontiguousarray(np.asarray(sensors, dtype=np.int32).reshape(-1, 2))
+    out = C.c_void_p()
+    _check(load_library().lbm_tape_create(C.c_void_p(h), sens.ctypes.data_as(C.POINTER(C.c_int32)), sens.shape[0],
+                                          int(n_steps), int(checkpoint_every),
+                                          C.byref(allocator) if allocator is not None else None, C.byref(out)))
+    return out.value
+
+
+def lbm_tape_destroy(t: int):
+    if t:
+        load_library().lbm_tape_destroy(C.c_void_p(t))
+
+
+class Tape:
+    """Recording of n_steps time steps of a Lattice (F32 or F64 storage) with
+    the misfit of w at the sensor sites, and the transposed sweep that turns
+    it into dL/dw*_e(t_n), dL/dw0 and dL/dwdot0 (include/lbm_adjoint.h).
+
+    sensors: (ns, 2) integer (i, j) sites.  checkpoint_every: 0 keeps the
+    misfits of every step, k > 0 keeps a state snapshot every k steps and
+    recomputes each segment in the backward sweep."""
+
+    def __init__(self, lattice: Lattice, sensors, n_steps: int, checkpoint_every: int = 0,
+                 torch_allocator: bool = True):
+        self.lattice = lattice
+        self.torch = lattice.torch
+        self.sensors = np.ascontiguousarray(np.asarray(sensors, dtype=np.int32).reshape(-1, 2))
+        self.ns = self.sensors.shape[0]
+        self.n_steps = int(n_steps)
+        self._alloc = TorchAllocator(lattice.stream) if torch_allocator else None
+        self.t = lbm_tape_create(lattice.h, self.sensors, self.n_steps, checkpoint_every,
+                                 self._alloc.struct if self._alloc else None)
+
+    def forward(self, targets, loss_to_host: bool = True):
+        """Run n_steps steps of the lattice from its current state.  targets:
+        (n_steps, ns) FP64 (numpy array or CUDA tensor).  Returns L (float)
+        if loss_to_host, else None (no synchronisation)."""
+        lib = load_library()
+        torch = self.torch
+        if isinstance(targets, torch.Tensor) and targets.is_cuda:
+            tg = targets.to(torch.float64).contiguous()
+            assert tg.numel() == self.n_steps * self.ns
+            ptr, on_dev, keep = tg.data_ptr(), 1, tg
+        else:
+            keep = np.ascontiguousarray(np.asarray(targets, dtype=np.float64).reshape(self.n_steps, self.ns))
+            ptr, on_dev = keep.ctypes.data, 0
+        loss = C.c_double(0.0)
+        _check(lib.lbm_tape_forward(C.c_void_p(self.t), C.c_void_p(ptr), on_dev,
+                                    C.byref(loss) if loss_to_host else None))
+        del keep
+        return loss.value if loss_to_host else None
+
+    def backward(self, device: bool = True):
+        """(dload (4, n_steps) FP64, dw0 (ny, nx), dwdot0 (ny, nx)) as CUDA
+        tensors (enqueued on the lattice's stream) or, if not device, host
+        numpy arrays."""
+        lib = load_library()
+        lat = self.lattice
+        torch = self.torch
+        if device:
+            dload = torch.empty((4, self.n_steps), dtype=torch.float64, device="cuda")
+            dw = torch.empty((lat.ny, lat.nx), dtype=lat.torch_dtype, device="cuda")
+            dwd = torch.empty((lat.ny, lat.nx), dtype=lat.torch_dtype, device="cuda")
+            ptrs = (dload.data_ptr(), dw.data_ptr(), dwd.data_ptr())
+        else:
+            dload = np.empty((4, self.n_steps))
+            dw = np.empty((lat.ny, lat.nx), lat.np_dtype)
+            dwd = np.empty((lat.ny, lat.nx), lat.np_dtype)
+            ptrs = (dload.ctypes.data, dw.ctypes.data, dwd.ctypes.data)
+        _check(lib.lbm_tape_backward(C.c_void_p(self.t), C.c_void_p(ptrs[0]), int(device), C.c_void_p(ptrs[1]),
+                                     C.c_void_p(ptrs[2]), int(device), lat.dtype_code))
+        return dload, dw, dwd
+
+    def misfits(self) -> np.ndarray:
+        """(n_steps, ns) misfits w^n(x_k) - target of the last recording."""
+        out = np.empty((self.n_steps, self.ns))
+        _check(load_library().lbm_tape_misfits(C.c_void_p(self.t), C.c_void_p(out.ctypes.data), 0))
+        return out
+
+    def close(self):
+        if getattr(self, "t", None):
+            lbm_tape_destroy(self.t)
+            self.t = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sensor_misfit(tape: Tape, edge: str, u, w0, wdot0, targets):
+    """L = sum_{n,k} (w^n(x_k) - targets[n-1, k])^2 of tape.n_steps steps of
+    the tape's lattice from step 0, with the loading of `edge` set to the
+    series u (length n_steps) and initial fields (w0, wdot0), as a
+    differentiable function of u, w0 and wdot0 (torch.autograd).  The
+    gradient is that of the run with the cut schedule it took."""
+    return _SensorMisfit.apply(u, w0, wdot0, tape, edge, targets)
+
+
+def _autograd_function():
+    import torch
+
+    class SensorMisfitFn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, u, w0, wdot0, tape, edge, targets):
+            if u.numel() != tape.n_steps:
+                raise ValueError("the load series must have one value per recorded step")
+            lat = tape.lattice
+            lat.reset()
+            lat.set_loading(edge, "series", series=u)
+            lat.set_fields(w0.detach(), wdot0.detach())
+            loss = tape.forward(targets)
+            ctx.tape = tape
+            ctx.edge = A.EDGE_INDEX[edge]
+            ctx.u_meta = (u.dtype, u.device)
+            return torch.tensor(loss, dtype=torch.float64, device=w0.device)
+
+        @staticmethod
+        def backward(ctx, gL):
+            dload, dw, dwd = ctx.tape.backward(device=True)
+            gu = (gL * dload[ctx.edge]).to(ctx.u_meta[0]).to(ctx.u_meta[1])
+            return gu, (gL * dw).to(dw.dtype), (gL * dwd).to(dwd.dtype), None, None, None
+
+    return SensorMisfitFn
+
+
+class _Lazy:
+    fn = None
+
+    def apply(self, *args):
+        if _Lazy.fn is None:
+            _Lazy.fn = _autograd_function()
+        return _Lazy.fn.apply(*args)
+
+
+_SensorMisfit = _Lazy()

@@ -206,3 +206,56 @@ def adjoint_problem(nx: int = 1024, ny: int = 1024, n_steps: int = 8000, ns: int
 
 
 ADJOINT_STEPS = 8000
+
+
+def adjoint_case(kind: str, n_steps: int, seed: int, ns: int = 6):
+    """Small sensor-misfit problems whose cut schedule does not depend on the
+    fields (stationary or prescribed cracks), each Dirichlet edge loaded by a
+    seeded random series, with random initial fields, sensors and targets.
+    Returns (problem, loaded edges, w0, wd0, sensors (ns, 2), targets
+    (n_steps, ns)).  The "wide_*" kinds span several column blocks of the
+    CUDA kernels with a ragged last block."""
+    rng = np.random.default_rng(seed)
+    T = int(n_steps)
+    if kind == "macro_growth":
+        p = base_problem(24, 20, bc_mode="macroscopic")
+        p = with_crack(p, mode="prescribed", y=10.0, x_tip=5.3, v_rel=0.6)
+        loaded = ("bottom", "top")
+    elif kind == "bb_growth":
+        p = base_problem(22, 18, bc_mode="bounceback")
+        p = with_crack(p, mode="prescribed", y=9.0, x_tip=4.0, v_rel=0.5)
+        loaded = ("bottom", "top")
+    elif kind == "bb_periodic":
+        p = base_problem(20, 16, bc_mode="bounceback", edges=("periodic", "periodic", "dirichlet", "free"))
+        p = with_crack(p, mode="stationary", y=8.0, x_start=3.0, x_tip=11.0)
+        loaded = ("bottom",)
+    elif kind == "all_dirichlet":
+        p = base_problem(18, 15, bc_mode="macroscopic", edges=("dirichlet", "free", "dirichlet", "dirichlet"))
+        p = with_crack(p, mode="prescribed", y=7.0, x_start=6.0, x_tip=8.0, v_rel=0.3)
+        loaded = ("left", "bottom", "top")
+    elif kind == "scaled_units":
+        # dh, dt and c_s away from 1, so that every factor of dt, dh and g shows
+        p = base_problem(20, 18, bc_mode="macroscopic", cs=0.7, dh=0.5, dt=0.3)
+        p = with_crack(p, mode="prescribed", y=4.5, x_tip=2.6, v_rel=0.5)
+        loaded = ("bottom", "top")
+    elif kind == "no_crack":
+        p = base_problem(16, 14, edges=("free", "dirichlet", "periodic", "periodic"))
+        loaded = ("right",)
+    elif kind == "wide_macro":
+        p = base_problem(1100, 70, bc_mode="macroscopic", edges=("dirichlet", "free", "dirichlet", "dirichlet"))
+        p = with_crack(p, mode="prescribed", y=37.0, x_tip=500.7, v_rel=0.7)
+        loaded = ("left", "bottom", "top")
+    elif kind == "wide_bb":
+        p = base_problem(777, 41, bc_mode="bounceback", edges=("free", "dirichlet", "dirichlet", "free"))
+        p = with_crack(p, mode="prescribed", y=20.0, x_start=3.0, x_tip=505.0, v_rel=0.4)
+        loaded = ("right", "bottom")
+    else:
+        raise KeyError(kind)
+    for e in loaded:
+        p = with_series_load(p, e, 1e-3 * rng.standard_normal(T))
+    nx, ny = p["nx"], p["ny"]
+    w0 = 1e-3 * rng.standard_normal((ny, nx))
+    wd0 = 1e-4 * rng.standard_normal((ny, nx))
+    sens = np.stack([rng.integers(0, nx, ns), rng.integers(0, ny, ns)], axis=1).astype(np.int32)
+    tgt = 1e-3 * rng.standard_normal((T, ns))
+    return p, loaded, w0, wd0, sens, tgt

@@ -1,4 +1,4 @@
-"""The C-ABI library builds, loads and exports what include/lbm.h declares;
+"""The C-ABI library builds, loads and exports what include/*.h declare;
 its struct layouts agree with the Python binding; argument validation
 rejects bad configurations before touching a GPU.  No CUDA device needed."""
 import ctypes as C
@@ -12,7 +12,7 @@ from paper_2206_12412_gb300 import _abi as A
 from paper_2206_12412_gb300 import build as B
 from paper_2206_12412_gb300 import lbm
 
-HEADER = os.path.join(B.INCLUDE, "lbm.h")
+HEADERS = sorted(os.path.join(B.INCLUDE, f) for f in os.listdir(B.INCLUDE) if f.endswith(".h"))
 
 
 @pytest.fixture(scope="module")
@@ -21,14 +21,17 @@ def lib():
 
 
 def declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", text)))
+    names = set()
+    for path in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(path).read(), flags=re.S)
+        names |= set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", text))
+    return sorted(names)
 
 
 def test_header_declares_core_calls():
     names = declared_functions()
-    for core in ("lbm_create", "lbm_step", "lbm_fields", "lbm_crack_state", "lbm_destroy"):
+    for core in ("lbm_create", "lbm_step", "lbm_fields", "lbm_crack_state", "lbm_destroy", "lbm_tape_create",
+                 "lbm_tape_forward", "lbm_tape_backward"):
         assert core in names
 
 
@@ -89,7 +92,9 @@ def _structs(**over):
     ({"mat__rho": -1.0}, "rho"),
     ({"cr__y": 64.5}, "multiple of dh"),
     ({"cr__y": 2.0}, "too close"),
-    ({"cr__x_tip": 127.5}, "left of"),
+    ({"cr__x_tip": 128.0}, "left of"),
+    ({"cr__x_tip": 126.6}, "one intact column"),
+    ({"cr__x_start": 1.2}, "one intact column"),
     ({"cr__x_start": 40.0}, "x_start"),
     ({"cr__mode": 9}, "crack mode"),
 ])
@@ -121,5 +126,13 @@ def test_null_handles_are_rejected(lib):
     assert lib.lbm_sync(None) == A.LBM_ERR_ARG
     assert lib.lbm_fields(None, 0, None, 0, 0) == A.LBM_ERR_ARG
     assert lib.lbm_crack_state(None, None, None, None, None, None, 0, None) == A.LBM_ERR_ARG
+    assert lib.lbm_reset(None) == A.LBM_ERR_ARG
+    assert lib.lbm_set_loading(None, None) == A.LBM_ERR_ARG
+    out = C.c_void_p()
+    assert lib.lbm_tape_create(None, None, 0, 1, 0, None, C.byref(out)) == A.LBM_ERR_ARG
+    assert lib.lbm_tape_forward(None, None, 0, None) == A.LBM_ERR_ARG
+    assert lib.lbm_tape_backward(None, None, 0, None, None, 0, 0) == A.LBM_ERR_ARG
+    assert lib.lbm_tape_misfits(None, None, 0) == A.LBM_ERR_ARG
+    lib.lbm_tape_destroy(None)
     lib.lbm_destroy(None)
     assert lbm.lbm_last_error() != ""

@@ -104,7 +104,11 @@ def test_plain_128_stationary_2000_steps(oracle_mod, gpu, storage, bc_mode):
 
 def _mixed_problem(bc_mode, nx=37, ny=29):
     p = W.base_problem(nx, ny, bc_mode=bc_mode, edges=("free", "dirichlet", "dirichlet", "free"))
-    p = W.with_crack(p, mode="stationary", y=float(ny // 2), x_start=min(4.3, 0.2 * nx), x_tip=nx * 0.55)
+    # (a single intact column between the crack and the free left edge is an
+    # unstable ligament with macroscopic faces, rejected at create: start the
+    # crack at the edge on lattices too narrow for two columns)
+    x_start = min(4.3, 0.2 * nx) if 0.2 * nx >= 1.5 else 0.0
+    p = W.with_crack(p, mode="stationary", y=float(ny // 2), x_start=x_start, x_tip=nx * 0.55)
     p["loads"] = [{"edge": "right", "kind": "const", "amp": 3e-4, "t": 0.0},
                   {"edge": "bottom", "kind": "sin2", "amp": -5e-4, "t": 40.0}]
     return p

@@ -12,44 +12,7 @@ from paper_2206_12412_gb300 import workloads as W
 
 
 def _case(kind: str, T: int, seed: int):
-    """Small problems whose cut schedule does not depend on the fields
-    (stationary or prescribed cracks), with every Dirichlet edge loaded by a
-    random series."""
-    rng = np.random.default_rng(seed)
-    if kind == "macro_growth":
-        p = W.base_problem(24, 20, bc_mode="macroscopic")
-        p = W.with_crack(p, mode="prescribed", y=10.0, x_tip=5.3, v_rel=0.6)
-        loaded = ("bottom", "top")
-    elif kind == "bb_growth":
-        p = W.base_problem(22, 18, bc_mode="bounceback")
-        p = W.with_crack(p, mode="prescribed", y=9.0, x_tip=4.0, v_rel=0.5)
-        loaded = ("bottom", "top")
-    elif kind == "bb_periodic":
-        p = W.base_problem(20, 16, bc_mode="bounceback", edges=("periodic", "periodic", "dirichlet", "free"))
-        p = W.with_crack(p, mode="stationary", y=8.0, x_start=3.0, x_tip=11.0)
-        loaded = ("bottom",)
-    elif kind == "all_dirichlet":
-        p = W.base_problem(18, 15, bc_mode="macroscopic", edges=("dirichlet", "free", "dirichlet", "dirichlet"))
-        p = W.with_crack(p, mode="prescribed", y=7.0, x_start=6.0, x_tip=8.0, v_rel=0.3)
-        loaded = ("left", "bottom", "top")
-    elif kind == "scaled_units":
-        # dh, dt and c_s away from 1, so that every factor of dt, dh and g shows
-        p = W.base_problem(20, 18, bc_mode="macroscopic", cs=0.7, dh=0.5, dt=0.3)
-        p = W.with_crack(p, mode="prescribed", y=4.5, x_tip=2.6, v_rel=0.5)
-        loaded = ("bottom", "top")
-    elif kind == "no_crack":
-        p = W.base_problem(16, 14, edges=("free", "dirichlet", "periodic", "periodic"))
-        loaded = ("right",)
-    else:
-        raise KeyError(kind)
-    for e in loaded:
-        p = W.with_series_load(p, e, 1e-3 * rng.standard_normal(T))
-    nx, ny = p["nx"], p["ny"]
-    w0 = 1e-3 * rng.standard_normal((ny, nx))
-    wd0 = 1e-4 * rng.standard_normal((ny, nx))
-    sens = np.stack([rng.integers(0, nx, 6), rng.integers(0, ny, 6)], axis=1).astype(np.int32)
-    tgt = 1e-3 * rng.standard_normal((T, 6))
-    return p, loaded, w0, wd0, sens, tgt
+    return W.adjoint_case(kind, T, seed)
 
 
 def _loss(p, T, sens, tgt, w0, wd0):

@@ -366,7 +366,7 @@ def test_K_criterion_velocity_and_advance(oracle_mod):
     grew = 0
     for n in range(400):
         K, v, np_ = h["K"][n], h["v"][n], h["npairs"][n]
-        arrested = tip_prev == (p["nx"] - 1) * 2**32     # the tip stopped at the last column
+        arrested = tip_prev == p["nx"] * 2**32     # the tip stopped at the far edge
         if np_ > 0 and abs(K) > K_C and not arrested:
             x = mpmath.mpf(abs(K)) / mpmath.mpf(K_C)
             expect = mpmath.mpf(0.85) * mpmath.tanh(mpmath.sqrt(x**4 - 1))
@@ -378,7 +378,7 @@ def test_K_criterion_velocity_and_advance(oracle_mod):
             assert v == 0.0
         step = h["tip_q"][n] - tip_prev
         exact = mpmath.mpf(v) * mpmath.mpf(cs) * p["dt"] / p["dh"] * 2**32
-        clamp = (p["nx"] - 1) * 2**32
+        clamp = p["nx"] * 2**32
         if h["tip_q"][n] == clamp:
             assert tip_prev + exact + 0.5 >= clamp
         else:
@@ -390,7 +390,8 @@ def test_K_criterion_velocity_and_advance(oracle_mod):
 def test_prescribed_advance_cuts_and_clamp(oracle_mod):
     """Prescribed growth: Delta a = v c_s dt per step on the 2^-32 dh grid; the
     severed links are exactly those with x_start <= x_i <= tip (closed
-    segment); the tip stops at x = (nx - 1) dh."""
+    segment); the tip stops at the far edge x = nx dh, every link of the crack
+    row severed."""
     nx, ny, jc = 40, 16, 8
     p = W.base_problem(nx, ny, bc_mode="macroscopic")
     p = W.with_crack(p, mode="prescribed", y=float(jc), x_start=2.5, x_tip=10.0, v_rel=0.6)
@@ -400,7 +401,7 @@ def test_prescribed_advance_cuts_and_clamp(oracle_mod):
     for n in range(1, 121):
         o.step(1)
         c = o.crack()
-        expect = min(tip0 + n * dq, (nx - 1) * 2**32)
+        expect = min(tip0 + n * dq, nx * 2**32)
         assert c["tip_q"] == expect
         _, cv = o.cuts()
         assert np.array_equal(cv.astype(bool), crack_cuts(nx, ny, jc, 2.5, expect / 2**32))
