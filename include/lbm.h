@@ -258,6 +258,30 @@ lbm_status lbm_set_loading(lbm_handle *h, const lbm_loading *load);
 lbm_status lbm_set_wd_scale(lbm_handle *h, double scale);
 lbm_status lbm_get_wd_scale(const lbm_handle *h, double *scale);
 
+/* Copy the wdot plane of a lattice with 16-bit wdot storage
+ * (LBM_F32_WD_BF16 / LBM_F32_WD_F16) into host memory as a dense ny x nx FP32
+ * array -- the same values lbm_fields(h, LBM_FIELD_WDOT, dst, 0, LBM_F32)
+ * gives -- without allocating and without the handle's staging buffer: the
+ * conversion runs into one fixed device array of 2^20 floats (4 MiB) that
+ * belongs to the library.  The paper has no counterpart (this is a
+ * memory-management variant of a copy-out).  It is meant for callers that
+ * must not allocate device memory where they run -- for example a monitor
+ * thread sampling a running lattice while the application's device memory
+ * is fully committed, where an allocation could fail or synchronise the
+ * device -- and that must not disturb the handle's own staging buffer, which
+ * calls on the handle's stream use.  Limits and rules:
+ *   - lattices of at most 2^20 sites (LBM_ERR_ARG beyond); n_floats >= nx*ny;
+ *   - LBM_ERR_STATE for other storages (use lbm_fields);
+ *   - the first call on a device looks up the array's address and must not
+ *     be made while a stream is being captured;
+ *   - the array is shared by every call on the device: calls that overlap in
+ *     time race on it and must be serialised by the callers;
+ *   - nothing in the array needs to start at zero (a call reads back only
+ *     what it wrote);
+ *   - synchronises the handle's stream; applies the pending crack step first,
+ *     as lbm_fields does. */
+lbm_status lbm_wdot_to_host_noalloc(lbm_handle *h, float *dst_host, int64_t n_floats);
+
 /* Bytes of device memory the handle holds. */
 lbm_status lbm_device_bytes(const lbm_handle *h, int64_t *bytes);
 

@@ -91,6 +91,7 @@ PROTOTYPES = {
     "lbm_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "lbm_batch_destroy": (None, [C.c_void_p]),
     "lbm_reset": (C.c_int, [C.c_void_p]),
+    "lbm_wdot_to_host_noalloc": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_int64]),
     "lbm_set_loading": (C.c_int, [C.c_void_p, C.POINTER(Loading)]),
     "lbm_last_error": (C.c_char_p, []),
     # include/lbm_adjoint.h

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -870,6 +871,69 @@ lbm_status lbm_profile_read(lbm_handle *h, double *step_ms, int64_t *n_step, dou
         h->n_step = h->n_fin = 0;
     }
     return LBM_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------- copy-out of 16-bit wdot, no allocation
+//
+// The conversion of a 16-bit wdot plane to FP32 normally goes through the
+// handle's staging buffer (allocated by lbm_create).  lbm_wdot_to_host_noalloc
+// runs the same conversion kernel into one fixed device array that belongs to
+// the library, so it allocates nothing and leaves the handle's staging buffer
+// alone.  Nothing in the array needs to start at zero: a call reads back only
+// elements it has just written.  All calls on a device share the array, so
+// calls that overlap in time (from several threads, or on several streams)
+// race on it; callers serialise them.
+
+namespace {
+
+constexpr int64_t kNoAllocFloats = (int64_t)1 << 20;   // 4 MiB: lattices of up to 2^20 sites
+constexpr int kNoAllocDevices = 64;
+
+static __device__ __align__(256) float g_noalloc_wd[kNoAllocFloats];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kNoAllocDevices];
+
+// Address of the array on the current device, looked up on the first call on
+// that device (that call must not come while a stream is being captured).
+cudaError_t noalloc_scratch(float **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNoAllocDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_wd);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = static_cast<float *>(g_noalloc_addr[dev]);
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_wdot_to_host_noalloc(lbm_handle *h, float *dst_host, int64_t n_floats)
+{
+    if (!h || !dst_host) return fail(LBM_ERR_ARG, "handle or dst is NULL");
+    if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");
+    if (!wd16(h)) return fail(LBM_ERR_STATE, "only 16-bit wdot storage is converted; use lbm_fields");
+    const int64_t n = (int64_t)h->grid.nx * h->grid.ny;
+    if (n > kNoAllocFloats) return fail(LBM_ERR_ARG, "lattice larger than the fixed conversion array (2^20 sites)");
+    if (n_floats < n) return fail(LBM_ERR_ARG, "dst too small");
+    float *scratch = nullptr;
+    LBM_CUDA(noalloc_scratch(&scratch));
+    lbm_status rc = finalize(h);
+    if (rc != LBM_OK) return rc;
+    LBM_CUDA(wd_to_f32(h, scratch, h->wd_scale, h->stream));
+    LBM_CUDA(cudaMemcpyAsync(dst_host, scratch, (size_t)n * 4, cudaMemcpyDeviceToHost, h->stream));
+    return check_sticky(h);
 }
 
 lbm_status lbm_device_bytes(const lbm_handle *h, int64_t *bytes)

@@ -176,6 +176,14 @@ def lbm_set_loading(h: int, edge: str, kind: str, series=None, amp: float = 0.0,
     del keep
 
 
+def lbm_wdot_to_host_noalloc(h: int, dst: np.ndarray):
+    """16-bit wdot plane -> dst (float32, nx * ny), through the library's fixed
+    conversion array (no allocation)."""
+    assert dst.dtype == np.float32 and dst.flags.c_contiguous
+    _check(load_library().lbm_wdot_to_host_noalloc(C.c_void_p(h), dst.ctypes.data_as(C.POINTER(C.c_float)),
+                                                   dst.size))
+
+
 def lbm_last_error() -> str:
     return load_library().lbm_last_error().decode()
 
