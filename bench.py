@@ -43,7 +43,8 @@ UNIT = "GLUPS"
 BYTES_PER_SITE = 16            # FP32 moment form: read w, wdot; write w, wdot
 WORKLOAD = "kcrit_single_4096x2048_f32"
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_kernel_f32_4096x2048.md")
-KERNEL_SOURCE = os.path.join(ROOT, "paper_2206_12412_gb300", "csrc", "lbm_kernels.cu")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2206_12412_gb300", "csrc", f)
+                  for f in ("lbm_kernels.cu", "lbm_rows.cuh", "lbm_internal.cuh")]
 
 
 def dist_env():
@@ -60,12 +61,21 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def kernel_source_sha256() -> str:
+    """Hash of the files that define the step kernel (concatenated)."""
+    h = hashlib.sha256()
+    for path in KERNEL_SOURCES:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def traffic_from_profile():
     """Per-launch DRAM bytes of the step kernel from the committed ncu summary,
     or None if there is none or the kernel source changed since it was taken."""
     try:
         text = open(PROFILE_SUMMARY).read()
-        src = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
+        src = kernel_source_sha256()
     except OSError:
         return None
     m = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", text)
@@ -216,13 +226,13 @@ def measure_batched(lbm, W, torch, stream, steps, peak):
             "timing": "CUDA events around the whole run, no flush (state larger than L2)"}
 
 
-def measure_adjoint(lbm, W, torch, stream):
+def measure_adjoint(lbm, W, torch, stream, n_steps=None):
     """Sensor-misfit gradient on the 1024 x 1024, 8000-step problem (FP32,
     64 sensors): the plain forward run, the recording forward run and the
     transposed sweep, with stored misfits and with sqrt(T) checkpoints.  The
     16 MB state stays in L2 (the steps are timed back to back)."""
     import numpy as np
-    a = W.adjoint_problem()
+    a = W.adjoint_problem() if n_steps is None else W.adjoint_problem(n_steps=n_steps)
     p, T, sens = a["problem"], a["n_steps"], a["sensors"]
     ref = lbm.Lattice(W.with_series_load(p, "top", a["u_ref"]), "f32", stream=stream)
     tref = lbm.Tape(ref, sens, T)
@@ -457,6 +467,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-lattice batched measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the sensor-misfit gradient measurement")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="only the sensor-misfit gradient measurement (for ncu)")
+    ap.add_argument("--adjoint-steps", type=int, default=None, help="steps of the adjoint workload (default 8000)")
     ap.add_argument("--profile-only", action="store_true",
                     help="only prelude, warm-up and timed steps (for ncu); prints kernel times")
     args = ap.parse_args()
@@ -464,6 +477,16 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.adjoint_only:
+        # the sensor-misfit gradient alone (for profiling the adjoint kernel)
+        import torch
+        from paper_2206_12412_gb300 import lbm
+        from paper_2206_12412_gb300 import workloads as W
+        torch.cuda.set_device(local)
+        out = measure_adjoint(lbm, W, torch, torch.cuda.current_stream(), n_steps=args.adjoint_steps)
+        if rank == 0:
+            print(json.dumps({"adjoint_only": True, **out}), flush=True)
+        return 0
     return run_ours(args, rank, world, local)
 
 

@@ -48,13 +48,39 @@ __device__ __forceinline__ uint32_t col_bits(int x0, int lo, int hi)
     return b;
 }
 
-// Sources of state n on row j of this thread's columns: the sensors of the
-// CTA's list that lie there add 2 r to alpha and 2 r dt to m.
+// The sensor sources of state n that fall in one CTA: the first kMaxSrc of
+// its list staged in shared memory (site and value 2 r), any further ones
+// read from the global list.
+constexpr int kMaxSrc = 64;
+
+template <typename T> struct SrcTab {
+    const int32_t *sj, *si;   // shared memory, n_s entries
+    const T *sv;
+    int n_s;
+    int lo_g, hi_g;           // entries of the global list that were not staged
+    int64_t srow;             // misfit row of state n
+};
+
+// Sources on row j of this thread's columns: each sensor there adds 2 r to
+// alpha and 2 r dt to m.
 template <typename T, int N>
-__device__ __forceinline__ void add_sources(const AdjArgs<T> &a, int lo, int hi, int64_t srow, int x0, int j,
-                                            Row<T, N> &anew, Row<T, N> &mnew)
+__device__ __forceinline__ void add_sources(const AdjArgs<T> &a, const SrcTab<T> &S, int x0, int j, Row<T, N> &anew,
+                                            Row<T, N> &mnew)
 {
-    for (int q = lo; q < hi; ++q) {
+    for (int q = 0; q < S.n_s; ++q) {
+        if (S.sj[q] != j) continue;
+        const int di = S.si[q] - x0;
+        if (di < 0 || di >= N) continue;
+        const T v = S.sv[q];
+#pragma unroll
+        for (int kk = 0; kk < N; ++kk)
+            if (kk == di) {
+                anew.v[kk] += v;
+                mnew.v[kk] += a.dt * v;
+            }
+    }
+    const int64_t srow = S.srow;
+    for (int q = S.lo_g; q < S.hi_g; ++q) {
         const int k = a.s_ent[q];
         if (a.s_j[k] != j) continue;
         const int di = a.s_i[k] - x0;
@@ -69,30 +95,38 @@ __device__ __forceinline__ void add_sources(const AdjArgs<T> &a, int lo, int hi,
     }
 }
 
-// Sums of m along the four edges over this thread's sites of row j (FP64).
-template <typename T, int N>
-__device__ __forceinline__ void edge_sums(int nx, int ny, int x0, int j, const Row<T, N> &m, double (&es)[4])
+// Sums of m (the input plane) along the Dirichlet edges that this CTA
+// touches, over its own sites, in FP64: the thread's columns of row 0 /
+// ny - 1, and rows j0 .. j1-1 of column 0 / nx - 1.  Read back after the
+// march (the input plane is not written during the step), so that no
+// accumulator lives through the row loop.
+template <typename T>
+__device__ __forceinline__ void edge_sums(const AdjArgs<T> &a, int x0, int j0, int j1, bool on_t, bool on_b, bool on_l,
+                                          bool on_r, double (&es)[4])
 {
-    if (j == ny - 1 || j == 0) {
+    constexpr int N = Vec<T>::N;
+    const int64_t P = a.pitch;
+    const int nx = a.nx;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) es[e] = 0.0;
+    if (on_t || on_b) {
+        const T *row = a.w_in + (on_t ? (int64_t)(a.ny - 1) * P : 0) + x0;
         double s = 0.0;
 #pragma unroll
         for (int k = 0; k < N; ++k)
-            if (x0 + k < nx) s += (double)m.v[k];
-        if (j == ny - 1) es[TOP] += s;
-        if (j == 0) es[BOTTOM] += s;
+            if (x0 + k < nx) s += (double)row[k];
+        es[on_t ? TOP : BOTTOM] = s;
     }
-    if (x0 == 0) es[LEFT] += (double)m.v[0];
-    const int kr = nx - 1 - x0;
-#pragma unroll
-    for (int k = 0; k < N; ++k)
-        if (k == kr) es[RIGHT] += (double)m.v[k];
+    if (on_l && x0 == 0)
+        for (int j = j0; j < j1; ++j) es[LEFT] += (double)a.w_in[(int64_t)j * P];
+    if (on_r && x0 <= nx - 1 && nx - 1 < x0 + N)
+        for (int j = j0; j < j1; ++j) es[RIGHT] += (double)a.w_in[(int64_t)j * P + nx - 1];
 }
 
-// The bulk rows: the forward march with zero Dirichlet values, sources
-// (SRC) and edge sums (EDGE).
+// The bulk rows: the forward march with zero Dirichlet values and the
+// sources (SRC).
 template <typename T, bool EDGE, bool SRC>
-__device__ __forceinline__ void adj_march(const AdjArgs<T> &a, int cb, int j0, int j1, int lo, int hi, int64_t srow,
-                                          double (&es)[4], T &acc)
+__device__ __forceinline__ void adj_march(const AdjArgs<T> &a, int cb, int j0, int j1, const SrcTab<T> &S, T &acc)
 {
     constexpr int N = Vec<T>::N;
     typedef Row<T, N> R;
@@ -131,9 +165,8 @@ __device__ __forceinline__ void adj_march(const AdjArgs<T> &a, int cb, int j0, i
         if (lane == 31) rightN = hr;
         R mnew, anew;
         if (EDGE) {
-            edge_sums<T, N>(a.nx, a.ny, x0, j, mc, es);
             row_update(a, E, x0, j, mc, ma, mb, av, left0, rightN, 0u, 0u, mnew, anew);
-            if (SRC) add_sources<T, N>(a, lo, hi, srow, x0, j, anew, mnew);
+            if (SRC) add_sources<T, N>(a, S, x0, j, anew, mnew);
             if (x0 < a.nx) {
                 store_row(a, x0, j, mnew, anew, acc);
                 write_pads(a, x0, j, mnew);
@@ -147,7 +180,7 @@ __device__ __forceinline__ void adj_march(const AdjArgs<T> &a, int cb, int j0, i
                 anew.v[k] = av.v[k] + g * lap;
                 mnew.v[k] = mc.v[k] + dt * anew.v[k];
             }
-            if (SRC) add_sources<T, N>(a, lo, hi, srow, x0, j, anew, mnew);
+            if (SRC) add_sources<T, N>(a, S, x0, j, anew, mnew);
             stg_row(mout + (int64_t)j * P, mnew);
             stg_row(ap + (int64_t)j * P, anew);
             acc += mnew.v[0];
@@ -168,18 +201,20 @@ __device__ __forceinline__ void adj_march(const AdjArgs<T> &a, int cb, int j0, i
 // sources, then the crack-face correction for the columns severed in step
 // n - 1 (i_first .. il_p), all from registers.  Out of line (its register
 // demand would otherwise be the whole kernel's), with the arguments in shared
-// memory; returns the edge sums and the finiteness probe.
-template <typename T> struct CrackSums {
-    double es[4];
-    T acc;
-};
-
+// memory; returns the finiteness probe.
 template <typename T, int HH>
-__device__ __noinline__ CrackSums<T> adj_crack_rows(const AdjArgs<T> *sa, int cb, int j0, int il_n, int il_p, int lo,
-                                                    int hi, int64_t srow)
+__device__ __noinline__ T adj_crack_rows(const AdjArgs<T> *sa, int cb, int j0, int il_n, int il_p, const int32_t *ssj,
+                                         const int32_t *ssi, const T *ssv, int n_s, int lo_g, int hi_g, int64_t srow)
 {
     const AdjArgs<T> &a = *sa;
-    double es[4] = {0.0, 0.0, 0.0, 0.0};
+    SrcTab<T> S;
+    S.sj = ssj;
+    S.si = ssi;
+    S.sv = ssv;
+    S.n_s = n_s;
+    S.lo_g = lo_g;
+    S.hi_g = hi_g;
+    S.srow = srow;
     T acc = (T)0;
     constexpr int N = Vec<T>::N;
     typedef Row<T, N> R;
@@ -215,9 +250,8 @@ __device__ __noinline__ CrackSums<T> adj_crack_rows(const AdjArgs<T> *sa, int cb
         if (lane == 31) rightN = hr[q];
         const uint32_t cut_up = (below && j == jc - 1) ? cut_n : 0u;
         const uint32_t cut_dn = (!below && j == jc) ? cut_n : 0u;
-        edge_sums<T, N>(a.nx, a.ny, x0, j, m[q + 1], es);
         row_update(a, E, x0, j, m[q + 1], m[q + 2], m[q], av[q], left0, rightN, cut_up, cut_dn, o[q], od[q]);
-        add_sources<T, N>(a, lo, hi, srow, x0, j, od[q], o[q]);
+        add_sources<T, N>(a, S, x0, j, od[q], o[q]);
     }
     if (HH >= 3 && a.macro && cut_p) {
         const int qb = below ? HH - 1 : 0, qi = below ? HH - 2 : 1, qii = below ? HH - 3 : 2;
@@ -241,15 +275,12 @@ __device__ __noinline__ CrackSums<T> adj_crack_rows(const AdjArgs<T> *sa, int cb
             write_pads(a, x0, j0 + q, o[q]);
         }
     }
-    CrackSums<T> r;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) r.es[e] = es[e];
-    r.acc = acc;
-    return r;
+    return acc;
 }
 
 template <typename T>
-__device__ __forceinline__ void adjoint_cta(const AdjArgs<T> &a, int cb, int band, double *sred, AdjArgs<T> *sa)
+__device__ __forceinline__ void adjoint_cta(const AdjArgs<T> &a, int cb, int band, double *sred, AdjArgs<T> *sa,
+                                            int32_t *ssj, int32_t *ssi, T *ssv)
 {
     const unsigned kFull = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -266,7 +297,25 @@ __device__ __forceinline__ void adjoint_cta(const AdjArgs<T> &a, int cb, int ban
         hi = a.s_off[u + 1];
         srow = (n - 1) % a.ring;
     }
-    double es[4];
+    // stage this CTA's sources (the count is the same for all its threads)
+    const int n_s = min(hi - lo, kMaxSrc);
+    if (n_s > 0) {
+        for (int q = tid; q < n_s; q += kThreads) {
+            const int k = a.s_ent[lo + q];
+            ssj[q] = a.s_j[k];
+            ssi[q] = a.s_i[k];
+            ssv[q] = (T)(2.0 * a.resid[srow * a.ns + k]);
+        }
+        __syncthreads();
+    }
+    SrcTab<T> S;
+    S.sj = ssj;
+    S.si = ssi;
+    S.sv = ssv;
+    S.n_s = n_s;
+    S.lo_g = lo + n_s;
+    S.hi_g = hi;
+    S.srow = srow;
     T acc;
     if (a.crack_band >= 0 && (band == a.crack_band || band == a.crack_band + 1)) {
         const int il_n = a.i_last[n < a.n_steps ? n : a.n_steps - 1];
@@ -275,23 +324,18 @@ __device__ __forceinline__ void adjoint_cta(const AdjArgs<T> &a, int cb, int ban
         uint32_t *dst = reinterpret_cast<uint32_t *>(sa);
         for (int q = tid; q < (int)(sizeof(AdjArgs<T>) / 4); q += kThreads) dst[q] = src[q];
         __syncthreads();
-        const CrackSums<T> r = a.macro ? adj_crack_rows<T, 3>(sa, cb, j0, il_n, il_p, lo, hi, srow)
-                                       : adj_crack_rows<T, 1>(sa, cb, j0, il_n, il_p, lo, hi, srow);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) es[e] = r.es[e];
-        acc = r.acc;
+        acc = a.macro ? adj_crack_rows<T, 3>(sa, cb, j0, il_n, il_p, ssj, ssi, ssv, n_s, lo + n_s, hi, srow)
+                      : adj_crack_rows<T, 1>(sa, cb, j0, il_n, il_p, ssj, ssi, ssv, n_s, lo + n_s, hi, srow);
     } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) es[e] = 0.0;
         acc = (T)0;
         const bool edge = (cb == 0) | (cb == a.ncb - 1) | (j0 == 0) | (j1 == a.ny);
         const bool src = lo < hi;
         if (edge) {
-            if (src) adj_march<T, true, true>(a, cb, j0, j1, lo, hi, srow, es, acc);
-            else adj_march<T, true, false>(a, cb, j0, j1, lo, hi, srow, es, acc);
+            if (src) adj_march<T, true, true>(a, cb, j0, j1, S, acc);
+            else adj_march<T, true, false>(a, cb, j0, j1, S, acc);
         } else {
-            if (src) adj_march<T, false, true>(a, cb, j0, j1, lo, hi, srow, es, acc);
-            else adj_march<T, false, false>(a, cb, j0, j1, lo, hi, srow, es, acc);
+            if (src) adj_march<T, false, true>(a, cb, j0, j1, S, acc);
+            else adj_march<T, false, false>(a, cb, j0, j1, S, acc);
         }
     }
     if (__any_sync(kFull, !isfinite(acc)) && lane == 0) atomicOr(a.err, (uint32_t)ERR_NONFINITE);
@@ -301,6 +345,8 @@ __device__ __forceinline__ void adjoint_cta(const AdjArgs<T> &a, int cb, int ban
     const bool on_l = cb == 0 && a.edge[LEFT] == EDGE_DIRICHLET;
     const bool on_r = cb == a.ncb - 1 && a.edge[RIGHT] == EDGE_DIRICHLET;
     if ((on_t | on_b | on_l | on_r) && n < a.n_steps) {
+        double es[4];
+        edge_sums<T>(a, (cb * kThreads + tid) * Vec<T>::N, j0, j1, on_t, on_b, on_l, on_r, es);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             double v = es[e];
@@ -330,7 +376,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
 {
     __shared__ double sred[4 * (kThreads / 32)];
     __shared__ __align__(16) AdjArgs<T> sa;
-    adjoint_cta<T>(a, blockIdx.x, blockIdx.y, sred, &sa);
+    __shared__ int32_t ssj[kMaxSrc], ssi[kMaxSrc];
+    __shared__ T ssv[kMaxSrc];
+    adjoint_cta<T>(a, blockIdx.x, blockIdx.y, sred, &sa, ssj, ssi, ssv);
 }
 
 template <typename T> const void *adjoint_kernel_ptr()

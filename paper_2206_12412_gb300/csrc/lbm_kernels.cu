@@ -427,18 +427,17 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
         // the sensors this CTA owns: misfit of the new state (its own stores
         // are visible to the CTA after the barrier)
         __syncthreads();
-        if (tid == 0) {
-            const int64_t t = a.s_in->step - *r.n0;
-            if (t >= 0 && t < r.n_steps) {
-                const int u = band * a.ncb + cb;
-                const int lo = r.s_off[u], hi = r.s_off[u + 1];
-                for (int q = lo; q < hi; ++q) {
-                    const int k = r.s_ent[q];
-                    const double wv = (double)a.w_out[(int64_t)r.s_j[k] * a.pitch + r.s_i[k]];
-                    const double res = wv - r.target[t * r.ns + k];
-                    r.resid[(t % r.ring) * r.ns + k] = res;
-                    if (r.acc_loss) r.loss[k] += res * res;
-                }
+        const int64_t t = a.s_in->step - *r.n0;
+        if (t >= 0 && t < r.n_steps) {
+            // one thread per sensor of the list (each sensor appears once)
+            const int u = band * a.ncb + cb;
+            const int lo = r.s_off[u], hi = r.s_off[u + 1];
+            for (int q = lo + tid; q < hi; q += kThreads) {
+                const int k = r.s_ent[q];
+                const double wv = (double)a.w_out[(int64_t)r.s_j[k] * a.pitch + r.s_i[k]];
+                const double res = wv - r.target[t * r.ns + k];
+                r.resid[(t % r.ring) * r.ns + k] = res;
+                if (r.acc_loss) r.loss[k] += res * res;
             }
         }
     }

@@ -149,13 +149,15 @@ def gp_series(n: int, length: float, sigma: float, seed: int) -> np.ndarray:
     """Smooth random series of n samples: white noise filtered in the
     frequency domain by the square root of a squared-exponential spectrum of
     correlation length `length` (samples), scaled to standard deviation
-    sigma.  FP64."""
+    sigma over a draw of at least 8 correlation lengths (of which the first n
+    samples are returned).  FP64."""
     rng = np.random.default_rng(seed)
-    z = rng.standard_normal(n)
-    f = np.fft.rfftfreq(n)
+    m = max(int(n), int(np.ceil(8 * length)))   # at least 8 correlation lengths, so the scale is well defined
+    z = rng.standard_normal(m)
+    f = np.fft.rfftfreq(m)
     filt = np.exp(-(np.pi * length * f) ** 2)   # sqrt of exp(-2 pi^2 l^2 f^2)
-    x = np.fft.irfft(np.fft.rfft(z) * filt, n)
-    return sigma * x / max(float(np.std(x)), 1e-300)
+    x = np.fft.irfft(np.fft.rfft(z) * filt, m)
+    return (sigma * x / max(float(np.std(x)), 1e-300))[: int(n)]
 
 
 def sensor_sites(nx: int, ny: int, ns: int, seed: int, jc: int | None = None, margin: int = 2) -> np.ndarray:
