@@ -51,6 +51,22 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def reduce_max(pg, x: float, device="cpu") -> float:
+    """Max of x over the ranks of the process group (x itself without one)."""
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world: int, units_per_rank: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput in G units per second: every rank advances its own
+    replica (weak scaling), timed by the slowest rank."""
+    return world * units_per_rank * steps / seconds / 1e9
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -283,6 +299,27 @@ def measure_adjoint(lbm, W, torch, stream, n_steps=None):
     return out
 
 
+def measure_virtual_ranks(lbm, W, torch, stream, problem, steps=256):
+    """The benchmark lattice split into 1, 2, 4 and 8 row slabs on this GPU
+    (one batched step launch plus one halo-row exchange launch per step),
+    timed back to back (graph replay, no flush) against the undivided
+    lattice's graph replay."""
+    sites = problem["nx"] * problem["ny"]
+    out = {"timing": "CUDA events around graph replay of the steps, no flush", "steps": steps, "glups": {}}
+    for n in (1, 2, 4, 8):
+        d = lbm.Decomp(problem, n, "f32", stream=stream)
+        d.step(64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out["glups"][str(n)] = sites * steps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+        d.close()
+    return out
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
@@ -301,11 +338,7 @@ def run_ours(args, rank, world, local):
             pg.barrier()
 
     def allmax(x: float) -> float:
-        if pg is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(pg, x, "cuda")
 
     problem = W.kcrit_single()
     sites = problem["nx"] * problem["ny"]
@@ -357,7 +390,7 @@ def run_ours(args, rank, world, local):
     clk = clocks.stop()
     step_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     total_s = allmax(step_ms * 1e-3)
-    value = world * sites * args.steps / total_s / 1e9
+    value = replica_value(world, sites, args.steps, total_s)
 
     # the step kernel alone, timed by the library's events on the same stream
     lat.set_profiling(True)
@@ -390,6 +423,7 @@ def run_ours(args, rank, world, local):
 
     batched = measure_batched(lbm, W, torch, stream, 128, peak) if not args.no_batched else None
     adjoint = measure_adjoint(lbm, W, torch, stream) if not args.no_adjoint else None
+    vranks = measure_virtual_ranks(lbm, W, torch, stream, problem) if not args.no_virtual_ranks else None
 
     # steady back-to-back replay (CUDA graph, no flush): context only
     lat.sync()
@@ -444,6 +478,7 @@ def run_ours(args, rank, world, local):
         "mixed_precision": mixed,
         "batched": batched,
         "adjoint": adjoint,
+        "virtual_ranks": vranks,
         "wall_s": wall,
         "clocks": clk,
     }
@@ -467,6 +502,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-lattice batched measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the sensor-misfit gradient measurement")
+    ap.add_argument("--no-virtual-ranks", action="store_true", help="skip the row-slab decomposition measurement")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="only the sensor-misfit gradient measurement (for ncu)")
     ap.add_argument("--adjoint-steps", type=int, default=None, help="steps of the adjoint workload (default 8000)")

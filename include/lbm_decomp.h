@@ -1,0 +1,76 @@
+/*
+ * lbm_decomp.h -- a lattice split into row slabs ("virtual ranks") on one
+ * GPU, each slab its own lattice, with the halo rows exchanged after every
+ * step.
+ *
+ * The time step of Sec. 3 reads, at each site, only the four neighbours' w
+ * (the moment form), so a lattice split into slabs of whole rows needs, per
+ * step and per inner boundary, one row of w from each side: each slab keeps
+ * its neighbour's boundary row in its pad row beyond the boundary.  The
+ * crack's rows (the sub-bands jc-3 .. jc+2 with the macroscopic crack-face
+ * rule of Sec. 3.1, jc-1 and jc with bounce-back) lie inside one slab, which
+ * runs the crack step of Alg. 1 for the whole lattice; the site pairs of the
+ * K_III fit (eq. sif) and the severed links are all there, so no other data
+ * crosses a boundary.  A decomposed run is bit-identical to the undivided
+ * one.  The paper runs on one process; this layout is the way the method
+ * shards over devices, kept on one device here (one batched launch and one
+ * row-exchange launch per step).  Conventions are those of lbm.h.
+ */
+#ifndef LBM_DECOMP_H
+#define LBM_DECOMP_H
+
+#include "lbm.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_decomp lbm_decomp;
+
+/* Row starts of a split of ny rows into n_ranks slabs: near-even slabs of at
+ * least 2 rows whose boundaries avoid the crack rows [jc - hh, jc + hh)
+ * (a boundary that falls strictly inside moves to the nearer end); jc < 0
+ * means no crack.  hh = 3 with macroscopic crack faces, 1 with bounce-back.
+ * Writes n_ranks + 1 values (0 first, ny last) to row_start (host memory).
+ * LBM_ERR_ARG if no such split exists.  Host-only; touches no device. */
+lbm_status lbm_decomp_plan(int32_t ny, int32_t jc, int32_t hh, int32_t n_ranks, int32_t *row_start);
+
+/* Build the lattice of lbm_create as n_ranks slabs (arguments as for
+ * lbm_create; storage any).  row_start: n_ranks + 1 ascending row indices
+ * from 0 to ny with every slab at least 2 rows and the crack rows inside one
+ * slab, or NULL for lbm_decomp_plan's split.  Slab r holds rows row_start[r]
+ * .. row_start[r+1]-1; its inner bottom/top edges are halo edges, its other
+ * edges and loads those of the lattice; with FP16 wdot storage every slab
+ * takes the scale the undivided lattice would.  LBM_ERR_ARG for bad input. */
+lbm_status lbm_decomp_create(const lbm_grid *grid, const lbm_lattice *lattice, const lbm_material *material,
+                             const lbm_crack *crack, const lbm_loading *loads, int32_t n_loads, int32_t n_ranks,
+                             const int32_t *row_start, void *stream, const lbm_allocator *allocator,
+                             lbm_decomp **out);
+
+/* Enqueue n >= 0 time steps of every slab plus the halo exchange after each
+ * (CUDA-graph replay of 64-step chunks). */
+lbm_status lbm_decomp_step(lbm_decomp *d, int64_t n);
+
+/* Field `which` of the whole lattice as a dense ny x nx array (gathered from
+ * the slabs), as lbm_fields. */
+lbm_status lbm_decomp_fields(lbm_decomp *d, int32_t which, void *dst, int32_t dst_on_device, int32_t dtype);
+
+/* Overwrite field `which` of the whole lattice from a dense ny x nx array
+ * (scattered to the slabs, halo rows refreshed), as lbm_set_fields. */
+lbm_status lbm_decomp_set_fields(lbm_decomp *d, int32_t which, const void *src, int32_t src_on_device, int32_t dtype);
+
+/* Slab r: its handle (owned by the decomposition: read it -- fields, crack
+ * state, masks -- but do not step it, re-launch it or destroy it), its first
+ * row and its row count (any pointer may be NULL).  crack_rank receives the
+ * slab that holds the crack (-1 without a crack). */
+lbm_status lbm_decomp_rank(const lbm_decomp *d, int32_t rank, lbm_handle **slab, int32_t *row0, int32_t *rows);
+lbm_status lbm_decomp_info(const lbm_decomp *d, int32_t *n_ranks, int32_t *crack_rank);
+
+/* Release the slabs and the decomposition (NULL is ignored). */
+void lbm_decomp_destroy(lbm_decomp *d);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_DECOMP_H */

@@ -1,5 +1,5 @@
-"""ctypes mirror of include/lbm.h and include/lbm_adjoint.h (structs,
-constants, prototypes)."""
+"""ctypes mirror of include/lbm.h, include/lbm_adjoint.h and
+include/lbm_decomp.h (structs, constants, prototypes)."""
 from __future__ import annotations
 
 import ctypes as C
@@ -103,4 +103,16 @@ PROTOTYPES = {
                                     C.c_int32]),
     "lbm_tape_misfits": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "lbm_tape_destroy": (None, [C.c_void_p]),
+    # include/lbm_decomp.h
+    "lbm_decomp_plan": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_int32)]),
+    "lbm_decomp_create": (C.c_int, [C.POINTER(Grid), C.POINTER(Lattice_), C.POINTER(Material), C.POINTER(Crack),
+                                    C.POINTER(Loading), C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.c_void_p,
+                                    C.POINTER(Allocator), C.POINTER(C.c_void_p)]),
+    "lbm_decomp_step": (C.c_int, [C.c_void_p, C.c_int64]),
+    "lbm_decomp_fields": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int32]),
+    "lbm_decomp_set_fields": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int32]),
+    "lbm_decomp_rank": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p), C.POINTER(C.c_int32),
+                                  C.POINTER(C.c_int32)]),
+    "lbm_decomp_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "lbm_decomp_destroy": (None, [C.c_void_p]),
 }

@@ -306,6 +306,18 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lb
                       const lbm_crack *crack, const lbm_loading *loads, int32_t n_loads,
                       void *stream, const lbm_allocator *allocator, lbm_handle **out)
 {
+    return create_impl(grid, lattice, material, crack, loads, n_loads, stream, allocator, false, out);
+}
+
+}  // extern "C"
+
+namespace lbm {
+namespace host {
+
+lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const lbm_material *material,
+                       const lbm_crack *crack, const lbm_loading *loads, int32_t n_loads, void *stream,
+                       const lbm_allocator *allocator, bool slab, lbm_handle **out)
+{
     if (!out) return fail(LBM_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!grid || !lattice || !material) return fail(LBM_ERR_ARG, "grid, lattice and material are required");
@@ -314,7 +326,8 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lb
     if (!(grid->dh > 0.0) || !(grid->dt > 0.0) || !std::isfinite(grid->dh) || !std::isfinite(grid->dt))
         return fail(LBM_ERR_ARG, "dh and dt must be positive and finite");
     for (int e = 0; e < 4; ++e)
-        if (grid->edge[e] < LBM_EDGE_FREE || grid->edge[e] > LBM_EDGE_PERIODIC)
+        if (grid->edge[e] < LBM_EDGE_FREE ||
+            grid->edge[e] > (slab && (e == LBM_BOTTOM || e == LBM_TOP) ? (int)EDGE_HALO : LBM_EDGE_PERIODIC))
             return fail(LBM_ERR_ARG, "unknown edge kind");
     if ((grid->edge[LBM_LEFT] == LBM_EDGE_PERIODIC) != (grid->edge[LBM_RIGHT] == LBM_EDGE_PERIODIC) ||
         (grid->edge[LBM_BOTTOM] == LBM_EDGE_PERIODIC) != (grid->edge[LBM_TOP] == LBM_EDGE_PERIODIC))
@@ -576,6 +589,11 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lb
     clear_error();
     return LBM_OK;
 }
+
+}  // namespace host
+}  // namespace lbm
+
+extern "C" {
 
 lbm_status lbm_step(lbm_handle *h, int64_t n)
 {
@@ -1006,6 +1024,34 @@ cudaError_t enqueue_batch_step(const lbm_batch *b, int par, cudaStream_t s)
 }
 
 }  // namespace
+
+namespace lbm {
+namespace host {
+
+cudaError_t batch_enqueue(const lbm_batch *b, int par, cudaStream_t s) { return enqueue_batch_step(b, par, s); }
+
+int batch_parity(const lbm_batch *b) { return b->hs[0]->parity; }
+
+lbm_status batch_check(const lbm_batch *b)
+{
+    const int par0 = b->hs[0]->parity;
+    for (lbm_handle *h : b->hs) {
+        if (h->sticky != LBM_OK) return fail(h->sticky, "a lattice is in an error state");
+        if (h->parity != par0) return fail(LBM_ERR_STATE, "the lattices were stepped apart since the batch was made");
+    }
+    return LBM_OK;
+}
+
+void batch_mark_stepped(lbm_batch *b, int par, int64_t n)
+{
+    for (lbm_handle *h : b->hs) {
+        h->parity = par;
+        if (n > 0 && h->cp.mode != CRACK_NONE) h->pending = true;
+    }
+}
+
+}  // namespace host
+}  // namespace lbm
 
 extern "C" {
 

@@ -5,6 +5,8 @@
 #include "lbm.h"
 #include "lbm_internal.cuh"
 
+typedef struct lbm_batch lbm_batch;
+
 #include <string>
 #include <vector>
 
@@ -76,6 +78,12 @@ lbm_status cuda_fail(cudaError_t e, const char *what);
 void clear_error();
 const char *last_error();
 
+// lbm_create; with slab = true the bottom and top edges may also be
+// EDGE_HALO (inner edges of a row slab of a decomposed lattice).
+lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const lbm_material *material,
+                       const lbm_crack *crack, const lbm_loading *loads, int32_t n_loads, void *stream,
+                       const lbm_allocator *allocator, bool slab, lbm_handle **out);
+
 // Apply the pending crack step (if any) on the handle's stream.
 lbm_status finalize(lbm_handle *h);
 // Synchronise, then report sticky device errors.
@@ -108,6 +116,14 @@ inline void make_step_args(const lbm_handle *h, int par, StepArgs<T, D> &a)
     a.hist = h->hist;
 }
 
+// Batches (lbm_batch_*): enqueue one batched step reading parity `par`; the
+// common parity of the members; their state check; record n steps ending at
+// parity `par`.
+cudaError_t batch_enqueue(const lbm_batch *b, int par, cudaStream_t s);
+int batch_parity(const lbm_batch *b);
+lbm_status batch_check(const lbm_batch *b);
+void batch_mark_stepped(lbm_batch *b, int par, int64_t n);
+
 // Replays a fixed chunk of kernel launches that alternate between two
 // parities as a CUDA graph, captured on first use for the starting parity.
 struct ChunkGraph {
@@ -117,6 +133,8 @@ struct ChunkGraph {
     void reset();
 };
 
+constexpr int64_t kChunk = 64;   // launches per captured graph (even: parity is kept)
+
 }  // namespace host
 }  // namespace lbm
 
@@ -125,3 +143,51 @@ struct ChunkGraph {
         cudaError_t e_ = (call);                                        \
         if (e_ != cudaSuccess) return ::lbm::host::cuda_fail(e_, #call); \
     } while (0)
+
+namespace lbm {
+namespace host {
+
+// Launch n kernels that alternate between two parities, starting at `par`;
+// whole chunks replay a graph captured for the starting parity.
+template <typename F>
+inline lbm_status run_chunks(ChunkGraph &g, int64_t gen, cudaStream_t s, cudaStream_t cap, int64_t n, int &par, F &&enqueue)
+{
+    while (n > 0) {
+        if (n >= kChunk) {
+            if (g.exec && g.gen != gen) g.reset();
+            if (!g.exec) {
+                cudaGraph_t graph;
+                LBM_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+                cudaError_t ce = cudaSuccess;
+                int p = par;
+                for (int64_t q = 0; q < kChunk && ce == cudaSuccess; ++q) {
+                    ce = enqueue(p, cap);
+                    p ^= 1;
+                }
+                cudaError_t ee = cudaStreamEndCapture(cap, &graph);
+                if (ce != cudaSuccess) return cuda_fail(ce, "capturing a tape graph");
+                if (ee != cudaSuccess) return cuda_fail(ee, "cudaStreamEndCapture");
+                ee = cudaGraphInstantiate(&g.exec, graph, 0);
+                cudaGraphDestroy(graph);
+                if (ee != cudaSuccess) {
+                    g.exec = nullptr;
+                    return cuda_fail(ee, "cudaGraphInstantiate");
+                }
+                g.parity = par;
+                g.gen = gen;
+            }
+            if (g.parity == par) {
+                LBM_CUDA(cudaGraphLaunch(g.exec, s));
+                n -= kChunk;
+                continue;
+            }
+        }
+        LBM_CUDA(enqueue(par, s));
+        par ^= 1;
+        n -= 1;
+    }
+    return LBM_OK;
+}
+
+}  // namespace host
+}  // namespace lbm

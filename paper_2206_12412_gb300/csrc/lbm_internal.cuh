@@ -34,7 +34,10 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr int kThreads = 128;                       // threads per CTA of the step kernel
 constexpr int kMinBlocks = 8;                       // resident CTAs per SM the kernel is built for
 
-enum { EDGE_FREE = 0, EDGE_DIRICHLET = 1, EDGE_PERIODIC = 2 };
+// EDGE_HALO: an inner edge of a row slab of a decomposed lattice; the pad
+// row beyond it holds the neighbouring slab's boundary row, copied there
+// after every step, and is otherwise read like any neighbour row.
+enum { EDGE_FREE = 0, EDGE_DIRICHLET = 1, EDGE_PERIODIC = 2, EDGE_HALO = 3 };
 enum { LEFT = 0, RIGHT = 1, BOTTOM = 2, TOP = 3 };
 enum { CRACK_NONE = 0, CRACK_STATIONARY = 1, CRACK_PRESCRIBED = 2, CRACK_KCRIT = 3 };
 enum { LOAD_ZERO = 0, LOAD_LINEAR = 1, LOAD_SIN2 = 2, LOAD_HALFSINE = 3, LOAD_SERIES = 4, LOAD_CONST = 5 };
@@ -169,6 +172,12 @@ struct AdjArgs {
     int32_t slots, pad;
 };
 
+// One row copy of the halo exchange between row slabs (whole padded rows).
+struct RowCopy {
+    const void *src;
+    void *dst;
+};
+
 template <typename T, typename D> const void *step_kernel_ptr();
 template <typename T, typename D>
 cudaError_t launch_batch_step(const StepArgs<T, D> *descs, const BatchUnit *units, int n_units, int par, cudaStream_t s);
@@ -186,6 +195,7 @@ cudaError_t launch_wd_to_f32(const D *wd, int64_t pitch, int nx, int ny, float s
 template <typename D>
 cudaError_t launch_wd_from_f32(D *wd, int64_t pitch, int nx, int ny, float scale, const float *src, cudaStream_t s);
 template <typename T> cudaError_t launch_finalize(const FinalizeArgs<T> &a, cudaStream_t s);
+cudaError_t launch_exchange(const RowCopy *pairs, int n_pairs, int64_t row_bytes, cudaStream_t s);
 cudaError_t launch_wstar(CrackState *st, const LoadDesc *load, const int32_t *edge, double dt, cudaStream_t s);
 template <typename T> cudaError_t launch_fill_pads(T *w, int64_t pitch, int nx, int ny, const int32_t *edge, cudaStream_t s);
 

@@ -559,6 +559,27 @@ cudaError_t launch_finalize(const FinalizeArgs<T> &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------- halo exchange
+
+// Row slabs of a decomposed lattice: after each step, each boundary row of a
+// slab is copied into the halo row of its neighbour (CTA q copies pair q,
+// 16 bytes per thread per iteration; rows are 128-byte aligned and a whole
+// number of 16-byte words long).
+__global__ void exchange_kernel(const RowCopy *pairs, int64_t words)
+{
+    const RowCopy c = pairs[blockIdx.x];
+    const uint4 *src = static_cast<const uint4 *>(c.src);
+    uint4 *dst = static_cast<uint4 *>(c.dst);
+    for (int64_t q = threadIdx.x; q < words; q += blockDim.x) dst[q] = src[q];
+}
+
+cudaError_t launch_exchange(const RowCopy *pairs, int n_pairs, int64_t row_bytes, cudaStream_t s)
+{
+    if (n_pairs <= 0) return cudaSuccess;
+    exchange_kernel<<<(unsigned)n_pairs, 256, 0, s>>>(pairs, row_bytes / 16);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------- initial w*(t_0)
 
 struct WstarArgs {

@@ -16,8 +16,6 @@ using namespace lbm::host;
 
 namespace {
 
-constexpr int64_t kChunk = 64;   // launches per captured graph (even: parity is kept)
-
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
@@ -58,48 +56,6 @@ struct lbm_tape {
 };
 
 namespace {
-
-// Launch n kernels that alternate between two parities, starting at `par`;
-// whole chunks replay a graph captured for the starting parity.
-template <typename F>
-lbm_status run_chunks(ChunkGraph &g, int64_t gen, cudaStream_t s, cudaStream_t cap, int64_t n, int &par, F &&enqueue)
-{
-    while (n > 0) {
-        if (n >= kChunk) {
-            if (g.exec && g.gen != gen) g.reset();
-            if (!g.exec) {
-                cudaGraph_t graph;
-                LBM_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-                cudaError_t ce = cudaSuccess;
-                int p = par;
-                for (int64_t q = 0; q < kChunk && ce == cudaSuccess; ++q) {
-                    ce = enqueue(p, cap);
-                    p ^= 1;
-                }
-                cudaError_t ee = cudaStreamEndCapture(cap, &graph);
-                if (ce != cudaSuccess) return cuda_fail(ce, "capturing a tape graph");
-                if (ee != cudaSuccess) return cuda_fail(ee, "cudaStreamEndCapture");
-                ee = cudaGraphInstantiate(&g.exec, graph, 0);
-                cudaGraphDestroy(graph);
-                if (ee != cudaSuccess) {
-                    g.exec = nullptr;
-                    return cuda_fail(ee, "cudaGraphInstantiate");
-                }
-                g.parity = par;
-                g.gen = gen;
-            }
-            if (g.parity == par) {
-                LBM_CUDA(cudaGraphLaunch(g.exec, s));
-                n -= kChunk;
-                continue;
-            }
-        }
-        LBM_CUDA(enqueue(par, s));
-        par ^= 1;
-        n -= 1;
-    }
-    return LBM_OK;
-}
 
 RecArgs rec_args(const lbm_tape *t, int acc_loss)
 {

@@ -584,3 +584,107 @@ class _Lazy:
 
 
 _SensorMisfit = _Lazy()
+
+
+# ----------------------------------------------------- row-slab decomposition
+
+def lbm_decomp_plan(ny: int, jc: int, hh: int, n_ranks: int) -> list:
+    """Row starts of lbm_decomp_plan's split (host only)."""
+    out = (C.c_int32 * (n_ranks + 1))()
+    _check(load_library().lbm_decomp_plan(int(ny), int(jc), int(hh), int(n_ranks), out))
+    return list(out)
+
+
+class SlabView:
+    """Read-only view of one slab's handle (fields, crack state, masks)."""
+
+    def __init__(self, h: int, problem: dict, storage: str, row0: int, rows: int):
+        import torch
+        self.torch = torch
+        self.h = h
+        self.problem = problem
+        self.storage = storage
+        self.row0, self.ny, self.nx = row0, rows, int(problem["nx"])
+        self.np_dtype = np.float64 if storage == "f64" else np.float32
+
+    fields = Lattice.fields
+    cut_mask = Lattice.cut_mask
+    crack_state = Lattice.crack_state
+    history = Lattice.history
+    dtype_code = Lattice.dtype_code
+
+
+class Decomp:
+    """A lattice split into row slabs on one GPU (include/lbm_decomp.h):
+    one batched step launch and one halo-exchange launch per step, results
+    bit-identical to the undivided Lattice."""
+
+    def __init__(self, problem: dict, n_ranks: int, storage: str = "f32", row_start=None, stream=None,
+                 torch_allocator: bool = True):
+        import torch
+        self.torch = torch
+        self.problem = problem
+        self.storage = storage
+        self.nx, self.ny = int(problem["nx"]), int(problem["ny"])
+        self.np_dtype = np.float64 if storage == "f64" else np.float32
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+        g, lat, mat, cr, loads, keep = make_structs(problem, storage)
+        self._alloc = TorchAllocator(self.stream) if torch_allocator else None
+        arr = (A.Loading * max(len(loads), 1))(*loads)
+        rs = None
+        if row_start is not None:
+            rs = (C.c_int32 * (n_ranks + 1))(*[int(x) for x in row_start])
+        out = C.c_void_p()
+        _check(load_library().lbm_decomp_create(C.byref(g), C.byref(lat), C.byref(mat), C.byref(cr) if cr.mode else None,
+                                                arr if loads else None, len(loads), int(n_ranks), rs,
+                                                C.c_void_p(self.stream),
+                                                C.byref(self._alloc.struct) if self._alloc else None, C.byref(out)))
+        self.d = out.value
+        del keep
+
+    @property
+    def dtype_code(self) -> int:
+        return A.STORAGE["f64"] if self.storage == "f64" else A.STORAGE["f32"]
+
+    def step(self, n: int = 1):
+        _check(load_library().lbm_decomp_step(C.c_void_p(self.d), int(n)))
+
+    def set_fields(self, w=None, wdot=None):
+        for which, arr in (("w", w), ("wdot", wdot)):
+            if arr is None:
+                continue
+            a = np.ascontiguousarray(np.asarray(arr, dtype=self.np_dtype).reshape(self.ny, self.nx))
+            _check(load_library().lbm_decomp_set_fields(C.c_void_p(self.d), A.FIELD[which], C.c_void_p(a.ctypes.data),
+                                                        0, self.dtype_code))
+
+    def fields(self):
+        out = []
+        for which in ("w", "wdot"):
+            a = np.empty((self.ny, self.nx), self.np_dtype)
+            _check(load_library().lbm_decomp_fields(C.c_void_p(self.d), A.FIELD[which], C.c_void_p(a.ctypes.data), 0,
+                                                    self.dtype_code))
+            out.append(a)
+        return tuple(out)
+
+    def info(self) -> dict:
+        n, c = C.c_int32(), C.c_int32()
+        _check(load_library().lbm_decomp_info(C.c_void_p(self.d), C.byref(n), C.byref(c)))
+        return {"n_ranks": n.value, "crack_rank": c.value}
+
+    def rank(self, r: int) -> SlabView:
+        h, row0, rows = C.c_void_p(), C.c_int32(), C.c_int32()
+        _check(load_library().lbm_decomp_rank(C.c_void_p(self.d), int(r), C.byref(h), C.byref(row0), C.byref(rows)))
+        return SlabView(h.value, self.problem, self.storage, row0.value, rows.value)
+
+    def close(self):
+        if getattr(self, "d", None):
+            load_library().lbm_decomp_destroy(C.c_void_p(self.d))
+            self.d = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

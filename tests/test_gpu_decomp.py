@@ -1,0 +1,94 @@
+"""Row-slab decomposition (include/lbm_decomp.h): a lattice split into slabs
+with halo rows exchanged after every step gives the same bits as the
+undivided lattice -- fields, crack state, history and severed links."""
+import numpy as np
+import pytest
+
+from paper_2206_12412_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_12412_gb300 import lbm
+    lbm.load_library()
+    return lbm
+
+
+def _problem(kind: str):
+    if kind == "kcrit_macro":
+        p = W.base_problem(300, 96, bc_mode="macroscopic")
+        p = W.with_antisymmetric_ramp(p, 2e-3, 100.0)
+        K_C = 0.5 * W.strip_reference_K(0.25, 2e-3, 96.0)
+        return W.with_crack(p, mode="kcrit", y=48.0, x_tip=60.0, K_C=K_C, v_max=0.85, r0=2.0)
+    if kind == "prescribed_bb":
+        p = W.base_problem(530, 77, bc_mode="bounceback", edges=("dirichlet", "free", "dirichlet", "dirichlet"))
+        p = W.with_crack(p, mode="prescribed", y=30.0, x_start=4.0, x_tip=100.0, v_rel=0.5)
+        rng = np.random.default_rng(3)
+        for e in ("left", "bottom", "top"):
+            p = W.with_series_load(p, e, 1e-3 * rng.standard_normal(400))
+        return p
+    if kind == "periodic_y":
+        return W.base_problem(129, 64, edges=("free", "dirichlet", "periodic", "periodic"))
+    raise KeyError(kind)
+
+
+def _compare(gpu, p, storage, n_ranks, row_start=None, steps=(7, 64, 100)):
+    ref = gpu.Lattice(p, storage)
+    dec = gpu.Decomp(p, n_ranks, storage, row_start=row_start)
+    w0, wd0 = W.random_state(p["nx"], p["ny"], seed=n_ranks * 31 + p["ny"],
+                             dtype=np.float64 if storage == "f64" else np.float32)
+    ref.set_fields(w0, wd0)
+    dec.set_fields(w0, wd0)
+    for n in steps:
+        ref.step(n)
+        dec.step(n)
+        w_r, wd_r = ref.fields()
+        w_d, wd_d = dec.fields()
+        np.testing.assert_array_equal(w_d, w_r)
+        np.testing.assert_array_equal(wd_d, wd_r)
+    info = dec.info()
+    if info["crack_rank"] >= 0:
+        slab = dec.rank(info["crack_rank"])
+        assert slab.crack_state() == ref.crack_state()
+        hr, hd = ref.history(), slab.history()
+        for k in hr:
+            np.testing.assert_array_equal(hd[k], hr[k])
+        np.testing.assert_array_equal(slab.cut_mask("v"), ref.cut_mask("v")[slab.row0: slab.row0 + slab.ny])
+    dec.close()
+    ref.close()
+    return info
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+@pytest.mark.parametrize("n_ranks", [1, 2, 3, 5])
+def test_kcrit_growth_bit_identical(gpu, storage, n_ranks):
+    info = _compare(gpu, _problem("kcrit_macro"), storage, n_ranks)
+    assert info["n_ranks"] == n_ranks
+
+
+@pytest.mark.parametrize("row_start", [[0, 2, 77], [0, 27, 33, 77], [0, 29, 31, 40, 75, 77]])
+def test_uneven_slabs_with_loaded_edges(gpu, row_start):
+    """Bounce-back crack faces (crack rows 29 and 30), slabs ending right at
+    the crack rows, two-row slabs, all four edges loaded or free."""
+    _compare(gpu, _problem("prescribed_bb"), "f32", len(row_start) - 1, row_start=row_start)
+
+
+@pytest.mark.parametrize("n_ranks", [2, 4])
+def test_periodic_wrap_between_first_and_last_slab(gpu, n_ranks):
+    _compare(gpu, _problem("periodic_y"), "f64", n_ranks)
+
+
+def test_fp16_slabs_share_the_lattice_scale(gpu):
+    _compare(gpu, _problem("prescribed_bb"), "f32_f16", 3)
+
+
+def test_rejects_splits_through_the_crack_rows(gpu):
+    p = _problem("kcrit_macro")   # crack rows 45 .. 50 with macroscopic faces
+    for rs in ([0, 47, 96], [0, 48, 96], [0, 1, 96]):
+        with pytest.raises(gpu.LbmError):
+            gpu.Decomp(p, 2, "f32", row_start=rs)
