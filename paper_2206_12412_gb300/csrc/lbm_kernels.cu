@@ -291,7 +291,7 @@ __device__ __noinline__ T crack_rows(const T *w_in_, T *w_out_, D *wd_, T wd_sca
 // it comes from L2).  East/west neighbours come from the adjacent lanes by
 // warp shuffles; lanes 0 and 31 load the halo column.  The next row's loads
 // are issued before the current row is computed.  EDGE = false is the
-// interior version (no edge row or column in the CTA): the bare update.
+// interior version (no edge row or column in the warp): the bare update.
 template <typename T, typename D, bool EDGE>
 __device__ __forceinline__ void march(const StepArgs<T, D> &a, int cb, int j0, int j1, T &acc)
 {
@@ -416,7 +416,10 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
                 sS.wstar[e] = a.edge[e] == EDGE_DIRICHLET ? load_value(a.load[e], n, (double)p.dt) : 0.0;
             *a.s_out = sS;
         }
-        const bool edge = (cb == 0) | (cb == a.ncb - 1) | (j0 == 0) | (j1 == a.ny);
+        // the edge rules per warp: only warps whose columns reach an outer edge,
+        // and the bands holding the bottom and top rows, need them
+        const int xw0 = (cb * kThreads + (tid & ~31)) * N;   // first column of this warp
+        const bool edge = (xw0 == 0) | (xw0 + 32 * N - 1 >= nx - 1) | (j0 == 0) | (j1 == a.ny);
         if (edge) march<T, D, true>(a, cb, j0, j1, acc);
         else march<T, D, false>(a, cb, j0, j1, acc);
     }
