@@ -299,6 +299,33 @@ def measure_adjoint(lbm, W, torch, stream, n_steps=None):
     return out
 
 
+def measure_large(lbm, W, torch, stream, peak):
+    """The mixed-precision configuration: 16384 x 16384 (268 M sites, 4.3 GB
+    of FP32 state, far larger than L2), crack on the midline from 0 to 2048
+    growing at v = 0.5 c_s, +-1e-3 ramped over 2000 steps; the step kernel's
+    own CUDA-event time for FP32 storage and for 16-bit wdot storage."""
+    p = W.base_problem(16384, 16384, bc_mode="macroscopic")
+    p = W.with_crack(p, mode="prescribed", y=8192.0, x_tip=2048.0, v_rel=0.5)
+    p = W.with_antisymmetric_ramp(p, 1e-3, 2000.0)
+    p["hist_cap"] = 4096
+    sites = p["nx"] * p["ny"]
+    out = {"workload": "16384x16384, prescribed v=0.5 crack from 0 to 2048", "timing": "library CUDA events around "
+           "each step kernel, 20 steps after 20 (state far larger than L2)"}
+    for storage, bps in (("f32", 16), ("f32_bf16", 12), ("f32_f16", 12)):
+        lat = lbm.Lattice(p, storage, stream=stream)
+        lat.step(20)
+        lat.set_profiling(True)
+        lat.step(20)
+        lat.sync()
+        pr = lat.profile(reset=True)
+        k = pr["step_ms"] / max(pr["n_step"], 1) * 1e-3
+        out[storage] = {"kernel_us": k * 1e6, "glups": sites / k / 1e9, "bytes_per_site": bps,
+                        "achieved_gbs": bps * sites / k / 1e9, "frac": bps * sites / k / 1e9 / peak}
+        lat.close()
+        torch.cuda.empty_cache()
+    return out
+
+
 def measure_virtual_ranks(lbm, W, torch, stream, problem, steps=256):
     """The benchmark lattice split into 1, 2, 4 and 8 row slabs on this GPU
     (one batched step launch plus one halo-row exchange launch per step),
@@ -424,6 +451,7 @@ def run_ours(args, rank, world, local):
     batched = measure_batched(lbm, W, torch, stream, 128, peak) if not args.no_batched else None
     adjoint = measure_adjoint(lbm, W, torch, stream) if not args.no_adjoint else None
     vranks = measure_virtual_ranks(lbm, W, torch, stream, problem) if not args.no_virtual_ranks else None
+    large = measure_large(lbm, W, torch, stream, peak) if not args.no_large else None
 
     # steady back-to-back replay (CUDA graph, no flush): context only
     lat.sync()
@@ -479,6 +507,7 @@ def run_ours(args, rank, world, local):
         "batched": batched,
         "adjoint": adjoint,
         "virtual_ranks": vranks,
+        "large_lattice": large,
         "wall_s": wall,
         "clocks": clk,
     }
@@ -503,6 +532,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-lattice batched measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the sensor-misfit gradient measurement")
     ap.add_argument("--no-virtual-ranks", action="store_true", help="skip the row-slab decomposition measurement")
+    ap.add_argument("--no-large", action="store_true", help="skip the 16384 x 16384 storage comparison")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="only the sensor-misfit gradient measurement (for ncu)")
     ap.add_argument("--adjoint-steps", type=int, default=None, help="steps of the adjoint workload (default 8000)")
