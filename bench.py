@@ -208,11 +208,11 @@ def run_reference(args, rank, world):
     return 0
 
 
-def measure_batched(lbm, W, torch, stream, steps, peak):
+def measure_batched(lbm, W, torch, stream, steps, peak, count=256):
     """Batched form: 256 independent lattices of uneven sizes, one launch per
     step (graph replay), against the same lattices stepped one after another
     with the single-lattice path.  The 840 MB of state exceed L2."""
-    problems = W.batch_problems(256, seed=3)
+    problems = W.batch_problems(count, seed=3)
     sites = sum(p["nx"] * p["ny"] for p in problems)
 
     def timed(fn):
@@ -533,6 +533,9 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the sensor-misfit gradient measurement")
     ap.add_argument("--no-virtual-ranks", action="store_true", help="skip the row-slab decomposition measurement")
     ap.add_argument("--no-large", action="store_true", help="skip the 16384 x 16384 storage comparison")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="only the batched measurement, --steps steps of --batched-count lattices (for ncu)")
+    ap.add_argument("--batched-count", type=int, default=256, help="lattices in the batched measurement")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="only the sensor-misfit gradient measurement (for ncu)")
     ap.add_argument("--adjoint-steps", type=int, default=None, help="steps of the adjoint workload (default 8000)")
@@ -543,6 +546,17 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.batched_only:
+        # the batched form alone (for profiling the batch kernel)
+        import torch
+        from paper_2206_12412_gb300 import lbm
+        from paper_2206_12412_gb300 import workloads as W
+        torch.cuda.set_device(local)
+        peak, _ = measured_peaks()
+        out = measure_batched(lbm, W, torch, torch.cuda.current_stream(), args.steps, peak, count=args.batched_count)
+        if rank == 0:
+            print(json.dumps({"batched_only": True, **out}), flush=True)
+        return 0
     if args.adjoint_only:
         # the sensor-misfit gradient alone (for profiling the adjoint kernel)
         import torch

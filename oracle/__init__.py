@@ -64,6 +64,7 @@ class _Config(C.Structure):
         ("load_series", C.POINTER(C.c_double) * 4),
         ("load_n", C.c_int64 * 4),
         ("hist_cap", C.c_int64),
+        ("two_tips", C.c_int32), ("pad_", C.c_int32),
     ]
 
 
@@ -97,6 +98,13 @@ def _load():
         lib.orc_get_bpoints.restype = C.c_int32
         lib.orc_evaluate_K.argtypes = [P, d, C.c_int64, C.c_double, C.c_double, C.POINTER(C.c_int32)]
         lib.orc_evaluate_K.restype = C.c_double
+        lib.orc_evaluate_K_left.argtypes = [P, d, C.c_int64, C.c_double, C.c_double, C.POINTER(C.c_int32)]
+        lib.orc_evaluate_K_left.restype = C.c_double
+        lib.orc_get_history_left.argtypes = [P, d, d, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                             C.POINTER(C.c_int32), C.c_int64]
+        lib.orc_get_history_left.restype = C.c_int64
+        lib.orc_left_tip.argtypes = [P]
+        lib.orc_left_tip.restype = C.c_int64
         lib.orc_equilibrium.argtypes = [C.c_double, C.c_double, C.c_double, d]
         lib.orc_macro_poly.argtypes = [C.c_double] * 5
         lib.orc_macro_poly.restype = C.c_double
@@ -146,6 +154,7 @@ def make_config(problem: dict):
         cfg.r0 = float(cr.get("r0", 2.0 * cfg.dh))
         cfg.r_min_fixed = float(cr.get("r_min", 0.0))
         cfg.fit_width = float(cr.get("fit_width", cfg.dh))
+        cfg.two_tips = 1 if cr.get("two_tips") else 0
     keep = []
     for ld in problem.get("loads", []):
         e = EDGE_INDEX[ld["edge"]]
@@ -222,6 +231,25 @@ class Oracle:
                                      npairs.ctypes.data_as(C.POINTER(C.c_int32)),
                                      grew.ctypes.data_as(C.POINTER(C.c_int32)), cap)
         return {"K": K[:n], "v": v[:n], "tip_q": tip[:n], "npairs": npairs[:n], "grew": grew[:n]}
+
+    def history_left(self) -> dict:
+        """Per-step record of the left end of a two-tip crack."""
+        cap = int(self.problem.get("hist_cap", 1 << 16))
+        K = np.zeros(cap); v = np.zeros(cap)
+        tip = np.zeros(cap, np.int64); npairs = np.zeros(cap, np.int32); grew = np.zeros(cap, np.int32)
+        n = self.lib.orc_get_history_left(self.h, _dptr(K), _dptr(v), tip.ctypes.data_as(C.POINTER(C.c_int64)),
+                                          npairs.ctypes.data_as(C.POINTER(C.c_int32)),
+                                          grew.ctypes.data_as(C.POINTER(C.c_int32)), cap)
+        return {"K": K[:n], "v": v[:n], "tip_q": tip[:n], "npairs": npairs[:n], "grew": grew[:n]}
+
+    def left_tip_q(self) -> int:
+        return int(self.lib.orc_left_tip(self.h))
+
+    def evaluate_K_left(self, w: np.ndarray, tip_q: int, r_min: float, fit_width: float):
+        w = np.ascontiguousarray(w, dtype=np.float64).reshape(self.ny, self.nx)
+        npairs = C.c_int32(0)
+        K = self.lib.orc_evaluate_K_left(self.h, _dptr(w), int(tip_q), float(r_min), float(fit_width), C.byref(npairs))
+        return K, npairs.value
 
     def bpoints(self) -> np.ndarray:
         cap = 4 * (self.nx + self.ny) + 64

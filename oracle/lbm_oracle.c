@@ -82,6 +82,8 @@ typedef struct {
     const double *load_series[4];
     int64_t load_n[4];
     int64_t hist_cap;
+    int32_t two_tips;    /* both ends of the crack grow (the left one towards -x) */
+    int32_t pad_;
 } orc_config;
 
 typedef struct {
@@ -104,6 +106,14 @@ typedef struct {
     double v_prev, K_last;
     int32_t npairs_last, flags, arrested_for_good;
     int32_t *bprev, nbprev;
+    /* the left tip (two_tips): position, speed memory, last K, arrest, B_prev */
+    int64_t ltip_q;
+    double lv_prev, lK_last;
+    int32_t lnpairs_last, larrested;
+    int32_t *lbprev, nlbprev;
+    double *hKl, *hvl;
+    int64_t *htipl;
+    int32_t *hnpl, *hgrowl;
     orc_bpoint *bl;
     int32_t nbl, capbl;
     uint8_t *is_bpoint;
@@ -240,6 +250,7 @@ void orc_destroy(orc_state *s)
     free(s->w); free(s->w_old); free(s->cut_h); free(s->cut_v);
     free(s->bprev); free(s->bl); free(s->is_bpoint);
     free(s->hK); free(s->hv); free(s->htip); free(s->hnp); free(s->hgrow);
+    free(s->lbprev); free(s->hKl); free(s->hvl); free(s->htipl); free(s->hnpl); free(s->hgrowl);
     free(s->queue); free(s->inq); free(s->visited);
     for (int e = 0; e < 4; ++e) free(s->series[e]);
     free(s);
@@ -296,6 +307,7 @@ orc_state *orc_create(const orc_config *cfg)
     s->cut_v = xcalloc(n, 1);
     s->is_bpoint = xcalloc(n, 1);
     s->bprev = xcalloc(n, sizeof(int32_t));
+    s->lbprev = xcalloc(n, sizeof(int32_t));
     s->capbl = 64;
     s->bl = xcalloc((size_t)s->capbl, sizeof(orc_bpoint));
     s->queue = xcalloc(8 * n + 8, sizeof(int32_t));
@@ -308,6 +320,11 @@ orc_state *orc_create(const orc_config *cfg)
     s->htip = xcalloc((size_t)hc, sizeof(int64_t));
     s->hnp = xcalloc((size_t)hc, sizeof(int32_t));
     s->hgrow = xcalloc((size_t)hc, sizeof(int32_t));
+    s->hKl = xcalloc((size_t)hc, sizeof(double));
+    s->hvl = xcalloc((size_t)hc, sizeof(double));
+    s->htipl = xcalloc((size_t)hc, sizeof(int64_t));
+    s->hnpl = xcalloc((size_t)hc, sizeof(int32_t));
+    s->hgrowl = xcalloc((size_t)hc, sizeof(int32_t));
     for (int e = 0; e < 4; ++e) {
         if (cfg->load_kind[e] == ORC_LOAD_SERIES && cfg->load_n[e] > 0) {
             s->series[e] = malloc(sizeof(double) * (size_t)cfg->load_n[e]);
@@ -321,7 +338,12 @@ orc_state *orc_create(const orc_config *cfg)
     if (cfg->crack_mode != ORC_CRACK_NONE) {
         s->start_q = llrint(cfg->x_start / cfg->dh * (double)qone());
         s->tip_q = llrint(cfg->x_tip / cfg->dh * (double)qone());
+        s->ltip_q = s->start_q;
+        s->lv_prev = s->v_prev;
         initial_crack(s);
+        /* both tips start their CheckLinks from the initial boundary points */
+        memcpy(s->lbprev, s->bprev, sizeof(int32_t) * (size_t)s->nbprev);
+        s->nlbprev = s->nbprev;
     }
     return s;
 }
@@ -393,7 +415,8 @@ static void add_bpoint(orc_state *s, int32_t k)
     int nx = s->c.nx;
     int i = k % nx, j = k / nx;
     double bx = i + 0.5, by = j + 0.5;                   /* units of dh */
-    double x0 = (double)s->start_q / (double)qone(), x1 = (double)s->tip_q / (double)qone();
+    double x0 = (double)(s->c.two_tips ? s->ltip_q : s->start_q) / (double)qone();
+    double x1 = (double)s->tip_q / (double)qone();
     double yc = (double)s->c.jc;
     double cx = bx < x0 ? x0 : (bx > x1 ? x1 : bx);      /* closest point on the crack line segment */
     double cy = yc;
@@ -516,7 +539,8 @@ static void lbm_step(orc_state *s)
  * distance r = tip - (i + 1/2) dh along the crack lies in [r_min, r_min + W)
  * (Sec. 4.2): least squares of delta_i = (4K/mu) s_i, s_i = sqrt(r_i / 2pi)
  * (eq. sif).  With one pair this is K = delta (mu/4) sqrt(2pi/r). */
-static double evaluate_K(const orc_state *s, const double *w, int64_t tip_q, double r_min, double wfit, int32_t *npairs)
+static double evaluate_K_dir(const orc_state *s, const double *w, int64_t tip_q, double r_min, double wfit,
+                             int dir, int32_t *npairs)
 {
     int nx = s->c.nx, jc = s->c.jc;
     double dh = s->c.dh;
@@ -525,7 +549,8 @@ static double evaluate_K(const orc_state *s, const double *w, int64_t tip_q, dou
     double lo = r_min / dh, hi = (r_min + wfit) / dh;
     for (int i = 0; i < nx; ++i) {
         if (!s->cut_v[(jc - 1) * nx + i]) continue;       /* the pair must straddle the crack */
-        double r_h = (double)(tip_q - site_cx_q(i)) / (double)qone();
+        /* r along the crack behind the tip: tip - x_i for the right tip, x_i - tip for the left */
+        double r_h = (double)(dir > 0 ? tip_q - site_cx_q(i) : site_cx_q(i) - tip_q) / (double)qone();
         if (!(r_h >= lo && r_h < hi)) continue;
         double r = r_h * dh;
         double sfac = sqrt(r / (2.0 * ORC_PI));
@@ -539,9 +564,22 @@ static double evaluate_K(const orc_state *s, const double *w, int64_t tip_q, dou
     return s->c.mu / 4.0 * num / den;
 }
 
+static double evaluate_K(const orc_state *s, const double *w, int64_t tip_q, double r_min, double wfit, int32_t *npairs)
+{
+    return evaluate_K_dir(s, w, tip_q, r_min, wfit, +1, npairs);
+}
+
 double orc_evaluate_K(const orc_state *s, const double *w, int64_t tip_q, double r_min, double wfit, int32_t *npairs)
 {
     return evaluate_K(s, w, tip_q, r_min, wfit, npairs);
+}
+
+/* K at a left tip (a crack end growing towards -x): the pairs at r = x_i - tip
+ * in the window, the same opening delta = w(above) - w(below), so that a
+ * mirror-symmetric problem has the same K at both ends. */
+double orc_evaluate_K_left(const orc_state *s, const double *w, int64_t tip_q, double r_min, double wfit, int32_t *npairs)
+{
+    return evaluate_K_dir(s, w, tip_q, r_min, wfit, -1, npairs);
 }
 
 /* Alg. 1, CheckLinks: breadth-first search from the neighbours of the
@@ -611,49 +649,96 @@ static int cmp_i32(const void *a, const void *b)
     return (x > y) - (x < y);
 }
 
-/* Alg. 1, CrackGrowth, appended after the LBM step (Sec. 4.1). */
+/* The criterion of Alg. 1 for one tip (dir = +1: the right end, growing
+ * towards +x; -1: the left end of a two-tip crack, growing towards -x):
+ * r_min of eq. r(v) from that tip's previous speed, K (eq. sif), and the
+ * decision: prescribed growth, or |K| > K_C with the speed of eq. v-tanh. */
+static void tip_criterion(const orc_state *s, int dir, double v_prev, int64_t tip, double *K, double *v, int *propagate,
+                          int32_t *np)
+{
+    const orc_config *c = &s->c;
+    double r_min = c->r_min_fixed > 0.0 ? c->r_min_fixed : c->r0 / (1.0 - v_prev);  /* eq. r(v) */
+    *K = evaluate_K_dir(s, s->w, tip, r_min, c->fit_width, dir, np);
+    *propagate = 0;
+    *v = 0.0;
+    if (c->crack_mode == ORC_CRACK_PRESCRIBED) {
+        *propagate = 1;
+        *v = c->v_rel;
+    } else if (c->crack_mode == ORC_CRACK_KCRIT && *np > 0 && fabs(*K) > c->K_C) {
+        double ratio = fabs(*K) / c->K_C;
+        *propagate = 1;
+        *v = c->v_max * tanh(sqrt(ratio * ratio * ratio * ratio - 1.0));  /* eq. v-tanh */
+    }
+}
+
+/* Advance one tip by Delta a = adot dt (towards +x or -x, stopping at the far
+ * edge), sever the links the new segment intersects (CheckLinks from that
+ * tip's previous boundary points) and register the new boundary points
+ * (ProcessPoints).  Returns 1 if the tip moved. */
+static int tip_advance(orc_state *s, int dir, double v)
+{
+    const orc_config *c = &s->c;
+    double adot = v * s->cs;
+    int64_t dq = llrint(adot * c->dt / c->dh * (double)qone());   /* Delta a = adot dt */
+    int64_t yq = (int64_t)c->jc << ORC_Q;
+    int32_t B[64];
+    int nB;
+    if (dir > 0) {
+        int64_t prev = s->tip_q, next = prev + dq;
+        if (next >= s->clamp_q) { next = s->clamp_q; s->arrested_for_good = 1; s->flags |= ORC_FLAG_CLAMPED; }
+        if (next <= prev) return 0;
+        s->tip_q = next;
+        nB = checklinks(s, prev, yq, next, yq, B, 64);
+        qsort(B, (size_t)nB, sizeof(int32_t), cmp_i32);
+        for (int b = 0; b < nB; ++b) add_bpoint(s, B[b]);        /* ProcessPoints */
+        if (nB > 0) { memcpy(s->bprev, B, sizeof(int32_t) * (size_t)nB); s->nbprev = nB; }
+    } else {
+        int64_t prev = s->ltip_q, next = prev - dq;
+        if (next <= 0) { next = 0; s->larrested = 1; s->flags |= ORC_FLAG_CLAMPED; }
+        if (next >= prev) return 0;
+        s->ltip_q = next;
+        int32_t *keep = s->bprev, nkeep = s->nbprev;                /* CheckLinks from this tip's B_prev */
+        s->bprev = s->lbprev;
+        s->nbprev = s->nlbprev;
+        nB = checklinks(s, prev, yq, next, yq, B, 64);
+        s->bprev = keep;
+        s->nbprev = nkeep;
+        qsort(B, (size_t)nB, sizeof(int32_t), cmp_i32);
+        for (int b = 0; b < nB; ++b) add_bpoint(s, B[b]);
+        if (nB > 0) { memcpy(s->lbprev, B, sizeof(int32_t) * (size_t)nB); s->nlbprev = nB; }
+    }
+    return 1;
+}
+
+/* Alg. 1, CrackGrowth, appended after the LBM step (Sec. 4.1).  With two
+ * tips both criteria are evaluated on the same state, then the right tip
+ * and the left tip advance in that order. */
 static void crack_growth(orc_state *s)
 {
     const orc_config *c = &s->c;
     if (c->crack_mode == ORC_CRACK_NONE) return;
-    double r_min = c->r_min_fixed > 0.0 ? c->r_min_fixed : c->r0 / (1.0 - s->v_prev);  /* eq. r(v) */
-    int32_t np = 0;
-    double K = evaluate_K(s, s->w, s->tip_q, r_min, c->fit_width, &np);
-    int propagate = 0;
-    double v = 0.0;
-    if (c->crack_mode == ORC_CRACK_PRESCRIBED) {
-        propagate = 1;
-        v = c->v_rel;
-    } else if (c->crack_mode == ORC_CRACK_KCRIT && np > 0 && fabs(K) > c->K_C) {
-        double ratio = fabs(K) / c->K_C;
-        propagate = 1;
-        v = c->v_max * tanh(sqrt(ratio * ratio * ratio * ratio - 1.0));  /* eq. v-tanh */
-    }
-    if (!isfinite(K)) s->flags |= ORC_FLAG_NONFINITE;
+    double K, v, Kl = 0.0, vl = 0.0;
+    int propagate, propl = 0;
+    int32_t np, npl = 0;
+    tip_criterion(s, +1, s->v_prev, s->tip_q, &K, &v, &propagate, &np);
+    if (c->two_tips) tip_criterion(s, -1, s->lv_prev, s->ltip_q, &Kl, &vl, &propl, &npl);
+    if (!isfinite(K) || !isfinite(Kl)) s->flags |= ORC_FLAG_NONFINITE;
     if (s->arrested_for_good) { propagate = 0; v = 0.0; }
-    int grew = 0;
-    if (propagate) {
-        double adot = v * s->cs;
-        int64_t dq = llrint(adot * c->dt / c->dh * (double)qone());   /* Delta a = adot dt */
-        int64_t prev = s->tip_q, next = prev + dq;
-        if (next >= s->clamp_q) { next = s->clamp_q; s->arrested_for_good = 1; s->flags |= ORC_FLAG_CLAMPED; }
-        if (next > prev) {
-            int64_t yq = (int64_t)c->jc << ORC_Q;
-            int32_t B[64];
-            s->tip_q = next;
-            int nB = checklinks(s, prev, yq, next, yq, B, 64);
-            qsort(B, (size_t)nB, sizeof(int32_t), cmp_i32);
-            for (int b = 0; b < nB; ++b) add_bpoint(s, B[b]);        /* ProcessPoints */
-            if (nB > 0) { memcpy(s->bprev, B, sizeof(int32_t) * (size_t)nB); s->nbprev = nB; }
-            grew = 1;
-        }
-    }
+    if (s->larrested) { propl = 0; vl = 0.0; }
+    int grew = propagate ? tip_advance(s, +1, v) : 0;
+    int grewl = (c->two_tips && propl) ? tip_advance(s, -1, vl) : 0;
     s->v_prev = c->crack_mode == ORC_CRACK_PRESCRIBED ? c->v_rel : v;
     s->K_last = K;
     s->npairs_last = np;
+    if (c->two_tips) {
+        s->lv_prev = c->crack_mode == ORC_CRACK_PRESCRIBED ? c->v_rel : vl;
+        s->lK_last = Kl;
+        s->lnpairs_last = npl;
+    }
     if (s->hist_n < c->hist_cap) {
         int64_t h = s->hist_n;
         s->hK[h] = K; s->hv[h] = v; s->htip[h] = s->tip_q; s->hnp[h] = np; s->hgrow[h] = grew;
+        s->hKl[h] = Kl; s->hvl[h] = vl; s->htipl[h] = s->ltip_q; s->hnpl[h] = npl; s->hgrowl[h] = grewl;
     }
     s->hist_n += 1;
 }
@@ -698,6 +783,19 @@ int64_t orc_get_history(const orc_state *s, double *K, double *v, int64_t *tip_q
     }
     return n;
 }
+
+int64_t orc_get_history_left(const orc_state *s, double *K, double *v, int64_t *tip_q, int32_t *npairs, int32_t *grew,
+                             int64_t cap)
+{
+    int64_t n = s->hist_n < s->c.hist_cap ? s->hist_n : s->c.hist_cap;
+    if (n > cap) n = cap;
+    for (int64_t h = 0; h < n; ++h) {
+        K[h] = s->hKl[h]; v[h] = s->hvl[h]; tip_q[h] = s->htipl[h]; npairs[h] = s->hnpl[h]; grew[h] = s->hgrowl[h];
+    }
+    return n;
+}
+
+int64_t orc_left_tip(const orc_state *s) { return s->ltip_q; }
 
 int32_t orc_get_bpoints(const orc_state *s, int32_t *sites, int32_t cap)
 {

@@ -28,11 +28,13 @@ def base_problem(nx: int, ny: int, *, bc_mode: str = "macroscopic", edges=("free
 
 def with_crack(p: dict, *, mode: str, y: float, x_tip: float, x_start: float = 0.0, v_rel: float = 0.0,
                K_C: float = 0.0, v_max: float = 0.85, r0: float = 2.0, r_min: float = 0.0,
-               fit_width: float = 1.0) -> dict:
+               fit_width: float = 1.0, two_tips: bool = False) -> dict:
+    """A straight crack on y from x_start to x_tip; with two_tips the end at
+    x_start grows too (towards -x)."""
     q = dict(p)
     q["crack"] = {"mode": mode, "y": float(y), "x_start": float(x_start), "x_tip": float(x_tip),
                   "v_rel": float(v_rel), "K_C": float(K_C), "v_max": float(v_max), "r0": float(r0),
-                  "r_min": float(r_min), "fit_width": float(fit_width)}
+                  "r_min": float(r_min), "fit_width": float(fit_width), "two_tips": bool(two_tips)}
     return q
 
 
