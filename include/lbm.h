@@ -116,10 +116,13 @@ typedef struct lbm_material {
  * K_C, v_max: K-criterion and eq. v-tanh (LBM_CRACK_KCRIT).
  * r0: eq. r(v); r_min > 0 overrides it with a fixed evaluation distance.
  * fit_width: width W of the evaluation window [r_min, r_min + W) (dh if <= 0).
- * hist_cap: capacity of the per-step history ring (records kept on device). */
+ * hist_cap: capacity of the per-step history ring (records kept on device).
+ * two_tips: 1 lets the end at x_start grow too, towards -x (a centre crack
+ * with two tips, Sec. 5.2); each end runs the crack step of Alg. 1 with its
+ * own speed memory, and the left end stops at x = 0.  0: only x_tip grows. */
 typedef struct lbm_crack {
     int32_t mode;
-    int32_t reserved;
+    int32_t two_tips;
     double y, x_start, x_tip;
     double v_rel, K_C, v_max, r0, r_min, fit_width;
     int64_t hist_cap;
@@ -203,6 +206,12 @@ lbm_status lbm_cut_mask(lbm_handle *h, int32_t which, uint32_t *dst_host, int64_
  * number of records copied.  Synchronises the stream. */
 lbm_status lbm_crack_state(lbm_handle *h, lbm_crack_state_t *now, double *K_hist, double *v_hist,
                            int64_t *tip_hist, int32_t *npairs_hist, int64_t cap, int64_t *n_written);
+
+/* The same for the left end of a two-tip crack (tip_q, tip_x, K, v, r_min,
+ * npairs, flags of that end; step, n_cut and hist_n are shared).
+ * LBM_ERR_STATE if the crack has one growing end. */
+lbm_status lbm_crack_state_left(lbm_handle *h, lbm_crack_state_t *now, double *K_hist, double *v_hist,
+                                int64_t *tip_hist, int32_t *npairs_hist, int64_t cap, int64_t *n_written);
 
 /* Synchronise the handle's stream and report sticky device errors. */
 lbm_status lbm_sync(lbm_handle *h);

@@ -35,7 +35,7 @@ class Material(C.Structure):
 
 
 class Crack(C.Structure):
-    _fields_ = [("mode", C.c_int32), ("reserved", C.c_int32),
+    _fields_ = [("mode", C.c_int32), ("two_tips", C.c_int32),
                 ("y", C.c_double), ("x_start", C.c_double), ("x_tip", C.c_double),
                 ("v_rel", C.c_double), ("K_C", C.c_double), ("v_max", C.c_double),
                 ("r0", C.c_double), ("r_min", C.c_double), ("fit_width", C.c_double),
@@ -73,6 +73,9 @@ PROTOTYPES = {
     "lbm_crack_state": (C.c_int, [C.c_void_p, C.POINTER(CrackStateT), C.POINTER(C.c_double),
                                   C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                                   C.c_int64, C.POINTER(C.c_int64)]),
+    "lbm_crack_state_left": (C.c_int, [C.c_void_p, C.POINTER(CrackStateT), C.POINTER(C.c_double),
+                                       C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                       C.c_int64, C.POINTER(C.c_int64)]),
     "lbm_sync": (C.c_int, [C.c_void_p]),
     "lbm_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lbm_set_launch": (C.c_int, [C.c_void_p, C.c_int32]),

@@ -197,13 +197,14 @@ __device__ __forceinline__ void adj_march(const AdjArgs<T> &a, int cb, int j0, i
 }
 
 // A crack sub-band of HH rows (rows jc-HH .. jc-1 or jc .. jc+HH-1): the
-// stencil with the severed links of step n (columns i_first .. il_n), the
+// stencil with the severed links of step n (columns if_n .. il_n), the
 // sources, then the crack-face correction for the columns severed in step
-// n - 1 (i_first .. il_p), all from registers.  Out of line (its register
+// n - 1 (if_p .. il_p), all from registers.  Out of line (its register
 // demand would otherwise be the whole kernel's), with the arguments in shared
 // memory; returns the finiteness probe.
 template <typename T, int HH>
-__device__ __noinline__ T adj_crack_rows(const AdjArgs<T> *sa, int cb, int j0, int il_n, int il_p, const int32_t *ssj,
+__device__ __noinline__ T adj_crack_rows(const AdjArgs<T> *sa, int cb, int j0, int if_n, int il_n, int if_p, int il_p,
+                                         const int32_t *ssj,
                                          const int32_t *ssi, const T *ssv, int n_s, int lo_g, int hi_g, int64_t srow)
 {
     const AdjArgs<T> &a = *sa;
@@ -238,8 +239,8 @@ __device__ __noinline__ T adj_crack_rows(const AdjArgs<T> *sa, int cb, int j0, i
     EdgeValues<T> E;
 #pragma unroll
     for (int e = 0; e < 4; ++e) E.two_ws[e] = (T)0;
-    const uint32_t cut_n = col_bits<N>(x0, a.i_first, il_n);
-    const uint32_t cut_p = col_bits<N>(x0, a.i_first, il_p);
+    const uint32_t cut_n = col_bits<N>(x0, if_n, il_n);
+    const uint32_t cut_p = col_bits<N>(x0, if_p, il_p);
     R o[HH], od[HH];
 #pragma unroll
     for (int q = 0; q < HH; ++q) {
@@ -318,14 +319,15 @@ __device__ __forceinline__ void adjoint_cta(const AdjArgs<T> &a, int cb, int ban
     S.srow = srow;
     T acc;
     if (a.crack_band >= 0 && (band == a.crack_band || band == a.crack_band + 1)) {
-        const int il_n = a.i_last[n < a.n_steps ? n : a.n_steps - 1];
-        const int il_p = n >= 1 ? a.i_last[n - 1] : a.i_first - 1;
+        const int64_t nn = n < a.n_steps ? n : a.n_steps - 1;
+        const int if_n = a.i_first[nn], il_n = a.i_last[nn];
+        const int if_p = n >= 1 ? a.i_first[n - 1] : 1, il_p = n >= 1 ? a.i_last[n - 1] : 0;   // none before step 0
         const uint32_t *src = reinterpret_cast<const uint32_t *>(&a);
         uint32_t *dst = reinterpret_cast<uint32_t *>(sa);
         for (int q = tid; q < (int)(sizeof(AdjArgs<T>) / 4); q += kThreads) dst[q] = src[q];
         __syncthreads();
-        acc = a.macro ? adj_crack_rows<T, 3>(sa, cb, j0, il_n, il_p, ssj, ssi, ssv, n_s, lo + n_s, hi, srow)
-                      : adj_crack_rows<T, 1>(sa, cb, j0, il_n, il_p, ssj, ssi, ssv, n_s, lo + n_s, hi, srow);
+        acc = a.macro ? adj_crack_rows<T, 3>(sa, cb, j0, if_n, il_n, if_p, il_p, ssj, ssi, ssv, n_s, lo + n_s, hi, srow)
+                      : adj_crack_rows<T, 1>(sa, cb, j0, if_n, il_n, if_p, il_p, ssj, ssi, ssv, n_s, lo + n_s, hi, srow);
     } else {
         acc = (T)0;
         const bool edge = (cb == 0) | (cb == a.ncb - 1) | (j0 == 0) | (j1 == a.ny);

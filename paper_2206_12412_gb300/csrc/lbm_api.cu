@@ -190,7 +190,7 @@ lbm_status check_sticky(lbm_handle *h)
         h->sticky = LBM_ERR_CUDA;
         return cuda_fail(e, "synchronising the lattice stream");
     }
-    if ((err & ERR_NONFINITE) || (hs.flags & FLAG_NONFINITE)) {
+    if ((err & ERR_NONFINITE) || ((hs.r.flags | hs.l.flags) & FLAG_NONFINITE)) {
         h->sticky = LBM_ERR_UNSTABLE;
         return fail(LBM_ERR_UNSTABLE, "non-finite value in the fields or in K");
     }
@@ -368,6 +368,7 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
             return fail(LBM_ERR_ARG, "macroscopic crack faces need non-periodic left/right edges");
         if (cr.mode == LBM_CRACK_PRESCRIBED && !(cr.v_rel >= 0.0 && cr.v_rel < 1.0))
             return fail(LBM_ERR_ARG, "prescribed v_rel must lie in [0, 1)");
+        if (cr.two_tips != 0 && cr.two_tips != 1) return fail(LBM_ERR_ARG, "two_tips must be 0 or 1");
         if (cr.mode == LBM_CRACK_KCRIT && !(cr.K_C > 0.0 && cr.v_max >= 0.0 && cr.v_max < 1.0))
             return fail(LBM_ERR_ARG, "K-criterion needs K_C > 0 and 0 <= v_max < 1");
         if (!(cr.r_min > 0.0) && !(cr.r0 >= 0.0)) return fail(LBM_ERR_ARG, "r0 must be >= 0");
@@ -462,6 +463,12 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
     const size_t o_hv = off; off = align256(off + (size_t)hcap * 8);
     const size_t o_ht = off; off = align256(off + (size_t)hcap * 8);
     const size_t o_hn = off; off = align256(off + (size_t)hcap * 4);
+    if (cr.mode == LBM_CRACK_NONE) cr.two_tips = 0;
+    const int64_t hcap_l = cr.two_tips ? hcap : 1;   // records of the left end
+    const size_t o_hKl = off; off = align256(off + (size_t)hcap_l * 8);
+    const size_t o_hvl = off; off = align256(off + (size_t)hcap_l * 8);
+    const size_t o_htl = off; off = align256(off + (size_t)hcap_l * 8);
+    const size_t o_hnl = off; off = align256(off + (size_t)hcap_l * 4);
     size_t o_ser[4];
     for (int q = 0; q < 4; ++q) { o_ser[q] = off; off = align256(off + (size_t)h->load[q].n * 8); }
     h->block_bytes = off;
@@ -487,6 +494,10 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
     h->hist.v = reinterpret_cast<double *>(base + o_hv);
     h->hist.tip = reinterpret_cast<int64_t *>(base + o_ht);
     h->hist.np = reinterpret_cast<int32_t *>(base + o_hn);
+    h->hist.Kl = reinterpret_cast<double *>(base + o_hKl);
+    h->hist.vl = reinterpret_cast<double *>(base + o_hvl);
+    h->hist.tipl = reinterpret_cast<int64_t *>(base + o_htl);
+    h->hist.npl = reinterpret_cast<int32_t *>(base + o_hnl);
 
     cudaStream_t s = h->stream;
     auto bail = [&](lbm_status rc) {
@@ -517,6 +528,7 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
     cp.ny = grid->ny;
     cp.macro = lattice->bc_mode == LBM_BC_MACROSCOPIC;
     cp.words = h->words;
+    cp.two_tips = cr.two_tips ? 1 : 0;
     cp.mu = material->mu;
     cp.cs = cs;
     cp.dt = grid->dt;
@@ -559,10 +571,12 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
     // initial state: the initial crack's links (x_start <= x_i <= x_tip) severed
     CrackState hs;
     std::memset(&hs, 0, sizeof hs);
-    hs.tip_q = tip_q;
+    hs.r.tip_q = tip_q;
+    hs.l.tip_q = start_q;
     hs.i_first = 0;
     hs.i_last = -1;
-    hs.decided = 1;
+    hs.r.decided = 1;
+    hs.l.decided = 1;
     std::vector<uint32_t> row((size_t)h->words, 0u);
     if (cr.mode != LBM_CRACK_NONE) {
         const int64_t half = qone / 2;
@@ -572,7 +586,8 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
         if (last > grid->nx - 1) last = grid->nx - 1;
         hs.i_first = (int32_t)first;
         hs.i_last = (int32_t)(last < first ? first - 1 : last);
-        hs.v_prev = cr.mode == LBM_CRACK_PRESCRIBED ? cr.v_rel : 0.0;
+        hs.r.v_prev = cr.mode == LBM_CRACK_PRESCRIBED ? cr.v_rel : 0.0;
+        hs.l.v_prev = hs.r.v_prev;
         for (int i = hs.i_first; i <= hs.i_last; ++i) row[(size_t)(i >> 5)] |= 1u << (i & 31);
         e = cudaMemcpyAsync(h->cut_v + (size_t)(jc - 1) * h->words, row.data(), row.size() * 4, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return bail(cuda_fail(e, "writing the initial crack"));
@@ -777,26 +792,34 @@ lbm_status lbm_cut_mask(lbm_handle *h, int32_t which, uint32_t *dst_host, int64_
     return check_sticky(h);
 }
 
-lbm_status lbm_crack_state(lbm_handle *h, lbm_crack_state_t *now, double *K_hist, double *v_hist,
-                           int64_t *tip_hist, int32_t *npairs_hist, int64_t cap, int64_t *n_written)
+}  // extern "C"
+
+namespace {
+
+// The state of one end of the crack (left: the left end of a two-tip crack)
+// and its last records.
+lbm_status crack_state_impl(lbm_handle *h, bool left, lbm_crack_state_t *now, double *K_hist, double *v_hist,
+                            int64_t *tip_hist, int32_t *npairs_hist, int64_t cap, int64_t *n_written)
 {
     if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
+    if (left && !h->cp.two_tips) return fail(LBM_ERR_STATE, "the crack has one growing end");
     lbm_status rc = finalize(h);
     if (rc != LBM_OK) return rc;
     CrackState hs;
     LBM_CUDA(cudaMemcpyAsync(&hs, h->st + h->parity, sizeof hs, cudaMemcpyDeviceToHost, h->stream));
     LBM_CUDA(cudaStreamSynchronize(h->stream));
+    const TipState &E = left ? hs.l : hs.r;
     if (now) {
         now->step = hs.step;
-        now->tip_q = hs.tip_q;
+        now->tip_q = E.tip_q;
         now->n_cut = hs.i_last >= hs.i_first ? (int64_t)(hs.i_last - hs.i_first + 1) : 0;
         now->hist_n = hs.hist_n;
-        now->tip_x = (double)hs.tip_q * kTwoM32 * h->grid.dh;
-        now->K = hs.K;
-        now->v = hs.v;
-        now->r_min = hs.r_min;
-        now->npairs = hs.npairs;
-        now->flags = hs.flags;
+        now->tip_x = (double)E.tip_q * kTwoM32 * h->grid.dh;
+        now->K = E.K;
+        now->v = E.v;
+        now->r_min = E.r_min;
+        now->npairs = E.npairs;
+        now->flags = E.flags;
     }
     int64_t n = 0;
     const int64_t hcap = h->cp.hist_cap;
@@ -807,10 +830,12 @@ lbm_status lbm_crack_state(lbm_handle *h, lbm_crack_state_t *now, double *K_hist
         std::vector<double> K((size_t)hcap), v((size_t)hcap);
         std::vector<int64_t> tip((size_t)hcap);
         std::vector<int32_t> np((size_t)hcap);
-        LBM_CUDA(cudaMemcpyAsync(K.data(), h->hist.K, (size_t)hcap * 8, cudaMemcpyDeviceToHost, h->stream));
-        LBM_CUDA(cudaMemcpyAsync(v.data(), h->hist.v, (size_t)hcap * 8, cudaMemcpyDeviceToHost, h->stream));
-        LBM_CUDA(cudaMemcpyAsync(tip.data(), h->hist.tip, (size_t)hcap * 8, cudaMemcpyDeviceToHost, h->stream));
-        LBM_CUDA(cudaMemcpyAsync(np.data(), h->hist.np, (size_t)hcap * 4, cudaMemcpyDeviceToHost, h->stream));
+        LBM_CUDA(cudaMemcpyAsync(K.data(), left ? h->hist.Kl : h->hist.K, (size_t)hcap * 8, cudaMemcpyDeviceToHost, h->stream));
+        LBM_CUDA(cudaMemcpyAsync(v.data(), left ? h->hist.vl : h->hist.v, (size_t)hcap * 8, cudaMemcpyDeviceToHost, h->stream));
+        LBM_CUDA(cudaMemcpyAsync(tip.data(), left ? h->hist.tipl : h->hist.tip, (size_t)hcap * 8, cudaMemcpyDeviceToHost,
+                                 h->stream));
+        LBM_CUDA(cudaMemcpyAsync(np.data(), left ? h->hist.npl : h->hist.np, (size_t)hcap * 4, cudaMemcpyDeviceToHost,
+                                 h->stream));
         LBM_CUDA(cudaStreamSynchronize(h->stream));
         for (int64_t q = 0; q < n; ++q) {
             const size_t r = (size_t)((first + q) % hcap);
@@ -822,6 +847,22 @@ lbm_status lbm_crack_state(lbm_handle *h, lbm_crack_state_t *now, double *K_hist
     }
     if (n_written) *n_written = n;
     return check_sticky(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_crack_state(lbm_handle *h, lbm_crack_state_t *now, double *K_hist, double *v_hist,
+                           int64_t *tip_hist, int32_t *npairs_hist, int64_t cap, int64_t *n_written)
+{
+    return crack_state_impl(h, false, now, K_hist, v_hist, tip_hist, npairs_hist, cap, n_written);
+}
+
+lbm_status lbm_crack_state_left(lbm_handle *h, lbm_crack_state_t *now, double *K_hist, double *v_hist,
+                                int64_t *tip_hist, int32_t *npairs_hist, int64_t cap, int64_t *n_written)
+{
+    return crack_state_impl(h, true, now, K_hist, v_hist, tip_hist, npairs_hist, cap, n_written);
 }
 
 lbm_status lbm_sync(lbm_handle *h)

@@ -54,18 +54,26 @@ struct LoadDesc {
     int64_t n;
 };
 
-// Crack and step state after `step` LBM steps.  decided = 1 once the crack
-// step that follows LBM step `step` has been applied (Alg. 1 runs after every
-// LBM step); the step kernel applies a pending one before its own update.
+// State of one end of the crack.  decided = 1 once the crack step that
+// follows LBM step `step` has been applied to this end (Alg. 1 runs after
+// every LBM step); the step kernel applies a pending one before its update.
+struct TipState {
+    int64_t tip_q;         // tip x in units of 2^-32 dh
+    int32_t arrested, npairs;
+    int32_t grew, decided;
+    int32_t flags, pad;
+    double v_prev, K, v, r_min;
+};
+
+// Crack and step state after `step` LBM steps.  The right end (r) grows
+// towards +x; with two-tip cracks the left end (l) grows towards -x.  Each
+// end's crack step writes only its own fields (and i_last / i_first), so the
+// two ends may be handled by different CTAs in the same launch.
 struct CrackState {
     int64_t step;          // completed LBM steps
-    int64_t tip_q;         // tip x in units of 2^-32 dh
     int64_t hist_n;        // records written to the history ring
     int32_t i_first, i_last;  // severed crack links: columns i_first..i_last of V row jc-1
-    int32_t arrested, flags;
-    int32_t npairs, grew;
-    int32_t decided, pad;
-    double v_prev, K, v, r_min;
+    TipState r, l;
     double wstar[4];       // Dirichlet values w*(t_step) for the next LBM step
 };
 
@@ -73,14 +81,19 @@ struct CrackState {
 struct CrackParams {
     int32_t mode, jc, nx, ny;
     int32_t macro, words;
+    int32_t two_tips, pad;
     double mu, cs, dt, dh, K_C, v_max, r0, r_min_fixed, fit_width, v_rel;
     int64_t start_q, clamp_q, hist_cap;
 };
 
+// Per-step records of the right end and (two-tip cracks) the left end.
 struct History {
     double *K, *v;
     int64_t *tip;
     int32_t *np;
+    double *Kl, *vl;
+    int64_t *tipl;
+    int32_t *npl;
 };
 
 // One row band of the static partition: output rows [j0, j1).
@@ -132,14 +145,14 @@ struct BatchUnit {
 // entries s_off[u] .. s_off[u+1]-1 of s_ent, each an index k into s_i / s_j.
 // Step t of the recording (t = step - *n0, 0 <= t < n_steps) stores the misfit
 // r = w(x_k) - target[t][k] of the state it produces in resid[t % ring][k],
-// adds r^2 to loss[k] if acc_loss, and stores the last severed crack column
-// in force during step t in i_last[t].
+// adds r^2 to loss[k] if acc_loss, and stores the first and last severed
+// crack columns in force during step t in i_first[t], i_last[t].
 struct RecArgs {
     const int32_t *s_off, *s_ent, *s_i, *s_j;
     const double *target;
     double *resid;
     double *loss;
-    int32_t *i_last;
+    int32_t *i_first, *i_last;
     const int64_t *n0;
     int64_t n_steps, ring;
     int32_t ns, acc_loss;
@@ -159,8 +172,9 @@ struct AdjArgs {
     int32_t nx, ny, ncb, crack_band;
     int32_t edge[4];
     T g, dt;
-    int32_t jc, macro, i_first, ns;
+    int32_t jc, macro, pad0, ns;
     const Unit *units;
+    const int32_t *i_first;    // [n_steps] first severed column in force during forward step t
     const int32_t *i_last;     // [n_steps] last severed column in force during forward step t
     const int64_t *cnt_in;
     int64_t *cnt_out;

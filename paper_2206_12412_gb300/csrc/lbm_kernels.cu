@@ -57,34 +57,46 @@ __device__ __forceinline__ double load_value(const LoadDesc L, int64_t n, double
 
 // ------------------------------------------------------------ crack step
 //
-// Warp-collective crack handling of Alg. 1 for the state S (in shared
-// memory), given the fields w after the LBM step.  (1) K_III by least squares
-// of the crack opening over the site pairs straddling the crack at r in
-// [r_min, r_min + W) along the crack (eq. sif; Sec. 4.2 and eq. r(v)), in
-// FP64 with a warp reduction.  (2) The criterion: prescribed growth, or
-// |K| > K_C with v = v_max tanh(sqrt((K/K_C)^4 - 1)) (eq. v-tanh).  (3) The
-// advance Delta a = adot dt, rounded to the 2^-32 dh grid; the links at
-// x_i = (i + 1/2) dh with tip < x_i <= tip + Delta a are severed (closed
-// segment).  Lane 0 updates S and the cut mask and, if `commit`, writes the
-// history record.  Two CTAs may run it on the same state at once: both reach
-// the same decision and set the same mask bit.
+// Warp-collective crack handling of Alg. 1 for one end of the crack (dir =
+// +1: the right end, growing towards +x; -1: the left end of a two-tip
+// crack, growing towards -x) of the state S (in shared memory), given the
+// fields w after the LBM step.  (1) K_III by least squares of the crack
+// opening over the site pairs straddling the crack at r in [r_min, r_min + W)
+// behind the tip (eq. sif; Sec. 4.2 and eq. r(v) with this end's previous
+// speed), in FP64 with a warp reduction.  (2) The criterion: prescribed
+// growth, or |K| > K_C with v = v_max tanh(sqrt((K/K_C)^4 - 1)) (eq.
+// v-tanh).  (3) The advance Delta a = adot dt, rounded to the 2^-32 dh grid;
+// the links at x_i = (i + 1/2) dh between the old and the new tip are
+// severed (closed segment); the right end stops at x = nx dh, the left at 0.
+// Lane 0 updates this end's fields of S (and i_last or i_first) and the cut
+// mask and, if `commit`, writes this end's history record at hist_n (the
+// caller advances hist_n once per crack step).  Two CTAs may run it on the
+// same state at once: both reach the same decision and set the same bits.
 template <typename T>
 __device__ __forceinline__ void crack_step_warp(const CrackParams &p, const T *w, int64_t P, uint32_t *cut_v,
-                                                const History &hist, CrackState &S, bool commit)
+                                                const History &hist, CrackState &S, int dir, bool commit)
 {
     const int lane = threadIdx.x & 31;
-    if (p.mode == CRACK_NONE || S.decided) {
+    TipState &E = dir > 0 ? S.r : S.l;
+    if (p.mode == CRACK_NONE || E.decided) {
         __syncwarp();
-        if (lane == 0) S.decided = 1;
+        if (lane == 0) E.decided = 1;
         __syncwarp();
         return;
     }
-    const int64_t tip = S.tip_q;
+    const int64_t tip = E.tip_q;
     const int i_first = S.i_first, i_last = S.i_last;
-    const double r_min = p.r_min_fixed > 0.0 ? p.r_min_fixed : p.r0 / (1.0 - S.v_prev);   // eq. r(v)
+    const double r_min = p.r_min_fixed > 0.0 ? p.r_min_fixed : p.r0 / (1.0 - E.v_prev);   // eq. r(v)
     const double lo = r_min / p.dh, hi = (r_min + p.fit_width) / p.dh;
     const double tip_h = (double)tip * kTwoM32;
-    int c_lo = (int)floor(tip_h - hi - 0.5) - 1, c_hi = (int)floor(tip_h - lo - 0.5) + 1;
+    int c_lo, c_hi;
+    if (dir > 0) {
+        c_lo = (int)floor(tip_h - hi - 0.5) - 1;
+        c_hi = (int)floor(tip_h - lo - 0.5) + 1;
+    } else {
+        c_lo = (int)floor(tip_h + lo - 0.5) - 1;
+        c_hi = (int)floor(tip_h + hi - 0.5) + 1;
+    }
     c_lo = c_lo < i_first ? i_first : c_lo;
     c_hi = c_hi > i_last ? i_last : c_hi;
     const int jc = p.jc;
@@ -92,7 +104,8 @@ __device__ __forceinline__ void crack_step_warp(const CrackParams &p, const T *w
     int np = 0;
     for (int i = c_lo + lane; i <= c_hi; i += 32) {
         if (!((cut_v[(int64_t)(jc - 1) * p.words + (i >> 5)] >> (i & 31)) & 1u)) continue;
-        const double r_h = (double)(tip - ((int64_t)(2 * i + 1) << (kQBits - 1))) * kTwoM32;
+        const int64_t xq = (int64_t)(2 * i + 1) << (kQBits - 1);
+        const double r_h = (double)(dir > 0 ? tip - xq : xq - tip) * kTwoM32;
         if (!(r_h >= lo && r_h < hi)) continue;
         const double r = r_h * p.dh;
         const double sf = sqrt(r / (2.0 * kPi));
@@ -119,46 +132,69 @@ __device__ __forceinline__ void crack_step_warp(const CrackParams &p, const T *w
             propagate = 1;
             v = p.v_max * tanh(sqrt(ratio * ratio * ratio * ratio - 1.0));   // eq. v-tanh
         }
-        int32_t flags = S.flags;
+        int32_t flags = E.flags;
         if (!isfinite(K)) flags |= FLAG_NONFINITE;
-        if (S.arrested) { propagate = 0; v = 0.0; }
+        if (E.arrested) { propagate = 0; v = 0.0; }
         int grew = 0;
         int64_t tip_new = tip;
+        const int jr = p.jc - 1;
+        const int64_t half = (int64_t)1 << (kQBits - 1);
         if (propagate) {
             const double adot = v * p.cs;
             const int64_t dq = __double2ll_rn(adot * p.dt / p.dh * 4294967296.0);   // Delta a = adot dt
-            int64_t next = tip + dq;
-            if (next >= p.clamp_q) { next = p.clamp_q; S.arrested = 1; flags |= FLAG_CLAMPED; }
-            if (next > tip) {
-                int64_t last = (next - ((int64_t)1 << (kQBits - 1))) >> kQBits;
-                if (last > p.nx - 1) last = p.nx - 1;
-                const int jr = p.jc - 1;
-                for (int64_t i = (int64_t)i_last + 1; i <= last; ++i) {
-                    if (i < i_first) continue;
-                    atomicOr(&cut_v[(int64_t)jr * p.words + (i >> 5)], 1u << (i & 31));
+            if (dir > 0) {
+                int64_t next = tip + dq;
+                if (next >= p.clamp_q) { next = p.clamp_q; E.arrested = 1; flags |= FLAG_CLAMPED; }
+                if (next > tip) {
+                    int64_t last = (next - half) >> kQBits;   // largest i with x_i <= next
+                    if (last > p.nx - 1) last = p.nx - 1;
+                    for (int64_t i = (int64_t)i_last + 1; i <= last; ++i) {
+                        if (i < i_first) continue;
+                        atomicOr(&cut_v[(int64_t)jr * p.words + (i >> 5)], 1u << (i & 31));
+                    }
+                    if (last > i_last && last >= i_first) S.i_last = (int32_t)last;
+                    tip_new = next;
+                    grew = 1;
                 }
-                if (last > i_last && last >= i_first) S.i_last = (int32_t)last;
-                tip_new = next;
-                grew = 1;
+            } else {
+                int64_t next = tip - dq;
+                if (next <= 0) { next = 0; E.arrested = 1; flags |= FLAG_CLAMPED; }
+                if (next < tip) {
+                    int64_t first = (next - half + ((int64_t)1 << kQBits) - 1) >> kQBits;   // smallest i with x_i >= next
+                    if (first < 0) first = 0;
+                    for (int64_t i = first; i < (int64_t)i_first; ++i) {
+                        if (i > i_last) continue;
+                        atomicOr(&cut_v[(int64_t)jr * p.words + (i >> 5)], 1u << (i & 31));
+                    }
+                    if (first < i_first && first <= i_last) S.i_first = (int32_t)first;
+                    tip_new = next;
+                    grew = 1;
+                }
             }
         }
-        S.tip_q = tip_new;
-        S.v_prev = p.mode == CRACK_PRESCRIBED ? p.v_rel : v;
-        S.K = K;
-        S.v = v;
-        S.r_min = r_min;
-        S.npairs = np;
-        S.grew = grew;
-        S.flags = flags;
+        E.tip_q = tip_new;
+        E.v_prev = p.mode == CRACK_PRESCRIBED ? p.v_rel : v;
+        E.K = K;
+        E.v = v;
+        E.r_min = r_min;
+        E.npairs = np;
+        E.grew = grew;
+        E.flags = flags;
         if (commit && p.hist_cap > 0) {
             const int64_t h = S.hist_n % p.hist_cap;
-            hist.K[h] = K;
-            hist.v[h] = v;
-            hist.tip[h] = tip_new;
-            hist.np[h] = np;
+            if (dir > 0) {
+                hist.K[h] = K;
+                hist.v[h] = v;
+                hist.tip[h] = tip_new;
+                hist.np[h] = np;
+            } else {
+                hist.Kl[h] = K;
+                hist.vl[h] = v;
+                hist.tipl[h] = tip_new;
+                hist.npl[h] = np;
+            }
         }
-        S.hist_n += 1;
-        S.decided = 1;
+        E.decided = 1;
     }
     __syncwarp();
 }
@@ -377,26 +413,50 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
 
     if (a.crack_band >= 0 && (band == a.crack_band || band == a.crack_band + 1)) {
         // The crack step of Alg. 1 that follows the previous LBM step, by the
-        // two crack sub-band CTAs that own the next crack link: both reach the
-        // same decision; the one below the crack records it.
+        // two crack sub-band CTAs that own the next link of each end: both
+        // reach the same decision; the one below the crack records it, each
+        // end writing only its own fields of the next state.
+        const int cols = kThreads * N;
         int i_next = a.s_in->i_last + 1;
         i_next = max(i_next, a.s_in->i_first);
         i_next = min(max(i_next, 0), nx - 1);
+        int i_prev = a.s_in->i_first - 1;
+        i_prev = min(i_prev, a.s_in->i_last);
+        i_prev = min(max(i_prev, 0), nx - 1);
+        const bool right_here = cb == i_next / cols;
+        const bool left_here = p.two_tips && cb == i_prev / cols;
         const bool commit = band == a.crack_band;
-        if (cb == i_next / (kThreads * N) && tid < 32) {
+        if ((right_here || left_here) && tid < 32) {
             if (tid == 0) sS = *a.s_in;
             __syncwarp();
-            crack_step_warp<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, commit);
+            const bool pending = !sS.r.decided;   // not yet applied by a deferred crack step
+            if (right_here) crack_step_warp<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, +1, commit);
+            if (left_here) crack_step_warp<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, -1, commit);
             if (tid == 0 && commit) {
+                CrackState *o = a.s_out;
                 const int64_t n = sS.step + 1;
-                sS.step = n;
-                sS.decided = 0;
-                for (int e = 0; e < 4; ++e)
-                    sS.wstar[e] = a.edge[e] == EDGE_DIRICHLET ? load_value(a.load[e], n, (double)p.dt) : 0.0;
-                *a.s_out = sS;
+                if (right_here) {
+                    o->step = n;
+                    o->hist_n = sS.hist_n + (pending ? 1 : 0);
+                    o->i_last = sS.i_last;
+                    if (!p.two_tips) o->i_first = sS.i_first;
+                    o->r = sS.r;
+                    o->r.decided = 0;
+                    for (int e = 0; e < 4; ++e)
+                        o->wstar[e] = a.edge[e] == EDGE_DIRICHLET ? load_value(a.load[e], n, (double)p.dt) : 0.0;
+                }
+                if (left_here) {
+                    o->i_first = sS.i_first;
+                    o->l = sS.l;
+                    o->l.decided = 0;
+                }
                 if (REC) {
                     const int64_t t = n - 1 - *r.n0;
-                    if (t >= 0 && t < r.n_steps) r.i_last[t] = sS.i_last;
+                    if (t >= 0 && t < r.n_steps) {
+                        if (right_here) r.i_last[t] = sS.i_last;
+                        if (right_here && !p.two_tips) r.i_first[t] = sS.i_first;
+                        if (left_here) r.i_first[t] = sS.i_first;
+                    }
                 }
             }
         }
@@ -411,7 +471,8 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
             sS = *a.s_in;
             const int64_t n = sS.step + 1;
             sS.step = n;
-            sS.decided = 1;
+            sS.r.decided = 1;
+            sS.l.decided = 1;
             for (int e = 0; e < 4; ++e)
                 sS.wstar[e] = a.edge[e] == EDGE_DIRICHLET ? load_value(a.load[e], n, (double)p.dt) : 0.0;
             *a.s_out = sS;
@@ -551,8 +612,13 @@ __global__ void finalize_kernel(const FinalizeArgs<T> a)
     __shared__ CrackState sS;
     if (threadIdx.x == 0) sS = *a.st;
     __syncwarp();
-    crack_step_warp<T>(a.p, a.w, a.pitch, a.cut_v, a.hist, sS, true);
-    if (threadIdx.x == 0) *a.st = sS;
+    const bool pending = !sS.r.decided;
+    crack_step_warp<T>(a.p, a.w, a.pitch, a.cut_v, a.hist, sS, +1, true);
+    if (a.p.two_tips) crack_step_warp<T>(a.p, a.w, a.pitch, a.cut_v, a.hist, sS, -1, true);
+    if (threadIdx.x == 0) {
+        if (pending && a.p.mode != CRACK_NONE) sS.hist_n += 1;
+        *a.st = sS;
+    }
 }
 
 template <typename T>

@@ -36,7 +36,7 @@ struct lbm_tape {
     // device memory
     int32_t *s_i, *s_j, *s_off, *s_ent;
     double *target, *resid, *loss_acc, *loss, *part, *grad;
-    int32_t *i_last;
+    int32_t *i_first, *i_last;
     int64_t *n0, *cnt;
     void *m[2], *a;       // adjoint planes, element (0, 0)
     void *mbase[2], *abase;
@@ -67,6 +67,7 @@ RecArgs rec_args(const lbm_tape *t, int acc_loss)
     r.target = t->target;
     r.resid = t->resid;
     r.loss = t->loss_acc;
+    r.i_first = t->i_first;
     r.i_last = t->i_last;
     r.n0 = t->n0;
     r.n_steps = t->T;
@@ -95,7 +96,8 @@ void make_adj_args(const lbm_tape *t, int par, AdjArgs<T> &a)
     a.dt = (T)h->grid.dt;
     a.jc = h->jc;
     a.macro = h->cp.macro;
-    a.i_first = h->init_st.i_first;
+    a.pad0 = 0;
+    a.i_first = t->i_first;
     a.ns = t->ns;
     a.units = h->units;
     a.i_last = t->i_last;
@@ -282,6 +284,7 @@ lbm_status lbm_tape_create(lbm_handle *h, const int32_t *sensors, int32_t n_sens
     const size_t o_lo = off; off = align256(off + 8);
     const size_t o_pt = off; off = align256(off + T * 4 * (size_t)t->slots * 8);
     const size_t o_gr = off; off = align256(off + 4 * T * 8);
+    const size_t o_if = off; off = align256(off + T * 4);
     const size_t o_il = off; off = align256(off + T * 4);
     const size_t o_n0 = off; off = align256(off + 8);
     const size_t o_ct = off; off = align256(off + 16);
@@ -308,6 +311,7 @@ lbm_status lbm_tape_create(lbm_handle *h, const int32_t *sensors, int32_t n_sens
     t->loss = reinterpret_cast<double *>(b + o_lo);
     t->part = reinterpret_cast<double *>(b + o_pt);
     t->grad = reinterpret_cast<double *>(b + o_gr);
+    t->i_first = reinterpret_cast<int32_t *>(b + o_if);
     t->i_last = reinterpret_cast<int32_t *>(b + o_il);
     t->n0 = reinterpret_cast<int64_t *>(b + o_n0);
     t->cnt = reinterpret_cast<int64_t *>(b + o_ct);

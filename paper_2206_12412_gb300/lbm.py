@@ -87,13 +87,16 @@ def lbm_cut_mask(h: int, which: int, dst: np.ndarray):
     _check(load_library().lbm_cut_mask(C.c_void_p(h), which, dst.ctypes.data_as(C.POINTER(C.c_uint32)), dst.size))
 
 
-def lbm_crack_state(h: int, cap: int = 0):
+def lbm_crack_state(h: int, cap: int = 0, left: bool = False):
+    """Crack state and last `cap` records of the right end (left: the left
+    end of a two-tip crack)."""
     st = A.CrackStateT()
     K = np.zeros(max(cap, 1)); v = np.zeros(max(cap, 1))
     tip = np.zeros(max(cap, 1), np.int64); np_ = np.zeros(max(cap, 1), np.int32)
     nw = C.c_int64(0)
     d = C.POINTER(C.c_double)
-    _check(load_library().lbm_crack_state(
+    fn = load_library().lbm_crack_state_left if left else load_library().lbm_crack_state
+    _check(fn(
         C.c_void_p(h), C.byref(st), K.ctypes.data_as(d), v.ctypes.data_as(d),
         tip.ctypes.data_as(C.POINTER(C.c_int64)), np_.ctypes.data_as(C.POINTER(C.c_int32)), cap, C.byref(nw)))
     n = nw.value
@@ -218,6 +221,7 @@ def make_structs(problem: dict, storage: str = "f32"):
         cr.r_min = float(c.get("r_min", 0.0))
         cr.fit_width = float(c.get("fit_width", g.dh))
         cr.hist_cap = int(problem.get("hist_cap", 1 << 16))
+        cr.two_tips = 1 if c.get("two_tips") else 0
     loads = []
     keep = []
     for ld in problem.get("loads", []):
@@ -361,6 +365,16 @@ class Lattice:
         if cap is None:
             cap = int(self.problem.get("hist_cap", 1 << 16))
         return lbm_crack_state(self.h, cap)[1]
+
+    def crack_state_left(self):
+        """State of the left end of a two-tip crack."""
+        st, _ = lbm_crack_state(self.h, 0, left=True)
+        return {k: getattr(st, k) for k, _ in A.CrackStateT._fields_}
+
+    def history_left(self, cap: int | None = None) -> dict:
+        if cap is None:
+            cap = int(self.problem.get("hist_cap", 1 << 16))
+        return lbm_crack_state(self.h, cap, left=True)[1]
 
     def sync(self):
         lbm_sync(self.h)
@@ -611,6 +625,8 @@ class SlabView:
     cut_mask = Lattice.cut_mask
     crack_state = Lattice.crack_state
     history = Lattice.history
+    crack_state_left = Lattice.crack_state_left
+    history_left = Lattice.history_left
     dtype_code = Lattice.dtype_code
 
 
