@@ -64,7 +64,7 @@ class _Config(C.Structure):
         ("load_series", C.POINTER(C.c_double) * 4),
         ("load_n", C.c_int64 * 4),
         ("hist_cap", C.c_int64),
-        ("two_tips", C.c_int32), ("pad_", C.c_int32),
+        ("two_tips", C.c_int32), ("edge_macro", C.c_int32),
     ]
 
 
@@ -96,6 +96,10 @@ def _load():
         lib.orc_get_history.restype = C.c_int64
         lib.orc_get_bpoints.argtypes = [P, C.POINTER(C.c_int32), C.c_int32]
         lib.orc_get_bpoints.restype = C.c_int32
+        lib.orc_get_edge_points.argtypes = [P, C.POINTER(C.c_int32), C.c_int32]
+        lib.orc_get_edge_points.restype = C.c_int32
+        lib.orc_quadratic_through.argtypes = [C.c_double] * 7
+        lib.orc_quadratic_through.restype = C.c_double
         lib.orc_evaluate_K.argtypes = [P, d, C.c_int64, C.c_double, C.c_double, C.POINTER(C.c_int32)]
         lib.orc_evaluate_K.restype = C.c_double
         lib.orc_evaluate_K_left.argtypes = [P, d, C.c_int64, C.c_double, C.c_double, C.POINTER(C.c_int32)]
@@ -141,7 +145,11 @@ def make_config(problem: dict):
         cfg.edge[e] = EDGE[edges[e]]
     cfg.rho, cfg.mu = float(problem.get("rho", 1.0)), float(problem["mu"])
     cfg.omega = float(problem.get("omega", 1.0))
-    cfg.bc_mode = BC[problem.get("bc_mode", "bounceback")]
+    bc = problem.get("bc_mode", "bounceback")
+    # "macroscopic_edges": the macroscopic rule on the crack faces and on the
+    # free and Dirichlet outer edges (Sec. 3.1, Sec. 5.2)
+    cfg.bc_mode = BC["macroscopic" if bc == "macroscopic_edges" else bc]
+    cfg.edge_macro = 1 if bc == "macroscopic_edges" else 0
     cr = problem.get("crack") or {"mode": "none"}
     cfg.crack_mode = CRACK[cr.get("mode", "none")]
     if cfg.crack_mode:
@@ -257,6 +265,17 @@ class Oracle:
         n = self.lib.orc_get_bpoints(self.h, out.ctypes.data_as(C.POINTER(C.c_int32)), cap)
         return out[:n]
 
+    def edge_points(self) -> np.ndarray:
+        """Outer-edge boundary points of the macroscopic rule: rows (site,
+        x_I site, x_II site, rule (0 free, 1 Dirichlet), edge index)."""
+        cap = 2 * (self.nx + self.ny)
+        out = np.zeros((cap, 5), np.int32)
+        n = self.lib.orc_get_edge_points(self.h, out.ctypes.data_as(C.POINTER(C.c_int32)), cap)
+        return out[:n]
+
+    def flags(self) -> int:
+        return int(self.crack()["flags"])
+
     def evaluate_K(self, w: np.ndarray, tip_q: int, r_min: float, fit_width: float):
         w = np.ascontiguousarray(w, dtype=np.float64).reshape(self.ny, self.nx)
         npairs = C.c_int32(0)
@@ -279,6 +298,11 @@ def equilibrium(w: float, wdot: float, g: float) -> np.ndarray:
 
 def macro_poly(sB, sI, sII, wI, wII) -> float:
     return _load().orc_macro_poly(sB, sI, sII, wI, wII)
+
+
+def quadratic_through(s0, v0, s1, v1, s2, v2, x) -> float:
+    """The quadratic polynomial through three points, evaluated at x."""
+    return _load().orc_quadratic_through(s0, v0, s1, v1, s2, v2, x)
 
 
 def segments_intersect(p1, p2, q1, q2) -> bool:

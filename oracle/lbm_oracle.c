@@ -48,7 +48,16 @@
  *     half open; delta = w(above) - w(below), the criterion uses |K|;
  *   - r_min uses the v of the previous step (0 while arrested);
  *   - the tip stops (and stays) at the far edge x = nx dh, where the crack
- *     has severed every link of its row and split the body.
+ *     has severed every link of its row and split the body;
+ *   - with the macroscopic rule on the outer edges too (Sec. 5.2), an edge
+ *     site's polynomial lies along the edge's inward normal (x_I, x_II are
+ *     the next two sites); a corner between two such edges follows its
+ *     Dirichlet edge, or the bottom / top edge when both are of one kind;
+ *     a site next to a severed crack link follows the crack face; the
+ *     Dirichlet value is w*(t_n+1), the time of the unknown w_B; the system
+ *     S w_B = R couples the boundary points only through interior points
+ *     that are boundary points themselves and is solved exactly by sweeps
+ *     until a sweep changes no bit.
  */
 #include <math.h>
 #include <stdint.h>
@@ -83,7 +92,7 @@ typedef struct {
     int64_t load_n[4];
     int64_t hist_cap;
     int32_t two_tips;    /* both ends of the crack grow (the left one towards -x) */
-    int32_t pad_;
+    int32_t edge_macro;  /* the macroscopic rule (Sec. 3.1) on the outer edges too */
 } orc_config;
 
 typedef struct {
@@ -94,6 +103,13 @@ typedef struct {
     double wII[4];
     double sB, sI, sII;  /* distances from the crack face along the normal */
 } orc_bpoint;
+
+/* A boundary point of an outer edge under the macroscopic rule: its site,
+ * the two sites x_I, x_II one and two spacings inside along the inward
+ * normal of edge `edge`, and the rule (0: traction free, 1: Dirichlet). */
+typedef struct {
+    int32_t site, I, II, rule, edge;
+} orc_epoint;
 
 typedef struct {
     orc_config c;
@@ -114,6 +130,8 @@ typedef struct {
     double *hKl, *hvl;
     int64_t *htipl;
     int32_t *hnpl, *hgrowl;
+    orc_epoint *ep;      /* outer-edge boundary points (edge_macro) */
+    int32_t nep;
     orc_bpoint *bl;
     int32_t nbl, capbl;
     uint8_t *is_bpoint;
@@ -250,6 +268,7 @@ void orc_destroy(orc_state *s)
     free(s->w); free(s->w_old); free(s->cut_h); free(s->cut_v);
     free(s->bprev); free(s->bl); free(s->is_bpoint);
     free(s->hK); free(s->hv); free(s->htip); free(s->hnp); free(s->hgrow);
+    free(s->ep);
     free(s->lbprev); free(s->hKl); free(s->hvl); free(s->htipl); free(s->hnpl); free(s->hgrowl);
     free(s->queue); free(s->inq); free(s->visited);
     for (int e = 0; e < 4; ++e) free(s->series[e]);
@@ -257,6 +276,7 @@ void orc_destroy(orc_state *s)
 }
 
 static void add_bpoint(orc_state *s, int32_t k);
+static int build_edge_points(orc_state *s);
 
 /* Cut every link the initial crack segment intersects (brute force over all
  * links) and register both end points as boundary points; they form B_prev
@@ -344,6 +364,10 @@ orc_state *orc_create(const orc_config *cfg)
         /* both tips start their CheckLinks from the initial boundary points */
         memcpy(s->lbprev, s->bprev, sizeof(int32_t) * (size_t)s->nbprev);
         s->nlbprev = s->nbprev;
+    }
+    if (cfg->edge_macro && !build_edge_points(s)) {
+        orc_destroy(s);
+        return NULL;
     }
     return s;
 }
@@ -464,6 +488,131 @@ double orc_macro_poly(double sB, double sI, double sII, double wI, double wII)
     return macro_value(&b, w);
 }
 
+/* The quadratic polynomial through (s0, v0), (s1, v1), (s2, v2), evaluated
+ * at x (Lagrange form).  On a Dirichlet edge (Sec. 3.1) the three points are
+ * the boundary value at the edge and w at x_I and x_II. */
+static double quadratic_through(double s0, double v0, double s1, double v1, double s2, double v2, double x)
+{
+    return v0 * (x - s1) * (x - s2) / ((s0 - s1) * (s0 - s2))
+         + v1 * (x - s0) * (x - s2) / ((s1 - s0) * (s1 - s2))
+         + v2 * (x - s0) * (x - s1) / ((s2 - s0) * (s2 - s1));
+}
+
+double orc_quadratic_through(double s0, double v0, double s1, double v1, double s2, double v2, double x)
+{
+    return quadratic_through(s0, v0, s1, v1, s2, v2, x);
+}
+
+/* The outer-edge boundary points of the macroscopic rule (Sec. 3.1): every
+ * site next to a free or Dirichlet edge.  The outer edges lie half a spacing
+ * outside the edge sites, so along the inward normal x_B, x_I, x_II sit at
+ * the distances 1/2, 3/2, 5/2 dh from the edge and x_I, x_II are lattice
+ * sites (their bilinear interpolation is the site value).  A corner between
+ * two such edges follows the Dirichlet one; when both are of one kind it
+ * follows the bottom or top edge.  Returns 0 where the rule is not defined:
+ * fewer than four sites across a pair of edges (x_II would be a boundary
+ * point of the opposite edge), or a crack within four rows of the bottom or
+ * top edge (a crack face point's x_II would lie on the edge). */
+static int build_edge_points(orc_state *s)
+{
+    const orc_config *c = &s->c;
+    int nx = c->nx, ny = c->ny;
+    int onL = c->edge[ORC_LEFT] != ORC_PERIODIC, onR = c->edge[ORC_RIGHT] != ORC_PERIODIC;
+    int onB = c->edge[ORC_BOTTOM] != ORC_PERIODIC, onT = c->edge[ORC_TOP] != ORC_PERIODIC;
+    if ((onL || onR) && nx < 4) return 0;
+    if ((onB || onT) && ny < 4) return 0;
+    if (c->crack_mode != ORC_CRACK_NONE && (c->jc < 4 || c->jc > ny - 4)) return 0;
+    static const int NX_[4] = {1, -1, 0, 0}, NY_[4] = {0, 0, 1, -1};   /* inward normals */
+    s->ep = xcalloc((size_t)2 * ((size_t)nx + ny), sizeof(orc_epoint));
+    s->nep = 0;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            int eh = (onL && i == 0) ? ORC_LEFT : (onR && i == nx - 1) ? ORC_RIGHT : -1;
+            int ev = (onB && j == 0) ? ORC_BOTTOM : (onT && j == ny - 1) ? ORC_TOP : -1;
+            if (eh < 0 && ev < 0) continue;
+            int e;
+            if (eh >= 0 && ev >= 0)
+                e = (c->edge[eh] == ORC_DIRICHLET && c->edge[ev] != ORC_DIRICHLET) ? eh : ev;
+            else
+                e = ev >= 0 ? ev : eh;
+            orc_epoint *p = &s->ep[s->nep++];
+            p->site = j * nx + i;
+            p->I = (j + NY_[e]) * nx + (i + NX_[e]);
+            p->II = (j + 2 * NY_[e]) * nx + (i + 2 * NX_[e]);
+            p->edge = e;
+            p->rule = c->edge[e] == ORC_DIRICHLET;
+        }
+    return 1;
+}
+
+/* w_B of an outer-edge point from the quadratic along its normal, with the
+ * distances from the edge in units of dh: traction free, the polynomial
+ * a + b s^2 (zero normal derivative at the edge) through x_I and x_II;
+ * Dirichlet, the polynomial through (0, w*), x_I and x_II. */
+static double edge_value(const orc_epoint *p, const double *w, const double *wstar)
+{
+    const double sB = 0.5, sI = 1.5, sII = 2.5;
+    if (p->rule) return quadratic_through(0.0, wstar[p->edge], sI, w[p->I], sII, w[p->II], sB);
+    return orc_macro_poly(sB, sI, sII, w[p->I], w[p->II]);
+}
+
+/* eq. f-macro-bc: the distributions that site k misses (links leaving the
+ * domain or severed) share equally what makes sum_a f^a = (w_B - w(t)) / dt. */
+static void set_missing(orc_state *s, int32_t k, double wB)
+{
+    int miss[4], nmiss = 0;
+    double known = s->f[0][k];
+    for (int a = 1; a < 5; ++a) {
+        uint8_t *cut;
+        int32_t src = link_of(s, k, OPP[a], &cut);
+        if (src < 0 || *cut) miss[nmiss++] = a;
+        else known += s->f[a][k];
+    }
+    double target = (wB - s->w_old[k]) / s->c.dt;
+    for (int q = 0; q < nmiss; ++q) s->f[miss[q]][k] = (target - known) / (double)nmiss;
+    s->w[k] = wB;
+}
+
+/* The macroscopic rule (Sec. 3.1): solve S(t+dt) w_B(t+dt) = R(t+dt) for
+ * the boundary points of the crack faces and, if enabled, the outer edges,
+ * then set their missing distributions by eq. f-macro-bc.  Each point's
+ * equation reads w_B = polynomial(interior values), where an interior value
+ * may itself be a boundary unknown (a corner reads edge points; a crack face
+ * point on an edge column reads edge points).  Jacobi sweeps from the values
+ * of the LBM update: a sweep that changes no bit has met every equation. */
+static void boundary_solve(orc_state *s)
+{
+    int crack_rule = s->c.bc_mode == ORC_BC_MACROSCOPIC;
+    int nb = crack_rule ? s->nbl : 0;
+    int ne = s->c.edge_macro ? s->nep : 0;
+    if (nb + ne == 0) return;
+    size_t n = (size_t)s->c.nx * s->c.ny;
+    double wstar[4];
+    for (int e = 0; e < 4; ++e) wstar[e] = load_value(s, e, s->step + 1);   /* w*(t_n+1) */
+    double *cur = malloc(sizeof(double) * n);
+    double *val = malloc(sizeof(double) * (size_t)(nb + ne + 1));
+    int32_t *site = malloc(sizeof(int32_t) * (size_t)(nb + ne + 1));
+    int m = 0;
+    for (int b = 0; b < nb; ++b) site[m++] = s->bl[b].site;
+    for (int q = 0; q < ne; ++q)
+        if (!(crack_rule && s->is_bpoint[s->ep[q].site])) site[m++] = s->ep[q].site;
+    memcpy(cur, s->w, sizeof(double) * n);
+    int converged = 0;
+    for (int sweep = 0; sweep < 16 && !converged; ++sweep) {
+        int v = 0;
+        for (int b = 0; b < nb; ++b) val[v++] = macro_value(&s->bl[b], cur);
+        for (int q = 0; q < ne; ++q)
+            if (!(crack_rule && s->is_bpoint[s->ep[q].site])) val[v++] = edge_value(&s->ep[q], cur, wstar);
+        converged = 1;
+        for (int q = 0; q < m; ++q)
+            if (memcmp(&val[q], &cur[site[q]], sizeof(double)) != 0) converged = 0;
+        for (int q = 0; q < m; ++q) cur[site[q]] = val[q];
+    }
+    if (!converged) s->flags |= ORC_FLAG_UNSUPPORTED;
+    for (int q = 0; q < m; ++q) set_missing(s, site[q], cur[site[q]]);
+    free(cur); free(val); free(site);
+}
+
 /* -------------------------------------------------------------- LBM step */
 
 static void lbm_step(orc_state *s)
@@ -510,26 +659,8 @@ static void lbm_step(orc_state *s)
         double wdot = s->f[0][k] + s->f[1][k] + s->f[2][k] + s->f[3][k] + s->f[4][k];
         s->w[k] = s->w_old[k] + dt * wdot;
     }
-    /* macroscopic non-lattice-conforming rule on the crack boundary points */
-    if (s->c.bc_mode == ORC_BC_MACROSCOPIC && s->nbl > 0) {
-        double *wB = malloc(sizeof(double) * (size_t)s->nbl);
-        for (int b = 0; b < s->nbl; ++b) wB[b] = macro_value(&s->bl[b], s->w);
-        for (int b = 0; b < s->nbl; ++b) {
-            int32_t k = s->bl[b].site;
-            int miss[4], nmiss = 0;
-            double known = s->f[0][k];
-            for (int a = 1; a < 5; ++a) {
-                uint8_t *cut;
-                int32_t src = link_of(s, k, OPP[a], &cut);
-                if (src < 0 || *cut) miss[nmiss++] = a;
-                else known += s->f[a][k];
-            }
-            double target = (wB[b] - s->w_old[k]) / dt;     /* eq. f-macro-bc */
-            for (int q = 0; q < nmiss; ++q) s->f[miss[q]][k] = (target - known) / (double)nmiss;
-            s->w[k] = wB[b];
-        }
-        free(wB);
-    }
+    /* the macroscopic non-lattice-conforming rule on the boundary points */
+    boundary_solve(s);
     s->step += 1;
 }
 
@@ -797,6 +928,20 @@ int64_t orc_get_history_left(const orc_state *s, double *K, double *v, int64_t *
 
 int64_t orc_left_tip(const orc_state *s) { return s->ltip_q; }
 
+/* The outer-edge boundary points: site, x_I, x_II, rule and edge of each. */
+int32_t orc_get_edge_points(const orc_state *s, int32_t *out5, int32_t cap)
+{
+    int32_t n = 0;
+    for (int q = 0; q < s->nep && n < cap; ++q, ++n) {
+        out5[5 * n + 0] = s->ep[q].site;
+        out5[5 * n + 1] = s->ep[q].I;
+        out5[5 * n + 2] = s->ep[q].II;
+        out5[5 * n + 3] = s->ep[q].rule;
+        out5[5 * n + 4] = s->ep[q].edge;
+    }
+    return s->nep;
+}
+
 int32_t orc_get_bpoints(const orc_state *s, int32_t *sites, int32_t cap)
 {
     int32_t n = s->nbl < cap ? s->nbl : cap;
@@ -973,7 +1118,8 @@ int orc_adjoint(const orc_config *cfg, const double *w0, const double *wd0, int6
                 const int32_t *si, const int32_t *sj, const double *target, double *loss, double *trace,
                 double *dload, double *dw0, double *dwd0)
 {
-    if (T < 1 || ns < 0) return -1;
+    /* the transposed step covers the crack-face rule only, not the outer edges */
+    if (T < 1 || ns < 0 || cfg->edge_macro) return -1;
     orc_state *s = orc_create(cfg);
     if (!s) return -1;
     int nx = s->c.nx, ny = s->c.ny;

@@ -83,6 +83,29 @@ def kcrit_single(scale: int = 1, seed: int = 2, bc_mode: str = "macroscopic") ->
 KCRIT_SINGLE_STEPS = 50000
 
 
+def kcrit_centre_crack(scale: int = 1, bc_mode: str = "macroscopic_edges") -> dict:
+    """The K-criterion example of Sec. 5.2 with L = 64 / scale dh: an 8L x 3L
+    body (512 x 192 sites at scale 1), a centre crack of length L on the line
+    2L above the bottom edge (x in [3.5L, 4.5L]) whose two tips both grow,
+    K_C = 0.0055 mu sqrt(L), r0 = 0.03 L (about 2 dh at scale 1, kept at 2 dh),
+    v_max = 0.85; the bottom edge held at w* = 0, the top edge driven by
+    0.01 L sin(pi t / (8 L / c_s)) for t < 8 L / c_s and 0 afterwards, the
+    lateral edges and the crack faces traction free; the macroscopic rule on
+    every boundary.  Runs KCRIT_CENTRE_STEPS / scale steps (39.5 L / c_s)."""
+    Lh = 64 // scale
+    cs = 0.5
+    p = base_problem(8 * Lh, 3 * Lh, bc_mode=bc_mode, edges=("free", "free", "dirichlet", "dirichlet"), cs=cs)
+    mu = p["mu"]
+    p = with_crack(p, mode="kcrit", y=float(2 * Lh), x_start=3.5 * Lh, x_tip=4.5 * Lh,
+                   K_C=0.0055 * mu * math.sqrt(Lh), v_max=0.85, r0=2.0, two_tips=True)
+    p["loads"] = [{"edge": "bottom", "kind": "zero"},
+                  {"edge": "top", "kind": "halfsine", "amp": 0.01 * Lh, "t": 8.0 * Lh / cs}]
+    return p
+
+
+KCRIT_CENTRE_STEPS = 5050
+
+
 def prescribed_strip(nx: int, ny: int, v_rel: float, *, u0: float = 1e-3, t_ramp: float = 200.0,
                      crack_len: float | None = None, r_min: float = 0.0, bc_mode: str = "macroscopic") -> dict:
     """Strip with a midline edge crack growing at the prescribed speed."""

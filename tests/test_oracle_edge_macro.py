@@ -1,0 +1,360 @@
+"""Pins of the oracle's macroscopic rule on the outer edges (Sec. 3.1, used on
+every boundary of the K-criterion example of Sec. 5.2).
+
+The quadratic through the boundary condition and x_I, x_II (distances 1/2,
+3/2, 5/2 dh from an edge that lies half a spacing outside its sites) gives,
+worked out by hand:
+  traction free, p(s) = a + b s^2:        w_B = (3 w_I - w_II) / 2
+  Dirichlet, p(0) = w*:                   w_B = 8/15 w* + 2/3 w_I - 1/5 w_II
+One step is checked against a numpy restatement in the moment form
+(wdot' = wdot + g lap w, w' = w + dt wdot', then the rule with these numbers
+and wdot_B = (w_B - w_B(t)) / dt); standing waves against their closed forms
+(second-order convergence); a linear profile between two Dirichlet edges
+stays put; long runs stay bounded; the Sec. 5.2 geometry grows both tips
+mirror-symmetrically."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2206_12412_gb300 import workloads as W
+
+FREE_W = (1.5, -0.5)
+DIR_W = (8.0 / 15.0, 2.0 / 3.0, -1.0 / 5.0)
+L, R, B, T = 0, 1, 2, 3
+
+
+def test_quadratic_through_three_points(oracle_mod):
+    rng = np.random.default_rng(0)
+    for _ in range(50):
+        c = rng.standard_normal(3)
+        s = np.sort(rng.uniform(-3, 3, 3))
+        if np.min(np.diff(s)) < 0.1:
+            continue
+        x = rng.uniform(-3, 3)
+        q = lambda t: c[0] + c[1] * t + c[2] * t * t
+        got = oracle_mod.quadratic_through(s[0], q(s[0]), s[1], q(s[1]), s[2], q(s[2]), x)
+        assert got == pytest.approx(q(x), rel=1e-12, abs=1e-12)
+    # the Dirichlet edge weights at x_B
+    for k, wt in enumerate(DIR_W):
+        v = [0.0, 0.0, 0.0]
+        v[k] = 1.0
+        assert oracle_mod.quadratic_through(0.0, v[0], 1.5, v[1], 2.5, v[2], 0.5) == pytest.approx(wt, rel=1e-15)
+    # the traction-free even quadratic through x_I, x_II at x_B
+    assert oracle_mod.macro_poly(0.5, 1.5, 2.5, 1.0, 0.0) == pytest.approx(FREE_W[0], rel=1e-15)
+    assert oracle_mod.macro_poly(0.5, 1.5, 2.5, 0.0, 1.0) == pytest.approx(FREE_W[1], rel=1e-15)
+
+
+def _edge_problem(nx, ny, edges, **crack):
+    p = W.base_problem(nx, ny, bc_mode="macroscopic_edges", edges=edges)
+    if crack:
+        p = W.with_crack(p, **crack)
+    return p
+
+
+def test_edge_point_geometry(oracle_mod):
+    nx, ny = 7, 6
+    o = oracle_mod.Oracle(_edge_problem(nx, ny, ("dirichlet", "free", "dirichlet", "free")))
+    ep = {int(r[0]): tuple(int(x) for x in r[1:]) for r in o.edge_points()}
+    assert len(ep) == 2 * nx + 2 * ny - 4
+    site = lambda i, j: j * nx + i
+    # non-corner points: the next two sites along the inward normal
+    assert ep[site(0, 3)] == (site(1, 3), site(2, 3), 1, L)
+    assert ep[site(nx - 1, 2)] == (site(nx - 2, 2), site(nx - 3, 2), 0, R)
+    assert ep[site(4, 0)] == (site(4, 1), site(4, 2), 1, B)
+    assert ep[site(4, ny - 1)] == (site(4, ny - 2), site(4, ny - 3), 0, T)
+    # corners: the Dirichlet edge; two of one kind: bottom / top
+    assert ep[site(0, 0)] == (site(0, 1), site(0, 2), 1, B)              # left D, bottom D
+    assert ep[site(nx - 1, 0)] == (site(nx - 1, 1), site(nx - 1, 2), 1, B)  # right free, bottom D
+    assert ep[site(0, ny - 1)] == (site(1, ny - 1), site(2, ny - 1), 1, L)  # left D, top free
+    assert ep[site(nx - 1, ny - 1)][3] == T                                # both free
+    o.close()
+    # periodic edges carry no boundary points
+    o = oracle_mod.Oracle(_edge_problem(5, 6, ("periodic", "periodic", "free", "dirichlet")))
+    assert sorted(int(r[4]) for r in o.edge_points()) == [B] * 5 + [T] * 5
+    o.close()
+
+
+@pytest.mark.parametrize("shape,edges,crack", [
+    ((4, 9), ("free", "free", "dirichlet", "dirichlet"), None),
+    ((9, 3), ("periodic", "periodic", "free", "free"), None),
+    ((40, 20), ("free", "free", "dirichlet", "dirichlet"), dict(mode="stationary", y=3.0, x_tip=10.0)),
+    ((40, 20), ("free", "free", "dirichlet", "dirichlet"), dict(mode="stationary", y=17.0, x_tip=10.0)),
+])
+def test_rejected_where_the_rule_is_undefined(oracle_mod, shape, edges, crack):
+    p = _edge_problem(*shape, edges, **(crack or {}))
+    if shape == (4, 9):
+        oracle_mod.Oracle(p).close()        # four sites across is enough
+        p = _edge_problem(3, 9, edges)
+    with pytest.raises(ValueError):
+        oracle_mod.Oracle(p)
+    with pytest.raises(Exception):
+        oracle_mod.adjoint(_edge_problem(20, 20, edges), 2, [(5, 5)], np.zeros((2, 1)))
+
+
+def _numpy_step(p, w, wd, cut_v, wstar_next, jc=None):
+    """One step in the moment form with the macroscopic rule on the edges and
+    (if jc) on the faces of a horizontal crack whose severed V links (row
+    jc - 1) are cut_v[jc - 1]; the exact solution of the boundary system by
+    ordering: crack face points off the edge columns and edge points first,
+    corners and crack face points on edge columns last."""
+    ny, nx = w.shape
+    g = p["mu"] / p["rho"] * p["dt"] ** 2 / p["dh"] ** 2
+    dt = p["dt"]
+    # neighbour values, bounce-back (own value) across severed links; edge
+    # sites' own updates are replaced below, so their missing links do not matter
+    up = np.vstack([w[1:], w[-1:]])
+    dn = np.vstack([w[:1], w[:-1]])
+    lf = np.hstack([w[:, :1], w[:, :-1]])
+    rt = np.hstack([w[:, 1:], w[:, -1:]])
+    if jc is not None:
+        cols = np.nonzero(cut_v[jc - 1])[0]
+        up[jc - 1, cols] = w[jc - 1, cols]
+        dn[jc, cols] = w[jc, cols]
+    wd1 = wd + g * (up + dn + lf + rt - 4 * w)
+    w1 = w + dt * wd1
+    face = np.zeros_like(w, bool)
+    if jc is not None:
+        face[jc - 1, cols] = True
+        face[jc, cols] = True
+
+    def free(a, b):
+        return FREE_W[0] * a + FREE_W[1] * b
+
+    def dirichlet(ws, a, b):
+        return DIR_W[0] * ws + DIR_W[1] * a + DIR_W[2] * b
+
+    E = p["edges"]
+
+    def rule(e, a, b):
+        return dirichlet(wstar_next[e], a, b) if E[e] == "dirichlet" else free(a, b)
+
+    new = w1.copy()
+    # crack face points (column-local polynomial away from the crack)
+    if jc is not None:
+        for i in cols:
+            new[jc, i] = free(w1[jc + 1, i], w1[jc + 2, i])
+            new[jc - 1, i] = free(w1[jc - 2, i], w1[jc - 3, i])
+    # non-corner edge points (not crack face points)
+    for j in range(1, ny - 1):
+        if not face[j, 0]:
+            new[j, 0] = rule(L, new[j, 1], new[j, 2])
+        if not face[j, nx - 1]:
+            new[j, nx - 1] = rule(R, new[j, nx - 2], new[j, nx - 3])
+    for i in range(1, nx - 1):
+        new[0, i] = rule(B, new[1, i], new[2, i])
+        new[ny - 1, i] = rule(T, new[ny - 2, i], new[ny - 3, i])
+    # crack face points on the edge columns read the edge points above / below
+    if jc is not None:
+        for i in cols:
+            if i in (0, nx - 1):
+                new[jc, i] = free(new[jc + 1, i], new[jc + 2, i])
+                new[jc - 1, i] = free(new[jc - 2, i], new[jc - 3, i])
+    # corners
+    for (i, j, eh, ev, si, sj) in ((0, 0, L, B, 1, 1), (nx - 1, 0, R, B, -1, 1),
+                                   (0, ny - 1, L, T, 1, -1), (nx - 1, ny - 1, R, T, -1, -1)):
+        if E[eh] == "dirichlet" and E[ev] != "dirichlet":
+            new[j, i] = rule(eh, new[j, i + si], new[j, i + 2 * si])
+        else:
+            new[j, i] = rule(ev, new[j + sj, i], new[j + 2 * sj, i])
+    bnd = np.zeros_like(w, bool)
+    bnd[0, :] = bnd[-1, :] = bnd[:, 0] = bnd[:, -1] = True
+    bnd |= face
+    wd_new = np.where(bnd, (new - w) / dt, wd1)
+    return new, wd_new
+
+
+@pytest.mark.parametrize("edges", [("dirichlet", "free", "dirichlet", "free"), ("free", "free", "free", "free"),
+                                   ("dirichlet", "dirichlet", "dirichlet", "dirichlet"),
+                                   ("free", "dirichlet", "free", "dirichlet")])
+def test_one_step_against_the_moment_form(oracle_mod, edges):
+    nx, ny = 11, 9
+    p = _edge_problem(nx, ny, edges)
+    amps = {L: 0.3, R: -0.7, B: 0.45, T: 1.1}
+    # linear ramps: w*(t_1) = amp dt / t_ramp differs from w*(t_0) = 0
+    p["loads"] = [{"edge": n, "kind": "linear", "amp": amps[e], "t": 8.0}
+                  for e, n in enumerate(("left", "right", "bottom", "top")) if edges[e] == "dirichlet"]
+    wstar_next = [amps[e] / 8.0 for e in range(4)]
+    w0, wd0 = W.random_state(nx, ny, seed=3)
+    o = oracle_mod.Oracle(p)
+    o.set_fields(w0, wd0)
+    o.step(1)
+    w1, wd1 = o.fields()
+    ref_w, ref_wd = _numpy_step(p, w0, wd0, None, wstar_next)
+    np.testing.assert_allclose(w1, ref_w, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(wd1, ref_wd, rtol=0, atol=1e-13)
+    assert o.flags() == 0
+    # a second step from the first (the old boundary values are rule values)
+    o.step(1)
+    w2, wd2 = o.fields()
+    wstar2 = [amps[e] * 2.0 / 8.0 for e in range(4)]
+    ref_w2, ref_wd2 = _numpy_step(p, ref_w, ref_wd, None, wstar2)
+    np.testing.assert_allclose(w2, ref_w2, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(wd2, ref_wd2, rtol=0, atol=1e-13)
+    o.close()
+
+
+@pytest.mark.parametrize("x_start,x_tip", [(0.0, 7.3), (1.0, 7.3), (3.2, 40.0), (1.2, 40.0)])
+def test_crack_faces_meet_the_edges(oracle_mod, x_start, x_tip):
+    """A crack that reaches an edge column: its face points there read the
+    edge points above and below (the coupled boundary system); an edge point
+    next to the crack's first severed column reads the crack face points."""
+    nx, ny, jc = 40, 14, 6
+    p = _edge_problem(nx, ny, ("free", "free", "dirichlet", "dirichlet"),
+                      mode="stationary", y=float(jc), x_start=x_start, x_tip=x_tip)
+    p["loads"] = [{"edge": "top", "kind": "const", "amp": 0.2}, {"edge": "bottom", "kind": "const", "amp": -0.1}]
+    w0, wd0 = W.random_state(nx, ny, seed=5)
+    o = oracle_mod.Oracle(p)
+    o.set_fields(w0, wd0)
+    _, cv = o.cuts()
+    o.step(1)
+    w1, wd1 = o.fields()
+    ref_w, ref_wd = _numpy_step(p, w0, wd0, cv.astype(bool), [0.0, 0.0, -0.1, 0.2], jc=jc)
+    np.testing.assert_allclose(w1, ref_w, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(wd1, ref_wd, rtol=0, atol=1e-13)
+    o.close()
+
+
+def test_linear_profile_between_dirichlet_edges_is_steady(oracle_mod):
+    nx, ny = 12, 20
+    p = _edge_problem(nx, ny, ("free", "free", "dirichlet", "dirichlet"))
+    a, b = -0.3, 0.05
+    p["loads"] = [{"edge": "bottom", "kind": "const", "amp": a}, {"edge": "top", "kind": "const", "amp": a + b * ny}]
+    y = (np.arange(ny) + 0.5)[:, None] * np.ones((1, nx))
+    o = oracle_mod.Oracle(p)
+    o.set_fields(a + b * y, np.zeros((ny, nx)))
+    o.step(300)
+    w, wd = o.fields()
+    np.testing.assert_allclose(w, a + b * y, rtol=0, atol=1e-13)
+    assert np.abs(wd).max() < 1e-13
+    o.close()
+
+
+def _standing_wave_error(oracle_mod, n, axis, bc_mode):
+    """max |w - exact| after half a period of the lowest mode across n sites:
+    Dirichlet w* = 0 on both edges (sin mode) across y, or traction-free
+    edges (cos mode) across x."""
+    cs = 0.5
+    if axis == "y":
+        p = W.base_problem(4, n, bc_mode=bc_mode, edges=("periodic", "periodic", "dirichlet", "dirichlet"))
+        s = (np.arange(n) + 0.5) / n
+        prof = np.sin(np.pi * s)[:, None] * np.ones((1, 4))
+    else:
+        p = W.base_problem(n, 4, bc_mode=bc_mode, edges=("free", "free", "periodic", "periodic"))
+        s = (np.arange(n) + 0.5) / n
+        prof = np.ones((4, 1)) * np.cos(np.pi * s)[None, :]
+    omega = cs * np.pi / n
+    steps = n * 2   # t = n / c_s: half a period
+    # the scheme's wdot is the rate over the step that ends at the current
+    # time: start with w(0) and wdot(-dt/2) of w = prof cos(omega t)
+    o = oracle_mod.Oracle(p)
+    o.set_fields(prof, omega * prof * np.sin(omega * 0.5))
+    o.step(steps)
+    w, _ = o.fields()
+    exact = prof * math.cos(omega * steps)
+    o.close()
+    return np.abs(w - exact).max()
+
+
+@pytest.mark.parametrize("axis", ["y", "x"])
+def test_standing_waves_converge_at_second_order(oracle_mod, axis):
+    errs = [_standing_wave_error(oracle_mod, n, axis, "macroscopic_edges") for n in (16, 32, 64)]
+    ratios = [errs[0] / errs[1], errs[1] / errs[2]]
+    print(axis, errs, ratios)
+    assert errs[2] < 2e-3
+    assert min(ratios) > 3.0
+
+
+@pytest.mark.parametrize("edges", [("free", "free", "dirichlet", "dirichlet"), ("free", "free", "free", "free"),
+                                   ("dirichlet", "dirichlet", "dirichlet", "dirichlet"),
+                                   ("dirichlet", "free", "free", "dirichlet")])
+def test_long_runs_stay_bounded(oracle_mod, edges):
+    nx, ny = 36, 30
+    p = _edge_problem(nx, ny, edges)
+    w0, wd0 = W.random_state(nx, ny, seed=9)
+    o = oracle_mod.Oracle(p)
+    o.set_fields(w0, wd0)
+    o.step(3000)
+    w, wd = o.fields()
+    assert np.all(np.isfinite(w)) and np.abs(w).max() < 10 * (np.abs(w0).max() + 3000 * np.abs(wd0).max())
+    assert np.abs(wd).max() < 10 * (np.abs(wd0).max() + np.abs(w0).max())
+    assert o.flags() == 0
+    o.close()
+
+
+def test_corner_reading_is_immaterial(oracle_mod):
+    """The rules of two edges meeting at a corner are extrapolations along
+    different axes of values that the other edge's rule made, so they commute
+    -- either choice gives the corner the same value -- unless both edges are
+    Dirichlet with different values (then the bottom / top rule is taken)."""
+    nx, ny = 10, 8
+    edges = ("dirichlet", "free", "dirichlet", "free")
+    p = _edge_problem(nx, ny, edges)
+    p["loads"] = [{"edge": "left", "kind": "const", "amp": 0.4}, {"edge": "bottom", "kind": "const", "amp": -0.2}]
+    w0, wd0 = W.random_state(nx, ny, seed=11)
+    new, _ = _numpy_step(p, w0, wd0, None, [0.4, 0.0, -0.2, 0.0])
+    ws = {L: 0.4, B: -0.2}
+
+    def rule(e, a, b):
+        return DIR_W[0] * ws[e] + DIR_W[1] * a + DIR_W[2] * b if edges[e] == "dirichlet" else FREE_W[0] * a + FREE_W[1] * b
+
+    for (i, j, eh, ev, si, sj) in ((0, 0, L, B, 1, 1), (nx - 1, 0, R, B, -1, 1),
+                                   (0, ny - 1, L, T, 1, -1), (nx - 1, ny - 1, R, T, -1, -1)):
+        along_h = rule(eh, new[j, i + si], new[j, i + 2 * si])
+        along_v = rule(ev, new[j + sj, i], new[j + 2 * sj, i])
+        if edges[eh] == edges[ev] == "dirichlet":
+            assert abs(along_h - along_v) > 1e-3          # 8/15 * 8/15 (w*_L - w*_B) apart
+            assert new[j, i] == along_v
+        else:
+            assert along_h == pytest.approx(along_v, rel=1e-12, abs=1e-15)
+
+
+@pytest.fixture(scope="module")
+def centre_crack_run(oracle_mod):
+    p = W.kcrit_centre_crack()
+    o = oracle_mod.Oracle(p)
+    o.step(W.KCRIT_CENTRE_STEPS)
+    out = (p, o.history(), o.history_left(), o.crack(), o.fields())
+    o.close()
+    return out
+
+
+def _phases(grew, gap):
+    """Growth phases: runs of growing steps separated by more than `gap`."""
+    g = np.nonzero(grew)[0]
+    if g.size == 0:
+        return []
+    br = np.nonzero(np.diff(g) > gap)[0]
+    return list(zip(np.r_[g[0], g[br + 1]], np.r_[g[br], g[-1]]))
+
+
+def test_centre_crack_example_sec_5_2(centre_crack_run):
+    """The K-criterion example of Sec. 5.2 (512 x 192, L = 64 dh): both tips
+    start to grow on the first wave, K stays near K_C while a tip grows, growth
+    stops when the wave has passed, and a later wave makes the tips grow again
+    with K a little further above K_C and a higher speed; the two tips stay
+    mirror images."""
+    p, h, hl, info, (w, wd) = centre_crack_run
+    n = W.KCRIT_CENTRE_STEPS
+    Lh, cs, K_C = 64, 0.5, p["crack"]["K_C"]
+    t = np.arange(1, n + 1) * cs / Lh          # time in units of L / c_s
+    assert info["flags"] == 0 and np.all(np.isfinite(w))
+    # mirror symmetry of the two tips
+    np.testing.assert_array_equal(h["grew"][:n], hl["grew"][:n])
+    assert np.abs((512 * 2**32 - hl["tip_q"][:n]) - h["tip_q"][:n]).max() <= 16
+    phases = _phases(h["grew"][:n], gap=int(2 * Lh / cs))   # gaps of more than 2 L / c_s
+    assert len(phases) >= 2
+    (a0, b0), (a1, b1) = phases[0], phases[1]
+    # the first wave: the pulse reaches the crack after about 1 L / c_s
+    assert 1.0 < t[a0] < 2.5 and t[b0] < 4.0
+    # growth only above K_C (eq. v-tanh), and K hovers near K_C while growing
+    grow = h["grew"][:n].astype(bool)
+    ratio = np.abs(h["K"][:n][grow]) / K_C
+    assert ratio.min() > 1.0 and np.median(ratio) < 1.1 and ratio.max() < 1.3
+    # a quiet spell, then growth again at a higher speed
+    assert t[a1] - t[b0] > 5.0
+    assert h["v"][a1:b1 + 1].max() > h["v"][a0:b0 + 1].max()
+    assert np.abs(h["K"][a1:b1 + 1]).max() > np.abs(h["K"][a0:b0 + 1]).max()
+    # the crack grew but stayed inside the body
+    da = (h["tip_q"][n - 1] / 2**32 - 4.5 * Lh) / Lh
+    assert 0.1 < da < 2.0
