@@ -70,8 +70,13 @@ enum { LBM_FORM_MOMENT = 0 };
  * wdot * scale, see lbm_set_wd_scale), FP32 arithmetic; 12 bytes per site
  * update instead of 16.  Also the dtype codes of field exchange. */
 enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F32_WD_BF16 = 2, LBM_F32_WD_F16 = 3 };
-/* treatment of the crack faces */
-enum { LBM_BC_BOUNCEBACK = 0, LBM_BC_MACROSCOPIC = 1 };
+/* treatment of the boundaries.  BOUNCEBACK: link-local rules on the crack
+ * faces and the outer edges.  MACROSCOPIC: the macroscopic rule of Sec. 3.1
+ * on the crack faces, link-local rules on the outer edges.
+ * MACROSCOPIC_EDGES: the macroscopic rule on the crack faces and on every
+ * free or Dirichlet outer edge (all boundaries, as in Sec. 5.2), see
+ * lbm_lattice. */
+enum { LBM_BC_BOUNCEBACK = 0, LBM_BC_MACROSCOPIC = 1, LBM_BC_MACROSCOPIC_EDGES = 2 };
 /* crack modes (Alg. 1 "criterion") */
 enum { LBM_CRACK_NONE = 0, LBM_CRACK_STATIONARY = 1, LBM_CRACK_PRESCRIBED = 2, LBM_CRACK_KCRIT = 3 };
 /* loading kinds of a Dirichlet edge */
@@ -94,8 +99,23 @@ typedef struct lbm_grid {
 
 /* Lattice model.  velocity_set = LBM_D2Q5, form = LBM_FORM_MOMENT,
  * omega = dt / tau = 1 (the paper fixes tau = dt; Sec. 3).  storage is an
- * LBM_F64 / LBM_F32 / LBM_F32_WD_* code; bc_mode selects the crack-face
- * treatment. */
+ * LBM_F64 / LBM_F32 / LBM_F32_WD_* code; bc_mode an LBM_BC_* code.
+ *
+ * LBM_BC_MACROSCOPIC_EDGES (Sec. 3.1, eq. f-macro-bc): after every LBM
+ * update the boundary values w_B(t + dt) solve S w_B = R, each boundary
+ * point's equation being a quadratic polynomial along the inward normal
+ * evaluated at x_B.  An outer edge lies half a spacing outside its sites, so
+ * x_B, x_I, x_II sit at 1/2, 3/2, 5/2 dh from it and x_I, x_II are the next
+ * two sites: a traction-free edge gives w_B = (3 w_I - w_II) / 2, a
+ * Dirichlet edge w_B = 8/15 w*(t + dt) + 2/3 w_I - 1/5 w_II.  A corner
+ * between two such edges follows its Dirichlet edge, else the bottom / top
+ * edge (the two choices differ only between two Dirichlet edges); a
+ * site next to a severed crack link follows the crack face, whose x_I, x_II
+ * on an edge column are edge points themselves.  wdot_B = (w_B(t + dt) -
+ * w_B(t)) / dt.  One extra small kernel per time step applies it.  Needs at
+ * least 4 sites across each non-periodic pair of edges and a crack line at
+ * least 4 dh from the bottom and top edges; not available to lbm_batch_*,
+ * lbm_decomp_* or lbm_tape_* (their create calls reject it). */
 typedef struct lbm_lattice {
     int32_t velocity_set;
     int32_t form;
@@ -111,7 +131,8 @@ typedef struct lbm_material {
 } lbm_material;
 
 /* Straight crack along +x on the line y (a multiple of dh, at least 3 dh from
- * the bottom and top edges), from x_start to x_tip (physical units).
+ * the bottom and top edges, 4 dh with LBM_BC_MACROSCOPIC_EDGES), from
+ * x_start to x_tip (physical units).
  * v_rel: prescribed relative speed adot / c_s (LBM_CRACK_PRESCRIBED).
  * K_C, v_max: K-criterion and eq. v-tanh (LBM_CRACK_KCRIT).
  * r0: eq. r(v); r_min > 0 overrides it with a fixed evaluation distance.

@@ -12,7 +12,7 @@ STATUS_NAMES = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR
 EDGE = {"free": 0, "dirichlet": 1, "periodic": 2}
 EDGE_INDEX = {"left": 0, "right": 1, "bottom": 2, "top": 3}
 STORAGE = {"f64": 0, "f32": 1, "f32_bf16": 2, "f32_f16": 3}
-BC = {"bounceback": 0, "macroscopic": 1}
+BC = {"bounceback": 0, "macroscopic": 1, "macroscopic_edges": 2}
 CRACK = {"none": 0, "stationary": 1, "prescribed": 2, "kcrit": 3}
 LOAD = {"zero": 0, "linear": 1, "sin2": 2, "halfsine": 3, "series": 4, "const": 5}
 FIELD = {"w": 0, "wdot": 1}

@@ -70,7 +70,9 @@ cudaError_t enqueue_step_t(const lbm_handle *h, int par, cudaStream_t s)
 {
     StepArgs<T, D> a;
     make_step_args(h, par, a);
-    return launch_step(a, h->n_bands, s);
+    cudaError_t e = launch_step(a, h->n_bands, s);
+    if (e == cudaSuccess && h->edge_macro) e = launch_edge_rule(a, s);
+    return e;
 }
 
 cudaError_t enqueue_step(const lbm_handle *h, int par, cudaStream_t s)
@@ -336,8 +338,18 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
     if (lattice->form != LBM_FORM_MOMENT) return fail(LBM_ERR_ARG, "only the moment form is built");
     if (lattice->omega != 1.0) return fail(LBM_ERR_ARG, "omega = dt/tau must be 1 (tau = dt)");
     if (lattice->storage < LBM_F64 || lattice->storage > LBM_F32_WD_F16) return fail(LBM_ERR_ARG, "unknown storage");
-    if (lattice->bc_mode != LBM_BC_BOUNCEBACK && lattice->bc_mode != LBM_BC_MACROSCOPIC)
-        return fail(LBM_ERR_ARG, "unknown crack-face mode");
+    if (lattice->bc_mode < LBM_BC_BOUNCEBACK || lattice->bc_mode > LBM_BC_MACROSCOPIC_EDGES)
+        return fail(LBM_ERR_ARG, "unknown boundary mode");
+    const bool macro_faces = lattice->bc_mode != LBM_BC_BOUNCEBACK;
+    const bool macro_edges = lattice->bc_mode == LBM_BC_MACROSCOPIC_EDGES;
+    if (macro_edges) {
+        // x_II of an edge point must not be a boundary point of the opposite edge
+        if (slab) return fail(LBM_ERR_ARG, "the macroscopic rule on the outer edges is not built for row slabs");
+        if (grid->edge[LBM_LEFT] != LBM_EDGE_PERIODIC && grid->nx < 4)
+            return fail(LBM_ERR_ARG, "the macroscopic edge rule needs nx >= 4 between free or Dirichlet edges");
+        if (grid->edge[LBM_BOTTOM] != LBM_EDGE_PERIODIC && grid->ny < 4)
+            return fail(LBM_ERR_ARG, "the macroscopic edge rule needs ny >= 4 between free or Dirichlet edges");
+    }
     if (!(material->rho > 0.0) || !(material->mu > 0.0) || !std::isfinite(material->rho) || !std::isfinite(material->mu))
         return fail(LBM_ERR_ARG, "rho and mu must be positive and finite");
     const double cs = std::sqrt(material->mu / material->rho);
@@ -357,14 +369,14 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
         if (!std::isfinite(yj) || std::fabs(yj - std::nearbyint(yj)) > 1e-9)
             return fail(LBM_ERR_ARG, "the crack line y must be a multiple of dh (between two rows)");
         jc = (int32_t)std::nearbyint(yj);
-        const int margin = lattice->bc_mode == LBM_BC_MACROSCOPIC ? 3 : 1;
+        const int margin = macro_edges ? 4 : (macro_faces ? 3 : 1);
         if (jc < margin || jc > grid->ny - margin)
             return fail(LBM_ERR_ARG, "the crack line is too close to the bottom or top edge");
         if (!(cr.x_start >= 0.0) || !(cr.x_tip >= cr.x_start)) return fail(LBM_ERR_ARG, "need 0 <= x_start <= x_tip");
         start_q = llrint(cr.x_start / grid->dh * 4294967296.0);
         tip_q = llrint(cr.x_tip / grid->dh * 4294967296.0);
         if (tip_q >= clamp_q) return fail(LBM_ERR_ARG, "the initial tip must lie left of x = nx dh");
-        if (lattice->bc_mode == LBM_BC_MACROSCOPIC && grid->edge[LBM_LEFT] == LBM_EDGE_PERIODIC)
+        if (macro_faces && grid->edge[LBM_LEFT] == LBM_EDGE_PERIODIC)
             return fail(LBM_ERR_ARG, "macroscopic crack faces need non-periodic left/right edges");
         if (cr.mode == LBM_CRACK_PRESCRIBED && !(cr.v_rel >= 0.0 && cr.v_rel < 1.0))
             return fail(LBM_ERR_ARG, "prescribed v_rel must lie in [0, 1)");
@@ -372,15 +384,22 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
         if (cr.mode == LBM_CRACK_KCRIT && !(cr.K_C > 0.0 && cr.v_max >= 0.0 && cr.v_max < 1.0))
             return fail(LBM_ERR_ARG, "K-criterion needs K_C > 0 and 0 <= v_max < 1");
         if (!(cr.r_min > 0.0) && !(cr.r0 >= 0.0)) return fail(LBM_ERR_ARG, "r0 must be >= 0");
-        if (lattice->bc_mode == LBM_BC_MACROSCOPIC) {
-            // with the macroscopic crack-face rule a single intact column between
-            // the crack and a free edge is an unstable ligament (a mode localised
-            // there grows without bound); two or more columns, or none, are fine
+        if (macro_faces) {
+            // With the macroscopic crack-face rule a narrow intact ligament between
+            // a crack end and an edge carries a mode that grows without bound: one
+            // column at a link-local free edge, two columns at a link-local
+            // Dirichlet edge or at any edge under the macroscopic edge rule.  None,
+            // or five columns and more, are fine.
             const int64_t half = qone / 2;
             const int64_t first = -floor_div(-(start_q - half), qone), last = floor_div(tip_q - half, qone);
-            if (last >= first && ((first == 1 && grid->edge[LBM_LEFT] == LBM_EDGE_FREE) ||
-                                  (last == grid->nx - 2 && grid->edge[LBM_RIGHT] == LBM_EDGE_FREE)))
-                return fail(LBM_ERR_ARG, "macroscopic crack faces: the crack leaves one intact column at a free edge");
+            auto unstable = [&](int64_t width, int32_t kind) {
+                if (kind == LBM_EDGE_PERIODIC) return false;
+                if (macro_edges) return width == 2;
+                return width == (kind == LBM_EDGE_FREE ? 1 : 2);
+            };
+            if (last >= first && (unstable(first, grid->edge[LBM_LEFT]) ||
+                                  unstable(grid->nx - 1 - last, grid->edge[LBM_RIGHT])))
+                return fail(LBM_ERR_ARG, "macroscopic crack faces: the crack leaves an unstable narrow ligament at an edge");
         }
         if (!(cr.fit_width > 0.0)) cr.fit_width = grid->dh;
         if (cr.hist_cap <= 0) cr.hist_cap = kDefaultHistCap;
@@ -526,7 +545,8 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
     cp.jc = jc;
     cp.nx = grid->nx;
     cp.ny = grid->ny;
-    cp.macro = lattice->bc_mode == LBM_BC_MACROSCOPIC;
+    cp.macro = macro_faces;
+    h->edge_macro = macro_edges;
     cp.words = h->words;
     cp.two_tips = cr.two_tips ? 1 : 0;
     cp.mu = material->mu;
@@ -1108,6 +1128,7 @@ lbm_status lbm_batch_create(lbm_handle *const *handles, int32_t n, int32_t band_
         if (!h) return fail(LBM_ERR_ARG, "a lattice handle is NULL");
         if (h->sticky != LBM_OK) return fail(h->sticky, "a lattice is in an error state");
         if (h->lat.storage != handles[0]->lat.storage) return fail(LBM_ERR_ARG, "all lattices need the same storage");
+        if (h->edge_macro) return fail(LBM_ERR_ARG, "the batched step has no macroscopic rule on the outer edges");
         if (h->stream != handles[0]->stream) return fail(LBM_ERR_ARG, "all lattices need the same stream");
         if (h->parity != handles[0]->parity) return fail(LBM_ERR_STATE, "all lattices need the same number of steps");
         for (int k = 0; k < i; ++k)

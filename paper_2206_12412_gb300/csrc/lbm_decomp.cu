@@ -100,6 +100,8 @@ lbm_status lbm_decomp_create(const lbm_grid *grid, const lbm_lattice *lattice, c
     *out = nullptr;
     if (!grid || !lattice || !material) return fail(LBM_ERR_ARG, "grid, lattice and material are required");
     if (n_ranks < 1) return fail(LBM_ERR_ARG, "n_ranks must be >= 1");
+    if (lattice->bc_mode == LBM_BC_MACROSCOPIC_EDGES)
+        return fail(LBM_ERR_ARG, "the macroscopic rule on the outer edges is not built for row slabs");
     if (n_loads < 0 || (n_loads > 0 && !loads)) return fail(LBM_ERR_ARG, "bad loads array");
     for (int e = 0; e < 4; ++e)
         if (grid->edge[e] < LBM_EDGE_FREE || grid->edge[e] > LBM_EDGE_PERIODIC) return fail(LBM_ERR_ARG, "unknown edge kind");
@@ -111,7 +113,7 @@ lbm_status lbm_decomp_create(const lbm_grid *grid, const lbm_lattice *lattice, c
         if (!std::isfinite(yj) || std::fabs(yj - std::nearbyint(yj)) > 1e-9)
             return fail(LBM_ERR_ARG, "the crack line y must be a multiple of dh (between two rows)");
         jc = (int32_t)std::nearbyint(yj);
-        hh = lattice->bc_mode == LBM_BC_MACROSCOPIC ? 3 : 1;
+        hh = lattice->bc_mode != LBM_BC_BOUNCEBACK ? 3 : 1;
     }
     std::vector<int32_t> rs((size_t)n_ranks + 1);
     if (row_start) {

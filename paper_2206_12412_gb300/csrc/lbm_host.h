@@ -28,6 +28,7 @@ struct lbm_handle {
     int64_t pitch;       // elements per padded row
     int32_t words;       // 32-bit mask words per row
     int32_t jc;          // crack line y = jc dh
+    bool edge_macro;     // the macroscopic rule on the outer edges (one more kernel per step)
     // step kernel shape
     int32_t ncb;         // column blocks of kThreads vectors
     int32_t n_bands, band_rows, crack_band, sms, bps;

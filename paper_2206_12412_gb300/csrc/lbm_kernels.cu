@@ -676,6 +676,143 @@ cudaError_t launch_wstar(CrackState *st, const LoadDesc *load, const int32_t *ed
     return cudaGetLastError();
 }
 
+// ------------------------------------------- macroscopic rule on the edges
+//
+// The macroscopic rule (Sec. 3.1) on the free and Dirichlet outer edges, run
+// after the step kernel on the fields it wrote.  The boundary system S w_B =
+// R couples the boundary points only through interior points that are
+// boundary points themselves, in two levels:
+//   level 1: a non-corner edge point reads x_I, x_II along its edge's inward
+//            normal: bulk sites or crack-face points off the edge columns,
+//            all final after the step kernel;
+//   level 2: a corner reads two points of the other edge, and a crack-face
+//            point on an edge column reads the two edge points above or
+//            below it; each such read is a level-1 value that the thread
+//            computes itself.
+// So one thread per edge site solves its own equation exactly and no thread
+// reads a site another thread writes.  Polynomials, with the edge half a
+// spacing outside the sites (x_B, x_I, x_II at 1/2, 3/2, 5/2 dh): traction
+// free w_B = 1.5 w_I - 0.5 w_II; Dirichlet w_B = 8/15 w* + 2/3 w_I - 1/5 w_II
+// with w* at the new time level; a corner follows its Dirichlet edge, else
+// the bottom / top one.  wdot_B = (w_B - w_B(t)) / dt, and the pad images
+// of the site are refreshed.
+
+template <typename T>
+struct EdgeRule {
+    const T *wn;          // the new fields
+    int64_t pitch;
+    int32_t dir[4];       // 1: Dirichlet edge
+    T ws[4];              // w* at the new time level
+    __device__ __forceinline__ T w(int i, int j) const { return wn[(int64_t)j * pitch + i]; }
+    __device__ __forceinline__ T rule(int e, T wI, T wII) const
+    {
+        if (dir[e])
+            return (T)(8.0 / 15.0) * ws[e] + (T)(2.0 / 3.0) * wI - (T)0.2 * wII;
+        return (T)1.5 * wI - (T)0.5 * wII;
+    }
+    // a non-corner point of edge e from its two sites along the inward normal
+    __device__ __forceinline__ T point(int e, int i, int j) const
+    {
+        const int dx = e == LEFT ? 1 : (e == RIGHT ? -1 : 0);
+        const int dy = e == BOTTOM ? 1 : (e == TOP ? -1 : 0);
+        return rule(e, w(i + dx, j + dy), w(i + 2 * dx, j + 2 * dy));
+    }
+};
+
+__host__ __device__ __forceinline__ bool ruled(int kind) { return kind == EDGE_FREE || kind == EDGE_DIRICHLET; }
+
+template <typename T, typename D>
+__global__ void __launch_bounds__(128) edge_rule_kernel(const StepArgs<T, D> a)
+{
+    const int nx = a.nx, ny = a.ny;
+    const bool onL = ruled(a.edge[LEFT]), onR = ruled(a.edge[RIGHT]);
+    const bool onB = ruled(a.edge[BOTTOM]), onT = ruled(a.edge[TOP]);
+    const int nB = onB ? nx : 0, nT = onT ? nx : 0;
+    const int jlo = onB ? 1 : 0, jhi = onT ? ny - 2 : ny - 1;
+    const int nV = jhi >= jlo ? jhi - jlo + 1 : 0;
+    const int nL = onL ? nV : 0, nR = onR ? nV : 0;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int i, j;
+    if (t < nB) { i = t; j = 0; }
+    else if ((t -= nB) < nT) { i = t; j = ny - 1; }
+    else if ((t -= nT) < nL) { i = 0; j = jlo + t; }
+    else if ((t -= nL) < nR) { i = nx - 1; j = jlo + t; }
+    else return;
+
+    EdgeRule<T> R;
+    R.wn = a.w_out;
+    R.pitch = a.pitch;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        R.dir[e] = a.edge[e] == EDGE_DIRICHLET;
+        R.ws[e] = (T)a.s_out->wstar[e];
+    }
+    const int eh = (onL && i == 0) ? LEFT : ((onR && i == nx - 1) ? RIGHT : -1);
+    const int ev = (onB && j == 0) ? BOTTOM : ((onT && j == ny - 1) ? TOP : -1);
+    const int jc = a.p.jc;
+    bool face = false;
+    if (a.p.macro && a.p.mode != CRACK_NONE && (j == jc || j == jc - 1))
+        face = (a.cut_v[(int64_t)(jc - 1) * a.words + (i >> 5)] >> (i & 31)) & 1u;
+    T v;
+    if (face) {
+        // a crack-face point on an edge column (eh >= 0): its x_I, x_II are
+        // the edge points one and two rows further from the crack
+        const int s = j == jc ? 1 : -1;
+        v = (T)1.5 * R.point(eh, i, j + s) - (T)0.5 * R.point(eh, i, j + 2 * s);
+    } else if (eh >= 0 && ev >= 0) {
+        const int e = (a.edge[eh] == EDGE_DIRICHLET && a.edge[ev] != EDGE_DIRICHLET) ? eh : ev;
+        const int o = e == eh ? ev : eh;
+        const int dx = e == LEFT ? 1 : (e == RIGHT ? -1 : 0);
+        const int dy = e == BOTTOM ? 1 : (e == TOP ? -1 : 0);
+        v = R.rule(e, R.point(o, i + dx, j + dy), R.point(o, i + 2 * dx, j + 2 * dy));
+    } else {
+        v = R.point(eh >= 0 ? eh : ev, i, j);
+    }
+    const int64_t P = a.pitch, o = (int64_t)j * P + i;
+    const T wd = (v - a.w_in[o]) / a.dt;
+    a.w_out[o] = v;
+    WdIO<D>::put(a.wd + o, wd, a.wd_scale);
+    // pad images of the new value (bounce-back next to a free edge, the
+    // wrap-around next to a periodic one)
+    T *row = a.w_out + (int64_t)j * P;
+    if (i == 0) {
+        if (a.edge[LEFT] == EDGE_FREE) row[-1] = v;
+        else if (a.edge[LEFT] == EDGE_PERIODIC) row[nx] = v;
+    }
+    if (i == nx - 1) {
+        if (a.edge[RIGHT] == EDGE_FREE) row[nx] = v;
+        else if (a.edge[RIGHT] == EDGE_PERIODIC) row[-1] = v;
+    }
+    if (j == 0) {
+        if (a.edge[BOTTOM] == EDGE_FREE) a.w_out[i - P] = v;
+        else if (a.edge[BOTTOM] == EDGE_PERIODIC) a.w_out[(int64_t)ny * P + i] = v;
+    }
+    if (j == ny - 1) {
+        if (a.edge[TOP] == EDGE_FREE) a.w_out[(int64_t)ny * P + i] = v;
+        else if (a.edge[TOP] == EDGE_PERIODIC) a.w_out[i - P] = v;
+    }
+    if (!isfinite((double)v) || !isfinite((double)wd)) atomicOr(a.err, (uint32_t)ERR_NONFINITE);
+}
+
+template <typename T, typename D>
+int edge_rule_sites(const StepArgs<T, D> &a)
+{
+    const bool onL = ruled(a.edge[LEFT]), onR = ruled(a.edge[RIGHT]);
+    const bool onB = ruled(a.edge[BOTTOM]), onT = ruled(a.edge[TOP]);
+    const int jlo = onB ? 1 : 0, jhi = onT ? a.ny - 2 : a.ny - 1;
+    const int nV = jhi >= jlo ? jhi - jlo + 1 : 0;
+    return (onB ? a.nx : 0) + (onT ? a.nx : 0) + (onL ? nV : 0) + (onR ? nV : 0);
+}
+
+template <typename T, typename D>
+cudaError_t launch_edge_rule(const StepArgs<T, D> &a, cudaStream_t s)
+{
+    const int n = edge_rule_sites(a);
+    if (n == 0) return cudaSuccess;
+    edge_rule_kernel<T, D><<<(n + 127) / 128, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------ periodic pad images
 
 // Pad images for fields set from outside: the bounce-back image (the edge
@@ -734,6 +871,10 @@ template cudaError_t launch_wd_from_f32<__nv_bfloat16>(__nv_bfloat16 *, int64_t,
 template cudaError_t launch_wd_from_f32<__half>(__half *, int64_t, int, int, float, const float *, cudaStream_t);
 template cudaError_t launch_finalize<float>(const FinalizeArgs<float> &, cudaStream_t);
 template cudaError_t launch_finalize<double>(const FinalizeArgs<double> &, cudaStream_t);
+template cudaError_t launch_edge_rule<double, double>(const StepArgs<double, double> &, cudaStream_t);
+template cudaError_t launch_edge_rule<float, float>(const StepArgs<float, float> &, cudaStream_t);
+template cudaError_t launch_edge_rule<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> &, cudaStream_t);
+template cudaError_t launch_edge_rule<float, __half>(const StepArgs<float, __half> &, cudaStream_t);
 template cudaError_t launch_fill_pads<float>(float *, int64_t, int, int, const int32_t *, cudaStream_t);
 template cudaError_t launch_fill_pads<double>(double *, int64_t, int, int, const int32_t *, cudaStream_t);
 

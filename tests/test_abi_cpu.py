@@ -93,8 +93,15 @@ def _structs(**over):
     ({"cr__y": 64.5}, "multiple of dh"),
     ({"cr__y": 2.0}, "too close"),
     ({"cr__x_tip": 128.0}, "left of"),
-    ({"cr__x_tip": 126.6}, "one intact column"),
-    ({"cr__x_start": 1.2}, "one intact column"),
+    ({"cr__x_tip": 126.6}, "narrow ligament"),
+    ({"cr__x_start": 1.2}, "narrow ligament"),
+    ({"lat__bc_mode": 3}, "boundary mode"),
+    ({"lat__bc_mode": 2, "cr__x_start": 2.2}, "narrow ligament"),
+    ({"lat__bc_mode": 2, "cr__x_tip": 125.6}, "narrow ligament"),
+    ({"lat__bc_mode": 2, "cr__y": 3.0}, "too close"),
+    ({"lat__bc_mode": 2, "cr__y": 125.0}, "too close"),
+    ({"lat__bc_mode": 2, "g__nx": 3, "cr__mode": 0}, "nx >= 4"),
+    ({"lat__bc_mode": 2, "g__ny": 3, "cr__mode": 0}, "ny >= 4"),
     ({"cr__x_start": 40.0}, "x_start"),
     ({"cr__mode": 9}, "crack mode"),
 ])

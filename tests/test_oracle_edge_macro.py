@@ -358,3 +358,47 @@ def test_centre_crack_example_sec_5_2(centre_crack_run):
     # the crack grew but stayed inside the body
     da = (h["tip_q"][n - 1] / 2**32 - 4.5 * Lh) / Lh
     assert 0.1 < da < 2.0
+
+
+def _ligament_growth(oracle_mod, bc_mode, edge_kind, width, side, steps=6000):
+    """max |w| after `steps` steps of a stationary crack that leaves `width`
+    intact columns between its end and the left or right edge."""
+    nx, ny, jc = 48, 30, 13
+    edges = (edge_kind, "free", "dirichlet", "dirichlet") if side == "left" else ("free", edge_kind, "dirichlet", "dirichlet")
+    p = W.base_problem(nx, ny, bc_mode=bc_mode, edges=edges)
+    if side == "left":
+        p = W.with_crack(p, mode="stationary", y=float(jc), x_start=width + 0.2 if width else 0.0, x_tip=24.3)
+    else:
+        p = W.with_crack(p, mode="stationary", y=float(jc), x_start=20.0, x_tip=nx - width - 0.3)
+    p = W.with_antisymmetric_ramp(p, 1e-3, 40.0)
+    o = oracle_mod.Oracle(p)
+    _, cv = o.cuts()
+    cols = np.nonzero(cv[jc - 1])[0]
+    assert (cols[0] if side == "left" else nx - 1 - cols[-1]) == width
+    o.step(steps)
+    w, _ = o.fields()
+    o.close()
+    return np.abs(w).max()
+
+
+# (bc_mode, edge kind) -> the ligament width whose mode grows fastest; the
+# CUDA library rejects initial cracks that leave it (lbm_create)
+UNSTABLE_LIGAMENT = {("macroscopic", "free"): 1, ("macroscopic", "dirichlet"): 2,
+                     ("macroscopic_edges", "free"): 2, ("macroscopic_edges", "dirichlet"): 2}
+
+
+@pytest.mark.parametrize("side", ["left", "right"])
+@pytest.mark.parametrize("mode_edge", sorted(UNSTABLE_LIGAMENT))
+def test_narrow_ligaments_next_to_an_edge(oracle_mod, mode_edge, side):
+    """A crack that ends a column or two before an edge leaves a ligament in
+    which the extrapolating crack-face rule feeds back on itself: the listed
+    width grows by orders of magnitude within 6000 steps, while no ligament,
+    the other narrow width and ligaments of five or six columns stay at the
+    size of the load.  (Three or four columns next to a Dirichlet or
+    macroscopic edge grow too, slowly, in some geometries.)"""
+    bc_mode, edge_kind = mode_edge
+    bad = UNSTABLE_LIGAMENT[mode_edge]
+    assert _ligament_growth(oracle_mod, bc_mode, edge_kind, bad, side) > 1e-2
+    for width in sorted({0, 1, 2, 5, 6} - {bad}):
+        m = _ligament_growth(oracle_mod, bc_mode, edge_kind, width, side)
+        assert m < 5e-3, (width, m)
