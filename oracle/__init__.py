@@ -65,6 +65,7 @@ class _Config(C.Structure):
         ("load_n", C.c_int64 * 4),
         ("hist_cap", C.c_int64),
         ("two_tips", C.c_int32), ("edge_macro", C.c_int32),
+        ("q", C.c_int32), ("pad_", C.c_int32),
     ]
 
 
@@ -96,6 +97,9 @@ def _load():
         lib.orc_get_history.restype = C.c_int64
         lib.orc_get_bpoints.argtypes = [P, C.POINTER(C.c_int32), C.c_int32]
         lib.orc_get_bpoints.restype = C.c_int32
+        lib.orc_get_cuts_diag.argtypes = [P, C.c_char_p, C.c_char_p]
+        lib.orc_q.argtypes = [P]
+        lib.orc_q.restype = C.c_int32
         lib.orc_get_edge_points.argtypes = [P, C.POINTER(C.c_int32), C.c_int32]
         lib.orc_get_edge_points.restype = C.c_int32
         lib.orc_quadratic_through.argtypes = [C.c_double] * 7
@@ -150,6 +154,7 @@ def make_config(problem: dict):
     # free and Dirichlet outer edges (Sec. 3.1, Sec. 5.2)
     cfg.bc_mode = BC["macroscopic" if bc == "macroscopic_edges" else bc]
     cfg.edge_macro = 1 if bc == "macroscopic_edges" else 0
+    cfg.q = {"D2Q5": 5, "D2Q9": 9}[problem.get("lattice", "D2Q5")]
     cr = problem.get("crack") or {"mode": "none"}
     cfg.crack_mode = CRACK[cr.get("mode", "none")]
     if cfg.crack_mode:
@@ -212,7 +217,7 @@ class Oracle:
         return w, wd
 
     def distributions(self):
-        f = np.empty((5, self.ny, self.nx))
+        f = np.empty((self.lib.orc_q(self.h), self.ny, self.nx))
         self.lib.orc_get_distributions(self.h, _dptr(f))
         return f
 
@@ -225,6 +230,14 @@ class Oracle:
         cv = np.zeros((self.ny, self.nx), np.uint8)
         self.lib.orc_get_cuts(self.h, ch.ctypes.data_as(C.c_char_p), cv.ctypes.data_as(C.c_char_p))
         return ch, cv
+
+    def cuts_diag(self):
+        """D2Q9: (cut_d1, cut_d2) as (ny, nx) uint8: links (i,j)-(i+1,j+1) and
+        (i+1,j)-(i,j+1) severed (flags at (i,j))."""
+        d1 = np.zeros((self.ny, self.nx), np.uint8)
+        d2 = np.zeros((self.ny, self.nx), np.uint8)
+        self.lib.orc_get_cuts_diag(self.h, d1.ctypes.data_as(C.c_char_p), d2.ctypes.data_as(C.c_char_p))
+        return d1, d2
 
     def crack(self) -> dict:
         info = _CrackInfo()

@@ -93,6 +93,8 @@ typedef struct {
     int64_t hist_cap;
     int32_t two_tips;    /* both ends of the crack grow (the left one towards -x) */
     int32_t edge_macro;  /* the macroscopic rule (Sec. 3.1) on the outer edges too */
+    int32_t q;           /* velocity set: 5 (D2Q5, Sec. 3) or 9 (D2Q9) */
+    int32_t pad_;
 } orc_config;
 
 typedef struct {
@@ -115,9 +117,12 @@ typedef struct {
     orc_config c;
     int64_t step;
     double cs, g;
-    double *f[5], *fs[5], *w, *w_old;
+    int Q;               /* 5 or 9 distributions */
+    double *f[9], *fs[9], *w, *w_old;
     uint8_t *cut_h;      /* link (i,j)-(i+1,j), i = nx-1 is the periodic wrap */
     uint8_t *cut_v;      /* link (i,j)-(i,j+1), j = ny-1 is the periodic wrap */
+    uint8_t *cut_d1;     /* D2Q9: link (i,j)-(i+1,j+1) */
+    uint8_t *cut_d2;     /* D2Q9: link (i+1,j)-(i,j+1) */
     int64_t start_q, tip_q, clamp_q;
     double v_prev, K_last;
     int32_t npairs_last, flags, arrested_for_good;
@@ -144,10 +149,22 @@ typedef struct {
     double *series[4];
 } orc_state;
 
-/* D2Q5 lattice velocities in units of c = dh/dt (Sec. 3, eq. 2). */
-static const int CX[5] = {0, 1, 0, -1, 0};
-static const int CY[5] = {0, 0, 1, 0, -1};
-static const int OPP[5] = {0, 3, 4, 1, 2};
+/* Lattice velocities in units of c = dh/dt: D2Q5 (Sec. 3, eq. 2) uses
+ * 0..4; D2Q9 adds the diagonals 5..8. */
+static const int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+
+/* Equilibrium weight of a moving direction, in units of g.  D2Q5: 1.  D2Q9:
+ * 2/3 along the axes and 1/6 along the diagonals, the weights of the
+ * isotropic nine-point Laplacian; the diagonal neighbours lie sqrt(2) dh away,
+ * so the axis weight plus twice the diagonal weight is 1 and the wave speed
+ * stays c_s. */
+static double weight(const orc_state *s, int a)
+{
+    if (s->Q == 5) return 1.0;
+    return a <= 4 ? 2.0 / 3.0 : 1.0 / 6.0;
+}
 
 static int64_t qone(void) { return (int64_t)1 << ORC_Q; }
 
@@ -198,6 +215,18 @@ static void equilibrium(double w, double wdot, double g, double feq[5])
 
 void orc_equilibrium(double w, double wdot, double g, double *feq5) { equilibrium(w, wdot, g, feq5); }
 
+/* The same for the lattice of s: f_eq^a = weight_a g w (a >= 1), f_eq^0 =
+ * wdot minus their sum, so that sum_a f_eq^a = wdot. */
+static void equilibrium_q(const orc_state *s, double w, double wdot, double feq[9])
+{
+    double rest = wdot;
+    for (int a = 1; a < s->Q; ++a) {
+        feq[a] = weight(s, a) * s->g * w;
+        rest -= feq[a];
+    }
+    feq[0] = rest;
+}
+
 /* ------------------------------------------------------------------ geometry */
 
 static int64_t site_cx_q(int i) { return (int64_t)(2 * i + 1) << (ORC_Q - 1); }
@@ -231,30 +260,63 @@ int orc_segments_intersect(int64_t p1x, int64_t p1y, int64_t p2x, int64_t p2y,
     return 0;
 }
 
-/* Link between site k and its neighbour in direction a (a = 1..4).  Returns
- * the neighbour index, or -1 if the link leaves a non-periodic domain.  *cut
- * points at the severed flag of the link. */
-static int32_t link_of(const orc_state *s, int32_t k, int a, uint8_t **cut)
+/* Link between site k and its neighbour in direction a (a = 1..Q-1).
+ * Returns the neighbour index, or -1 if the link leaves a non-periodic
+ * domain.  *cut points at the severed flag of the link; *wrap is set when the
+ * link crosses a periodic edge (such a link lies outside the body's interior
+ * and no crack inside the body intersects it). */
+static int32_t link_of_w(const orc_state *s, int32_t k, int a, uint8_t **cut, int *wrap)
 {
     int nx = s->c.nx, ny = s->c.ny;
     int i = k % nx, j = k / nx;
     int ni = i + CX[a], nj = j + CY[a];
+    *wrap = 0;
     if (ni < 0 || ni >= nx) {
         int e = ni < 0 ? ORC_LEFT : ORC_RIGHT;
         if (s->c.edge[e] != ORC_PERIODIC) return -1;
         ni = (ni + nx) % nx;
+        *wrap = 1;
     }
     if (nj < 0 || nj >= ny) {
         int e = nj < 0 ? ORC_BOTTOM : ORC_TOP;
         if (s->c.edge[e] != ORC_PERIODIC) return -1;
         nj = (nj + ny) % ny;
+        *wrap = 1;
     }
-    /* the flag is stored at the site from which the link points in +x / +y */
+    /* the flag of an axis link is stored at the site from which it points in
+     * +x / +y, that of a diagonal link at the lower-left corner of its cell */
     if (a == 1) *cut = &s->cut_h[j * nx + i];
     else if (a == 3) *cut = &s->cut_h[nj * nx + ni];
     else if (a == 2) *cut = &s->cut_v[j * nx + i];
-    else *cut = &s->cut_v[nj * nx + ni];
+    else if (a == 4) *cut = &s->cut_v[nj * nx + ni];
+    else if (a == 5) *cut = &s->cut_d1[j * nx + i];
+    else if (a == 7) *cut = &s->cut_d1[nj * nx + ni];
+    else if (a == 6) *cut = &s->cut_d2[j * nx + ni];
+    else *cut = &s->cut_d2[nj * nx + i];
     return nj * nx + ni;
+}
+
+static int32_t link_of(const orc_state *s, int32_t k, int a, uint8_t **cut)
+{
+    int wrap;
+    return link_of_w(s, k, a, cut, &wrap);
+}
+
+/* The outer edge whose rule applies to the missing link of site k in
+ * direction b: the edge it crosses; a diagonal link through a corner of the
+ * body follows the Dirichlet edge if just one of the two is Dirichlet, else
+ * the bottom / top edge. */
+static int missing_edge(const orc_state *s, int32_t k, int b)
+{
+    int nx = s->c.nx, ny = s->c.ny;
+    int ni = k % nx + CX[b], nj = k / nx + CY[b];
+    int ex = (ni < 0 || ni >= nx) && s->c.edge[ni < 0 ? ORC_LEFT : ORC_RIGHT] != ORC_PERIODIC
+                 ? (ni < 0 ? ORC_LEFT : ORC_RIGHT) : -1;
+    int ey = (nj < 0 || nj >= ny) && s->c.edge[nj < 0 ? ORC_BOTTOM : ORC_TOP] != ORC_PERIODIC
+                 ? (nj < 0 ? ORC_BOTTOM : ORC_TOP) : -1;
+    if (ex >= 0 && ey >= 0)
+        return (s->c.edge[ex] == ORC_DIRICHLET && s->c.edge[ey] != ORC_DIRICHLET) ? ex : ey;
+    return ex >= 0 ? ex : ey;
 }
 
 /* ------------------------------------------------------------ state set-up */
@@ -264,8 +326,8 @@ static void *xcalloc(size_t n, size_t sz) { return calloc(n ? n : 1, sz); }
 void orc_destroy(orc_state *s)
 {
     if (!s) return;
-    for (int a = 0; a < 5; ++a) { free(s->f[a]); free(s->fs[a]); }
-    free(s->w); free(s->w_old); free(s->cut_h); free(s->cut_v);
+    for (int a = 0; a < 9; ++a) { free(s->f[a]); free(s->fs[a]); }
+    free(s->w); free(s->w_old); free(s->cut_h); free(s->cut_v); free(s->cut_d1); free(s->cut_d2);
     free(s->bprev); free(s->bl); free(s->is_bpoint);
     free(s->hK); free(s->hv); free(s->htip); free(s->hnp); free(s->hgrow);
     free(s->ep);
@@ -287,13 +349,14 @@ static void initial_crack(orc_state *s)
     int64_t yq = (int64_t)s->c.jc << ORC_Q;
     int32_t *B = malloc(sizeof(int32_t) * 4 * (size_t)nx * ny);
     int nB = 0;
+    static const int ONCE[4] = {1, 2, 5, 6};   /* each link once: +x, +y and the two upward diagonals */
     for (int32_t k = 0; k < nx * ny; ++k) {
-        for (int a = 1; a <= 2; ++a) {       /* each link once: +x and +y */
+        for (int q = 0; q < (s->Q == 9 ? 4 : 2); ++q) {
+            int a = ONCE[q], wrap;
             uint8_t *cut;
-            int32_t m = link_of(s, k, a, &cut);
-            if (m < 0) continue;
+            int32_t m = link_of_w(s, k, a, &cut, &wrap);
+            if (m < 0 || wrap) continue;
             int i = k % nx, j = k / nx, mi = m % nx, mj = m / nx;
-            if ((a == 1 && mi < i) || (a == 2 && mj < j)) continue;  /* periodic wrap link */
             if (orc_segments_intersect(site_cx_q(i), site_cx_q(j), site_cx_q(mi), site_cx_q(mj),
                                        s->start_q, yq, s->tip_q, yq)) {
                 *cut = 1;
@@ -315,16 +378,23 @@ static void initial_crack(orc_state *s)
 orc_state *orc_create(const orc_config *cfg)
 {
     if (cfg->nx < 1 || cfg->ny < 1 || !(cfg->dh > 0) || !(cfg->dt > 0)) return NULL;
+    int Q = cfg->q == 0 ? 5 : cfg->q;
+    if (Q != 5 && Q != 9) return NULL;
+    /* D2Q9 is built with the link-local rules only (no macroscopic rule) */
+    if (Q == 9 && (cfg->bc_mode != ORC_BC_BOUNCEBACK || cfg->edge_macro)) return NULL;
     orc_state *s = xcalloc(1, sizeof(orc_state));
     s->c = *cfg;
+    s->Q = Q;
     size_t n = (size_t)cfg->nx * cfg->ny;
     s->cs = sqrt(cfg->mu / cfg->rho);
     s->g = s->cs * s->cs * cfg->dt / (cfg->dh * cfg->dh);
-    for (int a = 0; a < 5; ++a) { s->f[a] = xcalloc(n, sizeof(double)); s->fs[a] = xcalloc(n, sizeof(double)); }
+    for (int a = 0; a < Q; ++a) { s->f[a] = xcalloc(n, sizeof(double)); s->fs[a] = xcalloc(n, sizeof(double)); }
     s->w = xcalloc(n, sizeof(double));
     s->w_old = xcalloc(n, sizeof(double));
     s->cut_h = xcalloc(n, 1);
     s->cut_v = xcalloc(n, 1);
+    s->cut_d1 = xcalloc(n, 1);
+    s->cut_d2 = xcalloc(n, 1);
     s->is_bpoint = xcalloc(n, 1);
     s->bprev = xcalloc(n, sizeof(int32_t));
     s->lbprev = xcalloc(n, sizeof(int32_t));
@@ -377,10 +447,10 @@ void orc_set_fields(orc_state *s, const double *w, const double *wdot)
 {
     size_t n = (size_t)s->c.nx * s->c.ny;
     for (size_t k = 0; k < n; ++k) {
-        double feq[5];
-        equilibrium(w[k], wdot[k], s->g, feq);
+        double feq[9];
+        equilibrium_q(s, w[k], wdot[k], feq);
         s->w[k] = w[k];
-        for (int a = 0; a < 5; ++a) s->f[a][k] = feq[a];
+        for (int a = 0; a < s->Q; ++a) s->f[a][k] = feq[a];
     }
 }
 
@@ -389,15 +459,17 @@ void orc_get_fields(const orc_state *s, double *w, double *wdot)
 {
     size_t n = (size_t)s->c.nx * s->c.ny;
     for (size_t k = 0; k < n; ++k) {
+        double sum = 0.0;
+        for (int a = 0; a < s->Q; ++a) sum += s->f[a][k];
         w[k] = s->w[k];
-        wdot[k] = s->f[0][k] + s->f[1][k] + s->f[2][k] + s->f[3][k] + s->f[4][k];
+        wdot[k] = sum;
     }
 }
 
 void orc_get_distributions(const orc_state *s, double *f5)
 {
     size_t n = (size_t)s->c.nx * s->c.ny;
-    for (int a = 0; a < 5; ++a) memcpy(f5 + (size_t)a * n, s->f[a], n * sizeof(double));
+    for (int a = 0; a < s->Q; ++a) memcpy(f5 + (size_t)a * n, s->f[a], n * sizeof(double));
 }
 
 void orc_get_cuts(const orc_state *s, uint8_t *cut_h, uint8_t *cut_v)
@@ -406,6 +478,17 @@ void orc_get_cuts(const orc_state *s, uint8_t *cut_h, uint8_t *cut_v)
     memcpy(cut_h, s->cut_h, n);
     memcpy(cut_v, s->cut_v, n);
 }
+
+/* D2Q9: the severed flags of the diagonal links (i,j)-(i+1,j+1) and
+ * (i+1,j)-(i,j+1), stored at (i,j). */
+void orc_get_cuts_diag(const orc_state *s, uint8_t *cut_d1, uint8_t *cut_d2)
+{
+    size_t n = (size_t)s->c.nx * s->c.ny;
+    memcpy(cut_d1, s->cut_d1, n);
+    memcpy(cut_d2, s->cut_d2, n);
+}
+
+int32_t orc_q(const orc_state *s) { return s->Q; }
 
 /* --------------------------------------------- macroscopic boundary points */
 
@@ -560,9 +643,9 @@ static double edge_value(const orc_epoint *p, const double *w, const double *wst
  * domain or severed) share equally what makes sum_a f^a = (w_B - w(t)) / dt. */
 static void set_missing(orc_state *s, int32_t k, double wB)
 {
-    int miss[4], nmiss = 0;
+    int miss[8], nmiss = 0;
     double known = s->f[0][k];
-    for (int a = 1; a < 5; ++a) {
+    for (int a = 1; a < s->Q; ++a) {
         uint8_t *cut;
         int32_t src = link_of(s, k, OPP[a], &cut);
         if (src < 0 || *cut) miss[nmiss++] = a;
@@ -625,10 +708,11 @@ static void lbm_step(orc_state *s)
 
     /* collision (eq. LBE, right-hand side) */
     for (size_t k = 0; k < n; ++k) {
-        double wdot = s->f[0][k] + s->f[1][k] + s->f[2][k] + s->f[3][k] + s->f[4][k];
-        double feq[5];
-        equilibrium(s->w[k], wdot, g, feq);
-        for (int a = 0; a < 5; ++a) s->fs[a][k] = s->f[a][k] - om * (s->f[a][k] - feq[a]);
+        double wdot = 0.0;
+        for (int a = 0; a < s->Q; ++a) wdot += s->f[a][k];
+        double feq[9];
+        equilibrium_q(s, s->w[k], wdot, feq);
+        for (int a = 0; a < s->Q; ++a) s->fs[a][k] = s->f[a][k] - om * (s->f[a][k] - feq[a]);
     }
     /* streaming along intact links (eq. LBE, left-hand side); a missing link
      * takes bounce-back (free edge, crack face) or anti-bounce-back (Dirichlet) */
@@ -636,16 +720,16 @@ static void lbm_step(orc_state *s)
         for (int i = 0; i < nx; ++i) {
             int32_t k = j * nx + i;
             s->f[0][k] = s->fs[0][k];
-            for (int a = 1; a < 5; ++a) {
+            for (int a = 1; a < s->Q; ++a) {
                 int b = OPP[a];
                 uint8_t *cut;
                 int32_t src = link_of(s, k, b, &cut);     /* f^a arrives from x - c^a */
                 if (src >= 0 && !*cut) {
                     s->f[a][k] = s->fs[a][src];
                 } else if (src < 0) {
-                    int e = (b == 1) ? ORC_RIGHT : (b == 3) ? ORC_LEFT : (b == 2) ? ORC_TOP : ORC_BOTTOM;
+                    int e = missing_edge(s, k, b);
                     if (s->c.edge[e] == ORC_DIRICHLET)
-                        s->f[a][k] = -s->fs[b][k] + 2.0 * g * wstar[e];
+                        s->f[a][k] = -s->fs[b][k] + 2.0 * weight(s, a) * g * wstar[e];
                     else
                         s->f[a][k] = s->fs[b][k];
                 } else {
@@ -656,7 +740,8 @@ static void lbm_step(orc_state *s)
     /* moment and Euler integration (eqs. distrib-macro, integration) */
     memcpy(s->w_old, s->w, n * sizeof(double));
     for (size_t k = 0; k < n; ++k) {
-        double wdot = s->f[0][k] + s->f[1][k] + s->f[2][k] + s->f[3][k] + s->f[4][k];
+        double wdot = 0.0;
+        for (int a = 0; a < s->Q; ++a) wdot += s->f[a][k];
         s->w[k] = s->w_old[k] + dt * wdot;
     }
     /* the macroscopic non-lattice-conforming rule on the boundary points */
@@ -729,7 +814,7 @@ static int checklinks(orc_state *s, int64_t ax, int64_t ay, int64_t bx, int64_t 
     memset(s->inq, 0, n);
     memset(s->visited, 0, n);
     for (int b = 0; b < s->nbprev; ++b)
-        for (int a = 1; a < 5; ++a) {
+        for (int a = 1; a < s->Q; ++a) {
             uint8_t *cut;
             int32_t m = link_of(s, s->bprev[b], a, &cut);
             if (m >= 0 && !*cut && !s->inq[m]) { s->inq[m] = 1; s->queue[qt++] = m; }
@@ -749,10 +834,11 @@ static int checklinks(orc_state *s, int64_t ax, int64_t ay, int64_t bx, int64_t 
         int32_t p = s->queue[qh++];
         s->visited[p] = 1;
         int pi = p % nx, pj = p / nx;
-        for (int a = 1; a < 5; ++a) {
+        for (int a = 1; a < s->Q; ++a) {
             uint8_t *cut;
-            int32_t m = link_of(s, p, a, &cut);
-            if (m < 0 || *cut) continue;
+            int wrap;
+            int32_t m = link_of_w(s, p, a, &cut, &wrap);
+            if (m < 0 || *cut || wrap) continue;   /* a link across a periodic edge lies outside the body */
             int mi = m % nx, mj = m / nx;
             if (!orc_segments_intersect(site_cx_q(pi), site_cx_q(pj), site_cx_q(mi), site_cx_q(mj), ax, ay, bx, by))
                 continue;
@@ -763,7 +849,7 @@ static int checklinks(orc_state *s, int64_t ax, int64_t ay, int64_t bx, int64_t 
             for (int q = 0; q < nB; ++q) { hp |= B[q] == p; hm |= B[q] == m; }
             if (!hp && nB < nBmax) B[nB++] = p;
             if (!hm && nB < nBmax) B[nB++] = m;
-            for (int c2 = 1; c2 < 5; ++c2) {
+            for (int c2 = 1; c2 < s->Q; ++c2) {
                 uint8_t *cut2;
                 int32_t r = link_of(s, m, c2, &cut2);
                 if (r >= 0 && !*cut2 && !s->visited[r] && !s->inq[r]) { s->inq[r] = 1; s->queue[qt++] = r; }
@@ -961,6 +1047,7 @@ int32_t orc_checklinks_standalone(int32_t nx, int32_t ny, uint8_t *cut_h, uint8_
     memset(&s, 0, sizeof s);
     s.c.nx = nx;
     s.c.ny = ny;
+    s.Q = 5;
     s.cut_h = cut_h;
     s.cut_v = cut_v;
     size_t n = (size_t)nx * ny;
@@ -1118,8 +1205,9 @@ int orc_adjoint(const orc_config *cfg, const double *w0, const double *wd0, int6
                 const int32_t *si, const int32_t *sj, const double *target, double *loss, double *trace,
                 double *dload, double *dw0, double *dwd0)
 {
-    /* the transposed step covers the crack-face rule only, not the outer edges */
-    if (T < 1 || ns < 0 || cfg->edge_macro) return -1;
+    /* the transposed step covers D2Q5 and the crack-face rule only, not the
+     * macroscopic rule on the outer edges */
+    if (T < 1 || ns < 0 || cfg->edge_macro || (cfg->q != 0 && cfg->q != 5)) return -1;
     orc_state *s = orc_create(cfg);
     if (!s) return -1;
     int nx = s->c.nx, ny = s->c.ny;
