@@ -326,6 +326,52 @@ def measure_large(lbm, W, torch, stream, peak):
     return out
 
 
+def measure_extensions(lbm, W, torch, stream, problem, peak, flush_l2, steps=100):
+    """The two extensions beyond the plain method.  D2Q9: the benchmark
+    workload on the nine-velocity lattice (bounce-back crack faces, FP32), the
+    update and crack launches timed by the library's CUDA events with the L2
+    flushed before each step, against 16 algorithmic bytes per site.  The
+    K-criterion centre-crack example of Sec. 5.2 (512 x 192, macroscopic rule
+    on every boundary, FP32): the whole 5050-step run timed with CUDA events
+    (graph replay; the state fits in L2, so it is launch-bound)."""
+    sites = problem["nx"] * problem["ny"]
+    q = dict(problem, bc_mode="bounceback", lattice="D2Q9")
+    lat = lbm.Lattice(q, "f32", stream=stream)
+    lat.step(500)
+    lat.set_profiling(True)
+    for _ in range(steps):
+        flush_l2()
+        lat.step(1)
+    lat.sync()
+    pr = lat.profile(reset=True)
+    k = pr["step_ms"] / max(pr["n_step"], 1) * 1e-3
+    d2q9 = {"workload": "kcrit_single 4096x2048, D2Q9, bounce-back faces, f32", "step_us": k * 1e6,
+            "glups": sites / k / 1e9, "bytes_per_site": 16, "achieved_gbs": 16 * sites / k / 1e9,
+            "frac": 16 * sites / k / 1e9 / peak, "launches_per_step": 2,
+            "timing": "library CUDA events around the update and crack launches, L2 flushed before each step"}
+    lat.close()
+
+    p = W.kcrit_centre_crack()
+    n = W.KCRIT_CENTRE_STEPS
+    lat = lbm.Lattice(p, "f32", stream=stream)
+    lat.step(64)          # capture the step graph
+    lat.reset()
+    lat.sync()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    lat.step(n)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    secs = ev0.elapsed_time(ev1) * 1e-3
+    hist = lat.history(cap=n)
+    centre = {"workload": "Sec. 5.2 centre crack 512x192, macroscopic rule on every boundary, f32, 5050 steps",
+              "run_ms": secs * 1e3, "us_per_step": secs / n * 1e6, "glups": p["nx"] * p["ny"] * n / secs / 1e9,
+              "launches_per_step": 2, "tip_right_final": float(hist["tip_q"][-1]) / 2**32,
+              "timing": "CUDA events around the whole run (graph replay, L2-resident state)"}
+    lat.close()
+    return {"d2q9": d2q9, "centre_crack_sec52": centre}
+
+
 def measure_virtual_ranks(lbm, W, torch, stream, problem, steps=256):
     """The benchmark lattice split into 1, 2, 4 and 8 row slabs on this GPU
     (one batched step launch plus one halo-row exchange launch per step),
@@ -452,6 +498,7 @@ def run_ours(args, rank, world, local):
     adjoint = measure_adjoint(lbm, W, torch, stream) if not args.no_adjoint else None
     vranks = measure_virtual_ranks(lbm, W, torch, stream, problem) if not args.no_virtual_ranks else None
     large = measure_large(lbm, W, torch, stream, peak) if not args.no_large else None
+    ext = measure_extensions(lbm, W, torch, stream, problem, peak, flush_l2) if not args.no_extensions else None
 
     # steady back-to-back replay (CUDA graph, no flush): context only
     lat.sync()
@@ -508,6 +555,7 @@ def run_ours(args, rank, world, local):
         "adjoint": adjoint,
         "virtual_ranks": vranks,
         "large_lattice": large,
+        "extensions": ext,
         "wall_s": wall,
         "clocks": clk,
     }
@@ -533,6 +581,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the sensor-misfit gradient measurement")
     ap.add_argument("--no-virtual-ranks", action="store_true", help="skip the row-slab decomposition measurement")
     ap.add_argument("--no-large", action="store_true", help="skip the 16384 x 16384 storage comparison")
+    ap.add_argument("--no-extensions", action="store_true", help="skip the D2Q9 and Sec. 5.2 example measurements")
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched measurement, --steps steps of --batched-count lattices (for ncu)")
     ap.add_argument("--batched-count", type=int, default=256, help="lattices in the batched measurement")

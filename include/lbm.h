@@ -62,7 +62,19 @@ typedef enum lbm_status {
 enum { LBM_EDGE_FREE = 0, LBM_EDGE_DIRICHLET = 1, LBM_EDGE_PERIODIC = 2 };
 /* edge indices into lbm_grid.edge and lbm_loading.edge */
 enum { LBM_LEFT = 0, LBM_RIGHT = 1, LBM_BOTTOM = 2, LBM_TOP = 3 };
-enum { LBM_D2Q5 = 0 };
+/* velocity sets.  LBM_D2Q5 (Sec. 3) is the method; LBM_D2Q9 (the paper notes
+ * that the crack handling carries over to it, Sec. 4.1) adds the diagonal
+ * links with equilibrium weights 2/3 g (axes) and 1/6 g (diagonals), the
+ * isotropic nine-point Laplacian, stable for c_s^2 dt^2 / dh^2 <= 3/4.
+ * D2Q9 is built with link-local boundaries only (bc_mode LBM_BC_BOUNCEBACK),
+ * FP64 or FP32 storage, and not for lbm_batch_*, lbm_decomp_* or lbm_tape_*.
+ * Its diagonal links between rows jc-1 and jc cross the crack line at
+ * x = (i + 1) dh and are severed when that point lies on the closed crack
+ * segment; a diagonal link leaving the body through a corner follows the
+ * Dirichlet edge if just one of the two is Dirichlet, else the bottom / top
+ * edge.  Each D2Q9 time step is two launches: the update, then the crack
+ * step of Alg. 1. */
+enum { LBM_D2Q5 = 0, LBM_D2Q9 = 1 };
 enum { LBM_FORM_MOMENT = 0 };
 /* storage of the fields.  LBM_F64: w and wdot in FP64, FP64 arithmetic.
  * LBM_F32: w and wdot in FP32, FP32 arithmetic.  LBM_F32_WD_BF16 /
@@ -97,7 +109,7 @@ typedef struct lbm_grid {
     int32_t edge[4];
 } lbm_grid;
 
-/* Lattice model.  velocity_set = LBM_D2Q5, form = LBM_FORM_MOMENT,
+/* Lattice model.  velocity_set = LBM_D2Q5 or LBM_D2Q9, form = LBM_FORM_MOMENT,
  * omega = dt / tau = 1 (the paper fixes tau = dt; Sec. 3).  storage is an
  * LBM_F64 / LBM_F32 / LBM_F32_WD_* code; bc_mode an LBM_BC_* code.
  *
@@ -125,7 +137,8 @@ typedef struct lbm_lattice {
 } lbm_lattice;
 
 /* Density and shear modulus; c_s = sqrt(mu / rho) (Sec. 2.1).  The update is
- * stable only for g = c_s^2 dt^2 / dh^2 <= 1/2; larger g is rejected. */
+ * stable only for g = c_s^2 dt^2 / dh^2 <= 1/2 (D2Q5; 3/4 for D2Q9); larger g
+ * is rejected. */
 typedef struct lbm_material {
     double rho, mu;
 } lbm_material;

@@ -4,6 +4,8 @@
 // step before host reads, and the copy-out calls.
 #include "lbm_host.h"
 
+#include <type_traits>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -70,6 +72,13 @@ cudaError_t enqueue_step_t(const lbm_handle *h, int par, cudaStream_t s)
 {
     StepArgs<T, D> a;
     make_step_args(h, par, a);
+    if constexpr (std::is_same<T, D>::value) {
+        if (h->q == 9) {
+            cudaError_t e = launch_d2q9_step(a, s);
+            if (e == cudaSuccess) e = launch_crack_step(a, s);
+            return e;
+        }
+    }
     cudaError_t e = launch_step(a, h->n_bands, s);
     if (e == cudaSuccess && h->edge_macro) e = launch_edge_rule(a, s);
     return e;
@@ -334,7 +343,14 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
     if ((grid->edge[LBM_LEFT] == LBM_EDGE_PERIODIC) != (grid->edge[LBM_RIGHT] == LBM_EDGE_PERIODIC) ||
         (grid->edge[LBM_BOTTOM] == LBM_EDGE_PERIODIC) != (grid->edge[LBM_TOP] == LBM_EDGE_PERIODIC))
         return fail(LBM_ERR_ARG, "periodic edges must come in opposite pairs");
-    if (lattice->velocity_set != LBM_D2Q5) return fail(LBM_ERR_ARG, "only the D2Q5 velocity set is built");
+    if (lattice->velocity_set != LBM_D2Q5 && lattice->velocity_set != LBM_D2Q9)
+        return fail(LBM_ERR_ARG, "unknown velocity set (D2Q5 or D2Q9)");
+    const bool d2q9 = lattice->velocity_set == LBM_D2Q9;
+    if (d2q9 && lattice->bc_mode != LBM_BC_BOUNCEBACK)
+        return fail(LBM_ERR_ARG, "D2Q9 is built with link-local boundaries only (LBM_BC_BOUNCEBACK)");
+    if (d2q9 && lattice->storage != LBM_F64 && lattice->storage != LBM_F32)
+        return fail(LBM_ERR_ARG, "D2Q9 needs LBM_F64 or LBM_F32 storage");
+    if (d2q9 && slab) return fail(LBM_ERR_ARG, "D2Q9 is not built for row slabs");
     if (lattice->form != LBM_FORM_MOMENT) return fail(LBM_ERR_ARG, "only the moment form is built");
     if (lattice->omega != 1.0) return fail(LBM_ERR_ARG, "omega = dt/tau must be 1 (tau = dt)");
     if (lattice->storage < LBM_F64 || lattice->storage > LBM_F32_WD_F16) return fail(LBM_ERR_ARG, "unknown storage");
@@ -354,7 +370,8 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
         return fail(LBM_ERR_ARG, "rho and mu must be positive and finite");
     const double cs = std::sqrt(material->mu / material->rho);
     const double g = cs * cs * grid->dt / (grid->dh * grid->dh);
-    if (g * grid->dt > 0.5) return fail(LBM_ERR_ARG, "unstable: c_s^2 dt^2 / dh^2 > 1/2");
+    if (g * grid->dt > (d2q9 ? 0.75 : 0.5))
+        return fail(LBM_ERR_ARG, d2q9 ? "unstable: c_s^2 dt^2 / dh^2 > 3/4" : "unstable: c_s^2 dt^2 / dh^2 > 1/2");
 
     lbm_crack cr;
     std::memset(&cr, 0, sizeof cr);
@@ -547,6 +564,7 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
     cp.ny = grid->ny;
     cp.macro = macro_faces;
     h->edge_macro = macro_edges;
+    h->q = d2q9 ? 9 : 5;
     cp.words = h->words;
     cp.two_tips = cr.two_tips ? 1 : 0;
     cp.mu = material->mu;
@@ -1129,6 +1147,7 @@ lbm_status lbm_batch_create(lbm_handle *const *handles, int32_t n, int32_t band_
         if (h->sticky != LBM_OK) return fail(h->sticky, "a lattice is in an error state");
         if (h->lat.storage != handles[0]->lat.storage) return fail(LBM_ERR_ARG, "all lattices need the same storage");
         if (h->edge_macro) return fail(LBM_ERR_ARG, "the batched step has no macroscopic rule on the outer edges");
+        if (h->q != 5) return fail(LBM_ERR_ARG, "the batched step is built for D2Q5 only");
         if (h->stream != handles[0]->stream) return fail(LBM_ERR_ARG, "all lattices need the same stream");
         if (h->parity != handles[0]->parity) return fail(LBM_ERR_STATE, "all lattices need the same number of steps");
         for (int k = 0; k < i; ++k)

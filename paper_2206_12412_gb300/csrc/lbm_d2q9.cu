@@ -1,0 +1,239 @@
+// lbm_d2q9.cu -- the D2Q9 time step (sm_103a).
+//
+// The paper builds its method on D2Q5 and notes that the crack handling
+// carries over to D2Q9 (Sec. 4.1).  With tau = dt the collision sets every
+// distribution to its equilibrium, f_eq^a = W_a g w (W = 2/3 on the axes,
+// 1/6 on the diagonals: the isotropic nine-point Laplacian, whose axis weight
+// plus twice its diagonal weight is 1, so the wave speed stays c_s), and the
+// step is the moment update
+//     wdot' = wdot + g sum_a W_a (w(x + c_a) - w(x)),    w' = w + dt wdot'.
+// A missing link streams back bounce-back (the site's own value: free edge,
+// severed crack link) or anti-bounce-back (2 w* - w: Dirichlet edge, with
+// w*(t_n)); a periodic edge wraps.  The diagonal links between rows jc-1 and
+// jc cross the crack line at x = (i + 1) dh and are severed when that point
+// lies on the closed segment between the crack's two ends (the ends only move
+// outwards, so the severed set follows from the tips in the state); the
+// vertical links come from the cut mask.  A diagonal link that leaves the
+// body through one of its corners follows the Dirichlet edge if just one of
+// the two edges is Dirichlet, else the bottom / top edge.
+//
+// The interior marches like the D2Q5 step kernel (16 bytes per site update:
+// w and wdot read and written once); the outer-edge warps and the edge and
+// crack rows take a per-site path with every rule.  The crack step of Alg. 1
+// runs after the update as a kernel of its own (lbm_kernels.cu).
+#include "lbm_internal.cuh"
+#include "lbm_rows.cuh"
+
+namespace lbm {
+
+constexpr int kRows9 = 16;   // rows of a CTA's band
+
+// The value a link streams back when it leaves the body (ox: across the
+// left / right edge, oy: across the bottom / top edge; dx, dy its direction):
+// anti-bounce-back 2 w* - w on a Dirichlet edge, bounce-back w otherwise; a
+// link through a corner follows the Dirichlet edge if just one of the two is
+// Dirichlet, else the bottom / top edge.
+// Twice the Dirichlet value of each edge, selected without indexing (so that
+// it stays in registers).
+template <typename T>
+struct TwoWs {
+    T l, r, b, t;
+    __device__ __forceinline__ T operator[](int e) const { return e == LEFT ? l : (e == RIGHT ? r : (e == BOTTOM ? b : t)); }
+};
+
+template <typename T>
+__device__ __forceinline__ T leaving(const int32_t *edge, const TwoWs<T> &two_ws, bool ox, bool oy, int dx, int dy, T w0)
+{
+    const int ex = dx < 0 ? LEFT : RIGHT, ey = dy < 0 ? BOTTOM : TOP;
+    int e = ox ? ex : ey;
+    if (ox && oy) e = (edge[ex] == EDGE_DIRICHLET && edge[ey] != EDGE_DIRICHLET) ? ex : ey;
+    return edge[e] == EDGE_DIRICHLET ? two_ws[e] - w0 : w0;
+}
+
+// One warp's march up rows [j0, j1): a thread owns one 16-byte vector of a
+// row, with rows j-1, j, j+1 of w in registers and the east / west
+// neighbours of all three rows from the adjacent lanes (lanes 0 and 31 load
+// the halo columns), so each w is loaded about once.  Rows beyond a periodic
+// edge are loaded from the other side (likewise the halo column of the
+// leftmost thread and the column-0 values the thread owning column nx - 1
+// needs).  Rows of warps away from the left and right edges (edge_warp
+// false) take the bare update unless they are the bottom or top row or a
+// crack row; the others substitute the value each missing or severed link
+// streams back.
+template <typename T>
+__device__ __forceinline__ T march9(const StepArgs<T, T> &a, int x0, int j0, int j1, int64_t lq, int64_t rq,
+                                    const TwoWs<T> &two_ws, bool edge_warp)
+{
+    constexpr bool SPECIAL = true;
+    constexpr int N = Vec<T>::N;
+    typedef Row<T, N> R;
+    const unsigned kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int nx = a.nx, ny = a.ny, jc = a.p.jc;
+    const bool crack = a.p.mode != CRACK_NONE;
+    const bool per_x = a.edge[LEFT] == EDGE_PERIODIC, per_y = a.edge[BOTTOM] == EDGE_PERIODIC;
+    const int kr = nx - 1 - x0;                       // element holding column nx - 1, if in [0, N)
+    const bool owns_last = SPECIAL && kr >= 0 && kr < N && per_x;
+    const int64_t P = a.pitch;
+    const T *wbase = a.w_in;
+    const int hl_col = (SPECIAL && x0 == 0 && per_x) ? nx - 1 : x0 - 1;
+    const T ga = a.g * (T)(2.0 / 3.0), gd = a.g * (T)(1.0 / 6.0), dt = a.dt;
+
+    // issue the loads of a row: the vector, the halo column of lanes 0 / 31
+    // (l, rt) and the east neighbour of column nx - 1 across a periodic edge (z)
+    auto load = [&](int r, R &v, T &l, T &rt, T &z) {
+        if (SPECIAL && per_y) r = r < 0 ? r + ny : (r >= ny ? r - ny : r);
+        const T *row = wbase + (int64_t)r * P;
+        ldg_row(row + x0, v);
+        l = lane == 0 ? row[hl_col] : (T)0;
+        rt = lane == 31 ? row[x0 + N] : (T)0;
+        z = owns_last ? row[0] : (T)0;
+    };
+    // the west / east neighbours of a row's first and last element, once its
+    // loads have arrived (one iteration after they were issued)
+    auto sides = [&](const R &v, T &l, T &rt) {
+        const T su = __shfl_up_sync(kFull, v.v[N - 1], 1), sd = __shfl_down_sync(kFull, v.v[0], 1);
+        if (lane != 0) l = su;
+        if (lane != 31) rt = sd;
+    };
+    R wb, wc, wa, wdv;
+    T lb, rb, zb, lc, rc, zc, la, ra, za;
+    load(j0 - 1, wb, lb, rb, zb);
+    load(j0, wc, lc, rc, zc);
+    load(j0 + 1, wa, la, ra, za);
+    ld_row(a.wd + x0 + (int64_t)j0 * P, wdv);
+    sides(wb, lb, rb);
+    sides(wc, lc, rc);
+    sides(wa, la, ra);
+    T acc = (T)0;
+    for (int j = j0; j < j1; ++j) {
+        R wn, wdn;
+        T ln = (T)0, rn = (T)0, zn = (T)0;
+        const bool more = j + 1 < j1;
+        if (more) {
+            load(j + 2, wn, ln, rn, zn);
+            ld_row(a.wd + x0 + (int64_t)(j + 1) * P, wdn);
+        }
+        R wnew, wdnew;
+        const bool crow = crack && (j == jc - 1 || j == jc);
+        if (!edge_warp && !crow && j != 0 && j != ny - 1) {
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                const T wl = k == 0 ? lc : wc.v[k - 1], wr = k == N - 1 ? rc : wc.v[k + 1];
+                const T al = k == 0 ? la : wa.v[k - 1], ar = k == N - 1 ? ra : wa.v[k + 1];
+                const T bl = k == 0 ? lb : wb.v[k - 1], br = k == N - 1 ? rb : wb.v[k + 1];
+                const T axis = ((wa.v[k] + wb.v[k]) + (wl + wr)) - (T)4 * wc.v[k];
+                const T diag = ((al + ar) + (bl + br)) - (T)4 * wc.v[k];
+                wdnew.v[k] = wdv.v[k] + (ga * axis + gd * diag);
+                wnew.v[k] = wc.v[k] + dt * wdnew.v[k];
+            }
+            stg_row(a.w_out + x0 + (int64_t)j * P, wnew);
+            stg_row(a.wd + x0 + (int64_t)j * P, wdnew);
+            acc += wnew.v[0];
+        } else {
+            uint32_t vbits = 0;
+            if (crow && x0 < nx) vbits = a.cut_v[(int64_t)(jc - 1) * a.words + (x0 >> 5)] >> (x0 & 31);
+            const bool below = j == jc - 1;           // crack row under the crack line: its links go up
+            const bool bot = j == 0 && !per_y, top = j == ny - 1 && !per_y;
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                const int i = x0 + k;
+                const T w0 = wc.v[k];
+                const bool lft = i == 0 && !per_x, rgt = i == nx - 1 && !per_x;
+                const bool wrapr = i == nx - 1 && per_x;
+                T wl = k == 0 ? lc : wc.v[k - 1], wr = k == N - 1 ? rc : wc.v[k + 1];
+                T al = k == 0 ? la : wa.v[k - 1], ar = k == N - 1 ? ra : wa.v[k + 1];
+                T bl = k == 0 ? lb : wb.v[k - 1], br = k == N - 1 ? rb : wb.v[k + 1];
+                T up = wa.v[k], dn = wb.v[k];
+                if (wrapr) { wr = zc; ar = za; br = zb; }
+                // the links across the crack line
+                bool cv = false, cl = false, cr = false;
+                if (crow) {
+                    cv = (vbits >> k) & 1u;
+                    const int64_t ml = (int64_t)i << kQBits, mr = (int64_t)(i + 1) << kQBits;
+                    cl = i >= 1 && lq <= ml && ml <= rq;
+                    cr = i + 1 <= nx - 1 && lq <= mr && mr <= rq;
+                }
+                // west, east, north, south
+                if (lft) wl = leaving(a.edge, two_ws, true, false, -1, 0, w0);
+                if (rgt) wr = leaving(a.edge, two_ws, true, false, 1, 0, w0);
+                if (top) up = leaving(a.edge, two_ws, false, true, 0, 1, w0);
+                else if (crow && below && cv) up = w0;
+                if (bot) dn = leaving(a.edge, two_ws, false, true, 0, -1, w0);
+                else if (crow && !below && cv) dn = w0;
+                // the diagonals
+                if (crow && below && cl) al = w0;
+                else if (lft || top) al = leaving(a.edge, two_ws, lft, top, -1, 1, w0);
+                if (crow && below && cr) ar = w0;
+                else if (rgt || top) ar = leaving(a.edge, two_ws, rgt, top, 1, 1, w0);
+                if (crow && !below && cl) bl = w0;
+                else if (lft || bot) bl = leaving(a.edge, two_ws, lft, bot, -1, -1, w0);
+                if (crow && !below && cr) br = w0;
+                else if (rgt || bot) br = leaving(a.edge, two_ws, rgt, bot, 1, -1, w0);
+                const T axis = ((up + dn) + (wl + wr)) - (T)4 * w0;
+                const T diag = ((al + ar) + (bl + br)) - (T)4 * w0;
+                wdnew.v[k] = wdv.v[k] + (ga * axis + gd * diag);
+                wnew.v[k] = w0 + dt * wdnew.v[k];
+            }
+            if (x0 + N <= nx) {
+                stg_row(a.w_out + x0 + (int64_t)j * P, wnew);
+                stg_row(a.wd + x0 + (int64_t)j * P, wdnew);
+            } else {
+#pragma unroll
+                for (int k = 0; k < N; ++k)
+                    if (x0 + k < nx) {
+                        a.w_out[x0 + k + (int64_t)j * P] = wnew.v[k];
+                        a.wd[x0 + k + (int64_t)j * P] = wdnew.v[k];
+                    }
+            }
+            if (x0 < nx) acc += wnew.v[0];
+        }
+        wb = wc; lb = lc; rb = rc; zb = zc;
+        wc = wa; lc = la; rc = ra; zc = za;
+        if (more) {
+            sides(wn, ln, rn);
+            wa = wn; la = ln; ra = rn; za = zn;
+            wdv = wdn;
+        }
+    }
+    return acc;
+}
+
+// The grid is (column blocks of kThreads vectors) x (bands of kRows9 rows).
+template <typename T>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBlocks - 2)
+    d2q9_step_kernel(const StepArgs<T, T> a)
+{
+    constexpr int N = Vec<T>::N;
+    const int lane = threadIdx.x & 31;
+    const int nx = a.nx, ny = a.ny, jc = a.p.jc;
+    const int x0 = (blockIdx.x * kThreads + threadIdx.x) * N;
+    const int xw0 = (blockIdx.x * kThreads + (threadIdx.x & ~31)) * N;
+    const int j0 = blockIdx.y * kRows9, j1 = min(j0 + kRows9, ny);
+    const bool crack = a.p.mode != CRACK_NONE;
+    const bool edge_warp = xw0 == 0 || xw0 + 32 * N - 1 >= nx - 1;
+    int64_t lq = 0, rq = -1;
+    if (crack) {
+        rq = a.s_in->r.tip_q;
+        lq = a.p.two_tips ? a.s_in->l.tip_q : a.p.start_q;
+    }
+    const TwoWs<T> two_ws{(T)2 * (T)a.s_in->wstar[LEFT], (T)2 * (T)a.s_in->wstar[RIGHT],
+                          (T)2 * (T)a.s_in->wstar[BOTTOM], (T)2 * (T)a.s_in->wstar[TOP]};
+    const T acc = march9<T>(a, x0, j0, j1, lq, rq, two_ws, edge_warp);
+    // a non-finite w (or wdot, which enters w) turns the sum of the first
+    // element of each vector non-finite within a step or two
+    if (__any_sync(0xffffffffu, !isfinite(acc)) && lane == 0) atomicOr(a.err, (uint32_t)ERR_NONFINITE);
+}
+
+template <typename T>
+cudaError_t launch_d2q9_step(const StepArgs<T, T> &a, cudaStream_t s)
+{
+    const dim3 grid((unsigned)a.ncb, (unsigned)((a.ny + kRows9 - 1) / kRows9));
+    d2q9_step_kernel<T><<<grid, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_d2q9_step<double>(const StepArgs<double, double> &, cudaStream_t);
+template cudaError_t launch_d2q9_step<float>(const StepArgs<float, float> &, cudaStream_t);
+
+}  // namespace lbm

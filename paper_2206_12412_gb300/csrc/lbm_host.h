@@ -29,6 +29,7 @@ struct lbm_handle {
     int32_t words;       // 32-bit mask words per row
     int32_t jc;          // crack line y = jc dh
     bool edge_macro;     // the macroscopic rule on the outer edges (one more kernel per step)
+    int32_t q;           // velocity set: 5 or 9 (D2Q9: its own update kernel and a crack kernel per step)
     // step kernel shape
     int32_t ncb;         // column blocks of kThreads vectors
     int32_t n_bands, band_rows, crack_band, sms, bps;

@@ -628,6 +628,42 @@ cudaError_t launch_finalize(const FinalizeArgs<T> &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// The crack step of Alg. 1 right after an LBM step, as a launch of its own
+// (one warp; used by the D2Q9 update, which has no crack band to host it):
+// reads the state after `step` steps from s_in (its crack step already
+// applied) and the new fields, applies the crack step that follows the new
+// step to both ends, and writes the state after step + 1 steps to s_out.
+template <typename T>
+__global__ void crack_kernel(const StepArgs<T, T> a)
+{
+    __shared__ CrackState sS;
+    if (threadIdx.x == 0) {
+        sS = *a.s_in;
+        sS.r.decided = 0;
+        sS.l.decided = 0;
+    }
+    __syncwarp();
+    crack_step_warp<T>(a.p, a.w_out, a.pitch, a.cut_v, a.hist, sS, +1, true);
+    if (a.p.two_tips) crack_step_warp<T>(a.p, a.w_out, a.pitch, a.cut_v, a.hist, sS, -1, true);
+    if (threadIdx.x == 0) {
+        const int64_t n = sS.step + 1;
+        sS.step = n;
+        if (a.p.mode != CRACK_NONE) sS.hist_n += 1;
+        sS.r.decided = 1;
+        sS.l.decided = 1;
+        for (int e = 0; e < 4; ++e)
+            sS.wstar[e] = a.edge[e] == EDGE_DIRICHLET ? load_value(a.load[e], n, (double)a.p.dt) : 0.0;
+        *a.s_out = sS;
+    }
+}
+
+template <typename T>
+cudaError_t launch_crack_step(const StepArgs<T, T> &a, cudaStream_t s)
+{
+    crack_kernel<T><<<1, 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------- halo exchange
 
 // Row slabs of a decomposed lattice: after each step, each boundary row of a
@@ -875,6 +911,8 @@ template cudaError_t launch_edge_rule<double, double>(const StepArgs<double, dou
 template cudaError_t launch_edge_rule<float, float>(const StepArgs<float, float> &, cudaStream_t);
 template cudaError_t launch_edge_rule<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> &, cudaStream_t);
 template cudaError_t launch_edge_rule<float, __half>(const StepArgs<float, __half> &, cudaStream_t);
+template cudaError_t launch_crack_step<double>(const StepArgs<double, double> &, cudaStream_t);
+template cudaError_t launch_crack_step<float>(const StepArgs<float, float> &, cudaStream_t);
 template cudaError_t launch_fill_pads<float>(float *, int64_t, int, int, const int32_t *, cudaStream_t);
 template cudaError_t launch_fill_pads<double>(double *, int64_t, int, int, const int32_t *, cudaStream_t);
 

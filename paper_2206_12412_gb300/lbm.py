@@ -202,7 +202,7 @@ def make_structs(problem: dict, storage: str = "f32"):
     for e in range(4):
         g.edge[e] = A.EDGE[edges[e]]
     lat = A.Lattice_()
-    lat.velocity_set, lat.form = 0, 0
+    lat.velocity_set, lat.form = A.VELOCITY_SET[problem.get("lattice", "D2Q5")], 0
     lat.omega = float(problem.get("omega", 1.0))
     lat.storage = A.STORAGE[storage]
     lat.bc_mode = A.BC[problem.get("bc_mode", "bounceback")]

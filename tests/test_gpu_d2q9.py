@@ -1,0 +1,160 @@
+"""The D2Q9 lattice (include/lbm.h: LBM_D2Q9) through the C ABI against the
+oracle's D2Q9: fields at the FP64 / FP32 tolerances of test_gpu_parity.py,
+tips and cut masks bit-exact; every edge kind and corner, periodic wraps of
+the diagonal links, ragged lattices, crack growth of one and two tips (the
+diagonal links severed with the vertical ones), single launches and graph
+chunks, and the calls that reject the lattice."""
+import numpy as np
+import pytest
+
+from paper_2206_12412_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_12412_gb300 import lbm
+    lbm.load_library()
+    return lbm
+
+
+def _problem(nx, ny, edges=("free", "free", "dirichlet", "dirichlet"), cs=0.5):
+    p = W.base_problem(nx, ny, bc_mode="bounceback", edges=edges, cs=cs)
+    p["lattice"] = "D2Q9"
+    return p
+
+
+def _close(o, g, tol, floor=0.0):
+    wo, wdo = o.fields()
+    wg, wdg = g.fields()
+    scale = max(np.abs(wo).max(), floor, 1e-300)
+    assert np.abs(wg - wo).max() <= tol * scale, np.abs(wg - wo).max() / scale
+    assert np.abs(wdg - wdo).max() <= tol * scale, np.abs(wdg - wdo).max() / scale
+
+
+EDGE_SETS = [("free", "free", "dirichlet", "dirichlet"), ("dirichlet", "free", "dirichlet", "free"),
+             ("dirichlet", "dirichlet", "dirichlet", "dirichlet"), ("periodic", "periodic", "free", "dirichlet"),
+             ("dirichlet", "free", "periodic", "periodic"), ("periodic",) * 4]
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("edges", EDGE_SETS)
+@pytest.mark.parametrize("shape", [(1, 3), (3, 5), (37, 29), (261, 33)])
+def test_edges_against_oracle(oracle_mod, gpu, storage, edges, shape):
+    nx, ny = shape
+    p = _problem(nx, ny, edges, cs=0.8)           # g = 0.64: above the D2Q5 bound, below 3/4
+    rng = np.random.default_rng(nx * 7 + ny)
+    p["loads"] = [{"edge": nm, "kind": "sin2", "amp": float(1e-3 * rng.uniform(0.5, 2)), "t": 40.0}
+                  for e, nm in enumerate(("left", "right", "bottom", "top")) if edges[e] == "dirichlet"]
+    o = oracle_mod.Oracle(p)
+    g = gpu.Lattice(p, storage)
+    init = W.random_state(nx, ny, seed=nx * ny, dtype=np.float64 if storage == "f64" else np.float32)
+    o.set_fields(*init)
+    g.set_fields(*init)
+    done = 0
+    for n in (7, 64, 29):
+        o.step(n)
+        g.step(n)
+        done += n
+        tol = TOL[storage]
+        if storage == "f32":
+            # the leapfrog is neutral, so FP32 rounding accumulates: each step
+            # rounds w and a sum of terms up to (16 g / 3) max|w|; on lattices
+            # of a few sites max|w| does not average it out.  Bound: twice
+            # n (1 + 16 g / 3) 2^-24 after n steps (2.6e-5 measured at n = 100).
+            tol = max(tol, 2 * done * (1 + 16 * 0.64 / 3) * 2.0**-24)
+        # anti-bounce-back terms 2 w* - w enter every edge site's update and are
+        # rounded on the scale of 2 w*, which on lattices of a few sites can
+        # exceed the field itself
+        floor = 2 * max((ld["amp"] for ld in p["loads"]), default=0.0) if storage == "f32" else 0.0
+        _close(o, g, tol, floor)
+    g.close()
+    o.close()
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("two_tips", [False, True])
+def test_prescribed_growth(oracle_mod, gpu, storage, two_tips):
+    nx, ny, jc = 300, 40, 20
+    p = _problem(nx, ny)
+    p = W.with_crack(p, mode="prescribed", y=float(jc), x_start=120.3 if two_tips else 0.0, x_tip=160.6,
+                     v_rel=0.6, two_tips=two_tips)
+    p = W.with_antisymmetric_ramp(p, 1e-3, 50.0)
+    o = oracle_mod.Oracle(p)
+    g = gpu.Lattice(p, storage)
+    for n in (5, 64, 200, 300):
+        o.step(n)
+        g.step(n)
+    _close(o, g, TOL[storage])
+    np.testing.assert_array_equal(g.cut_mask("v"), o.cuts()[1].astype(bool))
+    np.testing.assert_array_equal(g.history()["tip_q"], o.history()["tip_q"])
+    if two_tips:
+        np.testing.assert_array_equal(g.history_left()["tip_q"], o.history_left()["tip_q"])
+    g.close()
+    o.close()
+
+
+@pytest.mark.parametrize("edges", [("dirichlet", "dirichlet", "free", "dirichlet"), ("periodic", "periodic", "dirichlet", "free")])
+def test_edge_crack_at_a_dirichlet_or_periodic_side(oracle_mod, gpu, edges):
+    """A crack from x = 0 to x = nx: the diagonal links at the ends leave the
+    body through the side edges and take their rules, not the crack's."""
+    nx, ny = 50, 20
+    p = _problem(nx, ny, edges)
+    p["loads"] = [{"edge": nm, "kind": "const", "amp": 1e-3 * (e + 1)}
+                  for e, nm in enumerate(("left", "right", "bottom", "top")) if edges[e] == "dirichlet"]
+    p = W.with_crack(p, mode="prescribed", y=10.0, x_start=0.0, x_tip=40.2, v_rel=0.7)
+    o = oracle_mod.Oracle(p)
+    g = gpu.Lattice(p, "f64")
+    o.step(120)
+    g.step(120)
+    assert o.crack()["tip_q"] == nx * 2**32
+    _close(o, g, 1e-12)
+    g.close()
+    o.close()
+
+
+def test_kcrit_growth_fp64(oracle_mod, gpu):
+    nx, ny = 160, 48
+    p = _problem(nx, ny)
+    p = W.with_antisymmetric_ramp(p, 2e-3, 60.0)
+    K_C = 0.5 * W.strip_reference_K(0.25, 2e-3, 48.0)
+    p = W.with_crack(p, mode="kcrit", y=24.0, x_start=60.0, x_tip=90.0, K_C=K_C, v_max=0.85, r0=2.0, two_tips=True)
+    o = oracle_mod.Oracle(p)
+    g = gpu.Lattice(p, "f64")
+    o.step(500)
+    g.step(500)
+    ho, hg = o.history(), g.history()
+    assert ho["grew"].sum() > 10
+    np.testing.assert_array_equal(hg["tip_q"], ho["tip_q"])
+    np.testing.assert_array_equal(g.history_left()["tip_q"], o.history_left()["tip_q"])
+    np.testing.assert_allclose(hg["K"], ho["K"], rtol=1e-9, atol=1e-12 * K_C)
+    _close(o, g, 1e-12)
+    g.close()
+    o.close()
+
+
+def test_calls_that_reject_the_lattice(gpu):
+    p = _problem(64, 32)
+    g = gpu.Lattice(p, "f32")
+    with pytest.raises(gpu.LbmError):
+        gpu.Batch([g])
+    with pytest.raises(gpu.LbmError):
+        gpu.Tape(g, np.array([[5, 5]], np.int32), 4)
+    with pytest.raises(gpu.LbmError):
+        gpu.Decomp(p, 2, "f32")
+    g.close()
+    for storage in ("f32_bf16", "f32_f16"):
+        with pytest.raises(gpu.LbmError):
+            gpu.Lattice(p, storage)
+    for bc in ("macroscopic", "macroscopic_edges"):
+        q = dict(p, bc_mode=bc)
+        with pytest.raises(gpu.LbmError):
+            gpu.Lattice(q, "f32")
+    with pytest.raises(gpu.LbmError):
+        gpu.Lattice(_problem(64, 32, cs=0.9), "f32")     # g = 0.81 > 3/4
