@@ -326,6 +326,49 @@ def measure_large(lbm, W, torch, stream, peak):
     return out
 
 
+def step_time(lbm, p, storage, stream, flush_l2, prelude, steps):
+    """Mean time of one lbm_step(1) (library CUDA events around its launches)
+    with the L2 flushed before each step."""
+    lat = lbm.Lattice(p, storage, stream=stream)
+    lat.step(prelude)
+    lat.set_profiling(True)
+    for _ in range(steps):
+        flush_l2()
+        lat.step(1)
+    lat.sync()
+    pr = lat.profile(reset=True)
+    lat.close()
+    return pr["step_ms"] / max(pr["n_step"], 1) * 1e-3
+
+
+def crack_share(lbm, W, torch, stream, problem, flush_l2, t_crack, steps=100):
+    """The cost of the crack handling, the GPU analogue of the CPU-time share
+    the paper reports (Sec. 5.3): the benchmark lattice's step time with its
+    K-criterion crack against the same lattice, loads and state size with no
+    crack, and the same for the Sec. 5.2 example (whole 5050-step runs)."""
+    q = dict(problem, crack={"mode": "none"})
+    t_none = step_time(lbm, q, "f32", stream, flush_l2, 2500, steps)
+    out = {"kcrit_single": {"step_us_crack": t_crack * 1e6, "step_us_no_crack": t_none * 1e6,
+                            "share": 1.0 - t_none / t_crack}}
+    times = {}
+    for label, p in (("crack", W.kcrit_centre_crack()), ("none", dict(W.kcrit_centre_crack(), crack={"mode": "none"}))):
+        lat = lbm.Lattice(p, "f32", stream=stream)
+        lat.step(64)
+        lat.reset()
+        lat.sync()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        lat.step(W.KCRIT_CENTRE_STEPS)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        times[label] = ev0.elapsed_time(ev1) * 1e-3 / W.KCRIT_CENTRE_STEPS
+        lat.close()
+    out["centre_crack_sec52"] = {"step_us_crack": times["crack"] * 1e6, "step_us_no_crack": times["none"] * 1e6,
+                                 "share": 1.0 - times["none"] / times["crack"]}
+    out["paper"] = "CPU-time share of the crack step in the authors' Python code: 2.8 % (steady growth), 0.7 % (Sec. 5.2)"
+    return out
+
+
 def measure_extensions(lbm, W, torch, stream, problem, peak, flush_l2, steps=100):
     """The two extensions beyond the plain method.  D2Q9: the benchmark
     workload on the nine-velocity lattice (bounce-back crack faces, FP32), the
@@ -499,6 +542,8 @@ def run_ours(args, rank, world, local):
     vranks = measure_virtual_ranks(lbm, W, torch, stream, problem) if not args.no_virtual_ranks else None
     large = measure_large(lbm, W, torch, stream, peak) if not args.no_large else None
     ext = measure_extensions(lbm, W, torch, stream, problem, peak, flush_l2) if not args.no_extensions else None
+    if ext is not None:
+        ext["crack_share"] = crack_share(lbm, W, torch, stream, problem, flush_l2, kern_s)
 
     # steady back-to-back replay (CUDA graph, no flush): context only
     lat.sync()

@@ -219,7 +219,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
     }
     const TwoWs<T> two_ws{(T)2 * (T)a.s_in->wstar[LEFT], (T)2 * (T)a.s_in->wstar[RIGHT],
                           (T)2 * (T)a.s_in->wstar[BOTTOM], (T)2 * (T)a.s_in->wstar[TOP]};
-    const T acc = march9<T>(a, x0, j0, j1, lq, rq, two_ws, edge_warp);
+    // warps wholly right of the lattice have nothing to load or store
+    const T acc = xw0 < nx ? march9<T>(a, x0, j0, j1, lq, rq, two_ws, edge_warp) : (T)0;
     // a non-finite w (or wdot, which enters w) turns the sum of the first
     // element of each vector non-finite within a step or two
     if (__any_sync(0xffffffffu, !isfinite(acc)) && lane == 0) atomicOr(a.err, (uint32_t)ERR_NONFINITE);

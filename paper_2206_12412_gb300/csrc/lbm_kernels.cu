@@ -353,12 +353,13 @@ __device__ __forceinline__ void march(const StepArgs<T, D> &a, int cb, int j0, i
     EdgeValues<T> E;
     if (EDGE) E = edge_values<T>(a.s_in);
     for (int j = j0; j < j1; ++j) {
-        R wn, wdn;
+        R wn;
+        typename WdIO<D>::Raw wdn;   // converted after this row's update, when it has arrived
         T hln = (T)0, hrn = (T)0;
         const bool more = j + 1 < j1;
         if (more) {
             ldg_row(win + (int64_t)(j + 2) * P, wn);
-            WdIO<D>::load(wdp + (int64_t)(j + 1) * P, wdn, wd_inv);
+            WdIO<D>::fetch(wdp + (int64_t)(j + 1) * P, wdn);
             if (lane == 0) hln = win[(int64_t)(j + 1) * P - 1];
             if (lane == 31) hrn = win[(int64_t)(j + 1) * P + N];
         }
@@ -390,7 +391,7 @@ __device__ __forceinline__ void march(const StepArgs<T, D> &a, int cb, int j0, i
         wc = wa;
         if (more) {
             wa = wn;
-            wdv = wdn;
+            WdIO<D>::unpack(wdn, wdv, wd_inv);
             hl = hln;
             hr = hrn;
         }
@@ -481,8 +482,12 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
         // and the bands holding the bottom and top rows, need them
         const int xw0 = (cb * kThreads + (tid & ~31)) * N;   // first column of this warp
         const bool edge = (xw0 == 0) | (xw0 + 32 * N - 1 >= nx - 1) | (j0 == 0) | (j1 == a.ny);
-        if (edge) march<T, D, true>(a, cb, j0, j1, acc);
-        else march<T, D, false>(a, cb, j0, j1, acc);
+        // warps wholly right of the lattice (the ragged last column block) have
+        // nothing to load or store
+        if (xw0 < nx) {
+            if (edge) march<T, D, true>(a, cb, j0, j1, acc);
+            else march<T, D, false>(a, cb, j0, j1, acc);
+        }
     }
     // a non-finite w (or wdot, which enters w) turns the sum of the first
     // component of each vector non-finite within a step or two

@@ -51,25 +51,41 @@ __device__ __forceinline__ void stg_row(double *p, const Row<double, 2> &r)
 // Storage of wdot.  FP64 and FP32 store the value; the 16-bit forms store
 // wdot * scale rounded to nearest (BF16: scale 1; FP16: a power of two chosen
 // so that the values sit well inside FP16's range), arithmetic stays FP32.
+// fetch() issues the load of a row into its raw form and unpack() converts
+// it, so that a march can keep a 16-bit row in flight for a whole iteration
+// (converting right after the load would wait for it there).
 template <typename D> struct WdIO;
 template <> struct WdIO<double> {
+    typedef Row<double, 2> Raw;
+    static __device__ __forceinline__ void fetch(const double *p, Raw &r) { ld_row(p, r); }
+    static __device__ __forceinline__ void unpack(const Raw &q, Row<double, 2> &r, double) { r = q; }
     static __device__ __forceinline__ void load(const double *p, Row<double, 2> &r, double) { ld_row(p, r); }
     static __device__ __forceinline__ void store(double *p, const Row<double, 2> &r, double) { stg_row(p, r); }
     static __device__ __forceinline__ void put(double *p, double v, double) { *p = v; }
 };
 template <> struct WdIO<float> {
+    typedef Row<float, 4> Raw;
+    static __device__ __forceinline__ void fetch(const float *p, Raw &r) { ld_row(p, r); }
+    static __device__ __forceinline__ void unpack(const Raw &q, Row<float, 4> &r, float) { r = q; }
     static __device__ __forceinline__ void load(const float *p, Row<float, 4> &r, float) { ld_row(p, r); }
     static __device__ __forceinline__ void store(float *p, const Row<float, 4> &r, float) { stg_row(p, r); }
     static __device__ __forceinline__ void put(float *p, float v, float) { *p = v; }
 };
 template <> struct WdIO<__nv_bfloat16> {
-    static __device__ __forceinline__ void load(const __nv_bfloat16 *p, Row<float, 4> &r, float)
+    typedef uint2 Raw;
+    static __device__ __forceinline__ void fetch(const __nv_bfloat16 *p, Raw &q) { q = *reinterpret_cast<const uint2 *>(p); }
+    static __device__ __forceinline__ void unpack(const Raw &q, Row<float, 4> &r, float)
     {
-        const uint2 q = *reinterpret_cast<const uint2 *>(p);
         r.v[0] = __uint_as_float(q.x << 16);
         r.v[1] = __uint_as_float(q.x & 0xffff0000u);
         r.v[2] = __uint_as_float(q.y << 16);
         r.v[3] = __uint_as_float(q.y & 0xffff0000u);
+    }
+    static __device__ __forceinline__ void load(const __nv_bfloat16 *p, Row<float, 4> &r, float s)
+    {
+        Raw q;
+        fetch(p, q);
+        unpack(q, r, s);
     }
     static __device__ __forceinline__ void store(__nv_bfloat16 *p, const Row<float, 4> &r, float)
     {
@@ -85,9 +101,16 @@ template <> struct WdIO<__nv_bfloat16> {
 };
 template <> struct WdIO<__half> {
     // scale: stored = wdot * scale; loads multiply by 1 / scale (both exact powers of two)
+    typedef uint2 Raw;
+    static __device__ __forceinline__ void fetch(const __half *p, Raw &q) { q = *reinterpret_cast<const uint2 *>(p); }
     static __device__ __forceinline__ void load(const __half *p, Row<float, 4> &r, float inv)
     {
-        const uint2 q = *reinterpret_cast<const uint2 *>(p);
+        Raw q;
+        fetch(p, q);
+        unpack(q, r, inv);
+    }
+    static __device__ __forceinline__ void unpack(const Raw &q, Row<float, 4> &r, float inv)
+    {
         const __half2 lo = *reinterpret_cast<const __half2 *>(&q.x);
         const __half2 hi = *reinterpret_cast<const __half2 *>(&q.y);
         const float2 a = __half22float2(lo), b = __half22float2(hi);
