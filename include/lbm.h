@@ -72,8 +72,7 @@ enum { LBM_LEFT = 0, LBM_RIGHT = 1, LBM_BOTTOM = 2, LBM_TOP = 3 };
  * x = (i + 1) dh and are severed when that point lies on the closed crack
  * segment; a diagonal link leaving the body through a corner follows the
  * Dirichlet edge if just one of the two is Dirichlet, else the bottom / top
- * edge.  Each D2Q9 time step is two launches: the update, then the crack
- * step of Alg. 1. */
+ * edge. */
 enum { LBM_D2Q5 = 0, LBM_D2Q9 = 1 };
 enum { LBM_FORM_MOMENT = 0 };
 /* storage of the fields.  LBM_F64: w and wdot in FP64, FP64 arithmetic.

@@ -73,11 +73,7 @@ cudaError_t enqueue_step_t(const lbm_handle *h, int par, cudaStream_t s)
     StepArgs<T, D> a;
     make_step_args(h, par, a);
     if constexpr (std::is_same<T, D>::value) {
-        if (h->q == 9) {
-            cudaError_t e = launch_d2q9_step(a, s);
-            if (e == cudaSuccess) e = launch_crack_step(a, s);
-            return e;
-        }
+        if (h->q == 9) return launch_d2q9_step(a, s);
     }
     cudaError_t e = launch_step(a, h->n_bands, s);
     if (e == cudaSuccess && h->edge_macro) e = launch_edge_rule(a, s);

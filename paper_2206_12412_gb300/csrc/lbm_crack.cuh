@@ -1,0 +1,184 @@
+// lbm_crack.cuh -- device code shared by the time-step kernels: the
+// boundary value of a Dirichlet edge and the warp-collective crack step of
+// Alg. 1 for one end of the crack.
+#pragma once
+
+#include "lbm_internal.cuh"
+
+namespace lbm {
+
+// ------------------------------------------------------------ edge values
+
+__device__ __forceinline__ double load_value(const LoadDesc L, int64_t n, double dt)
+{
+    const double t = (double)n * dt;
+    switch (L.kind) {
+    case LOAD_LINEAR:
+        return (L.t <= 0.0 || t >= L.t) ? L.amp : L.amp * (t / L.t);
+    case LOAD_SIN2: {
+        if (L.t <= 0.0 || t >= L.t) return L.amp;
+        const double sn = sin(kPi * t / (2.0 * L.t));
+        return L.amp * sn * sn;
+    }
+    case LOAD_HALFSINE:
+        return t >= L.t ? 0.0 : L.amp * sin(kPi * t / L.t);
+    case LOAD_SERIES:
+        if (L.n <= 0) return 0.0;
+        return L.series[n < L.n ? n : L.n - 1];
+    case LOAD_CONST:
+        return L.amp;
+    default:
+        return 0.0;
+    }
+}
+
+// ------------------------------------------------------------ crack step
+//
+// Warp-collective crack handling of Alg. 1 for one end of the crack (dir =
+// +1: the right end, growing towards +x; -1: the left end of a two-tip
+// crack, growing towards -x) of the state S (in shared memory), given the
+// fields w after the LBM step.  (1) K_III by least squares of the crack
+// opening over the site pairs straddling the crack at r in [r_min, r_min + W)
+// behind the tip (eq. sif; Sec. 4.2 and eq. r(v) with this end's previous
+// speed), in FP64 with a warp reduction.  (2) The criterion: prescribed
+// growth, or |K| > K_C with v = v_max tanh(sqrt((K/K_C)^4 - 1)) (eq.
+// v-tanh).  (3) The advance Delta a = adot dt, rounded to the 2^-32 dh grid;
+// the links at x_i = (i + 1/2) dh between the old and the new tip are
+// severed (closed segment); the right end stops at x = nx dh, the left at 0.
+// Lane 0 updates this end's fields of S (and i_last or i_first) and the cut
+// mask and, if `commit`, writes this end's history record at hist_n (the
+// caller advances hist_n once per crack step).  Two CTAs may run it on the
+// same state at once: both reach the same decision and set the same bits.
+template <typename T>
+__device__ __forceinline__ void crack_step_warp(const CrackParams &p, const T *w, int64_t P, uint32_t *cut_v,
+                                                const History &hist, CrackState &S, int dir, bool commit)
+{
+    const int lane = threadIdx.x & 31;
+    TipState &E = dir > 0 ? S.r : S.l;
+    if (p.mode == CRACK_NONE || E.decided) {
+        __syncwarp();
+        if (lane == 0) E.decided = 1;
+        __syncwarp();
+        return;
+    }
+    const int64_t tip = E.tip_q;
+    const int i_first = S.i_first, i_last = S.i_last;
+    const double r_min = p.r_min_fixed > 0.0 ? p.r_min_fixed : p.r0 / (1.0 - E.v_prev);   // eq. r(v)
+    const double lo = r_min / p.dh, hi = (r_min + p.fit_width) / p.dh;
+    const double tip_h = (double)tip * kTwoM32;
+    int c_lo, c_hi;
+    if (dir > 0) {
+        c_lo = (int)floor(tip_h - hi - 0.5) - 1;
+        c_hi = (int)floor(tip_h - lo - 0.5) + 1;
+    } else {
+        c_lo = (int)floor(tip_h + lo - 0.5) - 1;
+        c_hi = (int)floor(tip_h + hi - 0.5) + 1;
+    }
+    c_lo = c_lo < i_first ? i_first : c_lo;
+    c_hi = c_hi > i_last ? i_last : c_hi;
+    const int jc = p.jc;
+    double num = 0.0, den = 0.0;
+    int np = 0;
+    for (int i = c_lo + lane; i <= c_hi; i += 32) {
+        // the pair's fields are loaded together with its mask word (the
+        // columns lie in [i_first, i_last], inside the lattice), so the two
+        // loads cost one round trip
+        const uint32_t word = cut_v[(int64_t)(jc - 1) * p.words + (i >> 5)];
+        const T above = w[(int64_t)jc * P + i], below = w[(int64_t)(jc - 1) * P + i];
+        if (!((word >> (i & 31)) & 1u)) continue;
+        const int64_t xq = (int64_t)(2 * i + 1) << (kQBits - 1);
+        const double r_h = (double)(dir > 0 ? tip - xq : xq - tip) * kTwoM32;
+        if (!(r_h >= lo && r_h < hi)) continue;
+        const double r = r_h * p.dh;
+        const double sf = sqrt(r / (2.0 * kPi));
+        const double delta = (double)above - (double)below;
+        num += delta * sf;
+        den += sf * sf;
+        ++np;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        num += __shfl_xor_sync(0xffffffffu, num, o);
+        den += __shfl_xor_sync(0xffffffffu, den, o);
+        np += __shfl_xor_sync(0xffffffffu, np, o);
+    }
+    if (lane == 0) {
+        const double K = np > 0 ? p.mu / 4.0 * num / den : 0.0;
+        int propagate = 0;
+        double v = 0.0;
+        if (p.mode == CRACK_PRESCRIBED) {
+            propagate = 1;
+            v = p.v_rel;
+        } else if (p.mode == CRACK_KCRIT && np > 0 && fabs(K) > p.K_C) {
+            const double ratio = fabs(K) / p.K_C;
+            propagate = 1;
+            v = p.v_max * tanh(sqrt(ratio * ratio * ratio * ratio - 1.0));   // eq. v-tanh
+        }
+        int32_t flags = E.flags;
+        if (!isfinite(K)) flags |= FLAG_NONFINITE;
+        if (E.arrested) { propagate = 0; v = 0.0; }
+        int grew = 0;
+        int64_t tip_new = tip;
+        const int jr = p.jc - 1;
+        const int64_t half = (int64_t)1 << (kQBits - 1);
+        if (propagate) {
+            const double adot = v * p.cs;
+            const int64_t dq = __double2ll_rn(adot * p.dt / p.dh * 4294967296.0);   // Delta a = adot dt
+            if (dir > 0) {
+                int64_t next = tip + dq;
+                if (next >= p.clamp_q) { next = p.clamp_q; E.arrested = 1; flags |= FLAG_CLAMPED; }
+                if (next > tip) {
+                    int64_t last = (next - half) >> kQBits;   // largest i with x_i <= next
+                    if (last > p.nx - 1) last = p.nx - 1;
+                    for (int64_t i = (int64_t)i_last + 1; i <= last; ++i) {
+                        if (i < i_first) continue;
+                        atomicOr(&cut_v[(int64_t)jr * p.words + (i >> 5)], 1u << (i & 31));
+                    }
+                    if (last > i_last && last >= i_first) S.i_last = (int32_t)last;
+                    tip_new = next;
+                    grew = 1;
+                }
+            } else {
+                int64_t next = tip - dq;
+                if (next <= 0) { next = 0; E.arrested = 1; flags |= FLAG_CLAMPED; }
+                if (next < tip) {
+                    int64_t first = (next - half + ((int64_t)1 << kQBits) - 1) >> kQBits;   // smallest i with x_i >= next
+                    if (first < 0) first = 0;
+                    for (int64_t i = first; i < (int64_t)i_first; ++i) {
+                        if (i > i_last) continue;
+                        atomicOr(&cut_v[(int64_t)jr * p.words + (i >> 5)], 1u << (i & 31));
+                    }
+                    if (first < i_first && first <= i_last) S.i_first = (int32_t)first;
+                    tip_new = next;
+                    grew = 1;
+                }
+            }
+        }
+        E.tip_q = tip_new;
+        E.v_prev = p.mode == CRACK_PRESCRIBED ? p.v_rel : v;
+        E.K = K;
+        E.v = v;
+        E.r_min = r_min;
+        E.npairs = np;
+        E.grew = grew;
+        E.flags = flags;
+        if (commit && p.hist_cap > 0) {
+            const int64_t h = S.hist_n % p.hist_cap;
+            if (dir > 0) {
+                hist.K[h] = K;
+                hist.v[h] = v;
+                hist.tip[h] = tip_new;
+                hist.np[h] = np;
+            } else {
+                hist.Kl[h] = K;
+                hist.vl[h] = v;
+                hist.tipl[h] = tip_new;
+                hist.npl[h] = np;
+            }
+        }
+        E.decided = 1;
+    }
+    __syncwarp();
+}
+
+}  // namespace lbm

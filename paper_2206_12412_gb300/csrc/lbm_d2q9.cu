@@ -19,8 +19,12 @@
 //
 // The interior marches like the D2Q5 step kernel (16 bytes per site update:
 // w and wdot read and written once); the outer-edge warps and the edge and
-// crack rows take a per-site path with every rule.  The crack step of Alg. 1
-// runs after the update as a kernel of its own (lbm_kernels.cu).
+// crack rows substitute what each missing or severed link streams back.  As
+// in the D2Q5 kernel, the crack step of Alg. 1 that follows step k - 1 is
+// applied at the start of step k, here by every CTA of the crack rows whose
+// columns a new cut can reach (a diagonal cut touches the columns on both
+// sides of its crossing): all reach the same decision, one records it.
+#include "lbm_crack.cuh"
 #include "lbm_internal.cuh"
 #include "lbm_rows.cuh"
 
@@ -205,17 +209,78 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
     d2q9_step_kernel(const StepArgs<T, T> a)
 {
     constexpr int N = Vec<T>::N;
-    const int lane = threadIdx.x & 31;
+    constexpr int cols = kThreads * N;
+    __shared__ CrackState sS;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int nx = a.nx, ny = a.ny, jc = a.p.jc;
-    const int x0 = (blockIdx.x * kThreads + threadIdx.x) * N;
-    const int xw0 = (blockIdx.x * kThreads + (threadIdx.x & ~31)) * N;
+    const int cb = blockIdx.x;
+    const int x0 = (cb * kThreads + tid) * N;
+    const int xw0 = (cb * kThreads + (tid & ~31)) * N;
     const int j0 = blockIdx.y * kRows9, j1 = min(j0 + kRows9, ny);
     const bool crack = a.p.mode != CRACK_NONE;
     const bool edge_warp = xw0 == 0 || xw0 + 32 * N - 1 >= nx - 1;
+    const CrackParams &p = a.p;
+    const CrackState *s_in = a.s_in;
     int64_t lq = 0, rq = -1;
     if (crack) {
-        rq = a.s_in->r.tip_q;
-        lq = a.p.two_tips ? a.s_in->l.tip_q : a.p.start_q;
+        // the CTAs of the crack rows near each end's next vertical link run
+        // its pending crack step: i_next for the right end, i_prev for the
+        // left one; the diagonal crossings a step can add lie between columns
+        // i_next - 1 and i_next + 2 (i_prev - 2 and i_prev + 1)
+        const bool crack_rows = (jc - 1 >= j0 && jc - 1 < j1) || (jc >= j0 && jc < j1);
+        const bool commit_band = jc - 1 >= j0 && jc - 1 < j1;
+        const int c0 = cb * cols, c1 = c0 + cols - 1;
+        int i_next = max(s_in->i_last + 1, s_in->i_first);
+        i_next = min(max(i_next, 0), nx - 1);
+        int i_prev = min(s_in->i_first - 1, s_in->i_last);
+        i_prev = min(max(i_prev, 0), nx - 1);
+        const bool right_here = crack_rows && c0 <= i_next + 2 && c1 >= i_next - 1;
+        const bool left_here = crack_rows && p.two_tips && c0 <= i_prev + 1 && c1 >= i_prev - 2;
+        if (right_here || left_here) {
+            const bool commit_r = right_here && commit_band && cb == i_next / cols;
+            const bool commit_l = left_here && commit_band && cb == i_prev / cols;
+            if (tid < 32) {
+                if (tid == 0) sS = *s_in;
+                __syncwarp();
+                const bool pending = !sS.r.decided;   // not yet applied by a deferred crack step
+                if (right_here) crack_step_warp<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, +1, commit_r);
+                if (left_here) crack_step_warp<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, -1, commit_l);
+                if (tid == 0 && commit_r) {
+                    CrackState *o = a.s_out;
+                    const int64_t n = sS.step + 1;
+                    o->step = n;
+                    o->hist_n = sS.hist_n + (pending ? 1 : 0);
+                    o->i_last = sS.i_last;
+                    if (!p.two_tips) o->i_first = sS.i_first;
+                    o->r = sS.r;
+                    o->r.decided = 0;
+                    for (int e = 0; e < 4; ++e)
+                        o->wstar[e] = a.edge[e] == EDGE_DIRICHLET ? load_value(a.load[e], n, (double)p.dt) : 0.0;
+                }
+                if (tid == 0 && commit_l) {
+                    CrackState *o = a.s_out;
+                    o->i_first = sS.i_first;
+                    o->l = sS.l;
+                    o->l.decided = 0;
+                }
+            }
+            __syncthreads();   // this CTA's new cuts and tips, for all of its threads
+            rq = sS.r.tip_q;
+            lq = p.two_tips ? sS.l.tip_q : p.start_q;
+        } else {
+            rq = s_in->r.tip_q;
+            lq = p.two_tips ? s_in->l.tip_q : p.start_q;
+        }
+    } else if (cb == 0 && blockIdx.y == 0 && tid == 0) {
+        // no crack: only the step counter and the Dirichlet values advance
+        CrackState st = *s_in;
+        const int64_t n = st.step + 1;
+        st.step = n;
+        st.r.decided = 1;
+        st.l.decided = 1;
+        for (int e = 0; e < 4; ++e)
+            st.wstar[e] = a.edge[e] == EDGE_DIRICHLET ? load_value(a.load[e], n, (double)p.dt) : 0.0;
+        *a.s_out = st;
     }
     const TwoWs<T> two_ws{(T)2 * (T)a.s_in->wstar[LEFT], (T)2 * (T)a.s_in->wstar[RIGHT],
                           (T)2 * (T)a.s_in->wstar[BOTTOM], (T)2 * (T)a.s_in->wstar[TOP]};

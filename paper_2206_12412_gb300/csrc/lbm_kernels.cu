@@ -21,6 +21,7 @@
 // link and writes state buffer (k + 1) & 1.  The macroscopic crack-face rule
 // (Sec. 3.1) is applied inside the crack band, whose rows jc-3 .. jc+2 form
 // a band of their own.
+#include "lbm_crack.cuh"
 #include "lbm_internal.cuh"
 #include "lbm_rows.cuh"
 
@@ -29,175 +30,6 @@
 #include <type_traits>
 
 namespace lbm {
-
-// ------------------------------------------------------------ edge values
-
-__device__ __forceinline__ double load_value(const LoadDesc L, int64_t n, double dt)
-{
-    const double t = (double)n * dt;
-    switch (L.kind) {
-    case LOAD_LINEAR:
-        return (L.t <= 0.0 || t >= L.t) ? L.amp : L.amp * (t / L.t);
-    case LOAD_SIN2: {
-        if (L.t <= 0.0 || t >= L.t) return L.amp;
-        const double sn = sin(kPi * t / (2.0 * L.t));
-        return L.amp * sn * sn;
-    }
-    case LOAD_HALFSINE:
-        return t >= L.t ? 0.0 : L.amp * sin(kPi * t / L.t);
-    case LOAD_SERIES:
-        if (L.n <= 0) return 0.0;
-        return L.series[n < L.n ? n : L.n - 1];
-    case LOAD_CONST:
-        return L.amp;
-    default:
-        return 0.0;
-    }
-}
-
-// ------------------------------------------------------------ crack step
-//
-// Warp-collective crack handling of Alg. 1 for one end of the crack (dir =
-// +1: the right end, growing towards +x; -1: the left end of a two-tip
-// crack, growing towards -x) of the state S (in shared memory), given the
-// fields w after the LBM step.  (1) K_III by least squares of the crack
-// opening over the site pairs straddling the crack at r in [r_min, r_min + W)
-// behind the tip (eq. sif; Sec. 4.2 and eq. r(v) with this end's previous
-// speed), in FP64 with a warp reduction.  (2) The criterion: prescribed
-// growth, or |K| > K_C with v = v_max tanh(sqrt((K/K_C)^4 - 1)) (eq.
-// v-tanh).  (3) The advance Delta a = adot dt, rounded to the 2^-32 dh grid;
-// the links at x_i = (i + 1/2) dh between the old and the new tip are
-// severed (closed segment); the right end stops at x = nx dh, the left at 0.
-// Lane 0 updates this end's fields of S (and i_last or i_first) and the cut
-// mask and, if `commit`, writes this end's history record at hist_n (the
-// caller advances hist_n once per crack step).  Two CTAs may run it on the
-// same state at once: both reach the same decision and set the same bits.
-template <typename T>
-__device__ __forceinline__ void crack_step_warp(const CrackParams &p, const T *w, int64_t P, uint32_t *cut_v,
-                                                const History &hist, CrackState &S, int dir, bool commit)
-{
-    const int lane = threadIdx.x & 31;
-    TipState &E = dir > 0 ? S.r : S.l;
-    if (p.mode == CRACK_NONE || E.decided) {
-        __syncwarp();
-        if (lane == 0) E.decided = 1;
-        __syncwarp();
-        return;
-    }
-    const int64_t tip = E.tip_q;
-    const int i_first = S.i_first, i_last = S.i_last;
-    const double r_min = p.r_min_fixed > 0.0 ? p.r_min_fixed : p.r0 / (1.0 - E.v_prev);   // eq. r(v)
-    const double lo = r_min / p.dh, hi = (r_min + p.fit_width) / p.dh;
-    const double tip_h = (double)tip * kTwoM32;
-    int c_lo, c_hi;
-    if (dir > 0) {
-        c_lo = (int)floor(tip_h - hi - 0.5) - 1;
-        c_hi = (int)floor(tip_h - lo - 0.5) + 1;
-    } else {
-        c_lo = (int)floor(tip_h + lo - 0.5) - 1;
-        c_hi = (int)floor(tip_h + hi - 0.5) + 1;
-    }
-    c_lo = c_lo < i_first ? i_first : c_lo;
-    c_hi = c_hi > i_last ? i_last : c_hi;
-    const int jc = p.jc;
-    double num = 0.0, den = 0.0;
-    int np = 0;
-    for (int i = c_lo + lane; i <= c_hi; i += 32) {
-        if (!((cut_v[(int64_t)(jc - 1) * p.words + (i >> 5)] >> (i & 31)) & 1u)) continue;
-        const int64_t xq = (int64_t)(2 * i + 1) << (kQBits - 1);
-        const double r_h = (double)(dir > 0 ? tip - xq : xq - tip) * kTwoM32;
-        if (!(r_h >= lo && r_h < hi)) continue;
-        const double r = r_h * p.dh;
-        const double sf = sqrt(r / (2.0 * kPi));
-        const double delta = (double)w[(int64_t)jc * P + i] - (double)w[(int64_t)(jc - 1) * P + i];
-        num += delta * sf;
-        den += sf * sf;
-        ++np;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        num += __shfl_xor_sync(0xffffffffu, num, o);
-        den += __shfl_xor_sync(0xffffffffu, den, o);
-        np += __shfl_xor_sync(0xffffffffu, np, o);
-    }
-    if (lane == 0) {
-        const double K = np > 0 ? p.mu / 4.0 * num / den : 0.0;
-        int propagate = 0;
-        double v = 0.0;
-        if (p.mode == CRACK_PRESCRIBED) {
-            propagate = 1;
-            v = p.v_rel;
-        } else if (p.mode == CRACK_KCRIT && np > 0 && fabs(K) > p.K_C) {
-            const double ratio = fabs(K) / p.K_C;
-            propagate = 1;
-            v = p.v_max * tanh(sqrt(ratio * ratio * ratio * ratio - 1.0));   // eq. v-tanh
-        }
-        int32_t flags = E.flags;
-        if (!isfinite(K)) flags |= FLAG_NONFINITE;
-        if (E.arrested) { propagate = 0; v = 0.0; }
-        int grew = 0;
-        int64_t tip_new = tip;
-        const int jr = p.jc - 1;
-        const int64_t half = (int64_t)1 << (kQBits - 1);
-        if (propagate) {
-            const double adot = v * p.cs;
-            const int64_t dq = __double2ll_rn(adot * p.dt / p.dh * 4294967296.0);   // Delta a = adot dt
-            if (dir > 0) {
-                int64_t next = tip + dq;
-                if (next >= p.clamp_q) { next = p.clamp_q; E.arrested = 1; flags |= FLAG_CLAMPED; }
-                if (next > tip) {
-                    int64_t last = (next - half) >> kQBits;   // largest i with x_i <= next
-                    if (last > p.nx - 1) last = p.nx - 1;
-                    for (int64_t i = (int64_t)i_last + 1; i <= last; ++i) {
-                        if (i < i_first) continue;
-                        atomicOr(&cut_v[(int64_t)jr * p.words + (i >> 5)], 1u << (i & 31));
-                    }
-                    if (last > i_last && last >= i_first) S.i_last = (int32_t)last;
-                    tip_new = next;
-                    grew = 1;
-                }
-            } else {
-                int64_t next = tip - dq;
-                if (next <= 0) { next = 0; E.arrested = 1; flags |= FLAG_CLAMPED; }
-                if (next < tip) {
-                    int64_t first = (next - half + ((int64_t)1 << kQBits) - 1) >> kQBits;   // smallest i with x_i >= next
-                    if (first < 0) first = 0;
-                    for (int64_t i = first; i < (int64_t)i_first; ++i) {
-                        if (i > i_last) continue;
-                        atomicOr(&cut_v[(int64_t)jr * p.words + (i >> 5)], 1u << (i & 31));
-                    }
-                    if (first < i_first && first <= i_last) S.i_first = (int32_t)first;
-                    tip_new = next;
-                    grew = 1;
-                }
-            }
-        }
-        E.tip_q = tip_new;
-        E.v_prev = p.mode == CRACK_PRESCRIBED ? p.v_rel : v;
-        E.K = K;
-        E.v = v;
-        E.r_min = r_min;
-        E.npairs = np;
-        E.grew = grew;
-        E.flags = flags;
-        if (commit && p.hist_cap > 0) {
-            const int64_t h = S.hist_n % p.hist_cap;
-            if (dir > 0) {
-                hist.K[h] = K;
-                hist.v[h] = v;
-                hist.tip[h] = tip_new;
-                hist.np[h] = np;
-            } else {
-                hist.Kl[h] = K;
-                hist.vl[h] = v;
-                hist.tipl[h] = tip_new;
-                hist.npl[h] = np;
-            }
-        }
-        E.decided = 1;
-    }
-    __syncwarp();
-}
 
 // ------------------------------------------------------------ step kernel
 //
@@ -633,42 +465,6 @@ cudaError_t launch_finalize(const FinalizeArgs<T> &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// The crack step of Alg. 1 right after an LBM step, as a launch of its own
-// (one warp; used by the D2Q9 update, which has no crack band to host it):
-// reads the state after `step` steps from s_in (its crack step already
-// applied) and the new fields, applies the crack step that follows the new
-// step to both ends, and writes the state after step + 1 steps to s_out.
-template <typename T>
-__global__ void crack_kernel(const StepArgs<T, T> a)
-{
-    __shared__ CrackState sS;
-    if (threadIdx.x == 0) {
-        sS = *a.s_in;
-        sS.r.decided = 0;
-        sS.l.decided = 0;
-    }
-    __syncwarp();
-    crack_step_warp<T>(a.p, a.w_out, a.pitch, a.cut_v, a.hist, sS, +1, true);
-    if (a.p.two_tips) crack_step_warp<T>(a.p, a.w_out, a.pitch, a.cut_v, a.hist, sS, -1, true);
-    if (threadIdx.x == 0) {
-        const int64_t n = sS.step + 1;
-        sS.step = n;
-        if (a.p.mode != CRACK_NONE) sS.hist_n += 1;
-        sS.r.decided = 1;
-        sS.l.decided = 1;
-        for (int e = 0; e < 4; ++e)
-            sS.wstar[e] = a.edge[e] == EDGE_DIRICHLET ? load_value(a.load[e], n, (double)a.p.dt) : 0.0;
-        *a.s_out = sS;
-    }
-}
-
-template <typename T>
-cudaError_t launch_crack_step(const StepArgs<T, T> &a, cudaStream_t s)
-{
-    crack_kernel<T><<<1, 32, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
 // ------------------------------------------------------- halo exchange
 
 // Row slabs of a decomposed lattice: after each step, each boundary row of a
@@ -916,8 +712,6 @@ template cudaError_t launch_edge_rule<double, double>(const StepArgs<double, dou
 template cudaError_t launch_edge_rule<float, float>(const StepArgs<float, float> &, cudaStream_t);
 template cudaError_t launch_edge_rule<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> &, cudaStream_t);
 template cudaError_t launch_edge_rule<float, __half>(const StepArgs<float, __half> &, cudaStream_t);
-template cudaError_t launch_crack_step<double>(const StepArgs<double, double> &, cudaStream_t);
-template cudaError_t launch_crack_step<float>(const StepArgs<float, float> &, cudaStream_t);
 template cudaError_t launch_fill_pads<float>(float *, int64_t, int, int, const int32_t *, cudaStream_t);
 template cudaError_t launch_fill_pads<double>(double *, int64_t, int, int, const int32_t *, cudaStream_t);
 
