@@ -120,7 +120,7 @@ __device__ __forceinline__ T march9(const StepArgs<T, T> &a, int x0, int j0, int
         }
         R wnew, wdnew;
         const bool crow = crack && (j == jc - 1 || j == jc);
-        if (!edge_warp && !crow && j != 0 && j != ny - 1) {
+        if (!crow && j != 0 && j != ny - 1) {
 #pragma unroll
             for (int k = 0; k < N; ++k) {
                 const T wl = k == 0 ? lc : wc.v[k - 1], wr = k == N - 1 ? rc : wc.v[k + 1];
@@ -131,9 +131,52 @@ __device__ __forceinline__ T march9(const StepArgs<T, T> &a, int x0, int j0, int
                 wdnew.v[k] = wdv.v[k] + (ga * axis + gd * diag);
                 wnew.v[k] = wc.v[k] + dt * wdnew.v[k];
             }
-            stg_row(a.w_out + x0 + (int64_t)j * P, wnew);
-            stg_row(a.wd + x0 + (int64_t)j * P, wdnew);
-            acc += wnew.v[0];
+            if (!edge_warp) {
+                stg_row(a.w_out + x0 + (int64_t)j * P, wnew);
+                stg_row(a.wd + x0 + (int64_t)j * P, wdnew);
+                acc += wnew.v[0];
+            } else {
+                // a warp at the left or right edge: redo the edge columns with
+                // the values their links across the edge stream back
+#pragma unroll
+                for (int k = 0; k < N; ++k) {
+                    const int i = x0 + k;
+                    if (!((i == 0 && !per_x) || i == nx - 1)) continue;
+                    const T w0 = wc.v[k];
+                    T wl = k == 0 ? lc : wc.v[k - 1], wr = k == N - 1 ? rc : wc.v[k + 1];
+                    T al = k == 0 ? la : wa.v[k - 1], ar = k == N - 1 ? ra : wa.v[k + 1];
+                    T bl = k == 0 ? lb : wb.v[k - 1], br = k == N - 1 ? rb : wb.v[k + 1];
+                    if (i == nx - 1) {
+                        if (per_x) { wr = zc; ar = za; br = zb; }
+                        else {
+                            wr = leaving(a.edge, two_ws, true, false, 1, 0, w0);
+                            ar = leaving(a.edge, two_ws, true, false, 1, 1, w0);
+                            br = leaving(a.edge, two_ws, true, false, 1, -1, w0);
+                        }
+                    }
+                    if (i == 0 && !per_x) {
+                        wl = leaving(a.edge, two_ws, true, false, -1, 0, w0);
+                        al = leaving(a.edge, two_ws, true, false, -1, 1, w0);
+                        bl = leaving(a.edge, two_ws, true, false, -1, -1, w0);
+                    }
+                    const T axis = ((wa.v[k] + wb.v[k]) + (wl + wr)) - (T)4 * w0;
+                    const T diag = ((al + ar) + (bl + br)) - (T)4 * w0;
+                    wdnew.v[k] = wdv.v[k] + (ga * axis + gd * diag);
+                    wnew.v[k] = w0 + dt * wdnew.v[k];
+                }
+                if (x0 + N <= nx) {
+                    stg_row(a.w_out + x0 + (int64_t)j * P, wnew);
+                    stg_row(a.wd + x0 + (int64_t)j * P, wdnew);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < N; ++k)
+                        if (x0 + k < nx) {
+                            a.w_out[x0 + k + (int64_t)j * P] = wnew.v[k];
+                            a.wd[x0 + k + (int64_t)j * P] = wdnew.v[k];
+                        }
+                }
+                if (x0 < nx) acc += wnew.v[0];
+            }
         } else {
             uint32_t vbits = 0;
             if (crow && x0 < nx) vbits = a.cut_v[(int64_t)(jc - 1) * a.words + (x0 >> 5)] >> (x0 & 31);
