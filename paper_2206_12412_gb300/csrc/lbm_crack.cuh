@@ -49,18 +49,23 @@ __device__ __forceinline__ double load_value(const LoadDesc L, int64_t n, double
 // mask and, if `commit`, writes this end's history record at hist_n (the
 // caller advances hist_n once per crack step).  Two CTAs may run it on the
 // same state at once: both reach the same decision and set the same bits.
-template <typename T>
-__device__ __forceinline__ void crack_step_warp(const CrackParams &p, const T *w, int64_t P, uint32_t *cut_v,
-                                                const History &hist, CrackState &S, int dir, bool commit)
+
+// The least-squares sums of step (1) for one end: num = sum delta_i s_i,
+// den = sum s_i^2 over the np pairs in the window, and the window's r_min.
+struct CrackSums {
+    double num, den, r_min;
+    int np;
+};
+
+// Step (1) for one end, by a group of G lanes (32: a warp; 16: a half warp,
+// so that one warp evaluates both ends at once); every lane of the group
+// gets the sums.  Reads S only.  All 32 lanes of the warp must call it.
+template <typename T, int G = 32>
+__device__ __forceinline__ CrackSums crack_eval_warp(const CrackParams &p, const T *w, int64_t P, const uint32_t *cut_v,
+                                                     const CrackState &S, int dir)
 {
-    const int lane = threadIdx.x & 31;
-    TipState &E = dir > 0 ? S.r : S.l;
-    if (p.mode == CRACK_NONE || E.decided) {
-        __syncwarp();
-        if (lane == 0) E.decided = 1;
-        __syncwarp();
-        return;
-    }
+    const int lane = threadIdx.x & (G - 1);
+    const TipState &E = dir > 0 ? S.r : S.l;
     const int64_t tip = E.tip_q;
     const int i_first = S.i_first, i_last = S.i_last;
     const double r_min = p.r_min_fixed > 0.0 ? p.r_min_fixed : p.r0 / (1.0 - E.v_prev);   // eq. r(v)
@@ -79,7 +84,7 @@ __device__ __forceinline__ void crack_step_warp(const CrackParams &p, const T *w
     const int jc = p.jc;
     double num = 0.0, den = 0.0;
     int np = 0;
-    for (int i = c_lo + lane; i <= c_hi; i += 32) {
+    for (int i = c_lo + lane; i <= c_hi; i += G) {
         // the pair's fields are loaded together with its mask word (the
         // columns lie in [i_first, i_last], inside the lattice), so the two
         // loads cost one round trip
@@ -97,87 +102,117 @@ __device__ __forceinline__ void crack_step_warp(const CrackParams &p, const T *w
         ++np;
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = G / 2; o > 0; o >>= 1) {
         num += __shfl_xor_sync(0xffffffffu, num, o);
         den += __shfl_xor_sync(0xffffffffu, den, o);
         np += __shfl_xor_sync(0xffffffffu, np, o);
     }
-    if (lane == 0) {
-        const double K = np > 0 ? p.mu / 4.0 * num / den : 0.0;
-        int propagate = 0;
-        double v = 0.0;
-        if (p.mode == CRACK_PRESCRIBED) {
-            propagate = 1;
-            v = p.v_rel;
-        } else if (p.mode == CRACK_KCRIT && np > 0 && fabs(K) > p.K_C) {
-            const double ratio = fabs(K) / p.K_C;
-            propagate = 1;
-            v = p.v_max * tanh(sqrt(ratio * ratio * ratio * ratio - 1.0));   // eq. v-tanh
-        }
-        int32_t flags = E.flags;
-        if (!isfinite(K)) flags |= FLAG_NONFINITE;
-        if (E.arrested) { propagate = 0; v = 0.0; }
-        int grew = 0;
-        int64_t tip_new = tip;
-        const int jr = p.jc - 1;
-        const int64_t half = (int64_t)1 << (kQBits - 1);
-        if (propagate) {
-            const double adot = v * p.cs;
-            const int64_t dq = __double2ll_rn(adot * p.dt / p.dh * 4294967296.0);   // Delta a = adot dt
-            if (dir > 0) {
-                int64_t next = tip + dq;
-                if (next >= p.clamp_q) { next = p.clamp_q; E.arrested = 1; flags |= FLAG_CLAMPED; }
-                if (next > tip) {
-                    int64_t last = (next - half) >> kQBits;   // largest i with x_i <= next
-                    if (last > p.nx - 1) last = p.nx - 1;
-                    for (int64_t i = (int64_t)i_last + 1; i <= last; ++i) {
-                        if (i < i_first) continue;
-                        atomicOr(&cut_v[(int64_t)jr * p.words + (i >> 5)], 1u << (i & 31));
-                    }
-                    if (last > i_last && last >= i_first) S.i_last = (int32_t)last;
-                    tip_new = next;
-                    grew = 1;
-                }
-            } else {
-                int64_t next = tip - dq;
-                if (next <= 0) { next = 0; E.arrested = 1; flags |= FLAG_CLAMPED; }
-                if (next < tip) {
-                    int64_t first = (next - half + ((int64_t)1 << kQBits) - 1) >> kQBits;   // smallest i with x_i >= next
-                    if (first < 0) first = 0;
-                    for (int64_t i = first; i < (int64_t)i_first; ++i) {
-                        if (i > i_last) continue;
-                        atomicOr(&cut_v[(int64_t)jr * p.words + (i >> 5)], 1u << (i & 31));
-                    }
-                    if (first < i_first && first <= i_last) S.i_first = (int32_t)first;
-                    tip_new = next;
-                    grew = 1;
-                }
-            }
-        }
-        E.tip_q = tip_new;
-        E.v_prev = p.mode == CRACK_PRESCRIBED ? p.v_rel : v;
-        E.K = K;
-        E.v = v;
-        E.r_min = r_min;
-        E.npairs = np;
-        E.grew = grew;
-        E.flags = flags;
-        if (commit && p.hist_cap > 0) {
-            const int64_t h = S.hist_n % p.hist_cap;
-            if (dir > 0) {
-                hist.K[h] = K;
-                hist.v[h] = v;
-                hist.tip[h] = tip_new;
-                hist.np[h] = np;
-            } else {
-                hist.Kl[h] = K;
-                hist.vl[h] = v;
-                hist.tipl[h] = tip_new;
-                hist.npl[h] = np;
-            }
-        }
-        E.decided = 1;
+    return CrackSums{num, den, r_min, np};
+}
+
+// K from the sums (eq. sif; least squares when the window holds several
+// pairs), then steps (2) and (3) for one end, by one thread: the criterion,
+// the advance, the severed links, this end's fields of S and, if `commit`,
+// its history record.
+__device__ __forceinline__ void crack_apply(const CrackParams &p, uint32_t *cut_v, const History &hist, CrackState &S,
+                                            int dir, bool commit, const CrackSums &c)
+{
+    const double K = c.np > 0 ? p.mu / 4.0 * c.num / c.den : 0.0;
+    const int np = c.np;
+    const double r_min = c.r_min;
+    TipState &E = dir > 0 ? S.r : S.l;
+    const int64_t tip = E.tip_q;
+    const int i_first = S.i_first, i_last = S.i_last;
+    int propagate = 0;
+    double v = 0.0;
+    if (p.mode == CRACK_PRESCRIBED) {
+        propagate = 1;
+        v = p.v_rel;
+    } else if (p.mode == CRACK_KCRIT && np > 0 && fabs(K) > p.K_C) {
+        const double ratio = fabs(K) / p.K_C;
+        propagate = 1;
+        v = p.v_max * tanh(sqrt(ratio * ratio * ratio * ratio - 1.0));   // eq. v-tanh
     }
+    int32_t flags = E.flags;
+    if (!isfinite(K)) flags |= FLAG_NONFINITE;
+    if (E.arrested) { propagate = 0; v = 0.0; }
+    int grew = 0;
+    int64_t tip_new = tip;
+    const int jr = p.jc - 1;
+    const int64_t half = (int64_t)1 << (kQBits - 1);
+    if (propagate) {
+        const double adot = v * p.cs;
+        const int64_t dq = __double2ll_rn(adot * p.dt / p.dh * 4294967296.0);   // Delta a = adot dt
+        if (dir > 0) {
+            int64_t next = tip + dq;
+            if (next >= p.clamp_q) { next = p.clamp_q; E.arrested = 1; flags |= FLAG_CLAMPED; }
+            if (next > tip) {
+                int64_t last = (next - half) >> kQBits;   // largest i with x_i <= next
+                if (last > p.nx - 1) last = p.nx - 1;
+                for (int64_t i = (int64_t)i_last + 1; i <= last; ++i) {
+                    if (i < i_first) continue;
+                    atomicOr(&cut_v[(int64_t)jr * p.words + (i >> 5)], 1u << (i & 31));
+                }
+                if (last > i_last && last >= i_first) S.i_last = (int32_t)last;
+                tip_new = next;
+                grew = 1;
+            }
+        } else {
+            int64_t next = tip - dq;
+            if (next <= 0) { next = 0; E.arrested = 1; flags |= FLAG_CLAMPED; }
+            if (next < tip) {
+                int64_t first = (next - half + ((int64_t)1 << kQBits) - 1) >> kQBits;   // smallest i with x_i >= next
+                if (first < 0) first = 0;
+                for (int64_t i = first; i < (int64_t)i_first; ++i) {
+                    if (i > i_last) continue;
+                    atomicOr(&cut_v[(int64_t)jr * p.words + (i >> 5)], 1u << (i & 31));
+                }
+                if (first < i_first && first <= i_last) S.i_first = (int32_t)first;
+                tip_new = next;
+                grew = 1;
+            }
+        }
+    }
+    E.tip_q = tip_new;
+    E.v_prev = p.mode == CRACK_PRESCRIBED ? p.v_rel : v;
+    E.K = K;
+    E.v = v;
+    E.r_min = r_min;
+    E.npairs = np;
+    E.grew = grew;
+    E.flags = flags;
+    if (commit && p.hist_cap > 0) {
+        const int64_t h = S.hist_n % p.hist_cap;
+        if (dir > 0) {
+            hist.K[h] = K;
+            hist.v[h] = v;
+            hist.tip[h] = tip_new;
+            hist.np[h] = np;
+        } else {
+            hist.Kl[h] = K;
+            hist.vl[h] = v;
+            hist.tipl[h] = tip_new;
+            hist.npl[h] = np;
+        }
+    }
+    E.decided = 1;
+}
+
+// Both steps for one end, by one warp (lane 0 applies).
+template <typename T>
+__device__ __forceinline__ void crack_step_warp(const CrackParams &p, const T *w, int64_t P, uint32_t *cut_v,
+                                                const History &hist, CrackState &S, int dir, bool commit)
+{
+    const int lane = threadIdx.x & 31;
+    TipState &E = dir > 0 ? S.r : S.l;
+    if (p.mode == CRACK_NONE || E.decided) {
+        __syncwarp();
+        if (lane == 0) E.decided = 1;
+        __syncwarp();
+        return;
+    }
+    const CrackSums c = crack_eval_warp<T>(p, w, P, cut_v, S, dir);
+    if (lane == 0) crack_apply(p, cut_v, hist, S, dir, commit, c);
     __syncwarp();
 }
 

@@ -232,7 +232,10 @@ __device__ __forceinline__ void march(const StepArgs<T, D> &a, int cb, int j0, i
 
 // One CTA of a time step: column block cb of band `band` of the lattice that
 // `a` describes (the kernel parameter block, or a copy in shared memory).
-template <typename T, typename D, bool REC>
+// BOTH: compiled with the path that evaluates the two ends of a two-tip
+// crack at once when one CTA holds both (kept out of the single-tip
+// kernels, whose march it slows through the larger kernel).
+template <typename T, typename D, bool REC, bool BOTH = false>
 __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int band, CrackState &sS, const RecArgs &r)
 {
     constexpr int N = Vec<T>::N;
@@ -259,12 +262,35 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
         const bool right_here = cb == i_next / cols;
         const bool left_here = p.two_tips && cb == i_prev / cols;
         const bool commit = band == a.crack_band;
+        const bool both = BOTH && right_here && left_here;
         if ((right_here || left_here) && tid < 32) {
             if (tid == 0) sS = *a.s_in;
             __syncwarp();
             const bool pending = !sS.r.decided;   // not yet applied by a deferred crack step
-            if (right_here) crack_step_warp<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, +1, commit);
-            if (left_here) crack_step_warp<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, -1, commit);
+            if (both) {
+                // both ends in this CTA: lanes 0-15 evaluate the right end and
+                // lanes 16-31 the left end at once, on the same state (the
+                // criteria of both ends before either advances); lane 0 then
+                // advances the right end and the left end in turn
+                const bool act_r = p.mode != CRACK_NONE && !sS.r.decided;
+                const bool act_l = p.mode != CRACK_NONE && !sS.l.decided;
+                const CrackSums c = crack_eval_warp<T, 16>(p, a.w_in, a.pitch, a.cut_v, sS, tid < 16 ? +1 : -1);
+                CrackSums cl;
+                cl.num = __shfl_sync(0xffffffffu, c.num, 16);
+                cl.den = __shfl_sync(0xffffffffu, c.den, 16);
+                cl.r_min = __shfl_sync(0xffffffffu, c.r_min, 16);
+                cl.np = __shfl_sync(0xffffffffu, c.np, 16);
+                if (tid == 0) {
+                    if (act_r) crack_apply(p, a.cut_v, a.hist, sS, +1, commit, c);
+                    if (act_l) crack_apply(p, a.cut_v, a.hist, sS, -1, commit, cl);
+                    sS.r.decided = 1;
+                    sS.l.decided = 1;
+                }
+                __syncwarp();
+            } else {
+                if (right_here) crack_step_warp<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, +1, commit);
+                if (left_here) crack_step_warp<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, -1, commit);
+            }
             if (tid == 0 && commit) {
                 CrackState *o = a.s_out;
                 const int64_t n = sS.step + 1;
@@ -344,11 +370,11 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
     }
 }
 
-template <typename T, typename D>
+template <typename T, typename D, bool BOTH>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBlocks - 2) step_kernel(const StepArgs<T, D> a)
 {
     __shared__ CrackState sS;
-    step_cta<T, D, false>(a, blockIdx.x, blockIdx.y, sS, RecArgs{});
+    step_cta<T, D, false, BOTH>(a, blockIdx.x, blockIdx.y, sS, RecArgs{});
 }
 
 // The step kernel with the recording of a forward run for the adjoint.
@@ -379,13 +405,16 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
 
 template <typename T, typename D> const void *step_kernel_ptr()
 {
-    return reinterpret_cast<const void *>(&step_kernel<T, D>);
+    return reinterpret_cast<const void *>(&step_kernel<T, D, false>);
 }
 
 template <typename T, typename D>
 cudaError_t launch_step(const StepArgs<T, D> &a, int bands, cudaStream_t s)
 {
-    step_kernel<T, D><<<dim3((unsigned)a.ncb, (unsigned)bands), kThreads, 0, s>>>(a);
+    if (a.p.two_tips)
+        step_kernel<T, D, true><<<dim3((unsigned)a.ncb, (unsigned)bands), kThreads, 0, s>>>(a);
+    else
+        step_kernel<T, D, false><<<dim3((unsigned)a.ncb, (unsigned)bands), kThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
