@@ -412,7 +412,31 @@ def measure_extensions(lbm, W, torch, stream, problem, peak, flush_l2, steps=100
               "launches_per_step": 2, "tip_right_final": float(hist["tip_q"][-1]) / 2**32,
               "timing": "CUDA events around the whole run (graph replay, L2-resident state)"}
     lat.close()
-    return {"d2q9": d2q9, "centre_crack_sec52": centre}
+
+    # a sweep of the same example over K_C (0.8 .. 1.2 K_C, 64 runs) as one batch
+    runs, steps_b = 64, 1024
+    lats = []
+    for q in range(runs):
+        pq = W.kcrit_centre_crack()
+        pq["crack"] = dict(pq["crack"], K_C=pq["crack"]["K_C"] * (0.8 + 0.4 * q / (runs - 1)))
+        pq["hist_cap"] = steps_b
+        lats.append(lbm.Lattice(pq, "f32", stream=stream))
+    b = lbm.Batch(lats)
+    b.step(64)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    b.step(steps_b)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    secs_b = ev0.elapsed_time(ev1) * 1e-3
+    sweep = {"workload": f"{runs} runs of the Sec. 5.2 example (K_C from 0.8 to 1.2 of the paper's), one batch, f32",
+             "steps": steps_b, "us_per_step": secs_b / steps_b * 1e6,
+             "glups": runs * p["nx"] * p["ny"] * steps_b / secs_b / 1e9,
+             "timing": "CUDA events around the batched steps (graph replay)"}
+    b.close()
+    for l in lats:
+        l.close()
+    return {"d2q9": d2q9, "centre_crack_sec52": centre, "centre_crack_sweep": sweep}
 
 
 def measure_virtual_ranks(lbm, W, torch, stream, problem, steps=256):

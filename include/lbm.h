@@ -125,8 +125,8 @@ typedef struct lbm_grid {
  * on an edge column are edge points themselves.  wdot_B = (w_B(t + dt) -
  * w_B(t)) / dt.  One extra small kernel per time step applies it.  Needs at
  * least 4 sites across each non-periodic pair of edges and a crack line at
- * least 4 dh from the bottom and top edges; not available to lbm_batch_*,
- * lbm_decomp_* or lbm_tape_* (their create calls reject it). */
+ * least 4 dh from the bottom and top edges; not available to lbm_decomp_*
+ * or lbm_tape_* (their create calls reject it). */
 typedef struct lbm_lattice {
     int32_t velocity_set;
     int32_t form;
@@ -340,7 +340,9 @@ void lbm_destroy(lbm_handle *h);
  * It re-partitions every lattice into bands of band_rows rows (0: 16) and
  * uploads a table of the step-kernel arguments of every lattice and a table
  * of all their (lattice, column block, band) units; allocator as in
- * lbm_create (NULL: cudaMalloc).  While the batch exists, step its lattices
+ * lbm_create (NULL: cudaMalloc).  D2Q5 lattices only.  Lattices with
+ * LBM_BC_MACROSCOPIC_EDGES get their outer-edge rule from one more batched
+ * launch per step (units of 128 edge sites).  While the batch exists, step its lattices
  * only through lbm_batch_step (stepping one alone makes lbm_batch_step return
  * LBM_ERR_STATE) and do not call lbm_set_launch or lbm_set_wd_scale on them.
  * Fields, masks and crack states are read through the member handles. */

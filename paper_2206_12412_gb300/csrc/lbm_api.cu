@@ -1063,6 +1063,8 @@ struct lbm_batch {
     void *descs;
     BatchUnit *units;
     int n_units;
+    BatchUnit *eunits;   // edge-rule units: 128 edge sites of one lattice (LBM_BC_MACROSCOPIC_EDGES)
+    int n_eunits;
     lbm_allocator alloc;
     bool custom_alloc;
     cudaStream_t stream;
@@ -1072,6 +1074,27 @@ struct lbm_batch {
 };
 
 namespace {
+
+// Edge-rule units of the lattices with the macroscopic rule on their outer
+// edges: 128 edge sites each (the batch step applies it after the update).
+template <typename T, typename D>
+void edge_units(const lbm_batch *b, std::vector<BatchUnit> &out)
+{
+    for (size_t i = 0; i < b->hs.size(); ++i) {
+        if (!b->hs[i]->edge_macro) continue;
+        StepArgs<T, D> a;
+        make_step_args(b->hs[i], 0, a);
+        const int n = edge_rule_count(a);
+        for (int t0 = 0; t0 < n; t0 += 128) {
+            BatchUnit u;
+            u.inst = (int32_t)i;
+            u.cb = t0;
+            u.band = 0;
+            u.pad = 0;
+            out.push_back(u);
+        }
+    }
+}
 
 template <typename T, typename D>
 void fill_descs(const lbm_batch *b, std::vector<char> &buf)
@@ -1084,17 +1107,22 @@ void fill_descs(const lbm_batch *b, std::vector<char> &buf)
     }
 }
 
+template <typename T, typename D>
+cudaError_t enqueue_batch_step_t(const lbm_batch *b, int par, cudaStream_t s)
+{
+    const StepArgs<T, D> *d = static_cast<const StepArgs<T, D> *>(b->descs);
+    cudaError_t e = launch_batch_step(d, b->units, b->n_units, par, s);
+    if (e == cudaSuccess && b->n_eunits > 0) e = launch_batch_edge_rule(d, b->eunits, b->n_eunits, par, s);
+    return e;
+}
+
 cudaError_t enqueue_batch_step(const lbm_batch *b, int par, cudaStream_t s)
 {
     switch (b->storage) {
-    case LBM_F32:
-        return launch_batch_step(static_cast<const StepArgs<float, float> *>(b->descs), b->units, b->n_units, par, s);
-    case LBM_F32_WD_BF16:
-        return launch_batch_step(static_cast<const StepArgs<float, __nv_bfloat16> *>(b->descs), b->units, b->n_units, par, s);
-    case LBM_F32_WD_F16:
-        return launch_batch_step(static_cast<const StepArgs<float, __half> *>(b->descs), b->units, b->n_units, par, s);
-    default:
-        return launch_batch_step(static_cast<const StepArgs<double, double> *>(b->descs), b->units, b->n_units, par, s);
+    case LBM_F32: return enqueue_batch_step_t<float, float>(b, par, s);
+    case LBM_F32_WD_BF16: return enqueue_batch_step_t<float, __nv_bfloat16>(b, par, s);
+    case LBM_F32_WD_F16: return enqueue_batch_step_t<float, __half>(b, par, s);
+    default: return enqueue_batch_step_t<double, double>(b, par, s);
     }
 }
 
@@ -1142,7 +1170,6 @@ lbm_status lbm_batch_create(lbm_handle *const *handles, int32_t n, int32_t band_
         if (!h) return fail(LBM_ERR_ARG, "a lattice handle is NULL");
         if (h->sticky != LBM_OK) return fail(h->sticky, "a lattice is in an error state");
         if (h->lat.storage != handles[0]->lat.storage) return fail(LBM_ERR_ARG, "all lattices need the same storage");
-        if (h->edge_macro) return fail(LBM_ERR_ARG, "the batched step has no macroscopic rule on the outer edges");
         if (h->q != 5) return fail(LBM_ERR_ARG, "the batched step is built for D2Q5 only");
         if (h->stream != handles[0]->stream) return fail(LBM_ERR_ARG, "all lattices need the same stream");
         if (h->parity != handles[0]->parity) return fail(LBM_ERR_STATE, "all lattices need the same number of steps");
@@ -1190,23 +1217,29 @@ lbm_status lbm_batch_create(lbm_handle *const *handles, int32_t n, int32_t band_
             }
     }
     std::vector<char> descs;
+    std::vector<BatchUnit> eunits;
     switch (b->storage) {
-    case LBM_F32: fill_descs<float, float>(b, descs); break;
-    case LBM_F32_WD_BF16: fill_descs<float, __nv_bfloat16>(b, descs); break;
-    case LBM_F32_WD_F16: fill_descs<float, __half>(b, descs); break;
-    default: fill_descs<double, double>(b, descs); break;
+    case LBM_F32: fill_descs<float, float>(b, descs); edge_units<float, float>(b, eunits); break;
+    case LBM_F32_WD_BF16: fill_descs<float, __nv_bfloat16>(b, descs); edge_units<float, __nv_bfloat16>(b, eunits); break;
+    case LBM_F32_WD_F16: fill_descs<float, __half>(b, descs); edge_units<float, __half>(b, eunits); break;
+    default: fill_descs<double, double>(b, descs); edge_units<double, double>(b, eunits); break;
     }
     b->n_units = (int)units.size();
+    b->n_eunits = (int)eunits.size();
     const size_t o_units = align256(descs.size());
-    b->block_bytes = o_units + units.size() * sizeof(BatchUnit);
+    const size_t o_eunits = o_units + align256(units.size() * sizeof(BatchUnit));
+    b->block_bytes = o_eunits + std::max<size_t>(eunits.size(), 1) * sizeof(BatchUnit);
     if (b->custom_alloc) b->block = b->alloc.alloc(b->block_bytes, b->alloc.ctx);
     else if (cudaMalloc(&b->block, b->block_bytes) != cudaSuccess) b->block = nullptr;
     if (!b->block) return bail(fail(LBM_ERR_OOM, "device allocation failed"));
     b->descs = b->block;
     b->units = reinterpret_cast<BatchUnit *>(static_cast<char *>(b->block) + o_units);
+    b->eunits = reinterpret_cast<BatchUnit *>(static_cast<char *>(b->block) + o_eunits);
     cudaError_t e = cudaMemcpyAsync(b->descs, descs.data(), descs.size(), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->units, units.data(), units.size() * sizeof(BatchUnit), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && !eunits.empty())
+        e = cudaMemcpyAsync(b->eunits, eunits.data(), eunits.size() * sizeof(BatchUnit), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return bail(cuda_fail(e, "uploading the batch tables"));

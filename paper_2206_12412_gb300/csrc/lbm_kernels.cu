@@ -588,7 +588,7 @@ struct EdgeRule {
 __host__ __device__ __forceinline__ bool ruled(int kind) { return kind == EDGE_FREE || kind == EDGE_DIRICHLET; }
 
 template <typename T, typename D>
-__global__ void __launch_bounds__(128) edge_rule_kernel(const StepArgs<T, D> a)
+__device__ __forceinline__ void edge_rule_at(const StepArgs<T, D> &a, int t)
 {
     const int nx = a.nx, ny = a.ny;
     const bool onL = ruled(a.edge[LEFT]), onR = ruled(a.edge[RIGHT]);
@@ -597,7 +597,6 @@ __global__ void __launch_bounds__(128) edge_rule_kernel(const StepArgs<T, D> a)
     const int jlo = onB ? 1 : 0, jhi = onT ? ny - 2 : ny - 1;
     const int nV = jhi >= jlo ? jhi - jlo + 1 : 0;
     const int nL = onL ? nV : 0, nR = onR ? nV : 0;
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
     int i, j;
     if (t < nB) { i = t; j = 0; }
     else if ((t -= nB) < nT) { i = t; j = ny - 1; }
@@ -661,6 +660,22 @@ __global__ void __launch_bounds__(128) edge_rule_kernel(const StepArgs<T, D> a)
 }
 
 template <typename T, typename D>
+__global__ void __launch_bounds__(128) edge_rule_kernel(const StepArgs<T, D> a)
+{
+    edge_rule_at(a, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// The same for the lattices of a batch: unit u covers edge sites cb ..
+// cb + 127 of lattice inst, whose arguments are read from the descriptor
+// table in device memory.
+template <typename T, typename D>
+__global__ void __launch_bounds__(128) batch_edge_rule_kernel(const StepArgs<T, D> *descs, const BatchUnit *units, int par)
+{
+    const BatchUnit u = units[blockIdx.x];
+    edge_rule_at(descs[2 * u.inst + par], u.cb + (int)threadIdx.x);
+}
+
+template <typename T, typename D>
 int edge_rule_sites(const StepArgs<T, D> &a)
 {
     const bool onL = ruled(a.edge[LEFT]), onR = ruled(a.edge[RIGHT]);
@@ -676,6 +691,21 @@ cudaError_t launch_edge_rule(const StepArgs<T, D> &a, cudaStream_t s)
     const int n = edge_rule_sites(a);
     if (n == 0) return cudaSuccess;
     edge_rule_kernel<T, D><<<(n + 127) / 128, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, typename D>
+int edge_rule_count(const StepArgs<T, D> &a)
+{
+    return edge_rule_sites(a);
+}
+
+template <typename T, typename D>
+cudaError_t launch_batch_edge_rule(const StepArgs<T, D> *descs, const BatchUnit *units, int n_units, int par,
+                                   cudaStream_t s)
+{
+    if (n_units <= 0) return cudaSuccess;
+    batch_edge_rule_kernel<T, D><<<(unsigned)n_units, 128, 0, s>>>(descs, units, par);
     return cudaGetLastError();
 }
 
@@ -737,6 +767,14 @@ template cudaError_t launch_wd_from_f32<__nv_bfloat16>(__nv_bfloat16 *, int64_t,
 template cudaError_t launch_wd_from_f32<__half>(__half *, int64_t, int, int, float, const float *, cudaStream_t);
 template cudaError_t launch_finalize<float>(const FinalizeArgs<float> &, cudaStream_t);
 template cudaError_t launch_finalize<double>(const FinalizeArgs<double> &, cudaStream_t);
+template int edge_rule_count<double, double>(const StepArgs<double, double> &);
+template int edge_rule_count<float, float>(const StepArgs<float, float> &);
+template int edge_rule_count<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> &);
+template int edge_rule_count<float, __half>(const StepArgs<float, __half> &);
+template cudaError_t launch_batch_edge_rule<double, double>(const StepArgs<double, double> *, const BatchUnit *, int, int, cudaStream_t);
+template cudaError_t launch_batch_edge_rule<float, float>(const StepArgs<float, float> *, const BatchUnit *, int, int, cudaStream_t);
+template cudaError_t launch_batch_edge_rule<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> *, const BatchUnit *, int, int, cudaStream_t);
+template cudaError_t launch_batch_edge_rule<float, __half>(const StepArgs<float, __half> *, const BatchUnit *, int, int, cudaStream_t);
 template cudaError_t launch_edge_rule<double, double>(const StepArgs<double, double> &, cudaStream_t);
 template cudaError_t launch_edge_rule<float, float>(const StepArgs<float, float> &, cudaStream_t);
 template cudaError_t launch_edge_rule<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> &, cudaStream_t);

@@ -4,7 +4,8 @@ ABI against the oracle: fields at the FP64 / FP32 tolerances of
 test_gpu_parity.py, tips and cut masks bit-exact; edge kinds, corners,
 ragged column blocks, crack faces on the edge columns, the graph-replayed
 chunks, the 16-bit wdot forms, the K-criterion centre-crack example of
-Sec. 5.2 at full size, and the calls that reject the mode."""
+Sec. 5.2 at full size, batches of such lattices against their solo runs,
+and the calls that reject the mode."""
 import numpy as np
 import pytest
 
@@ -183,11 +184,40 @@ def test_centre_crack_example_fp32(gpu, centre_oracle):
     g.close()
 
 
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+def test_batch_with_the_edge_rule_equals_solo_runs(gpu, storage):
+    """A parameter sweep of the Sec. 5.2 example (quarter size, K_C scaled by
+    0.8 .. 1.2) batched with a lattice under the link-local rules: each lattice
+    bit-identical to its own run, through single launches and graph chunks."""
+    probs = []
+    for f in (0.8, 0.9, 1.0, 1.1, 1.2):
+        p = W.kcrit_centre_crack(scale=4)
+        p["crack"] = dict(p["crack"], K_C=p["crack"]["K_C"] * f)
+        probs.append(p)
+    q = W.with_antisymmetric_ramp(W.base_problem(300, 70, bc_mode="macroscopic"), 1e-3, 40.0)
+    probs.append(W.with_crack(q, mode="prescribed", y=35.0, x_tip=60.0, v_rel=0.5))
+    solo = [gpu.Lattice(p, storage) for p in probs]
+    for l in solo:
+        l.step(400)
+    members = [gpu.Lattice(p, storage) for p in probs]
+    b = gpu.Batch(members)
+    for n in (3, 64, 333):
+        b.step(n)
+    for ls, lb in zip(solo, members):
+        ws, wds = ls.fields()
+        wb, wdb = lb.fields()
+        np.testing.assert_array_equal(wb, ws)
+        np.testing.assert_array_equal(wdb, wds)
+        assert lb.crack_state() == ls.crack_state()
+        np.testing.assert_array_equal(lb.history(cap=400)["tip_q"], ls.history(cap=400)["tip_q"])
+    b.close()
+    for l in solo + members:
+        l.close()
+
+
 def test_calls_that_reject_the_mode(gpu):
     p = W.base_problem(64, 32, bc_mode="macroscopic_edges")
     g = gpu.Lattice(p, "f32")
-    with pytest.raises(gpu.LbmError):
-        gpu.Batch([g])
     with pytest.raises(gpu.LbmError):
         gpu.Tape(g, np.array([[5, 5]], np.int32), 4)
     with pytest.raises(gpu.LbmError):
