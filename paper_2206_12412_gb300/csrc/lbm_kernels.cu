@@ -178,6 +178,12 @@ __device__ __forceinline__ void march(const StepArgs<T, D> &a, int cb, int j0, i
     ldg_row(win + (int64_t)j0 * P, wc);
     ldg_row(win + (int64_t)(j0 + 1) * P, wa);
     WdIO<D>::load(wdp + (int64_t)j0 * P, wdv, wd_inv);
+    // 16-bit wdot rows carry half the bytes of an FP32 row: keep two in
+    // flight (rows j + 1 and j + 2) so that a warp has as many wdot bytes
+    // outstanding as in FP32
+    constexpr bool DEEP = sizeof(D) == 2;
+    typename WdIO<D>::Raw wdq1;
+    if (DEEP && j0 + 1 < j1) WdIO<D>::fetch(wdp + (int64_t)(j0 + 1) * P, wdq1);
     T hl = (T)0, hr = (T)0;
     if (lane == 0) hl = win[(int64_t)j0 * P - 1];
     if (lane == 31) hr = win[(int64_t)j0 * P + N];
@@ -191,7 +197,11 @@ __device__ __forceinline__ void march(const StepArgs<T, D> &a, int cb, int j0, i
         const bool more = j + 1 < j1;
         if (more) {
             ldg_row(win + (int64_t)(j + 2) * P, wn);
-            WdIO<D>::fetch(wdp + (int64_t)(j + 1) * P, wdn);
+            if (DEEP) {
+                if (j + 2 < j1) WdIO<D>::fetch(wdp + (int64_t)(j + 2) * P, wdn);
+            } else {
+                WdIO<D>::fetch(wdp + (int64_t)(j + 1) * P, wdn);
+            }
             if (lane == 0) hln = win[(int64_t)(j + 1) * P - 1];
             if (lane == 31) hrn = win[(int64_t)(j + 1) * P + N];
         }
@@ -223,7 +233,12 @@ __device__ __forceinline__ void march(const StepArgs<T, D> &a, int cb, int j0, i
         wc = wa;
         if (more) {
             wa = wn;
-            WdIO<D>::unpack(wdn, wdv, wd_inv);
+            if (DEEP) {
+                WdIO<D>::unpack(wdq1, wdv, wd_inv);
+                wdq1 = wdn;
+            } else {
+                WdIO<D>::unpack(wdn, wdv, wd_inv);
+            }
             hl = hln;
             hr = hrn;
         }
