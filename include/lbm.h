@@ -324,6 +324,20 @@ lbm_status lbm_get_wd_scale(const lbm_handle *h, double *scale);
  *     as lbm_fields does. */
 lbm_status lbm_wdot_to_host_noalloc(lbm_handle *h, float *dst_host, int64_t n_floats);
 
+/* Checkpoint / resume.  lbm_save writes the whole state of the lattice to
+ * the file `path`: w and the stored wdot (padded planes, bit for bit), the
+ * cut masks, the crack state (both ends, after the pending crack step is
+ * applied), the history ring, the step counter (the loads' time) and the
+ * FP16 wdot scale, behind a header that records the configuration.  lbm_load
+ * reads such a file into a handle created with the same grid, lattice,
+ * material, crack and loads (LBM_ERR_ARG otherwise); stepping on from there
+ * gives the same bits as the run that was saved.  The paper has no
+ * counterpart (its runs are single programs).  Both synchronise the stream;
+ * LBM_ERR_IO when the file cannot be written or read, or is truncated or
+ * not a checkpoint. */
+lbm_status lbm_save(lbm_handle *h, const char *path);
+lbm_status lbm_load(lbm_handle *h, const char *path);
+
 /* Bytes of device memory the handle holds. */
 lbm_status lbm_device_bytes(const lbm_handle *h, int64_t *bytes);
 

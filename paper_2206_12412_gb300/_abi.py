@@ -88,6 +88,8 @@ PROTOTYPES = {
     "lbm_set_wd_scale": (C.c_int, [C.c_void_p, C.c_double]),
     "lbm_get_wd_scale": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "lbm_device_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "lbm_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "lbm_load": (C.c_int, [C.c_void_p, C.c_char_p]),
     "lbm_destroy": (None, [C.c_void_p]),
     "lbm_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_int32, C.POINTER(Allocator),
                                    C.POINTER(C.c_void_p)]),

@@ -1029,6 +1029,149 @@ lbm_status lbm_wdot_to_host_noalloc(lbm_handle *h, float *dst_host, int64_t n_fl
     return check_sticky(h);
 }
 
+}  // extern "C"
+
+namespace {
+
+// Checkpoint file: this header, then the w plane, the stored wdot plane, the
+// two cut masks, the crack state and the history ring of each end, as raw
+// bytes in that order.
+struct CkptHeader {
+    char magic[8];
+    int32_t version, crack_state_bytes;
+    lbm_grid grid;
+    lbm_lattice lat;
+    lbm_material mat;
+    lbm_crack crack;
+    int32_t load_kind[4];
+    double load_amp[4], load_t[4];
+    int64_t load_n[4];
+    int64_t pitch, plane_bytes, plane_d_bytes, mask_bytes, hist_cap, hist_cap_l;
+    int32_t words, ny;
+    double wd_scale;
+};
+constexpr char kCkptMagic[8] = {'L', 'B', 'M', 'C', 'K', 'P', 'T', '1'};
+
+void ckpt_header(const lbm_handle *h, CkptHeader &c)
+{
+    std::memset(&c, 0, sizeof c);
+    std::memcpy(c.magic, kCkptMagic, 8);
+    c.version = 1;
+    c.crack_state_bytes = (int32_t)sizeof(CrackState);
+    c.grid = h->grid;
+    c.lat = h->lat;
+    c.mat = h->mat;
+    c.crack = h->crack;
+    for (int e = 0; e < 4; ++e) {
+        c.load_kind[e] = h->load[e].kind;
+        c.load_amp[e] = h->load[e].amp;
+        c.load_t[e] = h->load[e].t;
+        c.load_n[e] = h->load[e].n;
+    }
+    c.pitch = h->pitch;
+    c.plane_bytes = (int64_t)h->plane_bytes;
+    c.plane_d_bytes = (int64_t)h->plane_d_bytes;
+    c.mask_bytes = (int64_t)h->grid.ny * h->words * 4;
+    c.hist_cap = h->cp.mode != CRACK_NONE ? h->cp.hist_cap : 1;
+    c.hist_cap_l = h->cp.two_tips ? c.hist_cap : 1;
+    c.words = h->words;
+    c.ny = h->grid.ny;
+    c.wd_scale = h->wd_scale;
+}
+
+// Every field but the wdot scale (which the checkpoint carries) must agree.
+bool ckpt_compatible(const CkptHeader &a, const CkptHeader &b)
+{
+    CkptHeader x = a, y = b;
+    x.wd_scale = y.wd_scale = 0.0;
+    return std::memcmp(&x, &y, sizeof x) == 0;
+}
+
+// The device buffers of a checkpoint, in file order, with their sizes.
+std::vector<std::pair<void *, size_t>> ckpt_buffers(lbm_handle *h, const CkptHeader &c)
+{
+    const History &H = h->hist;
+    return {{h->wbase[h->parity], (size_t)c.plane_bytes},
+            {h->wdbase, (size_t)c.plane_d_bytes},
+            {h->cut_h, (size_t)c.mask_bytes},
+            {h->cut_v, (size_t)c.mask_bytes},
+            {h->st + h->parity, sizeof(CrackState)},
+            {H.K, (size_t)c.hist_cap * 8},
+            {H.v, (size_t)c.hist_cap * 8},
+            {H.tip, (size_t)c.hist_cap * 8},
+            {H.np, (size_t)c.hist_cap * 4},
+            {H.Kl, (size_t)c.hist_cap_l * 8},
+            {H.vl, (size_t)c.hist_cap_l * 8},
+            {H.tipl, (size_t)c.hist_cap_l * 8},
+            {H.npl, (size_t)c.hist_cap_l * 4}};
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_save(lbm_handle *h, const char *path)
+{
+    if (!h || !path) return fail(LBM_ERR_ARG, "handle or path is NULL");
+    if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");
+    lbm_status rc = finalize(h);   // the state after the crack step of the last time step
+    if (rc != LBM_OK) return rc;
+    CkptHeader c;
+    ckpt_header(h, c);
+    const auto bufs = ckpt_buffers(h, c);
+    std::vector<std::vector<char>> host(bufs.size());
+    for (size_t q = 0; q < bufs.size(); ++q) {
+        host[q].resize(bufs[q].second);
+        LBM_CUDA(cudaMemcpyAsync(host[q].data(), bufs[q].first, bufs[q].second, cudaMemcpyDeviceToHost, h->stream));
+    }
+    rc = check_sticky(h);   // synchronises the stream
+    if (rc != LBM_OK) return rc;
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(LBM_ERR_IO, std::string("cannot open ") + path + " for writing");
+    bool ok = std::fwrite(&c, sizeof c, 1, f) == 1;
+    for (size_t q = 0; ok && q < host.size(); ++q) ok = std::fwrite(host[q].data(), 1, host[q].size(), f) == host[q].size();
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(LBM_ERR_IO, std::string("writing ") + path + " failed");
+    return LBM_OK;
+}
+
+lbm_status lbm_load(lbm_handle *h, const char *path)
+{
+    if (!h || !path) return fail(LBM_ERR_ARG, "handle or path is NULL");
+    if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(LBM_ERR_IO, std::string("cannot open ") + path);
+    CkptHeader c, mine;
+    if (std::fread(&c, sizeof c, 1, f) != 1 || std::memcmp(c.magic, kCkptMagic, 8) != 0 || c.version != 1) {
+        std::fclose(f);
+        return fail(LBM_ERR_IO, std::string(path) + " is not a lattice checkpoint");
+    }
+    ckpt_header(h, mine);
+    if (!ckpt_compatible(c, mine)) {
+        std::fclose(f);
+        return fail(LBM_ERR_ARG, "the checkpoint was written by a lattice of another configuration");
+    }
+    const auto bufs = ckpt_buffers(h, mine);
+    std::vector<std::vector<char>> host(bufs.size());
+    bool ok = true;
+    for (size_t q = 0; ok && q < bufs.size(); ++q) {
+        host[q].resize(bufs[q].second);
+        ok = std::fread(host[q].data(), 1, host[q].size(), f) == host[q].size();
+    }
+    std::fclose(f);
+    if (!ok) return fail(LBM_ERR_IO, std::string(path) + " is truncated");
+    cudaError_t e = cudaStreamSynchronize(h->stream);   // no step may be in flight on the buffers
+    if (e != cudaSuccess) return cuda_fail(e, "synchronising before the load");
+    for (size_t q = 0; q < bufs.size(); ++q)
+        LBM_CUDA(cudaMemcpyAsync(bufs[q].first, host[q].data(), bufs[q].second, cudaMemcpyHostToDevice, h->stream));
+    h->pending = false;               // the saved state had its crack step applied
+    if (h->wd_scale != c.wd_scale) {
+        h->wd_scale = c.wd_scale;
+        drop_graph(h);                // the scale is a kernel argument
+    }
+    return check_sticky(h);           // synchronises: the host buffers go out of scope
+}
+
 lbm_status lbm_device_bytes(const lbm_handle *h, int64_t *bytes)
 {
     if (!h || !bytes) return fail(LBM_ERR_ARG, "handle or bytes is NULL");

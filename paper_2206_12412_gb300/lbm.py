@@ -149,6 +149,14 @@ def lbm_device_bytes(h: int) -> int:
     return b.value
 
 
+def lbm_save(h: int, path: str):
+    _check(load_library().lbm_save(C.c_void_p(h), os.fsencode(path)))
+
+
+def lbm_load(h: int, path: str):
+    _check(load_library().lbm_load(C.c_void_p(h), os.fsencode(path)))
+
+
 def lbm_destroy(h: int):
     if h:
         load_library().lbm_destroy(C.c_void_p(h))
@@ -393,6 +401,14 @@ class Lattice:
 
     def device_bytes(self) -> int:
         return lbm_device_bytes(self.h)
+
+    def save(self, path: str):
+        """Write the lattice's whole state to a checkpoint file."""
+        lbm_save(self.h, path)
+
+    def load(self, path: str):
+        """Read a checkpoint written by a lattice of the same problem."""
+        lbm_load(self.h, path)
 
     def reset(self):
         """Back to step 0: zero fields, the initial crack, empty history."""

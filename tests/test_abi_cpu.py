@@ -133,6 +133,8 @@ def test_create_rejects_unpaired_periodic_and_bad_loads(lib):
 
 
 def test_null_handles_are_rejected(lib):
+    assert lib.lbm_save(None, b"/tmp/x.lbm") == A.LBM_ERR_ARG
+    assert lib.lbm_load(None, b"/tmp/x.lbm") == A.LBM_ERR_ARG
     assert lib.lbm_step(None, 1) == A.LBM_ERR_ARG
     assert lib.lbm_sync(None) == A.LBM_ERR_ARG
     assert lib.lbm_fields(None, 0, None, 0, 0) == A.LBM_ERR_ARG
