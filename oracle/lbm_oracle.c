@@ -380,8 +380,8 @@ orc_state *orc_create(const orc_config *cfg)
     if (cfg->nx < 1 || cfg->ny < 1 || !(cfg->dh > 0) || !(cfg->dt > 0)) return NULL;
     int Q = cfg->q == 0 ? 5 : cfg->q;
     if (Q != 5 && Q != 9) return NULL;
-    /* D2Q9 is built with the link-local rules only (no macroscopic rule) */
-    if (Q == 9 && (cfg->bc_mode != ORC_BC_BOUNCEBACK || cfg->edge_macro)) return NULL;
+    /* D2Q9 is built with the macroscopic rule on the crack faces, not on the outer edges */
+    if (Q == 9 && cfg->edge_macro) return NULL;
     orc_state *s = xcalloc(1, sizeof(orc_state));
     s->c = *cfg;
     s->Q = Q;
@@ -526,6 +526,10 @@ static void add_bpoint(orc_state *s, int32_t k)
     double x1 = (double)s->tip_q / (double)qone();
     double yc = (double)s->c.jc;
     double cx = bx < x0 ? x0 : (bx > x1 ? x1 : bx);      /* closest point on the crack line segment */
+    /* D2Q9: a site can lose only a diagonal link to the crack while its
+     * centre lies beyond an end of the segment; its boundary condition is
+     * that of the crack face the link crosses, whose normal is vertical */
+    if (s->Q == 9) cx = bx;
     double cy = yc;
     double dx = bx - cx, dy = by - cy;
     double d = sqrt(dx * dx + dy * dy);
