@@ -342,6 +342,49 @@ cudaError_t launch_d2q9_step(const StepArgs<T, T> &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// The macroscopic rule on the D2Q9 crack faces (Sec. 3.1), after the update:
+// a site of rows jc - 1 and jc is a boundary point when its column has a
+// severed vertical link or is one of the two columns of a severed diagonal
+// pair; it takes the normal of the crack face its link crosses, so x_I, x_II
+// are the next two sites of its column away from the crack:
+// w_B = 1.5 w_I - 0.5 w_II, wdot_B = (w_B - w_B(t)) / dt.  The crack state of
+// the step (the cuts in force during it) is the one the update wrote to
+// s_out.  One thread per column; x_I, x_II are never boundary points.
+template <typename T>
+__global__ void __launch_bounds__(128) d2q9_face_kernel(const StepArgs<T, T> a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.nx) return;
+    const int nx = a.nx, jc = a.p.jc;
+    const CrackState *st = a.s_out;
+    const int64_t rq = st->r.tip_q, lq = a.p.two_tips ? st->l.tip_q : a.p.start_q;
+    const int64_t ml = (int64_t)i << kQBits, mr = (int64_t)(i + 1) << kQBits;
+    const bool vcut = (a.cut_v[(int64_t)(jc - 1) * a.words + (i >> 5)] >> (i & 31)) & 1u;
+    const bool dl = i >= 1 && lq <= ml && ml <= rq, dr = i + 1 <= nx - 1 && lq <= mr && mr <= rq;
+    if (!(vcut || dl || dr)) return;
+    const int64_t P = a.pitch;
+    const T *wn = a.w_out;
+    const T inv_dt = (T)1 / a.dt;
+    const T up = (T)1.5 * wn[(int64_t)(jc + 1) * P + i] - (T)0.5 * wn[(int64_t)(jc + 2) * P + i];
+    const T dn = (T)1.5 * wn[(int64_t)(jc - 2) * P + i] - (T)0.5 * wn[(int64_t)(jc - 3) * P + i];
+    const int64_t ou = (int64_t)jc * P + i, od = (int64_t)(jc - 1) * P + i;
+    const T wdu = (up - a.w_in[ou]) * inv_dt, wdd = (dn - a.w_in[od]) * inv_dt;
+    a.w_out[ou] = up;
+    a.wd[ou] = wdu;
+    a.w_out[od] = dn;
+    a.wd[od] = wdd;
+    if (!isfinite(up) || !isfinite(dn)) atomicOr(a.err, (uint32_t)ERR_NONFINITE);
+}
+
+template <typename T>
+cudaError_t launch_d2q9_faces(const StepArgs<T, T> &a, cudaStream_t s)
+{
+    d2q9_face_kernel<T><<<(a.nx + 127) / 128, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_d2q9_faces<double>(const StepArgs<double, double> &, cudaStream_t);
+template cudaError_t launch_d2q9_faces<float>(const StepArgs<float, float> &, cudaStream_t);
 template cudaError_t launch_d2q9_step<double>(const StepArgs<double, double> &, cudaStream_t);
 template cudaError_t launch_d2q9_step<float>(const StepArgs<float, float> &, cudaStream_t);
 

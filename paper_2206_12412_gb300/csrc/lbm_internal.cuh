@@ -202,6 +202,7 @@ template <typename T, typename D>
 cudaError_t launch_batch_edge_rule(const StepArgs<T, D> *descs, const BatchUnit *units, int n_units, int par,
                                    cudaStream_t s);
 template <typename T> cudaError_t launch_d2q9_step(const StepArgs<T, T> &a, cudaStream_t s);
+template <typename T> cudaError_t launch_d2q9_faces(const StepArgs<T, T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_step_rec(const StepArgs<T, T> &a, const RecArgs &r, int bands, cudaStream_t s);
 template <typename T> const void *adjoint_kernel_ptr();
 template <typename T> cudaError_t launch_adjoint(const AdjArgs<T> &a, int bands, cudaStream_t s);

@@ -119,6 +119,53 @@ def test_edge_crack_at_a_dirichlet_or_periodic_side(oracle_mod, gpu, edges):
     o.close()
 
 
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("two_tips", [False, True])
+def test_macroscopic_crack_faces(oracle_mod, gpu, storage, two_tips):
+    """The macroscopic rule on the faces of a D2Q9 crack growing at a
+    prescribed speed (boundary points also in the columns reached only by a
+    severed diagonal pair), across column blocks and to the edges."""
+    nx, ny, jc = 620, 40, 20
+    p = _problem(nx, ny)
+    p["bc_mode"] = "macroscopic"
+    p = W.with_crack(p, mode="prescribed", y=float(jc), x_start=250.3 if two_tips else 0.0, x_tip=300.6,
+                     v_rel=0.6, two_tips=two_tips)
+    p = W.with_antisymmetric_ramp(p, 1e-3, 50.0)
+    o = oracle_mod.Oracle(p)
+    g = gpu.Lattice(p, storage)
+    for n in (5, 64, 300, 800):
+        o.step(n)
+        g.step(n)
+        _close(o, g, TOL[storage])
+    np.testing.assert_array_equal(g.cut_mask("v"), o.cuts()[1].astype(bool))
+    np.testing.assert_array_equal(g.history()["tip_q"], o.history()["tip_q"])
+    if two_tips:
+        np.testing.assert_array_equal(g.history_left()["tip_q"], o.history_left()["tip_q"])
+    g.close()
+    o.close()
+
+
+def test_kcrit_macroscopic_faces_fp64(oracle_mod, gpu):
+    nx, ny = 160, 48
+    p = _problem(nx, ny)
+    p["bc_mode"] = "macroscopic"
+    p = W.with_antisymmetric_ramp(p, 2e-3, 60.0)
+    K_C = 0.5 * W.strip_reference_K(0.25, 2e-3, 48.0)
+    p = W.with_crack(p, mode="kcrit", y=24.0, x_start=60.0, x_tip=90.0, K_C=K_C, v_max=0.85, r0=2.0, two_tips=True)
+    o = oracle_mod.Oracle(p)
+    g = gpu.Lattice(p, "f64")
+    o.step(500)
+    g.step(500)
+    ho, hg = o.history(), g.history()
+    assert ho["grew"].sum() > 10
+    np.testing.assert_array_equal(hg["tip_q"], ho["tip_q"])
+    np.testing.assert_array_equal(g.history_left()["tip_q"], o.history_left()["tip_q"])
+    np.testing.assert_allclose(hg["K"], ho["K"], rtol=1e-9, atol=1e-12 * K_C)
+    _close(o, g, 1e-12)
+    g.close()
+    o.close()
+
+
 def test_kcrit_growth_fp64(oracle_mod, gpu):
     nx, ny = 160, 48
     p = _problem(nx, ny)
@@ -152,9 +199,7 @@ def test_calls_that_reject_the_lattice(gpu):
     for storage in ("f32_bf16", "f32_f16"):
         with pytest.raises(gpu.LbmError):
             gpu.Lattice(p, storage)
-    for bc in ("macroscopic", "macroscopic_edges"):
-        q = dict(p, bc_mode=bc)
-        with pytest.raises(gpu.LbmError):
-            gpu.Lattice(q, "f32")
+    with pytest.raises(gpu.LbmError):
+        gpu.Lattice(dict(p, bc_mode="macroscopic_edges"), "f32")
     with pytest.raises(gpu.LbmError):
         gpu.Lattice(_problem(64, 32, cs=0.9), "f32")     # g = 0.81 > 3/4
