@@ -380,8 +380,6 @@ orc_state *orc_create(const orc_config *cfg)
     if (cfg->nx < 1 || cfg->ny < 1 || !(cfg->dh > 0) || !(cfg->dt > 0)) return NULL;
     int Q = cfg->q == 0 ? 5 : cfg->q;
     if (Q != 5 && Q != 9) return NULL;
-    /* D2Q9 is built with the macroscopic rule on the crack faces, not on the outer edges */
-    if (Q == 9 && cfg->edge_macro) return NULL;
     orc_state *s = xcalloc(1, sizeof(orc_state));
     s->c = *cfg;
     s->Q = Q;

@@ -281,9 +281,68 @@ def test_macroscopic_crack_faces(oracle_mod, x_start, x_tip, v_rel):
 
 
 def test_rejected_combinations(oracle_mod):
-    p = _problem(20, 20)
-    p["bc_mode"] = "macroscopic_edges"
-    with pytest.raises(ValueError):
-        oracle_mod.Oracle(p)
     with pytest.raises(Exception):
         oracle_mod.adjoint(_problem(20, 20), 2, [(5, 5)], np.zeros((2, 1)))
+
+
+def test_one_step_with_the_macroscopic_edge_rule(oracle_mod):
+    """D2Q9 with the macroscopic rule on the outer edges: one step is the
+    nine-point moment update followed by the edge rule of Sec. 3.1 on the
+    edge sites (w_B = (3 w_I - w_II)/2 on a free edge, 8/15 w*(t+dt) + 2/3 w_I
+    - 1/5 w_II on a Dirichlet edge; a corner follows its Dirichlet edge, else
+    the bottom / top edge), wdot_B = (w_B - w_B(t)) / dt."""
+    nx, ny = 9, 8
+    edges = ("dirichlet", "free", "dirichlet", "free")
+    p = _problem(nx, ny, edges)
+    p["bc_mode"] = "macroscopic_edges"
+    amps = {0: 0.3, 2: 0.45}
+    p["loads"] = [{"edge": "left", "kind": "linear", "amp": 0.3, "t": 8.0},
+                  {"edge": "bottom", "kind": "linear", "amp": 0.45, "t": 8.0}]
+    ws1 = [0.3 / 8.0, 0.0, 0.45 / 8.0, 0.0]          # w*(t_1)
+    w0, wd0 = W.random_state(nx, ny, seed=8)
+    o = oracle_mod.Oracle(p)
+    o.set_fields(w0, wd0)
+    o.step(1)
+    w1, wd1 = o.fields()
+    z = np.zeros((ny, nx), bool)
+    u, _ = _numpy_step(p, w0, wd0, z, z, [0.0] * 4)   # interior values (edge sites replaced below)
+    new = u.copy()
+
+    def rule(e, a, b):
+        if edges[e] == "dirichlet":
+            return 8.0 / 15.0 * ws1[e] + 2.0 / 3.0 * a - 0.2 * b
+        return 1.5 * a - 0.5 * b
+
+    for j in range(1, ny - 1):
+        new[j, 0] = rule(0, u[j, 1], u[j, 2])
+        new[j, nx - 1] = rule(1, u[j, nx - 2], u[j, nx - 3])
+    for i in range(1, nx - 1):
+        new[0, i] = rule(2, u[1, i], u[2, i])
+        new[ny - 1, i] = rule(3, u[ny - 2, i], u[ny - 3, i])
+    new[0, 0] = rule(2, new[1, 0], new[2, 0])                       # left D, bottom D: bottom
+    new[0, nx - 1] = rule(2, new[1, nx - 1], new[2, nx - 1])        # right free, bottom D: bottom
+    new[ny - 1, 0] = rule(0, new[ny - 1, 1], new[ny - 1, 2])        # left D, top free: left
+    new[ny - 1, nx - 1] = rule(3, new[ny - 2, nx - 1], new[ny - 3, nx - 1])   # free, free: top
+    edge = np.zeros((ny, nx), bool)
+    edge[0, :] = edge[-1, :] = edge[:, 0] = edge[:, -1] = True
+    np.testing.assert_allclose(w1, new, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(wd1[edge], (new - w0)[edge], rtol=0, atol=1e-14)
+    o.close()
+
+
+def test_centre_crack_example_on_d2q9(oracle_mod):
+    """The Sec. 5.2 configuration (quarter size) on D2Q9 with the macroscopic
+    rule on every boundary: both ends grow on the first wave and stay mirror
+    images; the run stays bounded."""
+    p = W.kcrit_centre_crack(scale=4)
+    p["lattice"] = "D2Q9"
+    o = oracle_mod.Oracle(p)
+    o.step(W.KCRIT_CENTRE_STEPS // 4)
+    h, hl = o.history(), o.history_left()
+    assert h["grew"].sum() > 5
+    np.testing.assert_array_equal(hl["grew"], h["grew"])
+    assert np.abs((128 * 2**32 - hl["tip_q"]) - h["tip_q"]).max() <= 16
+    w, _ = o.fields()
+    assert np.all(np.isfinite(w)) and np.abs(w).max() < 1.0
+    assert o.flags() & 2 == 0
+    o.close()
