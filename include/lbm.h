@@ -66,11 +66,13 @@ enum { LBM_LEFT = 0, LBM_RIGHT = 1, LBM_BOTTOM = 2, LBM_TOP = 3 };
  * that the crack handling carries over to it, Sec. 4.1) adds the diagonal
  * links with equilibrium weights 2/3 g (axes) and 1/6 g (diagonals), the
  * isotropic nine-point Laplacian, stable for c_s^2 dt^2 / dh^2 <= 3/4.
- * D2Q9 is built with link-local outer edges (bc_mode LBM_BC_BOUNCEBACK or
- * LBM_BC_MACROSCOPIC; with the latter a site that loses only a diagonal link
- * to the crack takes the normal of the crack face that link crosses, so every
- * boundary point has the column-local rule of the crack faces), FP64 or FP32
- * storage, and not for lbm_batch_*, lbm_decomp_* or lbm_tape_*.
+ * D2Q9 is built with every bc_mode (with LBM_BC_MACROSCOPIC and
+ * LBM_BC_MACROSCOPIC_EDGES a site that loses only a diagonal link to the
+ * crack takes the normal of the crack face that link crosses, so every
+ * crack-face point has the column-local rule of the crack faces; with
+ * LBM_BC_MACROSCOPIC_EDGES the outer-edge points take the edge rule of the
+ * D2Q5 lattice, along the edge's normal), FP64 or FP32 storage, and not for
+ * lbm_batch_*, lbm_decomp_* or lbm_tape_*.
  * Its diagonal links between rows jc-1 and jc cross the crack line at
  * x = (i + 1) dh and are severed when that point lies on the closed crack
  * segment; a diagonal link leaving the body through a corner follows the

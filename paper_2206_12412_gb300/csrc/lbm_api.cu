@@ -76,6 +76,7 @@ cudaError_t enqueue_step_t(const lbm_handle *h, int par, cudaStream_t s)
         if (h->q == 9) {
             cudaError_t e = launch_d2q9_step(a, s);
             if (e == cudaSuccess && h->cp.macro && h->cp.mode != CRACK_NONE) e = launch_d2q9_faces(a, s);
+            if (e == cudaSuccess && h->edge_macro) e = launch_edge_rule(a, s);
             return e;
         }
     }
@@ -346,8 +347,6 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
     if (lattice->velocity_set != LBM_D2Q5 && lattice->velocity_set != LBM_D2Q9)
         return fail(LBM_ERR_ARG, "unknown velocity set (D2Q5 or D2Q9)");
     const bool d2q9 = lattice->velocity_set == LBM_D2Q9;
-    if (d2q9 && lattice->bc_mode == LBM_BC_MACROSCOPIC_EDGES)
-        return fail(LBM_ERR_ARG, "D2Q9 is built without the macroscopic rule on the outer edges (link-local edges)");
     if (d2q9 && lattice->storage != LBM_F64 && lattice->storage != LBM_F32)
         return fail(LBM_ERR_ARG, "D2Q9 needs LBM_F64 or LBM_F32 storage");
     if (d2q9 && slab) return fail(LBM_ERR_ARG, "D2Q9 is not built for row slabs");
@@ -567,6 +566,7 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
     h->q = d2q9 ? 9 : 5;
     cp.words = h->words;
     cp.two_tips = cr.two_tips ? 1 : 0;
+    cp.q = d2q9 ? 9 : 5;
     cp.mu = material->mu;
     cp.cs = cs;
     cp.dt = grid->dt;

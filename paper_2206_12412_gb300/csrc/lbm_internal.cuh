@@ -81,7 +81,7 @@ struct CrackState {
 struct CrackParams {
     int32_t mode, jc, nx, ny;
     int32_t macro, words;
-    int32_t two_tips, pad;
+    int32_t two_tips, q;    // q: velocity set (5 or 9)
     double mu, cs, dt, dh, K_C, v_max, r0, r_min_fixed, fit_width, v_rel;
     int64_t start_q, clamp_q, hist_cap;
 };

@@ -631,8 +631,16 @@ __device__ __forceinline__ void edge_rule_at(const StepArgs<T, D> &a, int t)
     const int ev = (onB && j == 0) ? BOTTOM : ((onT && j == ny - 1) ? TOP : -1);
     const int jc = a.p.jc;
     bool face = false;
-    if (a.p.macro && a.p.mode != CRACK_NONE && (j == jc || j == jc - 1))
+    if (a.p.macro && a.p.mode != CRACK_NONE && (j == jc || j == jc - 1)) {
         face = (a.cut_v[(int64_t)(jc - 1) * a.words + (i >> 5)] >> (i & 31)) & 1u;
+        if (a.p.q == 9) {
+            // D2Q9: also a column of a severed diagonal pair (the crack state
+            // of the step, as the update wrote it)
+            const int64_t rq = a.s_out->r.tip_q, lq = a.p.two_tips ? a.s_out->l.tip_q : a.p.start_q;
+            const int64_t ml = (int64_t)i << kQBits, mr = (int64_t)(i + 1) << kQBits;
+            face |= (i >= 1 && lq <= ml && ml <= rq) || (i + 1 <= nx - 1 && lq <= mr && mr <= rq);
+        }
+    }
     T v;
     if (face) {
         // a crack-face point on an edge column (eh >= 0): its x_I, x_II are

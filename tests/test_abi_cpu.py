@@ -88,7 +88,6 @@ def _structs(**over):
     ({"lat__omega": 0.8}, "omega"),
     ({"lat__storage": 7}, "storage"),
     ({"lat__velocity_set": 3}, "D2Q5"),
-    ({"lat__velocity_set": 1, "lat__bc_mode": 2}, "link-local"),
     ({"lat__velocity_set": 1, "lat__bc_mode": 0, "lat__storage": 2}, "D2Q9 needs"),
     ({"lat__velocity_set": 1, "lat__bc_mode": 0, "mat__mu": 0.8}, "3/4"),
     ({"lat__velocity_set": 0, "mat__mu": 0.6}, "1/2"),
