@@ -66,6 +66,8 @@ class _Config(C.Structure):
         ("hist_cap", C.c_int64),
         ("two_tips", C.c_int32), ("edge_macro", C.c_int32),
         ("q", C.c_int32), ("pad_", C.c_int32),
+        ("line", C.c_int32), ("pad2_", C.c_int32),
+        ("y_start", C.c_double), ("y_tip", C.c_double),
     ]
 
 
@@ -108,6 +110,13 @@ def _load():
         lib.orc_evaluate_K.restype = C.c_double
         lib.orc_evaluate_K_left.argtypes = [P, d, C.c_int64, C.c_double, C.c_double, C.POINTER(C.c_int32)]
         lib.orc_evaluate_K_left.restype = C.c_double
+        lib.orc_evaluate_K_line.argtypes = [P, d, C.c_int64, C.c_int64, C.c_double, C.c_double, C.POINTER(C.c_int32)]
+        lib.orc_evaluate_K_line.restype = C.c_double
+        lib.orc_tip_y.argtypes = [P]
+        lib.orc_tip_y.restype = C.c_int64
+        lib.orc_get_history_y.argtypes = [P, C.POINTER(C.c_int64), C.c_int64]
+        lib.orc_get_history_y.restype = C.c_int64
+        lib.orc_direction.argtypes = [P, d]
         lib.orc_get_history_left.argtypes = [P, d, d, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                                              C.POINTER(C.c_int32), C.c_int64]
         lib.orc_get_history_left.restype = C.c_int64
@@ -157,10 +166,17 @@ def make_config(problem: dict):
     cfg.q = {"D2Q5": 5, "D2Q9": 9}[problem.get("lattice", "D2Q5")]
     cr = problem.get("crack") or {"mode": "none"}
     cfg.crack_mode = CRACK[cr.get("mode", "none")]
-    if cfg.crack_mode:
+    if cfg.crack_mode and "y_tip" in cr:
+        # a straight crack in any direction: from (x_start, y_start) through
+        # (x_tip, y_tip), growing along that direction
+        cfg.line = 1
+        cfg.x_start, cfg.y_start = float(cr["x_start"]), float(cr["y_start"])
+        cfg.x_tip, cfg.y_tip = float(cr["x_tip"]), float(cr["y_tip"])
+    elif cfg.crack_mode:
         jc = float(cr["y"]) / cfg.dh
         cfg.jc = int(round(jc))
         cfg.x_start, cfg.x_tip = float(cr.get("x_start", 0.0)), float(cr["x_tip"])
+    if cfg.crack_mode:
         cfg.v_rel = float(cr.get("v_rel", 0.0))
         cfg.K_C = float(cr.get("K_C", 0.0))
         cfg.v_max = float(cr.get("v_max", 0.85))
@@ -251,7 +267,31 @@ class Oracle:
         n = self.lib.orc_get_history(self.h, _dptr(K), _dptr(v), tip.ctypes.data_as(C.POINTER(C.c_int64)),
                                      npairs.ctypes.data_as(C.POINTER(C.c_int32)),
                                      grew.ctypes.data_as(C.POINTER(C.c_int32)), cap)
-        return {"K": K[:n], "v": v[:n], "tip_q": tip[:n], "npairs": npairs[:n], "grew": grew[:n]}
+        out = {"K": K[:n], "v": v[:n], "tip_q": tip[:n], "npairs": npairs[:n], "grew": grew[:n]}
+        if self._cfg.line:
+            ty = np.zeros(cap, np.int64)
+            self.lib.orc_get_history_y(self.h, ty.ctypes.data_as(C.POINTER(C.c_int64)), cap)
+            out["tip_yq"] = ty[:n]
+        return out
+
+    def tip_y_q(self) -> int:
+        """y of the tip (units of 2^-32 dh); the crack along +x keeps y = jc dh."""
+        return int(self.lib.orc_tip_y(self.h))
+
+    def direction(self):
+        """Unit direction of growth (c_x, c_y)."""
+        out = np.zeros(2)
+        self.lib.orc_direction(self.h, _dptr(out))
+        return float(out[0]), float(out[1])
+
+    def evaluate_K_line(self, w: np.ndarray, tip_xq: int, tip_yq: int, r_min: float, fit_width: float):
+        """K of a crack in any direction at the tip (tip_xq, tip_yq), from the
+        fields w and the oracle's current cut mask."""
+        w = np.ascontiguousarray(w, dtype=np.float64).reshape(self.ny, self.nx)
+        npairs = C.c_int32(0)
+        K = self.lib.orc_evaluate_K_line(self.h, _dptr(w), int(tip_xq), int(tip_yq), float(r_min), float(fit_width),
+                                         C.byref(npairs))
+        return K, npairs.value
 
     def history_left(self) -> dict:
         """Per-step record of the left end of a two-tip crack."""

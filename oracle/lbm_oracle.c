@@ -57,7 +57,14 @@
  *     Dirichlet value is w*(t_n+1), the time of the unknown w_B; the system
  *     S w_B = R couples the boundary points only through interior points
  *     that are boundary points themselves and is solved exactly by sweeps
- *     until a sweep changes no bit.
+ *     until a sweep changes no bit;
+ *   - a straight crack in any direction (Sec. 4.1) runs from its start
+ *     through its initial tip and grows along that direction c: each
+ *     component of Delta a c is rounded to the grid, so the crack is the
+ *     polyline of the tips, every segment tested exactly; its pairs for K
+ *     are the ends of the severed links, at r = (x_tip - m) . c from the
+ *     link midpoint m, with delta = w(left of c) - w(right of c); the tip
+ *     stops where it meets the body's boundary; the faces are link-local.
  */
 #include <math.h>
 #include <stdint.h>
@@ -95,6 +102,9 @@ typedef struct {
     int32_t edge_macro;  /* the macroscopic rule (Sec. 3.1) on the outer edges too */
     int32_t q;           /* velocity set: 5 (D2Q5, Sec. 3) or 9 (D2Q9) */
     int32_t pad_;
+    int32_t line;        /* a straight crack in any direction, from (x_start, y_start) through (x_tip, y_tip) */
+    int32_t pad2_;
+    double y_start, y_tip;
 } orc_config;
 
 typedef struct {
@@ -124,6 +134,9 @@ typedef struct {
     uint8_t *cut_d1;     /* D2Q9: link (i,j)-(i+1,j+1) */
     uint8_t *cut_d2;     /* D2Q9: link (i+1,j)-(i,j+1) */
     int64_t start_q, tip_q, clamp_q;
+    int64_t start_yq, tip_yq;   /* y of the crack's start and tip (y = jc dh for the crack along +x) */
+    double dir_x, dir_y;        /* unit direction of growth */
+    int64_t *htipy;
     double v_prev, K_last;
     int32_t npairs_last, flags, arrested_for_good;
     int32_t *bprev, nbprev;
@@ -331,7 +344,7 @@ void orc_destroy(orc_state *s)
     free(s->bprev); free(s->bl); free(s->is_bpoint);
     free(s->hK); free(s->hv); free(s->htip); free(s->hnp); free(s->hgrow);
     free(s->ep);
-    free(s->lbprev); free(s->hKl); free(s->hvl); free(s->htipl); free(s->hnpl); free(s->hgrowl);
+    free(s->lbprev); free(s->hKl); free(s->hvl); free(s->htipl); free(s->htipy); free(s->hnpl); free(s->hgrowl);
     free(s->queue); free(s->inq); free(s->visited);
     for (int e = 0; e < 4; ++e) free(s->series[e]);
     free(s);
@@ -346,7 +359,6 @@ static int build_edge_points(orc_state *s);
 static void initial_crack(orc_state *s)
 {
     int nx = s->c.nx, ny = s->c.ny;
-    int64_t yq = (int64_t)s->c.jc << ORC_Q;
     int32_t *B = malloc(sizeof(int32_t) * 4 * (size_t)nx * ny);
     int nB = 0;
     static const int ONCE[4] = {1, 2, 5, 6};   /* each link once: +x, +y and the two upward diagonals */
@@ -358,7 +370,7 @@ static void initial_crack(orc_state *s)
             if (m < 0 || wrap) continue;
             int i = k % nx, j = k / nx, mi = m % nx, mj = m / nx;
             if (orc_segments_intersect(site_cx_q(i), site_cx_q(j), site_cx_q(mi), site_cx_q(mj),
-                                       s->start_q, yq, s->tip_q, yq)) {
+                                       s->start_q, s->start_yq, s->tip_q, s->tip_yq)) {
                 *cut = 1;
                 B[nB++] = k;
                 B[nB++] = m;
@@ -371,8 +383,40 @@ static void initial_crack(orc_state *s)
         for (int q = 0; q < s->nbprev; ++q) dup |= s->bprev[q] == B[b];
         if (!dup) s->bprev[s->nbprev++] = B[b];
     }
-    for (int b = 0; b < s->nbprev; ++b) add_bpoint(s, s->bprev[b]);
+    if (!s->c.line)
+        for (int b = 0; b < s->nbprev; ++b) add_bpoint(s, s->bprev[b]);
     free(B);
+}
+
+/* A crack in any direction (Sec. 4.1: the crack is a line independent of
+ * the lattice, growing along a given direction): the start and the tip on
+ * the fixed-point grid, the unit direction from the one to the other, and
+ * the checks that the segment lies in the body [0, nx dh] x [0, ny dh] and
+ * that its line passes through no site centre (a site on the crack would
+ * be neither above nor below it).  The direction's components are formed
+ * without fused multiply-adds (volatile products), so that every
+ * implementation of this reading rounds them alike. */
+static int line_setup(orc_state *s)
+{
+    const orc_config *c = &s->c;
+    double sc = (double)qone() / c->dh;
+    s->start_q = llrint(c->x_start * sc);
+    s->start_yq = llrint(c->y_start * sc);
+    s->tip_q = llrint(c->x_tip * sc);
+    s->tip_yq = llrint(c->y_tip * sc);
+    int64_t X = (int64_t)c->nx << ORC_Q, Y = (int64_t)c->ny << ORC_Q;
+    if (s->start_q < 0 || s->start_q > X || s->tip_q < 0 || s->tip_q > X) return 0;
+    if (s->start_yq < 0 || s->start_yq > Y || s->tip_yq < 0 || s->tip_yq > Y) return 0;
+    if (s->start_q == s->tip_q && s->start_yq == s->tip_yq) return 0;
+    volatile double dx = (double)(s->tip_q - s->start_q), dy = (double)(s->tip_yq - s->start_yq);
+    volatile double xx = dx * dx, yy = dy * dy;
+    double len = sqrt(xx + yy);
+    s->dir_x = dx / len;
+    s->dir_y = dy / len;
+    for (int j = 0; j < c->ny; ++j)
+        for (int i = 0; i < c->nx; ++i)
+            if (orient(s->start_q, s->start_yq, s->tip_q, s->tip_yq, site_cx_q(i), site_cx_q(j)) == 0) return 0;
+    return 1;
 }
 
 orc_state *orc_create(const orc_config *cfg)
@@ -380,6 +424,17 @@ orc_state *orc_create(const orc_config *cfg)
     if (cfg->nx < 1 || cfg->ny < 1 || !(cfg->dh > 0) || !(cfg->dt > 0)) return NULL;
     int Q = cfg->q == 0 ? 5 : cfg->q;
     if (Q != 5 && Q != 9) return NULL;
+    /* a crack in any direction is built for D2Q5 with link-local faces and
+     * one growing end; its K window must lie more than half a spacing behind
+     * the tip (the links a step severs have their midpoints at most that far
+     * behind the old tip) */
+    if (cfg->line) {
+        if (Q != 5 || cfg->bc_mode != ORC_BC_BOUNCEBACK || cfg->edge_macro || cfg->two_tips ||
+            cfg->crack_mode == ORC_CRACK_NONE)
+            return NULL;
+        double rmin = cfg->r_min_fixed > 0.0 ? cfg->r_min_fixed : cfg->r0;
+        if (!(rmin > 0.5 * cfg->dh)) return NULL;
+    }
     orc_state *s = xcalloc(1, sizeof(orc_state));
     s->c = *cfg;
     s->Q = Q;
@@ -411,6 +466,7 @@ orc_state *orc_create(const orc_config *cfg)
     s->hKl = xcalloc((size_t)hc, sizeof(double));
     s->hvl = xcalloc((size_t)hc, sizeof(double));
     s->htipl = xcalloc((size_t)hc, sizeof(int64_t));
+    s->htipy = xcalloc((size_t)hc, sizeof(int64_t));
     s->hnpl = xcalloc((size_t)hc, sizeof(int32_t));
     s->hgrowl = xcalloc((size_t)hc, sizeof(int32_t));
     for (int e = 0; e < 4; ++e) {
@@ -426,6 +482,13 @@ orc_state *orc_create(const orc_config *cfg)
     if (cfg->crack_mode != ORC_CRACK_NONE) {
         s->start_q = llrint(cfg->x_start / cfg->dh * (double)qone());
         s->tip_q = llrint(cfg->x_tip / cfg->dh * (double)qone());
+        s->start_yq = s->tip_yq = (int64_t)cfg->jc << ORC_Q;
+        s->dir_x = 1.0;
+        s->dir_y = 0.0;
+        if (cfg->line && !line_setup(s)) {
+            orc_destroy(s);
+            return NULL;
+        }
         s->ltip_q = s->start_q;
         s->lv_prev = s->v_prev;
         initial_crack(s);
@@ -782,6 +845,63 @@ static double evaluate_K_dir(const orc_state *s, const double *w, int64_t tip_q,
     return s->c.mu / 4.0 * num / den;
 }
 
+/* K at the tip (tx, ty) of a crack in any direction (Sec. 4.2 read for a
+ * crack that is not aligned with the lattice): the pairs of sites adjacent
+ * to the crack are the two ends of each severed link; the pair's distance
+ * from the tip along the crack is that of the link's midpoint m,
+ * r = (x_tip - m) . c (c the unit direction of growth), and the opening is
+ * delta = w(left of c) - w(right of c), so that a crack along +x has the
+ * pairs, distances and opening of evaluate_K_dir.  The projection is formed
+ * without fused multiply-adds, as in line_setup. */
+static double evaluate_K_line(const orc_state *s, const double *w, int64_t tx, int64_t ty, double r_min, double wfit,
+                              int32_t *npairs)
+{
+    int nx = s->c.nx, ny = s->c.ny;
+    double dh = s->c.dh;
+    double num = 0.0, den = 0.0;
+    int np = 0;
+    double lo = r_min / dh, hi = (r_min + wfit) / dh;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i)
+            for (int vert = 0; vert <= 1; ++vert) {
+                int32_t k0 = j * nx + i, k1;
+                int64_t mx, my;
+                if (!vert) {
+                    if (i + 1 >= nx || !s->cut_h[k0]) continue;
+                    k1 = k0 + 1;
+                    mx = (int64_t)(i + 1) << ORC_Q;
+                    my = site_cx_q(j);
+                } else {
+                    if (j + 1 >= ny || !s->cut_v[k0]) continue;
+                    k1 = k0 + nx;
+                    mx = site_cx_q(i);
+                    my = (int64_t)(j + 1) << ORC_Q;
+                }
+                volatile double px = (double)(tx - mx) / (double)qone() * s->dir_x;
+                volatile double py = (double)(ty - my) / (double)qone() * s->dir_y;
+                double r_h = px + py;
+                if (!(r_h >= lo && r_h < hi)) continue;
+                /* k1 is the site at +x (horizontal link) or +y (vertical
+                 * link); it lies left of c when c_y < 0, resp. c_x > 0 */
+                int k1_left = vert ? s->dir_x > 0.0 : s->dir_y < 0.0;
+                double delta = k1_left ? w[k1] - w[k0] : w[k0] - w[k1];
+                double r = r_h * dh;
+                double sfac = sqrt(r / (2.0 * ORC_PI));
+                num += delta * sfac;
+                den += sfac * sfac;
+                ++np;
+            }
+    *npairs = np;
+    if (np == 0) return 0.0;
+    return s->c.mu / 4.0 * num / den;
+}
+
+double orc_evaluate_K_line(const orc_state *s, const double *w, int64_t tx, int64_t ty, double r_min, double wfit,
+                           int32_t *npairs)
+{
+    return evaluate_K_line(s, w, tx, ty, r_min, wfit, npairs);
+}
+
 static double evaluate_K(const orc_state *s, const double *w, int64_t tip_q, double r_min, double wfit, int32_t *npairs)
 {
     return evaluate_K_dir(s, w, tip_q, r_min, wfit, +1, npairs);
@@ -877,7 +997,8 @@ static void tip_criterion(const orc_state *s, int dir, double v_prev, int64_t ti
 {
     const orc_config *c = &s->c;
     double r_min = c->r_min_fixed > 0.0 ? c->r_min_fixed : c->r0 / (1.0 - v_prev);  /* eq. r(v) */
-    *K = evaluate_K_dir(s, s->w, tip, r_min, c->fit_width, dir, np);
+    *K = c->line ? evaluate_K_line(s, s->w, tip, s->tip_yq, r_min, c->fit_width, np)
+                 : evaluate_K_dir(s, s->w, tip, r_min, c->fit_width, dir, np);
     *propagate = 0;
     *v = 0.0;
     if (c->crack_mode == ORC_CRACK_PRESCRIBED) {
@@ -888,6 +1009,37 @@ static void tip_criterion(const orc_state *s, int dir, double v_prev, int64_t ti
         *propagate = 1;
         *v = c->v_max * tanh(sqrt(ratio * ratio * ratio * ratio - 1.0));  /* eq. v-tanh */
     }
+}
+
+/* A tip of a crack in any direction that would reach or cross the boundary
+ * of the body [0, nx dh] x [0, ny dh] stops on it, where the segment from
+ * the old tip (px, py) to (*qx, *qy) meets it first; the point is formed
+ * in exact integer arithmetic (the quotient truncated towards zero).
+ * Returns 1 if the tip was stopped. */
+static int line_clamp(const orc_state *s, int64_t px, int64_t py, int64_t *qx, int64_t *qy)
+{
+    int64_t X = (int64_t)s->c.nx << ORC_Q, Y = (int64_t)s->c.ny << ORC_Q;
+    int64_t dx = *qx - px, dy = *qy - py;
+    int hitx = (dx > 0 && *qx >= X) || (dx < 0 && *qx <= 0);
+    int hity = (dy > 0 && *qy >= Y) || (dy < 0 && *qy <= 0);
+    if (!hitx && !hity) return 0;
+    int64_t fx = dx > 0 ? X : 0, fy = dy > 0 ? Y : 0;
+    __int128 ux = (__int128)(fx - px), uy = (__int128)(fy - py);
+    int xfirst = hitx;
+    if (hitx && hity) {
+        /* the face met first: t_x = ux / dx against t_y = uy / dy, both in [0, 1] */
+        __int128 ax = ux < 0 ? -ux : ux, ay = uy < 0 ? -uy : uy;
+        __int128 adx = dx < 0 ? -(__int128)dx : dx, ady = dy < 0 ? -(__int128)dy : dy;
+        xfirst = ax * ady <= ay * adx;
+    }
+    if (xfirst) {
+        *qx = fx;
+        *qy = py + (int64_t)(ux * dy / dx);
+    } else {
+        *qy = fy;
+        *qx = px + (int64_t)(uy * dx / dy);
+    }
+    return 1;
 }
 
 /* Advance one tip by Delta a = adot dt (towards +x or -x, stopping at the far
@@ -902,6 +1054,21 @@ static int tip_advance(orc_state *s, int dir, double v)
     int64_t yq = (int64_t)c->jc << ORC_Q;
     int32_t B[64];
     int nB;
+    if (c->line) {
+        /* along the crack's direction: each component of Delta a c rounded
+         * to the grid (c = (1, 0) gives the advance below) */
+        double q = adot * c->dt / c->dh * (double)qone();
+        int64_t px = s->tip_q, py = s->tip_yq;
+        int64_t nxq = px + llrint(q * s->dir_x), nyq = py + llrint(q * s->dir_y);
+        if (line_clamp(s, px, py, &nxq, &nyq)) { s->arrested_for_good = 1; s->flags |= ORC_FLAG_CLAMPED; }
+        if (nxq == px && nyq == py) return 0;
+        s->tip_q = nxq;
+        s->tip_yq = nyq;
+        nB = checklinks(s, px, py, nxq, nyq, B, 64);
+        qsort(B, (size_t)nB, sizeof(int32_t), cmp_i32);
+        if (nB > 0) { memcpy(s->bprev, B, sizeof(int32_t) * (size_t)nB); s->nbprev = nB; }
+        return 1;
+    }
     if (dir > 0) {
         int64_t prev = s->tip_q, next = prev + dq;
         if (next >= s->clamp_q) { next = s->clamp_q; s->arrested_for_good = 1; s->flags |= ORC_FLAG_CLAMPED; }
@@ -958,6 +1125,7 @@ static void crack_growth(orc_state *s)
         int64_t h = s->hist_n;
         s->hK[h] = K; s->hv[h] = v; s->htip[h] = s->tip_q; s->hnp[h] = np; s->hgrow[h] = grew;
         s->hKl[h] = Kl; s->hvl[h] = vl; s->htipl[h] = s->ltip_q; s->hnpl[h] = npl; s->hgrowl[h] = grewl;
+        s->htipy[h] = s->tip_yq;
     }
     s->hist_n += 1;
 }
@@ -1015,6 +1183,21 @@ int64_t orc_get_history_left(const orc_state *s, double *K, double *v, int64_t *
 }
 
 int64_t orc_left_tip(const orc_state *s) { return s->ltip_q; }
+
+/* The tip's y (units of 2^-32 dh) now and per step (crack in any direction). */
+int64_t orc_tip_y(const orc_state *s) { return s->tip_yq; }
+int64_t orc_get_history_y(const orc_state *s, int64_t *tip_yq, int64_t cap)
+{
+    int64_t n = s->hist_n < s->c.hist_cap ? s->hist_n : s->c.hist_cap;
+    if (n > cap) n = cap;
+    for (int64_t h = 0; h < n; ++h) tip_yq[h] = s->htipy[h];
+    return n;
+}
+void orc_direction(const orc_state *s, double *dir2)
+{
+    dir2[0] = s->dir_x;
+    dir2[1] = s->dir_y;
+}
 
 /* The outer-edge boundary points: site, x_I, x_II, rule and edge of each. */
 int32_t orc_get_edge_points(const orc_state *s, int32_t *out5, int32_t cap)
