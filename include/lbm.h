@@ -166,6 +166,30 @@ typedef struct lbm_crack {
     int64_t hist_cap;
 } lbm_crack;
 
+/* Straight crack in any direction (Sec. 4.1: the crack is a line independent
+ * of the lattice that grows along a given direction), from (x_start, y_start)
+ * through the initial tip (x_tip, y_tip) (physical units, both in the closed
+ * body [0, nx dh] x [0, ny dh], distinct), growing from the tip along the
+ * unit direction c from the one to the other.  Both points are rounded to
+ * the 2^-32 dh grid; every advance Delta a c is rounded to it per
+ * component, and each step severs the H and V links that the segment from
+ * the old to the new tip meets (closed segments, exact), so the crack is
+ * the polyline of its tips; a tip that meets the body's boundary stops
+ * there.  The crack's line must pass through no site centre.  K (eq. sif)
+ * is fitted over the severed links whose midpoint m lies at
+ * r = (x_tip - m) . c in [r_min, r_min + W), with the opening
+ * w(left of c) - w(right of c) of the link's two sites; the window must
+ * start more than dh / 2 behind the tip (r0 > dh / 2, or r_min > dh / 2).
+ * The other fields are those of lbm_crack (two_tips does not exist: one end
+ * grows).  Built for D2Q5, LBM_BC_BOUNCEBACK, LBM_F64 or LBM_F32 storage. */
+typedef struct lbm_crack_line {
+    int32_t mode;
+    int32_t pad;
+    double x_start, y_start, x_tip, y_tip;
+    double v_rel, K_C, v_max, r0, r_min, fit_width;
+    int64_t hist_cap;
+} lbm_crack_line;
+
 /* Boundary value w*(t) of one Dirichlet edge:
  * LINEAR amp*min(t/t_ramp,1); SIN2 amp*sin^2(pi t/(2 t_ramp)) then amp
  * (Sec. 5.1); HALFSINE amp*sin(pi t/t_ramp) then 0 (Sec. 5.2); SERIES
@@ -213,6 +237,26 @@ typedef struct lbm_handle lbm_handle;
 lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lbm_material *material,
                       const lbm_crack *crack, const lbm_loading *loads, int32_t n_loads,
                       void *stream, const lbm_allocator *allocator, lbm_handle **out);
+
+/* The same with a straight crack in any direction (lbm_crack_line; crack
+ * must not be NULL and its mode not LBM_CRACK_NONE).  Every call below
+ * applies to the handle, except lbm_crack_state_left, lbm_set_launch (the
+ * step has a fixed launch shape), lbm_batch_create, the row slabs
+ * (lbm_decomp.h) and the adjoint (lbm_adjoint.h), which return
+ * LBM_ERR_ARG or LBM_ERR_STATE.  In lbm_crack_state, tip_q and tip_x are
+ * the tip's x and n_cut counts the severed links; lbm_line_tip gives its y.
+ * LBM_ERR_ARG for the cases listed at lbm_crack_line. */
+lbm_status lbm_create_line(const lbm_grid *grid, const lbm_lattice *lattice, const lbm_material *material,
+                           const lbm_crack_line *crack, const lbm_loading *loads, int32_t n_loads,
+                           void *stream, const lbm_allocator *allocator, lbm_handle **out);
+
+/* The tip of a crack in any direction: x and y in units of 2^-32 dh (either
+ * pointer may be NULL) and, if y_hist is not NULL, the y of the last
+ * min(cap, hist_n, hist_cap) per-step records in chronological order (their
+ * x, K, v and pairs come from lbm_crack_state); *n_written receives the
+ * number of records.  LBM_ERR_STATE for a handle without such a crack.
+ * Synchronises the stream. */
+lbm_status lbm_line_tip(lbm_handle *h, int64_t *x_q, int64_t *y_q, int64_t *y_hist, int64_t cap, int64_t *n_written);
 
 /* Enqueue n >= 0 time steps (each: bulk update, crack-face rule, crack step)
  * on the handle's stream.  Asynchronous; errors of the device work surface at

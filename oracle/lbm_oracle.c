@@ -399,11 +399,10 @@ static void initial_crack(orc_state *s)
 static int line_setup(orc_state *s)
 {
     const orc_config *c = &s->c;
-    double sc = (double)qone() / c->dh;
-    s->start_q = llrint(c->x_start * sc);
-    s->start_yq = llrint(c->y_start * sc);
-    s->tip_q = llrint(c->x_tip * sc);
-    s->tip_yq = llrint(c->y_tip * sc);
+    s->start_q = llrint(c->x_start / c->dh * (double)qone());
+    s->start_yq = llrint(c->y_start / c->dh * (double)qone());
+    s->tip_q = llrint(c->x_tip / c->dh * (double)qone());
+    s->tip_yq = llrint(c->y_tip / c->dh * (double)qone());
     int64_t X = (int64_t)c->nx << ORC_Q, Y = (int64_t)c->ny << ORC_Q;
     if (s->start_q < 0 || s->start_q > X || s->tip_q < 0 || s->tip_q > X) return 0;
     if (s->start_yq < 0 || s->start_yq > Y || s->tip_yq < 0 || s->tip_yq > Y) return 0;

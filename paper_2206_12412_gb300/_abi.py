@@ -43,6 +43,14 @@ class Crack(C.Structure):
                 ("hist_cap", C.c_int64)]
 
 
+class CrackLine(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("pad", C.c_int32),
+                ("x_start", C.c_double), ("y_start", C.c_double), ("x_tip", C.c_double), ("y_tip", C.c_double),
+                ("v_rel", C.c_double), ("K_C", C.c_double), ("v_max", C.c_double),
+                ("r0", C.c_double), ("r_min", C.c_double), ("fit_width", C.c_double),
+                ("hist_cap", C.c_int64)]
+
+
 class Loading(C.Structure):
     _fields_ = [("edge", C.c_int32), ("kind", C.c_int32), ("amp", C.c_double), ("t_ramp", C.c_double),
                 ("series", C.POINTER(C.c_double)), ("n_series", C.c_int64)]
@@ -67,6 +75,11 @@ PROTOTYPES = {
     "lbm_create": (C.c_int, [C.POINTER(Grid), C.POINTER(Lattice_), C.POINTER(Material), C.POINTER(Crack),
                              C.POINTER(Loading), C.c_int32, C.c_void_p, C.POINTER(Allocator),
                              C.POINTER(C.c_void_p)]),
+    "lbm_create_line": (C.c_int, [C.POINTER(Grid), C.POINTER(Lattice_), C.POINTER(Material), C.POINTER(CrackLine),
+                                  C.POINTER(Loading), C.c_int32, C.c_void_p, C.POINTER(Allocator),
+                                  C.POINTER(C.c_void_p)]),
+    "lbm_line_tip": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                               C.c_int64, C.POINTER(C.c_int64)]),
     "lbm_step": (C.c_int, [C.c_void_p, C.c_int64]),
     "lbm_fields": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int32]),
     "lbm_set_fields": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int32]),

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(PKG, "liblbm.so")
-SOURCES = ["lbm_kernels.cu", "lbm_adjoint.cu", "lbm_api.cu", "lbm_tape.cu", "lbm_decomp.cu", "lbm_d2q9.cu"]
+SOURCES = ["lbm_kernels.cu", "lbm_adjoint.cu", "lbm_api.cu", "lbm_tape.cu", "lbm_decomp.cu", "lbm_d2q9.cu", "lbm_line.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I" + INCLUDE, "-I" + CSRC]
 

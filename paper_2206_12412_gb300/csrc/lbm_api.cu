@@ -61,6 +61,79 @@ constexpr int64_t kDefaultHistCap = 65536;
 int64_t floor_div(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// ------------------------------------------ geometry of a crack in any direction
+// Exact on the 2^-32 dh grid (128-bit cross products).
+
+int64_t centre_q(int64_t i) { return (2 * i + 1) << (kQBits - 1); }
+
+int orient_q(int64_t ax, int64_t ay, int64_t bx, int64_t by, int64_t cx, int64_t cy)
+{
+    const __int128 v = (__int128)(bx - ax) * (__int128)(cy - ay) - (__int128)(by - ay) * (__int128)(cx - ax);
+    return (v > 0) - (v < 0);
+}
+
+bool within_q(int64_t ax, int64_t ay, int64_t bx, int64_t by, int64_t px, int64_t py)
+{
+    return px >= std::min(ax, bx) && px <= std::max(ax, bx) && py >= std::min(ay, by) && py <= std::max(ay, by);
+}
+
+// Do the closed segments p1p2 and q1q2 meet?
+bool segments_meet_q(int64_t p1x, int64_t p1y, int64_t p2x, int64_t p2y, int64_t q1x, int64_t q1y, int64_t q2x,
+                     int64_t q2y)
+{
+    const int a = orient_q(q1x, q1y, q2x, q2y, p1x, p1y), b = orient_q(q1x, q1y, q2x, q2y, p2x, p2y);
+    const int c = orient_q(p1x, p1y, p2x, p2y, q1x, q1y), d = orient_q(p1x, p1y, p2x, p2y, q2x, q2y);
+    if (a * b < 0 && c * d < 0) return true;
+    return (a == 0 && within_q(q1x, q1y, q2x, q2y, p1x, p1y)) || (b == 0 && within_q(q1x, q1y, q2x, q2y, p2x, p2y)) ||
+           (c == 0 && within_q(p1x, p1y, p2x, p2y, q1x, q1y)) || (d == 0 && within_q(p1x, p1y, p2x, p2y, q2x, q2y));
+}
+
+// Does the line through S and T pass through a site centre of the lattice?
+// Along the axis of its larger extent each column (row) holds one candidate
+// crossing; the sites next to it are tested exactly.
+bool line_hits_a_centre(const LineSpec &L, int nx, int ny)
+{
+    const int64_t dx = L.tip_xq - L.start_xq, dy = L.tip_yq - L.start_yq;
+    const bool by_col = (dx < 0 ? -dx : dx) >= (dy < 0 ? -dy : dy);
+    const int n = by_col ? nx : ny, m = by_col ? ny : nx;
+    for (int i = 0; i < n; ++i) {
+        const double c = ((double)i + 0.5) * 4294967296.0;
+        const double t = by_col ? (c - (double)L.start_xq) / (double)dx : (c - (double)L.start_yq) / (double)dy;
+        const double o = (by_col ? (double)L.start_yq + t * (double)dy : (double)L.start_xq + t * (double)dx) / 4294967296.0;
+        if (!(o > -2.0 && o < (double)m + 2.0)) continue;
+        const int j0 = (int)std::floor(o - 0.5);
+        for (int j = j0 - 1; j <= j0 + 2; ++j) {
+            if (j < 0 || j >= m) continue;
+            const int64_t cx = centre_q(by_col ? i : j), cy = centre_q(by_col ? j : i);
+            if (orient_q(L.start_xq, L.start_yq, L.tip_xq, L.tip_yq, cx, cy) == 0) return true;
+        }
+    }
+    return false;
+}
+
+// The initial crack: every H and V link the segment from the start to the
+// tip meets, as [H mask | V mask] (ny rows of `words` words each).
+std::vector<uint32_t> line_initial_masks(const LineSpec &L, int nx, int ny, int words)
+{
+    std::vector<uint32_t> m((size_t)2 * ny * words, 0u);
+    const int64_t one = (int64_t)1 << kQBits, half = one / 2;
+    const int64_t i0 = std::max<int64_t>(0, floor_div(std::min(L.start_xq, L.tip_xq) - 3 * half, one));
+    const int64_t i1 = std::min<int64_t>(nx - 1, floor_div(std::max(L.start_xq, L.tip_xq) + half, one) + 1);
+    const int64_t j0 = std::max<int64_t>(0, floor_div(std::min(L.start_yq, L.tip_yq) - 3 * half, one));
+    const int64_t j1 = std::min<int64_t>(ny - 1, floor_div(std::max(L.start_yq, L.tip_yq) + half, one) + 1);
+    const size_t vo = (size_t)ny * words;
+    for (int64_t j = j0; j <= j1; ++j)
+        for (int64_t i = i0; i <= i1; ++i) {
+            const int64_t cx = centre_q(i), cy = centre_q(j);
+            const size_t wi = (size_t)j * words + (size_t)(i >> 5);
+            if (i + 1 < nx && segments_meet_q(cx, cy, centre_q(i + 1), cy, L.start_xq, L.start_yq, L.tip_xq, L.tip_yq))
+                m[wi] |= 1u << (i & 31);
+            if (j + 1 < ny && segments_meet_q(cx, cy, cx, centre_q(j + 1), L.start_xq, L.start_yq, L.tip_xq, L.tip_yq))
+                m[vo + wi] |= 1u << (i & 31);
+        }
+    return m;
+}
+
 }  // namespace
 
 
@@ -73,6 +146,7 @@ cudaError_t enqueue_step_t(const lbm_handle *h, int par, cudaStream_t s)
     StepArgs<T, D> a;
     make_step_args(h, par, a);
     if constexpr (std::is_same<T, D>::value) {
+        if (h->line) return launch_line_step(a, s);
         if (h->q == 9) {
             cudaError_t e = launch_d2q9_step(a, s);
             if (e == cudaSuccess && h->cp.macro && h->cp.mode != CRACK_NONE) e = launch_d2q9_faces(a, s);
@@ -129,19 +203,21 @@ cudaError_t enqueue_finalize(const lbm_handle *h, cudaStream_t s)
         a.w = static_cast<const float *>(h->w[h->parity]);
         a.pitch = h->pitch;
         a.st = h->st + h->parity;
+        a.cut_h = h->cut_h;
         a.cut_v = h->cut_v;
         a.p = h->cp;
         a.hist = h->hist;
-        return launch_finalize(a, s);
+        return h->line ? launch_line_finalize(a, s) : launch_finalize(a, s);
     }
     FinalizeArgs<double> a;
     a.w = static_cast<const double *>(h->w[h->parity]);
     a.pitch = h->pitch;
     a.st = h->st + h->parity;
+    a.cut_h = h->cut_h;
     a.cut_v = h->cut_v;
     a.p = h->cp;
     a.hist = h->hist;
-    return launch_finalize(a, s);
+    return h->line ? launch_line_finalize(a, s) : launch_finalize(a, s);
 }
 
 cudaError_t drain_profile(lbm_handle *h)
@@ -248,7 +324,7 @@ std::vector<Unit> partition_rows(int ny, int rows, int jc, int hh)
 lbm_status plan_bands(lbm_handle *h, int rows)
 {
     const int ny = h->grid.ny;
-    const bool crack = h->cp.mode != CRACK_NONE;
+    const bool crack = h->cp.mode != CRACK_NONE && !h->cp.line;   // a line crack's kernel has no crack band
     const int hh = !crack ? 0 : (h->cp.macro ? 3 : 1);
     std::vector<Unit> best;
     if (rows > 0) {
@@ -321,6 +397,76 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lb
     return create_impl(grid, lattice, material, crack, loads, n_loads, stream, allocator, false, out);
 }
 
+lbm_status lbm_create_line(const lbm_grid *grid, const lbm_lattice *lattice, const lbm_material *material,
+                           const lbm_crack_line *crack, const lbm_loading *loads, int32_t n_loads,
+                           void *stream, const lbm_allocator *allocator, lbm_handle **out)
+{
+    if (!out) return fail(LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!grid || !lattice || !material || !crack) return fail(LBM_ERR_ARG, "grid, lattice, material and crack are required");
+    const lbm_crack_line &c = *crack;
+    if (c.mode < LBM_CRACK_STATIONARY || c.mode > LBM_CRACK_KCRIT)
+        return fail(LBM_ERR_ARG, "a crack in any direction needs a stationary, prescribed or K-criterion mode");
+    if (lattice->velocity_set != LBM_D2Q5) return fail(LBM_ERR_ARG, "a crack in any direction is built for D2Q5");
+    if (lattice->bc_mode != LBM_BC_BOUNCEBACK)
+        return fail(LBM_ERR_ARG, "a crack in any direction is built with link-local faces (LBM_BC_BOUNCEBACK)");
+    if (lattice->storage != LBM_F64 && lattice->storage != LBM_F32)
+        return fail(LBM_ERR_ARG, "a crack in any direction needs LBM_F64 or LBM_F32 storage");
+    if (grid->nx < 1 || grid->ny < 2 || !(grid->dh > 0.0) || !std::isfinite(grid->dh))
+        return fail(LBM_ERR_ARG, "need nx >= 1, ny >= 2 and a positive, finite dh");
+    if (c.mode == LBM_CRACK_PRESCRIBED && !(c.v_rel >= 0.0 && c.v_rel < 1.0))
+        return fail(LBM_ERR_ARG, "prescribed v_rel must lie in [0, 1)");
+    if (c.mode == LBM_CRACK_KCRIT && !(c.K_C > 0.0 && c.v_max >= 0.0 && c.v_max < 1.0))
+        return fail(LBM_ERR_ARG, "K-criterion needs K_C > 0 and 0 <= v_max < 1");
+    const double rmin = c.r_min > 0.0 ? c.r_min : c.r0;
+    if (!(rmin > 0.5 * grid->dh))
+        return fail(LBM_ERR_ARG, "the K window must start more than dh / 2 behind the tip (r0 or r_min)");
+    const double pts[4] = {c.x_start / grid->dh, c.y_start / grid->dh, c.x_tip / grid->dh, c.y_tip / grid->dh};
+    const double lim[4] = {(double)grid->nx, (double)grid->ny, (double)grid->nx, (double)grid->ny};
+    for (int q = 0; q < 4; ++q)
+        if (!(pts[q] >= 0.0 && pts[q] <= lim[q])) return fail(LBM_ERR_ARG, "the crack's start and tip must lie in the body");
+    LineSpec L;
+    L.start_xq = llrint(c.x_start / grid->dh * 4294967296.0);
+    L.start_yq = llrint(c.y_start / grid->dh * 4294967296.0);
+    L.tip_xq = llrint(c.x_tip / grid->dh * 4294967296.0);
+    L.tip_yq = llrint(c.y_tip / grid->dh * 4294967296.0);
+    const int64_t X = (int64_t)grid->nx << kQBits, Y = (int64_t)grid->ny << kQBits;
+    if (L.start_xq < 0 || L.start_xq > X || L.tip_xq < 0 || L.tip_xq > X || L.start_yq < 0 || L.start_yq > Y ||
+        L.tip_yq < 0 || L.tip_yq > Y)
+        return fail(LBM_ERR_ARG, "the crack's start and tip must lie in the body");
+    if (L.start_xq == L.tip_xq && L.start_yq == L.tip_yq) return fail(LBM_ERR_ARG, "the crack's start and tip coincide");
+    // the unit direction, its products kept apart from the sum (no fused
+    // multiply-add), as every implementation of this reading forms it
+    volatile double dx = (double)(L.tip_xq - L.start_xq), dy = (double)(L.tip_yq - L.start_yq);
+    volatile double xx = dx * dx, yy = dy * dy;
+    const double len = std::sqrt(xx + yy);
+    L.dir_x = dx / len;
+    L.dir_y = dy / len;
+    if (line_hits_a_centre(L, grid->nx, grid->ny)) return fail(LBM_ERR_ARG, "the crack's line passes through a site centre");
+    // the rows its links can touch: from the start to where the line leaves
+    // the body, widened by three rows
+    const double sx = (double)L.start_xq * kTwoM32, sy = (double)L.start_yq * kTwoM32;
+    const double tx = L.dir_x > 0.0 ? ((double)grid->nx - sx) / L.dir_x : (L.dir_x < 0.0 ? -sx / L.dir_x : 1e300);
+    const double ty = L.dir_y > 0.0 ? ((double)grid->ny - sy) / L.dir_y : (L.dir_y < 0.0 ? -sy / L.dir_y : 1e300);
+    const double ey = sy + std::min(tx, ty) * L.dir_y;
+    L.row_lo = (int32_t)std::max(0.0, std::floor(std::min(sy, ey)) - 3.0);
+    L.row_hi = (int32_t)std::min((double)grid->ny - 1.0, std::floor(std::max(sy, ey)) + 3.0);
+    lbm_crack cr;
+    std::memset(&cr, 0, sizeof cr);
+    cr.mode = c.mode;
+    cr.two_tips = 0;
+    cr.x_start = c.x_start;
+    cr.x_tip = c.x_tip;
+    cr.v_rel = c.v_rel;
+    cr.K_C = c.K_C;
+    cr.v_max = c.v_max;
+    cr.r0 = c.r0;
+    cr.r_min = c.r_min;
+    cr.fit_width = c.fit_width;
+    cr.hist_cap = c.hist_cap;
+    return create_impl(grid, lattice, material, &cr, loads, n_loads, stream, allocator, false, out, &L);
+}
+
 }  // extern "C"
 
 namespace lbm {
@@ -328,7 +474,7 @@ namespace host {
 
 lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const lbm_material *material,
                        const lbm_crack *crack, const lbm_loading *loads, int32_t n_loads, void *stream,
-                       const lbm_allocator *allocator, bool slab, lbm_handle **out)
+                       const lbm_allocator *allocator, bool slab, lbm_handle **out, const LineSpec *line)
 {
     if (!out) return fail(LBM_ERR_ARG, "out is NULL");
     *out = nullptr;
@@ -380,7 +526,13 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
     int64_t start_q = 0, tip_q = 0;
     const int64_t qone = (int64_t)1 << kQBits;
     const int64_t clamp_q = (int64_t)grid->nx * qone;   // the far edge: the crack splits the body
-    if (cr.mode != LBM_CRACK_NONE) {
+    if (line) {
+        // a crack in any direction, validated by lbm_create_line
+        start_q = line->start_xq;
+        tip_q = line->tip_xq;
+        if (!(cr.fit_width > 0.0)) cr.fit_width = grid->dh;
+        if (cr.hist_cap <= 0) cr.hist_cap = kDefaultHistCap;
+    } else if (cr.mode != LBM_CRACK_NONE) {
         const double yj = cr.y / grid->dh;
         if (!std::isfinite(yj) || std::fabs(yj - std::nearbyint(yj)) > 1e-9)
             return fail(LBM_ERR_ARG, "the crack line y must be a multiple of dh (between two rows)");
@@ -499,7 +651,7 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
     const size_t o_ht = off; off = align256(off + (size_t)hcap * 8);
     const size_t o_hn = off; off = align256(off + (size_t)hcap * 4);
     if (cr.mode == LBM_CRACK_NONE) cr.two_tips = 0;
-    const int64_t hcap_l = cr.two_tips ? hcap : 1;   // records of the left end
+    const int64_t hcap_l = (cr.two_tips || line) ? hcap : 1;   // records of the left end (a line crack's tip y)
     const size_t o_hKl = off; off = align256(off + (size_t)hcap_l * 8);
     const size_t o_hvl = off; off = align256(off + (size_t)hcap_l * 8);
     const size_t o_htl = off; off = align256(off + (size_t)hcap_l * 8);
@@ -579,6 +731,15 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
     cp.v_rel = cr.v_rel;
     cp.start_q = start_q;
     cp.clamp_q = clamp_q;
+    h->line = line != nullptr;
+    if (line) {
+        cp.line = 1;
+        cp.dir_x = line->dir_x;
+        cp.dir_y = line->dir_y;
+        cp.row_lo = line->row_lo;
+        cp.row_hi = line->row_hi;
+        cp.clamp_yq = (int64_t)grid->ny * qone;
+    }
     cp.hist_cap = cr.mode != LBM_CRACK_NONE ? cr.hist_cap : 0;
 
     h->wd_scale = 1.0;
@@ -616,7 +777,21 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
     hs.r.decided = 1;
     hs.l.decided = 1;
     std::vector<uint32_t> row((size_t)h->words, 0u);
-    if (cr.mode != LBM_CRACK_NONE) {
+    if (line) {
+        // every H and V link the initial segment meets, in exact arithmetic;
+        // kept as [H mask | V mask] for lbm_reset
+        hs.r.tip_q = line->tip_xq;
+        hs.r.tip_yq = line->tip_yq;
+        hs.l.tip_q = line->start_xq;
+        hs.l.tip_yq = line->start_yq;
+        hs.r.v_prev = cr.mode == LBM_CRACK_PRESCRIBED ? cr.v_rel : 0.0;
+        hs.l.v_prev = hs.r.v_prev;
+        row = line_initial_masks(*line, grid->nx, grid->ny, h->words);
+        const size_t n = (size_t)grid->ny * h->words;
+        e = cudaMemcpyAsync(h->cut_h, row.data(), n * 4, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->cut_v, row.data() + n, n * 4, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "writing the initial crack"));
+    } else if (cr.mode != LBM_CRACK_NONE) {
         const int64_t half = qone / 2;
         int64_t first = -floor_div(-(start_q - half), qone);   // smallest i with x_i >= x_start
         int64_t last = floor_div(tip_q - half, qone);          // largest i with x_i <= x_tip
@@ -771,9 +946,14 @@ lbm_status lbm_reset(lbm_handle *h)
     LBM_CUDA(cudaMemsetAsync(h->wdbase, 0, h->plane_d_bytes, s));
     LBM_CUDA(cudaMemsetAsync(h->cut_h, 0, mask, s));
     LBM_CUDA(cudaMemsetAsync(h->cut_v, 0, mask, s));
-    if (h->cp.mode != CRACK_NONE)
+    if (h->line) {
+        const size_t n = (size_t)h->grid.ny * h->words;
+        LBM_CUDA(cudaMemcpyAsync(h->cut_h, h->init_cut->data(), n * 4, cudaMemcpyHostToDevice, s));
+        LBM_CUDA(cudaMemcpyAsync(h->cut_v, h->init_cut->data() + n, n * 4, cudaMemcpyHostToDevice, s));
+    } else if (h->cp.mode != CRACK_NONE) {
         LBM_CUDA(cudaMemcpyAsync(h->cut_v + (size_t)(h->jc - 1) * h->words, h->init_cut->data(),
                                  h->init_cut->size() * 4, cudaMemcpyHostToDevice, s));
+    }
     LBM_CUDA(cudaMemcpyAsync(h->st, &h->init_st, sizeof(CrackState), cudaMemcpyHostToDevice, s));
     LBM_CUDA(launch_wstar(h->st, h->load, h->grid.edge, h->grid.dt, s));
     LBM_CUDA(cudaStreamSynchronize(s));
@@ -847,10 +1027,21 @@ lbm_status crack_state_impl(lbm_handle *h, bool left, lbm_crack_state_t *now, do
     LBM_CUDA(cudaMemcpyAsync(&hs, h->st + h->parity, sizeof hs, cudaMemcpyDeviceToHost, h->stream));
     LBM_CUDA(cudaStreamSynchronize(h->stream));
     const TipState &E = left ? hs.l : hs.r;
+    int64_t n_cut = hs.i_last >= hs.i_first ? (int64_t)(hs.i_last - hs.i_first + 1) : 0;
+    if (h->line && now) {
+        // a crack in any direction: the severed links of both masks
+        const size_t n = (size_t)h->grid.ny * h->words;
+        std::vector<uint32_t> m(2 * n);
+        LBM_CUDA(cudaMemcpyAsync(m.data(), h->cut_h, n * 4, cudaMemcpyDeviceToHost, h->stream));
+        LBM_CUDA(cudaMemcpyAsync(m.data() + n, h->cut_v, n * 4, cudaMemcpyDeviceToHost, h->stream));
+        LBM_CUDA(cudaStreamSynchronize(h->stream));
+        n_cut = 0;
+        for (uint32_t x : m) n_cut += __builtin_popcount(x);
+    }
     if (now) {
         now->step = hs.step;
         now->tip_q = E.tip_q;
-        now->n_cut = hs.i_last >= hs.i_first ? (int64_t)(hs.i_last - hs.i_first + 1) : 0;
+        now->n_cut = n_cut;
         now->hist_n = hs.hist_n;
         now->tip_x = (double)E.tip_q * kTwoM32 * h->grid.dh;
         now->K = E.K;
@@ -903,6 +1094,32 @@ lbm_status lbm_crack_state_left(lbm_handle *h, lbm_crack_state_t *now, double *K
     return crack_state_impl(h, true, now, K_hist, v_hist, tip_hist, npairs_hist, cap, n_written);
 }
 
+lbm_status lbm_line_tip(lbm_handle *h, int64_t *x_q, int64_t *y_q, int64_t *y_hist, int64_t cap, int64_t *n_written)
+{
+    if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
+    if (!h->line) return fail(LBM_ERR_STATE, "the handle has no crack in any direction");
+    lbm_status rc = finalize(h);
+    if (rc != LBM_OK) return rc;
+    CrackState hs;
+    LBM_CUDA(cudaMemcpyAsync(&hs, h->st + h->parity, sizeof hs, cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA(cudaStreamSynchronize(h->stream));
+    if (x_q) *x_q = hs.r.tip_q;
+    if (y_q) *y_q = hs.r.tip_yq;
+    int64_t n = 0;
+    const int64_t hcap = h->cp.hist_cap;
+    if (y_hist && cap > 0 && hcap > 0) {
+        n = hs.hist_n < hcap ? hs.hist_n : hcap;
+        if (n > cap) n = cap;
+        const int64_t first = hs.hist_n - n;
+        std::vector<int64_t> ty((size_t)hcap);
+        LBM_CUDA(cudaMemcpyAsync(ty.data(), h->hist.tipl, (size_t)hcap * 8, cudaMemcpyDeviceToHost, h->stream));
+        LBM_CUDA(cudaStreamSynchronize(h->stream));
+        for (int64_t q = 0; q < n; ++q) y_hist[q] = ty[(size_t)((first + q) % hcap)];
+    }
+    if (n_written) *n_written = n;
+    return check_sticky(h);
+}
+
 lbm_status lbm_sync(lbm_handle *h)
 {
     if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
@@ -920,6 +1137,7 @@ lbm_status lbm_set_launch(lbm_handle *h, int32_t band_rows)
 {
     if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
     if (band_rows < 0 || band_rows > (1 << 20)) return fail(LBM_ERR_ARG, "band_rows out of range");
+    if (h->line) return fail(LBM_ERR_STATE, "the step of a crack in any direction has a fixed launch shape");
     LBM_CUDA(cudaStreamSynchronize(h->stream));
     drop_graph(h);
     return plan_bands(h, band_rows);
@@ -929,8 +1147,8 @@ lbm_status lbm_get_launch(const lbm_handle *h, int32_t *band_rows, int32_t *ctas
                           int32_t *ctas_per_sm)
 {
     if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
-    if (band_rows) *band_rows = h->band_rows;
-    if (ctas) *ctas = h->n_bands * h->ncb;
+    if (band_rows) *band_rows = h->line ? kLineRows : h->band_rows;
+    if (ctas) *ctas = h->line ? h->ncb * ((h->grid.ny + kLineRows - 1) / kLineRows) : h->n_bands * h->ncb;
     if (threads) *threads = kThreads;
     if (ctas_per_sm) *ctas_per_sm = h->bps;
     return LBM_OK;
@@ -1318,6 +1536,7 @@ lbm_status lbm_batch_create(lbm_handle *const *handles, int32_t n, int32_t band_
         if (h->sticky != LBM_OK) return fail(h->sticky, "a lattice is in an error state");
         if (h->lat.storage != handles[0]->lat.storage) return fail(LBM_ERR_ARG, "all lattices need the same storage");
         if (h->q != 5) return fail(LBM_ERR_ARG, "the batched step is built for D2Q5 only");
+        if (h->line) return fail(LBM_ERR_ARG, "the batched step is built for cracks along +x");
         if (h->stream != handles[0]->stream) return fail(LBM_ERR_ARG, "all lattices need the same stream");
         if (h->parity != handles[0]->parity) return fail(LBM_ERR_STATE, "all lattices need the same number of steps");
         for (int k = 0; k < i; ++k)

@@ -30,6 +30,7 @@ struct lbm_handle {
     int32_t jc;          // crack line y = jc dh
     bool edge_macro;     // the macroscopic rule on the outer edges (one more kernel per step)
     int32_t q;           // velocity set: 5 or 9 (D2Q9: its own update kernel and a crack kernel per step)
+    bool line;           // a straight crack in any direction (line_step_kernel)
     // step kernel shape
     int32_t ncb;         // column blocks of kThreads vectors
     int32_t n_bands, band_rows, crack_band, sms, bps;
@@ -82,9 +83,18 @@ const char *last_error();
 
 // lbm_create; with slab = true the bottom and top edges may also be
 // EDGE_HALO (inner edges of a row slab of a decomposed lattice).
+// A straight crack in any direction, as lbm_create_line validated it: its
+// start and initial tip on the 2^-32 dh grid, the unit direction, and the
+// rows its severed links can touch.
+struct LineSpec {
+    int64_t start_xq, start_yq, tip_xq, tip_yq;
+    double dir_x, dir_y;
+    int32_t row_lo, row_hi;
+};
+
 lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const lbm_material *material,
                        const lbm_crack *crack, const lbm_loading *loads, int32_t n_loads, void *stream,
-                       const lbm_allocator *allocator, bool slab, lbm_handle **out);
+                       const lbm_allocator *allocator, bool slab, lbm_handle **out, const LineSpec *line = nullptr);
 
 // Apply the pending crack step (if any) on the handle's stream.
 lbm_status finalize(lbm_handle *h);

@@ -12,8 +12,10 @@
 //     wrap-around values; pads next to Dirichlet edges are not read.  The plane pointers point at (j = 0, i = 0).
 //   * cut masks: one bit per link, ceil(nx / 32) 32-bit words per row;
 //     H bit (i, j) = link (i,j)-(i+1,j), V bit (i, j) = link (i,j)-(i,j+1).
-//     Severed links of the straight crack all lie in V row jc-1; the rows
-//     they touch form the crack band of the step kernel's partition.
+//     Severed links of the crack along +x all lie in V row jc-1; the rows
+//     they touch form the crack band of the step kernel's partition.  A
+//     crack in any direction (line_step_kernel) severs H and V links of the
+//     rows [row_lo, row_hi] of its parameters.
 //   * CrackState x 2: the crack and step state, double buffered.  The step
 //     kernel of step k reads buffer k & 1 and its one writer CTA writes buffer
 //     (k + 1) & 1, so no CTA ever reads a state that another CTA is writing.
@@ -33,6 +35,7 @@ constexpr double kTwoM32 = 2.3283064365386963e-10;  // 2^-32
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kThreads = 128;                       // threads per CTA of the step kernel
 constexpr int kMinBlocks = 8;                       // resident CTAs per SM the kernel is built for
+constexpr int kLineRows = 16;                       // rows of a CTA's band in line_step_kernel
 
 // EDGE_HALO: an inner edge of a row slab of a decomposed lattice; the pad
 // row beyond it holds the neighbouring slab's boundary row, copied there
@@ -59,6 +62,7 @@ struct LoadDesc {
 // every LBM step); the step kernel applies a pending one before its update.
 struct TipState {
     int64_t tip_q;         // tip x in units of 2^-32 dh
+    int64_t tip_yq;        // tip y (a crack in any direction; else unused)
     int32_t arrested, npairs;
     int32_t grew, decided;
     int32_t flags, pad;
@@ -84,9 +88,15 @@ struct CrackParams {
     int32_t two_tips, q;    // q: velocity set (5 or 9)
     double mu, cs, dt, dh, K_C, v_max, r0, r_min_fixed, fit_width, v_rel;
     int64_t start_q, clamp_q, hist_cap;
+    // a crack in any direction (line = 1): unit direction of growth, the
+    // body's height in grid units, and the rows its severed links can touch
+    int32_t line, row_lo, row_hi, pad_l;
+    double dir_x, dir_y;
+    int64_t clamp_yq;
 };
 
-// Per-step records of the right end and (two-tip cracks) the left end.
+// Per-step records of the right end and (two-tip cracks) the left end; a
+// crack in any direction records its tip's y in tipl.
 struct History {
     double *K, *v;
     int64_t *tip;
@@ -113,7 +123,7 @@ struct StepArgs {
     int32_t crack_band;        // band that holds the crack rows (-1: none)
     int32_t edge[4];
     T g, dt;
-    const uint32_t *cut_h;
+    uint32_t *cut_h;
     uint32_t *cut_v;
     int32_t words;
     const Unit *units;
@@ -130,6 +140,7 @@ struct FinalizeArgs {
     const T *w;
     int64_t pitch;
     CrackState *st;
+    uint32_t *cut_h;
     uint32_t *cut_v;
     CrackParams p;
     History hist;
@@ -216,6 +227,8 @@ cudaError_t launch_wd_to_f32(const D *wd, int64_t pitch, int nx, int ny, float s
 template <typename D>
 cudaError_t launch_wd_from_f32(D *wd, int64_t pitch, int nx, int ny, float scale, const float *src, cudaStream_t s);
 template <typename T> cudaError_t launch_finalize(const FinalizeArgs<T> &a, cudaStream_t s);
+template <typename T> cudaError_t launch_line_step(const StepArgs<T, T> &a, cudaStream_t s);
+template <typename T> cudaError_t launch_line_finalize(const FinalizeArgs<T> &a, cudaStream_t s);
 cudaError_t launch_exchange(const RowCopy *pairs, int n_pairs, int64_t row_bytes, cudaStream_t s);
 cudaError_t launch_wstar(CrackState *st, const LoadDesc *load, const int32_t *edge, double dt, cudaStream_t s);
 template <typename T> cudaError_t launch_fill_pads(T *w, int64_t pitch, int nx, int ny, const int32_t *edge, cudaStream_t s);

@@ -240,6 +240,7 @@ lbm_status lbm_tape_create(lbm_handle *h, const int32_t *sensors, int32_t n_sens
         return fail(LBM_ERR_ARG, "the adjoint needs LBM_F64 or LBM_F32 storage");
     if (h->edge_macro) return fail(LBM_ERR_ARG, "the adjoint has no macroscopic rule on the outer edges");
     if (h->q != 5) return fail(LBM_ERR_ARG, "the adjoint is built for D2Q5 only");
+    if (h->line) return fail(LBM_ERR_ARG, "the adjoint is built for cracks along +x");
     if (n_sens < 0 || (n_sens > 0 && !sensors)) return fail(LBM_ERR_ARG, "bad sensor array");
     if (n_steps < 1 || n_steps > ((int64_t)1 << 31)) return fail(LBM_ERR_ARG, "n_steps must lie in [1, 2^31]");
     if (checkpoint_every < 0) return fail(LBM_ERR_ARG, "checkpoint_every must be >= 0");

@@ -70,6 +70,28 @@ def lbm_create(grid: A.Grid, lattice: A.Lattice_, material: A.Material, crack: A
     return out.value
 
 
+def lbm_create_line(grid: A.Grid, lattice: A.Lattice_, material: A.Material, crack: A.CrackLine,
+                    loads, stream: int = 0, allocator: A.Allocator | None = None) -> int:
+    lib = load_library()
+    n = len(loads)
+    arr = (A.Loading * max(n, 1))(*loads) if n else None
+    out = C.c_void_p()
+    _check(lib.lbm_create_line(C.byref(grid), C.byref(lattice), C.byref(material), C.byref(crack),
+                               arr, n, C.c_void_p(stream), C.byref(allocator) if allocator is not None else None,
+                               C.byref(out)))
+    return out.value
+
+
+def lbm_line_tip(h: int, cap: int = 0):
+    """(x_q, y_q) of the tip of a crack in any direction and the y of its last
+    `cap` records."""
+    x, y, nw = C.c_int64(0), C.c_int64(0), C.c_int64(0)
+    ys = np.zeros(max(cap, 1), np.int64)
+    _check(load_library().lbm_line_tip(C.c_void_p(h), C.byref(x), C.byref(y), ys.ctypes.data_as(C.POINTER(C.c_int64)),
+                                       cap, C.byref(nw)))
+    return x.value, y.value, ys[:nw.value]
+
+
 def lbm_step(h: int, n: int):
     _check(load_library().lbm_step(C.c_void_p(h), int(n)))
 
@@ -216,12 +238,18 @@ def make_structs(problem: dict, storage: str = "f32"):
     lat.bc_mode = A.BC[problem.get("bc_mode", "bounceback")]
     mat = A.Material()
     mat.rho, mat.mu = float(problem.get("rho", 1.0)), float(problem["mu"])
-    cr = A.Crack()
     c = problem.get("crack") or {"mode": "none"}
+    line = "y_tip" in c                       # a straight crack in any direction (lbm_create_line)
+    cr = A.CrackLine() if line else A.Crack()
     cr.mode = A.CRACK[c.get("mode", "none")]
     if cr.mode:
-        cr.y = float(c["y"])
-        cr.x_start, cr.x_tip = float(c.get("x_start", 0.0)), float(c["x_tip"])
+        if line:
+            cr.x_start, cr.y_start = float(c["x_start"]), float(c["y_start"])
+            cr.x_tip, cr.y_tip = float(c["x_tip"]), float(c["y_tip"])
+        else:
+            cr.y = float(c["y"])
+            cr.x_start, cr.x_tip = float(c.get("x_start", 0.0)), float(c["x_tip"])
+            cr.two_tips = 1 if c.get("two_tips") else 0
         cr.v_rel = float(c.get("v_rel", 0.0))
         cr.K_C = float(c.get("K_C", 0.0))
         cr.v_max = float(c.get("v_max", 0.85))
@@ -229,7 +257,6 @@ def make_structs(problem: dict, storage: str = "f32"):
         cr.r_min = float(c.get("r_min", 0.0))
         cr.fit_width = float(c.get("fit_width", g.dh))
         cr.hist_cap = int(problem.get("hist_cap", 1 << 16))
-        cr.two_tips = 1 if c.get("two_tips") else 0
     loads = []
     keep = []
     for ld in problem.get("loads", []):
@@ -290,8 +317,12 @@ class Lattice:
         self.stream = int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
         g, lat, mat, cr, loads, keep = make_structs(problem, storage)
         self._alloc = TorchAllocator(self.stream) if torch_allocator else None
-        self.h = lbm_create(g, lat, mat, cr if cr.mode else None, loads, self.stream,
-                            self._alloc.struct if self._alloc else None)
+        self.line = isinstance(cr, A.CrackLine)
+        if self.line:
+            self.h = lbm_create_line(g, lat, mat, cr, loads, self.stream, self._alloc.struct if self._alloc else None)
+        else:
+            self.h = lbm_create(g, lat, mat, cr if cr.mode else None, loads, self.stream,
+                                self._alloc.struct if self._alloc else None)
         del keep
 
     @property
@@ -370,9 +401,19 @@ class Lattice:
         return (d, hist) if cap else d
 
     def history(self, cap: int | None = None) -> dict:
+        """Per-step K, v, tip (x; with "tip_yq" the y of a crack in any
+        direction) and pairs, oldest first."""
         if cap is None:
             cap = int(self.problem.get("hist_cap", 1 << 16))
-        return lbm_crack_state(self.h, cap)[1]
+        h = lbm_crack_state(self.h, cap)[1]
+        if getattr(self, "line", False):
+            h["tip_yq"] = lbm_line_tip(self.h, cap)[2]
+        return h
+
+    def tip_q(self):
+        """(x, y) of the tip of a crack in any direction, units of 2^-32 dh."""
+        x, y, _ = lbm_line_tip(self.h)
+        return x, y
 
     def crack_state_left(self):
         """State of the left end of a two-tip crack."""

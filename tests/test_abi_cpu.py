@@ -46,7 +46,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_struct_layout_matches_header(tmp_path):
     structs = {"lbm_grid": A.Grid, "lbm_lattice": A.Lattice_, "lbm_material": A.Material, "lbm_crack": A.Crack,
-               "lbm_loading": A.Loading, "lbm_allocator": A.Allocator, "lbm_crack_state_t": A.CrackStateT}
+               "lbm_crack_line": A.CrackLine, "lbm_loading": A.Loading, "lbm_allocator": A.Allocator, "lbm_crack_state_t": A.CrackStateT}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "lbm.h"', "int main(void){"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
@@ -112,6 +112,42 @@ def test_create_rejects_bad_arguments(lib, over, msg):
     g, lat, mat, cr, loads, keep = _structs(**over)
     with pytest.raises(lbm.LbmError) as ei:
         lbm.lbm_create(g, lat, mat, cr, loads, 0, None)
+    assert ei.value.status == A.LBM_ERR_ARG
+    assert msg in str(ei.value)
+
+
+def _line_structs(**over):
+    from paper_2206_12412_gb300 import workloads as W
+    p = W.with_line_crack(W.base_problem(40, 32, bc_mode="bounceback"), mode="prescribed", start=(6.3, 7.1),
+                          tip=(14.2, 11.9), v_rel=0.6, r0=2.0)
+    g, lat, mat, cr, loads, keep = lbm.make_structs(p, over.pop("storage", "f64"))
+    for k, v in over.items():
+        obj, field = k.split("__")
+        setattr({"g": g, "lat": lat, "mat": mat, "cr": cr}[obj], field, v)
+    return g, lat, mat, cr, loads, keep
+
+
+@pytest.mark.parametrize("over,msg", [
+    ({"cr__mode": 0}, "K-criterion mode"),
+    ({"cr__mode": 5}, "K-criterion mode"),
+    ({"lat__velocity_set": 1}, "D2Q5"),
+    ({"lat__bc_mode": 1}, "link-local"),
+    ({"storage": "f32_bf16"}, "storage"),
+    ({"cr__r0": 0.5}, "dh / 2"),
+    ({"cr__r0": 0.0, "cr__r_min": 0.4}, "dh / 2"),
+    ({"cr__x_start": -0.1}, "in the body"),
+    ({"cr__y_tip": 32.5}, "in the body"),
+    ({"cr__x_tip": 6.3, "cr__y_tip": 7.1}, "coincide"),
+    ({"cr__x_start": 5.5, "cr__y_start": 5.5, "cr__x_tip": 9.5, "cr__y_tip": 9.5}, "site centre"),
+    ({"cr__x_start": 5.5, "cr__y_start": 3.0, "cr__x_tip": 5.5, "cr__y_tip": 9.0}, "site centre"),
+    ({"cr__v_rel": 1.0}, "v_rel"),
+    ({"cr__mode": 3, "cr__K_C": 0.0}, "K_C"),
+    ({"g__dh": 0.0}, "dh"),
+])
+def test_create_line_rejects_bad_arguments(lib, over, msg):
+    g, lat, mat, cr, loads, keep = _line_structs(**over)
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_create_line(g, lat, mat, cr, loads, 0, None)
     assert ei.value.status == A.LBM_ERR_ARG
     assert msg in str(ei.value)
 

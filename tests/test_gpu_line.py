@@ -1,0 +1,225 @@
+"""A straight crack in any direction (lbm_create_line, Sec. 4.1) through the
+C ABI against the oracle: FP64 fields within 1e-12 and FP32 within 1e-5 of
+the state's scale, tips (x and y) and both cut masks bit-exact, K within
+1e-9 (FP64) / 0.5 % (FP32) of its largest value; angles in all four
+quadrants, lattices spanning several column blocks and row bands with
+ragged ends, every edge kind, prescribed and K-criterion growth, stops on
+each face of the body and at a corner, single launches and graph chunks,
+the deferred crack step read between chunks, reset and checkpoint resume,
+and the calls that reject the handle."""
+import numpy as np
+import pytest
+
+from paper_2206_12412_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+Q = 1 << 32
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_12412_gb300 import lbm
+    lbm.load_library()
+    return lbm
+
+
+def _problem(nx, ny, edges=("free", "free", "dirichlet", "dirichlet"), u0=3e-3, t_ramp=40.0):
+    p = W.base_problem(nx, ny, bc_mode="bounceback", edges=edges, cs=0.5)
+    names = ("left", "right", "bottom", "top")
+    sign = {"left": -1.0, "right": 1.0, "bottom": -1.0, "top": 1.0}
+    p["loads"] = [{"edge": names[e], "kind": "linear", "amp": sign[names[e]] * u0, "t": t_ramp}
+                  for e in range(4) if edges[e] == "dirichlet"]
+    return p
+
+
+def _run(oracle_mod, gpu, p, storage, chunks):
+    o = oracle_mod.Oracle(p)
+    g = gpu.Lattice(p, storage)
+    for n in chunks:
+        o.step(n)
+        g.step(n)
+    return o, g
+
+
+def _close(o, g, tol):
+    wo, wdo = o.fields()
+    wg, wdg = g.fields()
+    scale = max(np.abs(wo).max(), 1e-300)
+    assert np.abs(wg - wo).max() <= tol * scale, np.abs(wg - wo).max() / scale
+    assert np.abs(wdg - wdo).max() <= tol * scale, np.abs(wdg - wdo).max() / scale
+
+
+def _masks(o, g):
+    ch, cv = o.cuts()
+    np.testing.assert_array_equal(g.cut_mask("h"), ch.astype(bool))
+    np.testing.assert_array_equal(g.cut_mask("v"), cv.astype(bool))
+
+
+def _tips(o, g, n):
+    ho, hg = o.history(), g.history(cap=n)
+    np.testing.assert_array_equal(hg["tip_q"], ho["tip_q"][-len(hg["tip_q"]):])
+    np.testing.assert_array_equal(hg["tip_yq"], ho["tip_yq"][-len(hg["tip_yq"]):])
+    np.testing.assert_array_equal(hg["npairs"], ho["npairs"][-len(hg["npairs"]):])
+    return ho, hg
+
+
+ANGLES = [  # (start, tip) on a 300 x 90 lattice: ~17, ~122, ~200 and ~-40 degrees
+    ((20.3, 30.7), (120.9, 61.2)),
+    ((230.4, 8.3), (200.1, 56.8)),
+    ((285.6, 70.2), (170.7, 28.4)),
+    ((15.7, 80.9), (80.2, 26.6)),
+]
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("start,tip", ANGLES)
+def test_prescribed_growth_against_oracle(oracle_mod, gpu, storage, start, tip):
+    nx, ny = 300 if storage == "f64" else 700, 90
+    sx = 1.0 if storage == "f64" else 700.0 / 300.0
+    p = _problem(nx, ny)
+    p = W.with_line_crack(p, mode="prescribed", start=(start[0] * sx, start[1]), tip=(tip[0] * sx, tip[1]),
+                          v_rel=0.7, r0=2.0, fit_width=2.0)
+    o, g = _run(oracle_mod, gpu, p, storage, [7, 64, 29, 100])
+    _close(o, g, TOL[storage])
+    _masks(o, g)
+    ho, hg = _tips(o, g, 200)
+    assert (np.diff(ho["tip_q"]) != 0).sum() > 50
+    np.testing.assert_allclose(hg["K"], ho["K"], rtol=0, atol=(1e-9 if storage == "f64" else 5e-3) * np.abs(ho["K"]).max())
+    st = g.crack_state()
+    assert st["n_cut"] == int(o.cuts()[0].sum() + o.cuts()[1].sum())
+    assert g.tip_q() == (int(ho["tip_q"][-1]), int(ho["tip_yq"][-1]))
+
+
+@pytest.mark.parametrize("start,tip", ANGLES[:2])
+def test_kcrit_growth_fp64(oracle_mod, gpu, start, tip):
+    p = _problem(300, 90, u0=4e-3, t_ramp=60.0)
+    K_C = 0.4 * W.strip_reference_K(0.25, 4e-3, 90.0)
+    p = W.with_line_crack(p, mode="kcrit", start=start, tip=tip, K_C=K_C, v_max=0.85, r0=2.0)
+    o, g = _run(oracle_mod, gpu, p, "f64", [150, 150])
+    ho, hg = _tips(o, g, 300)
+    assert (ho["v"] > 0).sum() > 10
+    np.testing.assert_allclose(hg["K"], ho["K"], rtol=0, atol=1e-9 * np.abs(ho["K"]).max())
+    _masks(o, g)
+    _close(o, g, TOL["f64"])
+
+
+def test_kcrit_growth_fp32_tolerance(oracle_mod, gpu):
+    """FP32 fields with an FP64 K decision: the tip follows the oracle's within
+    one spacing and the growth count within a few steps."""
+    p = _problem(300, 90, u0=4e-3, t_ramp=60.0)
+    K_C = 0.4 * W.strip_reference_K(0.25, 4e-3, 90.0)
+    p = W.with_line_crack(p, mode="kcrit", start=ANGLES[0][0], tip=ANGLES[0][1], K_C=K_C, v_max=0.85, r0=2.0)
+    o, g = _run(oracle_mod, gpu, p, "f32", [300])
+    ho, hg = o.history(), g.history(cap=300)
+    assert (ho["v"] > 0).sum() > 10
+    assert np.abs(hg["tip_q"] - ho["tip_q"]).max() < Q and np.abs(hg["tip_yq"] - ho["tip_yq"]).max() < Q
+    assert abs(int((hg["v"] > 0).sum()) - int((ho["v"] > 0).sum())) <= 3
+
+
+@pytest.mark.parametrize("edges", [("dirichlet", "free", "dirichlet", "free"), ("periodic", "periodic", "free", "dirichlet"),
+                                   ("dirichlet", "dirichlet", "periodic", "periodic"), ("free",) * 4])
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_edge_kinds(oracle_mod, gpu, edges, storage):
+    p = _problem(261, 70, edges=edges)
+    if edges == ("free",) * 4:
+        p["loads"] = []
+        init = W.random_state(261, 70, seed=5, dtype=np.float64 if storage == "f64" else np.float32)
+    else:
+        init = None
+    p = W.with_line_crack(p, mode="prescribed", start=(40.2, 12.6), tip=(90.9, 40.3), v_rel=0.8, r0=1.5)
+    o = oracle_mod.Oracle(p)
+    g = gpu.Lattice(p, storage)
+    if init is not None:
+        o.set_fields(*init)
+        g.set_fields(*init)
+    for n in (5, 64, 61):
+        o.step(n)
+        g.step(n)
+    _close(o, g, TOL[storage])
+    _masks(o, g)
+    _tips(o, g, 130)
+
+
+@pytest.mark.parametrize("start,tip,face", [
+    ((4.3, 3.1), (9.6, 6.4), "right"),
+    ((20.2, 3.3), (17.1, 9.8), "top"),
+    ((23.2, 17.8), (17.5, 14.4), "left"),
+    ((6.3, 19.6), (9.9, 12.7), "bottom"),
+    ((17.75, 9.5), (22.25, 18.5), "corner"),
+])
+def test_tip_stops_on_the_boundary(oracle_mod, gpu, start, tip, face):
+    nx, ny = 24, 22
+    p = W.with_line_crack(_problem(nx, ny), mode="prescribed", start=start, tip=tip, v_rel=0.8, r0=1.5)
+    o, g = _run(oracle_mod, gpu, p, "f64", [100, 5])
+    ho, hg = _tips(o, g, 105)
+    assert g.crack_state()["flags"] & 1
+    x, y = g.tip_q()
+    assert {"right": x == nx * Q, "top": y == ny * Q, "left": x == 0, "bottom": y == 0,
+            "corner": (x, y) == (nx * Q, ny * Q)}[face]
+    _masks(o, g)
+    _close(o, g, TOL["f64"])
+
+
+def test_along_x_matches_the_aligned_crack(oracle_mod, gpu):
+    """A line crack along +x on the GPU against the oracle's aligned crack."""
+    p = _problem(300, 90)
+    pa = W.with_crack(p, mode="prescribed", y=45.0, x_start=10.0, x_tip=60.0, v_rel=0.7)
+    pl = W.with_line_crack(p, mode="prescribed", start=(10.0, 45.0), tip=(60.0, 45.0), v_rel=0.7)
+    o = oracle_mod.Oracle(pa)
+    g = gpu.Lattice(pl, "f64")
+    o.step(200)
+    g.step(200)
+    _close(o, g, TOL["f64"])
+    np.testing.assert_array_equal(g.history(cap=200)["tip_q"], o.history()["tip_q"])
+    _masks(o, g)
+
+
+def test_reset_and_checkpoint(oracle_mod, gpu, tmp_path):
+    p = W.with_line_crack(_problem(300, 90), mode="prescribed", start=ANGLES[1][0], tip=ANGLES[1][1], v_rel=0.6)
+    g = gpu.Lattice(p, "f64")
+    g.step(70)
+    path = str(tmp_path / "line.lbm")
+    g.save(path)
+    g.step(90)
+    w1, wd1 = g.fields()
+    m1 = (g.cut_mask("h"), g.cut_mask("v"))
+    t1 = g.tip_q()
+    g.load(path)
+    g.step(90)
+    w2, wd2 = g.fields()
+    np.testing.assert_array_equal(w1, w2)
+    np.testing.assert_array_equal(wd1, wd2)
+    assert g.tip_q() == t1
+    np.testing.assert_array_equal(m1[0], g.cut_mask("h"))
+    np.testing.assert_array_equal(m1[1], g.cut_mask("v"))
+    g.reset()
+    g.step(160)
+    np.testing.assert_array_equal(g.fields()[0], w1)
+    assert g.tip_q() == t1
+    o = oracle_mod.Oracle(p)
+    o.step(160)
+    _masks(o, g)
+
+
+def test_calls_that_reject_the_handle(gpu):
+    p = W.with_line_crack(_problem(64, 32), mode="prescribed", start=(3.3, 4.1), tip=(9.2, 7.7), v_rel=0.5)
+    g = gpu.Lattice(p, "f32")
+    with pytest.raises(gpu.LbmError) as ei:
+        g.crack_state_left()
+    assert ei.value.status == gpu.A.LBM_ERR_STATE
+    with pytest.raises(gpu.LbmError) as ei:
+        gpu.lbm_set_launch(g.h, 8)
+    assert ei.value.status == gpu.A.LBM_ERR_STATE
+    with pytest.raises(gpu.LbmError):
+        gpu.Batch([g])
+    launch = gpu.lbm_get_launch(g.h)
+    assert launch["band_rows"] == 16
+    q = gpu.Lattice(W.plain_fp64(), "f64")
+    with pytest.raises(gpu.LbmError) as ei:
+        gpu.lbm_line_tip(q.h)
+    assert ei.value.status == gpu.A.LBM_ERR_STATE
