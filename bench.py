@@ -394,6 +394,28 @@ def measure_extensions(lbm, W, torch, stream, problem, peak, flush_l2, steps=100
             "timing": "library CUDA events around each step's launch, L2 flushed before each step"}
     lat.close()
 
+    # a straight crack in another direction (Sec. 4.1): the same lattice and
+    # loads, a K-criterion edge crack at 20 degrees, link-local faces
+    import numpy as np
+    ql = W.kcrit_line()
+    lat = lbm.Lattice(ql, "f32", stream=stream)
+    lat.step(2500)
+    x0, y0 = lat.tip_q()
+    lat.set_profiling(True)
+    for _ in range(steps):
+        flush_l2()
+        lat.step(1)
+    lat.sync()
+    pr = lat.profile(reset=True)
+    k = pr["step_ms"] / max(pr["n_step"], 1) * 1e-3
+    x1, y1 = lat.tip_q()
+    line = {"workload": "kcrit_line 4096x2048, crack at 20 degrees, bounce-back faces, f32", "step_us": k * 1e6,
+            "glups": sites / k / 1e9, "bytes_per_site": 16, "achieved_gbs": 16 * sites / k / 1e9,
+            "frac": 16 * sites / k / 1e9 / peak, "launches_per_step": 1, "kernel": "line_step_kernel<float>",
+            "tip_advance_dh": float(np.hypot(x1 - x0, y1 - y0)) / 2**32,
+            "timing": "library CUDA events around each step's launch, L2 flushed before each step"}
+    lat.close()
+
     p = W.kcrit_centre_crack()
     n = W.KCRIT_CENTRE_STEPS
     lat = lbm.Lattice(p, "f32", stream=stream)
@@ -436,7 +458,7 @@ def measure_extensions(lbm, W, torch, stream, problem, peak, flush_l2, steps=100
     b.close()
     for l in lats:
         l.close()
-    return {"d2q9": d2q9, "centre_crack_sec52": centre, "centre_crack_sweep": sweep}
+    return {"d2q9": d2q9, "line_crack": line, "centre_crack_sec52": centre, "centre_crack_sweep": sweep}
 
 
 def measure_virtual_ranks(lbm, W, torch, stream, problem, steps=256):
@@ -484,6 +506,9 @@ def run_ours(args, rank, world, local):
     if args.profile_only and args.lattice == "D2Q9":
         # the D2Q9 form of the workload (bounce-back crack faces), for its profile
         problem = dict(problem, bc_mode="bounceback", lattice="D2Q9")
+    if args.profile_only and args.crack == "line":
+        # the workload with its crack at 20 degrees (line_step_kernel), for its profile
+        problem = W.kcrit_line()
     sites = problem["nx"] * problem["ny"]
     stream = torch.cuda.current_stream()
     lat = lbm.Lattice(problem, "f32", stream=stream)
@@ -662,6 +687,8 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=None, help="steps of the adjoint workload (default 8000)")
     ap.add_argument("--lattice", default="D2Q5", choices=["D2Q5", "D2Q9"],
                     help="with --profile-only: the velocity set of the profiled workload")
+    ap.add_argument("--crack", default="x", choices=["x", "line"],
+                    help="with --profile-only: the crack of the profiled workload (along +x, or at 20 degrees)")
     ap.add_argument("--profile-only", action="store_true",
                     help="only prelude, warm-up and timed steps (for ncu); prints kernel times")
     args = ap.parse_args()

@@ -739,6 +739,18 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
         cp.row_lo = line->row_lo;
         cp.row_hi = line->row_hi;
         cp.clamp_yq = (int64_t)grid->ny * qone;
+        cp.start_yq = line->start_yq;
+        // bands as short as keeps every CTA of the step resident at once
+        int bps_line = 0;
+        const void *lk = h->esize == 8 ? line_step_kernel_ptr<double>() : line_step_kernel_ptr<float>();
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_line, lk, kThreads, 0);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "querying the line step kernel"));
+        // blocks that update the crack's band: one per row (or column) of the
+        // lattice's shorter side, at least one
+        cp.crack_ctas = (int32_t)std::max(1, std::min(grid->nx, grid->ny) / 16);
+        const int64_t slots = (int64_t)h->sms * std::max(bps_line, 1) - 1 - cp.crack_ctas;
+        const int64_t nb = std::max<int64_t>(1, slots / h->ncb);
+        cp.band = (int32_t)std::max<int64_t>(1, (grid->ny + nb - 1) / nb);
     }
     cp.hist_cap = cr.mode != LBM_CRACK_NONE ? cr.hist_cap : 0;
 
@@ -1147,8 +1159,10 @@ lbm_status lbm_get_launch(const lbm_handle *h, int32_t *band_rows, int32_t *ctas
                           int32_t *ctas_per_sm)
 {
     if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
-    if (band_rows) *band_rows = h->line ? kLineRows : h->band_rows;
-    if (ctas) *ctas = h->line ? h->ncb * ((h->grid.ny + kLineRows - 1) / kLineRows) : h->n_bands * h->ncb;
+    if (band_rows) *band_rows = h->line ? h->cp.band : h->band_rows;
+    if (ctas)
+        *ctas = h->line ? 1 + h->cp.crack_ctas + h->ncb * ((h->grid.ny + h->cp.band - 1) / h->cp.band)
+                        : h->n_bands * h->ncb;
     if (threads) *threads = kThreads;
     if (ctas_per_sm) *ctas_per_sm = h->bps;
     return LBM_OK;

@@ -35,7 +35,6 @@ constexpr double kTwoM32 = 2.3283064365386963e-10;  // 2^-32
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kThreads = 128;                       // threads per CTA of the step kernel
 constexpr int kMinBlocks = 8;                       // resident CTAs per SM the kernel is built for
-constexpr int kLineRows = 16;                       // rows of a CTA's band in line_step_kernel
 
 // EDGE_HALO: an inner edge of a row slab of a decomposed lattice; the pad
 // row beyond it holds the neighbouring slab's boundary row, copied there
@@ -90,9 +89,10 @@ struct CrackParams {
     int64_t start_q, clamp_q, hist_cap;
     // a crack in any direction (line = 1): unit direction of growth, the
     // body's height in grid units, and the rows its severed links can touch
-    int32_t line, row_lo, row_hi, pad_l;
+    int32_t line, row_lo, row_hi, band;   // band: rows of a CTA of line_step_kernel
     double dir_x, dir_y;
-    int64_t clamp_yq;
+    int64_t clamp_yq, start_yq;
+    int32_t crack_ctas, pad_c;   // blocks of line_step_kernel that update the crack's band
 };
 
 // Per-step records of the right end and (two-tip cracks) the left end; a
@@ -228,6 +228,7 @@ template <typename D>
 cudaError_t launch_wd_from_f32(D *wd, int64_t pitch, int nx, int ny, float scale, const float *src, cudaStream_t s);
 template <typename T> cudaError_t launch_finalize(const FinalizeArgs<T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_line_step(const StepArgs<T, T> &a, cudaStream_t s);
+template <typename T> const void *line_step_kernel_ptr();
 template <typename T> cudaError_t launch_line_finalize(const FinalizeArgs<T> &a, cudaStream_t s);
 cudaError_t launch_exchange(const RowCopy *pairs, int n_pairs, int64_t row_bytes, cudaStream_t s);
 cudaError_t launch_wstar(CrackState *st, const LoadDesc *load, const int32_t *edge, double dt, cudaStream_t s);

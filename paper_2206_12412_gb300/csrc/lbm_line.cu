@@ -18,14 +18,14 @@
 //
 // The update is the D2Q5 moment form with bounce-back on every severed
 // link, marched up the rows like the step kernel (16 bytes per site update),
-// reading the cut words of the rows the crack can reach.  As in the step
-// kernel, the crack step that follows step k - 1 is applied at the start of
-// step k, here by every CTA with sites within two spacings of the tip (the
-// links an advance of less than one spacing severs have both ends there):
-// all reach the same decision and set the same bits -- the new links lie
-// less than half a spacing behind the old tip, while the K window starts
-// more than half a spacing behind it, so no CTA's K sees another's new cuts
-// -- and the CTA holding the tip's cell records it.
+// reading the cut words where the rows come near the crack's line.  As in
+// the step kernel, the crack step that follows step k - 1 is applied at the
+// start of step k, here by one CTA of its own (block 0, scheduled first): it
+// runs the crack step and then updates the sites within three spacings of
+// the tip's cell -- the links an advance of less than one spacing severs
+// have both ends within two spacings of the old tip -- while the marching
+// CTAs skip those sites, so none of them waits for the crack step and the
+// cut bits they read are not changed during the launch.
 #include "lbm_crack.cuh"
 #include "lbm_internal.cuh"
 #include "lbm_rows.cuh"
@@ -254,156 +254,420 @@ __device__ void line_step_warp(const CrackParams &p, const T *w, int64_t P, uint
     __syncwarp();
 }
 
-// One warp's march up rows [j0, j1): a thread owns one 16-byte vector of a
-// row, with rows j-1, j, j+1 of w in registers and the east / west
-// neighbours of the centre row from the adjacent lanes (lanes 0 and 31 load
-// the halo columns).  Free and periodic edges come in through the pads,
-// Dirichlet edges by anti-bounce-back; a severed link (of the rows the crack
-// can reach) streams back the site's own value.
+// The pad images of the new value v of site (i, j) (free edges: the site's
+// own value; periodic edges: the wrap-around value), as write_pads does for a
+// row vector.
 template <typename T>
-__device__ __forceinline__ T line_march(const StepArgs<T, T> &a, const EdgeValues<T> &E, int x0, int j0, int j1)
+__device__ __forceinline__ void site_pads(const StepArgs<T, T> &a, int i, int j, T v)
+{
+    const int nx = a.nx, ny = a.ny;
+    const int64_t P = a.pitch;
+    T *row = a.w_out + (int64_t)j * P;
+    if (i == 0) {
+        if (a.edge[LEFT] == EDGE_FREE) row[-1] = v;
+        else if (a.edge[LEFT] == EDGE_PERIODIC) row[nx] = v;
+    }
+    if (i == nx - 1) {
+        if (a.edge[RIGHT] == EDGE_FREE) row[nx] = v;
+        else if (a.edge[RIGHT] == EDGE_PERIODIC) row[-1] = v;
+    }
+    if (j == 0) {
+        if (a.edge[BOTTOM] == EDGE_FREE) row[i - P] = v;
+        else if (a.edge[BOTTOM] == EDGE_PERIODIC) a.w_out[(int64_t)ny * P + i] = v;
+    }
+    if (j == ny - 1) {
+        if (a.edge[TOP] == EDGE_FREE) row[i + P] = v;
+        else if (a.edge[TOP] == EDGE_PERIODIC) a.w_out[i - P] = v;
+    }
+}
+
+// The update of one site with its severed links (the update of the march,
+// site by site); returns whether the new w is finite.
+template <typename T>
+__device__ __forceinline__ bool site_update(const StepArgs<T, T> &a, const EdgeValues<T> &E, int i, int j)
+{
+    const int nx = a.nx, ny = a.ny, words = a.words;
+    const int64_t P = a.pitch;
+    const T *r0 = a.w_in + (int64_t)j * P;
+    // every load first, so that they are in flight together
+    const uint32_t *ch = a.cut_h + (int64_t)j * words, *cv = a.cut_v + (int64_t)j * words;
+    const uint32_t hr_w = __ldcg(ch + (i >> 5));
+    const uint32_t hl_w = i >= 1 ? __ldcg(ch + ((i - 1) >> 5)) : 0u;
+    const uint32_t vu_w = j + 1 < ny ? __ldcg(cv + (i >> 5)) : 0u;
+    const uint32_t vd_w = j >= 1 ? __ldcg(cv - words + (i >> 5)) : 0u;
+    const T w0 = r0[i];
+    T wl = r0[i - 1], wr = r0[i + 1], u = r0[i + P], d = r0[i - P];
+    const int64_t o = (int64_t)j * P + i;
+    const T wdo = a.wd[o];
+    if (j == ny - 1 && a.edge[TOP] == EDGE_DIRICHLET) u = E.two_ws[TOP] - w0;
+    else if ((vu_w >> (i & 31)) & 1u) u = w0;
+    if (j == 0 && a.edge[BOTTOM] == EDGE_DIRICHLET) d = E.two_ws[BOTTOM] - w0;
+    else if ((vd_w >> (i & 31)) & 1u) d = w0;
+    if (i == 0 && a.edge[LEFT] == EDGE_DIRICHLET) wl = E.two_ws[LEFT] - w0;
+    else if ((hl_w >> ((i - 1) & 31)) & 1u) wl = w0;
+    if (i == nx - 1 && a.edge[RIGHT] == EDGE_DIRICHLET) wr = E.two_ws[RIGHT] - w0;
+    else if ((hr_w >> (i & 31)) & 1u) wr = w0;
+    const T lap = ((u + d) + (wl + wr)) - (T)4 * w0;
+    const T wdn = wdo + a.g * lap;
+    const T wn = w0 + a.dt * wdn;
+    a.w_out[o] = wn;
+    a.wd[o] = wdn;
+    site_pads(a, i, j, wn);
+    return isfinite(wn);
+}
+
+// Which block updates a site.  The tip's box (the sites within three
+// spacings of the tip's cell: every link the pending crack step can sever
+// has both ends there) belongs to block 0.  Both ends of a severed link lie
+// within one spacing of the crack (the polyline of the tips keeps to the
+// line through the start along c within rounding) and at most one spacing
+// behind the start or ahead of the tip; the crack blocks take every group
+// (kGroup consecutive sites of a row, aligned; a march thread's vector lies
+// in one) that meets the band around that stretch of the line -- the points closer
+// than 1.5 spacings to the line, from 2 spacings behind the start to 2 ahead
+// of the tip, widened by half a spacing along the row -- or the tip's box;
+// the march takes every other group.  The groups of row j are those from
+// sa(j) to sb(j), computed by one formula in explicitly rounded arithmetic,
+// so that every block finds the same set.
+constexpr int kGroup = 32;
+struct Claims {
+    int i0, i1, j0, j1;            // the tip's box
+    int r0, r1;                    // rows whose segments can be claimed
+    float sx, sy, cx, cy, t_hi;    // start, direction, the tip's distance along c plus 2
+    float inv_cx, inv_cy;          // 1 / c (0 where |c| is below 1e-6: the row is all in or all out)
+};
+
+__device__ __forceinline__ Claims claims(const CrackParams &p, const CrackState *s)
+{
+    const int64_t ti = s->r.tip_q >> kQBits, tj = s->r.tip_yq >> kQBits;   // tips lie in [0, nx] x [0, ny]
+    Claims c;
+    c.i0 = (int)hi64(0, ti - 3);
+    c.i1 = (int)lo64(p.nx - 1, ti + 3);
+    c.j0 = (int)hi64(0, tj - 3);
+    c.j1 = (int)lo64(p.ny - 1, tj + 3);
+    const int64_t ya = lo64(p.start_yq, s->r.tip_yq) >> kQBits, yb = hi64(p.start_yq, s->r.tip_yq) >> kQBits;
+    c.r0 = (int)hi64(0, lo64(ya - 3, c.j0));
+    c.r1 = (int)lo64(p.ny - 1, hi64(yb + 3, c.j1));
+    c.sx = (float)((double)p.start_q * kTwoM32);
+    c.sy = (float)((double)p.start_yq * kTwoM32);
+    c.cx = (float)p.dir_x;
+    c.cy = (float)p.dir_y;
+    const float tx = (float)((double)s->r.tip_q * kTwoM32), ty = (float)((double)s->r.tip_yq * kTwoM32);
+    c.t_hi = __fadd_rn(__fadd_rn(__fmul_rn(__fsub_rn(tx, c.sx), c.cx), __fmul_rn(__fsub_rn(ty, c.sy), c.cy)), 2.0f);
+    c.inv_cx = fabsf(c.cx) < 1e-6f ? 0.0f : __frcp_rn(c.cx);
+    c.inv_cy = fabsf(c.cy) < 1e-6f ? 0.0f : __frcp_rn(c.cy);
+    return c;
+}
+
+__device__ __forceinline__ bool in_box(const Claims &c, int i, int j) { return i >= c.i0 && i <= c.i1 && j >= c.j0 && j <= c.j1; }
+
+// The warp segments of row j (width W sites) that meet the band: sa .. sb
+// (empty if sa > sb).
+__device__ __forceinline__ void band_segs(const Claims &c, int j, int W, int nx, int &sa, int &sb)
+{
+    sa = 1;
+    sb = 0;
+    if (j < c.r0 || j > c.r1) return;
+    const float y = __fsub_rn((float)j + 0.5f, c.sy);
+    // |d| < 1.5 with d(x) = -(x - s_x) c_y + y c_x
+    const float dy = __fmul_rn(y, c.cx);
+    float xa = -3.0e38f, xb = 3.0e38f;
+    if (c.inv_cy != 0.0f) {
+        const float u = __fmul_rn(__fsub_rn(dy, 1.5f), c.inv_cy), v = __fmul_rn(__fadd_rn(dy, 1.5f), c.inv_cy);
+        xa = __fadd_rn(c.sx, fminf(u, v));
+        xb = __fadd_rn(c.sx, fmaxf(u, v));
+    } else if (!(fabsf(dy) < 1.5f)) {
+        return;
+    }
+    // -2 < t < t_hi with t(x) = (x - s_x) c_x + y c_y
+    const float ty = __fmul_rn(y, c.cy);
+    if (c.inv_cx != 0.0f) {
+        const float u = __fmul_rn(__fsub_rn(-2.0f, ty), c.inv_cx), v = __fmul_rn(__fsub_rn(c.t_hi, ty), c.inv_cx);
+        xa = fmaxf(xa, __fadd_rn(c.sx, fminf(u, v)));
+        xb = fminf(xb, __fadd_rn(c.sx, fmaxf(u, v)));
+    } else if (!(ty > -2.0f && ty < c.t_hi)) {
+        return;
+    }
+    // the columns whose centres lie within half a spacing of (xa, xb)
+    const float fa = fmaxf(__fsub_rn(xa, 1.0f), 0.0f), fb = fminf(xb, (float)nx);
+    if (!(fa <= fb)) return;
+    const int ca = (int)fa, cb = min((int)fb, nx - 1);
+    sa = ca / W;
+    sb = cb / W;
+}
+
+__device__ __forceinline__ bool seg_claimed(const Claims &c, int s, int j, int W, int nx)
+{
+    if (j >= c.j0 && j <= c.j1 && s >= c.i0 / W && s <= c.i1 / W) return true;
+    int sa, sb;
+    band_segs(c, j, W, nx, sa, sb);
+    return s >= sa && s <= sb;
+}
+
+// Block 0: the pending crack step (warp 0; it records the step and writes
+// the next state), then the tip's box with the cuts in force after it.
+template <typename T>
+__device__ void tip_cta(const StepArgs<T, T> &a, CrackState &sS, const EdgeValues<T> &E, const Claims &C)
+{
+    const int tid = threadIdx.x;
+    const CrackParams &p = a.p;
+    if (tid < 32) {
+        if (tid == 0) sS = *a.s_in;
+        __syncwarp();
+        const bool pending = !sS.r.decided;   // not yet applied by a deferred crack step
+        line_step_warp<T>(p, a.w_in, a.pitch, a.cut_h, a.cut_v, a.hist, sS, true);
+        if (tid == 0) {
+            CrackState *o = a.s_out;
+            const int64_t n = sS.step + 1;
+            o->step = n;
+            o->hist_n = sS.hist_n + (pending ? 1 : 0);
+            o->i_first = sS.i_first;
+            o->i_last = sS.i_last;
+            o->r = sS.r;
+            o->r.decided = 0;
+            o->l = sS.l;
+            for (int e = 0; e < 4; ++e)
+                o->wstar[e] = a.edge[e] == EDGE_DIRICHLET ? load_value(a.load[e], n, (double)p.dt) : 0.0;
+        }
+    }
+    __syncthreads();   // the new cuts, for every thread of the CTA
+    const int ni = C.i1 - C.i0 + 1, nj = C.j1 - C.j0 + 1;
+    bool ok = true;
+    for (int t = tid; t < ni * nj; t += blockDim.x) ok &= site_update(a, E, C.i0 + t % ni, C.j0 + t / ni);
+    if (!ok) atomicOr(a.err, (uint32_t)ERR_NONFINITE);
+}
+
+// The crack blocks: every site outside the tip's box of every claimed
+// group.  The rows r0 .. r1, each cut into stretches of 16 groups, are taken
+// in turn by the blocks; a block finds the groups of its stretch that the
+// band or the box claims (one evaluation of the band per stretch) and its
+// warps take them in turn, a site per lane.  The cuts they read are not
+// changed during the launch (new ones all lie in the box).
+template <typename T>
+__device__ void crack_cta(const StepArgs<T, T> &a, const EdgeValues<T> &E, const Claims &C, int blk)
+{
+    constexpr int kStretch = 16;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    const int ngroup = (a.nx + kGroup - 1) / kGroup, nstretch = (ngroup + kStretch - 1) / kStretch;
+    const int items = (C.r1 - C.r0 + 1) * nstretch;
+    const int bg0 = C.i0 / kGroup, bg1 = C.i1 / kGroup;
+    bool ok = true;
+    for (int q = blk; q < items; q += a.p.crack_ctas) {
+        const int j = C.r0 + q / nstretch, g0 = (q % nstretch) * kStretch, g1 = min(g0 + kStretch, ngroup) - 1;
+        int sa, sb;
+        band_segs(C, j, kGroup, a.nx, sa, sb);
+        const bool boxrow = j >= C.j0 && j <= C.j1;
+        // the claimed groups of the stretch: the band's range, and the box's
+        // (the two ranges overlap or not; each group is taken once)
+        const int ba = max(sa, g0), bb = min(sb, g1);
+        const int xa = boxrow ? max(bg0, g0) : 1, xb = boxrow ? min(bg1, g1) : 0;
+        const int nb = ba <= bb ? bb - ba + 1 : 0;
+        const int nx_ = xa <= xb ? xb - xa + 1 : 0;
+        for (int t = warp; t < nb + nx_; t += nwarp) {
+            int g;
+            if (t < nb) {
+                g = ba + t;
+            } else {
+                g = xa + (t - nb);
+                if (g >= ba && g <= bb) continue;   // already taken as a band group
+            }
+            const int i = g * kGroup + lane;
+            if (i < a.nx && !in_box(C, i, j)) ok &= site_update(a, E, i, j);
+        }
+    }
+    if (!ok) atomicOr(a.err, (uint32_t)ERR_NONFINITE);
+}
+
+// The march of a warp whose part of the band holds no edge row or column and
+// no claimed site: the bare update.
+template <typename T>
+__device__ __forceinline__ T line_march_bare(const StepArgs<T, T> &a, int x0, int j0, int j1)
 {
     constexpr int N = Vec<T>::N;
     typedef Row<T, N> R;
     const unsigned kFull = 0xffffffffu;
-    const uint32_t kMask = (1u << N) - 1u;
     const int lane = threadIdx.x & 31;
-    const int nx = a.nx, ny = a.ny;
     const int64_t P = a.pitch;
-    const T *wb = a.w_in;
-    const int rlo = a.p.row_lo, rhi = a.p.row_hi;
-    const bool own = x0 < nx;
-    auto load = [&](int r, R &v, T &l, T &rt) {
-        const T *row = wb + (int64_t)r * P;
-        ldg_row(row + x0, v);
-        l = lane == 0 ? row[x0 - 1] : (T)0;
-        rt = lane == 31 ? row[x0 + N] : (T)0;
-    };
-    auto sides = [&](const R &v, T &l, T &rt) {
-        const T su = __shfl_up_sync(kFull, v.v[N - 1], 1), sd = __shfl_down_sync(kFull, v.v[0], 1);
-        if (lane != 0) l = su;
-        if (lane != 31) rt = sd;
-    };
-    const bool dir_l = a.edge[LEFT] == EDGE_DIRICHLET, dir_r = a.edge[RIGHT] == EDGE_DIRICHLET;
+    const T *win = a.w_in + x0;
+    T *wout = a.w_out + x0;
+    T *wdp = a.wd + x0;
     R dn, c, up, wdv;
-    T lc, rc, lu, ru, l_, r_;
-    load(j0 - 1, dn, l_, r_);
-    load(j0, c, lc, rc);
-    load(j0 + 1, up, lu, ru);
-    ld_row(a.wd + x0 + (int64_t)j0 * P, wdv);
-    sides(c, lc, rc);
-    sides(up, lu, ru);
+    ldg_row(win + (int64_t)(j0 - 1) * P, dn);
+    ldg_row(win + (int64_t)j0 * P, c);
+    ldg_row(win + (int64_t)(j0 + 1) * P, up);
+    ld_row(wdp + (int64_t)j0 * P, wdv);
+    T hl = (T)0, hr = (T)0;
+    if (lane == 0) hl = win[(int64_t)j0 * P - 1];
+    if (lane == 31) hr = win[(int64_t)j0 * P + N];
+    const T g = a.g, dt = a.dt;
     T acc = (T)0;
     for (int j = j0; j < j1; ++j) {
         R nxt, wdn;
-        T ln = (T)0, rn = (T)0;
+        T hln = (T)0, hrn = (T)0;
         const bool more = j + 1 < j1;
         if (more) {
-            load(j + 2, nxt, ln, rn);
-            ld_row(a.wd + x0 + (int64_t)(j + 1) * P, wdn);
+            ldg_row(win + (int64_t)(j + 2) * P, nxt);
+            ld_row(wdp + (int64_t)(j + 1) * P, wdn);
+            if (lane == 0) hln = win[(int64_t)(j + 1) * P - 1];
+            if (lane == 31) hrn = win[(int64_t)(j + 1) * P + N];
         }
-        // severed links of this row's sites: to the east (cr), west (cl),
-        // north (cu) and south (cd)
-        uint32_t cr = 0u, cl = 0u, cu = 0u, cd = 0u;
-        if (j >= rlo && j <= rhi) {
-            const int64_t wo = (int64_t)(x0 >> 5);
-            const int sh = x0 & 31;
-            if (own) {
-                cr = (__ldcg(a.cut_h + (int64_t)j * a.words + wo) >> sh) & kMask;
-                if (j + 1 < ny) cu = (__ldcg(a.cut_v + (int64_t)j * a.words + wo) >> sh) & kMask;
-                if (j >= 1) cd = (__ldcg(a.cut_v + (int64_t)(j - 1) * a.words + wo) >> sh) & kMask;
-            }
-            uint32_t lb = (__shfl_up_sync(kFull, cr, 1) >> (N - 1)) & 1u;
-            if (lane == 0)
-                lb = (x0 >= 1 && x0 - 1 < nx) ? (__ldcg(a.cut_h + (int64_t)j * a.words + ((x0 - 1) >> 5)) >> ((x0 - 1) & 31)) & 1u
-                                              : 0u;
-            cl = ((cr << 1) | lb) & kMask;
-        }
-        const bool dir_t = j == ny - 1 && a.edge[TOP] == EDGE_DIRICHLET;
-        const bool dir_b = j == 0 && a.edge[BOTTOM] == EDGE_DIRICHLET;
+        T lc = __shfl_up_sync(kFull, c.v[N - 1], 1), rc = __shfl_down_sync(kFull, c.v[0], 1);
+        if (lane == 0) lc = hl;
+        if (lane == 31) rc = hr;
         R wn, wdnew;
 #pragma unroll
         for (int k = 0; k < N; ++k) {
-            const T w0 = c.v[k];
-            T wl = k == 0 ? lc : c.v[k - 1], wr = k == N - 1 ? rc : c.v[k + 1];
-            T u = up.v[k], d = dn.v[k];
-            if (dir_t) u = E.two_ws[TOP] - w0;
-            else if ((cu >> k) & 1u) u = w0;
-            if (dir_b) d = E.two_ws[BOTTOM] - w0;
-            else if ((cd >> k) & 1u) d = w0;
-            if (dir_l && x0 + k == 0) wl = E.two_ws[LEFT] - w0;
-            else if ((cl >> k) & 1u) wl = w0;
-            if (dir_r && x0 + k == nx - 1) wr = E.two_ws[RIGHT] - w0;
-            else if ((cr >> k) & 1u) wr = w0;
-            const T lap = ((u + d) + (wl + wr)) - (T)4 * w0;
-            wdnew.v[k] = wdv.v[k] + a.g * lap;
-            wn.v[k] = w0 + a.dt * wdnew.v[k];
+            const T wl = k == 0 ? lc : c.v[k - 1], wr = k == N - 1 ? rc : c.v[k + 1];
+            const T lap = ((up.v[k] + dn.v[k]) + (wl + wr)) - (T)4 * c.v[k];
+            wdnew.v[k] = wdv.v[k] + g * lap;
+            wn.v[k] = c.v[k] + dt * wdnew.v[k];
         }
-        T ac = (T)0;
-        store_row(a, x0, j, wn, wdnew, ac);
-        if (own) acc += ac;
-        write_pads(a, x0, j, wn);
+        stg_row(wout + (int64_t)j * P, wn);
+        stg_row(wdp + (int64_t)j * P, wdnew);
+        acc += wn.v[0];
         dn = c;
         c = up;
-        lc = lu;
-        rc = ru;
         if (more) {
-            sides(nxt, ln, rn);
             up = nxt;
-            lu = ln;
-            ru = rn;
             wdv = wdn;
+            hl = hln;
+            hr = hrn;
         }
     }
     return acc;
 }
 
-// The grid is (column blocks of kThreads vectors) x (bands of kLineRows rows).
-template <typename T>
-__global__ void __launch_bounds__(kThreads) line_step_kernel(const StepArgs<T, T> a)
+// The march of the other warps: with EDGE, Dirichlet edges by
+// anti-bounce-back and free and periodic edges through the pads (as the step
+// kernel's edge warps); with CHECK, no store in a row whose segment another
+// block claims.  No cut word is read: every site next to a severed link lies
+// in a claimed segment.
+template <typename T, bool EDGE, bool CHECK>
+__device__ __forceinline__ T line_march_edge(const StepArgs<T, T> &a, const EdgeValues<T> &E, const Claims &C, int x0,
+                                             int xw0, int j0, int j1)
 {
     constexpr int N = Vec<T>::N;
-    constexpr int cols = kThreads * N;
-    __shared__ CrackState sS;
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int cb = blockIdx.x;
-    const int x0 = (cb * kThreads + tid) * N;
-    const int xw0 = (cb * kThreads + (tid & ~31)) * N;
-    const int j0 = blockIdx.y * kLineRows, j1 = min(j0 + kLineRows, a.ny);
-    const CrackParams &p = a.p;
-    const CrackState *s_in = a.s_in;
-    // the tip's cell, and the CTAs with sites within reach of the pending
-    // crack step (a margin of one spacing beyond the two it needs)
-    const int ti = (int)lo64((int64_t)p.nx - 1, s_in->r.tip_q >> kQBits);
-    const int tj = (int)lo64((int64_t)p.ny - 1, s_in->r.tip_yq >> kQBits);
-    const int c0 = cb * cols, c1 = c0 + cols - 1;
-    const bool runner = c0 <= ti + 3 && c1 >= ti - 3 && j0 <= tj + 3 && j1 - 1 >= tj - 3;
-    if (runner) {
-        const bool commit = c0 <= ti && ti <= c1 && j0 <= tj && tj < j1;
-        if (tid < 32) {
-            if (tid == 0) sS = *s_in;
-            __syncwarp();
-            const bool pending = !sS.r.decided;   // not yet applied by a deferred crack step
-            line_step_warp<T>(p, a.w_in, a.pitch, a.cut_h, a.cut_v, a.hist, sS, commit);
-            if (tid == 0 && commit) {
-                CrackState *o = a.s_out;
-                const int64_t n = sS.step + 1;
-                o->step = n;
-                o->hist_n = sS.hist_n + (pending ? 1 : 0);
-                o->i_first = sS.i_first;
-                o->i_last = sS.i_last;
-                o->r = sS.r;
-                o->r.decided = 0;
-                o->l = sS.l;
-                for (int e = 0; e < 4; ++e)
-                    o->wstar[e] = a.edge[e] == EDGE_DIRICHLET ? load_value(a.load[e], n, (double)p.dt) : 0.0;
+    typedef Row<T, N> R;
+    const unsigned kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int nx = a.nx;
+    const int64_t P = a.pitch;
+    const T *wb = a.w_in;
+    const int grp = x0 / kGroup;
+    R dn, c, up, wdv;
+    ldg_row(wb + (int64_t)(j0 - 1) * P + x0, dn);
+    ldg_row(wb + (int64_t)j0 * P + x0, c);
+    ldg_row(wb + (int64_t)(j0 + 1) * P + x0, up);
+    ld_row(a.wd + x0 + (int64_t)j0 * P, wdv);
+    T hl = (T)0, hr = (T)0;
+    if (lane == 0) hl = wb[(int64_t)j0 * P + x0 - 1];
+    if (lane == 31) hr = wb[(int64_t)j0 * P + x0 + N];
+    T acc = (T)0;
+    for (int j = j0; j < j1; ++j) {
+        R nxt, wdn;
+        T hln = (T)0, hrn = (T)0;
+        const bool more = j + 1 < j1;
+        if (more) {
+            ldg_row(wb + (int64_t)(j + 2) * P + x0, nxt);
+            ld_row(a.wd + x0 + (int64_t)(j + 1) * P, wdn);
+            if (lane == 0) hln = wb[(int64_t)(j + 1) * P + x0 - 1];
+            if (lane == 31) hrn = wb[(int64_t)(j + 1) * P + x0 + N];
+        }
+        T lc = __shfl_up_sync(kFull, c.v[N - 1], 1), rc = __shfl_down_sync(kFull, c.v[0], 1);
+        if (lane == 0) lc = hl;
+        if (lane == 31) rc = hr;
+        if (!CHECK || !seg_claimed(C, grp, j, kGroup, nx)) {
+            R wn, wdnew;
+            if (EDGE) {
+                row_update(a, E, x0, j, c, up, dn, wdv, lc, rc, 0u, 0u, wn, wdnew);
+                if (x0 < nx) {
+                    T ac = (T)0;
+                    store_row(a, x0, j, wn, wdnew, ac);
+                    acc += ac;
+                    write_pads(a, x0, j, wn);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < N; ++k) {
+                    const T wl = k == 0 ? lc : c.v[k - 1], wr = k == N - 1 ? rc : c.v[k + 1];
+                    const T lap = ((up.v[k] + dn.v[k]) + (wl + wr)) - (T)4 * c.v[k];
+                    wdnew.v[k] = wdv.v[k] + a.g * lap;
+                    wn.v[k] = c.v[k] + a.dt * wdnew.v[k];
+                }
+                stg_row(a.w_out + x0 + (int64_t)j * P, wn);
+                stg_row(a.wd + x0 + (int64_t)j * P, wdnew);
+                acc += wn.v[0];
             }
         }
-        __syncthreads();   // this CTA's new cuts, for all of its threads
+        dn = c;
+        c = up;
+        if (more) {
+            up = nxt;
+            wdv = wdn;
+            hl = hln;
+            hr = hrn;
+        }
     }
-    const EdgeValues<T> E = edge_values<T>(s_in);
-    // warps wholly right of the lattice have nothing to load or store
-    const T acc = xw0 < a.nx ? line_march<T>(a, E, x0, j0, j1) : (T)0;
+    return acc;
+}
+
+// A 1-D grid: block 0 handles the tip (tip_cta), block 1 + cb + ncb * band
+// marches column block cb of band `band` (p.band rows; bands as short as
+// keeps every block resident at once), and the last p.crack_ctas blocks
+// update the claimed groups (crack_cta); the march is dispatched first.
+template <typename T>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBlocks - 2)
+    line_step_kernel(const StepArgs<T, T> a)
+{
+    constexpr int N = Vec<T>::N;
+    __shared__ CrackState sS;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const EdgeValues<T> E = edge_values<T>(a.s_in);
+    const Claims C = claims(a.p, a.s_in);
+    if (blockIdx.x == 0) {
+        tip_cta<T>(a, sS, E, C);
+        return;
+    }
+    const int n_march = a.ncb * ((a.ny + a.p.band - 1) / a.p.band);
+    if ((int)blockIdx.x > n_march) {
+        crack_cta<T>(a, E, C, (int)blockIdx.x - 1 - n_march);
+        return;
+    }
+    const int u = (int)blockIdx.x - 1;
+    const int cb = u % a.ncb, band = u / a.ncb;
+    const int x0 = (cb * kThreads + tid) * N;
+    const int xw0 = (cb * kThreads + (tid & ~31)) * N;
+    const int j0 = band * a.p.band, j1 = min(j0 + a.p.band, a.ny);
+    const int nx = a.nx, ny = a.ny;
+    if (xw0 >= nx) return;   // warps wholly right of the lattice have nothing to load or store
+    // can the warp's part of the band hold an edge row or column, or a
+    // claimed segment: the tip's box, or the band (the rectangle of the
+    // warp's sites against the strip |d| < 1.5, -2 < t < t_hi, with margins
+    // beyond the half-spacing widening; d and t are linear, so their
+    // extremes over the rectangle lie at its corners)?
+    constexpr int W = 32 * N;
+    const bool edge = xw0 == 0 || xw0 + W - 1 >= nx - 1 || j0 == 0 || j1 == ny;
+    bool check = j0 <= C.j1 && j1 - 1 >= C.j0 && xw0 + W - 1 >= (C.i0 / kGroup) * kGroup &&
+                 xw0 <= (C.i1 / kGroup) * kGroup + kGroup - 1;
+    if (!check && j1 - 1 >= C.r0 && j0 <= C.r1) {
+        const float xa = (float)xw0 + 0.5f - C.sx, xb = (float)(xw0 + W) - 0.5f - C.sx;
+        const float ya = (float)j0 + 0.5f - C.sy, yb = (float)(j1 - 1) + 0.5f - C.sy;
+        float dlo = 3.0e38f, dhi = -3.0e38f, tlo = 3.0e38f, thi = -3.0e38f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float x = (q & 1) ? xb : xa, y = (q & 2) ? yb : ya;
+            const float d = -x * C.cy + y * C.cx, t = x * C.cx + y * C.cy;
+            dlo = fminf(dlo, d);
+            dhi = fmaxf(dhi, d);
+            tlo = fminf(tlo, t);
+            thi = fmaxf(thi, t);
+        }
+        check = !(dlo > 3.0f || dhi < -3.0f || thi < -4.0f || tlo > C.t_hi + 2.0f);
+    }
+    T acc;
+    if (edge) acc = check ? line_march_edge<T, true, true>(a, E, C, x0, xw0, j0, j1)
+                          : line_march_edge<T, true, false>(a, E, C, x0, xw0, j0, j1);
+    else acc = check ? line_march_edge<T, false, true>(a, E, C, x0, xw0, j0, j1) : line_march_bare<T>(a, x0, j0, j1);
     // a non-finite w (or wdot, which enters w) turns the sum of the first
     // element of each vector non-finite within a step or two
     if (__any_sync(0xffffffffu, !isfinite(acc)) && lane == 0) atomicOr(a.err, (uint32_t)ERR_NONFINITE);
@@ -429,8 +693,8 @@ __global__ void line_finalize_kernel(const FinalizeArgs<T> a)
 template <typename T>
 cudaError_t launch_line_step(const StepArgs<T, T> &a, cudaStream_t s)
 {
-    const dim3 grid((unsigned)a.ncb, (unsigned)((a.ny + kLineRows - 1) / kLineRows));
-    line_step_kernel<T><<<grid, kThreads, 0, s>>>(a);
+    const unsigned bands = (unsigned)((a.ny + a.p.band - 1) / a.p.band);
+    line_step_kernel<T><<<1u + (unsigned)a.p.crack_ctas + (unsigned)a.ncb * bands, kThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -441,6 +705,10 @@ cudaError_t launch_line_finalize(const FinalizeArgs<T> &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <typename T> const void *line_step_kernel_ptr() { return reinterpret_cast<const void *>(&line_step_kernel<T>); }
+
+template const void *line_step_kernel_ptr<double>();
+template const void *line_step_kernel_ptr<float>();
 template cudaError_t launch_line_step<double>(const StepArgs<double, double> &, cudaStream_t);
 template cudaError_t launch_line_step<float>(const StepArgs<float, float> &, cudaStream_t);
 template cudaError_t launch_line_finalize<double>(const FinalizeArgs<double> &, cudaStream_t);

@@ -94,6 +94,23 @@ def kcrit_single(scale: int = 1, seed: int = 2, bc_mode: str = "macroscopic") ->
 KCRIT_SINGLE_STEPS = 50000
 
 
+def kcrit_line(scale: int = 1, seed: int = 2, degrees: float = 20.0) -> dict:
+    """kcrit_single with the crack in another direction (Sec. 4.1): an edge
+    crack from (0, ny/2 - 0.3) of length 512 / scale at `degrees` to +x,
+    link-local faces, the same loads and K-criterion; K_C is 0.35 K_ref
+    (1 + 0.1 U(-1, 1)), so that the inclined crack, loaded partly across its
+    faces, starts growing around mid-ramp too."""
+    nx, ny = 4096 // scale, 2048 // scale
+    rng = np.random.default_rng(seed)
+    K_C = 0.35 * strip_reference_K(0.25, 2e-3, float(ny)) * (1.0 + 0.1 * rng.uniform(-1.0, 1.0))
+    th = math.radians(degrees)
+    start = (0.0, ny / 2 - 0.3)
+    tip = (start[0] + 512.0 / scale * math.cos(th), start[1] + 512.0 / scale * math.sin(th))
+    p = base_problem(nx, ny, bc_mode="bounceback")
+    p = with_line_crack(p, mode="kcrit", start=start, tip=tip, K_C=K_C, v_max=0.85, r0=2.0)
+    return with_antisymmetric_ramp(p, 2e-3, 5000.0 / scale)
+
+
 def kcrit_centre_crack(scale: int = 1, bc_mode: str = "macroscopic_edges") -> dict:
     """The K-criterion example of Sec. 5.2 with L = 64 / scale dh: an 8L x 3L
     body (512 x 192 sites at scale 1), a centre crack of length L on the line

@@ -206,6 +206,32 @@ def test_reset_and_checkpoint(oracle_mod, gpu, tmp_path):
     _masks(o, g)
 
 
+@pytest.mark.parametrize("mode", ["kcrit", "prescribed"])
+def test_full_size_in_the_benchmark_shape(oracle_mod, gpu, mode):
+    """4096 x 2048 FP32, the benchmark's crack at 20 degrees (and the same
+    crack growing at a prescribed speed), in the launch shape the benchmark
+    times: every output after 12 steps from a seeded state."""
+    p = W.kcrit_line()
+    if mode == "prescribed":
+        p["crack"] = dict(p["crack"], mode="prescribed", v_rel=0.8)
+    init = W.random_state(p["nx"], p["ny"], seed=23, dtype=np.float32)
+    o = oracle_mod.Oracle(p)
+    g = gpu.Lattice(p, "f32")
+    o.set_fields(*init)
+    g.set_fields(*init)
+    o.step(12)
+    g.step(12)
+    _close(o, g, TOL["f32"])
+    _masks(o, g)
+    ho, hg = o.history(), g.history(cap=12)
+    np.testing.assert_array_equal(hg["npairs"], ho["npairs"])
+    np.testing.assert_allclose(hg["K"], ho["K"], rtol=0, atol=5e-3 * np.abs(ho["K"]).max())
+    if mode == "prescribed":
+        np.testing.assert_array_equal(hg["tip_q"], ho["tip_q"])
+        np.testing.assert_array_equal(hg["tip_yq"], ho["tip_yq"])
+        assert (np.diff(ho["tip_q"]) != 0).all()
+
+
 def test_calls_that_reject_the_handle(gpu):
     p = W.with_line_crack(_problem(64, 32), mode="prescribed", start=(3.3, 4.1), tip=(9.2, 7.7), v_rel=0.5)
     g = gpu.Lattice(p, "f32")
@@ -218,7 +244,7 @@ def test_calls_that_reject_the_handle(gpu):
     with pytest.raises(gpu.LbmError):
         gpu.Batch([g])
     launch = gpu.lbm_get_launch(g.h)
-    assert launch["band_rows"] == 16
+    assert launch["ctas"] == 1 + max(1, 32 // 16) + -(-64 // 512) * -(-32 // launch["band_rows"])
     q = gpu.Lattice(W.plain_fp64(), "f64")
     with pytest.raises(gpu.LbmError) as ei:
         gpu.lbm_line_tip(q.h)
