@@ -249,3 +249,28 @@ def test_calls_that_reject_the_handle(gpu):
     with pytest.raises(gpu.LbmError) as ei:
         gpu.lbm_line_tip(q.h)
     assert ei.value.status == gpu.A.LBM_ERR_STATE
+
+
+# directions where the band's description changes form: along the axes (one
+# component of c is 0), near them, and at 45 degrees (the switch between the
+# per-column and per-row descriptions)
+AXES = [
+    ((30.0, 61.3), (90.0, 61.3)),        # +x on a half row (the line crack's own code path)
+    ((250.0, 40.6), (200.0, 40.6)),      # -x
+    ((120.3, 10.0), (120.3, 60.0)),      # +y
+    ((150.6, 190.0), (150.6, 140.0)),    # -y
+    ((40.0, 20.3), (100.0, 80.3)),       # 45 degrees
+    ((260.0, 30.7), (200.0, 90.7)),      # 135 degrees
+    ((20.0, 100.2), (120.0, 100.72)),    # 0.3 degrees
+    ((170.2, 15.0), (170.72, 115.0)),    # 89.7 degrees
+]
+
+
+@pytest.mark.parametrize("start,tip", AXES)
+def test_directions_near_the_axes(oracle_mod, gpu, start, tip):
+    p = W.with_line_crack(_problem(300, 200), mode="prescribed", start=start, tip=tip, v_rel=0.7, r0=2.0)
+    o, g = _run(oracle_mod, gpu, p, "f32", [64, 86])
+    _close(o, g, TOL["f32"])
+    _masks(o, g)
+    ho, hg = _tips(o, g, 150)
+    assert (np.diff(ho["tip_q"]) != 0).sum() + (np.diff(ho["tip_yq"]) != 0).sum() > 50
