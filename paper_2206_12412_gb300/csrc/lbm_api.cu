@@ -745,10 +745,8 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
         const void *lk = h->esize == 8 ? line_step_kernel_ptr<double>() : line_step_kernel_ptr<float>();
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_line, lk, kThreads, 0);
         if (e != cudaSuccess) return bail(cuda_fail(e, "querying the line step kernel"));
-        // blocks that update the crack's band: one per row (or column) of the
-        // lattice's shorter side, at least one
-        cp.crack_ctas = (int32_t)std::max(1, std::min(grid->nx, grid->ny) / 16);
-        const int64_t slots = (int64_t)h->sms * std::max(bps_line, 1) - 1 - cp.crack_ctas;
+        // every slot but the tip block's goes to the march
+        const int64_t slots = (int64_t)h->sms * std::max(bps_line, 1) - 1;
         const int64_t nb = std::max<int64_t>(1, slots / h->ncb);
         cp.band = (int32_t)std::max<int64_t>(1, (grid->ny + nb - 1) / nb);
     }
@@ -1161,7 +1159,7 @@ lbm_status lbm_get_launch(const lbm_handle *h, int32_t *band_rows, int32_t *ctas
     if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
     if (band_rows) *band_rows = h->line ? h->cp.band : h->band_rows;
     if (ctas)
-        *ctas = h->line ? 1 + h->cp.crack_ctas + h->ncb * ((h->grid.ny + h->cp.band - 1) / h->cp.band)
+        *ctas = h->line ? 1 + h->ncb * ((h->grid.ny + h->cp.band - 1) / h->cp.band)
                         : h->n_bands * h->ncb;
     if (threads) *threads = kThreads;
     if (ctas_per_sm) *ctas_per_sm = h->bps;

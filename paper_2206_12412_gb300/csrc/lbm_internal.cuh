@@ -92,7 +92,6 @@ struct CrackParams {
     int32_t line, row_lo, row_hi, band;   // band: rows of a CTA of line_step_kernel
     double dir_x, dir_y;
     int64_t clamp_yq, start_yq;
-    int32_t crack_ctas, pad_c;   // blocks of line_step_kernel that update the crack's band
 };
 
 // Per-step records of the right end and (two-tip cracks) the left end; a

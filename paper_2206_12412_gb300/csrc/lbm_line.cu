@@ -437,14 +437,15 @@ __device__ void tip_cta(const StepArgs<T, T> &a, CrackState &sS, const EdgeValue
     if (!ok) atomicOr(a.err, (uint32_t)ERR_NONFINITE);
 }
 
-// The crack blocks: every site outside the tip's box of every claimed
+// The claimed groups: every site outside the tip's box of every claimed
 // group.  The rows r0 .. r1, each cut into stretches of 16 groups, are taken
-// in turn by the blocks; a block finds the groups of its stretch that the
-// band or the box claims (one evaluation of the band per stretch) and its
-// warps take them in turn, a site per lane.  The cuts they read are not
-// changed during the launch (new ones all lie in the box).
+// in turn by the `nblk` march blocks after their march; a block finds the
+// groups of its stretch that the band or the box claims (one evaluation of
+// the band per stretch) and its warps take them in turn, a site per lane.
+// The cuts they read are not changed during the launch (new ones all lie in
+// the box), and no march block writes a claimed site.
 template <typename T>
-__device__ void crack_cta(const StepArgs<T, T> &a, const EdgeValues<T> &E, const Claims &C, int blk)
+__device__ void claimed_groups(const StepArgs<T, T> &a, const EdgeValues<T> &E, const Claims &C, int blk, int nblk)
 {
     constexpr int kStretch = 16;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
@@ -452,7 +453,7 @@ __device__ void crack_cta(const StepArgs<T, T> &a, const EdgeValues<T> &E, const
     const int items = (C.r1 - C.r0 + 1) * nstretch;
     const int bg0 = C.i0 / kGroup, bg1 = C.i1 / kGroup;
     bool ok = true;
-    for (int q = blk; q < items; q += a.p.crack_ctas) {
+    for (int q = blk; q < items; q += nblk) {
         const int j = C.r0 + q / nstretch, g0 = (q % nstretch) * kStretch, g1 = min(g0 + kStretch, ngroup) - 1;
         int sa, sb;
         band_segs(C, j, kGroup, a.nx, sa, sb);
@@ -613,8 +614,8 @@ __device__ __forceinline__ T line_march_edge(const StepArgs<T, T> &a, const Edge
 
 // A 1-D grid: block 0 handles the tip (tip_cta), block 1 + cb + ncb * band
 // marches column block cb of band `band` (p.band rows; bands as short as
-// keeps every block resident at once), and the last p.crack_ctas blocks
-// update the claimed groups (crack_cta); the march is dispatched first.
+// keeps every block resident at once) and then takes its share of the
+// claimed groups.
 template <typename T>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBlocks - 2)
     line_step_kernel(const StepArgs<T, T> a)
@@ -629,17 +630,17 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
         return;
     }
     const int n_march = a.ncb * ((a.ny + a.p.band - 1) / a.p.band);
-    if ((int)blockIdx.x > n_march) {
-        crack_cta<T>(a, E, C, (int)blockIdx.x - 1 - n_march);
-        return;
-    }
     const int u = (int)blockIdx.x - 1;
     const int cb = u % a.ncb, band = u / a.ncb;
     const int x0 = (cb * kThreads + tid) * N;
     const int xw0 = (cb * kThreads + (tid & ~31)) * N;
     const int j0 = band * a.p.band, j1 = min(j0 + a.p.band, a.ny);
     const int nx = a.nx, ny = a.ny;
-    if (xw0 >= nx) return;   // warps wholly right of the lattice have nothing to load or store
+    // warps wholly right of the lattice have nothing to load or store
+    if (xw0 >= nx) {
+        claimed_groups<T>(a, E, C, u, n_march);
+        return;
+    }
     // can the warp's part of the band hold an edge row or column, or a
     // claimed segment: the tip's box, or the band (the rectangle of the
     // warp's sites against the strip |d| < 1.5, -2 < t < t_hi, with margins
@@ -671,6 +672,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
     // a non-finite w (or wdot, which enters w) turns the sum of the first
     // element of each vector non-finite within a step or two
     if (__any_sync(0xffffffffu, !isfinite(acc)) && lane == 0) atomicOr(a.err, (uint32_t)ERR_NONFINITE);
+    claimed_groups<T>(a, E, C, u, n_march);
 }
 
 // The pending crack step before the host reads the state (one warp).
@@ -694,7 +696,7 @@ template <typename T>
 cudaError_t launch_line_step(const StepArgs<T, T> &a, cudaStream_t s)
 {
     const unsigned bands = (unsigned)((a.ny + a.p.band - 1) / a.p.band);
-    line_step_kernel<T><<<1u + (unsigned)a.p.crack_ctas + (unsigned)a.ncb * bands, kThreads, 0, s>>>(a);
+    line_step_kernel<T><<<1u + (unsigned)a.ncb * bands, kThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

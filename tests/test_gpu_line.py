@@ -244,7 +244,7 @@ def test_calls_that_reject_the_handle(gpu):
     with pytest.raises(gpu.LbmError):
         gpu.Batch([g])
     launch = gpu.lbm_get_launch(g.h)
-    assert launch["ctas"] == 1 + max(1, 32 // 16) + -(-64 // 512) * -(-32 // launch["band_rows"])
+    assert launch["ctas"] == 1 + -(-64 // 512) * -(-32 // launch["band_rows"])
     q = gpu.Lattice(W.plain_fp64(), "f64")
     with pytest.raises(gpu.LbmError) as ei:
         gpu.lbm_line_tip(q.h)
