@@ -17,15 +17,17 @@
 // reading.
 //
 // The update is the D2Q5 moment form with bounce-back on every severed
-// link, marched up the rows like the step kernel (16 bytes per site update),
-// reading the cut words where the rows come near the crack's line.  As in
-// the step kernel, the crack step that follows step k - 1 is applied at the
-// start of step k, here by one CTA of its own (block 0, scheduled first): it
-// runs the crack step and then updates the sites within three spacings of
-// the tip's cell -- the links an advance of less than one spacing severs
-// have both ends within two spacings of the old tip -- while the marching
-// CTAs skip those sites, so none of them waits for the crack step and the
-// cut bits they read are not changed during the launch.
+// link.  As in the step kernel, the crack step that follows step k - 1 is
+// applied at the start of step k, here by one CTA of its own (block 0,
+// scheduled first): it runs the crack step and then updates the sites within
+// three spacings of the tip's cell -- the links an advance of less than one
+// spacing severs have both ends within two spacings of the old tip.  The
+// other CTAs march up the rows like the step kernel (16 bytes per site
+// update) without reading cut words, skipping the 32-site groups that meet
+// the band around the crack and the tip's box; after its march each CTA
+// updates a share of those groups site by site with their severed links.
+// No CTA waits for the crack step, and the cut bits the CTAs read are not
+// changed during the launch.
 #include "lbm_crack.cuh"
 #include "lbm_internal.cuh"
 #include "lbm_rows.cuh"
@@ -321,18 +323,18 @@ __device__ __forceinline__ bool site_update(const StepArgs<T, T> &a, const EdgeV
 // has both ends there) belongs to block 0.  Both ends of a severed link lie
 // within one spacing of the crack (the polyline of the tips keeps to the
 // line through the start along c within rounding) and at most one spacing
-// behind the start or ahead of the tip; the crack blocks take every group
-// (kGroup consecutive sites of a row, aligned; a march thread's vector lies
-// in one) that meets the band around that stretch of the line -- the points closer
-// than 1.5 spacings to the line, from 2 spacings behind the start to 2 ahead
-// of the tip, widened by half a spacing along the row -- or the tip's box;
-// the march takes every other group.  The groups of row j are those from
-// sa(j) to sb(j), computed by one formula in explicitly rounded arithmetic,
-// so that every block finds the same set.
+// behind the start or ahead of the tip.  Every group (kGroup consecutive
+// sites of a row, aligned; a march thread's vector lies in one) that meets
+// the band around that stretch of the line -- the points closer than 1.5
+// spacings to the line, from 2 spacings behind the start to 2 ahead of the
+// tip, widened by half a spacing along the row -- or the tip's box is
+// claimed: the march leaves it, and claimed_groups updates it with its cuts.
+// The groups of row j are those from sa(j) to sb(j), computed by one formula
+// in explicitly rounded arithmetic, so that every block finds the same set.
 constexpr int kGroup = 32;
 struct Claims {
     int i0, i1, j0, j1;            // the tip's box
-    int r0, r1;                    // rows whose segments can be claimed
+    int r0, r1;                    // rows whose groups can be claimed
     float sx, sy, cx, cy, t_hi;    // start, direction, the tip's distance along c plus 2
     float inv_cx, inv_cy;          // 1 / c (0 where |c| is below 1e-6: the row is all in or all out)
 };
@@ -361,8 +363,8 @@ __device__ __forceinline__ Claims claims(const CrackParams &p, const CrackState 
 
 __device__ __forceinline__ bool in_box(const Claims &c, int i, int j) { return i >= c.i0 && i <= c.i1 && j >= c.j0 && j <= c.j1; }
 
-// The warp segments of row j (width W sites) that meet the band: sa .. sb
-// (empty if sa > sb).
+// The groups of row j (W sites wide) that meet the band: sa .. sb (empty if
+// sa > sb).
 __device__ __forceinline__ void band_segs(const Claims &c, int j, int W, int nx, int &sa, int &sb)
 {
     sa = 1;
@@ -540,9 +542,8 @@ __device__ __forceinline__ T line_march_bare(const StepArgs<T, T> &a, int x0, in
 
 // The march of the other warps: with EDGE, Dirichlet edges by
 // anti-bounce-back and free and periodic edges through the pads (as the step
-// kernel's edge warps); with CHECK, no store in a row whose segment another
-// block claims.  No cut word is read: every site next to a severed link lies
-// in a claimed segment.
+// kernel's edge warps); with CHECK, no store to a claimed group.  No cut
+// word is read: every site next to a severed link lies in a claimed group.
 template <typename T, bool EDGE, bool CHECK>
 __device__ __forceinline__ T line_march_edge(const StepArgs<T, T> &a, const EdgeValues<T> &E, const Claims &C, int x0,
                                              int xw0, int j0, int j1)
