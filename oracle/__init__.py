@@ -117,6 +117,10 @@ def _load():
         lib.orc_get_history_y.argtypes = [P, C.POINTER(C.c_int64), C.c_int64]
         lib.orc_get_history_y.restype = C.c_int64
         lib.orc_direction.argtypes = [P, d]
+        lib.orc_left_tip_y.argtypes = [P]
+        lib.orc_left_tip_y.restype = C.c_int64
+        lib.orc_get_history_left_y.argtypes = [P, C.POINTER(C.c_int64), C.c_int64]
+        lib.orc_get_history_left_y.restype = C.c_int64
         lib.orc_get_history_left.argtypes = [P, d, d, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                                              C.POINTER(C.c_int32), C.c_int64]
         lib.orc_get_history_left.restype = C.c_int64
@@ -301,7 +305,15 @@ class Oracle:
         n = self.lib.orc_get_history_left(self.h, _dptr(K), _dptr(v), tip.ctypes.data_as(C.POINTER(C.c_int64)),
                                           npairs.ctypes.data_as(C.POINTER(C.c_int32)),
                                           grew.ctypes.data_as(C.POINTER(C.c_int32)), cap)
-        return {"K": K[:n], "v": v[:n], "tip_q": tip[:n], "npairs": npairs[:n], "grew": grew[:n]}
+        out = {"K": K[:n], "v": v[:n], "tip_q": tip[:n], "npairs": npairs[:n], "grew": grew[:n]}
+        if self._cfg.line:
+            ty = np.zeros(cap, np.int64)
+            self.lib.orc_get_history_left_y(self.h, ty.ctypes.data_as(C.POINTER(C.c_int64)), cap)
+            out["tip_yq"] = ty[:n]
+        return out
+
+    def left_tip_y_q(self) -> int:
+        return int(self.lib.orc_left_tip_y(self.h))
 
     def left_tip_q(self) -> int:
         return int(self.lib.orc_left_tip(self.h))

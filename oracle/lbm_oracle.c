@@ -64,7 +64,9 @@
  *     polyline of the tips, every segment tested exactly; its pairs for K
  *     are the ends of the severed links, at r = (x_tip - m) . c from the
  *     link midpoint m, with delta = w(left of c) - w(right of c); the tip
- *     stops where it meets the body's boundary; the faces are link-local.
+ *     stops where it meets the body's boundary; the faces are link-local;
+ *     with two growing ends the start is the left end, growing along -c,
+ *     with r = (m - x_tip) . c and the same delta.
  */
 #include <math.h>
 #include <stdint.h>
@@ -136,12 +138,12 @@ typedef struct {
     int64_t start_q, tip_q, clamp_q;
     int64_t start_yq, tip_yq;   /* y of the crack's start and tip (y = jc dh for the crack along +x) */
     double dir_x, dir_y;        /* unit direction of growth */
-    int64_t *htipy;
+    int64_t *htipy, *htipyl;
     double v_prev, K_last;
     int32_t npairs_last, flags, arrested_for_good;
     int32_t *bprev, nbprev;
     /* the left tip (two_tips): position, speed memory, last K, arrest, B_prev */
-    int64_t ltip_q;
+    int64_t ltip_q, ltip_yq;
     double lv_prev, lK_last;
     int32_t lnpairs_last, larrested;
     int32_t *lbprev, nlbprev;
@@ -344,7 +346,7 @@ void orc_destroy(orc_state *s)
     free(s->bprev); free(s->bl); free(s->is_bpoint);
     free(s->hK); free(s->hv); free(s->htip); free(s->hnp); free(s->hgrow);
     free(s->ep);
-    free(s->lbprev); free(s->hKl); free(s->hvl); free(s->htipl); free(s->htipy); free(s->hnpl); free(s->hgrowl);
+    free(s->lbprev); free(s->hKl); free(s->hvl); free(s->htipl); free(s->htipy); free(s->htipyl); free(s->hnpl); free(s->hgrowl);
     free(s->queue); free(s->inq); free(s->visited);
     for (int e = 0; e < 4; ++e) free(s->series[e]);
     free(s);
@@ -423,13 +425,11 @@ orc_state *orc_create(const orc_config *cfg)
     if (cfg->nx < 1 || cfg->ny < 1 || !(cfg->dh > 0) || !(cfg->dt > 0)) return NULL;
     int Q = cfg->q == 0 ? 5 : cfg->q;
     if (Q != 5 && Q != 9) return NULL;
-    /* a crack in any direction is built for D2Q5 with link-local faces and
-     * one growing end; its K window must lie more than half a spacing behind
-     * the tip (the links a step severs have their midpoints at most that far
-     * behind the old tip) */
+    /* a crack in any direction is built for D2Q5 with link-local faces; its
+     * K window must lie more than half a spacing behind the tip (the links a
+     * step severs have their midpoints at most that far behind the old tip) */
     if (cfg->line) {
-        if (Q != 5 || cfg->bc_mode != ORC_BC_BOUNCEBACK || cfg->edge_macro || cfg->two_tips ||
-            cfg->crack_mode == ORC_CRACK_NONE)
+        if (Q != 5 || cfg->bc_mode != ORC_BC_BOUNCEBACK || cfg->edge_macro || cfg->crack_mode == ORC_CRACK_NONE)
             return NULL;
         double rmin = cfg->r_min_fixed > 0.0 ? cfg->r_min_fixed : cfg->r0;
         if (!(rmin > 0.5 * cfg->dh)) return NULL;
@@ -466,6 +466,7 @@ orc_state *orc_create(const orc_config *cfg)
     s->hvl = xcalloc((size_t)hc, sizeof(double));
     s->htipl = xcalloc((size_t)hc, sizeof(int64_t));
     s->htipy = xcalloc((size_t)hc, sizeof(int64_t));
+    s->htipyl = xcalloc((size_t)hc, sizeof(int64_t));
     s->hnpl = xcalloc((size_t)hc, sizeof(int32_t));
     s->hgrowl = xcalloc((size_t)hc, sizeof(int32_t));
     for (int e = 0; e < 4; ++e) {
@@ -489,6 +490,7 @@ orc_state *orc_create(const orc_config *cfg)
             return NULL;
         }
         s->ltip_q = s->start_q;
+        s->ltip_yq = s->start_yq;
         s->lv_prev = s->v_prev;
         initial_crack(s);
         /* both tips start their CheckLinks from the initial boundary points */
@@ -848,12 +850,13 @@ static double evaluate_K_dir(const orc_state *s, const double *w, int64_t tip_q,
  * crack that is not aligned with the lattice): the pairs of sites adjacent
  * to the crack are the two ends of each severed link; the pair's distance
  * from the tip along the crack is that of the link's midpoint m,
- * r = (x_tip - m) . c (c the unit direction of growth), and the opening is
- * delta = w(left of c) - w(right of c), so that a crack along +x has the
- * pairs, distances and opening of evaluate_K_dir.  The projection is formed
- * without fused multiply-adds, as in line_setup. */
+ * r = (x_tip - m) . c (c the unit direction of growth; r = (m - x_tip) . c
+ * at the left end of a two-tip crack, dir = -1), and the opening is
+ * delta = w(left of c) - w(right of c) at both ends, so that a crack along
+ * +x has the pairs, distances and opening of evaluate_K_dir.  The
+ * projection is formed without fused multiply-adds, as in line_setup. */
 static double evaluate_K_line(const orc_state *s, const double *w, int64_t tx, int64_t ty, double r_min, double wfit,
-                              int32_t *npairs)
+                              int dir, int32_t *npairs)
 {
     int nx = s->c.nx, ny = s->c.ny;
     double dh = s->c.dh;
@@ -876,8 +879,9 @@ static double evaluate_K_line(const orc_state *s, const double *w, int64_t tx, i
                     mx = site_cx_q(i);
                     my = (int64_t)(j + 1) << ORC_Q;
                 }
-                volatile double px = (double)(tx - mx) / (double)qone() * s->dir_x;
-                volatile double py = (double)(ty - my) / (double)qone() * s->dir_y;
+                /* behind the tip: along -c from the right end, along +c from the left end */
+                volatile double px = (double)(dir > 0 ? tx - mx : mx - tx) / (double)qone() * s->dir_x;
+                volatile double py = (double)(dir > 0 ? ty - my : my - ty) / (double)qone() * s->dir_y;
                 double r_h = px + py;
                 if (!(r_h >= lo && r_h < hi)) continue;
                 /* k1 is the site at +x (horizontal link) or +y (vertical
@@ -898,7 +902,7 @@ static double evaluate_K_line(const orc_state *s, const double *w, int64_t tx, i
 double orc_evaluate_K_line(const orc_state *s, const double *w, int64_t tx, int64_t ty, double r_min, double wfit,
                            int32_t *npairs)
 {
-    return evaluate_K_line(s, w, tx, ty, r_min, wfit, npairs);
+    return evaluate_K_line(s, w, tx, ty, r_min, wfit, +1, npairs);
 }
 
 static double evaluate_K(const orc_state *s, const double *w, int64_t tip_q, double r_min, double wfit, int32_t *npairs)
@@ -996,7 +1000,7 @@ static void tip_criterion(const orc_state *s, int dir, double v_prev, int64_t ti
 {
     const orc_config *c = &s->c;
     double r_min = c->r_min_fixed > 0.0 ? c->r_min_fixed : c->r0 / (1.0 - v_prev);  /* eq. r(v) */
-    *K = c->line ? evaluate_K_line(s, s->w, tip, s->tip_yq, r_min, c->fit_width, np)
+    *K = c->line ? evaluate_K_line(s, s->w, tip, dir > 0 ? s->tip_yq : s->ltip_yq, r_min, c->fit_width, dir, np)
                  : evaluate_K_dir(s, s->w, tip, r_min, c->fit_width, dir, np);
     *propagate = 0;
     *v = 0.0;
@@ -1054,18 +1058,30 @@ static int tip_advance(orc_state *s, int dir, double v)
     int32_t B[64];
     int nB;
     if (c->line) {
-        /* along the crack's direction: each component of Delta a c rounded
-         * to the grid (c = (1, 0) gives the advance below) */
+        /* along the crack's direction (+c for the right end, -c for the
+         * left one): each component of Delta a c rounded to the grid
+         * (c = (1, 0) gives the advance below) */
         double q = adot * c->dt / c->dh * (double)qone();
-        int64_t px = s->tip_q, py = s->tip_yq;
-        int64_t nxq = px + llrint(q * s->dir_x), nyq = py + llrint(q * s->dir_y);
-        if (line_clamp(s, px, py, &nxq, &nyq)) { s->arrested_for_good = 1; s->flags |= ORC_FLAG_CLAMPED; }
+        int64_t px = dir > 0 ? s->tip_q : s->ltip_q, py = dir > 0 ? s->tip_yq : s->ltip_yq;
+        int64_t ax = llrint(q * s->dir_x), ay = llrint(q * s->dir_y);
+        int64_t nxq = dir > 0 ? px + ax : px - ax, nyq = dir > 0 ? py + ay : py - ay;
+        if (line_clamp(s, px, py, &nxq, &nyq)) {
+            if (dir > 0) s->arrested_for_good = 1;
+            else s->larrested = 1;
+            s->flags |= ORC_FLAG_CLAMPED;
+        }
         if (nxq == px && nyq == py) return 0;
-        s->tip_q = nxq;
-        s->tip_yq = nyq;
+        if (dir > 0) { s->tip_q = nxq; s->tip_yq = nyq; }
+        else { s->ltip_q = nxq; s->ltip_yq = nyq; }
+        int32_t *keep = s->bprev, nkeep = s->nbprev;   /* CheckLinks from this end's B_prev */
+        if (dir < 0) { s->bprev = s->lbprev; s->nbprev = s->nlbprev; }
         nB = checklinks(s, px, py, nxq, nyq, B, 64);
+        if (dir < 0) { s->bprev = keep; s->nbprev = nkeep; }
         qsort(B, (size_t)nB, sizeof(int32_t), cmp_i32);
-        if (nB > 0) { memcpy(s->bprev, B, sizeof(int32_t) * (size_t)nB); s->nbprev = nB; }
+        if (nB > 0) {
+            if (dir > 0) { memcpy(s->bprev, B, sizeof(int32_t) * (size_t)nB); s->nbprev = nB; }
+            else { memcpy(s->lbprev, B, sizeof(int32_t) * (size_t)nB); s->nlbprev = nB; }
+        }
         return 1;
     }
     if (dir > 0) {
@@ -1125,6 +1141,7 @@ static void crack_growth(orc_state *s)
         s->hK[h] = K; s->hv[h] = v; s->htip[h] = s->tip_q; s->hnp[h] = np; s->hgrow[h] = grew;
         s->hKl[h] = Kl; s->hvl[h] = vl; s->htipl[h] = s->ltip_q; s->hnpl[h] = npl; s->hgrowl[h] = grewl;
         s->htipy[h] = s->tip_yq;
+        s->htipyl[h] = s->ltip_yq;
     }
     s->hist_n += 1;
 }
@@ -1190,6 +1207,14 @@ int64_t orc_get_history_y(const orc_state *s, int64_t *tip_yq, int64_t cap)
     int64_t n = s->hist_n < s->c.hist_cap ? s->hist_n : s->c.hist_cap;
     if (n > cap) n = cap;
     for (int64_t h = 0; h < n; ++h) tip_yq[h] = s->htipy[h];
+    return n;
+}
+int64_t orc_left_tip_y(const orc_state *s) { return s->ltip_yq; }
+int64_t orc_get_history_left_y(const orc_state *s, int64_t *tip_yq, int64_t cap)
+{
+    int64_t n = s->hist_n < s->c.hist_cap ? s->hist_n : s->c.hist_cap;
+    if (n > cap) n = cap;
+    for (int64_t h = 0; h < n; ++h) tip_yq[h] = s->htipyl[h];
     return n;
 }
 void orc_direction(const orc_state *s, double *dir2)

@@ -39,13 +39,14 @@ def with_crack(p: dict, *, mode: str, y: float, x_tip: float, x_start: float = 0
 
 
 def with_line_crack(p: dict, *, mode: str, start, tip, v_rel: float = 0.0, K_C: float = 0.0, v_max: float = 0.85,
-                    r0: float = 2.0, r_min: float = 0.0, fit_width: float = 1.0) -> dict:
+                    r0: float = 2.0, r_min: float = 0.0, fit_width: float = 1.0, two_tips: bool = False) -> dict:
     """A straight crack in any direction (Sec. 4.1): from start = (x, y)
-    through tip = (x, y), growing from the tip along that direction."""
+    through tip = (x, y), growing from the tip along that direction; with
+    two_tips the start grows too, the opposite way."""
     q = dict(p)
     q["crack"] = {"mode": mode, "x_start": float(start[0]), "y_start": float(start[1]), "x_tip": float(tip[0]),
                   "y_tip": float(tip[1]), "v_rel": float(v_rel), "K_C": float(K_C), "v_max": float(v_max),
-                  "r0": float(r0), "r_min": float(r_min), "fit_width": float(fit_width), "two_tips": False}
+                  "r0": float(r0), "r_min": float(r_min), "fit_width": float(fit_width), "two_tips": bool(two_tips)}
     return q
 
 

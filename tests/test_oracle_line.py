@@ -277,3 +277,70 @@ def test_rejected_configurations(oracle_mod, change):
                           tip=change.get("tip", (8.0, 7.3)), v_rel=0.5, r0=change.get("r0", 2.0))
     with pytest.raises(ValueError):
         oracle_mod.Oracle(p)
+
+
+# ------------------------------------------------------ both ends growing
+
+def test_two_ends_along_x_are_the_aligned_centre_crack(oracle_mod):
+    p = _strip(120, 40)
+    K_C = 0.5 * W.strip_reference_K(0.25, 2e-3, 40.0)
+    for mode in ("kcrit", "prescribed"):
+        q1 = W.with_crack(p, mode=mode, y=20.0, x_start=45.0, x_tip=75.0, K_C=K_C, v_rel=0.6, r0=2.0, two_tips=True)
+        q2 = W.with_line_crack(p, mode=mode, start=(45.0, 20.0), tip=(75.0, 20.0), K_C=K_C, v_rel=0.6, r0=2.0,
+                               two_tips=True)
+        o1, o2 = oracle_mod.Oracle(q1), oracle_mod.Oracle(q2)
+        o1.step(300)
+        o2.step(300)
+        for a, b in ((o1.history(), o2.history()), (o1.history_left(), o2.history_left())):
+            assert a["grew"].sum() > 20
+            np.testing.assert_array_equal(a["tip_q"], b["tip_q"])
+            np.testing.assert_array_equal(a["K"], b["K"])
+            assert (b["tip_yq"] == 20 * Q).all()
+        np.testing.assert_array_equal(o1.fields()[0], o2.fields()[0])
+        for a, b in zip(o1.cuts(), o2.cuts()):
+            np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("deg", [23.0, 61.0, 137.0])
+@pytest.mark.parametrize("mode", ["prescribed", "kcrit"])
+def test_centre_crack_at_an_angle_is_point_symmetric(oracle_mod, deg, mode):
+    """A centre crack through the middle of the body with antisymmetric loads:
+    turning the body by 180 degrees about its middle maps the problem onto
+    itself with w -> -w, so the two ends see the same K and move
+    symmetrically, the fields satisfy w(x) = -w(R x) and the cut masks map
+    onto themselves."""
+    nx, ny = 64, 48
+    th = math.radians(deg)
+    c, s = math.cos(th), math.sin(th)
+    mid = (nx / 2 + 0.013, ny / 2 + 0.007)          # no site centre on the line
+    half = 6.0
+    start = (mid[0] - half * c, mid[1] - half * s)
+    tip = (mid[0] + half * c, mid[1] + half * s)
+    # make the start the exact mirror of the tip on the grid
+    tq = (int(np.rint(tip[0] * Q)), int(np.rint(tip[1] * Q)))
+    start = ((nx * Q - tq[0]) / Q, (ny * Q - tq[1]) / Q)
+    p = _strip(nx, ny, u0=3e-3, t_ramp=30.0)
+    K_C = 0.3 * W.strip_reference_K(0.25, 3e-3, float(ny))
+    p = W.with_line_crack(p, mode=mode, start=start, tip=tip, v_rel=0.5, K_C=K_C, r0=1.5, two_tips=True)
+    o = oracle_mod.Oracle(p)
+    o.step(120)
+    hr, hl = o.history(), o.history_left()
+    assert hr["grew"].sum() > 5 and hl["grew"].sum() > 5
+    np.testing.assert_allclose(hl["K"], hr["K"], rtol=1e-11, atol=1e-15)
+    assert np.abs(hl["tip_q"] - (nx * Q - hr["tip_q"])).max() <= 1
+    assert np.abs(hl["tip_yq"] - (ny * Q - hr["tip_yq"])).max() <= 1
+    w = o.fields()[0]
+    np.testing.assert_allclose(w, -w[::-1, ::-1], rtol=0, atol=1e-12 * np.abs(w).max())
+    ch, cv = o.cuts()
+    np.testing.assert_array_equal(ch[:, :-1], ch[::-1, -2::-1])
+    np.testing.assert_array_equal(cv[:-1, :], cv[-2::-1, ::-1])
+    # every cut is a link that one of the two polylines meets, and back
+    h_r, h_l = o.history(), o.history_left()
+    s_q = (int(np.rint(start[0] * Q)), int(np.rint(start[1] * Q)))
+    right = [s_q, tq] + [(int(x), int(y)) for x, y in zip(h_r["tip_q"], h_r["tip_yq"])]
+    left = [tq, s_q] + [(int(x), int(y)) for x, y in zip(h_l["tip_q"], h_l["tip_yq"])]
+    dedup = lambda pts: [pt for k, pt in enumerate(pts) if k == 0 or pt != pts[k - 1]]
+    e1 = _expected_mask(nx, ny, dedup(right))
+    e2 = _expected_mask(nx, ny, dedup(left))
+    np.testing.assert_array_equal(ch, e1[0] | e2[0])
+    np.testing.assert_array_equal(cv, e1[1] | e2[1])
