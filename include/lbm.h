@@ -180,11 +180,13 @@ typedef struct lbm_crack {
  * r = (x_tip - m) . c in [r_min, r_min + W), with the opening
  * w(left of c) - w(right of c) of the link's two sites; the window must
  * start more than dh / 2 behind the tip (r0 > dh / 2, or r_min > dh / 2).
- * The other fields are those of lbm_crack (two_tips does not exist: one end
- * grows).  Built for D2Q5, LBM_BC_BOUNCEBACK, LBM_F64 or LBM_F32 storage. */
+ * two_tips: 1 lets the start grow too, along -c, with its own speed memory
+ * and the same opening sign (a centre crack in that direction); its K window
+ * lies along +c behind it.  The other fields are those of lbm_crack.  Built
+ * for D2Q5, LBM_BC_BOUNCEBACK, LBM_F64 or LBM_F32 storage. */
 typedef struct lbm_crack_line {
     int32_t mode;
-    int32_t pad;
+    int32_t two_tips;
     double x_start, y_start, x_tip, y_tip;
     double v_rel, K_C, v_max, r0, r_min, fit_width;
     int64_t hist_cap;
@@ -240,11 +242,12 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lb
 
 /* The same with a straight crack in any direction (lbm_crack_line; crack
  * must not be NULL and its mode not LBM_CRACK_NONE).  Every call below
- * applies to the handle, except lbm_crack_state_left, lbm_set_launch (the
- * step has a fixed launch shape), lbm_batch_create, the row slabs
- * (lbm_decomp.h) and the adjoint (lbm_adjoint.h), which return
- * LBM_ERR_ARG or LBM_ERR_STATE.  In lbm_crack_state, tip_q and tip_x are
- * the tip's x and n_cut counts the severed links; lbm_line_tip gives its y.
+ * applies to the handle, except lbm_set_launch (the step has a fixed
+ * launch shape), lbm_batch_create, the row slabs (lbm_decomp.h) and the
+ * adjoint (lbm_adjoint.h), which return LBM_ERR_ARG or LBM_ERR_STATE.  In
+ * lbm_crack_state (lbm_crack_state_left: the start of a two-tip crack),
+ * tip_q and tip_x are the end's x and n_cut counts the severed links;
+ * lbm_line_tip (lbm_line_tip_left) gives its y.
  * LBM_ERR_ARG for the cases listed at lbm_crack_line. */
 lbm_status lbm_create_line(const lbm_grid *grid, const lbm_lattice *lattice, const lbm_material *material,
                            const lbm_crack_line *crack, const lbm_loading *loads, int32_t n_loads,
@@ -257,6 +260,11 @@ lbm_status lbm_create_line(const lbm_grid *grid, const lbm_lattice *lattice, con
  * number of records.  LBM_ERR_STATE for a handle without such a crack.
  * Synchronises the stream. */
 lbm_status lbm_line_tip(lbm_handle *h, int64_t *x_q, int64_t *y_q, int64_t *y_hist, int64_t cap, int64_t *n_written);
+
+/* The same for the start of a two-tip crack in any direction (its growing
+ * left end); LBM_ERR_STATE if the crack has one growing end. */
+lbm_status lbm_line_tip_left(lbm_handle *h, int64_t *x_q, int64_t *y_q, int64_t *y_hist, int64_t cap,
+                             int64_t *n_written);
 
 /* Enqueue n >= 0 time steps (each: bulk update, crack-face rule, crack step)
  * on the handle's stream.  Asynchronous; errors of the device work surface at

@@ -44,7 +44,7 @@ class Crack(C.Structure):
 
 
 class CrackLine(C.Structure):
-    _fields_ = [("mode", C.c_int32), ("pad", C.c_int32),
+    _fields_ = [("mode", C.c_int32), ("two_tips", C.c_int32),
                 ("x_start", C.c_double), ("y_start", C.c_double), ("x_tip", C.c_double), ("y_tip", C.c_double),
                 ("v_rel", C.c_double), ("K_C", C.c_double), ("v_max", C.c_double),
                 ("r0", C.c_double), ("r_min", C.c_double), ("fit_width", C.c_double),
@@ -80,6 +80,8 @@ PROTOTYPES = {
                                   C.POINTER(C.c_void_p)]),
     "lbm_line_tip": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                C.c_int64, C.POINTER(C.c_int64)]),
+    "lbm_line_tip_left": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                    C.c_int64, C.POINTER(C.c_int64)]),
     "lbm_step": (C.c_int, [C.c_void_p, C.c_int64]),
     "lbm_fields": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int32]),
     "lbm_set_fields": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int32]),

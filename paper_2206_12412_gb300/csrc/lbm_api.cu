@@ -451,10 +451,11 @@ lbm_status lbm_create_line(const lbm_grid *grid, const lbm_lattice *lattice, con
     const double ey = sy + std::min(tx, ty) * L.dir_y;
     L.row_lo = (int32_t)std::max(0.0, std::floor(std::min(sy, ey)) - 3.0);
     L.row_hi = (int32_t)std::min((double)grid->ny - 1.0, std::floor(std::max(sy, ey)) + 3.0);
+    if (c.two_tips != 0 && c.two_tips != 1) return fail(LBM_ERR_ARG, "two_tips must be 0 or 1");
     lbm_crack cr;
     std::memset(&cr, 0, sizeof cr);
     cr.mode = c.mode;
-    cr.two_tips = 0;
+    cr.two_tips = c.two_tips;
     cr.x_start = c.x_start;
     cr.x_tip = c.x_tip;
     cr.v_rel = c.v_rel;
@@ -651,11 +652,14 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
     const size_t o_ht = off; off = align256(off + (size_t)hcap * 8);
     const size_t o_hn = off; off = align256(off + (size_t)hcap * 4);
     if (cr.mode == LBM_CRACK_NONE) cr.two_tips = 0;
-    const int64_t hcap_l = (cr.two_tips || line) ? hcap : 1;   // records of the left end (a line crack's tip y)
+    const int64_t hcap_l = cr.two_tips ? hcap : 1;   // records of the left end
     const size_t o_hKl = off; off = align256(off + (size_t)hcap_l * 8);
     const size_t o_hvl = off; off = align256(off + (size_t)hcap_l * 8);
     const size_t o_htl = off; off = align256(off + (size_t)hcap_l * 8);
     const size_t o_hnl = off; off = align256(off + (size_t)hcap_l * 4);
+    // the tips' y of a crack in any direction
+    const size_t o_hty = off; off = align256(off + (size_t)(line ? hcap : 1) * 8);
+    const size_t o_htyl = off; off = align256(off + (size_t)(line ? hcap_l : 1) * 8);
     size_t o_ser[4];
     for (int q = 0; q < 4; ++q) { o_ser[q] = off; off = align256(off + (size_t)h->load[q].n * 8); }
     h->block_bytes = off;
@@ -685,6 +689,8 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
     h->hist.vl = reinterpret_cast<double *>(base + o_hvl);
     h->hist.tipl = reinterpret_cast<int64_t *>(base + o_htl);
     h->hist.npl = reinterpret_cast<int32_t *>(base + o_hnl);
+    h->hist.tipy = reinterpret_cast<int64_t *>(base + o_hty);
+    h->hist.tipyl = reinterpret_cast<int64_t *>(base + o_htyl);
 
     cudaStream_t s = h->stream;
     auto bail = [&](lbm_status rc) {
@@ -1104,17 +1110,26 @@ lbm_status lbm_crack_state_left(lbm_handle *h, lbm_crack_state_t *now, double *K
     return crack_state_impl(h, true, now, K_hist, v_hist, tip_hist, npairs_hist, cap, n_written);
 }
 
-lbm_status lbm_line_tip(lbm_handle *h, int64_t *x_q, int64_t *y_q, int64_t *y_hist, int64_t cap, int64_t *n_written)
+}  // extern "C"
+
+namespace {
+
+// The tip (left: the start of a two-tip crack) of a crack in any direction
+// and the y of its last records.
+lbm_status line_tip_impl(lbm_handle *h, bool left, int64_t *x_q, int64_t *y_q, int64_t *y_hist, int64_t cap,
+                         int64_t *n_written)
 {
     if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
     if (!h->line) return fail(LBM_ERR_STATE, "the handle has no crack in any direction");
+    if (left && !h->cp.two_tips) return fail(LBM_ERR_STATE, "the crack has one growing end");
     lbm_status rc = finalize(h);
     if (rc != LBM_OK) return rc;
     CrackState hs;
     LBM_CUDA(cudaMemcpyAsync(&hs, h->st + h->parity, sizeof hs, cudaMemcpyDeviceToHost, h->stream));
     LBM_CUDA(cudaStreamSynchronize(h->stream));
-    if (x_q) *x_q = hs.r.tip_q;
-    if (y_q) *y_q = hs.r.tip_yq;
+    const TipState &E = left ? hs.l : hs.r;
+    if (x_q) *x_q = E.tip_q;
+    if (y_q) *y_q = E.tip_yq;
     int64_t n = 0;
     const int64_t hcap = h->cp.hist_cap;
     if (y_hist && cap > 0 && hcap > 0) {
@@ -1122,12 +1137,28 @@ lbm_status lbm_line_tip(lbm_handle *h, int64_t *x_q, int64_t *y_q, int64_t *y_hi
         if (n > cap) n = cap;
         const int64_t first = hs.hist_n - n;
         std::vector<int64_t> ty((size_t)hcap);
-        LBM_CUDA(cudaMemcpyAsync(ty.data(), h->hist.tipl, (size_t)hcap * 8, cudaMemcpyDeviceToHost, h->stream));
+        LBM_CUDA(cudaMemcpyAsync(ty.data(), left ? h->hist.tipyl : h->hist.tipy, (size_t)hcap * 8,
+                                 cudaMemcpyDeviceToHost, h->stream));
         LBM_CUDA(cudaStreamSynchronize(h->stream));
         for (int64_t q = 0; q < n; ++q) y_hist[q] = ty[(size_t)((first + q) % hcap)];
     }
     if (n_written) *n_written = n;
     return check_sticky(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_line_tip(lbm_handle *h, int64_t *x_q, int64_t *y_q, int64_t *y_hist, int64_t cap, int64_t *n_written)
+{
+    return line_tip_impl(h, false, x_q, y_q, y_hist, cap, n_written);
+}
+
+lbm_status lbm_line_tip_left(lbm_handle *h, int64_t *x_q, int64_t *y_q, int64_t *y_hist, int64_t cap,
+                             int64_t *n_written)
+{
+    return line_tip_impl(h, true, x_q, y_q, y_hist, cap, n_written);
 }
 
 lbm_status lbm_sync(lbm_handle *h)
@@ -1337,7 +1368,9 @@ std::vector<std::pair<void *, size_t>> ckpt_buffers(lbm_handle *h, const CkptHea
             {H.Kl, (size_t)c.hist_cap_l * 8},
             {H.vl, (size_t)c.hist_cap_l * 8},
             {H.tipl, (size_t)c.hist_cap_l * 8},
-            {H.npl, (size_t)c.hist_cap_l * 4}};
+            {H.npl, (size_t)c.hist_cap_l * 4},
+            {H.tipy, (size_t)(h->line ? c.hist_cap : 1) * 8},
+            {H.tipyl, (size_t)(h->line ? c.hist_cap_l : 1) * 8}};
 }
 
 }  // namespace

@@ -95,7 +95,7 @@ struct CrackParams {
 };
 
 // Per-step records of the right end and (two-tip cracks) the left end; a
-// crack in any direction records its tip's y in tipl.
+// crack in any direction records its tips' y in tipy and tipyl.
 struct History {
     double *K, *v;
     int64_t *tip;
@@ -103,6 +103,7 @@ struct History {
     double *Kl, *vl;
     int64_t *tipl;
     int32_t *npl;
+    int64_t *tipy, *tipyl;
 };
 
 // One row band of the static partition: output rows [j0, j1).

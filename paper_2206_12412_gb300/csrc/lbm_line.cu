@@ -108,13 +108,16 @@ struct LineSums {
 // the crack line).
 template <typename T>
 __device__ LineSums line_eval_warp(const CrackParams &p, const T *w, int64_t P, const uint32_t *cut_h,
-                                   const uint32_t *cut_v, const TipState &E)
+                                   const uint32_t *cut_v, const TipState &E, int dir)
 {
     const int lane = threadIdx.x & 31;
     const double r_min = p.r_min_fixed > 0.0 ? p.r_min_fixed : p.r0 / (1.0 - E.v_prev);   // eq. r(v)
     const double lo = r_min / p.dh, hi = (r_min + p.fit_width) / p.dh;
     const double tx = (double)E.tip_q * kTwoM32, ty = (double)E.tip_yq * kTwoM32;
-    const double ax = tx - lo * p.dir_x, bx = tx - hi * p.dir_x, ay = ty - lo * p.dir_y, by = ty - hi * p.dir_y;
+    // the window lies behind the tip: along -c from the right end, along +c
+    // from the left end of a two-tip crack
+    const double sx = dir > 0 ? -p.dir_x : p.dir_x, sy = dir > 0 ? -p.dir_y : p.dir_y;
+    const double ax = tx + lo * sx, bx = tx + hi * sx, ay = ty + lo * sy, by = ty + hi * sy;
     const double X = (double)p.nx, Y = (double)p.ny;
     auto cl = [](double v, double lim) { return fmin(fmax(v, -4.0), lim + 4.0); };
     int i0 = (int)floor(cl(fmin(ax, bx), X) - 2.0), i1 = (int)ceil(cl(fmax(ax, bx), X) + 2.0);
@@ -146,8 +149,8 @@ __device__ LineSums line_eval_warp(const CrackParams &p, const T *w, int64_t P, 
                 my = (int64_t)(j + 1) << kQBits;
             }
             if (!cut) continue;
-            const double px = __dmul_rn((double)(E.tip_q - mx) * kTwoM32, p.dir_x);
-            const double py = __dmul_rn((double)(E.tip_yq - my) * kTwoM32, p.dir_y);
+            const double px = __dmul_rn((double)(dir > 0 ? E.tip_q - mx : mx - E.tip_q) * kTwoM32, p.dir_x);
+            const double py = __dmul_rn((double)(dir > 0 ? E.tip_yq - my : my - E.tip_yq) * kTwoM32, p.dir_y);
             const double r_h = __dadd_rn(px, py);
             if (!(r_h >= lo && r_h < hi)) continue;
             const double w0 = (double)w[(int64_t)j * P + i];
@@ -169,24 +172,17 @@ __device__ LineSums line_eval_warp(const CrackParams &p, const T *w, int64_t P, 
     return LineSums{num, den, r_min, np};
 }
 
-// The crack step of Alg. 1 for a crack in any direction, by one warp on the
-// state S (shared memory): K, the criterion, the advance (with the stop at
-// the boundary), the severed links, the tip's fields of S and, if `commit`,
-// the history record at hist_n (tip x in tip, tip y in tipl).
-template <typename T>
-__device__ void line_step_warp(const CrackParams &p, const T *w, int64_t P, uint32_t *cut_h, uint32_t *cut_v,
-                               const History &hist, CrackState &S, bool commit)
+// Steps (2)-(4) of the crack step for one end (dir = +1: the tip, growing
+// along c; -1: the start of a two-tip crack, growing along -c), by one warp
+// on the state S (shared memory), given that end's sums: K, the criterion,
+// the advance (with the stop at the boundary), the severed links, the end's
+// fields of S and, if `commit`, its history record at hist_n (x in tip /
+// tipl, y in tipy / tipyl).
+__device__ void line_apply_warp(const CrackParams &p, uint32_t *cut_h, uint32_t *cut_v, const History &hist,
+                                CrackState &S, int dir, bool commit, const LineSums &c)
 {
     const int lane = threadIdx.x & 31;
-    TipState &E = S.r;
-    if (p.mode == CRACK_NONE || E.decided) {
-        __syncwarp();
-        if (lane == 0) E.decided = 1;
-        __syncwarp();
-        return;
-    }
-    const LineSums c = line_eval_warp<T>(p, w, P, cut_h, cut_v, E);
-    // (2) the criterion and (3) the advance: the same scalars on every lane
+    TipState &E = dir > 0 ? S.r : S.l;
     const double K = c.np > 0 ? p.mu / 4.0 * c.num / c.den : 0.0;
     int propagate = 0;
     double v = 0.0;
@@ -207,14 +203,15 @@ __device__ void line_step_warp(const CrackParams &p, const T *w, int64_t P, uint
     if (propagate) {
         const double adot = v * p.cs;
         const double q = adot * p.dt / p.dh * 4294967296.0;   // Delta a = adot dt, in grid units
-        qx = px + __double2ll_rn(q * p.dir_x);
-        qy = py + __double2ll_rn(q * p.dir_y);
+        const int64_t ax = __double2ll_rn(q * p.dir_x), ay = __double2ll_rn(q * p.dir_y);
+        qx = dir > 0 ? px + ax : px - ax;
+        qy = dir > 0 ? py + ay : py - ay;
         if (line_clamp(p, px, py, qx, qy)) { arrested = 1; flags |= FLAG_CLAMPED; }
     }
     const int grew = (qx != px || qy != py) ? 1 : 0;
     if (grew) {
-        // (4) sever every link the segment (px, py)-(qx, qy) meets: both ends
-        // of such a link lie within one spacing of the segment
+        // sever every link the segment (px, py)-(qx, qy) meets: both ends of
+        // such a link lie within one spacing of the segment
         const int64_t one = (int64_t)1 << kQBits, half = one >> 1;
         const int i0 = (int)hi64(0, floor_div_q(lo64(px, qx) - 3 * half));
         const int i1 = (int)lo64(p.nx - 1, floor_div_q(hi64(px, qx) + half) + 1);
@@ -245,15 +242,44 @@ __device__ void line_step_warp(const CrackParams &p, const T *w, int64_t P, uint
         E.arrested = arrested;
         if (commit && p.hist_cap > 0) {
             const int64_t h = S.hist_n % p.hist_cap;
-            hist.K[h] = K;
-            hist.v[h] = v;
-            hist.tip[h] = qx;
-            hist.tipl[h] = qy;
-            hist.np[h] = c.np;
+            if (dir > 0) {
+                hist.K[h] = K;
+                hist.v[h] = v;
+                hist.tip[h] = qx;
+                hist.tipy[h] = qy;
+                hist.np[h] = c.np;
+            } else {
+                hist.Kl[h] = K;
+                hist.vl[h] = v;
+                hist.tipl[h] = qx;
+                hist.tipyl[h] = qy;
+                hist.npl[h] = c.np;
+            }
         }
         E.decided = 1;
     }
     __syncwarp();
+}
+
+// The whole crack step by one warp, as Alg. 1 orders it: the criteria of
+// both ends on the same state, then the right end's advance, then the left
+// end's (the finalize kernel).
+template <typename T>
+__device__ void line_step_warp(const CrackParams &p, const T *w, int64_t P, uint32_t *cut_h, uint32_t *cut_v,
+                               const History &hist, CrackState &S, bool commit)
+{
+    const int lane = threadIdx.x & 31;
+    if (p.mode == CRACK_NONE || S.r.decided) {
+        __syncwarp();
+        if (lane == 0) { S.r.decided = 1; S.l.decided = 1; }
+        __syncwarp();
+        return;
+    }
+    const LineSums cr = line_eval_warp<T>(p, w, P, cut_h, cut_v, S.r, +1);
+    LineSums cl{0.0, 0.0, 0.0, 0};
+    if (p.two_tips) cl = line_eval_warp<T>(p, w, P, cut_h, cut_v, S.l, -1);
+    line_apply_warp(p, cut_h, cut_v, hist, S, +1, commit, cr);
+    if (p.two_tips) line_apply_warp(p, cut_h, cut_v, hist, S, -1, commit, cl);
 }
 
 // The pad images of the new value v of site (i, j) (free edges: the site's
@@ -334,34 +360,60 @@ __device__ __forceinline__ bool site_update(const StepArgs<T, T> &a, const EdgeV
 constexpr int kGroup = 32;
 struct Claims {
     int i0, i1, j0, j1;            // the tip's box
+    int k0, k1, l0, l1;            // the left end's box (two-tip cracks; else empty)
     int r0, r1;                    // rows whose groups can be claimed
-    float sx, sy, cx, cy, t_hi;    // start, direction, the tip's distance along c plus 2
+    float sx, sy, cx, cy;          // start, direction
+    float t_lo, t_hi;              // the ends' distances along c from the start, minus / plus 2
     float inv_cx, inv_cy;          // 1 / c (0 where |c| is below 1e-6: the row is all in or all out)
 };
 
 __device__ __forceinline__ Claims claims(const CrackParams &p, const CrackState *s)
 {
-    const int64_t ti = s->r.tip_q >> kQBits, tj = s->r.tip_yq >> kQBits;   // tips lie in [0, nx] x [0, ny]
     Claims c;
+    // the boxes of the sites within three spacings of each growing end's
+    // cell (tips lie in [0, nx] x [0, ny])
+    const int64_t ti = s->r.tip_q >> kQBits, tj = s->r.tip_yq >> kQBits;
     c.i0 = (int)hi64(0, ti - 3);
     c.i1 = (int)lo64(p.nx - 1, ti + 3);
     c.j0 = (int)hi64(0, tj - 3);
     c.j1 = (int)lo64(p.ny - 1, tj + 3);
-    const int64_t ya = lo64(p.start_yq, s->r.tip_yq) >> kQBits, yb = hi64(p.start_yq, s->r.tip_yq) >> kQBits;
-    c.r0 = (int)hi64(0, lo64(ya - 3, c.j0));
-    c.r1 = (int)lo64(p.ny - 1, hi64(yb + 3, c.j1));
+    c.k0 = c.l0 = 1;
+    c.k1 = c.l1 = 0;
+    const int64_t lxq = p.two_tips ? s->l.tip_q : p.start_q, lyq = p.two_tips ? s->l.tip_yq : p.start_yq;
+    if (p.two_tips) {
+        const int64_t li = lxq >> kQBits, lj = lyq >> kQBits;
+        c.k0 = (int)hi64(0, li - 3);
+        c.k1 = (int)lo64(p.nx - 1, li + 3);
+        c.l0 = (int)hi64(0, lj - 3);
+        c.l1 = (int)lo64(p.ny - 1, lj + 3);
+    }
+    const int64_t ya = lo64(lyq, s->r.tip_yq) >> kQBits, yb = hi64(lyq, s->r.tip_yq) >> kQBits;
+    c.r0 = (int)hi64(0, lo64(ya - 3, lo64(c.j0, p.two_tips ? c.l0 : c.j0)));
+    c.r1 = (int)lo64(p.ny - 1, hi64(yb + 3, hi64(c.j1, p.two_tips ? c.l1 : c.j1)));
     c.sx = (float)((double)p.start_q * kTwoM32);
     c.sy = (float)((double)p.start_yq * kTwoM32);
     c.cx = (float)p.dir_x;
     c.cy = (float)p.dir_y;
     const float tx = (float)((double)s->r.tip_q * kTwoM32), ty = (float)((double)s->r.tip_yq * kTwoM32);
     c.t_hi = __fadd_rn(__fadd_rn(__fmul_rn(__fsub_rn(tx, c.sx), c.cx), __fmul_rn(__fsub_rn(ty, c.sy), c.cy)), 2.0f);
+    const float ux = (float)((double)lxq * kTwoM32), uy = (float)((double)lyq * kTwoM32);
+    c.t_lo = __fsub_rn(__fadd_rn(__fmul_rn(__fsub_rn(ux, c.sx), c.cx), __fmul_rn(__fsub_rn(uy, c.sy), c.cy)), 2.0f);
     c.inv_cx = fabsf(c.cx) < 1e-6f ? 0.0f : __frcp_rn(c.cx);
     c.inv_cy = fabsf(c.cy) < 1e-6f ? 0.0f : __frcp_rn(c.cy);
     return c;
 }
 
-__device__ __forceinline__ bool in_box(const Claims &c, int i, int j) { return i >= c.i0 && i <= c.i1 && j >= c.j0 && j <= c.j1; }
+__device__ __forceinline__ bool in_box(const Claims &c, int i, int j)
+{
+    return (i >= c.i0 && i <= c.i1 && j >= c.j0 && j <= c.j1) || (i >= c.k0 && i <= c.k1 && j >= c.l0 && j <= c.l1);
+}
+
+// Does group s (W sites wide) of row j meet one of the boxes?
+__device__ __forceinline__ bool box_group(const Claims &c, int s, int j, int W)
+{
+    return (j >= c.j0 && j <= c.j1 && s >= c.i0 / W && s <= c.i1 / W) ||
+           (j >= c.l0 && j <= c.l1 && c.k0 <= c.k1 && s >= c.k0 / W && s <= c.k1 / W);
+}
 
 // The groups of row j (W sites wide) that meet the band: sa .. sb (empty if
 // sa > sb).
@@ -381,13 +433,13 @@ __device__ __forceinline__ void band_segs(const Claims &c, int j, int W, int nx,
     } else if (!(fabsf(dy) < 1.5f)) {
         return;
     }
-    // -2 < t < t_hi with t(x) = (x - s_x) c_x + y c_y
+    // t_lo < t < t_hi with t(x) = (x - s_x) c_x + y c_y
     const float ty = __fmul_rn(y, c.cy);
     if (c.inv_cx != 0.0f) {
-        const float u = __fmul_rn(__fsub_rn(-2.0f, ty), c.inv_cx), v = __fmul_rn(__fsub_rn(c.t_hi, ty), c.inv_cx);
+        const float u = __fmul_rn(__fsub_rn(c.t_lo, ty), c.inv_cx), v = __fmul_rn(__fsub_rn(c.t_hi, ty), c.inv_cx);
         xa = fmaxf(xa, __fadd_rn(c.sx, fminf(u, v)));
         xb = fminf(xb, __fadd_rn(c.sx, fmaxf(u, v)));
-    } else if (!(ty > -2.0f && ty < c.t_hi)) {
+    } else if (!(ty > c.t_lo && ty < c.t_hi)) {
         return;
     }
     // the columns whose centres lie within half a spacing of (xa, xb)
@@ -400,24 +452,33 @@ __device__ __forceinline__ void band_segs(const Claims &c, int j, int W, int nx,
 
 __device__ __forceinline__ bool seg_claimed(const Claims &c, int s, int j, int W, int nx)
 {
-    if (j >= c.j0 && j <= c.j1 && s >= c.i0 / W && s <= c.i1 / W) return true;
+    if (box_group(c, s, j, W)) return true;
     int sa, sb;
     band_segs(c, j, W, nx, sa, sb);
     return s >= sa && s <= sb;
 }
 
-// Block 0: the pending crack step (warp 0; it records the step and writes
-// the next state), then the tip's box with the cuts in force after it.
+// Block 0: the pending crack step -- warp 0 the tip, warp 1 the left end of
+// a two-tip crack; both criteria are evaluated before either end severs a
+// link, as Alg. 1 orders them -- then the record and the next state (thread
+// 0), then the ends' boxes with the cuts in force after it.
 template <typename T>
 __device__ void tip_cta(const StepArgs<T, T> &a, CrackState &sS, const EdgeValues<T> &E, const Claims &C)
 {
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5;
     const CrackParams &p = a.p;
+    if (tid == 0) sS = *a.s_in;
+    __syncthreads();
+    const bool pending = !sS.r.decided;   // not yet applied by a deferred crack step
+    const bool active = p.mode != CRACK_NONE && pending;
+    const int dir = warp == 0 ? +1 : -1;
+    const bool mine = warp == 0 || (warp == 1 && p.two_tips);
+    LineSums cs{0.0, 0.0, 0.0, 0};
+    if (active && mine) cs = line_eval_warp<T>(p, a.w_in, a.pitch, a.cut_h, a.cut_v, dir > 0 ? sS.r : sS.l, dir);
+    __syncthreads();   // both criteria on the state before either end severs a link
+    if (active && mine) line_apply_warp(p, a.cut_h, a.cut_v, a.hist, sS, dir, true, cs);
+    __syncthreads();
     if (tid < 32) {
-        if (tid == 0) sS = *a.s_in;
-        __syncwarp();
-        const bool pending = !sS.r.decided;   // not yet applied by a deferred crack step
-        line_step_warp<T>(p, a.w_in, a.pitch, a.cut_h, a.cut_v, a.hist, sS, true);
         if (tid == 0) {
             CrackState *o = a.s_out;
             const int64_t n = sS.step + 1;
@@ -428,24 +489,30 @@ __device__ void tip_cta(const StepArgs<T, T> &a, CrackState &sS, const EdgeValue
             o->r = sS.r;
             o->r.decided = 0;
             o->l = sS.l;
+            o->l.decided = 0;
             for (int e = 0; e < 4; ++e)
                 o->wstar[e] = a.edge[e] == EDGE_DIRICHLET ? load_value(a.load[e], n, (double)p.dt) : 0.0;
         }
     }
     __syncthreads();   // the new cuts, for every thread of the CTA
-    const int ni = C.i1 - C.i0 + 1, nj = C.j1 - C.j0 + 1;
     bool ok = true;
+    const int ni = C.i1 - C.i0 + 1, nj = C.j1 - C.j0 + 1;
     for (int t = tid; t < ni * nj; t += blockDim.x) ok &= site_update(a, E, C.i0 + t % ni, C.j0 + t / ni);
+    // the left end's box, less the sites of the tip's
+    const int mi = C.k1 - C.k0 + 1, mj = C.l1 - C.l0 + 1;
+    for (int t = tid; t < (mi > 0 ? mi * mj : 0); t += blockDim.x) {
+        const int i = C.k0 + t % mi, j = C.l0 + t / mi;
+        if (!(i >= C.i0 && i <= C.i1 && j >= C.j0 && j <= C.j1)) ok &= site_update(a, E, i, j);
+    }
     if (!ok) atomicOr(a.err, (uint32_t)ERR_NONFINITE);
 }
 
-// The claimed groups: every site outside the tip's box of every claimed
-// group.  The rows r0 .. r1, each cut into stretches of 16 groups, are taken
+// The claimed groups: every site outside the boxes of every claimed group.  The rows r0 .. r1, each cut into stretches of 16 groups, are taken
 // in turn by the `nblk` march blocks after their march; a block finds the
-// groups of its stretch that the band or the box claims (one evaluation of
-// the band per stretch) and its warps take them in turn, a site per lane.
-// The cuts they read are not changed during the launch (new ones all lie in
-// the box), and no march block writes a claimed site.
+// groups of its stretch that the band or a box claims (one evaluation of the
+// band per stretch; its warps test four groups each) and updates them, a
+// site per lane.  The cuts they read are not changed during the launch (new
+// ones all lie in the boxes), and no march block writes a claimed site.
 template <typename T>
 __device__ void claimed_groups(const StepArgs<T, T> &a, const EdgeValues<T> &E, const Claims &C, int blk, int nblk)
 {
@@ -453,27 +520,14 @@ __device__ void claimed_groups(const StepArgs<T, T> &a, const EdgeValues<T> &E, 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
     const int ngroup = (a.nx + kGroup - 1) / kGroup, nstretch = (ngroup + kStretch - 1) / kStretch;
     const int items = (C.r1 - C.r0 + 1) * nstretch;
-    const int bg0 = C.i0 / kGroup, bg1 = C.i1 / kGroup;
     bool ok = true;
     for (int q = blk; q < items; q += nblk) {
         const int j = C.r0 + q / nstretch, g0 = (q % nstretch) * kStretch, g1 = min(g0 + kStretch, ngroup) - 1;
         int sa, sb;
         band_segs(C, j, kGroup, a.nx, sa, sb);
-        const bool boxrow = j >= C.j0 && j <= C.j1;
-        // the claimed groups of the stretch: the band's range, and the box's
-        // (the two ranges overlap or not; each group is taken once)
-        const int ba = max(sa, g0), bb = min(sb, g1);
-        const int xa = boxrow ? max(bg0, g0) : 1, xb = boxrow ? min(bg1, g1) : 0;
-        const int nb = ba <= bb ? bb - ba + 1 : 0;
-        const int nx_ = xa <= xb ? xb - xa + 1 : 0;
-        for (int t = warp; t < nb + nx_; t += nwarp) {
-            int g;
-            if (t < nb) {
-                g = ba + t;
-            } else {
-                g = xa + (t - nb);
-                if (g >= ba && g <= bb) continue;   // already taken as a band group
-            }
+        for (int t = warp; t <= g1 - g0; t += nwarp) {
+            const int g = g0 + t;
+            if (!((g >= sa && g <= sb) || box_group(C, g, j, kGroup))) continue;
             const int i = g * kGroup + lane;
             if (i < a.nx && !in_box(C, i, j)) ok &= site_update(a, E, i, j);
         }
@@ -643,14 +697,16 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
         return;
     }
     // can the warp's part of the band hold an edge row or column, or a
-    // claimed segment: the tip's box, or the band (the rectangle of the
-    // warp's sites against the strip |d| < 1.5, -2 < t < t_hi, with margins
+    // claimed group: a box, or the band (the rectangle of the warp's sites
+    // against the strip |d| < 1.5, t_lo < t < t_hi, with margins
     // beyond the half-spacing widening; d and t are linear, so their
     // extremes over the rectangle lie at its corners)?
     constexpr int W = 32 * N;
     const bool edge = xw0 == 0 || xw0 + W - 1 >= nx - 1 || j0 == 0 || j1 == ny;
-    bool check = j0 <= C.j1 && j1 - 1 >= C.j0 && xw0 + W - 1 >= (C.i0 / kGroup) * kGroup &&
-                 xw0 <= (C.i1 / kGroup) * kGroup + kGroup - 1;
+    bool check = (j0 <= C.j1 && j1 - 1 >= C.j0 && xw0 + W - 1 >= (C.i0 / kGroup) * kGroup &&
+                  xw0 <= (C.i1 / kGroup) * kGroup + kGroup - 1) ||
+                 (C.k0 <= C.k1 && j0 <= C.l1 && j1 - 1 >= C.l0 && xw0 + W - 1 >= (C.k0 / kGroup) * kGroup &&
+                  xw0 <= (C.k1 / kGroup) * kGroup + kGroup - 1);
     if (!check && j1 - 1 >= C.r0 && j0 <= C.r1) {
         const float xa = (float)xw0 + 0.5f - C.sx, xb = (float)(xw0 + W) - 0.5f - C.sx;
         const float ya = (float)j0 + 0.5f - C.sy, yb = (float)(j1 - 1) + 0.5f - C.sy;
@@ -664,7 +720,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
             tlo = fminf(tlo, t);
             thi = fmaxf(thi, t);
         }
-        check = !(dlo > 3.0f || dhi < -3.0f || thi < -4.0f || tlo > C.t_hi + 2.0f);
+        check = !(dlo > 3.0f || dhi < -3.0f || thi < C.t_lo - 2.0f || tlo > C.t_hi + 2.0f);
     }
     T acc;
     if (edge) acc = check ? line_march_edge<T, true, true>(a, E, C, x0, xw0, j0, j1)

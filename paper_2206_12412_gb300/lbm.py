@@ -82,13 +82,13 @@ def lbm_create_line(grid: A.Grid, lattice: A.Lattice_, material: A.Material, cra
     return out.value
 
 
-def lbm_line_tip(h: int, cap: int = 0):
-    """(x_q, y_q) of the tip of a crack in any direction and the y of its last
-    `cap` records."""
+def lbm_line_tip(h: int, cap: int = 0, left: bool = False):
+    """(x_q, y_q) of the tip (left: the growing start of a two-tip crack) of a
+    crack in any direction and the y of its last `cap` records."""
     x, y, nw = C.c_int64(0), C.c_int64(0), C.c_int64(0)
     ys = np.zeros(max(cap, 1), np.int64)
-    _check(load_library().lbm_line_tip(C.c_void_p(h), C.byref(x), C.byref(y), ys.ctypes.data_as(C.POINTER(C.c_int64)),
-                                       cap, C.byref(nw)))
+    fn = load_library().lbm_line_tip_left if left else load_library().lbm_line_tip
+    _check(fn(C.c_void_p(h), C.byref(x), C.byref(y), ys.ctypes.data_as(C.POINTER(C.c_int64)), cap, C.byref(nw)))
     return x.value, y.value, ys[:nw.value]
 
 
@@ -249,7 +249,7 @@ def make_structs(problem: dict, storage: str = "f32"):
         else:
             cr.y = float(c["y"])
             cr.x_start, cr.x_tip = float(c.get("x_start", 0.0)), float(c["x_tip"])
-            cr.two_tips = 1 if c.get("two_tips") else 0
+        cr.two_tips = 1 if c.get("two_tips") else 0
         cr.v_rel = float(c.get("v_rel", 0.0))
         cr.K_C = float(c.get("K_C", 0.0))
         cr.v_max = float(c.get("v_max", 0.85))
@@ -423,7 +423,15 @@ class Lattice:
     def history_left(self, cap: int | None = None) -> dict:
         if cap is None:
             cap = int(self.problem.get("hist_cap", 1 << 16))
-        return lbm_crack_state(self.h, cap, left=True)[1]
+        h = lbm_crack_state(self.h, cap, left=True)[1]
+        if getattr(self, "line", False):
+            h["tip_yq"] = lbm_line_tip(self.h, cap, left=True)[2]
+        return h
+
+    def tip_q_left(self):
+        """(x, y) of the growing start of a two-tip crack in any direction."""
+        x, y, _ = lbm_line_tip(self.h, left=True)
+        return x, y
 
     def sync(self):
         lbm_sync(self.h)

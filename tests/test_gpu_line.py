@@ -274,3 +274,93 @@ def test_directions_near_the_axes(oracle_mod, gpu, start, tip):
     _masks(o, g)
     ho, hg = _tips(o, g, 150)
     assert (np.diff(ho["tip_q"]) != 0).sum() + (np.diff(ho["tip_yq"]) != 0).sum() > 50
+
+
+# ------------------------------------------------------ both ends growing
+
+def _centre(nx, ny, deg, half):
+    """A centre crack through the middle of the body at `deg` degrees, its
+    start the exact mirror of its tip on the grid."""
+    th = np.radians(deg)
+    mid = (nx / 2 + 0.013, ny / 2 + 0.007)
+    tip = (mid[0] + half * np.cos(th), mid[1] + half * np.sin(th))
+    tq = (int(np.rint(tip[0] * Q)), int(np.rint(tip[1] * Q)))
+    return ((nx * Q - tq[0]) / Q, (ny * Q - tq[1]) / Q), tip
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("deg", [23.0, 61.0, 137.0, 200.0])
+def test_two_ends_prescribed(oracle_mod, gpu, storage, deg):
+    nx, ny = (300, 200) if storage == "f64" else (700, 200)
+    start, tip = _centre(nx, ny, deg, 20.0)
+    p = W.with_line_crack(_problem(nx, ny), mode="prescribed", start=start, tip=tip, v_rel=0.6, r0=2.0,
+                          two_tips=True)
+    o, g = _run(oracle_mod, gpu, p, storage, [7, 64, 49])
+    _close(o, g, TOL[storage])
+    _masks(o, g)
+    _tips(o, g, 120)
+    hl_o, hl_g = o.history_left(), g.history_left(cap=120)
+    np.testing.assert_array_equal(hl_g["tip_q"], hl_o["tip_q"])
+    np.testing.assert_array_equal(hl_g["tip_yq"], hl_o["tip_yq"])
+    np.testing.assert_array_equal(hl_g["npairs"], hl_o["npairs"])
+    assert (np.diff(hl_o["tip_q"]) != 0).sum() + (np.diff(hl_o["tip_yq"]) != 0).sum() > 50
+    assert g.tip_q_left() == (int(hl_o["tip_q"][-1]), int(hl_o["tip_yq"][-1]))
+
+
+@pytest.mark.parametrize("deg", [23.0, 137.0])
+def test_two_ends_kcrit_fp64(oracle_mod, gpu, deg):
+    nx, ny = 300, 200
+    start, tip = _centre(nx, ny, deg, 25.0)
+    p = _problem(nx, ny, u0=4e-3, t_ramp=60.0)
+    K_C = 0.3 * W.strip_reference_K(0.25, 4e-3, float(ny))
+    p = W.with_line_crack(p, mode="kcrit", start=start, tip=tip, K_C=K_C, v_max=0.85, r0=2.0, two_tips=True)
+    o, g = _run(oracle_mod, gpu, p, "f64", [150, 150])
+    ho, hg = _tips(o, g, 300)
+    hlo, hlg = o.history_left(), g.history_left(cap=300)
+    assert (ho["v"] > 0).sum() > 10 and (hlo["v"] > 0).sum() > 10
+    np.testing.assert_array_equal(hlg["tip_q"], hlo["tip_q"])
+    np.testing.assert_array_equal(hlg["tip_yq"], hlo["tip_yq"])
+    np.testing.assert_allclose(hlg["K"], hlo["K"], rtol=0, atol=1e-9 * np.abs(hlo["K"]).max())
+    _masks(o, g)
+    _close(o, g, TOL["f64"])
+
+
+def test_two_ends_along_x_match_the_aligned_centre_crack(oracle_mod, gpu):
+    p = _problem(300, 90)
+    pa = W.with_crack(p, mode="prescribed", y=45.0, x_start=130.0, x_tip=170.0, v_rel=0.7, two_tips=True)
+    pl = W.with_line_crack(p, mode="prescribed", start=(130.0, 45.0), tip=(170.0, 45.0), v_rel=0.7, two_tips=True)
+    o = oracle_mod.Oracle(pa)
+    g = gpu.Lattice(pl, "f64")
+    o.step(200)
+    g.step(200)
+    _close(o, g, TOL["f64"])
+    np.testing.assert_array_equal(g.history(cap=200)["tip_q"], o.history()["tip_q"])
+    np.testing.assert_array_equal(g.history_left(cap=200)["tip_q"], o.history_left()["tip_q"])
+    _masks(o, g)
+
+
+def test_two_ends_stop_on_the_boundary_and_resume(oracle_mod, gpu, tmp_path):
+    """Both ends run into the body's boundary; a checkpoint taken on the way
+    resumes bit-identically, records included."""
+    nx, ny = 40, 30
+    p = W.with_line_crack(_problem(nx, ny), mode="prescribed", start=(17.3, 12.1), tip=(23.9, 16.6), v_rel=0.8,
+                          r0=1.5, two_tips=True)
+    o = oracle_mod.Oracle(p)
+    g = gpu.Lattice(p, "f64")
+    o.step(20)
+    g.step(20)
+    path = str(tmp_path / "two.lbm")
+    g.save(path)
+    o.step(80)
+    g.step(80)
+    assert g.crack_state()["flags"] & 1 and g.crack_state_left()["flags"] & 1
+    _masks(o, g)
+    _close(o, g, TOL["f64"])
+    h1, l1 = g.history(cap=100), g.history_left(cap=100)
+    np.testing.assert_array_equal(l1["tip_yq"], o.history_left()["tip_yq"])
+    g.load(path)
+    g.step(80)
+    h2, l2 = g.history(cap=100), g.history_left(cap=100)
+    for a, b in ((h1, h2), (l1, l2)):
+        for k in ("tip_q", "tip_yq", "K"):
+            np.testing.assert_array_equal(a[k], b[k])
