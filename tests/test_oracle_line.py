@@ -344,3 +344,53 @@ def test_centre_crack_at_an_angle_is_point_symmetric(oracle_mod, deg, mode):
     e2 = _expected_mask(nx, ny, dedup(left))
     np.testing.assert_array_equal(ch, e1[0] | e2[0])
     np.testing.assert_array_equal(cv, e1[1] | e2[1])
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_lines_cut_exactly_their_polyline(oracle_mod, seed):
+    """Seeded random starts, directions and lengths (one or both ends growing,
+    prescribed speed): the cut mask is exactly the set of links that the
+    polylines of the ends meet, every advance is Delta a c rounded per
+    component, and every tip stays in the body."""
+    rng = np.random.default_rng(100 + seed)
+    nx, ny = int(rng.integers(20, 48)), int(rng.integers(20, 48))
+    while True:
+        th = rng.uniform(0.0, 2.0 * math.pi)
+        L = rng.uniform(2.0, 8.0)
+        sx, sy = rng.uniform(4.0, nx - 4.0), rng.uniform(4.0, ny - 4.0)
+        tip = (sx + L * math.cos(th), sy + L * math.sin(th))
+        if 0.5 < tip[0] < nx - 0.5 and 0.5 < tip[1] < ny - 0.5:
+            break
+    two = bool(seed % 2)
+    p = W.with_line_crack(_strip(nx, ny), mode="prescribed", start=(sx, sy), tip=tip, v_rel=float(rng.uniform(0.3, 0.9)),
+                          r0=1.5, two_tips=two)
+    o = oracle_mod.Oracle(p)
+    o.step(int(rng.integers(20, 80)))
+    s_q = (int(np.rint(sx * Q)), int(np.rint(sy * Q)))
+    t_q = (int(np.rint(tip[0] * Q)), int(np.rint(tip[1] * Q)))
+    hr = o.history()
+    dedup = lambda pts: [pt for k, pt in enumerate(pts) if k == 0 or pt != pts[k - 1]]
+    polys = [dedup([s_q, t_q] + [(int(x), int(y)) for x, y in zip(hr["tip_q"], hr["tip_yq"])])]
+    hists = [hr]
+    if two:
+        hl = o.history_left()
+        polys.append(dedup([t_q, s_q] + [(int(x), int(y)) for x, y in zip(hl["tip_q"], hl["tip_yq"])]))
+        hists.append(hl)
+    ch = np.zeros((ny, nx), np.uint8)
+    cv = np.zeros((ny, nx), np.uint8)
+    for poly in polys:
+        a, b = _expected_mask(nx, ny, poly)
+        ch |= a
+        cv |= b
+    och, ocv = o.cuts()
+    np.testing.assert_array_equal(och, ch)
+    np.testing.assert_array_equal(ocv, cv)
+    cx, cy = o.direction()
+    q = p["crack"]["v_rel"] * 0.5 * p["dt"] / p["dh"] * Q
+    for h, sign in zip(hists, (1, -1)):
+        x, y = np.asarray(h["tip_q"]), np.asarray(h["tip_yq"])
+        assert (x >= 0).all() and (x <= nx * Q).all() and (y >= 0).all() and (y <= ny * Q).all()
+        dx, dy = np.diff(x), np.diff(y)
+        free = (x[1:] > 0) & (x[1:] < nx * Q) & (y[1:] > 0) & (y[1:] < ny * Q)
+        np.testing.assert_array_equal(dx[free], sign * np.rint(q * cx) * np.ones(free.sum()))
+        np.testing.assert_array_equal(dy[free], sign * np.rint(q * cy) * np.ones(free.sum()))
