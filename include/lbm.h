@@ -183,7 +183,7 @@ typedef struct lbm_crack {
  * two_tips: 1 lets the start grow too, along -c, with its own speed memory
  * and the same opening sign (a centre crack in that direction); its K window
  * lies along +c behind it.  The other fields are those of lbm_crack.  Built
- * for D2Q5, LBM_BC_BOUNCEBACK, LBM_F64 or LBM_F32 storage. */
+ * for D2Q5 and LBM_BC_BOUNCEBACK, with every storage. */
 typedef struct lbm_crack_line {
     int32_t mode;
     int32_t two_tips;

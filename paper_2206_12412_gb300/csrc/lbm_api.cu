@@ -145,8 +145,8 @@ cudaError_t enqueue_step_t(const lbm_handle *h, int par, cudaStream_t s)
 {
     StepArgs<T, D> a;
     make_step_args(h, par, a);
+    if (h->line) return launch_line_step(a, s);
     if constexpr (std::is_same<T, D>::value) {
-        if (h->line) return launch_line_step(a, s);
         if (h->q == 9) {
             cudaError_t e = launch_d2q9_step(a, s);
             if (e == cudaSuccess && h->cp.macro && h->cp.mode != CRACK_NONE) e = launch_d2q9_faces(a, s);
@@ -410,8 +410,7 @@ lbm_status lbm_create_line(const lbm_grid *grid, const lbm_lattice *lattice, con
     if (lattice->velocity_set != LBM_D2Q5) return fail(LBM_ERR_ARG, "a crack in any direction is built for D2Q5");
     if (lattice->bc_mode != LBM_BC_BOUNCEBACK)
         return fail(LBM_ERR_ARG, "a crack in any direction is built with link-local faces (LBM_BC_BOUNCEBACK)");
-    if (lattice->storage != LBM_F64 && lattice->storage != LBM_F32)
-        return fail(LBM_ERR_ARG, "a crack in any direction needs LBM_F64 or LBM_F32 storage");
+    if (lattice->storage < LBM_F64 || lattice->storage > LBM_F32_WD_F16) return fail(LBM_ERR_ARG, "unknown storage");
     if (grid->nx < 1 || grid->ny < 2 || !(grid->dh > 0.0) || !std::isfinite(grid->dh))
         return fail(LBM_ERR_ARG, "need nx >= 1, ny >= 2 and a positive, finite dh");
     if (c.mode == LBM_CRACK_PRESCRIBED && !(c.v_rel >= 0.0 && c.v_rel < 1.0))
@@ -748,7 +747,10 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
         cp.start_yq = line->start_yq;
         // bands as short as keeps every CTA of the step resident at once
         int bps_line = 0;
-        const void *lk = h->esize == 8 ? line_step_kernel_ptr<double>() : line_step_kernel_ptr<float>();
+        const void *lk = lattice->storage == LBM_F64           ? line_step_kernel_ptr<double, double>()
+                         : lattice->storage == LBM_F32_WD_BF16 ? line_step_kernel_ptr<float, __nv_bfloat16>()
+                         : lattice->storage == LBM_F32_WD_F16  ? line_step_kernel_ptr<float, __half>()
+                                                               : line_step_kernel_ptr<float, float>();
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_line, lk, kThreads, 0);
         if (e != cudaSuccess) return bail(cuda_fail(e, "querying the line step kernel"));
         // every slot but the tip block's goes to the march

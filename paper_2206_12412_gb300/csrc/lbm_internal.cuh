@@ -227,8 +227,8 @@ cudaError_t launch_wd_to_f32(const D *wd, int64_t pitch, int nx, int ny, float s
 template <typename D>
 cudaError_t launch_wd_from_f32(D *wd, int64_t pitch, int nx, int ny, float scale, const float *src, cudaStream_t s);
 template <typename T> cudaError_t launch_finalize(const FinalizeArgs<T> &a, cudaStream_t s);
-template <typename T> cudaError_t launch_line_step(const StepArgs<T, T> &a, cudaStream_t s);
-template <typename T> const void *line_step_kernel_ptr();
+template <typename T, typename D> cudaError_t launch_line_step(const StepArgs<T, D> &a, cudaStream_t s);
+template <typename T, typename D> const void *line_step_kernel_ptr();
 template <typename T> cudaError_t launch_line_finalize(const FinalizeArgs<T> &a, cudaStream_t s);
 cudaError_t launch_exchange(const RowCopy *pairs, int n_pairs, int64_t row_bytes, cudaStream_t s);
 cudaError_t launch_wstar(CrackState *st, const LoadDesc *load, const int32_t *edge, double dt, cudaStream_t s);

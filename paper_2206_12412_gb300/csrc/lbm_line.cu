@@ -285,8 +285,8 @@ __device__ void line_step_warp(const CrackParams &p, const T *w, int64_t P, uint
 // The pad images of the new value v of site (i, j) (free edges: the site's
 // own value; periodic edges: the wrap-around value), as write_pads does for a
 // row vector.
-template <typename T>
-__device__ __forceinline__ void site_pads(const StepArgs<T, T> &a, int i, int j, T v)
+template <typename T, typename D>
+__device__ __forceinline__ void site_pads(const StepArgs<T, D> &a, int i, int j, T v)
 {
     const int nx = a.nx, ny = a.ny;
     const int64_t P = a.pitch;
@@ -311,8 +311,8 @@ __device__ __forceinline__ void site_pads(const StepArgs<T, T> &a, int i, int j,
 
 // The update of one site with its severed links (the update of the march,
 // site by site); returns whether the new w is finite.
-template <typename T>
-__device__ __forceinline__ bool site_update(const StepArgs<T, T> &a, const EdgeValues<T> &E, int i, int j)
+template <typename T, typename D>
+__device__ __forceinline__ bool site_update(const StepArgs<T, D> &a, const EdgeValues<T> &E, int i, int j)
 {
     const int nx = a.nx, ny = a.ny, words = a.words;
     const int64_t P = a.pitch;
@@ -326,7 +326,9 @@ __device__ __forceinline__ bool site_update(const StepArgs<T, T> &a, const EdgeV
     const T w0 = r0[i];
     T wl = r0[i - 1], wr = r0[i + 1], u = r0[i + P], d = r0[i - P];
     const int64_t o = (int64_t)j * P + i;
-    const T wdo = a.wd[o];
+    T wdo;
+    if constexpr (std::is_same<T, D>::value) wdo = a.wd[o];
+    else wdo = WdIO<D>::get(a.wd + o, a.wd_inv);
     if (j == ny - 1 && a.edge[TOP] == EDGE_DIRICHLET) u = E.two_ws[TOP] - w0;
     else if ((vu_w >> (i & 31)) & 1u) u = w0;
     if (j == 0 && a.edge[BOTTOM] == EDGE_DIRICHLET) d = E.two_ws[BOTTOM] - w0;
@@ -339,7 +341,7 @@ __device__ __forceinline__ bool site_update(const StepArgs<T, T> &a, const EdgeV
     const T wdn = wdo + a.g * lap;
     const T wn = w0 + a.dt * wdn;
     a.w_out[o] = wn;
-    a.wd[o] = wdn;
+    WdIO<D>::put(a.wd + o, wdn, a.wd_scale);
     site_pads(a, i, j, wn);
     return isfinite(wn);
 }
@@ -462,8 +464,8 @@ __device__ __forceinline__ bool seg_claimed(const Claims &c, int s, int j, int W
 // a two-tip crack; both criteria are evaluated before either end severs a
 // link, as Alg. 1 orders them -- then the record and the next state (thread
 // 0), then the ends' boxes with the cuts in force after it.
-template <typename T>
-__device__ void tip_cta(const StepArgs<T, T> &a, CrackState &sS, const EdgeValues<T> &E, const Claims &C)
+template <typename T, typename D>
+__device__ void tip_cta(const StepArgs<T, D> &a, CrackState &sS, const EdgeValues<T> &E, const Claims &C)
 {
     const int tid = threadIdx.x, warp = tid >> 5;
     const CrackParams &p = a.p;
@@ -513,8 +515,8 @@ __device__ void tip_cta(const StepArgs<T, T> &a, CrackState &sS, const EdgeValue
 // band per stretch; its warps test four groups each) and updates them, a
 // site per lane.  The cuts they read are not changed during the launch (new
 // ones all lie in the boxes), and no march block writes a claimed site.
-template <typename T>
-__device__ void claimed_groups(const StepArgs<T, T> &a, const EdgeValues<T> &E, const Claims &C, int blk, int nblk)
+template <typename T, typename D>
+__device__ void claimed_groups(const StepArgs<T, D> &a, const EdgeValues<T> &E, const Claims &C, int blk, int nblk)
 {
     constexpr int kStretch = 16;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
@@ -537,8 +539,8 @@ __device__ void claimed_groups(const StepArgs<T, T> &a, const EdgeValues<T> &E, 
 
 // The march of a warp whose part of the band holds no edge row or column and
 // no claimed site: the bare update.
-template <typename T>
-__device__ __forceinline__ T line_march_bare(const StepArgs<T, T> &a, int x0, int j0, int j1)
+template <typename T, typename D>
+__device__ __forceinline__ T line_march_bare(const StepArgs<T, D> &a, int x0, int j0, int j1)
 {
     constexpr int N = Vec<T>::N;
     typedef Row<T, N> R;
@@ -547,24 +549,26 @@ __device__ __forceinline__ T line_march_bare(const StepArgs<T, T> &a, int x0, in
     const int64_t P = a.pitch;
     const T *win = a.w_in + x0;
     T *wout = a.w_out + x0;
-    T *wdp = a.wd + x0;
+    D *wdp = a.wd + x0;
+    const T wd_inv = a.wd_inv, wd_scale = a.wd_scale;
     R dn, c, up, wdv;
     ldg_row(win + (int64_t)(j0 - 1) * P, dn);
     ldg_row(win + (int64_t)j0 * P, c);
     ldg_row(win + (int64_t)(j0 + 1) * P, up);
-    ld_row(wdp + (int64_t)j0 * P, wdv);
+    WdIO<D>::load(wdp + (int64_t)j0 * P, wdv, wd_inv);
     T hl = (T)0, hr = (T)0;
     if (lane == 0) hl = win[(int64_t)j0 * P - 1];
     if (lane == 31) hr = win[(int64_t)j0 * P + N];
     const T g = a.g, dt = a.dt;
     T acc = (T)0;
     for (int j = j0; j < j1; ++j) {
-        R nxt, wdn;
+        R nxt;
+        typename WdIO<D>::Raw wdn;   // converted after this row's update, when it has arrived
         T hln = (T)0, hrn = (T)0;
         const bool more = j + 1 < j1;
         if (more) {
             ldg_row(win + (int64_t)(j + 2) * P, nxt);
-            ld_row(wdp + (int64_t)(j + 1) * P, wdn);
+            WdIO<D>::fetch(wdp + (int64_t)(j + 1) * P, wdn);
             if (lane == 0) hln = win[(int64_t)(j + 1) * P - 1];
             if (lane == 31) hrn = win[(int64_t)(j + 1) * P + N];
         }
@@ -580,13 +584,13 @@ __device__ __forceinline__ T line_march_bare(const StepArgs<T, T> &a, int x0, in
             wn.v[k] = c.v[k] + dt * wdnew.v[k];
         }
         stg_row(wout + (int64_t)j * P, wn);
-        stg_row(wdp + (int64_t)j * P, wdnew);
+        WdIO<D>::store(wdp + (int64_t)j * P, wdnew, wd_scale);
         acc += wn.v[0];
         dn = c;
         c = up;
         if (more) {
             up = nxt;
-            wdv = wdn;
+            WdIO<D>::unpack(wdn, wdv, wd_inv);
             hl = hln;
             hr = hrn;
         }
@@ -598,8 +602,8 @@ __device__ __forceinline__ T line_march_bare(const StepArgs<T, T> &a, int x0, in
 // anti-bounce-back and free and periodic edges through the pads (as the step
 // kernel's edge warps); with CHECK, no store to a claimed group.  No cut
 // word is read: every site next to a severed link lies in a claimed group.
-template <typename T, bool EDGE, bool CHECK>
-__device__ __forceinline__ T line_march_edge(const StepArgs<T, T> &a, const EdgeValues<T> &E, const Claims &C, int x0,
+template <typename T, typename D, bool EDGE, bool CHECK>
+__device__ __forceinline__ T line_march_edge(const StepArgs<T, D> &a, const EdgeValues<T> &E, const Claims &C, int x0,
                                              int xw0, int j0, int j1)
 {
     constexpr int N = Vec<T>::N;
@@ -614,18 +618,19 @@ __device__ __forceinline__ T line_march_edge(const StepArgs<T, T> &a, const Edge
     ldg_row(wb + (int64_t)(j0 - 1) * P + x0, dn);
     ldg_row(wb + (int64_t)j0 * P + x0, c);
     ldg_row(wb + (int64_t)(j0 + 1) * P + x0, up);
-    ld_row(a.wd + x0 + (int64_t)j0 * P, wdv);
+    WdIO<D>::load(a.wd + x0 + (int64_t)j0 * P, wdv, a.wd_inv);
     T hl = (T)0, hr = (T)0;
     if (lane == 0) hl = wb[(int64_t)j0 * P + x0 - 1];
     if (lane == 31) hr = wb[(int64_t)j0 * P + x0 + N];
     T acc = (T)0;
     for (int j = j0; j < j1; ++j) {
-        R nxt, wdn;
+        R nxt;
+        typename WdIO<D>::Raw wdn;
         T hln = (T)0, hrn = (T)0;
         const bool more = j + 1 < j1;
         if (more) {
             ldg_row(wb + (int64_t)(j + 2) * P + x0, nxt);
-            ld_row(a.wd + x0 + (int64_t)(j + 1) * P, wdn);
+            WdIO<D>::fetch(a.wd + x0 + (int64_t)(j + 1) * P, wdn);
             if (lane == 0) hln = wb[(int64_t)(j + 1) * P + x0 - 1];
             if (lane == 31) hrn = wb[(int64_t)(j + 1) * P + x0 + N];
         }
@@ -651,7 +656,7 @@ __device__ __forceinline__ T line_march_edge(const StepArgs<T, T> &a, const Edge
                     wn.v[k] = c.v[k] + a.dt * wdnew.v[k];
                 }
                 stg_row(a.w_out + x0 + (int64_t)j * P, wn);
-                stg_row(a.wd + x0 + (int64_t)j * P, wdnew);
+                WdIO<D>::store(a.wd + x0 + (int64_t)j * P, wdnew, a.wd_scale);
                 acc += wn.v[0];
             }
         }
@@ -659,7 +664,7 @@ __device__ __forceinline__ T line_march_edge(const StepArgs<T, T> &a, const Edge
         c = up;
         if (more) {
             up = nxt;
-            wdv = wdn;
+            WdIO<D>::unpack(wdn, wdv, a.wd_inv);
             hl = hln;
             hr = hrn;
         }
@@ -671,9 +676,9 @@ __device__ __forceinline__ T line_march_edge(const StepArgs<T, T> &a, const Edge
 // marches column block cb of band `band` (p.band rows; bands as short as
 // keeps every block resident at once) and then takes its share of the
 // claimed groups.
-template <typename T>
+template <typename T, typename D>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBlocks - 2)
-    line_step_kernel(const StepArgs<T, T> a)
+    line_step_kernel(const StepArgs<T, D> a)
 {
     constexpr int N = Vec<T>::N;
     __shared__ CrackState sS;
@@ -681,7 +686,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
     const EdgeValues<T> E = edge_values<T>(a.s_in);
     const Claims C = claims(a.p, a.s_in);
     if (blockIdx.x == 0) {
-        tip_cta<T>(a, sS, E, C);
+        tip_cta<T, D>(a, sS, E, C);
         return;
     }
     const int n_march = a.ncb * ((a.ny + a.p.band - 1) / a.p.band);
@@ -693,7 +698,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
     const int nx = a.nx, ny = a.ny;
     // warps wholly right of the lattice have nothing to load or store
     if (xw0 >= nx) {
-        claimed_groups<T>(a, E, C, u, n_march);
+        claimed_groups<T, D>(a, E, C, u, n_march);
         return;
     }
     // can the warp's part of the band hold an edge row or column, or a
@@ -723,13 +728,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
         check = !(dlo > 3.0f || dhi < -3.0f || thi < C.t_lo - 2.0f || tlo > C.t_hi + 2.0f);
     }
     T acc;
-    if (edge) acc = check ? line_march_edge<T, true, true>(a, E, C, x0, xw0, j0, j1)
-                          : line_march_edge<T, true, false>(a, E, C, x0, xw0, j0, j1);
-    else acc = check ? line_march_edge<T, false, true>(a, E, C, x0, xw0, j0, j1) : line_march_bare<T>(a, x0, j0, j1);
+    if (edge) acc = check ? line_march_edge<T, D, true, true>(a, E, C, x0, xw0, j0, j1)
+                          : line_march_edge<T, D, true, false>(a, E, C, x0, xw0, j0, j1);
+    else acc = check ? line_march_edge<T, D, false, true>(a, E, C, x0, xw0, j0, j1) : line_march_bare<T, D>(a, x0, j0, j1);
     // a non-finite w (or wdot, which enters w) turns the sum of the first
     // element of each vector non-finite within a step or two
     if (__any_sync(0xffffffffu, !isfinite(acc)) && lane == 0) atomicOr(a.err, (uint32_t)ERR_NONFINITE);
-    claimed_groups<T>(a, E, C, u, n_march);
+    claimed_groups<T, D>(a, E, C, u, n_march);
 }
 
 // The pending crack step before the host reads the state (one warp).
@@ -749,11 +754,11 @@ __global__ void line_finalize_kernel(const FinalizeArgs<T> a)
 
 }  // namespace
 
-template <typename T>
-cudaError_t launch_line_step(const StepArgs<T, T> &a, cudaStream_t s)
+template <typename T, typename D>
+cudaError_t launch_line_step(const StepArgs<T, D> &a, cudaStream_t s)
 {
     const unsigned bands = (unsigned)((a.ny + a.p.band - 1) / a.p.band);
-    line_step_kernel<T><<<1u + (unsigned)a.ncb * bands, kThreads, 0, s>>>(a);
+    line_step_kernel<T, D><<<1u + (unsigned)a.ncb * bands, kThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -764,12 +769,20 @@ cudaError_t launch_line_finalize(const FinalizeArgs<T> &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <typename T> const void *line_step_kernel_ptr() { return reinterpret_cast<const void *>(&line_step_kernel<T>); }
+template <typename T, typename D>
+const void *line_step_kernel_ptr()
+{
+    return reinterpret_cast<const void *>(&line_step_kernel<T, D>);
+}
 
-template const void *line_step_kernel_ptr<double>();
-template const void *line_step_kernel_ptr<float>();
-template cudaError_t launch_line_step<double>(const StepArgs<double, double> &, cudaStream_t);
-template cudaError_t launch_line_step<float>(const StepArgs<float, float> &, cudaStream_t);
+template const void *line_step_kernel_ptr<double, double>();
+template const void *line_step_kernel_ptr<float, float>();
+template const void *line_step_kernel_ptr<float, __nv_bfloat16>();
+template const void *line_step_kernel_ptr<float, __half>();
+template cudaError_t launch_line_step<double, double>(const StepArgs<double, double> &, cudaStream_t);
+template cudaError_t launch_line_step<float, float>(const StepArgs<float, float> &, cudaStream_t);
+template cudaError_t launch_line_step<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> &, cudaStream_t);
+template cudaError_t launch_line_step<float, __half>(const StepArgs<float, __half> &, cudaStream_t);
 template cudaError_t launch_line_finalize<double>(const FinalizeArgs<double> &, cudaStream_t);
 template cudaError_t launch_line_finalize<float>(const FinalizeArgs<float> &, cudaStream_t);
 

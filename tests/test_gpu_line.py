@@ -364,3 +364,22 @@ def test_two_ends_stop_on_the_boundary_and_resume(oracle_mod, gpu, tmp_path):
     for a, b in ((h1, h2), (l1, l2)):
         for k in ("tip_q", "tip_yq", "K"):
             np.testing.assert_array_equal(a[k], b[k])
+
+
+# w of the 16-bit wdot forms: the bounds of test_gpu_mixed.py (stored wdot
+# rounded to 8 / 11 significant bits every step; not a parity bar)
+BOUND_16 = {"f32_bf16": 1e-2, "f32_f16": 1e-3}
+
+
+@pytest.mark.parametrize("storage", ["f32_bf16", "f32_f16"])
+@pytest.mark.parametrize("two", [False, True])
+def test_sixteen_bit_wdot(oracle_mod, gpu, storage, two):
+    nx, ny = 700, 200
+    start, tip = _centre(nx, ny, 33.0, 20.0)
+    p = W.with_line_crack(_problem(nx, ny), mode="prescribed", start=start, tip=tip, v_rel=0.6, r0=2.0, two_tips=two)
+    o, g = _run(oracle_mod, gpu, p, storage, [64, 86])
+    wo, _ = o.fields()
+    wg, _ = g.fields()
+    assert np.abs(wg - wo).max() < BOUND_16[storage] * np.abs(wo).max()
+    _masks(o, g)
+    _tips(o, g, 150)
