@@ -682,9 +682,16 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
 {
     constexpr int N = Vec<T>::N;
     __shared__ CrackState sS;
+    __shared__ Claims sC;                 // the claims and edge values, formed once per block
+    __shared__ EdgeValues<T> sE;
     const int tid = threadIdx.x, lane = tid & 31;
-    const EdgeValues<T> E = edge_values<T>(a.s_in);
-    const Claims C = claims(a.p, a.s_in);
+    if (tid == 0) {
+        sC = claims(a.p, a.s_in);
+        sE = edge_values<T>(a.s_in);
+    }
+    __syncthreads();
+    const EdgeValues<T> &E = sE;
+    const Claims &C = sC;
     if (blockIdx.x == 0) {
         tip_cta<T, D>(a, sS, E, C);
         return;
