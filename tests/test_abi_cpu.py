@@ -143,6 +143,7 @@ def _line_structs(**over):
     ({"cr__v_rel": 1.0}, "v_rel"),
     ({"cr__mode": 3, "cr__K_C": 0.0}, "K_C"),
     ({"g__dh": 0.0}, "dh"),
+    ({"cr__two_tips": 2}, "two_tips"),
 ])
 def test_create_line_rejects_bad_arguments(lib, over, msg):
     g, lat, mat, cr, loads, keep = _line_structs(**over)

@@ -394,3 +394,21 @@ def test_random_lines_cut_exactly_their_polyline(oracle_mod, seed):
         free = (x[1:] > 0) & (x[1:] < nx * Q) & (y[1:] > 0) & (y[1:] < ny * Q)
         np.testing.assert_array_equal(dx[free], sign * np.rint(q * cx) * np.ones(free.sum()))
         np.testing.assert_array_equal(dy[free], sign * np.rint(q * cy) * np.ones(free.sum()))
+
+
+def test_benchmark_line_workload_grows(oracle_mod):
+    """The benchmark's crack at 20 degrees (kcrit_line) at 1/16 scale: the
+    K-criterion starts the growth during the ramp and the tip keeps to the
+    crack's line until it stops on the top edge."""
+    p = W.kcrit_line(scale=16)
+    o = oracle_mod.Oracle(p)
+    o.step(3000)
+    h = o.history()
+    first = int(np.argmax(h["v"] > 0))
+    assert 0 < first < 5000 // 16
+    cr = p["crack"]
+    s_q = (cr["x_start"] * Q, cr["y_start"] * Q)
+    c = (math.cos(math.radians(20.0)), math.sin(math.radians(20.0)))
+    off = -(h["tip_q"] - s_q[0]) * c[1] + (h["tip_yq"] - s_q[1]) * c[0]
+    assert np.abs(off).max() < 1e-6 * Q
+    assert o.flags() & 1 and int(h["tip_yq"][-1]) == p["ny"] * Q
