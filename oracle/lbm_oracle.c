@@ -66,7 +66,10 @@
  *     link midpoint m, with delta = w(left of c) - w(right of c); the tip
  *     stops where it meets the body's boundary; the faces are link-local;
  *     with two growing ends the start is the left end, growing along -c,
- *     with r = (m - x_tip) . c and the same delta.
+ *     with r = (m - x_tip) . c and the same delta; with the macroscopic
+ *     rule on its faces a boundary point takes the normal of the line (its
+ *     x_I, x_II never reach across the crack), and the sweeps of the
+ *     boundary solve run until no bit changes (256 at most).
  */
 #include <math.h>
 #include <stdint.h>
@@ -385,7 +388,7 @@ static void initial_crack(orc_state *s)
         for (int q = 0; q < s->nbprev; ++q) dup |= s->bprev[q] == B[b];
         if (!dup) s->bprev[s->nbprev++] = B[b];
     }
-    if (!s->c.line)
+    if (!s->c.line || s->c.bc_mode == ORC_BC_MACROSCOPIC)
         for (int b = 0; b < s->nbprev; ++b) add_bpoint(s, s->bprev[b]);
     free(B);
 }
@@ -425,11 +428,12 @@ orc_state *orc_create(const orc_config *cfg)
     if (cfg->nx < 1 || cfg->ny < 1 || !(cfg->dh > 0) || !(cfg->dt > 0)) return NULL;
     int Q = cfg->q == 0 ? 5 : cfg->q;
     if (Q != 5 && Q != 9) return NULL;
-    /* a crack in any direction is built for D2Q5 with link-local faces; its
-     * K window must lie more than half a spacing behind the tip (the links a
-     * step severs have their midpoints at most that far behind the old tip) */
+    /* a crack in any direction is built for D2Q5 (link-local faces, or the
+     * macroscopic rule on the crack faces only); its K window must lie more
+     * than half a spacing behind the tip (the links a step severs have their
+     * midpoints at most that far behind the old tip) */
     if (cfg->line) {
-        if (Q != 5 || cfg->bc_mode != ORC_BC_BOUNCEBACK || cfg->edge_macro || cfg->crack_mode == ORC_CRACK_NONE)
+        if (Q != 5 || cfg->edge_macro || cfg->crack_mode == ORC_CRACK_NONE)
             return NULL;
         double rmin = cfg->r_min_fixed > 0.0 ? cfg->r_min_fixed : cfg->r0;
         if (!(rmin > 0.5 * cfg->dh)) return NULL;
@@ -578,9 +582,45 @@ static int bilinear(const orc_state *s, double px, double py, int32_t idx[4], do
 /* ProcessPoints for one new boundary point x_B (Sec. 3.1 and Alg. 1): the
  * closest point x_C on the crack, the normal through x_B, the interior points
  * x_I = x_B + dh n and x_II = x_B + 2 dh n with their bilinear stencils. */
+/* ProcessPoints for a crack in any direction (the reading for a crack that
+ * is not aligned with the lattice): x_B takes the normal n of the crack's
+ * line, pointing away from it, so its stencil depends on the site and the
+ * line alone; s_B is its distance from the line, and x_I = x_B + n dh,
+ * x_II = x_B + 2 n dh.  Every corner of their bilinear cells is x_B plus a
+ * step of the lattice in n's quadrant, so it lies at least as far from the
+ * line as x_B, on its side: the stencils never reach across the crack. */
+static void add_bpoint_line(orc_state *s, int32_t k, orc_bpoint *b)
+{
+    int nx = s->c.nx;
+    double bx = k % nx + 0.5, by = k / nx + 0.5;
+    double sx = (double)s->start_q / (double)qone(), sy = (double)s->start_yq / (double)qone();
+    double d = -(bx - sx) * s->dir_y + (by - sy) * s->dir_x;
+    double side = d > 0.0 ? 1.0 : -1.0;
+    double nxv = -s->dir_y * side, nyv = s->dir_x * side;   /* away from the line */
+    b->nI = bilinear(s, bx + nxv, by + nyv, b->idxI, b->wI);
+    b->nII = bilinear(s, bx + 2.0 * nxv, by + 2.0 * nyv, b->idxII, b->wII);
+    b->sB = fabs(d);
+    b->sI = fabs(d) + 1.0;
+    b->sII = fabs(d) + 2.0;
+    if (b->nI < 0 || b->nII < 0) s->flags |= ORC_FLAG_UNSUPPORTED;
+}
+
 static void add_bpoint(orc_state *s, int32_t k)
 {
     if (s->is_bpoint[k]) return;
+    if (s->c.line) {
+        if (s->nbl == s->capbl) {
+            s->capbl *= 2;
+            s->bl = realloc(s->bl, sizeof(orc_bpoint) * (size_t)s->capbl);
+        }
+        orc_bpoint *b = &s->bl[s->nbl];
+        memset(b, 0, sizeof(*b));
+        b->site = k;
+        add_bpoint_line(s, k, b);
+        s->is_bpoint[k] = 1;
+        s->nbl++;
+        return;
+    }
     int nx = s->c.nx;
     int i = k % nx, j = k / nx;
     double bx = i + 0.5, by = j + 0.5;                   /* units of dh */
@@ -747,7 +787,7 @@ static void boundary_solve(orc_state *s)
         if (!(crack_rule && s->is_bpoint[s->ep[q].site])) site[m++] = s->ep[q].site;
     memcpy(cur, s->w, sizeof(double) * n);
     int converged = 0;
-    for (int sweep = 0; sweep < 16 && !converged; ++sweep) {
+    for (int sweep = 0; sweep < 256 && !converged; ++sweep) {
         int v = 0;
         for (int b = 0; b < nb; ++b) val[v++] = macro_value(&s->bl[b], cur);
         for (int q = 0; q < ne; ++q)
@@ -1078,6 +1118,8 @@ static int tip_advance(orc_state *s, int dir, double v)
         nB = checklinks(s, px, py, nxq, nyq, B, 64);
         if (dir < 0) { s->bprev = keep; s->nbprev = nkeep; }
         qsort(B, (size_t)nB, sizeof(int32_t), cmp_i32);
+        if (c->bc_mode == ORC_BC_MACROSCOPIC)
+            for (int b = 0; b < nB; ++b) add_bpoint(s, B[b]);   /* ProcessPoints */
         if (nB > 0) {
             if (dir > 0) { memcpy(s->bprev, B, sizeof(int32_t) * (size_t)nB); s->nbprev = nB; }
             else { memcpy(s->lbprev, B, sizeof(int32_t) * (size_t)nB); s->nlbprev = nB; }

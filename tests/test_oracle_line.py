@@ -264,7 +264,7 @@ def test_tip_stops_on_the_boundary(oracle_mod, start, tip, face):
     {"start": (-0.5, 4.2), "tip": (6.0, 5.1)},        # outside the body
     {"start": (3.0, 4.2), "tip": (6.0, 30.0)},
     {"r0": 0.5},                                      # the K window reaches the new links
-    {"bc_mode": "macroscopic"},
+    {"bc_mode": "macroscopic_edges"},
     {"lattice": "D2Q9"},
 ])
 def test_rejected_configurations(oracle_mod, change):
@@ -412,3 +412,112 @@ def test_benchmark_line_workload_grows(oracle_mod):
     off = -(h["tip_q"] - s_q[0]) * c[1] + (h["tip_yq"] - s_q[1]) * c[0]
     assert np.abs(off).max() < 1e-6 * Q
     assert o.flags() & 1 and int(h["tip_yq"][-1]) == p["ny"] * Q
+
+
+# ------------------------------------------ the macroscopic rule (oracle only)
+
+@pytest.mark.parametrize("two", [False, True])
+def test_macroscopic_along_x_is_the_aligned_rule(oracle_mod, two):
+    """With c = (1, 0) every x_I, x_II is a site and the line's normal is the
+    face's: the rule of the aligned crack, bit for bit."""
+    p = W.base_problem(120, 48, bc_mode="macroscopic", edges=("free", "free", "dirichlet", "dirichlet"), cs=0.5)
+    p = W.with_antisymmetric_ramp(p, 2e-3, 60.0)
+    K_C = 0.5 * W.strip_reference_K(0.25, 2e-3, 48.0)
+    q1 = W.with_crack(p, mode="kcrit", y=24.0, x_start=45.0, x_tip=70.0, K_C=K_C, r0=2.0, two_tips=two)
+    q2 = W.with_line_crack(p, mode="kcrit", start=(45.0, 24.0), tip=(70.0, 24.0), K_C=K_C, r0=2.0, two_tips=two)
+    o1, o2 = oracle_mod.Oracle(q1), oracle_mod.Oracle(q2)
+    o1.step(250)
+    o2.step(250)
+    h1, h2 = o1.history(), o2.history()
+    assert h1["grew"].sum() > 10
+    np.testing.assert_array_equal(h1["tip_q"], h2["tip_q"])
+    np.testing.assert_array_equal(h1["K"], h2["K"])
+    np.testing.assert_array_equal(o1.fields()[0], o2.fields()[0])
+    np.testing.assert_array_equal(np.sort(o1.bpoints()), np.sort(o2.bpoints()))
+    assert o1.flags() == o2.flags() and not o1.flags() & 2
+
+
+@pytest.mark.parametrize("deg", [17.0, 45.0, 71.0, 143.0])
+def test_macroscopic_keeps_a_field_linear_along_the_crack(oracle_mod, deg):
+    """w = a t (t the distance along c) has no normal derivative on the crack
+    faces and is harmonic: after one step from it (with wdot = 0), every
+    boundary point of the rule holds a t(x_B) -- the quadratic's zero slope,
+    the distances s_B, s_I, s_II and the one-sided bilinear stencils all
+    have to be right for that."""
+    nx = ny = 64
+    th = math.radians(deg)
+    c, s = math.cos(th), math.sin(th)
+    mid = (32.013, 32.007)
+    start, tip = (mid[0] - 12 * c, mid[1] - 12 * s), (mid[0] + 12 * c, mid[1] + 12 * s)
+    p = W.base_problem(nx, ny, bc_mode="macroscopic", edges=("free",) * 4, cs=0.5)
+    p["loads"] = []
+    p = W.with_line_crack(p, mode="stationary", start=start, tip=tip, r0=2.0)
+    o = oracle_mod.Oracle(p)
+    cx, cy = o.direction()
+    sx, sy = np.rint(start[0] * Q) / Q, np.rint(start[1] * Q) / Q
+    X, Y = np.meshgrid(np.arange(nx) + 0.5, np.arange(ny) + 0.5)
+    a = 1e-3
+    w0 = a * ((X - sx) * cx + (Y - sy) * cy)
+    o.set_fields(w0, np.zeros_like(w0))
+    o.step(1)
+    bp = o.bpoints()
+    assert len(bp) > 20
+    w = o.fields()[0].ravel()
+    np.testing.assert_allclose(w[bp], w0.ravel()[bp], rtol=0, atol=1e-14)
+    assert o.flags() == 0
+
+
+def test_macroscopic_inclined_growth_stays_finite(oracle_mod):
+    """K-criterion growth at 30 degrees with the rule on the crack faces:
+    the run stays finite and grows (the rule's stability for this reading),
+    up to the step before the tip comes within reach of the top edge, where
+    the stencils of the points it creates would leave the body (flagged)."""
+    nx, ny = 96, 64
+    p = W.base_problem(nx, ny, bc_mode="macroscopic", edges=("free", "free", "dirichlet", "dirichlet"), cs=0.5)
+    p = W.with_antisymmetric_ramp(p, 3e-3, 40.0)
+    K_C = 0.3 * W.strip_reference_K(0.25, 3e-3, float(ny))
+    th = math.radians(30.0)
+    start = (20.3, 24.1)
+    tip = (start[0] + 15 * math.cos(th), start[1] + 15 * math.sin(th))
+    p = W.with_line_crack(p, mode="kcrit", start=start, tip=tip, K_C=K_C, r0=2.0)
+    o = oracle_mod.Oracle(p)
+    o.step(200)
+    h = o.history()
+    w = o.fields()[0]
+    assert np.isfinite(w).all() and np.abs(w).max() < 10 * 3e-3
+    assert (h["v"] > 0).sum() > 100
+    assert o.flags() == 0
+    o.step(100)                     # the tip reaches the top edge
+    assert o.flags() & 1 and o.flags() & 2
+
+
+@pytest.mark.parametrize("deg", [17.0, 45.0, 71.0, 143.0])
+def test_macroscopic_keeps_a_jump_across_the_crack(oracle_mod, deg):
+    """w = a t + g sign(d) (d the signed distance from the crack's line): on
+    each side linear along the crack, with a jump across it -- a stencil that
+    reached across the crack would mix the two sides.  After one step every
+    boundary point holds its own side's value."""
+    nx = ny = 64
+    th = math.radians(deg)
+    c, s = math.cos(th), math.sin(th)
+    mid = (32.013, 32.007)
+    start, tip = (mid[0] - 12 * c, mid[1] - 12 * s), (mid[0] + 12 * c, mid[1] + 12 * s)
+    p = W.base_problem(nx, ny, bc_mode="macroscopic", edges=("free",) * 4, cs=0.5)
+    p["loads"] = []
+    p = W.with_line_crack(p, mode="stationary", start=start, tip=tip, r0=2.0)
+    o = oracle_mod.Oracle(p)
+    cx, cy = o.direction()
+    sx, sy = np.rint(start[0] * Q) / Q, np.rint(start[1] * Q) / Q
+    X, Y = np.meshgrid(np.arange(nx) + 0.5, np.arange(ny) + 0.5)
+    t = (X - sx) * cx + (Y - sy) * cy
+    d = -(X - sx) * cy + (Y - sy) * cx
+    w0 = 1e-3 * t + 2e-3 * np.sign(d)
+    o.set_fields(w0, np.zeros_like(w0))
+    o.step(1)
+    bp = o.bpoints()
+    # the boundary points beside the crack's inner stretch (the ends' points
+    # see the field wrap around the tip, where it is no longer a solution)
+    inner = bp[(t.ravel()[bp] > 3.0) & (t.ravel()[bp] < 21.0)]
+    assert len(inner) > 20
+    w = o.fields()[0].ravel()
+    np.testing.assert_allclose(w[inner], w0.ravel()[inner], rtol=0, atol=1e-14)
