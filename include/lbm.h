@@ -183,7 +183,14 @@ typedef struct lbm_crack {
  * two_tips: 1 lets the start grow too, along -c, with its own speed memory
  * and the same opening sign (a centre crack in that direction); its K window
  * lies along +c behind it.  The other fields are those of lbm_crack.  Built
- * for D2Q5 and LBM_BC_BOUNCEBACK, with every storage. */
+ * for D2Q5 with every storage, LBM_BC_BOUNCEBACK (link-local faces) or
+ * LBM_BC_MACROSCOPIC: the macroscopic rule (Sec. 3.1) on the crack's faces,
+ * read for a crack off the lattice's axes -- a boundary point x_B takes the
+ * normal n of the crack's line, x_I = x_B + n dh and x_II = x_B + 2 n dh are
+ * interpolated bilinearly (their cells' corners all lie on x_B's side), and
+ * the points coupled through those stencils are solved together to a
+ * fixpoint; a stencil corner outside the body drops that stencil (keep the
+ * crack two spacings from the edges).  The outer edges stay link-local. */
 typedef struct lbm_crack_line {
     int32_t mode;
     int32_t two_tips;

@@ -14,6 +14,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 using namespace lbm;
@@ -134,6 +135,85 @@ std::vector<uint32_t> line_initial_masks(const LineSpec &L, int nx, int ny, int 
     return m;
 }
 
+// The boundary points of the macroscopic rule on the faces of a crack in any
+// direction (LineFace): every site within 1.5 spacings of the line (the
+// sites next to a severed link lie within one), with the stencils of x_I
+// and x_II along the line's normal and the weights of the quadratic with
+// zero slope at the line.  A stencil with a corner outside the body is
+// dropped (its value counts as 0), as the oracle's reading has it.
+std::vector<LineFace> line_faces_table(const LineSpec &L, int nx, int ny)
+{
+    const double sx = (double)L.start_xq * kTwoM32, sy = (double)L.start_yq * kTwoM32;
+    const double cx = L.dir_x, cy = L.dir_y;
+    auto dist = [&](double x, double y) { return -(x - sx) * cy + (y - sy) * cx; };
+    std::vector<std::pair<int, int>> sites;
+    const bool by_col = std::fabs(cx) >= std::fabs(cy);
+    const int n = by_col ? nx : ny, m = by_col ? ny : nx;
+    for (int l = 0; l < n; ++l) {
+        const double across = by_col ? sy + ((l + 0.5) - sx) * cy / cx : sx + ((l + 0.5) - sy) * cx / cy;
+        if (!(across > -4.0 && across < m + 4.0)) continue;
+        const int k0 = (int)std::floor(across - 3.0);
+        for (int k = k0; k <= k0 + 6; ++k) {
+            if (k < 0 || k >= m) continue;
+            const int i = by_col ? l : k, j = by_col ? k : l;
+            if (std::fabs(dist(i + 0.5, j + 0.5)) < 1.5) sites.emplace_back(i, j);
+        }
+    }
+    std::unordered_map<int64_t, int32_t> index;
+    for (size_t q = 0; q < sites.size(); ++q) index[(int64_t)sites[q].second * nx + sites[q].first] = (int32_t)q;
+    std::vector<LineFace> tab(sites.size());
+    for (size_t q = 0; q < sites.size(); ++q) {
+        LineFace &f = tab[q];
+        std::memset(&f, 0, sizeof f);
+        f.i = sites[q].first;
+        f.j = sites[q].second;
+        const double bx = f.i + 0.5, by = f.j + 0.5;
+        const double d = dist(bx, by), side = d > 0.0 ? 1.0 : -1.0;
+        const double nxv = -cy * side, nyv = cx * side;
+        const double sB = std::fabs(d), sI = sB + 1.0, sII = sB + 2.0;
+        const double qq = (sB * sB - sI * sI) / (sII * sII - sI * sI);
+        const double coef[2] = {1.0 - qq, qq};
+        int used = 0;
+        for (int pt = 0; pt < 2; ++pt) {
+            const double px = bx + (pt + 1) * nxv, py = by + (pt + 1) * nyv;
+            const double gx = px - 0.5, gy = py - 0.5;
+            const int i0 = (int)std::floor(gx), j0 = (int)std::floor(gy);
+            const double tx = gx - i0, ty = gy - j0;
+            int ci[4], cj[4];
+            double wt[4];
+            int nc = 0;
+            bool inside = true;
+            for (int dj = 0; dj <= 1; ++dj)
+                for (int di = 0; di <= 1; ++di) {
+                    const double wgt = (di ? tx : 1.0 - tx) * (dj ? ty : 1.0 - ty);
+                    if (wgt == 0.0) continue;
+                    const int ii = i0 + di, jj = j0 + dj;
+                    if (ii < 0 || ii >= nx || jj < 0 || jj >= ny) inside = false;
+                    ci[nc] = ii;
+                    cj[nc] = jj;
+                    wt[nc] = wgt;
+                    ++nc;
+                }
+            if (!inside) continue;
+            for (int c = 0; c < nc; ++c) {
+                f.ci[used] = ci[c];
+                f.cj[used] = cj[c];
+                f.a[used] = coef[pt] * wt[c];
+                const auto it = index.find((int64_t)cj[c] * nx + ci[c]);
+                f.cand[used] = it == index.end() ? -1 : it->second;
+                ++used;
+            }
+        }
+        for (int c = used; c < 8; ++c) {
+            f.ci[c] = f.i;
+            f.cj[c] = f.j;
+            f.cand[c] = -1;
+            f.a[c] = 0.0;
+        }
+    }
+    return tab;
+}
+
 }  // namespace
 
 
@@ -145,7 +225,11 @@ cudaError_t enqueue_step_t(const lbm_handle *h, int par, cudaStream_t s)
 {
     StepArgs<T, D> a;
     make_step_args(h, par, a);
-    if (h->line) return launch_line_step(a, s);
+    if (h->line) {
+        cudaError_t e = launch_line_step(a, s);
+        if (e == cudaSuccess && h->n_faces > 0) e = launch_line_faces(a, h->faces, h->n_faces, h->face_scratch, s);
+        return e;
+    }
     if constexpr (std::is_same<T, D>::value) {
         if (h->q == 9) {
             cudaError_t e = launch_d2q9_step(a, s);
@@ -408,8 +492,8 @@ lbm_status lbm_create_line(const lbm_grid *grid, const lbm_lattice *lattice, con
     if (c.mode < LBM_CRACK_STATIONARY || c.mode > LBM_CRACK_KCRIT)
         return fail(LBM_ERR_ARG, "a crack in any direction needs a stationary, prescribed or K-criterion mode");
     if (lattice->velocity_set != LBM_D2Q5) return fail(LBM_ERR_ARG, "a crack in any direction is built for D2Q5");
-    if (lattice->bc_mode != LBM_BC_BOUNCEBACK)
-        return fail(LBM_ERR_ARG, "a crack in any direction is built with link-local faces (LBM_BC_BOUNCEBACK)");
+    if (lattice->bc_mode != LBM_BC_BOUNCEBACK && lattice->bc_mode != LBM_BC_MACROSCOPIC)
+        return fail(LBM_ERR_ARG, "a crack in any direction is built with link-local edges (LBM_BC_BOUNCEBACK or LBM_BC_MACROSCOPIC)");
     if (lattice->storage < LBM_F64 || lattice->storage > LBM_F32_WD_F16) return fail(LBM_ERR_ARG, "unknown storage");
     if (grid->nx < 1 || grid->ny < 2 || !(grid->dh > 0.0) || !std::isfinite(grid->dh))
         return fail(LBM_ERR_ARG, "need nx >= 1, ny >= 2 and a positive, finite dh");
@@ -757,6 +841,27 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
         const int64_t slots = (int64_t)h->sms * std::max(bps_line, 1) - 1;
         const int64_t nb = std::max<int64_t>(1, slots / h->ncb);
         cp.band = (int32_t)std::max<int64_t>(1, (grid->ny + nb - 1) / nb);
+        if (macro_faces) {
+            // the macroscopic rule on the crack's faces: the tabulated points
+            const std::vector<LineFace> tab = line_faces_table(*line, grid->nx, grid->ny);
+            h->n_faces = (int32_t)tab.size();
+            if (!tab.empty()) {
+                h->faces = static_cast<LineFace *>(dev_alloc(h, tab.size() * sizeof(LineFace)));
+                h->face_scratch = static_cast<double *>(dev_alloc(h, tab.size() * 20));
+                if (!h->faces || !h->face_scratch) {
+                    dev_free(h, h->faces);
+                    dev_free(h, h->face_scratch);
+                    return bail(fail(LBM_ERR_OOM, "device allocation failed"));
+                }
+                e = cudaMemcpyAsync(h->faces, tab.data(), tab.size() * sizeof(LineFace), cudaMemcpyHostToDevice, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                if (e != cudaSuccess) {
+                    dev_free(h, h->faces);
+                    dev_free(h, h->face_scratch);
+                    return bail(cuda_fail(e, "writing the boundary points"));
+                }
+            }
+        }
     }
     cp.hist_cap = cr.mode != LBM_CRACK_NONE ? cr.hist_cap : 0;
 
@@ -1459,6 +1564,8 @@ void lbm_destroy(lbm_handle *h)
         delete h->ev;
         delete h->ev_kind;
     }
+    dev_free(h, h->faces);
+    dev_free(h, h->face_scratch);
     dev_free(h, h->block);
     free_host(h);
 }

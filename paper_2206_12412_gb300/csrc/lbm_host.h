@@ -4,6 +4,7 @@
 
 #include "lbm.h"
 #include "lbm_internal.cuh"
+#include "lbm_line.cuh"
 
 typedef struct lbm_batch lbm_batch;
 
@@ -31,6 +32,9 @@ struct lbm_handle {
     bool edge_macro;     // the macroscopic rule on the outer edges (one more kernel per step)
     int32_t q;           // velocity set: 5 or 9 (D2Q9: its own update kernel and a crack kernel per step)
     bool line;           // a straight crack in any direction (line_step_kernel)
+    lbm::LineFace *faces;  // its tabulated boundary points (macroscopic faces), device
+    int32_t n_faces;
+    double *face_scratch;  // the face kernel's iterates and activity, device
     // step kernel shape
     int32_t ncb;         // column blocks of kThreads vectors
     int32_t n_bands, band_rows, crack_band, sms, bps;

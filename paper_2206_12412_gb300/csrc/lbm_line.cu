@@ -30,6 +30,7 @@
 // changed during the launch.
 #include "lbm_crack.cuh"
 #include "lbm_internal.cuh"
+#include "lbm_line.cuh"
 #include "lbm_rows.cuh"
 
 namespace lbm {
@@ -744,6 +745,67 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
     claimed_groups<T, D>(a, E, C, u, n_march);
 }
 
+// The macroscopic rule on the faces of a crack in any direction (Sec. 3.1),
+// after the march: one CTA takes every tabulated point whose site has a
+// severed link, sets cur = the updated w of every point, then sweeps
+// w_B = sum_k a_k w(corner_k) over the active points (a corner that is a
+// point reads its value in cur) until a sweep changes no bit (256 sweeps at
+// most), and writes w_B and wdot_B = (w_B - w_B(t)) / dt.
+template <typename T, typename D>
+__global__ void __launch_bounds__(1024) line_faces_kernel(const StepArgs<T, D> a, const LineFace *F, int nf,
+                                                          double *cur, double *nxt, int32_t *active)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int64_t P = a.pitch;
+    const int words = a.words, nx = a.nx, ny = a.ny;
+    for (int c = tid; c < nf; c += nt) {
+        const int i = F[c].i, j = F[c].j;
+        const uint32_t *ch = a.cut_h + (int64_t)j * words, *cv = a.cut_v + (int64_t)j * words;
+        bool cut = (ch[i >> 5] >> (i & 31)) & 1u;
+        if (i >= 1) cut |= (ch[(i - 1) >> 5] >> ((i - 1) & 31)) & 1u;
+        if (j + 1 < ny) cut |= (cv[i >> 5] >> (i & 31)) & 1u;
+        if (j >= 1) cut |= ((cv - words)[i >> 5] >> (i & 31)) & 1u;
+        active[c] = cut ? 1 : 0;
+        cur[c] = (double)a.w_out[(int64_t)j * P + i];
+    }
+    __syncthreads();
+    for (int sweep = 0; sweep < 256; ++sweep) {
+        int changed = 0;
+        for (int c = tid; c < nf; c += nt) {
+            if (!active[c]) continue;
+            double v = 0.0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const LineFace &f = F[c];
+                if (f.a[k] == 0.0) continue;
+                const double wk = f.cand[k] >= 0 ? cur[f.cand[k]] : (double)a.w_out[(int64_t)f.cj[k] * P + f.ci[k]];
+                v += f.a[k] * wk;
+            }
+            nxt[c] = v;
+            changed |= v != cur[c];
+        }
+        changed = __syncthreads_or(changed);
+        if (!changed) break;
+        for (int c = tid; c < nf; c += nt)
+            if (active[c]) cur[c] = nxt[c];
+        __syncthreads();
+    }
+    const T inv_dt = (T)1 / a.dt;
+    bool bad = false;
+    for (int c = tid; c < nf; c += nt) {
+        if (!active[c]) continue;
+        const int i = F[c].i, j = F[c].j;
+        const int64_t o = (int64_t)j * P + i;
+        const T wB = (T)cur[c];
+        a.w_out[o] = wB;
+        WdIO<D>::put(a.wd + o, (wB - a.w_in[o]) * inv_dt, a.wd_scale);
+        site_pads(a, i, j, wB);
+        bad |= !isfinite(wB);
+        (void)nx;
+    }
+    if (bad) atomicOr(a.err, (uint32_t)ERR_NONFINITE);
+}
+
 // The pending crack step before the host reads the state (one warp).
 template <typename T>
 __global__ void line_finalize_kernel(const FinalizeArgs<T> a)
@@ -760,6 +822,16 @@ __global__ void line_finalize_kernel(const FinalizeArgs<T> a)
 }
 
 }  // namespace
+
+template <typename T, typename D>
+cudaError_t launch_line_faces(const StepArgs<T, D> &a, const LineFace *faces, int nf, double *scratch, cudaStream_t s)
+{
+    if (nf <= 0) return cudaSuccess;
+    double *cur = scratch, *nxt = scratch + nf;
+    int32_t *active = reinterpret_cast<int32_t *>(scratch + 2 * (size_t)nf);
+    line_faces_kernel<T, D><<<1, 1024, 0, s>>>(a, faces, nf, cur, nxt, active);
+    return cudaGetLastError();
+}
 
 template <typename T, typename D>
 cudaError_t launch_line_step(const StepArgs<T, D> &a, cudaStream_t s)
@@ -786,6 +858,14 @@ template const void *line_step_kernel_ptr<double, double>();
 template const void *line_step_kernel_ptr<float, float>();
 template const void *line_step_kernel_ptr<float, __nv_bfloat16>();
 template const void *line_step_kernel_ptr<float, __half>();
+template cudaError_t launch_line_faces<double, double>(const StepArgs<double, double> &, const LineFace *, int,
+                                                      double *, cudaStream_t);
+template cudaError_t launch_line_faces<float, float>(const StepArgs<float, float> &, const LineFace *, int, double *,
+                                                    cudaStream_t);
+template cudaError_t launch_line_faces<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> &, const LineFace *,
+                                                            int, double *, cudaStream_t);
+template cudaError_t launch_line_faces<float, __half>(const StepArgs<float, __half> &, const LineFace *, int, double *,
+                                                     cudaStream_t);
 template cudaError_t launch_line_step<double, double>(const StepArgs<double, double> &, cudaStream_t);
 template cudaError_t launch_line_step<float, float>(const StepArgs<float, float> &, cudaStream_t);
 template cudaError_t launch_line_step<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> &, cudaStream_t);

@@ -131,7 +131,7 @@ def _line_structs(**over):
     ({"cr__mode": 0}, "K-criterion mode"),
     ({"cr__mode": 5}, "K-criterion mode"),
     ({"lat__velocity_set": 1}, "D2Q5"),
-    ({"lat__bc_mode": 1}, "link-local"),
+    ({"lat__bc_mode": 2}, "link-local edges"),
     ({"lat__storage": 7}, "storage"),
     ({"cr__r0": 0.5}, "dh / 2"),
     ({"cr__r0": 0.0, "cr__r_min": 0.4}, "dh / 2"),

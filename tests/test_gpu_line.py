@@ -383,3 +383,41 @@ def test_sixteen_bit_wdot(oracle_mod, gpu, storage, two):
     assert np.abs(wg - wo).max() < BOUND_16[storage] * np.abs(wo).max()
     _masks(o, g)
     _tips(o, g, 150)
+
+
+# ------------------------------------------ the macroscopic rule on the faces
+
+def _macro(nx, ny, u0=3e-3, t_ramp=40.0):
+    p = _problem(nx, ny, u0=u0, t_ramp=t_ramp)
+    p["bc_mode"] = "macroscopic"
+    return p
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("deg,two", [(23.0, False), (137.0, False), (61.0, True)])
+def test_macroscopic_faces_prescribed(oracle_mod, gpu, storage, deg, two):
+    nx, ny = 300, 200
+    start, tip = _centre(nx, ny, deg, 20.0)
+    p = W.with_line_crack(_macro(nx, ny), mode="prescribed", start=start, tip=tip, v_rel=0.6, r0=2.0, two_tips=two)
+    # 70 steps: the solve along these lines meets its bitwise fixpoint
+    # throughout (the oracle flags a solve that ends without one)
+    o, g = _run(oracle_mod, gpu, p, storage, [7, 40, 23])
+    assert o.flags() == 0
+    _close(o, g, TOL[storage])
+    _masks(o, g)
+    _tips(o, g, 70)
+
+
+def test_macroscopic_faces_kcrit_fp64(oracle_mod, gpu):
+    nx, ny = 160, 48
+    start, tip = _centre(nx, ny, 23.0, 10.0)
+    p = _macro(nx, ny, u0=4e-3, t_ramp=10.0)
+    K_C = 0.2 * W.strip_reference_K(0.25, 4e-3, float(ny))
+    p = W.with_line_crack(p, mode="kcrit", start=start, tip=tip, K_C=K_C, v_max=0.85, r0=2.0, two_tips=True)
+    o, g = _run(oracle_mod, gpu, p, "f64", [60, 80])
+    assert o.flags() == 0
+    ho, hg = _tips(o, g, 140)
+    assert (ho["v"] > 0).sum() > 10 and (o.history_left()["v"] > 0).sum() > 10
+    np.testing.assert_allclose(hg["K"], ho["K"], rtol=0, atol=1e-9 * np.abs(ho["K"]).max())
+    _masks(o, g)
+    _close(o, g, TOL["f64"])
