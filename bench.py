@@ -509,6 +509,10 @@ def run_ours(args, rank, world, local):
     if args.profile_only and args.crack == "line":
         # the workload with its crack at 20 degrees (line_step_kernel), for its profile
         problem = W.kcrit_line()
+    if args.profile_only and args.crack == "line_macro":
+        # a centre crack at 20 degrees with the macroscopic rule on its faces
+        # (line_step_kernel, then line_faces_kernel), for its profile
+        problem = W.kcrit_line_centre()
     sites = problem["nx"] * problem["ny"]
     stream = torch.cuda.current_stream()
     lat = lbm.Lattice(problem, "f32", stream=stream)
@@ -687,8 +691,9 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=None, help="steps of the adjoint workload (default 8000)")
     ap.add_argument("--lattice", default="D2Q5", choices=["D2Q5", "D2Q9"],
                     help="with --profile-only: the velocity set of the profiled workload")
-    ap.add_argument("--crack", default="x", choices=["x", "line"],
-                    help="with --profile-only: the crack of the profiled workload (along +x, or at 20 degrees)")
+    ap.add_argument("--crack", default="x", choices=["x", "line", "line_macro"],
+                    help="with --profile-only: the crack of the profiled workload (along +x, or at 20 degrees; "
+                         "line_macro: a centre crack at 20 degrees with the macroscopic rule on its faces)")
     ap.add_argument("--profile-only", action="store_true",
                     help="only prelude, warm-up and timed steps (for ncu); prints kernel times")
     args = ap.parse_args()

@@ -847,7 +847,7 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
             h->n_faces = (int32_t)tab.size();
             if (!tab.empty()) {
                 h->faces = static_cast<LineFace *>(dev_alloc(h, tab.size() * sizeof(LineFace)));
-                h->face_scratch = static_cast<double *>(dev_alloc(h, tab.size() * 20));
+                h->face_scratch = static_cast<double *>(dev_alloc(h, tab.size() * lbm::kLineFaceScratch));
                 if (!h->faces || !h->face_scratch) {
                     dev_free(h, h->faces);
                     dev_free(h, h->face_scratch);

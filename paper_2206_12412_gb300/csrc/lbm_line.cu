@@ -746,18 +746,28 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
 }
 
 // The macroscopic rule on the faces of a crack in any direction (Sec. 3.1),
-// after the march: one CTA takes every tabulated point whose site has a
-// severed link, sets cur = the updated w of every point, then sweeps
-// w_B = sum_k a_k w(corner_k) over the active points (a corner that is a
-// point reads its value in cur) until a sweep changes no bit (256 sweeps at
-// most), and writes w_B and wdot_B = (w_B - w_B(t)) / dt.
+// after the march, in one CTA.  It lists the tabulated points whose site has
+// a severed link (the list's order is immaterial: each sweep reads only the
+// previous sweep's values) and, per point, sums once the terms of the
+// corners that are not points (their w is this step's update, fixed during
+// the solve) and notes the list positions of the corners that are.  Then it
+// sweeps w_B = base + sum over the coupled corners of a_k w_B(corner), the
+// values of two sweeps held in shared memory (in the scratch when the points
+// outnumber it), until a sweep changes no bit (256 sweeps at most), and
+// writes w_B and wdot_B = (w_B - w_B(t)) / dt.
+constexpr int kFaceShared = 3008;   // points whose two sweep values fit in 48 KB of static shared memory
+
 template <typename T, typename D>
 __global__ void __launch_bounds__(1024) line_faces_kernel(const StepArgs<T, D> a, const LineFace *F, int nf,
-                                                          double *cur, double *nxt, int32_t *active)
+                                                          FaceScratch z)
 {
+    __shared__ double sA[kFaceShared], sB[kFaceShared];
+    __shared__ int n_act;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int64_t P = a.pitch;
-    const int words = a.words, nx = a.nx, ny = a.ny;
+    const int words = a.words, ny = a.ny;
+    if (tid == 0) n_act = 0;
+    __syncthreads();
     for (int c = tid; c < nf; c += nt) {
         const int i = F[c].i, j = F[c].j;
         const uint32_t *ch = a.cut_h + (int64_t)j * words, *cv = a.cut_v + (int64_t)j * words;
@@ -765,43 +775,69 @@ __global__ void __launch_bounds__(1024) line_faces_kernel(const StepArgs<T, D> a
         if (i >= 1) cut |= (ch[(i - 1) >> 5] >> ((i - 1) & 31)) & 1u;
         if (j + 1 < ny) cut |= (cv[i >> 5] >> (i & 31)) & 1u;
         if (j >= 1) cut |= ((cv - words)[i >> 5] >> (i & 31)) & 1u;
-        active[c] = cut ? 1 : 0;
-        cur[c] = (double)a.w_out[(int64_t)j * P + i];
+        int q = -1;
+        if (cut) {
+            q = atomicAdd(&n_act, 1);
+            z.list[q] = c;
+        }
+        z.pos[c] = q;
+    }
+    __syncthreads();
+    const int na = n_act;
+    double *cur = na <= kFaceShared ? sA : z.buf_a;
+    double *nxt = na <= kFaceShared ? sB : z.buf_b;
+    for (int q = tid; q < na; q += nt) {
+        const LineFace &f = F[z.list[q]];
+        double base = 0.0;
+        uint32_t mask = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (f.a[k] == 0.0) continue;
+            const int m = f.cand[k];
+            const int pm = m >= 0 ? z.pos[m] : -1;
+            if (pm >= 0) {
+                mask |= 1u << k;
+                z.kpos[8 * (int64_t)q + k] = pm;
+            } else {
+                base += f.a[k] * (double)a.w_out[(int64_t)f.cj[k] * P + f.ci[k]];
+            }
+        }
+        z.base[q] = base;
+        z.mask[q] = mask;
+        cur[q] = (double)a.w_out[(int64_t)f.j * P + f.i];
     }
     __syncthreads();
     for (int sweep = 0; sweep < 256; ++sweep) {
         int changed = 0;
-        for (int c = tid; c < nf; c += nt) {
-            if (!active[c]) continue;
-            double v = 0.0;
+        for (int q = tid; q < na; q += nt) {
+            const LineFace &f = F[z.list[q]];
+            const uint32_t mask = z.mask[q];
+            double v = z.base[q];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const LineFace &f = F[c];
-                if (f.a[k] == 0.0) continue;
-                const double wk = f.cand[k] >= 0 ? cur[f.cand[k]] : (double)a.w_out[(int64_t)f.cj[k] * P + f.ci[k]];
-                v += f.a[k] * wk;
-            }
-            nxt[c] = v;
-            changed |= v != cur[c];
+            for (int k = 0; k < 8; ++k)
+                if ((mask >> k) & 1u) v += f.a[k] * cur[z.kpos[8 * (int64_t)q + k]];
+            nxt[q] = v;
+            changed |= v != cur[q];
         }
+        // every read of cur and write of nxt of this sweep is done: the next
+        // sweep reads nxt and overwrites cur
         changed = __syncthreads_or(changed);
+        double *t = cur;
+        cur = nxt;
+        nxt = t;
         if (!changed) break;
-        for (int c = tid; c < nf; c += nt)
-            if (active[c]) cur[c] = nxt[c];
-        __syncthreads();
     }
     const T inv_dt = (T)1 / a.dt;
     bool bad = false;
-    for (int c = tid; c < nf; c += nt) {
-        if (!active[c]) continue;
+    for (int q = tid; q < na; q += nt) {
+        const int c = z.list[q];
         const int i = F[c].i, j = F[c].j;
         const int64_t o = (int64_t)j * P + i;
-        const T wB = (T)cur[c];
+        const T wB = (T)cur[q];
         a.w_out[o] = wB;
         WdIO<D>::put(a.wd + o, (wB - a.w_in[o]) * inv_dt, a.wd_scale);
         site_pads(a, i, j, wB);
         bad |= !isfinite(wB);
-        (void)nx;
     }
     if (bad) atomicOr(a.err, (uint32_t)ERR_NONFINITE);
 }
@@ -827,9 +863,16 @@ template <typename T, typename D>
 cudaError_t launch_line_faces(const StepArgs<T, D> &a, const LineFace *faces, int nf, double *scratch, cudaStream_t s)
 {
     if (nf <= 0) return cudaSuccess;
-    double *cur = scratch, *nxt = scratch + nf;
-    int32_t *active = reinterpret_cast<int32_t *>(scratch + 2 * (size_t)nf);
-    line_faces_kernel<T, D><<<1, 1024, 0, s>>>(a, faces, nf, cur, nxt, active);
+    // the scratch holds kLineFaceScratch bytes per tabulated point
+    FaceScratch z;
+    z.buf_a = scratch;
+    z.buf_b = z.buf_a + nf;
+    z.base = z.buf_b + nf;
+    z.list = reinterpret_cast<int32_t *>(z.base + nf);
+    z.pos = z.list + nf;
+    z.mask = reinterpret_cast<uint32_t *>(z.pos + nf);
+    z.kpos = reinterpret_cast<int32_t *>(z.mask + nf);
+    line_faces_kernel<T, D><<<1, 1024, 0, s>>>(a, faces, nf, z);
     return cudaGetLastError();
 }
 

@@ -24,6 +24,19 @@ struct LineFace {
     double a[8];
 };
 
+// The device scratch of the face solve, per tabulated point: two sweeps'
+// values (used when the points outnumber the kernel's shared memory), the
+// fixed part of each point's sum, the list of points, each table entry's
+// position in it (-1: not a point), the mask of coupled corners and their
+// list positions.
+struct FaceScratch {
+    double *buf_a, *buf_b, *base;
+    int32_t *list, *pos;
+    uint32_t *mask;
+    int32_t *kpos;
+};
+constexpr size_t kLineFaceScratch = 3 * sizeof(double) + 3 * sizeof(int32_t) + 8 * sizeof(int32_t);
+
 template <typename T, typename D>
 cudaError_t launch_line_faces(const StepArgs<T, D> &a, const LineFace *faces, int nf, double *scratch, cudaStream_t s);
 

@@ -112,6 +112,25 @@ def kcrit_line(scale: int = 1, seed: int = 2, degrees: float = 20.0) -> dict:
     return with_antisymmetric_ramp(p, 2e-3, 5000.0 / scale)
 
 
+def kcrit_line_centre(scale: int = 1, seed: int = 2, degrees: float = 20.0, bc_mode: str = "macroscopic") -> dict:
+    """kcrit_line with a centre crack instead: length 512 / scale at `degrees`
+    to +x through the middle of the body (offset by a small fraction of a
+    spacing, so that its line meets no site centre), both ends growing, the
+    macroscopic rule on its faces by default (its stencils stay inside the
+    body, which an edge crack's would not at the mouth)."""
+    nx, ny = 4096 // scale, 2048 // scale
+    rng = np.random.default_rng(seed)
+    K_C = 0.35 * strip_reference_K(0.25, 2e-3, float(ny)) * (1.0 + 0.1 * rng.uniform(-1.0, 1.0))
+    th = math.radians(degrees)
+    half = 256.0 / scale
+    mid = (nx / 2 + 0.013, ny / 2 + 0.007)
+    start = (mid[0] - half * math.cos(th), mid[1] - half * math.sin(th))
+    tip = (mid[0] + half * math.cos(th), mid[1] + half * math.sin(th))
+    p = base_problem(nx, ny, bc_mode=bc_mode)
+    p = with_line_crack(p, mode="kcrit", start=start, tip=tip, K_C=K_C, v_max=0.85, r0=2.0, two_tips=True)
+    return with_antisymmetric_ramp(p, 2e-3, 5000.0 / scale)
+
+
 def kcrit_centre_crack(scale: int = 1, bc_mode: str = "macroscopic_edges") -> dict:
     """The K-criterion example of Sec. 5.2 with L = 64 / scale dh: an 8L x 3L
     body (512 x 192 sites at scale 1), a centre crack of length L on the line

@@ -421,3 +421,17 @@ def test_macroscopic_faces_kcrit_fp64(oracle_mod, gpu):
     np.testing.assert_allclose(hg["K"], ho["K"], rtol=0, atol=1e-9 * np.abs(ho["K"]).max())
     _masks(o, g)
     _close(o, g, TOL["f64"])
+
+
+def test_macroscopic_faces_beyond_the_kernels_shared_memory(oracle_mod, gpu):
+    """A centre crack long enough that its boundary points outnumber the face
+    solve's shared memory (3008 points), so the sweeps run in its scratch."""
+    nx, ny = 1800, 300
+    start, tip = _centre(nx, ny, 8.0, 860.0)
+    p = W.with_line_crack(_macro(nx, ny), mode="prescribed", start=start, tip=tip, v_rel=0.5, r0=2.0, two_tips=True)
+    o, g = _run(oracle_mod, gpu, p, "f64", [5, 7])
+    assert len(o.bpoints()) > 3008
+    assert o.flags() == 0
+    _close(o, g, TOL["f64"])
+    _masks(o, g)
+    _tips(o, g, 12)
