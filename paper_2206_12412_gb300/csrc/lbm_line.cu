@@ -754,7 +754,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
 // sweeps w_B = base + sum over the coupled corners of a_k w_B(corner), the
 // values of two sweeps held in shared memory (in the scratch when the points
 // outnumber it), until a sweep changes no bit (256 sweeps at most), and
-// writes w_B and wdot_B = (w_B - w_B(t)) / dt.
+// writes w_B and wdot_B = (w_B - w_B(t)) / dt.  Every corner but the point's
+// own site lies farther from the line than the point (each is the point plus
+// a lattice step in the normal's quadrant), so the coupling is acyclic apart
+// from that one term; solving it within the sweep leaves as many sweeps as
+// the coupling is deep.
 constexpr int kFaceShared = 3008;   // points whose two sweep values fit in 48 KB of static shared memory
 
 template <typename T, typename D>
@@ -812,12 +816,25 @@ __global__ void __launch_bounds__(1024) line_faces_kernel(const StepArgs<T, D> a
         for (int q = tid; q < na; q += nt) {
             const LineFace &f = F[z.list[q]];
             const uint32_t mask = z.mask[q];
-            double v = z.base[q];
+            double v = z.base[q], a_self = 0.0;
 #pragma unroll
             for (int k = 0; k < 8; ++k)
-                if ((mask >> k) & 1u) v += f.a[k] * cur[z.kpos[8 * (int64_t)q + k]];
-            nxt[q] = v;
-            changed |= v != cur[q];
+                if ((mask >> k) & 1u) {
+                    const int pk = z.kpos[8 * (int64_t)q + k];
+                    if (pk == q) a_self += f.a[k];
+                    else v += f.a[k] * cur[pk];
+                }
+            // the point's own site is a corner of its x_I cell (weight > 0,
+            // below 1): solve x = v + a_self x for it here, by iteration from
+            // its last value (monotone, so it settles in a few steps)
+            double x = cur[q];
+            for (int it = 0; it < 64; ++it) {
+                const double y = v + a_self * x;
+                if (y == x) break;
+                x = y;
+            }
+            nxt[q] = x;
+            changed |= x != cur[q];
         }
         // every read of cur and write of nxt of this sweep is done: the next
         // sweep reads nxt and overwrites cur
