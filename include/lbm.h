@@ -189,8 +189,10 @@ typedef struct lbm_crack {
  * normal n of the crack's line, x_I = x_B + n dh and x_II = x_B + 2 n dh are
  * interpolated bilinearly (their cells' corners all lie on x_B's side), and
  * the points coupled through those stencils are solved together to a
- * fixpoint; a stencil corner outside the body drops that stencil (keep the
- * crack two spacings from the edges).  The outer edges stay link-local. */
+ * fixpoint.  LBM_ERR_ARG when a point of the initial crack has its x_I or
+ * x_II cell outside the body; a point the crack reaches later with such a
+ * cell drops that stencil (keep the crack two spacings from the edges).
+ * The outer edges stay link-local. */
 typedef struct lbm_crack_line {
     int32_t mode;
     int32_t two_tips;

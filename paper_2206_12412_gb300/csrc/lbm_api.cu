@@ -140,8 +140,8 @@ std::vector<uint32_t> line_initial_masks(const LineSpec &L, int nx, int ny, int 
 // sites next to a severed link lie within one), with the stencils of x_I
 // and x_II along the line's normal and the weights of the quadratic with
 // zero slope at the line.  A stencil with a corner outside the body is
-// dropped (its value counts as 0), as the oracle's reading has it.
-std::vector<LineFace> line_faces_table(const LineSpec &L, int nx, int ny)
+// dropped (its value counts as 0) and the entry marked in `dropped`.
+std::vector<LineFace> line_faces_table(const LineSpec &L, int nx, int ny, std::vector<uint8_t> *dropped = nullptr)
 {
     const double sx = (double)L.start_xq * kTwoM32, sy = (double)L.start_yq * kTwoM32;
     const double cx = L.dir_x, cy = L.dir_y;
@@ -162,6 +162,7 @@ std::vector<LineFace> line_faces_table(const LineSpec &L, int nx, int ny)
     std::unordered_map<int64_t, int32_t> index;
     for (size_t q = 0; q < sites.size(); ++q) index[(int64_t)sites[q].second * nx + sites[q].first] = (int32_t)q;
     std::vector<LineFace> tab(sites.size());
+    if (dropped) dropped->assign(sites.size(), 0);
     for (size_t q = 0; q < sites.size(); ++q) {
         LineFace &f = tab[q];
         std::memset(&f, 0, sizeof f);
@@ -194,7 +195,10 @@ std::vector<LineFace> line_faces_table(const LineSpec &L, int nx, int ny)
                     wt[nc] = wgt;
                     ++nc;
                 }
-            if (!inside) continue;
+            if (!inside) {
+                if (dropped) (*dropped)[q] = 1;
+                continue;
+            }
             for (int c = 0; c < nc; ++c) {
                 f.ci[used] = ci[c];
                 f.cj[used] = cj[c];
@@ -526,6 +530,22 @@ lbm_status lbm_create_line(const lbm_grid *grid, const lbm_lattice *lattice, con
     L.dir_x = dx / len;
     L.dir_y = dy / len;
     if (line_hits_a_centre(L, grid->nx, grid->ny)) return fail(LBM_ERR_ARG, "the crack's line passes through a site centre");
+    if (lattice->bc_mode == LBM_BC_MACROSCOPIC) {
+        // every point of the initial crack (a site with a severed link) needs
+        // its x_I and x_II cells inside the body
+        std::vector<uint8_t> dropped;
+        const std::vector<LineFace> tab = line_faces_table(L, grid->nx, grid->ny, &dropped);
+        const int words = (grid->nx + 31) / 32;
+        const std::vector<uint32_t> m = line_initial_masks(L, grid->nx, grid->ny, words);
+        const size_t vo = (size_t)grid->ny * words;
+        auto cut = [&](size_t off, int i, int j) { return ((m[off + (size_t)j * words + (size_t)(i >> 5)] >> (i & 31)) & 1u) != 0; };
+        for (size_t q = 0; q < tab.size(); ++q) {
+            if (!dropped[q]) continue;
+            const int i = tab[q].i, j = tab[q].j;
+            if (cut(0, i, j) || (i >= 1 && cut(0, i - 1, j)) || (j + 1 < grid->ny && cut(vo, i, j)) || (j >= 1 && cut(vo, i, j - 1)))
+                return fail(LBM_ERR_ARG, "macroscopic crack faces: a point of the initial crack has its x_I or x_II cell outside the body (keep the crack two spacings from the edges)");
+        }
+    }
     // the rows its links can touch: from the start to where the line leaves
     // the body, widened by three rows
     const double sx = (double)L.start_xq * kTwoM32, sy = (double)L.start_yq * kTwoM32;

@@ -144,6 +144,9 @@ def _line_structs(**over):
     ({"cr__mode": 3, "cr__K_C": 0.0}, "K_C"),
     ({"g__dh": 0.0}, "dh"),
     ({"cr__two_tips": 2}, "two_tips"),
+    # the macroscopic rule: an edge crack's mouth, a crack one spacing from the bottom edge
+    ({"lat__bc_mode": 1, "cr__x_start": 0.0, "cr__y_start": 16.3, "cr__x_tip": 8.0, "cr__y_tip": 19.1}, "outside the body"),
+    ({"lat__bc_mode": 1, "cr__y_start": 1.2, "cr__y_tip": 5.9}, "outside the body"),
 ])
 def test_create_line_rejects_bad_arguments(lib, over, msg):
     g, lat, mat, cr, loads, keep = _line_structs(**over)
@@ -151,6 +154,18 @@ def test_create_line_rejects_bad_arguments(lib, over, msg):
         lbm.lbm_create_line(g, lat, mat, cr, loads, 0, None)
     assert ei.value.status == A.LBM_ERR_ARG
     assert msg in str(ei.value)
+
+
+def test_create_line_accepts_macroscopic_faces_inside_the_body(lib):
+    """The same crack inside the body passes every check with the macroscopic
+    rule (without a GPU the call stops later, at the device query)."""
+    g, lat, mat, cr, loads, keep = _line_structs(lat__bc_mode=1)
+    try:
+        h = lbm.lbm_create_line(g, lat, mat, cr, loads, 0, None)
+    except lbm.LbmError as e:
+        assert e.status != A.LBM_ERR_ARG, str(e)
+    else:
+        lbm.lbm_destroy(h)
 
 
 def test_create_rejects_unpaired_periodic_and_bad_loads(lib):
