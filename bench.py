@@ -416,6 +416,28 @@ def measure_extensions(lbm, W, torch, stream, problem, peak, flush_l2, steps=100
             "timing": "library CUDA events around each step's launch, L2 flushed before each step"}
     lat.close()
 
+    # a centre crack at 20 degrees with the macroscopic rule on its faces
+    # (line_step_kernel, then line_faces_kernel's fixpoint solve); a failure
+    # is reported in its entry rather than ending the other measurements
+    try:
+        qm = W.kcrit_line_centre()
+        lat = lbm.Lattice(qm, "f32", stream=stream)
+        lat.step(2500)
+        lat.set_profiling(True)
+        for _ in range(steps):
+            flush_l2()
+            lat.step(1)
+        lat.sync()
+        pr = lat.profile(reset=True)
+        km = pr["step_ms"] / max(pr["n_step"], 1) * 1e-3
+        line_macro = {"workload": "kcrit_line_centre 4096x2048, centre crack at 20 degrees, macroscopic faces, f32",
+                      "step_us": km * 1e6, "glups": sites / km / 1e9, "launches_per_step": 2,
+                      "kernels": "line_step_kernel<float>, line_faces_kernel<float>",
+                      "timing": "library CUDA events around each step's launches, L2 flushed before each step"}
+        lat.close()
+    except lbm.LbmError as e:
+        line_macro = {"error": str(e)[:300]}
+
     p = W.kcrit_centre_crack()
     n = W.KCRIT_CENTRE_STEPS
     lat = lbm.Lattice(p, "f32", stream=stream)
@@ -458,7 +480,8 @@ def measure_extensions(lbm, W, torch, stream, problem, peak, flush_l2, steps=100
     b.close()
     for l in lats:
         l.close()
-    return {"d2q9": d2q9, "line_crack": line, "centre_crack_sec52": centre, "centre_crack_sweep": sweep}
+    return {"d2q9": d2q9, "line_crack": line, "line_crack_macroscopic": line_macro, "centre_crack_sec52": centre,
+            "centre_crack_sweep": sweep}
 
 
 def measure_virtual_ranks(lbm, W, torch, stream, problem, steps=256):
