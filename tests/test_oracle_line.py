@@ -521,3 +521,43 @@ def test_macroscopic_keeps_a_jump_across_the_crack(oracle_mod, deg):
     assert len(inner) > 20
     w = o.fields()[0].ravel()
     np.testing.assert_allclose(w[inner], w0.ravel()[inner], rtol=0, atol=1e-14)
+
+
+def test_macroscopic_stencils_reach_only_away_from_the_line():
+    """The geometry the face solve rests on (Sec. 3.1 read for a crack off the
+    lattice's axes): every corner with weight of the x_I = x_B + n and
+    x_II = x_B + 2n cells lies strictly farther from the line than x_B, on
+    its side, except x_B's own site in the x_I cell, whose weight in w_B
+    stays below 0.2; so the points' coupling is acyclic apart from that term."""
+    rng = np.random.default_rng(7)
+    for _ in range(400):
+        th = rng.uniform(0.0, 2 * np.pi)
+        c = np.array([np.cos(th), np.sin(th)])
+        if min(abs(c[0]), abs(c[1])) < 1e-3:
+            continue
+        s0 = rng.uniform(0.0, 1.0, 2)
+        for i in range(-3, 4):
+            for j in range(-3, 4):
+                b = np.array([i + 0.5, j + 0.5])
+                d = -(b[0] - s0[0]) * c[1] + (b[1] - s0[1]) * c[0]
+                if not (0.0 < abs(d) < 1.5):
+                    continue
+                n = np.sign(d) * np.array([-c[1], c[0]])
+                sB, sI, sII = abs(d), abs(d) + 1.0, abs(d) + 2.0
+                qq = (sB ** 2 - sI ** 2) / (sII ** 2 - sI ** 2)
+                for m, coef in ((1, 1.0 - qq), (2, qq)):
+                    g = b + m * n - 0.5
+                    i0, j0 = np.floor(g).astype(int)
+                    t = g - np.array([i0, j0])
+                    for di in (0, 1):
+                        for dj in (0, 1):
+                            wgt = (t[0] if di else 1 - t[0]) * (t[1] if dj else 1 - t[1])
+                            if wgt == 0.0:
+                                continue
+                            k = np.array([i0 + di + 0.5, j0 + dj + 0.5])
+                            dk = -(k[0] - s0[0]) * c[1] + (k[1] - s0[1]) * c[0]
+                            assert np.sign(dk) == np.sign(d)
+                            if np.allclose(k, b):
+                                assert m == 1 and 0.0 < coef * wgt < 0.2
+                            else:
+                                assert abs(dk) > abs(d) + 1e-9
