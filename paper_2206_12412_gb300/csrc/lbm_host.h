@@ -34,7 +34,7 @@ struct lbm_handle {
     bool line;           // a straight crack in any direction (line_step_kernel)
     lbm::LineFace *faces;  // its tabulated boundary points (macroscopic faces), device
     int32_t n_faces;
-    double *face_scratch;  // the face kernel's iterates and activity, device
+    double *face_scratch;  // the face solve's scratch (lbm::FaceScratch, kLineFaceScratch bytes per point), device
     // step kernel shape
     int32_t ncb;         // column blocks of kThreads vectors
     int32_t n_bands, band_rows, crack_band, sms, bps;
