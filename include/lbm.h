@@ -373,17 +373,24 @@ lbm_status lbm_get_wd_scale(const lbm_handle *h, double *scale);
  * conversion runs into one fixed device array of 2^20 floats (4 MiB) that
  * belongs to the library.  The paper has no counterpart (this is a
  * memory-management variant of a copy-out).  It is meant for callers that
- * must not allocate device memory where they run -- for example a monitor
- * thread sampling a running lattice while the application's device memory
- * is fully committed, where an allocation could fail or synchronise the
- * device -- and that must not disturb the handle's own staging buffer, which
- * calls on the handle's stream use.  Limits and rules:
+ * cannot allocate device memory at the point where they read the field: an
+ * application whose device memory is fully committed to its own pools (an
+ * allocation would fail, or would first make the caching allocator release
+ * and synchronise), or code that reads the field between steps inside a loop
+ * that must not call into an allocator at all.  Limits and rules:
  *   - lattices of at most 2^20 sites (LBM_ERR_ARG beyond); n_floats >= nx*ny;
  *   - LBM_ERR_STATE for other storages (use lbm_fields);
- *   - the first call on a device looks up the array's address and must not
- *     be made while a stream is being captured;
- *   - the array is shared by every call on the device: calls that overlap in
- *     time race on it and must be serialised by the callers;
+ *   - like every call on a handle, it is not safe to make it while another
+ *     thread makes a call on the same handle (it applies the pending crack
+ *     step, changes the handle's bookkeeping and enqueues work on its
+ *     stream): serialise it with the handle's other calls, e.g. make it from
+ *     the thread that steps the lattice, between its lbm_step calls;
+ *   - the array's address is looked up on each call made outside a stream
+ *     capture; during a capture the last lookup on the device is used, so the
+ *     first call on a device must come before any stream capture;
+ *   - the array is shared by every call on the device, whichever handle:
+ *     calls that overlap on the GPU (from several threads, or on several
+ *     streams) race on it and must be serialised by the callers;
  *   - nothing in the array needs to start at zero (a call reads back only
  *     what it wrote);
  *   - synchronises the handle's stream; applies the pending crack step first,

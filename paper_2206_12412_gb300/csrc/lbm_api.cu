@@ -1369,7 +1369,9 @@ lbm_status lbm_profile_read(lbm_handle *h, double *step_ms, int64_t *n_step, dou
 // alone.  Nothing in the array needs to start at zero: a call reads back only
 // elements it has just written.  All calls on a device share the array, so
 // calls that overlap in time (from several threads, or on several streams)
-// race on it; callers serialise them.
+// race on it; callers serialise them.  Like every call on a handle, it must
+// also be serialised with the other calls on the same handle (it applies the
+// pending crack step and enqueues work on the handle's stream).
 
 namespace {
 
@@ -1381,20 +1383,29 @@ static __device__ __align__(256) float g_noalloc_wd[kNoAllocFloats];
 std::mutex g_noalloc_mu;
 void *g_noalloc_addr[kNoAllocDevices];
 
-// Address of the array on the current device, looked up on the first call on
-// that device (that call must not come while a stream is being captured).
-cudaError_t noalloc_scratch(float **out)
+// Address of the array on the current device.  It is looked up again on
+// every call made outside a stream capture (the module can load at another
+// address after the device's primary context is torn down and re-created);
+// during a capture, where the lookup is not allowed, the address of the last
+// lookup on this device is used, so a first call on a device must not come
+// while its stream is being captured.
+cudaError_t noalloc_scratch(cudaStream_t s, float **out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kNoAllocDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_wd);
         if (e != cudaSuccess) return e;
         g_noalloc_addr[dev] = p;
+    } else if (!g_noalloc_addr[dev]) {
+        return cudaErrorStreamCaptureUnsupported;
     }
     *out = static_cast<float *>(g_noalloc_addr[dev]);
     return cudaSuccess;
@@ -1413,7 +1424,10 @@ lbm_status lbm_wdot_to_host_noalloc(lbm_handle *h, float *dst_host, int64_t n_fl
     if (n > kNoAllocFloats) return fail(LBM_ERR_ARG, "lattice larger than the fixed conversion array (2^20 sites)");
     if (n_floats < n) return fail(LBM_ERR_ARG, "dst too small");
     float *scratch = nullptr;
-    LBM_CUDA(noalloc_scratch(&scratch));
+    LBM_CUDA(noalloc_scratch(h->stream, &scratch));
+    // the pending crack step goes first, in the stream order lbm_fields uses
+    // (it changes only the masks and the crack state, not wdot; check_sticky
+    // below would otherwise apply it after the copy)
     lbm_status rc = finalize(h);
     if (rc != LBM_OK) return rc;
     LBM_CUDA(wd_to_f32(h, scratch, h->wd_scale, h->stream));

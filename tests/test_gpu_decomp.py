@@ -92,3 +92,48 @@ def test_rejects_splits_through_the_crack_rows(gpu):
     for rs in ([0, 47, 96], [0, 48, 96], [0, 1, 96]):
         with pytest.raises(gpu.LbmError):
             gpu.Decomp(p, 2, "f32", row_start=rs)
+
+
+# ---------------------------------------------- row slabs vs the oracle
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("n_ranks", [2, 3, 5])
+def test_slabs_match_the_oracle(oracle_mod, gpu, storage, n_ranks):
+    """A K-criterion crack with macroscopic faces on a lattice cut into 2, 3
+    and 5 row slabs, against the FP64 oracle's undivided run of the same
+    problem from the same seeded state: fields within 1e-12 (FP64) / 1e-5
+    (FP32) relative max-norm (wdot on the scale of the state), the severed
+    links and the tip bit-exact (FP64, where the K decision margin exceeds
+    1e-9), K within 1e-9 / 0.5 % of max|K|, the FP32 tip within a spacing."""
+    from test_gpu_parity import compare_fields
+    p = _problem("kcrit_macro")
+    dec = gpu.Decomp(p, n_ranks, storage)
+    o = oracle_mod.Oracle(p)
+    w0, wd0 = W.random_state(p["nx"], p["ny"], seed=n_ranks * 7 + 3,
+                             dtype=np.float64 if storage == "f64" else np.float32)
+    dec.set_fields(w0, wd0)
+    o.set_fields(w0, wd0)
+    for n in (1, 99, 200):
+        dec.step(n)
+        o.step(n)
+    compare_fields(o, dec, storage)
+    info = dec.info()
+    slab = dec.rank(info["crack_rank"])
+    co, cs = o.crack(), slab.crack_state()
+    ho, hs = o.history(), slab.history()
+    assert cs["step"] == co["step"] and len(hs["K"]) == len(ho["K"]) > 0
+    assert (ho["v"] > 0).sum() > 5
+    K_C = p["crack"]["K_C"]
+    kscale = np.abs(ho["K"]).max()
+    assert np.abs(hs["K"] - ho["K"]).max() < (1e-9 if storage == "f64" else 5e-3) * kscale
+    assert np.array_equal(hs["npairs"], ho["npairs"])
+    margin = np.min(np.abs(np.abs(ho["K"][ho["npairs"] > 0]) / K_C - 1.0))
+    if storage == "f64" and margin > 1e-9:
+        assert cs["tip_q"] == co["tip_q"]
+        assert np.array_equal(hs["tip_q"], ho["tip_q"])
+        ch, cv = o.cuts()
+        np.testing.assert_array_equal(slab.cut_mask("v"), cv.astype(bool)[slab.row0: slab.row0 + slab.ny])
+    else:
+        assert np.abs(hs["tip_q"] - ho["tip_q"]).max() < 2**32
+    o.close()
+    dec.close()
