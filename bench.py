@@ -2,25 +2,31 @@
 """Throughput of the fused lattice Boltzmann time step with dynamic mode III
 crack propagation (arXiv 2206.12412) on GB300.
 
-Workload: the 4096 x 2048 FP32 single run with K-criterion propagation (edge
-crack to x = 512 on the midline, top/bottom ramped to +-2e-3 over 5000
-steps).  One benchmark step is one full time step of the method: the bulk
-stream + collide + integrate update of all 8.4 M sites with the crack-face
-rule and the crack step (K_III evaluation, criterion, advance, link cuts),
-one fused kernel launch.
+Headline workload: the 16384 x 16384 FP32 lattice (268 M sites, 4.3 GB of
+state, far larger than the 129 MB L2) with an edge crack on the midline
+from 0 to 2048 growing at the prescribed v = 0.5 c_s, top/bottom ramped to
++-1e-3 over 2000 steps.  One benchmark step is one full time step of the
+method: the bulk stream + collide + integrate update of every site with
+the macroscopic crack-face rule and the crack step (K_III evaluation,
+criterion, advance, link cuts), one fused kernel launch.
 
-Timing: the lattice first runs --prelude steps (load ramp active), then
---warmup untimed steps; each of the --steps timed steps is bracketed by CUDA
-events on the lattice's stream, with a 256 MiB buffer written and then read
-between steps (outside the events) so that every step starts with a cold,
-clean L2.  The step kernel is also timed by the library's own event hooks.
+Timing: the lattice first runs --prelude steps, then --warmup untimed
+steps; each of the --steps timed steps is bracketed by CUDA events on the
+lattice's stream.  The state is 33x the L2, so no flush is needed between
+steps.  The step kernel is also timed by the library's own event hooks
+(the roofline figure).  The rest of the JSON line: the former 4096 x 2048
+K-criterion headline (L2 flushed between steps), the 128 x 128 FP64
+configuration as graph replay, the 16-bit storage forms, the extensions
+(D2Q9, cracks in other directions, the Sec. 5.2 example), and last the
+three patterns (mixed precision, row slabs, adjoint, batches).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
---impl reference runs the plain FP64 CPU oracle on the same workload (the
-reference arm: there is no other implementation of the method).  With N > 1
-(torchrun) every rank runs its own independent replica (weak scaling, no data
-exchange); the reference arm runs on rank 0 only.
+--impl reference runs the FP64 CPU oracle on a bounded sample of the same
+workload on all host cores (the reference arm: there is no other
+implementation of the method).  With N > 1 (torchrun) every rank runs its
+own independent replica (weak scaling, no data exchange); the reference arm
+runs on rank 0 only.
 """
 from __future__ import annotations
 
@@ -28,6 +34,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import re
 import statistics
 import subprocess
@@ -41,10 +48,17 @@ sys.path.insert(0, ROOT)
 METRIC = "GLUPS and HBM GB/s vs GB300 roofline; batched and adjoint vs plain FP32 forward"
 UNIT = "GLUPS"
 BYTES_PER_SITE = 16            # FP32 moment form: read w, wdot; write w, wdot
-WORKLOAD = "kcrit_single_4096x2048_f32"
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_kernel_f32_4096x2048.md")
+WORKLOAD = "prescribed_v05_16384x16384_f32"
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_kernel_f32_8192x8192.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2206_12412_gb300", "csrc", f)
                   for f in ("lbm_kernels.cu", "lbm_rows.cuh", "lbm_internal.cuh", "lbm_crack.cuh")]
+
+
+def r4(x):
+    """A float rounded to 4 significant digits (keeps the JSON line short)."""
+    if x is None:
+        return None
+    return float(f"{float(x):.4g}")
 
 
 def dist_env():
@@ -86,9 +100,11 @@ def kernel_source_sha256() -> str:
     return h.hexdigest()
 
 
-def traffic_from_profile():
-    """Per-launch DRAM bytes of the step kernel from the committed ncu summary,
-    or None if there is none or the kernel source changed since it was taken."""
+def traffic_from_profile(sites: int):
+    """DRAM bytes of one step-kernel launch on `sites` sites, scaled from the
+    committed ncu summary of the 8192 x 8192 lattice (1 GB of state, so the
+    writes cannot stay in L2) by the sites per launch; None if there is no
+    summary or the kernel source changed since it was taken."""
     try:
         text = open(PROFILE_SUMMARY).read()
         src = kernel_source_sha256()
@@ -96,9 +112,28 @@ def traffic_from_profile():
         return None
     m = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", text)
     b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not m or not b or m.group(1) != src:
+    n = re.search(r"sites_per_launch:\s*([0-9]+)", text)
+    if not m or not b or not n or m.group(1) != src:
         return None
-    return float(b.group(1))
+    return float(b.group(1)) * sites / float(n.group(1))
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
 
 
 class ClockSampler:
@@ -149,63 +184,107 @@ class ClockSampler:
                 "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(problem, target_s=15.0):
-    """The FP64 CPU oracle, as it stands, single-threaded on a bounded sample."""
+# ------------------------------------------------------------ CPU oracle
+
+def oracle_band(rows: int = 64) -> dict:
+    """A band of rows of the headline workload for the CPU oracle: the full
+    16384-wide lattice, `rows` rows high, the crack on its midline from 0 to
+    2048 at v = 0.5, the same loads."""
+    from paper_2206_12412_gb300 import workloads as W
+    p = W.large_prescribed()
+    return dict(p, ny=rows, crack=dict(p["crack"], y=float(rows // 2)))
+
+
+def oracle_mlups(problem: dict, threads: int, target_s: float, max_steps: int = 100000):
+    """MLUPS of the FP64 oracle, as it stands, on `threads` host threads: one
+    step to size the sample, then consecutive steps for about target_s."""
     import oracle
-    oracle.build()
-    o = oracle.Oracle(problem)
+    o = oracle.Oracle(problem, threads=threads)
     t = time.perf_counter()
     o.step(1)
     t1 = time.perf_counter() - t
-    n = max(2, min(200, int(target_s / max(t1, 1e-6))))
+    n = max(2, min(max_steps, int(target_s / max(t1, 1e-6))))
     t = time.perf_counter()
     o.step(n)
     dt = time.perf_counter() - t
-    sites = problem["nx"] * problem["ny"]
+    used = o.threads
     o.close()
-    return {"value": sites * n / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{problem['nx']}x{problem['ny']} lattice, {n} consecutive steps from the initial state, "
-                      f"FP64 distribution form, one thread ({dt:.1f} s)"}
+    return problem["nx"] * problem["ny"] * n / dt / 1e6, n, dt, used
+
+
+def cpu_baseline():
+    """The FP64 CPU oracle timed on this host: the headline workload's row
+    band on all cores (the reported value) and on one thread, and the small
+    configurations (128 x 128, and the 512 x 256 downscale of the 4096 x 2048
+    K-criterion run) on one thread and all cores.  About 15-25 s in all."""
+    import oracle
+    from paper_2206_12412_gb300 import workloads as W
+    oracle.build()
+    ncore = host_cores()
+    band = oracle_band()
+    m_all, n_all, t_all, used = oracle_mlups(band, ncore, 6.0)
+    m_one, n_one, t_one, _ = oracle_mlups(band, 1, 4.0)
+    small = {}
+    for name, p in (("c1_128x128", W.plain_fp64("macroscopic")), ("c2_downscale_512x256", W.kcrit_single(scale=8))):
+        a, _, _, _ = oracle_mlups(p, 1, 1.5)
+        b, _, _, _ = oracle_mlups(p, ncore, 1.5)
+        small[name] = {"mlups_1": r4(a), f"mlups_{ncore}": r4(b)}
+    return {"value": r4(m_all / 1e3), "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"{band['nx']}x{band['ny']} row band of the workload, {n_all} steps on {used} threads "
+                      f"({t_all:.1f} s), FP64 distribution form",
+            "single_thread": r4(m_one / 1e3), "cpu_model": cpu_model(), "nproc": ncore, "small_mlups": small}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    from paper_2206_12412_gb300 import workloads as W
     import oracle
     oracle.build()
-    p = W.kcrit_single()
-    o = oracle.Oracle(p)
+    ncore = host_cores()
+    p = oracle_band()
+    o = oracle.Oracle(p, threads=ncore)
     sites = p["nx"] * p["ny"]
-    t = time.perf_counter()
-    o.step(1)
-    t1 = time.perf_counter() - t
-    # a step is the whole lattice if the run fits in ~3 minutes, else a band of rows
-    budget = 180.0
-    frac = min(1.0, budget / max(t1 * (args.steps + args.warmup), 1e-9))
-    if frac < 1.0:
-        o.close()
-        ny = max(16, int(p["ny"] * frac) // 2 * 2)
-        q = dict(p)
-        q["ny"] = ny
-        q["crack"] = dict(p["crack"], y=float(ny // 2))
-        p, o = q, oracle.Oracle(q)
-        sites = p["nx"] * ny
     o.step(args.warmup)
     t = time.perf_counter()
     o.step(args.steps)
     dt = time.perf_counter() - t
+    used = o.threads
+    o.close()
     value = sites * args.steps / dt / 1e9
-    sample = (f"{p['nx']}x{p['ny']} lattice per step" + ("" if frac >= 1.0 else " (row band of the 4096x2048 workload)")
-              + ", FP64 distribution form, one thread")
+    sample = (f"{p['nx']}x{p['ny']} row band of the 16384x16384 workload per step, FP64 distribution form, "
+              f"{used} threads ({cpu_model()})")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "nx": 4096, "ny": 2048},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "nx": 16384, "ny": 16384},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ------------------------------------------------------------- GPU parts
+
+def events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def timed(torch, stream, fn):
+    """Seconds of fn's GPU work, CUDA events on `stream`."""
+    e0, e1 = events(torch)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) * 1e-3
+
+
+def kernel_seconds(lat):
+    """Mean step-kernel time from the library's profiling events."""
+    lat.sync()
+    pr = lat.profile(reset=True)
+    return pr["step_ms"] / max(pr["n_step"], 1) * 1e-3
 
 
 def measure_batched(lbm, W, torch, stream, steps, peak, count=256):
@@ -214,32 +293,20 @@ def measure_batched(lbm, W, torch, stream, steps, peak, count=256):
     with the single-lattice path.  The 840 MB of state exceed L2."""
     problems = W.batch_problems(count, seed=3)
     sites = sum(p["nx"] * p["ny"] for p in problems)
-
-    def timed(fn):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) * 1e-3
-
     lats = [lbm.Lattice(p, "f32", stream=stream) for p in problems]
     batch = lbm.Batch(lats)
     batch.step(128)
-    t_b = timed(lambda: batch.step(steps))
+    t_b = timed(torch, stream, lambda: batch.step(steps))
     info = batch.info()
     batch.close()
     for l in lats:
         l.step(128)
-    t_s = timed(lambda: [l.step(steps) for l in lats])
+    t_s = timed(torch, stream, lambda: [l.step(steps) for l in lats])
     for l in lats:
         l.close()
-    return {"instances": len(problems), "sites": sites, "steps": steps, "ctas_per_step": info["ctas"],
-            "glups_batched": sites * steps / t_b / 1e9, "glups_sequential": sites * steps / t_s / 1e9,
-            "speedup": t_s / t_b, "achieved_gbs": 16 * sites * steps / t_b / 1e9,
-            "frac": 16 * sites * steps / t_b / 1e9 / peak,
-            "timing": "CUDA events around the whole run, no flush (state larger than L2)"}
+    return {"n": len(problems), "sites": sites, "steps": steps, "ctas": info["ctas"],
+            "glups": r4(sites * steps / t_b / 1e9), "glups_sequential": r4(sites * steps / t_s / 1e9),
+            "speedup": r4(t_s / t_b), "frac": r4(16 * sites * steps / t_b / 1e9 / peak)}
 
 
 def measure_adjoint(lbm, W, torch, stream, n_steps=None):
@@ -258,206 +325,140 @@ def measure_adjoint(lbm, W, torch, stream, n_steps=None):
     ref.close()
     lat = lbm.Lattice(p, "f32", stream=stream)
 
-    def timed(fn, reps=2):
-        best = float("inf")
-        for _ in range(reps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            e0.record(stream)
-            fn()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            best = min(best, e0.elapsed_time(e1))
-        return best
+    def best(fn, reps=2):
+        return min(timed(torch, stream, fn) for _ in range(reps)) * 1e3
 
     def plain():
         lat.reset()
         lat.step(T)
 
-    out = {"workload": f"sensor misfit {p['nx']}x{p['ny']} f32, {T} steps, {len(sens)} sensors, prescribed v=0.4",
-           "forward_ms": timed(plain)}
+    fwd = best(plain)
+    out = {"T": T, "fwd_ms": r4(fwd), "fwd_us_step": r4(fwd * 1e3 / T)}
     every_sqrt = int(round(np.sqrt(T)))
-    for every, key in ((0, "stored"), (every_sqrt, "checkpointed")):
+    for every, key in ((0, "stored"), (every_sqrt, "ckpt")):
         tape = lbm.Tape(lat, sens, T, checkpoint_every=every)
 
         def rec():
             lat.reset()
             tape.forward(targets, loss_to_host=False)
 
-        t_rec = timed(rec)
+        t_rec = best(rec)
         rec()
-        t_bwd = timed(lambda: tape.backward(device=True))
-        out[key] = {"checkpoint_every": every, "recording_forward_ms": t_rec, "adjoint_ms": t_bwd,
-                    "ratio_forward_plus_adjoint_over_forward": (t_rec + t_bwd) / out["forward_ms"]}
+        t_bwd = best(lambda: tape.backward(device=True))
+        out[key] = {"rec_ms": r4(t_rec), "adj_ms": r4(t_bwd), "ratio": r4((t_rec + t_bwd) / fwd)}
         tape.close()
-    sites = p["nx"] * p["ny"]
-    out["adjoint_us_per_step"] = out["stored"]["adjoint_ms"] * 1e3 / (T + 1)
-    out["forward_us_per_step"] = out["forward_ms"] * 1e3 / T
-    out["adjoint_l2_gbs"] = 16 * sites / (out["adjoint_us_per_step"] * 1e-6) / 1e9
-    out["timing"] = "CUDA events around whole runs (graph replay), best of 2, no flush (L2-resident state)"
     lat.close()
     return out
 
 
-def measure_large(lbm, W, torch, stream, peak):
-    """The mixed-precision configuration: 16384 x 16384 (268 M sites, 4.3 GB
-    of FP32 state, far larger than L2), crack on the midline from 0 to 2048
-    growing at v = 0.5 c_s, +-1e-3 ramped over 2000 steps; the step kernel's
-    own CUDA-event time for FP32 storage and for 16-bit wdot storage."""
-    p = W.base_problem(16384, 16384, bc_mode="macroscopic")
-    p = W.with_crack(p, mode="prescribed", y=8192.0, x_tip=2048.0, v_rel=0.5)
-    p = W.with_antisymmetric_ramp(p, 1e-3, 2000.0)
-    p["hist_cap"] = 4096
+def measure_storage_large(lbm, W, torch, stream, peak, n=16384):
+    """The 16-bit wdot storage forms on the headline lattice: the step
+    kernel's own CUDA-event time, 20 steps after 20."""
+    p = W.large_prescribed(n)
     sites = p["nx"] * p["ny"]
-    out = {"workload": "16384x16384, prescribed v=0.5 crack from 0 to 2048", "timing": "library CUDA events around "
-           "each step kernel, 20 steps after 20 (state far larger than L2)"}
-    for storage, bps in (("f32", 16), ("f32_bf16", 12), ("f32_f16", 12)):
+    out = {}
+    for storage, bps in (("f32_bf16", 12), ("f32_f16", 12)):
         lat = lbm.Lattice(p, storage, stream=stream)
         lat.step(20)
         lat.set_profiling(True)
         lat.step(20)
-        lat.sync()
-        pr = lat.profile(reset=True)
-        k = pr["step_ms"] / max(pr["n_step"], 1) * 1e-3
-        out[storage] = {"kernel_us": k * 1e6, "glups": sites / k / 1e9, "bytes_per_site": bps,
-                        "achieved_gbs": bps * sites / k / 1e9, "frac": bps * sites / k / 1e9 / peak}
+        k = kernel_seconds(lat)
+        out[storage] = {"us": r4(k * 1e6), "glups": r4(sites / k / 1e9), "frac": r4(bps * sites / k / 1e9 / peak)}
         lat.close()
         torch.cuda.empty_cache()
     return out
 
 
-def step_time(lbm, p, storage, stream, flush_l2, prelude, steps):
-    """Mean time of one lbm_step(1) (library CUDA events around its launches)
-    with the L2 flushed before each step."""
+def step_time(lbm, p, storage, stream, flush_l2, prelude, steps, lattice=None):
+    """Mean step-kernel time of lbm_step(1) (library CUDA events) with the
+    L2 flushed before each step."""
     lat = lbm.Lattice(p, storage, stream=stream)
     lat.step(prelude)
     lat.set_profiling(True)
     for _ in range(steps):
         flush_l2()
         lat.step(1)
-    lat.sync()
-    pr = lat.profile(reset=True)
+    k = kernel_seconds(lat)
     lat.close()
-    return pr["step_ms"] / max(pr["n_step"], 1) * 1e-3
+    return k
 
 
-def crack_share(lbm, W, torch, stream, problem, flush_l2, t_crack, steps=100):
+def measure_kcrit4096(lbm, W, torch, stream, peak, flush_l2, steps):
+    """The 4096 x 2048 K-criterion run (8.4 M sites, 134 MB of state, about
+    the size of L2): the step kernel's CUDA-event time with the L2 flushed
+    (written then read back, outside the events) before every step."""
+    p = W.kcrit_single()
+    k = step_time(lbm, p, "f32", stream, flush_l2, 2500, steps)
+    sites = p["nx"] * p["ny"]
+    return {"us": r4(k * 1e6), "glups": r4(sites / k / 1e9), "frac": r4(16 * sites / k / 1e9 / peak)}, k
+
+
+def measure_c1(lbm, W, torch, stream):
+    """The 128 x 128 FP64 configuration (stationary crack, 2000 steps) as
+    graph replay: 16 K sites, launch- and latency-bound, so microseconds per
+    step rather than a roofline fraction."""
+    p = W.plain_fp64("macroscopic")
+    lat = lbm.Lattice(p, "f64", stream=stream)
+    lat.step(W.PLAIN_FP64_STEPS)     # captures the step graphs
+    lat.reset()
+    secs = timed(torch, stream, lambda: lat.step(W.PLAIN_FP64_STEPS))
+    lat.close()
+    return {"us_step": r4(secs / W.PLAIN_FP64_STEPS * 1e6), "steps": W.PLAIN_FP64_STEPS}
+
+
+def crack_share(lbm, W, torch, stream, flush_l2, t_crack):
     """The cost of the crack handling, the GPU analogue of the CPU-time share
-    the paper reports (Sec. 5.3): the benchmark lattice's step time with its
-    K-criterion crack against the same lattice, loads and state size with no
-    crack, and the same for the Sec. 5.2 example (whole 5050-step runs)."""
-    q = dict(problem, crack={"mode": "none"})
-    t_none = step_time(lbm, q, "f32", stream, flush_l2, 2500, steps)
-    out = {"kcrit_single": {"step_us_crack": t_crack * 1e6, "step_us_no_crack": t_none * 1e6,
-                            "share": 1.0 - t_none / t_crack}}
+    the paper reports (Sec. 5.3): the step time with the crack against the
+    same lattice, loads and state size with no crack -- on the 4096 x 2048
+    K-criterion run and on the whole 5050-step Sec. 5.2 example."""
+    p = W.kcrit_single()
+    t_none = step_time(lbm, dict(p, crack={"mode": "none"}), "f32", stream, flush_l2, 2500, 100)
     times = {}
-    for label, p in (("crack", W.kcrit_centre_crack()), ("none", dict(W.kcrit_centre_crack(), crack={"mode": "none"}))):
-        lat = lbm.Lattice(p, "f32", stream=stream)
+    for label, q in (("crack", W.kcrit_centre_crack()), ("none", dict(W.kcrit_centre_crack(), crack={"mode": "none"}))):
+        lat = lbm.Lattice(q, "f32", stream=stream)
         lat.step(64)
         lat.reset()
-        lat.sync()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        lat.step(W.KCRIT_CENTRE_STEPS)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        times[label] = ev0.elapsed_time(ev1) * 1e-3 / W.KCRIT_CENTRE_STEPS
+        times[label] = timed(torch, stream, lambda: lat.step(W.KCRIT_CENTRE_STEPS)) / W.KCRIT_CENTRE_STEPS
         lat.close()
-    out["centre_crack_sec52"] = {"step_us_crack": times["crack"] * 1e6, "step_us_no_crack": times["none"] * 1e6,
-                                 "share": 1.0 - times["none"] / times["crack"]}
-    out["paper"] = "CPU-time share of the crack step in the authors' Python code: 2.8 % (steady growth), 0.7 % (Sec. 5.2)"
-    return out
+    return {"kcrit_4096": r4(1.0 - t_none / t_crack),
+            "sec52": r4(1.0 - times["none"] / times["crack"]),
+            "sec52_us": [r4(times["crack"] * 1e6), r4(times["none"] * 1e6)],
+            "paper_cpu_share": [0.028, 0.007]}
 
 
-def measure_extensions(lbm, W, torch, stream, problem, peak, flush_l2, steps=100):
-    """The two extensions beyond the plain method.  D2Q9: the benchmark
-    workload on the nine-velocity lattice (bounce-back crack faces, FP32), the
-    update and crack launches timed by the library's CUDA events with the L2
-    flushed before each step, against 16 algorithmic bytes per site.  The
-    K-criterion centre-crack example of Sec. 5.2 (512 x 192, macroscopic rule
-    on every boundary, FP32): the whole 5050-step run timed with CUDA events
-    (graph replay; the state fits in L2, so it is launch-bound)."""
-    sites = problem["nx"] * problem["ny"]
-    q = dict(problem, bc_mode="bounceback", lattice="D2Q9")
-    lat = lbm.Lattice(q, "f32", stream=stream)
-    lat.step(500)
-    lat.set_profiling(True)
-    for _ in range(steps):
-        flush_l2()
-        lat.step(1)
-    lat.sync()
-    pr = lat.profile(reset=True)
-    k = pr["step_ms"] / max(pr["n_step"], 1) * 1e-3
-    d2q9 = {"workload": "kcrit_single 4096x2048, D2Q9, bounce-back faces, f32", "step_us": k * 1e6,
-            "glups": sites / k / 1e9, "bytes_per_site": 16, "achieved_gbs": 16 * sites / k / 1e9,
-            "frac": 16 * sites / k / 1e9 / peak, "launches_per_step": 1,
-            "timing": "library CUDA events around each step's launch, L2 flushed before each step"}
-    lat.close()
-
-    # a straight crack in another direction (Sec. 4.1): the same lattice and
-    # loads, a K-criterion edge crack at 20 degrees, link-local faces
+def measure_extensions(lbm, W, torch, stream, peak, flush_l2, steps=100):
+    """The extensions beyond the plain method, on the 4096 x 2048 lattice with
+    the L2 flushed before each step (library CUDA events): D2Q9 with
+    bounce-back crack faces; an edge crack at 20 degrees with link-local
+    faces; a centre crack at 20 degrees with the macroscopic rule on its
+    faces (two launches per step).  Then the Sec. 5.2 example (512 x 192,
+    macroscopic rule on every boundary, 5050 steps, graph replay) and a sweep
+    of 64 such runs over K_C as one batch."""
     import numpy as np
-    ql = W.kcrit_line()
-    lat = lbm.Lattice(ql, "f32", stream=stream)
-    lat.step(2500)
-    x0, y0 = lat.tip_q()
-    lat.set_profiling(True)
-    for _ in range(steps):
-        flush_l2()
-        lat.step(1)
-    lat.sync()
-    pr = lat.profile(reset=True)
-    k = pr["step_ms"] / max(pr["n_step"], 1) * 1e-3
-    x1, y1 = lat.tip_q()
-    line = {"workload": "kcrit_line 4096x2048, crack at 20 degrees, bounce-back faces, f32", "step_us": k * 1e6,
-            "glups": sites / k / 1e9, "bytes_per_site": 16, "achieved_gbs": 16 * sites / k / 1e9,
-            "frac": 16 * sites / k / 1e9 / peak, "launches_per_step": 1, "kernel": "line_step_kernel<float>",
-            "tip_advance_dh": float(np.hypot(x1 - x0, y1 - y0)) / 2**32,
-            "timing": "library CUDA events around each step's launch, L2 flushed before each step"}
-    lat.close()
-
-    # a centre crack at 20 degrees with the macroscopic rule on its faces
-    # (line_step_kernel, then line_faces_kernel's fixpoint solve); a failure
-    # is reported in its entry rather than ending the other measurements
+    base = W.kcrit_single()
+    sites = base["nx"] * base["ny"]
+    out = {}
+    k = step_time(lbm, dict(base, bc_mode="bounceback", lattice="D2Q9"), "f32", stream, flush_l2, 500, steps)
+    out["d2q9"] = {"us": r4(k * 1e6), "glups": r4(sites / k / 1e9), "frac": r4(16 * sites / k / 1e9 / peak)}
+    k = step_time(lbm, W.kcrit_line(), "f32", stream, flush_l2, 2500, steps)
+    out["line"] = {"us": r4(k * 1e6), "glups": r4(sites / k / 1e9), "frac": r4(16 * sites / k / 1e9 / peak)}
     try:
-        qm = W.kcrit_line_centre()
-        lat = lbm.Lattice(qm, "f32", stream=stream)
-        lat.step(2500)
-        lat.set_profiling(True)
-        for _ in range(steps):
-            flush_l2()
-            lat.step(1)
-        lat.sync()
-        pr = lat.profile(reset=True)
-        km = pr["step_ms"] / max(pr["n_step"], 1) * 1e-3
-        line_macro = {"workload": "kcrit_line_centre 4096x2048, centre crack at 20 degrees, macroscopic faces, f32",
-                      "step_us": km * 1e6, "glups": sites / km / 1e9, "launches_per_step": 2,
-                      "kernels": "line_step_kernel<float>, line_faces_kernel<float>",
-                      "timing": "library CUDA events around each step's launches, L2 flushed before each step"}
-        lat.close()
+        km = step_time(lbm, W.kcrit_line_centre(), "f32", stream, flush_l2, 2500, steps)
+        out["line_macro"] = {"us": r4(km * 1e6), "glups": r4(sites / km / 1e9)}
     except lbm.LbmError as e:
-        line_macro = {"error": str(e)[:300]}
+        out["line_macro"] = {"error": str(e)[:200]}
 
     p = W.kcrit_centre_crack()
     n = W.KCRIT_CENTRE_STEPS
     lat = lbm.Lattice(p, "f32", stream=stream)
     lat.step(64)          # capture the step graph
     lat.reset()
-    lat.sync()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    lat.step(n)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    secs = ev0.elapsed_time(ev1) * 1e-3
+    secs = timed(torch, stream, lambda: lat.step(n))
     hist = lat.history(cap=n)
-    centre = {"workload": "Sec. 5.2 centre crack 512x192, macroscopic rule on every boundary, f32, 5050 steps",
-              "run_ms": secs * 1e3, "us_per_step": secs / n * 1e6, "glups": p["nx"] * p["ny"] * n / secs / 1e9,
-              "launches_per_step": 2, "tip_right_final": float(hist["tip_q"][-1]) / 2**32,
-              "timing": "CUDA events around the whole run (graph replay, L2-resident state)"}
+    out["sec52"] = {"us_step": r4(secs / n * 1e6), "glups": r4(p["nx"] * p["ny"] * n / secs / 1e9),
+                    "tip_final": r4(float(hist["tip_q"][-1]) / 2**32)}
     lat.close()
 
-    # a sweep of the same example over K_C (0.8 .. 1.2 K_C, 64 runs) as one batch
     runs, steps_b = 64, 1024
     lats = []
     for q in range(runs):
@@ -467,42 +468,80 @@ def measure_extensions(lbm, W, torch, stream, problem, peak, flush_l2, steps=100
         lats.append(lbm.Lattice(pq, "f32", stream=stream))
     b = lbm.Batch(lats)
     b.step(64)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    b.step(steps_b)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    secs_b = ev0.elapsed_time(ev1) * 1e-3
-    sweep = {"workload": f"{runs} runs of the Sec. 5.2 example (K_C from 0.8 to 1.2 of the paper's), one batch, f32",
-             "steps": steps_b, "us_per_step": secs_b / steps_b * 1e6,
-             "glups": runs * p["nx"] * p["ny"] * steps_b / secs_b / 1e9,
-             "timing": "CUDA events around the batched steps (graph replay)"}
+    secs_b = timed(torch, stream, lambda: b.step(steps_b))
+    out["sec52_sweep64"] = {"us_step": r4(secs_b / steps_b * 1e6),
+                            "glups": r4(runs * p["nx"] * p["ny"] * steps_b / secs_b / 1e9)}
     b.close()
     for l in lats:
         l.close()
-    return {"d2q9": d2q9, "line_crack": line, "line_crack_macroscopic": line_macro, "centre_crack_sec52": centre,
-            "centre_crack_sweep": sweep}
+    return out
 
 
 def measure_virtual_ranks(lbm, W, torch, stream, problem, steps=256):
-    """The benchmark lattice split into 1, 2, 4 and 8 row slabs on this GPU
+    """The 4096 x 2048 lattice split into 1, 2, 4 and 8 row slabs on this GPU
     (one batched step launch plus one halo-row exchange launch per step),
-    timed back to back (graph replay, no flush) against the undivided
-    lattice's graph replay."""
+    timed back to back (graph replay, no flush)."""
     sites = problem["nx"] * problem["ny"]
-    out = {"timing": "CUDA events around graph replay of the steps, no flush", "steps": steps, "glups": {}}
+    out = {}
     for n in (1, 2, 4, 8):
         d = lbm.Decomp(problem, n, "f32", stream=stream)
         d.step(64)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        d.step(steps)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        out["glups"][str(n)] = sites * steps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+        out[str(n)] = r4(sites * steps / timed(torch, stream, lambda: d.step(steps)) / 1e9)
         d.close()
     return out
+
+
+def measure_mixed_4096(lbm, W, torch, stream, peak, flush_l2, steps):
+    """The 16-bit wdot forms on the 4096 x 2048 K-criterion run (L2 flushed)."""
+    p = W.kcrit_single()
+    sites = p["nx"] * p["ny"]
+    out = {}
+    for storage in ("f32_bf16", "f32_f16"):
+        k = step_time(lbm, p, storage, stream, flush_l2, 2500, min(steps, 100))
+        out[storage] = {"glups": r4(sites / k / 1e9), "frac": r4(12 * sites / k / 1e9 / peak)}
+    return out
+
+
+def profile_problem(args, W):
+    """The workload of --profile-only (for ncu captures)."""
+    if args.workload == "large":
+        return W.large_prescribed(args.size)
+    if args.workload == "kcrit":
+        return W.kcrit_single()
+    if args.workload == "d2q9":
+        return dict(W.kcrit_single(), bc_mode="bounceback", lattice="D2Q9")
+    if args.workload == "line":
+        return W.kcrit_line()
+    if args.workload == "line_macro":
+        return W.kcrit_line_centre()
+    if args.workload == "sec52":
+        return W.kcrit_centre_crack()
+    raise ValueError(args.workload)
+
+
+def run_profile(args, W, lbm, torch, rank):
+    """Prelude, warm-up and timed steps of one workload, nothing else (for
+    ncu); prints the library's kernel times.  Large lattices are not flushed
+    (their state exceeds L2), the others are."""
+    p = profile_problem(args, W)
+    stream = torch.cuda.current_stream()
+    lat = lbm.Lattice(p, args.storage, stream=stream)
+    lat.step(args.prelude)
+    lat.sync()
+    big = p["nx"] * p["ny"] * 16 > (1 << 30)
+    flush = None if big else torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    lat.set_profiling(True)
+    for _ in range(args.warmup + args.steps):
+        if flush is not None:
+            flush.fill_(1)
+        lat.step(1)
+    lat.sync()
+    prof = lat.profile(reset=True)
+    if rank == 0:
+        print(json.dumps({"profile_only": True, "workload": args.workload, "nx": p["nx"], "ny": p["ny"],
+                          "steps": args.warmup + args.steps, **prof}), flush=True)
+    lat.close()
+    return 0
 
 
 def run_ours(args, rank, world, local):
@@ -512,6 +551,8 @@ def run_ours(args, rank, world, local):
     from paper_2206_12412_gb300 import workloads as W
 
     torch.cuda.set_device(local)
+    if args.profile_only:
+        return run_profile(args, W, lbm, torch, rank)
     pg = None
     if world > 1:
         import torch.distributed as dist
@@ -525,48 +566,18 @@ def run_ours(args, rank, world, local):
     def allmax(x: float) -> float:
         return reduce_max(pg, x, "cuda")
 
-    problem = W.kcrit_single()
-    if args.profile_only and args.lattice == "D2Q9":
-        # the D2Q9 form of the workload (bounce-back crack faces), for its profile
-        problem = dict(problem, bc_mode="bounceback", lattice="D2Q9")
-    if args.profile_only and args.crack == "line":
-        # the workload with its crack at 20 degrees (line_step_kernel), for its profile
-        problem = W.kcrit_line()
-    if args.profile_only and args.crack == "line_macro":
-        # a centre crack at 20 degrees with the macroscopic rule on its faces
-        # (line_step_kernel, then line_faces_kernel), for its profile
-        problem = W.kcrit_line_centre()
+    peak, peak_kind = measured_peaks()
+    problem = W.large_prescribed()
     sites = problem["nx"] * problem["ny"]
     stream = torch.cuda.current_stream()
     lat = lbm.Lattice(problem, "f32", stream=stream)
     lat.step(args.prelude)
-    lat.sync()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    flush_sum = torch.empty((), dtype=torch.int64, device="cuda")
-
-    def flush_l2():
-        # write a buffer twice the size of L2, then read it back: L2 ends up
-        # holding clean lines of the flush buffer, none of the lattice state
-        flush.fill_(1)
-        flush_sum.copy_(flush.view(torch.int64).sum())
-
-    if args.profile_only:
-        lat.set_profiling(True)
-        for _ in range(args.warmup + args.steps):
-            flush_l2()
-            lat.step(1)
-        lat.sync()
-        prof = lat.profile(reset=True)
-        if rank == 0:
-            print(json.dumps({"profile_only": True, "steps": args.warmup + args.steps, **prof}), flush=True)
-        lat.close()
-        return 0
-
-    # timed region: one step per pair of events, L2 flushed in between (outside the events)
     for _ in range(args.warmup):
-        flush_l2()
         lat.step(1)
     lat.sync()
+
+    # timed region: one step per pair of events; the 4.3 GB state is 33x the
+    # L2, so each step streams its inputs from HBM without a flush
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clocks = ClockSampler(local)
@@ -575,7 +586,6 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(args.steps):
-        flush_l2()
         starts[k].record(stream)
         lat.step(1)
         ends[k].record(stream)
@@ -590,57 +600,20 @@ def run_ours(args, rank, world, local):
     # the step kernel alone, timed by the library's events on the same stream
     lat.set_profiling(True)
     for _ in range(args.steps):
-        flush_l2()
         lat.step(1)
-    lat.sync()
-    prof = lat.profile(reset=True)
+    kern_s = kernel_seconds(lat)
     lat.set_profiling(False)
-    kern_s = prof["step_ms"] / max(prof["n_step"], 1) * 1e-3
     achieved = BYTES_PER_SITE * sites / kern_s / 1e9
-    peak, peak_kind = measured_peaks()
-    traffic = traffic_from_profile()
+    traffic = traffic_from_profile(sites)
 
-    # the same workload with wdot stored in 16 bits (12 bytes per site update)
-    mixed = {}
-    for storage in ("f32_bf16", "f32_f16"):
-        lm = lbm.Lattice(problem, storage, stream=stream)
-        lm.step(args.prelude)
-        lm.set_profiling(True)
-        for _ in range(min(args.steps, 100)):
-            flush_l2()
-            lm.step(1)
-        lm.sync()
-        pr = lm.profile(reset=True)
-        km = pr["step_ms"] / max(pr["n_step"], 1) * 1e-3
-        mixed[storage] = {"glups": sites / km / 1e9, "kernel_ms": km * 1e3, "bytes_per_site": 12,
-                          "achieved_gbs": 12 * sites / km / 1e9, "frac": 12 * sites / km / 1e9 / peak}
-        lm.close()
-
-    batched = measure_batched(lbm, W, torch, stream, 128, peak) if not args.no_batched else None
-    adjoint = measure_adjoint(lbm, W, torch, stream) if not args.no_adjoint else None
-    vranks = measure_virtual_ranks(lbm, W, torch, stream, problem) if not args.no_virtual_ranks else None
-    large = measure_large(lbm, W, torch, stream, peak) if not args.no_large else None
-    ext = measure_extensions(lbm, W, torch, stream, problem, peak, flush_l2) if not args.no_extensions else None
-    if ext is not None:
-        ext["crack_share"] = crack_share(lbm, W, torch, stream, problem, flush_l2, kern_s)
-
-    # steady back-to-back replay (CUDA graph, no flush): context only
-    lat.sync()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    lat.step(256)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    steady = sites * 256 / (ev0.elapsed_time(ev1) * 1e-3) / 1e9
-
-    # end to end through the public API with host buffers: upload the state from
-    # pinned memory, run the steps, read back the fields and the per-step crack record
+    # end to end through the public API with host buffers: upload the state
+    # from pinned memory, run the steps, read back the fields and the
+    # per-step crack record
     w_h = torch.empty((problem["ny"], problem["nx"]), dtype=torch.float32, pin_memory=True)
     wd_h = torch.empty_like(w_h, pin_memory=True)
     w_np, wd_np = w_h.numpy(), wd_h.numpy()
-    w0, wd0 = lat.fields()
-    w_np[...] = w0
-    wd_np[...] = wd0
+    lbm.lbm_fields(lat.h, 0, w_np.ctypes.data, False, lat.dtype_code)
+    lbm.lbm_fields(lat.h, 1, wd_np.ctypes.data, False, lat.dtype_code)
     e2e_vals = []
     for _ in range(2):
         barrier()
@@ -657,37 +630,61 @@ def run_ours(args, rank, world, local):
     plane = sites * 4
     h2d = 2 * plane / args.steps
     d2h = (2 * plane + len(hist["K"]) * (8 + 8 + 8 + 4)) / args.steps
+    launch = lat.launch()
+    lat.close()
+    del w_h, wd_h
+    torch.cuda.empty_cache()
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flush_sum = torch.empty((), dtype=torch.int64, device="cuda")
+
+    def flush_l2():
+        # write a buffer twice the size of L2, then read it back: L2 ends up
+        # holding clean lines of the flush buffer, none of the lattice state
+        flush.fill_(1)
+        flush_sum.copy_(flush.view(torch.int64).sum())
+
+    extra = {}
+    if not args.no_extensions:
+        extra["kcrit_4096x2048"], t_kcrit = measure_kcrit4096(lbm, W, torch, stream, peak, flush_l2, 100)
+        extra["c1_128x128_f64"] = measure_c1(lbm, W, torch, stream)
+        extra["extensions"] = measure_extensions(lbm, W, torch, stream, peak, flush_l2)
+        extra["crack_share"] = crack_share(lbm, W, torch, stream, flush_l2, t_kcrit)
+    patterns = {}
+    if not args.no_mixed:
+        patterns["mixed_precision"] = {"16384": measure_storage_large(lbm, W, torch, stream, peak),
+                                       "4096": measure_mixed_4096(lbm, W, torch, stream, peak, flush_l2, args.steps)}
+    if not args.no_virtual_ranks:
+        patterns["virtual_ranks"] = measure_virtual_ranks(lbm, W, torch, stream, W.kcrit_single())
+    if not args.no_adjoint:
+        patterns["adjoint"] = measure_adjoint(lbm, W, torch, stream)
+    if not args.no_batched:
+        patterns["batched"] = measure_batched(lbm, W, torch, stream, 128, peak)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "nx": problem["nx"], "ny": problem["ny"], "storage": "f32",
-                   "crack": "kcrit", "bc_mode": problem["bc_mode"], "prelude_steps": args.prelude,
-                   "l2": "flushed between timed steps (256 MiB buffer written then read, outside the events)",
+                   "crack": "prescribed v=0.5", "bc_mode": problem["bc_mode"], "prelude_steps": args.prelude,
+                   "l2": "inputs larger than L2 (4.3 GB state), no flush",
                    "parallelism": f"{world} independent replicas" if world > 1 else "single GPU",
-                   "launch": lat.launch()},
+                   "launch": launch},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": "step_kernel<float>", "kernel_ms": kern_s * 1e3, "bytes_per_site": BYTES_PER_SITE},
         "e2e": {"value": world * sites * args.steps / e2e_s / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps,
-        "steady_graph_glups": steady,
-        "mixed_precision": mixed,
-        "batched": batched,
-        "adjoint": adjoint,
-        "virtual_ranks": vranks,
-        "large_lattice": large,
-        "extensions": ext,
-        "wall_s": wall,
         "clocks": clk,
+        "wall_s": r4(wall),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(problem)
+        line["cpu_baseline"] = cpu_baseline()
+    line.update(extra)
+    line.update(patterns)
     if rank == 0:
-        print(json.dumps(line), flush=True)
-    lat.close()
+        print(json.dumps(line, separators=(",", ":")), flush=True)
     if pg is not None:
         pg.destroy_process_group()
     return 0
@@ -696,54 +693,51 @@ def run_ours(args, rank, world, local):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prelude", type=int, default=2500)
+    ap.add_argument("--prelude", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-lattice batched measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the sensor-misfit gradient measurement")
     ap.add_argument("--no-virtual-ranks", action="store_true", help="skip the row-slab decomposition measurement")
-    ap.add_argument("--no-large", action="store_true", help="skip the 16384 x 16384 storage comparison")
-    ap.add_argument("--no-extensions", action="store_true", help="skip the D2Q9 and Sec. 5.2 example measurements")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the 16-bit storage measurements")
+    ap.add_argument("--no-extensions", action="store_true",
+                    help="skip the 4096x2048, 128x128, D2Q9, line-crack and Sec. 5.2 measurements")
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched measurement, --steps steps of --batched-count lattices (for ncu)")
     ap.add_argument("--batched-count", type=int, default=256, help="lattices in the batched measurement")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="only the sensor-misfit gradient measurement (for ncu)")
     ap.add_argument("--adjoint-steps", type=int, default=None, help="steps of the adjoint workload (default 8000)")
-    ap.add_argument("--lattice", default="D2Q5", choices=["D2Q5", "D2Q9"],
-                    help="with --profile-only: the velocity set of the profiled workload")
-    ap.add_argument("--crack", default="x", choices=["x", "line", "line_macro"],
-                    help="with --profile-only: the crack of the profiled workload (along +x, or at 20 degrees; "
-                         "line_macro: a centre crack at 20 degrees with the macroscopic rule on its faces)")
     ap.add_argument("--profile-only", action="store_true",
-                    help="only prelude, warm-up and timed steps (for ncu); prints kernel times")
+                    help="only prelude, warm-up and timed steps of --workload (for ncu); prints kernel times")
+    ap.add_argument("--workload", default="large", choices=["large", "kcrit", "d2q9", "line", "line_macro", "sec52"],
+                    help="with --profile-only: large = the headline lattice at --size (16384: the headline "
+                         "itself), kcrit = 4096x2048 K-criterion, d2q9 / line / line_macro = its D2Q9 and "
+                         "20-degree forms, sec52 = the Sec. 5.2 example")
+    ap.add_argument("--size", type=int, default=16384, help="with --workload large: the lattice's side")
+    ap.add_argument("--storage", default="f32", choices=["f32", "f32_bf16", "f32_f16", "f64"],
+                    help="with --profile-only: the storage form")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
-    if args.batched_only:
-        # the batched form alone (for profiling the batch kernel)
+    if args.batched_only or args.adjoint_only:
         import torch
         from paper_2206_12412_gb300 import lbm
         from paper_2206_12412_gb300 import workloads as W
         torch.cuda.set_device(local)
-        peak, _ = measured_peaks()
-        out = measure_batched(lbm, W, torch, torch.cuda.current_stream(), args.steps, peak, count=args.batched_count)
+        if args.batched_only:
+            peak, _ = measured_peaks()
+            out = {"batched_only": True, **measure_batched(lbm, W, torch, torch.cuda.current_stream(), args.steps,
+                                                           peak, count=args.batched_count)}
+        else:
+            out = {"adjoint_only": True, **measure_adjoint(lbm, W, torch, torch.cuda.current_stream(),
+                                                           n_steps=args.adjoint_steps)}
         if rank == 0:
-            print(json.dumps({"batched_only": True, **out}), flush=True)
-        return 0
-    if args.adjoint_only:
-        # the sensor-misfit gradient alone (for profiling the adjoint kernel)
-        import torch
-        from paper_2206_12412_gb300 import lbm
-        from paper_2206_12412_gb300 import workloads as W
-        torch.cuda.set_device(local)
-        out = measure_adjoint(lbm, W, torch, torch.cuda.current_stream(), n_steps=args.adjoint_steps)
-        if rank == 0:
-            print(json.dumps({"adjoint_only": True, **out}), flush=True)
+            print(json.dumps(out), flush=True)
         return 0
     return run_ours(args, rank, world, local)
 

@@ -165,6 +165,7 @@ typedef struct {
     int32_t *queue;
     uint8_t *inq, *visited;
     double *series[4];
+    int32_t threads;     /* OpenMP threads of the per-site loops (1 unless set) */
 } orc_state;
 
 /* Lattice velocities in units of c = dh/dt: D2Q5 (Sec. 3, eq. 2) uses
@@ -812,7 +813,14 @@ static void lbm_step(orc_state *s)
     double wstar[4];
     for (int e = 0; e < 4; ++e) wstar[e] = load_value(s, e, s->step);
 
+    /* The three per-site loops below touch only their own site (collision,
+     * moment) or read the post-collision values of other sites (streaming),
+     * so they may run on several threads without changing any result; the
+     * thread count is 1 unless orc_set_threads raised it (timing runs only). */
+    int nth = s->threads > 1 ? s->threads : 1;
+    (void)nth;
     /* collision (eq. LBE, right-hand side) */
+#pragma omp parallel for num_threads(nth) schedule(static) if (nth > 1)
     for (size_t k = 0; k < n; ++k) {
         double wdot = 0.0;
         for (int a = 0; a < s->Q; ++a) wdot += s->f[a][k];
@@ -822,6 +830,7 @@ static void lbm_step(orc_state *s)
     }
     /* streaming along intact links (eq. LBE, left-hand side); a missing link
      * takes bounce-back (free edge, crack face) or anti-bounce-back (Dirichlet) */
+#pragma omp parallel for num_threads(nth) schedule(static) if (nth > 1)
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             int32_t k = j * nx + i;
@@ -845,6 +854,7 @@ static void lbm_step(orc_state *s)
         }
     /* moment and Euler integration (eqs. distrib-macro, integration) */
     memcpy(s->w_old, s->w, n * sizeof(double));
+#pragma omp parallel for num_threads(nth) schedule(static) if (nth > 1)
     for (size_t k = 0; k < n; ++k) {
         double wdot = 0.0;
         for (int a = 0; a < s->Q; ++a) wdot += s->f[a][k];
@@ -1186,6 +1196,20 @@ static void crack_growth(orc_state *s)
         s->htipyl[h] = s->ltip_yq;
     }
     s->hist_n += 1;
+}
+
+/* Threads for the per-site loops of the LBM step (timing of the CPU baseline;
+ * results do not depend on it).  Returns the count in force: 1 when the
+ * library was built without OpenMP. */
+int32_t orc_set_threads(orc_state *s, int32_t n)
+{
+#ifdef _OPENMP
+    s->threads = n > 1 ? n : 1;
+#else
+    (void)n;
+    s->threads = 1;
+#endif
+    return s->threads;
 }
 
 /* Advance n time steps: the LBM step including its boundary rules, then the

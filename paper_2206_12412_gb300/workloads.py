@@ -95,6 +95,21 @@ def kcrit_single(scale: int = 1, seed: int = 2, bc_mode: str = "macroscopic") ->
 KCRIT_SINGLE_STEPS = 50000
 
 
+def large_prescribed(n: int = 16384, bc_mode: str = "macroscopic") -> dict:
+    """n x n (16384 x 16384: 268 M sites, 4.3 GB of FP32 state): an edge crack
+    on the midline from 0 to n / 8 growing at the prescribed v = 0.5 c_s,
+    top and bottom ramped to +-1e-3 over 2000 steps; 20 000 steps (it advances
+    0.25 dh per step, so at n = 16384 the tip goes from 2048 to 7048)."""
+    p = base_problem(n, n, bc_mode=bc_mode)
+    p = with_crack(p, mode="prescribed", y=float(n // 2), x_tip=n / 8.0, v_rel=0.5)
+    p = with_antisymmetric_ramp(p, 1e-3, 2000.0)
+    p["hist_cap"] = 4096
+    return p
+
+
+LARGE_PRESCRIBED_STEPS = 20000
+
+
 def kcrit_line(scale: int = 1, seed: int = 2, degrees: float = 20.0) -> dict:
     """kcrit_single with the crack in another direction (Sec. 4.1): an edge
     crack from (0, ny/2 - 0.3) of length 512 / scale at `degrees` to +x,
