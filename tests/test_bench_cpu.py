@@ -53,3 +53,9 @@ def test_oracle_timing_sample_is_bounded(oracle_mod):
     from paper_2206_12412_gb300 import workloads as W
     mlups, n, dt, used = bench.oracle_mlups(W.plain_fp64("macroscopic"), 2, 0.3)
     assert mlups > 0 and n >= 2 and dt < 5.0 and used in (1, 2)
+
+
+def test_committed_summary_names_its_sites():
+    text = open(bench.PROFILE_SUMMARY).read()
+    assert "sites_per_launch: 67108864" in text and "dram_bytes_per_launch:" in text
+    assert bench.traffic_from_profile(16384 * 16384) == 4 * 1028276480
