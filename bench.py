@@ -296,8 +296,15 @@ def measure_batched(lbm, W, torch, stream, steps, peak, count=256):
     lats = [lbm.Lattice(p, "f32", stream=stream) for p in problems]
     batch = lbm.Batch(lats)
     batch.step(128)
+    t_d = timed(torch, stream, lambda: batch.step(steps))      # the default shape: 128 threads, 16-row bands
+    batch.tune(trial_steps=8)
+    batch.step(64)
     t_b = timed(torch, stream, lambda: batch.step(steps))
     info = batch.info()
+    # the same shape as one persistent cooperative launch (grid barrier between steps)
+    batch.set_persistent(True)
+    batch.step(8)
+    t_p = timed(torch, stream, lambda: batch.step(steps))
     batch.close()
     for l in lats:
         l.step(128)
@@ -305,8 +312,10 @@ def measure_batched(lbm, W, torch, stream, steps, peak, count=256):
     for l in lats:
         l.close()
     return {"n": len(problems), "sites": sites, "steps": steps, "ctas": info["ctas"],
-            "glups": r4(sites * steps / t_b / 1e9), "glups_sequential": r4(sites * steps / t_s / 1e9),
-            "speedup": r4(t_s / t_b), "frac": r4(16 * sites * steps / t_b / 1e9 / peak)}
+            "shape": [info["threads"], info["band_rows"]], "glups_default_shape": r4(sites * steps / t_d / 1e9),
+            "glups_persistent": r4(sites * steps / t_p / 1e9),
+            "glups_sequential": r4(sites * steps / t_s / 1e9), "speedup": r4(t_s / t_b),
+            "glups": r4(sites * steps / t_b / 1e9), "frac": r4(16 * sites * steps / t_b / 1e9 / peak)}
 
 
 def measure_adjoint(lbm, W, torch, stream, n_steps=None):

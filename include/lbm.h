@@ -444,6 +444,55 @@ lbm_status lbm_batch_step(lbm_batch *b, int64_t n);
 /* Number of lattices and CTAs per step of the batch (pointers may be NULL). */
 lbm_status lbm_batch_info(const lbm_batch *b, int32_t *n_lattices, int32_t *ctas);
 
+/* Launch shape of the batched step: CTAs of `threads` threads (32, 64 or 128;
+ * a column block is threads 16-byte vectors wide, i.e. 4 * threads FP32
+ * columns) over bands of band_rows >= 1 rows (the crack rows keep bands of
+ * their own).  Narrow column blocks leave fewer idle warps right of lattices
+ * whose width is not a multiple of 512 columns; short bands give more CTAs.
+ * The results do not depend on the shape (each lattice's time step is the
+ * same arithmetic).  lbm_batch_set_shape synchronises the stream and
+ * re-partitions every member lattice; lbm_batch_get_shape reads it back.
+ * The paper has no counterpart (its runs are single lattices). */
+lbm_status lbm_batch_set_shape(lbm_batch *b, int32_t threads, int32_t band_rows);
+lbm_status lbm_batch_get_shape(const lbm_batch *b, int32_t *threads, int32_t *band_rows);
+
+/* Autotuner of the batched step's launch shape: times trial_steps (2..1024)
+ * batched steps with CUDA events for every shape of threads in {32, 64, 128}
+ * x band_rows in {8, 16, 32, 64} (the first of three repetitions a warm-up),
+ * keeps the fastest, and caches it in the process under the device's SM
+ * count, the storage and the lattices' sizes and crack rows (a later batch of
+ * the same lattices takes the cached shape without trials; *from_cache = 1,
+ * *us_per_step = 0).  The trials advance the lattices, so the tuner first
+ * applies any pending crack step, copies every member's device state to a
+ * scratch allocation of the same total size (from the batch's allocator;
+ * LBM_ERR_OOM if it fails) and copies it back afterwards: the lattices end as
+ * they were.  Synchronises the stream.  Outputs may be NULL. */
+lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *threads, int32_t *band_rows,
+                          double *us_per_step, int32_t *from_cache);
+
+/* Persistent form of the batched step.  With enable != 0, lbm_batch_step(b,
+ * n) enqueues ONE cooperative launch (CTAs of the batch's shape, as many as
+ * are resident at once) that runs all n steps: each CTA takes every
+ * grid-size-th unit of a step, then every CTA meets at a grid barrier before
+ * the next step (and before the edge-rule units of a step).  A CTA waits at
+ * most budget_cycles clock cycles (0: 2^31, about 1 s) at a barrier; then
+ * it sets a timeout flag in every member lattice and returns, and the
+ * others give up at their next wait, so the launch always ends.  The next
+ * call that synchronises a member handle then returns LBM_ERR_TIMEOUT (and
+ * the handle stays in that error state).  Results are bit-identical to the
+ * per-step launches (enable = 0, the default: graph replay of one launch per
+ * step).  No counterpart in the paper. */
+lbm_status lbm_batch_set_persistent(lbm_batch *b, int32_t enable, int64_t budget_cycles);
+
+/* Diagnostic of the bounded device wait used by the persistent batched
+ * step: `ctas` CTAs (1..64) of a small kernel on `stream` meet at a grid
+ * barrier that expects `expected` (1..64) arrivals, each waiting at most
+ * budget_cycles (1e3..2^34) clock cycles.  Returns LBM_OK if the barrier
+ * completed for every CTA and LBM_ERR_TIMEOUT if a wait gave up (as it must
+ * when ctas < expected: nothing completes the barrier).  Allocates 256 bytes
+ * of device memory for the call; synchronises the stream. */
+lbm_status lbm_barrier_probe(int32_t ctas, int32_t expected, int64_t budget_cycles, void *stream);
+
 /* Release the batch (NULL is ignored); the member handles stay valid. */
 void lbm_batch_destroy(lbm_batch *b);
 

@@ -110,6 +110,12 @@ PROTOTYPES = {
                                    C.POINTER(C.c_void_p)]),
     "lbm_batch_step": (C.c_int, [C.c_void_p, C.c_int64]),
     "lbm_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "lbm_batch_set_shape": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    "lbm_batch_set_persistent": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
+    "lbm_barrier_probe": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, C.c_void_p]),
+    "lbm_batch_get_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "lbm_batch_tune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                 C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
     "lbm_batch_destroy": (None, [C.c_void_p]),
     "lbm_reset": (C.c_int, [C.c_void_p]),
     "lbm_wdot_to_host_noalloc": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_int64]),

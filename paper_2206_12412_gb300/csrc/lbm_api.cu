@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -365,6 +366,10 @@ lbm_status check_sticky(lbm_handle *h)
     if (e != cudaSuccess) {
         h->sticky = LBM_ERR_CUDA;
         return cuda_fail(e, "synchronising the lattice stream");
+    }
+    if (err & ERR_TIMEOUT) {
+        h->sticky = LBM_ERR_TIMEOUT;
+        return fail(LBM_ERR_TIMEOUT, "a bounded device wait gave up (grid barrier of a persistent batched step)");
     }
     if ((err & ERR_NONFINITE) || ((hs.r.flags | hs.l.flags) & FLAG_NONFINITE)) {
         h->sticky = LBM_ERR_UNSTABLE;
@@ -1618,6 +1623,12 @@ struct lbm_batch {
     int n_units;
     BatchUnit *eunits;   // edge-rule units: 128 edge sites of one lattice (LBM_BC_MACROSCOPIC_EDGES)
     int n_eunits;
+    int threads;         // threads per CTA: column blocks of threads 16-byte vectors
+    int band_rows;       // rows per band (the crack sub-bands have their own height)
+    bool persistent;     // lbm_batch_step as one cooperative launch (grid barrier between steps)
+    long long budget;    // clock64 cycles a CTA waits at that barrier before giving up
+    GridBarrier *bar;    // the barrier (own allocation, with the batch's error word after it)
+    uint32_t *err;
     lbm_allocator alloc;
     bool custom_alloc;
     cudaStream_t stream;
@@ -1661,10 +1672,30 @@ void fill_descs(const lbm_batch *b, std::vector<char> &buf)
 }
 
 template <typename T, typename D>
+cudaError_t enqueue_batch_persistent_t(const lbm_batch *b, int par, int64_t n, cudaStream_t s)
+{
+    const StepArgs<T, D> *d = static_cast<const StepArgs<T, D> *>(b->descs);
+    cudaError_t e = cudaMemsetAsync(b->bar, 0, sizeof(GridBarrier), s);
+    if (e != cudaSuccess) return e;
+    return launch_batch_persistent(d, (int)b->hs.size(), b->units, b->n_units, b->eunits, b->n_eunits, par, n, b->bar,
+                                   b->err, b->budget, b->threads, s);
+}
+
+cudaError_t enqueue_batch_persistent(const lbm_batch *b, int par, int64_t n, cudaStream_t s)
+{
+    switch (b->storage) {
+    case LBM_F32: return enqueue_batch_persistent_t<float, float>(b, par, n, s);
+    case LBM_F32_WD_BF16: return enqueue_batch_persistent_t<float, __nv_bfloat16>(b, par, n, s);
+    case LBM_F32_WD_F16: return enqueue_batch_persistent_t<float, __half>(b, par, n, s);
+    default: return enqueue_batch_persistent_t<double, double>(b, par, n, s);
+    }
+}
+
+template <typename T, typename D>
 cudaError_t enqueue_batch_step_t(const lbm_batch *b, int par, cudaStream_t s)
 {
     const StepArgs<T, D> *d = static_cast<const StepArgs<T, D> *>(b->descs);
-    cudaError_t e = launch_batch_step(d, b->units, b->n_units, par, s);
+    cudaError_t e = launch_batch_step(d, b->units, b->n_units, par, s, b->threads);
     if (e == cudaSuccess && b->n_eunits > 0) e = launch_batch_edge_rule(d, b->eunits, b->n_eunits, par, s);
     return e;
 }
@@ -1677,6 +1708,114 @@ cudaError_t enqueue_batch_step(const lbm_batch *b, int par, cudaStream_t s)
     case LBM_F32_WD_F16: return enqueue_batch_step_t<float, __half>(b, par, s);
     default: return enqueue_batch_step_t<double, double>(b, par, s);
     }
+}
+
+void batch_release_block(lbm_batch *b)
+{
+    if (!b->block) return;
+    cudaStreamSynchronize(b->stream);
+    if (b->custom_alloc) b->alloc.release(b->block, b->alloc.ctx);
+    else cudaFree(b->block);
+    b->block = nullptr;
+    b->block_bytes = 0;
+}
+
+void *batch_alloc(lbm_batch *b, size_t bytes)
+{
+    void *p = nullptr;
+    if (b->custom_alloc) p = b->alloc.alloc(bytes, b->alloc.ctx);
+    else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+    return p;
+}
+
+void batch_free(lbm_batch *b, void *p)
+{
+    if (!p) return;
+    if (b->custom_alloc) b->alloc.release(p, b->alloc.ctx);
+    else cudaFree(p);
+}
+
+// Re-partition every lattice into bands of `rows` rows and rebuild the unit
+// table for CTAs of `threads` threads (column blocks of threads 16-byte
+// vectors) and the descriptor table; the block grows when the tables do.
+lbm_status batch_build(lbm_batch *b, int threads, int rows)
+{
+    if (threads != 32 && threads != 64 && threads != kThreads)
+        return fail(LBM_ERR_ARG, "threads per CTA must be 32, 64 or 128");
+    if (rows < 1) return fail(LBM_ERR_ARG, "band_rows must be >= 1");
+    std::vector<BatchUnit> units;
+    for (size_t i = 0; i < b->hs.size(); ++i) {
+        lbm_handle *h = b->hs[i];
+        drop_graph(h);
+        lbm_status rc = plan_bands(h, rows);
+        if (rc != LBM_OK) return rc;
+        const int cols = threads * (int)(16 / h->esize);
+        const int ncb = (h->grid.nx + cols - 1) / cols;
+        for (int band = 0; band < h->n_bands; ++band)
+            for (int cb = 0; cb < ncb; ++cb) {
+                BatchUnit u;
+                u.inst = (int32_t)i;
+                u.cb = cb;
+                u.band = band;
+                u.pad = 0;
+                units.push_back(u);
+            }
+    }
+    std::vector<char> descs;
+    std::vector<BatchUnit> eunits;
+    switch (b->storage) {
+    case LBM_F32: fill_descs<float, float>(b, descs); edge_units<float, float>(b, eunits); break;
+    case LBM_F32_WD_BF16: fill_descs<float, __nv_bfloat16>(b, descs); edge_units<float, __nv_bfloat16>(b, eunits); break;
+    case LBM_F32_WD_F16: fill_descs<float, __half>(b, descs); edge_units<float, __half>(b, eunits); break;
+    default: fill_descs<double, double>(b, descs); edge_units<double, double>(b, eunits); break;
+    }
+    const size_t o_units = align256(descs.size());
+    const size_t o_eunits = o_units + align256(units.size() * sizeof(BatchUnit));
+    const size_t need = o_eunits + std::max<size_t>(eunits.size(), 1) * sizeof(BatchUnit);
+    if (need > b->block_bytes) {
+        batch_release_block(b);
+        b->block = batch_alloc(b, need);
+        if (!b->block) return fail(LBM_ERR_OOM, "device allocation failed");
+        b->block_bytes = need;
+    }
+    b->descs = b->block;
+    b->units = reinterpret_cast<BatchUnit *>(static_cast<char *>(b->block) + o_units);
+    b->eunits = reinterpret_cast<BatchUnit *>(static_cast<char *>(b->block) + o_eunits);
+    b->n_units = (int)units.size();
+    b->n_eunits = (int)eunits.size();
+    cudaError_t e = cudaMemcpyAsync(b->descs, descs.data(), descs.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->units, units.data(), units.size() * sizeof(BatchUnit), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && !eunits.empty())
+        e = cudaMemcpyAsync(b->eunits, eunits.data(), eunits.size() * sizeof(BatchUnit), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "uploading the batch tables");
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    b->threads = threads;
+    b->band_rows = rows;
+    return LBM_OK;
+}
+
+// Shapes chosen by lbm_batch_tune in this process, keyed by the device's SM
+// count, the storage and the lattices' sizes and crack bands.
+std::mutex g_tune_mu;
+std::map<std::string, std::pair<int, int>> g_tune_cache;
+
+std::string batch_key(const lbm_batch *b)
+{
+    std::vector<std::string> parts;
+    for (const lbm_handle *h : b->hs) {
+        const int hh = h->cp.mode == CRACK_NONE ? 0 : (h->cp.macro ? 3 : 1);
+        parts.push_back(std::to_string(h->grid.nx) + "x" + std::to_string(h->grid.ny) + "/" + std::to_string(h->jc) +
+                        "/" + std::to_string(hh) + (h->edge_macro ? "e" : ""));
+    }
+    std::sort(parts.begin(), parts.end());
+    std::string k = std::to_string(b->hs[0]->sms) + "|" + std::to_string(b->storage);
+    for (const std::string &p : parts) k += "," + p;
+    return k;
 }
 
 }  // namespace
@@ -1735,71 +1874,178 @@ lbm_status lbm_batch_create(lbm_handle *const *handles, int32_t n, int32_t band_
     b->hs.assign(handles, handles + n);
     b->storage = handles[0]->lat.storage;
     b->block = nullptr;
+    b->block_bytes = 0;
     b->stream = handles[0]->stream;
     b->cap_stream = nullptr;
     b->gexec = nullptr;
     b->gparity = -1;
+    b->threads = kThreads;
+    b->band_rows = 16;
+    b->persistent = false;
+    b->budget = (long long)1 << 31;
+    b->bar = nullptr;
+    b->err = nullptr;
     b->custom_alloc = allocator && allocator->alloc && allocator->release;
     if (b->custom_alloc) b->alloc = *allocator;
     auto bail = [&](lbm_status rc) {
-        if (b->block) {
-            cudaStreamSynchronize(b->stream);
-            if (b->custom_alloc) b->alloc.release(b->block, b->alloc.ctx);
-            else cudaFree(b->block);
-        }
+        batch_release_block(b);
+        batch_free(b, b->bar);
         if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
         delete b;
         return rc;
     };
-    // bands of band_rows rows (default 16): a batch has many CTAs, no need to fit one wave
-    std::vector<BatchUnit> units;
+    b->bar = static_cast<GridBarrier *>(batch_alloc(b, 256));
+    if (!b->bar) return bail(fail(LBM_ERR_OOM, "device allocation failed"));
+    b->err = reinterpret_cast<uint32_t *>(static_cast<char *>(static_cast<void *>(b->bar)) + 128);
+    {
+        cudaError_t e = cudaMemsetAsync(b->bar, 0, 256, b->stream);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "clearing the batch barrier"));
+    }
     for (int i = 0; i < n; ++i) {
-        lbm_handle *h = handles[i];
-        cudaError_t e = cudaStreamSynchronize(h->stream);
+        cudaError_t e = cudaStreamSynchronize(handles[i]->stream);
         if (e != cudaSuccess) return bail(cuda_fail(e, "synchronising a lattice"));
-        drop_graph(h);
-        lbm_status rc = plan_bands(h, band_rows > 0 ? band_rows : 16);
-        if (rc != LBM_OK) return bail(rc);
-        for (int band = 0; band < h->n_bands; ++band)
-            for (int cb = 0; cb < h->ncb; ++cb) {
-                BatchUnit u;
-                u.inst = i;
-                u.cb = cb;
-                u.band = band;
-                u.pad = 0;
-                units.push_back(u);
-            }
     }
-    std::vector<char> descs;
-    std::vector<BatchUnit> eunits;
-    switch (b->storage) {
-    case LBM_F32: fill_descs<float, float>(b, descs); edge_units<float, float>(b, eunits); break;
-    case LBM_F32_WD_BF16: fill_descs<float, __nv_bfloat16>(b, descs); edge_units<float, __nv_bfloat16>(b, eunits); break;
-    case LBM_F32_WD_F16: fill_descs<float, __half>(b, descs); edge_units<float, __half>(b, eunits); break;
-    default: fill_descs<double, double>(b, descs); edge_units<double, double>(b, eunits); break;
-    }
-    b->n_units = (int)units.size();
-    b->n_eunits = (int)eunits.size();
-    const size_t o_units = align256(descs.size());
-    const size_t o_eunits = o_units + align256(units.size() * sizeof(BatchUnit));
-    b->block_bytes = o_eunits + std::max<size_t>(eunits.size(), 1) * sizeof(BatchUnit);
-    if (b->custom_alloc) b->block = b->alloc.alloc(b->block_bytes, b->alloc.ctx);
-    else if (cudaMalloc(&b->block, b->block_bytes) != cudaSuccess) b->block = nullptr;
-    if (!b->block) return bail(fail(LBM_ERR_OOM, "device allocation failed"));
-    b->descs = b->block;
-    b->units = reinterpret_cast<BatchUnit *>(static_cast<char *>(b->block) + o_units);
-    b->eunits = reinterpret_cast<BatchUnit *>(static_cast<char *>(b->block) + o_eunits);
-    cudaError_t e = cudaMemcpyAsync(b->descs, descs.data(), descs.size(), cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->units, units.data(), units.size() * sizeof(BatchUnit), cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess && !eunits.empty())
-        e = cudaMemcpyAsync(b->eunits, eunits.data(), eunits.size() * sizeof(BatchUnit), cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
-    if (e != cudaSuccess) return bail(cuda_fail(e, "uploading the batch tables"));
+    // bands of band_rows rows (default 16), CTAs of 128 threads: a batch has
+    // many CTAs, no need to fit one wave; lbm_batch_tune picks a better shape
+    lbm_status rc = batch_build(b, kThreads, band_rows > 0 ? band_rows : 16);
+    if (rc != LBM_OK) return bail(rc);
+    cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "creating the capture stream"));
     *out = b;
     clear_error();
     return LBM_OK;
+}
+
+lbm_status lbm_batch_set_shape(lbm_batch *b, int32_t threads, int32_t band_rows)
+{
+    if (!b) return fail(LBM_ERR_ARG, "batch is NULL");
+    lbm_status rc = batch_check(b);
+    if (rc != LBM_OK) return rc;
+    for (lbm_handle *h : b->hs) LBM_CUDA(cudaStreamSynchronize(h->stream));
+    rc = batch_build(b, threads, band_rows);
+    if (rc == LBM_OK) clear_error();
+    return rc;
+}
+
+lbm_status lbm_batch_get_shape(const lbm_batch *b, int32_t *threads, int32_t *band_rows)
+{
+    if (!b) return fail(LBM_ERR_ARG, "batch is NULL");
+    if (threads) *threads = b->threads;
+    if (band_rows) *band_rows = b->band_rows;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *threads, int32_t *band_rows,
+                          double *us_per_step, int32_t *from_cache)
+{
+    if (!b) return fail(LBM_ERR_ARG, "batch is NULL");
+    if (trial_steps < 2 || trial_steps > 1024) return fail(LBM_ERR_ARG, "trial_steps must be in [2, 1024]");
+    lbm_status rc = batch_check(b);
+    if (rc != LBM_OK) return rc;
+    const std::string key = batch_key(b);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            for (lbm_handle *h : b->hs) LBM_CUDA(cudaStreamSynchronize(h->stream));
+            rc = batch_build(b, it->second.first, it->second.second);
+            if (rc != LBM_OK) return rc;
+            if (threads) *threads = b->threads;
+            if (band_rows) *band_rows = b->band_rows;
+            if (us_per_step) *us_per_step = 0.0;
+            if (from_cache) *from_cache = 1;
+            clear_error();
+            return LBM_OK;
+        }
+    }
+    // the trials advance the lattices: keep every lattice's device block and
+    // host step state, and put them back afterwards
+    for (lbm_handle *h : b->hs) {
+        rc = finalize(h);
+        if (rc != LBM_OK) return rc;
+        LBM_CUDA(cudaStreamSynchronize(h->stream));
+    }
+    size_t total = 0;
+    std::vector<size_t> off;
+    for (lbm_handle *h : b->hs) {
+        off.push_back(total);
+        total = align256(total + h->block_bytes);
+    }
+    void *snap = batch_alloc(b, std::max<size_t>(total, 256));
+    if (!snap) return fail(LBM_ERR_OOM, "device allocation failed (state snapshot for the trials)");
+    std::vector<int> par0;
+    std::vector<bool> pend0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto done = [&](lbm_status r) {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaStreamSynchronize(b->stream);
+        batch_free(b, snap);
+        return r;
+    };
+    for (size_t i = 0; i < b->hs.size(); ++i) {
+        lbm_handle *h = b->hs[i];
+        par0.push_back(h->parity);
+        pend0.push_back(h->pending);
+        cudaError_t e = cudaMemcpyAsync(static_cast<char *>(snap) + off[i], h->block, h->block_bytes,
+                                        cudaMemcpyDeviceToDevice, b->stream);
+        if (e != cudaSuccess) return done(cuda_fail(e, "saving the lattices' state"));
+    }
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return done(fail(LBM_ERR_CUDA, "creating timing events"));
+    const int shapes_t[3] = {32, 64, kThreads};
+    const int shapes_r[4] = {8, 16, 32, 64};
+    int best_t = b->threads, best_r = b->band_rows;
+    double best = 1e300;
+    int par = b->hs[0]->parity;
+    for (int ti = 0; ti < 3; ++ti)
+        for (int ri = 0; ri < 4; ++ri) {
+            rc = batch_build(b, shapes_t[ti], shapes_r[ri]);
+            if (rc != LBM_OK) return done(rc);
+            double t_min = 1e300;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaError_t e = cudaEventRecord(e0, b->stream);
+                for (int q = 0; q < trial_steps && e == cudaSuccess; ++q) {
+                    e = enqueue_batch_step(b, par, b->stream);
+                    par ^= 1;
+                }
+                if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) return done(cuda_fail(e, "timing a batch shape"));
+                if (rep > 0) t_min = std::min(t_min, (double)ms);   // the first repetition warms up
+            }
+            if (t_min < best) {
+                best = t_min;
+                best_t = shapes_t[ti];
+                best_r = shapes_r[ri];
+            }
+        }
+    for (size_t i = 0; i < b->hs.size(); ++i) {
+        lbm_handle *h = b->hs[i];
+        cudaError_t e = cudaMemcpyAsync(h->block, static_cast<char *>(snap) + off[i], h->block_bytes,
+                                        cudaMemcpyDeviceToDevice, b->stream);
+        if (e != cudaSuccess) return done(cuda_fail(e, "restoring the lattices' state"));
+        h->parity = par0[i];
+        h->pending = pend0[i];
+    }
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return done(cuda_fail(e, "restoring the lattices' state"));
+    // the restored blocks hold the unit tables of the shape in force at the
+    // snapshot: partition again for the chosen shape
+    rc = batch_build(b, best_t, best_r);
+    if (rc != LBM_OK) return done(rc);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = std::make_pair(best_t, best_r);
+    }
+    if (threads) *threads = best_t;
+    if (band_rows) *band_rows = best_r;
+    if (us_per_step) *us_per_step = best * 1e3 / trial_steps;
+    if (from_cache) *from_cache = 0;
+    clear_error();
+    return done(LBM_OK);
 }
 
 lbm_status lbm_batch_step(lbm_batch *b, int64_t n)
@@ -1813,6 +2059,11 @@ lbm_status lbm_batch_step(lbm_batch *b, int64_t n)
     }
     int par = par0;
     int64_t left = n;
+    if (b->persistent && n > 0) {
+        LBM_CUDA(enqueue_batch_persistent(b, par, n, b->stream));
+        par ^= (int)(n & 1);
+        left = 0;
+    }
     while (left > 0) {
         if (left >= kGraphChunk) {
             if (!b->gexec) {
@@ -1863,11 +2114,40 @@ void lbm_batch_destroy(lbm_batch *b)
     cudaStreamSynchronize(b->stream);
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-    if (b->block) {
-        if (b->custom_alloc) b->alloc.release(b->block, b->alloc.ctx);
-        else cudaFree(b->block);
-    }
+    batch_release_block(b);
+    batch_free(b, b->bar);
     delete b;
+}
+
+lbm_status lbm_batch_set_persistent(lbm_batch *b, int32_t enable, int64_t budget_cycles)
+{
+    if (!b) return fail(LBM_ERR_ARG, "batch is NULL");
+    if (budget_cycles < 0 || budget_cycles > ((int64_t)1 << 40)) return fail(LBM_ERR_ARG, "budget out of range");
+    b->persistent = enable != 0;
+    b->budget = budget_cycles > 0 ? (long long)budget_cycles : (long long)1 << 31;
+    clear_error();
+    return LBM_OK;
+}
+
+lbm_status lbm_barrier_probe(int32_t ctas, int32_t expected, int64_t budget_cycles, void *stream)
+{
+    if (ctas < 1 || ctas > 64 || expected < 1 || expected > 64) return fail(LBM_ERR_ARG, "ctas and expected in [1, 64]");
+    if (budget_cycles < 1000 || budget_cycles > ((int64_t)1 << 34)) return fail(LBM_ERR_ARG, "budget out of range");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void *mem = nullptr;
+    LBM_CUDA(cudaMalloc(&mem, 256));
+    GridBarrier *bar = static_cast<GridBarrier *>(mem);
+    uint32_t *err = reinterpret_cast<uint32_t *>(static_cast<char *>(mem) + 128);
+    uint32_t host_err = 0;
+    cudaError_t e = cudaMemsetAsync(mem, 0, 256, s);
+    if (e == cudaSuccess) e = launch_barrier_probe(bar, ctas, expected, (long long)budget_cycles, err, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&host_err, err, sizeof host_err, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(mem);
+    if (e != cudaSuccess) return cuda_fail(e, "running the barrier probe");
+    if (host_err & ERR_TIMEOUT) return fail(LBM_ERR_TIMEOUT, "the bounded wait at the grid barrier gave up");
+    clear_error();
+    return LBM_OK;
 }
 
 const char *lbm_last_error(void) { return last_error(); }

@@ -44,7 +44,7 @@ enum { LEFT = 0, RIGHT = 1, BOTTOM = 2, TOP = 3 };
 enum { CRACK_NONE = 0, CRACK_STATIONARY = 1, CRACK_PRESCRIBED = 2, CRACK_KCRIT = 3 };
 enum { LOAD_ZERO = 0, LOAD_LINEAR = 1, LOAD_SIN2 = 2, LOAD_HALFSINE = 3, LOAD_SERIES = 4, LOAD_CONST = 5 };
 enum { FLAG_CLAMPED = 1, FLAG_NONFINITE = 4 };
-enum { ERR_NONFINITE = 1 };
+enum { ERR_NONFINITE = 1, ERR_TIMEOUT = 2 };
 
 template <typename T> struct Pad { static constexpr int kElems = 128 / (int)sizeof(T); };
 template <typename T> struct Vec { static constexpr int N = 16 / (int)sizeof(T); };
@@ -197,6 +197,12 @@ struct AdjArgs {
     int32_t slots, pad;
 };
 
+// The grid barrier of the persistent batched kernel: arrivals of the current
+// round and the round number (zeroed before a launch).
+struct GridBarrier {
+    unsigned int count, gen;
+};
+
 // One row copy of the halo exchange between row slabs (whole padded rows).
 struct RowCopy {
     const void *src;
@@ -204,8 +210,18 @@ struct RowCopy {
 };
 
 template <typename T, typename D> const void *step_kernel_ptr();
+// The batched step as one cooperative launch of n_steps steps (a grid
+// barrier between steps, each wait bounded by `budget` clock64 cycles).
 template <typename T, typename D>
-cudaError_t launch_batch_step(const StepArgs<T, D> *descs, const BatchUnit *units, int n_units, int par, cudaStream_t s);
+cudaError_t launch_batch_persistent(const StepArgs<T, D> *descs, int n_lat, const BatchUnit *units, int n_units,
+                                    const BatchUnit *eunits, int n_eunits, int par0, int64_t n_steps,
+                                    GridBarrier *bar, uint32_t *err, long long budget, int threads, cudaStream_t s);
+cudaError_t launch_barrier_probe(GridBarrier *bar, int ctas, int expected, long long budget, uint32_t *err,
+                                 cudaStream_t s);
+// threads: 32, 64 or kThreads per CTA (the batch's column-block width)
+template <typename T, typename D>
+cudaError_t launch_batch_step(const StepArgs<T, D> *descs, const BatchUnit *units, int n_units, int par, cudaStream_t s,
+                              int threads = kThreads);
 template <typename T, typename D> cudaError_t launch_step(const StepArgs<T, D> &a, int bands, cudaStream_t s);
 template <typename T, typename D> cudaError_t launch_edge_rule(const StepArgs<T, D> &a, cudaStream_t s);
 template <typename T, typename D> int edge_rule_count(const StepArgs<T, D> &a);

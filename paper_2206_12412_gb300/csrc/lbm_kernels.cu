@@ -73,7 +73,7 @@ struct RowArgs {
 // crack-face rule (Sec. 3.1, HH = 3), the boundary point x_B next to a severed
 // link takes w_B = 1.5 w_I - 0.5 w_II from the two new values of its column
 // further away from the crack, and wdot(x_B) = (w_B(t+dt) - w_B(t)) / dt.
-template <typename T, typename D, int HH>
+template <typename T, typename D, int HH, int TH = kThreads, bool COH = false>
 __device__ __noinline__ T crack_rows(const T *w_in_, T *w_out_, D *wd_, T wd_scale_, int64_t pitch_, int nx_, int ny_,
                                      int jc_, int macro_, int edges, T g_, T dt_, const uint32_t *cut_v_, int words_,
                                      const CrackState *s_in_, int cb, int j0)
@@ -100,7 +100,7 @@ __device__ __noinline__ T crack_rows(const T *w_in_, T *w_out_, D *wd_, T wd_sca
     typedef Row<T, N> R;
     const unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int x0 = (cb * kThreads + threadIdx.x) * N;
+    const int x0 = (cb * TH + threadIdx.x) * N;
     const int jc = a.jc;
     const int64_t P = a.pitch;
     const T *win = a.w_in + x0;
@@ -108,7 +108,7 @@ __device__ __noinline__ T crack_rows(const T *w_in_, T *w_out_, D *wd_, T wd_sca
     R w[HH + 2], wd[HH];
     T hl[HH], hr[HH];
 #pragma unroll
-    for (int q = 0; q < HH + 2; ++q) ldg_row(win + (int64_t)(j0 - 1 + q) * P, w[q]);
+    for (int q = 0; q < HH + 2; ++q) load_w<COH>(win + (int64_t)(j0 - 1 + q) * P, w[q]);
 #pragma unroll
     for (int q = 0; q < HH; ++q) {
         WdIO<D>::load(a.wd + x0 + (int64_t)(j0 + q) * P, wd[q], a.wd_inv);
@@ -160,23 +160,23 @@ __device__ __noinline__ T crack_rows(const T *w_in_, T *w_out_, D *wd_, T wd_sca
 // warp shuffles; lanes 0 and 31 load the halo column.  The next row's loads
 // are issued before the current row is computed.  EDGE = false is the
 // interior version (no edge row or column in the warp): the bare update.
-template <typename T, typename D, bool EDGE>
+template <typename T, typename D, bool EDGE, int TH = kThreads, bool COH = false>
 __device__ __forceinline__ void march(const StepArgs<T, D> &a, int cb, int j0, int j1, T &acc)
 {
     constexpr int N = Vec<T>::N;
     typedef Row<T, N> R;
     const unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int x0 = (cb * kThreads + threadIdx.x) * N;
+    const int x0 = (cb * TH + threadIdx.x) * N;
     const int64_t P = a.pitch;
     const T *win = a.w_in + x0;
     T *wout = a.w_out + x0;
     D *wdp = a.wd + x0;
     const T wd_inv = a.wd_inv, wd_scale = a.wd_scale;
     R wb, wc, wa, wdv;
-    ldg_row(win + (int64_t)(j0 - 1) * P, wb);
-    ldg_row(win + (int64_t)j0 * P, wc);
-    ldg_row(win + (int64_t)(j0 + 1) * P, wa);
+    load_w<COH>(win + (int64_t)(j0 - 1) * P, wb);
+    load_w<COH>(win + (int64_t)j0 * P, wc);
+    load_w<COH>(win + (int64_t)(j0 + 1) * P, wa);
     WdIO<D>::load(wdp + (int64_t)j0 * P, wdv, wd_inv);
     // 16-bit wdot rows carry half the bytes of an FP32 row: keep two in
     // flight (rows j + 1 and j + 2) so that a warp has as many wdot bytes
@@ -196,7 +196,7 @@ __device__ __forceinline__ void march(const StepArgs<T, D> &a, int cb, int j0, i
         T hln = (T)0, hrn = (T)0;
         const bool more = j + 1 < j1;
         if (more) {
-            ldg_row(win + (int64_t)(j + 2) * P, wn);
+            load_w<COH>(win + (int64_t)(j + 2) * P, wn);
             if (DEEP) {
                 if (j + 2 < j1) WdIO<D>::fetch(wdp + (int64_t)(j + 2) * P, wdn);
             } else {
@@ -250,7 +250,11 @@ __device__ __forceinline__ void march(const StepArgs<T, D> &a, int cb, int j0, i
 // BOTH: compiled with the path that evaluates the two ends of a two-tip
 // crack at once when one CTA holds both (kept out of the single-tip
 // kernels, whose march it slows through the larger kernel).
-template <typename T, typename D, bool REC, bool BOTH = false>
+// TH: threads of the CTA (a column block is TH 16-byte vectors wide); the
+// single-lattice kernels use kThreads, the batched kernel any multiple of 32.
+// COH: w read with coherent loads (the persistent batched kernel, where the
+// same launch wrote it).
+template <typename T, typename D, bool REC, bool BOTH = false, int TH = kThreads, bool COH = false>
 __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int band, CrackState &sS, const RecArgs &r)
 {
     constexpr int N = Vec<T>::N;
@@ -267,7 +271,7 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
         // two crack sub-band CTAs that own the next link of each end: both
         // reach the same decision; the one below the crack records it, each
         // end writing only its own fields of the next state.
-        const int cols = kThreads * N;
+        const int cols = TH * N;
         int i_next = a.s_in->i_last + 1;
         i_next = max(i_next, a.s_in->i_first);
         i_next = min(max(i_next, 0), nx - 1);
@@ -335,10 +339,10 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
             }
         }
         const int edges = a.edge[0] | (a.edge[1] << 2) | (a.edge[2] << 4) | (a.edge[3] << 6);
-        acc = p.macro ? crack_rows<T, D, 3>(a.w_in, a.w_out, a.wd, a.wd_scale, a.pitch, a.nx, a.ny, p.jc, p.macro,
-                                            edges, a.g, a.dt, a.cut_v, a.words, a.s_in, cb, j0)
-                      : crack_rows<T, D, 1>(a.w_in, a.w_out, a.wd, a.wd_scale, a.pitch, a.nx, a.ny, p.jc, p.macro,
-                                            edges, a.g, a.dt, a.cut_v, a.words, a.s_in, cb, j0);
+        acc = p.macro ? crack_rows<T, D, 3, TH, COH>(a.w_in, a.w_out, a.wd, a.wd_scale, a.pitch, a.nx, a.ny, p.jc,
+                                                p.macro, edges, a.g, a.dt, a.cut_v, a.words, a.s_in, cb, j0)
+                      : crack_rows<T, D, 1, TH, COH>(a.w_in, a.w_out, a.wd, a.wd_scale, a.pitch, a.nx, a.ny, p.jc,
+                                                p.macro, edges, a.g, a.dt, a.cut_v, a.words, a.s_in, cb, j0);
     } else {
         if (a.crack_band < 0 && cb == 0 && band == 0 && tid == 0) {
             // no crack: only the step counter and the Dirichlet values advance
@@ -353,13 +357,13 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
         }
         // the edge rules per warp: only warps whose columns reach an outer edge,
         // and the bands holding the bottom and top rows, need them
-        const int xw0 = (cb * kThreads + (tid & ~31)) * N;   // first column of this warp
+        const int xw0 = (cb * TH + (tid & ~31)) * N;   // first column of this warp
         const bool edge = (xw0 == 0) | (xw0 + 32 * N - 1 >= nx - 1) | (j0 == 0) | (j1 == a.ny);
         // warps wholly right of the lattice (the ragged last column block) have
         // nothing to load or store
         if (xw0 < nx) {
-            if (edge) march<T, D, true>(a, cb, j0, j1, acc);
-            else march<T, D, false>(a, cb, j0, j1, acc);
+            if (edge) march<T, D, true, TH, COH>(a, cb, j0, j1, acc);
+            else march<T, D, false, TH, COH>(a, cb, j0, j1, acc);
         }
     }
     // a non-finite w (or wdot, which enters w) turns the sum of the first
@@ -374,7 +378,7 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
             // one thread per sensor of the list (each sensor appears once)
             const int u = band * a.ncb + cb;
             const int lo = r.s_off[u], hi = r.s_off[u + 1];
-            for (int q = lo + tid; q < hi; q += kThreads) {
+            for (int q = lo + tid; q < hi; q += TH) {
                 const int k = r.s_ent[q];
                 const double wv = (double)a.w_out[(int64_t)r.s_j[k] * a.pitch + r.s_i[k]];
                 const double res = wv - r.target[t * r.ns + k];
@@ -403,9 +407,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
 
 // Many independent lattices in one launch: CTA u runs unit u of the batch,
 // with its lattice's arguments (for the current parity) copied to shared
-// memory first.
-template <typename T, typename D>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBlocks - 2)
+// memory first.  TH threads per CTA: the column blocks of a batch are TH
+// vectors wide (TH * 4 FP32 columns), chosen per batch (lbm_batch_tune) so
+// that few warps fall right of their lattice.  Occupancy is register bound
+// at 64 registers, i.e. the same 32 warps per SM for every TH.
+template <typename T, typename D, int TH>
+__global__ void __launch_bounds__(TH, (sizeof(T) == 4 ? kMinBlocks : kMinBlocks - 2) * (kThreads / TH))
     batch_step_kernel(const StepArgs<T, D> *descs, const BatchUnit *units, int par)
 {
     __shared__ CrackState sS;
@@ -413,9 +420,151 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
     const BatchUnit u = units[blockIdx.x];
     const uint32_t *src = reinterpret_cast<const uint32_t *>(descs + 2 * u.inst + par);
     uint32_t *dst = reinterpret_cast<uint32_t *>(&sa);
-    for (int q = threadIdx.x; q < (int)(sizeof(StepArgs<T, D>) / 4); q += blockDim.x) dst[q] = src[q];
+    for (int q = threadIdx.x; q < (int)(sizeof(StepArgs<T, D>) / 4); q += TH) dst[q] = src[q];
     __syncthreads();
-    step_cta<T, D, false>(sa, u.cb, u.band, sS, RecArgs{});
+    step_cta<T, D, false, false, TH>(sa, u.cb, u.band, sS, RecArgs{});
+}
+
+// ----------------------------------------- persistent batched step
+//
+// One cooperative launch advances every lattice of a batch by n steps: each
+// CTA takes the units u = blockIdx.x, blockIdx.x + gridDim.x, ... of a step,
+// then all CTAs meet at a grid barrier before the next step (and between a
+// step and its edge-rule units).  The wait at the barrier is bounded: after
+// `budget` clock64 cycles a CTA sets ERR_TIMEOUT in the batch's error word
+// and in every lattice's, and returns; the others then give up at their next
+// wait (they see the flag), so the launch always ends.  w is read with
+// coherent loads, since the launch itself wrote the previous step's w.
+
+template <typename T, typename D>
+__device__ __forceinline__ void edge_rule_at(const StepArgs<T, D> &a, int t);
+
+// Arrive and wait until `expected` CTAs have arrived (bounded).  Returns
+// false (and sets ERR_TIMEOUT in *err) if the wait gave up.
+__device__ __forceinline__ bool grid_barrier(GridBarrier *bar, unsigned expected, long long budget, uint32_t *err)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned *vg = &bar->gen;
+        volatile uint32_t *ve = err;
+        const unsigned g = *vg;
+        __threadfence();   // this CTA's stores (ordered by the CTA barrier) before the arrival
+        if (atomicAdd(&bar->count, 1u) == expected - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*vg == g) {
+                if ((*ve & ERR_TIMEOUT) || clock64() - t0 > budget) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();   // the other CTAs' stores before this CTA's next loads
+        if (!ok) atomicOr(err, (uint32_t)ERR_TIMEOUT);
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <typename T, typename D>
+__device__ void flag_timeout(const StepArgs<T, D> *descs, int n_lat)
+{
+    for (int i = threadIdx.x; i < n_lat; i += blockDim.x) atomicOr(descs[2 * i].err, (uint32_t)ERR_TIMEOUT);
+}
+
+template <typename T, typename D, int TH>
+__global__ void __launch_bounds__(TH, (sizeof(T) == 4 ? kMinBlocks : kMinBlocks - 2) * (kThreads / TH))
+    batch_persistent_kernel(const StepArgs<T, D> *descs, int n_lat, const BatchUnit *units, int n_units,
+                            const BatchUnit *eunits, int n_eunits, int par0, int64_t n_steps, GridBarrier *bar,
+                            uint32_t *err, long long budget)
+{
+    __shared__ CrackState sS;
+    __shared__ __align__(16) StepArgs<T, D> sa;
+    const unsigned nb = gridDim.x;
+    for (int64_t k = 0; k < n_steps; ++k) {
+        const int par = par0 ^ (int)(k & 1);
+        for (int q = blockIdx.x; q < n_units; q += nb) {
+            const BatchUnit u = units[q];
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(descs + 2 * u.inst + par);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&sa);
+            __syncthreads();   // the previous unit is done with sa and sS
+            for (int t = threadIdx.x; t < (int)(sizeof(StepArgs<T, D>) / 4); t += TH) dst[t] = src[t];
+            __syncthreads();
+            step_cta<T, D, false, false, TH, true>(sa, u.cb, u.band, sS, RecArgs{});
+        }
+        if (n_eunits > 0) {
+            if (!grid_barrier(bar, nb, budget, err)) {
+                flag_timeout(descs, n_lat);
+                return;
+            }
+            for (int q = blockIdx.x; q < n_eunits; q += nb) {
+                const BatchUnit u = eunits[q];
+                for (int t = threadIdx.x; t < 128; t += TH) edge_rule_at(descs[2 * u.inst + par], u.cb + t);
+            }
+        }
+        if (!grid_barrier(bar, nb, budget, err)) {
+            flag_timeout(descs, n_lat);
+            return;
+        }
+    }
+}
+
+// A diagnostic of the bounded wait: `ctas` CTAs meet at a barrier that
+// expects `expected` arrivals; with fewer CTAs than expected nothing
+// completes it and every wait gives up after `budget` cycles.
+__global__ void barrier_probe_kernel(GridBarrier *bar, unsigned expected, long long budget, uint32_t *err)
+{
+    grid_barrier(bar, expected, budget, err);
+}
+
+cudaError_t launch_barrier_probe(GridBarrier *bar, int ctas, int expected, long long budget, uint32_t *err,
+                                 cudaStream_t s)
+{
+    barrier_probe_kernel<<<(unsigned)ctas, 32, 0, s>>>(bar, (unsigned)expected, budget, err);
+    return cudaGetLastError();
+}
+
+template <typename T, typename D>
+cudaError_t persistent_grid(int threads, int n_units, int *grid)
+{
+    const void *fn = nullptr;
+    switch (threads) {
+    case 32: fn = reinterpret_cast<const void *>(&batch_persistent_kernel<T, D, 32>); break;
+    case 64: fn = reinterpret_cast<const void *>(&batch_persistent_kernel<T, D, 64>); break;
+    case kThreads: fn = reinterpret_cast<const void *>(&batch_persistent_kernel<T, D, kThreads>); break;
+    default: return cudaErrorInvalidValue;
+    }
+    int dev = 0, sms = 0, bps = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, threads, 0);
+    if (e != cudaSuccess) return e;
+    const int cap = sms * bps;
+    *grid = n_units < cap ? n_units : cap;
+    return *grid > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
+}
+
+template <typename T, typename D>
+cudaError_t launch_batch_persistent(const StepArgs<T, D> *descs, int n_lat, const BatchUnit *units, int n_units,
+                                    const BatchUnit *eunits, int n_eunits, int par0, int64_t n_steps,
+                                    GridBarrier *bar, uint32_t *err, long long budget, int threads, cudaStream_t s)
+{
+    int grid = 0;
+    cudaError_t e = persistent_grid<T, D>(threads, n_units, &grid);
+    if (e != cudaSuccess) return e;
+    void *args[] = {(void *)&descs, (void *)&n_lat, (void *)&units, (void *)&n_units, (void *)&eunits,
+                    (void *)&n_eunits, (void *)&par0, (void *)&n_steps, (void *)&bar, (void *)&err, (void *)&budget};
+    const void *fn = threads == 32 ? reinterpret_cast<const void *>(&batch_persistent_kernel<T, D, 32>)
+                   : threads == 64 ? reinterpret_cast<const void *>(&batch_persistent_kernel<T, D, 64>)
+                                   : reinterpret_cast<const void *>(&batch_persistent_kernel<T, D, kThreads>);
+    return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3((unsigned)threads), args, 0, s);
 }
 
 template <typename T, typename D> const void *step_kernel_ptr()
@@ -441,9 +590,15 @@ cudaError_t launch_step_rec(const StepArgs<T, T> &a, const RecArgs &r, int bands
 }
 
 template <typename T, typename D>
-cudaError_t launch_batch_step(const StepArgs<T, D> *descs, const BatchUnit *units, int n_units, int par, cudaStream_t s)
+cudaError_t launch_batch_step(const StepArgs<T, D> *descs, const BatchUnit *units, int n_units, int par, cudaStream_t s,
+                              int threads)
 {
-    batch_step_kernel<T, D><<<(unsigned)n_units, kThreads, 0, s>>>(descs, units, par);
+    switch (threads) {
+    case 32: batch_step_kernel<T, D, 32><<<(unsigned)n_units, 32, 0, s>>>(descs, units, par); break;
+    case 64: batch_step_kernel<T, D, 64><<<(unsigned)n_units, 64, 0, s>>>(descs, units, par); break;
+    case kThreads: batch_step_kernel<T, D, kThreads><<<(unsigned)n_units, kThreads, 0, s>>>(descs, units, par); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
@@ -780,10 +935,14 @@ template cudaError_t launch_step<float, __nv_bfloat16>(const StepArgs<float, __n
 template cudaError_t launch_step<float, __half>(const StepArgs<float, __half> &, int, cudaStream_t);
 template cudaError_t launch_step_rec<double>(const StepArgs<double, double> &, const RecArgs &, int, cudaStream_t);
 template cudaError_t launch_step_rec<float>(const StepArgs<float, float> &, const RecArgs &, int, cudaStream_t);
-template cudaError_t launch_batch_step<double, double>(const StepArgs<double, double> *, const BatchUnit *, int, int, cudaStream_t);
-template cudaError_t launch_batch_step<float, float>(const StepArgs<float, float> *, const BatchUnit *, int, int, cudaStream_t);
-template cudaError_t launch_batch_step<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> *, const BatchUnit *, int, int, cudaStream_t);
-template cudaError_t launch_batch_step<float, __half>(const StepArgs<float, __half> *, const BatchUnit *, int, int, cudaStream_t);
+template cudaError_t launch_batch_step<double, double>(const StepArgs<double, double> *, const BatchUnit *, int, int, cudaStream_t, int);
+template cudaError_t launch_batch_step<float, float>(const StepArgs<float, float> *, const BatchUnit *, int, int, cudaStream_t, int);
+template cudaError_t launch_batch_step<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> *, const BatchUnit *, int, int, cudaStream_t, int);
+template cudaError_t launch_batch_step<float, __half>(const StepArgs<float, __half> *, const BatchUnit *, int, int, cudaStream_t, int);
+template cudaError_t launch_batch_persistent<double, double>(const StepArgs<double, double> *, int, const BatchUnit *, int, const BatchUnit *, int, int, int64_t, GridBarrier *, uint32_t *, long long, int, cudaStream_t);
+template cudaError_t launch_batch_persistent<float, float>(const StepArgs<float, float> *, int, const BatchUnit *, int, const BatchUnit *, int, int, int64_t, GridBarrier *, uint32_t *, long long, int, cudaStream_t);
+template cudaError_t launch_batch_persistent<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> *, int, const BatchUnit *, int, const BatchUnit *, int, int, int64_t, GridBarrier *, uint32_t *, long long, int, cudaStream_t);
+template cudaError_t launch_batch_persistent<float, __half>(const StepArgs<float, __half> *, int, const BatchUnit *, int, const BatchUnit *, int, int, int64_t, GridBarrier *, uint32_t *, long long, int, cudaStream_t);
 template cudaError_t launch_wd_to_f32<__nv_bfloat16>(const __nv_bfloat16 *, int64_t, int, int, float, float *, cudaStream_t);
 template cudaError_t launch_wd_to_f32<__half>(const __half *, int64_t, int, int, float, float *, cudaStream_t);
 template cudaError_t launch_wd_from_f32<__nv_bfloat16>(__nv_bfloat16 *, int64_t, int, int, float, const float *, cudaStream_t);

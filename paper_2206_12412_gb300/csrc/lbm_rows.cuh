@@ -39,6 +39,15 @@ __device__ __forceinline__ void ld_row(const double *p, Row<double, 2> &r)
     double2 q = *reinterpret_cast<const double2 *>(p);
     r.v[0] = q.x; r.v[1] = q.y;
 }
+// w of the input buffer: through the read-only path (NC), or with coherent
+// loads when the same launch wrote it (a persistent kernel that steps many
+// times, whose grid barrier orders the steps' stores and loads).
+template <bool COH, typename T, int N>
+__device__ __forceinline__ void load_w(const T *p, Row<T, N> &r)
+{
+    if (COH) ld_row(p, r);
+    else ldg_row(p, r);
+}
 __device__ __forceinline__ void stg_row(float *p, const Row<float, 4> &r)
 {
     *reinterpret_cast<float4 *>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);

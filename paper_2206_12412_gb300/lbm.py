@@ -490,6 +490,31 @@ def lbm_batch_info(b: int):
     return {"lattices": nl.value, "ctas": ct.value}
 
 
+def lbm_batch_set_shape(b: int, threads: int, band_rows: int):
+    _check(load_library().lbm_batch_set_shape(C.c_void_p(b), int(threads), int(band_rows)))
+
+
+def lbm_batch_get_shape(b: int):
+    t, r = C.c_int32(), C.c_int32()
+    _check(load_library().lbm_batch_get_shape(C.c_void_p(b), C.byref(t), C.byref(r)))
+    return {"threads": t.value, "band_rows": r.value}
+
+
+def lbm_batch_tune(b: int, trial_steps: int = 8):
+    t, r, us, fc = C.c_int32(), C.c_int32(), C.c_double(), C.c_int32()
+    _check(load_library().lbm_batch_tune(C.c_void_p(b), int(trial_steps), C.byref(t), C.byref(r), C.byref(us),
+                                         C.byref(fc)))
+    return {"threads": t.value, "band_rows": r.value, "us_per_step": us.value, "from_cache": bool(fc.value)}
+
+
+def lbm_batch_set_persistent(b: int, enable: bool, budget_cycles: int = 0):
+    _check(load_library().lbm_batch_set_persistent(C.c_void_p(b), 1 if enable else 0, int(budget_cycles)))
+
+
+def lbm_barrier_probe(ctas: int, expected: int, budget_cycles: int, stream: int = 0):
+    _check(load_library().lbm_barrier_probe(int(ctas), int(expected), int(budget_cycles), C.c_void_p(stream)))
+
+
 def lbm_batch_destroy(b: int):
     if b:
         load_library().lbm_batch_destroy(C.c_void_p(b))
@@ -508,7 +533,20 @@ class Batch:
         lbm_batch_step(self.b, n)
 
     def info(self) -> dict:
-        return lbm_batch_info(self.b)
+        return dict(lbm_batch_info(self.b), **lbm_batch_get_shape(self.b))
+
+    def set_shape(self, threads: int, band_rows: int):
+        lbm_batch_set_shape(self.b, threads, band_rows)
+
+    def set_persistent(self, enable: bool = True, budget_cycles: int = 0):
+        """One cooperative launch per lbm_batch_step call (grid barrier
+        between steps, each wait bounded by budget_cycles)."""
+        lbm_batch_set_persistent(self.b, enable, budget_cycles)
+
+    def tune(self, trial_steps: int = 8) -> dict:
+        """Pick the fastest launch shape (lbm_batch_tune); the lattices'
+        state is left as it was."""
+        return lbm_batch_tune(self.b, trial_steps)
 
     def close(self):
         if getattr(self, "b", None):

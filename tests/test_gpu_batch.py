@@ -168,3 +168,116 @@ def test_batch_matches_the_oracle(oracle_mod, gpu, storage):
         o.close()
         g.close()
     assert grew >= 6   # the cracks of most lattices moved within the run
+
+
+# ------------------------------------------------------ launch shapes, tuner
+
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+@pytest.mark.parametrize("threads,rows", [(32, 8), (64, 5), (32, 64), (128, 32)])
+def test_every_launch_shape_gives_the_solo_bits(gpu, storage, threads, rows):
+    """CTAs of 32, 64 or 128 threads over bands of any height: each lattice
+    of the batch still ends bit-identical to its solo run (graph chunks and
+    single launches)."""
+    ps = mixed_problems()
+    solo = [gpu.Lattice(p, storage) for p in ps]
+    mem = [gpu.Lattice(p, storage) for p in ps]
+    for p, s, m in zip(ps, solo, mem):
+        if p["crack"]["mode"] == "none":
+            init = W.random_state(p["nx"], p["ny"], seed=9, dtype=np.float64 if storage == "f64" else np.float32)
+            s.set_fields(*init)
+            m.set_fields(*init)
+    b = gpu.Batch(mem)
+    b.set_shape(threads, rows)
+    info = b.info()
+    assert (info["threads"], info["band_rows"]) == (threads, rows)
+    b.step(3)
+    b.step(130)
+    for s in solo:
+        s.step(133)
+    for s, m in zip(solo, mem):
+        _same(s, m)
+    b.close()
+
+
+def test_tune_leaves_the_lattices_as_they_were_and_caches_the_shape(gpu):
+    ps = W.batch_problems(12, seed=8)
+    solo = [gpu.Lattice(p, "f32") for p in ps]
+    mem = [gpu.Lattice(p, "f32") for p in ps]
+    b = gpu.Batch(mem)
+    b.step(37)                       # a pending crack step at the tuning call
+    r = b.tune(trial_steps=6)
+    assert r["threads"] in (32, 64, 128) and r["band_rows"] in (8, 16, 32, 64)
+    assert not r["from_cache"] and r["us_per_step"] > 0
+    assert (b.info()["threads"], b.info()["band_rows"]) == (r["threads"], r["band_rows"])
+    b.step(63)
+    for s in solo:
+        s.step(100)
+    for s, m in zip(solo, mem):
+        _same(s, m)                  # the trials left no trace
+    b.close()
+    # a second batch of the same lattices takes the cached shape
+    mem2 = [gpu.Lattice(p, "f32") for p in ps]
+    b2 = gpu.Batch(mem2)
+    r2 = b2.tune(trial_steps=6)
+    assert r2["from_cache"] and (r2["threads"], r2["band_rows"]) == (r["threads"], r["band_rows"])
+    b2.close()
+
+
+def test_shape_arguments_are_checked(gpu):
+    ps = W.batch_problems(2, seed=6)
+    lats = [gpu.Lattice(p, "f32") for p in ps]
+    b = gpu.Batch(lats)
+    for t, r in ((48, 16), (256, 16), (32, 0)):
+        with pytest.raises(gpu.LbmError) as ei:
+            b.set_shape(t, r)
+        assert ei.value.status == -1
+    with pytest.raises(gpu.LbmError):
+        b.tune(trial_steps=1)
+    b.close()
+
+
+# ----------------------------------------------------- persistent batched form
+
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+@pytest.mark.parametrize("threads,rows", [(128, 16), (32, 32)])
+def test_persistent_launch_gives_the_solo_bits(gpu, storage, threads, rows):
+    """One cooperative launch for many steps (grid barrier between steps),
+    including a lattice with the macroscopic rule on its outer edges (its
+    edge-rule units after a second barrier): bit-identical to solo runs."""
+    ps = mixed_problems()[:6] + [W.kcrit_centre_crack(scale=2)]
+    solo = [gpu.Lattice(p, storage) for p in ps]
+    mem = [gpu.Lattice(p, storage) for p in ps]
+    for p, s, m in zip(ps, solo, mem):
+        if p["crack"]["mode"] == "none":
+            init = W.random_state(p["nx"], p["ny"], seed=13, dtype=np.float64 if storage == "f64" else np.float32)
+            s.set_fields(*init)
+            m.set_fields(*init)
+    b = gpu.Batch(mem)
+    b.set_shape(threads, rows)
+    b.set_persistent(True)
+    b.step(1)
+    b.step(150)
+    b.set_persistent(False)
+    b.step(64)                       # and back to per-step launches
+    for s in solo:
+        s.step(215)
+    for s, m in zip(solo, mem):
+        _same(s, m)
+    b.close()
+
+
+def test_bounded_barrier_wait_gives_up_with_a_timeout(gpu):
+    """A barrier that expects more CTAs than were launched is never
+    completed: every wait gives up after its budget and the call returns
+    LBM_ERR_TIMEOUT; a barrier that all its CTAs reach completes."""
+    import torch
+    s = torch.cuda.current_stream().cuda_stream
+    gpu.lbm_barrier_probe(4, 4, 1 << 24, s)
+    gpu.lbm_barrier_probe(1, 1, 1000, s)
+    with pytest.raises(gpu.LbmError) as ei:
+        gpu.lbm_barrier_probe(1, 2, 200000, s)
+    assert ei.value.status == -5
+    with pytest.raises(gpu.LbmError) as ei:
+        gpu.lbm_barrier_probe(3, 8, 200000, s)
+    assert ei.value.status == -5
+    gpu.lbm_barrier_probe(2, 2, 1 << 24, s)   # the device is still usable
