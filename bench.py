@@ -287,6 +287,21 @@ def kernel_seconds(lat):
     return pr["step_ms"] / max(pr["n_step"], 1) * 1e-3
 
 
+def profile_batched(lbm, W, torch, stream, steps, shape, count=256):
+    """Only the batched steps of the 256-lattice workload at a given launch
+    shape (for ncu captures of the batch kernel)."""
+    problems = W.batch_problems(count, seed=3)
+    lats = [lbm.Lattice(p, "f32", stream=stream) for p in problems]
+    batch = lbm.Batch(lats)
+    batch.set_shape(*shape)
+    secs = timed(torch, stream, lambda: batch.step(steps))
+    sites = sum(p["nx"] * p["ny"] for p in problems)
+    batch.close()
+    for l in lats:
+        l.close()
+    return {"shape": list(shape), "steps": steps, "glups": r4(sites * steps / secs / 1e9)}
+
+
 def measure_batched(lbm, W, torch, stream, steps, peak, count=256):
     """Batched form: 256 independent lattices of uneven sizes, one launch per
     step (graph replay), against the same lattices stepped one after another
@@ -716,6 +731,8 @@ def main():
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched measurement, --steps steps of --batched-count lattices (for ncu)")
     ap.add_argument("--batched-count", type=int, default=256, help="lattices in the batched measurement")
+    ap.add_argument("--batched-shape", default=None,
+                    help="with --batched-only: THREADS,ROWS -- only the batched steps at that launch shape")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="only the sensor-misfit gradient measurement (for ncu)")
     ap.add_argument("--adjoint-steps", type=int, default=None, help="steps of the adjoint workload (default 8000)")
@@ -738,7 +755,11 @@ def main():
         from paper_2206_12412_gb300 import lbm
         from paper_2206_12412_gb300 import workloads as W
         torch.cuda.set_device(local)
-        if args.batched_only:
+        if args.batched_only and args.batched_shape:
+            shape = tuple(int(x) for x in args.batched_shape.split(","))
+            out = {"batched_only": True, **profile_batched(lbm, W, torch, torch.cuda.current_stream(), args.steps,
+                                                           shape, count=args.batched_count)}
+        elif args.batched_only:
             peak, _ = measured_peaks()
             out = {"batched_only": True, **measure_batched(lbm, W, torch, torch.cuda.current_stream(), args.steps,
                                                            peak, count=args.batched_count)}

@@ -102,8 +102,13 @@ enum { LBM_LOAD_ZERO = 0, LBM_LOAD_LINEAR = 1, LBM_LOAD_SIN2 = 2, LBM_LOAD_HALFS
 enum { LBM_FIELD_W = 0, LBM_FIELD_WDOT = 1 };
 /* cut masks */
 enum { LBM_MASK_H = 0, LBM_MASK_V = 1 };
-/* bits of lbm_crack_state_t.flags */
-enum { LBM_FLAG_CLAMPED = 1, LBM_FLAG_NONFINITE = 4 };
+/* bits of lbm_crack_state_t.flags.  CLAMPED: the tip reached the body's
+ * boundary and stopped.  UNSUPPORTED: with macroscopic faces on a crack in
+ * any direction, a boundary point whose x_I or x_II cell reaches outside the
+ * body came under the rule (its stencil is dropped, so its value is not the
+ * rule's; the crack grew within two spacings of an edge).  NONFINITE: K or
+ * the fields stopped being finite. */
+enum { LBM_FLAG_CLAMPED = 1, LBM_FLAG_UNSUPPORTED = 2, LBM_FLAG_NONFINITE = 4 };
 
 /* Lattice extent and spacing.  dh, dt > 0.  edge[] holds an LBM_EDGE_* per
  * edge index; periodic edges come in opposite pairs. */
@@ -330,6 +335,19 @@ lbm_status lbm_set_launch(lbm_handle *h, int32_t band_rows);
  * and how many CTAs of the step kernel an SM holds (any pointer may be NULL). */
 lbm_status lbm_get_launch(const lbm_handle *h, int32_t *band_rows, int32_t *ctas, int32_t *threads,
                           int32_t *ctas_per_sm);
+
+/* The solve of the macroscopic rule on the faces of a crack in any direction
+ * (lbm_create_line with LBM_BC_MACROSCOPIC; Sec. 3.1, S w_B = R).  mode 0
+ * (default): the chunked solve -- one CTA per 256 consecutive boundary
+ * entries along the line, each solving its entries and the entries they
+ * depend on level by level (a point's stencil corners lie strictly farther
+ * from the line, so the coupling is acyclic apart from the point's own site)
+ * -- wherever the coupling is at most 64 levels deep, else the one-CTA
+ * solve; mode 1: always the one-CTA Jacobi solve to a bitwise fixpoint.
+ * Both give the rule's solution (not the same last bits).  *chunked (may be
+ * NULL) tells which one runs.  Synchronises the stream; no effect on other
+ * lattices. */
+lbm_status lbm_set_face_solve(lbm_handle *h, int32_t mode, int32_t *chunked);
 
 /* Kernel timing: while enabled, lbm_step launches every step directly (no
  * graph) with CUDA events on the handle's stream around the step kernel, and

@@ -198,6 +198,7 @@ std::vector<LineFace> line_faces_table(const LineSpec &L, int nx, int ny, std::v
                 }
             if (!inside) {
                 if (dropped) (*dropped)[q] = 1;
+                f.flags |= lbm::FACE_DROPPED;
                 continue;
             }
             for (int c = 0; c < nc; ++c) {
@@ -219,6 +220,100 @@ std::vector<LineFace> line_faces_table(const LineSpec &L, int nx, int ny, std::v
     return tab;
 }
 
+// The chunked face solve's tables (FaceChunk): chunks of kFaceChunk
+// consecutive table entries with the transitive closure of their coupled
+// corners, sorted by level.  Returns false (leaving the one-CTA solve in
+// use) when the coupling has a cycle through more than one entry, is deeper
+// than kFaceLevels, or a chunk's closure exceeds kFaceItemsMax.
+bool line_face_chunks(const std::vector<LineFace> &tab, std::vector<lbm::FaceChunk> &chunks,
+                      std::vector<lbm::FaceItem> &items)
+{
+    using lbm::kFaceChunk;
+    using lbm::kFaceItemsMax;
+    using lbm::kFaceLevels;
+    const int n = (int)tab.size();
+    auto corners = [&](int e, std::vector<int> &out) {
+        out.clear();
+        for (int k = 0; k < 8; ++k)
+            if (tab[e].a[k] != 0.0 && tab[e].cand[k] >= 0 && tab[e].cand[k] != e) out.push_back(tab[e].cand[k]);
+    };
+    // levels by depth-first search (0: unvisited, 1: on the stack, 2: done)
+    std::vector<int> level(n, 0), state(n, 0);
+    std::vector<int> cs;
+    for (int r = 0; r < n; ++r) {
+        if (state[r]) continue;
+        std::vector<std::pair<int, int>> stack{{r, 0}};
+        state[r] = 1;
+        while (!stack.empty()) {
+            const int e = stack.back().first;
+            corners(e, cs);
+            int &next = stack.back().second;
+            if (next < (int)cs.size()) {
+                const int m = cs[next++];
+                if (state[m] == 1) return false;   // a cycle
+                if (state[m] == 0) {
+                    state[m] = 1;
+                    stack.push_back({m, 0});
+                }
+                continue;
+            }
+            int lv = 0;
+            for (int m : cs) lv = std::max(lv, level[m] + 1);
+            if (lv >= kFaceLevels) return false;
+            level[e] = lv;
+            state[e] = 2;
+            stack.pop_back();
+        }
+    }
+    chunks.clear();
+    items.clear();
+    std::vector<int> local(n, -1);
+    for (int lo = 0; lo < n; lo += kFaceChunk) {
+        const int hi = std::min(n, lo + kFaceChunk);
+        std::vector<int> clo;
+        for (int e = lo; e < hi; ++e) {
+            local[e] = 0;
+            clo.push_back(e);
+        }
+        for (size_t q = 0; q < clo.size(); ++q) {
+            corners(clo[q], cs);
+            for (int m : cs)
+                if (local[m] < 0) {
+                    local[m] = 0;
+                    clo.push_back(m);
+                }
+        }
+        if ((int)clo.size() > kFaceItemsMax) return false;
+        std::stable_sort(clo.begin(), clo.end(), [&](int x, int y) {
+            return level[x] != level[y] ? level[x] < level[y] : x < y;
+        });
+        for (size_t q = 0; q < clo.size(); ++q) local[clo[q]] = (int)q;
+        lbm::FaceChunk c;
+        std::memset(&c, 0, sizeof c);
+        c.off = (int32_t)items.size();
+        c.n = (int32_t)clo.size();
+        c.own_lo = lo;
+        c.own_hi = hi;
+        for (int L = 0; L <= kFaceLevels; ++L) {
+            int q = 0;
+            while (q < (int)clo.size() && level[clo[q]] < L) ++q;
+            c.lv[L] = q;
+        }
+        for (int e : clo) {
+            lbm::FaceItem it;
+            it.f = e;
+            for (int k = 0; k < 8; ++k) {
+                const int m = tab[e].cand[k];
+                it.kl[k] = (int16_t)((tab[e].a[k] != 0.0 && m >= 0) ? local[m] : -1);
+            }
+            items.push_back(it);
+        }
+        chunks.push_back(c);
+        for (int e : clo) local[e] = -1;
+    }
+    return true;
+}
+
 }  // namespace
 
 
@@ -232,7 +327,10 @@ cudaError_t enqueue_step_t(const lbm_handle *h, int par, cudaStream_t s)
     make_step_args(h, par, a);
     if (h->line) {
         cudaError_t e = launch_line_step(a, s);
-        if (e == cudaSuccess && h->n_faces > 0) e = launch_line_faces(a, h->faces, h->n_faces, h->face_scratch, s);
+        if (e == cudaSuccess && h->n_face_chunks > 0 && h->face_solve == 0)
+            e = launch_line_faces_chunked(a, h->faces, h->face_chunks, h->n_face_chunks, h->face_items, s);
+        else if (e == cudaSuccess && h->n_faces > 0)
+            e = launch_line_faces(a, h->faces, h->n_faces, h->face_scratch, s);
         return e;
     }
     if constexpr (std::is_same<T, D>::value) {
@@ -870,8 +968,16 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
             // the macroscopic rule on the crack's faces: the tabulated points
             const std::vector<LineFace> tab = line_faces_table(*line, grid->nx, grid->ny);
             h->n_faces = (int32_t)tab.size();
+            std::vector<lbm::FaceChunk> chunks;
+            std::vector<lbm::FaceItem> items;
+            const bool chunked = !tab.empty() && line_face_chunks(tab, chunks, items);
             if (!tab.empty()) {
-                h->faces = static_cast<LineFace *>(dev_alloc(h, tab.size() * sizeof(LineFace)));
+                // the table, the chunk tables (the chunked solve, where the
+                // coupling allows it) and the one-CTA solve's scratch
+                const size_t o_ch = align256(tab.size() * sizeof(LineFace));
+                const size_t o_it = o_ch + align256(chunks.size() * sizeof(lbm::FaceChunk));
+                const size_t fbytes = o_it + items.size() * sizeof(lbm::FaceItem);
+                h->faces = static_cast<LineFace *>(dev_alloc(h, fbytes));
                 h->face_scratch = static_cast<double *>(dev_alloc(h, tab.size() * lbm::kLineFaceScratch));
                 if (!h->faces || !h->face_scratch) {
                     dev_free(h, h->faces);
@@ -879,6 +985,18 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
                     return bail(fail(LBM_ERR_OOM, "device allocation failed"));
                 }
                 e = cudaMemcpyAsync(h->faces, tab.data(), tab.size() * sizeof(LineFace), cudaMemcpyHostToDevice, s);
+                if (chunked) {
+                    char *base = reinterpret_cast<char *>(h->faces);
+                    h->face_chunks = reinterpret_cast<lbm::FaceChunk *>(base + o_ch);
+                    h->face_items = reinterpret_cast<lbm::FaceItem *>(base + o_it);
+                    h->n_face_chunks = (int32_t)chunks.size();
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(h->face_chunks, chunks.data(), chunks.size() * sizeof(lbm::FaceChunk),
+                                            cudaMemcpyHostToDevice, s);
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(h->face_items, items.data(), items.size() * sizeof(lbm::FaceItem),
+                                            cudaMemcpyHostToDevice, s);
+                }
                 if (e == cudaSuccess) e = cudaStreamSynchronize(s);
                 if (e != cudaSuccess) {
                     dev_free(h, h->faces);
@@ -1314,6 +1432,20 @@ lbm_status lbm_set_launch(lbm_handle *h, int32_t band_rows)
     LBM_CUDA(cudaStreamSynchronize(h->stream));
     drop_graph(h);
     return plan_bands(h, band_rows);
+}
+
+lbm_status lbm_set_face_solve(lbm_handle *h, int32_t mode, int32_t *chunked)
+{
+    if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
+    if (mode != 0 && mode != 1) return fail(LBM_ERR_ARG, "mode must be 0 (chunked where possible) or 1 (one CTA)");
+    if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");
+    LBM_CUDA(cudaStreamSynchronize(h->stream));
+    h->face_solve = mode;
+    drop_graph(h);
+    h->gen += 1;
+    if (chunked) *chunked = (h->n_face_chunks > 0 && mode == 0) ? 1 : 0;
+    clear_error();
+    return LBM_OK;
 }
 
 lbm_status lbm_get_launch(const lbm_handle *h, int32_t *band_rows, int32_t *ctas, int32_t *threads,

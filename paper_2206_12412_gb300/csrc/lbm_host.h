@@ -34,7 +34,11 @@ struct lbm_handle {
     bool line;           // a straight crack in any direction (line_step_kernel)
     lbm::LineFace *faces;  // its tabulated boundary points (macroscopic faces), device
     int32_t n_faces;
-    double *face_scratch;  // the face solve's scratch (lbm::FaceScratch, kLineFaceScratch bytes per point), device
+    double *face_scratch;  // the one-CTA face solve's scratch (lbm::FaceScratch, kLineFaceScratch bytes per point), device
+    lbm::FaceChunk *face_chunks;   // the chunked face solve's tables (inside the faces allocation), device
+    lbm::FaceItem *face_items;
+    int32_t n_face_chunks;         // 0: the one-CTA solve
+    int32_t face_solve;            // 0: chunked where the table allows, 1: always the one-CTA solve
     // step kernel shape
     int32_t ncb;         // column blocks of kThreads vectors
     int32_t n_bands, band_rows, crack_band, sms, bps;

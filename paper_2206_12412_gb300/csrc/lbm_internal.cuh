@@ -43,7 +43,7 @@ enum { EDGE_FREE = 0, EDGE_DIRICHLET = 1, EDGE_PERIODIC = 2, EDGE_HALO = 3 };
 enum { LEFT = 0, RIGHT = 1, BOTTOM = 2, TOP = 3 };
 enum { CRACK_NONE = 0, CRACK_STATIONARY = 1, CRACK_PRESCRIBED = 2, CRACK_KCRIT = 3 };
 enum { LOAD_ZERO = 0, LOAD_LINEAR = 1, LOAD_SIN2 = 2, LOAD_HALFSINE = 3, LOAD_SERIES = 4, LOAD_CONST = 5 };
-enum { FLAG_CLAMPED = 1, FLAG_NONFINITE = 4 };
+enum { FLAG_CLAMPED = 1, FLAG_UNSUPPORTED = 2, FLAG_NONFINITE = 4 };
 enum { ERR_NONFINITE = 1, ERR_TIMEOUT = 2 };
 
 template <typename T> struct Pad { static constexpr int kElems = 128 / (int)sizeof(T); };

@@ -745,8 +745,110 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
     claimed_groups<T, D>(a, E, C, u, n_march);
 }
 
+// Is tabulated site (i, j) a boundary point now, i.e. is one of its links
+// severed (read after the step, so the cuts of this step's crack step count)?
+template <typename T, typename D>
+__device__ __forceinline__ bool face_is_point(const StepArgs<T, D> &a, int i, int j)
+{
+    const int words = a.words;
+    const uint32_t *ch = a.cut_h + (int64_t)j * words, *cv = a.cut_v + (int64_t)j * words;
+    bool cut = (ch[i >> 5] >> (i & 31)) & 1u;
+    if (i >= 1) cut |= (ch[(i - 1) >> 5] >> ((i - 1) & 31)) & 1u;
+    if (j + 1 < a.ny) cut |= (cv[i >> 5] >> (i & 31)) & 1u;
+    if (j >= 1) cut |= ((cv - words)[i >> 5] >> (i & 31)) & 1u;
+    return cut;
+}
+
+// Report a point the rule does not support (a dropped stencil) or a solve
+// that did not settle: FLAG_UNSUPPORTED in the state after this step, both
+// ends (lbm_crack_state and lbm_crack_state_left read it).
+template <typename T, typename D>
+__device__ __forceinline__ void face_unsupported(const StepArgs<T, D> &a)
+{
+    atomicOr(&a.s_out->r.flags, (int32_t)FLAG_UNSUPPORTED);
+    atomicOr(&a.s_out->l.flags, (int32_t)FLAG_UNSUPPORTED);
+}
+
 // The macroscopic rule on the faces of a crack in any direction (Sec. 3.1),
-// after the march, in one CTA.  It lists the tabulated points whose site has
+// after the march: chunk blockIdx.x of the table (see FaceChunk), one CTA
+// each.  A CTA whose own entries hold no point leaves at once; the others
+// read which of their items are points and the items' current w (this
+// step's update), then solve the points level by level -- a point's value
+// w_B = sum_k a_k w(corner_k) reads only corners of lower levels (solved,
+// or fixed where they are no point) and its own site, whose weight (below
+// 0.2) is solved by a scalar iteration -- and write their own points' w_B,
+// wdot_B = (w_B - w_B(t)) / dt and pad images.  Items that several chunks
+// hold are computed alike in each (same inputs, same order of terms).
+template <typename T, typename D>
+__global__ void __launch_bounds__(256) line_faces_chunk_kernel(const StepArgs<T, D> a, const LineFace *F,
+                                                               const FaceChunk *Cs, const FaceItem *I)
+{
+    __shared__ double val[kFaceItemsMax];
+    __shared__ uint8_t act[kFaceItemsMax];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const FaceChunk &C = Cs[blockIdx.x];
+    const int64_t P = a.pitch;
+    int any = 0;
+    for (int c = C.own_lo + tid; c < C.own_hi; c += nt) any |= face_is_point(a, F[c].i, F[c].j);
+    if (!__syncthreads_or(any)) return;
+    for (int l = tid; l < C.n; l += nt) {
+        const LineFace &f = F[I[C.off + l].f];
+        act[l] = face_is_point(a, f.i, f.j);
+        val[l] = (double)a.w_out[(int64_t)f.j * P + f.i];
+    }
+    __syncthreads();
+    int stuck = 0;
+    for (int L = 0; L < kFaceLevels; ++L) {
+        const int lo = C.lv[L], hi = C.lv[L + 1];
+        if (lo == hi) continue;   // the same for every thread of the CTA
+        for (int l = lo + tid; l < hi; l += nt) {
+            if (!act[l]) continue;
+            const FaceItem it = I[C.off + l];
+            const LineFace &f = F[it.f];
+            double v = 0.0, a_self = 0.0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const double ak = f.a[k];
+                if (ak == 0.0) continue;
+                const int m = it.kl[k];
+                if (m == l) a_self += ak;
+                else v += ak * (m >= 0 ? val[m] : (double)a.w_out[(int64_t)f.cj[k] * P + f.ci[k]]);
+            }
+            // x = v + a_self x, by iteration from the site's update (monotone
+            // in x, so it settles)
+            double x = val[l];
+            int it_n = 0;
+            for (; it_n < 64; ++it_n) {
+                const double y = v + a_self * x;
+                if (y == x) break;
+                x = y;
+            }
+            stuck |= it_n == 64;
+            val[l] = x;
+        }
+        __syncthreads();
+    }
+    const T inv_dt = (T)1 / a.dt;
+    bool bad = false, drop = false;
+    for (int l = tid; l < C.n; l += nt) {
+        const int c = I[C.off + l].f;
+        if (!act[l] || c < C.own_lo || c >= C.own_hi) continue;
+        const LineFace &f = F[c];
+        const int64_t o = (int64_t)f.j * P + f.i;
+        const T wB = (T)val[l];
+        a.w_out[o] = wB;
+        WdIO<D>::put(a.wd + o, (wB - a.w_in[o]) * inv_dt, a.wd_scale);
+        site_pads(a, f.i, f.j, wB);
+        bad |= !isfinite(wB);
+        drop |= (f.flags & FACE_DROPPED) != 0;
+    }
+    if (bad) atomicOr(a.err, (uint32_t)ERR_NONFINITE);
+    if (drop || stuck) face_unsupported(a);
+}
+
+// The macroscopic rule on the faces of a crack in any direction (Sec. 3.1),
+// after the march, in one CTA (the form for tables the chunked solve does
+// not take: a coupling deeper than kFaceLevels or a chunk too wide).  It lists the tabulated points whose site has
 // a severed link (the list's order is immaterial: each sweep reads only the
 // previous sweep's values) and, per point, sums once the terms of the
 // corners that are not points (their w is this step's update, fixed during
@@ -769,18 +871,11 @@ __global__ void __launch_bounds__(1024) line_faces_kernel(const StepArgs<T, D> a
     __shared__ int n_act;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int64_t P = a.pitch;
-    const int words = a.words, ny = a.ny;
     if (tid == 0) n_act = 0;
     __syncthreads();
     for (int c = tid; c < nf; c += nt) {
-        const int i = F[c].i, j = F[c].j;
-        const uint32_t *ch = a.cut_h + (int64_t)j * words, *cv = a.cut_v + (int64_t)j * words;
-        bool cut = (ch[i >> 5] >> (i & 31)) & 1u;
-        if (i >= 1) cut |= (ch[(i - 1) >> 5] >> ((i - 1) & 31)) & 1u;
-        if (j + 1 < ny) cut |= (cv[i >> 5] >> (i & 31)) & 1u;
-        if (j >= 1) cut |= ((cv - words)[i >> 5] >> (i & 31)) & 1u;
         int q = -1;
-        if (cut) {
+        if (face_is_point(a, F[c].i, F[c].j)) {
             q = atomicAdd(&n_act, 1);
             z.list[q] = c;
         }
@@ -811,8 +906,9 @@ __global__ void __launch_bounds__(1024) line_faces_kernel(const StepArgs<T, D> a
         cur[q] = (double)a.w_out[(int64_t)f.j * P + f.i];
     }
     __syncthreads();
-    for (int sweep = 0; sweep < 256; ++sweep) {
-        int changed = 0;
+    int changed = 1;
+    for (int sweep = 0; sweep < 256 && changed; ++sweep) {
+        changed = 0;
         for (int q = tid; q < na; q += nt) {
             const LineFace &f = F[z.list[q]];
             const uint32_t mask = z.mask[q];
@@ -842,10 +938,9 @@ __global__ void __launch_bounds__(1024) line_faces_kernel(const StepArgs<T, D> a
         double *t = cur;
         cur = nxt;
         nxt = t;
-        if (!changed) break;
     }
     const T inv_dt = (T)1 / a.dt;
-    bool bad = false;
+    bool bad = false, drop = false;
     for (int q = tid; q < na; q += nt) {
         const int c = z.list[q];
         const int i = F[c].i, j = F[c].j;
@@ -855,8 +950,11 @@ __global__ void __launch_bounds__(1024) line_faces_kernel(const StepArgs<T, D> a
         WdIO<D>::put(a.wd + o, (wB - a.w_in[o]) * inv_dt, a.wd_scale);
         site_pads(a, i, j, wB);
         bad |= !isfinite(wB);
+        drop |= (F[c].flags & FACE_DROPPED) != 0;
     }
     if (bad) atomicOr(a.err, (uint32_t)ERR_NONFINITE);
+    // a dropped stencil in use, or 256 sweeps that still changed a value
+    if ((drop || (changed && tid == 0))) face_unsupported(a);
 }
 
 // The pending crack step before the host reads the state (one warp).
@@ -894,6 +992,15 @@ cudaError_t launch_line_faces(const StepArgs<T, D> &a, const LineFace *faces, in
 }
 
 template <typename T, typename D>
+cudaError_t launch_line_faces_chunked(const StepArgs<T, D> &a, const LineFace *faces, const FaceChunk *chunks,
+                                      int n_chunks, const FaceItem *items, cudaStream_t s)
+{
+    if (n_chunks <= 0) return cudaSuccess;
+    line_faces_chunk_kernel<T, D><<<(unsigned)n_chunks, 256, 0, s>>>(a, faces, chunks, items);
+    return cudaGetLastError();
+}
+
+template <typename T, typename D>
 cudaError_t launch_line_step(const StepArgs<T, D> &a, cudaStream_t s)
 {
     const unsigned bands = (unsigned)((a.ny + a.p.band - 1) / a.p.band);
@@ -926,6 +1033,10 @@ template cudaError_t launch_line_faces<float, __nv_bfloat16>(const StepArgs<floa
                                                             int, double *, cudaStream_t);
 template cudaError_t launch_line_faces<float, __half>(const StepArgs<float, __half> &, const LineFace *, int, double *,
                                                      cudaStream_t);
+template cudaError_t launch_line_faces_chunked<double, double>(const StepArgs<double, double> &, const LineFace *, const FaceChunk *, int, const FaceItem *, cudaStream_t);
+template cudaError_t launch_line_faces_chunked<float, float>(const StepArgs<float, float> &, const LineFace *, const FaceChunk *, int, const FaceItem *, cudaStream_t);
+template cudaError_t launch_line_faces_chunked<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> &, const LineFace *, const FaceChunk *, int, const FaceItem *, cudaStream_t);
+template cudaError_t launch_line_faces_chunked<float, __half>(const StepArgs<float, __half> &, const LineFace *, const FaceChunk *, int, const FaceItem *, cudaStream_t);
 template cudaError_t launch_line_step<double, double>(const StepArgs<double, double> &, cudaStream_t);
 template cudaError_t launch_line_step<float, float>(const StepArgs<float, float> &, cudaStream_t);
 template cudaError_t launch_line_step<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> &, cudaStream_t);

@@ -18,10 +18,39 @@ namespace lbm {
 // Unused corners have a_k = 0; cand[k] is the corner's index in the table
 // (-1: not a tabulated site).  The rule applies to the site once one of its
 // links is severed.
+// flags bit FACE_DROPPED: a stencil of the point has a corner outside the
+// body and was left out (the rule is not supported there; the solve reports
+// FLAG_UNSUPPORTED once such a point is governed by the rule).
 struct LineFace {
     int32_t i, j;
     int32_t ci[8], cj[8], cand[8];
+    int32_t flags, pad;
     double a[8];
+};
+enum { FACE_DROPPED = 1 };
+
+// The chunked face solve.  The table is ordered along the line (it is built
+// column by column, or row by row for steep lines).  Chunk c owns the
+// entries [own_lo, own_hi); its items are the owned entries and every entry
+// they depend on through the coupled corners, transitively (all within a few
+// spacings along the line), sorted by level: an entry's level is 0 if no
+// corner but its own site is a table entry, else one more than the highest
+// level among those corners.  Every coupled corner lies strictly farther
+// from the line than its point, so the levels are finite and a pass level
+// by level, each level reading only lower ones, solves the system exactly.
+// kl[k]: the item index (within the chunk) of corner k, or -1 when corner k
+// is not a table entry (or has weight 0).
+constexpr int kFaceChunk = 256;      // entries a CTA owns
+constexpr int kFaceLevels = 64;      // deepest coupling the chunked solve takes
+constexpr int kFaceItemsMax = 1024;  // items a CTA holds in shared memory
+struct FaceItem {
+    int32_t f;
+    int16_t kl[8];
+};
+struct FaceChunk {
+    int32_t off, n, own_lo, own_hi;
+    int32_t lv[kFaceLevels + 1];     // items of level L: [lv[L], lv[L + 1])
+    int32_t pad[3];
 };
 
 // The device scratch of the face solve, per tabulated point: two sweeps'
@@ -39,5 +68,8 @@ constexpr size_t kLineFaceScratch = 3 * sizeof(double) + 3 * sizeof(int32_t) + 8
 
 template <typename T, typename D>
 cudaError_t launch_line_faces(const StepArgs<T, D> &a, const LineFace *faces, int nf, double *scratch, cudaStream_t s);
+template <typename T, typename D>
+cudaError_t launch_line_faces_chunked(const StepArgs<T, D> &a, const LineFace *faces, const FaceChunk *chunks,
+                                      int n_chunks, const FaceItem *items, cudaStream_t s);
 
 }  // namespace lbm

@@ -137,6 +137,12 @@ def lbm_set_launch(h: int, band_rows: int):
     _check(load_library().lbm_set_launch(C.c_void_p(h), int(band_rows)))
 
 
+def lbm_set_face_solve(h: int, mode: int) -> bool:
+    ch = C.c_int32()
+    _check(load_library().lbm_set_face_solve(C.c_void_p(h), int(mode), C.byref(ch)))
+    return bool(ch.value)
+
+
 def lbm_get_launch(h: int) -> dict:
     r, c, t, s = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
     _check(load_library().lbm_get_launch(C.c_void_p(h), C.byref(r), C.byref(c), C.byref(t), C.byref(s)))
@@ -352,6 +358,12 @@ class Lattice:
 
     def set_launch(self, band_rows: int):
         lbm_set_launch(self.h, band_rows)
+
+    def set_face_solve(self, mode: int) -> bool:
+        """0: the chunked solve of the line crack's macroscopic faces where
+        the coupling allows it, 1: the one-CTA solve; returns whether the
+        chunked one runs."""
+        return lbm_set_face_solve(self.h, mode)
 
     def launch(self):
         return lbm_get_launch(self.h)

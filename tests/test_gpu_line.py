@@ -37,9 +37,12 @@ def _problem(nx, ny, edges=("free", "free", "dirichlet", "dirichlet"), u0=3e-3, 
     return p
 
 
-def _run(oracle_mod, gpu, p, storage, chunks):
+def _run(oracle_mod, gpu, p, storage, chunks, solve=None):
     o = oracle_mod.Oracle(p)
     g = gpu.Lattice(p, storage)
+    if solve is not None:
+        # the macroscopic faces' solve: 0 chunked (where the coupling allows), 1 one CTA
+        g.chunked = g.set_face_solve(solve)
     for n in chunks:
         o.step(n)
         g.step(n)
@@ -393,16 +396,21 @@ def _macro(nx, ny, u0=3e-3, t_ramp=40.0):
     return p
 
 
+@pytest.mark.parametrize("solve", [0, 1])
 @pytest.mark.parametrize("storage", ["f64", "f32"])
-@pytest.mark.parametrize("deg,two", [(23.0, False), (137.0, False), (61.0, True)])
-def test_macroscopic_faces_prescribed(oracle_mod, gpu, storage, deg, two):
+@pytest.mark.parametrize("deg,two", [(23.0, False), (137.0, False), (61.0, True), (2.0, True), (0.5, True)])
+def test_macroscopic_faces_prescribed(oracle_mod, gpu, storage, deg, two, solve):
+    """Both solves of the faces' system: the chunked one (a CTA per stretch of
+    the line, level by level; at 0.5 degrees the coupling is deeper than it
+    takes, so the one-CTA solve runs) and the one-CTA Jacobi solve."""
     nx, ny = 300, 200
     start, tip = _centre(nx, ny, deg, 20.0)
     p = W.with_line_crack(_macro(nx, ny), mode="prescribed", start=start, tip=tip, v_rel=0.6, r0=2.0, two_tips=two)
     # 70 steps: the solve along these lines meets its bitwise fixpoint
     # throughout (the oracle flags a solve that ends without one)
-    o, g = _run(oracle_mod, gpu, p, storage, [7, 40, 23])
-    assert o.flags() == 0
+    o, g = _run(oracle_mod, gpu, p, storage, [7, 40, 23], solve=solve)
+    assert g.chunked == (solve == 0 and deg != 0.5)
+    assert o.flags() == 0 and g.crack_state()["flags"] == 0
     _close(o, g, TOL[storage])
     _masks(o, g)
     _tips(o, g, 70)
@@ -414,8 +422,8 @@ def test_macroscopic_faces_kcrit_fp64(oracle_mod, gpu):
     p = _macro(nx, ny, u0=4e-3, t_ramp=10.0)
     K_C = 0.2 * W.strip_reference_K(0.25, 4e-3, float(ny))
     p = W.with_line_crack(p, mode="kcrit", start=start, tip=tip, K_C=K_C, v_max=0.85, r0=2.0, two_tips=True)
-    o, g = _run(oracle_mod, gpu, p, "f64", [60, 80])
-    assert o.flags() == 0
+    o, g = _run(oracle_mod, gpu, p, "f64", [60, 80], solve=0)
+    assert o.flags() == 0 and g.chunked
     ho, hg = _tips(o, g, 140)
     assert (ho["v"] > 0).sum() > 10 and (o.history_left()["v"] > 0).sum() > 10
     np.testing.assert_allclose(hg["K"], ho["K"], rtol=0, atol=1e-9 * np.abs(ho["K"]).max())
@@ -429,9 +437,45 @@ def test_macroscopic_faces_beyond_the_kernels_shared_memory(oracle_mod, gpu):
     nx, ny = 1800, 300
     start, tip = _centre(nx, ny, 8.0, 860.0)
     p = W.with_line_crack(_macro(nx, ny), mode="prescribed", start=start, tip=tip, v_rel=0.5, r0=2.0, two_tips=True)
-    o, g = _run(oracle_mod, gpu, p, "f64", [5, 7])
+    o, g = _run(oracle_mod, gpu, p, "f64", [5, 7], solve=1)
     assert len(o.bpoints()) > 3008
     assert o.flags() == 0
     _close(o, g, TOL["f64"])
     _masks(o, g)
     _tips(o, g, 12)
+
+
+@pytest.mark.parametrize("solve", [0, 1])
+def test_unsupported_face_points_are_flagged_like_the_oracle(oracle_mod, gpu, solve):
+    """A crack with macroscopic faces that grows to within two spacings of an
+    edge: a new boundary point whose x_I or x_II cell reaches outside the
+    body is not supported by the rule; the oracle flags it when it adds the
+    point (at step n_f), the GPU when its face solve first uses the point
+    (the next step).  Both report FLAG_UNSUPPORTED = 2 from then on, neither
+    before; the fields agree until then."""
+    import math
+    nx, ny = 160, 60
+    start, ang = (60.3, 30.2), math.radians(23.0)
+    tip = (start[0] + 20 * math.cos(ang), start[1] + 20 * math.sin(ang))
+    p = W.with_line_crack(_macro(nx, ny), mode="prescribed", start=start, tip=tip, v_rel=0.7, r0=2.0, two_tips=False)
+    o = oracle_mod.Oracle(p)
+    n_f = 0
+    while not o.flags() & 2:
+        o.step(1)
+        n_f += 1
+        assert n_f < 400
+    assert 100 < n_f
+    o.close()
+    o = oracle_mod.Oracle(p)
+    g = gpu.Lattice(p, "f64")
+    g.set_face_solve(solve)
+    o.step(n_f - 2)
+    g.step(n_f - 2)
+    assert o.flags() == 0 and g.crack_state()["flags"] == 0
+    _close(o, g, TOL["f64"])
+    _masks(o, g)
+    o.step(4)
+    g.step(4)
+    assert o.flags() & 2 and g.crack_state()["flags"] & 2
+    o.close()
+    g.close()
