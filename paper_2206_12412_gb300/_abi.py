@@ -143,4 +143,9 @@ PROTOTYPES = {
                                   C.POINTER(C.c_int32)]),
     "lbm_decomp_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "lbm_decomp_destroy": (None, [C.c_void_p]),
+    "lbm_slab_create": (C.c_int, [C.POINTER(Grid), C.POINTER(Lattice_), C.POINTER(Material), C.POINTER(Crack),
+                                  C.POINTER(Loading), C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
+                                  C.POINTER(Allocator), C.POINTER(C.c_void_p)]),
+    "lbm_slab_export": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32]),
+    "lbm_slab_import": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32]),
 }

@@ -500,10 +500,12 @@ std::vector<Unit> partition_rows(int ny, int rows, int jc, int hh)
         for (int j = a; j < b; j = std::min(j + rows, b)) push(j, std::min(j + rows, b));
     };
     if (hh > 0) {
-        fill(0, jc - hh);
-        push(jc - hh, jc);
-        push(jc, jc + hh);
-        fill(jc + hh, ny);
+        // a row slab whose boundary is the crack line holds one sub-band
+        const bool below = jc >= hh, above = jc + hh <= ny;
+        fill(0, below ? jc - hh : jc);
+        if (below) push(jc - hh, jc);
+        if (above) push(jc, jc + hh);
+        fill(above ? jc + hh : jc, ny);
     } else {
         fill(0, ny);
     }
@@ -536,7 +538,11 @@ lbm_status plan_bands(lbm_handle *h, int rows)
     h->crack_band = -1;
     for (int b = 0; b < h->n_bands; ++b) {
         h->band_rows = std::max(h->band_rows, best[b].j1 - best[b].j0);
-        if (crack && best[b].j0 == h->jc - hh && best[b].j1 == h->jc) h->crack_band = b;
+        // the first crack sub-band: below the crack line, else (a slab whose
+        // bottom boundary is the crack line) above it
+        const bool sub = h->jc >= hh ? (best[b].j0 == h->jc - hh && best[b].j1 == h->jc)
+                                     : (best[b].j0 == h->jc && best[b].j1 == h->jc + hh);
+        if (crack && sub && h->crack_band < 0) h->crack_band = b;
     }
     if (crack && h->crack_band < 0) return fail(LBM_ERR_ARG, "the crack rows form no band of their own");
     LBM_CUDA(cudaMemcpyAsync(h->units, best.data(), best.size() * sizeof(Unit), cudaMemcpyHostToDevice, h->stream));
@@ -679,6 +685,26 @@ lbm_status lbm_create_line(const lbm_grid *grid, const lbm_lattice *lattice, con
 namespace lbm {
 namespace host {
 
+// The scale of FP16 wdot storage (stored = wdot * scale): a power of two
+// that puts the largest rate the Dirichlet loads impose near 2^10, leaving a
+// factor 64 below FP16's largest value for waves.
+double fp16_wd_scale(const lbm_grid *grid, const lbm_loading *loads, int32_t n_loads)
+{
+    double rate = 0.0;
+    for (int r = 0; r < n_loads; ++r) {
+        const lbm_loading &L = loads[r];
+        if (L.edge < 0 || L.edge > 3 || grid->edge[L.edge] != LBM_EDGE_DIRICHLET) continue;
+        const double T = L.t_ramp > grid->dt ? L.t_ramp : grid->dt;
+        if (L.kind == LBM_LOAD_LINEAR) rate = std::max(rate, std::fabs(L.amp) / T);
+        else if (L.kind == LBM_LOAD_SIN2 || L.kind == LBM_LOAD_HALFSINE) rate = std::max(rate, 3.2 * std::fabs(L.amp) / T);
+        else if (L.kind == LBM_LOAD_SERIES)
+            for (int64_t k = 1; L.series && k < L.n_series; ++k)
+                rate = std::max(rate, std::fabs(L.series[k] - L.series[k - 1]) / grid->dt);
+    }
+    double scale = rate > 0.0 ? std::ldexp(1.0, 10 - (int)std::ceil(std::log2(rate))) : 1024.0;
+    return std::min(std::max(scale, std::ldexp(1.0, -40)), std::ldexp(1.0, 60));
+}
+
 lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const lbm_material *material,
                        const lbm_crack *crack, const lbm_loading *loads, int32_t n_loads, void *stream,
                        const lbm_allocator *allocator, bool slab, lbm_handle **out, const LineSpec *line)
@@ -745,8 +771,17 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
             return fail(LBM_ERR_ARG, "the crack line y must be a multiple of dh (between two rows)");
         jc = (int32_t)std::nearbyint(yj);
         const int margin = macro_edges ? 4 : (macro_faces ? 3 : 1);
-        if (jc < margin || jc > grid->ny - margin)
+        // a row slab may have the crack line on a halo boundary (the
+        // neighbouring slab holds the other side's rows)
+        const bool on_lo = slab && jc == 0 && grid->edge[LBM_BOTTOM] == EDGE_HALO;
+        const bool on_hi = slab && jc == grid->ny && grid->edge[LBM_TOP] == EDGE_HALO;
+        const int hh_rows = macro_faces ? 3 : 1;
+        if (on_lo || on_hi) {
+            if (grid->ny < hh_rows + (on_lo && on_hi ? hh_rows : 0))
+                return fail(LBM_ERR_ARG, "a slab whose boundary is the crack line needs the crack rows of its side");
+        } else if (jc < margin || jc > grid->ny - margin) {
             return fail(LBM_ERR_ARG, "the crack line is too close to the bottom or top edge");
+        }
         if (!(cr.x_start >= 0.0) || !(cr.x_tip >= cr.x_start)) return fail(LBM_ERR_ARG, "need 0 <= x_start <= x_tip");
         start_q = llrint(cr.x_start / grid->dh * 4294967296.0);
         tip_q = llrint(cr.x_tip / grid->dh * 4294967296.0);
@@ -843,13 +878,16 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
     const size_t plane_d = (size_t)(grid->ny + 2) * (size_t)h->pitch * h->esize_d;
     const size_t staging = h->esize_d == 2 ? (size_t)grid->nx * grid->ny * 4 : 0;
     const size_t mask = (size_t)grid->ny * (size_t)h->words * 4;
+    // the V mask has one more row below row 0: the links across the bottom
+    // boundary of a row slab whose boundary is the crack line
+    const size_t mask_v = mask + (size_t)h->words * 4;
     size_t off = 0;
     const size_t o_w0 = off; off = align256(off + plane);
     const size_t o_w1 = off; off = align256(off + plane);
     const size_t o_wd = off; off = align256(off + plane_d);
     const size_t o_sg = off; off = align256(off + staging);
     const size_t o_ch = off; off = align256(off + mask);
-    const size_t o_cv = off; off = align256(off + mask);
+    const size_t o_cv = off; off = align256(off + mask_v);
     const size_t o_st = off; off = align256(off + 2 * sizeof(CrackState));
     const size_t o_er = off; off = align256(off + sizeof(uint32_t));
     const size_t o_un = off; off = align256(off + (size_t)grid->ny * sizeof(Unit));
@@ -883,7 +921,7 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
     h->plane_d_bytes = plane_d;
     h->staging = staging ? reinterpret_cast<float *>(base + o_sg) : nullptr;
     h->cut_h = reinterpret_cast<uint32_t *>(base + o_ch);
-    h->cut_v = reinterpret_cast<uint32_t *>(base + o_cv);
+    h->cut_v = reinterpret_cast<uint32_t *>(base + o_cv) + h->words;
     h->st = reinterpret_cast<CrackState *>(base + o_st);
     h->err = reinterpret_cast<uint32_t *>(base + o_er);
     h->units = reinterpret_cast<Unit *>(base + o_un);
@@ -926,6 +964,10 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
     cp.nx = grid->nx;
     cp.ny = grid->ny;
     cp.macro = macro_faces;
+    {
+        const int hh_rows = macro_faces ? 3 : 1;
+        cp.sides = (jc >= hh_rows ? 1 : 0) | (jc + hh_rows <= grid->ny ? 2 : 0);
+    }
     h->edge_macro = macro_edges;
     h->q = d2q9 ? 9 : 5;
     cp.words = h->words;
@@ -1008,27 +1050,7 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
     }
     cp.hist_cap = cr.mode != LBM_CRACK_NONE ? cr.hist_cap : 0;
 
-    h->wd_scale = 1.0;
-    if (lattice->storage == LBM_F32_WD_F16) {
-        // a power of two that puts the largest rate the loads impose near 2^10,
-        // leaving a factor 64 below FP16's largest value for waves
-        double rate = 0.0;
-        for (int q = 0; q < 4; ++q) {
-            const LoadDesc &L = h->load[q];
-            if (grid->edge[q] != LBM_EDGE_DIRICHLET) continue;
-            const double T = L.t > grid->dt ? L.t : grid->dt;
-            if (L.kind == LBM_LOAD_LINEAR) rate = std::max(rate, std::fabs(L.amp) / T);
-            else if (L.kind == LBM_LOAD_SIN2 || L.kind == LBM_LOAD_HALFSINE) rate = std::max(rate, 3.2 * std::fabs(L.amp) / T);
-            else if (L.kind == LBM_LOAD_SERIES) {
-                const lbm_loading *Ls = nullptr;
-                for (int r = 0; r < n_loads; ++r) if (loads[r].edge == q) Ls = &loads[r];
-                for (int64_t k = 1; Ls && k < Ls->n_series; ++k)
-                    rate = std::max(rate, std::fabs(Ls->series[k] - Ls->series[k - 1]) / grid->dt);
-            }
-        }
-        h->wd_scale = rate > 0.0 ? std::ldexp(1.0, 10 - (int)std::ceil(std::log2(rate))) : 1024.0;
-        h->wd_scale = std::min(std::max(h->wd_scale, std::ldexp(1.0, -40)), std::ldexp(1.0, 60));
-    }
+    h->wd_scale = lattice->storage == LBM_F32_WD_F16 ? fp16_wd_scale(grid, loads, n_loads) : 1.0;
 
     lbm_status rc = plan_bands(h, 0);
     if (rc != LBM_OK) return bail(rc);
@@ -1068,7 +1090,7 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
         hs.r.v_prev = cr.mode == LBM_CRACK_PRESCRIBED ? cr.v_rel : 0.0;
         hs.l.v_prev = hs.r.v_prev;
         for (int i = hs.i_first; i <= hs.i_last; ++i) row[(size_t)(i >> 5)] |= 1u << (i & 31);
-        e = cudaMemcpyAsync(h->cut_v + (size_t)(jc - 1) * h->words, row.data(), row.size() * 4, cudaMemcpyHostToDevice, s);
+        e = cudaMemcpyAsync(h->cut_v + (ptrdiff_t)(jc - 1) * h->words, row.data(), row.size() * 4, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return bail(cuda_fail(e, "writing the initial crack"));
     }
     h->init_st = hs;
@@ -1211,13 +1233,13 @@ lbm_status lbm_reset(lbm_handle *h)
     LBM_CUDA(cudaMemsetAsync(h->wbase[1], 0, h->plane_bytes, s));
     LBM_CUDA(cudaMemsetAsync(h->wdbase, 0, h->plane_d_bytes, s));
     LBM_CUDA(cudaMemsetAsync(h->cut_h, 0, mask, s));
-    LBM_CUDA(cudaMemsetAsync(h->cut_v, 0, mask, s));
+    LBM_CUDA(cudaMemsetAsync(h->cut_v - h->words, 0, mask + (size_t)h->words * 4, s));   // with the row below row 0
     if (h->line) {
         const size_t n = (size_t)h->grid.ny * h->words;
         LBM_CUDA(cudaMemcpyAsync(h->cut_h, h->init_cut->data(), n * 4, cudaMemcpyHostToDevice, s));
         LBM_CUDA(cudaMemcpyAsync(h->cut_v, h->init_cut->data() + n, n * 4, cudaMemcpyHostToDevice, s));
     } else if (h->cp.mode != CRACK_NONE) {
-        LBM_CUDA(cudaMemcpyAsync(h->cut_v + (size_t)(h->jc - 1) * h->words, h->init_cut->data(),
+        LBM_CUDA(cudaMemcpyAsync(h->cut_v + (ptrdiff_t)(h->jc - 1) * h->words, h->init_cut->data(),
                                  h->init_cut->size() * 4, cudaMemcpyHostToDevice, s));
     }
     LBM_CUDA(cudaMemcpyAsync(h->st, &h->init_st, sizeof(CrackState), cudaMemcpyHostToDevice, s));
@@ -1599,7 +1621,7 @@ void ckpt_header(const lbm_handle *h, CkptHeader &c)
 {
     std::memset(&c, 0, sizeof c);
     std::memcpy(c.magic, kCkptMagic, 8);
-    c.version = 1;
+    c.version = 2;
     c.crack_state_bytes = (int32_t)sizeof(CrackState);
     c.grid = h->grid;
     c.lat = h->lat;
@@ -1637,7 +1659,7 @@ std::vector<std::pair<void *, size_t>> ckpt_buffers(lbm_handle *h, const CkptHea
     return {{h->wbase[h->parity], (size_t)c.plane_bytes},
             {h->wdbase, (size_t)c.plane_d_bytes},
             {h->cut_h, (size_t)c.mask_bytes},
-            {h->cut_v, (size_t)c.mask_bytes},
+            {h->cut_v - h->words, (size_t)c.mask_bytes + (size_t)c.words * 4},   // with the row below row 0
             {h->st + h->parity, sizeof(CrackState)},
             {H.K, (size_t)c.hist_cap * 8},
             {H.v, (size_t)c.hist_cap * 8},
@@ -1687,7 +1709,7 @@ lbm_status lbm_load(lbm_handle *h, const char *path)
     FILE *f = std::fopen(path, "rb");
     if (!f) return fail(LBM_ERR_IO, std::string("cannot open ") + path);
     CkptHeader c, mine;
-    if (std::fread(&c, sizeof c, 1, f) != 1 || std::memcmp(c.magic, kCkptMagic, 8) != 0 || c.version != 1) {
+    if (std::fread(&c, sizeof c, 1, f) != 1 || std::memcmp(c.magic, kCkptMagic, 8) != 0 || c.version != 2) {
         std::fclose(f);
         return fail(LBM_ERR_IO, std::string(path) + " is not a lattice checkpoint");
     }

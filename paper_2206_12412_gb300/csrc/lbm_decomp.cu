@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -31,14 +32,22 @@ struct lbm_decomp {
 
 namespace {
 
+// An inner boundary may not cut the crack's rows [jc - hh, jc + hh) except
+// on the crack line itself, where the slabs on both sides each hold their
+// side's hh rows.
+bool boundary_ok(int32_t b, int32_t below, int32_t above, int32_t jc, int32_t hh)
+{
+    if (jc < 0 || b <= jc - hh || b >= jc + hh) return true;
+    return b == jc && below >= hh && above >= hh;
+}
+
 bool valid_split(int32_t ny, int32_t jc, int32_t hh, int32_t n, const int32_t *rs)
 {
     if (rs[0] != 0 || rs[n] != ny) return false;
     for (int r = 0; r < n; ++r)
         if (rs[r + 1] - rs[r] < 2) return false;
-    if (jc >= 0)
-        for (int r = 1; r < n; ++r)
-            if (rs[r] > jc - hh && rs[r] < jc + hh) return false;
+    for (int r = 1; r < n; ++r)
+        if (!boundary_ok(rs[r], rs[r] - rs[r - 1], rs[r + 1] - rs[r], jc, hh)) return false;
     return true;
 }
 
@@ -80,12 +89,18 @@ lbm_status lbm_decomp_plan(int32_t ny, int32_t jc, int32_t hh, int32_t n_ranks, 
     std::vector<int32_t> rs((size_t)n_ranks + 1);
     for (int r = 0; r <= n_ranks; ++r) {
         int32_t b = (int32_t)(((int64_t)r * ny + n_ranks / 2) / n_ranks);
-        if (jc >= 0 && r > 0 && r < n_ranks && b > jc - hh && b < jc + hh)
-            b = (b - (jc - hh) <= (jc + hh) - b) ? jc - hh : jc + hh;
+        if (jc >= 0 && r > 0 && r < n_ranks && b > jc - hh && b < jc + hh && b != jc) {
+            // the nearest of the crack rows' ends and the crack line itself
+            const int32_t c[3] = {jc - hh, jc, jc + hh};
+            int32_t best = c[0];
+            for (int q = 1; q < 3; ++q)
+                if (std::abs(c[q] - b) < std::abs(best - b)) best = c[q];
+            b = best;
+        }
         rs[(size_t)r] = b;
     }
     if (!valid_split(ny, jc, hh, n_ranks, rs.data()))
-        return fail(LBM_ERR_ARG, "no split into slabs of >= 2 rows keeps the crack rows in one slab");
+        return fail(LBM_ERR_ARG, "no split into slabs of >= 2 rows keeps each side's crack rows in one slab");
     std::copy(rs.begin(), rs.end(), row_start);
     clear_error();
     return LBM_OK;
@@ -120,7 +135,7 @@ lbm_status lbm_decomp_create(const lbm_grid *grid, const lbm_lattice *lattice, c
     if (row_start) {
         std::copy(row_start, row_start + n_ranks + 1, rs.begin());
         if (!valid_split(ny, jc, hh, n_ranks, rs.data()))
-            return fail(LBM_ERR_ARG, "row_start must run from 0 to ny in slabs of >= 2 rows, the crack rows in one slab");
+            return fail(LBM_ERR_ARG, "row_start must run from 0 to ny in slabs of >= 2 rows; a boundary may cut the crack rows only on the crack line");
     } else {
         lbm_status rc = lbm_decomp_plan(ny, jc, hh, n_ranks, rs.data());
         if (rc != LBM_OK) return rc;
@@ -151,11 +166,12 @@ lbm_status lbm_decomp_create(const lbm_grid *grid, const lbm_lattice *lattice, c
         }
         lbm_crack c;
         std::memset(&c, 0, sizeof c);
-        const bool mine = has_crack && jc > j0 && jc < j1;
+        // the crack line inside the slab, or on one of its inner boundaries
+        const bool mine = has_crack && ((jc > j0 && jc < j1) || (jc == j0 && r > 0) || (jc == j1 && r < n_ranks - 1));
         if (mine) {
             c = *crack;
             c.y = crack->y - (double)j0 * grid->dh;
-            d->crack_rank = r;
+            if (d->crack_rank < 0) d->crack_rank = r;
         }
         std::vector<lbm_loading> L;
         for (int q = 0; q < n_loads; ++q) {
@@ -302,6 +318,100 @@ void lbm_decomp_destroy(lbm_decomp *d)
     if (!d) return;
     cudaStreamSynchronize(d->stream);
     free_decomp(d);
+}
+
+// ------------------------------------------ one slab per process (or device)
+
+lbm_status lbm_slab_create(const lbm_grid *grid, const lbm_lattice *lattice, const lbm_material *material,
+                           const lbm_crack *crack, const lbm_loading *loads, int32_t n_loads, int32_t row0,
+                           int32_t rows, void *stream, const lbm_allocator *allocator, lbm_handle **out)
+{
+    if (!out) return fail(LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!grid || !lattice || !material) return fail(LBM_ERR_ARG, "grid, lattice and material are required");
+    if (lattice->bc_mode == LBM_BC_MACROSCOPIC_EDGES)
+        return fail(LBM_ERR_ARG, "the macroscopic rule on the outer edges is not built for row slabs");
+    if (lattice->velocity_set != LBM_D2Q5) return fail(LBM_ERR_ARG, "row slabs are built for D2Q5 only");
+    if (n_loads < 0 || (n_loads > 0 && !loads)) return fail(LBM_ERR_ARG, "bad loads array");
+    for (int e = 0; e < 4; ++e)
+        if (grid->edge[e] < LBM_EDGE_FREE || grid->edge[e] > LBM_EDGE_PERIODIC) return fail(LBM_ERR_ARG, "unknown edge kind");
+    const int32_t ny = grid->ny, r1 = row0 + rows;
+    if (row0 < 0 || rows < 2 || r1 > ny) return fail(LBM_ERR_ARG, "the slab must be >= 2 rows inside [0, ny)");
+    const bool has_crack = crack && crack->mode != LBM_CRACK_NONE;
+    int32_t jc = -1, hh = 0;
+    if (has_crack) {
+        const double yj = crack->y / grid->dh;
+        if (!std::isfinite(yj) || std::fabs(yj - std::nearbyint(yj)) > 1e-9)
+            return fail(LBM_ERR_ARG, "the crack line y must be a multiple of dh (between two rows)");
+        jc = (int32_t)std::nearbyint(yj);
+        hh = lattice->bc_mode != LBM_BC_BOUNCEBACK ? 3 : 1;
+    }
+    // this slab's side of each inner boundary (the neighbour checks its own)
+    if ((row0 > 0 && !boundary_ok(row0, hh, rows, jc, hh)) || (r1 < ny && !boundary_ok(r1, rows, hh, jc, hh)))
+        return fail(LBM_ERR_ARG, "a slab boundary may cut the crack rows only on the crack line");
+    const bool periodic_y = grid->edge[LBM_BOTTOM] == LBM_EDGE_PERIODIC;
+    lbm_grid g = *grid;
+    g.ny = rows;
+    if (row0 > 0 || periodic_y) g.edge[LBM_BOTTOM] = EDGE_HALO;
+    if (r1 < ny || periodic_y) g.edge[LBM_TOP] = EDGE_HALO;
+    lbm_crack c;
+    std::memset(&c, 0, sizeof c);
+    const bool mine = has_crack && ((jc > row0 && jc < r1) || (jc == row0 && row0 > 0) || (jc == r1 && r1 < ny));
+    if (mine) {
+        c = *crack;
+        c.y = crack->y - (double)row0 * grid->dh;
+    }
+    std::vector<lbm_loading> L;
+    for (int q = 0; q < n_loads; ++q) {
+        const int e = loads[q].edge;
+        if ((e == LBM_BOTTOM || e == LBM_TOP) && g.edge[e] == EDGE_HALO) continue;
+        L.push_back(loads[q]);
+    }
+    lbm_handle *h = nullptr;
+    lbm_status rc = create_impl(&g, lattice, material, mine ? &c : nullptr, L.empty() ? nullptr : L.data(),
+                                (int32_t)L.size(), stream, allocator, true, &h);
+    if (rc != LBM_OK) return rc;
+    if (lattice->storage == LBM_F32_WD_F16) {
+        // every slab takes the scale of the undivided lattice
+        rc = lbm_set_wd_scale(h, fp16_wd_scale(grid, loads, n_loads));
+        if (rc != LBM_OK) {
+            lbm_destroy(h);
+            return rc;
+        }
+    }
+    *out = h;
+    clear_error();
+    return LBM_OK;
+}
+
+lbm_status lbm_slab_export(lbm_handle *h, int32_t side, void *dst, int32_t dst_on_device)
+{
+    if (!h || !dst) return fail(LBM_ERR_ARG, "handle or dst is NULL");
+    if (side != 0 && side != 1) return fail(LBM_ERR_ARG, "side must be 0 (bottom row) or 1 (top row)");
+    if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");
+    const int j = side == 0 ? 0 : h->grid.ny - 1;
+    const char *src = static_cast<const char *>(h->w[h->parity]) + (int64_t)j * h->pitch * (int64_t)h->esize;
+    const size_t bytes = (size_t)h->grid.nx * h->esize;
+    LBM_CUDA(cudaMemcpyAsync(dst, src, bytes, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                             h->stream));
+    if (!dst_on_device) LBM_CUDA(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_slab_import(lbm_handle *h, int32_t side, const void *src, int32_t src_on_device)
+{
+    if (!h || !src) return fail(LBM_ERR_ARG, "handle or src is NULL");
+    if (side != 0 && side != 1) return fail(LBM_ERR_ARG, "side must be 0 (below row 0) or 1 (above the top row)");
+    if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");
+    if (h->grid.edge[side == 0 ? LBM_BOTTOM : LBM_TOP] != EDGE_HALO)
+        return fail(LBM_ERR_ARG, "that side of the slab is an outer edge, not a halo");
+    const int j = side == 0 ? -1 : h->grid.ny;
+    char *dst = static_cast<char *>(h->w[h->parity]) + (int64_t)j * h->pitch * (int64_t)h->esize;
+    const size_t bytes = (size_t)h->grid.nx * h->esize;
+    LBM_CUDA(cudaMemcpyAsync(dst, src, bytes, src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                             h->stream));
+    if (!src_on_device) LBM_CUDA(cudaStreamSynchronize(h->stream));   // a pageable source may be reused
+    return LBM_OK;
 }
 
 }  // extern "C"

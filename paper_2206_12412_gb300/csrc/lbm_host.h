@@ -104,6 +104,8 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
                        const lbm_crack *crack, const lbm_loading *loads, int32_t n_loads, void *stream,
                        const lbm_allocator *allocator, bool slab, lbm_handle **out, const LineSpec *line = nullptr);
 
+// The FP16 wdot scale lbm_create picks for these loads.
+double fp16_wd_scale(const lbm_grid *grid, const lbm_loading *loads, int32_t n_loads);
 // Apply the pending crack step (if any) on the handle's stream.
 lbm_status finalize(lbm_handle *h);
 // Synchronise, then report sticky device errors.

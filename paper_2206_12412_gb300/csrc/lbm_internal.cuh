@@ -92,6 +92,9 @@ struct CrackParams {
     int32_t line, row_lo, row_hi, band;   // band: rows of a CTA of line_step_kernel
     double dir_x, dir_y;
     int64_t clamp_yq, start_yq;
+    // the crack sub-bands this lattice holds: 1 below the crack line, 2 above
+    // (3: both; a row slab whose boundary is the crack line holds one)
+    int32_t sides, pad_s;
 };
 
 // Per-step records of the right end and (two-tip cracks) the left end; a

@@ -266,11 +266,13 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
     const CrackParams &p = a.p;
     T acc = (T)0;
 
-    if (a.crack_band >= 0 && (band == a.crack_band || band == a.crack_band + 1)) {
+    if (a.crack_band >= 0 && (band == a.crack_band || (band == a.crack_band + 1 && p.sides == 3))) {
         // The crack step of Alg. 1 that follows the previous LBM step, by the
         // two crack sub-band CTAs that own the next link of each end: both
-        // reach the same decision; the one below the crack records it, each
-        // end writing only its own fields of the next state.
+        // reach the same decision; the lower one records it, each end
+        // writing only its own fields of the next state.  (A row slab whose
+        // boundary is the crack line holds one of the two sub-bands and
+        // reads the other side's row from its halo: it records its own.)
         const int cols = TH * N;
         int i_next = a.s_in->i_last + 1;
         i_next = max(i_next, a.s_in->i_first);

@@ -771,30 +771,63 @@ __device__ __forceinline__ void face_unsupported(const StepArgs<T, D> &a)
 
 // The macroscopic rule on the faces of a crack in any direction (Sec. 3.1),
 // after the march: chunk blockIdx.x of the table (see FaceChunk), one CTA
-// each.  A CTA whose own entries hold no point leaves at once; the others
-// read which of their items are points and the items' current w (this
-// step's update), then solve the points level by level -- a point's value
-// w_B = sum_k a_k w(corner_k) reads only corners of lower levels (solved,
-// or fixed where they are no point) and its own site, whose weight (below
-// 0.2) is solved by a scalar iteration -- and write their own points' w_B,
+// each.  A CTA whose own entries hold no point leaves at once.  The others
+// gather, for every item, in one parallel pass: whether it is a point, its
+// current w (this step's update), the part of its sum over corners that are
+// no table entry (fixed during the solve), its own site's weight and its
+// coupled corners' weights and item indices -- all into shared memory.  Then
+// they solve the points level by level from shared memory alone: w_B = base
+// + sum over coupled corners of a_k w(corner) reads only lower levels (solved
+// points, or the update of items that are no point) and its own site, whose
+// weight (below 0.2) is solved by a scalar iteration from the update
+// (monotone, so it settles).  Last, each CTA writes its own points' w_B,
 // wdot_B = (w_B - w_B(t)) / dt and pad images.  Items that several chunks
-// hold are computed alike in each (same inputs, same order of terms).
+// hold are computed alike in each.  The arithmetic is in the storage's type
+// T (FP32 for FP32 storage: GB300's FP64 rate is a small fraction of its
+// FP32 rate).
 template <typename T, typename D>
 __global__ void __launch_bounds__(256) line_faces_chunk_kernel(const StepArgs<T, D> a, const LineFace *F,
                                                                const FaceChunk *Cs, const FaceItem *I)
 {
-    __shared__ double val[kFaceItemsMax];
-    __shared__ uint8_t act[kFaceItemsMax];
+    extern __shared__ __align__(16) unsigned char face_smem[];
     const int tid = threadIdx.x, nt = blockDim.x;
     const FaceChunk &C = Cs[blockIdx.x];
     const int64_t P = a.pitch;
     int any = 0;
     for (int c = C.own_lo + tid; c < C.own_hi; c += nt) any |= face_is_point(a, F[c].i, F[c].j);
     if (!__syncthreads_or(any)) return;
-    for (int l = tid; l < C.n; l += nt) {
-        const LineFace &f = F[I[C.off + l].f];
+    const int n = C.n;
+    T *val = reinterpret_cast<T *>(face_smem);        // [n]
+    T *base = val + n;                                 // [n]
+    T *aself = base + n;                               // [n]
+    T *ac = aself + n;                                 // [8 n] weights of the coupled corners
+    int16_t *kc = reinterpret_cast<int16_t *>(ac + 8 * n);   // [8 n] their items (-1: unused)
+    uint8_t *act = reinterpret_cast<uint8_t *>(kc + 8 * n);  // [n]
+    for (int l = tid; l < n; l += nt) {
+        const FaceItem it = I[C.off + l];
+        const LineFace &f = F[it.f];
         act[l] = face_is_point(a, f.i, f.j);
-        val[l] = (double)a.w_out[(int64_t)f.j * P + f.i];
+        val[l] = a.w_out[(int64_t)f.j * P + f.i];
+        T b = (T)0, s = (T)0;
+        int q = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const T ak = (T)f.a[k];
+            if (ak == (T)0) continue;
+            const int m = it.kl[k];
+            if (m == l) {
+                s += ak;
+            } else if (m >= 0) {
+                ac[8 * l + q] = ak;
+                kc[8 * l + q] = (int16_t)m;
+                ++q;
+            } else {
+                b += ak * a.w_out[(int64_t)f.cj[k] * P + f.ci[k]];
+            }
+        }
+        for (int k = q; k < 8; ++k) kc[8 * l + k] = -1;
+        base[l] = b;
+        aself[l] = s;
     }
     __syncthreads();
     int stuck = 0;
@@ -803,23 +836,18 @@ __global__ void __launch_bounds__(256) line_faces_chunk_kernel(const StepArgs<T,
         if (lo == hi) continue;   // the same for every thread of the CTA
         for (int l = lo + tid; l < hi; l += nt) {
             if (!act[l]) continue;
-            const FaceItem it = I[C.off + l];
-            const LineFace &f = F[it.f];
-            double v = 0.0, a_self = 0.0;
+            T v = base[l];
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
-                const double ak = f.a[k];
-                if (ak == 0.0) continue;
-                const int m = it.kl[k];
-                if (m == l) a_self += ak;
-                else v += ak * (m >= 0 ? val[m] : (double)a.w_out[(int64_t)f.cj[k] * P + f.ci[k]]);
+                const int m = kc[8 * l + k];
+                if (m < 0) break;
+                v += ac[8 * l + k] * val[m];
             }
-            // x = v + a_self x, by iteration from the site's update (monotone
-            // in x, so it settles)
-            double x = val[l];
+            const T s = aself[l];
+            T x = val[l];
             int it_n = 0;
             for (; it_n < 64; ++it_n) {
-                const double y = v + a_self * x;
+                const T y = v + s * x;
                 if (y == x) break;
                 x = y;
             }
@@ -830,12 +858,12 @@ __global__ void __launch_bounds__(256) line_faces_chunk_kernel(const StepArgs<T,
     }
     const T inv_dt = (T)1 / a.dt;
     bool bad = false, drop = false;
-    for (int l = tid; l < C.n; l += nt) {
+    for (int l = tid; l < n; l += nt) {
         const int c = I[C.off + l].f;
         if (!act[l] || c < C.own_lo || c >= C.own_hi) continue;
         const LineFace &f = F[c];
         const int64_t o = (int64_t)f.j * P + f.i;
-        const T wB = (T)val[l];
+        const T wB = val[l];
         a.w_out[o] = wB;
         WdIO<D>::put(a.wd + o, (wB - a.w_in[o]) * inv_dt, a.wd_scale);
         site_pads(a, f.i, f.j, wB);
@@ -843,7 +871,7 @@ __global__ void __launch_bounds__(256) line_faces_chunk_kernel(const StepArgs<T,
         drop |= (f.flags & FACE_DROPPED) != 0;
     }
     if (bad) atomicOr(a.err, (uint32_t)ERR_NONFINITE);
-    if (drop || stuck) face_unsupported(a);
+    if (__syncthreads_or(drop || stuck) && tid == 0) face_unsupported(a);
 }
 
 // The macroscopic rule on the faces of a crack in any direction (Sec. 3.1),
@@ -996,7 +1024,12 @@ cudaError_t launch_line_faces_chunked(const StepArgs<T, D> &a, const LineFace *f
                                       int n_chunks, const FaceItem *items, cudaStream_t s)
 {
     if (n_chunks <= 0) return cudaSuccess;
-    line_faces_chunk_kernel<T, D><<<(unsigned)n_chunks, 256, 0, s>>>(a, faces, chunks, items);
+    // shared memory for kFaceItemsMax items: 11 T and 8 int16 and one byte each
+    const size_t smem = (size_t)kFaceItemsMax * (11 * sizeof(T) + 8 * sizeof(int16_t) + 1);
+    cudaError_t e = cudaFuncSetAttribute(line_faces_chunk_kernel<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    line_faces_chunk_kernel<T, D><<<(unsigned)n_chunks, 256, smem, s>>>(a, faces, chunks, items);
     return cudaGetLastError();
 }
 

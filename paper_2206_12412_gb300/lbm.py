@@ -745,6 +745,64 @@ class SlabView:
     dtype_code = Lattice.dtype_code
 
 
+class Slab(Lattice):
+    """Rows row0 .. row0 + rows - 1 of the lattice `problem` describes, as a
+    lattice of its own (lbm_slab_create): one per process (or device).  Its
+    halo rows come from the neighbouring slabs: after set_fields and after
+    every step(1), call exchange(send_recv) -- or export_rows / import_rows
+    with a transport of your own -- before anything else on the handle."""
+
+    def __init__(self, problem: dict, row0: int, rows: int, storage: str = "f32", stream=None,
+                 torch_allocator: bool = True):
+        import torch
+        self.torch = torch
+        self.problem = problem
+        self.storage = storage
+        self.row0, self.rows = int(row0), int(rows)
+        self.nx, self.ny = int(problem["nx"]), self.rows
+        self.global_ny = int(problem["ny"])
+        self.np_dtype = np.float64 if storage == "f64" else np.float32
+        self.torch_dtype = torch.float64 if storage == "f64" else torch.float32
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream_obj = stream
+        self.stream = int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+        g, lat, mat, cr, loads, keep = make_structs(problem, storage)
+        self._alloc = TorchAllocator(self.stream) if torch_allocator else None
+        self.line = False
+        arr = (A.Loading * max(len(loads), 1))(*loads)
+        out = C.c_void_p()
+        _check(load_library().lbm_slab_create(C.byref(g), C.byref(lat), C.byref(mat), C.byref(cr) if cr.mode else None,
+                                              arr if loads else None, len(loads), self.row0, self.rows,
+                                              C.c_void_p(self.stream),
+                                              C.byref(self._alloc.struct) if self._alloc else None, C.byref(out)))
+        self.h = out.value
+        periodic = problem.get("edges", ("free", "free", "dirichlet", "dirichlet"))[2] == "periodic"
+        self.halo = (self.row0 > 0 or periodic, self.row0 + self.rows < self.global_ny or periodic)
+        del keep
+
+    def export_rows(self):
+        """The slab's bottom and top rows of w (host arrays of nx values)."""
+        out = []
+        for side in (0, 1):
+            a = np.empty(self.nx, self.np_dtype)
+            _check(load_library().lbm_slab_export(C.c_void_p(self.h), side, C.c_void_p(a.ctypes.data), 0))
+            out.append(a)
+        return out
+
+    def import_rows(self, below=None, above=None):
+        """The neighbours' boundary rows into the halo rows (None: leave)."""
+        for side, a in ((0, below), (1, above)):
+            if a is None:
+                continue
+            a = np.ascontiguousarray(a, dtype=self.np_dtype)
+            _check(load_library().lbm_slab_import(C.c_void_p(self.h), side, C.c_void_p(a.ctypes.data), 0))
+
+    def set_fields(self, w=None, wdot=None):
+        """This slab's rows of the lattice's fields (rows x nx arrays)."""
+        Lattice.set_fields(self, w, wdot)
+
+
 class Decomp:
     """A lattice split into row slabs on one GPU (include/lbm_decomp.h):
     one batched step launch and one halo-exchange launch per step, results

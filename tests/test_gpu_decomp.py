@@ -88,10 +88,65 @@ def test_fp16_slabs_share_the_lattice_scale(gpu):
 
 
 def test_rejects_splits_through_the_crack_rows(gpu):
-    p = _problem("kcrit_macro")   # crack rows 45 .. 50 with macroscopic faces
-    for rs in ([0, 47, 96], [0, 48, 96], [0, 1, 96]):
+    p = _problem("kcrit_macro")   # crack rows 45 .. 50 with macroscopic faces, crack line 48
+    for rs in ([0, 47, 96], [0, 49, 96], [0, 46, 96], [0, 1, 96], [0, 46, 48, 96]):
         with pytest.raises(gpu.LbmError):
-            gpu.Decomp(p, 2, "f32", row_start=rs)
+            gpu.Decomp(p, len(rs) - 1, "f32", row_start=rs)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("kind,row_start", [("kcrit_macro", [0, 48, 96]), ("kcrit_macro", [0, 20, 48, 51, 96]),
+                                            ("prescribed_bb", [0, 30, 77]), ("prescribed_bb", [0, 12, 30, 32, 77])])
+def test_boundary_on_the_crack_line(gpu, storage, kind, row_start):
+    """A slab boundary on the crack line: the slabs on both sides hold their
+    side's crack rows, read the other side's row from their halo, and each
+    runs the crack step -- the same K, decisions and severed links -- so the
+    run stays bit-identical to the undivided lattice, and both slabs report
+    the undivided lattice's crack state and history."""
+    p = _problem(kind)
+    info = _compare(gpu, p, storage, len(row_start) - 1, row_start=row_start)
+    jc = int(round(p["crack"]["y"]))
+    ref = gpu.Lattice(p, storage)
+    dec = gpu.Decomp(p, len(row_start) - 1, storage, row_start=row_start)
+    w0, wd0 = W.random_state(p["nx"], p["ny"], seed=5, dtype=np.float64 if storage == "f64" else np.float32)
+    ref.set_fields(w0, wd0)
+    dec.set_fields(w0, wd0)
+    ref.step(150)
+    dec.step(150)
+    lo, hi = row_start.index(jc) - 1, row_start.index(jc)
+    assert info["crack_rank"] == lo
+    for r in (lo, hi):
+        slab = dec.rank(r)
+        assert slab.crack_state() == ref.crack_state()
+        hr, hs = ref.history(), slab.history()
+        for k in hr:
+            np.testing.assert_array_equal(hs[k], hr[k])
+    assert (ref.history()["v"] > 0).sum() > 5
+    np.testing.assert_array_equal(dec.fields()[0], ref.fields()[0])
+    dec.close()
+    ref.close()
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_boundary_on_the_crack_line_matches_the_oracle(oracle_mod, gpu, storage):
+    from test_gpu_parity import compare_fields
+    p = _problem("kcrit_macro")
+    dec = gpu.Decomp(p, 2, storage, row_start=[0, 48, 96])
+    o = oracle_mod.Oracle(p)
+    w0, wd0 = W.random_state(p["nx"], p["ny"], seed=17, dtype=np.float64 if storage == "f64" else np.float32)
+    dec.set_fields(w0, wd0)
+    o.set_fields(w0, wd0)
+    dec.step(250)
+    o.step(250)
+    compare_fields(o, dec, storage)
+    ho, hs = o.history(), dec.rank(1).history()
+    assert (ho["v"] > 0).sum() > 5
+    assert np.abs(hs["K"] - ho["K"]).max() < (1e-9 if storage == "f64" else 5e-3) * np.abs(ho["K"]).max()
+    margin = np.min(np.abs(np.abs(ho["K"][ho["npairs"] > 0]) / p["crack"]["K_C"] - 1.0))
+    if storage == "f64" and margin > 1e-9:
+        np.testing.assert_array_equal(hs["tip_q"], ho["tip_q"])
+    o.close()
+    dec.close()
 
 
 # ---------------------------------------------- row slabs vs the oracle

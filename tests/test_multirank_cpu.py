@@ -61,15 +61,24 @@ def test_decomp_plan(ny, jc, hh, n):
     rs = lbm.lbm_decomp_plan(ny, jc, hh, n)
     assert rs[0] == 0 and rs[-1] == ny and len(rs) == n + 1
     assert all(b - a >= 2 for a, b in zip(rs, rs[1:]))
-    if jc >= 0:   # the crack rows stay inside one slab
-        assert not any(jc - hh < b < jc + hh for b in rs[1:-1])
-        assert sum(1 for a, b in zip(rs, rs[1:]) if a <= jc - hh and jc + hh <= b) == 1
+    if jc >= 0:   # each side's crack rows stay inside one slab (a boundary may be the crack line)
+        assert not any(jc - hh < b < jc + hh and b != jc for b in rs[1:-1])
+        below = [k for k, (a, b) in enumerate(zip(rs, rs[1:])) if a <= jc - hh and jc <= b]
+        above = [k for k, (a, b) in enumerate(zip(rs, rs[1:])) if a <= jc and jc + hh <= b]
+        assert len(below) == 1 and len(above) == 1
     even = [round(r * ny / n) for r in range(n + 1)]
     assert max(abs(a - b) for a, b in zip(rs, even)) <= max(hh, 1)
+
+
+def test_decomp_plan_puts_a_near_boundary_on_the_crack_line():
+    # an even boundary one row off the crack line goes onto it
+    assert lbm.lbm_decomp_plan(100, 51, 3, 2) == [0, 51, 100]
+    assert lbm.lbm_decomp_plan(100, 49, 3, 2) == [0, 49, 100]
+    assert lbm.lbm_decomp_plan(100, 49, 1, 2) == [0, 50, 100]   # 50 is outside the rows 48, 49
 
 
 def test_decomp_plan_rejects_impossible_splits():
     with pytest.raises(lbm.LbmError):
         lbm.lbm_decomp_plan(10, -1, 0, 6)        # slabs of fewer than 2 rows
     with pytest.raises(lbm.LbmError):
-        lbm.lbm_decomp_plan(12, 6, 3, 4)         # the crack rows take 6 of 12 rows
+        lbm.lbm_decomp_plan(12, 6, 3, 5)         # the crack rows take 6 of 12 rows: five slabs cannot avoid them
