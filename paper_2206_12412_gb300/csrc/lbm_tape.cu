@@ -241,6 +241,8 @@ lbm_status lbm_tape_create(lbm_handle *h, const int32_t *sensors, int32_t n_sens
     if (h->edge_macro) return fail(LBM_ERR_ARG, "the adjoint has no macroscopic rule on the outer edges");
     if (h->q != 5) return fail(LBM_ERR_ARG, "the adjoint is built for D2Q5 only");
     if (h->line) return fail(LBM_ERR_ARG, "the adjoint is built for cracks along +x");
+    if (h->grid.edge[LBM_BOTTOM] == EDGE_HALO || h->grid.edge[LBM_TOP] == EDGE_HALO)
+        return fail(LBM_ERR_ARG, "the adjoint is not built for row slabs");
     if (n_sens < 0 || (n_sens > 0 && !sensors)) return fail(LBM_ERR_ARG, "bad sensor array");
     if (n_steps < 1 || n_steps > ((int64_t)1 << 31)) return fail(LBM_ERR_ARG, "n_steps must lie in [1, 2^31]");
     if (checkpoint_every < 0) return fail(LBM_ERR_ARG, "checkpoint_every must be >= 0");
