@@ -626,6 +626,12 @@ def run_ours(args, rank, world, local):
     for _ in range(args.steps):
         lat.step(1)
     kern_s = kernel_seconds(lat)
+    # the same kernel with its interior CTAs staging rows by bulk copies (A/B)
+    lat.set_bulk(True)
+    for _ in range(args.steps):
+        lat.step(1)
+    kern_bulk_s = kernel_seconds(lat)
+    lat.set_bulk(False)
     lat.set_profiling(False)
     achieved = BYTES_PER_SITE * sites / kern_s / 1e9
     traffic = traffic_from_profile(sites)
@@ -700,6 +706,8 @@ def run_ours(args, rank, world, local):
         "e2e": {"value": world * sites * args.steps / e2e_s / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps,
+        "bulk_march": {"us": r4(kern_bulk_s * 1e6), "frac": r4(BYTES_PER_SITE * sites / kern_bulk_s / 1e9 / peak),
+                       "register_us": r4(kern_s * 1e6)},
         "clocks": clk,
         "wall_s": r4(wall),
     }

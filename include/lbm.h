@@ -349,6 +349,20 @@ lbm_status lbm_get_launch(const lbm_handle *h, int32_t *band_rows, int32_t *ctas
  * lattices. */
 lbm_status lbm_set_face_solve(lbm_handle *h, int32_t mode, int32_t *chunked);
 
+/* How the step kernel's interior CTAs (no edge row or column, not the crack
+ * rows) read their rows.  enable = 0 (default): each thread loads its row
+ * segments into registers one row ahead.  enable = 1: the CTA stages them in
+ * a ring of shared-memory slots filled by bulk asynchronous copies
+ * (cp.async.bulk on mbarriers) up to four rows ahead, so the bytes in flight
+ * do not depend on the number of resident warps.  The arithmetic is the same
+ * (identical results).  Taken only for FP32 w storage (LBM_F32 and the
+ * 16-bit wdot forms), D2Q5 and a crack along +x; ignored otherwise.  Every
+ * wait of the staged path is bounded: a copy that does not arrive within a
+ * clock budget (about a second) ends the launch with LBM_ERR_TIMEOUT at the
+ * next synchronising call.  Synchronises the stream and re-partitions the
+ * rows for the chosen kernel's occupancy (as lbm_set_launch(h, 0)). */
+lbm_status lbm_set_bulk(lbm_handle *h, int32_t enable);
+
 /* Kernel timing: while enabled, lbm_step launches every step directly (no
  * graph) with CUDA events on the handle's stream around the step kernel, and
  * the deferred crack step that synchronising calls apply first is timed the

@@ -341,7 +341,7 @@ cudaError_t enqueue_step_t(const lbm_handle *h, int par, cudaStream_t s)
             return e;
         }
     }
-    cudaError_t e = launch_step(a, h->n_bands, s);
+    cudaError_t e = launch_step(a, h->n_bands, s, h->bulk);
     if (e == cudaSuccess && h->edge_macro) e = launch_edge_rule(a, s);
     return e;
 }
@@ -356,12 +356,12 @@ cudaError_t enqueue_step(const lbm_handle *h, int par, cudaStream_t s)
     }
 }
 
-const void *step_kernel_for(int storage)
+const void *step_kernel_for(int storage, bool bulk = false)
 {
     switch (storage) {
-    case LBM_F32: return step_kernel_ptr<float, float>();
-    case LBM_F32_WD_BF16: return step_kernel_ptr<float, __nv_bfloat16>();
-    case LBM_F32_WD_F16: return step_kernel_ptr<float, __half>();
+    case LBM_F32: return step_kernel_ptr<float, float>(bulk);
+    case LBM_F32_WD_BF16: return step_kernel_ptr<float, __nv_bfloat16>(bulk);
+    case LBM_F32_WD_F16: return step_kernel_ptr<float, __half>(bulk);
     default: return step_kernel_ptr<double, double>();
     }
 }
@@ -1454,6 +1454,23 @@ lbm_status lbm_set_launch(lbm_handle *h, int32_t band_rows)
     LBM_CUDA(cudaStreamSynchronize(h->stream));
     drop_graph(h);
     return plan_bands(h, band_rows);
+}
+
+lbm_status lbm_set_bulk(lbm_handle *h, int32_t enable)
+{
+    if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
+    if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");
+    const bool on = enable != 0 && h->esize == 4 && !h->line && h->q == 5;
+    LBM_CUDA(cudaStreamSynchronize(h->stream));
+    int bps = 0;
+    LBM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, step_kernel_for(h->lat.storage, on), kThreads, 0));
+    if (bps < 1) return fail(LBM_ERR_ARG, "the step kernel does not fit on an SM");
+    h->bulk = on;
+    h->bps = bps;
+    drop_graph(h);
+    lbm_status rc = plan_bands(h, 0);
+    if (rc == LBM_OK) clear_error();
+    return rc;
 }
 
 lbm_status lbm_set_face_solve(lbm_handle *h, int32_t mode, int32_t *chunked)

@@ -42,6 +42,7 @@ struct lbm_handle {
     // step kernel shape
     int32_t ncb;         // column blocks of kThreads vectors
     int32_t n_bands, band_rows, crack_band, sms, bps;
+    bool bulk;           // interior CTAs stage their rows by bulk copies (lbm_set_bulk; FP32 w, D2Q5, crack along +x)
     Unit *units;         // device table, capacity ny
     std::vector<Unit> *units_h;   // host copy of the current partition
     int64_t gen;         // bumped whenever step-kernel arguments or the partition change

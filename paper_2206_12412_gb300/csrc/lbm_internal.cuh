@@ -212,7 +212,8 @@ struct RowCopy {
     void *dst;
 };
 
-template <typename T, typename D> const void *step_kernel_ptr();
+// bulk: the step kernel whose interior CTAs stage rows by bulk copies (FP32 w)
+template <typename T, typename D> const void *step_kernel_ptr(bool bulk = false);
 // The batched step as one cooperative launch of n_steps steps (a grid
 // barrier between steps, each wait bounded by `budget` clock64 cycles).
 template <typename T, typename D>
@@ -225,7 +226,8 @@ cudaError_t launch_barrier_probe(GridBarrier *bar, int ctas, int expected, long 
 template <typename T, typename D>
 cudaError_t launch_batch_step(const StepArgs<T, D> *descs, const BatchUnit *units, int n_units, int par, cudaStream_t s,
                               int threads = kThreads);
-template <typename T, typename D> cudaError_t launch_step(const StepArgs<T, D> &a, int bands, cudaStream_t s);
+template <typename T, typename D>
+cudaError_t launch_step(const StepArgs<T, D> &a, int bands, cudaStream_t s, bool bulk = false);
 template <typename T, typename D> cudaError_t launch_edge_rule(const StepArgs<T, D> &a, cudaStream_t s);
 template <typename T, typename D> int edge_rule_count(const StepArgs<T, D> &a);
 template <typename T, typename D>

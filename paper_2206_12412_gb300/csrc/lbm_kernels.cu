@@ -21,6 +21,7 @@
 // link and writes state buffer (k + 1) & 1.  The macroscopic crack-face rule
 // (Sec. 3.1) is applied inside the crack band, whose rows jc-3 .. jc+2 form
 // a band of their own.
+#include "lbm_bulk.cuh"
 #include "lbm_crack.cuh"
 #include "lbm_internal.cuh"
 #include "lbm_rows.cuh"
@@ -245,6 +246,122 @@ __device__ __forceinline__ void march(const StepArgs<T, D> &a, int cb, int j0, i
     }
 }
 
+// The bare update of an interior CTA (no edge row or column, no severed
+// link) with its rows staged in shared memory by bulk asynchronous copies
+// instead of per-thread loads: thread 0 keeps the copies of w rows up to
+// SW - 3 = 4 ahead of the row being updated, and of wdot rows up to SD - 1
+// = 4 ahead, in flight, each completing on its slot's mbarrier (16 KB per
+// CTA, 130 KB per SM, whatever the number of warps), and refills the slots
+// the CTA has finished with after each row.  A w slot holds the block's 512
+// columns and one 16-byte vector on each side (the east / west neighbours of
+// the block's edge columns).  Same arithmetic, in the same order, as the
+// register march: the results are bit-identical.  Every wait gives up after
+// a clock budget; then the CTA sets ERR_TIMEOUT, waits (again bounded) for
+// its copies still in flight, and stops.
+template <typename T, typename D>
+struct BulkRing {
+    static constexpr int N = Vec<T>::N;
+    static constexpr int SW = 7, SD = 5;               // w slots (rows j-1, j, j+1 and 4 ahead), wdot slots
+    static constexpr int WROW = kThreads * N + 2 * N;  // w elements of a slot
+    static constexpr int DROW = kThreads * N;          // wdot elements of a slot
+    T w[SW][WROW];
+    D wd[SD][DROW];
+    uint64_t bar_w[SW], bar_d[SD];
+};
+
+template <typename T, typename D>
+__device__ __forceinline__ void march_bulk(const StepArgs<T, D> &a, int cb, int j0, int j1, BulkRing<T, D> &R, T &acc)
+{
+    typedef BulkRing<T, D> B;
+    constexpr int N = Vec<T>::N;
+    const unsigned kFull = 0xffffffffu;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int xb = cb * kThreads * N;
+    const int64_t P = a.pitch;
+    const T *wsrc = a.w_in + xb - N;
+    const D *dsrc = a.wd + xb;
+    const uint32_t wbytes = B::WROW * sizeof(T), dbytes = B::DROW * sizeof(D);
+    const int nw = j1 - j0 + 2;   // w rows j0 - 1 .. j1
+    const int nd = j1 - j0;       // wdot rows j0 .. j1 - 1
+    const long long budget = (long long)1 << 31;
+    int iw = 0, id = 0;           // copies issued (thread 0)
+    if (tid == 0) {
+        for (int q = 0; q < B::SW; ++q) mbar_init(&R.bar_w[q]);
+        for (int q = 0; q < B::SD; ++q) mbar_init(&R.bar_d[q]);
+        mbar_init_fence();
+        for (; iw < B::SW && iw < nw; ++iw) bulk_load(R.w[iw], wsrc + (int64_t)(j0 - 1 + iw) * P, wbytes, &R.bar_w[iw]);
+        for (; id < B::SD && id < nd; ++id) bulk_load(R.wd[id], dsrc + (int64_t)(j0 + id) * P, dbytes, &R.bar_d[id]);
+    }
+    __syncthreads();   // the barriers are initialised before anyone waits on them
+    const T g = a.g, dt = a.dt, wd_inv = a.wd_inv, wd_scale = a.wd_scale;
+    T *wout = a.w_out + xb + tid * N;
+    D *wdout = a.wd + xb + tid * N;
+    int ok = mbar_wait(&R.bar_w[0], 0, budget) && mbar_wait(&R.bar_w[1], 0, budget);
+    for (int q = 0; q < nd; ++q) {
+        const int ia = q + 2;   // w index of row j + 1
+        ok = ok && mbar_wait(&R.bar_w[ia % B::SW], (ia / B::SW) & 1, budget) &&
+             mbar_wait(&R.bar_d[q % B::SD], (q / B::SD) & 1, budget);
+        if (ok) {
+            const T *rb = R.w[q % B::SW] + N + tid * N;
+            const T *rc = R.w[(q + 1) % B::SW] + N + tid * N;
+            const T *ra = R.w[ia % B::SW] + N + tid * N;
+            Row<T, N> wb, wc, wa, wdv;
+            ld_row(rb, wb);
+            ld_row(rc, wc);
+            ld_row(ra, wa);
+            typename WdIO<D>::Raw raw;
+            WdIO<D>::fetch(R.wd[q % B::SD] + tid * N, raw);
+            WdIO<D>::unpack(raw, wdv, wd_inv);
+            T left0 = __shfl_up_sync(kFull, wc.v[N - 1], 1);
+            T rightN = __shfl_down_sync(kFull, wc.v[0], 1);
+            if (lane == 0) left0 = rc[-1];
+            if (lane == 31) rightN = rc[N];
+            Row<T, N> wnew, wdnew;
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                const T wl = k == 0 ? left0 : wc.v[k - 1];
+                const T wr = k == N - 1 ? rightN : wc.v[k + 1];
+                const T lap = ((wa.v[k] + wb.v[k]) + (wl + wr)) - (T)4 * wc.v[k];
+                wdnew.v[k] = wdv.v[k] + g * lap;
+                wnew.v[k] = wc.v[k] + dt * wdnew.v[k];
+            }
+            const int64_t o = (int64_t)(j0 + q) * P;
+            stg_row(wout + o, wnew);
+            WdIO<D>::store(wdout + o, wdnew, wd_scale);
+            acc += wnew.v[0];
+        }
+        // every thread is done with w row j - 1 and wdot row j: refill their slots
+        ok = __syncthreads_and(ok);
+        if (!ok) break;
+        if (tid == 0) {
+            if (iw < nw) {
+                bulk_load(R.w[iw % B::SW], wsrc + (int64_t)(j0 - 1 + iw) * P, wbytes, &R.bar_w[iw % B::SW]);
+                ++iw;
+            }
+            if (id < nd) {
+                bulk_load(R.wd[id % B::SD], dsrc + (int64_t)(j0 + id) * P, dbytes, &R.bar_d[id % B::SD]);
+                ++id;
+            }
+        }
+    }
+    if (!ok) {
+        // a copy did not arrive within the budget: report it, and let the
+        // copies still in flight land (bounded) before the CTA leaves
+        if (tid == 0) {
+            atomicOr(a.err, (uint32_t)ERR_TIMEOUT);
+            for (int q = 0; q < B::SW && q < iw; ++q) {
+                const int last = q + B::SW * ((iw - 1 - q) / B::SW);
+                mbar_wait(&R.bar_w[q], (last / B::SW) & 1, budget);
+            }
+            for (int q = 0; q < B::SD && q < id; ++q) {
+                const int last = q + B::SD * ((id - 1 - q) / B::SD);
+                mbar_wait(&R.bar_d[q], (last / B::SD) & 1, budget);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // One CTA of a time step: column block cb of band `band` of the lattice that
 // `a` describes (the kernel parameter block, or a copy in shared memory).
 // BOTH: compiled with the path that evaluates the two ends of a two-tip
@@ -254,8 +371,11 @@ __device__ __forceinline__ void march(const StepArgs<T, D> &a, int cb, int j0, i
 // single-lattice kernels use kThreads, the batched kernel any multiple of 32.
 // COH: w read with coherent loads (the persistent batched kernel, where the
 // same launch wrote it).
+// ring: the shared-memory ring of the bulk march (nullptr: every CTA takes
+// the register march).
 template <typename T, typename D, bool REC, bool BOTH = false, int TH = kThreads, bool COH = false>
-__device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int band, CrackState &sS, const RecArgs &r)
+__device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int band, CrackState &sS, const RecArgs &r,
+                                         BulkRing<T, D> *ring = nullptr)
 {
     constexpr int N = Vec<T>::N;
     const unsigned kFull = 0xffffffffu;
@@ -361,9 +481,15 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
         // and the bands holding the bottom and top rows, need them
         const int xw0 = (cb * TH + (tid & ~31)) * N;   // first column of this warp
         const bool edge = (xw0 == 0) | (xw0 + 32 * N - 1 >= nx - 1) | (j0 == 0) | (j1 == a.ny);
-        // warps wholly right of the lattice (the ragged last column block) have
-        // nothing to load or store
-        if (xw0 < nx) {
+        // a CTA with no edge row or column anywhere takes the bulk march
+        // when there is a ring (uniform across the CTA: its barriers)
+        const int xb = cb * TH * N;
+        const bool inner = xb > 0 && xb + TH * N < nx && j0 > 0 && j1 < a.ny;
+        if (ring != nullptr && TH == kThreads && inner) {
+            march_bulk<T, D>(a, cb, j0, j1, *ring, acc);
+        } else if (xw0 < nx) {
+            // warps wholly right of the lattice (the ragged last column block)
+            // have nothing to load or store
             if (edge) march<T, D, true, TH, COH>(a, cb, j0, j1, acc);
             else march<T, D, false, TH, COH>(a, cb, j0, j1, acc);
         }
@@ -396,6 +522,16 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
 {
     __shared__ CrackState sS;
     step_cta<T, D, false, BOTH>(a, blockIdx.x, blockIdx.y, sS, RecArgs{});
+}
+
+// The step kernel whose interior CTAs stage their rows with bulk copies
+// (FP32 w; see march_bulk).
+template <typename T, typename D, bool BOTH>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) step_kernel_bulk(const StepArgs<T, D> a)
+{
+    __shared__ CrackState sS;
+    __shared__ __align__(128) BulkRing<T, D> ring;
+    step_cta<T, D, false, BOTH>(a, blockIdx.x, blockIdx.y, sS, RecArgs{}, &ring);
 }
 
 // The step kernel with the recording of a forward run for the adjoint.
@@ -569,18 +705,28 @@ cudaError_t launch_batch_persistent(const StepArgs<T, D> *descs, int n_lat, cons
     return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3((unsigned)threads), args, 0, s);
 }
 
-template <typename T, typename D> const void *step_kernel_ptr()
+template <typename T, typename D> const void *step_kernel_ptr(bool bulk)
 {
+    if constexpr (sizeof(T) == 4)
+        if (bulk) return reinterpret_cast<const void *>(&step_kernel_bulk<T, D, false>);
     return reinterpret_cast<const void *>(&step_kernel<T, D, false>);
 }
 
 template <typename T, typename D>
-cudaError_t launch_step(const StepArgs<T, D> &a, int bands, cudaStream_t s)
+cudaError_t launch_step(const StepArgs<T, D> &a, int bands, cudaStream_t s, bool bulk)
 {
+    const dim3 grid((unsigned)a.ncb, (unsigned)bands);
+    if constexpr (sizeof(T) == 4) {
+        if (bulk) {
+            if (a.p.two_tips) step_kernel_bulk<T, D, true><<<grid, kThreads, 0, s>>>(a);
+            else step_kernel_bulk<T, D, false><<<grid, kThreads, 0, s>>>(a);
+            return cudaGetLastError();
+        }
+    }
     if (a.p.two_tips)
-        step_kernel<T, D, true><<<dim3((unsigned)a.ncb, (unsigned)bands), kThreads, 0, s>>>(a);
+        step_kernel<T, D, true><<<grid, kThreads, 0, s>>>(a);
     else
-        step_kernel<T, D, false><<<dim3((unsigned)a.ncb, (unsigned)bands), kThreads, 0, s>>>(a);
+        step_kernel<T, D, false><<<grid, kThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -927,14 +1073,14 @@ cudaError_t launch_fill_pads(T *w, int64_t pitch, int nx, int ny, const int32_t 
     return cudaGetLastError();
 }
 
-template const void *step_kernel_ptr<double, double>();
-template const void *step_kernel_ptr<float, float>();
-template const void *step_kernel_ptr<float, __nv_bfloat16>();
-template const void *step_kernel_ptr<float, __half>();
-template cudaError_t launch_step<double, double>(const StepArgs<double, double> &, int, cudaStream_t);
-template cudaError_t launch_step<float, float>(const StepArgs<float, float> &, int, cudaStream_t);
-template cudaError_t launch_step<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> &, int, cudaStream_t);
-template cudaError_t launch_step<float, __half>(const StepArgs<float, __half> &, int, cudaStream_t);
+template const void *step_kernel_ptr<double, double>(bool);
+template const void *step_kernel_ptr<float, float>(bool);
+template const void *step_kernel_ptr<float, __nv_bfloat16>(bool);
+template const void *step_kernel_ptr<float, __half>(bool);
+template cudaError_t launch_step<double, double>(const StepArgs<double, double> &, int, cudaStream_t, bool);
+template cudaError_t launch_step<float, float>(const StepArgs<float, float> &, int, cudaStream_t, bool);
+template cudaError_t launch_step<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> &, int, cudaStream_t, bool);
+template cudaError_t launch_step<float, __half>(const StepArgs<float, __half> &, int, cudaStream_t, bool);
 template cudaError_t launch_step_rec<double>(const StepArgs<double, double> &, const RecArgs &, int, cudaStream_t);
 template cudaError_t launch_step_rec<float>(const StepArgs<float, float> &, const RecArgs &, int, cudaStream_t);
 template cudaError_t launch_batch_step<double, double>(const StepArgs<double, double> *, const BatchUnit *, int, int, cudaStream_t, int);

@@ -790,9 +790,13 @@ __global__ void __launch_bounds__(256) line_faces_chunk_kernel(const StepArgs<T,
                                                                const FaceChunk *Cs, const FaceItem *I)
 {
     extern __shared__ __align__(16) unsigned char face_smem[];
+    __shared__ int slv[kFaceLevels + 1];
     const int tid = threadIdx.x, nt = blockDim.x;
     const FaceChunk &C = Cs[blockIdx.x];
     const int64_t P = a.pitch;
+    // the level offsets, read once (the level loop below must not wait on
+    // a global load per level)
+    for (int L = tid; L <= kFaceLevels; L += nt) slv[L] = C.lv[L];
     int any = 0;
     for (int c = C.own_lo + tid; c < C.own_hi; c += nt) any |= face_is_point(a, F[c].i, F[c].j);
     if (!__syncthreads_or(any)) return;
@@ -804,8 +808,14 @@ __global__ void __launch_bounds__(256) line_faces_chunk_kernel(const StepArgs<T,
     int16_t *kc = reinterpret_cast<int16_t *>(ac + 8 * n);   // [8 n] their items (-1: unused)
     uint8_t *act = reinterpret_cast<uint8_t *>(kc + 8 * n);  // [n]
     for (int l = tid; l < n; l += nt) {
+        // the whole record and w at all its corners first (unused corners name
+        // the site itself), so the loads go out together rather than one
+        // dependent chain per corner
         const FaceItem it = I[C.off + l];
-        const LineFace &f = F[it.f];
+        const LineFace f = F[it.f];
+        T wk[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) wk[k] = a.w_out[(int64_t)f.cj[k] * P + f.ci[k]];
         act[l] = face_is_point(a, f.i, f.j);
         val[l] = a.w_out[(int64_t)f.j * P + f.i];
         T b = (T)0, s = (T)0;
@@ -822,7 +832,7 @@ __global__ void __launch_bounds__(256) line_faces_chunk_kernel(const StepArgs<T,
                 kc[8 * l + q] = (int16_t)m;
                 ++q;
             } else {
-                b += ak * a.w_out[(int64_t)f.cj[k] * P + f.ci[k]];
+                b += ak * wk[k];
             }
         }
         for (int k = q; k < 8; ++k) kc[8 * l + k] = -1;
@@ -832,7 +842,8 @@ __global__ void __launch_bounds__(256) line_faces_chunk_kernel(const StepArgs<T,
     __syncthreads();
     int stuck = 0;
     for (int L = 0; L < kFaceLevels; ++L) {
-        const int lo = C.lv[L], hi = C.lv[L + 1];
+        const int lo = slv[L], hi = slv[L + 1];
+        if (lo >= n) break;       // no item of this level or above
         if (lo == hi) continue;   // the same for every thread of the CTA
         for (int l = lo + tid; l < hi; l += nt) {
             if (!act[l]) continue;

@@ -359,6 +359,11 @@ class Lattice:
     def set_launch(self, band_rows: int):
         lbm_set_launch(self.h, band_rows)
 
+    def set_bulk(self, enable: bool = True):
+        """Stage the interior CTAs' rows by bulk asynchronous copies
+        (lbm_set_bulk); same results."""
+        _check(load_library().lbm_set_bulk(C.c_void_p(self.h), 1 if enable else 0))
+
     def set_face_solve(self, mode: int) -> bool:
         """0: the chunked solve of the line crack's macroscopic faces where
         the coupling allows it, 1: the one-CTA solve; returns whether the
