@@ -27,7 +27,7 @@ _lib = None
 
 QONE = 1 << 32  # tip fixed point: 1 dh = 2^32 units
 
-EDGE = {"free": 0, "dirichlet": 1, "periodic": 2}
+EDGE = {"free": 0, "dirichlet": 1, "periodic": 2, "halo": 3}
 EDGE_INDEX = {"left": 0, "right": 1, "bottom": 2, "top": 3}
 BC = {"bounceback": 0, "macroscopic": 1}
 CRACK = {"none": 0, "stationary": 1, "prescribed": 2, "kcrit": 3}
@@ -144,6 +144,10 @@ def _load():
         lib.orc_checklinks_standalone.restype = C.c_int32
         lib.orc_load_value.argtypes = [P, C.c_int32, C.c_int64]
         lib.orc_load_value.restype = C.c_double
+        lib.orc_collide.argtypes = [P]
+        lib.orc_finish_step.argtypes = [P]
+        lib.orc_fs_row.argtypes = [P, C.c_int32, d]
+        lib.orc_set_halo.argtypes = [P, C.c_int32, d]
         lib.orc_set_threads.argtypes = [P, C.c_int32]
         lib.orc_set_threads.restype = C.c_int32
         lib.orc_g.argtypes = [P]
@@ -254,6 +258,27 @@ class Oracle:
 
     def step(self, n: int = 1):
         self.lib.orc_step(self.h, int(n))
+
+    # row slabs (bottom / top edges of kind "halo"): a step is collide(),
+    # then the exchange of the post-collision rows that cross the slab's
+    # boundaries (fs_row -> the neighbour's set_halo), then finish_step()
+    def collide(self):
+        self.lib.orc_collide(self.h)
+
+    def fs_row(self, side: int) -> np.ndarray:
+        """Post-collision values leaving across the bottom (side 0) or top (1) edge."""
+        out = np.empty(self.nx)
+        self.lib.orc_fs_row(self.h, int(side), _dptr(out))
+        return out
+
+    def set_halo(self, side: int, row):
+        """The neighbour's values arriving across the bottom (side 0) or top (1) edge."""
+        r = np.ascontiguousarray(row, dtype=np.float64)
+        assert r.size == self.nx
+        self.lib.orc_set_halo(self.h, int(side), _dptr(r))
+
+    def finish_step(self):
+        self.lib.orc_finish_step(self.h)
 
     def cuts(self):
         """(cut_h, cut_v) as (ny, nx) uint8: link (i,j)-(i+1,j) / (i,j)-(i,j+1) severed."""

@@ -79,7 +79,11 @@
 #define ORC_Q 32 /* fixed point: 1 dh = 2^32 units */
 #define ORC_PI 3.14159265358979323846
 
-enum { ORC_FREE = 0, ORC_DIRICHLET = 1, ORC_PERIODIC = 2 };
+/* ORC_HALO: a bottom or top edge inside a lattice split into row slabs; the
+ * distribution that crosses it into the slab is the neighbouring slab's
+ * post-collision value, handed over between the collision and the streaming
+ * (orc_collide / orc_fs_row / orc_set_halo / orc_finish_step). */
+enum { ORC_FREE = 0, ORC_DIRICHLET = 1, ORC_PERIODIC = 2, ORC_HALO = 3 };
 enum { ORC_LEFT = 0, ORC_RIGHT = 1, ORC_BOTTOM = 2, ORC_TOP = 3 };
 enum { ORC_BC_BOUNCEBACK = 0, ORC_BC_MACROSCOPIC = 1 };
 enum { ORC_CRACK_NONE = 0, ORC_CRACK_STATIONARY = 1, ORC_CRACK_PRESCRIBED = 2, ORC_CRACK_KCRIT = 3 };
@@ -166,6 +170,7 @@ typedef struct {
     uint8_t *inq, *visited;
     double *series[4];
     int32_t threads;     /* OpenMP threads of the per-site loops (1 unless set) */
+    double *halo[2];     /* ORC_HALO edges: f^2 arriving at row 0, f^4 arriving at row ny-1 (nx each) */
 } orc_state;
 
 /* Lattice velocities in units of c = dh/dt: D2Q5 (Sec. 3, eq. 2) uses
@@ -353,6 +358,7 @@ void orc_destroy(orc_state *s)
     free(s->lbprev); free(s->hKl); free(s->hvl); free(s->htipl); free(s->htipy); free(s->htipyl); free(s->hnpl); free(s->hgrowl);
     free(s->queue); free(s->inq); free(s->visited);
     for (int e = 0; e < 4; ++e) free(s->series[e]);
+    free(s->halo[0]); free(s->halo[1]);
     free(s);
 }
 
@@ -439,10 +445,18 @@ orc_state *orc_create(const orc_config *cfg)
         double rmin = cfg->r_min_fixed > 0.0 ? cfg->r_min_fixed : cfg->r0;
         if (!(rmin > 0.5 * cfg->dh)) return NULL;
     }
+    /* halo edges (row slabs): bottom / top only, D2Q5, not with the
+     * macroscopic rule on the outer edges, nor a crack in any direction */
+    for (int e = 0; e < 4; ++e) {
+        if (cfg->edge[e] != ORC_HALO) continue;
+        if ((e != ORC_BOTTOM && e != ORC_TOP) || Q != 5 || cfg->edge_macro || cfg->line) return NULL;
+    }
     orc_state *s = xcalloc(1, sizeof(orc_state));
     s->c = *cfg;
     s->Q = Q;
     size_t n = (size_t)cfg->nx * cfg->ny;
+    s->halo[0] = xcalloc((size_t)cfg->nx, sizeof(double));
+    s->halo[1] = xcalloc((size_t)cfg->nx, sizeof(double));
     s->cs = sqrt(cfg->mu / cfg->rho);
     s->g = s->cs * s->cs * cfg->dt / (cfg->dh * cfg->dh);
     for (int a = 0; a < Q; ++a) { s->f[a] = xcalloc(n, sizeof(double)); s->fs[a] = xcalloc(n, sizeof(double)); }
@@ -805,18 +819,13 @@ static void boundary_solve(orc_state *s)
 
 /* -------------------------------------------------------------- LBM step */
 
-static void lbm_step(orc_state *s)
+/* The LBM step in two parts: the collision, and the rest (streaming, moment,
+ * integration, the macroscopic rule).  A lattice split into row slabs hands
+ * its boundary rows' post-collision values to the neighbours in between. */
+static void lbm_collide(orc_state *s)
 {
-    int nx = s->c.nx, ny = s->c.ny;
-    size_t n = (size_t)nx * ny;
-    double g = s->g, om = s->c.omega, dt = s->c.dt;
-    double wstar[4];
-    for (int e = 0; e < 4; ++e) wstar[e] = load_value(s, e, s->step);
-
-    /* The three per-site loops below touch only their own site (collision,
-     * moment) or read the post-collision values of other sites (streaming),
-     * so they may run on several threads without changing any result; the
-     * thread count is 1 unless orc_set_threads raised it (timing runs only). */
+    size_t n = (size_t)s->c.nx * s->c.ny;
+    double om = s->c.omega;
     int nth = s->threads > 1 ? s->threads : 1;
     (void)nth;
     /* collision (eq. LBE, right-hand side) */
@@ -828,6 +837,30 @@ static void lbm_step(orc_state *s)
         equilibrium_q(s, s->w[k], wdot, feq);
         for (int a = 0; a < s->Q; ++a) s->fs[a][k] = s->f[a][k] - om * (s->f[a][k] - feq[a]);
     }
+}
+
+static void lbm_stream_rest(orc_state *s);
+
+static void lbm_step(orc_state *s)
+{
+    lbm_collide(s);
+    lbm_stream_rest(s);
+}
+
+static void lbm_stream_rest(orc_state *s)
+{
+    int nx = s->c.nx, ny = s->c.ny;
+    size_t n = (size_t)nx * ny;
+    double g = s->g, dt = s->c.dt;
+    double wstar[4];
+    for (int e = 0; e < 4; ++e) wstar[e] = load_value(s, e, s->step);
+
+    /* The per-site loops (the collision above, and below) touch only their
+     * own site or read the post-collision values of other sites, so they may
+     * run on several threads without changing any result; the thread count
+     * is 1 unless orc_set_threads raised it (timing runs only). */
+    int nth = s->threads > 1 ? s->threads : 1;
+    (void)nth;
     /* streaming along intact links (eq. LBE, left-hand side); a missing link
      * takes bounce-back (free edge, crack face) or anti-bounce-back (Dirichlet) */
 #pragma omp parallel for num_threads(nth) schedule(static) if (nth > 1)
@@ -845,6 +878,8 @@ static void lbm_step(orc_state *s)
                     int e = missing_edge(s, k, b);
                     if (s->c.edge[e] == ORC_DIRICHLET)
                         s->f[a][k] = -s->fs[b][k] + 2.0 * weight(s, a) * g * wstar[e];
+                    else if (s->c.edge[e] == ORC_HALO)   /* from the neighbouring slab */
+                        s->f[a][k] = s->halo[e == ORC_BOTTOM ? 0 : 1][i];
                     else
                         s->f[a][k] = s->fs[b][k];
                 } else {
@@ -1196,6 +1231,34 @@ static void crack_growth(orc_state *s)
         s->htipyl[h] = s->ltip_yq;
     }
     s->hist_n += 1;
+}
+
+/* Row slabs: orc_collide runs the collision of the next step; orc_fs_row
+ * copies the post-collision values that leave the slab across its bottom
+ * (side 0: f*^4 of row 0) or top (side 1: f*^2 of row ny-1) edge; the
+ * neighbour hands them to orc_set_halo (side 0: they arrive at row 0 as f^2,
+ * side 1: at row ny-1 as f^4); orc_finish_step completes the step (streaming
+ * and the rest, then the crack handling of Alg. 1).  orc_collide followed by
+ * orc_finish_step is orc_step(s, 1). */
+void orc_collide(orc_state *s) { lbm_collide(s); }
+
+void orc_fs_row(const orc_state *s, int32_t side, double *out)
+{
+    int nx = s->c.nx;
+    size_t row = side == 0 ? 0 : (size_t)(s->c.ny - 1) * nx;
+    const double *fs = s->fs[side == 0 ? 4 : 2];
+    for (int i = 0; i < nx; ++i) out[i] = fs[row + i];
+}
+
+void orc_set_halo(orc_state *s, int32_t side, const double *in)
+{
+    for (int i = 0; i < s->c.nx; ++i) s->halo[side == 0 ? 0 : 1][i] = in[i];
+}
+
+void orc_finish_step(orc_state *s)
+{
+    lbm_stream_rest(s);
+    crack_growth(s);
 }
 
 /* Threads for the per-site loops of the LBM step (timing of the CPU baseline;

@@ -84,9 +84,14 @@ def _run_ranks(row_start, storage, steps, seed):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     world = len(row_start) - 1
-    mp.start_processes(_worker, args=(world, _free_port(), row_start, storage, steps, seed, q), nprocs=world,
-                       join=True, start_method="spawn")
-    return sorted((q.get(timeout=120) for _ in range(world)), key=lambda t: t[0])
+    pc = mp.start_processes(_worker, args=(world, _free_port(), row_start, storage, steps, seed, q), nprocs=world,
+                            join=False, start_method="spawn")
+    # take the results before joining: a child cannot exit while its queue
+    # still holds data the parent has not read
+    res = sorted((q.get(timeout=120) for _ in range(world)), key=lambda t: t[0])
+    while not pc.join(timeout=60):
+        pass
+    return res
 
 
 @pytest.mark.parametrize("storage", ["f64", "f32"])
