@@ -550,6 +550,8 @@ def run_profile(args, W, lbm, torch, rank):
     p = profile_problem(args, W)
     stream = torch.cuda.current_stream()
     lat = lbm.Lattice(p, args.storage, stream=stream)
+    if args.bulk:
+        lat.set_bulk(True)
     lat.step(args.prelude)
     lat.sync()
     big = p["nx"] * p["ny"] * 16 > (1 << 30)
@@ -753,6 +755,7 @@ def main():
     ap.add_argument("--size", type=int, default=16384, help="with --workload large: the lattice's side")
     ap.add_argument("--storage", default="f32", choices=["f32", "f32_bf16", "f32_f16", "f64"],
                     help="with --profile-only: the storage form")
+    ap.add_argument("--bulk", action="store_true", help="with --profile-only: the bulk-copy march (lbm_set_bulk)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
