@@ -376,12 +376,13 @@ def measure_adjoint(lbm, W, torch, stream, n_steps=None):
 
 
 def measure_storage_large(lbm, W, torch, stream, peak, n=16384):
-    """The 16-bit wdot storage forms on the headline lattice: the step
-    kernel's own CUDA-event time, 20 steps after 20."""
+    """The 12-byte storage forms on the headline lattice (leapfrog FP32, and
+    FP32 w with 16-bit wdot): the step kernel's own CUDA-event time, 20 steps
+    after 20."""
     p = W.large_prescribed(n)
     sites = p["nx"] * p["ny"]
     out = {}
-    for storage, bps in (("f32_bf16", 12), ("f32_f16", 12)):
+    for storage, bps in (("f32_lf", 12), ("f32_bf16", 12), ("f32_f16", 12)):
         lat = lbm.Lattice(p, storage, stream=stream)
         lat.step(20)
         lat.set_profiling(True)
@@ -516,11 +517,11 @@ def measure_virtual_ranks(lbm, W, torch, stream, problem, steps=256):
 
 
 def measure_mixed_4096(lbm, W, torch, stream, peak, flush_l2, steps):
-    """The 16-bit wdot forms on the 4096 x 2048 K-criterion run (L2 flushed)."""
+    """The 12-byte storage forms on the 4096 x 2048 K-criterion run (L2 flushed)."""
     p = W.kcrit_single()
     sites = p["nx"] * p["ny"]
     out = {}
-    for storage in ("f32_bf16", "f32_f16"):
+    for storage in ("f32_lf", "f32_bf16", "f32_f16"):
         k = step_time(lbm, p, storage, stream, flush_l2, 2500, min(steps, 100))
         out[storage] = {"glups": r4(sites / k / 1e9), "frac": r4(12 * sites / k / 1e9 / peak)}
     return out

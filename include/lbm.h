@@ -84,8 +84,15 @@ enum { LBM_FORM_MOMENT = 0 };
  * LBM_F32: w and wdot in FP32, FP32 arithmetic.  LBM_F32_WD_BF16 /
  * LBM_F32_WD_F16: w in FP32, wdot stored in 16 bits (BF16, or FP16 holding
  * wdot * scale, see lbm_set_wd_scale), FP32 arithmetic; 12 bytes per site
- * update instead of 16.  Also the dtype codes of field exchange. */
-enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F32_WD_BF16 = 2, LBM_F32_WD_F16 = 3 };
+ * update instead of 16.  LBM_F32_LEAPFROG: the state kept as w_n and w_{n-1}
+ * in FP32 (the Euler integration of Sec. 3 makes wdot_n = (w_n - w_{n-1}) /
+ * dt, eq. integration), FP32 arithmetic, w_{n+1} = w_n + ((w_n - w_{n-1}) +
+ * g dt lap) written over w_{n-1}: 12 bytes per site update with FP32 state;
+ * wdot is formed when read (LBM_FIELD_WDOT) and, when set, stored as
+ * w_{n-1} = w_n - dt wdot against the current w (set W before WDOT).  D2Q5
+ * with a crack along +x (not lbm_create_line, D2Q9 or tapes).  LBM_F64 and
+ * LBM_F32 are also the dtype codes of field exchange. */
+enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F32_WD_BF16 = 2, LBM_F32_WD_F16 = 3, LBM_F32_LEAPFROG = 4 };
 /* treatment of the boundaries.  BOUNCEBACK: link-local rules on the crack
  * faces and the outer edges.  MACROSCOPIC: the macroscopic rule of Sec. 3.1
  * on the crack faces, link-local rules on the outer edges.

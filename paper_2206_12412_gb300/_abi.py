@@ -11,7 +11,7 @@ STATUS_NAMES = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR
 
 EDGE = {"free": 0, "dirichlet": 1, "periodic": 2}
 EDGE_INDEX = {"left": 0, "right": 1, "bottom": 2, "top": 3}
-STORAGE = {"f64": 0, "f32": 1, "f32_bf16": 2, "f32_f16": 3}
+STORAGE = {"f64": 0, "f32": 1, "f32_bf16": 2, "f32_f16": 3, "f32_lf": 4}
 BC = {"bounceback": 0, "macroscopic": 1, "macroscopic_edges": 2}
 VELOCITY_SET = {"D2Q5": 0, "D2Q9": 1}
 CRACK = {"none": 0, "stationary": 1, "prescribed": 2, "kcrit": 3}

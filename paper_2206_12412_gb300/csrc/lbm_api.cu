@@ -216,6 +216,7 @@ std::vector<LineFace> line_faces_table(const LineSpec &L, int nx, int ny, std::v
             f.cand[c] = -1;
             f.a[c] = 0.0;
         }
+        for (int c = 0; c < 8; ++c) f.af[c] = (float)f.a[c];
     }
     return tab;
 }
@@ -325,13 +326,15 @@ cudaError_t enqueue_step_t(const lbm_handle *h, int par, cudaStream_t s)
 {
     StepArgs<T, D> a;
     make_step_args(h, par, a);
-    if (h->line) {
-        cudaError_t e = launch_line_step(a, s);
-        if (e == cudaSuccess && h->n_face_chunks > 0 && h->face_solve == 0)
-            e = launch_line_faces_chunked(a, h->faces, h->face_chunks, h->n_face_chunks, h->face_items, s);
-        else if (e == cudaSuccess && h->n_faces > 0)
-            e = launch_line_faces(a, h->faces, h->n_faces, h->face_scratch, s);
-        return e;
+    if constexpr (!std::is_same<D, Lf>::value) {   // a crack in any direction has no leapfrog storage
+        if (h->line) {
+            cudaError_t e = launch_line_step(a, s);
+            if (e == cudaSuccess && h->n_face_chunks > 0 && h->face_solve == 0)
+                e = launch_line_faces_chunked(a, h->faces, h->face_chunks, h->n_face_chunks, h->face_items, s);
+            else if (e == cudaSuccess && h->n_faces > 0)
+                e = launch_line_faces(a, h->faces, h->n_faces, h->face_scratch, s);
+            return e;
+        }
     }
     if constexpr (std::is_same<T, D>::value) {
         if (h->q == 9) {
@@ -352,6 +355,7 @@ cudaError_t enqueue_step(const lbm_handle *h, int par, cudaStream_t s)
     case LBM_F32: return enqueue_step_t<float, float>(h, par, s);
     case LBM_F32_WD_BF16: return enqueue_step_t<float, __nv_bfloat16>(h, par, s);
     case LBM_F32_WD_F16: return enqueue_step_t<float, __half>(h, par, s);
+    case LBM_F32_LEAPFROG: return enqueue_step_t<float, Lf>(h, par, s);
     default: return enqueue_step_t<double, double>(h, par, s);
     }
 }
@@ -362,6 +366,7 @@ const void *step_kernel_for(int storage, bool bulk = false)
     case LBM_F32: return step_kernel_ptr<float, float>(bulk);
     case LBM_F32_WD_BF16: return step_kernel_ptr<float, __nv_bfloat16>(bulk);
     case LBM_F32_WD_F16: return step_kernel_ptr<float, __half>(bulk);
+    case LBM_F32_LEAPFROG: return step_kernel_ptr<float, Lf>(bulk);
     default: return step_kernel_ptr<double, double>();
     }
 }
@@ -731,7 +736,7 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
     if (d2q9 && slab) return fail(LBM_ERR_ARG, "D2Q9 is not built for row slabs");
     if (lattice->form != LBM_FORM_MOMENT) return fail(LBM_ERR_ARG, "only the moment form is built");
     if (lattice->omega != 1.0) return fail(LBM_ERR_ARG, "omega = dt/tau must be 1 (tau = dt)");
-    if (lattice->storage < LBM_F64 || lattice->storage > LBM_F32_WD_F16) return fail(LBM_ERR_ARG, "unknown storage");
+    if (lattice->storage < LBM_F64 || lattice->storage > LBM_F32_LEAPFROG) return fail(LBM_ERR_ARG, "unknown storage");
     if (lattice->bc_mode < LBM_BC_BOUNCEBACK || lattice->bc_mode > LBM_BC_MACROSCOPIC_EDGES)
         return fail(LBM_ERR_ARG, "unknown boundary mode");
     const bool macro_faces = lattice->bc_mode != LBM_BC_BOUNCEBACK;
@@ -825,7 +830,10 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
     h->crack = cr;
     h->jc = jc;
     h->esize = lattice->storage == LBM_F64 ? 8 : 4;
-    h->esize_d = lattice->storage == LBM_F64 ? 8 : (lattice->storage == LBM_F32 ? 4 : 2);
+    // leapfrog storage has no wdot plane (its "wdot plane" is the other w buffer)
+    h->esize_d = lattice->storage == LBM_F64 ? 8
+               : lattice->storage == LBM_F32 ? 4
+               : lattice->storage == LBM_F32_LEAPFROG ? 0 : 2;
     h->g = g;
     h->stream = (cudaStream_t)stream;
     h->sticky = LBM_OK;
@@ -876,7 +884,7 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
     // one block for everything, carved at 256-byte boundaries
     const size_t plane = (size_t)(grid->ny + 2) * (size_t)h->pitch * h->esize;
     const size_t plane_d = (size_t)(grid->ny + 2) * (size_t)h->pitch * h->esize_d;
-    const size_t staging = h->esize_d == 2 ? (size_t)grid->nx * grid->ny * 4 : 0;
+    const size_t staging = (h->esize_d == 2 || h->esize_d == 0) ? (size_t)grid->nx * grid->ny * 4 : 0;
     const size_t mask = (size_t)grid->ny * (size_t)h->words * 4;
     // the V mask has one more row below row 0: the links across the bottom
     // boundary of a row slab whose boundary is the crack line
@@ -913,7 +921,7 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
     const size_t origin = ((size_t)h->pitch + (size_t)xoff) * h->esize;   // row 0, column 0
     h->w[0] = base + o_w0 + origin;
     h->w[1] = base + o_w1 + origin;
-    h->wd = base + o_wd + ((size_t)h->pitch + (size_t)xoff) * h->esize_d;
+    h->wd = h->esize_d ? base + o_wd + ((size_t)h->pitch + (size_t)xoff) * h->esize_d : nullptr;
     h->wbase[0] = base + o_w0;
     h->wbase[1] = base + o_w1;
     h->wdbase = base + o_wd;
@@ -1161,7 +1169,14 @@ lbm_status lbm_fields(lbm_handle *h, int32_t which, void *dst, int32_t dst_on_de
     if (dtype != exchange_dtype(h)) return fail(LBM_ERR_ARG, "dtype must be LBM_F64 for F64 storage, LBM_F32 otherwise");
     const size_t row = (size_t)h->grid.nx * h->esize;
     const cudaMemcpyKind kind = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    if (which == LBM_FIELD_WDOT && wd16(h)) {
+    if (which == LBM_FIELD_WDOT && h->esize_d == 0) {
+        // leapfrog storage: wdot_n = (w_n - w_{n-1}) / dt
+        float *conv = dst_on_device ? static_cast<float *>(dst) : h->staging;
+        LBM_CUDA(launch_lf_wdot(static_cast<const float *>(h->w[h->parity]), static_cast<const float *>(h->w[h->parity ^ 1]),
+                                h->pitch, h->grid.nx, h->grid.ny, (float)h->grid.dt, conv, h->stream));
+        if (!dst_on_device)
+            LBM_CUDA(cudaMemcpyAsync(dst, conv, (size_t)h->grid.nx * h->grid.ny * 4, cudaMemcpyDeviceToHost, h->stream));
+    } else if (which == LBM_FIELD_WDOT && wd16(h)) {
         float *conv = dst_on_device ? static_cast<float *>(dst) : h->staging;
         LBM_CUDA(wd_to_f32(h, conv, h->wd_scale, h->stream));
         if (!dst_on_device)
@@ -1183,7 +1198,16 @@ lbm_status lbm_set_fields(lbm_handle *h, int32_t which, const void *src, int32_t
     lbm_status rc = finalize(h);   // the pending crack step reads the fields being replaced
     if (rc != LBM_OK) return rc;
     const size_t row = (size_t)h->grid.nx * h->esize;
-    if (which == LBM_FIELD_WDOT && wd16(h)) {
+    if (which == LBM_FIELD_WDOT && h->esize_d == 0) {
+        // leapfrog storage: w_{n-1} = w_n - dt wdot_n, against the current w
+        const float *conv = static_cast<const float *>(src);
+        if (!src_on_device) {
+            LBM_CUDA(cudaMemcpyAsync(h->staging, src, (size_t)h->grid.nx * h->grid.ny * 4, cudaMemcpyHostToDevice, h->stream));
+            conv = h->staging;
+        }
+        LBM_CUDA(launch_lf_set_wdot(static_cast<const float *>(h->w[h->parity]), static_cast<float *>(h->w[h->parity ^ 1]),
+                                    h->pitch, h->grid.nx, h->grid.ny, (float)h->grid.dt, conv, h->stream));
+    } else if (which == LBM_FIELD_WDOT && wd16(h)) {
         const float *conv = static_cast<const float *>(src);
         if (!src_on_device) {
             LBM_CUDA(cudaMemcpyAsync(h->staging, src, (size_t)h->grid.nx * h->grid.ny * 4, cudaMemcpyHostToDevice, h->stream));
@@ -1231,7 +1255,7 @@ lbm_status lbm_reset(lbm_handle *h)
     const size_t mask = (size_t)h->grid.ny * (size_t)h->words * 4;
     LBM_CUDA(cudaMemsetAsync(h->wbase[0], 0, h->plane_bytes, s));
     LBM_CUDA(cudaMemsetAsync(h->wbase[1], 0, h->plane_bytes, s));
-    LBM_CUDA(cudaMemsetAsync(h->wdbase, 0, h->plane_d_bytes, s));
+    if (h->plane_d_bytes) LBM_CUDA(cudaMemsetAsync(h->wdbase, 0, h->plane_d_bytes, s));
     LBM_CUDA(cudaMemsetAsync(h->cut_h, 0, mask, s));
     LBM_CUDA(cudaMemsetAsync(h->cut_v - h->words, 0, mask + (size_t)h->words * 4, s));   // with the row below row 0
     if (h->line) {
@@ -1652,7 +1676,8 @@ void ckpt_header(const lbm_handle *h, CkptHeader &c)
     }
     c.pitch = h->pitch;
     c.plane_bytes = (int64_t)h->plane_bytes;
-    c.plane_d_bytes = (int64_t)h->plane_d_bytes;
+    // leapfrog storage: the second plane is w_{n-1}
+    c.plane_d_bytes = (int64_t)(h->esize_d ? h->plane_d_bytes : h->plane_bytes);
     c.mask_bytes = (int64_t)h->grid.ny * h->words * 4;
     c.hist_cap = h->cp.mode != CRACK_NONE ? h->cp.hist_cap : 1;
     c.hist_cap_l = h->cp.two_tips ? c.hist_cap : 1;
@@ -1674,7 +1699,7 @@ std::vector<std::pair<void *, size_t>> ckpt_buffers(lbm_handle *h, const CkptHea
 {
     const History &H = h->hist;
     return {{h->wbase[h->parity], (size_t)c.plane_bytes},
-            {h->wdbase, (size_t)c.plane_d_bytes},
+            {h->esize_d ? h->wdbase : h->wbase[h->parity ^ 1], (size_t)c.plane_d_bytes},
             {h->cut_h, (size_t)c.mask_bytes},
             {h->cut_v - h->words, (size_t)c.mask_bytes + (size_t)c.words * 4},   // with the row below row 0
             {h->st + h->parity, sizeof(CrackState)},
@@ -1858,6 +1883,7 @@ cudaError_t enqueue_batch_persistent(const lbm_batch *b, int par, int64_t n, cud
     case LBM_F32: return enqueue_batch_persistent_t<float, float>(b, par, n, s);
     case LBM_F32_WD_BF16: return enqueue_batch_persistent_t<float, __nv_bfloat16>(b, par, n, s);
     case LBM_F32_WD_F16: return enqueue_batch_persistent_t<float, __half>(b, par, n, s);
+    case LBM_F32_LEAPFROG: return enqueue_batch_persistent_t<float, Lf>(b, par, n, s);
     default: return enqueue_batch_persistent_t<double, double>(b, par, n, s);
     }
 }
@@ -1877,6 +1903,7 @@ cudaError_t enqueue_batch_step(const lbm_batch *b, int par, cudaStream_t s)
     case LBM_F32: return enqueue_batch_step_t<float, float>(b, par, s);
     case LBM_F32_WD_BF16: return enqueue_batch_step_t<float, __nv_bfloat16>(b, par, s);
     case LBM_F32_WD_F16: return enqueue_batch_step_t<float, __half>(b, par, s);
+    case LBM_F32_LEAPFROG: return enqueue_batch_step_t<float, Lf>(b, par, s);
     default: return enqueue_batch_step_t<double, double>(b, par, s);
     }
 }
@@ -1938,6 +1965,7 @@ lbm_status batch_build(lbm_batch *b, int threads, int rows)
     case LBM_F32: fill_descs<float, float>(b, descs); edge_units<float, float>(b, eunits); break;
     case LBM_F32_WD_BF16: fill_descs<float, __nv_bfloat16>(b, descs); edge_units<float, __nv_bfloat16>(b, eunits); break;
     case LBM_F32_WD_F16: fill_descs<float, __half>(b, descs); edge_units<float, __half>(b, eunits); break;
+    case LBM_F32_LEAPFROG: fill_descs<float, Lf>(b, descs); edge_units<float, Lf>(b, eunits); break;
     default: fill_descs<double, double>(b, descs); edge_units<double, double>(b, eunits); break;
     }
     const size_t o_units = align256(descs.size());

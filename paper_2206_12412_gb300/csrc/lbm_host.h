@@ -9,6 +9,7 @@
 typedef struct lbm_batch lbm_batch;
 
 #include <string>
+#include <type_traits>
 #include <vector>
 
 using lbm::Unit;
@@ -117,7 +118,10 @@ inline void make_step_args(const lbm_handle *h, int par, StepArgs<T, D> &a)
 {
     a.w_in = static_cast<const T *>(h->w[par]);
     a.w_out = static_cast<T *>(h->w[par ^ 1]);
-    a.wd = static_cast<D *>(h->wd);
+    if constexpr (std::is_same<D, lbm::Lf>::value)
+        a.wd = reinterpret_cast<D *>(a.w_out);   // leapfrog: w_{n-1}, overwritten by the step
+    else
+        a.wd = static_cast<D *>(h->wd);
     a.wd_scale = (T)h->wd_scale;
     a.wd_inv = (T)(1.0 / h->wd_scale);
     a.pitch = h->pitch;

@@ -46,6 +46,12 @@ enum { LOAD_ZERO = 0, LOAD_LINEAR = 1, LOAD_SIN2 = 2, LOAD_HALFSINE = 3, LOAD_SE
 enum { FLAG_CLAMPED = 1, FLAG_UNSUPPORTED = 2, FLAG_NONFINITE = 4 };
 enum { ERR_NONFINITE = 1, ERR_TIMEOUT = 2 };
 
+// The "wdot" element type of leapfrog storage (LBM_F32_LEAPFROG): the plane it
+// names is the previous w, i.e. the step's output buffer (see WdIO<Lf>).
+struct Lf {
+    float v;
+};
+
 template <typename T> struct Pad { static constexpr int kElems = 128 / (int)sizeof(T); };
 template <typename T> struct Vec { static constexpr int N = 16 / (int)sizeof(T); };
 
@@ -245,6 +251,12 @@ template <typename T>
 cudaError_t launch_adjoint_out(const T *a, const T *m, int64_t pitch, int nx, int ny, T dt, T *dw, T *dwd, cudaStream_t s);
 template <typename D>
 cudaError_t launch_wd_to_f32(const D *wd, int64_t pitch, int nx, int ny, float scale, float *dst, cudaStream_t s);
+// Leapfrog storage: wdot_n = (w_n - w_{n-1}) / dt into a dense array, and
+// w_{n-1} = w_n - dt wdot_n from one.
+cudaError_t launch_lf_wdot(const float *w, const float *wprev, int64_t pitch, int nx, int ny, float dt, float *dst,
+                           cudaStream_t s);
+cudaError_t launch_lf_set_wdot(const float *w, float *wprev, int64_t pitch, int nx, int ny, float dt, const float *src,
+                               cudaStream_t s);
 template <typename D>
 cudaError_t launch_wd_from_f32(D *wd, int64_t pitch, int nx, int ny, float scale, const float *src, cudaStream_t s);
 template <typename T> cudaError_t launch_finalize(const FinalizeArgs<T> &a, cudaStream_t s);

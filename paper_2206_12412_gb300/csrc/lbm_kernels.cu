@@ -223,8 +223,7 @@ __device__ __forceinline__ void march(const StepArgs<T, D> &a, int cb, int j0, i
                 const T wl = k == 0 ? left0 : wc.v[k - 1];
                 const T wr = k == N - 1 ? rightN : wc.v[k + 1];
                 const T lap = ((wa.v[k] + wb.v[k]) + (wl + wr)) - (T)4 * wc.v[k];
-                wdnew.v[k] = wdv.v[k] + g * lap;
-                wnew.v[k] = wc.v[k] + dt * wdnew.v[k];
+                site_update<T, D>(wc.v[k], wdv.v[k], lap, g, dt, wnew.v[k], wdnew.v[k]);
             }
             stg_row(wout + (int64_t)j * P, wnew);
             WdIO<D>::store(wdp + (int64_t)j * P, wdnew, wd_scale);
@@ -322,8 +321,7 @@ __device__ __forceinline__ void march_bulk(const StepArgs<T, D> &a, int cb, int 
                 const T wl = k == 0 ? left0 : wc.v[k - 1];
                 const T wr = k == N - 1 ? rightN : wc.v[k + 1];
                 const T lap = ((wa.v[k] + wb.v[k]) + (wl + wr)) - (T)4 * wc.v[k];
-                wdnew.v[k] = wdv.v[k] + g * lap;
-                wnew.v[k] = wc.v[k] + dt * wdnew.v[k];
+                site_update<T, D>(wc.v[k], wdv.v[k], lap, g, dt, wnew.v[k], wdnew.v[k]);
             }
             const int64_t o = (int64_t)(j0 + q) * P;
             stg_row(wout + o, wnew);
@@ -786,6 +784,40 @@ cudaError_t launch_wd_from_f32(D *wd, int64_t pitch, int nx, int ny, float scale
     return cudaGetLastError();
 }
 
+// --------------------------------------------- leapfrog storage: wdot
+
+__global__ void lf_wdot_kernel(const float *w, const float *wprev, int64_t P, int nx, int ny, float dt, float *dst)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nx * ny) return;
+    const int64_t o = (t / nx) * P + t % nx;
+    dst[t] = (w[o] - wprev[o]) / dt;
+}
+
+__global__ void lf_set_wdot_kernel(const float *w, float *wprev, int64_t P, int nx, int ny, float dt, const float *src)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nx * ny) return;
+    const int64_t o = (t / nx) * P + t % nx;
+    wprev[o] = w[o] - dt * src[t];
+}
+
+cudaError_t launch_lf_wdot(const float *w, const float *wprev, int64_t pitch, int nx, int ny, float dt, float *dst,
+                           cudaStream_t s)
+{
+    const int64_t n = (int64_t)nx * ny;
+    lf_wdot_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w, wprev, pitch, nx, ny, dt, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lf_set_wdot(const float *w, float *wprev, int64_t pitch, int nx, int ny, float dt, const float *src,
+                               cudaStream_t s)
+{
+    const int64_t n = (int64_t)nx * ny;
+    lf_set_wdot_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w, wprev, pitch, nx, ny, dt, src);
+    return cudaGetLastError();
+}
+
 // ----------------------------------------------------- pending crack step
 
 // The crack step that follows the last enqueued LBM step, applied in place
@@ -1109,6 +1141,13 @@ template cudaError_t launch_edge_rule<double, double>(const StepArgs<double, dou
 template cudaError_t launch_edge_rule<float, float>(const StepArgs<float, float> &, cudaStream_t);
 template cudaError_t launch_edge_rule<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> &, cudaStream_t);
 template cudaError_t launch_edge_rule<float, __half>(const StepArgs<float, __half> &, cudaStream_t);
+template const void *step_kernel_ptr<float, Lf>(bool);
+template cudaError_t launch_step<float, Lf>(const StepArgs<float, Lf> &, int, cudaStream_t, bool);
+template cudaError_t launch_batch_step<float, Lf>(const StepArgs<float, Lf> *, const BatchUnit *, int, int, cudaStream_t, int);
+template cudaError_t launch_batch_persistent<float, Lf>(const StepArgs<float, Lf> *, int, const BatchUnit *, int, const BatchUnit *, int, int, int64_t, GridBarrier *, uint32_t *, long long, int, cudaStream_t);
+template int edge_rule_count<float, Lf>(const StepArgs<float, Lf> &);
+template cudaError_t launch_batch_edge_rule<float, Lf>(const StepArgs<float, Lf> *, const BatchUnit *, int, int, cudaStream_t);
+template cudaError_t launch_edge_rule<float, Lf>(const StepArgs<float, Lf> &, cudaStream_t);
 template cudaError_t launch_fill_pads<float>(float *, int64_t, int, int, const int32_t *, cudaStream_t);
 template cudaError_t launch_fill_pads<double>(double *, int64_t, int, int, const int32_t *, cudaStream_t);
 

@@ -805,8 +805,9 @@ __global__ void __launch_bounds__(256) line_faces_chunk_kernel(const StepArgs<T,
     T *base = val + n;                                 // [n]
     T *aself = base + n;                               // [n]
     T *ac = aself + n;                                 // [8 n] weights of the coupled corners
-    int16_t *kc = reinterpret_cast<int16_t *>(ac + 8 * n);   // [8 n] their items (-1: unused)
-    uint8_t *act = reinterpret_cast<uint8_t *>(kc + 8 * n);  // [n]
+    int32_t *site = reinterpret_cast<int32_t *>(ac + 8 * n);  // [2 n] the item's (i, j)
+    int16_t *kc = reinterpret_cast<int16_t *>(site + 2 * n);  // [8 n] coupled corners' items (-1: unused)
+    uint8_t *act = reinterpret_cast<uint8_t *>(kc + 8 * n);   // [n] point (bit 0), own (bit 1), dropped (bit 2)
     for (int l = tid; l < n; l += nt) {
         // the whole record and w at all its corners first (unused corners name
         // the site itself), so the loads go out together rather than one
@@ -816,13 +817,16 @@ __global__ void __launch_bounds__(256) line_faces_chunk_kernel(const StepArgs<T,
         T wk[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) wk[k] = a.w_out[(int64_t)f.cj[k] * P + f.ci[k]];
-        act[l] = face_is_point(a, f.i, f.j);
+        act[l] = (face_is_point(a, f.i, f.j) ? 1 : 0) | (it.f >= C.own_lo && it.f < C.own_hi ? 2 : 0) |
+                 ((f.flags & FACE_DROPPED) ? 4 : 0);
+        site[2 * l] = f.i;
+        site[2 * l + 1] = f.j;
         val[l] = a.w_out[(int64_t)f.j * P + f.i];
         T b = (T)0, s = (T)0;
         int q = 0;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            const T ak = (T)f.a[k];
+            const T ak = sizeof(T) == 4 ? (T)f.af[k] : (T)f.a[k];
             if (ak == (T)0) continue;
             const int m = it.kl[k];
             if (m == l) {
@@ -846,7 +850,7 @@ __global__ void __launch_bounds__(256) line_faces_chunk_kernel(const StepArgs<T,
         if (lo >= n) break;       // no item of this level or above
         if (lo == hi) continue;   // the same for every thread of the CTA
         for (int l = lo + tid; l < hi; l += nt) {
-            if (!act[l]) continue;
+            if (!(act[l] & 1)) continue;
             T v = base[l];
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
@@ -870,16 +874,15 @@ __global__ void __launch_bounds__(256) line_faces_chunk_kernel(const StepArgs<T,
     const T inv_dt = (T)1 / a.dt;
     bool bad = false, drop = false;
     for (int l = tid; l < n; l += nt) {
-        const int c = I[C.off + l].f;
-        if (!act[l] || c < C.own_lo || c >= C.own_hi) continue;
-        const LineFace &f = F[c];
-        const int64_t o = (int64_t)f.j * P + f.i;
+        if ((act[l] & 3) != 3) continue;   // own points only
+        const int i = site[2 * l], j = site[2 * l + 1];
+        const int64_t o = (int64_t)j * P + i;
         const T wB = val[l];
         a.w_out[o] = wB;
         WdIO<D>::put(a.wd + o, (wB - a.w_in[o]) * inv_dt, a.wd_scale);
-        site_pads(a, f.i, f.j, wB);
+        site_pads(a, i, j, wB);
         bad |= !isfinite(wB);
-        drop |= (f.flags & FACE_DROPPED) != 0;
+        drop |= (act[l] & 4) != 0;
     }
     if (bad) atomicOr(a.err, (uint32_t)ERR_NONFINITE);
     if (__syncthreads_or(drop || stuck) && tid == 0) face_unsupported(a);
@@ -1035,8 +1038,8 @@ cudaError_t launch_line_faces_chunked(const StepArgs<T, D> &a, const LineFace *f
                                       int n_chunks, const FaceItem *items, cudaStream_t s)
 {
     if (n_chunks <= 0) return cudaSuccess;
-    // shared memory for kFaceItemsMax items: 11 T and 8 int16 and one byte each
-    const size_t smem = (size_t)kFaceItemsMax * (11 * sizeof(T) + 8 * sizeof(int16_t) + 1);
+    // shared memory for kFaceItemsMax items: 11 T, 2 int32, 8 int16 and one byte each
+    const size_t smem = (size_t)kFaceItemsMax * (11 * sizeof(T) + 2 * sizeof(int32_t) + 8 * sizeof(int16_t) + 1);
     cudaError_t e = cudaFuncSetAttribute(line_faces_chunk_kernel<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;

@@ -26,6 +26,7 @@ struct LineFace {
     int32_t ci[8], cj[8], cand[8];
     int32_t flags, pad;
     double a[8];
+    float af[8];     // the weights rounded to FP32 (the FP32 solve: no FP64 conversion on the GPU)
 };
 enum { FACE_DROPPED = 1 };
 

@@ -92,3 +92,46 @@ def test_fp16_overflow_is_reported(gpu):
     with pytest.raises(gpu.LbmError) as ei:
         g.sync()
     assert ei.value.status == -4
+
+
+# ------------------ the mixed-precision configuration's crop-equivalent run
+
+C5_STEPS = 3000
+C5_BOUNDS = {"f32": (5e-5, 5e-5), "f32_lf": (5e-5, 5e-5), "f32_f16": (3e-3, 3e-3), "f32_bf16": (3e-2, 3e-2)}
+
+
+@pytest.fixture(scope="module")
+def c5_oracle(oracle_mod):
+    """The FP64 oracle on the 1024 x 1024 crop-equivalent of the 16384 x 16384
+    mixed-precision workload (crack from 0 to 128 on the midline growing at
+    v = 0.5 c_s, +-1e-3 ramped over 2000 steps, macroscopic crack faces),
+    3000 steps (the tip reaches 878), on all host cores."""
+    import os
+    p = W.large_prescribed(1024)
+    o = oracle_mod.Oracle(p, threads=len(os.sched_getaffinity(0)))
+    o.step(C5_STEPS)
+    w, _ = o.fields()
+    h = o.history()
+    ch, cv = o.cuts()
+    o.close()
+    return p, w, h, cv
+
+
+@pytest.mark.parametrize("storage", ["f32", "f32_lf", "f32_f16", "f32_bf16"])
+def test_c5_crop_equivalent_error_vs_oracle(c5_oracle, gpu, storage):
+    """Every FP32-w storage form against the FP64 oracle on that run: the
+    relative max-norm of w at the end and of K(t) over all 3000 steps; the
+    prescribed tips and the severed links exact.  Prints the figures."""
+    p, wo, ho, cvo = c5_oracle
+    g = gpu.Lattice(p, storage)
+    g.step(C5_STEPS)
+    w, _ = g.fields()
+    hg = g.history()
+    ew = rel(w, wo)
+    ek = np.abs(hg["K"] - ho["K"]).max() / np.abs(ho["K"]).max()
+    print(f"\nC5 crop-equivalent 1024^2, {C5_STEPS} steps, {storage}: w rel max-norm {ew:.3e}, K(t) {ek:.3e}")
+    bw, bk = C5_BOUNDS[storage]
+    assert ew < bw and ek < bk
+    np.testing.assert_array_equal(hg["tip_q"], ho["tip_q"])
+    np.testing.assert_array_equal(g.cut_mask("v"), cvo.astype(bool))
+    g.close()
