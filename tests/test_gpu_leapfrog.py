@@ -146,8 +146,9 @@ def test_wdot_is_formed_from_the_two_planes(gpu):
     g.set_fields(w, wd)
     w2, wd2 = g.fields()
     np.testing.assert_array_equal(w2, w)
-    # wdot = (w - (w - dt wdot)) / dt: exact up to the rounding of w - dt wdot
-    assert np.all(np.abs(wd2 - wd) <= np.abs(w) * 2.0 ** -23 + 1e-30)
+    # wdot = (w - (w - dt wdot)) / dt (dt = 1): the two roundings, of w - dt wdot
+    # and of the difference, each at most half an ulp of |w| + |dt wdot|
+    assert np.all(np.abs(wd2 - wd) <= 2.0 ** -23 * (np.abs(w) + np.abs(wd)) + 1e-30)
 
 
 def test_rejected_where_not_built(gpu):
