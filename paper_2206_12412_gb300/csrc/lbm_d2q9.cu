@@ -64,11 +64,14 @@ __device__ __forceinline__ T leaving(const int32_t *edge, const TwoWs<T> &two_ws
 // false) take the bare update unless they are the bottom or top row or a
 // crack row; the others substitute the value each missing or severed link
 // streams back.
-template <typename T>
+// SPECIAL = false: a warp away from the left and right edges in a band that
+// holds no edge row, no crack row and no row beyond a periodic edge (its
+// rows are all bare updates): compiled without the periodic remapping, the
+// corner column loads and the per-row checks.
+template <typename T, bool SPECIAL = true>
 __device__ __forceinline__ T march9(const StepArgs<T, T> &a, int x0, int j0, int j1, int64_t lq, int64_t rq,
                                     const TwoWs<T> &two_ws, bool edge_warp)
 {
-    constexpr bool SPECIAL = true;
     constexpr int N = Vec<T>::N;
     typedef Row<T, N> R;
     const unsigned kFull = 0xffffffffu;
@@ -82,6 +85,7 @@ __device__ __forceinline__ T march9(const StepArgs<T, T> &a, int x0, int j0, int
     const T *wbase = a.w_in;
     const int hl_col = (SPECIAL && x0 == 0 && per_x) ? nx - 1 : x0 - 1;
     const T ga = a.g * (T)(2.0 / 3.0), gd = a.g * (T)(1.0 / 6.0), dt = a.dt;
+    const T c0 = a.g * (T)(-10.0 / 3.0);   // -4 (2/3 + 1/6) g: the site's own weight
 
     // issue the loads of a row: the vector, the halo column of lanes 0 / 31
     // (l, rt) and the east neighbour of column nx - 1 across a periodic edge (z)
@@ -119,8 +123,30 @@ __device__ __forceinline__ T march9(const StepArgs<T, T> &a, int x0, int j0, int
             ld_row(a.wd + x0 + (int64_t)(j + 1) * P, wdn);
         }
         R wnew, wdnew;
-        const bool crow = crack && (j == jc - 1 || j == jc);
-        if (!crow && j != 0 && j != ny - 1) {
+        const bool crow = SPECIAL && crack && (j == jc - 1 || j == jc);
+        if (!SPECIAL) {
+            // the bare update from the column sums of the rows above and
+            // below, s_k = w_a + w_b: the axis sum is s_k + (w_W + w_E), the
+            // diagonal sum s_{k-1} + s_{k+1}, and the weights are folded in:
+            // wdot' = wdot - (10/3) g w + (2/3) g axis + (1/6) g diagonal
+            T sc[N + 2];
+            sc[0] = la + lb;
+#pragma unroll
+            for (int k = 0; k < N; ++k) sc[k + 1] = wa.v[k] + wb.v[k];
+            sc[N + 1] = ra + rb;
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                const T wl = k == 0 ? lc : wc.v[k - 1], wr = k == N - 1 ? rc : wc.v[k + 1];
+                T d = wdv.v[k] + c0 * wc.v[k];
+                d += ga * (sc[k + 1] + (wl + wr));
+                d += gd * (sc[k] + sc[k + 2]);
+                wdnew.v[k] = d;
+                wnew.v[k] = wc.v[k] + dt * d;
+            }
+            stg_row(a.w_out + x0 + (int64_t)j * P, wnew);
+            stg_row(a.wd + x0 + (int64_t)j * P, wdnew);
+            acc += wnew.v[0];
+        } else if (!crow && j != 0 && j != ny - 1) {
 #pragma unroll
             for (int k = 0; k < N; ++k) {
                 const T wl = k == 0 ? lc : wc.v[k - 1], wr = k == N - 1 ? rc : wc.v[k + 1];
@@ -327,8 +353,16 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
     }
     const TwoWs<T> two_ws{(T)2 * (T)a.s_in->wstar[LEFT], (T)2 * (T)a.s_in->wstar[RIGHT],
                           (T)2 * (T)a.s_in->wstar[BOTTOM], (T)2 * (T)a.s_in->wstar[TOP]};
-    // warps wholly right of the lattice have nothing to load or store
-    const T acc = xw0 < nx ? march9<T>(a, x0, j0, j1, lq, rq, two_ws, edge_warp) : (T)0;
+    // warps wholly right of the lattice have nothing to load or store; a warp
+    // away from the left / right edges in a band of bare rows takes the
+    // march compiled without the edge and crack handling
+    const bool per_y = a.edge[BOTTOM] == EDGE_PERIODIC;
+    const bool bare_band = j0 > 0 && j1 < ny && !(crack && j0 <= jc && j1 >= jc - 1) && !per_y;
+    T acc = (T)0;
+    if (xw0 < nx) {
+        if (!edge_warp && bare_band) acc = march9<T, false>(a, x0, j0, j1, lq, rq, two_ws, false);
+        else acc = march9<T, true>(a, x0, j0, j1, lq, rq, two_ws, edge_warp);
+    }
     // a non-finite w (or wdot, which enters w) turns the sum of the first
     // element of each vector non-finite within a step or two
     if (__any_sync(0xffffffffu, !isfinite(acc)) && lane == 0) atomicOr(a.err, (uint32_t)ERR_NONFINITE);
