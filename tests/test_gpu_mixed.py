@@ -97,7 +97,9 @@ def test_fp16_overflow_is_reported(gpu):
 # ------------------ the mixed-precision configuration's crop-equivalent run
 
 C5_STEPS = 3000
-C5_BOUNDS = {"f32": (5e-5, 5e-5), "f32_lf": (5e-5, 5e-5), "f32_f16": (3e-3, 3e-3), "f32_bf16": (3e-2, 3e-2)}
+# measured (GB300): w 1.52e-5 / K 6.47e-5 (f32), 1.32e-5 / 5.92e-5 (leapfrog),
+# 1.27e-4 / 5.15e-4 (FP16 wdot), 1.64e-3 / 1.02e-2 (BF16 wdot); bounds about 3x
+C5_BOUNDS = {"f32": (5e-5, 2e-4), "f32_lf": (5e-5, 2e-4), "f32_f16": (4e-4, 1.5e-3), "f32_bf16": (5e-3, 3e-2)}
 
 
 @pytest.fixture(scope="module")
