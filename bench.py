@@ -302,10 +302,12 @@ def profile_batched(lbm, W, torch, stream, steps, shape, count=256):
     return {"shape": list(shape), "steps": steps, "glups": r4(sites * steps / secs / 1e9)}
 
 
-def measure_batched(lbm, W, torch, stream, steps, peak, count=256):
+def measure_batched(lbm, W, torch, stream, steps, peak, count=256, full_steps=None):
     """Batched form: 256 independent lattices of uneven sizes, one launch per
     step (graph replay), against the same lattices stepped one after another
-    with the single-lattice path.  The 840 MB of state exceed L2."""
+    with the single-lattice path.  The 840 MB of state exceed L2.  With
+    full_steps, the tuned batch then runs the configuration's whole length
+    (20 000 steps) as one timed run."""
     problems = W.batch_problems(count, seed=3)
     sites = sum(p["nx"] * p["ny"] for p in problems)
     lats = [lbm.Lattice(p, "f32", stream=stream) for p in problems]
@@ -316,6 +318,12 @@ def measure_batched(lbm, W, torch, stream, steps, peak, count=256):
     batch.step(64)
     t_b = timed(torch, stream, lambda: batch.step(steps))
     info = batch.info()
+    full = None
+    if full_steps:
+        for l in lats:
+            l.reset()
+        t_f = timed(torch, stream, lambda: batch.step(full_steps))
+        full = {"steps": full_steps, "s": r4(t_f), "glups": r4(sites * full_steps / t_f / 1e9)}
     # the same shape as one persistent cooperative launch (grid barrier between steps)
     batch.set_persistent(True)
     batch.step(8)
@@ -330,7 +338,8 @@ def measure_batched(lbm, W, torch, stream, steps, peak, count=256):
             "shape": [info["threads"], info["band_rows"]], "glups_default_shape": r4(sites * steps / t_d / 1e9),
             "glups_persistent": r4(sites * steps / t_p / 1e9),
             "glups_sequential": r4(sites * steps / t_s / 1e9), "speedup": r4(t_s / t_b),
-            "glups": r4(sites * steps / t_b / 1e9), "frac": r4(16 * sites * steps / t_b / 1e9 / peak)}
+            "glups": r4(sites * steps / t_b / 1e9), "frac": r4(16 * sites * steps / t_b / 1e9 / peak),
+            "full_run": full}
 
 
 def measure_adjoint(lbm, W, torch, stream, n_steps=None):
@@ -692,7 +701,7 @@ def run_ours(args, rank, world, local):
     if not args.no_adjoint:
         patterns["adjoint"] = measure_adjoint(lbm, W, torch, stream)
     if not args.no_batched:
-        patterns["batched"] = measure_batched(lbm, W, torch, stream, 128, peak)
+        patterns["batched"] = measure_batched(lbm, W, torch, stream, 128, peak, full_steps=W.BATCH_STEPS)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

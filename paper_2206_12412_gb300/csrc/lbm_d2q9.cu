@@ -85,7 +85,6 @@ __device__ __forceinline__ T march9(const StepArgs<T, T> &a, int x0, int j0, int
     const T *wbase = a.w_in;
     const int hl_col = (SPECIAL && x0 == 0 && per_x) ? nx - 1 : x0 - 1;
     const T ga = a.g * (T)(2.0 / 3.0), gd = a.g * (T)(1.0 / 6.0), dt = a.dt;
-    const T c0 = a.g * (T)(-10.0 / 3.0);   // -4 (2/3 + 1/6) g: the site's own weight
 
     // issue the loads of a row: the vector, the halo column of lanes 0 / 31
     // (l, rt) and the east neighbour of column nx - 1 across a periodic edge (z)
@@ -126,9 +125,10 @@ __device__ __forceinline__ T march9(const StepArgs<T, T> &a, int x0, int j0, int
         const bool crow = SPECIAL && crack && (j == jc - 1 || j == jc);
         if (!SPECIAL) {
             // the bare update from the column sums of the rows above and
-            // below, s_k = w_a + w_b: the axis sum is s_k + (w_W + w_E), the
-            // diagonal sum s_{k-1} + s_{k+1}, and the weights are folded in:
-            // wdot' = wdot - (10/3) g w + (2/3) g axis + (1/6) g diagonal
+            // below, s_k = w_a + w_b, each formed once: the axis sum is
+            // s_k + (w_W + w_E) (as in the general path), the diagonal sum
+            // s_{k-1} + s_{k+1}; each difference with 4 w is taken before the
+            // weights, so the rounding stays at the scale of the Laplacians
             T sc[N + 2];
             sc[0] = la + lb;
 #pragma unroll
@@ -137,11 +137,10 @@ __device__ __forceinline__ T march9(const StepArgs<T, T> &a, int x0, int j0, int
 #pragma unroll
             for (int k = 0; k < N; ++k) {
                 const T wl = k == 0 ? lc : wc.v[k - 1], wr = k == N - 1 ? rc : wc.v[k + 1];
-                T d = wdv.v[k] + c0 * wc.v[k];
-                d += ga * (sc[k + 1] + (wl + wr));
-                d += gd * (sc[k] + sc[k + 2]);
-                wdnew.v[k] = d;
-                wnew.v[k] = wc.v[k] + dt * d;
+                const T axis = (sc[k + 1] + (wl + wr)) - (T)4 * wc.v[k];
+                const T diag = (sc[k] + sc[k + 2]) - (T)4 * wc.v[k];
+                wdnew.v[k] = wdv.v[k] + (ga * axis + gd * diag);
+                wnew.v[k] = wc.v[k] + dt * wdnew.v[k];
             }
             stg_row(a.w_out + x0 + (int64_t)j * P, wnew);
             stg_row(a.wd + x0 + (int64_t)j * P, wdnew);
