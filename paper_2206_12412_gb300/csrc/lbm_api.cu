@@ -1057,6 +1057,9 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
         }
     }
     cp.hist_cap = cr.mode != LBM_CRACK_NONE ? cr.hist_cap : 0;
+    // ((v c_s) dt / dh) 2^32, rounded to nearest (even): the crack step's own
+    // expression for the advance, formed once
+    cp.dq_prescribed = cr.mode == LBM_CRACK_PRESCRIBED ? llrint(cr.v_rel * cs * grid->dt / grid->dh * 4294967296.0) : 0;
 
     h->wd_scale = lattice->storage == LBM_F32_WD_F16 ? fp16_wd_scale(grid, loads, n_loads) : 1.0;
 

@@ -68,8 +68,12 @@ __device__ __forceinline__ CrackSums crack_eval_warp(const CrackParams &p, const
     const TipState &E = dir > 0 ? S.r : S.l;
     const int64_t tip = E.tip_q;
     const int i_first = S.i_first, i_last = S.i_last;
-    const double r_min = p.r_min_fixed > 0.0 ? p.r_min_fixed : p.r0 / (1.0 - E.v_prev);   // eq. r(v)
-    const double lo = r_min / p.dh, hi = (r_min + p.fit_width) / p.dh;
+    // eq. r(v); the divisions are skipped where they are exact (v = 0, dh = 1):
+    // FP64 instructions are few per cycle on GB300, and this chain is on
+    // the crack step's critical path
+    const double r_min = p.r_min_fixed > 0.0 ? p.r_min_fixed : (E.v_prev == 0.0 ? p.r0 : p.r0 / (1.0 - E.v_prev));
+    const double lo = p.dh == 1.0 ? r_min : r_min / p.dh;
+    const double hi = p.dh == 1.0 ? r_min + p.fit_width : (r_min + p.fit_width) / p.dh;
     const double tip_h = (double)tip * kTwoM32;
     int c_lo, c_hi;
     if (dir > 0) {
@@ -94,12 +98,24 @@ __device__ __forceinline__ CrackSums crack_eval_warp(const CrackParams &p, const
         const int64_t xq = (int64_t)(2 * i + 1) << (kQBits - 1);
         const double r_h = (double)(dir > 0 ? tip - xq : xq - tip) * kTwoM32;
         if (!(r_h >= lo && r_h < hi)) continue;
-        const double r = r_h * p.dh;
+        const double r = p.dh == 1.0 ? r_h : r_h * p.dh;
         const double sf = sqrt(r / (2.0 * kPi));
         const double delta = (double)above - (double)below;
         num += delta * sf;
         den += sf * sf;
         ++np;
+    }
+    // with the pairs in one lane of the group (the one-pair window W = dh
+    // always), that lane's sums are the group's: adding the other lanes'
+    // zeros cannot change them, so one shuffle replaces the reduction tree
+    const unsigned gmask = G == 32 ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
+    const unsigned holders = __ballot_sync(0xffffffffu, np > 0) & gmask;
+    if (__popc(holders) <= 1) {
+        const int src = holders ? __ffs(holders) - 1 : (threadIdx.x & 31 & ~(G - 1));
+        num = __shfl_sync(0xffffffffu, num, src);
+        den = __shfl_sync(0xffffffffu, den, src);
+        np = __shfl_sync(0xffffffffu, np, src);
+        return CrackSums{num, den, r_min, np};
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) {
@@ -141,8 +157,14 @@ __device__ __forceinline__ void crack_apply(const CrackParams &p, uint32_t *cut_
     const int jr = p.jc - 1;
     const int64_t half = (int64_t)1 << (kQBits - 1);
     if (propagate) {
-        const double adot = v * p.cs;
-        const int64_t dq = __double2ll_rn(adot * p.dt / p.dh * 4294967296.0);   // Delta a = adot dt
+        // Delta a = adot dt on the 2^-32 dh grid (prescribed growth: the step
+        // the host formed with the same expression, once)
+        int64_t dq = p.dq_prescribed;
+        if (p.mode != CRACK_PRESCRIBED) {
+            const double adot = v * p.cs;
+            const double a1 = p.dt == 1.0 ? adot : adot * p.dt;
+            dq = __double2ll_rn((p.dh == 1.0 ? a1 : a1 / p.dh) * 4294967296.0);
+        }
         if (dir > 0) {
             int64_t next = tip + dq;
             if (next >= p.clamp_q) { next = p.clamp_q; E.arrested = 1; flags |= FLAG_CLAMPED; }

@@ -101,6 +101,9 @@ struct CrackParams {
     // the crack sub-bands this lattice holds: 1 below the crack line, 2 above
     // (3: both; a row slab whose boundary is the crack line holds one)
     int32_t sides, pad_s;
+    // prescribed growth: the advance v_rel c_s dt on the 2^-32 dh grid,
+    // formed on the host as the crack step would form it
+    int64_t dq_prescribed;
 };
 
 // Per-step records of the right end and (two-tip cracks) the left end; a

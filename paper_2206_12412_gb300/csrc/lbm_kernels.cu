@@ -402,6 +402,16 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
         const bool left_here = p.two_tips && cb == i_prev / cols;
         const bool commit = band == a.crack_band;
         const bool both = BOTH && right_here && left_here;
+        if ((right_here || left_here) && tid == 0) {
+            // the rows this CTA updates after the crack step, brought into L2
+            // while the crack step runs (its FP64 chain is the long pole)
+            const int hh = p.macro ? 3 : 1;
+            const int64_t xb = (int64_t)cb * TH * N;
+            for (int q = -1; q <= hh; ++q)
+                bulk_prefetch_l2(a.w_in + (int64_t)(j0 + q) * a.pitch + xb, (uint32_t)(TH * N * sizeof(T)));
+            for (int q = 0; q < hh; ++q)
+                bulk_prefetch_l2(a.wd + (int64_t)(j0 + q) * a.pitch + xb, (uint32_t)(TH * N * sizeof(D)));
+        }
         if ((right_here || left_here) && tid < 32) {
             if (tid == 0) sS = *a.s_in;
             __syncwarp();
