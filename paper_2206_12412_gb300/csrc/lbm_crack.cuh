@@ -127,24 +127,26 @@ __device__ __forceinline__ CrackSums crack_eval_warp(const CrackParams &p, const
 }
 
 // K from the sums (eq. sif; least squares when the window holds several
-// pairs), then steps (2) and (3) for one end, by one thread: the criterion,
-// the advance, the severed links, this end's fields of S and, if `commit`,
-// its history record.
-__device__ __forceinline__ void crack_apply(const CrackParams &p, uint32_t *cut_v, const History &hist, CrackState &S,
-                                            int dir, bool commit, const CrackSums &c)
+// pairs) and step (2), the criterion, for one end: the FP64 part of the
+// crack step, which reads this end's state only (so the two ends of a
+// two-tip crack can decide at once, in different lanes).
+struct CrackDecision {
+    double K, v;
+    int64_t dq;          // the advance on the 2^-32 dh grid (propagate only)
+    int32_t propagate, flags;
+};
+
+__device__ __forceinline__ CrackDecision crack_decide(const CrackParams &p, const CrackState &S, int dir,
+                                                      const CrackSums &c)
 {
     const double K = c.np > 0 ? p.mu / 4.0 * c.num / c.den : 0.0;
-    const int np = c.np;
-    const double r_min = c.r_min;
-    TipState &E = dir > 0 ? S.r : S.l;
-    const int64_t tip = E.tip_q;
-    const int i_first = S.i_first, i_last = S.i_last;
+    const TipState &E = dir > 0 ? S.r : S.l;
     int propagate = 0;
     double v = 0.0;
     if (p.mode == CRACK_PRESCRIBED) {
         propagate = 1;
         v = p.v_rel;
-    } else if (p.mode == CRACK_KCRIT && np > 0 && fabs(K) > p.K_C) {
+    } else if (p.mode == CRACK_KCRIT && c.np > 0 && fabs(K) > p.K_C) {
         const double ratio = fabs(K) / p.K_C;
         propagate = 1;
         v = p.v_max * tanh(sqrt(ratio * ratio * ratio * ratio - 1.0));   // eq. v-tanh
@@ -152,19 +154,36 @@ __device__ __forceinline__ void crack_apply(const CrackParams &p, uint32_t *cut_
     int32_t flags = E.flags;
     if (!isfinite(K)) flags |= FLAG_NONFINITE;
     if (E.arrested) { propagate = 0; v = 0.0; }
+    // Delta a = adot dt on the 2^-32 dh grid (prescribed growth: the step the
+    // host formed with the same expression, once)
+    int64_t dq = p.dq_prescribed;
+    if (propagate && p.mode != CRACK_PRESCRIBED) {
+        const double adot = v * p.cs;
+        const double a1 = p.dt == 1.0 ? adot : adot * p.dt;
+        dq = __double2ll_rn((p.dh == 1.0 ? a1 : a1 / p.dh) * 4294967296.0);
+    }
+    return CrackDecision{K, v, dq, propagate, flags};
+}
+
+// Step (3) for one end, by one thread: the advance, the severed links, this
+// end's fields of S and, if `commit`, its history record.
+__device__ __forceinline__ void crack_commit(const CrackParams &p, uint32_t *cut_v, const History &hist, CrackState &S,
+                                             int dir, bool commit, const CrackSums &c, const CrackDecision &d)
+{
+    const double K = d.K, v = d.v;
+    const int np = c.np;
+    const double r_min = c.r_min;
+    TipState &E = dir > 0 ? S.r : S.l;
+    const int64_t tip = E.tip_q;
+    const int i_first = S.i_first, i_last = S.i_last;
+    const int propagate = d.propagate;
+    int32_t flags = d.flags;
     int grew = 0;
     int64_t tip_new = tip;
     const int jr = p.jc - 1;
     const int64_t half = (int64_t)1 << (kQBits - 1);
     if (propagate) {
-        // Delta a = adot dt on the 2^-32 dh grid (prescribed growth: the step
-        // the host formed with the same expression, once)
-        int64_t dq = p.dq_prescribed;
-        if (p.mode != CRACK_PRESCRIBED) {
-            const double adot = v * p.cs;
-            const double a1 = p.dt == 1.0 ? adot : adot * p.dt;
-            dq = __double2ll_rn((p.dh == 1.0 ? a1 : a1 / p.dh) * 4294967296.0);
-        }
+        const int64_t dq = d.dq;
         if (dir > 0) {
             int64_t next = tip + dq;
             if (next >= p.clamp_q) { next = p.clamp_q; E.arrested = 1; flags |= FLAG_CLAMPED; }
@@ -218,6 +237,13 @@ __device__ __forceinline__ void crack_apply(const CrackParams &p, uint32_t *cut_
         }
     }
     E.decided = 1;
+}
+
+
+__device__ __forceinline__ void crack_apply(const CrackParams &p, uint32_t *cut_v, const History &hist, CrackState &S,
+                                            int dir, bool commit, const CrackSums &c)
+{
+    crack_commit(p, cut_v, hist, S, dir, commit, c, crack_decide(p, S, dir, c));
 }
 
 // Both steps for one end, by one warp (lane 0 applies).

@@ -129,6 +129,8 @@ inline void make_step_args(const lbm_handle *h, int par, StepArgs<T, D> &a)
     a.ny = h->grid.ny;
     a.ncb = h->ncb;
     a.crack_band = h->crack_band;
+    a.n_bands = h->n_bands;
+    a.pad_nb = 0;
     for (int e = 0; e < 4; ++e) { a.edge[e] = h->grid.edge[e]; a.load[e] = h->load[e]; }
     a.g = (T)h->g;
     a.dt = (T)h->grid.dt;

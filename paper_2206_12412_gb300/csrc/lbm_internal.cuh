@@ -133,6 +133,7 @@ struct StepArgs {
     int32_t nx, ny;
     int32_t ncb;               // column blocks of kThreads * 16 bytes
     int32_t crack_band;        // band that holds the crack rows (-1: none)
+    int32_t n_bands, pad_nb;   // bands of the partition
     int32_t edge[4];
     T g, dt;
     uint32_t *cut_h;

@@ -424,14 +424,24 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
                 const bool act_r = p.mode != CRACK_NONE && !sS.r.decided;
                 const bool act_l = p.mode != CRACK_NONE && !sS.l.decided;
                 const CrackSums c = crack_eval_warp<T, 16>(p, a.w_in, a.pitch, a.cut_v, sS, tid < 16 ? +1 : -1);
+                // each end's criterion (the FP64 part) in its half warp's first
+                // lane at once: lane 0 the right end, lane 16 the left end
+                CrackDecision dd = {};
+                if ((tid & 15) == 0) dd = crack_decide(p, sS, tid < 16 ? +1 : -1, c);
                 CrackSums cl;
                 cl.num = __shfl_sync(0xffffffffu, c.num, 16);
                 cl.den = __shfl_sync(0xffffffffu, c.den, 16);
                 cl.r_min = __shfl_sync(0xffffffffu, c.r_min, 16);
                 cl.np = __shfl_sync(0xffffffffu, c.np, 16);
+                CrackDecision dl;
+                dl.K = __shfl_sync(0xffffffffu, dd.K, 16);
+                dl.v = __shfl_sync(0xffffffffu, dd.v, 16);
+                dl.dq = __shfl_sync(0xffffffffu, dd.dq, 16);
+                dl.propagate = __shfl_sync(0xffffffffu, dd.propagate, 16);
+                dl.flags = __shfl_sync(0xffffffffu, dd.flags, 16);
                 if (tid == 0) {
-                    if (act_r) crack_apply(p, a.cut_v, a.hist, sS, +1, commit, c);
-                    if (act_l) crack_apply(p, a.cut_v, a.hist, sS, -1, commit, cl);
+                    if (act_r) crack_commit(p, a.cut_v, a.hist, sS, +1, commit, c, dd);
+                    if (act_l) crack_commit(p, a.cut_v, a.hist, sS, -1, commit, cl, dl);
                     sS.r.decided = 1;
                     sS.l.decided = 1;
                 }
@@ -450,8 +460,12 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
                     if (!p.two_tips) o->i_first = sS.i_first;
                     o->r = sS.r;
                     o->r.decided = 0;
-                    for (int e = 0; e < 4; ++e)
-                        o->wstar[e] = a.edge[e] == EDGE_DIRICHLET ? load_value(a.load[e], n, (double)p.dt) : 0.0;
+                    // the Dirichlet values of the next step come from another
+                    // CTA when there is one (see below): their FP64 sin of the
+                    // sin^2 and half-sine loads stays off this CTA's path
+                    if (a.n_bands <= 2)
+                        for (int e = 0; e < 4; ++e)
+                            o->wstar[e] = a.edge[e] == EDGE_DIRICHLET ? load_value(a.load[e], n, (double)p.dt) : 0.0;
                 }
                 if (left_here) {
                     o->i_first = sS.i_first;
@@ -501,6 +515,15 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
             if (edge) march<T, D, true, TH, COH>(a, cb, j0, j1, acc);
             else march<T, D, false, TH, COH>(a, cb, j0, j1, acc);
         }
+    }
+    // with a crack, the Dirichlet values w*(t_{n+1}) of the next step are
+    // written by the first CTA of the first band that is no crack sub-band
+    // (its own fields of the next state; the writer CTA writes the others)
+    if (a.crack_band >= 0 && a.n_bands > 2 && cb == 0 && tid == 0 &&
+        band == (a.crack_band > 0 ? 0 : a.crack_band + (p.sides == 3 ? 2 : 1))) {
+        const int64_t n = a.s_in->step + 1;
+        for (int e = 0; e < 4; ++e)
+            a.s_out->wstar[e] = a.edge[e] == EDGE_DIRICHLET ? load_value(a.load[e], n, (double)p.dt) : 0.0;
     }
     // a non-finite w (or wdot, which enters w) turns the sum of the first
     // component of each vector non-finite within a step or two
