@@ -486,7 +486,9 @@ lbm_status lbm_batch_info(const lbm_batch *b, int32_t *n_lattices, int32_t *ctas
 /* Launch shape of the batched step: CTAs of `threads` threads (32, 64 or 128;
  * a column block is threads 16-byte vectors wide, i.e. 4 * threads FP32
  * columns) over bands of band_rows >= 1 rows (the crack rows keep bands of
- * their own).  Narrow column blocks leave fewer idle warps right of lattices
+ * their own), or with band_rows = 0 bands as tall as one wave of resident
+ * CTAs allows, about equally tall in every lattice (long marches, few halo
+ * rows, no second wave).  Narrow column blocks leave fewer idle warps right of lattices
  * whose width is not a multiple of 512 columns; short bands give more CTAs.
  * The results do not depend on the shape (each lattice's time step is the
  * same arithmetic).  lbm_batch_set_shape synchronises the stream and
@@ -497,7 +499,8 @@ lbm_status lbm_batch_get_shape(const lbm_batch *b, int32_t *threads, int32_t *ba
 
 /* Autotuner of the batched step's launch shape: times trial_steps (2..1024)
  * batched steps with CUDA events for every shape of threads in {32, 64, 128}
- * x band_rows in {8, 16, 32, 64} (the first of three repetitions a warm-up),
+ * x band_rows in {0 (one wave), 8, 16, 32, 64} (the first of three
+ * repetitions a warm-up),
  * keeps the fastest, and caches it in the process under the device's SM
  * count, the storage and the lattices' sizes and crack rows (a later batch of
  * the same lattices takes the cached shape without trials; *from_cache = 1,

@@ -1911,6 +1911,18 @@ cudaError_t enqueue_batch_step(const lbm_batch *b, int par, cudaStream_t s)
     }
 }
 
+// The batched step kernel for a storage and CTA width (for occupancy queries).
+cudaError_t batch_kernel_ptr(int storage, int threads, const void **fn)
+{
+    switch (storage) {
+    case LBM_F32: return batch_step_kernel_ptr<float, float>(threads, fn);
+    case LBM_F32_WD_BF16: return batch_step_kernel_ptr<float, __nv_bfloat16>(threads, fn);
+    case LBM_F32_WD_F16: return batch_step_kernel_ptr<float, __half>(threads, fn);
+    case LBM_F32_LEAPFROG: return batch_step_kernel_ptr<float, Lf>(threads, fn);
+    default: return batch_step_kernel_ptr<double, double>(threads, fn);
+    }
+}
+
 void batch_release_block(lbm_batch *b)
 {
     if (!b->block) return;
@@ -1936,19 +1948,67 @@ void batch_free(lbm_batch *b, void *p)
     else cudaFree(p);
 }
 
-// Re-partition every lattice into bands of `rows` rows and rebuild the unit
-// table for CTAs of `threads` threads (column blocks of threads 16-byte
-// vectors) and the descriptor table; the block grows when the tables do.
+// Band heights of a batch whose CTAs all fit in one wave (rows = 0): every
+// lattice's bands about equally tall, as tall as the resident slots allow,
+// so each CTA marches a long band (few halo rows) and no second wave or tail
+// of short units follows.  Returns per lattice the height to partition with.
+lbm_status batch_one_wave(lbm_batch *b, int threads, std::vector<int> &heights)
+{
+    const void *fn = nullptr;
+    cudaError_t e = batch_kernel_ptr(b->storage, threads, &fn);
+    if (e != cudaSuccess) return cuda_fail(e, "selecting the batch kernel");
+    int bps = 0;
+    LBM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, threads, 0));
+    const int64_t slots = (int64_t)b->hs[0]->sms * std::max(bps, 1);
+    heights.assign(b->hs.size(), 1);
+    // strip-rows: column blocks x rows, the crack sub-bands apart
+    int64_t total = 0;
+    int64_t crack_units = 0;
+    std::vector<int> ncb(b->hs.size()), body(b->hs.size());
+    for (size_t i = 0; i < b->hs.size(); ++i) {
+        const lbm_handle *h = b->hs[i];
+        const int cols = threads * (int)(16 / h->esize);
+        ncb[i] = (h->grid.nx + cols - 1) / cols;
+        const bool crack = h->cp.mode != CRACK_NONE && !h->cp.line;
+        const int hh = !crack ? 0 : (h->cp.macro ? 3 : 1);
+        const int nsub = !crack ? 0 : ((h->jc >= hh ? 1 : 0) + (h->jc + hh <= h->grid.ny ? 1 : 0));
+        body[i] = h->grid.ny - nsub * hh;
+        total += (int64_t)ncb[i] * body[i];
+        crack_units += (int64_t)ncb[i] * nsub;
+    }
+    const int64_t free_slots = std::max<int64_t>(slots - crack_units, 1);
+    for (int64_t target = std::max<int64_t>(1, (total + free_slots - 1) / free_slots);; ++target) {
+        int64_t units = crack_units;
+        for (size_t i = 0; i < b->hs.size(); ++i) {
+            const int nb = std::max<int64_t>(1, (body[i] + target / 2) / target);
+            const int rows = (body[i] + nb - 1) / nb;
+            heights[i] = std::max(rows, 1);
+            units += (int64_t)ncb[i] * ((body[i] + heights[i] - 1) / heights[i] + 2);   // + pieces around the crack
+        }
+        if (units <= slots || target > 1 << 20) break;
+    }
+    return LBM_OK;
+}
+
+// Re-partition every lattice into bands of `rows` rows (0: the single-wave
+// heights of batch_one_wave) and rebuild the unit table for CTAs of
+// `threads` threads (column blocks of threads 16-byte vectors) and the
+// descriptor table; the block grows when the tables do.
 lbm_status batch_build(lbm_batch *b, int threads, int rows)
 {
     if (threads != 32 && threads != 64 && threads != kThreads)
         return fail(LBM_ERR_ARG, "threads per CTA must be 32, 64 or 128");
-    if (rows < 1) return fail(LBM_ERR_ARG, "band_rows must be >= 1");
+    if (rows < 0) return fail(LBM_ERR_ARG, "band_rows must be >= 0");
+    std::vector<int> heights(b->hs.size(), rows);
+    if (rows == 0) {
+        lbm_status rc = batch_one_wave(b, threads, heights);
+        if (rc != LBM_OK) return rc;
+    }
     std::vector<BatchUnit> units;
     for (size_t i = 0; i < b->hs.size(); ++i) {
         lbm_handle *h = b->hs[i];
         drop_graph(h);
-        lbm_status rc = plan_bands(h, rows);
+        lbm_status rc = plan_bands(h, heights[i]);
         if (rc != LBM_OK) return rc;
         const int cols = threads * (int)(16 / h->esize);
         const int ncb = (h->grid.nx + cols - 1) / cols;
@@ -2196,12 +2256,12 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *threads, i
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return done(fail(LBM_ERR_CUDA, "creating timing events"));
     const int shapes_t[3] = {32, 64, kThreads};
-    const int shapes_r[4] = {8, 16, 32, 64};
+    const int shapes_r[5] = {0, 8, 16, 32, 64};   // 0: every CTA resident in one wave
     int best_t = b->threads, best_r = b->band_rows;
     double best = 1e300;
     int par = b->hs[0]->parity;
     for (int ti = 0; ti < 3; ++ti)
-        for (int ri = 0; ri < 4; ++ri) {
+        for (int ri = 0; ri < 5; ++ri) {
             rc = batch_build(b, shapes_t[ti], shapes_r[ri]);
             if (rc != LBM_OK) return done(rc);
             double t_min = 1e300;

@@ -232,6 +232,7 @@ cudaError_t launch_batch_persistent(const StepArgs<T, D> *descs, int n_lat, cons
                                     GridBarrier *bar, uint32_t *err, long long budget, int threads, cudaStream_t s);
 cudaError_t launch_barrier_probe(GridBarrier *bar, int ctas, int expected, long long budget, uint32_t *err,
                                  cudaStream_t s);
+template <typename T, typename D> cudaError_t batch_step_kernel_ptr(int threads, const void **fn);
 // threads: 32, 64 or kThreads per CTA (the batch's column-block width)
 template <typename T, typename D>
 cudaError_t launch_batch_step(const StepArgs<T, D> *descs, const BatchUnit *units, int n_units, int par, cudaStream_t s,

@@ -769,6 +769,17 @@ cudaError_t launch_step_rec(const StepArgs<T, T> &a, const RecArgs &r, int bands
 }
 
 template <typename T, typename D>
+cudaError_t batch_step_kernel_ptr(int threads, const void **fn)
+{
+    switch (threads) {
+    case 32: *fn = reinterpret_cast<const void *>(&batch_step_kernel<T, D, 32>); return cudaSuccess;
+    case 64: *fn = reinterpret_cast<const void *>(&batch_step_kernel<T, D, 64>); return cudaSuccess;
+    case kThreads: *fn = reinterpret_cast<const void *>(&batch_step_kernel<T, D, kThreads>); return cudaSuccess;
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T, typename D>
 cudaError_t launch_batch_step(const StepArgs<T, D> *descs, const BatchUnit *units, int n_units, int par, cudaStream_t s,
                               int threads)
 {
@@ -1181,6 +1192,11 @@ template cudaError_t launch_batch_persistent<float, Lf>(const StepArgs<float, Lf
 template int edge_rule_count<float, Lf>(const StepArgs<float, Lf> &);
 template cudaError_t launch_batch_edge_rule<float, Lf>(const StepArgs<float, Lf> *, const BatchUnit *, int, int, cudaStream_t);
 template cudaError_t launch_edge_rule<float, Lf>(const StepArgs<float, Lf> &, cudaStream_t);
+template cudaError_t batch_step_kernel_ptr<double, double>(int, const void **);
+template cudaError_t batch_step_kernel_ptr<float, float>(int, const void **);
+template cudaError_t batch_step_kernel_ptr<float, __nv_bfloat16>(int, const void **);
+template cudaError_t batch_step_kernel_ptr<float, __half>(int, const void **);
+template cudaError_t batch_step_kernel_ptr<float, Lf>(int, const void **);
 template cudaError_t launch_fill_pads<float>(float *, int64_t, int, int, const int32_t *, cudaStream_t);
 template cudaError_t launch_fill_pads<double>(double *, int64_t, int, int, const int32_t *, cudaStream_t);
 

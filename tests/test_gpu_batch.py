@@ -173,7 +173,7 @@ def test_batch_matches_the_oracle(oracle_mod, gpu, storage):
 # ------------------------------------------------------ launch shapes, tuner
 
 @pytest.mark.parametrize("storage", ["f32", "f64"])
-@pytest.mark.parametrize("threads,rows", [(32, 8), (64, 5), (32, 64), (128, 32)])
+@pytest.mark.parametrize("threads,rows", [(32, 8), (64, 5), (32, 64), (128, 32), (32, 0), (128, 0)])
 def test_every_launch_shape_gives_the_solo_bits(gpu, storage, threads, rows):
     """CTAs of 32, 64 or 128 threads over bands of any height: each lattice
     of the batch still ends bit-identical to its solo run (graph chunks and
@@ -206,7 +206,7 @@ def test_tune_leaves_the_lattices_as_they_were_and_caches_the_shape(gpu):
     b = gpu.Batch(mem)
     b.step(37)                       # a pending crack step at the tuning call
     r = b.tune(trial_steps=6)
-    assert r["threads"] in (32, 64, 128) and r["band_rows"] in (8, 16, 32, 64)
+    assert r["threads"] in (32, 64, 128) and r["band_rows"] in (0, 8, 16, 32, 64)
     assert not r["from_cache"] and r["us_per_step"] > 0
     assert (b.info()["threads"], b.info()["band_rows"]) == (r["threads"], r["band_rows"])
     b.step(63)
@@ -227,7 +227,7 @@ def test_shape_arguments_are_checked(gpu):
     ps = W.batch_problems(2, seed=6)
     lats = [gpu.Lattice(p, "f32") for p in ps]
     b = gpu.Batch(lats)
-    for t, r in ((48, 16), (256, 16), (32, 0)):
+    for t, r in ((48, 16), (256, 16), (32, -1)):
         with pytest.raises(gpu.LbmError) as ei:
             b.set_shape(t, r)
         assert ei.value.status == -1
