@@ -273,7 +273,7 @@ __device__ __forceinline__ T march9(const StepArgs<T, T> &a, int x0, int j0, int
 
 // The grid is (column blocks of kThreads vectors) x (bands of kRows9 rows).
 template <typename T>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : kMinBlocks - 2)
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBlocks - 2)
     d2q9_step_kernel(const StepArgs<T, T> a)
 {
     constexpr int N = Vec<T>::N;
