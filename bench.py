@@ -2,17 +2,19 @@
 """Throughput of the fused lattice Boltzmann time step with dynamic mode III
 crack propagation (arXiv 2206.12412) on GB300.
 
-Headline workload: the 16384 x 16384 FP32 lattice (268 M sites, 4.3 GB of
+Headline workload: the 16384 x 16384 FP32 lattice (268 M sites, 2.1 GB of
 state, far larger than the 129 MB L2) with an edge crack on the midline
 from 0 to 2048 growing at the prescribed v = 0.5 c_s, top/bottom ramped to
-+-1e-3 over 2000 steps.  One benchmark step is one full time step of the
-method: the bulk stream + collide + integrate update of every site with
-the macroscopic crack-face rule and the crack step (K_III evaluation,
-criterion, advance, link cuts), one fused kernel launch.
++-1e-3 over 2000 steps, its state stored as the two FP32 planes w_n and
+w_{n-1} (leapfrog storage: 12 bytes per site update; the FP32 moment form,
+w and wdot, 16 bytes, is measured beside it).  One benchmark step is one
+full time step of the method: the bulk stream + collide + integrate update
+of every site with the macroscopic crack-face rule and the crack step
+(K_III evaluation, criterion, advance, link cuts), one fused kernel launch.
 
 Timing: the lattice first runs --prelude steps, then --warmup untimed
 steps; each of the --steps timed steps is bracketed by CUDA events on the
-lattice's stream.  The state is 33x the L2, so no flush is needed between
+lattice's stream.  The state is 16x the L2, so no flush is needed between
 steps.  The step kernel is also timed by the library's own event hooks
 (the roofline figure).  The rest of the JSON line: the former 4096 x 2048
 K-criterion headline (L2 flushed between steps), the 128 x 128 FP64
@@ -47,9 +49,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GLUPS and HBM GB/s vs GB300 roofline; batched and adjoint vs plain FP32 forward"
 UNIT = "GLUPS"
-BYTES_PER_SITE = 16            # FP32 moment form: read w, wdot; write w, wdot
+HEADLINE_STORAGE = "f32_lf"    # FP32 leapfrog storage: the state as w_n, w_{n-1}
+BYTES_PER_SITE = 12            # read w_n and w_{n-1}, write w_{n+1} (FP32)
 WORKLOAD = "prescribed_v05_16384x16384_f32"
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_kernel_f32_8192x8192.md")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_kernel_leapfrog_f32_8192x8192.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2206_12412_gb300", "csrc", f)
                   for f in ("lbm_kernels.cu", "lbm_rows.cuh", "lbm_internal.cuh", "lbm_crack.cuh")]
 
@@ -293,7 +296,9 @@ def profile_batched(lbm, W, torch, stream, steps, shape, count=256):
     problems = W.batch_problems(count, seed=3)
     lats = [lbm.Lattice(p, "f32", stream=stream) for p in problems]
     batch = lbm.Batch(lats)
-    batch.set_shape(*shape)
+    batch.set_shape(*shape[:2])
+    if len(shape) > 2:
+        batch.set_lookahead(shape[2])
     secs = timed(torch, stream, lambda: batch.step(steps))
     sites = sum(p["nx"] * p["ny"] for p in problems)
     batch.close()
@@ -318,6 +323,13 @@ def measure_batched(lbm, W, torch, stream, steps, peak, count=256, full_steps=No
     batch.step(64)
     t_b = timed(torch, stream, lambda: batch.step(steps))
     info = batch.info()
+    # the tuned shape with the other row lookahead of the march
+    la = info["lookahead"]
+    batch.set_lookahead(3 - la)
+    batch.step(16)
+    t_o = timed(torch, stream, lambda: batch.step(steps))
+    batch.set_lookahead(la)
+    lookahead_ab = {str(la): r4(sites * steps / t_b / 1e9), str(3 - la): r4(sites * steps / t_o / 1e9)}
     full = None
     if full_steps:
         for l in lats:
@@ -334,12 +346,25 @@ def measure_batched(lbm, W, torch, stream, steps, peak, count=256, full_steps=No
     t_s = timed(torch, stream, lambda: [l.step(steps) for l in lats])
     for l in lats:
         l.close()
+    # the same batch in leapfrog storage (12 bytes per site update)
+    lf = [lbm.Lattice(p, "f32_lf", stream=stream) for p in problems]
+    blf = lbm.Batch(lf)
+    blf.tune(trial_steps=8)
+    blf.step(64)
+    t_lf = timed(torch, stream, lambda: blf.step(steps))
+    lf_shape = blf.info()
+    blf.close()
+    for l in lf:
+        l.close()
     return {"n": len(problems), "sites": sites, "steps": steps, "ctas": info["ctas"],
-            "shape": [info["threads"], info["band_rows"]], "glups_default_shape": r4(sites * steps / t_d / 1e9),
+            "shape": [info["threads"], info["band_rows"], info["lookahead"]],
+            "glups_default_shape": r4(sites * steps / t_d / 1e9), "glups_by_lookahead": lookahead_ab,
             "glups_persistent": r4(sites * steps / t_p / 1e9),
             "glups_sequential": r4(sites * steps / t_s / 1e9), "speedup": r4(t_s / t_b),
             "glups": r4(sites * steps / t_b / 1e9), "frac": r4(16 * sites * steps / t_b / 1e9 / peak),
-            "full_run": full}
+            "full_run": full,
+            "leapfrog": {"glups": r4(sites * steps / t_lf / 1e9), "frac": r4(12 * sites * steps / t_lf / 1e9 / peak),
+                         "shape": [lf_shape["threads"], lf_shape["band_rows"], lf_shape["lookahead"]]}}
 
 
 def measure_adjoint(lbm, W, torch, stream, n_steps=None):
@@ -385,13 +410,13 @@ def measure_adjoint(lbm, W, torch, stream, n_steps=None):
 
 
 def measure_storage_large(lbm, W, torch, stream, peak, n=16384):
-    """The 12-byte storage forms on the headline lattice (leapfrog FP32, and
+    """The other storage forms on the headline lattice (the FP32 moment form,
     FP32 w with 16-bit wdot): the step kernel's own CUDA-event time, 20 steps
     after 20."""
     p = W.large_prescribed(n)
     sites = p["nx"] * p["ny"]
     out = {}
-    for storage, bps in (("f32_lf", 12), ("f32_bf16", 12), ("f32_f16", 12)):
+    for storage, bps in (("f32", 16), ("f32_bf16", 12), ("f32_f16", 12)):
         lat = lbm.Lattice(p, storage, stream=stream)
         lat.step(20)
         lat.set_profiling(True)
@@ -606,13 +631,13 @@ def run_ours(args, rank, world, local):
     problem = W.large_prescribed()
     sites = problem["nx"] * problem["ny"]
     stream = torch.cuda.current_stream()
-    lat = lbm.Lattice(problem, "f32", stream=stream)
+    lat = lbm.Lattice(problem, HEADLINE_STORAGE, stream=stream)
     lat.step(args.prelude)
     for _ in range(args.warmup):
         lat.step(1)
     lat.sync()
 
-    # timed region: one step per pair of events; the 4.3 GB state is 33x the
+    # timed region: one step per pair of events; the 2.1 GB state is 16x the
     # L2, so each step streams its inputs from HBM without a flush
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -707,14 +732,14 @@ def run_ours(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nx": problem["nx"], "ny": problem["ny"], "storage": "f32",
+        "config": {"workload": WORKLOAD, "nx": problem["nx"], "ny": problem["ny"], "storage": "f32_leapfrog",
                    "crack": "prescribed v=0.5", "bc_mode": problem["bc_mode"], "prelude_steps": args.prelude,
-                   "l2": "inputs larger than L2 (4.3 GB state), no flush",
+                   "l2": "inputs larger than L2 (2.1 GB state), no flush",
                    "parallelism": f"{world} independent replicas" if world > 1 else "single GPU",
                    "launch": launch},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "step_kernel<float>", "kernel_ms": kern_s * 1e3, "bytes_per_site": BYTES_PER_SITE},
+                     "kernel": "step_kernel<float, Lf>", "kernel_ms": kern_s * 1e3, "bytes_per_site": BYTES_PER_SITE},
         "e2e": {"value": world * sites * args.steps / e2e_s / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps,
@@ -752,7 +777,7 @@ def main():
                     help="only the batched measurement, --steps steps of --batched-count lattices (for ncu)")
     ap.add_argument("--batched-count", type=int, default=256, help="lattices in the batched measurement")
     ap.add_argument("--batched-shape", default=None,
-                    help="with --batched-only: THREADS,ROWS -- only the batched steps at that launch shape")
+                    help="with --batched-only: THREADS,ROWS[,LOOKAHEAD] -- only the batched steps at that launch shape")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="only the sensor-misfit gradient measurement (for ncu)")
     ap.add_argument("--adjoint-steps", type=int, default=None, help="steps of the adjoint workload (default 8000)")
@@ -763,7 +788,7 @@ def main():
                          "itself), kcrit = 4096x2048 K-criterion, d2q9 / line / line_macro = its D2Q9 and "
                          "20-degree forms, sec52 = the Sec. 5.2 example")
     ap.add_argument("--size", type=int, default=16384, help="with --workload large: the lattice's side")
-    ap.add_argument("--storage", default="f32", choices=["f32", "f32_bf16", "f32_f16", "f64"],
+    ap.add_argument("--storage", default="f32", choices=["f32", "f32_lf", "f32_bf16", "f32_f16", "f64"],
                     help="with --profile-only: the storage form")
     ap.add_argument("--bulk", action="store_true", help="with --profile-only: the bulk-copy march (lbm_set_bulk)")
     args = ap.parse_args()

@@ -330,7 +330,7 @@ lbm_status lbm_sync(lbm_handle *h);
 /* Move later work to another stream (the caller orders the two streams). */
 lbm_status lbm_set_stream(lbm_handle *h, void *stream);
 
-/* Launch shape of the step kernel.  Each CTA marches over a band of at most
+/* Launch shape of the step kernel (D2Q5 and D2Q9).  Each CTA marches over a band of at most
  * band_rows rows of one column block; 0 picks the built-in partition (the
  * shortest bands for which every CTA of a step is resident at once).  The rows
  * next to the crack line (jc-3 .. jc+2 with macroscopic crack faces, jc-1 and
@@ -369,6 +369,20 @@ lbm_status lbm_set_face_solve(lbm_handle *h, int32_t mode, int32_t *chunked);
  * next synchronising call.  Synchronises the stream and re-partitions the
  * rows for the chosen kernel's occupancy (as lbm_set_launch(h, 0)). */
 lbm_status lbm_set_bulk(lbm_handle *h, int32_t enable);
+
+/* How consecutive kernels of the time steps are launched.  enable != 0:
+ * chained by programmatic dependent launch -- the CTAs of a step's kernel
+ * (and of the edge-rule, face and crack-face kernels that follow it) are
+ * dispatched while the kernel before it still runs and wait on the device
+ * for it to complete, so no launch gap separates the steps of a lattice.
+ * enable = 0: plain launches.  The default is chained for lattices of at most
+ * 2^18 sites, whose steps take a few microseconds and are bound by launch
+ * latency, and plain for larger ones, where early-resident CTAs of the next
+ * step cost more than the gap they save.  The arithmetic is the same
+ * (identical results).  Synchronises the stream and drops the cached step
+ * graph.  lbm_batch_set_chained does the same for a batch's launches (plain
+ * by default).  No counterpart in the paper. */
+lbm_status lbm_set_chained(lbm_handle *h, int32_t enable);
 
 /* Kernel timing: while enabled, lbm_step launches every step directly (no
  * graph) with CUDA events on the handle's stream around the step kernel, and
@@ -497,11 +511,25 @@ lbm_status lbm_batch_info(const lbm_batch *b, int32_t *n_lattices, int32_t *ctas
 lbm_status lbm_batch_set_shape(lbm_batch *b, int32_t threads, int32_t band_rows);
 lbm_status lbm_batch_get_shape(const lbm_batch *b, int32_t *threads, int32_t *band_rows);
 
+/* Row lookahead of the batched step's march: with rows = 1 (the default) a
+ * warp keeps the loads of the row after next in flight while it updates a
+ * row; with rows = 2 it keeps two rows of loads in flight (eight more
+ * registers a thread, so 28 instead of 32 resident warps per SM), which
+ * hides more of the memory latency of short bands.  Same arithmetic: the
+ * results do not depend on it.  rows other than 1 or 2: LBM_ERR_ARG.
+ * lbm_batch_set_lookahead synchronises the stream and re-partitions (the
+ * single-wave band heights of band_rows = 0 depend on the resident CTAs);
+ * lbm_batch_get_lookahead reads it back.  No counterpart in the paper. */
+lbm_status lbm_batch_set_lookahead(lbm_batch *b, int32_t rows);
+/* Chained launches of the batched step (as lbm_set_chained; default off). */
+lbm_status lbm_batch_set_chained(lbm_batch *b, int32_t enable);
+lbm_status lbm_batch_get_lookahead(const lbm_batch *b, int32_t *rows);
+
 /* Autotuner of the batched step's launch shape: times trial_steps (2..1024)
- * batched steps with CUDA events for every shape of threads in {32, 64, 128}
- * x band_rows in {0 (one wave), 8, 16, 32, 64} (the first of three
- * repetitions a warm-up),
- * keeps the fastest, and caches it in the process under the device's SM
+ * batched steps with CUDA events for every shape of lookahead in {1, 2} x
+ * threads in {32, 64, 128} x band_rows in {0 (one wave), 8, 16, 32, 64}
+ * (the first of three repetitions a warm-up), keeps the fastest (its
+ * lookahead is read back with lbm_batch_get_lookahead), and caches it in the process under the device's SM
  * count, the storage and the lattices' sizes and crack rows (a later batch of
  * the same lattices takes the cached shape without trials; *from_cache = 1,
  * *us_per_step = 0).  The trials advance the lattices, so the tuner first

@@ -112,10 +112,14 @@ PROTOTYPES = {
     "lbm_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "lbm_set_face_solve": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
     "lbm_set_bulk": (C.c_int, [C.c_void_p, C.c_int32]),
+    "lbm_set_chained": (C.c_int, [C.c_void_p, C.c_int32]),
+    "lbm_batch_set_chained": (C.c_int, [C.c_void_p, C.c_int32]),
     "lbm_batch_set_shape": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     "lbm_batch_set_persistent": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
     "lbm_barrier_probe": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, C.c_void_p]),
     "lbm_batch_get_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "lbm_batch_set_lookahead": (C.c_int, [C.c_void_p, C.c_int32]),
+    "lbm_batch_get_lookahead": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "lbm_batch_tune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                  C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
     "lbm_batch_destroy": (None, [C.c_void_p]),

@@ -30,7 +30,6 @@
 
 namespace lbm {
 
-constexpr int kRows9 = 16;   // rows of a CTA's band
 
 // The value a link streams back when it leaves the body (ox: across the
 // left / right edge, oy: across the bottom / top edge; dx, dy its direction):
@@ -126,9 +125,11 @@ __device__ __forceinline__ T march9(const StepArgs<T, T> &a, int x0, int j0, int
         if (!SPECIAL) {
             // the bare update from the column sums of the rows above and
             // below, s_k = w_a + w_b, each formed once: the axis sum is
-            // s_k + (w_W + w_E) (as in the general path), the diagonal sum
-            // s_{k-1} + s_{k+1}; each difference with 4 w is taken before the
-            // weights, so the rounding stays at the scale of the Laplacians
+            // s_k + (w_W + w_E), the diagonal sum s_{k-1} + s_{k+1} (the
+            // general path groups both alike, so that every path, and so
+            // every band partition, gives the same bits); each difference
+            // with 4 w is taken before the weights, so the rounding stays at
+            // the scale of the Laplacians
             T sc[N + 2];
             sc[0] = la + lb;
 #pragma unroll
@@ -152,7 +153,7 @@ __device__ __forceinline__ T march9(const StepArgs<T, T> &a, int x0, int j0, int
                 const T al = k == 0 ? la : wa.v[k - 1], ar = k == N - 1 ? ra : wa.v[k + 1];
                 const T bl = k == 0 ? lb : wb.v[k - 1], br = k == N - 1 ? rb : wb.v[k + 1];
                 const T axis = ((wa.v[k] + wb.v[k]) + (wl + wr)) - (T)4 * wc.v[k];
-                const T diag = ((al + ar) + (bl + br)) - (T)4 * wc.v[k];
+                const T diag = ((al + bl) + (ar + br)) - (T)4 * wc.v[k];
                 wdnew.v[k] = wdv.v[k] + (ga * axis + gd * diag);
                 wnew.v[k] = wc.v[k] + dt * wdnew.v[k];
             }
@@ -185,7 +186,7 @@ __device__ __forceinline__ T march9(const StepArgs<T, T> &a, int x0, int j0, int
                         bl = leaving(a.edge, two_ws, true, false, -1, -1, w0);
                     }
                     const T axis = ((wa.v[k] + wb.v[k]) + (wl + wr)) - (T)4 * w0;
-                    const T diag = ((al + ar) + (bl + br)) - (T)4 * w0;
+                    const T diag = ((al + bl) + (ar + br)) - (T)4 * w0;
                     wdnew.v[k] = wdv.v[k] + (ga * axis + gd * diag);
                     wnew.v[k] = w0 + dt * wdnew.v[k];
                 }
@@ -243,7 +244,7 @@ __device__ __forceinline__ T march9(const StepArgs<T, T> &a, int x0, int j0, int
                 if (crow && !below && cr) br = w0;
                 else if (rgt || bot) br = leaving(a.edge, two_ws, rgt, bot, 1, -1, w0);
                 const T axis = ((up + dn) + (wl + wr)) - (T)4 * w0;
-                const T diag = ((al + ar) + (bl + br)) - (T)4 * w0;
+                const T diag = ((al + bl) + (ar + br)) - (T)4 * w0;
                 wdnew.v[k] = wdv.v[k] + (ga * axis + gd * diag);
                 wnew.v[k] = w0 + dt * wdnew.v[k];
             }
@@ -271,11 +272,17 @@ __device__ __forceinline__ T march9(const StepArgs<T, T> &a, int x0, int j0, int
     return acc;
 }
 
-// The grid is (column blocks of kThreads vectors) x (bands of kRows9 rows).
+// The grid is (column blocks of kThreads vectors) x (the handle's bands: as
+// for the D2Q5 step, the crack rows jc - 1 and jc lie in sub-bands of their
+// own, one or three rows tall, so that the CTAs that run the pending crack
+// step first have few rows after it, and the other bands are as tall as one
+// wave of resident CTAs allows).
 template <typename T>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBlocks - 2)
     d2q9_step_kernel(const StepArgs<T, T> a)
 {
+    pdl_wait();
+    pdl_trigger();
     constexpr int N = Vec<T>::N;
     constexpr int cols = kThreads * N;
     __shared__ CrackState sS;
@@ -284,7 +291,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
     const int cb = blockIdx.x;
     const int x0 = (cb * kThreads + tid) * N;
     const int xw0 = (cb * kThreads + (tid & ~31)) * N;
-    const int j0 = blockIdx.y * kRows9, j1 = min(j0 + kRows9, ny);
+    const Unit U = a.units[blockIdx.y];
+    const int j0 = U.j0, j1 = U.j1;
     const bool crack = a.p.mode != CRACK_NONE;
     const bool edge_warp = xw0 == 0 || xw0 + 32 * N - 1 >= nx - 1;
     const CrackParams &p = a.p;
@@ -370,9 +378,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
 template <typename T>
 cudaError_t launch_d2q9_step(const StepArgs<T, T> &a, cudaStream_t s)
 {
-    const dim3 grid((unsigned)a.ncb, (unsigned)((a.ny + kRows9 - 1) / kRows9));
-    d2q9_step_kernel<T><<<grid, kThreads, 0, s>>>(a);
-    return cudaGetLastError();
+    const dim3 grid((unsigned)a.ncb, (unsigned)a.n_bands);
+    return launch_chained(d2q9_step_kernel<T>, grid, dim3(kThreads), 0, s, a.chained != 0, a);
 }
 
 // The macroscopic rule on the D2Q9 crack faces (Sec. 3.1), after the update:
@@ -386,6 +393,8 @@ cudaError_t launch_d2q9_step(const StepArgs<T, T> &a, cudaStream_t s)
 template <typename T>
 __global__ void __launch_bounds__(128) d2q9_face_kernel(const StepArgs<T, T> a)
 {
+    pdl_wait();
+    pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.nx) return;
     const int nx = a.nx, jc = a.p.jc;
@@ -412,8 +421,8 @@ __global__ void __launch_bounds__(128) d2q9_face_kernel(const StepArgs<T, T> a)
 template <typename T>
 cudaError_t launch_d2q9_faces(const StepArgs<T, T> &a, cudaStream_t s)
 {
-    d2q9_face_kernel<T><<<(a.nx + 127) / 128, 128, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_chained(d2q9_face_kernel<T>, dim3((unsigned)((a.nx + 127) / 128)), dim3(128), 0, s, a.chained != 0,
+                          a);
 }
 
 template cudaError_t launch_d2q9_faces<double>(const StepArgs<double, double> &, cudaStream_t);

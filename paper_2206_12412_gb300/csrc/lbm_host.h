@@ -44,6 +44,7 @@ struct lbm_handle {
     int32_t ncb;         // column blocks of kThreads vectors
     int32_t n_bands, band_rows, crack_band, sms, bps;
     bool bulk;           // interior CTAs stage their rows by bulk copies (lbm_set_bulk; FP32 w, D2Q5, crack along +x)
+    bool chained;        // the kernels of a step launched chained (programmatic dependent launch; lbm_set_chained)
     Unit *units;         // device table, capacity ny
     std::vector<Unit> *units_h;   // host copy of the current partition
     int64_t gen;         // bumped whenever step-kernel arguments or the partition change
@@ -130,7 +131,7 @@ inline void make_step_args(const lbm_handle *h, int par, StepArgs<T, D> &a)
     a.ncb = h->ncb;
     a.crack_band = h->crack_band;
     a.n_bands = h->n_bands;
-    a.pad_nb = 0;
+    a.chained = h->chained ? 1 : 0;
     for (int e = 0; e < 4; ++e) { a.edge[e] = h->grid.edge[e]; a.load[e] = h->load[e]; }
     a.g = (T)h->g;
     a.dt = (T)h->grid.dt;

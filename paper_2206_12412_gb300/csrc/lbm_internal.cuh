@@ -35,6 +35,7 @@ constexpr double kTwoM32 = 2.3283064365386963e-10;  // 2^-32
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kThreads = 128;                       // threads per CTA of the step kernel
 constexpr int kMinBlocks = 8;                       // resident CTAs per SM the kernel is built for
+constexpr int64_t kChainedSites = int64_t(1) << 18;  // lattices up to this size launch their steps chained
 
 // EDGE_HALO: an inner edge of a row slab of a decomposed lattice; the pad
 // row beyond it holds the neighbouring slab's boundary row, copied there
@@ -45,6 +46,41 @@ enum { CRACK_NONE = 0, CRACK_STATIONARY = 1, CRACK_PRESCRIBED = 2, CRACK_KCRIT =
 enum { LOAD_ZERO = 0, LOAD_LINEAR = 1, LOAD_SIN2 = 2, LOAD_HALFSINE = 3, LOAD_SERIES = 4, LOAD_CONST = 5 };
 enum { FLAG_CLAMPED = 1, FLAG_UNSUPPORTED = 2, FLAG_NONFINITE = 4 };
 enum { ERR_NONFINITE = 1, ERR_TIMEOUT = 2 };
+
+// Programmatic dependent launch.  A kernel launched with the programmatic
+// stream serialisation attribute (launch_chained below) may become resident
+// while the kernel before it in the stream is still running.  pdl_wait()
+// blocks until that kernel has completed and its memory operations are
+// visible; for a kernel launched without the attribute it returns at once.
+// pdl_trigger() lets the next kernel launch once every CTA of this one has
+// issued it (or exited).  Every kernel of the per-step chain calls both first
+// thing, before it touches memory: the next step's CTAs are then dispatched
+// while this step runs and start the moment it ends, instead of after a
+// launch gap and a ramp.  The next kernel launches only after every CTA of
+// this one has started, so its waiting CTAs never hold a slot that one of
+// this kernel's CTAs still needs.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launch `kernel` on `s`, chained to the previous kernel of the stream by
+// programmatic dependent launch when `chained` (the kernel must call
+// pdl_wait() before it touches memory), as a plain launch otherwise.
+template <typename... P, typename... A>
+inline cudaError_t launch_chained(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                  bool chained, A &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = chained ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<A &&>(args)...);
+}
 
 // The "wdot" element type of leapfrog storage (LBM_F32_LEAPFROG): the plane it
 // names is the previous w, i.e. the step's output buffer (see WdIO<Lf>).
@@ -133,7 +169,8 @@ struct StepArgs {
     int32_t nx, ny;
     int32_t ncb;               // column blocks of kThreads * 16 bytes
     int32_t crack_band;        // band that holds the crack rows (-1: none)
-    int32_t n_bands, pad_nb;   // bands of the partition
+    int32_t n_bands;           // bands of the partition
+    int32_t chained;           // host side: launch chained to the previous kernel (launch_chained)
     int32_t edge[4];
     T g, dt;
     uint32_t *cut_h;
@@ -232,18 +269,19 @@ cudaError_t launch_batch_persistent(const StepArgs<T, D> *descs, int n_lat, cons
                                     GridBarrier *bar, uint32_t *err, long long budget, int threads, cudaStream_t s);
 cudaError_t launch_barrier_probe(GridBarrier *bar, int ctas, int expected, long long budget, uint32_t *err,
                                  cudaStream_t s);
-template <typename T, typename D> cudaError_t batch_step_kernel_ptr(int threads, const void **fn);
-// threads: 32, 64 or kThreads per CTA (the batch's column-block width)
+// threads: 32, 64 or kThreads per CTA (the batch's column-block width);
+// lookahead: 1 or 2 rows of loads ahead in the march
+template <typename T, typename D> cudaError_t batch_step_kernel_ptr(int threads, int lookahead, const void **fn);
 template <typename T, typename D>
 cudaError_t launch_batch_step(const StepArgs<T, D> *descs, const BatchUnit *units, int n_units, int par, cudaStream_t s,
-                              int threads = kThreads);
+                              int threads = kThreads, int lookahead = 1, bool chained = false);
 template <typename T, typename D>
 cudaError_t launch_step(const StepArgs<T, D> &a, int bands, cudaStream_t s, bool bulk = false);
 template <typename T, typename D> cudaError_t launch_edge_rule(const StepArgs<T, D> &a, cudaStream_t s);
 template <typename T, typename D> int edge_rule_count(const StepArgs<T, D> &a);
 template <typename T, typename D>
 cudaError_t launch_batch_edge_rule(const StepArgs<T, D> *descs, const BatchUnit *units, int n_units, int par,
-                                   cudaStream_t s);
+                                   cudaStream_t s, bool chained = false);
 template <typename T> cudaError_t launch_d2q9_step(const StepArgs<T, T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_d2q9_faces(const StepArgs<T, T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_step_rec(const StepArgs<T, T> &a, const RecArgs &r, int bands, cudaStream_t s);

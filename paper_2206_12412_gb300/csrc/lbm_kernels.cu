@@ -45,67 +45,50 @@ namespace lbm {
 // sub-bands runs the march below, which holds no severed link (all severed
 // links of the straight crack lie between rows jc-1 and jc).  The crack
 // sub-bands (rows jc-3 .. jc-1 and jc .. jc+2 with the macroscopic rule, rows
-// jc-1 and jc otherwise) run crack_rows; their CTAs that own the next crack
-// link first run the crack step of the previous time step.
-
-// The fields of StepArgs that the crack sub-bands need.  Their out-of-line
-// code receives them as scalars and rebuilds this struct (taking the address
-// of the kernel parameter block would move all of it to local memory, and a
-// struct argument copied field by field from it was not passed reliably).
-template <typename T, typename D>
-struct RowArgs {
-    const T *w_in;
-    T *w_out;
-    D *wd;
-    T wd_scale, wd_inv;
-    int64_t pitch;
-    int32_t nx, ny, jc, macro;
-    int32_t edge[4];
-    T g, dt;
-    const uint32_t *cut_v;
-    int32_t words;
-    const CrackState *s_in;
-};
+// jc-1 and jc otherwise) run crack_band; their CTAs that own the next crack
+// link also run the crack step of the previous time step.
 
 // A crack sub-band of HH rows: rows jc-HH .. jc-1 (below the crack) or
-// jc .. jc+HH-1 (above).  All of its loads are issued at once, then the rows
-// are computed from registers, so the sub-band costs about one memory latency
-// even while the rest of the lattice saturates HBM.  With the macroscopic
-// crack-face rule (Sec. 3.1, HH = 3), the boundary point x_B next to a severed
-// link takes w_B = 1.5 w_I - 0.5 w_II from the two new values of its column
-// further away from the crack, and wdot(x_B) = (w_B(t+dt) - w_B(t)) / dt.
-template <typename T, typename D, int HH, int TH = kThreads, bool COH = false>
-__device__ __noinline__ T crack_rows(const T *w_in_, T *w_out_, D *wd_, T wd_scale_, int64_t pitch_, int nx_, int ny_,
-                                     int jc_, int macro_, int edges, T g_, T dt_, const uint32_t *cut_v_, int words_,
-                                     const CrackState *s_in_, int cb, int j0)
+// jc .. jc+HH-1 (above), one CTA per column block, with the crack step of Alg.
+// 1 that follows the previous LBM step in the CTAs of the two sub-bands that
+// own the next link of an end (both reach the same decision; the lower one
+// records it, each end writing only its own fields of the next state; a row
+// slab whose boundary is the crack line holds one sub-band and reads the
+// other side's row from its halo, and records its own).  The CTA issues every
+// load of its rows and the load of the state at once (the rows do not depend
+// on the state), then hands the pair rows jc - 1 and jc it holds to the crack
+// step through shared memory, so the crack step's window costs no round trip
+// of its own when it lies in the CTA's columns; its rows are computed from
+// registers once the step has decided.  With the macroscopic crack-face rule
+// (Sec. 3.1, HH = 3), the boundary point x_B next to a severed link takes w_B
+// = 1.5 w_I - 0.5 w_II from the two new values of its column further away
+// from the crack, and wdot(x_B) = (w_B(t+dt) - w_B(t)) / dt.  The arguments
+// come from shared memory (a copy of the kernel's), as this code is out of
+// line.  Returns the sum the non-finite check reads.
+template <typename T, typename D, int HH, int TH, bool COH, bool BOTH, bool REC>
+__device__ __noinline__ T crack_band(const StepArgs<T, D> *ap, CrackState *sSp, PairStash<T> *st, int cb, int band,
+                                     int j0, const int64_t *rec_n0, int64_t rec_n_steps, int32_t *rec_il,
+                                     int32_t *rec_if)
 {
-    RowArgs<T, D> a;
-    a.w_in = w_in_;
-    a.w_out = w_out_;
-    a.wd = wd_;
-    a.wd_scale = wd_scale_;
-    a.wd_inv = (T)1 / wd_scale_;
-    a.pitch = pitch_;
-    a.nx = nx_;
-    a.ny = ny_;
-    a.jc = jc_;
-    a.macro = macro_;
-    for (int e = 0; e < 4; ++e) a.edge[e] = (edges >> (2 * e)) & 3;
-    a.g = g_;
-    a.dt = dt_;
-    a.cut_v = cut_v_;
-    a.words = words_;
-    a.s_in = s_in_;
-    T acc = (T)0;
+    const StepArgs<T, D> &a = *ap;
+    CrackState &sS = *sSp;
+    const CrackParams &p = a.p;
     constexpr int N = Vec<T>::N;
     typedef Row<T, N> R;
     const unsigned kFull = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int x0 = (cb * TH + threadIdx.x) * N;
-    const int jc = a.jc;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int cols = TH * N;
+    const int nx = a.nx, jc = p.jc;
+    const int x0 = (cb * TH + tid) * N;
     const int64_t P = a.pitch;
     const T *win = a.w_in + x0;
     const bool below = j0 + HH == jc;
+    T acc = (T)0;
+
+    // (1) every load at once: the state, the rows, the thread's cut bits
+    // before this step's crack step (bits of that step may or may not be in
+    // yet: the other sub-band CTA sets the same bits at its own pace)
+    if (tid == 0) sS = *a.s_in;
     R w[HH + 2], wd[HH];
     T hl[HH], hr[HH];
 #pragma unroll
@@ -116,10 +99,122 @@ __device__ __noinline__ T crack_rows(const T *w_in_, T *w_out_, D *wd_, T wd_sca
         hl[q] = lane == 0 ? win[(int64_t)(j0 + q) * P - 1] : (T)0;
         hr[q] = lane == 31 ? win[(int64_t)(j0 + q) * P + N] : (T)0;
     }
-    const EdgeValues<T> E = edge_values<T>(a.s_in);
-    __syncthreads();   // the crack step of the writer CTA has severed the next link
-    const uint32_t cut = x0 < a.nx ? (a.cut_v[(int64_t)(jc - 1) * a.words + (x0 >> 5)] >> (x0 & 31)) & ((1u << N) - 1u) : 0u;
-    (void)jc;
+    const uint32_t cut0 = x0 < nx ? (a.cut_v[(int64_t)(jc - 1) * a.words + (x0 >> 5)] >> (x0 & 31)) & ((1u << N) - 1u) : 0u;
+    __syncthreads();   // the state
+
+    // (2) does this CTA own the next link of an end?  (The same for all its
+    // threads: the barriers below are uniform.)
+    const int il0 = sS.i_last, if0 = sS.i_first;   // before the crack step
+    int i_next = max(il0 + 1, if0);
+    i_next = min(max(i_next, 0), nx - 1);
+    int i_prev = min(if0 - 1, il0);
+    i_prev = min(max(i_prev, 0), nx - 1);
+    const bool right_here = cb == i_next / cols;
+    const bool left_here = p.two_tips && cb == i_prev / cols;
+    const bool commit = band == a.crack_band;
+    const bool both = BOTH && right_here && left_here;
+    const bool stepping = right_here || left_here;
+    const EdgeValues<T> E = edge_values<T>(&sS);   // wstar: the crack step leaves it alone
+    if (stepping) {
+        // the pair rows jc - 1 and jc of the CTA's columns (w[] holds rows
+        // j0 - 1 .. j0 + HH) and the cut bits, for the K fit
+        const int qa = below ? HH + 1 : 1, qb = below ? HH : 0;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            st->above[tid * N + k] = w[qa].v[k];
+            st->below[tid * N + k] = w[qb].v[k];
+        }
+        st->cut[tid] = (uint8_t)cut0;
+        if (tid == 0) {
+            st->x0 = cb * cols;
+            st->n = min(cols, nx - cb * cols);
+        }
+    }
+    __syncthreads();   // every thread has il0, if0 (the crack step advances sS) and the stash
+
+    // (3) the crack step, by warp 0
+    if (stepping && tid < 32) {
+        const bool pending = !sS.r.decided;   // not yet applied by a deferred crack step
+        if (both) {
+            // both ends in this CTA: lanes 0-15 evaluate the right end and
+            // lanes 16-31 the left end at once, on the same state (the
+            // criteria of both ends before either advances); lane 0 then
+            // advances the right end and the left end in turn
+            const bool act_r = p.mode != CRACK_NONE && !sS.r.decided;
+            const bool act_l = p.mode != CRACK_NONE && !sS.l.decided;
+            const CrackSums c = crack_eval_warp<T, 16>(p, a.w_in, a.pitch, a.cut_v, sS, tid < 16 ? +1 : -1, st);
+            // each end's criterion (the FP64 part) in its half warp's first
+            // lane at once: lane 0 the right end, lane 16 the left end
+            CrackDecision dd = {};
+            if ((tid & 15) == 0) dd = crack_decide(p, sS, tid < 16 ? +1 : -1, c);
+            CrackSums cl;
+            cl.num = __shfl_sync(0xffffffffu, c.num, 16);
+            cl.den = __shfl_sync(0xffffffffu, c.den, 16);
+            cl.r_min = __shfl_sync(0xffffffffu, c.r_min, 16);
+            cl.np = __shfl_sync(0xffffffffu, c.np, 16);
+            CrackDecision dl;
+            dl.K = __shfl_sync(0xffffffffu, dd.K, 16);
+            dl.v = __shfl_sync(0xffffffffu, dd.v, 16);
+            dl.dq = __shfl_sync(0xffffffffu, dd.dq, 16);
+            dl.propagate = __shfl_sync(0xffffffffu, dd.propagate, 16);
+            dl.flags = __shfl_sync(0xffffffffu, dd.flags, 16);
+            if (tid == 0) {
+                if (act_r) crack_commit(p, a.cut_v, a.hist, sS, +1, commit, c, dd);
+                if (act_l) crack_commit(p, a.cut_v, a.hist, sS, -1, commit, cl, dl);
+                sS.r.decided = 1;
+                sS.l.decided = 1;
+            }
+            __syncwarp();
+        } else {
+            if (right_here) crack_step_warp<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, +1, commit, st);
+            if (left_here) crack_step_warp<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, -1, commit, st);
+        }
+        if (tid == 0 && commit) {
+            CrackState *o = a.s_out;
+            const int64_t n = sS.step + 1;
+            if (right_here) {
+                o->step = n;
+                o->hist_n = sS.hist_n + (pending ? 1 : 0);
+                o->i_last = sS.i_last;
+                if (!p.two_tips) o->i_first = sS.i_first;
+                o->r = sS.r;
+                o->r.decided = 0;
+                // the Dirichlet values of the next step come from another
+                // CTA when there is one (see step_cta): their FP64 sin of
+                // the sin^2 and half-sine loads stays off this CTA's path
+                if (a.n_bands <= 2)
+                    for (int e = 0; e < 4; ++e)
+                        o->wstar[e] = a.edge[e] == EDGE_DIRICHLET ? load_value(a.load[e], n, (double)p.dt) : 0.0;
+            }
+            if (left_here) {
+                o->i_first = sS.i_first;
+                o->l = sS.l;
+                o->l.decided = 0;
+            }
+            if (REC) {
+                const int64_t t = n - 1 - *rec_n0;
+                if (t >= 0 && t < rec_n_steps) {
+                    if (right_here) rec_il[t] = sS.i_last;
+                    if (right_here && !p.two_tips) rec_if[t] = sS.i_first;
+                    if (left_here) rec_if[t] = sS.i_first;
+                }
+            }
+        }
+    }
+    __syncthreads();   // the decision
+
+    // (4) the rows.  The links this step severed: an end moves less than one
+    // spacing per step, so they are the columns between the old and the new
+    // last (first) cut link, (il0, i_last] on the right, [i_first, if0) on
+    // the left
+    const int il1 = sS.i_last, if1 = sS.i_first;
+    uint32_t fresh = 0u;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const int i = x0 + k;
+        if ((i > il0 && i <= il1) || (i >= if1 && i < if0)) fresh |= 1u << k;
+    }
+    const uint32_t cut = x0 < nx ? (cut0 | fresh) : 0u;
     R o[HH], od[HH];
 #pragma unroll
     for (int q = 0; q < HH; ++q) {
@@ -132,7 +227,7 @@ __device__ __noinline__ T crack_rows(const T *w_in_, T *w_out_, D *wd_, T wd_sca
         const uint32_t cut_dn = (!below && j == jc) ? cut : 0u;
         row_update(a, E, x0, j, w[q + 1], w[q + 2], w[q], wd[q], left0, rightN, cut_up, cut_dn, o[q], od[q]);
     }
-    if (HH >= 3 && a.macro && cut) {
+    if (HH >= 3 && p.macro && cut) {
         // x_B on row jc-1 (x_I, x_II on jc-2, jc-3) or on row jc (jc+1, jc+2)
         const int qb = below ? HH - 1 : 0, qi = below ? HH - 2 : 1, qii = below ? HH - 3 : 2;
 #pragma unroll
@@ -143,7 +238,7 @@ __device__ __noinline__ T crack_rows(const T *w_in_, T *w_out_, D *wd_, T wd_sca
                 o[qb].v[k] = wB;
             }
     }
-    if (x0 < a.nx) {
+    if (x0 < nx) {
 #pragma unroll
         for (int q = 0; q < HH; ++q) {
             store_row(a, x0, j0 + q, o[q], od[q], acc);
@@ -161,9 +256,14 @@ __device__ __noinline__ T crack_rows(const T *w_in_, T *w_out_, D *wd_, T wd_sca
 // warp shuffles; lanes 0 and 31 load the halo column.  The next row's loads
 // are issued before the current row is computed.  EDGE = false is the
 // interior version (no edge row or column in the warp): the bare update.
-template <typename T, typename D, bool EDGE, int TH = kThreads, bool COH = false>
+template <typename T, typename D, bool EDGE, int TH = kThreads, bool COH = false, int LA = 1>
 __device__ __forceinline__ void march(const StepArgs<T, D> &a, int cb, int j0, int j1, T &acc)
 {
+    // LA: how many rows ahead of row j + 1 the w rows (and the halo values
+    // of lanes 0 and 31) are loaded: 1 keeps row j + 2 in flight while row j
+    // is updated, 2 keeps rows j + 2 and j + 3 (a second row of loads in
+    // flight per warp for short bands, at eight more registers)
+    static_assert(LA == 1 || LA == 2, "lookahead of one or two rows");
     constexpr int N = Vec<T>::N;
     typedef Row<T, N> R;
     const unsigned kFull = 0xffffffffu;
@@ -174,20 +274,25 @@ __device__ __forceinline__ void march(const StepArgs<T, D> &a, int cb, int j0, i
     T *wout = a.w_out + x0;
     D *wdp = a.wd + x0;
     const T wd_inv = a.wd_inv, wd_scale = a.wd_scale;
-    R wb, wc, wa, wdv;
+    R wb, wc, wa, wq, wdv;
     load_w<COH>(win + (int64_t)(j0 - 1) * P, wb);
     load_w<COH>(win + (int64_t)j0 * P, wc);
     load_w<COH>(win + (int64_t)(j0 + 1) * P, wa);
+    if (LA == 2 && j0 + 1 < j1) load_w<COH>(win + (int64_t)(j0 + 2) * P, wq);
     WdIO<D>::load(wdp + (int64_t)j0 * P, wdv, wd_inv);
-    // 16-bit wdot rows carry half the bytes of an FP32 row: keep two in
-    // flight (rows j + 1 and j + 2) so that a warp has as many wdot bytes
-    // outstanding as in FP32
-    constexpr bool DEEP = sizeof(D) == 2;
+    // wdot rows two ahead (rows j + 1 and j + 2 in flight) with a lookahead
+    // of two, and for 16-bit wdot rows, which carry half the bytes of an
+    // FP32 row, so that a warp has as many wdot bytes outstanding as in FP32
+    constexpr bool WD2 = sizeof(D) == 2 || LA == 2;
     typename WdIO<D>::Raw wdq1;
-    if (DEEP && j0 + 1 < j1) WdIO<D>::fetch(wdp + (int64_t)(j0 + 1) * P, wdq1);
-    T hl = (T)0, hr = (T)0;
+    if (WD2 && j0 + 1 < j1) WdIO<D>::fetch(wdp + (int64_t)(j0 + 1) * P, wdq1);
+    T hl = (T)0, hr = (T)0, hlq = (T)0, hrq = (T)0;
     if (lane == 0) hl = win[(int64_t)j0 * P - 1];
     if (lane == 31) hr = win[(int64_t)j0 * P + N];
+    if (LA == 2 && j0 + 1 < j1) {
+        if (lane == 0) hlq = win[(int64_t)(j0 + 1) * P - 1];
+        if (lane == 31) hrq = win[(int64_t)(j0 + 1) * P + N];
+    }
     const T g = a.g, dt = a.dt;
     EdgeValues<T> E;
     if (EDGE) E = edge_values<T>(a.s_in);
@@ -196,9 +301,16 @@ __device__ __forceinline__ void march(const StepArgs<T, D> &a, int cb, int j0, i
         typename WdIO<D>::Raw wdn;   // converted after this row's update, when it has arrived
         T hln = (T)0, hrn = (T)0;
         const bool more = j + 1 < j1;
-        if (more) {
+        if (LA == 2) {
+            if (j + 2 < j1) {
+                load_w<COH>(win + (int64_t)(j + 3) * P, wn);
+                WdIO<D>::fetch(wdp + (int64_t)(j + 2) * P, wdn);
+                if (lane == 0) hln = win[(int64_t)(j + 2) * P - 1];
+                if (lane == 31) hrn = win[(int64_t)(j + 2) * P + N];
+            }
+        } else if (more) {
             load_w<COH>(win + (int64_t)(j + 2) * P, wn);
-            if (DEEP) {
+            if (WD2) {
                 if (j + 2 < j1) WdIO<D>::fetch(wdp + (int64_t)(j + 2) * P, wdn);
             } else {
                 WdIO<D>::fetch(wdp + (int64_t)(j + 1) * P, wdn);
@@ -232,15 +344,24 @@ __device__ __forceinline__ void march(const StepArgs<T, D> &a, int cb, int j0, i
         wb = wc;
         wc = wa;
         if (more) {
-            wa = wn;
-            if (DEEP) {
+            if (LA == 2) {
+                wa = wq;
+                wq = wn;
+                hl = hlq;
+                hr = hrq;
+                hlq = hln;
+                hrq = hrn;
+            } else {
+                wa = wn;
+                hl = hln;
+                hr = hrn;
+            }
+            if (WD2) {
                 WdIO<D>::unpack(wdq1, wdv, wd_inv);
                 wdq1 = wdn;
             } else {
                 WdIO<D>::unpack(wdn, wdv, wd_inv);
             }
-            hl = hln;
-            hr = hrn;
         }
     }
 }
@@ -371,7 +492,7 @@ __device__ __forceinline__ void march_bulk(const StepArgs<T, D> &a, int cb, int 
 // same launch wrote it).
 // ring: the shared-memory ring of the bulk march (nullptr: every CTA takes
 // the register march).
-template <typename T, typename D, bool REC, bool BOTH = false, int TH = kThreads, bool COH = false>
+template <typename T, typename D, bool REC, bool BOTH = false, int TH = kThreads, bool COH = false, int LA = 1>
 __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int band, CrackState &sS, const RecArgs &r,
                                          BulkRing<T, D> *ring = nullptr)
 {
@@ -385,108 +506,17 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
     T acc = (T)0;
 
     if (a.crack_band >= 0 && (band == a.crack_band || (band == a.crack_band + 1 && p.sides == 3))) {
-        // The crack step of Alg. 1 that follows the previous LBM step, by the
-        // two crack sub-band CTAs that own the next link of each end: both
-        // reach the same decision; the lower one records it, each end
-        // writing only its own fields of the next state.  (A row slab whose
-        // boundary is the crack line holds one of the two sub-bands and
-        // reads the other side's row from its halo: it records its own.)
-        const int cols = TH * N;
-        int i_next = a.s_in->i_last + 1;
-        i_next = max(i_next, a.s_in->i_first);
-        i_next = min(max(i_next, 0), nx - 1);
-        int i_prev = a.s_in->i_first - 1;
-        i_prev = min(i_prev, a.s_in->i_last);
-        i_prev = min(max(i_prev, 0), nx - 1);
-        const bool right_here = cb == i_next / cols;
-        const bool left_here = p.two_tips && cb == i_prev / cols;
-        const bool commit = band == a.crack_band;
-        const bool both = BOTH && right_here && left_here;
-        if ((right_here || left_here) && tid == 0) {
-            // the rows this CTA updates after the crack step, brought into L2
-            // while the crack step runs (its FP64 chain is the long pole)
-            const int hh = p.macro ? 3 : 1;
-            const int64_t xb = (int64_t)cb * TH * N;
-            for (int q = -1; q <= hh; ++q)
-                bulk_prefetch_l2(a.w_in + (int64_t)(j0 + q) * a.pitch + xb, (uint32_t)(TH * N * sizeof(T)));
-            for (int q = 0; q < hh; ++q)
-                bulk_prefetch_l2(a.wd + (int64_t)(j0 + q) * a.pitch + xb, (uint32_t)(TH * N * sizeof(D)));
-        }
-        if ((right_here || left_here) && tid < 32) {
-            if (tid == 0) sS = *a.s_in;
-            __syncwarp();
-            const bool pending = !sS.r.decided;   // not yet applied by a deferred crack step
-            if (both) {
-                // both ends in this CTA: lanes 0-15 evaluate the right end and
-                // lanes 16-31 the left end at once, on the same state (the
-                // criteria of both ends before either advances); lane 0 then
-                // advances the right end and the left end in turn
-                const bool act_r = p.mode != CRACK_NONE && !sS.r.decided;
-                const bool act_l = p.mode != CRACK_NONE && !sS.l.decided;
-                const CrackSums c = crack_eval_warp<T, 16>(p, a.w_in, a.pitch, a.cut_v, sS, tid < 16 ? +1 : -1);
-                // each end's criterion (the FP64 part) in its half warp's first
-                // lane at once: lane 0 the right end, lane 16 the left end
-                CrackDecision dd = {};
-                if ((tid & 15) == 0) dd = crack_decide(p, sS, tid < 16 ? +1 : -1, c);
-                CrackSums cl;
-                cl.num = __shfl_sync(0xffffffffu, c.num, 16);
-                cl.den = __shfl_sync(0xffffffffu, c.den, 16);
-                cl.r_min = __shfl_sync(0xffffffffu, c.r_min, 16);
-                cl.np = __shfl_sync(0xffffffffu, c.np, 16);
-                CrackDecision dl;
-                dl.K = __shfl_sync(0xffffffffu, dd.K, 16);
-                dl.v = __shfl_sync(0xffffffffu, dd.v, 16);
-                dl.dq = __shfl_sync(0xffffffffu, dd.dq, 16);
-                dl.propagate = __shfl_sync(0xffffffffu, dd.propagate, 16);
-                dl.flags = __shfl_sync(0xffffffffu, dd.flags, 16);
-                if (tid == 0) {
-                    if (act_r) crack_commit(p, a.cut_v, a.hist, sS, +1, commit, c, dd);
-                    if (act_l) crack_commit(p, a.cut_v, a.hist, sS, -1, commit, cl, dl);
-                    sS.r.decided = 1;
-                    sS.l.decided = 1;
-                }
-                __syncwarp();
-            } else {
-                if (right_here) crack_step_warp<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, +1, commit);
-                if (left_here) crack_step_warp<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, -1, commit);
-            }
-            if (tid == 0 && commit) {
-                CrackState *o = a.s_out;
-                const int64_t n = sS.step + 1;
-                if (right_here) {
-                    o->step = n;
-                    o->hist_n = sS.hist_n + (pending ? 1 : 0);
-                    o->i_last = sS.i_last;
-                    if (!p.two_tips) o->i_first = sS.i_first;
-                    o->r = sS.r;
-                    o->r.decided = 0;
-                    // the Dirichlet values of the next step come from another
-                    // CTA when there is one (see below): their FP64 sin of the
-                    // sin^2 and half-sine loads stays off this CTA's path
-                    if (a.n_bands <= 2)
-                        for (int e = 0; e < 4; ++e)
-                            o->wstar[e] = a.edge[e] == EDGE_DIRICHLET ? load_value(a.load[e], n, (double)p.dt) : 0.0;
-                }
-                if (left_here) {
-                    o->i_first = sS.i_first;
-                    o->l = sS.l;
-                    o->l.decided = 0;
-                }
-                if (REC) {
-                    const int64_t t = n - 1 - *r.n0;
-                    if (t >= 0 && t < r.n_steps) {
-                        if (right_here) r.i_last[t] = sS.i_last;
-                        if (right_here && !p.two_tips) r.i_first[t] = sS.i_first;
-                        if (left_here) r.i_first[t] = sS.i_first;
-                    }
-                }
-            }
-        }
-        const int edges = a.edge[0] | (a.edge[1] << 2) | (a.edge[2] << 4) | (a.edge[3] << 6);
-        acc = p.macro ? crack_rows<T, D, 3, TH, COH>(a.w_in, a.w_out, a.wd, a.wd_scale, a.pitch, a.nx, a.ny, p.jc,
-                                                p.macro, edges, a.g, a.dt, a.cut_v, a.words, a.s_in, cb, j0)
-                      : crack_rows<T, D, 1, TH, COH>(a.w_in, a.w_out, a.wd, a.wd_scale, a.pitch, a.nx, a.ny, p.jc,
-                                                p.macro, edges, a.g, a.dt, a.cut_v, a.words, a.s_in, cb, j0);
+        // a crack sub-band (and the crack step of Alg. 1 where it owns the
+        // next link of an end): out of line, on a copy of the arguments in
+        // shared memory (by assignment: no address of the parameter block)
+        __shared__ __align__(16) StepArgs<T, D> sA;
+        __shared__ PairStash<T> stash;
+        if (tid == 0) sA = a;
+        __syncthreads();
+        acc = p.macro ? crack_band<T, D, 3, TH, COH, BOTH, REC>(&sA, &sS, &stash, cb, band, j0, r.n0, r.n_steps,
+                                                               r.i_last, r.i_first)
+                      : crack_band<T, D, 1, TH, COH, BOTH, REC>(&sA, &sS, &stash, cb, band, j0, r.n0, r.n_steps,
+                                                               r.i_last, r.i_first);
     } else {
         if (a.crack_band < 0 && cb == 0 && band == 0 && tid == 0) {
             // no crack: only the step counter and the Dirichlet values advance
@@ -512,8 +542,8 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
         } else if (xw0 < nx) {
             // warps wholly right of the lattice (the ragged last column block)
             // have nothing to load or store
-            if (edge) march<T, D, true, TH, COH>(a, cb, j0, j1, acc);
-            else march<T, D, false, TH, COH>(a, cb, j0, j1, acc);
+            if (edge) march<T, D, true, TH, COH, LA>(a, cb, j0, j1, acc);
+            else march<T, D, false, TH, COH, LA>(a, cb, j0, j1, acc);
         }
     }
     // with a crack, the Dirichlet values w*(t_{n+1}) of the next step are
@@ -552,6 +582,8 @@ template <typename T, typename D, bool BOTH>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBlocks - 2) step_kernel(const StepArgs<T, D> a)
 {
     __shared__ CrackState sS;
+    pdl_wait();
+    pdl_trigger();
     step_cta<T, D, false, BOTH>(a, blockIdx.x, blockIdx.y, sS, RecArgs{});
 }
 
@@ -562,6 +594,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) step_kernel_bulk(const S
 {
     __shared__ CrackState sS;
     __shared__ __align__(128) BulkRing<T, D> ring;
+    pdl_wait();
+    pdl_trigger();
     step_cta<T, D, false, BOTH>(a, blockIdx.x, blockIdx.y, sS, RecArgs{}, &ring);
 }
 
@@ -579,19 +613,24 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
 // memory first.  TH threads per CTA: the column blocks of a batch are TH
 // vectors wide (TH * 4 FP32 columns), chosen per batch (lbm_batch_tune) so
 // that few warps fall right of their lattice.  Occupancy is register bound
-// at 64 registers, i.e. the same 32 warps per SM for every TH.
-template <typename T, typename D, int TH>
-__global__ void __launch_bounds__(TH, (sizeof(T) == 4 ? kMinBlocks : kMinBlocks - 2) * (kThreads / TH))
+// at 64 registers, i.e. the same 32 warps per SM for every TH.  LA: the
+// march's lookahead in rows; two rows take eight more registers (28 warps
+// per SM) for twice the loads in flight per warp.
+template <typename T, typename D, int TH, int LA>
+__global__ void __launch_bounds__(TH, (sizeof(T) == 4 ? kMinBlocks : kMinBlocks - 2) * (kThreads / TH) -
+                                          (LA == 2 ? kThreads / TH : 0))
     batch_step_kernel(const StepArgs<T, D> *descs, const BatchUnit *units, int par)
 {
     __shared__ CrackState sS;
     __shared__ __align__(16) StepArgs<T, D> sa;
+    pdl_wait();
+    pdl_trigger();
     const BatchUnit u = units[blockIdx.x];
     const uint32_t *src = reinterpret_cast<const uint32_t *>(descs + 2 * u.inst + par);
     uint32_t *dst = reinterpret_cast<uint32_t *>(&sa);
     for (int q = threadIdx.x; q < (int)(sizeof(StepArgs<T, D>) / 4); q += TH) dst[q] = src[q];
     __syncthreads();
-    step_cta<T, D, false, false, TH>(sa, u.cb, u.band, sS, RecArgs{});
+    step_cta<T, D, false, false, TH, false, LA>(sa, u.cb, u.band, sS, RecArgs{});
 }
 
 // ----------------------------------------- persistent batched step
@@ -747,18 +786,14 @@ template <typename T, typename D>
 cudaError_t launch_step(const StepArgs<T, D> &a, int bands, cudaStream_t s, bool bulk)
 {
     const dim3 grid((unsigned)a.ncb, (unsigned)bands);
+    const bool ch = a.chained != 0;
     if constexpr (sizeof(T) == 4) {
-        if (bulk) {
-            if (a.p.two_tips) step_kernel_bulk<T, D, true><<<grid, kThreads, 0, s>>>(a);
-            else step_kernel_bulk<T, D, false><<<grid, kThreads, 0, s>>>(a);
-            return cudaGetLastError();
-        }
+        if (bulk)
+            return a.p.two_tips ? launch_chained(step_kernel_bulk<T, D, true>, grid, dim3(kThreads), 0, s, ch, a)
+                                : launch_chained(step_kernel_bulk<T, D, false>, grid, dim3(kThreads), 0, s, ch, a);
     }
-    if (a.p.two_tips)
-        step_kernel<T, D, true><<<grid, kThreads, 0, s>>>(a);
-    else
-        step_kernel<T, D, false><<<grid, kThreads, 0, s>>>(a);
-    return cudaGetLastError();
+    return a.p.two_tips ? launch_chained(step_kernel<T, D, true>, grid, dim3(kThreads), 0, s, ch, a)
+                        : launch_chained(step_kernel<T, D, false>, grid, dim3(kThreads), 0, s, ch, a);
 }
 
 template <typename T>
@@ -769,27 +804,45 @@ cudaError_t launch_step_rec(const StepArgs<T, T> &a, const RecArgs &r, int bands
 }
 
 template <typename T, typename D>
-cudaError_t batch_step_kernel_ptr(int threads, const void **fn)
+cudaError_t batch_step_kernel_ptr(int threads, int lookahead, const void **fn)
 {
+    const bool deep = lookahead == 2;
+    if (lookahead != 1 && !deep) return cudaErrorInvalidValue;
     switch (threads) {
-    case 32: *fn = reinterpret_cast<const void *>(&batch_step_kernel<T, D, 32>); return cudaSuccess;
-    case 64: *fn = reinterpret_cast<const void *>(&batch_step_kernel<T, D, 64>); return cudaSuccess;
-    case kThreads: *fn = reinterpret_cast<const void *>(&batch_step_kernel<T, D, kThreads>); return cudaSuccess;
+    case 32:
+        *fn = deep ? reinterpret_cast<const void *>(&batch_step_kernel<T, D, 32, 2>)
+                   : reinterpret_cast<const void *>(&batch_step_kernel<T, D, 32, 1>);
+        return cudaSuccess;
+    case 64:
+        *fn = deep ? reinterpret_cast<const void *>(&batch_step_kernel<T, D, 64, 2>)
+                   : reinterpret_cast<const void *>(&batch_step_kernel<T, D, 64, 1>);
+        return cudaSuccess;
+    case kThreads:
+        *fn = deep ? reinterpret_cast<const void *>(&batch_step_kernel<T, D, kThreads, 2>)
+                   : reinterpret_cast<const void *>(&batch_step_kernel<T, D, kThreads, 1>);
+        return cudaSuccess;
     default: return cudaErrorInvalidValue;
     }
 }
 
 template <typename T, typename D>
 cudaError_t launch_batch_step(const StepArgs<T, D> *descs, const BatchUnit *units, int n_units, int par, cudaStream_t s,
-                              int threads)
+                              int threads, int lookahead, bool chained)
 {
-    switch (threads) {
-    case 32: batch_step_kernel<T, D, 32><<<(unsigned)n_units, 32, 0, s>>>(descs, units, par); break;
-    case 64: batch_step_kernel<T, D, 64><<<(unsigned)n_units, 64, 0, s>>>(descs, units, par); break;
-    case kThreads: batch_step_kernel<T, D, kThreads><<<(unsigned)n_units, kThreads, 0, s>>>(descs, units, par); break;
-    default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
+    const void *fn = nullptr;
+    cudaError_t e = batch_step_kernel_ptr<T, D>(threads, lookahead, &fn);
+    if (e != cudaSuccess) return e;
+    void *args[] = {(void *)&descs, (void *)&units, (void *)&par};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)n_units);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = chained ? 1 : 0;
+    return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 // ------------------------------------------ wdot planes in 16-bit storage
@@ -1064,6 +1117,8 @@ __device__ __forceinline__ void edge_rule_at(const StepArgs<T, D> &a, int t)
 template <typename T, typename D>
 __global__ void __launch_bounds__(128) edge_rule_kernel(const StepArgs<T, D> a)
 {
+    pdl_wait();
+    pdl_trigger();
     edge_rule_at(a, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
@@ -1073,6 +1128,8 @@ __global__ void __launch_bounds__(128) edge_rule_kernel(const StepArgs<T, D> a)
 template <typename T, typename D>
 __global__ void __launch_bounds__(128) batch_edge_rule_kernel(const StepArgs<T, D> *descs, const BatchUnit *units, int par)
 {
+    pdl_wait();
+    pdl_trigger();
     const BatchUnit u = units[blockIdx.x];
     edge_rule_at(descs[2 * u.inst + par], u.cb + (int)threadIdx.x);
 }
@@ -1092,8 +1149,7 @@ cudaError_t launch_edge_rule(const StepArgs<T, D> &a, cudaStream_t s)
 {
     const int n = edge_rule_sites(a);
     if (n == 0) return cudaSuccess;
-    edge_rule_kernel<T, D><<<(n + 127) / 128, 128, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_chained(edge_rule_kernel<T, D>, dim3((unsigned)((n + 127) / 128)), dim3(128), 0, s, a.chained != 0, a);
 }
 
 template <typename T, typename D>
@@ -1104,11 +1160,11 @@ int edge_rule_count(const StepArgs<T, D> &a)
 
 template <typename T, typename D>
 cudaError_t launch_batch_edge_rule(const StepArgs<T, D> *descs, const BatchUnit *units, int n_units, int par,
-                                   cudaStream_t s)
+                                   cudaStream_t s, bool chained)
 {
     if (n_units <= 0) return cudaSuccess;
-    batch_edge_rule_kernel<T, D><<<(unsigned)n_units, 128, 0, s>>>(descs, units, par);
-    return cudaGetLastError();
+    return launch_chained(batch_edge_rule_kernel<T, D>, dim3((unsigned)n_units), dim3(128), 0, s, chained, descs, units,
+                          par);
 }
 
 // ------------------------------------------------------ periodic pad images
@@ -1159,10 +1215,10 @@ template cudaError_t launch_step<float, __nv_bfloat16>(const StepArgs<float, __n
 template cudaError_t launch_step<float, __half>(const StepArgs<float, __half> &, int, cudaStream_t, bool);
 template cudaError_t launch_step_rec<double>(const StepArgs<double, double> &, const RecArgs &, int, cudaStream_t);
 template cudaError_t launch_step_rec<float>(const StepArgs<float, float> &, const RecArgs &, int, cudaStream_t);
-template cudaError_t launch_batch_step<double, double>(const StepArgs<double, double> *, const BatchUnit *, int, int, cudaStream_t, int);
-template cudaError_t launch_batch_step<float, float>(const StepArgs<float, float> *, const BatchUnit *, int, int, cudaStream_t, int);
-template cudaError_t launch_batch_step<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> *, const BatchUnit *, int, int, cudaStream_t, int);
-template cudaError_t launch_batch_step<float, __half>(const StepArgs<float, __half> *, const BatchUnit *, int, int, cudaStream_t, int);
+template cudaError_t launch_batch_step<double, double>(const StepArgs<double, double> *, const BatchUnit *, int, int, cudaStream_t, int, int, bool);
+template cudaError_t launch_batch_step<float, float>(const StepArgs<float, float> *, const BatchUnit *, int, int, cudaStream_t, int, int, bool);
+template cudaError_t launch_batch_step<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> *, const BatchUnit *, int, int, cudaStream_t, int, int, bool);
+template cudaError_t launch_batch_step<float, __half>(const StepArgs<float, __half> *, const BatchUnit *, int, int, cudaStream_t, int, int, bool);
 template cudaError_t launch_batch_persistent<double, double>(const StepArgs<double, double> *, int, const BatchUnit *, int, const BatchUnit *, int, int, int64_t, GridBarrier *, uint32_t *, long long, int, cudaStream_t);
 template cudaError_t launch_batch_persistent<float, float>(const StepArgs<float, float> *, int, const BatchUnit *, int, const BatchUnit *, int, int, int64_t, GridBarrier *, uint32_t *, long long, int, cudaStream_t);
 template cudaError_t launch_batch_persistent<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> *, int, const BatchUnit *, int, const BatchUnit *, int, int, int64_t, GridBarrier *, uint32_t *, long long, int, cudaStream_t);
@@ -1177,26 +1233,26 @@ template int edge_rule_count<double, double>(const StepArgs<double, double> &);
 template int edge_rule_count<float, float>(const StepArgs<float, float> &);
 template int edge_rule_count<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> &);
 template int edge_rule_count<float, __half>(const StepArgs<float, __half> &);
-template cudaError_t launch_batch_edge_rule<double, double>(const StepArgs<double, double> *, const BatchUnit *, int, int, cudaStream_t);
-template cudaError_t launch_batch_edge_rule<float, float>(const StepArgs<float, float> *, const BatchUnit *, int, int, cudaStream_t);
-template cudaError_t launch_batch_edge_rule<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> *, const BatchUnit *, int, int, cudaStream_t);
-template cudaError_t launch_batch_edge_rule<float, __half>(const StepArgs<float, __half> *, const BatchUnit *, int, int, cudaStream_t);
+template cudaError_t launch_batch_edge_rule<double, double>(const StepArgs<double, double> *, const BatchUnit *, int, int, cudaStream_t, bool);
+template cudaError_t launch_batch_edge_rule<float, float>(const StepArgs<float, float> *, const BatchUnit *, int, int, cudaStream_t, bool);
+template cudaError_t launch_batch_edge_rule<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> *, const BatchUnit *, int, int, cudaStream_t, bool);
+template cudaError_t launch_batch_edge_rule<float, __half>(const StepArgs<float, __half> *, const BatchUnit *, int, int, cudaStream_t, bool);
 template cudaError_t launch_edge_rule<double, double>(const StepArgs<double, double> &, cudaStream_t);
 template cudaError_t launch_edge_rule<float, float>(const StepArgs<float, float> &, cudaStream_t);
 template cudaError_t launch_edge_rule<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> &, cudaStream_t);
 template cudaError_t launch_edge_rule<float, __half>(const StepArgs<float, __half> &, cudaStream_t);
 template const void *step_kernel_ptr<float, Lf>(bool);
 template cudaError_t launch_step<float, Lf>(const StepArgs<float, Lf> &, int, cudaStream_t, bool);
-template cudaError_t launch_batch_step<float, Lf>(const StepArgs<float, Lf> *, const BatchUnit *, int, int, cudaStream_t, int);
+template cudaError_t launch_batch_step<float, Lf>(const StepArgs<float, Lf> *, const BatchUnit *, int, int, cudaStream_t, int, int, bool);
 template cudaError_t launch_batch_persistent<float, Lf>(const StepArgs<float, Lf> *, int, const BatchUnit *, int, const BatchUnit *, int, int, int64_t, GridBarrier *, uint32_t *, long long, int, cudaStream_t);
 template int edge_rule_count<float, Lf>(const StepArgs<float, Lf> &);
-template cudaError_t launch_batch_edge_rule<float, Lf>(const StepArgs<float, Lf> *, const BatchUnit *, int, int, cudaStream_t);
+template cudaError_t launch_batch_edge_rule<float, Lf>(const StepArgs<float, Lf> *, const BatchUnit *, int, int, cudaStream_t, bool);
 template cudaError_t launch_edge_rule<float, Lf>(const StepArgs<float, Lf> &, cudaStream_t);
-template cudaError_t batch_step_kernel_ptr<double, double>(int, const void **);
-template cudaError_t batch_step_kernel_ptr<float, float>(int, const void **);
-template cudaError_t batch_step_kernel_ptr<float, __nv_bfloat16>(int, const void **);
-template cudaError_t batch_step_kernel_ptr<float, __half>(int, const void **);
-template cudaError_t batch_step_kernel_ptr<float, Lf>(int, const void **);
+template cudaError_t batch_step_kernel_ptr<double, double>(int, int, const void **);
+template cudaError_t batch_step_kernel_ptr<float, float>(int, int, const void **);
+template cudaError_t batch_step_kernel_ptr<float, __nv_bfloat16>(int, int, const void **);
+template cudaError_t batch_step_kernel_ptr<float, __half>(int, int, const void **);
+template cudaError_t batch_step_kernel_ptr<float, Lf>(int, int, const void **);
 template cudaError_t launch_fill_pads<float>(float *, int64_t, int, int, const int32_t *, cudaStream_t);
 template cudaError_t launch_fill_pads<double>(double *, int64_t, int, int, const int32_t *, cudaStream_t);
 

@@ -681,6 +681,8 @@ template <typename T, typename D>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBlocks - 2)
     line_step_kernel(const StepArgs<T, D> a)
 {
+    pdl_wait();
+    pdl_trigger();
     constexpr int N = Vec<T>::N;
     __shared__ CrackState sS;
     __shared__ Claims sC;                 // the claims and edge values, formed once per block
@@ -771,12 +773,13 @@ __device__ __forceinline__ void face_unsupported(const StepArgs<T, D> &a)
 
 // The macroscopic rule on the faces of a crack in any direction (Sec. 3.1),
 // after the march: chunk blockIdx.x of the table (see FaceChunk), one CTA
-// each.  A CTA whose own entries hold no point leaves at once.  The others
-// gather, for every item, in one parallel pass: whether it is a point, its
-// current w (this step's update), the part of its sum over corners that are
-// no table entry (fixed during the solve), its own site's weight and its
-// coupled corners' weights and item indices -- all into shared memory.  Then
-// they solve the points level by level from shared memory alone: w_B = base
+// each, a thread per item.  Each CTA gathers, for every item, in one
+// parallel pass: whether it is a point, its current w (this step's update),
+// the part of its sum over corners that are no table entry (fixed during the
+// solve), its own site's weight and its coupled corners' weights and item
+// indices -- all into shared memory.  A CTA whose own entries hold no point
+// then leaves.  The others solve the points level by level from shared
+// memory alone: w_B = base
 // + sum over coupled corners of a_k w(corner) reads only lower levels (solved
 // points, or the update of items that are no point) and its own site, whose
 // weight (below 0.2) is solved by a scalar iteration from the update
@@ -786,20 +789,19 @@ __device__ __forceinline__ void face_unsupported(const StepArgs<T, D> &a)
 // T (FP32 for FP32 storage: GB300's FP64 rate is a small fraction of its
 // FP32 rate).
 template <typename T, typename D>
-__global__ void __launch_bounds__(256) line_faces_chunk_kernel(const StepArgs<T, D> a, const LineFace *F,
-                                                               const FaceChunk *Cs, const FaceItem *I)
+__global__ void __launch_bounds__(kFaceItemsMax, 1) line_faces_chunk_kernel(const StepArgs<T, D> a, const FaceChunk *Cs,
+                                                                         const FaceItem *I)
 {
     extern __shared__ __align__(16) unsigned char face_smem[];
     __shared__ int slv[kFaceLevels + 1];
+    pdl_wait();
+    pdl_trigger();
     const int tid = threadIdx.x, nt = blockDim.x;
     const FaceChunk &C = Cs[blockIdx.x];
     const int64_t P = a.pitch;
     // the level offsets, read once (the level loop below must not wait on
     // a global load per level)
     for (int L = tid; L <= kFaceLevels; L += nt) slv[L] = C.lv[L];
-    int any = 0;
-    for (int c = C.own_lo + tid; c < C.own_hi; c += nt) any |= face_is_point(a, F[c].i, F[c].j);
-    if (!__syncthreads_or(any)) return;
     const int n = C.n;
     T *val = reinterpret_cast<T *>(face_smem);        // [n]
     T *base = val + n;                                 // [n]
@@ -808,17 +810,19 @@ __global__ void __launch_bounds__(256) line_faces_chunk_kernel(const StepArgs<T,
     int32_t *site = reinterpret_cast<int32_t *>(ac + 8 * n);  // [2 n] the item's (i, j)
     int16_t *kc = reinterpret_cast<int16_t *>(site + 2 * n);  // [8 n] coupled corners' items (-1: unused)
     uint8_t *act = reinterpret_cast<uint8_t *>(kc + 8 * n);   // [n] point (bit 0), own (bit 1), dropped (bit 2)
+    int own_point = 0;
     for (int l = tid; l < n; l += nt) {
         // the whole record and w at all its corners first (unused corners name
         // the site itself), so the loads go out together rather than one
         // dependent chain per corner
-        const FaceItem it = I[C.off + l];
-        const LineFace f = F[it.f];
+        const FaceItem &it = I[C.off + l];
+        const LineFace &f = it.rec;
         T wk[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) wk[k] = a.w_out[(int64_t)f.cj[k] * P + f.ci[k]];
-        act[l] = (face_is_point(a, f.i, f.j) ? 1 : 0) | (it.f >= C.own_lo && it.f < C.own_hi ? 2 : 0) |
-                 ((f.flags & FACE_DROPPED) ? 4 : 0);
+        const bool point = face_is_point(a, f.i, f.j), own = it.f >= C.own_lo && it.f < C.own_hi;
+        own_point |= point && own;
+        act[l] = (point ? 1 : 0) | (own ? 2 : 0) | ((f.flags & FACE_DROPPED) ? 4 : 0);
         site[2 * l] = f.i;
         site[2 * l + 1] = f.j;
         val[l] = a.w_out[(int64_t)f.j * P + f.i];
@@ -843,7 +847,8 @@ __global__ void __launch_bounds__(256) line_faces_chunk_kernel(const StepArgs<T,
         base[l] = b;
         aself[l] = s;
     }
-    __syncthreads();
+    // a CTA whose own entries hold no point has nothing to write
+    if (!__syncthreads_or(own_point)) return;
     int stuck = 0;
     for (int L = 0; L < kFaceLevels; ++L) {
         const int lo = slv[L], hi = slv[L + 1];
@@ -911,6 +916,8 @@ __global__ void __launch_bounds__(1024) line_faces_kernel(const StepArgs<T, D> a
 {
     __shared__ double sA[kFaceShared], sB[kFaceShared];
     __shared__ int n_act;
+    pdl_wait();
+    pdl_trigger();
     const int tid = threadIdx.x, nt = blockDim.x;
     const int64_t P = a.pitch;
     if (tid == 0) n_act = 0;
@@ -1029,13 +1036,12 @@ cudaError_t launch_line_faces(const StepArgs<T, D> &a, const LineFace *faces, in
     z.pos = z.list + nf;
     z.mask = reinterpret_cast<uint32_t *>(z.pos + nf);
     z.kpos = reinterpret_cast<int32_t *>(z.mask + nf);
-    line_faces_kernel<T, D><<<1, 1024, 0, s>>>(a, faces, nf, z);
-    return cudaGetLastError();
+    return launch_chained(line_faces_kernel<T, D>, dim3(1), dim3(1024), 0, s, a.chained != 0, a, faces, nf, z);
 }
 
 template <typename T, typename D>
-cudaError_t launch_line_faces_chunked(const StepArgs<T, D> &a, const LineFace *faces, const FaceChunk *chunks,
-                                      int n_chunks, const FaceItem *items, cudaStream_t s)
+cudaError_t launch_line_faces_chunked(const StepArgs<T, D> &a, const FaceChunk *chunks, int n_chunks,
+                                      const FaceItem *items, cudaStream_t s)
 {
     if (n_chunks <= 0) return cudaSuccess;
     // shared memory for kFaceItemsMax items: 11 T, 2 int32, 8 int16 and one byte each
@@ -1043,16 +1049,18 @@ cudaError_t launch_line_faces_chunked(const StepArgs<T, D> &a, const LineFace *f
     cudaError_t e = cudaFuncSetAttribute(line_faces_chunk_kernel<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    line_faces_chunk_kernel<T, D><<<(unsigned)n_chunks, 256, smem, s>>>(a, faces, chunks, items);
-    return cudaGetLastError();
+    // a thread per item a CTA can hold: the gather's chains of dependent
+    // loads (item record, face record, corner values) then go out in one round
+    return launch_chained(line_faces_chunk_kernel<T, D>, dim3((unsigned)n_chunks), dim3(kFaceItemsMax), smem, s,
+                          a.chained != 0, a, chunks, items);
 }
 
 template <typename T, typename D>
 cudaError_t launch_line_step(const StepArgs<T, D> &a, cudaStream_t s)
 {
     const unsigned bands = (unsigned)((a.ny + a.p.band - 1) / a.p.band);
-    line_step_kernel<T, D><<<1u + (unsigned)a.ncb * bands, kThreads, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_chained(line_step_kernel<T, D>, dim3(1u + (unsigned)a.ncb * bands), dim3(kThreads), 0, s,
+                          a.chained != 0, a);
 }
 
 template <typename T>
@@ -1080,10 +1088,10 @@ template cudaError_t launch_line_faces<float, __nv_bfloat16>(const StepArgs<floa
                                                             int, double *, cudaStream_t);
 template cudaError_t launch_line_faces<float, __half>(const StepArgs<float, __half> &, const LineFace *, int, double *,
                                                      cudaStream_t);
-template cudaError_t launch_line_faces_chunked<double, double>(const StepArgs<double, double> &, const LineFace *, const FaceChunk *, int, const FaceItem *, cudaStream_t);
-template cudaError_t launch_line_faces_chunked<float, float>(const StepArgs<float, float> &, const LineFace *, const FaceChunk *, int, const FaceItem *, cudaStream_t);
-template cudaError_t launch_line_faces_chunked<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> &, const LineFace *, const FaceChunk *, int, const FaceItem *, cudaStream_t);
-template cudaError_t launch_line_faces_chunked<float, __half>(const StepArgs<float, __half> &, const LineFace *, const FaceChunk *, int, const FaceItem *, cudaStream_t);
+template cudaError_t launch_line_faces_chunked<double, double>(const StepArgs<double, double> &, const FaceChunk *, int, const FaceItem *, cudaStream_t);
+template cudaError_t launch_line_faces_chunked<float, float>(const StepArgs<float, float> &, const FaceChunk *, int, const FaceItem *, cudaStream_t);
+template cudaError_t launch_line_faces_chunked<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> &, const FaceChunk *, int, const FaceItem *, cudaStream_t);
+template cudaError_t launch_line_faces_chunked<float, __half>(const StepArgs<float, __half> &, const FaceChunk *, int, const FaceItem *, cudaStream_t);
 template cudaError_t launch_line_step<double, double>(const StepArgs<double, double> &, cudaStream_t);
 template cudaError_t launch_line_step<float, float>(const StepArgs<float, float> &, cudaStream_t);
 template cudaError_t launch_line_step<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> &, cudaStream_t);

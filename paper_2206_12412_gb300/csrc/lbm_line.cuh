@@ -39,14 +39,19 @@ enum { FACE_DROPPED = 1 };
 // level among those corners.  Every coupled corner lies strictly farther
 // from the line than its point, so the levels are finite and a pass level
 // by level, each level reading only lower ones, solves the system exactly.
-// kl[k]: the item index (within the chunk) of corner k, or -1 when corner k
-// is not a table entry (or has weight 0).
+// An item carries a copy of its entry's record (so that the solve's gather
+// reads the item, then the corners' values: no dependent load of the table
+// between them), the entry's index f, and kl[k]: the item index (within the
+// chunk) of corner k, or -1 when corner k is not a table entry (or has
+// weight 0).
 constexpr int kFaceChunk = 256;      // entries a CTA owns
 constexpr int kFaceLevels = 64;      // deepest coupling the chunked solve takes
-constexpr int kFaceItemsMax = 1024;  // items a CTA holds in shared memory
+constexpr int kFaceItemsMax = 1024;  // items a CTA holds in shared memory (a thread each)
 struct FaceItem {
+    LineFace rec;
     int32_t f;
     int16_t kl[8];
+    int32_t pad;
 };
 struct FaceChunk {
     int32_t off, n, own_lo, own_hi;
@@ -70,7 +75,7 @@ constexpr size_t kLineFaceScratch = 3 * sizeof(double) + 3 * sizeof(int32_t) + 8
 template <typename T, typename D>
 cudaError_t launch_line_faces(const StepArgs<T, D> &a, const LineFace *faces, int nf, double *scratch, cudaStream_t s);
 template <typename T, typename D>
-cudaError_t launch_line_faces_chunked(const StepArgs<T, D> &a, const LineFace *faces, const FaceChunk *chunks,
-                                      int n_chunks, const FaceItem *items, cudaStream_t s);
+cudaError_t launch_line_faces_chunked(const StepArgs<T, D> &a, const FaceChunk *chunks, int n_chunks,
+                                      const FaceItem *items, cudaStream_t s);
 
 }  // namespace lbm

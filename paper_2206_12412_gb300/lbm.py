@@ -364,6 +364,12 @@ class Lattice:
         (lbm_set_bulk); same results."""
         _check(load_library().lbm_set_bulk(C.c_void_p(self.h), 1 if enable else 0))
 
+    def set_chained(self, enable: bool = True):
+        """Launch the kernels of consecutive steps chained by programmatic
+        dependent launch (lbm_set_chained; the default) or plainly; same
+        results."""
+        _check(load_library().lbm_set_chained(C.c_void_p(self.h), 1 if enable else 0))
+
     def set_face_solve(self, mode: int) -> bool:
         """0: the chunked solve of the line crack's macroscopic faces where
         the coupling allows it, 1: the one-CTA solve; returns whether the
@@ -517,11 +523,22 @@ def lbm_batch_get_shape(b: int):
     return {"threads": t.value, "band_rows": r.value}
 
 
+def lbm_batch_set_lookahead(b: int, rows: int):
+    _check(load_library().lbm_batch_set_lookahead(C.c_void_p(b), int(rows)))
+
+
+def lbm_batch_get_lookahead(b: int) -> int:
+    r = C.c_int32()
+    _check(load_library().lbm_batch_get_lookahead(C.c_void_p(b), C.byref(r)))
+    return r.value
+
+
 def lbm_batch_tune(b: int, trial_steps: int = 8):
     t, r, us, fc = C.c_int32(), C.c_int32(), C.c_double(), C.c_int32()
     _check(load_library().lbm_batch_tune(C.c_void_p(b), int(trial_steps), C.byref(t), C.byref(r), C.byref(us),
                                          C.byref(fc)))
-    return {"threads": t.value, "band_rows": r.value, "us_per_step": us.value, "from_cache": bool(fc.value)}
+    return {"threads": t.value, "band_rows": r.value, "lookahead": lbm_batch_get_lookahead(b),
+            "us_per_step": us.value, "from_cache": bool(fc.value)}
 
 
 def lbm_batch_set_persistent(b: int, enable: bool, budget_cycles: int = 0):
@@ -550,10 +567,18 @@ class Batch:
         lbm_batch_step(self.b, n)
 
     def info(self) -> dict:
-        return dict(lbm_batch_info(self.b), **lbm_batch_get_shape(self.b))
+        return dict(lbm_batch_info(self.b), **lbm_batch_get_shape(self.b), lookahead=lbm_batch_get_lookahead(self.b))
 
     def set_shape(self, threads: int, band_rows: int):
         lbm_batch_set_shape(self.b, threads, band_rows)
+
+    def set_lookahead(self, rows: int):
+        """Rows of loads the march keeps in flight ahead (1 or 2)."""
+        lbm_batch_set_lookahead(self.b, rows)
+
+    def set_chained(self, enable: bool = True):
+        """Chained launches of the batched step (lbm_batch_set_chained)."""
+        _check(load_library().lbm_batch_set_chained(C.c_void_p(self.b), 1 if enable else 0))
 
     def set_persistent(self, enable: bool = True, budget_cycles: int = 0):
         """One cooperative launch per lbm_batch_step call (grid barrier

@@ -199,6 +199,36 @@ def test_every_launch_shape_gives_the_solo_bits(gpu, storage, threads, rows):
     b.close()
 
 
+@pytest.mark.parametrize("storage", ["f32", "f64", "f32_bf16", "f32_f16", "f32_lf"])
+@pytest.mark.parametrize("threads,rows", [(32, 1), (64, 2), (128, 3), (32, 16), (128, 0)])
+def test_two_row_lookahead_gives_the_solo_bits(gpu, storage, threads, rows):
+    """The march with two rows of loads in flight (and bands of 1, 2 or 3
+    rows, where the lookahead runs past the band) is the same arithmetic:
+    each lattice ends bit-identical to its solo run."""
+    ps = mixed_problems()
+    solo = [gpu.Lattice(p, storage) for p in ps]
+    mem = [gpu.Lattice(p, storage) for p in ps]
+    for p, s, m in zip(ps, solo, mem):
+        if p["crack"]["mode"] == "none":
+            init = W.random_state(p["nx"], p["ny"], seed=21, dtype=np.float64 if storage == "f64" else np.float32)
+            s.set_fields(*init)
+            m.set_fields(*init)
+    b = gpu.Batch(mem)
+    b.set_shape(threads, rows)
+    b.set_lookahead(2)
+    info = b.info()
+    assert (info["threads"], info["band_rows"], info["lookahead"]) == (threads, rows, 2)
+    b.step(3)
+    b.step(130)
+    b.set_lookahead(1)
+    b.step(7)
+    for s in solo:
+        s.step(140)
+    for s, m in zip(solo, mem):
+        _same(s, m)
+    b.close()
+
+
 def test_tune_leaves_the_lattices_as_they_were_and_caches_the_shape(gpu):
     ps = W.batch_problems(12, seed=8)
     solo = [gpu.Lattice(p, "f32") for p in ps]
@@ -206,9 +236,10 @@ def test_tune_leaves_the_lattices_as_they_were_and_caches_the_shape(gpu):
     b = gpu.Batch(mem)
     b.step(37)                       # a pending crack step at the tuning call
     r = b.tune(trial_steps=6)
-    assert r["threads"] in (32, 64, 128) and r["band_rows"] in (0, 8, 16, 32, 64)
+    assert r["threads"] in (32, 64, 128) and r["band_rows"] in (0, 8, 16, 32, 64) and r["lookahead"] in (1, 2)
     assert not r["from_cache"] and r["us_per_step"] > 0
-    assert (b.info()["threads"], b.info()["band_rows"]) == (r["threads"], r["band_rows"])
+    info = b.info()
+    assert (info["threads"], info["band_rows"], info["lookahead"]) == (r["threads"], r["band_rows"], r["lookahead"])
     b.step(63)
     for s in solo:
         s.step(100)
@@ -219,7 +250,8 @@ def test_tune_leaves_the_lattices_as_they_were_and_caches_the_shape(gpu):
     mem2 = [gpu.Lattice(p, "f32") for p in ps]
     b2 = gpu.Batch(mem2)
     r2 = b2.tune(trial_steps=6)
-    assert r2["from_cache"] and (r2["threads"], r2["band_rows"]) == (r["threads"], r["band_rows"])
+    assert r2["from_cache"] and (r2["threads"], r2["band_rows"], r2["lookahead"]) == \
+        (r["threads"], r["band_rows"], r["lookahead"])
     b2.close()
 
 
@@ -230,6 +262,10 @@ def test_shape_arguments_are_checked(gpu):
     for t, r in ((48, 16), (256, 16), (32, -1)):
         with pytest.raises(gpu.LbmError) as ei:
             b.set_shape(t, r)
+        assert ei.value.status == -1
+    for la in (0, 3):
+        with pytest.raises(gpu.LbmError) as ei:
+            b.set_lookahead(la)
         assert ei.value.status == -1
     with pytest.raises(gpu.LbmError):
         b.tune(trial_steps=1)

@@ -220,6 +220,37 @@ def test_centre_crack_example_on_d2q9(oracle_mod, gpu, scale):
     o.close()
 
 
+@pytest.mark.parametrize("macro", [False, True])
+def test_band_shapes_give_the_same_bits(oracle_mod, gpu, macro):
+    """The D2Q9 step takes the handle's band table (the crack rows in
+    sub-bands of their own): bands of 1, 5 and 64 rows and the built-in
+    single-wave partition all give the oracle's run, and the same bits."""
+    nx, ny, jc = 300, 40, 20
+    p = _problem(nx, ny)
+    if macro:
+        p["bc_mode"] = "macroscopic"
+    p = W.with_crack(p, mode="prescribed", y=float(jc), x_start=120.3, x_tip=160.6, v_rel=0.6, two_tips=True)
+    p = W.with_antisymmetric_ramp(p, 1e-3, 50.0)
+    o = oracle_mod.Oracle(p)
+    o.step(150)
+    ref = None
+    for rows in (0, 1, 5, 64):
+        g = gpu.Lattice(p, "f32")
+        g.set_launch(rows)
+        g.step(7)
+        g.step(143)
+        _close(o, g, TOL["f32"])
+        np.testing.assert_array_equal(g.cut_mask("v"), o.cuts()[1].astype(bool))
+        np.testing.assert_array_equal(g.history()["tip_q"], o.history()["tip_q"])
+        w, wd = g.fields()
+        if ref is None:
+            ref = (w, wd)
+        else:
+            assert np.array_equal(ref[0], w) and np.array_equal(ref[1], wd)
+        g.close()
+    o.close()
+
+
 def test_kcrit_growth_fp64(oracle_mod, gpu):
     nx, ny = 160, 48
     p = _problem(nx, ny)
