@@ -477,10 +477,15 @@ void lbm_destroy(lbm_handle *h);
  *
  * lbm_batch_create groups n existing handles (not owned; they must outlive
  * the batch) of the same storage, on the same stream, stepped equally often.
- * It re-partitions every lattice into bands of band_rows rows (0: 16) and
+ * It re-partitions every lattice into bands of band_rows rows (0: 16; -1:
+ * the balanced step of lbm_batch_set_shape) and
  * uploads a table of the step-kernel arguments of every lattice and a table
  * of all their (lattice, column block, band) units; allocator as in
- * lbm_create (NULL: cudaMalloc).  D2Q5 lattices only.  Lattices with
+ * lbm_create (NULL: cudaMalloc).  All lattices of one velocity set: D2Q5,
+ * or D2Q9 (a D2Q9 batch takes CTAs of 128 threads over bands, a lookahead of
+ * one row, no balanced and no persistent form; its lattices with the
+ * macroscopic rule on their crack faces get it from one more batched launch
+ * per step, units of 128 columns).  Lattices with
  * LBM_BC_MACROSCOPIC_EDGES get their outer-edge rule from one more batched
  * launch per step (units of 128 edge sites).  While the batch exists, step its lattices
  * only through lbm_batch_step (stepping one alone makes lbm_batch_step return
@@ -502,7 +507,13 @@ lbm_status lbm_batch_info(const lbm_batch *b, int32_t *n_lattices, int32_t *ctas
  * columns) over bands of band_rows >= 1 rows (the crack rows keep bands of
  * their own), or with band_rows = 0 bands as tall as one wave of resident
  * CTAs allows, about equally tall in every lattice (long marches, few halo
- * rows, no second wave).  Narrow column blocks leave fewer idle warps right of lattices
+ * rows, no second wave), or with band_rows = -1 the balanced step: as many
+ * CTAs as are resident at once, each marching a run of row pieces of about
+ * the same total height (a lattice's rows outside its crack sub-bands are cut
+ * into row blocks of about one CTA's share, column block by column block, and
+ * that sequence into one run per CTA; the crack sub-bands stay units of their
+ * own), so that lattices of any heights fill one wave evenly; lbm_batch_info
+ * then reports those CTAs.  Narrow column blocks leave fewer idle warps right of lattices
  * whose width is not a multiple of 512 columns; short bands give more CTAs.
  * The results do not depend on the shape (each lattice's time step is the
  * same arithmetic).  lbm_batch_set_shape synchronises the stream and
@@ -527,7 +538,8 @@ lbm_status lbm_batch_get_lookahead(const lbm_batch *b, int32_t *rows);
 
 /* Autotuner of the batched step's launch shape: times trial_steps (2..1024)
  * batched steps with CUDA events for every shape of lookahead in {1, 2} x
- * threads in {32, 64, 128} x band_rows in {0 (one wave), 8, 16, 32, 64}
+ * threads in {32, 64, 128} x band_rows in {-1 (balanced), 0 (one wave), 8, 16,
+ * 32, 64}
  * (the first of three repetitions a warm-up), keeps the fastest (its
  * lookahead is read back with lbm_batch_get_lookahead), and caches it in the process under the device's SM
  * count, the storage and the lattices' sizes and crack rows (a later batch of

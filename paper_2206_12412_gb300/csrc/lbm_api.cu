@@ -1839,8 +1839,14 @@ struct lbm_batch {
     int n_units;
     BatchUnit *eunits;   // edge-rule units: 128 edge sites of one lattice (LBM_BC_MACROSCOPIC_EDGES)
     int n_eunits;
+    int q;               // velocity set of every member (5: D2Q5, 9: D2Q9)
+    BatchUnit *funits;   // D2Q9 crack-face units: 128 columns of one lattice with macroscopic crack faces
+    int n_funits;
+    BatchPiece *pieces;  // balanced step (band_rows = -1): the pieces of every CTA ...
+    int32_t *poff;       // ... CTA c runs pieces poff[c] .. poff[c + 1] - 1
+    int n_pcta;          // CTAs of the balanced step (0: the per-band launch)
     int threads;         // threads per CTA: column blocks of threads 16-byte vectors
-    int band_rows;       // rows per band (the crack sub-bands have their own height)
+    int band_rows;       // rows per band (the crack sub-bands have their own height); -1: balanced
     int lookahead;       // rows of loads the march keeps ahead (1 or 2)
     bool chained;        // each step's launches chained by programmatic dependent launch
     bool persistent;     // lbm_batch_step as one cooperative launch (grid barrier between steps)
@@ -1914,7 +1920,18 @@ template <typename T, typename D>
 cudaError_t enqueue_batch_step_t(const lbm_batch *b, int par, cudaStream_t s)
 {
     const StepArgs<T, D> *d = static_cast<const StepArgs<T, D> *>(b->descs);
-    cudaError_t e = launch_batch_step(d, b->units, b->n_units, par, s, b->threads, b->lookahead, b->chained);
+    if constexpr (std::is_same<T, D>::value) {
+        if (b->q == 9) {
+            cudaError_t e = launch_batch_d2q9(d, b->units, b->n_units, b->funits, b->n_funits, par, s, b->chained);
+            if (e == cudaSuccess && b->n_eunits > 0)
+                e = launch_batch_edge_rule(d, b->eunits, b->n_eunits, par, s, b->chained);
+            return e;
+        }
+    }
+    cudaError_t e = b->n_pcta > 0
+                        ? launch_batch_pieces(d, b->pieces, b->poff, b->n_pcta, par, s, b->threads, b->lookahead,
+                                              b->chained)
+                        : launch_batch_step(d, b->units, b->n_units, par, s, b->threads, b->lookahead, b->chained);
     if (e == cudaSuccess && b->n_eunits > 0) e = launch_batch_edge_rule(d, b->eunits, b->n_eunits, par, s, b->chained);
     return e;
 }
@@ -1940,6 +1957,17 @@ cudaError_t batch_kernel_ptr(int storage, int threads, int la, const void **fn)
     case LBM_F32_WD_F16: return batch_step_kernel_ptr<float, __half>(threads, la, fn);
     case LBM_F32_LEAPFROG: return batch_step_kernel_ptr<float, Lf>(threads, la, fn);
     default: return batch_step_kernel_ptr<double, double>(threads, la, fn);
+    }
+}
+
+cudaError_t batch_piece_ptr(int storage, int threads, int la, const void **fn)
+{
+    switch (storage) {
+    case LBM_F32: return batch_piece_kernel_ptr<float, float>(threads, la, fn);
+    case LBM_F32_WD_BF16: return batch_piece_kernel_ptr<float, __nv_bfloat16>(threads, la, fn);
+    case LBM_F32_WD_F16: return batch_piece_kernel_ptr<float, __half>(threads, la, fn);
+    case LBM_F32_LEAPFROG: return batch_piece_kernel_ptr<float, Lf>(threads, la, fn);
+    default: return batch_piece_kernel_ptr<double, double>(threads, la, fn);
     }
 }
 
@@ -2010,6 +2038,123 @@ lbm_status batch_one_wave(lbm_batch *b, int threads, int la, std::vector<int> &h
     return LBM_OK;
 }
 
+// The pieces of the balanced step (band_rows = -1).  Every lattice keeps its
+// band table (bands of 16 rows; the crack sub-bands are units of their own,
+// as in the per-band launch); the rows outside the crack sub-bands are cut
+// into row blocks about as tall as one CTA's share of all rows, column block
+// by column block, and this sequence (lattice by lattice, row block by row
+// block, column block by column block, a lattice's crack sub-band units
+// after its rows below the crack) is cut into one contiguous run per CTA of
+// equal weight (a row of a column block weighs 1, a crack sub-band unit its
+// rows plus four, for the loads it issues at once and the crack step).  So
+// every CTA marches about the same number of rows whatever the lattices'
+// heights, the CTAs of horizontally adjacent column blocks march the same
+// rows at about the same time (their halo columns meet in L2), and a piece
+// that would leave fewer than four rows of its row block is given them.
+lbm_status batch_plan_pieces(lbm_batch *b, int threads, int la, std::vector<BatchPiece> &pieces,
+                             std::vector<int32_t> &off)
+{
+    const void *fn = nullptr;
+    cudaError_t e = batch_piece_ptr(b->storage, threads, la, &fn);
+    if (e != cudaSuccess) return cuda_fail(e, "selecting the balanced batch kernel");
+    int bps = 0;
+    LBM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, threads, 0));
+    const int64_t slots = (int64_t)b->hs[0]->sms * std::max(bps, 1);
+    struct Item {
+        int32_t inst, cb, j0, j1, duty, weight;
+    };
+    // first pass: the number of CTAs (at least 16 rows each) and a CTA's share
+    int64_t weight = 0;
+    for (size_t i = 0; i < b->hs.size(); ++i) {
+        const lbm_handle *h = b->hs[i];
+        const int cols = threads * (int)(16 / h->esize);
+        const int ncb = (h->grid.nx + cols - 1) / cols;
+        const int hh = h->crack_band < 0 ? 0 : (h->cp.macro ? 3 : 1);
+        const int nsub = h->crack_band < 0 ? 0 : (h->cp.sides == 3 ? 2 : 1);
+        weight += (int64_t)ncb * (h->grid.ny - nsub * hh) + (int64_t)ncb * nsub * (hh + 4);
+    }
+    const int64_t n_cta = std::max<int64_t>(1, std::min<int64_t>(slots, weight / 16));
+    const double share = (double)weight / (double)n_cta;
+    std::vector<Item> seq;
+    for (size_t i = 0; i < b->hs.size(); ++i) {
+        const lbm_handle *h = b->hs[i];
+        const std::vector<Unit> &U = *h->units_h;
+        const int cols = threads * (int)(16 / h->esize);
+        const int ncb = (h->grid.nx + cols - 1) / cols;
+        if (ncb > 32767) return fail(LBM_ERR_ARG, "lattice too wide for the balanced batch");
+        const int cband = h->crack_band;
+        const int hh = cband < 0 ? 0 : (h->cp.macro ? 3 : 1);
+        const int nsub = cband < 0 ? 0 : (h->cp.sides == 3 ? 2 : 1);
+        auto is_crack = [&](int band) { return cband >= 0 && (band == cband || (band == cband + 1 && nsub == 2)); };
+        // the band that carries the per-step state duty in the per-band launch
+        const int dband = cband < 0 ? 0 : (h->n_bands > 2 ? (cband > 0 ? 0 : cband + nsub) : -1);
+        const int dkind = cband < 0 ? 1 : 2;
+        int band = 0;
+        while (band < h->n_bands) {
+            if (is_crack(band)) {
+                for (int cb = 0; cb < ncb; ++cb) seq.push_back({(int32_t)i, cb, -(band + 1), 0, 0, hh + 4});
+                ++band;
+                continue;
+            }
+            const int r0 = U[band].j0;
+            int r1 = U[band].j1;
+            const bool duty_here = band == dband;
+            ++band;
+            while (band < h->n_bands && !is_crack(band)) r1 = U[band++].j1;
+            // row blocks of about one CTA's share
+            const int H = r1 - r0;
+            const int nblk = std::max(1, (int)std::lround((double)H / std::max(share, 1.0)));
+            for (int k = 0; k < nblk; ++k) {
+                const int a0 = r0 + (int)((int64_t)H * k / nblk), a1 = r0 + (int)((int64_t)H * (k + 1) / nblk);
+                if (a1 <= a0) continue;
+                for (int cb = 0; cb < ncb; ++cb)
+                    seq.push_back({(int32_t)i, cb, a0, a1, (k == 0 && cb == 0 && duty_here) ? dkind : 0, a1 - a0});
+            }
+        }
+    }
+    // cut the sequence into n_cta runs, each about the weight left over the
+    // CTAs left (so that short runs early on do not pile work on the last)
+    pieces.clear();
+    off.assign(1, 0);
+    int64_t c = 0;
+    double load = 0.0, left = (double)weight;
+    double target = left / (double)n_cta;
+    auto next_cta = [&]() {
+        off.push_back((int32_t)pieces.size());
+        left -= load;
+        load = 0.0;
+        ++c;
+        target = left / (double)(n_cta - c);
+    };
+    for (const Item &it : seq) {
+        if (it.j0 < 0) {
+            if (load > 0.0 && load + 0.5 * it.weight > target && c < n_cta - 1) next_cta();
+            pieces.push_back({it.inst, (int16_t)it.cb, 0, it.j0, it.j1});
+            load += it.weight;
+            continue;
+        }
+        int r = it.j0;
+        bool first = true;
+        while (r < it.j1) {
+            if (load > 0.0 && load >= target - 0.5 && c < n_cta - 1) next_cta();
+            int take = c == n_cta - 1 ? it.j1 - r : std::max(1, (int)std::ceil(target - load - 1e-9));
+            take = std::min(take, it.j1 - r);
+            if (it.j1 - r - take < 4) take = it.j1 - r;   // no sliver of under four rows left behind
+            if (take < 4 && load > 0.0 && c < n_cta - 1 && it.j1 - r >= 4) {
+                next_cta();   // nor a piece of under four rows at a run's end
+                continue;
+            }
+            pieces.push_back({it.inst, (int16_t)it.cb, (int16_t)(first ? it.duty : 0), r, r + take});
+            first = false;
+            r += take;
+            load += take;
+        }
+    }
+    while (c < n_cta) next_cta();
+    if ((int64_t)off.size() != n_cta + 1) return fail(LBM_ERR_ARG, "balanced batch: inconsistent piece table");
+    return LBM_OK;
+}
+
 // Re-partition every lattice into bands of `rows` rows (0: the single-wave
 // heights of batch_one_wave) and rebuild the unit table for CTAs of
 // `threads` threads (column blocks of threads 16-byte vectors) and the
@@ -2019,9 +2164,14 @@ lbm_status batch_build(lbm_batch *b, int threads, int rows, int la)
 {
     if (threads != 32 && threads != 64 && threads != kThreads)
         return fail(LBM_ERR_ARG, "threads per CTA must be 32, 64 or 128");
-    if (rows < 0) return fail(LBM_ERR_ARG, "band_rows must be >= 0");
+    if (rows < -1) return fail(LBM_ERR_ARG, "band_rows must be >= 0, or -1 (balanced)");
     if (la != 1 && la != 2) return fail(LBM_ERR_ARG, "lookahead must be 1 or 2 rows");
-    std::vector<int> heights(b->hs.size(), rows);
+    if (b->q == 9 && (threads != kThreads || la != 1 || rows < 0))
+        return fail(LBM_ERR_ARG, "a D2Q9 batch takes CTAs of 128 threads, bands of rows >= 0 and a lookahead of one row");
+    const bool balanced = rows == -1;
+    // the balanced step keeps bands of 16 rows for its crack sub-bands and for
+    // the persistent form
+    std::vector<int> heights(b->hs.size(), balanced ? 16 : rows);
     if (rows == 0) {
         lbm_status rc = batch_one_wave(b, threads, la, heights);
         if (rc != LBM_OK) return rc;
@@ -2053,9 +2203,27 @@ lbm_status batch_build(lbm_batch *b, int threads, int rows, int la)
     case LBM_F32_LEAPFROG: fill_descs<float, Lf>(b, descs); edge_units<float, Lf>(b, eunits); break;
     default: fill_descs<double, double>(b, descs); edge_units<double, double>(b, eunits); break;
     }
+    // D2Q9 lattices with the macroscopic rule on their crack faces: units of
+    // 128 columns for the face launch that follows the update
+    std::vector<BatchUnit> funits;
+    if (b->q == 9)
+        for (size_t i = 0; i < b->hs.size(); ++i) {
+            const lbm_handle *h = b->hs[i];
+            if (!h->cp.macro || h->cp.mode == CRACK_NONE) continue;
+            for (int c0 = 0; c0 < h->grid.nx; c0 += 128) funits.push_back(BatchUnit{(int32_t)i, c0, 0, 0});
+        }
+    std::vector<BatchPiece> pieces;
+    std::vector<int32_t> poff;
+    if (balanced) {
+        lbm_status rc = batch_plan_pieces(b, threads, la, pieces, poff);
+        if (rc != LBM_OK) return rc;
+    }
     const size_t o_units = align256(descs.size());
     const size_t o_eunits = o_units + align256(units.size() * sizeof(BatchUnit));
-    const size_t need = o_eunits + std::max<size_t>(eunits.size(), 1) * sizeof(BatchUnit);
+    const size_t o_funits = o_eunits + align256(std::max<size_t>(eunits.size(), 1) * sizeof(BatchUnit));
+    const size_t o_pieces = o_funits + align256(std::max<size_t>(funits.size(), 1) * sizeof(BatchUnit));
+    const size_t o_poff = o_pieces + align256(pieces.size() * sizeof(BatchPiece));
+    const size_t need = o_poff + std::max<size_t>(poff.size(), 1) * sizeof(int32_t);
     if (need > b->block_bytes) {
         batch_release_block(b);
         b->block = batch_alloc(b, need);
@@ -2065,9 +2233,22 @@ lbm_status batch_build(lbm_batch *b, int threads, int rows, int la)
     b->descs = b->block;
     b->units = reinterpret_cast<BatchUnit *>(static_cast<char *>(b->block) + o_units);
     b->eunits = reinterpret_cast<BatchUnit *>(static_cast<char *>(b->block) + o_eunits);
+    b->funits = reinterpret_cast<BatchUnit *>(static_cast<char *>(b->block) + o_funits);
+    b->n_funits = (int)funits.size();
+    b->pieces = reinterpret_cast<BatchPiece *>(static_cast<char *>(b->block) + o_pieces);
+    b->poff = reinterpret_cast<int32_t *>(static_cast<char *>(b->block) + o_poff);
     b->n_units = (int)units.size();
     b->n_eunits = (int)eunits.size();
+    b->n_pcta = balanced ? (int)poff.size() - 1 : 0;
     cudaError_t e = cudaMemcpyAsync(b->descs, descs.data(), descs.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && !funits.empty())
+        e = cudaMemcpyAsync(b->funits, funits.data(), funits.size() * sizeof(BatchUnit), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess && balanced && !pieces.empty())
+        e = cudaMemcpyAsync(b->pieces, pieces.data(), pieces.size() * sizeof(BatchPiece), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess && balanced)
+        e = cudaMemcpyAsync(b->poff, poff.data(), poff.size() * sizeof(int32_t), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->units, units.data(), units.size() * sizeof(BatchUnit), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess && !eunits.empty())
@@ -2144,13 +2325,13 @@ lbm_status lbm_batch_create(lbm_handle *const *handles, int32_t n, int32_t band_
     if (!out) return fail(LBM_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!handles || n < 1) return fail(LBM_ERR_ARG, "need at least one lattice");
-    if (band_rows < 0) return fail(LBM_ERR_ARG, "band_rows must be >= 0");
+    if (band_rows < -1) return fail(LBM_ERR_ARG, "band_rows must be >= 0, or -1 (balanced)");
     for (int i = 0; i < n; ++i) {
         const lbm_handle *h = handles[i];
         if (!h) return fail(LBM_ERR_ARG, "a lattice handle is NULL");
         if (h->sticky != LBM_OK) return fail(h->sticky, "a lattice is in an error state");
         if (h->lat.storage != handles[0]->lat.storage) return fail(LBM_ERR_ARG, "all lattices need the same storage");
-        if (h->q != 5) return fail(LBM_ERR_ARG, "the batched step is built for D2Q5 only");
+        if (h->q != handles[0]->q) return fail(LBM_ERR_ARG, "all lattices need the same velocity set");
         if (h->line) return fail(LBM_ERR_ARG, "the batched step is built for cracks along +x");
         if (h->stream != handles[0]->stream) return fail(LBM_ERR_ARG, "all lattices need the same stream");
         if (h->parity != handles[0]->parity) return fail(LBM_ERR_STATE, "all lattices need the same number of steps");
@@ -2167,6 +2348,12 @@ lbm_status lbm_batch_create(lbm_handle *const *handles, int32_t n, int32_t band_
     b->cap_stream = nullptr;
     b->gexec = nullptr;
     b->gparity = -1;
+    b->q = handles[0]->q;
+    b->funits = nullptr;
+    b->n_funits = 0;
+    b->pieces = nullptr;
+    b->poff = nullptr;
+    b->n_pcta = 0;
     b->threads = kThreads;
     b->band_rows = 16;
     b->lookahead = 1;
@@ -2197,7 +2384,7 @@ lbm_status lbm_batch_create(lbm_handle *const *handles, int32_t n, int32_t band_
     }
     // bands of band_rows rows (default 16), CTAs of 128 threads: a batch has
     // many CTAs, no need to fit one wave; lbm_batch_tune picks a better shape
-    lbm_status rc = batch_build(b, kThreads, band_rows > 0 ? band_rows : 16, 1);
+    lbm_status rc = batch_build(b, kThreads, band_rows != 0 ? band_rows : 16, 1);
     if (rc != LBM_OK) return bail(rc);
     cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return bail(cuda_fail(e, "creating the capture stream"));
@@ -2318,13 +2505,15 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *threads, i
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return done(fail(LBM_ERR_CUDA, "creating timing events"));
     const int shapes_t[3] = {32, 64, kThreads};
-    const int shapes_r[5] = {0, 8, 16, 32, 64};   // 0: every CTA resident in one wave
+    const int shapes_r[6] = {-1, 0, 8, 16, 32, 64};   // -1: balanced pieces; 0: every CTA resident in one wave
     int best_t = b->threads, best_r = b->band_rows, best_la = b->lookahead;
     double best = 1e300;
     int par = b->hs[0]->parity;
-    for (int la = 1; la <= 2; ++la)
-        for (int ti = 0; ti < 3; ++ti)
-            for (int ri = 0; ri < 5; ++ri) {
+    // a D2Q9 batch: CTAs of 128 threads, a lookahead of one row, bands only
+    const bool d9 = b->q == 9;
+    for (int la = 1; la <= (d9 ? 1 : 2); ++la)
+        for (int ti = d9 ? 2 : 0; ti < 3; ++ti)
+            for (int ri = d9 ? 1 : 0; ri < 6; ++ri) {
                 rc = batch_build(b, shapes_t[ti], shapes_r[ri], la);
                 if (rc != LBM_OK) return done(rc);
                 double t_min = 1e300;
@@ -2430,7 +2619,7 @@ lbm_status lbm_batch_info(const lbm_batch *b, int32_t *n_lattices, int32_t *ctas
 {
     if (!b) return fail(LBM_ERR_ARG, "batch is NULL");
     if (n_lattices) *n_lattices = (int32_t)b->hs.size();
-    if (ctas) *ctas = b->n_units;
+    if (ctas) *ctas = b->n_pcta > 0 ? b->n_pcta : b->n_units;
     return LBM_OK;
 }
 
@@ -2449,6 +2638,7 @@ lbm_status lbm_batch_set_persistent(lbm_batch *b, int32_t enable, int64_t budget
 {
     if (!b) return fail(LBM_ERR_ARG, "batch is NULL");
     if (budget_cycles < 0 || budget_cycles > ((int64_t)1 << 40)) return fail(LBM_ERR_ARG, "budget out of range");
+    if (enable && b->q == 9) return fail(LBM_ERR_ARG, "the persistent batched step is built for D2Q5 only");
     b->persistent = enable != 0;
     b->budget = budget_cycles > 0 ? (long long)budget_cycles : (long long)1 << 31;
     clear_error();

@@ -50,19 +50,6 @@ __device__ __forceinline__ double load_value(const LoadDesc L, int64_t n, double
 // caller advances hist_n once per crack step).  Two CTAs may run it on the
 // same state at once: both reach the same decision and set the same bits.
 
-// The pair rows jc - 1 and jc of a crack sub-band CTA's columns x0 .. x0 + n
-// - 1 (w before the step; the CTA holds them in registers for its own
-// update), and each thread's cut bits of row jc - 1 for its N columns, so
-// that step (1) reads its window from shared memory when it lies in these
-// columns.  The window's links were severed in earlier steps (r > 0 behind
-// the tip), so the bits the crack step of this step adds never matter there.
-template <typename T> struct PairStash {
-    T above[kThreads * Vec<T>::N];   // row jc
-    T below[kThreads * Vec<T>::N];   // row jc - 1
-    uint8_t cut[kThreads];
-    int32_t x0, n;
-};
-
 // The least-squares sums of step (1) for one end: num = sum delta_i s_i,
 // den = sum s_i^2 over the np pairs in the window, and the window's r_min.
 struct CrackSums {
@@ -75,9 +62,8 @@ struct CrackSums {
 // gets the sums.  Reads S only.  All 32 lanes of the warp must call it.
 template <typename T, int G = 32>
 __device__ __forceinline__ CrackSums crack_eval_warp(const CrackParams &p, const T *w, int64_t P, const uint32_t *cut_v,
-                                                     const CrackState &S, int dir, const PairStash<T> *st = nullptr)
+                                                     const CrackState &S, int dir)
 {
-    constexpr int N = Vec<T>::N;
     const int lane = threadIdx.x & (G - 1);
     const TipState &E = dir > 0 ? S.r : S.l;
     const int64_t tip = E.tip_q;
@@ -100,27 +86,15 @@ __device__ __forceinline__ CrackSums crack_eval_warp(const CrackParams &p, const
     c_lo = c_lo < i_first ? i_first : c_lo;
     c_hi = c_hi > i_last ? i_last : c_hi;
     const int jc = p.jc;
-    const bool stashed = st != nullptr && c_lo >= st->x0 && c_hi < st->x0 + st->n;
     double num = 0.0, den = 0.0;
     int np = 0;
     for (int i = c_lo + lane; i <= c_hi; i += G) {
-        T above, below;
-        bool severed;
-        if (stashed) {
-            const int c = i - st->x0;
-            above = st->above[c];
-            below = st->below[c];
-            severed = (st->cut[c / N] >> (c % N)) & 1u;
-        } else {
-            // the pair's fields are loaded together with its mask word (the
-            // columns lie in [i_first, i_last], inside the lattice), so the
-            // two loads cost one round trip
-            const uint32_t word = cut_v[(int64_t)(jc - 1) * p.words + (i >> 5)];
-            above = w[(int64_t)jc * P + i];
-            below = w[(int64_t)(jc - 1) * P + i];
-            severed = (word >> (i & 31)) & 1u;
-        }
-        if (!severed) continue;
+        // the pair's fields are loaded together with its mask word (the
+        // columns lie in [i_first, i_last], inside the lattice), so the two
+        // loads cost one round trip
+        const uint32_t word = cut_v[(int64_t)(jc - 1) * p.words + (i >> 5)];
+        const T above = w[(int64_t)jc * P + i], below = w[(int64_t)(jc - 1) * P + i];
+        if (!((word >> (i & 31)) & 1u)) continue;
         const int64_t xq = (int64_t)(2 * i + 1) << (kQBits - 1);
         const double r_h = (double)(dir > 0 ? tip - xq : xq - tip) * kTwoM32;
         if (!(r_h >= lo && r_h < hi)) continue;
@@ -275,8 +249,7 @@ __device__ __forceinline__ void crack_apply(const CrackParams &p, uint32_t *cut_
 // Both steps for one end, by one warp (lane 0 applies).
 template <typename T>
 __device__ __forceinline__ void crack_step_warp(const CrackParams &p, const T *w, int64_t P, uint32_t *cut_v,
-                                                const History &hist, CrackState &S, int dir, bool commit,
-                                                const PairStash<T> *st = nullptr)
+                                                const History &hist, CrackState &S, int dir, bool commit)
 {
     const int lane = threadIdx.x & 31;
     TipState &E = dir > 0 ? S.r : S.l;
@@ -286,7 +259,7 @@ __device__ __forceinline__ void crack_step_warp(const CrackParams &p, const T *w
         __syncwarp();
         return;
     }
-    const CrackSums c = crack_eval_warp<T>(p, w, P, cut_v, S, dir, st);
+    const CrackSums c = crack_eval_warp<T>(p, w, P, cut_v, S, dir);
     if (lane == 0) crack_apply(p, cut_v, hist, S, dir, commit, c);
     __syncwarp();
 }

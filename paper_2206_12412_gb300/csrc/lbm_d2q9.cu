@@ -277,21 +277,18 @@ __device__ __forceinline__ T march9(const StepArgs<T, T> &a, int x0, int j0, int
 // own, one or three rows tall, so that the CTAs that run the pending crack
 // step first have few rows after it, and the other bands are as tall as one
 // wave of resident CTAs allows).
+// One CTA of the D2Q9 step: column block cb of band `band` of the lattice
+// that `a` describes (the kernel parameter block, or a copy in shared memory).
 template <typename T>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBlocks - 2)
-    d2q9_step_kernel(const StepArgs<T, T> a)
+__device__ __forceinline__ void d2q9_cta(const StepArgs<T, T> &a, int cb, int band, CrackState &sS)
 {
-    pdl_wait();
-    pdl_trigger();
     constexpr int N = Vec<T>::N;
     constexpr int cols = kThreads * N;
-    __shared__ CrackState sS;
     const int tid = threadIdx.x, lane = tid & 31;
     const int nx = a.nx, ny = a.ny, jc = a.p.jc;
-    const int cb = blockIdx.x;
     const int x0 = (cb * kThreads + tid) * N;
     const int xw0 = (cb * kThreads + (tid & ~31)) * N;
-    const Unit U = a.units[blockIdx.y];
+    const Unit U = a.units[band];
     const int j0 = U.j0, j1 = U.j1;
     const bool crack = a.p.mode != CRACK_NONE;
     const bool edge_warp = xw0 == 0 || xw0 + 32 * N - 1 >= nx - 1;
@@ -347,7 +344,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
             rq = s_in->r.tip_q;
             lq = p.two_tips ? s_in->l.tip_q : p.start_q;
         }
-    } else if (cb == 0 && blockIdx.y == 0 && tid == 0) {
+    } else if (cb == 0 && band == 0 && tid == 0) {
         // no crack: only the step counter and the Dirichlet values advance
         CrackState st = *s_in;
         const int64_t n = st.step + 1;
@@ -376,6 +373,36 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
 }
 
 template <typename T>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBlocks - 2)
+    d2q9_step_kernel(const StepArgs<T, T> a)
+{
+    __shared__ CrackState sS;
+    pdl_wait();
+    pdl_trigger();
+    d2q9_cta<T>(a, blockIdx.x, blockIdx.y, sS);
+}
+
+// Many D2Q9 lattices in one launch: CTA u runs unit u of the batch (column
+// block cb of band `band` of lattice inst) with its lattice's arguments for
+// the current parity copied to shared memory first; the per-CTA code is the
+// single-lattice kernel's, so each lattice ends bit-identical to its solo run.
+template <typename T>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBlocks - 2)
+    batch_d2q9_kernel(const StepArgs<T, T> *descs, const BatchUnit *units, int par)
+{
+    __shared__ CrackState sS;
+    __shared__ __align__(16) StepArgs<T, T> sa;
+    pdl_wait();
+    pdl_trigger();
+    const BatchUnit u = units[blockIdx.x];
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(descs + 2 * u.inst + par);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(&sa);
+    for (int q = threadIdx.x; q < (int)(sizeof(StepArgs<T, T>) / 4); q += kThreads) dst[q] = src[q];
+    __syncthreads();
+    d2q9_cta<T>(sa, u.cb, u.band, sS);
+}
+
+template <typename T>
 cudaError_t launch_d2q9_step(const StepArgs<T, T> &a, cudaStream_t s)
 {
     const dim3 grid((unsigned)a.ncb, (unsigned)a.n_bands);
@@ -391,11 +418,8 @@ cudaError_t launch_d2q9_step(const StepArgs<T, T> &a, cudaStream_t s)
 // the step (the cuts in force during it) is the one the update wrote to
 // s_out.  One thread per column; x_I, x_II are never boundary points.
 template <typename T>
-__global__ void __launch_bounds__(128) d2q9_face_kernel(const StepArgs<T, T> a)
+__device__ __forceinline__ void d2q9_face_at(const StepArgs<T, T> &a, int i)
 {
-    pdl_wait();
-    pdl_trigger();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.nx) return;
     const int nx = a.nx, jc = a.p.jc;
     const CrackState *st = a.s_out;
@@ -419,12 +443,49 @@ __global__ void __launch_bounds__(128) d2q9_face_kernel(const StepArgs<T, T> a)
 }
 
 template <typename T>
+__global__ void __launch_bounds__(128) d2q9_face_kernel(const StepArgs<T, T> a)
+{
+    pdl_wait();
+    pdl_trigger();
+    d2q9_face_at(a, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// The face rule of many D2Q9 lattices in one launch: unit u covers columns
+// u.cb .. u.cb + 127 of lattice u.inst.
+template <typename T>
+__global__ void __launch_bounds__(128) batch_d2q9_face_kernel(const StepArgs<T, T> *descs, const BatchUnit *units, int par)
+{
+    pdl_wait();
+    pdl_trigger();
+    const BatchUnit u = units[blockIdx.x];
+    d2q9_face_at(descs[2 * u.inst + par], u.cb + (int)threadIdx.x);
+}
+
+template <typename T>
 cudaError_t launch_d2q9_faces(const StepArgs<T, T> &a, cudaStream_t s)
 {
     return launch_chained(d2q9_face_kernel<T>, dim3((unsigned)((a.nx + 127) / 128)), dim3(128), 0, s, a.chained != 0,
                           a);
 }
 
+template <typename T>
+cudaError_t launch_batch_d2q9(const StepArgs<T, T> *descs, const BatchUnit *units, int n_units, const BatchUnit *funits,
+                             int n_funits, int par, cudaStream_t s, bool chained)
+{
+    cudaError_t e = cudaSuccess;
+    if (n_units > 0)
+        e = launch_chained(batch_d2q9_kernel<T>, dim3((unsigned)n_units), dim3(kThreads), 0, s, chained, descs, units,
+                           par);
+    if (e == cudaSuccess && n_funits > 0)
+        e = launch_chained(batch_d2q9_face_kernel<T>, dim3((unsigned)n_funits), dim3(128), 0, s, chained, descs, funits,
+                           par);
+    return e;
+}
+
+template cudaError_t launch_batch_d2q9<double>(const StepArgs<double, double> *, const BatchUnit *, int,
+                                               const BatchUnit *, int, int, cudaStream_t, bool);
+template cudaError_t launch_batch_d2q9<float>(const StepArgs<float, float> *, const BatchUnit *, int,
+                                              const BatchUnit *, int, int, cudaStream_t, bool);
 template cudaError_t launch_d2q9_faces<double>(const StepArgs<double, double> &, cudaStream_t);
 template cudaError_t launch_d2q9_faces<float>(const StepArgs<float, float> &, cudaStream_t);
 template cudaError_t launch_d2q9_step<double>(const StepArgs<double, double> &, cudaStream_t);

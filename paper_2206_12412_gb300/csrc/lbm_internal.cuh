@@ -201,6 +201,20 @@ struct BatchUnit {
     int32_t inst, cb, band, pad;
 };
 
+// One piece of work of a balanced batched step (band_rows = -1): rows j0 ..
+// j1 - 1 of column block cb of lattice inst, all outside its crack sub-bands,
+// or (j0 < 0) the whole crack sub-band number -j0 - 1 of the lattice's band
+// table.  duty: 1 = advance the step counter and the Dirichlet values of a
+// lattice without a crack, 2 = write the next step's Dirichlet values of a
+// lattice with one (the piece that holds the first row of the band the
+// per-band launch gives that duty), 0 = none.  A CTA of the balanced step
+// runs the pieces off[c] .. off[c + 1] - 1 one after another.
+struct BatchPiece {
+    int32_t inst;
+    int16_t cb, duty;
+    int32_t j0, j1;
+};
+
 // Recording of a forward run for the adjoint (see the adjoint kernel).  The
 // sensors of each unit (CTA of the step kernel: band * ncb + cb) are the
 // entries s_off[u] .. s_off[u+1]-1 of s_ent, each an index k into s_i / s_j.
@@ -275,6 +289,12 @@ template <typename T, typename D> cudaError_t batch_step_kernel_ptr(int threads,
 template <typename T, typename D>
 cudaError_t launch_batch_step(const StepArgs<T, D> *descs, const BatchUnit *units, int n_units, int par, cudaStream_t s,
                               int threads = kThreads, int lookahead = 1, bool chained = false);
+// The balanced batched step: n_cta CTAs, CTA c running pieces off[c] ..
+// off[c + 1] - 1.
+template <typename T, typename D> cudaError_t batch_piece_kernel_ptr(int threads, int lookahead, const void **fn);
+template <typename T, typename D>
+cudaError_t launch_batch_pieces(const StepArgs<T, D> *descs, const BatchPiece *pieces, const int32_t *off, int n_cta,
+                                int par, cudaStream_t s, int threads, int lookahead, bool chained);
 template <typename T, typename D>
 cudaError_t launch_step(const StepArgs<T, D> &a, int bands, cudaStream_t s, bool bulk = false);
 template <typename T, typename D> cudaError_t launch_edge_rule(const StepArgs<T, D> &a, cudaStream_t s);
@@ -284,6 +304,11 @@ cudaError_t launch_batch_edge_rule(const StepArgs<T, D> *descs, const BatchUnit 
                                    cudaStream_t s, bool chained = false);
 template <typename T> cudaError_t launch_d2q9_step(const StepArgs<T, T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_d2q9_faces(const StepArgs<T, T> &a, cudaStream_t s);
+// A batch of D2Q9 lattices: the step units, then the crack-face units (128
+// columns of one lattice with the macroscopic rule on its crack faces).
+template <typename T>
+cudaError_t launch_batch_d2q9(const StepArgs<T, T> *descs, const BatchUnit *units, int n_units, const BatchUnit *funits,
+                             int n_funits, int par, cudaStream_t s, bool chained);
 template <typename T> cudaError_t launch_step_rec(const StepArgs<T, T> &a, const RecArgs &r, int bands, cudaStream_t s);
 template <typename T> const void *adjoint_kernel_ptr();
 template <typename T> cudaError_t launch_adjoint(const AdjArgs<T> &a, int bands, cudaStream_t s);

@@ -45,50 +45,68 @@ namespace lbm {
 // sub-bands runs the march below, which holds no severed link (all severed
 // links of the straight crack lie between rows jc-1 and jc).  The crack
 // sub-bands (rows jc-3 .. jc-1 and jc .. jc+2 with the macroscopic rule, rows
-// jc-1 and jc otherwise) run crack_band; their CTAs that own the next crack
-// link also run the crack step of the previous time step.
+// jc-1 and jc otherwise) run crack_rows; their CTAs that own the next crack
+// link first run the crack step of the previous time step.
+
+// The fields of StepArgs that the crack sub-bands need.  Their out-of-line
+// code receives them as scalars and rebuilds this struct (taking the address
+// of the kernel parameter block would move all of it to local memory, and a
+// struct argument copied field by field from it was not passed reliably).
+template <typename T, typename D>
+struct RowArgs {
+    const T *w_in;
+    T *w_out;
+    D *wd;
+    T wd_scale, wd_inv;
+    int64_t pitch;
+    int32_t nx, ny, jc, macro;
+    int32_t edge[4];
+    T g, dt;
+    const uint32_t *cut_v;
+    int32_t words;
+    const CrackState *s_in;
+};
 
 // A crack sub-band of HH rows: rows jc-HH .. jc-1 (below the crack) or
-// jc .. jc+HH-1 (above), one CTA per column block, with the crack step of Alg.
-// 1 that follows the previous LBM step in the CTAs of the two sub-bands that
-// own the next link of an end (both reach the same decision; the lower one
-// records it, each end writing only its own fields of the next state; a row
-// slab whose boundary is the crack line holds one sub-band and reads the
-// other side's row from its halo, and records its own).  The CTA issues every
-// load of its rows and the load of the state at once (the rows do not depend
-// on the state), then hands the pair rows jc - 1 and jc it holds to the crack
-// step through shared memory, so the crack step's window costs no round trip
-// of its own when it lies in the CTA's columns; its rows are computed from
-// registers once the step has decided.  With the macroscopic crack-face rule
-// (Sec. 3.1, HH = 3), the boundary point x_B next to a severed link takes w_B
-// = 1.5 w_I - 0.5 w_II from the two new values of its column further away
-// from the crack, and wdot(x_B) = (w_B(t+dt) - w_B(t)) / dt.  The arguments
-// come from shared memory (a copy of the kernel's), as this code is out of
-// line.  Returns the sum the non-finite check reads.
-template <typename T, typename D, int HH, int TH, bool COH, bool BOTH, bool REC>
-__device__ __noinline__ T crack_band(const StepArgs<T, D> *ap, CrackState *sSp, PairStash<T> *st, int cb, int band,
-                                     int j0, const int64_t *rec_n0, int64_t rec_n_steps, int32_t *rec_il,
-                                     int32_t *rec_if)
+// jc .. jc+HH-1 (above).  All of its loads are issued at once, then the rows
+// are computed from registers, so the sub-band costs about one memory latency
+// even while the rest of the lattice saturates HBM.  With the macroscopic
+// crack-face rule (Sec. 3.1, HH = 3), the boundary point x_B next to a severed
+// link takes w_B = 1.5 w_I - 0.5 w_II from the two new values of its column
+// further away from the crack, and wdot(x_B) = (w_B(t+dt) - w_B(t)) / dt.
+template <typename T, typename D, int HH, int TH = kThreads, bool COH = false>
+__device__ __noinline__ T crack_rows(const T *w_in_, T *w_out_, D *wd_, T wd_scale_, int64_t pitch_, int nx_, int ny_,
+                                     int jc_, int macro_, int edges, T g_, T dt_, const uint32_t *cut_v_, int words_,
+                                     const CrackState *s_in_, int cb, int j0, int il0, int if0,
+                                     const CrackState *post)
 {
-    const StepArgs<T, D> &a = *ap;
-    CrackState &sS = *sSp;
-    const CrackParams &p = a.p;
+    RowArgs<T, D> a;
+    a.w_in = w_in_;
+    a.w_out = w_out_;
+    a.wd = wd_;
+    a.wd_scale = wd_scale_;
+    a.wd_inv = (T)1 / wd_scale_;
+    a.pitch = pitch_;
+    a.nx = nx_;
+    a.ny = ny_;
+    a.jc = jc_;
+    a.macro = macro_;
+    for (int e = 0; e < 4; ++e) a.edge[e] = (edges >> (2 * e)) & 3;
+    a.g = g_;
+    a.dt = dt_;
+    a.cut_v = cut_v_;
+    a.words = words_;
+    a.s_in = s_in_;
+    T acc = (T)0;
     constexpr int N = Vec<T>::N;
     typedef Row<T, N> R;
     const unsigned kFull = 0xffffffffu;
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int cols = TH * N;
-    const int nx = a.nx, jc = p.jc;
-    const int x0 = (cb * TH + tid) * N;
+    const int lane = threadIdx.x & 31;
+    const int x0 = (cb * TH + threadIdx.x) * N;
+    const int jc = a.jc;
     const int64_t P = a.pitch;
     const T *win = a.w_in + x0;
     const bool below = j0 + HH == jc;
-    T acc = (T)0;
-
-    // (1) every load at once: the state, the rows, the thread's cut bits
-    // before this step's crack step (bits of that step may or may not be in
-    // yet: the other sub-band CTA sets the same bits at its own pace)
-    if (tid == 0) sS = *a.s_in;
     R w[HH + 2], wd[HH];
     T hl[HH], hr[HH];
 #pragma unroll
@@ -99,122 +117,25 @@ __device__ __noinline__ T crack_band(const StepArgs<T, D> *ap, CrackState *sSp, 
         hl[q] = lane == 0 ? win[(int64_t)(j0 + q) * P - 1] : (T)0;
         hr[q] = lane == 31 ? win[(int64_t)(j0 + q) * P + N] : (T)0;
     }
-    const uint32_t cut0 = x0 < nx ? (a.cut_v[(int64_t)(jc - 1) * a.words + (x0 >> 5)] >> (x0 & 31)) & ((1u << N) - 1u) : 0u;
-    __syncthreads();   // the state
-
-    // (2) does this CTA own the next link of an end?  (The same for all its
-    // threads: the barriers below are uniform.)
-    const int il0 = sS.i_last, if0 = sS.i_first;   // before the crack step
-    int i_next = max(il0 + 1, if0);
-    i_next = min(max(i_next, 0), nx - 1);
-    int i_prev = min(if0 - 1, il0);
-    i_prev = min(max(i_prev, 0), nx - 1);
-    const bool right_here = cb == i_next / cols;
-    const bool left_here = p.two_tips && cb == i_prev / cols;
-    const bool commit = band == a.crack_band;
-    const bool both = BOTH && right_here && left_here;
-    const bool stepping = right_here || left_here;
-    const EdgeValues<T> E = edge_values<T>(&sS);   // wstar: the crack step leaves it alone
-    if (stepping) {
-        // the pair rows jc - 1 and jc of the CTA's columns (w[] holds rows
-        // j0 - 1 .. j0 + HH) and the cut bits, for the K fit
-        const int qa = below ? HH + 1 : 1, qb = below ? HH : 0;
+    const EdgeValues<T> E = edge_values<T>(a.s_in);
+    // the cut bits before this step's crack step (the other sub-band CTA may
+    // be setting its bits meanwhile: the same bits this CTA adds below)
+    const uint32_t cut0 = x0 < a.nx ? (a.cut_v[(int64_t)(jc - 1) * a.words + (x0 >> 5)] >> (x0 & 31)) & ((1u << N) - 1u) : 0u;
+    __syncthreads();   // the crack step of this CTA (post != nullptr) has decided
+    // the links the crack step severed: an end moves less than one spacing
+    // per step, so they are the columns between the old and the new last
+    // (first) severed link, (il0, i_last] on the right, [i_first, if0) on
+    // the left; a CTA that ran no crack step holds none of them
+    uint32_t fresh = 0u;
+    if (post != nullptr) {
+        const int il1 = post->i_last, if1 = post->i_first;
 #pragma unroll
         for (int k = 0; k < N; ++k) {
-            st->above[tid * N + k] = w[qa].v[k];
-            st->below[tid * N + k] = w[qb].v[k];
-        }
-        st->cut[tid] = (uint8_t)cut0;
-        if (tid == 0) {
-            st->x0 = cb * cols;
-            st->n = min(cols, nx - cb * cols);
+            const int i = x0 + k;
+            if ((i > il0 && i <= il1) || (i >= if1 && i < if0)) fresh |= 1u << k;
         }
     }
-    __syncthreads();   // every thread has il0, if0 (the crack step advances sS) and the stash
-
-    // (3) the crack step, by warp 0
-    if (stepping && tid < 32) {
-        const bool pending = !sS.r.decided;   // not yet applied by a deferred crack step
-        if (both) {
-            // both ends in this CTA: lanes 0-15 evaluate the right end and
-            // lanes 16-31 the left end at once, on the same state (the
-            // criteria of both ends before either advances); lane 0 then
-            // advances the right end and the left end in turn
-            const bool act_r = p.mode != CRACK_NONE && !sS.r.decided;
-            const bool act_l = p.mode != CRACK_NONE && !sS.l.decided;
-            const CrackSums c = crack_eval_warp<T, 16>(p, a.w_in, a.pitch, a.cut_v, sS, tid < 16 ? +1 : -1, st);
-            // each end's criterion (the FP64 part) in its half warp's first
-            // lane at once: lane 0 the right end, lane 16 the left end
-            CrackDecision dd = {};
-            if ((tid & 15) == 0) dd = crack_decide(p, sS, tid < 16 ? +1 : -1, c);
-            CrackSums cl;
-            cl.num = __shfl_sync(0xffffffffu, c.num, 16);
-            cl.den = __shfl_sync(0xffffffffu, c.den, 16);
-            cl.r_min = __shfl_sync(0xffffffffu, c.r_min, 16);
-            cl.np = __shfl_sync(0xffffffffu, c.np, 16);
-            CrackDecision dl;
-            dl.K = __shfl_sync(0xffffffffu, dd.K, 16);
-            dl.v = __shfl_sync(0xffffffffu, dd.v, 16);
-            dl.dq = __shfl_sync(0xffffffffu, dd.dq, 16);
-            dl.propagate = __shfl_sync(0xffffffffu, dd.propagate, 16);
-            dl.flags = __shfl_sync(0xffffffffu, dd.flags, 16);
-            if (tid == 0) {
-                if (act_r) crack_commit(p, a.cut_v, a.hist, sS, +1, commit, c, dd);
-                if (act_l) crack_commit(p, a.cut_v, a.hist, sS, -1, commit, cl, dl);
-                sS.r.decided = 1;
-                sS.l.decided = 1;
-            }
-            __syncwarp();
-        } else {
-            if (right_here) crack_step_warp<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, +1, commit, st);
-            if (left_here) crack_step_warp<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, -1, commit, st);
-        }
-        if (tid == 0 && commit) {
-            CrackState *o = a.s_out;
-            const int64_t n = sS.step + 1;
-            if (right_here) {
-                o->step = n;
-                o->hist_n = sS.hist_n + (pending ? 1 : 0);
-                o->i_last = sS.i_last;
-                if (!p.two_tips) o->i_first = sS.i_first;
-                o->r = sS.r;
-                o->r.decided = 0;
-                // the Dirichlet values of the next step come from another
-                // CTA when there is one (see step_cta): their FP64 sin of
-                // the sin^2 and half-sine loads stays off this CTA's path
-                if (a.n_bands <= 2)
-                    for (int e = 0; e < 4; ++e)
-                        o->wstar[e] = a.edge[e] == EDGE_DIRICHLET ? load_value(a.load[e], n, (double)p.dt) : 0.0;
-            }
-            if (left_here) {
-                o->i_first = sS.i_first;
-                o->l = sS.l;
-                o->l.decided = 0;
-            }
-            if (REC) {
-                const int64_t t = n - 1 - *rec_n0;
-                if (t >= 0 && t < rec_n_steps) {
-                    if (right_here) rec_il[t] = sS.i_last;
-                    if (right_here && !p.two_tips) rec_if[t] = sS.i_first;
-                    if (left_here) rec_if[t] = sS.i_first;
-                }
-            }
-        }
-    }
-    __syncthreads();   // the decision
-
-    // (4) the rows.  The links this step severed: an end moves less than one
-    // spacing per step, so they are the columns between the old and the new
-    // last (first) cut link, (il0, i_last] on the right, [i_first, if0) on
-    // the left
-    const int il1 = sS.i_last, if1 = sS.i_first;
-    uint32_t fresh = 0u;
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-        const int i = x0 + k;
-        if ((i > il0 && i <= il1) || (i >= if1 && i < if0)) fresh |= 1u << k;
-    }
-    const uint32_t cut = x0 < nx ? (cut0 | fresh) : 0u;
+    const uint32_t cut = x0 < a.nx ? (cut0 | fresh) : 0u;
     R o[HH], od[HH];
 #pragma unroll
     for (int q = 0; q < HH; ++q) {
@@ -227,7 +148,7 @@ __device__ __noinline__ T crack_band(const StepArgs<T, D> *ap, CrackState *sSp, 
         const uint32_t cut_dn = (!below && j == jc) ? cut : 0u;
         row_update(a, E, x0, j, w[q + 1], w[q + 2], w[q], wd[q], left0, rightN, cut_up, cut_dn, o[q], od[q]);
     }
-    if (HH >= 3 && p.macro && cut) {
+    if (HH >= 3 && a.macro && cut) {
         // x_B on row jc-1 (x_I, x_II on jc-2, jc-3) or on row jc (jc+1, jc+2)
         const int qb = below ? HH - 1 : 0, qi = below ? HH - 2 : 1, qii = below ? HH - 3 : 2;
 #pragma unroll
@@ -238,7 +159,7 @@ __device__ __noinline__ T crack_band(const StepArgs<T, D> *ap, CrackState *sSp, 
                 o[qb].v[k] = wB;
             }
     }
-    if (x0 < nx) {
+    if (x0 < a.nx) {
 #pragma unroll
         for (int q = 0; q < HH; ++q) {
             store_row(a, x0, j0 + q, o[q], od[q], acc);
@@ -481,6 +402,32 @@ __device__ __forceinline__ void march_bulk(const StepArgs<T, D> &a, int cb, int 
     }
 }
 
+// A lattice without a crack: only the step counter and the Dirichlet values
+// advance (one thread of the CTA that holds band 0, column block 0).
+template <typename T, typename D>
+__device__ __forceinline__ void advance_without_crack(const StepArgs<T, D> &a, CrackState &sS)
+{
+    sS = *a.s_in;
+    const int64_t n = sS.step + 1;
+    sS.step = n;
+    sS.r.decided = 1;
+    sS.l.decided = 1;
+    for (int e = 0; e < 4; ++e)
+        sS.wstar[e] = a.edge[e] == EDGE_DIRICHLET ? load_value(a.load[e], n, (double)a.p.dt) : 0.0;
+    *a.s_out = sS;
+}
+
+// A lattice with a crack: the Dirichlet values w*(t_{n+1}) of the next step
+// (its own fields of the next state; the crack step's writer CTA writes the
+// others).
+template <typename T, typename D>
+__device__ __forceinline__ void next_dirichlet_values(const StepArgs<T, D> &a)
+{
+    const int64_t n = a.s_in->step + 1;
+    for (int e = 0; e < 4; ++e)
+        a.s_out->wstar[e] = a.edge[e] == EDGE_DIRICHLET ? load_value(a.load[e], n, (double)a.p.dt) : 0.0;
+}
+
 // One CTA of a time step: column block cb of band `band` of the lattice that
 // `a` describes (the kernel parameter block, or a copy in shared memory).
 // BOTH: compiled with the path that evaluates the two ends of a two-tip
@@ -506,29 +453,116 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
     T acc = (T)0;
 
     if (a.crack_band >= 0 && (band == a.crack_band || (band == a.crack_band + 1 && p.sides == 3))) {
-        // a crack sub-band (and the crack step of Alg. 1 where it owns the
-        // next link of an end): out of line, on a copy of the arguments in
-        // shared memory (by assignment: no address of the parameter block)
-        __shared__ __align__(16) StepArgs<T, D> sA;
-        __shared__ PairStash<T> stash;
-        if (tid == 0) sA = a;
-        __syncthreads();
-        acc = p.macro ? crack_band<T, D, 3, TH, COH, BOTH, REC>(&sA, &sS, &stash, cb, band, j0, r.n0, r.n_steps,
-                                                               r.i_last, r.i_first)
-                      : crack_band<T, D, 1, TH, COH, BOTH, REC>(&sA, &sS, &stash, cb, band, j0, r.n0, r.n_steps,
-                                                               r.i_last, r.i_first);
-    } else {
-        if (a.crack_band < 0 && cb == 0 && band == 0 && tid == 0) {
-            // no crack: only the step counter and the Dirichlet values advance
-            sS = *a.s_in;
-            const int64_t n = sS.step + 1;
-            sS.step = n;
-            sS.r.decided = 1;
-            sS.l.decided = 1;
-            for (int e = 0; e < 4; ++e)
-                sS.wstar[e] = a.edge[e] == EDGE_DIRICHLET ? load_value(a.load[e], n, (double)p.dt) : 0.0;
-            *a.s_out = sS;
+        // The crack step of Alg. 1 that follows the previous LBM step, by the
+        // two crack sub-band CTAs that own the next link of each end: both
+        // reach the same decision; the lower one records it, each end
+        // writing only its own fields of the next state.  (A row slab whose
+        // boundary is the crack line holds one of the two sub-bands and
+        // reads the other side's row from its halo: it records its own.)
+        const int cols = TH * N;
+        // the state, for the crack step, loaded at once with the two fields
+        // every thread reads (an unused copy where no end is in this CTA)
+        if (tid == 0) sS = *a.s_in;
+        const int il0 = a.s_in->i_last, if0 = a.s_in->i_first;   // before the crack step
+        int i_next = il0 + 1;
+        i_next = max(i_next, if0);
+        i_next = min(max(i_next, 0), nx - 1);
+        int i_prev = if0 - 1;
+        i_prev = min(i_prev, il0);
+        i_prev = min(max(i_prev, 0), nx - 1);
+        const bool right_here = cb == i_next / cols;
+        const bool left_here = p.two_tips && cb == i_prev / cols;
+        const bool commit = band == a.crack_band;
+        const bool both = BOTH && right_here && left_here;
+        if ((right_here || left_here) && tid == 0) {
+            // the rows this CTA updates after the crack step, brought into L2
+            // while the crack step runs (its FP64 chain is the long pole)
+            const int hh = p.macro ? 3 : 1;
+            const int64_t xb = (int64_t)cb * TH * N;
+            for (int q = -1; q <= hh; ++q)
+                bulk_prefetch_l2(a.w_in + (int64_t)(j0 + q) * a.pitch + xb, (uint32_t)(TH * N * sizeof(T)));
+            for (int q = 0; q < hh; ++q)
+                bulk_prefetch_l2(a.wd + (int64_t)(j0 + q) * a.pitch + xb, (uint32_t)(TH * N * sizeof(D)));
         }
+        if ((right_here || left_here) && tid < 32) {
+            __syncwarp();
+            const bool pending = !sS.r.decided;   // not yet applied by a deferred crack step
+            if (both) {
+                // both ends in this CTA: lanes 0-15 evaluate the right end and
+                // lanes 16-31 the left end at once, on the same state (the
+                // criteria of both ends before either advances); lane 0 then
+                // advances the right end and the left end in turn
+                const bool act_r = p.mode != CRACK_NONE && !sS.r.decided;
+                const bool act_l = p.mode != CRACK_NONE && !sS.l.decided;
+                const CrackSums c = crack_eval_warp<T, 16>(p, a.w_in, a.pitch, a.cut_v, sS, tid < 16 ? +1 : -1);
+                // each end's criterion (the FP64 part) in its half warp's first
+                // lane at once: lane 0 the right end, lane 16 the left end
+                CrackDecision dd = {};
+                if ((tid & 15) == 0) dd = crack_decide(p, sS, tid < 16 ? +1 : -1, c);
+                CrackSums cl;
+                cl.num = __shfl_sync(0xffffffffu, c.num, 16);
+                cl.den = __shfl_sync(0xffffffffu, c.den, 16);
+                cl.r_min = __shfl_sync(0xffffffffu, c.r_min, 16);
+                cl.np = __shfl_sync(0xffffffffu, c.np, 16);
+                CrackDecision dl;
+                dl.K = __shfl_sync(0xffffffffu, dd.K, 16);
+                dl.v = __shfl_sync(0xffffffffu, dd.v, 16);
+                dl.dq = __shfl_sync(0xffffffffu, dd.dq, 16);
+                dl.propagate = __shfl_sync(0xffffffffu, dd.propagate, 16);
+                dl.flags = __shfl_sync(0xffffffffu, dd.flags, 16);
+                if (tid == 0) {
+                    if (act_r) crack_commit(p, a.cut_v, a.hist, sS, +1, commit, c, dd);
+                    if (act_l) crack_commit(p, a.cut_v, a.hist, sS, -1, commit, cl, dl);
+                    sS.r.decided = 1;
+                    sS.l.decided = 1;
+                }
+                __syncwarp();
+            } else {
+                if (right_here) crack_step_warp<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, +1, commit);
+                if (left_here) crack_step_warp<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, -1, commit);
+            }
+            if (tid == 0 && commit) {
+                CrackState *o = a.s_out;
+                const int64_t n = sS.step + 1;
+                if (right_here) {
+                    o->step = n;
+                    o->hist_n = sS.hist_n + (pending ? 1 : 0);
+                    o->i_last = sS.i_last;
+                    if (!p.two_tips) o->i_first = sS.i_first;
+                    o->r = sS.r;
+                    o->r.decided = 0;
+                    // the Dirichlet values of the next step come from another
+                    // CTA when there is one (see below): their FP64 sin of the
+                    // sin^2 and half-sine loads stays off this CTA's path
+                    if (a.n_bands <= 2)
+                        for (int e = 0; e < 4; ++e)
+                            o->wstar[e] = a.edge[e] == EDGE_DIRICHLET ? load_value(a.load[e], n, (double)p.dt) : 0.0;
+                }
+                if (left_here) {
+                    o->i_first = sS.i_first;
+                    o->l = sS.l;
+                    o->l.decided = 0;
+                }
+                if (REC) {
+                    const int64_t t = n - 1 - *r.n0;
+                    if (t >= 0 && t < r.n_steps) {
+                        if (right_here) r.i_last[t] = sS.i_last;
+                        if (right_here && !p.two_tips) r.i_first[t] = sS.i_first;
+                        if (left_here) r.i_first[t] = sS.i_first;
+                    }
+                }
+            }
+        }
+        const int edges = a.edge[0] | (a.edge[1] << 2) | (a.edge[2] << 4) | (a.edge[3] << 6);
+        const CrackState *post = (right_here || left_here) ? &sS : nullptr;
+        acc = p.macro ? crack_rows<T, D, 3, TH, COH>(a.w_in, a.w_out, a.wd, a.wd_scale, a.pitch, a.nx, a.ny, p.jc,
+                                                p.macro, edges, a.g, a.dt, a.cut_v, a.words, a.s_in, cb, j0, il0,
+                                                if0, post)
+                      : crack_rows<T, D, 1, TH, COH>(a.w_in, a.w_out, a.wd, a.wd_scale, a.pitch, a.nx, a.ny, p.jc,
+                                                p.macro, edges, a.g, a.dt, a.cut_v, a.words, a.s_in, cb, j0, il0,
+                                                if0, post);
+    } else {
+        if (a.crack_band < 0 && cb == 0 && band == 0 && tid == 0) advance_without_crack(a, sS);
         // the edge rules per warp: only warps whose columns reach an outer edge,
         // and the bands holding the bottom and top rows, need them
         const int xw0 = (cb * TH + (tid & ~31)) * N;   // first column of this warp
@@ -550,11 +584,8 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
     // written by the first CTA of the first band that is no crack sub-band
     // (its own fields of the next state; the writer CTA writes the others)
     if (a.crack_band >= 0 && a.n_bands > 2 && cb == 0 && tid == 0 &&
-        band == (a.crack_band > 0 ? 0 : a.crack_band + (p.sides == 3 ? 2 : 1))) {
-        const int64_t n = a.s_in->step + 1;
-        for (int e = 0; e < 4; ++e)
-            a.s_out->wstar[e] = a.edge[e] == EDGE_DIRICHLET ? load_value(a.load[e], n, (double)p.dt) : 0.0;
-    }
+        band == (a.crack_band > 0 ? 0 : a.crack_band + (p.sides == 3 ? 2 : 1)))
+        next_dirichlet_values(a);
     // a non-finite w (or wdot, which enters w) turns the sum of the first
     // component of each vector non-finite within a step or two
     if (__any_sync(kFull, !isfinite(acc)) && lane == 0) atomicOr(a.err, (uint32_t)ERR_NONFINITE);
@@ -631,6 +662,66 @@ __global__ void __launch_bounds__(TH, (sizeof(T) == 4 ? kMinBlocks : kMinBlocks 
     for (int q = threadIdx.x; q < (int)(sizeof(StepArgs<T, D>) / 4); q += TH) dst[q] = src[q];
     __syncthreads();
     step_cta<T, D, false, false, TH, false, LA>(sa, u.cb, u.band, sS, RecArgs{});
+}
+
+// The balanced batched step (band_rows = -1): as many CTAs as are resident at
+// once, each running a list of pieces (BatchPiece) chosen on the host so that
+// every CTA has about the same number of rows to march, whatever the
+// lattices' heights: a crack sub-band runs the per-band code, any other piece
+// marches its rows exactly as the band that holds them would (the same per-
+// warp edge handling, the same per-site arithmetic), so the results are
+// bit-identical to the per-band launch.  One wave, no tail of short units,
+// and long marches with few halo rows.
+template <typename T, typename D, int TH, int LA>
+__device__ __forceinline__ void piece_rows(const StepArgs<T, D> &a, int cb, int j0, int j1, int duty, CrackState &sS)
+{
+    constexpr int N = Vec<T>::N;
+    const int tid = threadIdx.x;
+    T acc = (T)0;
+    if (duty == 1 && tid == 0) advance_without_crack(a, sS);
+    if (duty == 2 && tid == 0) next_dirichlet_values(a);
+    const int xw0 = (cb * TH + (tid & ~31)) * N;   // first column of this warp
+    if (xw0 < a.nx) {
+        if ((xw0 == 0) | (xw0 + 32 * N - 1 >= a.nx - 1)) {
+            march<T, D, true, TH, false, LA>(a, cb, j0, j1, acc);
+        } else {
+            // the bottom and top rows of the lattice take the edge rules, the
+            // rows between them the bare update (a piece is often a long run
+            // from an outer edge)
+            const int lo = j0 == 0 ? 1 : j0, hi = j1 == a.ny ? a.ny - 1 : j1;
+            if (j0 == 0) march<T, D, true, TH, false, LA>(a, cb, 0, 1, acc);
+            if (lo < hi) march<T, D, false, TH, false, LA>(a, cb, lo, hi, acc);
+            if (j1 == a.ny && a.ny - 1 >= lo) march<T, D, true, TH, false, LA>(a, cb, a.ny - 1, a.ny, acc);
+        }
+    }
+    if (__any_sync(0xffffffffu, !isfinite(acc)) && (tid & 31) == 0) atomicOr(a.err, (uint32_t)ERR_NONFINITE);
+}
+
+template <typename T, typename D, int TH, int LA>
+__global__ void __launch_bounds__(TH, (sizeof(T) == 4 ? kMinBlocks : kMinBlocks - 2) * (kThreads / TH) -
+                                          (LA == 2 ? kThreads / TH : 0))
+    batch_piece_kernel(const StepArgs<T, D> *descs, const BatchPiece *pieces, const int32_t *off, int par)
+{
+    __shared__ CrackState sS;
+    __shared__ __align__(16) StepArgs<T, D> sa;
+    pdl_wait();
+    pdl_trigger();
+    const int q0 = off[blockIdx.x], q1 = off[blockIdx.x + 1];
+    int cur = -1;
+    for (int q = q0; q < q1; ++q) {
+        const BatchPiece u = pieces[q];
+        // every thread is done with the previous piece (its arguments, sS)
+        if (q > q0) __syncthreads();
+        if (u.inst != cur) {
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(descs + 2 * u.inst + par);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&sa);
+            for (int k = threadIdx.x; k < (int)(sizeof(StepArgs<T, D>) / 4); k += TH) dst[k] = src[k];
+            __syncthreads();
+            cur = u.inst;
+        }
+        if (u.j0 < 0) step_cta<T, D, false, false, TH, false, LA>(sa, u.cb, -u.j0 - 1, sS, RecArgs{});
+        else piece_rows<T, D, TH, LA>(sa, u.cb, u.j0, u.j1, u.duty, sS);
+    }
 }
 
 // ----------------------------------------- persistent batched step
@@ -835,6 +926,49 @@ cudaError_t launch_batch_step(const StepArgs<T, D> *descs, const BatchUnit *unit
     void *args[] = {(void *)&descs, (void *)&units, (void *)&par};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)n_units);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = chained ? 1 : 0;
+    return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+template <typename T, typename D>
+cudaError_t batch_piece_kernel_ptr(int threads, int lookahead, const void **fn)
+{
+    const bool deep = lookahead == 2;
+    if (lookahead != 1 && !deep) return cudaErrorInvalidValue;
+    switch (threads) {
+    case 32:
+        *fn = deep ? reinterpret_cast<const void *>(&batch_piece_kernel<T, D, 32, 2>)
+                   : reinterpret_cast<const void *>(&batch_piece_kernel<T, D, 32, 1>);
+        return cudaSuccess;
+    case 64:
+        *fn = deep ? reinterpret_cast<const void *>(&batch_piece_kernel<T, D, 64, 2>)
+                   : reinterpret_cast<const void *>(&batch_piece_kernel<T, D, 64, 1>);
+        return cudaSuccess;
+    case kThreads:
+        *fn = deep ? reinterpret_cast<const void *>(&batch_piece_kernel<T, D, kThreads, 2>)
+                   : reinterpret_cast<const void *>(&batch_piece_kernel<T, D, kThreads, 1>);
+        return cudaSuccess;
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T, typename D>
+cudaError_t launch_batch_pieces(const StepArgs<T, D> *descs, const BatchPiece *pieces, const int32_t *off, int n_cta,
+                                int par, cudaStream_t s, int threads, int lookahead, bool chained)
+{
+    const void *fn = nullptr;
+    cudaError_t e = batch_piece_kernel_ptr<T, D>(threads, lookahead, &fn);
+    if (e != cudaSuccess) return e;
+    if (n_cta <= 0) return cudaSuccess;
+    void *args[] = {(void *)&descs, (void *)&pieces, (void *)&off, (void *)&par};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)n_cta);
     cfg.blockDim = dim3((unsigned)threads);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -1253,6 +1387,16 @@ template cudaError_t batch_step_kernel_ptr<float, float>(int, int, const void **
 template cudaError_t batch_step_kernel_ptr<float, __nv_bfloat16>(int, int, const void **);
 template cudaError_t batch_step_kernel_ptr<float, __half>(int, int, const void **);
 template cudaError_t batch_step_kernel_ptr<float, Lf>(int, int, const void **);
+template cudaError_t batch_piece_kernel_ptr<double, double>(int, int, const void **);
+template cudaError_t launch_batch_pieces<double, double>(const StepArgs<double, double> *, const BatchPiece *, const int32_t *, int, int, cudaStream_t, int, int, bool);
+template cudaError_t batch_piece_kernel_ptr<float, float>(int, int, const void **);
+template cudaError_t launch_batch_pieces<float, float>(const StepArgs<float, float> *, const BatchPiece *, const int32_t *, int, int, cudaStream_t, int, int, bool);
+template cudaError_t batch_piece_kernel_ptr<float, __nv_bfloat16>(int, int, const void **);
+template cudaError_t launch_batch_pieces<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> *, const BatchPiece *, const int32_t *, int, int, cudaStream_t, int, int, bool);
+template cudaError_t batch_piece_kernel_ptr<float, __half>(int, int, const void **);
+template cudaError_t launch_batch_pieces<float, __half>(const StepArgs<float, __half> *, const BatchPiece *, const int32_t *, int, int, cudaStream_t, int, int, bool);
+template cudaError_t batch_piece_kernel_ptr<float, Lf>(int, int, const void **);
+template cudaError_t launch_batch_pieces<float, Lf>(const StepArgs<float, Lf> *, const BatchPiece *, const int32_t *, int, int, cudaStream_t, int, int, bool);
 template cudaError_t launch_fill_pads<float>(float *, int64_t, int, int, const int32_t *, cudaStream_t);
 template cudaError_t launch_fill_pads<double>(double *, int64_t, int, int, const int32_t *, cudaStream_t);
 

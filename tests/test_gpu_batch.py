@@ -128,19 +128,20 @@ def oracle_batch_problems():
     return ps
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32"])
-def test_batch_matches_the_oracle(oracle_mod, gpu, storage):
+@pytest.mark.parametrize("storage,rows", [("f64", 16), ("f32", 16), ("f32", -1)])
+def test_batch_matches_the_oracle(oracle_mod, gpu, storage, rows):
     """Every lattice of one batch (one launch per step for all eight) against
     the FP64 oracle on the same problem, element by element: fields within
     1e-12 (FP64) / 1e-5 (FP32) relative max-norm (wdot on the scale of the
     state), cut masks and tips bit-exact in FP64 where the oracle's K
     decision margin exceeds 1e-9, K within 1e-9 / 0.5 % of max|K|; in FP32
-    the K-criterion tips within one spacing and the growth count within 3."""
+    the K-criterion tips within one spacing and the growth count within 3.
+    Bands of 16 rows, and the balanced step (rows = -1) in FP32."""
     from test_gpu_parity import compare_crack, compare_fields, compare_masks
     ps = oracle_batch_problems()
     steps = 400
     lats = [gpu.Lattice(p, storage) for p in ps]
-    b = gpu.Batch(lats)
+    b = gpu.Batch(lats, band_rows=rows)
     b.step(1)
     b.step(steps - 1)
     b.close()
@@ -173,12 +174,15 @@ def test_batch_matches_the_oracle(oracle_mod, gpu, storage):
 # ------------------------------------------------------ launch shapes, tuner
 
 @pytest.mark.parametrize("storage", ["f32", "f64"])
-@pytest.mark.parametrize("threads,rows", [(32, 8), (64, 5), (32, 64), (128, 32), (32, 0), (128, 0)])
+@pytest.mark.parametrize("threads,rows", [(32, 8), (64, 5), (32, 64), (128, 32), (32, 0), (128, 0),
+                                          (32, -1), (64, -1), (128, -1)])
 def test_every_launch_shape_gives_the_solo_bits(gpu, storage, threads, rows):
-    """CTAs of 32, 64 or 128 threads over bands of any height: each lattice
-    of the batch still ends bit-identical to its solo run (graph chunks and
-    single launches)."""
-    ps = mixed_problems()
+    """CTAs of 32, 64 or 128 threads over bands of any height, and the
+    balanced step (rows = -1: runs of row pieces, several lattices per CTA,
+    a lattice with the macroscopic rule on its outer edges among them): each
+    lattice of the batch still ends bit-identical to its solo run (graph
+    chunks and single launches)."""
+    ps = mixed_problems() + [W.kcrit_centre_crack(scale=2)]
     solo = [gpu.Lattice(p, storage) for p in ps]
     mem = [gpu.Lattice(p, storage) for p in ps]
     for p, s, m in zip(ps, solo, mem):
@@ -200,7 +204,7 @@ def test_every_launch_shape_gives_the_solo_bits(gpu, storage, threads, rows):
 
 
 @pytest.mark.parametrize("storage", ["f32", "f64", "f32_bf16", "f32_f16", "f32_lf"])
-@pytest.mark.parametrize("threads,rows", [(32, 1), (64, 2), (128, 3), (32, 16), (128, 0)])
+@pytest.mark.parametrize("threads,rows", [(32, 1), (64, 2), (128, 3), (32, 16), (128, 0), (64, -1)])
 def test_two_row_lookahead_gives_the_solo_bits(gpu, storage, threads, rows):
     """The march with two rows of loads in flight (and bands of 1, 2 or 3
     rows, where the lookahead runs past the band) is the same arithmetic:
@@ -236,7 +240,7 @@ def test_tune_leaves_the_lattices_as_they_were_and_caches_the_shape(gpu):
     b = gpu.Batch(mem)
     b.step(37)                       # a pending crack step at the tuning call
     r = b.tune(trial_steps=6)
-    assert r["threads"] in (32, 64, 128) and r["band_rows"] in (0, 8, 16, 32, 64) and r["lookahead"] in (1, 2)
+    assert r["threads"] in (32, 64, 128) and r["band_rows"] in (-1, 0, 8, 16, 32, 64) and r["lookahead"] in (1, 2)
     assert not r["from_cache"] and r["us_per_step"] > 0
     info = b.info()
     assert (info["threads"], info["band_rows"], info["lookahead"]) == (r["threads"], r["band_rows"], r["lookahead"])
@@ -259,7 +263,7 @@ def test_shape_arguments_are_checked(gpu):
     ps = W.batch_problems(2, seed=6)
     lats = [gpu.Lattice(p, "f32") for p in ps]
     b = gpu.Batch(lats)
-    for t, r in ((48, 16), (256, 16), (32, -1)):
+    for t, r in ((48, 16), (256, 16), (32, -2)):
         with pytest.raises(gpu.LbmError) as ei:
             b.set_shape(t, r)
         assert ei.value.status == -1
@@ -275,7 +279,7 @@ def test_shape_arguments_are_checked(gpu):
 # ----------------------------------------------------- persistent batched form
 
 @pytest.mark.parametrize("storage", ["f32", "f64"])
-@pytest.mark.parametrize("threads,rows", [(128, 16), (32, 32)])
+@pytest.mark.parametrize("threads,rows", [(128, 16), (32, 32), (64, -1)])
 def test_persistent_launch_gives_the_solo_bits(gpu, storage, threads, rows):
     """One cooperative launch for many steps (grid barrier between steps),
     including a lattice with the macroscopic rule on its outer edges (its

@@ -274,8 +274,19 @@ def test_kcrit_growth_fp64(oracle_mod, gpu):
 def test_calls_that_reject_the_lattice(gpu):
     p = _problem(64, 32)
     g = gpu.Lattice(p, "f32")
+    d5 = gpu.Lattice(W.base_problem(64, 32), "f32")
     with pytest.raises(gpu.LbmError):
-        gpu.Batch([g])
+        gpu.Batch([g, d5])                           # D2Q5 and D2Q9 in one batch
+    d5.close()
+    b = gpu.Batch([g])
+    for t, r in ((64, 16), (32, 8), (128, -1)):      # D2Q9 batches: 128 threads, bands
+        with pytest.raises(gpu.LbmError):
+            b.set_shape(t, r)
+    with pytest.raises(gpu.LbmError):
+        b.set_lookahead(2)
+    with pytest.raises(gpu.LbmError):
+        b.set_persistent(True)
+    b.close()
     with pytest.raises(gpu.LbmError):
         gpu.Tape(g, np.array([[5, 5]], np.int32), 4)
     with pytest.raises(gpu.LbmError):
@@ -286,3 +297,127 @@ def test_calls_that_reject_the_lattice(gpu):
             gpu.Lattice(p, storage)
     with pytest.raises(gpu.LbmError):
         gpu.Lattice(_problem(64, 32, cs=0.9), "f32")     # g = 0.81 > 3/4
+
+
+# ------------------------------------------------------------ D2Q9 batches
+
+def _batch_problems():
+    """Uneven D2Q9 lattices: bounce-back and macroscopic crack faces,
+    prescribed and K-criterion growth of one and two ends, the Sec. 5.2
+    configuration (macroscopic rule on every boundary) at a quarter of its
+    size, a lattice without a crack and one with periodic edges."""
+    ps = []
+    p = _problem(300, 40)
+    p = W.with_crack(p, mode="prescribed", y=20.0, x_start=120.3, x_tip=160.6, v_rel=0.6, two_tips=True)
+    ps.append(W.with_antisymmetric_ramp(p, 1e-3, 50.0))
+    p = _problem(620, 40)
+    p["bc_mode"] = "macroscopic"
+    p = W.with_crack(p, mode="prescribed", y=20.0, x_start=0.0, x_tip=300.6, v_rel=0.6)
+    ps.append(W.with_antisymmetric_ramp(p, 1e-3, 50.0))
+    p = _problem(160, 48)
+    p["bc_mode"] = "macroscopic"
+    p = W.with_antisymmetric_ramp(p, 2e-3, 60.0)
+    K_C = 0.5 * W.strip_reference_K(0.25, 2e-3, 48.0)
+    ps.append(W.with_crack(p, mode="kcrit", y=24.0, x_start=60.0, x_tip=90.0, K_C=K_C, v_max=0.85, r0=2.0,
+                           two_tips=True))
+    p = W.kcrit_centre_crack(scale=4)
+    p["lattice"] = "D2Q9"
+    ps.append(p)
+    ps.append(_problem(97, 45))
+    ps.append(_problem(50, 34, ("periodic",) * 4))
+    return ps
+
+
+def _same(a, b):
+    wa, wda = a.fields()
+    wb, wdb = b.fields()
+    assert np.array_equal(wa, wb) and np.array_equal(wda, wdb)
+    assert np.array_equal(a.cut_mask("v"), b.cut_mask("v"))
+    assert a.crack_state() == b.crack_state()
+    ha, hb = a.history(), b.history()
+    for k in ha:
+        assert np.array_equal(ha[k], hb[k])
+
+
+def _pair(gpu, ps, storage, seed):
+    solo = [gpu.Lattice(p, storage) for p in ps]
+    mem = [gpu.Lattice(p, storage) for p in ps]
+    for p, s_, m in zip(ps, solo, mem):
+        if p["crack"]["mode"] == "none":
+            init = W.random_state(p["nx"], p["ny"], seed=seed, dtype=np.float64 if storage == "f64" else np.float32)
+            s_.set_fields(*init)
+            m.set_fields(*init)
+    return solo, mem
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("rows", [0, 5, 32])
+def test_d2q9_batch_equals_solo_runs(gpu, storage, rows):
+    """One launch per step advances every D2Q9 lattice of the batch (then one
+    launch for the crack-face rule and one for the edge rule): each lattice
+    ends bit-identical to the same lattice stepped alone."""
+    ps = _batch_problems()
+    solo, mem = _pair(gpu, ps, storage, seed=17)
+    b = gpu.Batch(mem)
+    b.set_shape(128, rows)
+    b.step(1)
+    b.step(150)
+    for s_ in solo:
+        s_.step(151)
+    for s_, m in zip(solo, mem):
+        _same(s_, m)
+    b.close()
+
+
+def test_d2q9_batch_matches_the_oracle(oracle_mod, gpu):
+    """The batched D2Q9 lattices against the FP64 oracle, element by element:
+    fields within 1e-12 of max|w| (2 max|w*| on the Sec. 5.2 lattice, whose
+    edge values dominate), cut masks and both ends' tips exact."""
+    ps = _batch_problems()
+    steps = 300
+    lats, _ = _pair(gpu, ps, "f64", seed=23)
+    inits = {}
+    for q, p in enumerate(ps):
+        if p["crack"]["mode"] == "none":
+            inits[q] = W.random_state(p["nx"], p["ny"], seed=23, dtype=np.float64)
+    b = gpu.Batch(lats)
+    b.step(steps)
+    b.close()
+    for q, (p, g) in enumerate(zip(ps, lats)):
+        o = oracle_mod.Oracle(p)
+        if q in inits:
+            o.set_fields(*inits[q])
+        o.step(steps)
+        ws = max((abs(L.get("amp", 0.0)) for L in p.get("loads", [])), default=0.0)
+        _close(o, g, 1e-12, floor=2 * ws)
+        np.testing.assert_array_equal(g.cut_mask("v"), o.cuts()[1].astype(bool))
+        mode = p["crack"]["mode"]
+        if mode != "none":
+            ends = [(g.history(cap=steps), o.history())]
+            if p["crack"].get("two_tips"):
+                ends.append((g.history_left(cap=steps), o.history_left()))
+            for hg, ho in ends:
+                if mode == "kcrit":
+                    # every growth decision exact; the advance within 2 units
+                    # of the 2^-32 dh grid (see test_centre_crack_example_on_d2q9)
+                    np.testing.assert_array_equal(hg["v"] > 0, ho["v"][:steps] > 0)
+                    assert np.abs(hg["tip_q"] - ho["tip_q"][:steps]).max() <= 2
+                else:
+                    np.testing.assert_array_equal(hg["tip_q"], ho["tip_q"][:steps])
+        o.close()
+        g.close()
+
+
+def test_d2q9_batch_tune_keeps_the_lattices(gpu):
+    ps = _batch_problems()
+    solo, mem = _pair(gpu, ps, "f32", seed=29)
+    b = gpu.Batch(mem)
+    b.step(40)
+    r = b.tune(trial_steps=4)
+    assert r["threads"] == 128 and r["lookahead"] == 1 and r["band_rows"] in (0, 8, 16, 32, 64)
+    b.step(60)
+    for s_ in solo:
+        s_.step(100)
+    for s_, m in zip(solo, mem):
+        _same(s_, m)
+    b.close()
