@@ -485,6 +485,33 @@ def crack_share(lbm, W, torch, stream, flush_l2, t_crack):
             "paper_cpu_share": [0.028, 0.007]}
 
 
+def line_sweep(lbm, W, torch, stream, count=32, steps_l=256):
+    """A batch of lattices of 512 x 256, each with an edge crack in another
+    direction (0 to 87 degrees, prescribed v = 0.5, link-local faces), against
+    the same lattices stepped one after another."""
+    import numpy as np
+    lines = []
+    for q in range(count):
+        th = np.radians(2.8 * q)
+        pq = W.with_line_crack(W.with_antisymmetric_ramp(W.base_problem(512, 256, bc_mode="bounceback"), 1e-3, 200.0),
+                               mode="prescribed",
+                               start=(0.0, 128.37), tip=(40.0 * np.cos(th) + 0.013, 128.37 + 40.0 * np.sin(th)),
+                               v_rel=0.5, r0=2.0)
+        pq["hist_cap"] = 2 * steps_l
+        lines.append(lbm.Lattice(pq, "f32", stream=stream))
+    for l in lines:
+        l.step(8)
+    t_seq = timed(torch, stream, lambda: [l.step(steps_l) for l in lines])
+    b = lbm.Batch(lines)
+    b.step(8)
+    t_b = timed(torch, stream, lambda: b.step(steps_l))
+    b.close()
+    for l in lines:
+        l.close()
+    return {"us_step": r4(t_b / steps_l * 1e6), "glups": r4(count * 512 * 256 * steps_l / t_b / 1e9),
+            "speedup": r4(t_seq / t_b)}
+
+
 def measure_extensions(lbm, W, torch, stream, peak, flush_l2, steps=100):
     """The extensions beyond the plain method, on the 4096 x 2048 lattice with
     the L2 flushed before each step (library CUDA events): D2Q9 with
@@ -543,6 +570,14 @@ def measure_extensions(lbm, W, torch, stream, peak, flush_l2, steps=100):
         b.close()
         for l in lats:
             l.close()
+
+    # 32 lattices of 512 x 256 with an edge crack in another direction each
+    # (0 to 87 degrees, prescribed v = 0.5, link-local faces) as one batch,
+    # against the same lattices one after another
+    try:
+        out["line_sweep32"] = line_sweep(lbm, W, torch, stream)
+    except lbm.LbmError as e:
+        out["line_sweep32"] = {"error": str(e)[:200]}
     return out
 
 

@@ -485,7 +485,12 @@ void lbm_destroy(lbm_handle *h);
  * or D2Q9 (a D2Q9 batch takes CTAs of 128 threads over bands, a lookahead of
  * one row, no balanced and no persistent form; its lattices with the
  * macroscopic rule on their crack faces get it from one more batched launch
- * per step, units of 128 columns).  Lattices with
+ * per step, units of 128 columns); or lattices with a crack in any direction
+ * (lbm_create_line; all members of that kind: each keeps its own fixed
+ * line-step grid, the batch takes CTAs of 128 threads and a lookahead of one
+ * row, band_rows is ignored, there is no balanced and no persistent form, and
+ * each lattice with the macroscopic rule on its faces runs its face solve as
+ * its own launch after the batched step).  Lattices with
  * LBM_BC_MACROSCOPIC_EDGES get their outer-edge rule from one more batched
  * launch per step (units of 128 edge sites).  While the batch exists, step its lattices
  * only through lbm_batch_step (stepping one alone makes lbm_batch_step return

@@ -1840,6 +1840,7 @@ struct lbm_batch {
     BatchUnit *eunits;   // edge-rule units: 128 edge sites of one lattice (LBM_BC_MACROSCOPIC_EDGES)
     int n_eunits;
     int q;               // velocity set of every member (5: D2Q5, 9: D2Q9)
+    bool line;           // every member has a crack in any direction (lbm_create_line)
     BatchUnit *funits;   // D2Q9 crack-face units: 128 columns of one lattice with macroscopic crack faces
     int n_funits;
     BatchPiece *pieces;  // balanced step (band_rows = -1): the pieces of every CTA ...
@@ -1920,6 +1921,25 @@ template <typename T, typename D>
 cudaError_t enqueue_batch_step_t(const lbm_batch *b, int par, cudaStream_t s)
 {
     const StepArgs<T, D> *d = static_cast<const StepArgs<T, D> *>(b->descs);
+    if constexpr (!std::is_same<D, Lf>::value) {   // a crack in any direction has no leapfrog storage
+        if (b->line) {
+            // the batched line step, then the face rule of each lattice with
+            // macroscopic faces (its own launch, as for the lattice alone)
+            cudaError_t e = launch_batch_line(d, b->units, b->n_units, par, s, b->chained);
+            for (const lbm_handle *h : b->hs) {
+                if (e != cudaSuccess) break;
+                if (h->n_face_chunks == 0 && h->n_faces == 0) continue;
+                StepArgs<T, D> a;
+                make_step_args(h, par, a);
+                a.chained = b->chained ? 1 : 0;
+                if (h->n_face_chunks > 0 && h->face_solve == 0)
+                    e = launch_line_faces_chunked(a, h->face_chunks, h->n_face_chunks, h->face_items, s);
+                else if (h->n_faces > 0)
+                    e = launch_line_faces(a, h->faces, h->n_faces, h->face_scratch, s);
+            }
+            return e;
+        }
+    }
     if constexpr (std::is_same<T, D>::value) {
         if (b->q == 9) {
             cudaError_t e = launch_batch_d2q9(d, b->units, b->n_units, b->funits, b->n_funits, par, s, b->chained);
@@ -2168,6 +2188,8 @@ lbm_status batch_build(lbm_batch *b, int threads, int rows, int la)
     if (la != 1 && la != 2) return fail(LBM_ERR_ARG, "lookahead must be 1 or 2 rows");
     if (b->q == 9 && (threads != kThreads || la != 1 || rows < 0))
         return fail(LBM_ERR_ARG, "a D2Q9 batch takes CTAs of 128 threads, bands of rows >= 0 and a lookahead of one row");
+    if (b->line && (threads != kThreads || la != 1 || rows < 0))
+        return fail(LBM_ERR_ARG, "a batch of cracks in any direction takes CTAs of 128 threads and a lookahead of one row");
     const bool balanced = rows == -1;
     // the balanced step keeps bands of 16 rows for its crack sub-bands and for
     // the persistent form
@@ -2177,22 +2199,33 @@ lbm_status batch_build(lbm_batch *b, int threads, int rows, int la)
         if (rc != LBM_OK) return rc;
     }
     std::vector<BatchUnit> units;
-    for (size_t i = 0; i < b->hs.size(); ++i) {
-        lbm_handle *h = b->hs[i];
-        drop_graph(h);
-        lbm_status rc = plan_bands(h, heights[i]);
-        if (rc != LBM_OK) return rc;
-        const int cols = threads * (int)(16 / h->esize);
-        const int ncb = (h->grid.nx + cols - 1) / cols;
-        for (int band = 0; band < h->n_bands; ++band)
-            for (int cb = 0; cb < ncb; ++cb) {
-                BatchUnit u;
-                u.inst = (int32_t)i;
-                u.cb = cb;
-                u.band = band;
-                u.pad = 0;
-                units.push_back(u);
-            }
+    if (b->line) {
+        // each lattice keeps its own line-step grid: block 0 the tip CTA, then
+        // its march blocks (bands of the lattice's fixed height)
+        for (size_t i = 0; i < b->hs.size(); ++i) {
+            lbm_handle *h = b->hs[i];
+            drop_graph(h);
+            const int n = 1 + h->ncb * ((h->grid.ny + h->cp.band - 1) / h->cp.band);
+            for (int u = 0; u < n; ++u) units.push_back(BatchUnit{(int32_t)i, u, 0, 0});
+        }
+    } else {
+        for (size_t i = 0; i < b->hs.size(); ++i) {
+            lbm_handle *h = b->hs[i];
+            drop_graph(h);
+            lbm_status rc = plan_bands(h, heights[i]);
+            if (rc != LBM_OK) return rc;
+            const int cols = threads * (int)(16 / h->esize);
+            const int ncb = (h->grid.nx + cols - 1) / cols;
+            for (int band = 0; band < h->n_bands; ++band)
+                for (int cb = 0; cb < ncb; ++cb) {
+                    BatchUnit u;
+                    u.inst = (int32_t)i;
+                    u.cb = cb;
+                    u.band = band;
+                    u.pad = 0;
+                    units.push_back(u);
+                }
+        }
     }
     std::vector<char> descs;
     std::vector<BatchUnit> eunits;
@@ -2332,7 +2365,8 @@ lbm_status lbm_batch_create(lbm_handle *const *handles, int32_t n, int32_t band_
         if (h->sticky != LBM_OK) return fail(h->sticky, "a lattice is in an error state");
         if (h->lat.storage != handles[0]->lat.storage) return fail(LBM_ERR_ARG, "all lattices need the same storage");
         if (h->q != handles[0]->q) return fail(LBM_ERR_ARG, "all lattices need the same velocity set");
-        if (h->line) return fail(LBM_ERR_ARG, "the batched step is built for cracks along +x");
+        if (h->line != handles[0]->line)
+            return fail(LBM_ERR_ARG, "a batch holds cracks along +x or cracks in any direction, not both");
         if (h->stream != handles[0]->stream) return fail(LBM_ERR_ARG, "all lattices need the same stream");
         if (h->parity != handles[0]->parity) return fail(LBM_ERR_STATE, "all lattices need the same number of steps");
         for (int k = 0; k < i; ++k)
@@ -2349,6 +2383,7 @@ lbm_status lbm_batch_create(lbm_handle *const *handles, int32_t n, int32_t band_
     b->gexec = nullptr;
     b->gparity = -1;
     b->q = handles[0]->q;
+    b->line = handles[0]->line;
     b->funits = nullptr;
     b->n_funits = 0;
     b->pieces = nullptr;
@@ -2509,11 +2544,12 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *threads, i
     int best_t = b->threads, best_r = b->band_rows, best_la = b->lookahead;
     double best = 1e300;
     int par = b->hs[0]->parity;
-    // a D2Q9 batch: CTAs of 128 threads, a lookahead of one row, bands only
-    const bool d9 = b->q == 9;
+    // a D2Q9 batch: CTAs of 128 threads, a lookahead of one row, bands only;
+    // a batch of cracks in any direction: its lattices' fixed grids, one shape
+    const bool d9 = b->q == 9 || b->line;
     for (int la = 1; la <= (d9 ? 1 : 2); ++la)
         for (int ti = d9 ? 2 : 0; ti < 3; ++ti)
-            for (int ri = d9 ? 1 : 0; ri < 6; ++ri) {
+            for (int ri = d9 ? 1 : 0; ri < (b->line ? 2 : 6); ++ri) {
                 rc = batch_build(b, shapes_t[ti], shapes_r[ri], la);
                 if (rc != LBM_OK) return done(rc);
                 double t_min = 1e300;
@@ -2638,7 +2674,8 @@ lbm_status lbm_batch_set_persistent(lbm_batch *b, int32_t enable, int64_t budget
 {
     if (!b) return fail(LBM_ERR_ARG, "batch is NULL");
     if (budget_cycles < 0 || budget_cycles > ((int64_t)1 << 40)) return fail(LBM_ERR_ARG, "budget out of range");
-    if (enable && b->q == 9) return fail(LBM_ERR_ARG, "the persistent batched step is built for D2Q5 only");
+    if (enable && (b->q == 9 || b->line))
+        return fail(LBM_ERR_ARG, "the persistent batched step is built for D2Q5 cracks along +x only");
     b->persistent = enable != 0;
     b->budget = budget_cycles > 0 ? (long long)budget_cycles : (long long)1 << 31;
     clear_error();

@@ -304,6 +304,11 @@ cudaError_t launch_batch_edge_rule(const StepArgs<T, D> *descs, const BatchUnit 
                                    cudaStream_t s, bool chained = false);
 template <typename T> cudaError_t launch_d2q9_step(const StepArgs<T, T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_d2q9_faces(const StepArgs<T, T> &a, cudaStream_t s);
+// A batch of lattices with a crack in any direction: unit (inst, cb = block
+// of that lattice's line-step grid).
+template <typename T, typename D>
+cudaError_t launch_batch_line(const StepArgs<T, D> *descs, const BatchUnit *units, int n_units, int par, cudaStream_t s,
+                              bool chained);
 // A batch of D2Q9 lattices: the step units, then the crack-face units (128
 // columns of one lattice with the macroscopic rule on its crack faces).
 template <typename T>

@@ -678,15 +678,10 @@ __device__ __forceinline__ T line_march_edge(const StepArgs<T, D> &a, const Edge
 // keeps every block resident at once) and then takes its share of the
 // claimed groups.
 template <typename T, typename D>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBlocks - 2)
-    line_step_kernel(const StepArgs<T, D> a)
+__device__ __forceinline__ void line_cta(const StepArgs<T, D> &a, int blk, CrackState &sS, Claims &sC,
+                                         EdgeValues<T> &sE)
 {
-    pdl_wait();
-    pdl_trigger();
     constexpr int N = Vec<T>::N;
-    __shared__ CrackState sS;
-    __shared__ Claims sC;                 // the claims and edge values, formed once per block
-    __shared__ EdgeValues<T> sE;
     const int tid = threadIdx.x, lane = tid & 31;
     if (tid == 0) {
         sC = claims(a.p, a.s_in);
@@ -695,12 +690,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
     __syncthreads();
     const EdgeValues<T> &E = sE;
     const Claims &C = sC;
-    if (blockIdx.x == 0) {
+    if (blk == 0) {
         tip_cta<T, D>(a, sS, E, C);
         return;
     }
     const int n_march = a.ncb * ((a.ny + a.p.band - 1) / a.p.band);
-    const int u = (int)blockIdx.x - 1;
+    const int u = blk - 1;
     const int cb = u % a.ncb, band = u / a.ncb;
     const int x0 = (cb * kThreads + tid) * N;
     const int xw0 = (cb * kThreads + (tid & ~31)) * N;
@@ -745,6 +740,41 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBl
     // element of each vector non-finite within a step or two
     if (__any_sync(0xffffffffu, !isfinite(acc)) && lane == 0) atomicOr(a.err, (uint32_t)ERR_NONFINITE);
     claimed_groups<T, D>(a, E, C, u, n_march);
+}
+
+template <typename T, typename D>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBlocks - 2)
+    line_step_kernel(const StepArgs<T, D> a)
+{
+    __shared__ CrackState sS;
+    __shared__ Claims sC;                 // the claims and edge values, formed once per block
+    __shared__ EdgeValues<T> sE;
+    pdl_wait();
+    pdl_trigger();
+    line_cta<T, D>(a, blockIdx.x, sS, sC, sE);
+}
+
+// Many lattices with a crack in any direction in one launch: unit u is block
+// u.cb of lattice u.inst's grid (0: the tip CTA, then its march blocks),
+// run with the lattice's arguments for the current parity copied to shared
+// memory first; the per-CTA code is the single-lattice kernel's, so each
+// lattice ends bit-identical to its solo run.
+template <typename T, typename D>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : kMinBlocks - 2)
+    batch_line_kernel(const StepArgs<T, D> *descs, const BatchUnit *units, int par)
+{
+    __shared__ CrackState sS;
+    __shared__ Claims sC;
+    __shared__ EdgeValues<T> sE;
+    __shared__ __align__(16) StepArgs<T, D> sa;
+    pdl_wait();
+    pdl_trigger();
+    const BatchUnit u = units[blockIdx.x];
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(descs + 2 * u.inst + par);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(&sa);
+    for (int q = threadIdx.x; q < (int)(sizeof(StepArgs<T, D>) / 4); q += kThreads) dst[q] = src[q];
+    __syncthreads();
+    line_cta<T, D>(sa, u.cb, sS, sC, sE);
 }
 
 // Is tabulated site (i, j) a boundary point now, i.e. is one of its links
@@ -1063,6 +1093,15 @@ cudaError_t launch_line_step(const StepArgs<T, D> &a, cudaStream_t s)
                           a.chained != 0, a);
 }
 
+template <typename T, typename D>
+cudaError_t launch_batch_line(const StepArgs<T, D> *descs, const BatchUnit *units, int n_units, int par, cudaStream_t s,
+                              bool chained)
+{
+    if (n_units <= 0) return cudaSuccess;
+    return launch_chained(batch_line_kernel<T, D>, dim3((unsigned)n_units), dim3(kThreads), 0, s, chained, descs, units,
+                          par);
+}
+
 template <typename T>
 cudaError_t launch_line_finalize(const FinalizeArgs<T> &a, cudaStream_t s)
 {
@@ -1096,6 +1135,14 @@ template cudaError_t launch_line_step<double, double>(const StepArgs<double, dou
 template cudaError_t launch_line_step<float, float>(const StepArgs<float, float> &, cudaStream_t);
 template cudaError_t launch_line_step<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> &, cudaStream_t);
 template cudaError_t launch_line_step<float, __half>(const StepArgs<float, __half> &, cudaStream_t);
+template cudaError_t launch_batch_line<double, double>(const StepArgs<double, double> *, const BatchUnit *, int, int,
+                                                  cudaStream_t, bool);
+template cudaError_t launch_batch_line<float, float>(const StepArgs<float, float> *, const BatchUnit *, int, int,
+                                                  cudaStream_t, bool);
+template cudaError_t launch_batch_line<float, __nv_bfloat16>(const StepArgs<float, __nv_bfloat16> *, const BatchUnit *, int, int,
+                                                  cudaStream_t, bool);
+template cudaError_t launch_batch_line<float, __half>(const StepArgs<float, __half> *, const BatchUnit *, int, int,
+                                                  cudaStream_t, bool);
 template cudaError_t launch_line_finalize<double>(const FinalizeArgs<double> &, cudaStream_t);
 template cudaError_t launch_line_finalize<float>(const FinalizeArgs<float> &, cudaStream_t);
 

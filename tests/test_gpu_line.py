@@ -244,8 +244,16 @@ def test_calls_that_reject_the_handle(gpu):
     with pytest.raises(gpu.LbmError) as ei:
         gpu.lbm_set_launch(g.h, 8)
     assert ei.value.status == gpu.A.LBM_ERR_STATE
+    straight = gpu.Lattice(W.prescribed_strip(64, 32, 0.4), "f32")
     with pytest.raises(gpu.LbmError):
-        gpu.Batch([g])
+        gpu.Batch([g, straight])       # cracks along +x and in any direction apart
+    straight.close()
+    b = gpu.Batch([g])
+    with pytest.raises(gpu.LbmError):
+        b.set_shape(64, 16)
+    with pytest.raises(gpu.LbmError):
+        b.set_persistent(True)
+    b.close()
     launch = gpu.lbm_get_launch(g.h)
     assert launch["ctas"] == 1 + -(-64 // 512) * -(-32 // launch["band_rows"])
     q = gpu.Lattice(W.plain_fp64(), "f64")
@@ -479,3 +487,92 @@ def test_unsupported_face_points_are_flagged_like_the_oracle(oracle_mod, gpu, so
     assert o.flags() & 2 and g.crack_state()["flags"] & 2
     o.close()
     g.close()
+
+
+# ------------------------------------------------------------------ batches
+
+def _line_batch_problems():
+    """Uneven lattices with cracks in any direction: the four quadrant angles
+    (prescribed), K-criterion growth, both ends of a centre crack, and the
+    macroscopic rule on the faces (one and two ends), on lattices of one to
+    two column blocks with ragged ends."""
+    ps = []
+    for start, tip in ANGLES:
+        ps.append(W.with_line_crack(_problem(300, 90), mode="prescribed", start=start, tip=tip, v_rel=0.7, r0=2.0,
+                                    fit_width=2.0))
+    q = _problem(300, 90, u0=4e-3, t_ramp=60.0)
+    K_C = 0.4 * W.strip_reference_K(0.25, 4e-3, 90.0)
+    ps.append(W.with_line_crack(q, mode="kcrit", start=ANGLES[0][0], tip=ANGLES[0][1], K_C=K_C, v_max=0.85, r0=2.0))
+    start, tip = _centre(300, 200, 137.0, 20.0)
+    ps.append(W.with_line_crack(_problem(300, 200), mode="prescribed", start=start, tip=tip, v_rel=0.6, r0=2.0,
+                                two_tips=True))
+    start, tip = _centre(300, 200, 23.0, 20.0)
+    ps.append(W.with_line_crack(_macro(300, 200), mode="prescribed", start=start, tip=tip, v_rel=0.6, r0=2.0))
+    start, tip = _centre(300, 200, 61.0, 20.0)
+    ps.append(W.with_line_crack(_macro(300, 200), mode="prescribed", start=start, tip=tip, v_rel=0.6, r0=2.0,
+                                two_tips=True))
+    ps.append(W.with_line_crack(_problem(97, 45), mode="prescribed", start=(10.3, 12.1), tip=(40.6, 30.2), v_rel=0.5))
+    return ps
+
+
+def _same(a, b):
+    wa, wda = a.fields()
+    wb, wdb = b.fields()
+    assert np.array_equal(wa, wb) and np.array_equal(wda, wdb)
+    for k in ("h", "v"):
+        assert np.array_equal(a.cut_mask(k), b.cut_mask(k))
+    assert a.crack_state() == b.crack_state()
+    ha, hb = a.history(), b.history()
+    for k in ha:
+        assert np.array_equal(ha[k], hb[k])
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f32_bf16"])
+@pytest.mark.parametrize("solve", [0, 1])
+def test_batch_equals_solo_runs(gpu, storage, solve):
+    """One launch per step advances every lattice's line step (tip CTAs and
+    march blocks of all lattices), then each lattice with macroscopic faces
+    runs its face solve: each lattice ends bit-identical to its solo run."""
+    ps = _line_batch_problems()
+    solo = [gpu.Lattice(p, storage) for p in ps]
+    mem = [gpu.Lattice(p, storage) for p in ps]
+    for s_, m in zip(solo, mem):
+        s_.set_face_solve(solve)
+        m.set_face_solve(solve)
+    b = gpu.Batch(mem)
+    b.step(1)
+    b.step(120)
+    for s_ in solo:
+        s_.step(121)
+    for s_, m in zip(solo, mem):
+        _same(s_, m)
+    r = b.tune(trial_steps=4)
+    assert r["threads"] == 128 and r["lookahead"] == 1
+    b.step(30)
+    for s_ in solo:
+        s_.step(30)
+    for s_, m in zip(solo, mem):
+        _same(s_, m)
+    b.close()
+
+
+def test_batch_matches_the_oracle(oracle_mod, gpu):
+    """The batched lattices against the FP64 oracle: fields within 1e-12,
+    both cut masks and the prescribed tips (x and y) exact; the K-criterion
+    lattice's tips and K as in test_kcrit_growth_fp64."""
+    ps = _line_batch_problems()
+    steps = 150
+    lats = [gpu.Lattice(p, "f64") for p in ps]
+    b = gpu.Batch(lats)
+    b.step(steps)
+    b.close()
+    for p, g in zip(ps, lats):
+        o = oracle_mod.Oracle(p)
+        o.step(steps)
+        _close(o, g, TOL["f64"])
+        _masks(o, g)
+        ho, hg = _tips(o, g, steps)
+        if p["crack"]["mode"] == "kcrit":
+            np.testing.assert_allclose(hg["K"], ho["K"], rtol=0, atol=1e-9 * np.abs(ho["K"]).max())
+        o.close()
+        g.close()
