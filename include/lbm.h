@@ -142,8 +142,11 @@ typedef struct lbm_grid {
  * on an edge column are edge points themselves.  wdot_B = (w_B(t + dt) -
  * w_B(t)) / dt.  One extra small kernel per time step applies it.  Needs at
  * least 4 sites across each non-periodic pair of edges and a crack line at
- * least 4 dh from the bottom and top edges; not available to lbm_decomp_*
- * or lbm_tape_* (their create calls reject it). */
+ * least 4 dh from the bottom and top edges (from a row slab's halo edge the
+ * crack rows need only lie inside the slab).  Row slabs (lbm_decomp_*,
+ * lbm_slab_*) apply it to each slab's own edge sites after the step, before
+ * the boundary rows are exchanged; every slab then needs at least 4 rows.
+ * Not available to lbm_tape_* (its create call rejects it). */
 typedef struct lbm_lattice {
     int32_t velocity_set;
     int32_t form;

@@ -15,8 +15,14 @@
  * rows jc-1 and jc) are one own row and the halo row on either side, so both
  * form the same sums in the same order, reach the same K, the same decision
  * and the same severed links (each slab keeps its copy of the crack state
- * and of the crack row of the cut mask).  No other data crosses a boundary:
- * a decomposed run is bit-identical to the undivided one.  The paper runs on
+ * and of the crack row of the cut mask).  With LBM_BC_MACROSCOPIC_EDGES each
+ * slab applies the edge rule to its own edge sites (the left and right edge
+ * points of its rows; the bottom / top edge and corners in the first / last
+ * slab; the crack-face points on the edge columns, whose x_I, x_II are edge
+ * points of the same slab) after its step and before the exchange: every
+ * equation reads sites of its own row, or of rows of the same slab, and
+ * slabs take at least 4 rows.  No other data crosses a boundary: a
+ * decomposed run is bit-identical to the undivided one.  The paper runs on
  * one process.  lbm_decomp_* keeps all slabs on one device (one batched
  * launch and one row-exchange launch per step); lbm_slab_* gives one slab to
  * each process (or device), which exchange the boundary rows themselves.

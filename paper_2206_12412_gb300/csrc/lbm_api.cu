@@ -744,8 +744,11 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
     const bool macro_faces = lattice->bc_mode != LBM_BC_BOUNCEBACK;
     const bool macro_edges = lattice->bc_mode == LBM_BC_MACROSCOPIC_EDGES;
     if (macro_edges) {
-        // x_II of an edge point must not be a boundary point of the opposite edge
-        if (slab) return fail(LBM_ERR_ARG, "the macroscopic rule on the outer edges is not built for row slabs");
+        // x_II of an edge point must not be a boundary point of the opposite
+        // edge; in a row slab, x_II of a point of a ruled bottom or top edge,
+        // and the edge points a corner reads, must lie in the slab (its halo
+        // rows hold the previous step's rows when the rule runs): a slab
+        // takes at least four rows
         if (grid->edge[LBM_LEFT] != LBM_EDGE_PERIODIC && grid->nx < 4)
             return fail(LBM_ERR_ARG, "the macroscopic edge rule needs nx >= 4 between free or Dirichlet edges");
         if (grid->edge[LBM_BOTTOM] != LBM_EDGE_PERIODIC && grid->ny < 4)
@@ -777,7 +780,11 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
         if (!std::isfinite(yj) || std::fabs(yj - std::nearbyint(yj)) > 1e-9)
             return fail(LBM_ERR_ARG, "the crack line y must be a multiple of dh (between two rows)");
         jc = (int32_t)std::nearbyint(yj);
+        // the crack rows keep `margin` rows from a bottom or top edge; from a
+        // row slab's halo edge they need only lie inside the slab
         const int margin = macro_edges ? 4 : (macro_faces ? 3 : 1);
+        const int margin_lo = grid->edge[LBM_BOTTOM] == EDGE_HALO ? (macro_faces ? 3 : 1) : margin;
+        const int margin_hi = grid->edge[LBM_TOP] == EDGE_HALO ? (macro_faces ? 3 : 1) : margin;
         // a row slab may have the crack line on a halo boundary (the
         // neighbouring slab holds the other side's rows)
         const bool on_lo = slab && jc == 0 && grid->edge[LBM_BOTTOM] == EDGE_HALO;
@@ -786,7 +793,7 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
         if (on_lo || on_hi) {
             if (grid->ny < hh_rows + (on_lo && on_hi ? hh_rows : 0))
                 return fail(LBM_ERR_ARG, "a slab whose boundary is the crack line needs the crack rows of its side");
-        } else if (jc < margin || jc > grid->ny - margin) {
+        } else if (jc < margin_lo || jc > grid->ny - margin_hi) {
             return fail(LBM_ERR_ARG, "the crack line is too close to the bottom or top edge");
         }
         if (!(cr.x_start >= 0.0) || !(cr.x_tip >= cr.x_start)) return fail(LBM_ERR_ARG, "need 0 <= x_start <= x_tip");

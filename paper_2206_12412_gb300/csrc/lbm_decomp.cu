@@ -115,8 +115,6 @@ lbm_status lbm_decomp_create(const lbm_grid *grid, const lbm_lattice *lattice, c
     *out = nullptr;
     if (!grid || !lattice || !material) return fail(LBM_ERR_ARG, "grid, lattice and material are required");
     if (n_ranks < 1) return fail(LBM_ERR_ARG, "n_ranks must be >= 1");
-    if (lattice->bc_mode == LBM_BC_MACROSCOPIC_EDGES)
-        return fail(LBM_ERR_ARG, "the macroscopic rule on the outer edges is not built for row slabs");
     if (lattice->velocity_set != LBM_D2Q5) return fail(LBM_ERR_ARG, "row slabs are built for D2Q5 only");
     if (n_loads < 0 || (n_loads > 0 && !loads)) return fail(LBM_ERR_ARG, "bad loads array");
     for (int e = 0; e < 4; ++e)
@@ -329,8 +327,6 @@ lbm_status lbm_slab_create(const lbm_grid *grid, const lbm_lattice *lattice, con
     if (!out) return fail(LBM_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!grid || !lattice || !material) return fail(LBM_ERR_ARG, "grid, lattice and material are required");
-    if (lattice->bc_mode == LBM_BC_MACROSCOPIC_EDGES)
-        return fail(LBM_ERR_ARG, "the macroscopic rule on the outer edges is not built for row slabs");
     if (lattice->velocity_set != LBM_D2Q5) return fail(LBM_ERR_ARG, "row slabs are built for D2Q5 only");
     if (n_loads < 0 || (n_loads > 0 && !loads)) return fail(LBM_ERR_ARG, "bad loads array");
     for (int e = 0; e < 4; ++e)

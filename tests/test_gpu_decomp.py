@@ -192,3 +192,101 @@ def test_slabs_match_the_oracle(oracle_mod, gpu, storage, n_ranks):
         assert np.abs(hs["tip_q"] - ho["tip_q"]).max() < 2**32
     o.close()
     dec.close()
+
+
+# ---------------------------------- the macroscopic rule on every boundary
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("row_start", [None, [0, 64, 96], [0, 30, 61, 96], [0, 4, 50, 67, 96]])
+def test_edge_rule_on_every_boundary_in_slabs(gpu, storage, row_start):
+    """The Sec. 5.2 configuration at half size (256 x 96: centre crack, both
+    ends growing, the macroscopic rule on every boundary): each slab applies
+    the rule to its own edge sites after the step and before the rows are
+    exchanged -- the left and right edge points of every slab, the bottom and
+    top edges and the corners in the first and last slab, the crack-face
+    points on the edge columns in the slabs that hold the crack rows -- so the
+    slabs stay bit-identical to the undivided lattice; the boundary may lie on
+    the crack line, at the end of the crack rows, or cut a four-row slab."""
+    p = W.kcrit_centre_crack(scale=2)
+    n_ranks = 3 if row_start is None else len(row_start) - 1
+    _compare(gpu, p, storage, n_ranks, row_start=row_start)
+
+
+def test_edge_rule_slabs_through_crack_growth(gpu):
+    """The same problem from rest through the half-sine pulse until both
+    ends have grown, on two slabs split at the crack line (both run the
+    crack step) and on three."""
+    p = W.kcrit_centre_crack(scale=2)
+    n = W.KCRIT_CENTRE_STEPS // 2
+    ref = gpu.Lattice(p, "f64")
+    ref.step(n)
+    assert (ref.history(cap=n)["v"] > 0).sum() > 3 and (ref.history_left(cap=n)["v"] > 0).sum() > 3
+    w_r, wd_r = ref.fields()
+    for rs in ([0, 64, 96], None):
+        dec = gpu.Decomp(p, 2 if rs else 3, "f64", row_start=rs)
+        dec.step(1)
+        dec.step(n - 1)
+        w_d, wd_d = dec.fields()
+        np.testing.assert_array_equal(w_d, w_r)
+        np.testing.assert_array_equal(wd_d, wd_r)
+        slab = dec.rank(dec.info()["crack_rank"])
+        assert slab.crack_state() == ref.crack_state()
+        np.testing.assert_array_equal(slab.history(cap=n)["tip_q"], ref.history(cap=n)["tip_q"])
+        np.testing.assert_array_equal(slab.history_left(cap=n)["tip_q"], ref.history_left(cap=n)["tip_q"])
+        dec.close()
+    ref.close()
+
+
+def test_edge_rule_slabs_match_the_oracle(oracle_mod, gpu):
+    """Three slabs with the macroscopic rule on every boundary against the
+    FP64 oracle's undivided run: fields within 1e-12 of max(max|w|, 2 max|w*|)
+    (the Dirichlet values dominate the scale), the cut mask and both tips
+    exact."""
+    p = W.kcrit_centre_crack(scale=2)
+    n = 800
+    dec = gpu.Decomp(p, 3, "f64")
+    o = oracle_mod.Oracle(p)
+    dec.step(n)
+    o.step(n)
+    wo, wdo = o.fields()
+    wg, wdg = dec.fields()
+    ws = max(abs(L.get("amp", 0.0)) for L in p["loads"])
+    scale = max(np.abs(wo).max(), 2 * ws)
+    assert np.abs(wg - wo).max() <= 1e-12 * scale and np.abs(wdg - wdo).max() <= 1e-12 * scale
+    slab = dec.rank(dec.info()["crack_rank"])
+    np.testing.assert_array_equal(slab.history(cap=n)["tip_q"], o.history()["tip_q"][:n])
+    np.testing.assert_array_equal(slab.history_left(cap=n)["tip_q"], o.history_left()["tip_q"][:n])
+    ch, cv = o.cuts()
+    np.testing.assert_array_equal(slab.cut_mask("v"), cv.astype(bool)[slab.row0: slab.row0 + slab.ny])
+    o.close()
+    dec.close()
+
+
+def test_edge_rule_slab_handles_exchanging_on_the_host(gpu):
+    """One slab handle per part (the per-process form, lbm_slab_*), boundary
+    rows exported and imported on the host after every step: with the
+    macroscopic rule on every boundary, bit-identical to the undivided
+    lattice."""
+    p = W.kcrit_centre_crack(scale=2)
+    rs = [0, 40, 64, 96]
+    ref = gpu.Lattice(p, "f32")
+    slabs = [gpu.Slab(p, rs[r], rs[r + 1] - rs[r], "f32") for r in range(3)]
+
+    def exchange():
+        rows = [s.export_rows() for s in slabs]
+        for r, s in enumerate(slabs):
+            s.import_rows(rows[r - 1][1] if r > 0 else None, rows[r + 1][0] if r < 2 else None)
+
+    exchange()
+    for _ in range(150):
+        for s in slabs:
+            s.step(1)
+        exchange()
+    ref.step(150)
+    w_r, wd_r = ref.fields()
+    for r, s in enumerate(slabs):
+        w, wd = s.fields()
+        np.testing.assert_array_equal(w, w_r[rs[r]: rs[r + 1]])
+        np.testing.assert_array_equal(wd, wd_r[rs[r]: rs[r + 1]])
+        s.close()
+    ref.close()

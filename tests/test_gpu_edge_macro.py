@@ -221,7 +221,7 @@ def test_calls_that_reject_the_mode(gpu):
     with pytest.raises(gpu.LbmError):
         gpu.Tape(g, np.array([[5, 5]], np.int32), 4)
     with pytest.raises(gpu.LbmError):
-        gpu.Decomp(p, 2, "f32")
+        gpu.Decomp(p, 11, "f32")       # slabs of under four rows
     g.close()
     for bad in (W.base_problem(3, 32, bc_mode="macroscopic_edges"),
                 W.with_crack(W.base_problem(64, 32, bc_mode="macroscopic_edges"), mode="stationary", y=3.0, x_tip=9.0),
