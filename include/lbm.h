@@ -521,7 +521,10 @@ lbm_status lbm_batch_info(const lbm_batch *b, int32_t *n_lattices, int32_t *ctas
  * into row blocks of about one CTA's share, column block by column block, and
  * that sequence into one run per CTA; the crack sub-bands stay units of their
  * own), so that lattices of any heights fill one wave evenly; lbm_batch_info
- * then reports those CTAs.  Narrow column blocks leave fewer idle warps right of lattices
+ * then reports those CTAs; or with band_rows = -2 tapered bands: the
+ * lattices' units are launched largest lattice first, in bands of 48 rows,
+ * and the smallest lattices holding the last sixth of the sites take bands
+ * of 8 rows, so that the units handed out last are short.  Narrow column blocks leave fewer idle warps right of lattices
  * whose width is not a multiple of 512 columns; short bands give more CTAs.
  * The results do not depend on the shape (each lattice's time step is the
  * same arithmetic).  lbm_batch_set_shape synchronises the stream and
@@ -547,7 +550,7 @@ lbm_status lbm_batch_get_lookahead(const lbm_batch *b, int32_t *rows);
 /* Autotuner of the batched step's launch shape: times trial_steps (2..1024)
  * batched steps with CUDA events for every shape of lookahead in {1, 2} x
  * threads in {32, 64, 128} x band_rows in {-1 (balanced), 0 (one wave), 8, 16,
- * 32, 64}
+ * 32, 64, -2 (tapered)}
  * (the first of three repetitions a warm-up), keeps the fastest (its
  * lookahead is read back with lbm_batch_get_lookahead), and caches it in the process under the device's SM
  * count, the storage and the lattices' sizes and crack rows (a later batch of

@@ -2191,10 +2191,10 @@ lbm_status batch_build(lbm_batch *b, int threads, int rows, int la)
 {
     if (threads != 32 && threads != 64 && threads != kThreads)
         return fail(LBM_ERR_ARG, "threads per CTA must be 32, 64 or 128");
-    if (rows < -1) return fail(LBM_ERR_ARG, "band_rows must be >= 0, or -1 (balanced)");
+    if (rows < -2) return fail(LBM_ERR_ARG, "band_rows must be >= 0, -1 (balanced) or -2 (tapered)");
     if (la != 1 && la != 2) return fail(LBM_ERR_ARG, "lookahead must be 1 or 2 rows");
-    if (b->q == 9 && (threads != kThreads || la != 1 || rows < 0))
-        return fail(LBM_ERR_ARG, "a D2Q9 batch takes CTAs of 128 threads, bands of rows >= 0 and a lookahead of one row");
+    if (b->q == 9 && (threads != kThreads || la != 1 || rows == -1))
+        return fail(LBM_ERR_ARG, "a D2Q9 batch takes CTAs of 128 threads, bands (not the balanced form) and a lookahead of one row");
     if (b->line && (threads != kThreads || la != 1 || rows < 0))
         return fail(LBM_ERR_ARG, "a batch of cracks in any direction takes CTAs of 128 threads and a lookahead of one row");
     const bool balanced = rows == -1;
@@ -2204,6 +2204,26 @@ lbm_status batch_build(lbm_batch *b, int threads, int rows, int la)
     if (rows == 0) {
         lbm_status rc = batch_one_wave(b, threads, la, heights);
         if (rc != LBM_OK) return rc;
+    }
+    // the order the lattices' units are launched in
+    std::vector<size_t> order(b->hs.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    if (rows == -2) {
+        // tapered: the lattices by size, largest first; bands of 48 rows
+        // (few halo rows) until the smallest lattices that hold the last
+        // sixth of the sites, which take bands of 8 rows, so that the units
+        // the dispatcher hands out last are short and the step ends with a
+        // short tail
+        std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+            return (int64_t)b->hs[x]->grid.nx * b->hs[x]->grid.ny > (int64_t)b->hs[y]->grid.nx * b->hs[y]->grid.ny;
+        });
+        int64_t total = 0, seen = 0;
+        for (const lbm_handle *h : b->hs) total += (int64_t)h->grid.nx * h->grid.ny;
+        for (size_t k = 0; k < order.size(); ++k) {
+            const lbm_handle *h = b->hs[order[k]];
+            heights[order[k]] = seen * 6 < total * 5 ? 48 : 8;
+            seen += (int64_t)h->grid.nx * h->grid.ny;
+        }
     }
     std::vector<BatchUnit> units;
     if (b->line) {
@@ -2216,7 +2236,7 @@ lbm_status batch_build(lbm_batch *b, int threads, int rows, int la)
             for (int u = 0; u < n; ++u) units.push_back(BatchUnit{(int32_t)i, u, 0, 0});
         }
     } else {
-        for (size_t i = 0; i < b->hs.size(); ++i) {
+        for (size_t i : order) {
             lbm_handle *h = b->hs[i];
             drop_graph(h);
             lbm_status rc = plan_bands(h, heights[i]);
@@ -2547,7 +2567,7 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *threads, i
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return done(fail(LBM_ERR_CUDA, "creating timing events"));
     const int shapes_t[3] = {32, 64, kThreads};
-    const int shapes_r[6] = {-1, 0, 8, 16, 32, 64};   // -1: balanced pieces; 0: every CTA resident in one wave
+    const int shapes_r[7] = {-1, 0, 8, 16, 32, 64, -2};   // -1: balanced; 0: one wave; -2: tapered
     int best_t = b->threads, best_r = b->band_rows, best_la = b->lookahead;
     double best = 1e300;
     int par = b->hs[0]->parity;
@@ -2556,7 +2576,7 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *threads, i
     const bool d9 = b->q == 9 || b->line;
     for (int la = 1; la <= (d9 ? 1 : 2); ++la)
         for (int ti = d9 ? 2 : 0; ti < 3; ++ti)
-            for (int ri = d9 ? 1 : 0; ri < (b->line ? 2 : 6); ++ri) {
+            for (int ri = d9 ? 1 : 0; ri < (b->line ? 2 : 7); ++ri) {
                 rc = batch_build(b, shapes_t[ti], shapes_r[ri], la);
                 if (rc != LBM_OK) return done(rc);
                 double t_min = 1e300;

@@ -175,7 +175,7 @@ def test_batch_matches_the_oracle(oracle_mod, gpu, storage, rows):
 
 @pytest.mark.parametrize("storage", ["f32", "f64"])
 @pytest.mark.parametrize("threads,rows", [(32, 8), (64, 5), (32, 64), (128, 32), (32, 0), (128, 0),
-                                          (32, -1), (64, -1), (128, -1)])
+                                          (32, -1), (64, -1), (128, -1), (64, -2), (128, -2)])
 def test_every_launch_shape_gives_the_solo_bits(gpu, storage, threads, rows):
     """CTAs of 32, 64 or 128 threads over bands of any height, and the
     balanced step (rows = -1: runs of row pieces, several lattices per CTA,
@@ -240,7 +240,7 @@ def test_tune_leaves_the_lattices_as_they_were_and_caches_the_shape(gpu):
     b = gpu.Batch(mem)
     b.step(37)                       # a pending crack step at the tuning call
     r = b.tune(trial_steps=6)
-    assert r["threads"] in (32, 64, 128) and r["band_rows"] in (-1, 0, 8, 16, 32, 64) and r["lookahead"] in (1, 2)
+    assert r["threads"] in (32, 64, 128) and r["band_rows"] in (-2, -1, 0, 8, 16, 32, 64) and r["lookahead"] in (1, 2)
     assert not r["from_cache"] and r["us_per_step"] > 0
     info = b.info()
     assert (info["threads"], info["band_rows"], info["lookahead"]) == (r["threads"], r["band_rows"], r["lookahead"])
@@ -263,7 +263,7 @@ def test_shape_arguments_are_checked(gpu):
     ps = W.batch_problems(2, seed=6)
     lats = [gpu.Lattice(p, "f32") for p in ps]
     b = gpu.Batch(lats)
-    for t, r in ((48, 16), (256, 16), (32, -2)):
+    for t, r in ((48, 16), (256, 16), (32, -3)):
         with pytest.raises(gpu.LbmError) as ei:
             b.set_shape(t, r)
         assert ei.value.status == -1

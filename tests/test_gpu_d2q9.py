@@ -351,7 +351,7 @@ def _pair(gpu, ps, storage, seed):
 
 
 @pytest.mark.parametrize("storage", ["f64", "f32"])
-@pytest.mark.parametrize("rows", [0, 5, 32])
+@pytest.mark.parametrize("rows", [0, 5, 32, -2])
 def test_d2q9_batch_equals_solo_runs(gpu, storage, rows):
     """One launch per step advances every D2Q9 lattice of the batch (then one
     launch for the crack-face rule and one for the edge rule): each lattice
@@ -414,7 +414,7 @@ def test_d2q9_batch_tune_keeps_the_lattices(gpu):
     b = gpu.Batch(mem)
     b.step(40)
     r = b.tune(trial_steps=4)
-    assert r["threads"] == 128 and r["lookahead"] == 1 and r["band_rows"] in (0, 8, 16, 32, 64)
+    assert r["threads"] == 128 and r["lookahead"] == 1 and r["band_rows"] in (-2, 0, 8, 16, 32, 64)
     b.step(60)
     for s_ in solo:
         s_.step(100)
