@@ -28,7 +28,10 @@
  *     reads or replaces the state, or by the next lbm_step;
  *   - a device-side error (a non-finite field) is sticky: every later call on
  *     the handle returns LBM_ERR_UNSTABLE;
- *   - lbm_last_error() describes the most recent failure on the calling thread.
+ *   - lbm_last_error() describes the most recent failure on the calling thread;
+ *   - a handle lives on the device that was current when it was created; make
+ *     every call on it with that device current (the library does not switch
+ *     devices).
  *
  * Geometry: sites sit at cell centres ((i + 1/2) dh, (j + 1/2) dh),
  * 0 <= i < nx, 0 <= j < ny; outer edges lie on half links.  Field planes are
