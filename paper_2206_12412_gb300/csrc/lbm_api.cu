@@ -330,7 +330,12 @@ cudaError_t enqueue_step_t(const lbm_handle *h, int par, cudaStream_t s)
     make_step_args(h, par, a);
     if constexpr (!std::is_same<D, Lf>::value) {   // a crack in any direction has no leapfrog storage
         if (h->line) {
-            cudaError_t e = launch_line_step(a, s);
+            cudaError_t e;
+            {
+                lbm::NvtxRange r("K1 line step");
+                e = launch_line_step(a, s);
+            }
+            lbm::NvtxRange r("K2 line faces");
             if (e == cudaSuccess && h->n_face_chunks > 0 && h->face_solve == 0)
                 e = launch_line_faces_chunked(a, h->face_chunks, h->n_face_chunks, h->face_items, s);
             else if (e == cudaSuccess && h->n_faces > 0)
@@ -340,14 +345,26 @@ cudaError_t enqueue_step_t(const lbm_handle *h, int par, cudaStream_t s)
     }
     if constexpr (std::is_same<T, D>::value) {
         if (h->q == 9) {
-            cudaError_t e = launch_d2q9_step(a, s);
+            cudaError_t e;
+            {
+                lbm::NvtxRange r("K1 d2q9 step");
+                e = launch_d2q9_step(a, s);
+            }
+            lbm::NvtxRange r("K2 d2q9 faces / edge rule");
             if (e == cudaSuccess && h->cp.macro && h->cp.mode != CRACK_NONE) e = launch_d2q9_faces(a, s);
             if (e == cudaSuccess && h->edge_macro) e = launch_edge_rule(a, s);
             return e;
         }
     }
-    cudaError_t e = launch_step(a, h->n_bands, s, h->bulk);
-    if (e == cudaSuccess && h->edge_macro) e = launch_edge_rule(a, s);
+    cudaError_t e;
+    {
+        lbm::NvtxRange r("K1 step");
+        e = launch_step(a, h->n_bands, s, h->bulk);
+    }
+    if (e == cudaSuccess && h->edge_macro) {
+        lbm::NvtxRange r("K2 edge rule");
+        e = launch_edge_rule(a, s);
+    }
     return e;
 }
 
@@ -453,6 +470,7 @@ namespace host {
 lbm_status finalize(lbm_handle *h)
 {
     if (!h->pending) return LBM_OK;
+    lbm::NvtxRange r("K3 crack step (finalize)");
     LBM_CUDA(timed(h, 1, [&] { return enqueue_finalize(h, h->stream); }));
     h->pending = false;
     return LBM_OK;
@@ -1137,6 +1155,7 @@ extern "C" {
 
 lbm_status lbm_step(lbm_handle *h, int64_t n)
 {
+    lbm::NvtxRange nvtx_("lbm_step");
     if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
     if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");
     if (n < 0) return fail(LBM_ERR_ARG, "n must be >= 0");
@@ -1179,6 +1198,7 @@ static int32_t exchange_dtype(const lbm_handle *h) { return h->esize == 8 ? LBM_
 
 lbm_status lbm_fields(lbm_handle *h, int32_t which, void *dst, int32_t dst_on_device, int32_t dtype)
 {
+    lbm::NvtxRange nvtx_("lbm_fields");
     if (!h || !dst) return fail(LBM_ERR_ARG, "handle or dst is NULL");
     if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");
     if (which != LBM_FIELD_W && which != LBM_FIELD_WDOT) return fail(LBM_ERR_ARG, "unknown field");
@@ -1207,6 +1227,7 @@ lbm_status lbm_fields(lbm_handle *h, int32_t which, void *dst, int32_t dst_on_de
 
 lbm_status lbm_set_fields(lbm_handle *h, int32_t which, const void *src, int32_t src_on_device, int32_t dtype)
 {
+    lbm::NvtxRange nvtx_("lbm_set_fields");
     if (!h || !src) return fail(LBM_ERR_ARG, "handle or src is NULL");
     if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");
     if (which != LBM_FIELD_W && which != LBM_FIELD_WDOT) return fail(LBM_ERR_ARG, "unknown field");
@@ -1347,6 +1368,7 @@ namespace {
 lbm_status crack_state_impl(lbm_handle *h, bool left, lbm_crack_state_t *now, double *K_hist, double *v_hist,
                             int64_t *tip_hist, int32_t *npairs_hist, int64_t cap, int64_t *n_written)
 {
+    lbm::NvtxRange nvtx_("lbm_crack_state");
     if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
     if (left && !h->cp.two_tips) return fail(LBM_ERR_STATE, "the crack has one growing end");
     lbm_status rc = finalize(h);
@@ -1748,6 +1770,7 @@ extern "C" {
 
 lbm_status lbm_save(lbm_handle *h, const char *path)
 {
+    lbm::NvtxRange nvtx_("lbm_save");
     if (!h || !path) return fail(LBM_ERR_ARG, "handle or path is NULL");
     if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");
     lbm_status rc = finalize(h);   // the state after the crack step of the last time step
@@ -1773,6 +1796,7 @@ lbm_status lbm_save(lbm_handle *h, const char *path)
 
 lbm_status lbm_load(lbm_handle *h, const char *path)
 {
+    lbm::NvtxRange nvtx_("lbm_load");
     if (!h || !path) return fail(LBM_ERR_ARG, "handle or path is NULL");
     if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");
     FILE *f = std::fopen(path, "rb");
@@ -2511,6 +2535,7 @@ lbm_status lbm_batch_get_shape(const lbm_batch *b, int32_t *threads, int32_t *ba
 lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *threads, int32_t *band_rows,
                           double *us_per_step, int32_t *from_cache)
 {
+    lbm::NvtxRange nvtx_("lbm_batch_tune");
     if (!b) return fail(LBM_ERR_ARG, "batch is NULL");
     if (trial_steps < 2 || trial_steps > 1024) return fail(LBM_ERR_ARG, "trial_steps must be in [2, 1024]");
     lbm_status rc = batch_check(b);
@@ -2628,6 +2653,7 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *threads, i
 
 lbm_status lbm_batch_step(lbm_batch *b, int64_t n)
 {
+    lbm::NvtxRange nvtx_("lbm_batch_step");
     if (!b) return fail(LBM_ERR_ARG, "batch is NULL");
     if (n < 0) return fail(LBM_ERR_ARG, "n must be >= 0");
     const int par0 = b->hs[0]->parity;

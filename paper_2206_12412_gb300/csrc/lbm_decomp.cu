@@ -256,6 +256,7 @@ lbm_status lbm_decomp_create(const lbm_grid *grid, const lbm_lattice *lattice, c
 
 lbm_status lbm_decomp_step(lbm_decomp *d, int64_t n)
 {
+    lbm::NvtxRange nvtx_("lbm_decomp_step");
     if (!d) return fail(LBM_ERR_ARG, "decomposition is NULL");
     if (n < 0) return fail(LBM_ERR_ARG, "n must be >= 0");
     lbm_status rc = batch_check(d->batch);
@@ -382,6 +383,7 @@ lbm_status lbm_slab_create(const lbm_grid *grid, const lbm_lattice *lattice, con
 
 lbm_status lbm_slab_export(lbm_handle *h, int32_t side, void *dst, int32_t dst_on_device)
 {
+    lbm::NvtxRange nvtx_("lbm_slab_export");
     if (!h || !dst) return fail(LBM_ERR_ARG, "handle or dst is NULL");
     if (side != 0 && side != 1) return fail(LBM_ERR_ARG, "side must be 0 (bottom row) or 1 (top row)");
     if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");
@@ -396,6 +398,7 @@ lbm_status lbm_slab_export(lbm_handle *h, int32_t side, void *dst, int32_t dst_o
 
 lbm_status lbm_slab_import(lbm_handle *h, int32_t side, const void *src, int32_t src_on_device)
 {
+    lbm::NvtxRange nvtx_("lbm_slab_import");
     if (!h || !src) return fail(LBM_ERR_ARG, "handle or src is NULL");
     if (side != 0 && side != 1) return fail(LBM_ERR_ARG, "side must be 0 (below row 0) or 1 (above the top row)");
     if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");

@@ -12,6 +12,37 @@ typedef struct lbm_batch lbm_batch;
 #include <type_traits>
 #include <vector>
 
+#ifndef LBM_NO_NVTX
+#include <nvtx3/nvToolsExt.h>
+#endif
+
+namespace lbm {
+// A named range on the host timeline, for profilers (Nsight Systems, or
+// ncu's --nvtx-include filters): one per C-ABI call that enqueues or waits
+// for GPU work, and one per kernel family of a time step (K1 the step with
+// the deferred crack step, K2 the crack-face and edge-rule solves, K3 the
+// stand-alone crack step).  NVTX v3 is header-only; with no tool attached a
+// range costs one indirect call.  Compile with -DLBM_NO_NVTX to drop them.
+struct NvtxRange {
+    explicit NvtxRange(const char *name)
+    {
+#ifndef LBM_NO_NVTX
+        nvtxRangePushA(name);
+#else
+        (void)name;
+#endif
+    }
+    ~NvtxRange()
+    {
+#ifndef LBM_NO_NVTX
+        nvtxRangePop();
+#endif
+    }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace lbm
+
 using lbm::Unit;
 using lbm::CrackState;
 using lbm::History;

@@ -354,6 +354,7 @@ lbm_status lbm_tape_create(lbm_handle *h, const int32_t *sensors, int32_t n_sens
 
 lbm_status lbm_tape_forward(lbm_tape *t, const double *targets, int32_t targets_on_device, double *loss)
 {
+    lbm::NvtxRange nvtx_("lbm_tape_forward");
     if (!t) return fail(LBM_ERR_ARG, "tape is NULL");
     if (!targets && t->ns > 0) return fail(LBM_ERR_ARG, "targets is NULL");
     lbm_handle *h = t->h;
@@ -403,6 +404,7 @@ lbm_status lbm_tape_loss_device(const lbm_tape *t, const double **loss)
 lbm_status lbm_tape_backward(lbm_tape *t, double *dL_dload, int32_t load_on_device, void *dL_dw0, void *dL_dwdot0,
                              int32_t fields_on_device, int32_t dtype)
 {
+    lbm::NvtxRange nvtx_("lbm_tape_backward");
     if (!t) return fail(LBM_ERR_ARG, "tape is NULL");
     lbm_handle *h = t->h;
     if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");
