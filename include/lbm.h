@@ -310,6 +310,18 @@ lbm_status lbm_fields(lbm_handle *h, int32_t which, void *dst, int32_t dst_on_de
  * step counter and history are left unchanged. */
 lbm_status lbm_set_fields(lbm_handle *h, int32_t which, const void *src, int32_t src_on_device, int32_t dtype);
 
+/* lbm_fields / lbm_set_fields for an ny x nx array whose rows lie row_stride
+ * >= nx elements apart (for example nx columns of a wider array): element
+ * (j, i) at dst[j * row_stride + i].  The same fields (w, wdot of Sec. 3:
+ * the state (w, wdot) that the moment form of the update advances), the
+ * same dtype rule, the same host/device and synchronisation rules; the
+ * elements between rows are left untouched.  row_stride == nx is the dense
+ * call; row_stride < nx returns LBM_ERR_ARG. */
+lbm_status lbm_fields_strided(lbm_handle *h, int32_t which, void *dst, int32_t dst_on_device, int32_t dtype,
+                              int64_t row_stride);
+lbm_status lbm_set_fields_strided(lbm_handle *h, int32_t which, const void *src, int32_t src_on_device, int32_t dtype,
+                                  int64_t row_stride);
+
 /* Copy a cut mask into host memory: row j occupies words_per_row =
  * ceil(nx / 32) words starting at j * words_per_row; bit b of word w is
  * column 32 w + b.  LBM_MASK_H bit (i, j): link (i,j)-(i+1,j) severed (i =
@@ -505,6 +517,24 @@ void lbm_destroy(lbm_handle *h);
 typedef struct lbm_batch lbm_batch;
 lbm_status lbm_batch_create(lbm_handle *const *handles, int32_t n, int32_t band_rows, const lbm_allocator *allocator,
                             lbm_batch **out);
+
+/* Create n lattices (member i as lbm_create(&grids[i], &lattices[i],
+ * &materials[i], cracks ? &cracks[i] : NULL, loads ? loads[i] : NULL,
+ * n_loads ? n_loads[i] : 0, stream, allocator)) and group them as
+ * lbm_batch_create(..., band_rows, allocator) does.  The batch owns them:
+ * lbm_batch_destroy destroys them too (lbm_batch_member gives each handle,
+ * for reading fields, masks and crack states; do not destroy those handles).
+ * The paper has no batches: many independent runs of the method (Sec. 3,
+ * Alg. 1), each exactly as one lattice, advance in one launch per step.
+ * loads and n_loads are both NULL or both given.  On error nothing is left
+ * allocated and the message names the member that failed. */
+lbm_status lbm_create_batch(int32_t n, const lbm_grid *grids, const lbm_lattice *lattices, const lbm_material *materials,
+                            const lbm_crack *cracks, const lbm_loading *const *loads, const int32_t *n_loads,
+                            void *stream, const lbm_allocator *allocator, int32_t band_rows, lbm_batch **out);
+
+/* Member i (0 <= i < n) of a batch: the handle, in the order given at
+ * create.  LBM_ERR_ARG for an index out of range. */
+lbm_status lbm_batch_member(const lbm_batch *b, int32_t i, lbm_handle **h);
 
 /* Enqueue n >= 0 time steps of every lattice of the batch on the shared
  * stream (CUDA-graph replay of 64-step chunks). */

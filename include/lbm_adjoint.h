@@ -91,6 +91,19 @@ lbm_status lbm_tape_misfits(lbm_tape *t, double *dst, int32_t dst_on_device);
 /* Release the tape (NULL is ignored); synchronises the handle's stream. */
 void lbm_tape_destroy(lbm_tape *t);
 
+/* The whole sensor-misfit gradient in one call: lbm_tape_create(h, sensors,
+ * n_sens, n_steps, checkpoint_every, allocator), lbm_tape_forward(targets,
+ * targets_on_device, loss), lbm_tape_backward(dL_dload, load_on_device,
+ * dL_dw0, dL_dwdot0, fields_on_device, dtype), lbm_tape_destroy -- the same
+ * arguments, meanings and results (bit-identical to that sequence).  The
+ * handle ends n_steps on, as after lbm_tape_forward; the stream is
+ * synchronised before returning, so every output is complete.  The error of
+ * the first call that fails is returned and the tape is released. */
+lbm_status lbm_adjoint(lbm_handle *h, const int32_t *sensors, int32_t n_sens, int64_t n_steps, int32_t checkpoint_every,
+                       const double *targets, int32_t targets_on_device, double *loss, double *dL_dload,
+                       int32_t load_on_device, void *dL_dw0, void *dL_dwdot0, int32_t fields_on_device, int32_t dtype,
+                       const lbm_allocator *allocator);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,8 +21,13 @@
  * slab; the crack-face points on the edge columns, whose x_I, x_II are edge
  * points of the same slab) after its step and before the exchange: every
  * equation reads sites of its own row, or of rows of the same slab, and
- * slabs take at least 4 rows.  No other data crosses a boundary: a
- * decomposed run is bit-identical to the undivided one.  The paper runs on
+ * slabs take at least 4 rows.  A D2Q9 lattice (LBM_D2Q9) splits the same
+ * way: its nine-point update reads rows j-1, j, j+1 only, so the one halo
+ * row per side still carries everything (the diagonal neighbours are sites
+ * of that row); its crack rows stay inside one slab (its diagonal cuts, its
+ * crack step and its crack-face rule read both sides of the crack line), so
+ * no boundary may lie on the crack line.  No other data crosses a boundary:
+ * a decomposed run is bit-identical to the undivided one.  The paper runs on
  * one process.  lbm_decomp_* keeps all slabs on one device (one batched
  * launch and one row-exchange launch per step); lbm_slab_* gives one slab to
  * each process (or device), which exchange the boundary rows themselves.
@@ -43,15 +48,17 @@ typedef struct lbm_decomp lbm_decomp;
  * least 2 rows whose boundaries avoid the crack rows [jc - hh, jc + hh)
  * except the crack line jc itself (a boundary that falls strictly inside
  * moves to the nearest of jc - hh, jc and jc + hh); jc < 0 means no crack.  hh = 3 with macroscopic crack faces, 1 with bounce-back.
+ * This is the D2Q5 split; lbm_decomp_create plans a D2Q9 lattice's split
+ * itself, moving a boundary to the nearer of jc - hh and jc + hh.
  * Writes n_ranks + 1 values (0 first, ny last) to row_start (host memory).
  * LBM_ERR_ARG if no such split exists.  Host-only; touches no device. */
 lbm_status lbm_decomp_plan(int32_t ny, int32_t jc, int32_t hh, int32_t n_ranks, int32_t *row_start);
 
 /* Build the lattice of lbm_create as n_ranks slabs (arguments as for
- * lbm_create; storage any).  row_start: n_ranks + 1 ascending row indices
- * from 0 to ny with every slab at least 2 rows and no boundary inside the
- * crack rows but the crack line (then with the hh rows of each side in its
- * slab), or NULL for lbm_decomp_plan's split.  Slab r holds rows row_start[r]
+ * lbm_create; storage any the lattice takes).  row_start: n_ranks + 1
+ * ascending row indices from 0 to ny with every slab at least 2 rows and no
+ * boundary inside the crack rows but, for D2Q5, the crack line (then with
+ * the hh rows of each side in its slab), or NULL for the planned split.  Slab r holds rows row_start[r]
  * .. row_start[r+1]-1; its inner bottom/top edges are halo edges, its other
  * edges and loads those of the lattice; with FP16 wdot storage every slab
  * takes the scale the undivided lattice would.  LBM_ERR_ARG for bad input. */
@@ -89,7 +96,8 @@ void lbm_decomp_destroy(lbm_decomp *d);
  * periodic in y, otherwise the lattice's edge with its load.  The crack goes
  * to the slab when the crack line lies inside it or on one of its halo
  * boundaries (LBM_ERR_ARG when a boundary cuts the crack rows elsewhere, or
- * the slab lacks its side's crack rows).  FP16 wdot storage takes the scale
+ * the slab lacks its side's crack rows; for D2Q9, when a boundary cuts the
+ * crack rows at all, the crack line included).  FP16 wdot storage takes the scale
  * of the undivided lattice.  The handle is an ordinary lattice handle (step,
  * read, checkpoint and destroy it with the lbm.h calls; no batches or
  * tapes).

@@ -85,6 +85,8 @@ PROTOTYPES = {
     "lbm_step": (C.c_int, [C.c_void_p, C.c_int64]),
     "lbm_fields": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int32]),
     "lbm_set_fields": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int32]),
+    "lbm_fields_strided": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int32, C.c_int64]),
+    "lbm_set_fields_strided": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int32, C.c_int64]),
     "lbm_cut_mask": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_uint32), C.c_int64]),
     "lbm_crack_state": (C.c_int, [C.c_void_p, C.POINTER(CrackStateT), C.POINTER(C.c_double),
                                   C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
@@ -109,6 +111,10 @@ PROTOTYPES = {
     "lbm_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_int32, C.POINTER(Allocator),
                                    C.POINTER(C.c_void_p)]),
     "lbm_batch_step": (C.c_int, [C.c_void_p, C.c_int64]),
+    "lbm_create_batch": (C.c_int, [C.c_int32, C.POINTER(Grid), C.POINTER(Lattice_), C.POINTER(Material),
+                                   C.POINTER(Crack), C.POINTER(C.POINTER(Loading)), C.POINTER(C.c_int32),
+                                   C.c_void_p, C.POINTER(Allocator), C.c_int32, C.POINTER(C.c_void_p)]),
+    "lbm_batch_member": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]),
     "lbm_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "lbm_set_face_solve": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
     "lbm_set_bulk": (C.c_int, [C.c_void_p, C.c_int32]),
@@ -136,6 +142,9 @@ PROTOTYPES = {
                                     C.c_int32]),
     "lbm_tape_misfits": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "lbm_tape_destroy": (None, [C.c_void_p]),
+    "lbm_adjoint": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32, C.c_int64, C.c_int32, C.c_void_p,
+                              C.c_int32, C.POINTER(C.c_double), C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                              C.c_int32, C.c_int32, C.POINTER(Allocator)]),
     # include/lbm_decomp.h
     "lbm_decomp_plan": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_int32)]),
     "lbm_decomp_create": (C.c_int, [C.POINTER(Grid), C.POINTER(Lattice_), C.POINTER(Material), C.POINTER(Crack),

@@ -753,7 +753,6 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
     const bool d2q9 = lattice->velocity_set == LBM_D2Q9;
     if (d2q9 && lattice->storage != LBM_F64 && lattice->storage != LBM_F32)
         return fail(LBM_ERR_ARG, "D2Q9 needs LBM_F64 or LBM_F32 storage");
-    if (d2q9 && slab) return fail(LBM_ERR_ARG, "D2Q9 is not built for row slabs");
     if (lattice->form != LBM_FORM_MOMENT) return fail(LBM_ERR_ARG, "only the moment form is built");
     if (lattice->omega != 1.0) return fail(LBM_ERR_ARG, "omega = dt/tau must be 1 (tau = dt)");
     if (lattice->storage < LBM_F64 || lattice->storage > LBM_F32_LEAPFROG) return fail(LBM_ERR_ARG, "unknown storage");
@@ -808,6 +807,10 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
         const bool on_lo = slab && jc == 0 && grid->edge[LBM_BOTTOM] == EDGE_HALO;
         const bool on_hi = slab && jc == grid->ny && grid->edge[LBM_TOP] == EDGE_HALO;
         const int hh_rows = macro_faces ? 3 : 1;
+        // a D2Q9 slab holds both sides' crack rows: its crack step, diagonal
+        // cuts and face rule read the rows on both sides of the line
+        if (d2q9 && (on_lo || on_hi))
+            return fail(LBM_ERR_ARG, "a D2Q9 row slab needs the crack rows of both sides of the crack line inside it");
         if (on_lo || on_hi) {
             if (grid->ny < hh_rows + (on_lo && on_hi ? hh_rows : 0))
                 return fail(LBM_ERR_ARG, "a slab whose boundary is the crack line needs the crack rows of its side");
@@ -1255,6 +1258,77 @@ lbm_status lbm_set_fields(lbm_handle *h, int32_t which, const void *src, int32_t
         void *dst = which == LBM_FIELD_W ? h->w[h->parity] : h->wd;
         LBM_CUDA(cudaMemcpy2DAsync(dst, (size_t)h->pitch * h->esize, src, row, row, (size_t)h->grid.ny,
                                    src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+        if (which == LBM_FIELD_W) {
+            cudaError_t e = h->esize == 4
+                ? launch_fill_pads<float>(static_cast<float *>(dst), h->pitch, h->grid.nx, h->grid.ny, h->grid.edge, h->stream)
+                : launch_fill_pads<double>(static_cast<double *>(dst), h->pitch, h->grid.nx, h->grid.ny, h->grid.edge, h->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "filling pads");
+        }
+    }
+    if (!src_on_device) LBM_CUDA(cudaStreamSynchronize(h->stream));   // pageable source may be reused
+    return LBM_OK;
+}
+
+// Strided forms: row j of the caller's array starts row_stride elements after
+// row j - 1 (row_stride >= nx), e.g. a column window of a wider array.
+lbm_status lbm_fields_strided(lbm_handle *h, int32_t which, void *dst, int32_t dst_on_device, int32_t dtype,
+                              int64_t row_stride)
+{
+    lbm::NvtxRange nvtx_("lbm_fields_strided");
+    if (!h || !dst) return fail(LBM_ERR_ARG, "handle or dst is NULL");
+    if (row_stride < h->grid.nx) return fail(LBM_ERR_ARG, "row_stride must be >= nx");
+    if (row_stride == h->grid.nx) return lbm_fields(h, which, dst, dst_on_device, dtype);
+    if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");
+    if (which != LBM_FIELD_W && which != LBM_FIELD_WDOT) return fail(LBM_ERR_ARG, "unknown field");
+    if (dtype != exchange_dtype(h)) return fail(LBM_ERR_ARG, "dtype must be LBM_F64 for F64 storage, LBM_F32 otherwise");
+    const size_t row = (size_t)h->grid.nx * h->esize;
+    const cudaMemcpyKind kind = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const void *src;
+    size_t spitch;
+    if (which == LBM_FIELD_WDOT && (h->esize_d == 0 || wd16(h))) {
+        // converted to a dense FP32 array first (leapfrog: (w_n - w_{n-1}) / dt)
+        if (h->esize_d == 0)
+            LBM_CUDA(launch_lf_wdot(static_cast<const float *>(h->w[h->parity]), static_cast<const float *>(h->w[h->parity ^ 1]),
+                                    h->pitch, h->grid.nx, h->grid.ny, (float)h->grid.dt, h->staging, h->stream));
+        else
+            LBM_CUDA(wd_to_f32(h, h->staging, h->wd_scale, h->stream));
+        src = h->staging;
+        spitch = row;
+    } else {
+        src = which == LBM_FIELD_W ? h->w[h->parity] : h->wd;
+        spitch = (size_t)h->pitch * h->esize;
+    }
+    LBM_CUDA(cudaMemcpy2DAsync(dst, (size_t)row_stride * h->esize, src, spitch, row, (size_t)h->grid.ny, kind, h->stream));
+    if (!dst_on_device) return check_sticky(h);
+    return LBM_OK;
+}
+
+lbm_status lbm_set_fields_strided(lbm_handle *h, int32_t which, const void *src, int32_t src_on_device, int32_t dtype,
+                                  int64_t row_stride)
+{
+    lbm::NvtxRange nvtx_("lbm_set_fields_strided");
+    if (!h || !src) return fail(LBM_ERR_ARG, "handle or src is NULL");
+    if (row_stride < h->grid.nx) return fail(LBM_ERR_ARG, "row_stride must be >= nx");
+    if (row_stride == h->grid.nx) return lbm_set_fields(h, which, src, src_on_device, dtype);
+    if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");
+    if (which != LBM_FIELD_W && which != LBM_FIELD_WDOT) return fail(LBM_ERR_ARG, "unknown field");
+    if (dtype != exchange_dtype(h)) return fail(LBM_ERR_ARG, "dtype must be LBM_F64 for F64 storage, LBM_F32 otherwise");
+    const size_t row = (size_t)h->grid.nx * h->esize;
+    const cudaMemcpyKind kind = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (which == LBM_FIELD_WDOT && (h->esize_d == 0 || wd16(h))) {
+        // gathered into a dense FP32 array on the device, then converted as
+        // lbm_set_fields converts (which applies the pending crack step first;
+        // the staging array is not read by that step)
+        LBM_CUDA(cudaMemcpy2DAsync(h->staging, row, src, (size_t)row_stride * h->esize, row, (size_t)h->grid.ny, kind,
+                                   h->stream));
+        lbm_status rc = lbm_set_fields(h, which, h->staging, 1, dtype);
+        if (rc != LBM_OK) return rc;
+    } else {
+        lbm_status rc = finalize(h);   // the pending crack step reads the fields being replaced
+        if (rc != LBM_OK) return rc;
+        void *dst = which == LBM_FIELD_W ? h->w[h->parity] : h->wd;
+        LBM_CUDA(cudaMemcpy2DAsync(dst, (size_t)h->pitch * h->esize, src, (size_t)row_stride * h->esize, row,
+                                   (size_t)h->grid.ny, kind, h->stream));
         if (which == LBM_FIELD_W) {
             cudaError_t e = h->esize == 4
                 ? launch_fill_pads<float>(static_cast<float *>(dst), h->pitch, h->grid.nx, h->grid.ny, h->grid.edge, h->stream)
@@ -1891,6 +1965,7 @@ struct lbm_batch {
     cudaStream_t cap_stream;
     cudaGraphExec_t gexec;
     int gparity;
+    bool owns;           // made by lbm_create_batch: the member handles are destroyed with the batch
 };
 
 namespace {
@@ -2450,6 +2525,7 @@ lbm_status lbm_batch_create(lbm_handle *const *handles, int32_t n, int32_t band_
     b->err = nullptr;
     b->custom_alloc = allocator && allocator->alloc && allocator->release;
     if (b->custom_alloc) b->alloc = *allocator;
+    b->owns = false;
     auto bail = [&](lbm_status rc) {
         batch_release_block(b);
         batch_free(b, b->bar);
@@ -2720,7 +2796,52 @@ void lbm_batch_destroy(lbm_batch *b)
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     batch_release_block(b);
     batch_free(b, b->bar);
+    if (b->owns)
+        for (lbm_handle *h : b->hs) lbm_destroy(h);
     delete b;
+}
+
+lbm_status lbm_create_batch(int32_t n, const lbm_grid *grids, const lbm_lattice *lattices, const lbm_material *materials,
+                            const lbm_crack *cracks, const lbm_loading *const *loads, const int32_t *n_loads,
+                            void *stream, const lbm_allocator *allocator, int32_t band_rows, lbm_batch **out)
+{
+    lbm::NvtxRange nvtx_("lbm_create_batch");
+    if (!out) return fail(LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || !grids || !lattices || !materials) return fail(LBM_ERR_ARG, "need n >= 1 and the grid, lattice and material arrays");
+    if ((loads == nullptr) != (n_loads == nullptr)) return fail(LBM_ERR_ARG, "loads and n_loads come together");
+    std::vector<lbm_handle *> hs;
+    hs.reserve((size_t)n);
+    auto drop = [&](lbm_status rc) {
+        const std::string msg = last_error();
+        for (lbm_handle *h : hs) lbm_destroy(h);
+        return fail(rc, "lattice " + std::to_string(hs.size()) + ": " + msg);
+    };
+    for (int32_t i = 0; i < n; ++i) {
+        lbm_handle *h = nullptr;
+        lbm_status rc = lbm_create(grids + i, lattices + i, materials + i, cracks ? cracks + i : nullptr,
+                                   loads ? loads[i] : nullptr, n_loads ? n_loads[i] : 0, stream, allocator, &h);
+        if (rc != LBM_OK) return drop(rc);
+        hs.push_back(h);
+    }
+    lbm_batch *b = nullptr;
+    lbm_status rc = lbm_batch_create(hs.data(), n, band_rows, allocator, &b);
+    if (rc != LBM_OK) {
+        const std::string msg = last_error();
+        for (lbm_handle *h : hs) lbm_destroy(h);
+        return fail(rc, msg);
+    }
+    b->owns = true;
+    *out = b;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_member(const lbm_batch *b, int32_t i, lbm_handle **h)
+{
+    if (!b || !h) return fail(LBM_ERR_ARG, "batch or h is NULL");
+    if (i < 0 || i >= (int32_t)b->hs.size()) return fail(LBM_ERR_ARG, "member index out of range");
+    *h = b->hs[(size_t)i];
+    return LBM_OK;
 }
 
 lbm_status lbm_batch_set_persistent(lbm_batch *b, int32_t enable, int64_t budget_cycles)

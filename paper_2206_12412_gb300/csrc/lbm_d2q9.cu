@@ -38,6 +38,24 @@ namespace lbm {
 // Dirichlet, else the bottom / top edge.
 // Twice the Dirichlet value of each edge, selected without indexing (so that
 // it stays in registers).
+// The rate and integration of one D2Q9 site, with every rounding fixed:
+// wdot' = wdot + (g_a axis + g_d diag) as fma(g_a, axis, g_d diag) and
+// w' = fma(dt, wdot', w).  The sum of two products could otherwise be
+// contracted into an FMA either way round, and a compiler may choose
+// differently in different code paths (the bare, interior and edge-row
+// updates); fixed here, every path -- and so every band partition and every
+// row-slab split -- gives the same bits.
+__device__ __forceinline__ float d9_rate(float wd, float axis, float diag, float ga, float gd)
+{
+    return __fadd_rn(wd, __fmaf_rn(ga, axis, __fmul_rn(gd, diag)));
+}
+__device__ __forceinline__ double d9_rate(double wd, double axis, double diag, double ga, double gd)
+{
+    return __dadd_rn(wd, __fma_rn(ga, axis, __dmul_rn(gd, diag)));
+}
+__device__ __forceinline__ float d9_integrate(float w, float wd, float dt) { return __fmaf_rn(dt, wd, w); }
+__device__ __forceinline__ double d9_integrate(double w, double wd, double dt) { return __fma_rn(dt, wd, w); }
+
 template <typename T>
 struct TwoWs {
     T l, r, b, t;
@@ -78,6 +96,7 @@ __device__ __forceinline__ T march9(const StepArgs<T, T> &a, int x0, int j0, int
     const int nx = a.nx, ny = a.ny, jc = a.p.jc;
     const bool crack = a.p.mode != CRACK_NONE;
     const bool per_x = a.edge[LEFT] == EDGE_PERIODIC, per_y = a.edge[BOTTOM] == EDGE_PERIODIC;
+    const bool halo_b = a.edge[BOTTOM] == EDGE_HALO, halo_t = a.edge[TOP] == EDGE_HALO;
     const int kr = nx - 1 - x0;                       // element holding column nx - 1, if in [0, N)
     const bool owns_last = SPECIAL && kr >= 0 && kr < N && per_x;
     const int64_t P = a.pitch;
@@ -140,13 +159,13 @@ __device__ __forceinline__ T march9(const StepArgs<T, T> &a, int x0, int j0, int
                 const T wl = k == 0 ? lc : wc.v[k - 1], wr = k == N - 1 ? rc : wc.v[k + 1];
                 const T axis = (sc[k + 1] + (wl + wr)) - (T)4 * wc.v[k];
                 const T diag = (sc[k] + sc[k + 2]) - (T)4 * wc.v[k];
-                wdnew.v[k] = wdv.v[k] + (ga * axis + gd * diag);
-                wnew.v[k] = wc.v[k] + dt * wdnew.v[k];
+                wdnew.v[k] = d9_rate(wdv.v[k], axis, diag, ga, gd);
+                wnew.v[k] = d9_integrate(wc.v[k], wdnew.v[k], dt);
             }
             stg_row(a.w_out + x0 + (int64_t)j * P, wnew);
             stg_row(a.wd + x0 + (int64_t)j * P, wdnew);
             acc += wnew.v[0];
-        } else if (!crow && j != 0 && j != ny - 1) {
+        } else if (!crow && (j != 0 || halo_b) && (j != ny - 1 || halo_t)) {
 #pragma unroll
             for (int k = 0; k < N; ++k) {
                 const T wl = k == 0 ? lc : wc.v[k - 1], wr = k == N - 1 ? rc : wc.v[k + 1];
@@ -154,8 +173,8 @@ __device__ __forceinline__ T march9(const StepArgs<T, T> &a, int x0, int j0, int
                 const T bl = k == 0 ? lb : wb.v[k - 1], br = k == N - 1 ? rb : wb.v[k + 1];
                 const T axis = ((wa.v[k] + wb.v[k]) + (wl + wr)) - (T)4 * wc.v[k];
                 const T diag = ((al + bl) + (ar + br)) - (T)4 * wc.v[k];
-                wdnew.v[k] = wdv.v[k] + (ga * axis + gd * diag);
-                wnew.v[k] = wc.v[k] + dt * wdnew.v[k];
+                wdnew.v[k] = d9_rate(wdv.v[k], axis, diag, ga, gd);
+                wnew.v[k] = d9_integrate(wc.v[k], wdnew.v[k], dt);
             }
             if (!edge_warp) {
                 stg_row(a.w_out + x0 + (int64_t)j * P, wnew);
@@ -187,8 +206,8 @@ __device__ __forceinline__ T march9(const StepArgs<T, T> &a, int x0, int j0, int
                     }
                     const T axis = ((wa.v[k] + wb.v[k]) + (wl + wr)) - (T)4 * w0;
                     const T diag = ((al + bl) + (ar + br)) - (T)4 * w0;
-                    wdnew.v[k] = wdv.v[k] + (ga * axis + gd * diag);
-                    wnew.v[k] = w0 + dt * wdnew.v[k];
+                    wdnew.v[k] = d9_rate(wdv.v[k], axis, diag, ga, gd);
+                    wnew.v[k] = d9_integrate(w0, wdnew.v[k], dt);
                 }
                 if (x0 + N <= nx) {
                     stg_row(a.w_out + x0 + (int64_t)j * P, wnew);
@@ -207,7 +226,9 @@ __device__ __forceinline__ T march9(const StepArgs<T, T> &a, int x0, int j0, int
             uint32_t vbits = 0;
             if (crow && x0 < nx) vbits = a.cut_v[(int64_t)(jc - 1) * a.words + (x0 >> 5)] >> (x0 & 31);
             const bool below = j == jc - 1;           // crack row under the crack line: its links go up
-            const bool bot = j == 0 && !per_y, top = j == ny - 1 && !per_y;
+            // a row slab's halo edge is no edge: the row beyond it is the
+            // neighbouring slab's, loaded like any other row
+            const bool bot = j == 0 && !per_y && !halo_b, top = j == ny - 1 && !per_y && !halo_t;
 #pragma unroll
             for (int k = 0; k < N; ++k) {
                 const int i = x0 + k;
@@ -245,8 +266,8 @@ __device__ __forceinline__ T march9(const StepArgs<T, T> &a, int x0, int j0, int
                 else if (rgt || bot) br = leaving(a.edge, two_ws, rgt, bot, 1, -1, w0);
                 const T axis = ((up + dn) + (wl + wr)) - (T)4 * w0;
                 const T diag = ((al + bl) + (ar + br)) - (T)4 * w0;
-                wdnew.v[k] = wdv.v[k] + (ga * axis + gd * diag);
-                wnew.v[k] = w0 + dt * wdnew.v[k];
+                wdnew.v[k] = d9_rate(wdv.v[k], axis, diag, ga, gd);
+                wnew.v[k] = d9_integrate(w0, wdnew.v[k], dt);
             }
             if (x0 + N <= nx) {
                 stg_row(a.w_out + x0 + (int64_t)j * P, wnew);
@@ -361,7 +382,9 @@ __device__ __forceinline__ void d2q9_cta(const StepArgs<T, T> &a, int cb, int ba
     // away from the left / right edges in a band of bare rows takes the
     // march compiled without the edge and crack handling
     const bool per_y = a.edge[BOTTOM] == EDGE_PERIODIC;
-    const bool bare_band = j0 > 0 && j1 < ny && !(crack && j0 <= jc && j1 >= jc - 1) && !per_y;
+    // (the rows next to a row slab's halo edge are bare rows too)
+    const bool bare_band = (j0 > 0 || a.edge[BOTTOM] == EDGE_HALO) && (j1 < ny || a.edge[TOP] == EDGE_HALO) &&
+                           !(crack && j0 <= jc && j1 >= jc - 1) && !per_y;
     T acc = (T)0;
     if (xw0 < nx) {
         if (!edge_warp && bare_band) acc = march9<T, false>(a, x0, j0, j1, lq, rq, two_ws, false);

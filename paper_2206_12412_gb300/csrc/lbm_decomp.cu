@@ -33,22 +33,52 @@ struct lbm_decomp {
 namespace {
 
 // An inner boundary may not cut the crack's rows [jc - hh, jc + hh) except
-// on the crack line itself, where the slabs on both sides each hold their
-// side's hh rows.
-bool boundary_ok(int32_t b, int32_t below, int32_t above, int32_t jc, int32_t hh)
+// on the crack line itself (line_ok: D2Q5), where the slabs on both sides
+// each hold their side's hh rows.  A D2Q9 lattice keeps all 2 hh rows in one
+// slab: its diagonal cuts, crack step and face rule read both sides.
+bool boundary_ok(int32_t b, int32_t below, int32_t above, int32_t jc, int32_t hh, bool line_ok = true)
 {
     if (jc < 0 || b <= jc - hh || b >= jc + hh) return true;
-    return b == jc && below >= hh && above >= hh;
+    return line_ok && b == jc && below >= hh && above >= hh;
 }
 
-bool valid_split(int32_t ny, int32_t jc, int32_t hh, int32_t n, const int32_t *rs)
+bool valid_split(int32_t ny, int32_t jc, int32_t hh, int32_t n, const int32_t *rs, bool line_ok = true)
 {
     if (rs[0] != 0 || rs[n] != ny) return false;
     for (int r = 0; r < n; ++r)
         if (rs[r + 1] - rs[r] < 2) return false;
     for (int r = 1; r < n; ++r)
-        if (!boundary_ok(rs[r], rs[r] - rs[r - 1], rs[r + 1] - rs[r], jc, hh)) return false;
+        if (!boundary_ok(rs[r], rs[r] - rs[r - 1], rs[r + 1] - rs[r], jc, hh, line_ok)) return false;
     return true;
+}
+
+// Even slabs, each inner boundary that would cut the crack rows moved to the
+// nearest allowed row (an end of the crack rows, or the crack line itself
+// when line_ok).
+lbm_status plan_split(int32_t ny, int32_t jc, int32_t hh, int32_t n_ranks, int32_t *row_start, bool line_ok)
+{
+    if (!row_start) return fail(LBM_ERR_ARG, "row_start is NULL");
+    if (n_ranks < 1 || ny < 2 * n_ranks) return fail(LBM_ERR_ARG, "need 1 <= n_ranks <= ny / 2");
+    if (jc >= 0 && (hh < 0 || jc - hh < 0 || jc + hh > ny)) return fail(LBM_ERR_ARG, "crack rows outside the lattice");
+    std::vector<int32_t> rs((size_t)n_ranks + 1);
+    for (int r = 0; r <= n_ranks; ++r) {
+        int32_t b = (int32_t)(((int64_t)r * ny + n_ranks / 2) / n_ranks);
+        if (jc >= 0 && r > 0 && r < n_ranks && b > jc - hh && b < jc + hh && !(line_ok && b == jc)) {
+            // the nearest of the crack rows' ends (and the crack line itself)
+            const int32_t c[3] = {jc - hh, line_ok ? jc : jc + hh, jc + hh};
+            int32_t best = c[0];
+            for (int q = 1; q < 3; ++q)
+                if (std::abs(c[q] - b) < std::abs(best - b)) best = c[q];
+            b = best;
+        }
+        rs[(size_t)r] = b;
+    }
+    if (!valid_split(ny, jc, hh, n_ranks, rs.data(), line_ok))
+        return fail(LBM_ERR_ARG, line_ok ? "no split into slabs of >= 2 rows keeps each side's crack rows in one slab"
+                                         : "no split into slabs of >= 2 rows keeps the crack rows in one slab");
+    std::copy(rs.begin(), rs.end(), row_start);
+    clear_error();
+    return LBM_OK;
 }
 
 // First byte of padded row j of buffer p of slab h.
@@ -83,27 +113,7 @@ extern "C" {
 
 lbm_status lbm_decomp_plan(int32_t ny, int32_t jc, int32_t hh, int32_t n_ranks, int32_t *row_start)
 {
-    if (!row_start) return fail(LBM_ERR_ARG, "row_start is NULL");
-    if (n_ranks < 1 || ny < 2 * n_ranks) return fail(LBM_ERR_ARG, "need 1 <= n_ranks <= ny / 2");
-    if (jc >= 0 && (hh < 0 || jc - hh < 0 || jc + hh > ny)) return fail(LBM_ERR_ARG, "crack rows outside the lattice");
-    std::vector<int32_t> rs((size_t)n_ranks + 1);
-    for (int r = 0; r <= n_ranks; ++r) {
-        int32_t b = (int32_t)(((int64_t)r * ny + n_ranks / 2) / n_ranks);
-        if (jc >= 0 && r > 0 && r < n_ranks && b > jc - hh && b < jc + hh && b != jc) {
-            // the nearest of the crack rows' ends and the crack line itself
-            const int32_t c[3] = {jc - hh, jc, jc + hh};
-            int32_t best = c[0];
-            for (int q = 1; q < 3; ++q)
-                if (std::abs(c[q] - b) < std::abs(best - b)) best = c[q];
-            b = best;
-        }
-        rs[(size_t)r] = b;
-    }
-    if (!valid_split(ny, jc, hh, n_ranks, rs.data()))
-        return fail(LBM_ERR_ARG, "no split into slabs of >= 2 rows keeps each side's crack rows in one slab");
-    std::copy(rs.begin(), rs.end(), row_start);
-    clear_error();
-    return LBM_OK;
+    return plan_split(ny, jc, hh, n_ranks, row_start, true);
 }
 
 lbm_status lbm_decomp_create(const lbm_grid *grid, const lbm_lattice *lattice, const lbm_material *material,
@@ -115,11 +125,11 @@ lbm_status lbm_decomp_create(const lbm_grid *grid, const lbm_lattice *lattice, c
     *out = nullptr;
     if (!grid || !lattice || !material) return fail(LBM_ERR_ARG, "grid, lattice and material are required");
     if (n_ranks < 1) return fail(LBM_ERR_ARG, "n_ranks must be >= 1");
-    if (lattice->velocity_set != LBM_D2Q5) return fail(LBM_ERR_ARG, "row slabs are built for D2Q5 only");
     if (n_loads < 0 || (n_loads > 0 && !loads)) return fail(LBM_ERR_ARG, "bad loads array");
     for (int e = 0; e < 4; ++e)
         if (grid->edge[e] < LBM_EDGE_FREE || grid->edge[e] > LBM_EDGE_PERIODIC) return fail(LBM_ERR_ARG, "unknown edge kind");
     const int ny = grid->ny;
+    const bool line_ok = lattice->velocity_set != LBM_D2Q9;   // a boundary on the crack line (D2Q5 only)
     const bool has_crack = crack && crack->mode != LBM_CRACK_NONE;
     int32_t jc = -1, hh = 0;
     if (has_crack) {
@@ -132,10 +142,11 @@ lbm_status lbm_decomp_create(const lbm_grid *grid, const lbm_lattice *lattice, c
     std::vector<int32_t> rs((size_t)n_ranks + 1);
     if (row_start) {
         std::copy(row_start, row_start + n_ranks + 1, rs.begin());
-        if (!valid_split(ny, jc, hh, n_ranks, rs.data()))
-            return fail(LBM_ERR_ARG, "row_start must run from 0 to ny in slabs of >= 2 rows; a boundary may cut the crack rows only on the crack line");
+        if (!valid_split(ny, jc, hh, n_ranks, rs.data(), line_ok))
+            return fail(LBM_ERR_ARG, line_ok ? "row_start must run from 0 to ny in slabs of >= 2 rows; a boundary may cut the crack rows only on the crack line"
+                                             : "row_start must run from 0 to ny in slabs of >= 2 rows; a D2Q9 boundary may not cut the crack rows");
     } else {
-        lbm_status rc = lbm_decomp_plan(ny, jc, hh, n_ranks, rs.data());
+        lbm_status rc = plan_split(ny, jc, hh, n_ranks, rs.data(), line_ok);
         if (rc != LBM_OK) return rc;
     }
 
@@ -328,7 +339,6 @@ lbm_status lbm_slab_create(const lbm_grid *grid, const lbm_lattice *lattice, con
     if (!out) return fail(LBM_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!grid || !lattice || !material) return fail(LBM_ERR_ARG, "grid, lattice and material are required");
-    if (lattice->velocity_set != LBM_D2Q5) return fail(LBM_ERR_ARG, "row slabs are built for D2Q5 only");
     if (n_loads < 0 || (n_loads > 0 && !loads)) return fail(LBM_ERR_ARG, "bad loads array");
     for (int e = 0; e < 4; ++e)
         if (grid->edge[e] < LBM_EDGE_FREE || grid->edge[e] > LBM_EDGE_PERIODIC) return fail(LBM_ERR_ARG, "unknown edge kind");
@@ -344,8 +354,11 @@ lbm_status lbm_slab_create(const lbm_grid *grid, const lbm_lattice *lattice, con
         hh = lattice->bc_mode != LBM_BC_BOUNCEBACK ? 3 : 1;
     }
     // this slab's side of each inner boundary (the neighbour checks its own)
-    if ((row0 > 0 && !boundary_ok(row0, hh, rows, jc, hh)) || (r1 < ny && !boundary_ok(r1, rows, hh, jc, hh)))
-        return fail(LBM_ERR_ARG, "a slab boundary may cut the crack rows only on the crack line");
+    const bool line_ok = lattice->velocity_set != LBM_D2Q9;
+    if ((row0 > 0 && !boundary_ok(row0, hh, rows, jc, hh, line_ok)) ||
+        (r1 < ny && !boundary_ok(r1, rows, hh, jc, hh, line_ok)))
+        return fail(LBM_ERR_ARG, line_ok ? "a slab boundary may cut the crack rows only on the crack line"
+                                         : "a D2Q9 slab boundary may not cut the crack rows");
     const bool periodic_y = grid->edge[LBM_BOTTOM] == LBM_EDGE_PERIODIC;
     lbm_grid g = *grid;
     g.ny = rows;

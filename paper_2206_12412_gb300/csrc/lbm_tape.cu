@@ -483,4 +483,21 @@ void lbm_tape_destroy(lbm_tape *t)
     free_tape(t);
 }
 
+lbm_status lbm_adjoint(lbm_handle *h, const int32_t *sensors, int32_t n_sens, int64_t n_steps, int32_t checkpoint_every,
+                       const double *targets, int32_t targets_on_device, double *loss, double *dL_dload,
+                       int32_t load_on_device, void *dL_dw0, void *dL_dwdot0, int32_t fields_on_device, int32_t dtype,
+                       const lbm_allocator *allocator)
+{
+    lbm::NvtxRange nvtx_("lbm_adjoint");
+    lbm_tape *t = nullptr;
+    lbm_status rc = lbm_tape_create(h, sensors, n_sens, n_steps, checkpoint_every, allocator, &t);
+    if (rc != LBM_OK) return rc;
+    rc = lbm_tape_forward(t, targets, targets_on_device, loss);
+    if (rc == LBM_OK) rc = lbm_tape_backward(t, dL_dload, load_on_device, dL_dw0, dL_dwdot0, fields_on_device, dtype);
+    const std::string msg = rc == LBM_OK ? std::string() : std::string(last_error());
+    lbm_tape_destroy(t);   // synchronises the handle's stream: the outputs are complete
+    if (rc != LBM_OK) return fail(rc, msg);
+    return LBM_OK;
+}
+
 }  // extern "C"

@@ -104,6 +104,16 @@ def lbm_set_fields(h: int, which: int, src_ptr: int, on_device: bool, dtype: int
     _check(load_library().lbm_set_fields(C.c_void_p(h), which, C.c_void_p(src_ptr), int(bool(on_device)), dtype))
 
 
+def lbm_fields_strided(h: int, which: int, dst_ptr: int, on_device: bool, dtype: int, row_stride: int):
+    _check(load_library().lbm_fields_strided(C.c_void_p(h), which, C.c_void_p(dst_ptr), int(bool(on_device)), dtype,
+                                             int(row_stride)))
+
+
+def lbm_set_fields_strided(h: int, which: int, src_ptr: int, on_device: bool, dtype: int, row_stride: int):
+    _check(load_library().lbm_set_fields_strided(C.c_void_p(h), which, C.c_void_p(src_ptr), int(bool(on_device)),
+                                                 dtype, int(row_stride)))
+
+
 def lbm_cut_mask(h: int, which: int, dst: np.ndarray):
     assert dst.dtype == np.uint32 and dst.flags.c_contiguous
     _check(load_library().lbm_cut_mask(C.c_void_p(h), which, dst.ctypes.data_as(C.POINTER(C.c_uint32)), dst.size))
@@ -554,6 +564,37 @@ def lbm_batch_destroy(b: int):
         load_library().lbm_batch_destroy(C.c_void_p(b))
 
 
+def lbm_create_batch(problems, storage: str = "f32", stream: int = 0, allocator: A.Allocator | None = None,
+                     band_rows: int = 0) -> int:
+    """lbm_create_batch over problem dicts (one storage for all): the batch
+    owns its lattices."""
+    n = len(problems)
+    grids, lats, mats, cracks = (A.Grid * n)(), (A.Lattice_ * n)(), (A.Material * n)(), (A.Crack * n)()
+    load_arrs, nloads, keep = [], (C.c_int32 * n)(), []
+    for i, p in enumerate(problems):
+        g, lat, mat, cr, loads, k = make_structs(p, storage)
+        if isinstance(cr, A.CrackLine):
+            raise ValueError("lbm_create_batch takes cracks along +x (lbm_crack)")
+        grids[i], lats[i], mats[i], cracks[i] = g, lat, mat, cr
+        arr = (A.Loading * max(len(loads), 1))(*loads)
+        load_arrs.append(C.cast(arr, C.POINTER(A.Loading)))
+        nloads[i] = len(loads)
+        keep += [arr, k]
+    lptrs = (C.POINTER(A.Loading) * n)(*load_arrs)
+    out = C.c_void_p()
+    _check(load_library().lbm_create_batch(n, grids, lats, mats, cracks, lptrs, nloads, C.c_void_p(stream),
+                                           C.byref(allocator) if allocator is not None else None, int(band_rows),
+                                           C.byref(out)))
+    del keep
+    return out.value
+
+
+def lbm_batch_member(b: int, i: int) -> int:
+    out = C.c_void_p()
+    _check(load_library().lbm_batch_member(C.c_void_p(b), int(i), C.byref(out)))
+    return out.value
+
+
 class Batch:
     """Several Lattice objects advanced together, one kernel launch per step."""
 
@@ -695,6 +736,25 @@ class Tape:
             self.close()
         except Exception:
             pass
+
+
+def lbm_adjoint(lattice: Lattice, sensors, n_steps: int, targets, checkpoint_every: int = 0,
+                allocator: A.Allocator | None = None):
+    """The one-call form of a tape's forward run and transposed sweep
+    (lbm_adjoint): (L, dload (4, n_steps), dw0 (ny, nx), dwdot0 (ny, nx)) as
+    host numpy arrays."""
+    sens = np.ascontiguousarray(np.asarray(sensors, dtype=np.int32).reshape(-1, 2))
+    tg = np.ascontiguousarray(np.asarray(targets, dtype=np.float64).reshape(int(n_steps), sens.shape[0]))
+    loss = C.c_double(0.0)
+    dload = np.empty((4, int(n_steps)))
+    dw = np.empty((lattice.ny, lattice.nx), lattice.np_dtype)
+    dwd = np.empty((lattice.ny, lattice.nx), lattice.np_dtype)
+    _check(load_library().lbm_adjoint(C.c_void_p(lattice.h), sens.ctypes.data_as(C.POINTER(C.c_int32)),
+                                      sens.shape[0], int(n_steps), int(checkpoint_every), C.c_void_p(tg.ctypes.data),
+                                      0, C.byref(loss), C.c_void_p(dload.ctypes.data), 0, C.c_void_p(dw.ctypes.data),
+                                      C.c_void_p(dwd.ctypes.data), 0, lattice.dtype_code,
+                                      C.byref(allocator) if allocator is not None else None))
+    return loss.value, dload, dw, dwd
 
 
 def sensor_misfit(tape: Tape, edge: str, u, w0, wdot0, targets):

@@ -289,8 +289,6 @@ def test_calls_that_reject_the_lattice(gpu):
     b.close()
     with pytest.raises(gpu.LbmError):
         gpu.Tape(g, np.array([[5, 5]], np.int32), 4)
-    with pytest.raises(gpu.LbmError):
-        gpu.Decomp(p, 2, "f32")
     g.close()
     for storage in ("f32_bf16", "f32_f16"):
         with pytest.raises(gpu.LbmError):
