@@ -46,9 +46,11 @@ const char *last_error() { return g_err.c_str(); }
 
 void ChunkGraph::reset()
 {
-    if (exec) cudaGraphExecDestroy(exec);
-    exec = nullptr;
-    parity = -1;
+    for (auto &lv : exec)
+        for (auto &ex : lv) {
+            if (ex) cudaGraphExecDestroy(ex);
+            ex = nullptr;
+        }
     gen = -1;
 }
 
@@ -57,7 +59,6 @@ void ChunkGraph::reset()
 
 namespace {
 
-constexpr int64_t kGraphChunk = 64;   // time steps per captured graph (even)
 constexpr int64_t kDefaultHistCap = 65536;
 
 int64_t floor_div(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
@@ -356,6 +357,7 @@ cudaError_t enqueue_step_t(const lbm_handle *h, int par, cudaStream_t s)
             return e;
         }
     }
+    a.k_cta = use_k_cta(h) ? 1 : 0;
     cudaError_t e;
     {
         lbm::NvtxRange r("K1 step");
@@ -599,14 +601,7 @@ void free_host(lbm_handle *h)
     delete h;
 }
 
-void drop_graph(lbm_handle *h)
-{
-    if (h->gexec) {
-        cudaGraphExecDestroy(h->gexec);
-        h->gexec = nullptr;
-        h->gparity = -1;
-    }
-}
+void drop_graph(lbm_handle *h) { h->steps.reset(); }
 
 }  // namespace
 
@@ -871,7 +866,7 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
     h->g = g;
     h->stream = (cudaStream_t)stream;
     h->sticky = LBM_OK;
-    h->gparity = -1;
+    h->steps.gen = -1;
     h->units_h = new (std::nothrow) std::vector<Unit>();
     h->init_cut = new (std::nothrow) std::vector<uint32_t>();
     if (!h->units_h || !h->init_cut) {
@@ -1163,31 +1158,15 @@ lbm_status lbm_step(lbm_handle *h, int64_t n)
     if (h->sticky != LBM_OK) return fail(h->sticky, "the handle is in an error state");
     if (n < 0) return fail(LBM_ERR_ARG, "n must be >= 0");
     if (n > 0 && h->cp.mode != CRACK_NONE) h->pending = true;
+    if (!h->profiling) {
+        // runs of steps replay graphs of 64, 32, ..., 2 steps
+        int par = h->parity;
+        const lbm_status rc = run_chunks(h->steps, h->gen, h->stream, h->cap_stream, n, par,
+                                         [&](int p, cudaStream_t s) { return enqueue_step(h, p, s); });
+        h->parity = par;
+        return rc;
+    }
     while (n > 0) {
-        if (n >= kGraphChunk && !h->profiling) {
-            if (!h->gexec) {
-                cudaGraph_t graph;
-                LBM_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-                cudaError_t ce = cudaSuccess;
-                int par = h->parity;
-                for (int64_t q = 0; q < kGraphChunk && ce == cudaSuccess; ++q) {
-                    ce = enqueue_step(h, par, h->cap_stream);
-                    par ^= 1;
-                }
-                cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &graph);
-                if (ce != cudaSuccess) return cuda_fail(ce, "capturing the step graph");
-                if (ee != cudaSuccess) return cuda_fail(ee, "cudaStreamEndCapture");
-                ee = cudaGraphInstantiate(&h->gexec, graph, 0);
-                cudaGraphDestroy(graph);
-                if (ee != cudaSuccess) { h->gexec = nullptr; return cuda_fail(ee, "cudaGraphInstantiate"); }
-                h->gparity = h->parity;
-            }
-            if (h->parity == h->gparity) {
-                LBM_CUDA(cudaGraphLaunch(h->gexec, h->stream));
-                n -= kGraphChunk;
-                continue;
-            }
-        }
         LBM_CUDA(timed(h, 0, [&] { return enqueue_step(h, h->parity, h->stream); }));
         h->parity ^= 1;
         n -= 1;
@@ -1963,8 +1942,7 @@ struct lbm_batch {
     bool custom_alloc;
     cudaStream_t stream;
     cudaStream_t cap_stream;
-    cudaGraphExec_t gexec;
-    int gparity;
+    ChunkGraph graph;    // graphs of runs of batched steps
     bool owns;           // made by lbm_create_batch: the member handles are destroyed with the batch
 };
 
@@ -2414,10 +2392,7 @@ lbm_status batch_build(lbm_batch *b, int threads, int rows, int la)
         e = cudaMemcpyAsync(b->eunits, eunits.data(), eunits.size() * sizeof(BatchUnit), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return cuda_fail(e, "uploading the batch tables");
-    if (b->gexec) {
-        cudaGraphExecDestroy(b->gexec);
-        b->gexec = nullptr;
-    }
+    b->graph.reset();
     b->threads = threads;
     b->band_rows = rows;
     b->lookahead = la;
@@ -2506,8 +2481,7 @@ lbm_status lbm_batch_create(lbm_handle *const *handles, int32_t n, int32_t band_
     b->block_bytes = 0;
     b->stream = handles[0]->stream;
     b->cap_stream = nullptr;
-    b->gexec = nullptr;
-    b->gparity = -1;
+    b->graph.gen = -1;
     b->q = handles[0]->q;
     b->line = handles[0]->line;
     b->funits = nullptr;
@@ -2585,10 +2559,7 @@ lbm_status lbm_batch_set_chained(lbm_batch *b, int32_t enable)
     if (rc != LBM_OK) return rc;
     for (lbm_handle *h : b->hs) LBM_CUDA(cudaStreamSynchronize(h->stream));
     b->chained = enable != 0;
-    if (b->gexec) {
-        cudaGraphExecDestroy(b->gexec);
-        b->gexec = nullptr;
-    }
+    b->graph.reset();
     clear_error();
     return LBM_OK;
 }
@@ -2744,34 +2715,11 @@ lbm_status lbm_batch_step(lbm_batch *b, int64_t n)
         par ^= (int)(n & 1);
         left = 0;
     }
-    while (left > 0) {
-        if (left >= kGraphChunk) {
-            if (!b->gexec) {
-                cudaGraph_t graph;
-                LBM_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
-                cudaError_t ce = cudaSuccess;
-                int p = par;
-                for (int64_t q = 0; q < kGraphChunk && ce == cudaSuccess; ++q) {
-                    ce = enqueue_batch_step(b, p, b->cap_stream);
-                    p ^= 1;
-                }
-                cudaError_t ee = cudaStreamEndCapture(b->cap_stream, &graph);
-                if (ce != cudaSuccess) return cuda_fail(ce, "capturing the batch graph");
-                if (ee != cudaSuccess) return cuda_fail(ee, "cudaStreamEndCapture");
-                ee = cudaGraphInstantiate(&b->gexec, graph, 0);
-                cudaGraphDestroy(graph);
-                if (ee != cudaSuccess) { b->gexec = nullptr; return cuda_fail(ee, "cudaGraphInstantiate"); }
-                b->gparity = par;
-            }
-            if (par == b->gparity) {
-                LBM_CUDA(cudaGraphLaunch(b->gexec, b->stream));
-                left -= kGraphChunk;
-                continue;
-            }
-        }
-        LBM_CUDA(enqueue_batch_step(b, par, b->stream));
-        par ^= 1;
-        left -= 1;
+    if (left > 0) {
+        // runs of steps replay graphs of 64, 32, ..., 2 batched steps
+        const lbm_status rc = run_chunks(b->graph, 0, b->stream, b->cap_stream, left, par,
+                                         [&](int p, cudaStream_t s) { return enqueue_batch_step(b, p, s); });
+        if (rc != LBM_OK) return rc;
     }
     for (lbm_handle *h : b->hs) {
         h->parity = par;
@@ -2792,7 +2740,7 @@ void lbm_batch_destroy(lbm_batch *b)
 {
     if (!b) return;
     cudaStreamSynchronize(b->stream);
-    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->graph.reset();
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     batch_release_block(b);
     batch_free(b, b->bar);

@@ -246,6 +246,98 @@ __device__ __forceinline__ void crack_apply(const CrackParams &p, uint32_t *cut_
     crack_commit(p, cut_v, hist, S, dir, commit, c, crack_decide(p, S, dir, c));
 }
 
+// Prescribed growth whose K fit the step kernel's record CTA forms
+// (crack_record_prescribed): the decision of Alg. 1 needs no K -- the speed
+// is given, so eq. r(v) and the advance use it -- and this end advances at
+// once, by one thread: the severed links, this end's fields of S but K, r_min
+// and the pair count, and, if `commit`, its history's tip and speed.
+__device__ __forceinline__ void crack_advance_prescribed(const CrackParams &p, uint32_t *cut_v, const History &hist,
+                                                         CrackState &S, int dir, bool commit)
+{
+    TipState &E = dir > 0 ? S.r : S.l;
+    if (p.mode == CRACK_NONE || E.decided) {
+        E.decided = 1;
+        return;
+    }
+    CrackDecision d;
+    d.K = 0.0;
+    d.v = E.arrested ? 0.0 : p.v_rel;
+    d.dq = p.dq_prescribed;
+    d.propagate = E.arrested ? 0 : 1;
+    d.flags = E.flags;
+    const CrackSums c = {0.0, 0.0, 0.0, 0};
+    const int64_t h = p.hist_cap > 0 ? S.hist_n % p.hist_cap : 0;
+    crack_commit(p, cut_v, hist, S, dir, false, c, d);
+    if (commit && p.hist_cap > 0) {
+        if (dir > 0) {
+            hist.v[h] = d.v;
+            hist.tip[h] = E.tip_q;
+        } else {
+            hist.vl[h] = d.v;
+            hist.tipl[h] = E.tip_q;
+        }
+    }
+}
+
+// The fields of this end's decision that crack_advance_prescribed forms (all
+// of the state's end but K, r_min and the pair count).
+__device__ __forceinline__ void copy_tip_decision(TipState &o, const TipState &s)
+{
+    o.tip_q = s.tip_q;
+    o.tip_yq = s.tip_yq;
+    o.arrested = s.arrested;
+    o.grew = s.grew;
+    o.flags = s.flags;
+    o.v_prev = s.v_prev;
+    o.v = s.v;
+}
+
+// The other half of a prescribed-growth crack step, by one warp of a CTA
+// that updates no rows: the K fit of eq. sif from the state before the step
+// (S_old, as crack_step_warp reads it) and the fields the step follows -- the
+// same sums in the same order, so the same K -- written to this end's K,
+// r_min and pair count in S_out and to the history.  A non-finite K sets the
+// launch's error word.  All 32 lanes must call it.
+template <typename T>
+__device__ __forceinline__ void crack_record_prescribed(const CrackParams &p, const T *w, int64_t P,
+                                                        const uint32_t *cut_v, const History &hist,
+                                                        const CrackState &S_old, CrackState *S_out, uint32_t *err,
+                                                        int dir)
+{
+    const TipState &E = dir > 0 ? S_old.r : S_old.l;
+    TipState &O = dir > 0 ? S_out->r : S_out->l;
+    if (E.decided) {
+        // applied already (a deferred crack step before a host read): carry
+        // its K over, as the advancing CTA carries the rest of the state
+        if ((threadIdx.x & 31) == 0) {
+            O.K = E.K;
+            O.r_min = E.r_min;
+            O.npairs = E.npairs;
+        }
+        return;
+    }
+    // the window lies behind the old tip, where every link is severed
+    // already: the bits the advancing CTA sets meanwhile are not read
+    const CrackSums c = crack_eval_warp<T>(p, w, P, cut_v, S_old, dir);
+    if ((threadIdx.x & 31) == 0) {
+        const double K = c.np > 0 ? p.mu / 4.0 * c.num / c.den : 0.0;
+        O.K = K;
+        O.r_min = c.r_min;
+        O.npairs = c.np;
+        if (!isfinite(K)) atomicOr(err, (uint32_t)ERR_NONFINITE);
+        if (p.hist_cap > 0) {
+            const int64_t h = S_old.hist_n % p.hist_cap;
+            if (dir > 0) {
+                hist.K[h] = K;
+                hist.np[h] = c.np;
+            } else {
+                hist.Kl[h] = K;
+                hist.npl[h] = c.np;
+            }
+        }
+    }
+}
+
 // Both steps for one end, by one warp (lane 0 applies).
 template <typename T>
 __device__ __forceinline__ void crack_step_warp(const CrackParams &p, const T *w, int64_t P, uint32_t *cut_v,

@@ -49,6 +49,26 @@ using lbm::History;
 using lbm::LoadDesc;
 using lbm::CrackParams;
 
+namespace lbm {
+namespace host {
+
+// Replays runs of kernel launches that alternate between two parities as
+// CUDA graphs: a ladder of graphs of kChunk, kChunk / 2, ..., 2 launches, each
+// captured on first use for the starting parity it is needed at, so that a
+// run of any length (a checkpoint segment of sqrt(T) steps, say) replays as
+// at most one graph per level plus one single launch.
+struct ChunkGraph {
+    static constexpr int kLevels = 6;              // 64, 32, 16, 8, 4, 2 launches
+    cudaGraphExec_t exec[kLevels][2] = {};         // [level][starting parity]
+    int64_t gen = -1;
+    void reset();
+};
+
+constexpr int64_t kChunk = 64;   // launches of the largest graph (every size is even: parity is kept)
+
+}  // namespace host
+}  // namespace lbm
+
 struct lbm_handle {
     lbm_grid grid;
     lbm_lattice lat;
@@ -103,8 +123,7 @@ struct lbm_handle {
     bool pending;        // the crack step after the last enqueued LBM step is not applied yet
     cudaStream_t stream;
     cudaStream_t cap_stream;
-    cudaGraphExec_t gexec;
-    int gparity;
+    lbm::host::ChunkGraph steps;   // graphs of runs of time steps (lbm_step)
     lbm_status sticky;
     // CUDA-event timing (lbm_set_profiling)
     int profiling;
@@ -163,6 +182,7 @@ inline void make_step_args(const lbm_handle *h, int par, StepArgs<T, D> &a)
     a.crack_band = h->crack_band;
     a.n_bands = h->n_bands;
     a.chained = h->chained ? 1 : 0;
+    a.k_cta = 0;   // set by the single-lattice launches that add the record CTA
     for (int e = 0; e < 4; ++e) { a.edge[e] = h->grid.edge[e]; a.load[e] = h->load[e]; }
     a.g = (T)h->g;
     a.dt = (T)h->grid.dt;
@@ -177,6 +197,16 @@ inline void make_step_args(const lbm_handle *h, int par, StepArgs<T, D> &a)
     a.hist = h->hist;
 }
 
+// Whether the single-lattice step launch adds the record CTA of a
+// prescribed-growth crack step (StepArgs::k_cta): D2Q5 with a crack along +x,
+// and only when the grid leaves a resident slot free for it, so that it runs
+// alongside the first wave instead of after it.
+inline bool use_k_cta(const lbm_handle *h)
+{
+    return h->cp.mode == lbm::CRACK_PRESCRIBED && !h->line && h->q == 5 &&
+           (int64_t)(h->n_bands + 1) * h->ncb <= (int64_t)h->sms * h->bps;
+}
+
 // Batches (lbm_batch_*): enqueue one batched step reading parity `par`; the
 // common parity of the members; their state check; record n steps ending at
 // parity `par`.
@@ -185,16 +215,6 @@ int batch_parity(const lbm_batch *b);
 lbm_status batch_check(const lbm_batch *b);
 void batch_mark_stepped(lbm_batch *b, int par, int64_t n);
 
-// Replays a fixed chunk of kernel launches that alternate between two
-// parities as a CUDA graph, captured on first use for the starting parity.
-struct ChunkGraph {
-    cudaGraphExec_t exec = nullptr;
-    int parity = -1;
-    int64_t gen = -1;
-    void reset();
-};
-
-constexpr int64_t kChunk = 64;   // launches per captured graph (even: parity is kept)
 
 }  // namespace host
 }  // namespace lbm
@@ -208,44 +228,51 @@ constexpr int64_t kChunk = 64;   // launches per captured graph (even: parity is
 namespace lbm {
 namespace host {
 
-// Launch n kernels that alternate between two parities, starting at `par`;
-// whole chunks replay a graph captured for the starting parity.
+// Launch n kernels that alternate between two parities, starting at `par`:
+// the largest graph of the ladder that fits, repeatedly, then one single
+// launch for an odd remainder.
 template <typename F>
 inline lbm_status run_chunks(ChunkGraph &g, int64_t gen, cudaStream_t s, cudaStream_t cap, int64_t n, int &par, F &&enqueue)
 {
+    if (g.gen != gen) {
+        g.reset();
+        g.gen = gen;
+    }
     while (n > 0) {
-        if (n >= kChunk) {
-            if (g.exec && g.gen != gen) g.reset();
-            if (!g.exec) {
-                cudaGraph_t graph;
-                LBM_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-                cudaError_t ce = cudaSuccess;
-                int p = par;
-                for (int64_t q = 0; q < kChunk && ce == cudaSuccess; ++q) {
-                    ce = enqueue(p, cap);
-                    p ^= 1;
-                }
-                cudaError_t ee = cudaStreamEndCapture(cap, &graph);
-                if (ce != cudaSuccess) return cuda_fail(ce, "capturing a tape graph");
-                if (ee != cudaSuccess) return cuda_fail(ee, "cudaStreamEndCapture");
-                ee = cudaGraphInstantiate(&g.exec, graph, 0);
-                cudaGraphDestroy(graph);
-                if (ee != cudaSuccess) {
-                    g.exec = nullptr;
-                    return cuda_fail(ee, "cudaGraphInstantiate");
-                }
-                g.parity = par;
-                g.gen = gen;
+        int lv = 0;
+        int64_t size = kChunk;
+        while (lv < ChunkGraph::kLevels && size > n) {
+            ++lv;
+            size >>= 1;
+        }
+        if (lv == ChunkGraph::kLevels) {   // one launch left
+            LBM_CUDA(enqueue(par, s));
+            par ^= 1;
+            n -= 1;
+            continue;
+        }
+        cudaGraphExec_t &ex = g.exec[lv][par];
+        if (!ex) {
+            cudaGraph_t graph;
+            LBM_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+            cudaError_t ce = cudaSuccess;
+            int p = par;
+            for (int64_t q = 0; q < size && ce == cudaSuccess; ++q) {
+                ce = enqueue(p, cap);
+                p ^= 1;
             }
-            if (g.parity == par) {
-                LBM_CUDA(cudaGraphLaunch(g.exec, s));
-                n -= kChunk;
-                continue;
+            cudaError_t ee = cudaStreamEndCapture(cap, &graph);
+            if (ce != cudaSuccess) return cuda_fail(ce, "capturing a step graph");
+            if (ee != cudaSuccess) return cuda_fail(ee, "cudaStreamEndCapture");
+            ee = cudaGraphInstantiate(&ex, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ee != cudaSuccess) {
+                ex = nullptr;
+                return cuda_fail(ee, "cudaGraphInstantiate");
             }
         }
-        LBM_CUDA(enqueue(par, s));
-        par ^= 1;
-        n -= 1;
+        LBM_CUDA(cudaGraphLaunch(ex, s));
+        n -= size;   // an even number of launches: the parity is kept
     }
     return LBM_OK;
 }

@@ -171,6 +171,8 @@ struct StepArgs {
     int32_t crack_band;        // band that holds the crack rows (-1: none)
     int32_t n_bands;           // bands of the partition
     int32_t chained;           // host side: launch chained to the previous kernel (launch_chained)
+    int32_t k_cta;             // 1: the grid has one more band row (band n_bands) whose first CTA
+                               // forms the K record of a prescribed-growth crack step
     int32_t edge[4];
     T g, dt;
     uint32_t *cut_h;

@@ -446,11 +446,28 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
     constexpr int N = Vec<T>::N;
     const unsigned kFull = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31;
+    const CrackParams &p = a.p;
+    if (a.k_cta && band == a.n_bands) {
+        // the record CTA of a prescribed-growth crack step (band n_bands has
+        // no unit): the K fit for the history (warp 0 the right end, warp 1
+        // the left one), at the same time as the crack sub-bands advance the
+        // tip and update their rows
+        if (cb == 0) {
+            if (tid == 0) sS = *a.s_in;
+            __syncthreads();
+            if (tid < 32)
+                crack_record_prescribed<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, a.s_out, a.err, +1);
+            else if (tid < 64 && p.two_tips)
+                crack_record_prescribed<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, a.s_out, a.err, -1);
+        }
+        return;
+    }
     const Unit U = a.units[band];
     const int j0 = U.j0, j1 = U.j1;
     const int nx = a.nx;
-    const CrackParams &p = a.p;
     T acc = (T)0;
+    // prescribed growth with a record CTA: the crack sub-bands only advance
+    const bool rec_elsewhere = a.k_cta && p.mode == CRACK_PRESCRIBED;
 
     if (a.crack_band >= 0 && (band == a.crack_band || (band == a.crack_band + 1 && p.sides == 3))) {
         // The crack step of Alg. 1 that follows the previous LBM step, by the
@@ -474,7 +491,7 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
         const bool left_here = p.two_tips && cb == i_prev / cols;
         const bool commit = band == a.crack_band;
         const bool both = BOTH && right_here && left_here;
-        if ((right_here || left_here) && tid == 0) {
+        if ((right_here || left_here) && tid == 0 && !rec_elsewhere) {
             // the rows this CTA updates after the crack step, brought into L2
             // while the crack step runs (its FP64 chain is the long pole)
             const int hh = p.macro ? 3 : 1;
@@ -487,7 +504,15 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
         if ((right_here || left_here) && tid < 32) {
             __syncwarp();
             const bool pending = !sS.r.decided;   // not yet applied by a deferred crack step
-            if (both) {
+            if (rec_elsewhere) {
+                // the advance needs no K: lane 0 advances each end here (the
+                // right end first, as below), the record CTA forms K
+                if (tid == 0) {
+                    if (right_here) crack_advance_prescribed(p, a.cut_v, a.hist, sS, +1, commit);
+                    if (left_here) crack_advance_prescribed(p, a.cut_v, a.hist, sS, -1, commit);
+                }
+                __syncwarp();
+            } else if (both) {
                 // both ends in this CTA: lanes 0-15 evaluate the right end and
                 // lanes 16-31 the left end at once, on the same state (the
                 // criteria of both ends before either advances); lane 0 then
@@ -529,7 +554,8 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
                     o->hist_n = sS.hist_n + (pending ? 1 : 0);
                     o->i_last = sS.i_last;
                     if (!p.two_tips) o->i_first = sS.i_first;
-                    o->r = sS.r;
+                    if (rec_elsewhere) copy_tip_decision(o->r, sS.r);   // K, r_min, npairs: the record CTA
+                    else o->r = sS.r;
                     o->r.decided = 0;
                     // the Dirichlet values of the next step come from another
                     // CTA when there is one (see below): their FP64 sin of the
@@ -540,7 +566,8 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
                 }
                 if (left_here) {
                     o->i_first = sS.i_first;
-                    o->l = sS.l;
+                    if (rec_elsewhere) copy_tip_decision(o->l, sS.l);
+                    else o->l = sS.l;
                     o->l.decided = 0;
                 }
                 if (REC) {
@@ -876,7 +903,7 @@ template <typename T, typename D> const void *step_kernel_ptr(bool bulk)
 template <typename T, typename D>
 cudaError_t launch_step(const StepArgs<T, D> &a, int bands, cudaStream_t s, bool bulk)
 {
-    const dim3 grid((unsigned)a.ncb, (unsigned)bands);
+    const dim3 grid((unsigned)a.ncb, (unsigned)(bands + (a.k_cta ? 1 : 0)));
     const bool ch = a.chained != 0;
     if constexpr (sizeof(T) == 4) {
         if (bulk)
@@ -890,7 +917,7 @@ cudaError_t launch_step(const StepArgs<T, D> &a, int bands, cudaStream_t s, bool
 template <typename T>
 cudaError_t launch_step_rec(const StepArgs<T, T> &a, const RecArgs &r, int bands, cudaStream_t s)
 {
-    step_rec_kernel<T><<<dim3((unsigned)a.ncb, (unsigned)bands), kThreads, 0, s>>>(a, r);
+    step_rec_kernel<T><<<dim3((unsigned)a.ncb, (unsigned)(bands + (a.k_cta ? 1 : 0))), kThreads, 0, s>>>(a, r);
     return cudaGetLastError();
 }
 

@@ -127,12 +127,14 @@ lbm_status record_steps(lbm_tape *t, int64_t n, int acc_loss)
         rc = run_chunks(t->g_rec[acc_loss], h->gen, h->stream, t->cap, n, par, [&](int p, cudaStream_t s) {
             StepArgs<double, double> a;
             make_step_args(h, p, a);
+            a.k_cta = use_k_cta(h) ? 1 : 0;
             return launch_step_rec<double>(a, r, h->n_bands, s);
         });
     } else {
         rc = run_chunks(t->g_rec[acc_loss], h->gen, h->stream, t->cap, n, par, [&](int p, cudaStream_t s) {
             StepArgs<float, float> a;
             make_step_args(h, p, a);
+            a.k_cta = use_k_cta(h) ? 1 : 0;
             return launch_step_rec<float>(a, r, h->n_bands, s);
         });
     }
