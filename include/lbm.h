@@ -74,8 +74,9 @@ enum { LBM_LEFT = 0, LBM_RIGHT = 1, LBM_BOTTOM = 2, LBM_TOP = 3 };
  * crack takes the normal of the crack face that link crosses, so every
  * crack-face point has the column-local rule of the crack faces; with
  * LBM_BC_MACROSCOPIC_EDGES the outer-edge points take the edge rule of the
- * D2Q5 lattice, along the edge's normal), FP64 or FP32 storage, and not for
- * lbm_batch_*, lbm_decomp_* or lbm_tape_*.
+ * D2Q5 lattice, along the edge's normal), FP64 or FP32 storage, in batches
+ * of D2Q9 lattices and in row slabs (lbm_decomp.h: the crack rows inside one
+ * slab), and not for lbm_tape_*.
  * Its diagonal links between rows jc-1 and jc cross the crack line at
  * x = (i + 1) dh and are severed when that point lies on the closed crack
  * segment; a diagonal link leaving the body through a corner follows the
@@ -269,9 +270,10 @@ lbm_status lbm_create(const lbm_grid *grid, const lbm_lattice *lattice, const lb
 
 /* The same with a straight crack in any direction (lbm_crack_line; crack
  * must not be NULL and its mode not LBM_CRACK_NONE).  Every call below
- * applies to the handle, except lbm_set_launch (the step has a fixed
- * launch shape), lbm_batch_create, the row slabs (lbm_decomp.h) and the
- * adjoint (lbm_adjoint.h), which return LBM_ERR_ARG or LBM_ERR_STATE.  In
+ * applies to the handle (lbm_set_launch sets the march bands of its step;
+ * lbm_batch_create takes it in a batch of such lattices), except the row
+ * slabs (lbm_decomp.h) and the adjoint (lbm_adjoint.h), which return
+ * LBM_ERR_ARG or LBM_ERR_STATE.  In
  * lbm_crack_state (lbm_crack_state_left: the start of a two-tip crack),
  * tip_q and tip_x are the end's x and n_cut counts the severed links;
  * lbm_line_tip (lbm_line_tip_left) gives its y.
@@ -348,9 +350,11 @@ lbm_status lbm_sync(lbm_handle *h);
 /* Move later work to another stream (the caller orders the two streams). */
 lbm_status lbm_set_stream(lbm_handle *h, void *stream);
 
-/* Launch shape of the step kernel (D2Q5 and D2Q9).  Each CTA marches over a band of at most
- * band_rows rows of one column block; 0 picks the built-in partition (the
- * shortest bands for which every CTA of a step is resident at once).  The rows
+/* Launch shape of the step kernel (D2Q5, D2Q9 and a crack in any
+ * direction).  Each CTA marches over a band of at most band_rows rows of one
+ * column block; 0 picks the built-in partition (D2Q5 and a crack in any
+ * direction: the shortest bands for which every CTA of a step is resident at
+ * once; D2Q9: about three waves of shorter bands).  The rows
  * next to the crack line (jc-3 .. jc+2 with macroscopic crack faces, jc-1 and
  * jc otherwise) always form two bands of their own.  Synchronises the stream
  * and drops the cached step graph. */

@@ -1050,6 +1050,7 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
         const int64_t slots = (int64_t)h->sms * std::max(bps_line, 1) - 1;
         const int64_t nb = std::max<int64_t>(1, slots / h->ncb);
         cp.band = (int32_t)std::max<int64_t>(1, (grid->ny + nb - 1) / nb);
+        h->line_band0 = cp.band;
         if (macro_faces) {
             // the macroscopic rule on the crack's faces: the tabulated points
             const std::vector<LineFace> tab = line_faces_table(*line, grid->nx, grid->ny);
@@ -1572,9 +1573,16 @@ lbm_status lbm_set_launch(lbm_handle *h, int32_t band_rows)
 {
     if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
     if (band_rows < 0 || band_rows > (1 << 20)) return fail(LBM_ERR_ARG, "band_rows out of range");
-    if (h->line) return fail(LBM_ERR_STATE, "the step of a crack in any direction has a fixed launch shape");
     LBM_CUDA(cudaStreamSynchronize(h->stream));
     drop_graph(h);
+    if (h->line) {
+        // the march blocks of a crack in any direction: bands of band_rows
+        // rows (every kernel computes its grid and its blocks' rows from it)
+        h->cp.band = band_rows > 0 ? std::min(band_rows, h->grid.ny) : h->line_band0;
+        h->gen += 1;
+        clear_error();
+        return LBM_OK;
+    }
     return plan_bands(h, band_rows);
 }
 

@@ -84,6 +84,7 @@ struct lbm_handle {
     bool edge_macro;     // the macroscopic rule on the outer edges (one more kernel per step)
     int32_t q;           // velocity set: 5 or 9 (D2Q9: its own update kernel and a crack kernel per step)
     bool line;           // a straight crack in any direction (line_step_kernel)
+    int32_t line_band0;  // its built-in march band height (lbm_set_launch(h, 0))
     lbm::LineFace *faces;  // its tabulated boundary points (macroscopic faces), device
     int32_t n_faces;
     double *face_scratch;  // the one-CTA face solve's scratch (lbm::FaceScratch, kLineFaceScratch bytes per point), device

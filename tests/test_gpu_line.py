@@ -241,9 +241,6 @@ def test_calls_that_reject_the_handle(gpu):
     with pytest.raises(gpu.LbmError) as ei:
         g.crack_state_left()
     assert ei.value.status == gpu.A.LBM_ERR_STATE
-    with pytest.raises(gpu.LbmError) as ei:
-        gpu.lbm_set_launch(g.h, 8)
-    assert ei.value.status == gpu.A.LBM_ERR_STATE
     straight = gpu.Lattice(W.prescribed_strip(64, 32, 0.4), "f32")
     with pytest.raises(gpu.LbmError):
         gpu.Batch([g, straight])       # cracks along +x and in any direction apart
@@ -576,3 +573,37 @@ def test_batch_matches_the_oracle(oracle_mod, gpu):
             np.testing.assert_allclose(hg["K"], ho["K"], rtol=0, atol=1e-9 * np.abs(ho["K"]).max())
         o.close()
         g.close()
+
+
+@pytest.mark.parametrize("macro", [False, True])
+def test_band_heights_give_the_same_bits(gpu, macro):
+    """lbm_set_launch sets the march bands of the step of a crack in any
+    direction: every band height gives the same bits (a site's update does
+    not depend on which block makes it) through the growth of the crack, and
+    0 restores the built-in height."""
+    p = W.kcrit_line_centre(scale=8) if macro else W.kcrit_line(scale=8)
+    runs = []
+    band0 = None
+    for rows in (0, 1, 3, 7, 64):
+        g = gpu.Lattice(p, "f32")
+        if rows == 0:
+            band0 = gpu.lbm_get_launch(g.h)["band_rows"]
+        else:
+            gpu.lbm_set_launch(g.h, rows)
+            launch = gpu.lbm_get_launch(g.h)
+            assert launch["band_rows"] == rows
+            assert launch["ctas"] == 1 + -(-p["nx"] // 512) * -(-p["ny"] // rows)
+        g.step(1)
+        g.step(600)
+        runs.append((g.fields(), g.cut_mask("h"), g.cut_mask("v"), g.crack_state(), g.tip_q()))
+        if rows:
+            gpu.lbm_set_launch(g.h, 0)
+            assert gpu.lbm_get_launch(g.h)["band_rows"] == band0
+        g.close()
+    (f0, h0, v0, c0, t0) = runs[0]
+    for f, h, v, c, t in runs[1:]:
+        np.testing.assert_array_equal(f[0], f0[0])
+        np.testing.assert_array_equal(f[1], f0[1])
+        np.testing.assert_array_equal(h, h0)
+        np.testing.assert_array_equal(v, v0)
+        assert c == c0 and t == t0
