@@ -620,6 +620,8 @@ def profile_problem(args, W):
         return W.kcrit_line_centre()
     if args.workload == "sec52":
         return W.kcrit_centre_crack()
+    if args.workload == "adjoint_fwd":
+        return W.adjoint_problem()["problem"]
     raise ValueError(args.workload)
 
 
@@ -828,10 +830,11 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=None, help="steps of the adjoint workload (default 8000)")
     ap.add_argument("--profile-only", action="store_true",
                     help="only prelude, warm-up and timed steps of --workload (for ncu); prints kernel times")
-    ap.add_argument("--workload", default="large", choices=["large", "kcrit", "d2q9", "line", "line_macro", "sec52"],
+    ap.add_argument("--workload", default="large", choices=["large", "kcrit", "d2q9", "line", "line_macro", "sec52", "adjoint_fwd"],
                     help="with --profile-only: large = the headline lattice at --size (16384: the headline "
                          "itself), kcrit = 4096x2048 K-criterion, d2q9 / line / line_macro = its D2Q9 and "
-                         "20-degree forms, sec52 = the Sec. 5.2 example")
+                         "20-degree forms, sec52 = the Sec. 5.2 example, adjoint_fwd = the 1024 x 1024 prescribed-growth "
+                         "forward of the adjoint configuration")
     ap.add_argument("--size", type=int, default=16384, help="with --workload large: the lattice's side")
     ap.add_argument("--storage", default="f32", choices=["f32", "f32_lf", "f32_bf16", "f32_f16", "f64"],
                     help="with --profile-only: the storage form")
