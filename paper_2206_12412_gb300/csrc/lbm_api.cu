@@ -1097,6 +1097,7 @@ lbm_status create_impl(const lbm_grid *grid, const lbm_lattice *lattice, const l
     // ((v c_s) dt / dh) 2^32, rounded to nearest (even): the crack step's own
     // expression for the advance, formed once
     cp.dq_prescribed = cr.mode == LBM_CRACK_PRESCRIBED ? llrint(cr.v_rel * cs * grid->dt / grid->dh * 4294967296.0) : 0;
+    cp.dq_max = cr.mode == LBM_CRACK_KCRIT ? llrint(cr.v_max * cs * grid->dt / grid->dh * 4294967296.0) + 1 : 0;
 
     h->wd_scale = lattice->storage == LBM_F32_WD_F16 ? fp16_wd_scale(grid, loads, n_loads) : 1.0;
 

@@ -338,6 +338,64 @@ __device__ __forceinline__ void crack_record_prescribed(const CrackParams &p, co
     }
 }
 
+// Whether the pending crack step of S can sever a link: an end that still
+// grows (not decided, not arrested) reaches the centre of the next link it
+// would sever if it advanced by p.dq_max, more than any step of the
+// K-criterion advances.  When it cannot, the rows next to the crack do not
+// depend on the step's decision (only its state and history do).
+__device__ __forceinline__ bool crack_cut_in_reach(const CrackParams &p, const CrackState &S)
+{
+    const int64_t half = (int64_t)1 << (kQBits - 1);
+    bool reach = false;
+    if (!S.r.decided && !S.r.arrested) {
+        // the first column a right-end advance can sever
+        const int64_t i = max((int64_t)S.i_last + 1, (int64_t)S.i_first);
+        if (i <= p.nx - 1) reach |= ((2 * i + 1) * half) <= S.r.tip_q + p.dq_max;
+    }
+    if (p.two_tips && !S.l.decided && !S.l.arrested) {
+        // the first column a left-end advance can sever
+        const int64_t i = min((int64_t)S.i_first - 1, (int64_t)S.i_last);
+        if (i >= 0) reach |= ((2 * i + 1) * half) >= S.l.tip_q - p.dq_max;
+    }
+    return reach;
+}
+
+// The crack step of both ends of a two-tip crack by one warp: lanes 0-15
+// evaluate the right end and lanes 16-31 the left end at once, on the same
+// state (the criteria of both ends before either advances); lane 0 then
+// advances the right end and the left end in turn.
+template <typename T>
+__device__ __forceinline__ void crack_step_both(const CrackParams &p, const T *w, int64_t P, uint32_t *cut_v,
+                                                const History &hist, CrackState &S, bool commit)
+{
+    const int lane = threadIdx.x & 31;
+    const bool act_r = p.mode != CRACK_NONE && !S.r.decided;
+    const bool act_l = p.mode != CRACK_NONE && !S.l.decided;
+    const CrackSums c = crack_eval_warp<T, 16>(p, w, P, cut_v, S, lane < 16 ? +1 : -1);
+    // each end's criterion (the FP64 part) in its half warp's first lane at
+    // once: lane 0 the right end, lane 16 the left end
+    CrackDecision dd = {};
+    if ((lane & 15) == 0) dd = crack_decide(p, S, lane < 16 ? +1 : -1, c);
+    CrackSums cl;
+    cl.num = __shfl_sync(0xffffffffu, c.num, 16);
+    cl.den = __shfl_sync(0xffffffffu, c.den, 16);
+    cl.r_min = __shfl_sync(0xffffffffu, c.r_min, 16);
+    cl.np = __shfl_sync(0xffffffffu, c.np, 16);
+    CrackDecision dl;
+    dl.K = __shfl_sync(0xffffffffu, dd.K, 16);
+    dl.v = __shfl_sync(0xffffffffu, dd.v, 16);
+    dl.dq = __shfl_sync(0xffffffffu, dd.dq, 16);
+    dl.propagate = __shfl_sync(0xffffffffu, dd.propagate, 16);
+    dl.flags = __shfl_sync(0xffffffffu, dd.flags, 16);
+    if (lane == 0) {
+        if (act_r) crack_commit(p, cut_v, hist, S, +1, commit, c, dd);
+        if (act_l) crack_commit(p, cut_v, hist, S, -1, commit, cl, dl);
+        S.r.decided = 1;
+        S.l.decided = 1;
+    }
+    __syncwarp();
+}
+
 // Both steps for one end, by one warp (lane 0 applies).
 template <typename T>
 __device__ __forceinline__ void crack_step_warp(const CrackParams &p, const T *w, int64_t P, uint32_t *cut_v,

@@ -198,13 +198,15 @@ inline void make_step_args(const lbm_handle *h, int par, StepArgs<T, D> &a)
     a.hist = h->hist;
 }
 
-// Whether the single-lattice step launch adds the record CTA of a
-// prescribed-growth crack step (StepArgs::k_cta): D2Q5 with a crack along +x,
-// and only when the grid leaves a resident slot free for it, so that it runs
-// alongside the first wave instead of after it.
+// Whether the single-lattice step launch adds the record CTA (StepArgs::k_cta)
+// that runs the part of a crack step the rows next to the crack do not wait
+// for: the K fit of prescribed growth, or the whole step of K-criterion
+// growth that cannot sever a link in it.  D2Q5 with a crack along +x, and only
+// when the grid leaves a resident slot free for it, so that it runs alongside
+// the first wave instead of after it.
 inline bool use_k_cta(const lbm_handle *h)
 {
-    return h->cp.mode == lbm::CRACK_PRESCRIBED && !h->line && h->q == 5 &&
+    return (h->cp.mode == lbm::CRACK_PRESCRIBED || h->cp.mode == lbm::CRACK_KCRIT) && !h->line && h->q == 5 &&
            (int64_t)(h->n_bands + 1) * h->ncb <= (int64_t)h->sms * h->bps;
 }
 

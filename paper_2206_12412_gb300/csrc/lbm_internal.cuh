@@ -140,6 +140,9 @@ struct CrackParams {
     // prescribed growth: the advance v_rel c_s dt on the 2^-32 dh grid,
     // formed on the host as the crack step would form it
     int64_t dq_prescribed;
+    // K-criterion growth: one unit more than the largest advance of a step,
+    // v_max c_s dt on the same grid (v of eq. v-tanh never exceeds v_max)
+    int64_t dq_max;
 };
 
 // Per-step records of the right end and (two-tip cracks) the left end; a
@@ -171,8 +174,10 @@ struct StepArgs {
     int32_t crack_band;        // band that holds the crack rows (-1: none)
     int32_t n_bands;           // bands of the partition
     int32_t chained;           // host side: launch chained to the previous kernel (launch_chained)
-    int32_t k_cta;             // 1: the grid has one more band row (band n_bands) whose first CTA
-                               // forms the K record of a prescribed-growth crack step
+    int32_t k_cta;             // 1: the grid has one more band row (band n_bands) whose first CTA,
+                               // the record CTA, runs the part of the crack step that the rows next
+                               // to the crack do not wait for (prescribed growth: the K fit;
+                               // K-criterion growth out of reach of a new cut: the whole step)
     int32_t edge[4];
     T g, dt;
     uint32_t *cut_h;

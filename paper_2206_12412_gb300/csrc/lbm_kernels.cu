@@ -455,10 +455,48 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
         if (cb == 0) {
             if (tid == 0) sS = *a.s_in;
             __syncthreads();
-            if (tid < 32)
-                crack_record_prescribed<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, a.s_out, a.err, +1);
-            else if (tid < 64 && p.two_tips)
-                crack_record_prescribed<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, a.s_out, a.err, -1);
+            if (p.mode == CRACK_PRESCRIBED) {
+                if (tid < 32)
+                    crack_record_prescribed<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, a.s_out, a.err, +1);
+                else if (tid < 64 && p.two_tips)
+                    crack_record_prescribed<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, a.s_out, a.err, -1);
+            } else if (p.mode == CRACK_KCRIT && !REC && !crack_cut_in_reach(p, sS)) {
+                // K-criterion growth that cannot sever a link in this step:
+                // the whole crack step here, by the warps the crack sub-band
+                // CTAs would run it with (the same sums in the same order),
+                // while those CTAs update their rows
+                constexpr int cols = TH * Vec<T>::N;
+                int i_next = max(sS.i_last + 1, sS.i_first);
+                i_next = min(max(i_next, 0), a.nx - 1);
+                int i_prev = min(sS.i_first - 1, sS.i_last);
+                i_prev = min(max(i_prev, 0), a.nx - 1);
+                const bool pending = !sS.r.decided;
+                if (BOTH && p.two_tips && i_next / cols == i_prev / cols) {
+                    if (tid < 32) crack_step_both<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, true);
+                } else if (tid < 32) {
+                    crack_step_warp<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, +1, true);
+                } else if (tid < 64 && p.two_tips) {
+                    crack_step_warp<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, -1, true);
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    CrackState *o = a.s_out;
+                    const int64_t n = sS.step + 1;
+                    o->step = n;
+                    o->hist_n = sS.hist_n + (pending ? 1 : 0);
+                    o->i_last = sS.i_last;
+                    o->i_first = sS.i_first;
+                    o->r = sS.r;
+                    o->r.decided = 0;
+                    if (p.two_tips) {
+                        o->l = sS.l;
+                        o->l.decided = 0;
+                    }
+                    if (a.n_bands <= 2)
+                        for (int e = 0; e < 4; ++e)
+                            o->wstar[e] = a.edge[e] == EDGE_DIRICHLET ? load_value(a.load[e], n, (double)p.dt) : 0.0;
+                }
+            }
         }
         return;
     }
@@ -501,7 +539,15 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
             for (int q = 0; q < hh; ++q)
                 bulk_prefetch_l2(a.wd + (int64_t)(j0 + q) * a.pitch + xb, (uint32_t)(TH * N * sizeof(D)));
         }
-        if ((right_here || left_here) && tid < 32) {
+        // K-criterion growth that cannot sever a link in this step: the
+        // record CTA runs the whole crack step; this CTA's rows need no
+        // decision (sS keeps the severed columns of s_in: no fresh cut)
+        bool kc_elsewhere = false;
+        if ((right_here || left_here) && tid < 32 && a.k_cta && p.mode == CRACK_KCRIT && !REC) {
+            __syncwarp();
+            kc_elsewhere = !crack_cut_in_reach(p, sS);
+        }
+        if ((right_here || left_here) && tid < 32 && !kc_elsewhere) {
             __syncwarp();
             const bool pending = !sS.r.decided;   // not yet applied by a deferred crack step
             if (rec_elsewhere) {
@@ -513,35 +559,9 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
                 }
                 __syncwarp();
             } else if (both) {
-                // both ends in this CTA: lanes 0-15 evaluate the right end and
-                // lanes 16-31 the left end at once, on the same state (the
-                // criteria of both ends before either advances); lane 0 then
-                // advances the right end and the left end in turn
-                const bool act_r = p.mode != CRACK_NONE && !sS.r.decided;
-                const bool act_l = p.mode != CRACK_NONE && !sS.l.decided;
-                const CrackSums c = crack_eval_warp<T, 16>(p, a.w_in, a.pitch, a.cut_v, sS, tid < 16 ? +1 : -1);
-                // each end's criterion (the FP64 part) in its half warp's first
-                // lane at once: lane 0 the right end, lane 16 the left end
-                CrackDecision dd = {};
-                if ((tid & 15) == 0) dd = crack_decide(p, sS, tid < 16 ? +1 : -1, c);
-                CrackSums cl;
-                cl.num = __shfl_sync(0xffffffffu, c.num, 16);
-                cl.den = __shfl_sync(0xffffffffu, c.den, 16);
-                cl.r_min = __shfl_sync(0xffffffffu, c.r_min, 16);
-                cl.np = __shfl_sync(0xffffffffu, c.np, 16);
-                CrackDecision dl;
-                dl.K = __shfl_sync(0xffffffffu, dd.K, 16);
-                dl.v = __shfl_sync(0xffffffffu, dd.v, 16);
-                dl.dq = __shfl_sync(0xffffffffu, dd.dq, 16);
-                dl.propagate = __shfl_sync(0xffffffffu, dd.propagate, 16);
-                dl.flags = __shfl_sync(0xffffffffu, dd.flags, 16);
-                if (tid == 0) {
-                    if (act_r) crack_commit(p, a.cut_v, a.hist, sS, +1, commit, c, dd);
-                    if (act_l) crack_commit(p, a.cut_v, a.hist, sS, -1, commit, cl, dl);
-                    sS.r.decided = 1;
-                    sS.l.decided = 1;
-                }
-                __syncwarp();
+                // both ends in this CTA: their criteria at once, then the
+                // right end's advance and the left end's
+                crack_step_both<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, commit);
             } else {
                 if (right_here) crack_step_warp<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, +1, commit);
                 if (left_here) crack_step_warp<T>(p, a.w_in, a.pitch, a.cut_v, a.hist, sS, -1, commit);

@@ -1,12 +1,16 @@
-"""Prescribed crack growth with the K fit in a CTA of its own: with a given
-speed the decision of Alg. 1 needs no K, so the step kernel advances the tip
-in the crack sub-band CTAs at once and forms the K of the history (eq. sif)
-in one more CTA, beside the rows.  The batched kernel keeps the crack step
-whole (K fit, then decision, in the sub-band CTA), so a batch of one lattice
-is the reference: every field, mask, state and history entry -- K, pair
-counts and r_min included -- must be bit-identical, also when host reads
-apply the deferred crack step between launches, for one and two growing
-ends, FP64 and FP32, and in the adjoint's recording steps."""
+"""The record CTA of the step kernel: a CTA of its own that runs the crack
+step of Alg. 1 beside the rows when the rows next to the crack do not need
+its decision.  With a prescribed speed the decision needs no K, so the crack
+sub-band CTAs advance the tip at once and the record CTA forms the K of the
+history (eq. sif).  With the K-criterion, a step whose tip cannot reach the
+next link to sever even at v_max leaves those rows unchanged whatever K is,
+so the record CTA runs the whole step (K fit, eq. v-tanh, advance) while the
+rows are updated; otherwise the sub-band CTAs run it first, as before.  The
+batched kernel always runs the whole step in the sub-band CTA, so a batch of
+one lattice is the reference: every field, mask, state and history entry --
+K, pair counts and r_min included -- must be bit-identical, also when host
+reads apply the deferred crack step between launches, for one and two
+growing ends, FP64 and FP32, and in the adjoint's recording steps."""
 import numpy as np
 import pytest
 
@@ -93,4 +97,38 @@ def test_record_cta_in_the_adjoint_recording(gpu, storage, kind):
     tape.close()
     ref.close()
     lat.close()
+    ref_lat.close()
+
+
+def _kcrit_problems():
+    a = W.kcrit_single(scale=8)                 # 512 x 256, one end, macroscopic faces
+    b = W.kcrit_centre_crack(scale=2)           # Sec. 5.2 at half size: two ends, the rule on every boundary
+    c = W.kcrit_single(scale=8, bc_mode="bounceback")
+    return {"kcrit_single": (a, 900), "sec52_half": (b, W.KCRIT_CENTRE_STEPS // 2), "kcrit_bb": (c, 900)}
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("kind", ["kcrit_single", "sec52_half", "kcrit_bb"])
+def test_kcrit_steps_out_of_reach_give_the_bits_of_the_whole_crack_step(gpu, storage, kind):
+    p, n = _kcrit_problems()[kind]
+    p = dict(p, hist_cap=max(n + 16, 4096))
+    solo = gpu.Lattice(p, storage)
+    ref_lat = gpu.Lattice(p, storage)
+    ref = gpu.Batch([ref_lat])
+    solo.step(1)
+    ref.step(1)
+    solo.step(n - 40)
+    ref.step(n - 40)
+    for _ in range(5):       # host reads between single steps
+        solo.step(1)
+        solo.crack_state()
+        ref.step(1)
+    solo.step(34)
+    ref.step(34)
+    two = p["crack"].get("two_tips", False)
+    h = solo.history(cap=n)
+    assert (h["v"] > 0).sum() > 3, "the crack should grow in this run"
+    _same(solo, ref_lat, two_tips=two)
+    ref.close()
+    solo.close()
     ref_lat.close()
