@@ -448,10 +448,11 @@ __device__ __forceinline__ void step_cta(const StepArgs<T, D> &a, int cb, int ba
     const int tid = threadIdx.x, lane = tid & 31;
     const CrackParams &p = a.p;
     if (a.k_cta && band == a.n_bands) {
-        // the record CTA of a prescribed-growth crack step (band n_bands has
-        // no unit): the K fit for the history (warp 0 the right end, warp 1
-        // the left one), at the same time as the crack sub-bands advance the
-        // tip and update their rows
+        // the record CTA (band n_bands has no unit), at the same time as the
+        // crack sub-bands update their rows: for prescribed growth the K fit
+        // for the history (warp 0 the right end, warp 1 the left one) while
+        // the sub-bands advance the tip; for K-criterion growth that cannot
+        // sever a link in this step the whole crack step
         if (cb == 0) {
             if (tid == 0) sS = *a.s_in;
             __syncthreads();
