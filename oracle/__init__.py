@@ -148,6 +148,8 @@ def _load():
         lib.orc_finish_step.argtypes = [P]
         lib.orc_fs_row.argtypes = [P, C.c_int32, d]
         lib.orc_set_halo.argtypes = [P, C.c_int32, d]
+        lib.orc_halo_width.argtypes = [P]
+        lib.orc_halo_width.restype = C.c_int32
         lib.orc_set_threads.argtypes = [P, C.c_int32]
         lib.orc_set_threads.restype = C.c_int32
         lib.orc_g.argtypes = [P]
@@ -266,15 +268,17 @@ class Oracle:
         self.lib.orc_collide(self.h)
 
     def fs_row(self, side: int) -> np.ndarray:
-        """Post-collision values leaving across the bottom (side 0) or top (1) edge."""
-        out = np.empty(self.nx)
+        """Post-collision values leaving across the bottom (side 0) or top (1)
+        edge: halo_width() rows of nx (D2Q5: the y direction; D2Q9: it and
+        the two diagonals)."""
+        out = np.empty(self.nx * self.lib.orc_halo_width(self.h))
         self.lib.orc_fs_row(self.h, int(side), _dptr(out))
         return out
 
     def set_halo(self, side: int, row):
         """The neighbour's values arriving across the bottom (side 0) or top (1) edge."""
         r = np.ascontiguousarray(row, dtype=np.float64)
-        assert r.size == self.nx
+        assert r.size == self.nx * self.lib.orc_halo_width(self.h)
         self.lib.orc_set_halo(self.h, int(side), _dptr(r))
 
     def finish_step(self):

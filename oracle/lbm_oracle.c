@@ -79,10 +79,11 @@
 #define ORC_Q 32 /* fixed point: 1 dh = 2^32 units */
 #define ORC_PI 3.14159265358979323846
 
-/* ORC_HALO: a bottom or top edge inside a lattice split into row slabs; the
- * distribution that crosses it into the slab is the neighbouring slab's
- * post-collision value, handed over between the collision and the streaming
- * (orc_collide / orc_fs_row / orc_set_halo / orc_finish_step). */
+/* ORC_HALO: a bottom or top edge inside a lattice split into row slabs; each
+ * distribution that crosses it into the slab (D2Q5: the one along y; D2Q9:
+ * that one and the two diagonals) is the neighbouring slab's post-collision
+ * value at the link's source site, handed over between the collision and the
+ * streaming (orc_collide / orc_fs_row / orc_set_halo / orc_finish_step). */
 enum { ORC_FREE = 0, ORC_DIRICHLET = 1, ORC_PERIODIC = 2, ORC_HALO = 3 };
 enum { ORC_LEFT = 0, ORC_RIGHT = 1, ORC_BOTTOM = 2, ORC_TOP = 3 };
 enum { ORC_BC_BOUNCEBACK = 0, ORC_BC_MACROSCOPIC = 1 };
@@ -170,7 +171,8 @@ typedef struct {
     uint8_t *inq, *visited;
     double *series[4];
     int32_t threads;     /* OpenMP threads of the per-site loops (1 unless set) */
-    double *halo[2];     /* ORC_HALO edges: f^2 arriving at row 0, f^4 arriving at row ny-1 (nx each) */
+    double *halo[2][3];  /* ORC_HALO edges: the neighbour's boundary row of f*^a for each direction a
+                            arriving at row 0 (2, then 5, 6) / at row ny-1 (4, then 7, 8), nx each */
 } orc_state;
 
 /* Lattice velocities in units of c = dh/dt: D2Q5 (Sec. 3, eq. 2) uses
@@ -338,10 +340,20 @@ static int missing_edge(const orc_state *s, int32_t k, int b)
                  ? (ni < 0 ? ORC_LEFT : ORC_RIGHT) : -1;
     int ey = (nj < 0 || nj >= ny) && s->c.edge[nj < 0 ? ORC_BOTTOM : ORC_TOP] != ORC_PERIODIC
                  ? (nj < 0 ? ORC_BOTTOM : ORC_TOP) : -1;
-    if (ex >= 0 && ey >= 0)
+    if (ex >= 0 && ey >= 0) {
+        /* across a row slab's boundary the lattice goes on: the link leaves
+         * the body through the left / right edge alone */
+        if (s->c.edge[ey] == ORC_HALO) return ex;
         return (s->c.edge[ex] == ORC_DIRICHLET && s->c.edge[ey] != ORC_DIRICHLET) ? ex : ey;
+    }
     return ex >= 0 ? ex : ey;
 }
+
+/* Row slabs: the directions that cross a slab's boundary, in the order the
+ * boundary rows are handed over: upwards (across a top edge, arriving at the
+ * next slab's row 0) 2, 5, 6; downwards 4, 7, 8 (D2Q5: 2 / 4 alone). */
+static const int HALO_UP[3] = {2, 5, 6}, HALO_DOWN[3] = {4, 7, 8};
+static int halo_slot(int a) { return (a == 2 || a == 4) ? 0 : (a == 5 || a == 7) ? 1 : 2; }
 
 /* ------------------------------------------------------------ state set-up */
 
@@ -358,7 +370,8 @@ void orc_destroy(orc_state *s)
     free(s->lbprev); free(s->hKl); free(s->hvl); free(s->htipl); free(s->htipy); free(s->htipyl); free(s->hnpl); free(s->hgrowl);
     free(s->queue); free(s->inq); free(s->visited);
     for (int e = 0; e < 4; ++e) free(s->series[e]);
-    free(s->halo[0]); free(s->halo[1]);
+    for (int e = 0; e < 2; ++e)
+        for (int d = 0; d < 3; ++d) free(s->halo[e][d]);
     free(s);
 }
 
@@ -445,18 +458,18 @@ orc_state *orc_create(const orc_config *cfg)
         double rmin = cfg->r_min_fixed > 0.0 ? cfg->r_min_fixed : cfg->r0;
         if (!(rmin > 0.5 * cfg->dh)) return NULL;
     }
-    /* halo edges (row slabs): bottom / top only, D2Q5, not with the
-     * macroscopic rule on the outer edges, nor a crack in any direction */
+    /* halo edges (row slabs): bottom / top only, not with the macroscopic
+     * rule on the outer edges, nor a crack in any direction */
     for (int e = 0; e < 4; ++e) {
         if (cfg->edge[e] != ORC_HALO) continue;
-        if ((e != ORC_BOTTOM && e != ORC_TOP) || Q != 5 || cfg->edge_macro || cfg->line) return NULL;
+        if ((e != ORC_BOTTOM && e != ORC_TOP) || cfg->edge_macro || cfg->line) return NULL;
     }
     orc_state *s = xcalloc(1, sizeof(orc_state));
     s->c = *cfg;
     s->Q = Q;
     size_t n = (size_t)cfg->nx * cfg->ny;
-    s->halo[0] = xcalloc((size_t)cfg->nx, sizeof(double));
-    s->halo[1] = xcalloc((size_t)cfg->nx, sizeof(double));
+    for (int e = 0; e < 2; ++e)
+        for (int d = 0; d < 3; ++d) s->halo[e][d] = xcalloc((size_t)cfg->nx, sizeof(double));
     s->cs = sqrt(cfg->mu / cfg->rho);
     s->g = s->cs * s->cs * cfg->dt / (cfg->dh * cfg->dh);
     for (int a = 0; a < Q; ++a) { s->f[a] = xcalloc(n, sizeof(double)); s->fs[a] = xcalloc(n, sizeof(double)); }
@@ -878,8 +891,13 @@ static void lbm_stream_rest(orc_state *s)
                     int e = missing_edge(s, k, b);
                     if (s->c.edge[e] == ORC_DIRICHLET)
                         s->f[a][k] = -s->fs[b][k] + 2.0 * weight(s, a) * g * wstar[e];
-                    else if (s->c.edge[e] == ORC_HALO)   /* from the neighbouring slab */
-                        s->f[a][k] = s->halo[e == ORC_BOTTOM ? 0 : 1][i];
+                    else if (s->c.edge[e] == ORC_HALO) {   /* from the neighbouring slab */
+                        /* its source site's column in the neighbour's boundary
+                         * row (across a periodic left / right edge, wrapped) */
+                        int si = i - CX[a];
+                        if (si < 0 || si >= nx) si = (si + nx) % nx;
+                        s->f[a][k] = s->halo[e == ORC_BOTTOM ? 0 : 1][halo_slot(a)][si];
+                    }
                     else
                         s->f[a][k] = s->fs[b][k];
                 } else {
@@ -1235,24 +1253,33 @@ static void crack_growth(orc_state *s)
 
 /* Row slabs: orc_collide runs the collision of the next step; orc_fs_row
  * copies the post-collision values that leave the slab across its bottom
- * (side 0: f*^4 of row 0) or top (side 1: f*^2 of row ny-1) edge; the
+ * (side 0: f*^4, then f*^7, f*^8 with D2Q9, of row 0) or top (side 1: f*^2,
+ * then f*^5, f*^6, of row ny-1) edge, orc_halo_width rows of nx; the
  * neighbour hands them to orc_set_halo (side 0: they arrive at row 0 as f^2,
- * side 1: at row ny-1 as f^4); orc_finish_step completes the step (streaming
+ * f^5, f^6; side 1: at row ny-1 as f^4, f^7, f^8), each read at its link's
+ * source column; orc_finish_step completes the step (streaming
  * and the rest, then the crack handling of Alg. 1).  orc_collide followed by
  * orc_finish_step is orc_step(s, 1). */
 void orc_collide(orc_state *s) { lbm_collide(s); }
 
+/* Values per column of a boundary row handed over: 1 (D2Q5) or 3 (D2Q9). */
+int32_t orc_halo_width(const orc_state *s) { return s->Q == 9 ? 3 : 1; }
+
 void orc_fs_row(const orc_state *s, int32_t side, double *out)
 {
-    int nx = s->c.nx;
+    int nx = s->c.nx, nw = s->Q == 9 ? 3 : 1;
     size_t row = side == 0 ? 0 : (size_t)(s->c.ny - 1) * nx;
-    const double *fs = s->fs[side == 0 ? 4 : 2];
-    for (int i = 0; i < nx; ++i) out[i] = fs[row + i];
+    for (int d = 0; d < nw; ++d) {
+        const double *fs = s->fs[side == 0 ? HALO_DOWN[d] : HALO_UP[d]];
+        for (int i = 0; i < nx; ++i) out[(size_t)d * nx + i] = fs[row + i];
+    }
 }
 
 void orc_set_halo(orc_state *s, int32_t side, const double *in)
 {
-    for (int i = 0; i < s->c.nx; ++i) s->halo[side == 0 ? 0 : 1][i] = in[i];
+    int nx = s->c.nx, nw = s->Q == 9 ? 3 : 1;
+    for (int d = 0; d < nw; ++d)
+        for (int i = 0; i < nx; ++i) s->halo[side == 0 ? 0 : 1][d][i] = in[(size_t)d * nx + i];
 }
 
 void orc_finish_step(orc_state *s)

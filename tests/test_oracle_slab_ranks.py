@@ -6,7 +6,10 @@ scheme needs per step -- and together reproduce the undivided oracle run bit
 for bit: fields, severed links, the crack's tip and K history.  With the
 crack rows inside one slab, K is formed there from whole site pairs (no sum
 crosses ranks).  Also a lattice periodic in y, whose wrap-around joins the
-last slab to the first."""
+last slab to the first.  On D2Q9 three values per column cross a boundary
+(the axis and both diagonals), each read at its link's source column; a
+diagonal that also leaves through a left or right edge keeps that edge's
+rule, and across periodic left / right edges the source column wraps."""
 import os
 import socket
 
@@ -33,6 +36,21 @@ def _problem(kind):
         return W.with_crack(p, mode="kcrit", y=26.0, x_tip=30.0, K_C=K_C, v_max=0.85, r0=2.0)
     if kind == "periodic":
         return W.base_problem(64, 30, edges=("free", "dirichlet", "periodic", "periodic"))
+    if kind == "kcrit_d2q9":
+        return dict(_problem("kcrit"), lattice="D2Q9")
+    if kind == "periodic_d2q9":
+        # periodic in x and y: diagonal sources wrap across the left / right
+        # edges too
+        return dict(W.base_problem(64, 30, edges=("periodic", "periodic", "periodic", "periodic")), lattice="D2Q9")
+    if kind == "loaded_d2q9":
+        # a Dirichlet left edge and a free right edge meet the slab boundary:
+        # the corner diagonals take the left / right rules
+        p = W.base_problem(48, 26, edges=("dirichlet", "free", "dirichlet", "dirichlet"))
+        p = dict(p, lattice="D2Q9")
+        p["loads"] = [{"edge": "left", "kind": "sin2", "amp": 1e-3, "t": 30.0},
+                      {"edge": "bottom", "kind": "const", "amp": -5e-4, "t": 0.0},
+                      {"edge": "top", "kind": "linear", "amp": 8e-4, "t": 40.0}]
+        return p
     raise KeyError(kind)
 
 
@@ -89,7 +107,9 @@ def _worker(rank, world, port, kind, row_start, steps, q):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("kind,row_start", [("kcrit", [0, 14, 40]), ("kcrit", [0, 31, 40]), ("periodic", [0, 13, 30])])
+@pytest.mark.parametrize("kind,row_start", [("kcrit", [0, 14, 40]), ("kcrit", [0, 31, 40]), ("periodic", [0, 13, 30]),
+                                            ("kcrit_d2q9", [0, 14, 40]), ("kcrit_d2q9", [0, 31, 40]),
+                                            ("periodic_d2q9", [0, 13, 30]), ("loaded_d2q9", [0, 9, 26])])
 def test_two_gloo_ranks_match_the_undivided_oracle(oracle_mod, kind, row_start):
     steps = 120
     ctx = mp.get_context("spawn")
@@ -112,7 +132,7 @@ def test_two_gloo_ranks_match_the_undivided_oracle(oracle_mod, kind, row_start):
     np.testing.assert_array_equal(np.concatenate([r[2] for r in res]), wd)
     _, cv = o.cuts()
     np.testing.assert_array_equal(np.concatenate([r[3] for r in res]), cv)
-    if kind == "kcrit":
+    if kind.startswith("kcrit"):
         holder = [r for r in res if r[4] is not None]
         assert len(holder) == 1
         _, _, _, _, cr, hist = holder[0]
